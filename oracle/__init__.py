@@ -1,0 +1,277 @@
+"""Plain FP64 CPU oracle of the PORTA formal-solver hot path (test infrastructure only).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package. It shares no code with the CUDA
+library: the C sources in this directory restate the paper (Stepan &
+Trujillo Bueno 2013, arXiv:1307.4217) directly, one plain loop nest in
+double precision.
+
+Parity pins: see ``tests/test_oracle_*.py``.
+"""
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB = os.path.join(_HERE, "liboracle.so")
+_SRCS = ["or_quad.c", "or_besser.c", "or_sweep.c", "or_see.c", "oracle.h", "or_common.h"]
+
+MODEL_UNPOL = 0
+MODEL_HANLE = 1
+BESSER = 0
+DELOPAR = 1
+
+
+def build(force=False):
+    """Compile liboracle.so with gcc (no fast-math, no FMA contraction)."""
+    if not force and os.path.exists(_LIB):
+        newest = max(os.path.getmtime(os.path.join(_HERE, s)) for s in _SRCS)
+        if os.path.getmtime(_LIB) >= newest:
+            return _LIB
+    subprocess.run(["sh", os.path.join(_HERE, "build.sh")], check=True)
+    return _LIB
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        _lib = ctypes.CDLL(_LIB)
+        _declare(_lib)
+    return _lib
+
+
+class _Problem(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+        ("lx", ctypes.c_double), ("ly", ctypes.c_double),
+        ("z", ctypes.c_void_p),
+        ("model", ctypes.c_int),
+        ("chi", ctypes.c_void_p), ("eps", ctypes.c_void_p), ("bpl", ctypes.c_void_p),
+        ("vel", ctypes.c_void_p), ("bx", ctypes.c_void_p), ("by", ctypes.c_void_p),
+        ("bz", ctypes.c_void_p),
+        ("zeta", ctypes.c_double), ("gbar", ctypes.c_double), ("bcrit", ctypes.c_double),
+        ("n_mu", ctypes.c_int), ("n_chi", ctypes.c_int), ("n_nu", ctypes.c_int),
+        ("x_max", ctypes.c_double),
+        ("method", ctypes.c_int),
+    ]
+
+
+_P = ctypes.c_void_p
+_D = ctypes.c_double
+_I = ctypes.c_int
+
+
+def _declare(L):
+    sig = {
+        "or_gauss_legendre01": (_I, [_I, _P, _P]),
+        "or_rays": (_I, [_P, _P, _P, _P]),
+        "or_freqs": (_I, [_I, _D, _P, _P]),
+        "or_tkq": (None, [_D, _D, _P]),
+        "or_coeffs": (None, [_D, _P]),
+        "or_control_point": (_D, [_D, _D, _D, _D, _D, _I, _I]),
+        "or_solve_1d": (_I, [_I, _P, _P, _D, _I, _P]),
+        "or_step": (_I, [_I, _P, _P, _P, _P, _P, _D, _P, _D, _D, _I, _I, _P, _P]),
+        "or_hanle_solve": (_I, [_D, _D, _D, _D, _P, _P]),
+        "or_see_update": (_I, [_P, _P, _P, _P, _P]),
+        "or_sweep_ray": (_I, [_P, _P, _I, _I, _P, _P]),
+        "or_formal_solve": (_I, [_P, _P, _P, _P]),
+        "or_formal_solve_part": (_I, [_P, _P, _I, _I, _I, _I, _P, _P]),
+        "or_emergent": (_I, [_P, _P, _I, _P, _P, _P]),
+        "or_flops_reset": (None, [_I]),
+        "or_flops_get": (ctypes.c_longlong, []),
+        "or_nray": (_I, [_P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _ptr(a):
+    return a.ctypes.data if a is not None else None
+
+
+def ns_of(model):
+    return 1 if model == MODEL_UNPOL else 4
+
+
+def nl_of(model):
+    return 1 if model == MODEL_UNPOL else 6
+
+
+def nj_of(model):
+    return 1 if model == MODEL_UNPOL else 6
+
+
+class Problem:
+    """Holds the arrays referenced by the C problem struct (keeps them alive).
+
+    ``atm`` is a dict with keys nx, ny, nz, lx, ly, z, chi, eps, bpl, vel and,
+    for the polarized model, bx, by, bz (per-voxel arrays in (nz, ny, nx) order),
+    plus the atomic constants zeta, gbar, bcrit.
+    """
+
+    def __init__(self, atm, model, n_mu, n_chi, n_nu, x_max=4.0, method=BESSER):
+        self.model = model
+        self.shape = (atm["nz"], atm["ny"], atm["nx"])
+        self.nvox = int(np.prod(self.shape))
+        self._keep = {}
+        for k in ("z", "chi", "eps", "bpl", "vel", "bx", "by", "bz"):
+            v = atm.get(k)
+            self._keep[k] = _f64(v).ravel() if v is not None else None
+        s = _Problem()
+        s.nx, s.ny, s.nz = atm["nx"], atm["ny"], atm["nz"]
+        s.lx, s.ly = float(atm["lx"]), float(atm["ly"])
+        for k in ("z", "chi", "eps", "bpl", "vel", "bx", "by", "bz"):
+            setattr(s, k, _ptr(self._keep[k]))
+        s.model = model
+        s.zeta = float(atm.get("zeta", 0.0))
+        s.gbar = float(atm.get("gbar", 1.0))
+        s.bcrit = float(atm.get("bcrit", 25.0))
+        s.n_mu, s.n_chi, s.n_nu = n_mu, n_chi, n_nu
+        s.x_max = float(x_max)
+        s.method = method
+        self.s = s
+        self.nray = 2 * n_mu * n_chi
+        self.n_nu = n_nu
+
+    @property
+    def ref(self):
+        return ctypes.byref(self.s)
+
+
+def gauss_legendre01(n):
+    x = np.zeros(n); w = np.zeros(n)
+    assert lib().or_gauss_legendre01(n, _ptr(x), _ptr(w)) == 0
+    return x, w
+
+
+def rays(prob):
+    n = prob.nray
+    mu, chi, w = np.zeros(n), np.zeros(n), np.zeros(n)
+    assert lib().or_rays(prob.ref, _ptr(mu), _ptr(chi), _ptr(w)) == 0
+    return mu, chi, w
+
+
+def freqs(n_nu, x_max):
+    x, w = np.zeros(n_nu), np.zeros(n_nu)
+    assert lib().or_freqs(n_nu, float(x_max), _ptr(x), _ptr(w)) == 0
+    return x, w
+
+
+def tkq(mu, chi):
+    t = np.zeros(18)
+    lib().or_tkq(float(mu), float(chi), _ptr(t))
+    return t.reshape(3, 6)
+
+
+def coeffs(tau):
+    c = np.zeros(6)
+    lib().or_coeffs(float(tau), _ptr(c))
+    return c
+
+
+def control_point(yM, yO, yP, hM, hP, has_p=True, method=BESSER):
+    return lib().or_control_point(yM, yO, yP, hM, hP, int(has_p), method)
+
+
+def solve_1d(tau, S, I0, method=BESSER):
+    tau = _f64(tau); S = _f64(S)
+    out = np.zeros_like(tau)
+    assert lib().or_solve_1d(len(tau), _ptr(tau), _ptr(S), float(I0), method, _ptr(out)) == 0
+    return out
+
+
+def step(ns, IM, etaM, epsM, etaO, epsO, etaP_I, epsP, dsM, dsP, has_p=True, method=BESSER):
+    a = [_f64(x) for x in (IM, etaM, epsM, etaO, epsO, epsP)]
+    IO = np.zeros(ns); ls = np.zeros(1)
+    rc = lib().or_step(ns, _ptr(a[0]), _ptr(a[1]), _ptr(a[2]), _ptr(a[3]), _ptr(a[4]), float(etaP_I),
+                       _ptr(a[5]), float(dsM), float(dsP), int(has_p), method, _ptr(IO), _ptr(ls))
+    assert rc == 0
+    return IO, ls[0]
+
+
+def hanle_solve(gamma, b, rhs6):
+    rhs6 = _f64(rhs6); out = np.zeros(6)
+    assert lib().or_hanle_solve(float(gamma), float(b[0]), float(b[1]), float(b[2]), _ptr(rhs6), _ptr(out)) == 0
+    return out
+
+
+def formal_solve(prob, rho, rays_range=None, freq_range=None):
+    rho = _f64(rho).ravel()
+    assert rho.size == prob.nvox * nl_of(prob.model)
+    jkq = np.zeros(prob.nvox * nj_of(prob.model)); ls = np.zeros(prob.nvox)
+    m0, m1 = rays_range if rays_range else (0, prob.nray)
+    j0, j1 = freq_range if freq_range else (0, prob.n_nu)
+    rc = lib().or_formal_solve_part(prob.ref, _ptr(rho), m0, m1, j0, j1, _ptr(jkq), _ptr(ls))
+    assert rc == 0, rc
+    return jkq.reshape(prob.shape + (nj_of(prob.model),)), ls.reshape(prob.shape)
+
+
+def sweep_ray(prob, rho, m, j):
+    rho = _f64(rho).ravel()
+    ns = ns_of(prob.model)
+    I = np.zeros(prob.nvox * ns); ls = np.zeros(prob.nvox)
+    assert lib().or_sweep_ray(prob.ref, _ptr(rho), m, j, _ptr(I), _ptr(ls)) == 0
+    return I.reshape(prob.shape + (ns,)), ls.reshape(prob.shape)
+
+
+def see_update(prob, jkq, lstar, rho):
+    jkq = _f64(jkq).ravel(); lstar = _f64(lstar).ravel()
+    rho = _f64(rho).copy().ravel()
+    mc = np.zeros(1)
+    assert lib().or_see_update(prob.ref, _ptr(jkq), _ptr(lstar), _ptr(rho), _ptr(mc)) == 0
+    return rho.reshape(prob.shape + (nl_of(prob.model),)), float(mc[0])
+
+
+def emergent(prob, rho, mu, chi):
+    rho = _f64(rho).ravel()
+    mu = _f64(mu); chi = _f64(chi)
+    ns = ns_of(prob.model)
+    nz, ny, nx = prob.shape
+    out = np.zeros(len(mu) * prob.n_nu * ny * nx * ns)
+    assert lib().or_emergent(prob.ref, _ptr(rho), len(mu), _ptr(mu), _ptr(chi), _ptr(out)) == 0
+    return out.reshape(len(mu), prob.n_nu, ny, nx, ns)
+
+
+def initial_rho(prob, atm):
+    """Starting point of the iteration: S^0_0 = B, all other components 0."""
+    nl = nl_of(prob.model)
+    rho = np.zeros(prob.shape + (nl,))
+    rho[..., 0] = np.asarray(atm["bpl"]).reshape(prob.shape)
+    return rho
+
+
+def jacobi(prob, atm, rho=None, tol=1e-8, max_iter=1000):
+    """Jacobi (ALI) iteration to a maximum relative change below tol."""
+    rho = initial_rho(prob, atm) if rho is None else rho
+    hist = []
+    for _ in range(max_iter):
+        jkq, ls = formal_solve(prob, rho)
+        rho, mc = see_update(prob, jkq, ls, rho)
+        hist.append(mc)
+        if mc < tol:
+            break
+    return rho, hist
+
+
+def flops_per_update(prob, rho, m=0, j=None):
+    """Floating-point operations the oracle counts for one voxel.ray.frequency update
+    (node coefficients counted once per node, not per interpolation corner)."""
+    L = lib()
+    j = prob.n_nu // 2 if j is None else j
+    L.or_flops_reset(1)
+    formal_solve(prob, rho, rays_range=(m, m + 1), freq_range=(j, j + 1))
+    n = L.or_flops_get()
+    L.or_flops_reset(0)
+    return n / prob.nvox

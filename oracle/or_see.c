@@ -1,0 +1,111 @@
+/*
+ * Statistical equilibrium (Eq. 2) of the oracle (test infrastructure only):
+ * Jacobi (ALI) update with the diagonal of the Lambda operator (Sec. 2, Sec. 5).
+ *
+ * Unknowns per voxel are multipolar components of the line source function,
+ * S^K_Q, proportional to rho^K_Q of the upper level (lower level J = 0,
+ * unpolarized, so the line absorption is unpolarized).
+ *
+ * Two-level atom, CRD, no stimulated emission:
+ *   S^K_Q + i (1-eps) Gamma_u sum_Q' K^K_QQ'(B) S^K_Q' = (1-eps) w^(K) J^K_Q + eps B delta_K0 delta_Q0
+ * with Gamma_u = |B| / bcrit and K^K_QQ' the matrix of the angular momentum
+ * component along the field direction (theta_B, chi_B):
+ *   K_QQ = Q cos(theta_B),
+ *   K_Q,Q-1 = 1/2 sin(theta_B) e^{+i chi_B} sqrt((K+Q)(K-Q+1)),
+ *   K_Q,Q+1 = 1/2 sin(theta_B) e^{-i chi_B} sqrt((K-Q)(K+Q+1)).
+ * Jacobi step: S^0_0 is updated implicitly with Lambda-bar*,
+ *   S00 <- S00 + [(1-eps) J00 + eps B - S00] / [1 - (1-eps) Lambda-bar*],
+ * the K = 2 components explicitly from the current J^2_Q (5x5 Hanle solve).
+ */
+#include <math.h>
+#include "or_common.h"
+#include <complex.h>
+#undef I
+#define IU _Complex_I
+
+/* solve sum_Q' (delta_QQ' + i gamma K_QQ') S_Q' = rhs_Q for K = 2; rhs6 and s6 in the
+   real layout (X00, X20, Re X21, Im X21, Re X22, Im X22); entry 0 is ignored/zeroed */
+int or_hanle_solve(double gamma, double bx, double by, double bz, const double *rhs6, double *s6)
+{
+    const int K = 2;
+    double b = sqrt(bx * bx + by * by + bz * bz);
+    double ct = b > 0 ? bz / b : 1.0;
+    double st = sqrt(fmax(0.0, 1.0 - ct * ct));
+    double chib = (bx == 0.0 && by == 0.0) ? 0.0 : atan2(by, bx);
+    double complex M[5][5], r[5], x[5];
+    double complex rq[3] = {rhs6[1], rhs6[2] + IU * rhs6[3], rhs6[4] + IU * rhs6[5]};
+    for (int a = 0; a < 5; a++) {
+        int Q = a - 2;
+        /* rhs_{-Q} = (-1)^Q conj(rhs_Q) */
+        r[a] = Q >= 0 ? rq[Q] : ((Q % 2) ? -1.0 : 1.0) * conj(rq[-Q]);
+        for (int c = 0; c < 5; c++) {
+            int Qp = c - 2;
+            double complex k = 0.0;
+            if (Qp == Q) k = Q * ct;
+            else if (Qp == Q - 1) k = 0.5 * st * cexp(IU * chib) * sqrt((double)(K + Q) * (K - Q + 1));
+            else if (Qp == Q + 1) k = 0.5 * st * cexp(-IU * chib) * sqrt((double)(K - Q) * (K + Q + 1));
+            M[a][c] = (a == c ? 1.0 : 0.0) + IU * gamma * k;
+        }
+    }
+    /* complex Gaussian elimination with partial pivoting */
+    for (int c = 0; c < 5; c++) {
+        int piv = c;
+        for (int a = c + 1; a < 5; a++) if (cabs(M[a][c]) > cabs(M[piv][c])) piv = a;
+        if (cabs(M[piv][c]) == 0.0) return -1;
+        if (piv != c) {
+            for (int q = 0; q < 5; q++) { double complex t = M[c][q]; M[c][q] = M[piv][q]; M[piv][q] = t; }
+            double complex t = r[c]; r[c] = r[piv]; r[piv] = t;
+        }
+        for (int a = c + 1; a < 5; a++) {
+            double complex f = M[a][c] / M[c][c];
+            for (int q = c; q < 5; q++) M[a][q] -= f * M[c][q];
+            r[a] -= f * r[c];
+        }
+    }
+    for (int a = 4; a >= 0; a--) {
+        double complex s = r[a];
+        for (int q = a + 1; q < 5; q++) s -= M[a][q] * x[q];
+        x[a] = s / M[a][a];
+    }
+    s6[0] = 0.0;
+    s6[1] = creal(x[2]);
+    s6[2] = creal(x[3]); s6[3] = cimag(x[3]);
+    s6[4] = creal(x[4]); s6[5] = cimag(x[4]);
+    return 0;
+}
+
+int or_see_update(const or_problem *p, const double *jkq, const double *lstar, double *rho, double *max_change)
+{
+    long nv = (long)p->nx * p->ny * p->nz;
+    double mc = 0.0;
+    for (long v = 0; v < nv; v++) {
+        double e = p->eps[v], B = p->bpl[v];
+        if (p->model == OR_MODEL_UNPOL) {
+            double S = rho[v];
+            double dS = ((1.0 - e) * jkq[v] + e * B - S) / (1.0 - (1.0 - e) * lstar[v]);
+            double ch = fabs(dS) / fabs(S);
+            if (ch > mc || ch != ch) mc = ch;
+            rho[v] = S + dS;
+        } else {
+            double *s = rho + 6 * v;
+            const double *J = jkq + 6 * v;
+            double S00 = s[0];
+            double dS = ((1.0 - e) * J[0] + e * B - S00) / (1.0 - (1.0 - e) * lstar[v]);
+            double S00n = S00 + dS;
+            double rhs[6], s2[6];
+            for (int c = 0; c < 6; c++) rhs[c] = (1.0 - e) * J[c];
+            double gamma = (1.0 - e) * sqrt(p->bx[v] * p->bx[v] + p->by[v] * p->by[v] + p->bz[v] * p->bz[v]) / p->bcrit;
+            if (or_hanle_solve(gamma, p->bx[v], p->by[v], p->bz[v], rhs, s2) != 0) return -3;
+            double ch = fabs(dS) / fabs(S00);
+            if (ch > mc || ch != ch) mc = ch;
+            for (int c = 1; c < 6; c++) {
+                double d = fabs(s2[c] / S00n - s[c] / S00);
+                if (d > mc || d != d) mc = d;
+            }
+            s[0] = S00n;
+            for (int c = 1; c < 6; c++) s[c] = s2[c];
+        }
+    }
+    if (max_change) *max_change = mc;
+    return 0;
+}

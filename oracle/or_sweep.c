@@ -1,0 +1,269 @@
+/*
+ * 3D short-characteristics formal solution of the oracle (test infrastructure only).
+ *
+ * Sec. 3.1: for each ray direction the grid is swept in topological order;
+ * the upwind point M and downwind point P of the short characteristic through
+ * grid point O lie on the neighbouring horizontal planes, where the
+ * transfer coefficients (emission and absorption) and the upwind Stokes
+ * vector are interpolated bilinearly from the 4 surrounding nodes. The grid
+ * is periodic in x and y. Bottom boundary (rays with mu > 0): I = (B, 0, 0, 0);
+ * top boundary (mu < 0): I = 0; Lambda* = 0 on the boundary plane.
+ * Sec. 4.2: directions in the outer loop, frequencies in the inner loop; the
+ * line profile is renormalized per direction on the frequency quadrature.
+ * Eq. 1: J^K_Q = sum_p sum_m w_m T^K_Q(p, Omega_m) sum_j wt_j I_p(nu_j, Omega_m).
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#include "or_common.h"
+
+typedef struct {
+    double mu, chi, w;
+    double ox, oy, oz;     /* unit direction */
+    double t[18];          /* T^K_Q(i, Omega) */
+} or_ray;
+
+static void make_ray(double mu, double chi, double w, or_ray *r)
+{
+    double st = sqrt(fmax(0.0, 1.0 - mu * mu));
+    r->mu = mu; r->chi = chi; r->w = w;
+    r->ox = st * cos(chi); r->oy = st * sin(chi); r->oz = mu;
+    or_tkq(mu, chi, r->t);
+}
+
+/* node coefficients at an interpolation corner: each node's coefficients are
+   computed once per (ray, frequency) in the algorithm; the oracle recomputes
+   them per corner, which the flop count leaves out */
+static void node_coeffs(const or_problem *p, const double *rho, long v, const or_ray *r, double x,
+                        double eta[7], double eps[4]);
+static void corner_coeffs(const or_problem *p, const double *rho, long v, const or_ray *r, double x,
+                          double eta[7], double eps[4])
+{
+    int on = or_count_on;
+    or_count_on = 0;
+    node_coeffs(p, rho, v, r, x, eta, eps);
+    or_count_on = on;
+}
+
+static long vox(const or_problem *p, int i, int j, int k) { return ((long)k * p->ny + j) * p->nx + i; }
+
+/* Doppler shift (Doppler widths) of the profile seen along the ray: the
+   vertical velocity projected on Omega. */
+static double shift(const or_problem *p, long v, const or_ray *r) { return p->vel ? p->vel[v] * r->oz : 0.0; }
+
+/* Emission source vector S_i(Omega) = sum_KQ (-1)^Q T^K_Q(i,Omega) S^K_{-Q}
+   = S00 T00 + S20 T20 + 2 Re(T21 conj S21) + 2 Re(T22 conj S22)   (i = I, Q, U) */
+static double angular_source(const double *t6, const double *s)
+{
+    return t6[0] * s[0] + t6[1] * s[1] + 2.0 * (t6[2] * s[2] + t6[3] * s[3]) + 2.0 * (t6[4] * s[4] + t6[5] * s[5]);
+}
+
+/*
+ * Transfer coefficients at a grid node for ray r and reduced frequency x:
+ *   eta_I = chi exp(-(x - s)^2)    (line-centre opacity times the Gaussian profile shape)
+ * Unpolarized two-level atom: eps_I = eta_I S.
+ * Polarized two-level atom (Jl = 0 -> Ju = 1, w^(2) = 1): eps_i = eta_I S_i(Omega), i = I, Q, U;
+ * weak-field Zeeman: eta_V = -gbar zeta (B.Omega) d(eta_I)/dx = 2 gbar zeta (x - s)(B.Omega) eta_I,
+ * eps_V = S^0_0 eta_V; eta_Q = eta_U = rho_Q = rho_U = rho_V = 0.
+ */
+static void node_coeffs(const or_problem *p, const double *rho, long v, const or_ray *r, double x,
+                        double eta[7], double eps[4])
+{
+    double xs = x - shift(p, v, r);
+    double etaI = p->chi[v] * exp(-xs * xs);
+    for (int q = 0; q < 7; q++) eta[q] = 0.0;
+    eta[0] = etaI;
+    OR_FLOPS(5);
+    if (p->model == OR_MODEL_UNPOL) {
+        eps[0] = etaI * rho[v];
+        OR_FLOPS(1);
+        return;
+    }
+    const double *s = rho + 6 * v;
+    double bpar = p->bx[v] * r->ox + p->by[v] * r->oy + p->bz[v] * r->oz;
+    eta[3] = 2.0 * p->gbar * p->zeta * xs * bpar * etaI;
+    for (int i = 0; i < 3; i++) eps[i] = etaI * angular_source(r->t + 6 * i, s);
+    eps[3] = s[0] * eta[3];
+    OR_FLOPS(5 + 5 + 3 * 12 + 1);
+}
+
+/* bilinear interpolation weights on a periodic plane at cell coordinates (xc, yc) */
+static void bilinear(const or_problem *p, double xc, double yc, int ii[4], int jj[4], double w[4])
+{
+    double fx0 = floor(xc), fy0 = floor(yc);
+    double fx = xc - fx0, fy = yc - fy0;
+    long i0 = (long)fx0, j0 = (long)fy0;
+    int ia = (int)(((i0 % p->nx) + p->nx) % p->nx), ja = (int)(((j0 % p->ny) + p->ny) % p->ny);
+    int ib = (ia + 1) % p->nx, jb = (ja + 1) % p->ny;
+    ii[0] = ia; jj[0] = ja; w[0] = (1 - fx) * (1 - fy);
+    ii[1] = ib; jj[1] = ja; w[1] = fx * (1 - fy);
+    ii[2] = ia; jj[2] = jb; w[2] = (1 - fx) * fy;
+    ii[3] = ib; jj[3] = jb; w[3] = fx * fy;
+}
+
+/* one (ray, frequency) sweep; I (nvox*ns) and lstar (nvox) are outputs */
+static int sweep(const or_problem *p, const double *rho, const or_ray *r, double x, double *I, double *lstar)
+{
+    int ns = or_ns(p->model);
+    int nx = p->nx, ny = p->ny, nz = p->nz;
+    double dx = p->lx / nx, dy = p->ly / ny;
+    int up = r->mu > 0;
+    for (int ks = 0; ks < nz; ks++) {
+        int k = up ? ks : nz - 1 - ks;
+        if (ks == 0) {
+            for (int j = 0; j < ny; j++)
+                for (int i = 0; i < nx; i++) {
+                    long v = vox(p, i, j, k);
+                    for (int s = 0; s < ns; s++) I[v * ns + s] = 0.0;
+                    if (up) I[v * ns] = p->bpl[v];
+                    lstar[v] = 0.0;
+                }
+            continue;
+        }
+        int ku = up ? k - 1 : k + 1;
+        int has_p = ks + 1 < nz;
+        int kd = up ? k + 1 : k - 1;
+        double amu = fabs(r->mu);
+        double dsM = fabs(p->z[k] - p->z[ku]) / amu;
+        double dsP = has_p ? fabs(p->z[kd] - p->z[k]) / amu : 0.0;
+        for (int j = 0; j < ny; j++)
+            for (int i = 0; i < nx; i++) {
+                long v = vox(p, i, j, k);
+                int ii[4], jj[4];
+                double w[4];
+                double etaM[7] = {0}, epsM[4] = {0}, IM[4] = {0};
+                bilinear(p, i - dsM * r->ox / dx, j - dsM * r->oy / dy, ii, jj, w);
+                for (int c = 0; c < 4; c++) {
+                    long u = vox(p, ii[c], jj[c], ku);
+                    double e7[7], e4[4];
+                    corner_coeffs(p, rho, u, r, x, e7, e4);
+                    for (int q = 0; q < 7; q++) etaM[q] += w[c] * e7[q];
+                    for (int s = 0; s < ns; s++) { epsM[s] += w[c] * e4[s]; IM[s] += w[c] * I[u * ns + s]; }
+                }
+                OR_FLOPS(4 * 2 * (2 + 2 * ns));   /* eta_I, eta_V, eps, I at 4 corners */
+                double etaO[7], epsO[4];
+                node_coeffs(p, rho, v, r, x, etaO, epsO);
+                double etaP = 0.0, epsP[4] = {0};
+                if (has_p) {
+                    bilinear(p, i + dsP * r->ox / dx, j + dsP * r->oy / dy, ii, jj, w);
+                    for (int c = 0; c < 4; c++) {
+                        long u = vox(p, ii[c], jj[c], kd);
+                        double e7[7], e4[4];
+                        corner_coeffs(p, rho, u, r, x, e7, e4);
+                        etaP += w[c] * e7[0];
+                        for (int s = 0; s < ns; s++) epsP[s] += w[c] * e4[s];
+                    }
+                    OR_FLOPS(4 * 2 * (1 + ns));
+                }
+                double lo;
+                if (or_step(ns, IM, etaM, epsM, etaO, epsO, etaP, epsP, dsM, dsP, has_p, p->method,
+                            I + v * ns, &lo) != 0)
+                    return -3;
+                lstar[v] = lo;
+            }
+    }
+    return 0;
+}
+
+static int check(const or_problem *p)
+{
+    if (!p || p->nx < 1 || p->ny < 1 || p->nz < 2 || p->n_mu < 1 || p->n_chi < 1 || p->n_nu < 1) return -1;
+    if (p->model != OR_MODEL_UNPOL && p->model != OR_MODEL_HANLE) return -1;
+    if (p->model == OR_MODEL_HANLE && (!p->bx || !p->by || !p->bz)) return -1;
+    return 0;
+}
+
+int or_sweep_ray(const or_problem *p, const double *rho, int m, int j, double *I, double *lstar)
+{
+    if (check(p)) return -1;
+    int nr = or_nray(p);
+    if (m < 0 || m >= nr || j < 0 || j >= p->n_nu) return -1;
+    double *mu = malloc(sizeof(double) * nr), *ch = malloc(sizeof(double) * nr), *w = malloc(sizeof(double) * nr);
+    double *xf = malloc(sizeof(double) * p->n_nu), *wf = malloc(sizeof(double) * p->n_nu);
+    or_rays(p, mu, ch, w);
+    or_freqs(p->n_nu, p->x_max, xf, wf);
+    or_ray r;
+    make_ray(mu[m], ch[m], w[m], &r);
+    int rc = sweep(p, rho, &r, xf[j], I, lstar);
+    free(mu); free(ch); free(w); free(xf); free(wf);
+    return rc;
+}
+
+int or_formal_solve_part(const or_problem *p, const double *rho, int m0, int m1, int j0, int j1,
+                         double *jkq, double *lstar)
+{
+    if (check(p)) return -1;
+    int ns = or_ns(p->model), nj = or_nj(p->model), nr = or_nray(p), nn = p->n_nu;
+    long nv = (long)p->nx * p->ny * p->nz;
+    if (m0 < 0 || m1 > nr || m0 > m1 || j0 < 0 || j1 > nn || j0 > j1) return -1;
+    double *mu = malloc(sizeof(double) * nr), *ch = malloc(sizeof(double) * nr), *w = malloc(sizeof(double) * nr);
+    double *xf = malloc(sizeof(double) * nn), *wf = malloc(sizeof(double) * nn);
+    double *I = malloc(sizeof(double) * nv * ns), *lo = malloc(sizeof(double) * nv);
+    double *norm = malloc(sizeof(double) * nv);
+    if (!mu || !ch || !w || !xf || !wf || !I || !lo || !norm) return -2;
+    or_rays(p, mu, ch, w);
+    or_freqs(nn, p->x_max, xf, wf);
+    memset(jkq, 0, sizeof(double) * nv * nj);
+    memset(lstar, 0, sizeof(double) * nv);
+    int rc = 0;
+    for (int m = m0; m < m1 && rc == 0; m++) {                 /* directions: outer loop */
+        or_ray r;
+        make_ray(mu[m], ch[m], w[m], &r);
+        /* profile normalization on the frequency quadrature, per voxel and direction */
+        for (long v = 0; v < nv; v++) {
+            double s = shift(p, v, &r), sum = 0.0;
+            for (int j = 0; j < nn; j++) sum += wf[j] * exp(-(xf[j] - s) * (xf[j] - s)) / sqrt(M_PI);
+            norm[v] = sum;
+        }
+        for (int j = j0; j < j1 && rc == 0; j++) {             /* frequencies: inner loop */
+            rc = sweep(p, rho, &r, xf[j], I, lo);
+            for (long v = 0; v < nv; v++) {
+                double xs = xf[j] - shift(p, v, &r);
+                double wt = r.w * wf[j] * exp(-xs * xs) / sqrt(M_PI) / norm[v];
+                const double *Iv = I + v * ns;
+                if (p->model == OR_MODEL_UNPOL) {
+                    jkq[v] += wt * Iv[0];
+                    OR_FLOPS(2);
+                } else {
+                    for (int c = 0; c < 6; c++)
+                        jkq[v * 6 + c] += wt * (r.t[c] * Iv[0] + r.t[6 + c] * Iv[1] + r.t[12 + c] * Iv[2]);
+                    OR_FLOPS(6 * 7);
+                }
+                lstar[v] += wt * lo[v];
+                OR_FLOPS(2 + 7);   /* Lambda* accumulation; weight (profile and normalization) */
+            }
+        }
+    }
+    free(mu); free(ch); free(w); free(xf); free(wf); free(I); free(lo); free(norm);
+    return rc;
+}
+
+int or_formal_solve(const or_problem *p, const double *rho, double *jkq, double *lstar)
+{
+    if (check(p)) return -1;
+    return or_formal_solve_part(p, rho, 0, or_nray(p), 0, p->n_nu, jkq, lstar);
+}
+
+int or_emergent(const or_problem *p, const double *rho, int ndir, const double *mu, const double *chi, double *out)
+{
+    if (check(p)) return -1;
+    int ns = or_ns(p->model), nn = p->n_nu;
+    long nv = (long)p->nx * p->ny * p->nz, nxy = (long)p->nx * p->ny;
+    double *xf = malloc(sizeof(double) * nn), *wf = malloc(sizeof(double) * nn);
+    double *I = malloc(sizeof(double) * nv * ns), *lo = malloc(sizeof(double) * nv);
+    if (!xf || !wf || !I || !lo) return -2;
+    or_freqs(nn, p->x_max, xf, wf);
+    int rc = 0;
+    for (int d = 0; d < ndir && rc == 0; d++) {
+        if (!(mu[d] > 0.0 && mu[d] <= 1.0)) { rc = -1; break; }
+        or_ray r;
+        make_ray(mu[d], chi[d], 0.0, &r);
+        for (int j = 0; j < nn && rc == 0; j++) {
+            rc = sweep(p, rho, &r, xf[j], I, lo);
+            const double *top = I + (long)(p->nz - 1) * nxy * ns;
+            memcpy(out + ((long)d * nn + j) * nxy * ns, top, sizeof(double) * nxy * ns);
+        }
+    }
+    free(xf); free(wf); free(I); free(lo);
+    return rc;
+}

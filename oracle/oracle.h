@@ -1,0 +1,98 @@
+/*
+ * Plain FP64 CPU oracle of the PORTA formal-solver hot path
+ * (Stepan & Trujillo Bueno 2013, arXiv:1307.4217).
+ *
+ * TEST INFRASTRUCTURE ONLY. This code exists so that tests, the smoke check
+ * and the CPU-baseline leg of the benchmark can check the CUDA library against
+ * a slow, obviously correct restatement of the paper. The product path never
+ * calls it, and it shares no code, header or table with the CUDA library.
+ *
+ * Everything is double precision, single threaded, with loops in the order
+ * the paper gives (directions outer, frequencies inner, Sec. 4.2; grid planes
+ * in topological order, Sec. 3.1).
+ *
+ * Voxel index: v = (k*ny + j)*nx + i, i along x, j along y, k along z (k = 0
+ * is the bottom plane).
+ */
+#ifndef PORTA_ORACLE_H
+#define PORTA_ORACLE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { OR_MODEL_UNPOL = 0,   /* two-level atom, Stokes I only (non-LTE problem of the 1st kind) */
+       OR_MODEL_HANLE = 1 }; /* two-level atom Jl=0 -> Ju=1, rho^K_Q K=0,2, Hanle + weak-field Zeeman */
+
+enum { OR_BESSER = 0, OR_DELOPAR = 1 };
+
+typedef struct {
+    int nx, ny, nz;
+    double lx, ly;            /* horizontal periods (km); spacing lx/nx, ly/ny */
+    const double *z;          /* nz heights (km), strictly increasing */
+    int model;
+    /* per-voxel atmosphere (nvox doubles each; bx..bz may be NULL for the unpolarized model) */
+    const double *chi;        /* line-centre opacity (1/km) */
+    const double *eps;        /* collisional destruction probability */
+    const double *bpl;        /* Planck function */
+    const double *vel;        /* vertical velocity in Doppler widths */
+    const double *bx, *by, *bz; /* magnetic field (G) */
+    double zeta;              /* Zeeman splitting per gauss, Doppler widths */
+    double gbar;              /* effective Lande factor */
+    double bcrit;             /* Hanle critical field (G): Gamma_u = |B|/bcrit */
+    int n_mu, n_chi, n_nu;    /* inclinations per hemisphere, azimuths, frequencies */
+    double x_max;             /* frequency grid covers [-x_max, x_max] Doppler widths */
+    int method;               /* OR_BESSER or OR_DELOPAR */
+} or_problem;
+
+/* number of unknowns per voxel (rho), Stokes parameters, radiation-field components */
+int or_nl(int model);
+int or_ns(int model);
+int or_nj(int model);
+int or_nray(const or_problem *p);
+
+/* ---- quadratures (Sec. 4.2 and App. A: Gauss inclinations, trapezoid azimuths/frequencies) ---- */
+int or_gauss_legendre01(int n, double *x, double *w);
+int or_rays(const or_problem *p, double *mu, double *chi, double *w);
+int or_freqs(int n_nu, double x_max, double *x, double *w);
+
+/* ---- spherical tensors T^K_Q(i, Omega), K = 0, 2, i = I, Q, U (Eq. 1; LL04 Tab. 5.6, gamma = 0)
+   t[i*6 + c], c = (T00, T20, Re T21, Im T21, Re T22, Im T22) ---- */
+void or_tkq(double mu, double chi, double t[18]);
+
+/* ---- BESSER coefficients and control point (Sec. 3.2, 3.3) ---- */
+void or_coeffs(double tau, double c[6]);   /* e^-tau, psi'_M, psi'_O, omega_M, omega_O, omega_C */
+double or_control_point(double yM, double yO, double yP, double hM, double hP, int has_p, int method);
+/* one-ray unpolarized formal solution on a grid of optical depths (Sec. 3.4) */
+int or_solve_1d(int n, const double *tau, const double *S, double I0, int method, double *Iout);
+/* one 4x4 (or scalar) BESSER-DELO step (Eq. 7). eta*: 7 propagation-matrix elements
+   (eta_I, eta_Q, eta_U, eta_V, rho_Q, rho_U, rho_V); eps*: ns emissivities. */
+int or_step(int ns, const double *IM, const double *etaM, const double *epsM,
+            const double *etaO, const double *epsO, double etaP_I, const double *epsP,
+            double dsM, double dsP, int has_p, int method, double *IO, double *lstar);
+
+/* ---- SEE (Eq. 2) for the two supported atoms ---- */
+int or_hanle_solve(double gamma, double bx, double by, double bz, const double *rhs6, double *s6);
+int or_see_update(const or_problem *p, const double *jkq, const double *lstar,
+                  double *rho, double *max_change);
+
+/* ---- 3D short-characteristics formal solution ---- */
+/* one ray m, one frequency j, full grid: I (nvox*ns) and Lambda* (nvox) */
+int or_sweep_ray(const or_problem *p, const double *rho, int m, int j, double *Iout, double *lstar);
+/* all rays and frequencies: J^K_Q (nvox*nj) and Lambda-bar* (nvox) */
+int or_formal_solve(const or_problem *p, const double *rho, double *jkq, double *lstar);
+/* subset of rays [m0, m1) and frequencies [j0, j1): same outputs, partial sums */
+int or_formal_solve_part(const or_problem *p, const double *rho, int m0, int m1, int j0, int j1,
+                         double *jkq, double *lstar);
+/* emergent Stokes at the top plane for ndir outgoing directions (mu > 0): out[d][j][y][x][ns] */
+int or_emergent(const or_problem *p, const double *rho, int ndir, const double *mu,
+                const double *chi, double *out);
+
+/* flop counter for one update (counted once per voxel.ray.frequency) */
+void or_flops_reset(int enable);
+long long or_flops_get(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,125 @@
+"""Pins of the oracle's statistical-equilibrium solve (Eq. 2) for the polarized
+two-level atom (Hanle effect). The 5x5 complex spherical-tensor system is checked
+against an independent Cartesian formulation of the same physics: the alignment
+tensor A (symmetric, traceless 3x3) precesses about the field direction, so in
+statistical equilibrium A + Gamma [b, A] = R with b v = B_hat x v."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+
+
+def _sph_to_cart(s6):
+    s0, s1, s2 = s6[1], complex(s6[2], s6[3]), complex(s6[4], s6[5])
+    azz = s0 / math.sqrt(1.5)
+    axz, ayz = -s1.real, -s1.imag
+    d, axy = 2 * s2.real, s2.imag
+    axx = (-azz + d) / 2
+    ayy = (-azz - d) / 2
+    return np.array([[axx, axy, axz], [axy, ayy, ayz], [axz, ayz, azz]])
+
+
+def _cart_to_sph(A):
+    return np.array([0.0, math.sqrt(1.5) * A[2, 2], -A[0, 2], -A[1, 2], 0.5 * (A[0, 0] - A[1, 1]), A[0, 1]])
+
+
+def _cross(b):
+    return np.array([[0, -b[2], b[1]], [b[2], 0, -b[0]], [-b[1], b[0], 0]])
+
+
+def _hanle_cartesian(gamma, bvec, rhs6):
+    bh = np.asarray(bvec, float)
+    n = np.linalg.norm(bh)
+    bh = bh / n if n > 0 else np.array([0, 0, 1.0])
+    X = _cross(bh)
+    R = _sph_to_cart(rhs6)
+    # vec(A) + gamma vec(X A - A X) = vec(R)
+    I3 = np.eye(3)
+    M = np.eye(9) + gamma * (np.kron(X, I3) - np.kron(I3, X.T))
+    A = np.linalg.solve(M, R.reshape(9)).reshape(3, 3)
+    return _cart_to_sph(A)
+
+
+def test_roundtrip_maps():
+    rng = np.random.default_rng(0)
+    s = rng.normal(size=6)
+    s[0] = 0
+    assert np.allclose(_cart_to_sph(_sph_to_cart(s)), s)
+
+
+def test_hanle_matches_cartesian_precession():
+    rng = np.random.default_rng(1)
+    for _ in range(300):
+        gamma = 10 ** rng.uniform(-2, 2)
+        b = rng.normal(size=3)
+        rhs = rng.normal(size=6)
+        rhs[0] = 0
+        got = oracle.hanle_solve(gamma, b, rhs)
+        want = _hanle_cartesian(gamma, b, rhs)
+        assert np.allclose(got[1:], want[1:], rtol=1e-12, atol=1e-13)
+
+
+def test_hanle_vertical_field_closed_form():
+    rng = np.random.default_rng(2)
+    for _ in range(50):
+        gamma = 10 ** rng.uniform(-2, 2)
+        rhs = rng.normal(size=6)
+        got = oracle.hanle_solve(gamma, [0, 0, 3.0], rhs)
+        for Q, (re, im) in [(1, (2, 3)), (2, (4, 5))]:
+            want = complex(rhs[re], rhs[im]) / (1 + 1j * Q * gamma)
+            assert complex(got[re], got[im]) == pytest.approx(want, rel=1e-13)
+        assert got[1] == pytest.approx(rhs[1], rel=1e-14)
+
+
+def test_hanle_zero_field_and_saturation():
+    rng = np.random.default_rng(3)
+    rhs = rng.normal(size=6)
+    rhs[0] = 0
+    assert np.allclose(oracle.hanle_solve(0.0, [0, 0, 0], rhs)[1:], rhs[1:])
+    # strong field: only the part of the alignment symmetric about B survives (uniaxial tensor)
+    b = rng.normal(size=3)
+    s = oracle.hanle_solve(1e7, b, rhs)
+    A = _sph_to_cart(s)
+    bh = b / np.linalg.norm(b)
+    assert np.allclose(A @ bh, (bh @ A @ bh) * bh, atol=1e-6)
+    # and equals the projection of R onto the uniaxial tensors about B
+    R = _sph_to_cart(rhs)
+    P = np.outer(bh, bh) - np.eye(3) / 3
+    proj = (np.tensordot(R, P) / np.tensordot(P, P)) * P
+    assert np.allclose(A, proj, atol=1e-6)
+
+
+def test_hanle_rotational_covariance():
+    """Rotating field and radiation tensor by alpha about z multiplies S^2_Q by e^{iQ alpha}."""
+    rng = np.random.default_rng(4)
+    for _ in range(50):
+        gamma = 10 ** rng.uniform(-1, 1)
+        b = rng.normal(size=3)
+        rhs = rng.normal(size=6)
+        rhs[0] = 0
+        a = rng.uniform(0, 2 * math.pi)
+        Rz = np.array([[math.cos(a), -math.sin(a), 0], [math.sin(a), math.cos(a), 0], [0, 0, 1]])
+        rot = lambda s: np.array([0, s[1], *(lambda c: (c.real, c.imag))(complex(s[2], s[3]) * np.exp(1j * a)),
+                                  *(lambda c: (c.real, c.imag))(complex(s[4], s[5]) * np.exp(2j * a))])
+        s1 = oracle.hanle_solve(gamma, b, rhs)
+        s2 = oracle.hanle_solve(gamma, Rz @ b, rot(rhs))
+        assert np.allclose(s2[1:], rot(s1)[1:], atol=1e-12)
+
+
+def test_see_unpolarized_fixed_point():
+    """At S = (1-eps) J + eps B the Jacobi update leaves S unchanged; otherwise the
+    update solves S' = (1-eps)(J + L*(S'-S)) + eps B exactly."""
+    import synth
+    atm = synth.plane_parallel_box(2, 2, 3)
+    p = oracle.Problem(atm, 0, 2, 4, 3)
+    rng = np.random.default_rng(9)
+    J = rng.uniform(0.2, 1, size=p.shape + (1,))
+    L = rng.uniform(0, 0.99, size=p.shape)
+    S = rng.uniform(0.2, 1, size=p.shape + (1,))
+    S2, _ = oracle.see_update(p, J, L, S)
+    e = atm["eps"][..., None]
+    lhs = S2
+    rhs = (1 - e) * (J + L[..., None] * (S2 - S)) + e * atm["bpl"][..., None]
+    assert np.allclose(lhs, rhs, rtol=1e-14)
