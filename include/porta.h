@@ -1,0 +1,196 @@
+/*
+ * porta.h -- C ABI of the GB300 (sm_103a) formal-solver library for 3D
+ * non-LTE polarized radiative transfer with the short-characteristics BESSER
+ * method of Stepan & Trujillo Bueno (2013, "PORTA", arXiv:1307.4217).
+ *
+ * What the library computes (one Jacobi iteration of the non-LTE problem):
+ *   porta_formal_solve    -- Sec. 3: for every ray direction and frequency the
+ *                            grid is swept in topological order; at each point O
+ *                            the Stokes vector follows from the BESSER-DELO step
+ *                            (Eq. 7) between the upwind point M and O, with the
+ *                            transfer coefficients and I_M interpolated bilinearly
+ *                            on the neighbouring horizontal planes. The
+ *                            frequency-integrated Stokes parameters and Lambda*
+ *                            (Eq. 13) are reduced on the fly per ray.
+ *   porta_accumulate_jkq  -- Eq. 1: J^K_Q = sum_p sum_m w_m T^K_Q(p, Omega_m)
+ *                            sum_nu wt_nu I_p, and the angle- and profile-averaged
+ *                            Lambda-bar*, summed in FP64 in a fixed order.
+ *   porta_see_update      -- Eq. 2 with the Jacobi (ALI) step of Sec. 5: the
+ *                            per-voxel statistical-equilibrium solve for the
+ *                            multipolar components of the source function, in FP64,
+ *                            and the maximum relative change (Sec. 5.3, R_c).
+ *   porta_emergent_stokes -- Sec. 1: emergent Stokes profiles at the top of the
+ *                            box for arbitrary outgoing lines of sight.
+ *
+ * Atomic models (Sec. 2; physics of LL04 Ch. 10 for a two-level atom):
+ *   PORTA_MODEL_TWOLEVEL_UNPOL  unpolarized two-level atom, CRD, Stokes I only.
+ *     Unknown per voxel (NL = 1): the line source function S.
+ *     Radiation field per voxel (NJ = 1): J-bar.
+ *   PORTA_MODEL_TWOLEVEL_HANLE  two-level atom Jl = 0 -> Ju = 1, CRD, Stokes IQUV,
+ *     scattering polarization, Hanle effect and weak-field longitudinal Zeeman
+ *     effect (eta_V, eps_V). Unknowns per voxel (NL = 6): the multipolar source
+ *     function components (S^0_0, S^2_0, Re S^2_1, Im S^2_1, Re S^2_2, Im S^2_2),
+ *     proportional to rho^K_Q of the upper level. Radiation field (NJ = 6): the
+ *     same six real components of J^K_Q.
+ *
+ * Conventions
+ *   * Voxel index v = (k*ny + j)*nx + i; k = 0 is the bottom plane; the grid is
+ *     periodic in x and y (Sec. 4.2, "following the strategy of Auer et al.").
+ *   * Per-voxel arrays are nvox = nx*ny*nz doubles; rho is nvox*NL doubles with
+ *     the NL components of a voxel contiguous; J^K_Q output is nvox*NJ doubles.
+ *   * Rays: 2*n_mu*n_chi directions; ray m = ((h*n_mu) + i)*n_chi + a with h = 0
+ *     for mu > 0 (upward), h = 1 downward; Gauss-Legendre inclinations per
+ *     hemisphere, azimuths chi_a = (a + 1/2) 2 pi / n_chi, weights summing to 1.
+ *   * Frequencies: n_nu nodes uniformly spaced on [-x_max, x_max] Doppler widths,
+ *     trapezoid weights, Gaussian profile renormalized per voxel and direction
+ *     on this quadrature (Sec. 4.2).
+ *   * Boundary conditions: I = (B, 0, 0, 0) entering at the bottom, I = 0
+ *     entering at the top.
+ *   * Memory: the library owns all device memory it allocates (in porta_create
+ *     and porta_set_atmosphere) and frees it in porta_destroy. Inputs are
+ *     copied; callers keep ownership of their buffers. Arguments named `where`
+ *     say whether a caller pointer is host (PORTA_HOST) or device
+ *     (PORTA_DEVICE) memory.
+ *   * Streams: every call enqueues on the stream given to porta_set_stream
+ *     (default: the legacy default stream). Calls that return host data
+ *     synchronize that stream.
+ *   * Errors: every int-returning function returns PORTA_OK (0) or a negative
+ *     status; porta_last_error gives a message. Invalid arguments are rejected
+ *     before anything is launched. A context is not thread-safe.
+ */
+#ifndef PORTA_H
+#define PORTA_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PORTA_OK        0
+#define PORTA_EINVAL   -1   /* invalid argument (shape, pointer, value, NaN input) */
+#define PORTA_ENOMEM   -2   /* device or host allocation failed */
+#define PORTA_ECUDA    -3   /* CUDA runtime error */
+#define PORTA_ESTATE   -4   /* call order: a required input has not been set */
+#define PORTA_EKERNEL  -7   /* a kernel reported a failure (error word set) */
+
+#define PORTA_MODEL_TWOLEVEL_UNPOL 0
+#define PORTA_MODEL_TWOLEVEL_HANLE 1
+
+#define PORTA_FP64 0        /* sweeps in FP64 ("plain" form) */
+#define PORTA_FP32 1        /* sweeps in FP32; SEE, J^K_Q sums and residual in FP64 */
+
+#define PORTA_HOST   0
+#define PORTA_DEVICE 1
+
+typedef struct porta_ctx porta_ctx;
+
+/* Cartesian grid (App. A): nz heights z (host pointer, strictly increasing,
+   same length unit as lx, ly); horizontal spacing lx/nx, ly/ny. */
+typedef struct {
+    int nx, ny, nz;
+    double lx, ly;
+    const double *z;
+} porta_grid;
+
+/* Atomic model. zeta: Zeeman splitting per gauss in Doppler widths; gbar:
+   effective Lande factor; bcrit: Hanle critical field in gauss, so that the
+   upper-level Hanle parameter is Gamma_u = |B| / bcrit. */
+typedef struct {
+    int model;
+    double zeta, gbar, bcrit;
+} porta_atom;
+
+/* Quadratures: n_mu Gauss inclinations per hemisphere, n_chi azimuths,
+   n_nu frequencies on [-x_max, x_max]. */
+typedef struct {
+    int n_mu, n_chi, n_nu;
+    double x_max;
+} porta_quad;
+
+/* Options. precision: PORTA_FP64 or PORTA_FP32. cluster and nu_group select
+   the sweep decomposition (CTAs per ray cluster, frequencies per pass); 0
+   lets the library choose. */
+typedef struct {
+    int precision;
+    int cluster;
+    int nu_group;
+} porta_opts;
+
+/* Per-voxel atmosphere (nvox doubles each): chi = line-centre opacity per unit
+   length, eps = collisional destruction probability, bpl = Planck function,
+   vel = vertical velocity in Doppler widths (its projection on the ray shifts
+   the profile), bx, by, bz = magnetic field in gauss (NULL for the unpolarized
+   model). */
+typedef struct {
+    const double *chi, *eps, *bpl, *vel, *bx, *by, *bz;
+} porta_atmos;
+
+/* Create a context: validates sizes, builds the quadratures and the per-ray
+   plane geometry, allocates device buffers. Returns PORTA_EINVAL for
+   nx, ny < 1, nz < 2, non-increasing z, n_mu, n_chi, n_nu < 1, unknown model
+   or precision. *out is NULL on failure. */
+int porta_create(const porta_grid *g, const porta_atom *a, const porta_quad *q,
+                 const porta_opts *o, porta_ctx **out);
+
+/* Free all device and host memory of the context (NULL is a no-op). */
+void porta_destroy(porta_ctx *c);
+
+/* Message of the last failed call on this context (never NULL). */
+const char *porta_last_error(const porta_ctx *c);
+
+/* Stream for all subsequent work (a cudaStream_t; NULL = default stream). */
+int porta_set_stream(porta_ctx *c, void *stream);
+
+/* Sizes: rays, frequencies, voxels, unknowns per voxel (NL), radiation-field
+   components (NJ), Stokes parameters (NS). Any pointer may be NULL. */
+int porta_sizes(const porta_ctx *c, int *nray, int *nnu, long long *nvox, int *nl, int *nj, int *ns);
+
+/* Ray directions and weights of the angular quadrature (host arrays of nray). */
+int porta_rays(const porta_ctx *c, double *mu, double *chi, double *w);
+
+/* Copy the atmosphere in (Sec. 2). Rejects non-finite values, chi <= 0,
+   eps outside (0, 1], and a missing field for the Hanle model. Also
+   precomputes the per-voxel, per-ray profile normalization (Sec. 4.2). */
+int porta_set_atmosphere(porta_ctx *c, const porta_atmos *a, int where);
+
+/* Set / get the unknowns (nvox*NL doubles, FP64). porta_set_rho rejects
+   non-finite values and S^0_0 <= 0. */
+int porta_set_rho(porta_ctx *c, const double *rho, int where);
+int porta_get_rho(porta_ctx *c, double *rho, int where);
+
+/* Formal solution for all rays and frequencies with the current rho
+   (Sec. 3). Requires the atmosphere and rho (PORTA_ESTATE otherwise).
+   Enqueues only; results stay on the device until porta_accumulate_jkq. */
+int porta_formal_solve(porta_ctx *c);
+
+/* Sum the per-ray partial integrals into J^K_Q (nvox*NJ) and Lambda-bar*
+   (nvox), FP64, fixed summation order (Eq. 1). Either output pointer may be
+   NULL (result kept on the device for porta_see_update). Requires a
+   preceding porta_formal_solve. */
+int porta_accumulate_jkq(porta_ctx *c, double *jkq, double *lstar, int where);
+
+/* Jacobi (ALI) update of rho from the accumulated J^K_Q and Lambda-bar*
+   (Eq. 2; Sec. 5). max_change (host pointer, may be NULL) receives
+   max over voxels of |dS00|/|S00| and, for the Hanle model, of
+   |d(S^2_Q/S^0_0)|; passing it synchronizes the stream. */
+int porta_see_update(porta_ctx *c, double *max_change);
+
+/* Emergent Stokes vectors at the top plane for ndir outgoing directions
+   (host arrays mu in (0, 1], chi in radians). out: ndir*n_nu*ny*nx*NS doubles,
+   layout [dir][nu][y][x][stokes]. Uses the current rho. */
+int porta_emergent_stokes(porta_ctx *c, int ndir, const double *mu, const double *chi,
+                          double *out, int where);
+
+/* Diagnostic: Stokes vectors of one ray m for all frequencies at every voxel,
+   as computed inside porta_formal_solve (same kernel and launch shape).
+   out: n_nu*nvox*NS doubles, layout [nu][voxel][stokes]; lstar: n_nu*nvox
+   (may be NULL). Runs a full formal solution. */
+int porta_probe_ray(porta_ctx *c, int m, double *out, double *lstar, int where);
+
+/* Launch statistics of the last formal solution: clusters launched, CTAs per
+   cluster, frequencies per pass, dynamic shared memory per CTA (bytes). */
+int porta_launch_info(const porta_ctx *c, int *clusters, int *cluster_size, int *nu_group, int *smem_bytes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PORTA_H */

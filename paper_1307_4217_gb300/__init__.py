@@ -1,0 +1,17 @@
+"""GB300 (sm_103a) formal solver of the PORTA method (Stepan & Trujillo Bueno
+2013, arXiv:1307.4217): short-characteristics BESSER formal solution of the
+Stokes-vector transfer equation, J^K_Q / Lambda* accumulation and the Jacobi
+statistical-equilibrium update, behind the C ABI of include/porta.h.
+
+All computation runs in the CUDA library ``libporta_gb300.so``; this package
+only marshals arguments (``binding``). Importing it loads the library and
+raises if it is missing -- there is no CPU fallback.
+"""
+from .binding import (  # noqa: F401
+    PORTA_OK, PORTA_EINVAL, PORTA_ENOMEM, PORTA_ECUDA, PORTA_ESTATE, PORTA_EKERNEL,
+    PORTA_MODEL_TWOLEVEL_UNPOL, PORTA_MODEL_TWOLEVEL_HANLE, PORTA_FP64, PORTA_FP32,
+    PORTA_HOST, PORTA_DEVICE, PortaError, Context, lib, library_path,
+    porta_create, porta_destroy, porta_last_error, porta_set_stream, porta_sizes, porta_rays,
+    porta_set_atmosphere, porta_set_rho, porta_get_rho, porta_formal_solve, porta_accumulate_jkq,
+    porta_see_update, porta_emergent_stokes, porta_probe_ray, porta_launch_info,
+)

@@ -1,0 +1,312 @@
+"""ctypes binding of include/porta.h: the same entry points under the same
+names, plus a small ``Context`` convenience wrapper. Argument marshalling only.
+
+Arrays may be numpy arrays (host memory) or CUDA torch tensors (device
+memory); the ``where`` argument of the C ABI is derived from the array type.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+PORTA_OK, PORTA_EINVAL, PORTA_ENOMEM, PORTA_ECUDA, PORTA_ESTATE, PORTA_EKERNEL = 0, -1, -2, -3, -4, -7
+PORTA_MODEL_TWOLEVEL_UNPOL, PORTA_MODEL_TWOLEVEL_HANLE = 0, 1
+PORTA_FP64, PORTA_FP32 = 0, 1
+PORTA_HOST, PORTA_DEVICE = 0, 1
+
+_STATUS = {0: "PORTA_OK", -1: "PORTA_EINVAL", -2: "PORTA_ENOMEM", -3: "PORTA_ECUDA", -4: "PORTA_ESTATE",
+           -7: "PORTA_EKERNEL"}
+
+
+def library_path():
+    return _build.LIB
+
+
+class _Grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("lx", ctypes.c_double), ("ly", ctypes.c_double), ("z", ctypes.c_void_p)]
+
+
+class _Atom(ctypes.Structure):
+    _fields_ = [("model", ctypes.c_int), ("zeta", ctypes.c_double), ("gbar", ctypes.c_double),
+                ("bcrit", ctypes.c_double)]
+
+
+class _Quad(ctypes.Structure):
+    _fields_ = [("n_mu", ctypes.c_int), ("n_chi", ctypes.c_int), ("n_nu", ctypes.c_int),
+                ("x_max", ctypes.c_double)]
+
+
+class _Opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("cluster", ctypes.c_int), ("nu_group", ctypes.c_int)]
+
+
+class _Atmos(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_void_p) for k in ("chi", "eps", "bpl", "vel", "bx", "by", "bz")]
+
+
+_P, _I, _D, _LL = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_longlong
+_SIGS = {
+    "porta_create": (_I, [_P, _P, _P, _P, _P]),
+    "porta_destroy": (None, [_P]),
+    "porta_last_error": (ctypes.c_char_p, [_P]),
+    "porta_set_stream": (_I, [_P, _P]),
+    "porta_sizes": (_I, [_P, _P, _P, _P, _P, _P, _P]),
+    "porta_rays": (_I, [_P, _P, _P, _P]),
+    "porta_set_atmosphere": (_I, [_P, _P, _I]),
+    "porta_set_rho": (_I, [_P, _P, _I]),
+    "porta_get_rho": (_I, [_P, _P, _I]),
+    "porta_formal_solve": (_I, [_P]),
+    "porta_accumulate_jkq": (_I, [_P, _P, _P, _I]),
+    "porta_see_update": (_I, [_P, _P]),
+    "porta_emergent_stokes": (_I, [_P, _I, _P, _P, _P, _I]),
+    "porta_probe_ray": (_I, [_P, _I, _P, _P, _I]),
+    "porta_launch_info": (_I, [_P, _P, _P, _P, _P]),
+}
+
+_lib = None
+
+
+def lib(build_if_missing=True):
+    """Load libporta_gb300.so (building it in-tree if missing). Raises if it cannot be loaded."""
+    global _lib
+    if _lib is None:
+        path = library_path()
+        if build_if_missing and (not os.path.exists(path)):
+            _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library {path} is missing; run __graft_entry__.build()")
+        L = ctypes.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+class PortaError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _ptr_where(a):
+    """(pointer, where, keepalive) for a numpy array or a CUDA tensor."""
+    if a is None:
+        return None, PORTA_HOST, None
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float64 or not a.flags.c_contiguous:
+            a = np.ascontiguousarray(a, dtype=np.float64)
+        return a.ctypes.data, PORTA_HOST, a
+    # torch tensor
+    if getattr(a, "is_cuda", False):
+        import torch
+        if a.dtype != torch.float64 or not a.is_contiguous():
+            raise TypeError("device arrays must be contiguous float64 CUDA tensors")
+        return a.data_ptr(), PORTA_DEVICE, a
+    if a.__class__.__module__.startswith("torch"):
+        a = a.detach().cpu().numpy()
+        return _ptr_where(a)
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a.ctypes.data, PORTA_HOST, a
+
+
+# ---- thin wrappers with the C names -------------------------------------------------
+
+def porta_create(grid, atom, quad, opts):
+    h = ctypes.c_void_p()
+    rc = lib().porta_create(ctypes.byref(grid), ctypes.byref(atom), ctypes.byref(quad),
+                            ctypes.byref(opts) if opts is not None else None, ctypes.byref(h))
+    return rc, h
+
+
+def porta_destroy(h):
+    lib().porta_destroy(h)
+
+
+def porta_last_error(h):
+    return lib().porta_last_error(h).decode()
+
+
+def porta_set_stream(h, stream):
+    return lib().porta_set_stream(h, stream)
+
+
+def porta_sizes(h):
+    nray, nnu, nl, nj, ns = (ctypes.c_int() for _ in range(5))
+    nvox = ctypes.c_longlong()
+    rc = lib().porta_sizes(h, ctypes.byref(nray), ctypes.byref(nnu), ctypes.byref(nvox), ctypes.byref(nl),
+                           ctypes.byref(nj), ctypes.byref(ns))
+    return rc, dict(nray=nray.value, nnu=nnu.value, nvox=nvox.value, nl=nl.value, nj=nj.value, ns=ns.value)
+
+
+def porta_rays(h, nray):
+    mu, chi, w = np.zeros(nray), np.zeros(nray), np.zeros(nray)
+    rc = lib().porta_rays(h, mu.ctypes.data, chi.ctypes.data, w.ctypes.data)
+    return rc, (mu, chi, w)
+
+
+def porta_set_atmosphere(h, atmos, where):
+    return lib().porta_set_atmosphere(h, ctypes.byref(atmos), where)
+
+
+def porta_set_rho(h, ptr, where):
+    return lib().porta_set_rho(h, ptr, where)
+
+
+def porta_get_rho(h, ptr, where):
+    return lib().porta_get_rho(h, ptr, where)
+
+
+def porta_formal_solve(h):
+    return lib().porta_formal_solve(h)
+
+
+def porta_accumulate_jkq(h, jkq_ptr, lstar_ptr, where):
+    return lib().porta_accumulate_jkq(h, jkq_ptr, lstar_ptr, where)
+
+
+def porta_see_update(h, out=None):
+    if out is None:
+        return lib().porta_see_update(h, None)
+    return lib().porta_see_update(h, ctypes.byref(out))
+
+
+def porta_emergent_stokes(h, ndir, mu_ptr, chi_ptr, out_ptr, where):
+    return lib().porta_emergent_stokes(h, ndir, mu_ptr, chi_ptr, out_ptr, where)
+
+
+def porta_probe_ray(h, m, out_ptr, lstar_ptr, where):
+    return lib().porta_probe_ray(h, m, out_ptr, lstar_ptr, where)
+
+
+def porta_launch_info(h):
+    v = [ctypes.c_int() for _ in range(4)]
+    rc = lib().porta_launch_info(h, *[ctypes.byref(x) for x in v])
+    return rc, dict(clusters=v[0].value, cluster=v[1].value, nu_group=v[2].value, smem=v[3].value)
+
+
+# ---- convenience wrapper ------------------------------------------------------------
+
+class Context:
+    """One solver context (grid + atom + quadratures) on the current CUDA device.
+
+    ``atm`` is a dict with nx, ny, nz, lx, ly, z and the atomic constants zeta,
+    gbar, bcrit (as produced by ``synth``).
+    """
+
+    def __init__(self, atm, model, n_mu, n_chi, n_nu, x_max=4.0, precision=PORTA_FP32, cluster=0, nu_group=0):
+        self._keep = []
+        z = np.ascontiguousarray(atm["z"], dtype=np.float64)
+        self._keep.append(z)
+        g = _Grid(atm["nx"], atm["ny"], atm["nz"], float(atm["lx"]), float(atm["ly"]), z.ctypes.data)
+        a = _Atom(model, float(atm.get("zeta", 0.0)), float(atm.get("gbar", 1.0)), float(atm.get("bcrit", 25.0)))
+        q = _Quad(n_mu, n_chi, n_nu, float(x_max))
+        o = _Opts(precision, cluster, nu_group)
+        self.h = None
+        rc, h = porta_create(g, a, q, o)
+        if rc != PORTA_OK:
+            raise PortaError(rc, "porta_create failed")
+        self.h = h
+        rc, s = porta_sizes(h)
+        self.__dict__.update(s)
+        self.shape = (atm["nz"], atm["ny"], atm["nx"])
+        self.model = model
+
+    def close(self):
+        if self.h is not None:
+            porta_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc != PORTA_OK:
+            raise PortaError(rc, porta_last_error(self.h))
+
+    def set_stream(self, stream):
+        """stream: a torch.cuda.Stream, an integer handle, or None."""
+        handle = getattr(stream, "cuda_stream", stream)
+        self._check(porta_set_stream(self.h, ctypes.c_void_p(handle or 0)))
+
+    def rays(self):
+        rc, r = porta_rays(self.h, self.nray)
+        self._check(rc)
+        return r
+
+    def set_atmosphere(self, atm):
+        arrs = {}
+        where = None
+        for k in ("chi", "eps", "bpl", "vel", "bx", "by", "bz"):
+            v = atm.get(k)
+            if v is None:
+                arrs[k] = None
+                continue
+            p, w, keep = _ptr_where(v)
+            arrs[k] = p
+            self._keep.append(keep)
+            where = w if where is None else where
+            if w != where:
+                raise TypeError("atmosphere arrays must all be host or all device")
+        s = _Atmos(*[arrs[k] for k in ("chi", "eps", "bpl", "vel", "bx", "by", "bz")])
+        self._check(porta_set_atmosphere(self.h, s, where))
+
+    def set_rho(self, rho):
+        p, w, keep = _ptr_where(rho)
+        self._check(porta_set_rho(self.h, p, w))
+
+    def get_rho(self, out=None):
+        if out is None:
+            out = np.zeros(self.shape + (self.nl,))
+        p, w, keep = _ptr_where(out)
+        self._check(porta_get_rho(self.h, p, w))
+        return out if w == PORTA_DEVICE or keep is out else keep.reshape(self.shape + (self.nl,))
+
+    def formal_solve(self):
+        self._check(porta_formal_solve(self.h))
+
+    def accumulate_jkq(self, jkq=None, lstar=None, want=True):
+        if want and jkq is None:
+            jkq = np.zeros(self.shape + (self.nj,))
+            lstar = np.zeros(self.shape)
+        pj, wj, kj = _ptr_where(jkq)
+        pl, wl, kl = _ptr_where(lstar)
+        where = wj if jkq is not None else wl
+        self._check(porta_accumulate_jkq(self.h, pj, pl, where))
+        return jkq, lstar
+
+    def see_update(self, residual=True):
+        if not residual:
+            self._check(porta_see_update(self.h, None))
+            return None
+        out = ctypes.c_double()
+        self._check(porta_see_update(self.h, out))
+        return out.value
+
+    def emergent_stokes(self, mu, chi, out=None):
+        mu = np.ascontiguousarray(mu, dtype=np.float64)
+        chi = np.ascontiguousarray(chi, dtype=np.float64)
+        nz, ny, nx = self.shape
+        if out is None:
+            out = np.zeros((len(mu), self.nnu, ny, nx, self.ns))
+        p, w, keep = _ptr_where(out)
+        self._check(porta_emergent_stokes(self.h, len(mu), mu.ctypes.data, chi.ctypes.data, p, w))
+        return out
+
+    def probe_ray(self, m):
+        out = np.zeros((self.nnu,) + self.shape + (self.ns,))
+        ls = np.zeros((self.nnu,) + self.shape)
+        self._check(porta_probe_ray(self.h, m, out.ctypes.data, ls.ctypes.data, PORTA_HOST))
+        return out, ls
+
+    def launch_info(self):
+        rc, info = porta_launch_info(self.h)
+        self._check(rc)
+        return info

@@ -1,0 +1,791 @@
+// C ABI of the formal-solver library (include/porta.h): argument checks,
+// quadratures and per-ray plane geometry (host, FP64), device buffers, and the
+// launch sequence formal_solve -> accumulate_jkq -> see_update.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "porta.h"
+#include "porta_internal.cuh"
+#include "see_kernels.cuh"
+
+using namespace porta;
+
+namespace {
+
+const char *kNullCtx = "null context";
+
+int fail(porta_ctx *c, int code, const std::string &msg)
+{
+    if (c) c->err = msg;
+    return code;
+}
+
+#define CK(call)                                                                               \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess)                                                                 \
+            return fail(c, PORTA_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));   \
+    } while (0)
+
+template <typename T>
+cudaError_t dalloc(T **p, size_t n)
+{
+    *p = nullptr;
+    if (n == 0) return cudaSuccess;
+    return cudaMalloc((void **)p, n * sizeof(T));
+}
+
+// Gauss-Legendre nodes/weights on (0, 1): Newton's method on the Legendre
+// polynomial P_n evaluated by its three-term recurrence.
+void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w)
+{
+    x.assign(n, 0.0);
+    w.assign(n, 0.0);
+    for (int i = 0; i < n; ++i) {
+        double t = std::cos(M_PI * (4.0 * i + 3.0) / (4.0 * n + 2.0));
+        double dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double pm1 = 1.0, p = t;
+            for (int k = 1; k < n; ++k) {
+                double pn = ((2 * k + 1) * t * p - k * pm1) / (k + 1);
+                pm1 = p;
+                p = pn;
+            }
+            if (n == 1) { p = t; pm1 = 1.0; }
+            dp = n * (pm1 - t * p) / (1.0 - t * t);
+            double dt = p / dp;
+            t -= dt;
+            if (std::fabs(dt) < 1e-16) {
+                // one more derivative evaluation at the final node
+                pm1 = 1.0; p = t;
+                for (int k = 1; k < n; ++k) {
+                    double pn = ((2 * k + 1) * t * p - k * pm1) / (k + 1);
+                    pm1 = p;
+                    p = pn;
+                }
+                if (n == 1) { p = t; pm1 = 1.0; }
+                dp = n * (pm1 - t * p) / (1.0 - t * t);
+                break;
+            }
+        }
+        x[n - 1 - i] = 0.5 * (t + 1.0);
+        w[n - 1 - i] = 1.0 / ((1.0 - t * t) * dp * dp);   // (2/((1-t^2) P'^2)) / 2
+    }
+}
+
+// T^K_Q(i, Omega) for i = I, Q, U from the polarization tensors of the ray
+// frame: with e_a = dOmega/dtheta and e_b = z x Omega / |z x Omega|, Stokes
+// I, Q, U correspond to e_a e_a + e_b e_b, e_a e_a - e_b e_b, e_a e_b + e_b e_a;
+// T^0_0 is half the trace and T^2_Q = -sqrt(3)/2 times the spherical
+// components of the traceless part (A_0 = sqrt(3/2) A_zz, A_1 = -(A_xz + i A_yz),
+// A_2 = (A_xx - A_yy + 2 i A_xy)/2). Output rows of 6 reals per Stokes parameter.
+void tkq_tensors(double mu, double chi, double out[18])
+{
+    double st = std::sqrt(std::max(0.0, 1.0 - mu * mu));
+    double ea[3] = {mu * std::cos(chi), mu * std::sin(chi), -st};
+    double eb[3] = {-std::sin(chi), std::cos(chi), 0.0};
+    for (int i = 0; i < 3; ++i) {
+        double t[3][3];
+        for (int r = 0; r < 3; ++r)
+            for (int s = 0; s < 3; ++s) {
+                double aa = ea[r] * ea[s], bb = eb[r] * eb[s], ab = ea[r] * eb[s] + eb[r] * ea[s];
+                t[r][s] = i == 0 ? aa + bb : (i == 1 ? aa - bb : ab);
+            }
+        double tr = t[0][0] + t[1][1] + t[2][2];
+        double A[3][3];
+        for (int r = 0; r < 3; ++r)
+            for (int s = 0; s < 3; ++s) A[r][s] = t[r][s] - (r == s ? tr / 3.0 : 0.0);
+        const double k = -std::sqrt(3.0) / 2.0;
+        out[6 * i + 0] = tr / 2.0;
+        out[6 * i + 1] = k * std::sqrt(1.5) * A[2][2];
+        out[6 * i + 2] = k * (-A[0][2]);
+        out[6 * i + 3] = k * (-A[1][2]);
+        out[6 * i + 4] = k * 0.5 * (A[0][0] - A[1][1]);
+        out[6 * i + 5] = k * A[0][1];
+    }
+}
+
+long long wrapll(long long a, long long n)
+{
+    long long r = a % n;
+    return r < 0 ? r + n : r;
+}
+
+// plane geometry of one direction in sweep order (see PlaneGeom)
+template <typename Real>
+void plane_geometry(const porta_ctx *c, double mu, double chi, PlaneGeom<Real> *g)
+{
+    const bool up = mu > 0;
+    const double st = std::sqrt(std::max(0.0, 1.0 - mu * mu));
+    const double ox = st * std::cos(chi), oy = st * std::sin(chi);
+    const double hx = c->lx / c->nx, hy = c->ly / c->ny, amu = std::fabs(mu);
+    long long ax = 0, ay = 0;
+    for (int q = 0; q < c->nz; ++q) {
+        int kz = up ? q : c->nz - 1 - q;
+        PlaneGeom<Real> p{};
+        p.kz = kz;
+        if (q > 0) {
+            int ku = up ? kz - 1 : kz + 1;
+            double ds = std::fabs(c->z[kz] - c->z[ku]) / amu;
+            double dx = ds * ox / hx, dy = ds * oy / hy;
+            double cx = std::ceil(dx), cy = std::ceil(dy);
+            ax = wrapll(ax + (long long)cx, c->nx);
+            ay = wrapll(ay + (long long)cy, c->ny);
+            p.tx = (Real)(cx - dx);
+            p.ty = (Real)(cy - dy);
+            p.ds = (Real)ds;
+        }
+        p.ax = (int)ax;
+        p.ay = (int)ay;
+        g[q] = p;
+    }
+}
+
+template <typename Real>
+RayDev<Real> ray_dev(double mu, double chi)
+{
+    RayDev<Real> r{};
+    double st = std::sqrt(std::max(0.0, 1.0 - mu * mu));
+    r.mu = (Real)mu;
+    r.ox = (Real)(st * std::cos(chi));
+    r.oy = (Real)(st * std::sin(chi));
+    r.oz = (Real)mu;
+    double t[18];
+    tkq_tensors(mu, chi, t);
+    for (int i = 0; i < 18; ++i) r.t[i] = (Real)t[i];
+    return r;
+}
+
+int ns_of(int model) { return model == PORTA_MODEL_TWOLEVEL_UNPOL ? 1 : 4; }
+int nl_of(int model) { return model == PORTA_MODEL_TWOLEVEL_UNPOL ? 1 : 6; }
+
+const int kThreads = 256;
+const int kSmemLimit = 220 * 1024;
+
+// Launch shape of the sweep: cluster size C (CTAs sharing one ray's plane)
+// and frequencies per pass F. Estimated time of a candidate (in units of one
+// point update) = waves of rays x per-ray work per CTA, where per-ray work
+// counts the point updates, the ring fills (halo rows included) and the
+// partial-integral writes of each frequency pass, and the plane barriers.
+template <typename Real, int NS>
+int choose_launch(porta_ctx *c, LaunchCfg &best, int force_c, int force_f, int nitems)
+{
+    const int NW = NS == 1 ? 4 : 8;
+    double best_cost = 1e300;
+    best = LaunchCfg{};
+    for (int C : {1, 2, 4, 8, 16}) {
+        if (force_c > 0 && C != force_c) continue;
+        if (C > c->ny) continue;
+        int rmax = (c->ny + C - 1) / C;
+        long long ring = 3LL * (rmax + 2) * c->nx * NW * (long long)sizeof(Real);
+        long long per_nu = 2LL * rmax * c->nx * NS * (long long)sizeof(Real);
+        if (ring + per_nu > kSmemLimit) continue;
+        int fmax = (int)std::min<long long>(c->n_nu, (kSmemLimit - ring) / per_nu);
+        if (force_f > 0) {
+            if (force_f > fmax) continue;
+            fmax = force_f;
+        }
+        int G = (c->n_nu + fmax - 1) / fmax;
+        int F = (c->n_nu + G - 1) / G;
+        int smem = (int)(ring + F * per_nu);
+        int act = 0;
+        if (max_active_clusters<Real, NS>(C, smem, kThreads, &act) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        if (act < 1) continue;
+        int ncl = std::min(act, nitems);
+        double waves = std::ceil((double)nitems / ncl);
+        double pts = (double)rmax * c->nx;
+        double slots = std::ceil(pts / kThreads) * kThreads;   // thread slots per frequency
+        double per_plane = G * (slots * F + 0.15 * (rmax + 2) * c->nx + 0.05 * pts + 300.0);
+        double cost = waves * per_plane;
+        if (cost < best_cost) {
+            best_cost = cost;
+            best.cluster = C;
+            best.F = F;
+            best.threads = kThreads;
+            best.smem = smem;
+            best.clusters = ncl;
+        }
+    }
+    return best.cluster > 0 ? PORTA_OK : PORTA_EINVAL;
+}
+
+template <typename Real>
+SweepArgs<Real> base_args(porta_ctx *c)
+{
+    SweepArgs<Real> a{};
+    a.nx = c->nx;
+    a.ny = c->ny;
+    a.nz = c->nz;
+    a.nnu = c->n_nu;
+    a.nvox = c->nvox;
+    a.bfac = (Real)(2.0 * c->gbar * c->zeta);
+    const Real *atm = (const Real *)c->d_atm;
+    a.chi = atm;
+    a.vel = atm + c->nvox;
+    a.bx = atm + 2 * c->nvox;
+    a.by = atm + 3 * c->nvox;
+    a.bz = atm + 4 * c->nvox;
+    a.bpl = atm + 5 * c->nvox;
+    a.rho = (const Real *)c->d_rhoR;
+    a.xf = (const Real *)c->d_freq;
+    a.wf = (const Real *)c->d_freq + c->n_nu;
+    a.probe_ray = -1;
+    return a;
+}
+
+template <typename Real>
+int formal_solve_t(porta_ctx *c, int probe_ray, Real *probe, Real *probe_ls)
+{
+    SweepArgs<Real> a = base_args<Real>(c);
+    a.geom = (const PlaneGeom<Real> *)c->d_geom;
+    a.rays = (const RayDev<Real> *)c->d_rays;
+    a.invn = (const Real *)c->d_invn;
+    a.part = c->d_part;
+    a.nitems = c->nray;
+    a.probe_ray = probe_ray;
+    a.probe = probe;
+    a.probe_ls = probe_ls;
+    LaunchCfg cfg;
+    int rc = c->ns == 1 ? choose_launch<Real, 1>(c, cfg, c->opt_cluster, c->opt_nu_group, c->nray)
+                        : choose_launch<Real, 4>(c, cfg, c->opt_cluster, c->opt_nu_group, c->nray);
+    if (rc) return fail(c, rc, "no sweep launch shape fits this grid (shared memory / cluster limits)");
+    a.F = cfg.F;
+    a.ngroups = (c->n_nu + cfg.F - 1) / cfg.F;
+    a.rmax = (c->ny + cfg.cluster - 1) / cfg.cluster;
+    cudaError_t e = c->ns == 1 ? launch_sweep<Real, 1>(a, MODE_JKQ, cfg, c->stream)
+                               : launch_sweep<Real, 4>(a, MODE_JKQ, cfg, c->stream);
+    if (e != cudaSuccess) return fail(c, PORTA_ECUDA, std::string("sweep launch: ") + cudaGetErrorString(e));
+    c->last = cfg;
+    return PORTA_OK;
+}
+
+template <typename Real>
+int emergent_t(porta_ctx *c, int ndir, const double *mu, const double *chi, double *dout)
+{
+    std::vector<PlaneGeom<Real>> geom((size_t)ndir * c->nz);
+    std::vector<RayDev<Real>> rays(ndir);
+    for (int d = 0; d < ndir; ++d) {
+        plane_geometry<Real>(c, mu[d], chi[d], geom.data() + (size_t)d * c->nz);
+        rays[d] = ray_dev<Real>(mu[d], chi[d]);
+    }
+    PlaneGeom<Real> *dg = nullptr;
+    RayDev<Real> *dr = nullptr;
+    CK(dalloc(&dg, geom.size()));
+    cudaError_t e2 = dalloc(&dr, rays.size());
+    if (e2 != cudaSuccess) { cudaFree(dg); return fail(c, PORTA_ENOMEM, "emergent: device allocation"); }
+    int rc = PORTA_OK;
+    do {
+        cudaError_t e = cudaMemcpyAsync(dg, geom.data(), geom.size() * sizeof(geom[0]), cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dr, rays.data(), rays.size() * sizeof(rays[0]), cudaMemcpyHostToDevice, c->stream);
+        if (e != cudaSuccess) { rc = fail(c, PORTA_ECUDA, cudaGetErrorString(e)); break; }
+        SweepArgs<Real> a = base_args<Real>(c);
+        a.geom = dg;
+        a.rays = dr;
+        a.out = dout;
+        LaunchCfg cfg;
+        rc = c->ns == 1 ? choose_launch<Real, 1>(c, cfg, c->opt_cluster, c->opt_nu_group, c->nray)
+                        : choose_launch<Real, 4>(c, cfg, c->opt_cluster, c->opt_nu_group, c->nray);
+        if (rc) { rc = fail(c, rc, "no sweep launch shape fits this grid"); break; }
+        a.F = cfg.F;
+        a.ngroups = (c->n_nu + cfg.F - 1) / cfg.F;
+        a.rmax = (c->ny + cfg.cluster - 1) / cfg.cluster;
+        a.nitems = ndir * a.ngroups;
+        cfg.clusters = std::min(cfg.clusters, a.nitems);
+        e = c->ns == 1 ? launch_sweep<Real, 1>(a, MODE_EMERGENT, cfg, c->stream)
+                       : launch_sweep<Real, 4>(a, MODE_EMERGENT, cfg, c->stream);
+        if (e != cudaSuccess) { rc = fail(c, PORTA_ECUDA, std::string("emergent launch: ") + cudaGetErrorString(e)); break; }
+        e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) rc = fail(c, PORTA_ECUDA, std::string("emergent: ") + cudaGetErrorString(e));
+    } while (0);
+    cudaStreamSynchronize(c->stream);
+    cudaFree(dg);
+    cudaFree(dr);
+    return rc;
+}
+
+void free_all(porta_ctx *c)
+{
+    void *ptrs[] = {c->d_atm, c->d_eps, c->d_bpl, c->d_b, c->d_rho, c->d_rhoR, c->d_invn, c->d_geom, c->d_rays,
+                    c->d_freq, c->d_part, c->d_tw, c->d_jkq, c->d_lstar, c->d_resid, c->d_err};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+}
+
+bool finite_host(const double *x, long long n)
+{
+    for (long long i = 0; i < n; ++i)
+        if (!std::isfinite(x[i])) return false;
+    return true;
+}
+
+// copy n doubles from a caller buffer (host or device) into device memory
+int copy_in(porta_ctx *c, double *dst, const double *src, long long n, int where)
+{
+    cudaError_t e = cudaMemcpyAsync(dst, src, n * sizeof(double),
+                                    where == PORTA_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return fail(c, PORTA_ECUDA, std::string("copy in: ") + cudaGetErrorString(e));
+    return PORTA_OK;
+}
+
+// number of entries of a device array outside (lo, hi] (NaN counts)
+int count_bad(porta_ctx *c, const double *d, long long n, double lo, double hi, unsigned long long *out)
+{
+    CK(cudaMemsetAsync(c->d_resid, 0, sizeof(unsigned long long), c->stream));
+    CK(run_count_bad(n, d, lo, hi, c->d_resid, c->stream));
+    CK(cudaMemcpyAsync(out, c->d_resid, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return PORTA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int porta_create(const porta_grid *g, const porta_atom *at, const porta_quad *q, const porta_opts *o, porta_ctx **out)
+{
+    if (!out) return PORTA_EINVAL;
+    *out = nullptr;
+    if (!g || !at || !q || !g->z) return PORTA_EINVAL;
+    if (g->nx < 1 || g->ny < 1 || g->nz < 2 || !(g->lx > 0) || !(g->ly > 0)) return PORTA_EINVAL;
+    if (q->n_mu < 1 || q->n_chi < 1 || q->n_nu < 1 || !(q->x_max > 0) || !std::isfinite(q->x_max)) return PORTA_EINVAL;
+    if (at->model != PORTA_MODEL_TWOLEVEL_UNPOL && at->model != PORTA_MODEL_TWOLEVEL_HANLE) return PORTA_EINVAL;
+    if (at->model == PORTA_MODEL_TWOLEVEL_HANLE && !(at->bcrit > 0)) return PORTA_EINVAL;
+    int prec = o ? o->precision : PORTA_FP32;
+    if (prec != PORTA_FP32 && prec != PORTA_FP64) return PORTA_EINVAL;
+    for (int k = 0; k < g->nz; ++k)
+        if (!std::isfinite(g->z[k]) || (k > 0 && !(g->z[k] > g->z[k - 1]))) return PORTA_EINVAL;
+    long long nvox = (long long)g->nx * g->ny * g->nz;
+    if (nvox > (1LL << 31)) return PORTA_EINVAL;
+
+    porta_ctx *c = new (std::nothrow) porta_ctx();
+    if (!c) return PORTA_ENOMEM;
+    c->nx = g->nx; c->ny = g->ny; c->nz = g->nz;
+    c->lx = g->lx; c->ly = g->ly;
+    c->z.assign(g->z, g->z + g->nz);
+    c->model = at->model;
+    c->ns = ns_of(at->model);
+    c->nl = nl_of(at->model);
+    c->nj = c->nl;
+    c->zeta = at->zeta; c->gbar = at->gbar; c->bcrit = at->bcrit;
+    c->n_mu = q->n_mu; c->n_chi = q->n_chi; c->n_nu = q->n_nu; c->x_max = q->x_max;
+    c->precision = prec;
+    c->opt_cluster = o ? o->cluster : 0;
+    c->opt_nu_group = o ? o->nu_group : 0;
+    c->nvox = nvox;
+    c->nray = 2 * q->n_mu * q->n_chi;
+    c->rsz = prec == PORTA_FP32 ? sizeof(float) : sizeof(double);
+
+    // angular quadrature: Gauss inclinations per hemisphere x equally weighted azimuths at midpoints
+    std::vector<double> xg, wg;
+    gauss_legendre(q->n_mu, xg, wg);
+    c->mu.resize(c->nray); c->chi.resize(c->nray); c->w.resize(c->nray);
+    for (int h = 0; h < 2; ++h)
+        for (int i = 0; i < q->n_mu; ++i)
+            for (int a = 0; a < q->n_chi; ++a) {
+                int m = (h * q->n_mu + i) * q->n_chi + a;
+                c->mu[m] = h == 0 ? xg[i] : -xg[i];
+                c->chi[m] = (a + 0.5) * 2.0 * M_PI / q->n_chi;
+                c->w[m] = 0.5 * wg[i] / q->n_chi;
+            }
+    // frequency quadrature: uniform nodes, trapezoid weights
+    c->xf.resize(q->n_nu); c->wf.resize(q->n_nu);
+    if (q->n_nu == 1) { c->xf[0] = 0.0; c->wf[0] = 1.0; }
+    else {
+        double dx = 2.0 * q->x_max / (q->n_nu - 1);
+        for (int j = 0; j < q->n_nu; ++j) {
+            c->xf[j] = -q->x_max + j * dx;
+            c->wf[j] = (j == 0 || j == q->n_nu - 1) ? 0.5 * dx : dx;
+        }
+    }
+    c->tkq.resize((size_t)c->nray * 18);
+    for (int m = 0; m < c->nray; ++m) tkq_tensors(c->mu[m], c->chi[m], &c->tkq[(size_t)m * 18]);
+
+    int rc = PORTA_OK;
+    auto ok = [&](cudaError_t e) {
+        if (e != cudaSuccess && rc == PORTA_OK) {
+            rc = e == cudaErrorMemoryAllocation ? PORTA_ENOMEM : PORTA_ECUDA;
+            c->err = cudaGetErrorString(e);
+        }
+    };
+    const size_t R = c->rsz;
+    ok(cudaMalloc(&c->d_atm, 6 * nvox * R));
+    ok(dalloc(&c->d_eps, nvox));
+    ok(dalloc(&c->d_bpl, nvox));
+    ok(dalloc(&c->d_b, 3 * nvox));
+    ok(dalloc(&c->d_rho, nvox * c->nl));
+    ok(cudaMalloc(&c->d_rhoR, nvox * c->nl * R));
+    ok(cudaMalloc(&c->d_invn, (size_t)c->nray * nvox * R));
+    ok(cudaMalloc(&c->d_geom, (size_t)c->nray * c->nz * (prec == PORTA_FP32 ? sizeof(PlaneGeom<float>) : sizeof(PlaneGeom<double>))));
+    ok(cudaMalloc(&c->d_rays, (size_t)c->nray * (prec == PORTA_FP32 ? sizeof(RayDev<float>) : sizeof(RayDev<double>))));
+    ok(cudaMalloc(&c->d_freq, 2 * (size_t)c->n_nu * R));
+    ok(cudaMalloc(&c->d_part, (size_t)c->nray * nvox * (c->ns == 1 ? 2 : 4) * R));
+    ok(dalloc(&c->d_tw, (size_t)c->nray * 19));
+    ok(dalloc(&c->d_jkq, nvox * c->nj));
+    ok(dalloc(&c->d_lstar, nvox));
+    ok(dalloc(&c->d_resid, 1));
+    ok(dalloc(&c->d_err, 1));
+    if (rc == PORTA_OK) {
+        ok(cudaMemset(c->d_atm, 0, 6 * nvox * R));
+        // geometry, rays, frequencies, angular weights
+        std::vector<double> tw((size_t)c->nray * 19);
+        for (int m = 0; m < c->nray; ++m) {
+            tw[m * 19] = c->w[m];
+            for (int i = 0; i < 18; ++i) tw[m * 19 + 1 + i] = c->tkq[(size_t)m * 18 + i];
+        }
+        ok(cudaMemcpy(c->d_tw, tw.data(), tw.size() * sizeof(double), cudaMemcpyHostToDevice));
+        if (prec == PORTA_FP32) {
+            std::vector<PlaneGeom<float>> geom((size_t)c->nray * c->nz);
+            std::vector<RayDev<float>> rays(c->nray);
+            std::vector<float> fr(2 * c->n_nu);
+            for (int m = 0; m < c->nray; ++m) {
+                plane_geometry<float>(c, c->mu[m], c->chi[m], geom.data() + (size_t)m * c->nz);
+                rays[m] = ray_dev<float>(c->mu[m], c->chi[m]);
+            }
+            for (int j = 0; j < c->n_nu; ++j) { fr[j] = (float)c->xf[j]; fr[c->n_nu + j] = (float)c->wf[j]; }
+            ok(cudaMemcpy(c->d_geom, geom.data(), geom.size() * sizeof(geom[0]), cudaMemcpyHostToDevice));
+            ok(cudaMemcpy(c->d_rays, rays.data(), rays.size() * sizeof(rays[0]), cudaMemcpyHostToDevice));
+            ok(cudaMemcpy(c->d_freq, fr.data(), fr.size() * sizeof(float), cudaMemcpyHostToDevice));
+        } else {
+            std::vector<PlaneGeom<double>> geom((size_t)c->nray * c->nz);
+            std::vector<RayDev<double>> rays(c->nray);
+            std::vector<double> fr(2 * c->n_nu);
+            for (int m = 0; m < c->nray; ++m) {
+                plane_geometry<double>(c, c->mu[m], c->chi[m], geom.data() + (size_t)m * c->nz);
+                rays[m] = ray_dev<double>(c->mu[m], c->chi[m]);
+            }
+            for (int j = 0; j < c->n_nu; ++j) { fr[j] = c->xf[j]; fr[c->n_nu + j] = c->wf[j]; }
+            ok(cudaMemcpy(c->d_geom, geom.data(), geom.size() * sizeof(geom[0]), cudaMemcpyHostToDevice));
+            ok(cudaMemcpy(c->d_rays, rays.data(), rays.size() * sizeof(rays[0]), cudaMemcpyHostToDevice));
+            ok(cudaMemcpy(c->d_freq, fr.data(), fr.size() * sizeof(double), cudaMemcpyHostToDevice));
+        }
+        // a launch shape must exist for this grid
+        LaunchCfg cfg;
+        int r2 = prec == PORTA_FP32
+                     ? (c->ns == 1 ? choose_launch<float, 1>(c, cfg, c->opt_cluster, c->opt_nu_group, c->nray)
+                                   : choose_launch<float, 4>(c, cfg, c->opt_cluster, c->opt_nu_group, c->nray))
+                     : (c->ns == 1 ? choose_launch<double, 1>(c, cfg, c->opt_cluster, c->opt_nu_group, c->nray)
+                                   : choose_launch<double, 4>(c, cfg, c->opt_cluster, c->opt_nu_group, c->nray));
+        if (rc == PORTA_OK && r2 != PORTA_OK) {
+            rc = PORTA_EINVAL;
+            c->err = "no sweep launch shape fits this grid (nx too large for shared memory)";
+        }
+    }
+    if (rc != PORTA_OK) {
+        free_all(c);
+        delete c;
+        return rc;
+    }
+    *out = c;
+    return PORTA_OK;
+}
+
+void porta_destroy(porta_ctx *c)
+{
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    else cudaDeviceSynchronize();
+    free_all(c);
+    delete c;
+}
+
+const char *porta_last_error(const porta_ctx *c) { return c ? c->err.c_str() : kNullCtx; }
+
+int porta_set_stream(porta_ctx *c, void *stream)
+{
+    if (!c) return PORTA_EINVAL;
+    c->stream = (cudaStream_t)stream;
+    return PORTA_OK;
+}
+
+int porta_sizes(const porta_ctx *c, int *nray, int *nnu, long long *nvox, int *nl, int *nj, int *ns)
+{
+    if (!c) return PORTA_EINVAL;
+    if (nray) *nray = c->nray;
+    if (nnu) *nnu = c->n_nu;
+    if (nvox) *nvox = c->nvox;
+    if (nl) *nl = c->nl;
+    if (nj) *nj = c->nj;
+    if (ns) *ns = c->ns;
+    return PORTA_OK;
+}
+
+int porta_rays(const porta_ctx *c, double *mu, double *chi, double *w)
+{
+    if (!c) return PORTA_EINVAL;
+    for (int m = 0; m < c->nray; ++m) {
+        if (mu) mu[m] = c->mu[m];
+        if (chi) chi[m] = c->chi[m];
+        if (w) w[m] = c->w[m];
+    }
+    return PORTA_OK;
+}
+
+int porta_set_atmosphere(porta_ctx *c, const porta_atmos *a, int where)
+{
+    if (!c) return PORTA_EINVAL;
+    if (!a || !a->chi || !a->eps || !a->bpl || !a->vel) return fail(c, PORTA_EINVAL, "atmosphere: missing array");
+    const bool pol = c->model == PORTA_MODEL_TWOLEVEL_HANLE;
+    if (pol && (!a->bx || !a->by || !a->bz)) return fail(c, PORTA_EINVAL, "atmosphere: magnetic field required");
+    if (where != PORTA_HOST && where != PORTA_DEVICE) return fail(c, PORTA_EINVAL, "atmosphere: bad `where`");
+    const long long n = c->nvox;
+    // stage FP64 copies on the device: eps, bpl, field (kept), chi and vel (temporary)
+    double *tmp = nullptr;
+    CK(dalloc(&tmp, 2 * n));
+    int rc = PORTA_OK;
+    do {
+        if ((rc = copy_in(c, tmp, a->chi, n, where))) break;
+        if ((rc = copy_in(c, tmp + n, a->vel, n, where))) break;
+        if ((rc = copy_in(c, c->d_eps, a->eps, n, where))) break;
+        if ((rc = copy_in(c, c->d_bpl, a->bpl, n, where))) break;
+        if (pol) {
+            if ((rc = copy_in(c, c->d_b, a->bx, n, where))) break;
+            if ((rc = copy_in(c, c->d_b + n, a->by, n, where))) break;
+            if ((rc = copy_in(c, c->d_b + 2 * n, a->bz, n, where))) break;
+        } else {
+            cudaMemsetAsync(c->d_b, 0, 3 * n * sizeof(double), c->stream);
+        }
+        unsigned long long bad = 0;
+        if ((rc = count_bad(c, tmp, n, 0.0, 1e300, &bad))) break;
+        if (bad) { rc = fail(c, PORTA_EINVAL, "atmosphere: chi must be finite and > 0"); break; }
+        if ((rc = count_bad(c, c->d_eps, n, 0.0, 1.0, &bad))) break;
+        if (bad) { rc = fail(c, PORTA_EINVAL, "atmosphere: eps must lie in (0, 1]"); break; }
+        if ((rc = count_bad(c, c->d_bpl, n, -1e300, 1e300, &bad))) break;
+        if (bad) { rc = fail(c, PORTA_EINVAL, "atmosphere: Planck function must be finite"); break; }
+        if ((rc = count_bad(c, tmp + n, n, -1e300, 1e300, &bad))) break;
+        if (bad) { rc = fail(c, PORTA_EINVAL, "atmosphere: velocity must be finite"); break; }
+        if (pol) {
+            if ((rc = count_bad(c, c->d_b, 3 * n, -1e300, 1e300, &bad))) break;
+            if (bad) { rc = fail(c, PORTA_EINVAL, "atmosphere: magnetic field must be finite"); break; }
+        }
+        // sweep copies (Real): chi, vel, bx, by, bz, bpl
+        cudaError_t e;
+        const size_t R = c->rsz;
+        char *atm = (char *)c->d_atm;
+        if (c->precision == PORTA_FP32) {
+            e = run_to_real<float>(n, tmp, atm, c->stream);
+            if (e == cudaSuccess) e = run_to_real<float>(n, tmp + n, atm + n * R, c->stream);
+            if (e == cudaSuccess) e = run_to_real<float>(3 * n, c->d_b, atm + 2 * n * R, c->stream);
+            if (e == cudaSuccess) e = run_to_real<float>(n, c->d_bpl, atm + 5 * n * R, c->stream);
+        } else {
+            e = run_to_real<double>(n, tmp, atm, c->stream);
+            if (e == cudaSuccess) e = run_to_real<double>(n, tmp + n, atm + n * R, c->stream);
+            if (e == cudaSuccess) e = run_to_real<double>(3 * n, c->d_b, atm + 2 * n * R, c->stream);
+            if (e == cudaSuccess) e = run_to_real<double>(n, c->d_bpl, atm + 5 * n * R, c->stream);
+        }
+        if (e != cudaSuccess) { rc = fail(c, PORTA_ECUDA, cudaGetErrorString(e)); break; }
+        // profile normalization per voxel and ray
+        double *dq = nullptr;
+        e = dalloc(&dq, (size_t)c->nray + 2 * c->n_nu);
+        if (e != cudaSuccess) { rc = fail(c, PORTA_ENOMEM, "atmosphere: allocation"); break; }
+        std::vector<double> hq(c->mu);
+        hq.insert(hq.end(), c->xf.begin(), c->xf.end());
+        hq.insert(hq.end(), c->wf.begin(), c->wf.end());
+        e = cudaMemcpyAsync(dq, hq.data(), hq.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess)
+            e = c->precision == PORTA_FP32
+                    ? run_profile_norm<float>(n, c->nray, c->n_nu, dq, dq + c->nray, dq + c->nray + c->n_nu, tmp + n, c->d_invn, c->stream)
+                    : run_profile_norm<double>(n, c->nray, c->n_nu, dq, dq + c->nray, dq + c->nray + c->n_nu, tmp + n, c->d_invn, c->stream);
+        cudaError_t e2 = cudaStreamSynchronize(c->stream);
+        cudaFree(dq);
+        if (e == cudaSuccess) e = e2;
+        if (e != cudaSuccess) { rc = fail(c, PORTA_ECUDA, cudaGetErrorString(e)); break; }
+    } while (0);
+    cudaStreamSynchronize(c->stream);
+    cudaFree(tmp);
+    if (rc == PORTA_OK) {
+        c->have_atm = true;
+        c->have_fs = c->have_jkq = false;
+    }
+    return rc;
+}
+
+int porta_set_rho(porta_ctx *c, const double *rho, int where)
+{
+    if (!c) return PORTA_EINVAL;
+    if (!rho || (where != PORTA_HOST && where != PORTA_DEVICE)) return fail(c, PORTA_EINVAL, "set_rho: bad argument");
+    const long long n = c->nvox * c->nl;
+    if (where == PORTA_HOST) {
+        if (!finite_host(rho, n)) return fail(c, PORTA_EINVAL, "set_rho: non-finite value");
+        for (long long v = 0; v < c->nvox; ++v)
+            if (!(rho[v * c->nl] > 0)) return fail(c, PORTA_EINVAL, "set_rho: S^0_0 must be > 0");
+    }
+    int rc = copy_in(c, c->d_rho, rho, n, where);
+    if (rc) return rc;
+    if (where == PORTA_DEVICE) {
+        unsigned long long bad = 0;
+        if ((rc = count_bad(c, c->d_rho, n, -1e300, 1e300, &bad))) return rc;
+        if (bad) return fail(c, PORTA_EINVAL, "set_rho: non-finite value");
+    }
+    cudaError_t e = c->precision == PORTA_FP32 ? run_rho_convert<float>(c->nvox, c->nl, c->d_rho, c->d_rhoR, c->stream)
+                                               : run_rho_convert<double>(c->nvox, c->nl, c->d_rho, c->d_rhoR, c->stream);
+    if (e != cudaSuccess) return fail(c, PORTA_ECUDA, cudaGetErrorString(e));
+    if (where == PORTA_HOST) CK(cudaStreamSynchronize(c->stream));
+    c->have_rho = true;
+    c->have_fs = c->have_jkq = false;
+    return PORTA_OK;
+}
+
+int porta_get_rho(porta_ctx *c, double *rho, int where)
+{
+    if (!c) return PORTA_EINVAL;
+    if (!rho || (where != PORTA_HOST && where != PORTA_DEVICE)) return fail(c, PORTA_EINVAL, "get_rho: bad argument");
+    if (!c->have_rho) return fail(c, PORTA_ESTATE, "get_rho: rho has not been set");
+    CK(cudaMemcpyAsync(rho, c->d_rho, c->nvox * c->nl * sizeof(double),
+                       where == PORTA_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+    if (where == PORTA_HOST) CK(cudaStreamSynchronize(c->stream));
+    return PORTA_OK;
+}
+
+int porta_formal_solve(porta_ctx *c)
+{
+    if (!c) return PORTA_EINVAL;
+    if (!c->have_atm) return fail(c, PORTA_ESTATE, "formal_solve: atmosphere not set");
+    if (!c->have_rho) return fail(c, PORTA_ESTATE, "formal_solve: rho not set");
+    int rc = c->precision == PORTA_FP32 ? formal_solve_t<float>(c, -1, nullptr, nullptr)
+                                        : formal_solve_t<double>(c, -1, nullptr, nullptr);
+    if (rc == PORTA_OK) {
+        c->have_fs = true;
+        c->have_jkq = false;
+    }
+    return rc;
+}
+
+int porta_accumulate_jkq(porta_ctx *c, double *jkq, double *lstar, int where)
+{
+    if (!c) return PORTA_EINVAL;
+    if (!c->have_fs) return fail(c, PORTA_ESTATE, "accumulate_jkq: no formal solution");
+    if (where != PORTA_HOST && where != PORTA_DEVICE) return fail(c, PORTA_EINVAL, "accumulate_jkq: bad `where`");
+    cudaError_t e;
+    if (c->precision == PORTA_FP32)
+        e = c->ns == 1 ? run_jkq_finalize<float, 1>(c->nvox, c->nray, c->d_part, c->d_tw, c->d_jkq, c->d_lstar, c->stream)
+                       : run_jkq_finalize<float, 4>(c->nvox, c->nray, c->d_part, c->d_tw, c->d_jkq, c->d_lstar, c->stream);
+    else
+        e = c->ns == 1 ? run_jkq_finalize<double, 1>(c->nvox, c->nray, c->d_part, c->d_tw, c->d_jkq, c->d_lstar, c->stream)
+                       : run_jkq_finalize<double, 4>(c->nvox, c->nray, c->d_part, c->d_tw, c->d_jkq, c->d_lstar, c->stream);
+    if (e != cudaSuccess) return fail(c, PORTA_ECUDA, std::string("accumulate_jkq: ") + cudaGetErrorString(e));
+    cudaMemcpyKind k = where == PORTA_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (jkq) CK(cudaMemcpyAsync(jkq, c->d_jkq, c->nvox * c->nj * sizeof(double), k, c->stream));
+    if (lstar) CK(cudaMemcpyAsync(lstar, c->d_lstar, c->nvox * sizeof(double), k, c->stream));
+    if (where == PORTA_HOST && (jkq || lstar)) CK(cudaStreamSynchronize(c->stream));
+    c->have_jkq = true;
+    return PORTA_OK;
+}
+
+int porta_see_update(porta_ctx *c, double *max_change)
+{
+    if (!c) return PORTA_EINVAL;
+    if (!c->have_jkq) return fail(c, PORTA_ESTATE, "see_update: J^K_Q not accumulated");
+    CK(cudaMemsetAsync(c->d_resid, 0, sizeof(unsigned long long), c->stream));
+    cudaError_t e = c->precision == PORTA_FP32
+                        ? run_see<float>(c->nvox, c->nl, c->model, c->bcrit, c->d_eps, c->d_bpl, c->d_b, c->d_jkq,
+                                         c->d_lstar, c->d_rho, c->d_rhoR, c->d_resid, c->stream)
+                        : run_see<double>(c->nvox, c->nl, c->model, c->bcrit, c->d_eps, c->d_bpl, c->d_b, c->d_jkq,
+                                          c->d_lstar, c->d_rho, c->d_rhoR, c->d_resid, c->stream);
+    if (e != cudaSuccess) return fail(c, PORTA_ECUDA, std::string("see_update: ") + cudaGetErrorString(e));
+    c->have_fs = c->have_jkq = false;
+    if (max_change) {
+        unsigned long long bits = 0;
+        CK(cudaMemcpyAsync(&bits, c->d_resid, sizeof(bits), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        double v;
+        std::memcpy(&v, &bits, sizeof(v));
+        *max_change = v;
+    }
+    return PORTA_OK;
+}
+
+int porta_emergent_stokes(porta_ctx *c, int ndir, const double *mu, const double *chi, double *out, int where)
+{
+    if (!c) return PORTA_EINVAL;
+    if (ndir < 1 || !mu || !chi || !out || (where != PORTA_HOST && where != PORTA_DEVICE))
+        return fail(c, PORTA_EINVAL, "emergent_stokes: bad argument");
+    for (int d = 0; d < ndir; ++d)
+        if (!(mu[d] > 0.0 && mu[d] <= 1.0) || !std::isfinite(chi[d]))
+            return fail(c, PORTA_EINVAL, "emergent_stokes: mu must lie in (0, 1], chi finite");
+    if (!c->have_atm || !c->have_rho) return fail(c, PORTA_ESTATE, "emergent_stokes: atmosphere or rho not set");
+    const long long n = (long long)ndir * c->n_nu * c->nx * c->ny * c->ns;
+    double *dout = out;
+    if (where == PORTA_HOST) CK(dalloc(&dout, n));
+    int rc = c->precision == PORTA_FP32 ? emergent_t<float>(c, ndir, mu, chi, dout) : emergent_t<double>(c, ndir, mu, chi, dout);
+    if (where == PORTA_HOST) {
+        if (rc == PORTA_OK) {
+            cudaError_t e = cudaMemcpy(out, dout, n * sizeof(double), cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) rc = fail(c, PORTA_ECUDA, cudaGetErrorString(e));
+        }
+        cudaFree(dout);
+    }
+    return rc;
+}
+
+int porta_probe_ray(porta_ctx *c, int m, double *out, double *lstar, int where)
+{
+    if (!c) return PORTA_EINVAL;
+    if (m < 0 || m >= c->nray || !out || (where != PORTA_HOST && where != PORTA_DEVICE))
+        return fail(c, PORTA_EINVAL, "probe_ray: bad argument");
+    if (!c->have_atm || !c->have_rho) return fail(c, PORTA_ESTATE, "probe_ray: atmosphere or rho not set");
+    const long long n = (long long)c->n_nu * c->nvox;
+    void *pr = nullptr, *pl = nullptr;
+    CK(cudaMalloc(&pr, n * c->ns * c->rsz));
+    cudaError_t e = cudaMalloc(&pl, n * c->rsz);
+    if (e != cudaSuccess) { cudaFree(pr); return fail(c, PORTA_ENOMEM, "probe_ray: allocation"); }
+    int rc = c->precision == PORTA_FP32 ? formal_solve_t<float>(c, m, (float *)pr, (float *)pl)
+                                        : formal_solve_t<double>(c, m, (double *)pr, (double *)pl);
+    double *d1 = nullptr, *d2 = nullptr;
+    if (rc == PORTA_OK) {
+        e = dalloc(&d1, n * c->ns);
+        if (e == cudaSuccess) e = dalloc(&d2, n);
+        if (e == cudaSuccess) {
+            if (c->precision == PORTA_FP32) {
+                // widen float -> double on the host side of the copy
+                std::vector<float> h1(n * c->ns), h2(n);
+                e = cudaMemcpyAsync(h1.data(), pr, h1.size() * sizeof(float), cudaMemcpyDeviceToHost, c->stream);
+                if (e == cudaSuccess) e = cudaMemcpyAsync(h2.data(), pl, h2.size() * sizeof(float), cudaMemcpyDeviceToHost, c->stream);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+                std::vector<double> g1(h1.begin(), h1.end()), g2(h2.begin(), h2.end());
+                if (e == cudaSuccess) e = cudaMemcpy(d1, g1.data(), g1.size() * sizeof(double), cudaMemcpyHostToDevice);
+                if (e == cudaSuccess) e = cudaMemcpy(d2, g2.data(), g2.size() * sizeof(double), cudaMemcpyHostToDevice);
+            } else {
+                e = cudaMemcpyAsync(d1, pr, n * c->ns * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+                if (e == cudaSuccess) e = cudaMemcpyAsync(d2, pl, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+            }
+        }
+        cudaMemcpyKind k = where == PORTA_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(out, d1, n * c->ns * sizeof(double), k, c->stream);
+        if (e == cudaSuccess && lstar) e = cudaMemcpyAsync(lstar, d2, n * sizeof(double), k, c->stream);
+        cudaError_t e2 = cudaStreamSynchronize(c->stream);
+        if (e == cudaSuccess) e = e2;
+        if (e != cudaSuccess) rc = fail(c, PORTA_ECUDA, std::string("probe_ray: ") + cudaGetErrorString(e));
+    }
+    cudaStreamSynchronize(c->stream);
+    cudaFree(pr);
+    cudaFree(pl);
+    if (d1) cudaFree(d1);
+    if (d2) cudaFree(d2);
+    if (rc == PORTA_OK) {
+        c->have_fs = true;
+        c->have_jkq = false;
+    }
+    return rc;
+}
+
+int porta_launch_info(const porta_ctx *c, int *clusters, int *cluster_size, int *nu_group, int *smem_bytes)
+{
+    if (!c) return PORTA_EINVAL;
+    if (clusters) *clusters = c->last.clusters;
+    if (cluster_size) *cluster_size = c->last.cluster;
+    if (nu_group) *nu_group = c->last.F;
+    if (smem_bytes) *smem_bytes = c->last.smem;
+    return PORTA_OK;
+}
+
+}  // extern "C"

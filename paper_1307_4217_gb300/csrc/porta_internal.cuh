@@ -1,0 +1,115 @@
+// Internal declarations of the GB300 formal-solver library (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "porta.h"
+
+namespace porta {
+
+// Per-plane geometry of one ray, in sweep order q = 0..nz-1 (q = 0 is the
+// boundary plane where the ray enters). The sweep works in a sheared frame
+// that follows the characteristics: sheared node (c, r) of plane q is the
+// physical node ((c + ax) mod nx, (r + ay) mod ny) of level kz. For q >= 1 the
+// horizontal displacement from the upwind point M to O is d = ds * Omega_xy /
+// spacing (cells); with ax(q) = ax(q-1) + ceil(d) the upwind corners of sheared
+// node (c, r) are sheared (c|c+1, r|r+1) on plane q-1 with weights
+// (1-t, t), t = ceil(d) - d, and the downwind corners are (c-1|c, r-1|r) on plane
+// q+1 with weights (t', 1-t') taken from plane q+1.
+template <typename Real>
+struct PlaneGeom {
+    int ax, ay, kz, pad;
+    Real tx, ty, ds, pad2;   // ds = path length M -> O (q >= 1)
+};
+
+// Per-ray constants: direction and the angular tensors T^K_Q(i, Omega) for
+// i = I, Q, U (rows of 6: T00, T20, Re T21, Im T21, Re T22, Im T22).
+template <typename Real>
+struct RayDev {
+    Real mu, ox, oy, oz;
+    Real t[18];
+    Real pad[2];
+};
+
+enum SweepMode { MODE_JKQ = 0, MODE_EMERGENT = 1 };
+
+template <typename Real>
+struct SweepArgs {
+    int nx, ny, nz, nnu;
+    long long nvox;
+    int nitems;          // work items: rays (J mode) or directions x groups (emergent)
+    int ngroups, F;      // frequency groups and frequencies per group
+    int rmax;            // max sheared rows per CTA
+    Real bfac;           // 2 * gbar * zeta (weak-field Zeeman, eta_V / (eta_I x B.Omega))
+    const PlaneGeom<Real> *geom;   // [ray][nz]
+    const RayDev<Real> *rays;      // [ray]
+    const Real *xf, *wf;           // frequency nodes and trapezoid weights
+    // atmosphere (SoA, Real) and unknowns
+    const Real *chi, *vel, *bx, *by, *bz, *bpl;
+    const Real *rho;               // [nl][nvox]
+    const Real *invn;              // [ray][nvox] profile normalization (J mode)
+    void *part;                    // [ray][nvox] partial integrals (J mode)
+    double *out;                   // emergent: [dir][nu][ny][nx][ns]
+    int probe_ray;                 // -1 or the ray whose Stokes vectors are written to probe
+    Real *probe;                   // [nu][nvox][ns]
+    Real *probe_ls;                // [nu][nvox]
+};
+
+struct LaunchCfg {
+    int cluster;     // CTAs per cluster
+    int F;           // frequencies per pass
+    int threads;
+    int smem;        // dynamic shared memory bytes
+    int clusters;    // clusters launched
+};
+
+template <typename Real, int NS>
+cudaError_t launch_sweep(const SweepArgs<Real> &a, int mode, LaunchCfg &cfg, cudaStream_t st);
+
+template <typename Real, int NS>
+int sweep_smem_bytes(int nx, int rmax, int F);
+
+template <typename Real, int NS>
+cudaError_t max_active_clusters(int cluster, int smem, int threads, int *out);
+
+}  // namespace porta
+
+struct porta_ctx {
+    int nx = 0, ny = 0, nz = 0;
+    double lx = 0, ly = 0;
+    std::vector<double> z;
+    int model = 0, ns = 1, nl = 1, nj = 1;
+    double zeta = 0, gbar = 1, bcrit = 25;
+    int n_mu = 0, n_chi = 0, n_nu = 0;
+    double x_max = 4;
+    int precision = PORTA_FP32;
+    int opt_cluster = 0, opt_nu_group = 0;
+    long long nvox = 0;
+    int nray = 0;
+    std::vector<double> mu, chi, w, xf, wf, tkq;  // quadratures, T^K_Q per ray (18)
+    cudaStream_t stream = nullptr;
+    std::string err;
+    bool have_atm = false, have_rho = false, have_fs = false, have_jkq = false;
+
+    // device memory
+    size_t rsz = 4;                 // sizeof(Real) of the sweep
+    void *d_atm = nullptr;          // Real SoA: chi, vel, bx, by, bz, bpl
+    double *d_eps = nullptr;        // FP64 per-voxel eps, bpl, B (SEE)
+    double *d_bpl = nullptr;
+    double *d_b = nullptr;          // 3*nvox
+    double *d_rho = nullptr;        // nvox*nl FP64
+    void *d_rhoR = nullptr;         // nl*nvox Real
+    void *d_invn = nullptr;         // nray*nvox Real
+    void *d_geom = nullptr;         // nray*nz PlaneGeom
+    void *d_rays = nullptr;         // nray RayDev
+    void *d_freq = nullptr;         // xf, wf (Real)
+    void *d_part = nullptr;         // nray*nvox*(ns==1 ? 2 : 4) Real
+    double *d_tw = nullptr;         // nray*19 FP64: w_m, T (18)
+    double *d_jkq = nullptr, *d_lstar = nullptr;
+    unsigned long long *d_resid = nullptr;
+    int *d_err = nullptr;
+    // last launch of the formal solution
+    porta::LaunchCfg last{};
+};

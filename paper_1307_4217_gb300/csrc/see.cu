@@ -1,0 +1,222 @@
+// Per-voxel kernels around the formal solution: profile normalization
+// (Sec. 4.2), conversion of the unknowns for the sweep, the FP64 sum of the
+// per-ray partial integrals into J^K_Q and Lambda-bar* (Eq. 1), and the
+// Jacobi (ALI) statistical-equilibrium update with its convergence residual
+// (Eq. 2, Sec. 5).
+#include "device_math.cuh"
+#include "see_kernels.cuh"
+
+namespace porta {
+
+// invn[m][v] = 1 / sum_j w_j exp(-(x_j - vel_v mu_m)^2): the profile is
+// renormalized on the frequency quadrature for each voxel and direction.
+template <typename Real>
+__global__ void profile_norm_kernel(long long nvox, int nray, int nnu, const double *mu, const double *xf,
+                                    const double *wf, const double *vel, Real *invn)
+{
+    long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (idx >= nvox * nray) return;
+    int m = (int)(idx / nvox);
+    long long v = idx - (long long)m * nvox;
+    double s = vel[v] * mu[m], sum = 0.0;
+    for (int j = 0; j < nnu; ++j) {
+        double xs = xf[j] - s;
+        sum += wf[j] * exp(-xs * xs);
+    }
+    invn[idx] = (Real)(1.0 / sum);
+}
+
+// rho (FP64, [v][nl]) -> sweep copy (Real, [c][v])
+template <typename Real>
+__global__ void rho_convert_kernel(long long nvox, int nl, const double *rho, Real *out)
+{
+    long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (v >= nvox) return;
+    for (int c = 0; c < nl; ++c) out[c * nvox + v] = (Real)rho[v * nl + c];
+}
+
+// J^K_Q(v) = sum_m w_m sum_p T^K_Q(p, m) P_p(m, v) and Lambda-bar*(v) = sum_m w_m P_L(m, v),
+// summed in FP64 over rays in ascending order (deterministic).
+template <typename Real, int NS>
+__global__ void jkq_finalize_kernel(long long nvox, int nray, const void *part, const double *tw,
+                                    double *jkq, double *lstar)
+{
+    long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (v >= nvox) return;
+    if constexpr (NS == 1) {
+        const Real *p = reinterpret_cast<const Real *>(part);
+        double J = 0.0, L = 0.0;
+        for (int m = 0; m < nray; ++m) {
+            const Real *q = p + 2 * ((long long)m * nvox + v);
+            double w = tw[m * 19];
+            J += w * (double)q[0];
+            L += w * (double)q[1];
+        }
+        jkq[v] = J;
+        lstar[v] = L;
+    } else {
+        const Real *p = reinterpret_cast<const Real *>(part);
+        double J[6] = {0, 0, 0, 0, 0, 0}, L = 0.0;
+        for (int m = 0; m < nray; ++m) {
+            const Real *q = p + 4 * ((long long)m * nvox + v);
+            const double *t = tw + m * 19;
+            double w = t[0];
+            double pI = w * (double)q[0], pQ = w * (double)q[1], pU = w * (double)q[2];
+#pragma unroll
+            for (int c = 0; c < 6; ++c) J[c] += t[1 + c] * pI + t[7 + c] * pQ + t[13 + c] * pU;
+            L += w * (double)q[3];
+        }
+#pragma unroll
+        for (int c = 0; c < 6; ++c) jkq[v * 6 + c] = J[c];
+        lstar[v] = L;
+    }
+}
+
+// atomic max of non-negative doubles through their IEEE bit patterns (the
+// ordering of the bit patterns is that of the values for non-negative doubles)
+__device__ __forceinline__ void atomic_max_nonneg(unsigned long long *addr, double v)
+{
+    atomicMax(addr, (unsigned long long)__double_as_longlong(v));
+}
+
+// Jacobi update (FP64). Unpolarized: S <- S + [(1-eps)J + eps B - S] / [1 - (1-eps) L*].
+// Hanle: S^0_0 as above with J^0_0; K = 2 from (1 + i (1-eps) Gamma_u K(B)) S^2 = (1-eps) J^2.
+template <typename Real>
+__global__ void see_kernel(long long nvox, int nl, int model, double bcrit, const double *eps, const double *bpl,
+                           const double *bvec, const double *jkq, const double *lstar, double *rho, Real *rhoR,
+                           unsigned long long *resid)
+{
+    long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    double change = 0.0;
+    if (v < nvox) {
+        const double e = eps[v], B = bpl[v];
+        if (model == PORTA_MODEL_TWOLEVEL_UNPOL) {
+            const double S = rho[v];
+            const double dS = ((1.0 - e) * jkq[v] + e * B - S) / (1.0 - (1.0 - e) * lstar[v]);
+            const double Sn = S + dS;
+            change = fabs(dS) / fabs(S);
+            rho[v] = Sn;
+            rhoR[v] = (Real)Sn;
+        } else {
+            double *s = rho + 6 * v;
+            const double *J = jkq + 6 * v;
+            const double S00 = s[0];
+            const double dS = ((1.0 - e) * J[0] + e * B - S00) / (1.0 - (1.0 - e) * lstar[v]);
+            const double S00n = S00 + dS;
+            const double bx = bvec[v], by = bvec[nvox + v], bz = bvec[2 * nvox + v];
+            const double gam = (1.0 - e) / bcrit;   // Gamma = (1-eps) |B| / bcrit; times B/|B| below
+            double r[5], x[5];
+#pragma unroll
+            for (int c = 0; c < 5; ++c) r[c] = (1.0 - e) * J[1 + c];
+            hanle_solve5(gam * bx, gam * by, gam * bz, r, x);
+            change = fabs(dS) / fabs(S00);
+#pragma unroll
+            for (int c = 0; c < 5; ++c) change = fmax(change, fabs(x[c] / S00n - s[1 + c] / S00));
+            s[0] = S00n;
+            rhoR[v] = (Real)S00n;
+#pragma unroll
+            for (int c = 0; c < 5; ++c) {
+                s[1 + c] = x[c];
+                rhoR[(1 + c) * nvox + v] = (Real)x[c];
+            }
+        }
+    }
+    // a non-finite change (NaN input or breakdown) is reported as 1e300
+    if (!(change <= 1e300)) change = 1e300;
+    // block max, then one atomic per block
+    __shared__ double red[32];
+    double m = change;
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) red[wid] = m;
+    __syncthreads();
+    if (wid == 0) {
+        int nw = (blockDim.x + 31) >> 5;
+        double mm = lane < nw ? red[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) mm = fmax(mm, __shfl_xor_sync(0xffffffffu, mm, o));
+        if (lane == 0) atomic_max_nonneg(resid, mm);
+    }
+}
+
+// finite-value checks of inputs (count of offending entries)
+__global__ void count_bad_kernel(long long n, const double *x, double lo_excl, double hi_incl, unsigned long long *bad)
+{
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double v = x[i];
+    if (!(v > lo_excl && v <= hi_incl)) atomicAdd(bad, 1ULL);
+}
+
+template <typename Real>
+__global__ void to_real_kernel(long long n, const double *x, Real *y)
+{
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) y[i] = (Real)x[i];
+}
+
+static inline unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+template <typename Real>
+cudaError_t run_profile_norm(long long nvox, int nray, int nnu, const double *mu, const double *xf, const double *wf,
+                             const double *vel, void *invn, cudaStream_t st)
+{
+    profile_norm_kernel<Real><<<nblk(nvox * nray, 256), 256, 0, st>>>(nvox, nray, nnu, mu, xf, wf, vel, (Real *)invn);
+    return cudaGetLastError();
+}
+
+template <typename Real>
+cudaError_t run_rho_convert(long long nvox, int nl, const double *rho, void *out, cudaStream_t st)
+{
+    rho_convert_kernel<Real><<<nblk(nvox, 256), 256, 0, st>>>(nvox, nl, rho, (Real *)out);
+    return cudaGetLastError();
+}
+
+template <typename Real, int NS>
+cudaError_t run_jkq_finalize(long long nvox, int nray, const void *part, const double *tw, double *jkq, double *lstar,
+                             cudaStream_t st)
+{
+    jkq_finalize_kernel<Real, NS><<<nblk(nvox, 256), 256, 0, st>>>(nvox, nray, part, tw, jkq, lstar);
+    return cudaGetLastError();
+}
+
+template <typename Real>
+cudaError_t run_see(long long nvox, int nl, int model, double bcrit, const double *eps, const double *bpl,
+                    const double *bvec, const double *jkq, const double *lstar, double *rho, void *rhoR,
+                    unsigned long long *resid, cudaStream_t st)
+{
+    see_kernel<Real><<<nblk(nvox, 256), 256, 0, st>>>(nvox, nl, model, bcrit, eps, bpl, bvec, jkq, lstar, rho,
+                                                      (Real *)rhoR, resid);
+    return cudaGetLastError();
+}
+
+cudaError_t run_count_bad(long long n, const double *x, double lo_excl, double hi_incl, unsigned long long *bad,
+                          cudaStream_t st)
+{
+    count_bad_kernel<<<nblk(n, 256), 256, 0, st>>>(n, x, lo_excl, hi_incl, bad);
+    return cudaGetLastError();
+}
+
+template <typename Real>
+cudaError_t run_to_real(long long n, const double *x, void *y, cudaStream_t st)
+{
+    to_real_kernel<Real><<<nblk(n, 256), 256, 0, st>>>(n, x, (Real *)y);
+    return cudaGetLastError();
+}
+
+#define INST(R)                                                                                                \
+    template cudaError_t run_profile_norm<R>(long long, int, int, const double *, const double *, const double *,\
+                                             const double *, void *, cudaStream_t);                           \
+    template cudaError_t run_rho_convert<R>(long long, int, const double *, void *, cudaStream_t);              \
+    template cudaError_t run_jkq_finalize<R, 1>(long long, int, const void *, const double *, double *, double *, \
+                                                cudaStream_t);                                                 \
+    template cudaError_t run_jkq_finalize<R, 4>(long long, int, const void *, const double *, double *, double *, \
+                                                cudaStream_t);                                                 \
+    template cudaError_t run_see<R>(long long, int, int, double, const double *, const double *, const double *, \
+                                    const double *, const double *, double *, void *, unsigned long long *,     \
+                                    cudaStream_t);                                                             \
+    template cudaError_t run_to_real<R>(long long, const double *, void *, cudaStream_t);
+INST(float)
+INST(double)
+#undef INST
+
+}  // namespace porta

@@ -1,0 +1,26 @@
+// Launchers of the per-voxel kernels (see.cu); internal to the library.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "porta.h"
+
+namespace porta {
+
+template <typename Real>
+cudaError_t run_profile_norm(long long nvox, int nray, int nnu, const double *mu, const double *xf, const double *wf,
+                             const double *vel, void *invn, cudaStream_t st);
+template <typename Real>
+cudaError_t run_rho_convert(long long nvox, int nl, const double *rho, void *out, cudaStream_t st);
+template <typename Real, int NS>
+cudaError_t run_jkq_finalize(long long nvox, int nray, const void *part, const double *tw, double *jkq, double *lstar,
+                             cudaStream_t st);
+template <typename Real>
+cudaError_t run_see(long long nvox, int nl, int model, double bcrit, const double *eps, const double *bpl,
+                    const double *bvec, const double *jkq, const double *lstar, double *rho, void *rhoR,
+                    unsigned long long *resid, cudaStream_t st);
+cudaError_t run_count_bad(long long n, const double *x, double lo_excl, double hi_incl, unsigned long long *bad,
+                          cudaStream_t st);
+template <typename Real>
+cudaError_t run_to_real(long long n, const double *x, void *y, cudaStream_t st);
+
+}  // namespace porta
