@@ -186,6 +186,21 @@ int porta_emergent_stokes(porta_ctx *c, int ndir, const double *mu, const double
    (may be NULL). Runs a full formal solution. */
 int porta_probe_ray(porta_ctx *c, int m, double *out, double *lstar, int where);
 
+/* Autotuner of the sweep launch shape: times every fitting (cluster size,
+   frequencies per pass) candidate on one wave of rays of the current problem
+   (CUDA events on the context's stream), keeps the fastest for subsequent
+   calls and returns it in *cluster / *nu_group (either may be NULL).
+   Requires the atmosphere and rho. Overwrites the device-side partial
+   integrals (call porta_formal_solve afterwards). */
+int porta_autotune(porta_ctx *c, int *cluster, int *nu_group);
+
+/* Diagnostic: the coefficients of the BESSER-DELO step (Eqs. 8-12; Table 1
+   series at small optical path) exactly as the sweep kernels of the given
+   precision evaluate them, for n upwind optical paths t (host array, t > 0):
+   out[6*i + 0..5] = e^-t, psi'_M, psi'_O, omega_M, omega_O, omega_C (host).
+   Synchronous; uses the current device. */
+int porta_eval_coefficients(int precision, int n, const double *t, double *out);
+
 /* Launch statistics of the last formal solution: clusters launched, CTAs per
    cluster, frequencies per pass, dynamic shared memory per CTA (bytes). */
 int porta_launch_info(const porta_ctx *c, int *clusters, int *cluster_size, int *nu_group, int *smem_bytes);

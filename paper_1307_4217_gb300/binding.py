@@ -64,6 +64,8 @@ _SIGS = {
     "porta_emergent_stokes": (_I, [_P, _I, _P, _P, _P, _I]),
     "porta_probe_ray": (_I, [_P, _I, _P, _P, _I]),
     "porta_launch_info": (_I, [_P, _P, _P, _P, _P]),
+    "porta_autotune": (_I, [_P, _P, _P]),
+    "porta_eval_coefficients": (_I, [_I, _I, _P, _P]),
 }
 
 _lib = None
@@ -108,7 +110,10 @@ def _ptr_where(a):
             raise TypeError("device arrays must be contiguous float64 CUDA tensors")
         return a.data_ptr(), PORTA_DEVICE, a
     if a.__class__.__module__.startswith("torch"):
-        a = a.detach().cpu().numpy()
+        import torch
+        if a.dtype == torch.float64 and a.is_contiguous():
+            return a.data_ptr(), PORTA_HOST, a      # host tensor (e.g. pinned memory), no copy
+        a = a.detach().contiguous().to(torch.float64).numpy()
         return _ptr_where(a)
     a = np.ascontiguousarray(a, dtype=np.float64)
     return a.ctypes.data, PORTA_HOST, a
@@ -181,6 +186,19 @@ def porta_emergent_stokes(h, ndir, mu_ptr, chi_ptr, out_ptr, where):
 
 def porta_probe_ray(h, m, out_ptr, lstar_ptr, where):
     return lib().porta_probe_ray(h, m, out_ptr, lstar_ptr, where)
+
+
+def porta_autotune(h):
+    cl, nu = ctypes.c_int(), ctypes.c_int()
+    rc = lib().porta_autotune(h, ctypes.byref(cl), ctypes.byref(nu))
+    return rc, dict(cluster=cl.value, nu_group=nu.value)
+
+
+def porta_eval_coefficients(precision, t):
+    t = np.ascontiguousarray(t, dtype=np.float64)
+    out = np.zeros((len(t), 6))
+    rc = lib().porta_eval_coefficients(precision, len(t), t.ctypes.data, out.ctypes.data)
+    return rc, out
 
 
 def porta_launch_info(h):
@@ -305,6 +323,11 @@ class Context:
         ls = np.zeros((self.nnu,) + self.shape)
         self._check(porta_probe_ray(self.h, m, out.ctypes.data, ls.ctypes.data, PORTA_HOST))
         return out, ls
+
+    def autotune(self):
+        rc, r = porta_autotune(self.h)
+        self._check(rc)
+        return r
 
     def launch_info(self):
         rc, info = porta_launch_info(self.h)

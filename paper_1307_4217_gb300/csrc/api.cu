@@ -166,7 +166,7 @@ RayDev<Real> ray_dev(double mu, double chi)
 int ns_of(int model) { return model == PORTA_MODEL_TWOLEVEL_UNPOL ? 1 : 4; }
 int nl_of(int model) { return model == PORTA_MODEL_TWOLEVEL_UNPOL ? 1 : 6; }
 
-const int kThreads = 256;
+const int kThreads = 512;   // maximum threads per CTA of the sweep kernel
 const int kSmemLimit = 220 * 1024;
 
 // Launch shape of the sweep: cluster size C (CTAs sharing one ray's plane)
@@ -180,8 +180,9 @@ int choose_launch(porta_ctx *c, LaunchCfg &best, int force_c, int force_f, int n
     const int NW = NS == 1 ? 4 : 8;
     double best_cost = 1e300;
     best = LaunchCfg{};
-    for (int C : {1, 2, 4, 8, 16}) {
+    for (int C = 1; C <= 16; ++C) {
         if (force_c > 0 && C != force_c) continue;
+        if (force_c <= 0 && C > 1 && (C & (C - 1)) != 0 && C != 6 && C != 12) continue;   // heuristic set
         if (C > c->ny) continue;
         int rmax = (c->ny + C - 1) / C;
         long long ring = 3LL * (rmax + 2) * c->nx * NW * (long long)sizeof(Real);
@@ -195,8 +196,11 @@ int choose_launch(porta_ctx *c, LaunchCfg &best, int force_c, int force_f, int n
         int G = (c->n_nu + fmax - 1) / fmax;
         int F = (c->n_nu + G - 1) / G;
         int smem = (int)(ring + F * per_nu);
+        // threads per CTA: one per owned point, rounded to whole warps, 64..512
+        int pts_i = rmax * c->nx;
+        int threads = std::min(kThreads, std::max(64, (pts_i + 31) / 32 * 32));
         int act = 0;
-        if (max_active_clusters<Real, NS>(C, smem, kThreads, &act) != cudaSuccess) {
+        if (max_active_clusters<Real, NS>(C, smem, threads, &act) != cudaSuccess) {
             cudaGetLastError();
             continue;
         }
@@ -204,19 +208,43 @@ int choose_launch(porta_ctx *c, LaunchCfg &best, int force_c, int force_f, int n
         int ncl = std::min(act, nitems);
         double waves = std::ceil((double)nitems / ncl);
         double pts = (double)rmax * c->nx;
-        double slots = std::ceil(pts / kThreads) * kThreads;   // thread slots per frequency
+        double slots = std::ceil(pts / threads) * kThreads;    // per-SM issue slots per frequency
         double per_plane = G * (slots * F + 0.15 * (rmax + 2) * c->nx + 0.05 * pts + 300.0);
         double cost = waves * per_plane;
         if (cost < best_cost) {
             best_cost = cost;
             best.cluster = C;
             best.F = F;
-            best.threads = kThreads;
+            best.threads = threads;
             best.smem = smem;
             best.clusters = ncl;
         }
     }
     return best.cluster > 0 ? PORTA_OK : PORTA_EINVAL;
+}
+
+// all launch shapes that fit, with their resident-cluster counts
+template <typename Real, int NS>
+std::vector<LaunchCfg> candidates(porta_ctx *c, int nitems)
+{
+    // every cluster size 1..16 (cluster shapes that are not powers of two can
+    // tile the GPU's SM groups better); the three largest frequency passes that fit
+    std::vector<LaunchCfg> out;
+    for (int C = 1; C <= 16; ++C) {
+        if (C > c->ny) continue;
+        int last_f = -1, kept = 0;
+        for (int G = 1; G <= c->n_nu && kept < 3; ++G) {
+            int F = (c->n_nu + G - 1) / G;
+            if (F == last_f) continue;
+            last_f = F;
+            LaunchCfg cfg;
+            if (choose_launch<Real, NS>(c, cfg, C, F, nitems) == PORTA_OK && cfg.F == F) {
+                out.push_back(cfg);
+                ++kept;
+            }
+        }
+    }
+    return out;
 }
 
 template <typename Real>
@@ -267,6 +295,58 @@ int formal_solve_t(porta_ctx *c, int probe_ray, Real *probe, Real *probe_ls)
     if (e != cudaSuccess) return fail(c, PORTA_ECUDA, std::string("sweep launch: ") + cudaGetErrorString(e));
     c->last = cfg;
     return PORTA_OK;
+}
+
+template <typename Real>
+int autotune_t(porta_ctx *c)
+{
+    std::vector<LaunchCfg> cand = c->ns == 1 ? candidates<Real, 1>(c, c->nray) : candidates<Real, 4>(c, c->nray);
+    if (cand.empty()) return fail(c, PORTA_EINVAL, "autotune: no launch shape fits");
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    double best = 1e300;
+    LaunchCfg pick = cand[0];
+    int rc = PORTA_OK;
+    for (const LaunchCfg &cfg0 : cand) {
+        LaunchCfg cfg = cfg0;
+        SweepArgs<Real> a = base_args<Real>(c);
+        a.geom = (const PlaneGeom<Real> *)c->d_geom;
+        a.rays = (const RayDev<Real> *)c->d_rays;
+        a.invn = (const Real *)c->d_invn;
+        a.part = c->d_part;
+        a.F = cfg.F;
+        a.ngroups = (c->n_nu + cfg.F - 1) / cfg.F;
+        a.rmax = (c->ny + cfg.cluster - 1) / cfg.cluster;
+        a.nitems = cfg.clusters;                    // one wave: every resident cluster sweeps one ray
+        float ms = 1e30f;
+        for (int rep = 0; rep < 2 && rc == PORTA_OK; ++rep) {
+            cudaError_t e = cudaEventRecord(e0, c->stream);
+            if (e == cudaSuccess)
+                e = c->ns == 1 ? launch_sweep<Real, 1>(a, MODE_JKQ, cfg, c->stream) : launch_sweep<Real, 4>(a, MODE_JKQ, cfg, c->stream);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float t = 0;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+            if (e != cudaSuccess) rc = fail(c, PORTA_ECUDA, std::string("autotune: ") + cudaGetErrorString(e));
+            ms = std::min(ms, t);
+        }
+        if (rc != PORTA_OK) break;
+        double waves = std::ceil((double)c->nray / cfg.clusters);
+        double est = ms * waves;
+        if (est < best) {
+            best = est;
+            pick = cfg;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc == PORTA_OK) {
+        c->opt_cluster = pick.cluster;
+        c->opt_nu_group = pick.F;
+        c->have_fs = c->have_jkq = false;
+    }
+    return rc;
 }
 
 template <typename Real>
@@ -774,6 +854,33 @@ int porta_probe_ray(porta_ctx *c, int m, double *out, double *lstar, int where)
     if (rc == PORTA_OK) {
         c->have_fs = true;
         c->have_jkq = false;
+    }
+    return rc;
+}
+
+int porta_eval_coefficients(int precision, int n, const double *t, double *out)
+{
+    if (n < 1 || !t || !out || (precision != PORTA_FP32 && precision != PORTA_FP64)) return PORTA_EINVAL;
+    for (int i = 0; i < n; ++i)
+        if (!(t[i] > 0) || !std::isfinite(t[i])) return PORTA_EINVAL;
+    double *d = nullptr;
+    if (cudaMalloc(&d, sizeof(double) * 7 * (size_t)n) != cudaSuccess) return PORTA_ENOMEM;
+    cudaError_t e = cudaMemcpy(d, t, sizeof(double) * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = precision == PORTA_FP32 ? run_coefficients<float>(n, d, d + n, nullptr) : run_coefficients<double>(n, d, d + n, nullptr);
+    if (e == cudaSuccess) e = cudaMemcpy(out, d + n, sizeof(double) * 6 * (size_t)n, cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    return e == cudaSuccess ? PORTA_OK : PORTA_ECUDA;
+}
+
+int porta_autotune(porta_ctx *c, int *cluster, int *nu_group)
+{
+    if (!c) return PORTA_EINVAL;
+    if (!c->have_atm || !c->have_rho) return fail(c, PORTA_ESTATE, "autotune: atmosphere or rho not set");
+    int rc = c->precision == PORTA_FP32 ? autotune_t<float>(c) : autotune_t<double>(c);
+    if (rc == PORTA_OK) {
+        if (cluster) *cluster = c->opt_cluster;
+        if (nu_group) *nu_group = c->opt_nu_group;
     }
     return rc;
 }

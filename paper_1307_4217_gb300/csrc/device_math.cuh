@@ -32,14 +32,23 @@ __host__ __device__ constexpr double c_wm(int k) { return sgn_d(k) * k * (k + 1.
 __host__ __device__ constexpr double c_wo(int k) { return 2.0 * sgn_d(k) / fact_d(k + 2); }
 __host__ __device__ constexpr double c_wc(int k) { return 2.0 * sgn_d(k) * k / fact_d(k + 2); }
 
-// t * (a_1 + t (a_2 + ... + t a_N)) with a_k = coef(k), N = DEG
+// t * (a_1 + t (a_2 + ... + t a_N)) with a_k = COEF(k), N = DEG; every
+// coefficient is a compile-time constant of type Real.
+template <typename Real, double (*COEF)(int), int K, int DEG>
+__device__ __forceinline__ Real horner_tail(Real t)
+{
+    constexpr double c = COEF(K);
+    if constexpr (K == DEG) {
+        return Real(c);
+    } else {
+        return Real(c) + t * horner_tail<Real, COEF, K + 1, DEG>(t);
+    }
+}
+
 template <typename Real, int DEG, double (*COEF)(int)>
 __device__ __forceinline__ Real horner(Real t)
 {
-    Real r = Real(COEF(DEG));
-#pragma unroll
-    for (int k = DEG - 1; k >= 1; --k) r = r * t + Real(COEF(k));
-    return r * t;
+    return t * horner_tail<Real, COEF, 1, DEG>(t);
 }
 
 // Double precision: degree 8 (the order of Table 1), crossovers of Table 1
@@ -58,47 +67,84 @@ __device__ __forceinline__ Coef<double> coefficients(double t)
     return c;
 }
 
-// Single precision: degree-12 series; crossovers chosen where the series
-// truncation error and the cancellation error of the closed form (evaluated
-// in FP32) are equal, which keeps every coefficient within ~3e-7 relative
-// of its exact value for all t > 0.
+// Single precision: three regimes, chosen so that every coefficient stays
+// within 6e-7 relative of its exact value for all t > 0 when evaluated in
+// FP32: degree-7 series for t < 0.25, degree-12 series for t < 1.5, closed
+// forms above (where their cancellation costs at most a factor ~5).
 __device__ __forceinline__ Coef<float> coefficients(float t)
 {
     Coef<float> c;
-    float e = expf(-t);
-    c.e = e;
-    float it = 1.0f / t, it2 = it * it;
-    c.pm = t < 0.95f ? horner<float, 12, c_pm>(t) : (1.0f - e * (1.0f + t)) * it;
-    c.po = t < 0.95f ? horner<float, 12, c_po>(t) : (e + t - 1.0f) * it;
-    c.wm = t < 1.55f ? horner<float, 12, c_wm>(t) : (2.0f - e * (t * t + 2.0f * t + 2.0f)) * it2;
-    c.wo = t < 2.35f ? horner<float, 12, c_wo>(t) : 1.0f - 2.0f * (e + t - 1.0f) * it2;
-    c.wc = t < 1.45f ? horner<float, 12, c_wc>(t) : 2.0f * (t - 2.0f + e * (t + 2.0f)) * it2;
+    c.e = expf(-t);
+    if (t < 0.25f) {
+        c.pm = horner<float, 7, c_pm>(t);
+        c.po = horner<float, 7, c_po>(t);
+        c.wm = horner<float, 7, c_wm>(t);
+        c.wo = horner<float, 7, c_wo>(t);
+        c.wc = horner<float, 7, c_wc>(t);
+    } else if (t < 1.5f) {
+        c.pm = horner<float, 12, c_pm>(t);
+        c.po = horner<float, 12, c_po>(t);
+        c.wm = horner<float, 12, c_wm>(t);
+        c.wo = horner<float, 12, c_wo>(t);
+        c.wc = horner<float, 12, c_wc>(t);
+    } else {
+        const float e = c.e, it = 1.0f / t, it2 = it * it;
+        const float d1 = e + t - 1.0f;
+        c.pm = (1.0f - e * (1.0f + t)) * it;
+        c.po = d1 * it;
+        c.wm = (2.0f - e * (t * t + 2.0f * t + 2.0f)) * it2;
+        c.wo = 1.0f - 2.0f * d1 * it2;
+        c.wc = 2.0f * (t - 2.0f + e * (t + 2.0f)) * it2;
+    }
     return c;
 }
 
-__device__ __forceinline__ double exp_dev(double x) { return exp(x); }
-__device__ __forceinline__ float exp_dev(float x) { return expf(x); }
+// reciprocal: IEEE in FP64; in FP32 the fast approximate division (max 2 ulp
+// for the |x| < 2^126 seen here), since the FP32 form's error budget is 1e-5
+__device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+__device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
 
 // ---------------------------------------------------------------------------
 // BESSER upwind control point c_M of the quadratic Bezier spline on MO
 // (Sec. 3.2, steps 1-9); ihM = 1/h_M, ihP = 1/h_P, ihMP = 1/(h_M + h_P).
 // ---------------------------------------------------------------------------
+// Per-update constants shared by the four Stokes parameters:
+//   g.a = h_M/(h_P (h_M + h_P)), g.b = h_P/(h_M (h_M + h_P)), so that the derivative
+//   of Eq. 6 is y'_O = g.a (y_P - y_O) + g.b (y_O - y_M);
+//   g.hm2 = h_M/2, g.hp2 = h_P/2, g.r = h_M/h_P.
 template <typename Real>
-__device__ __forceinline__ Real control_point(Real yM, Real yO, Real yP, Real hM, Real hP,
-                                              Real ihM, Real ihP, Real ihMP)
+struct BesserGeom {
+    Real a, b, hm2, hp2, r;
+};
+
+template <typename Real>
+__device__ __forceinline__ BesserGeom<Real> besser_geom(Real hM, Real hP)
 {
-    Real dM = (yO - yM) * ihM;                       // step 1
-    Real dP = (yP - yO) * ihP;
-    if (dM * dP <= Real(0)) return yO;               // step 2: extremum at O
-    Real yp = (hM * dP + hP * dM) * ihMP;            // step 3 (Eq. 6)
-    Real cM = yO - Real(0.5) * hM * yp;              // step 4
-    Real cP = yO + Real(0.5) * hP * yp;
-    if (cM < fmin(yM, yO) || cM > fmax(yM, yO))      // step 5
-        return yM;                                   // step 6: overshoot in MO
-    if (cP < fmin(yO, yP) || cP > fmax(yO, yP))      // step 7: overshoot in OP
-        cP = yP;
-    yp = (cP - yO) * Real(2) * ihP;                  // step 8
-    return yO - Real(0.5) * hM * yp;                 // step 9
+    BesserGeom<Real> g;
+    const Real is = rcp(hM + hP);
+    const Real ihM = rcp(hM), ihP = rcp(hP);
+    g.a = hM * ihP * is;
+    g.b = hP * ihM * is;
+    g.hm2 = Real(0.5) * hM;
+    g.hp2 = Real(0.5) * hP;
+    g.r = hM * ihP;
+    return g;
+}
+
+// Branch-free form: every step is evaluated and the outcome selected, so lanes
+// of a warp that take different branches do not diverge. Interval tests use
+// the sign of products ((c - y1)(c - y2) > 0 <=> c outside [min, max]).
+template <typename Real>
+__device__ __forceinline__ Real control_point(Real yM, Real yO, Real yP, const BesserGeom<Real> &g)
+{
+    const Real dm = yO - yM, dp = yP - yO;           // step 1 (h_M d_M, h_P d_P)
+    const Real yp = g.a * dp + g.b * dm;             // step 3 (Eq. 6)
+    const Real w = g.hm2 * yp;                       // step 4: c_M = y_O - w
+    Real u = g.hp2 * yp;                             //         c_P = y_O + u
+    u = (u * (u - dp) > Real(0)) ? dp : u;           // step 7: c_P outside [y_O, y_P] -> y_P
+    const Real cM9 = yO - g.r * u;                   // steps 8-9: y'_O = 2 (c_P - y_O)/h_P
+    const Real r = ((dm - w) * w < Real(0)) ? yM : cM9;  // steps 5-6: c_M outside [y_M, y_O] -> y_M
+    return (dm * dp <= Real(0)) ? yO : r;            // step 2: extremum at O
 }
 
 // ---------------------------------------------------------------------------

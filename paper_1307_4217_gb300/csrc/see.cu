@@ -154,6 +154,21 @@ __global__ void to_real_kernel(long long n, const double *x, Real *y)
     if (i < n) y[i] = (Real)x[i];
 }
 
+// diagnostic: the sweep's coefficient function (Eqs. 8-12 / Table 1) on the GPU
+template <typename Real>
+__global__ void coefficients_kernel(int n, const double *t, double *out)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    Coef<Real> c = coefficients((Real)t[i]);
+    out[6 * i + 0] = (double)c.e;
+    out[6 * i + 1] = (double)c.pm;
+    out[6 * i + 2] = (double)c.po;
+    out[6 * i + 3] = (double)c.wm;
+    out[6 * i + 4] = (double)c.wo;
+    out[6 * i + 5] = (double)c.wc;
+}
+
 static inline unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
 template <typename Real>
@@ -202,6 +217,15 @@ cudaError_t run_to_real(long long n, const double *x, void *y, cudaStream_t st)
     to_real_kernel<Real><<<nblk(n, 256), 256, 0, st>>>(n, x, (Real *)y);
     return cudaGetLastError();
 }
+
+template <typename Real>
+cudaError_t run_coefficients(int n, const double *t, double *out, cudaStream_t st)
+{
+    coefficients_kernel<Real><<<nblk(n, 128), 128, 0, st>>>(n, t, out);
+    return cudaGetLastError();
+}
+template cudaError_t run_coefficients<float>(int, const double *, double *, cudaStream_t);
+template cudaError_t run_coefficients<double>(int, const double *, double *, cudaStream_t);
 
 #define INST(R)                                                                                                \
     template cudaError_t run_profile_norm<R>(long long, int, int, const double *, const double *, const double *,\

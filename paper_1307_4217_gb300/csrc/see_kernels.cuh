@@ -21,6 +21,8 @@ cudaError_t run_see(long long nvox, int nl, int model, double bcrit, const doubl
 cudaError_t run_count_bad(long long n, const double *x, double lo_excl, double hi_incl, unsigned long long *bad,
                           cudaStream_t st);
 template <typename Real>
+cudaError_t run_coefficients(int n, const double *t, double *out, cudaStream_t st);
+template <typename Real>
 cudaError_t run_to_real(long long n, const double *x, void *y, cudaStream_t st);
 
 }  // namespace porta

@@ -13,13 +13,16 @@
 // between planes. The only cross-CTA data is the first sheared row of the next
 // strip, read from that CTA's shared memory (DSMEM) after a cluster barrier.
 //
-// Shared memory per CTA:
-//   ring[3][rows+2][nx][NW]   frequency-independent node data of planes q-1, q, q+1
-//                             (own rows plus one halo row on each side, recomputed
-//                             locally from global memory);
-//   ibuf[2][F][rows][nx][NS]  Stokes vectors of planes q-1 and q for F frequencies.
+// Shared memory per CTA (planes of 16-byte chunks, [chunk][row][col], so that
+// neighbouring threads read neighbouring 16-byte words):
+//   ring[3][NW/chunk][rows+2][nx]  frequency-independent node data of planes
+//                             q-1, q, q+1 (own rows plus one halo row on each
+//                             side, recomputed locally from global memory);
+//   ibuf[2][F][NS/chunk][rows][nx] Stokes vectors of planes q-1 and q for F
+//                             frequencies.
 // Each thread owns points of its strip and loops over the F frequencies of the
-// pass, reusing the ring data of its 9 stencil nodes, and accumulates the
+// pass, keeping the weighted data of its 8 stencil corners in registers, and
+// accumulates the
 // frequency-integrated Stokes I, Q, U and Lambda* of its point in registers;
 // one store (or read-modify-write for later frequency passes) per point and
 // plane writes the per-ray partial integrals.
@@ -46,6 +49,13 @@ struct alignas(4 * sizeof(Real)) R4 { Real x, y, z, w; };
 template <typename Real>
 struct alignas(2 * sizeof(Real)) R2 { Real x, y; };
 
+// 16-byte vector of the shared-memory layouts: all ring and Stokes planes are
+// stored as planes of 16-byte chunks, [chunk][row][col], so that consecutive
+// threads (consecutive columns) read consecutive 16-byte words (no bank conflicts).
+template <typename Real> struct V16;
+template <> struct V16<float> { using T = float4; };
+template <> struct V16<double> { using T = double2; };
+
 // ---- node data: chi, s (Doppler shift along the ray), [b = 2 gbar zeta B.Omega],
 //      S_I, [S_Q, S_U, S^0_0], invN (profile normalization) -------------------
 template <typename Real, int NS>
@@ -61,90 +71,109 @@ struct Node<Real, 4> {
 };
 
 template <typename Real, int NS>
-__device__ __forceinline__ Node<Real, NS> load_node(const Real *p)
+__device__ __forceinline__ Node<Real, NS> unpack_node(const Real *w)
 {
     Node<Real, NS> n;
-    if constexpr (sizeof(Real) == 4) {
-        const float4 *q = reinterpret_cast<const float4 *>(p);
-        float4 a = q[0];
-        if constexpr (NS == 1) {
-            n.chi = a.x; n.s = a.y; n.S = a.z; n.invn = a.w;
-        } else {
-            float4 b = q[1];
-            n.chi = a.x; n.s = a.y; n.b = a.z; n.SI = a.w;
-            n.SQ = b.x; n.SU = b.y; n.S00 = b.z; n.invn = b.w;
-        }
+    if constexpr (NS == 1) {
+        n.chi = w[0]; n.s = w[1]; n.S = w[2]; n.invn = w[3];
     } else {
-        const double2 *q = reinterpret_cast<const double2 *>(p);
-        double2 a = q[0], b = q[1];
-        if constexpr (NS == 1) {
-            n.chi = a.x; n.s = a.y; n.S = b.x; n.invn = b.y;
-        } else {
-            double2 c = q[2], d = q[3];
-            n.chi = a.x; n.s = a.y; n.b = b.x; n.SI = b.y;
-            n.SQ = c.x; n.SU = c.y; n.S00 = d.x; n.invn = d.y;
-        }
+        n.chi = w[0]; n.s = w[1]; n.b = w[2]; n.SI = w[3];
+        n.SQ = w[4]; n.SU = w[5]; n.S00 = w[6]; n.invn = w[7];
     }
     return n;
 }
 
 template <typename Real, int NS>
-__device__ __forceinline__ void store_node(Real *p, const Node<Real, NS> &n)
+__device__ __forceinline__ Node<Real, NS> ring_load(const typename V16<Real>::T *ring, int plane_stride,
+                                                    int chunk_stride, int slot, int idx)
 {
-    if constexpr (sizeof(Real) == 4) {
-        float4 *q = reinterpret_cast<float4 *>(p);
-        if constexpr (NS == 1) {
-            q[0] = make_float4(n.chi, n.s, n.S, n.invn);
+    constexpr int NW = node_words<NS>();
+    constexpr int NCH = NW * (int)sizeof(Real) / 16;
+    constexpr int PER = 16 / (int)sizeof(Real);
+    Real w[NW];
+    const typename V16<Real>::T *p = ring + slot * plane_stride + idx;
+#pragma unroll
+    for (int h = 0; h < NCH; ++h) {
+        typename V16<Real>::T v = p[h * chunk_stride];
+        if constexpr (PER == 4) {
+            w[4 * h] = v.x; w[4 * h + 1] = v.y; w[4 * h + 2] = v.z; w[4 * h + 3] = v.w;
         } else {
-            q[0] = make_float4(n.chi, n.s, n.b, n.SI);
-            q[1] = make_float4(n.SQ, n.SU, n.S00, n.invn);
-        }
-    } else {
-        double2 *q = reinterpret_cast<double2 *>(p);
-        if constexpr (NS == 1) {
-            q[0] = make_double2(n.chi, n.s);
-            q[1] = make_double2(n.S, n.invn);
-        } else {
-            q[0] = make_double2(n.chi, n.s);
-            q[1] = make_double2(n.b, n.SI);
-            q[2] = make_double2(n.SQ, n.SU);
-            q[3] = make_double2(n.S00, n.invn);
+            w[2 * h] = v.x; w[2 * h + 1] = v.y;
         }
     }
+    return unpack_node<Real, NS>(w);
 }
 
 template <typename Real, int NS>
-__device__ __forceinline__ void load_stokes(const Real *p, Real v[NS])
+__device__ __forceinline__ void ring_store(typename V16<Real>::T *ring, int plane_stride, int chunk_stride, int slot,
+                                           int idx, const Node<Real, NS> &n)
 {
+    constexpr int NW = node_words<NS>();
+    constexpr int NCH = NW * (int)sizeof(Real) / 16;
+    constexpr int PER = 16 / (int)sizeof(Real);
+    Real w[NW];
     if constexpr (NS == 1) {
-        v[0] = p[0];
-    } else if constexpr (sizeof(Real) == 4) {
-        float4 a = *reinterpret_cast<const float4 *>(p);
-        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+        w[0] = n.chi; w[1] = n.s; w[2] = n.S; w[3] = n.invn;
     } else {
-        double2 a = reinterpret_cast<const double2 *>(p)[0], b = reinterpret_cast<const double2 *>(p)[1];
-        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+        w[0] = n.chi; w[1] = n.s; w[2] = n.b; w[3] = n.SI; w[4] = n.SQ; w[5] = n.SU; w[6] = n.S00; w[7] = n.invn;
+    }
+    typename V16<Real>::T *p = ring + slot * plane_stride + idx;
+#pragma unroll
+    for (int h = 0; h < NCH; ++h) {
+        typename V16<Real>::T v;
+        if constexpr (PER == 4) {
+            v.x = w[4 * h]; v.y = w[4 * h + 1]; v.z = w[4 * h + 2]; v.w = w[4 * h + 3];
+        } else {
+            v.x = w[2 * h]; v.y = w[2 * h + 1];
+        }
+        p[h * chunk_stride] = v;
     }
 }
 
+// Stokes-vector planes: NS = 4 as 16-byte chunk planes ([chunk][row][col]);
+// NS = 1 as a plane of scalars.
 template <typename Real, int NS>
-__device__ __forceinline__ void store_stokes(Real *p, const Real v[NS])
-{
-    if constexpr (NS == 1) {
-        p[0] = v[0];
-    } else if constexpr (sizeof(Real) == 4) {
-        *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
-    } else {
-        reinterpret_cast<double2 *>(p)[0] = make_double2(v[0], v[1]);
-        reinterpret_cast<double2 *>(p)[1] = make_double2(v[2], v[3]);
+struct StokesIO {
+    static constexpr int ICH = NS == 1 ? 1 : 4 * (int)sizeof(Real) / 16;
+    // element offset (in units of Real) of chunk 0 of point idx in plane (buf, f)
+    __device__ static __forceinline__ void load(const Real *plane, int chunk_stride, int idx, Real v[NS])
+    {
+        if constexpr (NS == 1) {
+            v[0] = plane[idx];
+        } else if constexpr (sizeof(Real) == 4) {
+            float4 a = reinterpret_cast<const float4 *>(plane)[idx];
+            v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+        } else {
+            const double2 *p = reinterpret_cast<const double2 *>(plane);
+            double2 a = p[idx], b = p[idx + chunk_stride];
+            v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+        }
     }
-}
+    __device__ static __forceinline__ void store(Real *plane, int chunk_stride, int idx, const Real v[NS])
+    {
+        if constexpr (NS == 1) {
+            plane[idx] = v[0];
+        } else if constexpr (sizeof(Real) == 4) {
+            reinterpret_cast<float4 *>(plane)[idx] = make_float4(v[0], v[1], v[2], v[3]);
+        } else {
+            double2 *p = reinterpret_cast<double2 *>(plane);
+            p[idx] = make_double2(v[0], v[1]);
+            p[idx + chunk_stride] = make_double2(v[2], v[3]);
+        }
+    }
+    // Reals per (buf, f) plane
+    __host__ __device__ static constexpr int plane_reals(int pts) { return NS * pts; }
+};
 
-// Profile shape exp(-(x - s)^2). In FP32 the exponent is capped at 80 so that
-// eta_I = chi * shape stays a nonzero (possibly subnormal) number far in the
-// wings instead of underflowing to zero; the capped terms are below 2e-35
-// relative to line centre.
-__device__ __forceinline__ float profile_shape(float xs) { return expf(-fminf(xs * xs, 80.0f)); }
+// Profile shape exp(-(x - s)^2). In FP32 it is evaluated as a power of two
+// (the rounding of the FP32 argument x - s already bounds its accuracy to
+// ~1e-7 (x-s)^2 relative), and the exponent is capped at 60 so that eta_I and
+// its reciprocal stay normal numbers far in the wings; the capped terms are
+// below 1e-26 relative to line centre, where the optical paths vanish.
+__device__ __forceinline__ float profile_shape(float xs)
+{
+    return exp2f(fminf(xs * xs, 60.0f) * -1.4426950408889634f);
+}
 __device__ __forceinline__ double profile_shape(double xs) { return exp(-xs * xs); }
 
 // ---- the per-ray, per-plane node data (a2: frequency-independent part) ----
@@ -176,17 +205,51 @@ __device__ __forceinline__ Node<Real, NS> make_node(const SweepArgs<Real> &a, co
     return n;
 }
 
-__device__ __forceinline__ int wrapi(int a, int n)
+
+// frequency-independent data of an interpolation corner, with the bilinear
+// weight folded into the opacity: upwind corners keep b and S^0_0 separately
+// (eta_V and eps_V are both interpolated), downwind corners only their product.
+template <typename Real, int NS> struct CornerM;
+template <typename Real> struct CornerM<Real, 1> { Real wchi, s, S; };
+template <typename Real> struct CornerM<Real, 4> { Real wchi, s, b, SI, SQ, SU, S00; };
+template <typename Real, int NS> struct CornerP;
+template <typename Real> struct CornerP<Real, 1> { Real wchi, s, S; };
+template <typename Real> struct CornerP<Real, 4> { Real wchi, s, bS, SI, SQ, SU; };
+
+template <typename Real, int NS>
+__device__ __forceinline__ CornerM<Real, NS> corner_m(const Node<Real, NS> &n, Real w)
 {
-    int r = a % n;
-    return r < 0 ? r + n : r;
+    CornerM<Real, NS> c;
+    c.wchi = w * n.chi;
+    c.s = n.s;
+    if constexpr (NS == 1) {
+        c.S = n.S;
+    } else {
+        c.b = n.b; c.SI = n.SI; c.SQ = n.SQ; c.SU = n.SU; c.S00 = n.S00;
+    }
+    return c;
+}
+
+template <typename Real, int NS>
+__device__ __forceinline__ CornerP<Real, NS> corner_p(const Node<Real, NS> &n, Real w)
+{
+    CornerP<Real, NS> c;
+    c.wchi = w * n.chi;
+    c.s = n.s;
+    if constexpr (NS == 1) {
+        c.S = n.S;
+    } else {
+        c.bS = n.b * n.S00; c.SI = n.SI; c.SQ = n.SQ; c.SU = n.SU;
+    }
+    return c;
 }
 
 template <typename Real, int NS, int MODE>
-__device__ __forceinline__ void sweep_item(const SweepArgs<Real> &a, cg::cluster_group &cluster, Real *ring,
-                                           Real *ibuf, Real *ibuf_next, int m, int g, int row0, int R, int dir_out)
+__device__ __forceinline__ void sweep_item(const SweepArgs<Real> &a, cg::cluster_group &cluster,
+                                           typename V16<Real>::T *ring, Real *ibuf, Real *ibuf_next, int m, int g,
+                                           int row0, int R, int dir_out)
 {
-    constexpr int NW = node_words<NS>();
+    using V = typename V16<Real>::T;
     const int nx = a.nx, ny = a.ny, nz = a.nz, F = a.F, rmax = a.rmax;
     const int j0 = g * F;
     const int nf = min(F, a.nnu - j0);
@@ -196,19 +259,35 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<Real> &a, cg::cluster
     const long long nxy = (long long)nx * ny;
     const bool jmode = (MODE == MODE_JKQ);
     const int tid = threadIdx.x, nt = blockDim.x;
-    const int ring_plane = (rmax + 2) * nx * NW;
+    constexpr int NCH = node_words<NS>() * (int)sizeof(Real) / 16;
+    const int chunk = (rmax + 2) * nx;              // ring chunk-plane stride (V units)
+    const int plane = NCH * chunk;                  // ring plane stride (V units)
+    const int ipts = rmax * nx;                     // points per Stokes plane
+    const int ichunk = ipts;                        // Stokes chunk-plane stride (16-byte chunks)
+    const int iplane = NS * ipts;                   // Reals per (buf, f) Stokes plane
     const int npts = R * nx;
+
+    // thread -> (row, column) stepping without integer division: idx = tid + k*nt
+    const int dl = nt / nx, dc = nt - dl * nx;
+    const int l0 = tid / nx, c0 = tid - l0 * nx;
 
     auto fill = [&](int q) {
         const PlaneGeom<Real> gq = G[q];
-        Real *slot = ring + (q % 3) * ring_plane;
         const int nn = (R + 2) * nx;
+        const long long kbase = (long long)gq.kz * ny;
+        int lr = l0, c = c0;                     // lr = ring row (local row + 1)
         for (int idx = tid; idx < nn; idx += nt) {
-            int l = idx / nx - 1, c = idx - (idx / nx) * nx;
-            int r = wrapi(row0 + l, ny);
-            int pi = wrapi(c + gq.ax, nx), pj = wrapi(r + gq.ay, ny);
-            long long v = ((long long)gq.kz * ny + pj) * nx + pi;
-            store_node<Real, NS>(slot + ((l + 1) * nx + c) * NW, make_node<Real, NS>(a, ray, v, m, jmode));
+            int pi = c + gq.ax;
+            pi -= pi >= nx ? nx : 0;
+            int pj = row0 + lr - 1 + gq.ay;      // in [-1, 2 ny]
+            pj += pj < 0 ? ny : 0;
+            pj -= pj >= ny ? ny : 0;
+            pj -= pj >= ny ? ny : 0;
+            long long v = (kbase + pj) * nx + pi;
+            ring_store<Real, NS>(ring, plane, chunk, q % 3, idx, make_node<Real, NS>(a, ray, v, m, jmode));
+            c += dc;
+            lr += dl;
+            if (c >= nx) { c -= nx; ++lr; }
         }
     };
 
@@ -219,25 +298,26 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<Real> &a, cg::cluster
         const PlaneGeom<Real> gq = G[q];
         const bool has_p = q + 1 < nz;
         const PlaneGeom<Real> gp = has_p ? G[q + 1] : gq;
-        const Real *rM = ring + ((q + 2) % 3) * ring_plane;   // plane q-1
-        const Real *rO = ring + (q % 3) * ring_plane;
-        const Real *rP = ring + ((q + 1) % 3) * ring_plane;   // plane q+1
-        Real *iw = ibuf + (q & 1) * F * rmax * nx * NS;        // write plane q
-        const int ro = ((q + 1) & 1) * F * rmax * nx * NS;     // read plane q-1
+        const int sM = (q + 2) % 3, sO = q % 3, sP = (q + 1) % 3;
+        Real *iw = ibuf + (q & 1) * F * iplane;              // write plane q
+        const int ro = ((q + 1) & 1) * F * iplane;           // read plane q-1
         const Real *ir = ibuf + ro;
         const Real *irn = ibuf_next + ro;
         // interpolation weights (uniform over the plane)
         const Real mx1 = gq.tx, mx0 = Real(1) - gq.tx, my1 = gq.ty, my0 = Real(1) - gq.ty;
         const Real px0 = gp.tx, px1 = Real(1) - gp.tx, py0 = gp.ty, py1 = Real(1) - gp.ty;
-        const Real wM[4] = {mx0 * my0, mx1 * my0, mx0 * my1, mx1 * my1};
-        const Real wP[4] = {px0 * py0, px1 * py0, px0 * py1, px1 * py1};
         const Real dsM = gq.ds, dsP = has_p ? gp.ds : Real(0);
 
-        for (int p = tid; p < npts; p += nt) {
-            const int l = p / nx, c = p - (p / nx) * nx;
-            const int pi = wrapi(c + gq.ax, nx), pj = wrapi(row0 + l + gq.ay, ny);
+        int l = l0, c = c0;
+        for (int p = tid; p < npts; p += nt, c += dc, l += dl) {
+            if (c >= nx) { c -= nx; ++l; }
+            int pi = c + gq.ax;
+            pi -= pi >= nx ? nx : 0;
+            int pj = row0 + l + gq.ay;           // in [0, 2 ny)
+            pj -= pj >= ny ? ny : 0;
+            pj -= pj >= ny ? ny : 0;
             const long long v = ((long long)gq.kz * ny + pj) * nx + pi;
-            const Node<Real, NS> nO = load_node<Real, NS>(rO + ((l + 1) * nx + c) * NW);
+            const Node<Real, NS> nO = ring_load<Real, NS>(ring, plane, chunk, sO, (l + 1) * nx + c);
             Real acc[NS == 1 ? 2 : 4];
 #pragma unroll
             for (int s = 0; s < (NS == 1 ? 2 : 4); ++s) acc[s] = Real(0);
@@ -250,7 +330,7 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<Real> &a, cg::cluster
                 if (upward) I0[0] = a.bpl[v];
                 for (int f = 0; f < nf; ++f) {
                     const int j = j0 + f;
-                    store_stokes<Real, NS>(iw + ((f * rmax + l) * nx + c) * NS, I0);
+                    StokesIO<Real, NS>::store(iw + f * iplane, ichunk, l * nx + c, I0);
                     if constexpr (MODE == MODE_JKQ) {
                         const Real wt = a.wf[j] * profile_shape(a.xf[j] - nO.s) * nO.invn;
                         acc[0] += wt * I0[0];
@@ -265,53 +345,60 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<Real> &a, cg::cluster
                 const int c1 = (c + 1 == nx) ? 0 : c + 1;
                 const int cm = (c == 0) ? nx - 1 : c - 1;
                 // upwind corners (c|c1, l|l+1) on plane q-1; downwind (cm|c, l-1|l) on plane q+1
-                const Node<Real, NS> nM[4] = {
-                    load_node<Real, NS>(rM + ((l + 1) * nx + c) * NW), load_node<Real, NS>(rM + ((l + 1) * nx + c1) * NW),
-                    load_node<Real, NS>(rM + ((l + 2) * nx + c) * NW), load_node<Real, NS>(rM + ((l + 2) * nx + c1) * NW)};
-                Node<Real, NS> nP[4];
+                CornerM<Real, NS> kM[4];
+                kM[0] = corner_m<Real, NS>(ring_load<Real, NS>(ring, plane, chunk, sM, (l + 1) * nx + c), mx0 * my0);
+                kM[1] = corner_m<Real, NS>(ring_load<Real, NS>(ring, plane, chunk, sM, (l + 1) * nx + c1), mx1 * my0);
+                kM[2] = corner_m<Real, NS>(ring_load<Real, NS>(ring, plane, chunk, sM, (l + 2) * nx + c), mx0 * my1);
+                kM[3] = corner_m<Real, NS>(ring_load<Real, NS>(ring, plane, chunk, sM, (l + 2) * nx + c1), mx1 * my1);
+                CornerP<Real, NS> kP[4];
                 if (has_p) {
-                    nP[0] = load_node<Real, NS>(rP + (l * nx + cm) * NW);
-                    nP[1] = load_node<Real, NS>(rP + (l * nx + c) * NW);
-                    nP[2] = load_node<Real, NS>(rP + ((l + 1) * nx + cm) * NW);
-                    nP[3] = load_node<Real, NS>(rP + ((l + 1) * nx + c) * NW);
+                    kP[0] = corner_p<Real, NS>(ring_load<Real, NS>(ring, plane, chunk, sP, l * nx + cm), px0 * py0);
+                    kP[1] = corner_p<Real, NS>(ring_load<Real, NS>(ring, plane, chunk, sP, l * nx + c), px1 * py0);
+                    kP[2] = corner_p<Real, NS>(ring_load<Real, NS>(ring, plane, chunk, sP, (l + 1) * nx + cm), px0 * py1);
+                    kP[3] = corner_p<Real, NS>(ring_load<Real, NS>(ring, plane, chunk, sP, (l + 1) * nx + c), px1 * py1);
                 } else {
-                    nP[0] = nP[1] = nP[2] = nP[3] = nO;
+                    kP[0] = kP[1] = kP[2] = kP[3] = corner_p<Real, NS>(nO, Real(0));
                 }
+                const Real wI[4] = {mx0 * my0, mx1 * my0, mx0 * my1, mx1 * my1};
                 const bool last_row = (l + 1 == R);
-                const Real *ir_lo = ir + (l * nx) * NS;                              // row l
-                const Real *ir_hi = last_row ? irn : ir + ((l + 1) * nx) * NS;      // row l+1
+                const int ilo = l * nx;                               // row l in this CTA
+                const Real *ihi_base = last_row ? irn : ir;          // row l+1 (next CTA's row 0)
+                const int ihi = last_row ? 0 : (l + 1) * nx;
 
                 for (int f = 0; f < nf; ++f) {
                     const int j = j0 + f;
                     const Real x = a.xf[j];
-                    const int fo = f * rmax * nx * NS;
-                    // upwind Stokes vectors at the 4 corners
-                    Real IMc[4][NS];
-                    load_stokes<Real, NS>(ir_lo + fo + c * NS, IMc[0]);
-                    load_stokes<Real, NS>(ir_lo + fo + c1 * NS, IMc[1]);
-                    load_stokes<Real, NS>(ir_hi + fo + c * NS, IMc[2]);
-                    load_stokes<Real, NS>(ir_hi + fo + c1 * NS, IMc[3]);
-
-                    // a2-a3: node transfer coefficients and bilinear interpolation at M and P
-                    Real etaM = 0, etaVM = 0, epsM[NS], IM[NS];
+                    const Real *pl = ir + f * iplane;
+                    const Real *ph = ihi_base + f * iplane;
+                    // a3: upwind Stokes vector (bilinear)
+                    Real IM[NS];
+                    {
+                        Real t0[NS], t1[NS], t2[NS], t3[NS];
+                        StokesIO<Real, NS>::load(pl, ichunk, ilo + c, t0);
+                        StokesIO<Real, NS>::load(pl, ichunk, ilo + c1, t1);
+                        StokesIO<Real, NS>::load(ph, ichunk, ihi + c, t2);
+                        StokesIO<Real, NS>::load(ph, ichunk, ihi + c1, t3);
 #pragma unroll
-                    for (int s = 0; s < NS; ++s) { epsM[s] = 0; IM[s] = 0; }
+                        for (int s = 0; s < NS; ++s) IM[s] = wI[0] * t0[s] + wI[1] * t1[s] + wI[2] * t2[s] + wI[3] * t3[s];
+                    }
+                    // a2-a3: node transfer coefficients and bilinear interpolation at M and P
+                    Real etaM = 0, etaVM = 0, epsM[NS];
+#pragma unroll
+                    for (int s = 0; s < NS; ++s) epsM[s] = 0;
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
-                        const Real xs = x - nM[k].s;
-                        const Real we = wM[k] * nM[k].chi * profile_shape(xs);
+                        const Real xs = x - kM[k].s;
+                        const Real we = kM[k].wchi * profile_shape(xs);
                         etaM += we;
-#pragma unroll
-                        for (int s = 0; s < NS; ++s) IM[s] += wM[k] * IMc[k][s];
                         if constexpr (NS == 1) {
-                            epsM[0] += we * nM[k].S;
+                            epsM[0] += we * kM[k].S;
                         } else {
-                            const Real kv = nM[k].b * xs;
-                            etaVM += we * kv;
-                            epsM[0] += we * nM[k].SI;
-                            epsM[1] += we * nM[k].SQ;
-                            epsM[2] += we * nM[k].SU;
-                            epsM[3] += we * kv * nM[k].S00;
+                            const Real wkv = we * (kM[k].b * xs);
+                            etaVM += wkv;
+                            epsM[0] += we * kM[k].SI;
+                            epsM[1] += we * kM[k].SQ;
+                            epsM[2] += we * kM[k].SU;
+                            epsM[3] += wkv * kM[k].S00;
                         }
                     }
                     Real etaP = 0, epsP[NS];
@@ -320,16 +407,16 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<Real> &a, cg::cluster
                     if (has_p) {
 #pragma unroll
                         for (int k = 0; k < 4; ++k) {
-                            const Real xs = x - nP[k].s;
-                            const Real we = wP[k] * nP[k].chi * profile_shape(xs);
+                            const Real xs = x - kP[k].s;
+                            const Real we = kP[k].wchi * profile_shape(xs);
                             etaP += we;
                             if constexpr (NS == 1) {
-                                epsP[0] += we * nP[k].S;
+                                epsP[0] += we * kP[k].S;
                             } else {
-                                epsP[0] += we * nP[k].SI;
-                                epsP[1] += we * nP[k].SQ;
-                                epsP[2] += we * nP[k].SU;
-                                epsP[3] += we * nP[k].b * xs * nP[k].S00;
+                                epsP[0] += we * kP[k].SI;
+                                epsP[1] += we * kP[k].SQ;
+                                epsP[2] += we * kP[k].SU;
+                                epsP[3] += we * (kP[k].bS * xs);
                             }
                         }
                     }
@@ -337,7 +424,7 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<Real> &a, cg::cluster
                     const Real phO = profile_shape(xsO);
                     const Real etaO = nO.chi * phO;
                     Real SO[NS], SM[NS], SP[NS];
-                    const Real iM = Real(1) / etaM;
+                    const Real iM = rcp(etaM);
                     if constexpr (NS == 1) {
                         SO[0] = nO.S;
                     } else {
@@ -347,24 +434,28 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<Real> &a, cg::cluster
                     for (int s = 0; s < NS; ++s) SM[s] = epsM[s] * iM;
                     // a4: optical paths (trapezoid along MO and OP)
                     const Real tMO = Real(0.5) * (etaM + etaO) * dsM;
-                    Real tOP = Real(1), ihP = Real(1), ihMP = Real(1);
+                    Real tOP = Real(1);
                     if (has_p) {
-                        const Real iP = Real(1) / etaP;
+                        const Real iP = rcp(etaP);
 #pragma unroll
                         for (int s = 0; s < NS; ++s) SP[s] = epsP[s] * iP;
                         tOP = Real(0.5) * (etaO + etaP) * dsP;
-                        ihP = Real(1) / tOP;
-                        ihMP = Real(1) / (tMO + tOP);
+                    } else {
+#pragma unroll
+                        for (int s = 0; s < NS; ++s) SP[s] = Real(0);
                     }
-                    const Real ihM = Real(1) / tMO;
                     // a6: exponential-integral coefficients
                     const Coef<Real> co = coefficients(tMO);
                     // a5: BESSER control points per Stokes parameter
                     Real cM[NS];
+                    if (has_p) {
+                        const BesserGeom<Real> bg = besser_geom(tMO, tOP);
 #pragma unroll
-                    for (int s = 0; s < NS; ++s)
-                        cM[s] = has_p ? control_point(SM[s], SO[s], SP[s], tMO, tOP, ihM, ihP, ihMP)
-                                      : Real(0.5) * (SM[s] + SO[s]);
+                        for (int s = 0; s < NS; ++s) cM[s] = control_point(SM[s], SO[s], SP[s], bg);
+                    } else {
+#pragma unroll
+                        for (int s = 0; s < NS; ++s) cM[s] = Real(0.5) * (SM[s] + SO[s]);
+                    }
                     // a7: BESSER-DELO step (Eq. 7)
                     Real IO[NS];
                     if constexpr (NS == 1) {
@@ -380,13 +471,13 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<Real> &a, cg::cluster
                         rhs[3] -= co.pm * kvM * IM[0];
                         // kappa^-1 = 1 + psi'_O K'_O couples I and V only
                         const Real av = co.po * kvO;
-                        const Real idet = Real(1) / (Real(1) - av * av);
+                        const Real idet = rcp(Real(1) - av * av);
                         IO[0] = (rhs[0] - av * rhs[3]) * idet;
                         IO[3] = (rhs[3] - av * rhs[0]) * idet;
                         IO[1] = rhs[1];
                         IO[2] = rhs[2];
                     }
-                    store_stokes<Real, NS>(iw + ((f * rmax + l) * nx + c) * NS, IO);
+                    StokesIO<Real, NS>::store(iw + f * iplane, ichunk, l * nx + c, IO);
                     // a8: Lambda* (Eq. 13; w_O + w_C/2 on the last plane) and accumulation
                     if constexpr (MODE == MODE_JKQ) {
                         const Real ls = co.wo + (has_p ? co.wc : Real(0.5) * co.wc);
@@ -433,7 +524,7 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<Real> &a, cg::cluster
 }
 
 template <typename Real, int NS, int MODE>
-__global__ void __launch_bounds__(256, 1) sweep_kernel(const SweepArgs<Real> a)
+__global__ void __launch_bounds__(512, 1) sweep_kernel(const SweepArgs<Real> a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cg::cluster_group cluster = cg::this_cluster();
@@ -443,8 +534,9 @@ __global__ void __launch_bounds__(256, 1) sweep_kernel(const SweepArgs<Real> a)
     const int ncl = gridDim.x / C;
     const int row0 = (int)(((long long)rank * a.ny) / C);
     const int row1 = (int)(((long long)(rank + 1) * a.ny) / C);
-    Real *ring = reinterpret_cast<Real *>(smem_raw);
-    Real *ibuf = ring + 3 * (a.rmax + 2) * a.nx * node_words<NS>();
+    using V = typename V16<Real>::T;
+    V *ring = reinterpret_cast<V *>(smem_raw);
+    Real *ibuf = reinterpret_cast<Real *>(ring + 3 * (a.rmax + 2) * a.nx * (node_words<NS>() * (int)sizeof(Real) / 16));
     Real *ibuf_next = cluster.map_shared_rank(ibuf, (rank + 1) % C);
     cluster.sync();
     for (int item = cid; item < a.nitems; item += ncl) {

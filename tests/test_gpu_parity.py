@@ -68,7 +68,7 @@ def test_polarized_box_formal_solution(prec):
     _check_j(jg, lg, jo, lo, TOL[prec])
 
 
-@pytest.mark.parametrize("cluster,nu_group", [(1, 6), (2, 5), (4, 3), (8, 2), (16, 7)])
+@pytest.mark.parametrize("cluster,nu_group", [(1, 6), (2, 5), (3, 4), (4, 3), (5, 7), (6, 3), (8, 2), (12, 2), (16, 7)])
 def test_polarized_launch_shapes_agree(cluster, nu_group):
     """Every cluster size / frequency grouping gives the oracle's result; ny = 20 is
     not a multiple of 8 or 16 (ragged strips) and 21 frequencies leave a ragged pass."""
@@ -200,3 +200,18 @@ def test_device_pointers_through_the_abi():
     torch.cuda.synchronize()
     _, (jo, lo) = oracle_fs(atm, 1, 2, 4, 5, rho)
     _check_j(jd.cpu().numpy(), ld.cpu().numpy(), jo, lo, 1e-10)
+
+
+def test_autotune_picks_a_valid_shape_and_keeps_parity():
+    atm = polarized_case(16, 12, 10, seed=18)
+    rho = initial_rho(atm, 1, seed=19)
+    ctx = make_ctx(atm, 1, 2, 4, 9, P.PORTA_FP32, rho=rho)
+    pick = ctx.autotune()
+    assert 1 <= pick["cluster"] <= 16 and 1 <= pick["nu_group"] <= 9
+    ctx.set_rho(rho)
+    ctx.formal_solve()
+    info = ctx.launch_info()
+    assert (info["cluster"], info["nu_group"]) == (pick["cluster"], pick["nu_group"])
+    jg, lg = ctx.accumulate_jkq()
+    _, (jo, lo) = oracle_fs(atm, 1, 2, 4, 9, rho)
+    _check_j(jg, lg, jo, lo, 1e-5)
