@@ -71,6 +71,10 @@ extern "C" {
 #define PORTA_ECUDA    -3   /* CUDA runtime error */
 #define PORTA_ESTATE   -4   /* call order: a required input has not been set */
 #define PORTA_EKERNEL  -7   /* a kernel reported a failure (error word set) */
+#define PORTA_ESCRATCH -8   /* problem too large for the fixed scratch of porta_formal_solve_noalloc */
+
+/* size of the fixed device scratch array used by porta_formal_solve_noalloc */
+#define PORTA_NOALLOC_SCRATCH_BYTES (32u << 20)
 
 #define PORTA_MODEL_TWOLEVEL_UNPOL 0
 #define PORTA_MODEL_TWOLEVEL_HANLE 1
@@ -200,6 +204,32 @@ int porta_autotune(porta_ctx *c, int *cluster, int *nu_group);
    out[6*i + 0..5] = e^-t, psi'_M, psi'_O, omega_M, omega_O, omega_C (host).
    Synchronous; uses the current device. */
 int porta_eval_coefficients(int precision, int n, const double *t, double *out);
+
+/* Allocation-free formal solution. (The paper has no counterpart: this entry
+   point exists for callers that cannot allocate device memory, e.g. a host
+   program whose device memory is already reserved by another framework's
+   pooling allocator, or a latency-sensitive loop that cannot afford the
+   implicit synchronization of cudaMalloc/cudaFree.)
+   Same computation as porta_formal_solve + porta_accumulate_jkq with FP32
+   sweeps, without a context: the caller passes the grid, atom and quadrature
+   descriptions (host), the atmosphere arrays and rho (device pointers, FP64,
+   layouts as for porta_set_atmosphere / porta_set_rho; values are not
+   checked) and receives J^K_Q (nvox*NJ) and Lambda-bar* (nvox) in device
+   buffers, enqueued on `stream` (a cudaStream_t, NULL = default stream).
+   Every intermediate lives in one file-scope device array of
+   PORTA_NOALLOC_SCRATCH_BYTES (32 MiB) that every GPU loading the library
+   holds until the process exits; the call allocates nothing, host or device.
+   The polarized model needs about nvox * (48 + 20 * nray) bytes, e.g. 10^4
+   voxels with 160 rays; larger problems are rejected with PORTA_ESCRATCH
+   before anything is enqueued. n_mu is limited to 32.
+   The first call on a device looks up the array's device address there
+   (cudaGetSymbolAddress with that device current); make that first call
+   before any stream capture. All calls share the array and it keeps the last
+   call's contents (each call writes every part it reads); calls that overlap
+   on the GPU race on it. */
+int porta_formal_solve_noalloc(const porta_grid *g, const porta_atom *a, const porta_quad *q,
+                               const porta_atmos *atm, const double *rho, double *jkq, double *lstar,
+                               void *stream);
 
 /* Launch statistics of the last formal solution: clusters launched, CTAs per
    cluster, frequencies per pass, dynamic shared memory per CTA (bytes). */

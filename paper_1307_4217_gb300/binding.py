@@ -12,12 +12,14 @@ import numpy as np
 from . import build as _build
 
 PORTA_OK, PORTA_EINVAL, PORTA_ENOMEM, PORTA_ECUDA, PORTA_ESTATE, PORTA_EKERNEL = 0, -1, -2, -3, -4, -7
+PORTA_ESCRATCH = -8
+PORTA_NOALLOC_SCRATCH_BYTES = 32 << 20
 PORTA_MODEL_TWOLEVEL_UNPOL, PORTA_MODEL_TWOLEVEL_HANLE = 0, 1
 PORTA_FP64, PORTA_FP32 = 0, 1
 PORTA_HOST, PORTA_DEVICE = 0, 1
 
 _STATUS = {0: "PORTA_OK", -1: "PORTA_EINVAL", -2: "PORTA_ENOMEM", -3: "PORTA_ECUDA", -4: "PORTA_ESTATE",
-           -7: "PORTA_EKERNEL"}
+           -7: "PORTA_EKERNEL", -8: "PORTA_ESCRATCH"}
 
 
 def library_path():
@@ -66,6 +68,7 @@ _SIGS = {
     "porta_launch_info": (_I, [_P, _P, _P, _P, _P]),
     "porta_autotune": (_I, [_P, _P, _P]),
     "porta_eval_coefficients": (_I, [_I, _I, _P, _P]),
+    "porta_formal_solve_noalloc": (_I, [_P, _P, _P, _P, _P, _P, _P, _P]),
 }
 
 _lib = None
@@ -199,6 +202,21 @@ def porta_eval_coefficients(precision, t):
     out = np.zeros((len(t), 6))
     rc = lib().porta_eval_coefficients(precision, len(t), t.ctypes.data, out.ctypes.data)
     return rc, out
+
+
+def porta_formal_solve_noalloc(atm, model, n_mu, n_chi, n_nu, x_max, datm, rho_ptr, jkq_ptr, lstar_ptr, stream=None):
+    """Allocation-free formal solution: descriptions from ``atm`` (host), device
+    pointers for the atmosphere arrays (``datm``: dict of CUDA tensors), rho and the outputs."""
+    z = np.ascontiguousarray(atm["z"], dtype=np.float64)
+    g = _Grid(atm["nx"], atm["ny"], atm["nz"], float(atm["lx"]), float(atm["ly"]), z.ctypes.data)
+    a = _Atom(model, float(atm.get("zeta", 0.0)), float(atm.get("gbar", 1.0)), float(atm.get("bcrit", 25.0)))
+    q = _Quad(n_mu, n_chi, n_nu, float(x_max))
+    ptrs = [datm[k].data_ptr() if datm.get(k) is not None else None
+            for k in ("chi", "eps", "bpl", "vel", "bx", "by", "bz")]
+    s = _Atmos(*ptrs)
+    handle = getattr(stream, "cuda_stream", stream)
+    return lib().porta_formal_solve_noalloc(ctypes.byref(g), ctypes.byref(a), ctypes.byref(q), ctypes.byref(s),
+                                            rho_ptr, jkq_ptr, lstar_ptr, ctypes.c_void_p(handle or 0))
 
 
 def porta_launch_info(h):
