@@ -36,39 +36,57 @@ __global__ void rho_convert_kernel(long long nvox, int nl, const double *rho, Re
 }
 
 // J^K_Q(v) = sum_m w_m sum_p T^K_Q(p, m) P_p(m, v) and Lambda-bar*(v) = sum_m w_m P_L(m, v),
-// summed in FP64 over rays in ascending order (deterministic).
+// summed over rays in ascending order (deterministic). FP64 partials are summed
+// in FP64; FP32 partials (FP32 sweep) in FP32 with compensated (Kahan) sums,
+// whose error for nray terms is ~2 ulp independent of nray, instead of FP64
+// arithmetic on the GPU's low-rate FP64 pipe.
+template <typename Real>
+struct KahanSum {
+    Real s = 0, c = 0;
+    __device__ __forceinline__ void add(Real x)
+    {
+        if constexpr (sizeof(Real) == 8) {
+            s += x;                       // FP64: plain sum
+        } else {
+            Real y = x - c;
+            Real t = s + y;
+            c = (t - s) - y;
+            s = t;
+        }
+    }
+};
+
 template <typename Real, int NS>
 __global__ void jkq_finalize_kernel(long long nvox, int nray, const void *part, const double *tw,
                                     double *jkq, double *lstar)
 {
     long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (v >= nvox) return;
+    const Real *p = reinterpret_cast<const Real *>(part);
     if constexpr (NS == 1) {
-        const Real *p = reinterpret_cast<const Real *>(part);
-        double J = 0.0, L = 0.0;
+        KahanSum<Real> J, L;
         for (int m = 0; m < nray; ++m) {
             const Real *q = p + 2 * ((long long)m * nvox + v);
-            double w = tw[m * 19];
-            J += w * (double)q[0];
-            L += w * (double)q[1];
+            const Real w = (Real)tw[m * 19];
+            J.add(w * q[0]);
+            L.add(w * q[1]);
         }
-        jkq[v] = J;
-        lstar[v] = L;
+        jkq[v] = (double)J.s;
+        lstar[v] = (double)L.s;
     } else {
-        const Real *p = reinterpret_cast<const Real *>(part);
-        double J[6] = {0, 0, 0, 0, 0, 0}, L = 0.0;
+        KahanSum<Real> J[6], L;
         for (int m = 0; m < nray; ++m) {
             const Real *q = p + 4 * ((long long)m * nvox + v);
             const double *t = tw + m * 19;
-            double w = t[0];
-            double pI = w * (double)q[0], pQ = w * (double)q[1], pU = w * (double)q[2];
+            const Real w = (Real)t[0];
+            const Real pI = w * q[0], pQ = w * q[1], pU = w * q[2];
 #pragma unroll
-            for (int c = 0; c < 6; ++c) J[c] += t[1 + c] * pI + t[7 + c] * pQ + t[13 + c] * pU;
-            L += w * (double)q[3];
+            for (int c = 0; c < 6; ++c) J[c].add((Real)t[1 + c] * pI + (Real)t[7 + c] * pQ + (Real)t[13 + c] * pU);
+            L.add(w * q[3]);
         }
 #pragma unroll
-        for (int c = 0; c < 6; ++c) jkq[v * 6 + c] = J[c];
-        lstar[v] = L;
+        for (int c = 0; c < 6; ++c) jkq[v * 6 + c] = (double)J[c].s;
+        lstar[v] = (double)L.s;
     }
 }
 

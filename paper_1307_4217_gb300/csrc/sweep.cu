@@ -244,6 +244,17 @@ __device__ __forceinline__ CornerP<Real, NS> corner_p(const Node<Real, NS> &n, R
     return c;
 }
 
+// split cluster barrier (PTX barrier.cluster): arrive with release semantics,
+// wait with acquire semantics; all threads of all CTAs of the cluster take part
+__device__ __forceinline__ void cluster_arrive_release()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait_acquire()
+{
+    asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
+
 template <typename Real, int NS, int MODE>
 __device__ __forceinline__ void sweep_item(const SweepArgs<Real> &a, cg::cluster_group &cluster,
                                            typename V16<Real>::T *ring, Real *ibuf, Real *ibuf_next, int m, int g,
@@ -292,9 +303,9 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<Real> &a, cg::cluster
     };
 
     fill(0);
+    if (nz > 1) fill(1);
+    __syncthreads();
     for (int q = 0; q < nz; ++q) {
-        if (q + 1 < nz) fill(q + 1);
-        __syncthreads();
         const PlaneGeom<Real> gq = G[q];
         const bool has_p = q + 1 < nz;
         const PlaneGeom<Real> gp = has_p ? G[q + 1] : gq;
@@ -519,7 +530,16 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<Real> &a, cg::cluster
                 }
             }
         }
-        cluster.sync();
+        // Plane q is done in this CTA: nobody here reads ring slot (q-1)%3 or
+        // the Stokes plane of q-1 any more. Arrive on the cluster barrier
+        // (release: the new Stokes plane becomes visible to the neighbour CTA),
+        // refill the free ring slot with plane q+2 while the other CTAs
+        // finish, then wait (acquire) before plane q+1 reads the neighbour's data.
+        __syncthreads();
+        cluster_arrive_release();
+        if (q + 2 < nz) fill(q + 2);
+        __syncthreads();
+        cluster_wait_acquire();
     }
 }
 
