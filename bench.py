@@ -42,7 +42,7 @@ WORKLOAD = ("polarized two-level atom (Jl=0->Ju=1, Hanle + weak-field Zeeman), r
 # algorithmic floating-point operations per voxel.ray.frequency update of the
 # formal solution (stage-by-stage count of the method, each node's transfer
 # coefficients counted once per ray and frequency; derivation in the design doc)
-F_ALG = 361
+F_ALG = 293
 # FP32 issue peak of the GB300: 152 SMs x 128 FP32 lanes x 2 flops (FMA) x 2070 MHz
 SMS, LANES, SM_MAX_MHZ = 152, 128, 2070.0
 PEAK_FP32_TFLOPS = SMS * LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
