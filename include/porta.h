@@ -135,6 +135,15 @@ typedef struct {
 int porta_create(const porta_grid *g, const porta_atom *a, const porta_quad *q,
                  const porta_opts *o, porta_ctx **out);
 
+/* Batched problem: nbox independent boxes of uneven size (grids[b]) sharing
+   the atomic model and the quadratures. Voxel arrays (atmosphere, rho, J^K_Q,
+   Lambda-bar*) are the boxes' arrays concatenated in box order. Every
+   formal solution sweeps all (box, ray) pairs in one persistent launch,
+   largest boxes first. porta_emergent_stokes and porta_probe_ray take
+   single-box contexts only. Errors as porta_create (for every grid). */
+int porta_batch_create(int nbox, const porta_grid *grids, const porta_atom *a, const porta_quad *q,
+                       const porta_opts *o, porta_ctx **out);
+
 /* Free all device and host memory of the context (NULL is a no-op). */
 void porta_destroy(porta_ctx *c);
 

@@ -10,8 +10,8 @@ raises if it is missing -- there is no CPU fallback.
 from .binding import (  # noqa: F401
     PORTA_OK, PORTA_EINVAL, PORTA_ENOMEM, PORTA_ECUDA, PORTA_ESTATE, PORTA_EKERNEL,
     PORTA_MODEL_TWOLEVEL_UNPOL, PORTA_MODEL_TWOLEVEL_HANLE, PORTA_FP64, PORTA_FP32,
-    PORTA_HOST, PORTA_DEVICE, PortaError, Context, lib, library_path,
-    porta_create, porta_destroy, porta_last_error, porta_set_stream, porta_sizes, porta_rays,
+    PORTA_HOST, PORTA_DEVICE, PortaError, Context, BatchContext, lib, library_path,
+    porta_create, porta_batch_create, porta_destroy, porta_last_error, porta_set_stream, porta_sizes, porta_rays,
     porta_set_atmosphere, porta_set_rho, porta_get_rho, porta_formal_solve, porta_accumulate_jkq,
     porta_see_update, porta_emergent_stokes, porta_probe_ray, porta_launch_info, porta_autotune, porta_eval_coefficients,
     porta_formal_solve_noalloc, PORTA_ESCRATCH, PORTA_NOALLOC_SCRATCH_BYTES,

@@ -52,6 +52,7 @@ class _Atmos(ctypes.Structure):
 _P, _I, _D, _LL = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_longlong
 _SIGS = {
     "porta_create": (_I, [_P, _P, _P, _P, _P]),
+    "porta_batch_create": (_I, [_I, _P, _P, _P, _P, _P]),
     "porta_destroy": (None, [_P]),
     "porta_last_error": (ctypes.c_char_p, [_P]),
     "porta_set_stream": (_I, [_P, _P]),
@@ -128,6 +129,14 @@ def porta_create(grid, atom, quad, opts):
     h = ctypes.c_void_p()
     rc = lib().porta_create(ctypes.byref(grid), ctypes.byref(atom), ctypes.byref(quad),
                             ctypes.byref(opts) if opts is not None else None, ctypes.byref(h))
+    return rc, h
+
+
+def porta_batch_create(grids, atom, quad, opts):
+    arr = (_Grid * len(grids))(*grids)
+    h = ctypes.c_void_p()
+    rc = lib().porta_batch_create(len(grids), arr, ctypes.byref(atom), ctypes.byref(quad),
+                                  ctypes.byref(opts) if opts is not None else None, ctypes.byref(h))
     return rc, h
 
 
@@ -351,3 +360,45 @@ class Context:
         rc, info = porta_launch_info(self.h)
         self._check(rc)
         return info
+
+
+class BatchContext(Context):
+    """Several independent boxes of uneven size sharing atom and quadratures
+    (porta_batch_create). Voxel arrays are the boxes' arrays (raveled in
+    (nz, ny, nx) order) concatenated in box order; results come back the same way."""
+
+    def __init__(self, atms, model, n_mu, n_chi, n_nu, x_max=4.0, precision=PORTA_FP32, cluster=0, nu_group=0):
+        self._keep = []
+        grids = []
+        for atm in atms:
+            z = np.ascontiguousarray(atm["z"], dtype=np.float64)
+            self._keep.append(z)
+            grids.append(_Grid(atm["nx"], atm["ny"], atm["nz"], float(atm["lx"]), float(atm["ly"]), z.ctypes.data))
+        a0 = atms[0]
+        a = _Atom(model, float(a0.get("zeta", 0.0)), float(a0.get("gbar", 1.0)), float(a0.get("bcrit", 25.0)))
+        q = _Quad(n_mu, n_chi, n_nu, float(x_max))
+        o = _Opts(precision, cluster, nu_group)
+        self.h = None
+        rc, h = porta_batch_create(grids, a, q, o)
+        if rc != PORTA_OK:
+            raise PortaError(rc, "porta_batch_create failed")
+        self.h = h
+        rc, s = porta_sizes(h)
+        self.__dict__.update(s)
+        self.box_sizes = [int(t["nx"]) * int(t["ny"]) * int(t["nz"]) for t in atms]
+        self.offsets = np.concatenate([[0], np.cumsum(self.box_sizes)])
+        self.shape = (int(self.offsets[-1]),)
+        self.model = model
+
+    @staticmethod
+    def concat(atms, key):
+        if atms[0].get(key) is None:
+            return None
+        return np.concatenate([np.asarray(t[key], dtype=np.float64).ravel() for t in atms])
+
+    def set_atmosphere(self, atms):
+        Context.set_atmosphere(self, {k: self.concat(atms, k) for k in ("chi", "eps", "bpl", "vel", "bx", "by", "bz")})
+
+    def split(self, arr):
+        """Per-box views of a concatenated voxel array."""
+        return [arr[self.offsets[b]:self.offsets[b + 1]] for b in range(len(self.box_sizes))]

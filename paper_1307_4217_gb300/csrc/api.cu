@@ -118,26 +118,28 @@ long long wrapll(long long a, long long n)
     return r < 0 ? r + n : r;
 }
 
-// plane geometry of one direction in sweep order (see PlaneGeom)
+// plane geometry of one direction in sweep order (see PlaneGeom) for a grid
+// nx x ny x nz with periods lx, ly and heights z
 template <typename Real>
-void plane_geometry(const porta_ctx *c, double mu, double chi, PlaneGeom<Real> *g)
+void plane_geometry(int nx, int ny, int nz, double lx, double ly, const double *z, double mu, double chi,
+                    PlaneGeom<Real> *g)
 {
     const bool up = mu > 0;
     const double st = std::sqrt(std::max(0.0, 1.0 - mu * mu));
     const double ox = st * std::cos(chi), oy = st * std::sin(chi);
-    const double hx = c->lx / c->nx, hy = c->ly / c->ny, amu = std::fabs(mu);
+    const double hx = lx / nx, hy = ly / ny, amu = std::fabs(mu);
     long long ax = 0, ay = 0;
-    for (int q = 0; q < c->nz; ++q) {
-        int kz = up ? q : c->nz - 1 - q;
+    for (int q = 0; q < nz; ++q) {
+        int kz = up ? q : nz - 1 - q;
         PlaneGeom<Real> p{};
         p.kz = kz;
         if (q > 0) {
             int ku = up ? kz - 1 : kz + 1;
-            double ds = std::fabs(c->z[kz] - c->z[ku]) / amu;
+            double ds = std::fabs(z[kz] - z[ku]) / amu;
             double dx = ds * ox / hx, dy = ds * oy / hy;
             double cx = std::ceil(dx), cy = std::ceil(dy);
-            ax = wrapll(ax + (long long)cx, c->nx);
-            ay = wrapll(ay + (long long)cy, c->ny);
+            ax = wrapll(ax + (long long)cx, nx);
+            ay = wrapll(ay + (long long)cy, ny);
             p.tx = (Real)(cx - dx);
             p.ty = (Real)(cy - dy);
             p.ds = (Real)ds;
@@ -169,48 +171,79 @@ int nl_of(int model) { return model == PORTA_MODEL_TWOLEVEL_UNPOL ? 1 : 6; }
 const int kThreads = 512;   // maximum threads per CTA of the sweep kernel
 const int kSmemLimit = 220 * 1024;
 
+// Shared-memory capacities of a launch with cluster size C over all boxes:
+// ring plane (16-byte chunks) and Stokes-plane points, each the maximum over boxes.
+template <typename Real, int NS>
+void launch_caps(const porta_ctx *c, int C, int &ring_plane, int &ipts_max)
+{
+    const int nch = (NS == 1 ? 4 : 8) * (int)sizeof(Real) / 16;
+    ring_plane = 0;
+    ipts_max = 0;
+    for (const BoxDev &b : c->boxes) {
+        const int rmax = (b.ny + C - 1) / C;
+        ring_plane = std::max(ring_plane, nch * (rmax + 2) * b.nx);
+        ipts_max = std::max(ipts_max, rmax * b.nx);
+    }
+}
+
+int max_ny(const porta_ctx *c)
+{
+    int m = 0;
+    for (const BoxDev &b : c->boxes) m = std::max(m, b.ny);
+    return m;
+}
+
 // Launch shape of the sweep: cluster size C (CTAs sharing one ray's plane)
 // and frequencies per pass F. Estimated time of a candidate (in units of one
-// point update) = waves of rays x per-ray work per CTA, where per-ray work
-// counts the point updates, the ring fills (halo rows included) and the
-// partial-integral writes of each frequency pass, and the plane barriers.
+// point update): the (box, ray) work items spread over the resident clusters,
+// each item costing, per plane and frequency pass, the thread slots of its
+// point updates, the ring fill (halo rows included), the partial-integral
+// writes and a barrier.
 template <typename Real, int NS>
 int choose_launch(porta_ctx *c, LaunchCfg &best, int force_c, int force_f, int nitems)
 {
-    const int NW = NS == 1 ? 4 : 8;
+    const int NA = NS == 1 ? 2 : 4;
     double best_cost = 1e300;
     best = LaunchCfg{};
+    const int ny_max = max_ny(c);
     for (int C = 1; C <= 16; ++C) {
         if (force_c > 0 && C != force_c) continue;
         if (force_c <= 0 && C > 1 && (C & (C - 1)) != 0 && C != 6 && C != 12) continue;   // heuristic set
-        if (C > c->ny) continue;
-        int rmax = (c->ny + C - 1) / C;
-        long long ring = 3LL * (rmax + 2) * c->nx * NW * (long long)sizeof(Real);
-        long long per_nu = 2LL * rmax * c->nx * NS * (long long)sizeof(Real);
-        if (ring + per_nu > kSmemLimit) continue;
-        int fmax = (int)std::min<long long>(c->n_nu, (kSmemLimit - ring) / per_nu);
+        if (C > ny_max) continue;
+        int ring_plane, ipts_max;
+        launch_caps<Real, NS>(c, C, ring_plane, ipts_max);
+        const long long ring = 3LL * ring_plane * 16;
+        const long long per_nu = 2LL * ipts_max * NS * (long long)sizeof(Real);
+        const long long scratch = (long long)kThreads * NA * (long long)sizeof(Real);
+        if (ring + per_nu + scratch > kSmemLimit) continue;
+        int fmax = (int)std::min<long long>(c->n_nu, (kSmemLimit - ring - scratch) / per_nu);
         if (force_f > 0) {
             if (force_f > fmax) continue;
             fmax = force_f;
         }
-        int G = (c->n_nu + fmax - 1) / fmax;
-        int F = (c->n_nu + G - 1) / G;
-        int smem = (int)(ring + F * per_nu);
-        // threads per CTA: one per owned point, rounded to whole warps, 64..512
-        int pts_i = rmax * c->nx;
-        int threads = std::min(kThreads, std::max(64, (pts_i + 31) / 32 * 32));
+        const int G = (c->n_nu + fmax - 1) / fmax;
+        const int F = (c->n_nu + G - 1) / G;
+        // threads: the strip's points times the frequency lanes they can use, whole warps, 64..512
+        const int threads = std::min(kThreads, std::max(64, (ipts_max * F + 31) / 32 * 32));
+        const int smem = sweep_smem_bytes<Real, NS>(ring_plane, ipts_max, F, threads);
         int act = 0;
         if (max_active_clusters<Real, NS>(C, smem, threads, &act) != cudaSuccess) {
             cudaGetLastError();
             continue;
         }
         if (act < 1) continue;
-        int ncl = std::min(act, nitems);
-        double waves = std::ceil((double)nitems / ncl);
-        double pts = (double)rmax * c->nx;
-        double slots = std::ceil(pts / threads) * kThreads;    // per-SM issue slots per frequency
-        double per_plane = G * (slots * F + 0.15 * (rmax + 2) * c->nx + 0.05 * pts + 300.0);
-        double cost = waves * per_plane;
+        const int ncl = std::min(act, nitems);
+        double total = 0.0, item_max = 0.0;
+        for (const BoxDev &b : c->boxes) {
+            const int rmax = (b.ny + C - 1) / C;
+            const double pts = (double)rmax * b.nx;
+            const double slots = std::ceil(pts * F / threads) * kThreads;   // per-SM issue slots per pass
+            const double item = b.nz * G * (slots + 0.15 * (rmax + 2) * b.nx + 0.05 * pts + 300.0);
+            total += item * c->nray;
+            item_max = std::max(item_max, item);
+        }
+        const double cost = c->nbox == 1 ? std::ceil((double)nitems / ncl) * item_max
+                                         : std::max(total / ncl, item_max) * 1.05;
         if (cost < best_cost) {
             best_cost = cost;
             best.cluster = C;
@@ -230,8 +263,9 @@ std::vector<LaunchCfg> candidates(porta_ctx *c, int nitems)
     // every cluster size 1..16 (cluster shapes that are not powers of two can
     // tile the GPU's SM groups better); the three largest frequency passes that fit
     std::vector<LaunchCfg> out;
+    const int ny_max = max_ny(c);
     for (int C = 1; C <= 16; ++C) {
-        if (C > c->ny) continue;
+        if (C > ny_max) continue;
         int last_f = -1, kept = 0;
         for (int G = 1; G <= c->n_nu && kept < 3; ++G) {
             int F = (c->n_nu + G - 1) / G;
@@ -251,11 +285,10 @@ template <typename Real>
 SweepArgs<Real> base_args(porta_ctx *c)
 {
     SweepArgs<Real> a{};
-    a.nx = c->nx;
-    a.ny = c->ny;
-    a.nz = c->nz;
     a.nnu = c->n_nu;
+    a.nray = c->nray;
     a.nvox = c->nvox;
+    a.boxes = (const BoxDev *)c->d_boxes;
     a.bfac = (Real)(2.0 * c->gbar * c->zeta);
     const Real *atm = (const Real *)c->d_atm;
     a.chi = atm;
@@ -271,25 +304,43 @@ SweepArgs<Real> base_args(porta_ctx *c)
     return a;
 }
 
+// fill the launch-dependent fields of the arguments
 template <typename Real>
-int formal_solve_t(porta_ctx *c, int probe_ray, Real *probe, Real *probe_ls)
+void shape_args(porta_ctx *c, SweepArgs<Real> &a, const LaunchCfg &cfg)
+{
+    a.F = cfg.F;
+    a.ngroups = (c->n_nu + cfg.F - 1) / cfg.F;
+    if (c->ns == 1)
+        launch_caps<Real, 1>(c, cfg.cluster, a.ring_plane, a.ipts_max);
+    else
+        launch_caps<Real, 4>(c, cfg.cluster, a.ring_plane, a.ipts_max);
+}
+
+template <typename Real>
+SweepArgs<Real> jkq_args(porta_ctx *c)
 {
     SweepArgs<Real> a = base_args<Real>(c);
     a.geom = (const PlaneGeom<Real> *)c->d_geom;
     a.rays = (const RayDev<Real> *)c->d_rays;
     a.invn = (const Real *)c->d_invn;
     a.part = c->d_part;
-    a.nitems = c->nray;
+    a.items = c->d_items;
+    a.nitems = c->nbox * c->nray;
+    return a;
+}
+
+template <typename Real>
+int formal_solve_t(porta_ctx *c, int probe_ray, Real *probe, Real *probe_ls)
+{
+    SweepArgs<Real> a = jkq_args<Real>(c);
     a.probe_ray = probe_ray;
     a.probe = probe;
     a.probe_ls = probe_ls;
     LaunchCfg cfg;
-    int rc = c->ns == 1 ? choose_launch<Real, 1>(c, cfg, c->opt_cluster, c->opt_nu_group, c->nray)
-                        : choose_launch<Real, 4>(c, cfg, c->opt_cluster, c->opt_nu_group, c->nray);
+    int rc = c->ns == 1 ? choose_launch<Real, 1>(c, cfg, c->opt_cluster, c->opt_nu_group, a.nitems)
+                        : choose_launch<Real, 4>(c, cfg, c->opt_cluster, c->opt_nu_group, a.nitems);
     if (rc) return fail(c, rc, "no sweep launch shape fits this grid (shared memory / cluster limits)");
-    a.F = cfg.F;
-    a.ngroups = (c->n_nu + cfg.F - 1) / cfg.F;
-    a.rmax = (c->ny + cfg.cluster - 1) / cfg.cluster;
+    shape_args<Real>(c, a, cfg);
     cudaError_t e = c->ns == 1 ? launch_sweep<Real, 1>(a, MODE_JKQ, cfg, c->stream)
                                : launch_sweep<Real, 4>(a, MODE_JKQ, cfg, c->stream);
     if (e != cudaSuccess) return fail(c, PORTA_ECUDA, std::string("sweep launch: ") + cudaGetErrorString(e));
@@ -300,7 +351,8 @@ int formal_solve_t(porta_ctx *c, int probe_ray, Real *probe, Real *probe_ls)
 template <typename Real>
 int autotune_t(porta_ctx *c)
 {
-    std::vector<LaunchCfg> cand = c->ns == 1 ? candidates<Real, 1>(c, c->nray) : candidates<Real, 4>(c, c->nray);
+    const int nitems = c->nbox * c->nray;
+    std::vector<LaunchCfg> cand = c->ns == 1 ? candidates<Real, 1>(c, nitems) : candidates<Real, 4>(c, nitems);
     if (cand.empty()) return fail(c, PORTA_EINVAL, "autotune: no launch shape fits");
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
@@ -310,15 +362,11 @@ int autotune_t(porta_ctx *c)
     int rc = PORTA_OK;
     for (const LaunchCfg &cfg0 : cand) {
         LaunchCfg cfg = cfg0;
-        SweepArgs<Real> a = base_args<Real>(c);
-        a.geom = (const PlaneGeom<Real> *)c->d_geom;
-        a.rays = (const RayDev<Real> *)c->d_rays;
-        a.invn = (const Real *)c->d_invn;
-        a.part = c->d_part;
-        a.F = cfg.F;
-        a.ngroups = (c->n_nu + cfg.F - 1) / cfg.F;
-        a.rmax = (c->ny + cfg.cluster - 1) / cfg.cluster;
-        a.nitems = cfg.clusters;                    // one wave: every resident cluster sweeps one ray
+        SweepArgs<Real> a = jkq_args<Real>(c);
+        shape_args<Real>(c, a, cfg);
+        // one box: time one wave (every resident cluster sweeps one ray);
+        // batches: time the whole launch (items differ in size)
+        if (c->nbox == 1) a.nitems = cfg.clusters;
         float ms = 1e30f;
         for (int rep = 0; rep < 2 && rc == PORTA_OK; ++rep) {
             cudaError_t e = cudaEventRecord(e0, c->stream);
@@ -332,7 +380,7 @@ int autotune_t(porta_ctx *c)
             ms = std::min(ms, t);
         }
         if (rc != PORTA_OK) break;
-        double waves = std::ceil((double)c->nray / cfg.clusters);
+        double waves = c->nbox == 1 ? std::ceil((double)c->nray / cfg.clusters) : 1.0;
         double est = ms * waves;
         if (est < best) {
             best = est;
@@ -355,7 +403,7 @@ int emergent_t(porta_ctx *c, int ndir, const double *mu, const double *chi, doub
     std::vector<PlaneGeom<Real>> geom((size_t)ndir * c->nz);
     std::vector<RayDev<Real>> rays(ndir);
     for (int d = 0; d < ndir; ++d) {
-        plane_geometry<Real>(c, mu[d], chi[d], geom.data() + (size_t)d * c->nz);
+        plane_geometry<Real>(c->nx, c->ny, c->nz, c->lx, c->ly, c->z.data(), mu[d], chi[d], geom.data() + (size_t)d * c->nz);
         rays[d] = ray_dev<Real>(mu[d], chi[d]);
     }
     PlaneGeom<Real> *dg = nullptr;
@@ -376,9 +424,7 @@ int emergent_t(porta_ctx *c, int ndir, const double *mu, const double *chi, doub
         rc = c->ns == 1 ? choose_launch<Real, 1>(c, cfg, c->opt_cluster, c->opt_nu_group, c->nray)
                         : choose_launch<Real, 4>(c, cfg, c->opt_cluster, c->opt_nu_group, c->nray);
         if (rc) { rc = fail(c, rc, "no sweep launch shape fits this grid"); break; }
-        a.F = cfg.F;
-        a.ngroups = (c->n_nu + cfg.F - 1) / cfg.F;
-        a.rmax = (c->ny + cfg.cluster - 1) / cfg.cluster;
+        shape_args<Real>(c, a, cfg);
         a.nitems = ndir * a.ngroups;
         cfg.clusters = std::min(cfg.clusters, a.nitems);
         e = c->ns == 1 ? launch_sweep<Real, 1>(a, MODE_EMERGENT, cfg, c->stream)
@@ -396,7 +442,8 @@ int emergent_t(porta_ctx *c, int ndir, const double *mu, const double *chi, doub
 void free_all(porta_ctx *c)
 {
     void *ptrs[] = {c->d_atm, c->d_eps, c->d_bpl, c->d_b, c->d_rho, c->d_rhoR, c->d_invn, c->d_geom, c->d_rays,
-                    c->d_freq, c->d_part, c->d_tw, c->d_jkq, c->d_lstar, c->d_resid, c->d_err};
+                    c->d_freq, c->d_part, c->d_tw, c->d_jkq, c->d_lstar, c->d_resid, c->d_err, c->d_boxes,
+                    c->d_items};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }
@@ -431,20 +478,27 @@ int count_bad(porta_ctx *c, const double *d, long long n, double lo, double hi, 
 
 extern "C" {
 
-int porta_create(const porta_grid *g, const porta_atom *at, const porta_quad *q, const porta_opts *o, porta_ctx **out)
+static int create_impl(int nbox, const porta_grid *grids, const porta_atom *at, const porta_quad *q,
+                       const porta_opts *o, porta_ctx **out)
 {
     if (!out) return PORTA_EINVAL;
     *out = nullptr;
-    if (!g || !at || !q || !g->z) return PORTA_EINVAL;
-    if (g->nx < 1 || g->ny < 1 || g->nz < 2 || !(g->lx > 0) || !(g->ly > 0)) return PORTA_EINVAL;
+    if (nbox < 1 || !grids || !at || !q) return PORTA_EINVAL;
+    long long nvox = 0, nplane = 0;
+    for (int b = 0; b < nbox; ++b) {
+        const porta_grid *gb = &grids[b];
+        if (!gb->z || gb->nx < 1 || gb->ny < 1 || gb->nz < 2 || !(gb->lx > 0) || !(gb->ly > 0)) return PORTA_EINVAL;
+        for (int k = 0; k < gb->nz; ++k)
+            if (!std::isfinite(gb->z[k]) || (k > 0 && !(gb->z[k] > gb->z[k - 1]))) return PORTA_EINVAL;
+        nvox += (long long)gb->nx * gb->ny * gb->nz;
+        nplane += gb->nz;
+    }
+    const porta_grid *g = &grids[0];
     if (q->n_mu < 1 || q->n_chi < 1 || q->n_nu < 1 || !(q->x_max > 0) || !std::isfinite(q->x_max)) return PORTA_EINVAL;
     if (at->model != PORTA_MODEL_TWOLEVEL_UNPOL && at->model != PORTA_MODEL_TWOLEVEL_HANLE) return PORTA_EINVAL;
     if (at->model == PORTA_MODEL_TWOLEVEL_HANLE && !(at->bcrit > 0)) return PORTA_EINVAL;
     int prec = o ? o->precision : PORTA_FP32;
     if (prec != PORTA_FP32 && prec != PORTA_FP64) return PORTA_EINVAL;
-    for (int k = 0; k < g->nz; ++k)
-        if (!std::isfinite(g->z[k]) || (k > 0 && !(g->z[k] > g->z[k - 1]))) return PORTA_EINVAL;
-    long long nvox = (long long)g->nx * g->ny * g->nz;
     if (nvox > (1LL << 31)) return PORTA_EINVAL;
 
     porta_ctx *c = new (std::nothrow) porta_ctx();
@@ -463,6 +517,23 @@ int porta_create(const porta_grid *g, const porta_atom *at, const porta_quad *q,
     c->opt_nu_group = o ? o->nu_group : 0;
     c->nvox = nvox;
     c->nray = 2 * q->n_mu * q->n_chi;
+    c->nbox = nbox;
+    {
+        long long v0 = 0, g0 = 0;
+        for (int b = 0; b < nbox; ++b) {
+            const porta_grid *gb = &grids[b];
+            BoxDev d{};
+            d.nx = gb->nx; d.ny = gb->ny; d.nz = gb->nz;
+            d.vox0 = v0;
+            d.geom0 = g0;
+            v0 += (long long)gb->nx * gb->ny * gb->nz;
+            g0 += (long long)c->nray * gb->nz;
+            c->boxes.push_back(d);
+            c->bz.emplace_back(gb->z, gb->z + gb->nz);
+            c->blx.push_back(gb->lx);
+            c->bly.push_back(gb->ly);
+        }
+    }
     c->rsz = prec == PORTA_FP32 ? sizeof(float) : sizeof(double);
 
     // angular quadrature: Gauss inclinations per hemisphere x equally weighted azimuths at midpoints
@@ -505,7 +576,9 @@ int porta_create(const porta_grid *g, const porta_atom *at, const porta_quad *q,
     ok(dalloc(&c->d_rho, nvox * c->nl));
     ok(cudaMalloc(&c->d_rhoR, nvox * c->nl * R));
     ok(cudaMalloc(&c->d_invn, (size_t)c->nray * nvox * R));
-    ok(cudaMalloc(&c->d_geom, (size_t)c->nray * c->nz * (prec == PORTA_FP32 ? sizeof(PlaneGeom<float>) : sizeof(PlaneGeom<double>))));
+    ok(cudaMalloc(&c->d_geom, (size_t)c->nray * nplane * (prec == PORTA_FP32 ? sizeof(PlaneGeom<float>) : sizeof(PlaneGeom<double>))));
+    ok(cudaMalloc(&c->d_boxes, (size_t)nbox * sizeof(BoxDev)));
+    ok(dalloc(&c->d_items, (size_t)nbox * c->nray));
     ok(cudaMalloc(&c->d_rays, (size_t)c->nray * (prec == PORTA_FP32 ? sizeof(RayDev<float>) : sizeof(RayDev<double>))));
     ok(cudaMalloc(&c->d_freq, 2 * (size_t)c->n_nu * R));
     ok(cudaMalloc(&c->d_part, (size_t)c->nray * nvox * (c->ns == 1 ? 2 : 4) * R));
@@ -523,26 +596,42 @@ int porta_create(const porta_grid *g, const porta_atom *at, const porta_quad *q,
             for (int i = 0; i < 18; ++i) tw[m * 19 + 1 + i] = c->tkq[(size_t)m * 18 + i];
         }
         ok(cudaMemcpy(c->d_tw, tw.data(), tw.size() * sizeof(double), cudaMemcpyHostToDevice));
+        // boxes and work items: (box, ray) pairs by decreasing box size (longest first)
+        ok(cudaMemcpy(c->d_boxes, c->boxes.data(), nbox * sizeof(BoxDev), cudaMemcpyHostToDevice));
+        std::vector<int> items((size_t)nbox * c->nray);
+        std::vector<int> order(nbox);
+        for (int b = 0; b < nbox; ++b) order[b] = b;
+        std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+            const BoxDev &p = c->boxes[x], &r = c->boxes[y];
+            return (long long)p.nx * p.ny * p.nz > (long long)r.nx * r.ny * r.nz;
+        });
+        for (int i = 0; i < nbox; ++i)
+            for (int m = 0; m < c->nray; ++m) items[(size_t)i * c->nray + m] = order[i] * c->nray + m;
+        ok(cudaMemcpy(c->d_items, items.data(), items.size() * sizeof(int), cudaMemcpyHostToDevice));
         if (prec == PORTA_FP32) {
-            std::vector<PlaneGeom<float>> geom((size_t)c->nray * c->nz);
+            std::vector<PlaneGeom<float>> geom((size_t)c->nray * nplane);
             std::vector<RayDev<float>> rays(c->nray);
             std::vector<float> fr(2 * c->n_nu);
-            for (int m = 0; m < c->nray; ++m) {
-                plane_geometry<float>(c, c->mu[m], c->chi[m], geom.data() + (size_t)m * c->nz);
-                rays[m] = ray_dev<float>(c->mu[m], c->chi[m]);
-            }
+            for (int b = 0; b < nbox; ++b)
+                for (int m = 0; m < c->nray; ++m)
+                    plane_geometry<float>(c->boxes[b].nx, c->boxes[b].ny, c->boxes[b].nz, c->blx[b], c->bly[b],
+                                          c->bz[b].data(), c->mu[m], c->chi[m],
+                                          geom.data() + c->boxes[b].geom0 + (size_t)m * c->boxes[b].nz);
+            for (int m = 0; m < c->nray; ++m) rays[m] = ray_dev<float>(c->mu[m], c->chi[m]);
             for (int j = 0; j < c->n_nu; ++j) { fr[j] = (float)c->xf[j]; fr[c->n_nu + j] = (float)c->wf[j]; }
             ok(cudaMemcpy(c->d_geom, geom.data(), geom.size() * sizeof(geom[0]), cudaMemcpyHostToDevice));
             ok(cudaMemcpy(c->d_rays, rays.data(), rays.size() * sizeof(rays[0]), cudaMemcpyHostToDevice));
             ok(cudaMemcpy(c->d_freq, fr.data(), fr.size() * sizeof(float), cudaMemcpyHostToDevice));
         } else {
-            std::vector<PlaneGeom<double>> geom((size_t)c->nray * c->nz);
+            std::vector<PlaneGeom<double>> geom((size_t)c->nray * nplane);
             std::vector<RayDev<double>> rays(c->nray);
             std::vector<double> fr(2 * c->n_nu);
-            for (int m = 0; m < c->nray; ++m) {
-                plane_geometry<double>(c, c->mu[m], c->chi[m], geom.data() + (size_t)m * c->nz);
-                rays[m] = ray_dev<double>(c->mu[m], c->chi[m]);
-            }
+            for (int b = 0; b < nbox; ++b)
+                for (int m = 0; m < c->nray; ++m)
+                    plane_geometry<double>(c->boxes[b].nx, c->boxes[b].ny, c->boxes[b].nz, c->blx[b], c->bly[b],
+                                           c->bz[b].data(), c->mu[m], c->chi[m],
+                                           geom.data() + c->boxes[b].geom0 + (size_t)m * c->boxes[b].nz);
+            for (int m = 0; m < c->nray; ++m) rays[m] = ray_dev<double>(c->mu[m], c->chi[m]);
             for (int j = 0; j < c->n_nu; ++j) { fr[j] = c->xf[j]; fr[c->n_nu + j] = c->wf[j]; }
             ok(cudaMemcpy(c->d_geom, geom.data(), geom.size() * sizeof(geom[0]), cudaMemcpyHostToDevice));
             ok(cudaMemcpy(c->d_rays, rays.data(), rays.size() * sizeof(rays[0]), cudaMemcpyHostToDevice));
@@ -567,6 +656,21 @@ int porta_create(const porta_grid *g, const porta_atom *at, const porta_quad *q,
     }
     *out = c;
     return PORTA_OK;
+}
+
+int porta_create(const porta_grid *g, const porta_atom *at, const porta_quad *q, const porta_opts *o, porta_ctx **out)
+{
+    if (!g) {
+        if (out) *out = nullptr;
+        return PORTA_EINVAL;
+    }
+    return create_impl(1, g, at, q, o, out);
+}
+
+int porta_batch_create(int nbox, const porta_grid *grids, const porta_atom *at, const porta_quad *q,
+                       const porta_opts *o, porta_ctx **out)
+{
+    return create_impl(nbox, grids, at, q, o, out);
 }
 
 void porta_destroy(porta_ctx *c)
@@ -792,6 +896,7 @@ int porta_emergent_stokes(porta_ctx *c, int ndir, const double *mu, const double
     for (int d = 0; d < ndir; ++d)
         if (!(mu[d] > 0.0 && mu[d] <= 1.0) || !std::isfinite(chi[d]))
             return fail(c, PORTA_EINVAL, "emergent_stokes: mu must lie in (0, 1], chi finite");
+    if (c->nbox != 1) return fail(c, PORTA_EINVAL, "emergent_stokes: single-box contexts only");
     if (!c->have_atm || !c->have_rho) return fail(c, PORTA_ESTATE, "emergent_stokes: atmosphere or rho not set");
     const long long n = (long long)ndir * c->n_nu * c->nx * c->ny * c->ns;
     double *dout = out;
@@ -812,6 +917,7 @@ int porta_probe_ray(porta_ctx *c, int m, double *out, double *lstar, int where)
     if (!c) return PORTA_EINVAL;
     if (m < 0 || m >= c->nray || !out || (where != PORTA_HOST && where != PORTA_DEVICE))
         return fail(c, PORTA_EINVAL, "probe_ray: bad argument");
+    if (c->nbox != 1) return fail(c, PORTA_EINVAL, "probe_ray: single-box contexts only");
     if (!c->have_atm || !c->have_rho) return fail(c, PORTA_ESTATE, "probe_ray: atmosphere or rho not set");
     const long long n = (long long)c->n_nu * c->nvox;
     void *pr = nullptr, *pl = nullptr;

@@ -103,6 +103,7 @@ struct TableArgs {
     double lx, ly, x_max;
     GaussNodes gl;
     const double *z;
+    BoxDev *box;
     RayDev<float> *rays;
     PlaneGeom<float> *geom;
     double *mu, *tw, *xd, *wd;
@@ -117,6 +118,9 @@ __global__ void noalloc_tables_kernel(TableArgs a)
     const int nray = 2 * a.n_mu * a.n_chi;
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m == 0) {
+        BoxDev b{};
+        b.nx = a.nx; b.ny = a.ny; b.nz = a.nz;
+        *a.box = b;
         for (int j = 0; j < a.n_nu; ++j) {
             double x = 0.0, w = 1.0;
             if (a.n_nu > 1) {
@@ -186,7 +190,7 @@ __global__ void noalloc_tables_kernel(TableArgs a)
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-    size_t atm, rho, invn, part, geom, rays, xf, xd, mu, tw, z, total;
+    size_t atm, rho, invn, part, geom, rays, xf, xd, mu, tw, z, box, total;
 };
 
 Layout layout(long long nvox, int nray, int nz, int nnu, int nl, int ns)
@@ -204,6 +208,7 @@ Layout layout(long long nvox, int nray, int nz, int nnu, int nl, int ns)
     L.mu = o;   o = align256(o + (size_t)nray * sizeof(double));
     L.tw = o;   o = align256(o + (size_t)nray * 19 * sizeof(double));
     L.z = o;    o = align256(o + (size_t)nz * sizeof(double));
+    L.box = o;  o = align256(o + sizeof(BoxDev));
     L.total = o;
     return L;
 }
@@ -230,15 +235,17 @@ int run(const porta_grid *g, const porta_atom *at, const porta_quad *q, const po
     for (int C = 1; C <= 16; ++C) {
         if (C > g->ny) break;
         const int rmax = (g->ny + C - 1) / C;
-        const long long ring = 3LL * (rmax + 2) * g->nx * (NS == 1 ? 4 : 8) * 4;
-        const long long per_nu = 2LL * rmax * g->nx * NS * 4;
+        const int ring_plane = (NS == 1 ? 1 : 2) * (rmax + 2) * g->nx;
+        const int ipts = rmax * g->nx;
+        const long long ring = 3LL * ring_plane * 16;
+        const long long per_nu = 2LL * ipts * NS * 4;
+        const long long scratch = 512LL * (NS == 1 ? 2 : 4) * 4;
         const long long limit = 220 * 1024;
-        if (ring + per_nu > limit) continue;
-        const int fmax = (int)std::min<long long>(q->n_nu, (limit - ring) / per_nu);
+        if (ring + per_nu + scratch > limit) continue;
+        const int fmax = (int)std::min<long long>(q->n_nu, (limit - ring - scratch) / per_nu);
         const int G = (q->n_nu + fmax - 1) / fmax, F = (q->n_nu + G - 1) / G;
-        const int smem = (int)(ring + F * per_nu);
-        const int pts = rmax * g->nx;
-        const int threads = std::min(512, std::max(64, (pts + 31) / 32 * 32));
+        const int threads = std::min(512, std::max(64, (ipts * F + 31) / 32 * 32));
+        const int smem = sweep_smem_bytes<float, NS>(ring_plane, ipts, F, threads);
         int act = 0;
         if (max_active_clusters<float, NS>(C, smem, threads, &act) != cudaSuccess) {
             cudaGetLastError();
@@ -246,9 +253,9 @@ int run(const porta_grid *g, const porta_atom *at, const porta_quad *q, const po
         }
         if (act < 1) continue;
         const int ncl = std::min(act, nray);
-        const double slots = std::ceil((double)pts / threads) * 512.0;
+        const double slots = std::ceil((double)ipts * F / threads) * 512.0;
         const double cost = std::ceil((double)nray / ncl) * G *
-                            (slots * F + 0.15 * (rmax + 2) * g->nx + 0.05 * pts + 300.0);
+                            (slots + 0.15 * (rmax + 2) * g->nx + 0.05 * ipts + 300.0);
         if (cost < best_cost) {
             best_cost = cost;
             best.cluster = C; best.F = F; best.threads = threads; best.smem = smem; best.clusters = ncl;
@@ -263,6 +270,7 @@ int run(const porta_grid *g, const porta_atom *at, const porta_quad *q, const po
     ta.lx = g->lx; ta.ly = g->ly; ta.x_max = q->x_max;
     gauss_nodes(q->n_mu, ta.gl);
     ta.z = (const double *)(B + L.z);
+    ta.box = (BoxDev *)(B + L.box);
     ta.rays = (RayDev<float> *)(B + L.rays);
     ta.geom = (PlaneGeom<float> *)(B + L.geom);
     ta.mu = (double *)(B + L.mu);
@@ -289,7 +297,9 @@ int run(const porta_grid *g, const porta_atom *at, const porta_quad *q, const po
     if (e != cudaSuccess) return PORTA_ECUDA;
 
     SweepArgs<float> a{};
-    a.nx = g->nx; a.ny = g->ny; a.nz = g->nz; a.nnu = q->n_nu; a.nvox = nvox;
+    a.nnu = q->n_nu; a.nray = nray; a.nvox = nvox;
+    a.boxes = ta.box;
+    a.items = nullptr;
     a.bfac = (float)(2.0 * at->gbar * at->zeta);
     a.chi = d_atm; a.vel = d_atm + nvox; a.bx = d_atm + 2 * nvox; a.by = d_atm + 3 * nvox; a.bz = d_atm + 4 * nvox;
     a.bpl = d_atm + 5 * nvox;
@@ -302,7 +312,11 @@ int run(const porta_grid *g, const porta_atom *at, const porta_quad *q, const po
     a.nitems = nray;
     a.F = best.F;
     a.ngroups = (q->n_nu + best.F - 1) / best.F;
-    a.rmax = (g->ny + best.cluster - 1) / best.cluster;
+    {
+        const int rmax = (g->ny + best.cluster - 1) / best.cluster;
+        a.ring_plane = (NS == 1 ? 1 : 2) * (rmax + 2) * g->nx;
+        a.ipts_max = rmax * g->nx;
+    }
     e = launch_sweep<float, NS>(a, MODE_JKQ, best, st);
     if (e == cudaSuccess) e = run_jkq_finalize<float, NS>(nvox, nray, B + L.part, ta.tw, jkq, lstar, st);
     return e == cudaSuccess ? PORTA_OK : PORTA_ECUDA;

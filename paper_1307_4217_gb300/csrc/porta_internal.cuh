@@ -35,15 +35,26 @@ struct RayDev {
 
 enum SweepMode { MODE_JKQ = 0, MODE_EMERGENT = 1 };
 
+// One box of a (possibly batched) problem: sizes, first voxel in the
+// concatenated voxel arrays, first plane record of its ray geometry
+// ([ray][nz] PlaneGeom records).
+struct BoxDev {
+    int nx, ny, nz, pad;
+    long long vox0, geom0;
+};
+
 template <typename Real>
 struct SweepArgs {
-    int nx, ny, nz, nnu;
-    long long nvox;
-    int nitems;          // work items: rays (J mode) or directions x groups (emergent)
+    int nnu, nray;
+    long long nvox;      // voxels of all boxes
+    int nitems;          // work items: (box, ray) pairs (J mode) or directions x groups (emergent)
+    const int *items;    // J mode: item -> box * nray + ray, ordered by decreasing cost
+    const BoxDev *boxes;
     int ngroups, F;      // frequency groups and frequencies per group
-    int rmax;            // max sheared rows per CTA
+    int ring_plane;      // shared-memory ring plane capacity (16-byte chunks), max over boxes
+    int ipts_max;        // Stokes-plane capacity (points), max over boxes
     Real bfac;           // 2 * gbar * zeta (weak-field Zeeman, eta_V / (eta_I x B.Omega))
-    const PlaneGeom<Real> *geom;   // [ray][nz]
+    const PlaneGeom<Real> *geom;   // per box: [ray][nz]
     const RayDev<Real> *rays;      // [ray]
     const Real *xf, *wf;           // frequency nodes and trapezoid weights
     // atmosphere (SoA, Real) and unknowns
@@ -68,8 +79,10 @@ struct LaunchCfg {
 template <typename Real, int NS>
 cudaError_t launch_sweep(const SweepArgs<Real> &a, int mode, LaunchCfg &cfg, cudaStream_t st);
 
+// shared memory of the sweep: ring (3 planes of `ring_plane` chunks),
+// Stokes planes (2 x F x ipts_max points), lane-reduction scratch
 template <typename Real, int NS>
-int sweep_smem_bytes(int nx, int rmax, int F);
+int sweep_smem_bytes(int ring_plane, int ipts_max, int F, int threads);
 
 template <typename Real, int NS>
 cudaError_t max_active_clusters(int cluster, int smem, int threads, int *out);
@@ -109,6 +122,13 @@ struct porta_ctx {
     double *d_tw = nullptr;         // nray*19 FP64: w_m, T (18)
     double *d_jkq = nullptr, *d_lstar = nullptr;
     unsigned long long *d_resid = nullptr;
+    // batched problems: per-box sizes, grids and offsets
+    int nbox = 1;
+    std::vector<porta::BoxDev> boxes;
+    std::vector<std::vector<double>> bz;
+    std::vector<double> blx, bly;
+    void *d_boxes = nullptr;       // nbox BoxDev
+    int *d_items = nullptr;        // nbox*nray work items ordered by decreasing cost
     int *d_err = nullptr;
     // last launch of the formal solution
     porta::LaunchCfg last{};

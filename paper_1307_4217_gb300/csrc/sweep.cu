@@ -39,9 +39,9 @@ template <int NS>
 __host__ __device__ constexpr int node_words() { return NS == 1 ? 4 : 8; }
 
 template <typename Real, int NS>
-int sweep_smem_bytes(int nx, int rmax, int F)
+int sweep_smem_bytes(int ring_plane, int ipts_max, int F, int threads)
 {
-    return (3 * (rmax + 2) * nx * node_words<NS>() + 2 * F * rmax * nx * NS) * (int)sizeof(Real);
+    return 3 * ring_plane * 16 + (2 * F * ipts_max * NS + threads * (NS == 1 ? 2 : 4)) * (int)sizeof(Real);
 }
 
 template <typename Real>
@@ -255,46 +255,81 @@ __device__ __forceinline__ void cluster_wait_acquire()
     asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
 }
 
+// per-ray partial integrals of a point: store on the first frequency pass,
+// read-modify-write on later passes
+template <typename Real, int NS>
+__device__ __forceinline__ void accumulate_partial(const SweepArgs<Real> &a, int m, long long v, int g, const Real *acc)
+{
+    if constexpr (NS == 1) {
+        R2<Real> *pp = reinterpret_cast<R2<Real> *>(a.part) + (long long)m * a.nvox + v;
+        R2<Real> o = {acc[0], acc[1]};
+        if (g > 0) { R2<Real> old = *pp; o.x += old.x; o.y += old.y; }
+        *pp = o;
+    } else {
+        R4<Real> *pp = reinterpret_cast<R4<Real> *>(a.part) + (long long)m * a.nvox + v;
+        R4<Real> o = {acc[0], acc[1], acc[2], acc[3]};
+        if (g > 0) { R4<Real> old = *pp; o.x += old.x; o.y += old.y; o.z += old.z; o.w += old.w; }
+        *pp = o;
+    }
+}
+
 template <typename Real, int NS, int MODE>
 __device__ __forceinline__ void sweep_item(const SweepArgs<Real> &a, cg::cluster_group &cluster,
-                                           typename V16<Real>::T *ring, Real *ibuf, Real *ibuf_next, int m, int g,
-                                           int row0, int R, int dir_out)
+                                           typename V16<Real>::T *ring, Real *ibuf, Real *lane_buf, int box, int m,
+                                           int g, int rank, int C, int dir_out)
 {
     using V = typename V16<Real>::T;
-    const int nx = a.nx, ny = a.ny, nz = a.nz, F = a.F, rmax = a.rmax;
+    constexpr int NA = NS == 1 ? 2 : 4;                  // accumulated quantities per point
+    const BoxDev B = a.boxes[box];
+    const int nx = B.nx, ny = B.ny, nz = B.nz, F = a.F;
+    const int rmax = (ny + C - 1) / C;
+    const int row0 = (int)(((long long)rank * ny) / C);
+    const int R = (int)(((long long)(rank + 1) * ny) / C) - row0;
+    // The sheared row after this strip, (row0 + R) mod ny, is row 0 of the CTA
+    // that owns it: the largest rank k with floor(k ny / C) <= row (CTAs own no
+    // rows when ny < C).
+    const int next_row = (row0 + R) % ny;
+    const int next_owner = (int)(((long long)(next_row + 1) * C + ny - 1) / ny) - 1;
+    const Real *ibuf_next = cluster.map_shared_rank(ibuf, next_owner);
     const int j0 = g * F;
     const int nf = min(F, a.nnu - j0);
-    const PlaneGeom<Real> *G = a.geom + (long long)m * nz;
+    const PlaneGeom<Real> *G = a.geom + B.geom0 + (long long)m * nz;
     const RayDev<Real> ray = a.rays[m];
     const bool upward = ray.mu > Real(0);
     const long long nxy = (long long)nx * ny;
     const bool jmode = (MODE == MODE_JKQ);
     const int tid = threadIdx.x, nt = blockDim.x;
     constexpr int NCH = node_words<NS>() * (int)sizeof(Real) / 16;
-    const int chunk = (rmax + 2) * nx;              // ring chunk-plane stride (V units)
-    const int plane = NCH * chunk;                  // ring plane stride (V units)
+    const int chunk = (rmax + 2) * nx;              // ring chunk-plane stride (16-byte chunks)
+    const int plane = NCH * chunk;                  // ring plane stride
     const int ipts = rmax * nx;                     // points per Stokes plane
     const int ichunk = ipts;                        // Stokes chunk-plane stride (16-byte chunks)
     const int iplane = NS * ipts;                   // Reals per (buf, f) Stokes plane
     const int npts = R * nx;
 
-    // thread -> (row, column) stepping without integer division: idx = tid + k*nt
+    // Frequency lanes: when the strip has fewer points than threads, threads
+    // tid = lane * npts + p share point p and take frequencies lane, lane + L, ...
+    const int L = npts > 0 ? max(1, min(nf, nt / npts)) : 1;
+    const int lane = L > 1 ? tid / npts : 0;
+    const int pstart = L > 1 ? (lane < L ? tid - lane * npts : npts) : tid;
+    const int pstep = L > 1 ? npts : nt;
+
+    // thread -> (row, column) stepping without integer division in the loops
     const int dl = nt / nx, dc = nt - dl * nx;
-    const int l0 = tid / nx, c0 = tid - l0 * nx;
 
     auto fill = [&](int q) {
         const PlaneGeom<Real> gq = G[q];
         const int nn = (R + 2) * nx;
         const long long kbase = (long long)gq.kz * ny;
-        int lr = l0, c = c0;                     // lr = ring row (local row + 1)
+        int lr = tid / nx, c = tid - (tid / nx) * nx;      // lr = ring row (local row + 1)
         for (int idx = tid; idx < nn; idx += nt) {
             int pi = c + gq.ax;
             pi -= pi >= nx ? nx : 0;
-            int pj = row0 + lr - 1 + gq.ay;      // in [-1, 2 ny]
+            int pj = row0 + lr - 1 + gq.ay;                  // in [-1, 2 ny]
             pj += pj < 0 ? ny : 0;
             pj -= pj >= ny ? ny : 0;
             pj -= pj >= ny ? ny : 0;
-            long long v = (kbase + pj) * nx + pi;
+            const long long v = B.vox0 + (kbase + pj) * nx + pi;
             ring_store<Real, NS>(ring, plane, chunk, q % 3, idx, make_node<Real, NS>(a, ray, v, m, jmode));
             c += dc;
             lr += dl;
@@ -319,19 +354,26 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<Real> &a, cg::cluster
         const Real px0 = gp.tx, px1 = Real(1) - gp.tx, py0 = gp.ty, py1 = Real(1) - gp.ty;
         const Real dsM = gq.ds, dsP = has_p ? gp.ds : Real(0);
 
-        int l = l0, c = c0;
-        for (int p = tid; p < npts; p += nt, c += dc, l += dl) {
-            if (c >= nx) { c -= nx; ++l; }
+        long long v_lane = 0;
+        int p_lane = 0;
+        Real acc[NA];
+        int l = pstart / nx, c = pstart - (pstart / nx) * nx;
+        for (int p = pstart; p < npts; p += pstep) {
+            if (p != pstart) {
+                c += dc;
+                l += dl;
+                if (c >= nx) { c -= nx; ++l; }
+            }
             int pi = c + gq.ax;
             pi -= pi >= nx ? nx : 0;
             int pj = row0 + l + gq.ay;           // in [0, 2 ny)
             pj -= pj >= ny ? ny : 0;
             pj -= pj >= ny ? ny : 0;
-            const long long v = ((long long)gq.kz * ny + pj) * nx + pi;
+            const long long vloc = ((long long)gq.kz * ny + pj) * nx + pi;
+            const long long v = B.vox0 + vloc;
             const Node<Real, NS> nO = ring_load<Real, NS>(ring, plane, chunk, sO, (l + 1) * nx + c);
-            Real acc[NS == 1 ? 2 : 4];
 #pragma unroll
-            for (int s = 0; s < (NS == 1 ? 2 : 4); ++s) acc[s] = Real(0);
+            for (int s = 0; s < NA; ++s) acc[s] = Real(0);
 
             if (q == 0) {
                 // boundary plane: I = (B, 0, 0, 0) entering at the bottom, 0 at the top; Lambda* = 0
@@ -339,7 +381,7 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<Real> &a, cg::cluster
 #pragma unroll
                 for (int s = 0; s < NS; ++s) I0[s] = Real(0);
                 if (upward) I0[0] = a.bpl[v];
-                for (int f = 0; f < nf; ++f) {
+                for (int f = lane; f < nf; f += L) {
                     const int j = j0 + f;
                     StokesIO<Real, NS>::store(iw + f * iplane, ichunk, l * nx + c, I0);
                     if constexpr (MODE == MODE_JKQ) {
@@ -376,7 +418,7 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<Real> &a, cg::cluster
                 const Real *ihi_base = last_row ? irn : ir;          // row l+1 (next CTA's row 0)
                 const int ihi = last_row ? 0 : (l + 1) * nx;
 
-                for (int f = 0; f < nf; ++f) {
+                for (int f = lane; f < nf; f += L) {
                     const int j = j0 + f;
                     const Real x = a.xf[j];
                     const Real *pl = ir + f * iplane;
@@ -517,16 +559,28 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<Real> &a, cg::cluster
                 }
             }
             if constexpr (MODE == MODE_JKQ) {
-                if constexpr (NS == 1) {
-                    R2<Real> *pp = reinterpret_cast<R2<Real> *>(a.part) + (long long)m * a.nvox + v;
-                    R2<Real> o = {acc[0], acc[1]};
-                    if (g > 0) { R2<Real> old = *pp; o.x += old.x; o.y += old.y; }
-                    *pp = o;
+                if (L == 1) {
+                    accumulate_partial<Real, NS>(a, m, v, g, acc);
                 } else {
-                    R4<Real> *pp = reinterpret_cast<R4<Real> *>(a.part) + (long long)m * a.nvox + v;
-                    R4<Real> o = {acc[0], acc[1], acc[2], acc[3]};
-                    if (g > 0) { R4<Real> old = *pp; o.x += old.x; o.y += old.y; o.z += old.z; o.w += old.w; }
-                    *pp = o;
+#pragma unroll
+                    for (int s = 0; s < NA; ++s) lane_buf[(s * L + lane) * npts + p] = acc[s];
+                    v_lane = v;
+                    p_lane = p;
+                }
+            }
+        }
+        if constexpr (MODE == MODE_JKQ) {
+            if (L > 1) {
+                // fixed-order sum over the frequency lanes of each point
+                __syncthreads();
+                if (lane == 0 && pstart < npts) {
+                    Real tot[NA];
+#pragma unroll
+                    for (int s = 0; s < NA; ++s) {
+                        tot[s] = Real(0);
+                        for (int k = 0; k < L; ++k) tot[s] += lane_buf[(s * L + k) * npts + p_lane];
+                    }
+                    accumulate_partial<Real, NS>(a, m, v_lane, g, tot);
                 }
             }
         }
@@ -552,20 +606,20 @@ __global__ void __launch_bounds__(512, 1) sweep_kernel(const SweepArgs<Real> a)
     const int rank = (int)cluster.block_rank();
     const int cid = blockIdx.x / C;
     const int ncl = gridDim.x / C;
-    const int row0 = (int)(((long long)rank * a.ny) / C);
-    const int row1 = (int)(((long long)(rank + 1) * a.ny) / C);
     using V = typename V16<Real>::T;
     V *ring = reinterpret_cast<V *>(smem_raw);
-    Real *ibuf = reinterpret_cast<Real *>(ring + 3 * (a.rmax + 2) * a.nx * (node_words<NS>() * (int)sizeof(Real) / 16));
-    Real *ibuf_next = cluster.map_shared_rank(ibuf, (rank + 1) % C);
+    Real *ibuf = reinterpret_cast<Real *>(ring + 3 * a.ring_plane);
+    Real *lane_buf = ibuf + 2 * a.F * NS * a.ipts_max;
     cluster.sync();
     for (int item = cid; item < a.nitems; item += ncl) {
         if constexpr (MODE == MODE_JKQ) {
+            const int code = a.items ? a.items[item] : item;
+            const int box = code / a.nray, m = code - box * a.nray;
             for (int g = 0; g < a.ngroups; ++g)
-                sweep_item<Real, NS, MODE>(a, cluster, ring, ibuf, ibuf_next, item, g, row0, row1 - row0, 0);
+                sweep_item<Real, NS, MODE>(a, cluster, ring, ibuf, lane_buf, box, m, g, rank, C, 0);
         } else {
             const int d = item / a.ngroups, g = item - d * a.ngroups;
-            sweep_item<Real, NS, MODE>(a, cluster, ring, ibuf, ibuf_next, d, g, row0, row1 - row0, d);
+            sweep_item<Real, NS, MODE>(a, cluster, ring, ibuf, lane_buf, 0, d, g, rank, C, d);
         }
     }
 }
@@ -628,7 +682,7 @@ cudaError_t launch_sweep(const SweepArgs<Real> &a, int mode, LaunchCfg &cfg, cud
 }
 
 #define PORTA_INST(R, N)                                                                           \
-    template int sweep_smem_bytes<R, N>(int, int, int);                                            \
+    template int sweep_smem_bytes<R, N>(int, int, int, int);                                            \
     template cudaError_t max_active_clusters<R, N>(int, int, int, int *);                          \
     template cudaError_t launch_sweep<R, N>(const SweepArgs<R> &, int, LaunchCfg &, cudaStream_t);
 PORTA_INST(float, 1)
