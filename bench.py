@@ -82,6 +82,8 @@ def args_parse():
     ap.add_argument("--cpu-sample-rays", type=int, default=4)
     ap.add_argument("--cluster", type=int, default=0, help="force the sweep cluster size (skips the autotuner)")
     ap.add_argument("--nu-group", type=int, default=0, help="force frequencies per pass (skips the autotuner)")
+    ap.add_argument("--workload", choices=["pol64", "batched256"], default="pol64",
+                    help="pol64: the 64^3 polarized box (default); batched256: 256 uneven boxes in one launch")
     return ap.parse_args()
 
 
@@ -188,6 +190,67 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+# ---------------------------------------------------------------- workloads
+
+class Workload:
+    """A benchmarked problem: its context factory, update count per formal
+    solution, and the oracle sample used for the CPU baseline."""
+
+    def __init__(self, name, rank):
+        import paper_1307_4217_gb300 as P
+        self.name = name
+        if name == "pol64":
+            self.atm = synth.random_box(NX, NY, NZ, seed=rank)
+            self.quad = (N_MU, N_CHI, N_NU)
+            self.updates = UPDATES
+            self.desc = WORKLOAD
+            self.rho0 = np.zeros((NZ, NY, NX, 6))
+            self.rho0[..., 0] = self.atm["bpl"]
+            self.config = {"grid": [NX, NY, NZ], "rays": NRAY, "frequencies": N_NU}
+        elif name == "batched256":
+            self.atms = synth.batched_boxes(256, seed=rank)
+            self.quad = (4, 10, 21)
+            nvox = sum(a["nx"] * a["ny"] * a["nz"] for a in self.atms)
+            self.updates = nvox * 80 * 21
+            self.desc = ("256 independent polarized two-level boxes (Nx = Ny in {8,16,24,32,48}, Nz in 16..64, "
+                         "own seeds), 80 rays, 21 frequencies; one Jacobi iteration of all boxes per step "
+                         "(one persistent sweep launch, FP32 sweeps, FP64 SEE)")
+            self.rho0 = np.concatenate([np.stack([a["bpl"].ravel()] + [np.zeros(a["bpl"].size)] * 5, axis=1)
+                                        for a in self.atms])
+            self.config = {"boxes": 256, "voxels": nvox, "rays": 80, "frequencies": 21}
+        else:
+            raise ValueError(name)
+        self.P = P
+
+    def context(self, precision, cluster, nu_group):
+        P = self.P
+        if self.name == "pol64":
+            ctx = P.Context(self.atm, P.PORTA_MODEL_TWOLEVEL_HANLE, *self.quad, precision=precision,
+                            cluster=cluster, nu_group=nu_group)
+            ctx.set_atmosphere(self.atm)
+        else:
+            ctx = P.BatchContext(self.atms, P.PORTA_MODEL_TWOLEVEL_HANLE, *self.quad, precision=precision,
+                                 cluster=cluster, nu_group=nu_group)
+            ctx.set_atmosphere(self.atms)
+        ctx.set_rho(self.rho0)
+        return ctx
+
+    def oracle_sample(self, nrays):
+        import oracle
+        if self.name == "pol64":
+            return oracle_sample(nrays)
+        # a few boxes of the batch, all rays and frequencies
+        t0 = time.perf_counter()
+        n = 0
+        for b in (0, 85, 170):
+            a = self.atms[b]
+            p = oracle.Problem(a, oracle.MODEL_HANLE, *self.quad)
+            oracle.formal_solve(p, oracle.initial_rho(p, a))
+            n += a["nx"] * a["ny"] * a["nz"] * 80 * 21
+        dt = time.perf_counter() - t0
+        return n / dt, dt, f"boxes 0, 85, 170 of the batch, all rays and frequencies ({n} updates, {dt:.1f} s)"
+
+
 # ---------------------------------------------------------------- GPU arm
 
 def run_cuda(args):
@@ -203,23 +266,17 @@ def run_cuda(args):
     dev = torch.device("cuda", local)
     B.build()
 
-    # Each rank solves its own box (independent replicas: weak scaling, no data-path collective).
-    atm = synth.random_box(NX, NY, NZ, seed=rank)
-    rho0 = np.zeros((NZ, NY, NX, 6))
-    rho0[..., 0] = atm["bpl"]
+    # Each rank solves its own problem (independent replicas: weak scaling, no data-path collective).
+    wl = Workload(args.workload, rank)
     stream = torch.cuda.Stream(device=dev)
-
     forced = args.cluster > 0 or args.nu_group > 0
 
     def make(precision):
-        ctx = P.Context(atm, P.PORTA_MODEL_TWOLEVEL_HANLE, N_MU, N_CHI, N_NU, precision=precision,
-                        cluster=args.cluster, nu_group=args.nu_group)
+        ctx = wl.context(precision, args.cluster, args.nu_group)
         ctx.set_stream(stream)
-        ctx.set_atmosphere(atm)
-        ctx.set_rho(rho0)
         if not forced:
             ctx.autotune()          # launch-shape autotuner (outside the timed region)
-            ctx.set_rho(rho0)
+            ctx.set_rho(wl.rho0)
         return ctx
 
     ctx = make(P.PORTA_FP32)
@@ -231,71 +288,69 @@ def run_cuda(args):
             torch.distributed.barrier()
 
     with torch.cuda.stream(stream):
+        # warm-up: eager calls, then the captured graph of one Jacobi iteration
         for _ in range(args.warmup):
             ctx.formal_solve()
             ctx.accumulate_jkq(want=False)
             ctx.see_update(residual=False)
+        ctx.run_iterations(1, residual=False)
         barrier()
-        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+        # timed steps: one graph replay (formal solution, J^K_Q sums, SEE, residual) each
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(args.steps)]
         sampler = ClockSampler(local)
         sampler.start()
         barrier()
         for k in range(args.steps):
             flush.zero_()                       # L2 flush between timed steps (outside the events)
             ev[k][0].record(stream)
-            ctx.formal_solve()
+            ctx.run_iterations(1, residual=False)
             ev[k][1].record(stream)
-            ctx.accumulate_jkq(want=False)
-            ctx.see_update(residual=False)
-            ev[k][2].record(stream)
         barrier()
         clocks = sampler.stop()
-    step_ms = sum(e[0].elapsed_time(e[2]) for e in ev) / args.steps
-    sweep_ms = sum(e[0].elapsed_time(e[1]) for e in ev) / args.steps
-    info = ctx.launch_info()
-    residual = None
-
-    # end to end through the ABI with pinned host buffers: rho in, J^K_Q + Lambda* + residual out
-    rho_h = torch.from_numpy(rho0.copy()).pin_memory()
-    jkq_h = torch.empty((NZ, NY, NX, 6), dtype=torch.float64).pin_memory()
-    ls_h = torch.empty((NZ, NY, NX), dtype=torch.float64).pin_memory()
-    with torch.cuda.stream(stream):
-        for _ in range(1):
-            ctx.set_rho(rho_h)
+        step_ms = sum(e[0].elapsed_time(e[1]) for e in ev) / args.steps
+        # sweep kernel alone (eager formal solutions), for the roofline
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(args.steps)]
+        for k in range(args.steps):
+            flush.zero_()
+            evs[k][0].record(stream)
             ctx.formal_solve()
-            ctx.accumulate_jkq(jkq_h, ls_h)
-            ctx.see_update()
+            evs[k][1].record(stream)
+        barrier()
+        sweep_ms = sum(e[0].elapsed_time(e[1]) for e in evs) / args.steps
+    info = ctx.launch_info()
+
+    # end to end through the ABI with pinned host buffers: rho in, one iteration, rho and residual out
+    rho_h = torch.from_numpy(wl.rho0.copy()).pin_memory()
+    rho_out = torch.empty_like(rho_h).pin_memory()
+    with torch.cuda.stream(stream):
+        ctx.set_rho(rho_h)
+        ctx.run_iterations(1)
+        ctx.get_rho(rho_out)
         barrier()
         t0 = time.perf_counter()
         for _ in range(args.steps):
             ctx.set_rho(rho_h)
-            ctx.formal_solve()
-            ctx.accumulate_jkq(jkq_h, ls_h)
-            residual = ctx.see_update()
+            residual = ctx.run_iterations(1)
+            ctx.get_rho(rho_out)
         barrier()
         e2e_s = (time.perf_counter() - t0) / args.steps
     h2d = rho_h.numel() * 8
-    d2h = (jkq_h.numel() + ls_h.numel() + 1) * 8
+    d2h = rho_out.numel() * 8 + 8
 
-    # FP64 plain form of the same step
+    # FP64 plain form of the same step (single box only: the FP64 batch takes ~15 s per step)
     fp64 = None
-    if args.fp64_steps > 0:
+    if args.fp64_steps > 0 and wl.name == "pol64":
         ctx64 = make(P.PORTA_FP64)
         with torch.cuda.stream(stream):
-            ctx64.formal_solve()
-            ctx64.accumulate_jkq(want=False)
-            ctx64.see_update(residual=False)
+            ctx64.run_iterations(1, residual=False)
             barrier()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            for _ in range(args.fp64_steps):
-                ctx64.formal_solve()
-                ctx64.accumulate_jkq(want=False)
-                ctx64.see_update(residual=False)
+            ctx64.run_iterations(args.fp64_steps, residual=False)
             e1.record(stream)
             barrier()
         ms64 = e0.elapsed_time(e1) / args.fp64_steps
-        fp64 = {"value": world * UPDATES / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64, "dtype": "f64",
+        fp64 = {"value": world * wl.updates / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64, "dtype": "f64",
                 "launch": ctx64.launch_info()}
         ctx64.close()
 
@@ -309,27 +364,29 @@ def run_cuda(args):
             torch.distributed.destroy_process_group()
         return
 
-    achieved = F_ALG * UPDATES / (sweep_ms * 1e-3) / 1e12
+    achieved = F_ALG * wl.updates / (sweep_ms * 1e-3) / 1e12
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        v, dt, sample = oracle_sample(args.cpu_sample_rays)
+        v, dt, sample = wl.oracle_sample(args.cpu_sample_rays)
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+    cfg = {"workload": wl.desc, **wl.config, "updates_per_step": wl.updates, "seed": "rank",
+           "l2": "flushed between timed steps (256 MiB write)", "parallelism": f"replicas x{world}",
+           "sweep_launch": info, "launch_shape": "forced" if forced else "autotuned",
+           "step": "one CUDA-graph replay of a Jacobi iteration (sweep, J^K_Q sums, SEE, residual)"}
     line = {
-        "metric": METRIC, "value": world * UPDATES / (step_ms * 1e-3), "unit": UNIT, "n_gpus": world,
+        "metric": METRIC, "value": world * wl.updates / (step_ms * 1e-3), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "grid": [NX, NY, NZ], "rays": NRAY, "frequencies": N_NU,
-                   "updates_per_step": UPDATES, "seed": "rank", "l2": "flushed between timed steps (256 MiB write)",
-                   "parallelism": f"replicas x{world}", "sweep_launch": info,
-                   "launch_shape": "forced" if forced else "autotuned"},
+        "config": cfg,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": PEAK_FP32_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / PEAK_FP32_TFLOPS, "traffic": measured_traffic(),
+                     "frac": achieved / PEAK_FP32_TFLOPS,
+                     "traffic": measured_traffic() if wl.name == "pol64" else None,
                      "kernel": "sweep_kernel<float,4,JKQ>", "flops_per_update": F_ALG,
                      "kernel_ms": sweep_ms,
                      "peak_basis": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (derived, not measured)"},
         "cpu_baseline": cpu,
         "clocks": clocks,
-        "e2e": {"value": world * UPDATES / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+        "e2e": {"value": world * wl.updates / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "residual": residual},
         "gpu_launches": 3 * args.steps,
         "fp64_plain": fp64,

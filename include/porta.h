@@ -240,6 +240,15 @@ int porta_formal_solve_noalloc(const porta_grid *g, const porta_atom *a, const p
                                const porta_atmos *atm, const double *rho, double *jkq, double *lstar,
                                void *stream);
 
+/* Jacobi iterations as a CUDA graph: on first use (and after
+   porta_autotune or a stream change) one iteration -- porta_formal_solve,
+   porta_accumulate_jkq, porta_see_update with its residual -- is captured on
+   the context's stream into a CUDA graph; the graph is then launched
+   `iterations` times. Needs a non-default stream (porta_set_stream),
+   the atmosphere and rho. max_change (host, may be NULL) receives the
+   residual of the last iteration (synchronizes the stream). */
+int porta_run_iterations(porta_ctx *c, int iterations, double *max_change);
+
 /* Launch statistics of the last formal solution: clusters launched, CTAs per
    cluster, frequencies per pass, dynamic shared memory per CTA (bytes). */
 int porta_launch_info(const porta_ctx *c, int *clusters, int *cluster_size, int *nu_group, int *smem_bytes);

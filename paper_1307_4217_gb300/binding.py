@@ -68,6 +68,7 @@ _SIGS = {
     "porta_probe_ray": (_I, [_P, _I, _P, _P, _I]),
     "porta_launch_info": (_I, [_P, _P, _P, _P, _P]),
     "porta_autotune": (_I, [_P, _P, _P]),
+    "porta_run_iterations": (_I, [_P, _I, _P]),
     "porta_eval_coefficients": (_I, [_I, _I, _P, _P]),
     "porta_formal_solve_noalloc": (_I, [_P, _P, _P, _P, _P, _P, _P, _P]),
 }
@@ -228,6 +229,10 @@ def porta_formal_solve_noalloc(atm, model, n_mu, n_chi, n_nu, x_max, datm, rho_p
                                             rho_ptr, jkq_ptr, lstar_ptr, ctypes.c_void_p(handle or 0))
 
 
+def porta_run_iterations(h, iterations, out=None):
+    return lib().porta_run_iterations(h, iterations, ctypes.byref(out) if out is not None else None)
+
+
 def porta_launch_info(h):
     v = [ctypes.c_int() for _ in range(4)]
     rc = lib().porta_launch_info(h, *[ctypes.byref(x) for x in v])
@@ -350,6 +355,12 @@ class Context:
         ls = np.zeros((self.nnu,) + self.shape)
         self._check(porta_probe_ray(self.h, m, out.ctypes.data, ls.ctypes.data, PORTA_HOST))
         return out, ls
+
+    def run_iterations(self, n, residual=True):
+        """n Jacobi iterations replayed from a captured CUDA graph (needs set_stream)."""
+        out = ctypes.c_double() if residual else None
+        self._check(porta_run_iterations(self.h, n, out))
+        return out.value if residual else None
 
     def autotune(self):
         rc, r = porta_autotune(self.h)

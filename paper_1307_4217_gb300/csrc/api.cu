@@ -112,6 +112,15 @@ void tkq_tensors(double mu, double chi, double out[18])
     }
 }
 
+void drop_graph(porta_ctx *c)
+{
+    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    c->graph_exec = nullptr;
+    c->graph = nullptr;
+    c->graph_stream = nullptr;
+}
+
 long long wrapll(long long a, long long n)
 {
     long long r = a % n;
@@ -365,8 +374,13 @@ int autotune_t(porta_ctx *c)
         SweepArgs<Real> a = jkq_args<Real>(c);
         shape_args<Real>(c, a, cfg);
         // one box: time one wave (every resident cluster sweeps one ray);
-        // batches: time the whole launch (items differ in size)
-        if (c->nbox == 1) a.nitems = cfg.clusters;
+        // batches: time a strided sample of the (box, ray) items
+        if (c->nbox == 1) {
+            a.nitems = cfg.clusters;
+        } else {
+            a.items = c->d_tune_items;
+            a.nitems = c->n_tune;
+        }
         float ms = 1e30f;
         for (int rep = 0; rep < 2 && rc == PORTA_OK; ++rep) {
             cudaError_t e = cudaEventRecord(e0, c->stream);
@@ -380,7 +394,8 @@ int autotune_t(porta_ctx *c)
             ms = std::min(ms, t);
         }
         if (rc != PORTA_OK) break;
-        double waves = c->nbox == 1 ? std::ceil((double)c->nray / cfg.clusters) : 1.0;
+        double waves = c->nbox == 1 ? std::ceil((double)c->nray / cfg.clusters)
+                                    : (double)c->nbox * c->nray / c->n_tune;
         double est = ms * waves;
         if (est < best) {
             best = est;
@@ -393,6 +408,7 @@ int autotune_t(porta_ctx *c)
         c->opt_cluster = pick.cluster;
         c->opt_nu_group = pick.F;
         c->have_fs = c->have_jkq = false;
+        drop_graph(c);
     }
     return rc;
 }
@@ -441,9 +457,10 @@ int emergent_t(porta_ctx *c, int ndir, const double *mu, const double *chi, doub
 
 void free_all(porta_ctx *c)
 {
+    drop_graph(c);
     void *ptrs[] = {c->d_atm, c->d_eps, c->d_bpl, c->d_b, c->d_rho, c->d_rhoR, c->d_invn, c->d_geom, c->d_rays,
                     c->d_freq, c->d_part, c->d_tw, c->d_jkq, c->d_lstar, c->d_resid, c->d_err, c->d_boxes,
-                    c->d_items};
+                    c->d_items, c->d_tune_items};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }
@@ -579,6 +596,8 @@ static int create_impl(int nbox, const porta_grid *grids, const porta_atom *at, 
     ok(cudaMalloc(&c->d_geom, (size_t)c->nray * nplane * (prec == PORTA_FP32 ? sizeof(PlaneGeom<float>) : sizeof(PlaneGeom<double>))));
     ok(cudaMalloc(&c->d_boxes, (size_t)nbox * sizeof(BoxDev)));
     ok(dalloc(&c->d_items, (size_t)nbox * c->nray));
+    c->n_tune = (int)std::min<long long>((long long)nbox * c->nray, 256);
+    ok(dalloc(&c->d_tune_items, (size_t)c->n_tune));
     ok(cudaMalloc(&c->d_rays, (size_t)c->nray * (prec == PORTA_FP32 ? sizeof(RayDev<float>) : sizeof(RayDev<double>))));
     ok(cudaMalloc(&c->d_freq, 2 * (size_t)c->n_nu * R));
     ok(cudaMalloc(&c->d_part, (size_t)c->nray * nvox * (c->ns == 1 ? 2 : 4) * R));
@@ -608,6 +627,10 @@ static int create_impl(int nbox, const porta_grid *grids, const porta_atom *at, 
         for (int i = 0; i < nbox; ++i)
             for (int m = 0; m < c->nray; ++m) items[(size_t)i * c->nray + m] = order[i] * c->nray + m;
         ok(cudaMemcpy(c->d_items, items.data(), items.size() * sizeof(int), cudaMemcpyHostToDevice));
+        // autotuner sample: every k-th item, keeping the mix of box sizes
+        std::vector<int> tune(c->n_tune);
+        for (int i = 0; i < c->n_tune; ++i) tune[i] = items[(size_t)i * items.size() / c->n_tune];
+        ok(cudaMemcpy(c->d_tune_items, tune.data(), tune.size() * sizeof(int), cudaMemcpyHostToDevice));
         if (prec == PORTA_FP32) {
             std::vector<PlaneGeom<float>> geom((size_t)c->nray * nplane);
             std::vector<RayDev<float>> rays(c->nray);
@@ -989,6 +1012,63 @@ int porta_autotune(porta_ctx *c, int *cluster, int *nu_group)
         if (nu_group) *nu_group = c->opt_nu_group;
     }
     return rc;
+}
+
+int porta_run_iterations(porta_ctx *c, int iterations, double *max_change)
+{
+    if (!c) return PORTA_EINVAL;
+    if (iterations < 0) return fail(c, PORTA_EINVAL, "run_iterations: negative count");
+    if (!c->have_atm || !c->have_rho) return fail(c, PORTA_ESTATE, "run_iterations: atmosphere or rho not set");
+    if (!c->stream) return fail(c, PORTA_ESTATE, "run_iterations: needs a non-default stream (porta_set_stream)");
+    if (c->graph_exec && c->graph_stream != c->stream) drop_graph(c);
+    if (!c->graph_exec) {
+        // capture one iteration: formal solution, J^K_Q sums, SEE update and residual
+        CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+        int rc = c->precision == PORTA_FP32 ? formal_solve_t<float>(c, -1, nullptr, nullptr)
+                                            : formal_solve_t<double>(c, -1, nullptr, nullptr);
+        cudaError_t e = cudaSuccess;
+        if (rc == PORTA_OK) {
+            if (c->precision == PORTA_FP32)
+                e = c->ns == 1 ? run_jkq_finalize<float, 1>(c->nvox, c->nray, c->d_part, c->d_tw, c->d_jkq, c->d_lstar, c->stream)
+                               : run_jkq_finalize<float, 4>(c->nvox, c->nray, c->d_part, c->d_tw, c->d_jkq, c->d_lstar, c->stream);
+            else
+                e = c->ns == 1 ? run_jkq_finalize<double, 1>(c->nvox, c->nray, c->d_part, c->d_tw, c->d_jkq, c->d_lstar, c->stream)
+                               : run_jkq_finalize<double, 4>(c->nvox, c->nray, c->d_part, c->d_tw, c->d_jkq, c->d_lstar, c->stream);
+            if (e == cudaSuccess) e = cudaMemsetAsync(c->d_resid, 0, sizeof(unsigned long long), c->stream);
+            if (e == cudaSuccess)
+                e = c->precision == PORTA_FP32
+                        ? run_see<float>(c->nvox, c->nl, c->model, c->bcrit, c->d_eps, c->d_bpl, c->d_b, c->d_jkq,
+                                         c->d_lstar, c->d_rho, c->d_rhoR, c->d_resid, c->stream)
+                        : run_see<double>(c->nvox, c->nl, c->model, c->bcrit, c->d_eps, c->d_bpl, c->d_b, c->d_jkq,
+                                          c->d_lstar, c->d_rho, c->d_rhoR, c->d_resid, c->stream);
+        }
+        cudaGraph_t g = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
+        if (rc != PORTA_OK) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        if (e == cudaSuccess) e = e2;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&c->graph_exec, g, 0);
+        if (e != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            c->graph_exec = nullptr;
+            return fail(c, PORTA_ECUDA, std::string("run_iterations: graph capture: ") + cudaGetErrorString(e));
+        }
+        c->graph = g;
+        c->graph_stream = c->stream;
+    }
+    for (int it = 0; it < iterations; ++it) CK(cudaGraphLaunch(c->graph_exec, c->stream));
+    c->have_fs = c->have_jkq = false;
+    if (max_change) {
+        unsigned long long bits = 0;
+        CK(cudaMemcpyAsync(&bits, c->d_resid, sizeof(bits), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        double v;
+        std::memcpy(&v, &bits, sizeof(v));
+        *max_change = v;
+    }
+    return PORTA_OK;
 }
 
 int porta_launch_info(const porta_ctx *c, int *clusters, int *cluster_size, int *nu_group, int *smem_bytes)

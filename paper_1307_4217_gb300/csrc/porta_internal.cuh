@@ -129,7 +129,13 @@ struct porta_ctx {
     std::vector<double> blx, bly;
     void *d_boxes = nullptr;       // nbox BoxDev
     int *d_items = nullptr;        // nbox*nray work items ordered by decreasing cost
+    int *d_tune_items = nullptr;   // strided sample of the work items for the autotuner
+    int n_tune = 0;
     int *d_err = nullptr;
+    // CUDA graph of one Jacobi iteration (porta_run_iterations)
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    cudaStream_t graph_stream = nullptr;
     // last launch of the formal solution
     porta::LaunchCfg last{};
 };

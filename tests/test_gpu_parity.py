@@ -215,3 +215,21 @@ def test_autotune_picks_a_valid_shape_and_keeps_parity():
     jg, lg = ctx.accumulate_jkq()
     _, (jo, lo) = oracle_fs(atm, 1, 2, 4, 9, rho)
     _check_j(jg, lg, jo, lo, 1e-5)
+
+
+def test_graph_iterations_match_eager_iterations():
+    torch = pytest.importorskip("torch")
+    atm = polarized_case(12, 10, 12, seed=25)
+    rho = initial_rho(atm, 1, seed=26)
+    eager = make_ctx(atm, 1, 3, 8, 9, P.PORTA_FP64, rho=rho)
+    for _ in range(3):
+        eager.formal_solve()
+        eager.accumulate_jkq(want=False)
+        mc_e = eager.see_update()
+    graph = make_ctx(atm, 1, 3, 8, 9, P.PORTA_FP64, rho=rho)
+    stream = torch.cuda.Stream()
+    graph.set_stream(stream)
+    mc_g = graph.run_iterations(1)
+    mc_g = graph.run_iterations(2)
+    assert mc_g == mc_e
+    assert np.array_equal(graph.get_rho(), eager.get_rho())
