@@ -83,6 +83,11 @@ def _declare(L):
         "or_formal_solve": (_I, [_P, _P, _P, _P]),
         "or_formal_solve_part": (_I, [_P, _P, _I, _I, _I, _I, _P, _P]),
         "or_emergent": (_I, [_P, _P, _I, _P, _P, _P]),
+        "or_emergent_vjp": (_I, [_P, _P, _I, _P, _P, _P, _P, _P, _P]),
+        "or_coeffs_deriv": (None, [_D, _P, _P]),
+        "or_control_point_vjp": (None, [_D, _D, _D, _D, _D, _I, _I, _D, _P]),
+        "or_step_vjp": (_I, [_I, _P, _P, _P, _P, _P, _D, _P, _D, _D, _I, _I, _P,
+                             _P, _P, _P, _P, _P, _P, _P]),
         "or_flops_reset": (None, [_I]),
         "or_flops_get": (ctypes.c_longlong, []),
         "or_nray": (_I, [_P]),
@@ -242,6 +247,50 @@ def emergent(prob, rho, mu, chi):
     out = np.zeros(len(mu) * prob.n_nu * ny * nx * ns)
     assert lib().or_emergent(prob.ref, _ptr(rho), len(mu), _ptr(mu), _ptr(chi), _ptr(out)) == 0
     return out.reshape(len(mu), prob.n_nu, ny, nx, ns)
+
+
+def coeffs_deriv(tau):
+    """d/dtau of (e^-tau, psi'_M, psi'_O, w_M, w_O, w_C)."""
+    c = coeffs(tau)
+    d = np.zeros(6)
+    lib().or_coeffs_deriv(float(tau), _ptr(c), _ptr(d))
+    return d
+
+
+def control_point_vjp(yM, yO, yP, hM, hP, has_p=True, method=BESSER, gc=1.0):
+    """Gradient of the control point with respect to (yM, yO, yP, hM, hP), times gc."""
+    g = np.zeros(5)
+    lib().or_control_point_vjp(yM, yO, yP, hM, hP, int(has_p), method, float(gc), _ptr(g))
+    return g
+
+
+def step_vjp(ns, IM, etaM, epsM, etaO, epsO, etaP_I, epsP, dsM, dsP, gIO, has_p=True, method=BESSER):
+    """Reverse mode of ``step``: gradients with respect to (IM, etaM[7], epsM, etaO[7], epsO, etaP_I, epsP)."""
+    a = [_f64(x) for x in (IM, etaM, epsM, etaO, epsO, epsP, gIO)]
+    out = dict(IM=np.zeros(ns), etaM=np.zeros(7), epsM=np.zeros(ns), etaO=np.zeros(7),
+               epsO=np.zeros(ns), etaP=np.zeros(1), epsP=np.zeros(ns))
+    rc = lib().or_step_vjp(ns, _ptr(a[0]), _ptr(a[1]), _ptr(a[2]), _ptr(a[3]), _ptr(a[4]), float(etaP_I),
+                           _ptr(a[5]), float(dsM), float(dsP), int(has_p), method, _ptr(a[6]),
+                           *[_ptr(out[k]) for k in ("IM", "etaM", "epsM", "etaO", "epsO", "etaP", "epsP")])
+    assert rc == 0
+    out["etaP"] = float(out["etaP"][0])
+    return out
+
+
+def emergent_vjp(prob, rho, mu, chi, gout):
+    """Adjoint of ``emergent``: gradients of sum(gout * emergent(...)) with respect to per-voxel
+    chi, e = chi S^0_0 (multipole ratios S^K_Q / S^0_0 fixed) and B (3, nz, ny, nx)."""
+    rho = _f64(rho).ravel()
+    mu = _f64(mu); chi = _f64(chi)
+    ns = ns_of(prob.model)
+    nz, ny, nx = prob.shape
+    gout = _f64(gout).ravel()
+    assert gout.size == len(mu) * prob.n_nu * ny * nx * ns
+    g_chi = np.zeros(prob.nvox); g_e = np.zeros(prob.nvox); g_b = np.zeros(3 * prob.nvox)
+    rc = lib().or_emergent_vjp(prob.ref, _ptr(rho), len(mu), _ptr(mu), _ptr(chi), _ptr(gout),
+                               _ptr(g_chi), _ptr(g_e), _ptr(g_b))
+    assert rc == 0, rc
+    return g_chi.reshape(prob.shape), g_e.reshape(prob.shape), g_b.reshape((3,) + prob.shape)
 
 
 def initial_rho(prob, atm):

@@ -205,3 +205,199 @@ int or_step(int ns, const double *IM, const double *etaM, const double *epsM,
     OR_FLOPS(2);
     return 0;
 }
+
+/* ------------------------------------------------------------------------
+ * Reverse mode of the step (adjoint sweep of the emergent Stokes vector).
+ * ------------------------------------------------------------------------ */
+
+/* d/dt of (e^-t, psi'_M, psi'_O, w_M, w_O, w_C), differentiating the closed
+   forms of Eqs. 8-12 and writing the result through the coefficients
+   themselves:
+     de = -e,               dpsi'_M = e - psi'_M/t,   dpsi'_O = psi'_M/t,
+     dw_M = e - 2 w_M/t,    dw_O = w_C/t,             dw_C = 2 (psi'_M - w_C)/t.
+   In these forms the cancellation is at most a factor of a few for every
+   t > 0, so the derivatives are as accurate as the coefficients. */
+void or_coeffs_deriv(double t, const double c[6], double dc[6])
+{
+    dc[0] = -c[0];
+    dc[1] = c[0] - c[1] / t;
+    dc[2] = c[1] / t;
+    dc[3] = c[0] - 2.0 * c[3] / t;
+    dc[4] = c[5] / t;
+    dc[5] = 2.0 * (c[1] - c[5]) / t;
+}
+
+/* Gradient of the control point (or_control_point) with respect to
+   (y_M, y_O, y_P, h_M, h_P), times gc, on the branch the control point takes:
+   reverse mode through steps 1-9 in the opposite order. */
+void or_control_point_vjp(double yM, double yO, double yP, double hM, double hP, int has_p, int method,
+                          double gc, double g[5])
+{
+    for (int i = 0; i < 5; i++) g[i] = 0.0;
+    if (!has_p) { g[0] = 0.5 * gc; g[1] = 0.5 * gc; return; }
+    double dM = (yO - yM) / hM, dP = (yP - yO) / hP;
+    double s = hM + hP;
+    double yp = (hM * dP + hP * dM) / s;
+    double g_yp;
+    if (method == OR_DELOPAR) {
+        /* c = y_O - h_M y'_O / 2 */
+        g[1] += gc;
+        g[3] += -0.5 * yp * gc;
+        g_yp = -0.5 * hM * gc;
+    } else {
+        if (dM * dP <= 0.0) { g[1] = gc; return; }                      /* step 2 */
+        double cM = yO - 0.5 * hM * yp, cP = yO + 0.5 * hP * yp;
+        if (cM < dmin(yM, yO) || cM > dmax(yM, yO)) { g[0] = gc; return; }   /* step 6 */
+        int clip = cP < dmin(yO, yP) || cP > dmax(yO, yP);               /* step 7 */
+        double cPv = clip ? yP : cP;
+        double yp2 = (cPv - yO) / (0.5 * hP);
+        /* step 9: c = y_O - h_M yp2 / 2 */
+        g[1] += gc;
+        g[3] += -0.5 * yp2 * gc;
+        double g_yp2 = -0.5 * hM * gc;
+        /* step 8: yp2 = 2 (c_P - y_O) / h_P */
+        double g_cP = 2.0 * g_yp2 / hP;
+        g[1] -= 2.0 * g_yp2 / hP;
+        g[4] -= 2.0 * (cPv - yO) / (hP * hP) * g_yp2;
+        if (clip) { g[2] += g_cP; return; }
+        /* step 4: c_P = y_O + h_P y'_O / 2 */
+        g[1] += g_cP;
+        g[4] += 0.5 * yp * g_cP;
+        g_yp = 0.5 * hP * g_cP;
+    }
+    /* step 3 (Eq. 6): y'_O = (h_M d_P + h_P d_M) / (h_M + h_P) */
+    g[3] += (dP - yp) / s * g_yp;
+    g[4] += (dM - yp) / s * g_yp;
+    double g_dP = hM / s * g_yp, g_dM = hP / s * g_yp;
+    /* step 1 */
+    g[1] += g_dM / hM;
+    g[0] -= g_dM / hM;
+    g[3] -= dM / hM * g_dM;
+    g[2] += g_dP / hP;
+    g[1] -= g_dP / hP;
+    g[4] -= dP / hP * g_dP;
+}
+
+/* gradient of K' (kprime) with respect to the seven propagation-matrix elements, added to g_eta */
+static void kprime_vjp(const double *eta, double gK[4][4], double *g_eta)
+{
+    double a = 1.0 / eta[0];
+    double gx[7];
+    gx[1] = gK[0][1] + gK[1][0];       /* eta_Q */
+    gx[2] = gK[0][2] + gK[2][0];       /* eta_U */
+    gx[3] = gK[0][3] + gK[3][0];       /* eta_V */
+    gx[4] = gK[2][3] - gK[3][2];       /* rho_Q */
+    gx[5] = gK[3][1] - gK[1][3];       /* rho_U */
+    gx[6] = gK[1][2] - gK[2][1];       /* rho_V */
+    for (int i = 1; i < 7; i++) {
+        g_eta[i] += gx[i] * a;
+        g_eta[0] -= gx[i] * eta[i] * a * a;
+    }
+}
+
+/*
+ * Reverse mode of or_step: given gIO = dL/dI_O, the gradients with respect
+ * to I_M, the interpolated propagation matrix and emissivity at M, the node
+ * values at O and the interpolated eta_I and emissivity at P (all outputs are
+ * overwritten). kappa^-1 I_O = rhs gives d rhs = kappa^-T gIO and
+ * d(kappa^-1) = -d rhs I_O^T; the rest follows the forward step backwards.
+ */
+int or_step_vjp(int ns, const double *IM, const double *etaM, const double *epsM,
+                const double *etaO, const double *epsO, double etaP_I, const double *epsP,
+                double dsM, double dsP, int has_p, int method, const double *gIO,
+                double *gIM, double *g_etaM, double *g_epsM, double *g_etaO, double *g_epsO,
+                double *g_etaP, double *g_epsP)
+{
+    double SM[4], SO[4], SP[4] = {0, 0, 0, 0};
+    for (int s = 0; s < ns; s++) {
+        SM[s] = epsM[s] / etaM[0];
+        SO[s] = epsO[s] / etaO[0];
+        if (has_p) SP[s] = epsP[s] / etaP_I;
+    }
+    double tauMO = 0.5 * (etaM[0] + etaO[0]) * dsM;
+    double tauOP = has_p ? 0.5 * (etaO[0] + etaP_I) * dsP : 0.0;
+    double c[6];
+    or_coeffs(tauMO, c);
+    double cM[4];
+    for (int s = 0; s < ns; s++) cM[s] = or_control_point(SM[s], SO[s], SP[s], tauMO, tauOP, has_p, method);
+
+    double g_c[6] = {0, 0, 0, 0, 0, 0}, g_SM[4] = {0, 0, 0, 0}, g_SO[4] = {0, 0, 0, 0};
+    double g_SP[4] = {0, 0, 0, 0}, g_cM[4] = {0, 0, 0, 0};
+    for (int s = 0; s < ns; s++) { gIM[s] = 0.0; g_epsM[s] = 0.0; g_epsO[s] = 0.0; g_epsP[s] = 0.0; }
+    for (int q = 0; q < 7; q++) { g_etaM[q] = 0.0; g_etaO[q] = 0.0; }
+    *g_etaP = 0.0;
+    if (ns == 1) {
+        /* I_O = e I_M + w_M S_M + w_O S_O + w_C c_M */
+        double g = gIO[0];
+        g_c[0] = g * IM[0]; gIM[0] = g * c[0];
+        g_c[3] = g * SM[0]; g_SM[0] = g * c[3];
+        g_c[4] = g * SO[0]; g_SO[0] = g * c[4];
+        g_c[5] = g * cM[0]; g_cM[0] = g * c[5];
+    } else {
+        double kM[4][4], kO[4][4], A[4][4], At[4][4], rhs[4], IO[4], g_rhs[4], b[4];
+        kprime(etaM, kM);
+        kprime(etaO, kO);
+        for (int r = 0; r < 4; r++) {
+            double acc = c[0] * IM[r];
+            for (int s = 0; s < 4; s++) acc -= c[1] * kM[r][s] * IM[s];
+            rhs[r] = acc + c[3] * SM[r] + c[4] * SO[r] + c[5] * cM[r];
+            for (int s = 0; s < 4; s++) A[r][s] = (r == s ? 1.0 : 0.0) + c[2] * kO[r][s];
+        }
+        for (int r = 0; r < 4; r++)
+            for (int s = 0; s < 4; s++) At[r][s] = A[s][r];
+        double Ac[4][4];
+        for (int r = 0; r < 4; r++) { b[r] = rhs[r]; for (int s = 0; s < 4; s++) Ac[r][s] = A[r][s]; }
+        if (gauss_solve(4, Ac, b, IO) != 0) return -1;
+        for (int r = 0; r < 4; r++) b[r] = gIO[r];
+        if (gauss_solve(4, At, b, g_rhs) != 0) return -1;
+        double g_kM[4][4], g_kO[4][4];
+        for (int r = 0; r < 4; r++)
+            for (int s = 0; s < 4; s++) {
+                double gA = -g_rhs[r] * IO[s];
+                g_c[2] += gA * kO[r][s];
+                g_kO[r][s] = c[2] * gA;
+                g_kM[r][s] = 0.0;
+            }
+        for (int r = 0; r < 4; r++) {
+            g_c[0] += g_rhs[r] * IM[r];
+            gIM[r] += c[0] * g_rhs[r];
+            for (int s = 0; s < 4; s++) {
+                g_c[1] -= g_rhs[r] * kM[r][s] * IM[s];
+                g_kM[r][s] -= g_rhs[r] * c[1] * IM[s];
+                gIM[s] -= g_rhs[r] * c[1] * kM[r][s];
+            }
+            g_c[3] += g_rhs[r] * SM[r]; g_SM[r] += c[3] * g_rhs[r];
+            g_c[4] += g_rhs[r] * SO[r]; g_SO[r] += c[4] * g_rhs[r];
+            g_c[5] += g_rhs[r] * cM[r]; g_cM[r] += c[5] * g_rhs[r];
+        }
+        kprime_vjp(etaM, g_kM, g_etaM);
+        kprime_vjp(etaO, g_kO, g_etaO);
+    }
+    double g_hM = 0.0, g_hP = 0.0;
+    for (int s = 0; s < ns; s++) {
+        double g5[5];
+        or_control_point_vjp(SM[s], SO[s], SP[s], tauMO, tauOP, has_p, method, g_cM[s], g5);
+        g_SM[s] += g5[0]; g_SO[s] += g5[1]; g_SP[s] += g5[2];
+        g_hM += g5[3]; g_hP += g5[4];
+    }
+    double dc[6];
+    or_coeffs_deriv(tauMO, c, dc);
+    for (int i = 0; i < 6; i++) g_hM += g_c[i] * dc[i];
+    g_etaM[0] += 0.5 * dsM * g_hM;
+    g_etaO[0] += 0.5 * dsM * g_hM;
+    if (has_p) {
+        g_etaO[0] += 0.5 * dsP * g_hP;
+        *g_etaP += 0.5 * dsP * g_hP;
+    }
+    for (int s = 0; s < ns; s++) {
+        g_epsM[s] += g_SM[s] / etaM[0];
+        g_etaM[0] -= g_SM[s] * SM[s] / etaM[0];
+        g_epsO[s] += g_SO[s] / etaO[0];
+        g_etaO[0] -= g_SO[s] * SO[s] / etaO[0];
+        if (has_p) {
+            g_epsP[s] += g_SP[s] / etaP_I;
+            *g_etaP -= g_SP[s] * SP[s] / etaP_I;
+        }
+    }
+    return 0;
+}

@@ -267,3 +267,131 @@ int or_emergent(const or_problem *p, const double *rho, int ndir, const double *
     free(xf); free(wf); free(I); free(lo);
     return rc;
 }
+
+/* ------------------------------------------------------------------------
+ * Adjoint of the emergent Stokes vector (reverse-mode sweep).
+ *
+ * Parameters per voxel: chi (line-centre opacity), e = chi S^0_0 (emission
+ * scale; the multipoles S^K_Q = rho^K_Q scale as e/chi with their ratios to
+ * S^0_0 held fixed) and B = (Bx, By, Bz). With phi = exp(-(x - s)^2) and
+ * beta = 2 gbar zeta, the node coefficients are
+ *   eta_I = chi phi,           eta_V = beta (x - s)(B.Omega) chi phi,
+ *   eps_i = e phi S_i/S^0_0,   eps_V = beta (x - s)(B.Omega) e phi
+ * (unpolarized atom: eps_I = e phi). The boundary intensity at the bottom is
+ * the Planck function, not a parameter.
+ * ------------------------------------------------------------------------ */
+/* add the parameter gradients of node v given dL/d(eta 7 elements) and dL/d(eps) at frequency x */
+static void node_vjp(const or_problem *p, const double *rho, long v, const or_ray *r, double x,
+                     const double *g_eta, const double *g_eps, double *g_chi, double *g_e, double *g_b)
+{
+    long nv = (long)p->nx * p->ny * p->nz;
+    double xs = x - shift(p, v, r);
+    double phi = exp(-xs * xs);
+    if (p->model == OR_MODEL_UNPOL) {
+        g_chi[v] += phi * g_eta[0];
+        g_e[v] += phi * g_eps[0];
+        return;
+    }
+    const double *s = rho + 6 * v;
+    double beta = 2.0 * p->gbar * p->zeta;
+    double bpar = p->bx[v] * r->ox + p->by[v] * r->oy + p->bz[v] * r->oz;
+    double chi = p->chi[v], e = chi * s[0];
+    g_chi[v] += phi * g_eta[0] + beta * xs * bpar * phi * g_eta[3];
+    double ge = beta * xs * bpar * phi * g_eps[3];
+    for (int i = 0; i < 3; i++) ge += phi * angular_source(r->t + 6 * i, s) / s[0] * g_eps[i];
+    g_e[v] += ge;
+    double gb = beta * xs * phi * (chi * g_eta[3] + e * g_eps[3]);
+    g_b[v] += gb * r->ox;
+    g_b[nv + v] += gb * r->oy;
+    g_b[2 * nv + v] += gb * r->oz;
+}
+
+int or_emergent_vjp(const or_problem *p, const double *rho, int ndir, const double *mu, const double *chi,
+                    const double *gout, double *g_chi, double *g_e, double *g_b)
+{
+    if (check(p)) return -1;
+    if (p->model != OR_MODEL_UNPOL && !g_b) return -1;
+    int ns = or_ns(p->model), nn = p->n_nu;
+    int nx = p->nx, ny = p->ny, nz = p->nz;
+    long nv = (long)nx * ny * nz, nxy = (long)nx * ny;
+    double dx = p->lx / nx, dy = p->ly / ny;
+    double *xf = malloc(sizeof(double) * nn), *wf = malloc(sizeof(double) * nn);
+    double *I = malloc(sizeof(double) * nv * ns), *lo = malloc(sizeof(double) * nv);
+    double *lam = malloc(sizeof(double) * nv * ns);
+    if (!xf || !wf || !I || !lo || !lam) return -2;
+    or_freqs(nn, p->x_max, xf, wf);
+    memset(g_chi, 0, sizeof(double) * nv);
+    memset(g_e, 0, sizeof(double) * nv);
+    if (g_b) memset(g_b, 0, sizeof(double) * 3 * nv);
+    int rc = 0;
+    for (int d = 0; d < ndir && rc == 0; d++) {
+        if (!(mu[d] > 0.0 && mu[d] <= 1.0)) { rc = -1; break; }
+        or_ray r;
+        make_ray(mu[d], chi[d], 0.0, &r);
+        double amu = fabs(r.mu);
+        for (int jf = 0; jf < nn && rc == 0; jf++) {
+            double x = xf[jf];
+            rc = sweep(p, rho, &r, x, I, lo);                    /* forward: I on every plane */
+            memset(lam, 0, sizeof(double) * nv * ns);
+            memcpy(lam + (long)(nz - 1) * nxy * ns, gout + ((long)d * nn + jf) * nxy * ns, sizeof(double) * nxy * ns);
+            for (int k = nz - 1; k >= 1 && rc == 0; k--) {       /* planes in reverse sweep order */
+                int ku = k - 1, kd = k + 1, has_p = k + 1 < nz;
+                double dsM = fabs(p->z[k] - p->z[ku]) / amu;
+                double dsP = has_p ? fabs(p->z[kd] - p->z[k]) / amu : 0.0;
+                for (int j = 0; j < ny; j++)
+                    for (int i = 0; i < nx; i++) {
+                        long v = vox(p, i, j, k);
+                        int iM[4], jM[4], iP[4], jP[4];
+                        double wM[4], wP[4];
+                        double etaM[7] = {0}, epsM[4] = {0}, IM[4] = {0};
+                        bilinear(p, i - dsM * r.ox / dx, j - dsM * r.oy / dy, iM, jM, wM);
+                        for (int c = 0; c < 4; c++) {
+                            long u = vox(p, iM[c], jM[c], ku);
+                            double e7[7], e4[4];
+                            node_coeffs(p, rho, u, &r, x, e7, e4);
+                            for (int q = 0; q < 7; q++) etaM[q] += wM[c] * e7[q];
+                            for (int s = 0; s < ns; s++) { epsM[s] += wM[c] * e4[s]; IM[s] += wM[c] * I[u * ns + s]; }
+                        }
+                        double etaO[7], epsO[4];
+                        node_coeffs(p, rho, v, &r, x, etaO, epsO);
+                        double etaP = 0.0, epsP[4] = {0};
+                        if (has_p) {
+                            bilinear(p, i + dsP * r.ox / dx, j + dsP * r.oy / dy, iP, jP, wP);
+                            for (int c = 0; c < 4; c++) {
+                                long u = vox(p, iP[c], jP[c], kd);
+                                double e7[7], e4[4];
+                                node_coeffs(p, rho, u, &r, x, e7, e4);
+                                etaP += wP[c] * e7[0];
+                                for (int s = 0; s < ns; s++) epsP[s] += wP[c] * e4[s];
+                            }
+                        }
+                        double gIM[4], gEM[7], gSM[4], gEO[7], gSO[4], gEP, gSP[4];
+                        if (or_step_vjp(ns, IM, etaM, epsM, etaO, epsO, etaP, epsP, dsM, dsP, has_p, p->method,
+                                        lam + v * ns, gIM, gEM, gSM, gEO, gSO, &gEP, gSP) != 0) {
+                            rc = -3;
+                            break;
+                        }
+                        /* transposed bilinear interpolation at M: scatter to the 4 upwind nodes */
+                        for (int c = 0; c < 4; c++) {
+                            long u = vox(p, iM[c], jM[c], ku);
+                            double ge7[7], ge4[4];
+                            for (int s = 0; s < ns; s++) lam[u * ns + s] += wM[c] * gIM[s];
+                            for (int q = 0; q < 7; q++) ge7[q] = wM[c] * gEM[q];
+                            for (int s = 0; s < ns; s++) ge4[s] = wM[c] * gSM[s];
+                            node_vjp(p, rho, u, &r, x, ge7, ge4, g_chi, g_e, g_b);
+                        }
+                        node_vjp(p, rho, v, &r, x, gEO, gSO, g_chi, g_e, g_b);
+                        if (has_p)
+                            for (int c = 0; c < 4; c++) {
+                                long u = vox(p, iP[c], jP[c], kd);
+                                double ge7[7] = {wP[c] * gEP, 0, 0, 0, 0, 0, 0}, ge4[4];
+                                for (int s = 0; s < ns; s++) ge4[s] = wP[c] * gSP[s];
+                                node_vjp(p, rho, u, &r, x, ge7, ge4, g_chi, g_e, g_b);
+                            }
+                    }
+            }
+        }
+    }
+    free(xf); free(wf); free(I); free(lo); free(lam);
+    return rc;
+}

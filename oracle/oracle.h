@@ -88,6 +88,21 @@ int or_formal_solve_part(const or_problem *p, const double *rho, int m0, int m1,
 int or_emergent(const or_problem *p, const double *rho, int ndir, const double *mu,
                 const double *chi, double *out);
 
+/* adjoint of or_emergent: gradients of L = sum gout * out with respect to per-voxel chi,
+   e = chi S^0_0 (ratios S^K_Q / S^0_0 fixed) and B (g_b: 3 x nvox, may be NULL for the
+   unpolarized model); gout has the layout of out */
+int or_emergent_vjp(const or_problem *p, const double *rho, int ndir, const double *mu,
+                    const double *chi, const double *gout, double *g_chi, double *g_e, double *g_b);
+/* reverse mode of the step coefficients, control point and step (derivatives for the adjoint) */
+void or_coeffs_deriv(double tau, const double c[6], double dc[6]);
+void or_control_point_vjp(double yM, double yO, double yP, double hM, double hP, int has_p, int method,
+                          double gc, double g[5]);
+int or_step_vjp(int ns, const double *IM, const double *etaM, const double *epsM,
+                const double *etaO, const double *epsO, double etaP_I, const double *epsP,
+                double dsM, double dsP, int has_p, int method, const double *gIO,
+                double *gIM, double *g_etaM, double *g_epsM, double *g_etaO, double *g_epsO,
+                double *g_etaP, double *g_epsP);
+
 /* flop counter for one update (counted once per voxel.ray.frequency) */
 void or_flops_reset(int enable);
 long long or_flops_get(void);

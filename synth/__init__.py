@@ -112,3 +112,11 @@ CONFIGS = {
     "pol64": dict(model=1, n_mu=5, n_chi=16, n_nu=21),
     "batched256": dict(model=1, n_mu=4, n_chi=10, n_nu=21),
 }
+
+
+def emergent_directions():
+    """Outgoing lines of sight of the differentiation workload: the vertical and
+    four oblique rays (mu = 0.5 at azimuths 0, pi/2, pi, 3 pi/2)."""
+    mu = np.array([1.0, 0.5, 0.5, 0.5, 0.5])
+    az = np.array([0.0, 0.0, 0.5 * np.pi, np.pi, 1.5 * np.pi])
+    return mu, az
