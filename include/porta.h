@@ -253,6 +253,38 @@ int porta_run_iterations(porta_ctx *c, int iterations, double *max_change);
    cluster, frequencies per pass, dynamic shared memory per CTA (bytes). */
 int porta_launch_info(const porta_ctx *c, int *clusters, int *cluster_size, int *nu_group, int *smem_bytes);
 
+/* Reverse mode of porta_emergent_stokes (gradients of emergent Stokes
+   profiles; the paper has no counterpart, Sec. 3 defines the forward map).
+   L = sum(grad_out * out) with out as porta_emergent_stokes writes it, at the
+   current atmosphere and rho, as a function of per-voxel
+     chi  (line-centre opacity),
+     e    = chi S^0_0 (emission scale; the multipoles rho^K_Q scale as e/chi
+            with their ratios to S^0_0 held fixed; needs S^0_0 > 0),
+     B    (magnetic field vector, through eta_V and eps_V of the weak-field
+            Zeeman term).
+   Runs the forward emergent sweep keeping the Stokes vectors of every plane
+   (a device tape of ndir*n_nu*nvox*NS reals, kept by the context for reuse),
+   then the adjoint sweep (planes in reverse order, the forward step
+   recomputed and differentiated on the branch the BESSER control point took),
+   then a fixed-order sum over directions and frequency groups; the result
+   does not depend on scheduling. The sweeps run in the context's precision;
+   gradients are accumulated per node in that precision and summed in FP64.
+   grad_out: ndir*n_nu*ny*nx*NS doubles, layout of porta_emergent_stokes.
+   out: the forward emergent Stokes (may be NULL). g_chi, g_e: nvox doubles;
+   g_b: 3*nvox doubles, [component x|y|z][voxel] (NULL allowed for the
+   unpolarized model). All caller arrays are host or device per `where`;
+   mu, chi are host arrays. Single-box contexts; PORTA_ESTATE without
+   atmosphere and rho. Synchronous. */
+int porta_emergent_vjp(porta_ctx *c, int ndir, const double *mu, const double *chi, const double *grad_out,
+                       double *out, double *g_chi, double *g_e, double *g_b, int where);
+
+/* Launch shape of the adjoint sweep: cluster size (1..16, <= ny) and
+   frequencies per pass; 0 selects automatically (cost model). */
+int porta_set_adjoint_launch(porta_ctx *c, int cluster, int nu_group);
+
+/* Launch statistics of the last adjoint sweep (as porta_launch_info). */
+int porta_adjoint_info(const porta_ctx *c, int *clusters, int *cluster_size, int *nu_group, int *smem_bytes);
+
 #ifdef __cplusplus
 }
 #endif

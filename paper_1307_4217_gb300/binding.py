@@ -71,6 +71,9 @@ _SIGS = {
     "porta_run_iterations": (_I, [_P, _I, _P]),
     "porta_eval_coefficients": (_I, [_I, _I, _P, _P]),
     "porta_formal_solve_noalloc": (_I, [_P, _P, _P, _P, _P, _P, _P, _P]),
+    "porta_emergent_vjp": (_I, [_P, _I, _P, _P, _P, _P, _P, _P, _P, _I]),
+    "porta_set_adjoint_launch": (_I, [_P, _I, _I]),
+    "porta_adjoint_info": (_I, [_P, _P, _P, _P, _P]),
 }
 
 _lib = None
@@ -239,6 +242,20 @@ def porta_launch_info(h):
     return rc, dict(clusters=v[0].value, cluster=v[1].value, nu_group=v[2].value, smem=v[3].value)
 
 
+def porta_emergent_vjp(h, ndir, mu_ptr, chi_ptr, grad_ptr, out_ptr, gchi_ptr, ge_ptr, gb_ptr, where):
+    return lib().porta_emergent_vjp(h, ndir, mu_ptr, chi_ptr, grad_ptr, out_ptr, gchi_ptr, ge_ptr, gb_ptr, where)
+
+
+def porta_set_adjoint_launch(h, cluster, nu_group):
+    return lib().porta_set_adjoint_launch(h, cluster, nu_group)
+
+
+def porta_adjoint_info(h):
+    v = [ctypes.c_int() for _ in range(4)]
+    rc = lib().porta_adjoint_info(h, *[ctypes.byref(x) for x in v])
+    return rc, dict(clusters=v[0].value, cluster=v[1].value, nu_group=v[2].value, smem=v[3].value)
+
+
 # ---- convenience wrapper ------------------------------------------------------------
 
 class Context:
@@ -349,6 +366,39 @@ class Context:
         p, w, keep = _ptr_where(out)
         self._check(porta_emergent_stokes(self.h, len(mu), mu.ctypes.data, chi.ctypes.data, p, w))
         return out
+
+    def emergent_vjp(self, mu, chi, grad_out, out=None, g_chi=None, g_e=None, g_b=None):
+        """Gradients of sum(grad_out * emergent_stokes(mu, chi)) with respect to per-voxel chi,
+        e = chi S^0_0 (multipole ratios fixed) and B: returns (g_chi, g_e, g_b[, out]).
+        grad_out and the optional output arrays are all numpy (host) or all CUDA tensors."""
+        mu = np.ascontiguousarray(mu, dtype=np.float64)
+        chi = np.ascontiguousarray(chi, dtype=np.float64)
+        pg, where, kg = _ptr_where(grad_out)
+        if g_chi is None:
+            if where == PORTA_DEVICE:
+                import torch
+                dev = grad_out.device
+                g_chi = torch.empty(self.shape, dtype=torch.float64, device=dev)
+                g_e = torch.empty(self.shape, dtype=torch.float64, device=dev)
+                g_b = torch.empty((3,) + self.shape, dtype=torch.float64, device=dev)
+            else:
+                g_chi, g_e, g_b = np.zeros(self.shape), np.zeros(self.shape), np.zeros((3,) + self.shape)
+        ptrs = []
+        for arr in (out, g_chi, g_e, g_b):
+            p, w, keep = _ptr_where(arr)
+            if arr is not None and w != where:
+                raise TypeError("grad_out and the outputs must all be host or all device")
+            ptrs.append(p)
+        self._check(porta_emergent_vjp(self.h, len(mu), mu.ctypes.data, chi.ctypes.data, pg, *ptrs, where))
+        return (g_chi, g_e, g_b) if out is None else (g_chi, g_e, g_b, out)
+
+    def set_adjoint_launch(self, cluster=0, nu_group=0):
+        self._check(porta_set_adjoint_launch(self.h, cluster, nu_group))
+
+    def adjoint_info(self):
+        rc, info = porta_adjoint_info(self.h)
+        self._check(rc)
+        return info
 
     def probe_ray(self, m):
         out = np.zeros((self.nnu,) + self.shape + (self.ns,))

@@ -1,0 +1,572 @@
+// Adjoint (reverse mode) of the emergent-Stokes formal solution (Sec. 3,
+// Eq. 7 with the BESSER control points of Sec. 3.2) at fixed multipoles.
+//
+// Parameters per voxel: the line-centre opacity chi, the emission scale
+// e = chi S^0_0 (the multipoles scale as e/chi with their ratios to S^0_0
+// fixed) and b = bfac B.Omega (bfac = 2 gbar zeta), so that with
+// phi = exp(-(x - s)^2) and xs = x - s the node coefficients are
+//   eta_I = chi phi,        eta_V = b xs chi phi,
+//   eps_i = e phi S_i/S00,  eps_V = b xs e phi      (unpolarized: eps = e phi).
+// Given dL/dI of the top plane (all frequencies of the emergent directions),
+// the kernel returns per (direction, frequency group) dL/dchi, dL/de and
+// dL/db of every node; a second kernel sums the groups in a fixed order and
+// turns dL/db into dL/dB = bfac sum_dir Omega dL/db.
+//
+// Decomposition: the forward sweep's. One thread-block cluster owns one
+// (direction, frequency group); the planes are visited in reverse sweep order
+// with the sheared rows split into strips, one per CTA. The forward Stokes
+// vectors of every plane come from the forward emergent sweep's tape; each
+// step is recomputed locally with the forward's arithmetic (so the control
+// point takes the forward's branch) and differentiated by hand. Every
+// transposed interpolation is a gather, not a scatter, so there are no atomics
+// and the result does not depend on scheduling:
+//   - the upwind Stokes adjoint of a node on plane q-1 gathers the dL/dI_M of
+//     the 4 points of plane q whose upwind stencil holds it;
+//   - the coefficient adjoint of a node on plane q collects its own term as O
+//     (step q), the dL/d(M interpolants) of 4 points of plane q+1 and the
+//     dL/d(P interpolants) of 4 points of plane q-1 (step q-1), and is turned
+//     into parameter gradients once complete.
+// In the sheared frame these stencils are the fixed neighbour offsets
+// (0|-1, 0|-1) and (0|+1, 0|+1); the one row across a strip boundary is read
+// from the neighbouring CTA's shared memory (DSMEM) after a cluster barrier.
+#include <cooperative_groups.h>
+
+#include <algorithm>
+
+#include "device_math.cuh"
+#include "porta_internal.cuh"
+#include "sweep_common.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace porta {
+
+// adjoint values stored per point and frequency:
+//   NM: dL/d(eta_I, [eta_V], eps[NS]) of the M interpolants, and of the node as O
+//   NP: dL/d(eta_I, eps[NS]) of the P interpolants (eta_V is not interpolated at P)
+template <int NS>
+__host__ __device__ constexpr int adj_nm() { return NS == 1 ? 2 : 6; }
+template <int NS>
+__host__ __device__ constexpr int adj_np() { return NS + 1; }
+
+template <typename Real, int NS>
+int adjoint_smem_bytes(int ring_plane, int ipts, int F)
+{
+    constexpr int NM = adj_nm<NS>(), NP = adj_np<NS>();
+    return 3 * ring_plane * 16 + F * ipts * (2 * NS + NM + NP + 2 * NM) * (int)sizeof(Real);
+}
+
+// CTA owning sheared row r when CTA k owns rows floor(k ny / C) .. floor((k+1) ny / C) - 1
+__device__ __forceinline__ int row_owner(int r, int ny, int C)
+{
+    return (int)(((long long)(r + 1) * C + ny - 1) / ny) - 1;
+}
+__device__ __forceinline__ int row_start(int k, int ny, int C) { return (int)(((long long)k * ny) / C); }
+
+// parameter gradients (chi, e, b) of one node at reduced frequency x from the
+// node's total adjoint t = dL/d(eta_I, [eta_V], eps[NS])
+template <typename Real, int NS>
+__device__ __forceinline__ void node_param_grad(const Node<Real, NS> &n, Real x, const Real *t, Real &gchi, Real &ge,
+                                                Real &gb)
+{
+    const Real xs = x - n.s;
+    const Real ph = profile_shape(xs);
+    if constexpr (NS == 1) {
+        gchi += ph * t[0];
+        ge += ph * t[1];
+    } else {
+        const Real bxs = n.b * xs;
+        const Real iS = rcp(n.S00);
+        gchi += ph * (t[0] + bxs * t[1]);
+        ge += ph * ((n.SI * t[2] + n.SQ * t[3] + n.SU * t[4]) * iS + bxs * t[5]);
+        gb += xs * ph * n.chi * (t[1] + n.S00 * t[5]);
+    }
+}
+
+template <typename Real, int NS>
+__device__ __forceinline__ void adjoint_item(const SweepArgs<Real> &a, cg::cluster_group &cluster,
+                                             typename V16<Real>::T *ring, Real *gI, Real *gM, Real *gP, Real *T,
+                                             int d, int g, int rank, int C, int item)
+{
+    constexpr int NM = adj_nm<NS>(), NP = adj_np<NS>();
+    constexpr int NCH = node_words<NS>() * (int)sizeof(Real) / 16;
+    const BoxDev B = a.boxes[0];
+    const int nx = B.nx, ny = B.ny, nz = B.nz, F = a.F;
+    const int rmax = (ny + C - 1) / C;
+    const int row0 = row_start(rank, ny, C);
+    const int R = row_start(rank + 1, ny, C) - row0;
+    // neighbours in the sheared frame: the owner of the row after the strip
+    // (its row 0) and of the row before it (its last row)
+    const int next_row = (row0 + R) % ny;
+    const int next_owner = row_owner(next_row, ny, C);
+    const int prev_row = (row0 + ny - 1) % ny;
+    const int prev_owner = row_owner(prev_row, ny, C);
+    const int prev_last = prev_row - row_start(prev_owner, ny, C);
+    const int ipts = a.ipts_max;
+    const Real *gI_prev = cluster.map_shared_rank(gI, prev_owner);
+    const Real *gM_prev = cluster.map_shared_rank(gM, prev_owner);
+    const Real *gP_next = cluster.map_shared_rank(gP, next_owner);
+    const int j0 = g * F;
+    const int nf = min(F, a.nnu - j0);
+    const PlaneGeom<Real> *G = a.geom + (long long)d * nz;
+    const RayDev<Real> ray = a.rays[d];
+    const long long nxy = (long long)nx * ny;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int chunk = (rmax + 2) * nx;
+    const int plane = NCH * chunk;
+    const int npts = R * nx;
+    const Real *tape = a.store + (long long)d * a.nnu * a.nvox * NS;
+    Real *gout_part = a.gpart + (long long)item * 3 * a.nvox;
+    // buffer offsets: gI[par][f][s][p], gM[f][k][p], gP[f][k][p], T[par][f][k][p]
+    auto xI = [&](int par, int f, int s, int p) { return ((par * F + f) * NS + s) * ipts + p; };
+    auto xM = [&](int f, int k, int p) { return (f * NM + k) * ipts + p; };
+    auto xP = [&](int f, int k, int p) { return (f * NP + k) * ipts + p; };
+    auto xT = [&](int par, int f, int k, int p) { return ((par * F + f) * NM + k) * ipts + p; };
+
+    auto fill = [&](int q) {
+        const PlaneGeom<Real> gq = G[q];
+        const int nn = (R + 2) * nx;
+        for (int idx = tid; idx < nn; idx += nt) {
+            const int lr = idx / nx, c = idx - lr * nx;
+            int pi = c + gq.ax;
+            pi -= pi >= nx ? nx : 0;
+            int pj = (row0 + lr - 1 + gq.ay) % ny;
+            pj += pj < 0 ? ny : 0;
+            const long long v = B.vox0 + ((long long)gq.kz * ny + pj) * nx + pi;
+            ring_store<Real, NS>(ring, plane, chunk, q % 3, idx, make_node<Real, NS>(a, ray, v, d, false));
+        }
+    };
+    // physical voxel of sheared node (c, local row l) of plane q
+    auto voxel = [&](const PlaneGeom<Real> &gq, int c, int l) {
+        int pi = c + gq.ax;
+        pi -= pi >= nx ? nx : 0;
+        const int pj = (row0 + l + gq.ay) % ny;
+        return ((long long)gq.kz * ny + pj) * nx + pi;
+    };
+    // parameter gradients of the nodes of plane pq (ring slot `slot`) from the
+    // adjoint totals T[par] plus, with_p, the P gathers of plane pq-1
+    auto finalize = [&](int pq, int slot, int par, bool with_p, const Real *wP) {
+        const PlaneGeom<Real> gq = G[pq];
+        for (int p = tid; p < npts; p += nt) {
+            const int l = p / nx, c = p - l * nx;
+            const int c1 = c + 1 == nx ? 0 : c + 1;
+            const Node<Real, NS> n = ring_load<Real, NS>(ring, plane, chunk, slot, (l + 1) * nx + c);
+            const bool last = l + 1 == R;
+            const Real *ph = last ? gP_next : gP;
+            const int lh = last ? 0 : (l + 1) * nx;
+            Real gchi = 0, ge = 0, gb = 0;
+            for (int f = 0; f < nf; ++f) {
+                Real t[NM];
+#pragma unroll
+                for (int k = 0; k < NM; ++k) t[k] = T[xT(par, f, k, p)];
+                if (with_p) {
+                    // node (c, l) of plane pq is corner (c-1|c, l-1|l) of the points
+                    // (c+1|c, l+1|l) of plane pq-1
+                    Real gp[NP];
+#pragma unroll
+                    for (int k = 0; k < NP; ++k)
+                        gp[k] = wP[0] * ph[xP(f, k, lh + c1)] + wP[1] * ph[xP(f, k, lh + c)] +
+                                wP[2] * gP[xP(f, k, l * nx + c1)] + wP[3] * gP[xP(f, k, l * nx + c)];
+                    t[0] += gp[0];
+#pragma unroll
+                    for (int s = 0; s < NS; ++s) t[NM - NS + s] += gp[1 + s];
+                }
+                node_param_grad<Real, NS>(n, a.xf[j0 + f], t, gchi, ge, gb);
+            }
+            const long long v = B.vox0 + voxel(gq, c, l);
+            gout_part[v] = gchi;
+            gout_part[a.nvox + v] = ge;
+            gout_part[2 * a.nvox + v] = gb;
+        }
+    };
+
+    fill(nz - 1);
+    fill(nz - 2);
+    for (int p = tid; p < npts; p += nt)
+        for (int f = 0; f < nf; ++f)
+#pragma unroll
+            for (int k = 0; k < NM; ++k) T[xT((nz - 1) & 1, f, k, p)] = Real(0);
+    __syncthreads();
+    cluster.sync();
+
+    for (int q = nz - 1; q >= 1; --q) {
+        const PlaneGeom<Real> gq = G[q], gm = G[q - 1];
+        const bool has_p = q + 1 < nz;
+        const PlaneGeom<Real> gp = has_p ? G[q + 1] : gq;
+        const int sM = (q + 2) % 3, sO = q % 3, sP = (q + 1) % 3;
+        const int par = q & 1, opar = par ^ 1;
+        const Real mx1 = gq.tx, mx0 = Real(1) - gq.tx, my1 = gq.ty, my0 = Real(1) - gq.ty;
+        const Real px0 = gp.tx, px1 = Real(1) - gp.tx, py0 = gp.ty, py1 = Real(1) - gp.ty;
+        const Real wM[4] = {mx0 * my0, mx1 * my0, mx0 * my1, mx1 * my1};
+        const Real wP[4] = {px0 * py0, px1 * py0, px0 * py1, px1 * py1};
+        // weights of the upwind stencils of plane q+1 (Stokes adjoint gather)
+        const Real nx1 = gp.tx, nx0 = Real(1) - gp.tx, ny1 = gp.ty, ny0 = Real(1) - gp.ty;
+        const Real wN[4] = {nx0 * ny0, nx1 * ny0, nx0 * ny1, nx1 * ny1};
+        const Real dsM = gq.ds, dsP = has_p ? gp.ds : Real(0);
+
+        // ---- phase 1: local reverse step at every point of the strip ----
+        for (int p = tid; p < npts; p += nt) {
+            const int l = p / nx, c = p - l * nx;
+            const int c1 = c + 1 == nx ? 0 : c + 1;
+            const int cm = c == 0 ? nx - 1 : c - 1;
+            const Node<Real, NS> nO = ring_load<Real, NS>(ring, plane, chunk, sO, (l + 1) * nx + c);
+            CornerM<Real, NS> kM[4];
+            kM[0] = corner_m<Real, NS>(ring_load<Real, NS>(ring, plane, chunk, sM, (l + 1) * nx + c), wM[0]);
+            kM[1] = corner_m<Real, NS>(ring_load<Real, NS>(ring, plane, chunk, sM, (l + 1) * nx + c1), wM[1]);
+            kM[2] = corner_m<Real, NS>(ring_load<Real, NS>(ring, plane, chunk, sM, (l + 2) * nx + c), wM[2]);
+            kM[3] = corner_m<Real, NS>(ring_load<Real, NS>(ring, plane, chunk, sM, (l + 2) * nx + c1), wM[3]);
+            CornerP<Real, NS> kP[4];
+            if (has_p) {
+                kP[0] = corner_p<Real, NS>(ring_load<Real, NS>(ring, plane, chunk, sP, l * nx + cm), wP[0]);
+                kP[1] = corner_p<Real, NS>(ring_load<Real, NS>(ring, plane, chunk, sP, l * nx + c), wP[1]);
+                kP[2] = corner_p<Real, NS>(ring_load<Real, NS>(ring, plane, chunk, sP, (l + 1) * nx + cm), wP[2]);
+                kP[3] = corner_p<Real, NS>(ring_load<Real, NS>(ring, plane, chunk, sP, (l + 1) * nx + c), wP[3]);
+            } else {
+                kP[0] = kP[1] = kP[2] = kP[3] = corner_p<Real, NS>(nO, Real(0));
+            }
+            // tape positions of the 4 upwind corners (plane q-1)
+            long long vM[4];
+            vM[0] = B.vox0 + voxel(gm, c, l);
+            vM[1] = B.vox0 + voxel(gm, c1, l);
+            vM[2] = B.vox0 + voxel(gm, c, l + 1);
+            vM[3] = B.vox0 + voxel(gm, c1, l + 1);
+            const long long vO = voxel(gq, c, l);
+            // rows of the Stokes-adjoint gather from plane q+1: (c|c-1, l|l-1)
+            const bool first = l == 0;
+            const Real *glo = first ? gI_prev : gI;
+            const int llo = first ? prev_last * nx : (l - 1) * nx;
+
+            for (int f = 0; f < nf; ++f) {
+                const int j = j0 + f;
+                const Real x = a.xf[j];
+                Real lam[NS];
+                if (q == nz - 1) {
+                    const double *go = a.gout + (((long long)d * a.nnu + j) * nxy + (vO - (long long)gq.kz * nxy)) * NS;
+#pragma unroll
+                    for (int s = 0; s < NS; ++s) lam[s] = (Real)go[s];
+                } else {
+#pragma unroll
+                    for (int s = 0; s < NS; ++s)
+                        lam[s] = wN[0] * gI[xI(opar, f, s, l * nx + c)] + wN[1] * gI[xI(opar, f, s, l * nx + cm)] +
+                                 wN[2] * glo[xI(opar, f, s, llo + c)] + wN[3] * glo[xI(opar, f, s, llo + cm)];
+                }
+                // ---- forward recomputation (the forward sweep's arithmetic) ----
+                Real IM[NS];
+#pragma unroll
+                for (int s = 0; s < NS; ++s) IM[s] = Real(0);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const Real *Ik = tape + ((long long)j * a.nvox + vM[k]) * NS;
+#pragma unroll
+                    for (int s = 0; s < NS; ++s) IM[s] += wM[k] * Ik[s];
+                }
+                Real etaM = 0, etaVM = 0, epsM[NS];
+#pragma unroll
+                for (int s = 0; s < NS; ++s) epsM[s] = 0;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const Real xs = x - kM[k].s;
+                    const Real we = kM[k].wchi * profile_shape(xs);
+                    etaM += we;
+                    if constexpr (NS == 1) {
+                        epsM[0] += we * kM[k].S;
+                    } else {
+                        const Real wkv = we * (kM[k].b * xs);
+                        etaVM += wkv;
+                        epsM[0] += we * kM[k].SI;
+                        epsM[1] += we * kM[k].SQ;
+                        epsM[2] += we * kM[k].SU;
+                        epsM[3] += wkv * kM[k].S00;
+                    }
+                }
+                Real etaP = 0, epsP[NS];
+#pragma unroll
+                for (int s = 0; s < NS; ++s) epsP[s] = 0;
+                if (has_p) {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const Real xs = x - kP[k].s;
+                        const Real we = kP[k].wchi * profile_shape(xs);
+                        etaP += we;
+                        if constexpr (NS == 1) {
+                            epsP[0] += we * kP[k].S;
+                        } else {
+                            epsP[0] += we * kP[k].SI;
+                            epsP[1] += we * kP[k].SQ;
+                            epsP[2] += we * kP[k].SU;
+                            epsP[3] += we * (kP[k].bS * xs);
+                        }
+                    }
+                }
+                const Real xsO = x - nO.s;
+                const Real phO = profile_shape(xsO);
+                const Real etaO = nO.chi * phO;
+                Real SO[NS], SM[NS], SP[NS];
+                const Real iM = rcp(etaM), iO = rcp(etaO);
+                if constexpr (NS == 1) {
+                    SO[0] = nO.S;
+                } else {
+                    SO[0] = nO.SI; SO[1] = nO.SQ; SO[2] = nO.SU; SO[3] = nO.b * xsO * nO.S00;
+                }
+#pragma unroll
+                for (int s = 0; s < NS; ++s) SM[s] = epsM[s] * iM;
+                const Real tMO = Real(0.5) * (etaM + etaO) * dsM;
+                Real tOP = Real(1), iP = Real(0);
+                if (has_p) {
+                    iP = rcp(etaP);
+#pragma unroll
+                    for (int s = 0; s < NS; ++s) SP[s] = epsP[s] * iP;
+                    tOP = Real(0.5) * (etaO + etaP) * dsP;
+                } else {
+#pragma unroll
+                    for (int s = 0; s < NS; ++s) SP[s] = Real(0);
+                }
+                const Coef<Real> co = coefficients(tMO);
+                const CoefD<Real> cd = coefficient_derivs(tMO, co);
+                CpGrad<Real> cp[NS];
+                if (has_p) {
+                    const BesserGrad<Real> bg = besser_grad(tMO, tOP);
+#pragma unroll
+                    for (int s = 0; s < NS; ++s) cp[s] = control_point_grad(SM[s], SO[s], SP[s], bg);
+                } else {
+#pragma unroll
+                    for (int s = 0; s < NS; ++s)
+                        cp[s] = CpGrad<Real>{Real(0.5) * (SM[s] + SO[s]), Real(0.5), Real(0.5), Real(0), Real(0), Real(0)};
+                }
+                // ---- reverse step ----
+                Real gr[NS], g_pm = 0, g_po = 0, g_kvM = 0, g_kvO = 0, kvM = 0, kvO = 0;
+                if constexpr (NS == 1) {
+                    gr[0] = lam[0];
+                } else {
+                    // I_O = kappa (rhs) with kappa^-1 = 1 + psi'_O K'_O coupling I and V
+                    kvM = etaVM * iM;
+                    kvO = nO.b * xsO;
+                    Real rr[4];
+#pragma unroll
+                    for (int s = 0; s < 4; ++s) rr[s] = co.e * IM[s] + co.wm * SM[s] + co.wo * SO[s] + co.wc * cp[s].c;
+                    rr[0] -= co.pm * kvM * IM[3];
+                    rr[3] -= co.pm * kvM * IM[0];
+                    const Real av = co.po * kvO;
+                    const Real idet = rcp(Real(1) - av * av);
+                    const Real IO0 = (rr[0] - av * rr[3]) * idet, IO3 = (rr[3] - av * rr[0]) * idet;
+                    gr[0] = (lam[0] - av * lam[3]) * idet;
+                    gr[3] = (lam[3] - av * lam[0]) * idet;
+                    gr[1] = lam[1];
+                    gr[2] = lam[2];
+                    const Real ga = (lam[0] * (Real(2) * av * IO0 - rr[3]) + lam[3] * (Real(2) * av * IO3 - rr[0])) * idet;
+                    g_po = ga * kvO;
+                    g_kvO = ga * co.po;
+                    const Real cr = gr[0] * IM[3] + gr[3] * IM[0];
+                    g_pm = -kvM * cr;
+                    g_kvM = -co.pm * cr;
+                }
+                Real g_e = 0, g_wm = 0, g_wo = 0, g_wc = 0, g_tM = 0, g_tP = 0;
+                Real gIM[NS], gSM[NS], gSO[NS], gSP[NS];
+#pragma unroll
+                for (int s = 0; s < NS; ++s) {
+                    g_e += gr[s] * IM[s];
+                    g_wm += gr[s] * SM[s];
+                    g_wo += gr[s] * SO[s];
+                    g_wc += gr[s] * cp[s].c;
+                    gIM[s] = gr[s] * co.e;
+                    const Real gc = gr[s] * co.wc;
+                    gSM[s] = gr[s] * co.wm + gc * cp[s].dyM;
+                    gSO[s] = gr[s] * co.wo + gc * cp[s].dyO;
+                    gSP[s] = gc * cp[s].dyP;
+                    g_tM += gc * cp[s].dhM;
+                    g_tP += gc * cp[s].dhP;
+                }
+                if constexpr (NS == 4) {
+                    gIM[3] -= gr[0] * co.pm * kvM;
+                    gIM[0] -= gr[3] * co.pm * kvM;
+                }
+                g_tM += g_e * cd.de + g_pm * cd.dpm + g_po * cd.dpo + g_wm * cd.dwm + g_wo * cd.dwo + g_wc * cd.dwc;
+                Real g_etaM = Real(0.5) * dsM * g_tM;
+                Real g_etaO = Real(0.5) * dsM * g_tM + Real(0.5) * dsP * g_tP;
+                Real g_etaP = Real(0.5) * dsP * g_tP;
+                Real gout_m[NM], gout_o[NM], gout_p[NP];
+#pragma unroll
+                for (int s = 0; s < NS; ++s) {
+                    gout_m[NM - NS + s] = gSM[s] * iM;
+                    g_etaM -= gSM[s] * SM[s] * iM;
+                    gout_o[NM - NS + s] = gSO[s] * iO;
+                    g_etaO -= gSO[s] * SO[s] * iO;
+                    gout_p[1 + s] = gSP[s] * iP;
+                    g_etaP -= gSP[s] * SP[s] * iP;
+                }
+                if constexpr (NS == 4) {
+                    gout_m[1] = g_kvM * iM;
+                    g_etaM -= g_kvM * kvM * iM;
+                    gout_o[1] = g_kvO * iO;
+                    g_etaO -= g_kvO * kvO * iO;
+                }
+                gout_m[0] = g_etaM;
+                gout_o[0] = g_etaO;
+                gout_p[0] = g_etaP;
+#pragma unroll
+                for (int s = 0; s < NS; ++s) gI[xI(par, f, s, p)] = gIM[s];
+#pragma unroll
+                for (int k = 0; k < NM; ++k) gM[xM(f, k, p)] = gout_m[k];
+#pragma unroll
+                for (int k = 0; k < NP; ++k) gP[xP(f, k, p)] = gout_p[k];
+#pragma unroll
+                for (int k = 0; k < NM; ++k) T[xT(par, f, k, p)] += gout_o[k];
+            }
+        }
+        __syncthreads();
+        cluster.sync();
+
+        // ---- phase 2: complete node adjoints ----
+        // (a) plane q+1 is complete once the P gathers of plane q are added
+        if (has_p) finalize(q + 1, sP, opar, true, wP);
+        // (b) the M gathers of plane q start the totals of plane q-1 (same
+        //     buffer and element as (a), read there before written here)
+        for (int p = tid; p < npts; p += nt) {
+            const int l = p / nx, c = p - l * nx;
+            const int cm = c == 0 ? nx - 1 : c - 1;
+            const bool first = l == 0;
+            const Real *mlo = first ? gM_prev : gM;
+            const int llo = first ? prev_last * nx : (l - 1) * nx;
+            for (int f = 0; f < nf; ++f)
+#pragma unroll
+                for (int k = 0; k < NM; ++k)
+                    T[xT(opar, f, k, p)] = wM[0] * gM[xM(f, k, l * nx + c)] + wM[1] * gM[xM(f, k, l * nx + cm)] +
+                                           wM[2] * mlo[xM(f, k, llo + c)] + wM[3] * mlo[xM(f, k, llo + cm)];
+        }
+        // (c) the boundary plane has no O or P terms: complete now
+        if (q == 1) finalize(0, sM, opar, false, wP);
+        __syncthreads();
+        cluster_arrive_release();
+        if (q - 2 >= 0) fill(q - 2);
+        __syncthreads();
+        cluster_wait_acquire();
+    }
+    // plane 1: no P terms (plane 0 is not swept)
+    finalize(1, 1, 1, false, nullptr);
+    __syncthreads();
+}
+
+template <typename Real, int NS>
+__global__ void __launch_bounds__(256) adjoint_kernel(const SweepArgs<Real> a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int NM = adj_nm<NS>(), NP = adj_np<NS>();
+    cg::cluster_group cluster = cg::this_cluster();
+    const int C = (int)cluster.num_blocks();
+    const int rank = (int)cluster.block_rank();
+    const int cid = blockIdx.x / C;
+    const int ncl = gridDim.x / C;
+    using V = typename V16<Real>::T;
+    V *ring = reinterpret_cast<V *>(smem_raw);
+    Real *gI = reinterpret_cast<Real *>(ring + 3 * a.ring_plane);
+    Real *gM = gI + 2 * a.F * NS * a.ipts_max;
+    Real *gP = gM + a.F * NM * a.ipts_max;
+    Real *T = gP + a.F * NP * a.ipts_max;
+    cluster.sync();
+    for (int item = cid; item < a.nitems; item += ncl) {
+        const int d = item / a.ngroups, g = item - d * a.ngroups;
+        adjoint_item<Real, NS>(a, cluster, ring, gI, gM, gP, T, d, g, rank, C, item);
+        cluster.sync();
+    }
+}
+
+// dL/dchi, dL/de, dL/dB of every voxel: the per-item partials summed in item order
+template <typename Real>
+__global__ void adjoint_reduce_kernel(const Real *gpart, int nitems, int ngroups, long long nvox,
+                                      const RayDev<Real> *rays, double bfac, double *g_chi, double *g_e, double *g_b)
+{
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < nvox; v += (long long)gridDim.x * blockDim.x) {
+        double sc = 0, se = 0, bx = 0, by = 0, bz = 0;
+        for (int it = 0; it < nitems; ++it) {
+            const Real *p = gpart + (long long)it * 3 * nvox;
+            const RayDev<Real> &r = rays[it / ngroups];
+            const double gb = (double)p[2 * nvox + v];
+            sc += (double)p[v];
+            se += (double)p[nvox + v];
+            bx += gb * (double)r.ox;
+            by += gb * (double)r.oy;
+            bz += gb * (double)r.oz;
+        }
+        g_chi[v] = sc;
+        g_e[v] = se;
+        if (g_b) {
+            g_b[v] = bfac * bx;
+            g_b[nvox + v] = bfac * by;
+            g_b[2 * nvox + v] = bfac * bz;
+        }
+    }
+}
+
+template <typename Real, int NS>
+static cudaError_t prepare_adjoint(int cluster, int smem)
+{
+    cudaError_t e = cudaFuncSetAttribute(adjoint_kernel<Real, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    if (cluster > 8) e = cudaFuncSetAttribute(adjoint_kernel<Real, NS>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    return e;
+}
+
+template <typename Real, int NS>
+cudaError_t adjoint_max_active_clusters(int cluster, int smem, int threads, int *out)
+{
+    cudaError_t e = prepare_adjoint<Real, NS>(cluster, smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3(cluster);
+    lc.blockDim = dim3(threads);
+    lc.dynamicSmemBytes = smem;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cluster;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    lc.attrs = at;
+    lc.numAttrs = 1;
+    return cudaOccupancyMaxActiveClusters(out, adjoint_kernel<Real, NS>, &lc);
+}
+
+template <typename Real, int NS>
+cudaError_t launch_adjoint(const SweepArgs<Real> &a, const LaunchCfg &cfg, cudaStream_t st)
+{
+    cudaError_t e = prepare_adjoint<Real, NS>(cfg.cluster, cfg.smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3(cfg.clusters * cfg.cluster);
+    lc.blockDim = dim3(cfg.threads);
+    lc.dynamicSmemBytes = cfg.smem;
+    lc.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cfg.cluster;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    lc.attrs = at;
+    lc.numAttrs = 1;
+    return cudaLaunchKernelEx(&lc, adjoint_kernel<Real, NS>, a);
+}
+
+template <typename Real>
+cudaError_t launch_adjoint_reduce(const Real *gpart, int nitems, int ngroups, long long nvox, const RayDev<Real> *rays,
+                                  double bfac, double *g_chi, double *g_e, double *g_b, cudaStream_t st)
+{
+    const int threads = 256;
+    const long long blocks = std::min<long long>((nvox + threads - 1) / threads, 152LL * 16);
+    adjoint_reduce_kernel<Real><<<(int)blocks, threads, 0, st>>>(gpart, nitems, ngroups, nvox, rays, bfac, g_chi, g_e, g_b);
+    return cudaGetLastError();
+}
+
+#define PORTA_ADJ_INST(R, N)                                                                        \
+    template int adjoint_smem_bytes<R, N>(int, int, int);                                           \
+    template cudaError_t adjoint_max_active_clusters<R, N>(int, int, int, int *);                   \
+    template cudaError_t launch_adjoint<R, N>(const SweepArgs<R> &, const LaunchCfg &, cudaStream_t);
+PORTA_ADJ_INST(float, 1)
+PORTA_ADJ_INST(float, 4)
+PORTA_ADJ_INST(double, 1)
+PORTA_ADJ_INST(double, 4)
+#undef PORTA_ADJ_INST
+template cudaError_t launch_adjoint_reduce<float>(const float *, int, int, long long, const RayDev<float> *, double,
+                                                  double *, double *, double *, cudaStream_t);
+template cudaError_t launch_adjoint_reduce<double>(const double *, int, int, long long, const RayDev<double> *, double,
+                                                   double *, double *, double *, cudaStream_t);
+
+}  // namespace porta

@@ -455,12 +455,155 @@ int emergent_t(porta_ctx *c, int ndir, const double *mu, const double *chi, doub
     return rc;
 }
 
+// grow-only device buffer held by the context
+cudaError_t ensure_buf(void **p, size_t &cap, size_t need)
+{
+    if (need <= cap && *p) return cudaSuccess;
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    cap = 0;
+    cudaError_t e = cudaMalloc(p, need);
+    if (e == cudaSuccess) cap = need;
+    return e;
+}
+
+const int kAdjThreads = 256;   // maximum threads per CTA of the adjoint kernel
+
+// Launch shape of the adjoint sweep: cluster size C and frequencies per pass
+// F. Estimated time: the (direction, frequency group) items spread over the
+// resident clusters, each costing per plane its point passes (F frequencies
+// per pass) plus the two cluster barriers, the ring fill and the node
+// finalization.
+template <typename Real, int NS>
+int choose_adjoint(porta_ctx *c, LaunchCfg &best, int force_c, int force_f, int ndir)
+{
+    best = LaunchCfg{};
+    double best_cost = 1e300;
+    for (int C = 1; C <= 16; ++C) {
+        if (force_c > 0 && C != force_c) continue;
+        if (force_c <= 0 && C > 1 && (C & (C - 1)) != 0 && C != 6 && C != 12) continue;
+        if (C > c->ny) continue;
+        int ring_plane, ipts;
+        launch_caps<Real, NS>(c, C, ring_plane, ipts);
+        const int threads = std::min(kAdjThreads, std::max(64, (ipts + 31) / 32 * 32));
+        int last_f = -1;
+        for (int G = 1; G <= c->n_nu; ++G) {
+            const int F = force_f > 0 ? force_f : (c->n_nu + G - 1) / G;
+            if (F == last_f) continue;
+            last_f = F;
+            const int smem = adjoint_smem_bytes<Real, NS>(ring_plane, ipts, F);
+            if (smem > kSmemLimit) continue;
+            int act = 0;
+            if (adjoint_max_active_clusters<Real, NS>(C, smem, threads, &act) != cudaSuccess) {
+                cudaGetLastError();
+                continue;
+            }
+            if (act < 1) continue;
+            const int Gr = (c->n_nu + F - 1) / F;
+            const int items = ndir * Gr;
+            const int ncl = std::min(act, items);
+            const double passes = std::ceil((double)ipts / threads);
+            const double item = c->nz * (passes * F * 3.0 + 0.5 * F + 4.0);
+            const double cost = std::ceil((double)items / ncl) * item;
+            if (cost < best_cost) {
+                best_cost = cost;
+                best.cluster = C;
+                best.F = F;
+                best.threads = threads;
+                best.smem = smem;
+                best.clusters = ncl;
+            }
+        }
+    }
+    return best.cluster > 0 ? PORTA_OK : PORTA_EINVAL;
+}
+
+// forward emergent sweep with the tape, adjoint sweep, fixed-order reduction;
+// all pointers are device memory; dout may be null
+template <typename Real>
+int emergent_vjp_t(porta_ctx *c, int ndir, const double *mu, const double *chi, const double *dgrad, double *dout,
+                   double *dg_chi, double *dg_e, double *dg_b)
+{
+    std::vector<PlaneGeom<Real>> geom((size_t)ndir * c->nz);
+    std::vector<RayDev<Real>> rays(ndir);
+    for (int d = 0; d < ndir; ++d) {
+        plane_geometry<Real>(c->nx, c->ny, c->nz, c->lx, c->ly, c->z.data(), mu[d], chi[d], geom.data() + (size_t)d * c->nz);
+        rays[d] = ray_dev<Real>(mu[d], chi[d]);
+    }
+    const long long nxy = (long long)c->nx * c->ny;
+    PlaneGeom<Real> *dg = nullptr;
+    RayDev<Real> *dr = nullptr;
+    double *scratch_out = nullptr;
+    CK(dalloc(&dg, geom.size()));
+    cudaError_t e2 = dalloc(&dr, rays.size());
+    if (e2 == cudaSuccess && !dout) e2 = dalloc(&scratch_out, (size_t)ndir * c->n_nu * nxy * c->ns);
+    int rc = PORTA_OK;
+    do {
+        if (e2 != cudaSuccess) { rc = fail(c, PORTA_ENOMEM, "emergent_vjp: device allocation"); break; }
+        cudaError_t e = cudaMemcpyAsync(dg, geom.data(), geom.size() * sizeof(geom[0]), cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dr, rays.data(), rays.size() * sizeof(rays[0]), cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess)
+            e = ensure_buf(&c->d_tape, c->tape_bytes, (size_t)ndir * c->n_nu * c->nvox * c->ns * sizeof(Real));
+        if (e != cudaSuccess) { rc = fail(c, PORTA_ENOMEM, std::string("emergent_vjp: ") + cudaGetErrorString(e)); break; }
+        // forward: emergent Stokes and the Stokes vectors of every plane
+        SweepArgs<Real> a = base_args<Real>(c);
+        a.geom = dg;
+        a.rays = dr;
+        a.out = dout ? dout : scratch_out;
+        a.store = (Real *)c->d_tape;
+        LaunchCfg cfg;
+        rc = c->ns == 1 ? choose_launch<Real, 1>(c, cfg, c->opt_cluster, c->opt_nu_group, c->nray)
+                        : choose_launch<Real, 4>(c, cfg, c->opt_cluster, c->opt_nu_group, c->nray);
+        if (rc) { rc = fail(c, rc, "no sweep launch shape fits this grid"); break; }
+        shape_args<Real>(c, a, cfg);
+        a.nitems = ndir * a.ngroups;
+        cfg.clusters = std::min(cfg.clusters, a.nitems);
+        e = c->ns == 1 ? launch_sweep<Real, 1>(a, MODE_EMERGENT, cfg, c->stream)
+                       : launch_sweep<Real, 4>(a, MODE_EMERGENT, cfg, c->stream);
+        if (e != cudaSuccess) { rc = fail(c, PORTA_ECUDA, std::string("emergent_vjp forward: ") + cudaGetErrorString(e)); break; }
+        // adjoint
+        LaunchCfg acfg;
+        rc = c->ns == 1 ? choose_adjoint<Real, 1>(c, acfg, c->adj_cluster, c->adj_nu_group, ndir)
+                        : choose_adjoint<Real, 4>(c, acfg, c->adj_cluster, c->adj_nu_group, ndir);
+        if (rc) { rc = fail(c, rc, "no adjoint launch shape fits this grid"); break; }
+        SweepArgs<Real> b = base_args<Real>(c);
+        b.geom = dg;
+        b.rays = dr;
+        b.store = (Real *)c->d_tape;
+        b.gout = dgrad;
+        b.F = acfg.F;
+        b.ngroups = (c->n_nu + acfg.F - 1) / acfg.F;
+        if (c->ns == 1)
+            launch_caps<Real, 1>(c, acfg.cluster, b.ring_plane, b.ipts_max);
+        else
+            launch_caps<Real, 4>(c, acfg.cluster, b.ring_plane, b.ipts_max);
+        b.nitems = ndir * b.ngroups;
+        acfg.clusters = std::min(acfg.clusters, b.nitems);
+        e = ensure_buf(&c->d_gpart, c->gpart_bytes, (size_t)b.nitems * 3 * c->nvox * sizeof(Real));
+        if (e != cudaSuccess) { rc = fail(c, PORTA_ENOMEM, "emergent_vjp: partial-gradient allocation"); break; }
+        b.gpart = (Real *)c->d_gpart;
+        e = c->ns == 1 ? launch_adjoint<Real, 1>(b, acfg, c->stream) : launch_adjoint<Real, 4>(b, acfg, c->stream);
+        if (e == cudaSuccess)
+            e = launch_adjoint_reduce<Real>((const Real *)c->d_gpart, b.nitems, b.ngroups, c->nvox, dr,
+                                            2.0 * c->gbar * c->zeta, dg_chi, dg_e, c->ns == 1 ? nullptr : dg_b, c->stream);
+        if (e != cudaSuccess) { rc = fail(c, PORTA_ECUDA, std::string("emergent_vjp adjoint: ") + cudaGetErrorString(e)); break; }
+        c->last_adj = acfg;
+        e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) rc = fail(c, PORTA_ECUDA, std::string("emergent_vjp: ") + cudaGetErrorString(e));
+    } while (0);
+    cudaStreamSynchronize(c->stream);
+    cudaFree(dg);
+    cudaFree(dr);
+    if (scratch_out) cudaFree(scratch_out);
+    return rc;
+}
+
 void free_all(porta_ctx *c)
 {
     drop_graph(c);
     void *ptrs[] = {c->d_atm, c->d_eps, c->d_bpl, c->d_b, c->d_rho, c->d_rhoR, c->d_invn, c->d_geom, c->d_rays,
                     c->d_freq, c->d_part, c->d_tw, c->d_jkq, c->d_lstar, c->d_resid, c->d_err, c->d_boxes,
-                    c->d_items, c->d_tune_items};
+                    c->d_items, c->d_tune_items, c->d_tape, c->d_gpart};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }
@@ -933,6 +1076,67 @@ int porta_emergent_stokes(porta_ctx *c, int ndir, const double *mu, const double
         cudaFree(dout);
     }
     return rc;
+}
+
+int porta_emergent_vjp(porta_ctx *c, int ndir, const double *mu, const double *chi, const double *grad_out,
+                       double *out, double *g_chi, double *g_e, double *g_b, int where)
+{
+    if (!c) return PORTA_EINVAL;
+    if (ndir < 1 || !mu || !chi || !grad_out || !g_chi || !g_e || (c->ns > 1 && !g_b) ||
+        (where != PORTA_HOST && where != PORTA_DEVICE))
+        return fail(c, PORTA_EINVAL, "emergent_vjp: bad argument");
+    for (int d = 0; d < ndir; ++d)
+        if (!(mu[d] > 0.0 && mu[d] <= 1.0) || !std::isfinite(chi[d]))
+            return fail(c, PORTA_EINVAL, "emergent_vjp: mu must lie in (0, 1], chi finite");
+    if (c->nbox != 1) return fail(c, PORTA_EINVAL, "emergent_vjp: single-box contexts only");
+    if (!c->have_atm || !c->have_rho) return fail(c, PORTA_ESTATE, "emergent_vjp: atmosphere or rho not set");
+    const long long nout = (long long)ndir * c->n_nu * c->nx * c->ny * c->ns;
+    const long long nv = c->nvox;
+    if (where == PORTA_DEVICE)
+        return c->precision == PORTA_FP32 ? emergent_vjp_t<float>(c, ndir, mu, chi, grad_out, out, g_chi, g_e, g_b)
+                                          : emergent_vjp_t<double>(c, ndir, mu, chi, grad_out, out, g_chi, g_e, g_b);
+    // host buffers: one device block for grad_out, out, g_chi, g_e, g_b
+    const long long nb = c->ns > 1 ? 3 * nv : 0;
+    double *blk = nullptr;
+    CK(dalloc(&blk, (size_t)(nout + (out ? nout : 0) + 2 * nv + nb)));
+    double *dgrad = blk, *dout = out ? blk + nout : nullptr;
+    double *dchi = blk + nout + (out ? nout : 0), *de = dchi + nv, *db = nb ? de + nv : nullptr;
+    int rc = PORTA_OK;
+    cudaError_t e = cudaMemcpy(dgrad, grad_out, nout * sizeof(double), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) rc = fail(c, PORTA_ECUDA, cudaGetErrorString(e));
+    if (rc == PORTA_OK)
+        rc = c->precision == PORTA_FP32 ? emergent_vjp_t<float>(c, ndir, mu, chi, dgrad, dout, dchi, de, db)
+                                        : emergent_vjp_t<double>(c, ndir, mu, chi, dgrad, dout, dchi, de, db);
+    if (rc == PORTA_OK) {
+        e = cudaMemcpy(g_chi, dchi, nv * sizeof(double), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(g_e, de, nv * sizeof(double), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess && db) e = cudaMemcpy(g_b, db, 3 * nv * sizeof(double), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess && out) e = cudaMemcpy(out, dout, nout * sizeof(double), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) rc = fail(c, PORTA_ECUDA, cudaGetErrorString(e));
+    }
+    cudaFree(blk);
+    return rc;
+}
+
+int porta_set_adjoint_launch(porta_ctx *c, int cluster, int nu_group)
+{
+    if (!c) return PORTA_EINVAL;
+    if (cluster < 0 || cluster > 16 || nu_group < 0 || nu_group > c->n_nu)
+        return fail(c, PORTA_EINVAL, "set_adjoint_launch: cluster in 0..16, nu_group in 0..n_nu");
+    if (cluster > c->ny) return fail(c, PORTA_EINVAL, "set_adjoint_launch: cluster larger than ny");
+    c->adj_cluster = cluster;
+    c->adj_nu_group = nu_group;
+    return PORTA_OK;
+}
+
+int porta_adjoint_info(const porta_ctx *c, int *clusters, int *cluster_size, int *nu_group, int *smem_bytes)
+{
+    if (!c) return PORTA_EINVAL;
+    if (clusters) *clusters = c->last_adj.clusters;
+    if (cluster_size) *cluster_size = c->last_adj.cluster;
+    if (nu_group) *nu_group = c->last_adj.F;
+    if (smem_bytes) *smem_bytes = c->last_adj.smem;
+    return PORTA_OK;
 }
 
 int porta_probe_ray(porta_ctx *c, int m, double *out, double *lstar, int where)

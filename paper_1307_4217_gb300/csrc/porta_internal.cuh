@@ -66,6 +66,10 @@ struct SweepArgs {
     int probe_ray;                 // -1 or the ray whose Stokes vectors are written to probe
     Real *probe;                   // [nu][nvox][ns]
     Real *probe_ls;                // [nu][nvox]
+    // reverse mode of the emergent sweep (single box)
+    Real *store;                   // emergent: null, or the Stokes vectors of every plane [dir][nu][nvox][ns]
+    const double *gout;            // adjoint: dL/dI on the top plane [dir][nu][ny][nx][ns]
+    Real *gpart;                   // adjoint: per (dir, frequency group) partial gradients [item][3][nvox]
 };
 
 struct LaunchCfg {
@@ -86,6 +90,19 @@ int sweep_smem_bytes(int ring_plane, int ipts_max, int F, int threads);
 
 template <typename Real, int NS>
 cudaError_t max_active_clusters(int cluster, int smem, int threads, int *out);
+
+// adjoint of the emergent sweep (adjoint.cu): shared memory of a launch with
+// ring plane `ring_plane` (16-byte chunks), `ipts` points per strip and F
+// frequencies per pass; occupancy; launch; the fixed-order sum over items
+template <typename Real, int NS>
+int adjoint_smem_bytes(int ring_plane, int ipts, int F);
+template <typename Real, int NS>
+cudaError_t adjoint_max_active_clusters(int cluster, int smem, int threads, int *out);
+template <typename Real, int NS>
+cudaError_t launch_adjoint(const SweepArgs<Real> &a, const LaunchCfg &cfg, cudaStream_t st);
+template <typename Real>
+cudaError_t launch_adjoint_reduce(const Real *gpart, int nitems, int ngroups, long long nvox, const RayDev<Real> *rays,
+                                  double bfac, double *g_chi, double *g_e, double *g_b, cudaStream_t st);
 
 }  // namespace porta
 
@@ -138,4 +155,12 @@ struct porta_ctx {
     cudaStream_t graph_stream = nullptr;
     // last launch of the formal solution
     porta::LaunchCfg last{};
+    // reverse mode of the emergent sweep: tape of the forward Stokes vectors,
+    // per-item partial gradients, forced launch shape (0 = automatic), last launch
+    void *d_tape = nullptr;
+    size_t tape_bytes = 0;
+    void *d_gpart = nullptr;
+    size_t gpart_bytes = 0;
+    int adj_cluster = 0, adj_nu_group = 0;
+    porta::LaunchCfg last_adj{};
 };
