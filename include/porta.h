@@ -279,8 +279,15 @@ int porta_emergent_vjp(porta_ctx *c, int ndir, const double *mu, const double *c
                        double *out, double *g_chi, double *g_e, double *g_b, int where);
 
 /* Launch shape of the adjoint sweep: cluster size (1..16, <= ny) and
-   frequencies per pass; 0 selects automatically (cost model). */
+   frequencies per pass. With both 0 (the default) the first
+   porta_emergent_vjp for a given number of directions times every fitting
+   shape once (CUDA events) and keeps the fastest. */
 int porta_set_adjoint_launch(porta_ctx *c, int cluster, int nu_group);
+
+/* Device time (ms, CUDA events on the context's stream) of the last
+   porta_emergent_vjp: the forward emergent sweep with its tape, and the
+   adjoint sweep with the reduction over directions and frequency groups. */
+int porta_adjoint_timing(const porta_ctx *c, float *forward_ms, float *adjoint_ms);
 
 /* Launch statistics of the last adjoint sweep (as porta_launch_info). */
 int porta_adjoint_info(const porta_ctx *c, int *clusters, int *cluster_size, int *nu_group, int *smem_bytes);

@@ -74,6 +74,7 @@ _SIGS = {
     "porta_emergent_vjp": (_I, [_P, _I, _P, _P, _P, _P, _P, _P, _P, _I]),
     "porta_set_adjoint_launch": (_I, [_P, _I, _I]),
     "porta_adjoint_info": (_I, [_P, _P, _P, _P, _P]),
+    "porta_adjoint_timing": (_I, [_P, _P, _P]),
 }
 
 _lib = None
@@ -256,6 +257,12 @@ def porta_adjoint_info(h):
     return rc, dict(clusters=v[0].value, cluster=v[1].value, nu_group=v[2].value, smem=v[3].value)
 
 
+def porta_adjoint_timing(h):
+    f, a = ctypes.c_float(), ctypes.c_float()
+    rc = lib().porta_adjoint_timing(h, ctypes.byref(f), ctypes.byref(a))
+    return rc, dict(forward_ms=f.value, adjoint_ms=a.value)
+
+
 # ---- convenience wrapper ------------------------------------------------------------
 
 class Context:
@@ -399,6 +406,11 @@ class Context:
         rc, info = porta_adjoint_info(self.h)
         self._check(rc)
         return info
+
+    def adjoint_timing(self):
+        rc, t = porta_adjoint_timing(self.h)
+        self._check(rc)
+        return t
 
     def probe_ray(self, m):
         out = np.zeros((self.nnu,) + self.shape + (self.ns,))

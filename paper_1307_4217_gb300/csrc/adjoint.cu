@@ -49,11 +49,59 @@ __host__ __device__ constexpr int adj_nm() { return NS == 1 ? 2 : 6; }
 template <int NS>
 __host__ __device__ constexpr int adj_np() { return NS + 1; }
 
+// bytes before the tape tile (16-byte aligned), and the whole shared memory:
+// ring, gI, gM, gP, T (per point and frequency), then the staged tape rows
+// of the upwind plane (tile_pts = (rows + 1) x nx points per frequency)
 template <typename Real, int NS>
-int adjoint_smem_bytes(int ring_plane, int ipts, int F)
+__host__ __device__ constexpr int adjoint_tile_offset(int ring_plane, int ipts, int F)
 {
-    constexpr int NM = adj_nm<NS>(), NP = adj_np<NS>();
-    return 3 * ring_plane * 16 + F * ipts * (2 * NS + NM + NP + 2 * NM) * (int)sizeof(Real);
+    return (3 * ring_plane * 16 + F * ipts * (2 * NS + adj_nm<NS>() + adj_np<NS>() + 2 * adj_nm<NS>()) * (int)sizeof(Real) +
+            15) / 16 * 16;
+}
+
+template <typename Real, int NS>
+int adjoint_smem_bytes(int ring_plane, int ipts, int tile_pts, int F)
+{
+    return adjoint_tile_offset<Real, NS>(ring_plane, ipts, F) + F * tile_pts * NS * (int)sizeof(Real);
+}
+
+// asynchronous global -> shared copy of one Stokes vector (cp.async, 4/8/16 bytes per instruction)
+template <int BYTES>
+__device__ __forceinline__ void cp_async_bytes(void *dst, const void *src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    if constexpr (BYTES == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(d), "l"(src), "n"(BYTES) : "memory");
+}
+template <typename Real, int NS>
+__device__ __forceinline__ void copy_stokes_async(Real *dst, const Real *src)
+{
+    constexpr int B = NS * (int)sizeof(Real);
+    if constexpr (B <= 16) {
+        cp_async_bytes<B>(dst, src);
+    } else {
+        cp_async_bytes<16>(dst, src);
+        cp_async_bytes<16>(dst + 16 / sizeof(Real), src + 16 / sizeof(Real));
+    }
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// one Stokes vector from shared memory (vector loads)
+template <typename Real, int NS>
+__device__ __forceinline__ void load_stokes(const Real *p, Real v[NS])
+{
+    if constexpr (NS == 4 && sizeof(Real) == 4) {
+        const float4 a = *reinterpret_cast<const float4 *>(p);
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    } else if constexpr (NS == 4) {
+        const double2 a = reinterpret_cast<const double2 *>(p)[0], b = reinterpret_cast<const double2 *>(p)[1];
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    } else {
+        v[0] = p[0];
+    }
 }
 
 // CTA owning sheared row r when CTA k owns rows floor(k ny / C) .. floor((k+1) ny / C) - 1
@@ -86,7 +134,7 @@ __device__ __forceinline__ void node_param_grad(const Node<Real, NS> &n, Real x,
 template <typename Real, int NS>
 __device__ __forceinline__ void adjoint_item(const SweepArgs<Real> &a, cg::cluster_group &cluster,
                                              typename V16<Real>::T *ring, Real *gI, Real *gM, Real *gP, Real *T,
-                                             int d, int g, int rank, int C, int item)
+                                             Real *tt, int d, int g, int rank, int C, int item)
 {
     constexpr int NM = adj_nm<NS>(), NP = adj_np<NS>();
     constexpr int NCH = node_words<NS>() * (int)sizeof(Real) / 16;
@@ -180,8 +228,24 @@ __device__ __forceinline__ void adjoint_item(const SweepArgs<Real> &a, cg::clust
         }
     };
 
+    // tape rows 0..R of the strip (sheared frame) of plane qq, all frequencies of the group
+    const int tile_pts = (rmax + 1) * nx;
+    auto stage = [&](int qq) {
+        const PlaneGeom<Real> gg = G[qq];
+        const int per = (R + 1) * nx;
+        for (int idx = tid; idx < per * nf; idx += nt) {
+            const int f = idx / per, r = idx - f * per;
+            const int lr = r / nx, c = r - lr * nx;
+            const long long v = B.vox0 + voxel(gg, c, lr);
+            copy_stokes_async<Real, NS>(tt + ((long long)f * tile_pts + r) * NS, tape + ((long long)(j0 + f) * a.nvox + v) * NS);
+        }
+        cp_async_commit();
+    };
+
     fill(nz - 1);
     fill(nz - 2);
+    stage(nz - 2);
+    cp_async_wait_all();
     for (int p = tid; p < npts; p += nt)
         for (int f = 0; f < nf; ++f)
 #pragma unroll
@@ -224,12 +288,6 @@ __device__ __forceinline__ void adjoint_item(const SweepArgs<Real> &a, cg::clust
             } else {
                 kP[0] = kP[1] = kP[2] = kP[3] = corner_p<Real, NS>(nO, Real(0));
             }
-            // tape positions of the 4 upwind corners (plane q-1)
-            long long vM[4];
-            vM[0] = B.vox0 + voxel(gm, c, l);
-            vM[1] = B.vox0 + voxel(gm, c1, l);
-            vM[2] = B.vox0 + voxel(gm, c, l + 1);
-            vM[3] = B.vox0 + voxel(gm, c1, l + 1);
             const long long vO = voxel(gq, c, l);
             // rows of the Stokes-adjoint gather from plane q+1: (c|c-1, l|l-1)
             const bool first = l == 0;
@@ -251,14 +309,17 @@ __device__ __forceinline__ void adjoint_item(const SweepArgs<Real> &a, cg::clust
                                  wN[2] * glo[xI(opar, f, s, llo + c)] + wN[3] * glo[xI(opar, f, s, llo + cm)];
                 }
                 // ---- forward recomputation (the forward sweep's arithmetic) ----
+                // upwind Stokes vector from the staged tape rows l, l+1 of plane q-1
                 Real IM[NS];
+                {
+                    const Real *tf = tt + (long long)f * tile_pts * NS;
+                    Real t0[NS], t1[NS], t2[NS], t3[NS];
+                    load_stokes<Real, NS>(tf + (l * nx + c) * NS, t0);
+                    load_stokes<Real, NS>(tf + (l * nx + c1) * NS, t1);
+                    load_stokes<Real, NS>(tf + ((l + 1) * nx + c) * NS, t2);
+                    load_stokes<Real, NS>(tf + ((l + 1) * nx + c1) * NS, t3);
 #pragma unroll
-                for (int s = 0; s < NS; ++s) IM[s] = Real(0);
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const Real *Ik = tape + ((long long)j * a.nvox + vM[k]) * NS;
-#pragma unroll
-                    for (int s = 0; s < NS; ++s) IM[s] += wM[k] * Ik[s];
+                    for (int s = 0; s < NS; ++s) IM[s] = wM[0] * t0[s] + wM[1] * t1[s] + wM[2] * t2[s] + wM[3] * t3[s];
                 }
                 Real etaM = 0, etaVM = 0, epsM[NS];
 #pragma unroll
@@ -322,16 +383,17 @@ __device__ __forceinline__ void adjoint_item(const SweepArgs<Real> &a, cg::clust
                     for (int s = 0; s < NS; ++s) SP[s] = Real(0);
                 }
                 const Coef<Real> co = coefficients(tMO);
-                const CoefD<Real> cd = coefficient_derivs(tMO, co);
-                CpGrad<Real> cp[NS];
+                // control points exactly as the forward sweep computes them; their
+                // partial derivatives are formed per Stokes parameter where used
+                BesserGrad<Real> bg{};
+                Real cM[NS];
                 if (has_p) {
-                    const BesserGrad<Real> bg = besser_grad(tMO, tOP);
+                    bg = besser_grad(tMO, tOP);
 #pragma unroll
-                    for (int s = 0; s < NS; ++s) cp[s] = control_point_grad(SM[s], SO[s], SP[s], bg);
+                    for (int s = 0; s < NS; ++s) cM[s] = control_point(SM[s], SO[s], SP[s], bg.g);
                 } else {
 #pragma unroll
-                    for (int s = 0; s < NS; ++s)
-                        cp[s] = CpGrad<Real>{Real(0.5) * (SM[s] + SO[s]), Real(0.5), Real(0.5), Real(0), Real(0), Real(0)};
+                    for (int s = 0; s < NS; ++s) cM[s] = Real(0.5) * (SM[s] + SO[s]);
                 }
                 // ---- reverse step ----
                 Real gr[NS], g_pm = 0, g_po = 0, g_kvM = 0, g_kvO = 0, kvM = 0, kvO = 0;
@@ -343,7 +405,7 @@ __device__ __forceinline__ void adjoint_item(const SweepArgs<Real> &a, cg::clust
                     kvO = nO.b * xsO;
                     Real rr[4];
 #pragma unroll
-                    for (int s = 0; s < 4; ++s) rr[s] = co.e * IM[s] + co.wm * SM[s] + co.wo * SO[s] + co.wc * cp[s].c;
+                    for (int s = 0; s < 4; ++s) rr[s] = co.e * IM[s] + co.wm * SM[s] + co.wo * SO[s] + co.wc * cM[s];
                     rr[0] -= co.pm * kvM * IM[3];
                     rr[3] -= co.pm * kvM * IM[0];
                     const Real av = co.po * kvO;
@@ -367,19 +429,22 @@ __device__ __forceinline__ void adjoint_item(const SweepArgs<Real> &a, cg::clust
                     g_e += gr[s] * IM[s];
                     g_wm += gr[s] * SM[s];
                     g_wo += gr[s] * SO[s];
-                    g_wc += gr[s] * cp[s].c;
+                    g_wc += gr[s] * cM[s];
                     gIM[s] = gr[s] * co.e;
                     const Real gc = gr[s] * co.wc;
-                    gSM[s] = gr[s] * co.wm + gc * cp[s].dyM;
-                    gSO[s] = gr[s] * co.wo + gc * cp[s].dyO;
-                    gSP[s] = gc * cp[s].dyP;
-                    g_tM += gc * cp[s].dhM;
-                    g_tP += gc * cp[s].dhP;
+                    CpGrad<Real> cp{cM[s], Real(0.5), Real(0.5), Real(0), Real(0), Real(0)};
+                    if (has_p) cp = control_point_grad(SM[s], SO[s], SP[s], bg);
+                    gSM[s] = gr[s] * co.wm + gc * cp.dyM;
+                    gSO[s] = gr[s] * co.wo + gc * cp.dyO;
+                    gSP[s] = gc * cp.dyP;
+                    g_tM += gc * cp.dhM;
+                    g_tP += gc * cp.dhP;
                 }
                 if constexpr (NS == 4) {
                     gIM[3] -= gr[0] * co.pm * kvM;
                     gIM[0] -= gr[3] * co.pm * kvM;
                 }
+                const CoefD<Real> cd = coefficient_derivs(tMO, co);
                 g_tM += g_e * cd.de + g_pm * cd.dpm + g_po * cd.dpo + g_wm * cd.dwm + g_wo * cd.dwo + g_wc * cd.dwc;
                 Real g_etaM = Real(0.5) * dsM * g_tM;
                 Real g_etaO = Real(0.5) * dsM * g_tM + Real(0.5) * dsP * g_tP;
@@ -437,7 +502,11 @@ __device__ __forceinline__ void adjoint_item(const SweepArgs<Real> &a, cg::clust
         if (q == 1) finalize(0, sM, opar, false, wP);
         __syncthreads();
         cluster_arrive_release();
-        if (q - 2 >= 0) fill(q - 2);
+        if (q - 2 >= 0) {
+            stage(q - 2);        // tape rows for step q-1, in flight during the refill and the barrier
+            fill(q - 2);
+        }
+        cp_async_wait_all();
         __syncthreads();
         cluster_wait_acquire();
     }
@@ -447,7 +516,7 @@ __device__ __forceinline__ void adjoint_item(const SweepArgs<Real> &a, cg::clust
 }
 
 template <typename Real, int NS>
-__global__ void __launch_bounds__(256) adjoint_kernel(const SweepArgs<Real> a)
+__global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 2 : 1) adjoint_kernel(const SweepArgs<Real> a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int NM = adj_nm<NS>(), NP = adj_np<NS>();
@@ -462,10 +531,11 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const SweepArgs<Real> a)
     Real *gM = gI + 2 * a.F * NS * a.ipts_max;
     Real *gP = gM + a.F * NM * a.ipts_max;
     Real *T = gP + a.F * NP * a.ipts_max;
+    Real *tt = reinterpret_cast<Real *>(smem_raw + adjoint_tile_offset<Real, NS>(a.ring_plane, a.ipts_max, a.F));
     cluster.sync();
     for (int item = cid; item < a.nitems; item += ncl) {
         const int d = item / a.ngroups, g = item - d * a.ngroups;
-        adjoint_item<Real, NS>(a, cluster, ring, gI, gM, gP, T, d, g, rank, C, item);
+        adjoint_item<Real, NS>(a, cluster, ring, gI, gM, gP, T, tt, d, g, rank, C, item);
         cluster.sync();
     }
 }
@@ -556,7 +626,7 @@ cudaError_t launch_adjoint_reduce(const Real *gpart, int nitems, int ngroups, lo
 }
 
 #define PORTA_ADJ_INST(R, N)                                                                        \
-    template int adjoint_smem_bytes<R, N>(int, int, int);                                           \
+    template int adjoint_smem_bytes<R, N>(int, int, int, int);                                      \
     template cudaError_t adjoint_max_active_clusters<R, N>(int, int, int, int *);                   \
     template cudaError_t launch_adjoint<R, N>(const SweepArgs<R> &, const LaunchCfg &, cudaStream_t);
 PORTA_ADJ_INST(float, 1)

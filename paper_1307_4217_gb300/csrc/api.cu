@@ -475,7 +475,8 @@ const int kAdjThreads = 256;   // maximum threads per CTA of the adjoint kernel
 // per pass) plus the two cluster barriers, the ring fill and the node
 // finalization.
 template <typename Real, int NS>
-int choose_adjoint(porta_ctx *c, LaunchCfg &best, int force_c, int force_f, int ndir)
+int choose_adjoint(porta_ctx *c, LaunchCfg &best, int force_c, int force_f, int ndir,
+                   std::vector<LaunchCfg> *all = nullptr)
 {
     best = LaunchCfg{};
     double best_cost = 1e300;
@@ -491,7 +492,7 @@ int choose_adjoint(porta_ctx *c, LaunchCfg &best, int force_c, int force_f, int 
             const int F = force_f > 0 ? force_f : (c->n_nu + G - 1) / G;
             if (F == last_f) continue;
             last_f = F;
-            const int smem = adjoint_smem_bytes<Real, NS>(ring_plane, ipts, F);
+            const int smem = adjoint_smem_bytes<Real, NS>(ring_plane, ipts, ipts + c->nx, F);
             if (smem > kSmemLimit) continue;
             int act = 0;
             if (adjoint_max_active_clusters<Real, NS>(C, smem, threads, &act) != cudaSuccess) {
@@ -505,6 +506,15 @@ int choose_adjoint(porta_ctx *c, LaunchCfg &best, int force_c, int force_f, int 
             const double passes = std::ceil((double)ipts / threads);
             const double item = c->nz * (passes * F * 3.0 + 0.5 * F + 4.0);
             const double cost = std::ceil((double)items / ncl) * item;
+            if (all) {
+                LaunchCfg k;
+                k.cluster = C;
+                k.F = F;
+                k.threads = threads;
+                k.smem = smem;
+                k.clusters = ncl;
+                all->push_back(k);
+            }
             if (cost < best_cost) {
                 best_cost = cost;
                 best.cluster = C;
@@ -546,6 +556,9 @@ int emergent_vjp_t(porta_ctx *c, int ndir, const double *mu, const double *chi, 
             e = ensure_buf(&c->d_tape, c->tape_bytes, (size_t)ndir * c->n_nu * c->nvox * c->ns * sizeof(Real));
         if (e != cudaSuccess) { rc = fail(c, PORTA_ENOMEM, std::string("emergent_vjp: ") + cudaGetErrorString(e)); break; }
         // forward: emergent Stokes and the Stokes vectors of every plane
+        for (int k = 0; k < 3 && e == cudaSuccess; ++k)
+            if (!c->adj_ev[k]) e = cudaEventCreate(&c->adj_ev[k]);
+        if (e != cudaSuccess) { rc = fail(c, PORTA_ECUDA, std::string("emergent_vjp: ") + cudaGetErrorString(e)); break; }
         SweepArgs<Real> a = base_args<Real>(c);
         a.geom = dg;
         a.rays = dr;
@@ -558,37 +571,78 @@ int emergent_vjp_t(porta_ctx *c, int ndir, const double *mu, const double *chi, 
         shape_args<Real>(c, a, cfg);
         a.nitems = ndir * a.ngroups;
         cfg.clusters = std::min(cfg.clusters, a.nitems);
-        e = c->ns == 1 ? launch_sweep<Real, 1>(a, MODE_EMERGENT, cfg, c->stream)
-                       : launch_sweep<Real, 4>(a, MODE_EMERGENT, cfg, c->stream);
+        e = cudaEventRecord(c->adj_ev[0], c->stream);
+        if (e == cudaSuccess)
+            e = c->ns == 1 ? launch_sweep<Real, 1>(a, MODE_EMERGENT, cfg, c->stream)
+                           : launch_sweep<Real, 4>(a, MODE_EMERGENT, cfg, c->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(c->adj_ev[1], c->stream);
         if (e != cudaSuccess) { rc = fail(c, PORTA_ECUDA, std::string("emergent_vjp forward: ") + cudaGetErrorString(e)); break; }
-        // adjoint
+        // adjoint: launch shape forced, or timed once per direction count over
+        // every fitting shape (each trial overwrites the same outputs)
         LaunchCfg acfg;
-        rc = c->ns == 1 ? choose_adjoint<Real, 1>(c, acfg, c->adj_cluster, c->adj_nu_group, ndir)
-                        : choose_adjoint<Real, 4>(c, acfg, c->adj_cluster, c->adj_nu_group, ndir);
+        std::vector<LaunchCfg> cand;
+        const bool forced = c->adj_cluster > 0 || c->adj_nu_group > 0;
+        const bool tune = !forced && c->adj_tuned_ndir != ndir;
+        rc = c->ns == 1 ? choose_adjoint<Real, 1>(c, acfg, c->adj_cluster, c->adj_nu_group, ndir, tune ? &cand : nullptr)
+                        : choose_adjoint<Real, 4>(c, acfg, c->adj_cluster, c->adj_nu_group, ndir, tune ? &cand : nullptr);
         if (rc) { rc = fail(c, rc, "no adjoint launch shape fits this grid"); break; }
-        SweepArgs<Real> b = base_args<Real>(c);
-        b.geom = dg;
-        b.rays = dr;
-        b.store = (Real *)c->d_tape;
-        b.gout = dgrad;
-        b.F = acfg.F;
-        b.ngroups = (c->n_nu + acfg.F - 1) / acfg.F;
-        if (c->ns == 1)
-            launch_caps<Real, 1>(c, acfg.cluster, b.ring_plane, b.ipts_max);
-        else
-            launch_caps<Real, 4>(c, acfg.cluster, b.ring_plane, b.ipts_max);
-        b.nitems = ndir * b.ngroups;
-        acfg.clusters = std::min(acfg.clusters, b.nitems);
-        e = ensure_buf(&c->d_gpart, c->gpart_bytes, (size_t)b.nitems * 3 * c->nvox * sizeof(Real));
+        if (!forced && !tune) acfg = c->adj_tuned;
+        e = ensure_buf(&c->d_gpart, c->gpart_bytes, (size_t)ndir * c->n_nu * 3 * c->nvox * sizeof(Real));
         if (e != cudaSuccess) { rc = fail(c, PORTA_ENOMEM, "emergent_vjp: partial-gradient allocation"); break; }
-        b.gpart = (Real *)c->d_gpart;
-        e = c->ns == 1 ? launch_adjoint<Real, 1>(b, acfg, c->stream) : launch_adjoint<Real, 4>(b, acfg, c->stream);
+        auto args_for = [&](LaunchCfg &k) {
+            SweepArgs<Real> b = base_args<Real>(c);
+            b.geom = dg;
+            b.rays = dr;
+            b.store = (Real *)c->d_tape;
+            b.gout = dgrad;
+            b.gpart = (Real *)c->d_gpart;
+            b.F = k.F;
+            b.ngroups = (c->n_nu + k.F - 1) / k.F;
+            if (c->ns == 1)
+                launch_caps<Real, 1>(c, k.cluster, b.ring_plane, b.ipts_max);
+            else
+                launch_caps<Real, 4>(c, k.cluster, b.ring_plane, b.ipts_max);
+            b.nitems = ndir * b.ngroups;
+            k.clusters = std::min(k.clusters, b.nitems);
+            return b;
+        };
+        if (tune) {
+            // the forward's time is read before the trials reuse the events
+            e = cudaEventSynchronize(c->adj_ev[1]);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&c->adj_fwd_ms, c->adj_ev[0], c->adj_ev[1]);
+            float best_ms = 1e30f;
+            for (LaunchCfg k : cand) {
+                SweepArgs<Real> b = args_for(k);
+                float ms = 0;
+                e = cudaEventRecord(c->adj_ev[1], c->stream);
+                if (e == cudaSuccess)
+                    e = c->ns == 1 ? launch_adjoint<Real, 1>(b, k, c->stream) : launch_adjoint<Real, 4>(b, k, c->stream);
+                if (e == cudaSuccess) e = cudaEventRecord(c->adj_ev[2], c->stream);
+                if (e == cudaSuccess) e = cudaEventSynchronize(c->adj_ev[2]);
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, c->adj_ev[1], c->adj_ev[2]);
+                if (e != cudaSuccess) break;
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    acfg = k;
+                }
+            }
+            if (e != cudaSuccess) { rc = fail(c, PORTA_ECUDA, std::string("emergent_vjp tuning: ") + cudaGetErrorString(e)); break; }
+            c->adj_tuned = acfg;
+            c->adj_tuned_ndir = ndir;
+            e = cudaEventRecord(c->adj_ev[1], c->stream);
+        }
+        SweepArgs<Real> b = args_for(acfg);
+        if (e == cudaSuccess)
+            e = c->ns == 1 ? launch_adjoint<Real, 1>(b, acfg, c->stream) : launch_adjoint<Real, 4>(b, acfg, c->stream);
         if (e == cudaSuccess)
             e = launch_adjoint_reduce<Real>((const Real *)c->d_gpart, b.nitems, b.ngroups, c->nvox, dr,
                                             2.0 * c->gbar * c->zeta, dg_chi, dg_e, c->ns == 1 ? nullptr : dg_b, c->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(c->adj_ev[2], c->stream);
         if (e != cudaSuccess) { rc = fail(c, PORTA_ECUDA, std::string("emergent_vjp adjoint: ") + cudaGetErrorString(e)); break; }
         c->last_adj = acfg;
         e = cudaStreamSynchronize(c->stream);
+        if (e == cudaSuccess && !tune) e = cudaEventElapsedTime(&c->adj_fwd_ms, c->adj_ev[0], c->adj_ev[1]);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&c->adj_rev_ms, c->adj_ev[1], c->adj_ev[2]);
         if (e != cudaSuccess) rc = fail(c, PORTA_ECUDA, std::string("emergent_vjp: ") + cudaGetErrorString(e));
     } while (0);
     cudaStreamSynchronize(c->stream);
@@ -601,6 +655,8 @@ int emergent_vjp_t(porta_ctx *c, int ndir, const double *mu, const double *chi, 
 void free_all(porta_ctx *c)
 {
     drop_graph(c);
+    for (cudaEvent_t &ev : c->adj_ev)
+        if (ev) cudaEventDestroy(ev);
     void *ptrs[] = {c->d_atm, c->d_eps, c->d_bpl, c->d_b, c->d_rho, c->d_rhoR, c->d_invn, c->d_geom, c->d_rays,
                     c->d_freq, c->d_part, c->d_tw, c->d_jkq, c->d_lstar, c->d_resid, c->d_err, c->d_boxes,
                     c->d_items, c->d_tune_items, c->d_tape, c->d_gpart};
@@ -1126,6 +1182,15 @@ int porta_set_adjoint_launch(porta_ctx *c, int cluster, int nu_group)
     if (cluster > c->ny) return fail(c, PORTA_EINVAL, "set_adjoint_launch: cluster larger than ny");
     c->adj_cluster = cluster;
     c->adj_nu_group = nu_group;
+    c->adj_tuned_ndir = 0;
+    return PORTA_OK;
+}
+
+int porta_adjoint_timing(const porta_ctx *c, float *forward_ms, float *adjoint_ms)
+{
+    if (!c) return PORTA_EINVAL;
+    if (forward_ms) *forward_ms = c->adj_fwd_ms;
+    if (adjoint_ms) *adjoint_ms = c->adj_rev_ms;
     return PORTA_OK;
 }
 

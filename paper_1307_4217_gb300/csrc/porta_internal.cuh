@@ -92,10 +92,11 @@ template <typename Real, int NS>
 cudaError_t max_active_clusters(int cluster, int smem, int threads, int *out);
 
 // adjoint of the emergent sweep (adjoint.cu): shared memory of a launch with
-// ring plane `ring_plane` (16-byte chunks), `ipts` points per strip and F
-// frequencies per pass; occupancy; launch; the fixed-order sum over items
+// ring plane `ring_plane` (16-byte chunks), `ipts` points per strip, tape
+// tiles of `tile_pts` points and F frequencies per pass; occupancy; launch;
+// the fixed-order sum over items
 template <typename Real, int NS>
-int adjoint_smem_bytes(int ring_plane, int ipts, int F);
+int adjoint_smem_bytes(int ring_plane, int ipts, int tile_pts, int F);
 template <typename Real, int NS>
 cudaError_t adjoint_max_active_clusters(int cluster, int smem, int threads, int *out);
 template <typename Real, int NS>
@@ -163,4 +164,8 @@ struct porta_ctx {
     size_t gpart_bytes = 0;
     int adj_cluster = 0, adj_nu_group = 0;
     porta::LaunchCfg last_adj{};
+    float adj_fwd_ms = 0.f, adj_rev_ms = 0.f;   // device time of the last porta_emergent_vjp
+    int adj_tuned_ndir = 0;                     // automatic shape: timed once per direction count
+    porta::LaunchCfg adj_tuned{};
+    cudaEvent_t adj_ev[3] = {nullptr, nullptr, nullptr};
 };
