@@ -49,7 +49,7 @@ PEAK_FP32_TFLOPS = SMS * LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
 L2_FLUSH_BYTES = 256 << 20
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "sweep_pol64_traffic.json")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_1307_4217_gb300", "csrc", f)
-                  for f in ("sweep.cu", "device_math.cuh", "porta_internal.cuh")]
+                  for f in ("sweep.cu", "sweep_common.cuh", "device_math.cuh", "porta_internal.cuh")]
 
 
 def kernel_hash():
@@ -80,6 +80,10 @@ def args_parse():
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-rays", type=int, default=4)
+    ap.add_argument("--adjoint-reps", type=int, default=5,
+                    help="timed calls of the emergent-Stokes adjoint (0 skips it)")
+    ap.add_argument("--adjoint-cluster", type=int, default=0, help="force the adjoint cluster size (skips its tuning)")
+    ap.add_argument("--adjoint-nu-group", type=int, default=0, help="force the adjoint frequencies per pass")
     ap.add_argument("--cluster", type=int, default=0, help="force the sweep cluster size (skips the autotuner)")
     ap.add_argument("--nu-group", type=int, default=0, help="force frequencies per pass (skips the autotuner)")
     ap.add_argument("--workload", choices=["pol64", "batched256"], default="pol64",
@@ -354,6 +358,37 @@ def run_cuda(args):
                 "launch": ctx64.launch_info()}
         ctx64.close()
 
+    # reverse mode of the emergent Stokes profiles (differentiation workload: the
+    # same 64^3 box, vertical + 4 oblique emergent rays, all frequencies), FP32:
+    # device time of the forward sweep with its tape and of the adjoint sweep
+    adjoint = None
+    if args.adjoint_reps > 0 and wl.name == "pol64":
+        import synth
+        mu, az = synth.emergent_directions()
+        nz, ny, nx = ctx.shape
+        gen = torch.Generator(device=dev).manual_seed(1234)
+        gout = torch.randn((len(mu), ctx.nnu, ny, nx, ctx.ns), dtype=torch.float64, device=dev, generator=gen)
+        gbuf = [torch.empty((nz, ny, nx), dtype=torch.float64, device=dev) for _ in range(2)]
+        gbuf.append(torch.empty((3, nz, ny, nx), dtype=torch.float64, device=dev))
+        ts = []
+        with torch.cuda.stream(stream):
+            ctx.set_rho(wl.rho0)
+            ctx.set_adjoint_launch(args.adjoint_cluster, args.adjoint_nu_group)
+            ctx.emergent_vjp(mu, az, gout, g_chi=gbuf[0], g_e=gbuf[1], g_b=gbuf[2])   # shape tuning
+            for _ in range(args.adjoint_reps):
+                ctx.emergent_vjp(mu, az, gout, g_chi=gbuf[0], g_e=gbuf[1], g_b=gbuf[2])
+                ts.append(ctx.adjoint_timing())
+        f_ms = float(np.median([t["forward_ms"] for t in ts]))
+        a_ms = float(np.median([t["adjoint_ms"] for t in ts]))
+        nupd = len(mu) * ctx.nnu * nx * ny * nz
+        adjoint = {"workload": f"{nx}x{ny}x{nz} polarized, {ctx.nnu} frequencies, vertical + 4 oblique (mu=0.5) "
+                               "emergent rays; gradients w.r.t. chi, e, B", "dtype": "f32",
+                   "forward_ms": f_ms, "adjoint_ms": a_ms, "ratio": a_ms / f_ms,
+                   "adjoint_updates_per_s": nupd / (a_ms * 1e-3), "reps": args.adjoint_reps,
+                   "launch": ctx.adjoint_info(),
+                   "timing": "CUDA events inside porta_emergent_vjp (forward emergent sweep with tape; "
+                             "adjoint sweep + fixed-order reduction), median"}
+
     # max over ranks
     if world > 1:
         t = torch.tensor([step_ms, sweep_ms, e2e_s], dtype=torch.float64, device=dev)
@@ -390,6 +425,7 @@ def run_cuda(args):
                 "d2h_bytes_per_step": d2h, "residual": residual},
         "gpu_launches": 3 * args.steps,
         "fp64_plain": fp64,
+        "adjoint": adjoint,
     }
     print(json.dumps(line))
     if world > 1:

@@ -189,7 +189,10 @@ int porta_see_update(porta_ctx *c, double *max_change);
 
 /* Emergent Stokes vectors at the top plane for ndir outgoing directions
    (host arrays mu in (0, 1], chi in radians). out: ndir*n_nu*ny*nx*NS doubles,
-   layout [dir][nu][y][x][stokes]. Uses the current rho. */
+   layout [dir][nu][y][x][stokes]. Uses the current rho. Unless porta_opts
+   fixed the launch shape, the first call for a given number of directions
+   times the fitting shapes (cluster size x frequencies per pass) and keeps
+   the fastest; results do not depend on the shape. */
 int porta_emergent_stokes(porta_ctx *c, int ndir, const double *mu, const double *chi,
                           double *out, int where);
 

@@ -33,6 +33,7 @@
 
 #include <algorithm>
 
+#include "adjoint_math.cuh"
 #include "device_math.cuh"
 #include "porta_internal.cuh"
 #include "sweep_common.cuh"
@@ -500,8 +501,11 @@ __device__ __forceinline__ void adjoint_item(const SweepArgs<Real> &a, cg::clust
         }
         // (c) the boundary plane has no O or P terms: complete now
         if (q == 1) finalize(0, sM, opar, false, wP);
+        // end of step: the DSMEM gathers of phase 2 have been consumed, so this
+        // barrier only orders them before the next phase 1 overwrites gM and gP
+        // (write after read): no release fence needed
         __syncthreads();
-        cluster_arrive_release();
+        cluster_arrive_relaxed();
         if (q - 2 >= 0) {
             stage(q - 2);        // tape rows for step q-1, in flight during the refill and the barrier
             fill(q - 2);

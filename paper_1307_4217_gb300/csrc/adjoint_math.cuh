@@ -1,0 +1,101 @@
+// Derivatives of the formal-solver step for the adjoint sweep (adjoint.cu):
+// t-derivatives of the Bezier/DELO coefficients (Eqs. 8-12) and the partial
+// derivatives of the BESSER control point (Sec. 3.2) on the branch it takes.
+#pragma once
+#include "device_math.cuh"
+
+namespace porta {
+
+// ---------------------------------------------------------------------------
+// Derivatives for the adjoint sweep.
+// d/dt of the step coefficients (Eqs. 8-12), from differentiating the closed
+// forms and writing the result through the coefficients themselves:
+//   de = -e,              dpsi'_M = e - psi'_M/t,   dpsi'_O = psi'_M/t,
+//   dw_M = e - 2 w_M/t,   dw_O = w_C/t,             dw_C = 2 (psi'_M - w_C)/t.
+// The cancellation in these forms is at most a factor of a few for every
+// t > 0, so they are as accurate as the coefficients (series or closed form).
+// ---------------------------------------------------------------------------
+template <typename Real>
+struct CoefD {
+    Real de, dpm, dpo, dwm, dwo, dwc;
+};
+
+template <typename Real>
+__device__ __forceinline__ CoefD<Real> coefficient_derivs(Real t, const Coef<Real> &c)
+{
+    CoefD<Real> d;
+    const Real it = rcp(t);
+    d.de = -c.e;
+    d.dpm = c.e - c.pm * it;
+    d.dpo = c.pm * it;
+    d.dwm = c.e - Real(2) * c.wm * it;
+    d.dwo = c.wc * it;
+    d.dwc = Real(2) * (c.pm - c.wc) * it;
+    return d;
+}
+
+// BESSER control point and its partial derivatives with respect to
+// (y_M, y_O, y_P, h_M, h_P) on the branch it takes (Sec. 3.2):
+//   step 2 (extremum at O): c = y_O;  step 6 (overshoot in MO): c = y_M;
+//   steps 7-9 with c_P clipped: c = y_O - (h_M/h_P)(y_P - y_O);
+//   otherwise (step 4): c = y_O - h_M^2 (y_P - y_O)/(2 h_P s) - h_P (y_O - y_M)/(2 s),
+//   s = h_M + h_P.
+// The branch tests are those of control_point on the same BesserGeom, so the
+// adjoint takes the branch the forward sweep took. The h-derivatives of the
+// parabola are linear in (d_P, d_M) = (y_P - y_O, y_O - y_M) with per-update
+// factors, computed once for the four Stokes parameters.
+template <typename Real>
+struct BesserGrad {
+    BesserGeom<Real> g;
+    Real dyM, dyP;          // parabola: dc/dy_M, dc/dy_P
+    Real hMp, hMm, hPp, hPm; // parabola: dc/dh_M = hMp d_P + hMm d_M, dc/dh_P = hPp d_P + hPm d_M
+    Real ihP;                // 1/h_P (clipped branch)
+};
+
+template <typename Real>
+__device__ __forceinline__ BesserGrad<Real> besser_grad(Real hM, Real hP)
+{
+    BesserGrad<Real> b;
+    b.g = besser_geom(hM, hP);
+    const Real is = rcp(hM + hP);
+    b.ihP = rcp(hP);
+    b.dyM = b.g.b * b.g.hm2;
+    b.dyP = -b.g.a * b.g.hm2;
+    // grouped as bounded ratios times one reciprocal: optical paths reach 1e-28
+    // in the far wings, where 1/(h_M + h_P)^2 alone would overflow FP32
+    const Real fM = hM * is, fP = hP * is, fq = (hM + Real(2) * hP) * is;   // in [0, 1], [0, 1], [1, 2]
+    b.hMp = -Real(0.5) * fM * fq * b.ihP;
+    b.hMm = Real(0.5) * fP * is;
+    b.hPp = Real(0.5) * fM * fq * b.g.r * b.ihP;
+    b.hPm = -Real(0.5) * fM * is;
+    return b;
+}
+
+template <typename Real>
+struct CpGrad {
+    Real c, dyM, dyO, dyP, dhM, dhP;
+};
+
+template <typename Real>
+__device__ __forceinline__ CpGrad<Real> control_point_grad(Real yM, Real yO, Real yP, const BesserGrad<Real> &b)
+{
+    const BesserGeom<Real> &g = b.g;
+    const Real dm = yO - yM, dp = yP - yO;
+    const Real yp = g.a * dp + g.b * dm;
+    const Real w = g.hm2 * yp;
+    const Real u = g.hp2 * yp;
+    CpGrad<Real> r;
+    if (!(dm * dp > Real(0))) {                       // step 2
+        r = CpGrad<Real>{yO, Real(0), Real(1), Real(0), Real(0), Real(0)};
+    } else if ((dm - w) * w < Real(0)) {              // steps 5-6
+        r = CpGrad<Real>{yM, Real(1), Real(0), Real(0), Real(0), Real(0)};
+    } else if (u * (u - dp) > Real(0)) {              // step 7 clipped, steps 8-9
+        r = CpGrad<Real>{yO - g.r * dp, Real(0), Real(1) + g.r, -g.r, -dp * b.ihP, g.r * dp * b.ihP};
+    } else {                                          // step 4
+        r = CpGrad<Real>{yO - w, b.dyM, Real(1) - b.dyM - b.dyP, b.dyP, b.hMp * dp + b.hMm * dm,
+                         b.hPp * dp + b.hPm * dm};
+    }
+    return r;
+}
+
+}  // namespace porta

@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "porta.h"
+#include "porta_ctx.h"
 #include "porta_internal.cuh"
 #include "see_kernels.cuh"
 
@@ -413,6 +414,70 @@ int autotune_t(porta_ctx *c)
     return rc;
 }
 
+// Launch shape of the emergent sweep for ndir directions: the one given in
+// porta_opts, else timed once per direction count over the fitting shapes
+// (cluster sizes x frequencies per pass; each trial rewrites the same outputs).
+// Leaves the arguments shaped for the chosen launch.
+template <typename Real, int NS>
+int emergent_shape(porta_ctx *c, SweepArgs<Real> &a, int ndir, LaunchCfg &cfg)
+{
+    auto shape = [&](LaunchCfg &k) {
+        shape_args<Real>(c, a, k);
+        a.nitems = ndir * a.ngroups;
+        k.clusters = std::min(k.clusters, a.nitems);
+    };
+    if (c->user_shape || c->emg_tuned_ndir == ndir) {
+        if (c->user_shape) {
+            int rc = choose_launch<Real, NS>(c, cfg, c->opt_cluster, c->opt_nu_group, ndir);
+            if (rc) return fail(c, rc, "no sweep launch shape fits this grid");
+        } else {
+            cfg = c->emg_tuned;
+        }
+        shape(cfg);
+        return PORTA_OK;
+    }
+    std::vector<LaunchCfg> cand;
+    const int sizes[] = {1, 2, 3, 4, 6, 8, 12, 16};
+    for (int C : sizes) {
+        if (C > c->ny) continue;
+        int last_f = -1;
+        for (int G = 1; G <= c->n_nu; ++G) {
+            const int F = (c->n_nu + G - 1) / G;
+            if (F == last_f) continue;
+            last_f = F;
+            LaunchCfg k;
+            if (choose_launch<Real, NS>(c, k, C, F, ndir * G) == PORTA_OK && k.F == F) cand.push_back(k);
+        }
+    }
+    if (cand.empty()) return fail(c, PORTA_EINVAL, "no sweep launch shape fits this grid");
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float best = 1e30f;
+    cudaError_t e = cudaSuccess;
+    for (LaunchCfg k : cand) {
+        shape(k);
+        float ms = 0;
+        e = cudaEventRecord(e0, c->stream);
+        if (e == cudaSuccess) e = launch_sweep<Real, NS>(a, MODE_EMERGENT, k, c->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) break;
+        if (ms < best) {
+            best = ms;
+            cfg = k;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return fail(c, PORTA_ECUDA, std::string("emergent shape timing: ") + cudaGetErrorString(e));
+    c->emg_tuned = cfg;
+    c->emg_tuned_ndir = ndir;
+    shape(cfg);
+    return PORTA_OK;
+}
+
 template <typename Real>
 int emergent_t(porta_ctx *c, int ndir, const double *mu, const double *chi, double *dout)
 {
@@ -437,12 +502,8 @@ int emergent_t(porta_ctx *c, int ndir, const double *mu, const double *chi, doub
         a.rays = dr;
         a.out = dout;
         LaunchCfg cfg;
-        rc = c->ns == 1 ? choose_launch<Real, 1>(c, cfg, c->opt_cluster, c->opt_nu_group, c->nray)
-                        : choose_launch<Real, 4>(c, cfg, c->opt_cluster, c->opt_nu_group, c->nray);
-        if (rc) { rc = fail(c, rc, "no sweep launch shape fits this grid"); break; }
-        shape_args<Real>(c, a, cfg);
-        a.nitems = ndir * a.ngroups;
-        cfg.clusters = std::min(cfg.clusters, a.nitems);
+        rc = c->ns == 1 ? emergent_shape<Real, 1>(c, a, ndir, cfg) : emergent_shape<Real, 4>(c, a, ndir, cfg);
+        if (rc) break;
         e = c->ns == 1 ? launch_sweep<Real, 1>(a, MODE_EMERGENT, cfg, c->stream)
                        : launch_sweep<Real, 4>(a, MODE_EMERGENT, cfg, c->stream);
         if (e != cudaSuccess) { rc = fail(c, PORTA_ECUDA, std::string("emergent launch: ") + cudaGetErrorString(e)); break; }
@@ -565,12 +626,8 @@ int emergent_vjp_t(porta_ctx *c, int ndir, const double *mu, const double *chi, 
         a.out = dout ? dout : scratch_out;
         a.store = (Real *)c->d_tape;
         LaunchCfg cfg;
-        rc = c->ns == 1 ? choose_launch<Real, 1>(c, cfg, c->opt_cluster, c->opt_nu_group, c->nray)
-                        : choose_launch<Real, 4>(c, cfg, c->opt_cluster, c->opt_nu_group, c->nray);
-        if (rc) { rc = fail(c, rc, "no sweep launch shape fits this grid"); break; }
-        shape_args<Real>(c, a, cfg);
-        a.nitems = ndir * a.ngroups;
-        cfg.clusters = std::min(cfg.clusters, a.nitems);
+        rc = c->ns == 1 ? emergent_shape<Real, 1>(c, a, ndir, cfg) : emergent_shape<Real, 4>(c, a, ndir, cfg);
+        if (rc) break;
         e = cudaEventRecord(c->adj_ev[0], c->stream);
         if (e == cudaSuccess)
             e = c->ns == 1 ? launch_sweep<Real, 1>(a, MODE_EMERGENT, cfg, c->stream)
@@ -729,6 +786,7 @@ static int create_impl(int nbox, const porta_grid *grids, const porta_atom *at, 
     c->zeta = at->zeta; c->gbar = at->gbar; c->bcrit = at->bcrit;
     c->n_mu = q->n_mu; c->n_chi = q->n_chi; c->n_nu = q->n_nu; c->x_max = q->x_max;
     c->precision = prec;
+    c->user_shape = o && (o->cluster > 0 || o->nu_group > 0);
     c->opt_cluster = o ? o->cluster : 0;
     c->opt_nu_group = o ? o->nu_group : 0;
     c->nvox = nvox;

@@ -2,9 +2,6 @@
 #pragma once
 #include <cuda_runtime.h>
 
-#include <string>
-#include <vector>
-
 #include "porta.h"
 
 namespace porta {
@@ -106,66 +103,3 @@ cudaError_t launch_adjoint_reduce(const Real *gpart, int nitems, int ngroups, lo
                                   double bfac, double *g_chi, double *g_e, double *g_b, cudaStream_t st);
 
 }  // namespace porta
-
-struct porta_ctx {
-    int nx = 0, ny = 0, nz = 0;
-    double lx = 0, ly = 0;
-    std::vector<double> z;
-    int model = 0, ns = 1, nl = 1, nj = 1;
-    double zeta = 0, gbar = 1, bcrit = 25;
-    int n_mu = 0, n_chi = 0, n_nu = 0;
-    double x_max = 4;
-    int precision = PORTA_FP32;
-    int opt_cluster = 0, opt_nu_group = 0;
-    long long nvox = 0;
-    int nray = 0;
-    std::vector<double> mu, chi, w, xf, wf, tkq;  // quadratures, T^K_Q per ray (18)
-    cudaStream_t stream = nullptr;
-    std::string err;
-    bool have_atm = false, have_rho = false, have_fs = false, have_jkq = false;
-
-    // device memory
-    size_t rsz = 4;                 // sizeof(Real) of the sweep
-    void *d_atm = nullptr;          // Real SoA: chi, vel, bx, by, bz, bpl
-    double *d_eps = nullptr;        // FP64 per-voxel eps, bpl, B (SEE)
-    double *d_bpl = nullptr;
-    double *d_b = nullptr;          // 3*nvox
-    double *d_rho = nullptr;        // nvox*nl FP64
-    void *d_rhoR = nullptr;         // nl*nvox Real
-    void *d_invn = nullptr;         // nray*nvox Real
-    void *d_geom = nullptr;         // nray*nz PlaneGeom
-    void *d_rays = nullptr;         // nray RayDev
-    void *d_freq = nullptr;         // xf, wf (Real)
-    void *d_part = nullptr;         // nray*nvox*(ns==1 ? 2 : 4) Real
-    double *d_tw = nullptr;         // nray*19 FP64: w_m, T (18)
-    double *d_jkq = nullptr, *d_lstar = nullptr;
-    unsigned long long *d_resid = nullptr;
-    // batched problems: per-box sizes, grids and offsets
-    int nbox = 1;
-    std::vector<porta::BoxDev> boxes;
-    std::vector<std::vector<double>> bz;
-    std::vector<double> blx, bly;
-    void *d_boxes = nullptr;       // nbox BoxDev
-    int *d_items = nullptr;        // nbox*nray work items ordered by decreasing cost
-    int *d_tune_items = nullptr;   // strided sample of the work items for the autotuner
-    int n_tune = 0;
-    int *d_err = nullptr;
-    // CUDA graph of one Jacobi iteration (porta_run_iterations)
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t graph_exec = nullptr;
-    cudaStream_t graph_stream = nullptr;
-    // last launch of the formal solution
-    porta::LaunchCfg last{};
-    // reverse mode of the emergent sweep: tape of the forward Stokes vectors,
-    // per-item partial gradients, forced launch shape (0 = automatic), last launch
-    void *d_tape = nullptr;
-    size_t tape_bytes = 0;
-    void *d_gpart = nullptr;
-    size_t gpart_bytes = 0;
-    int adj_cluster = 0, adj_nu_group = 0;
-    porta::LaunchCfg last_adj{};
-    float adj_fwd_ms = 0.f, adj_rev_ms = 0.f;   // device time of the last porta_emergent_vjp
-    int adj_tuned_ndir = 0;                     // automatic shape: timed once per direction count
-    porta::LaunchCfg adj_tuned{};
-    cudaEvent_t adj_ev[3] = {nullptr, nullptr, nullptr};
-};

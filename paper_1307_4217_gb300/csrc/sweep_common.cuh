@@ -217,6 +217,12 @@ __device__ __forceinline__ void cluster_arrive_release()
 {
     asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
 }
+// arrive without release semantics: for a barrier that only orders reads of
+// other CTAs' shared memory (values already consumed) before later writes
+__device__ __forceinline__ void cluster_arrive_relaxed()
+{
+    asm volatile("barrier.cluster.arrive.relaxed.aligned;\n" ::: "memory");
+}
 __device__ __forceinline__ void cluster_wait_acquire()
 {
     asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
