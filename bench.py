@@ -95,6 +95,20 @@ def dist_env():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
 
 
+def max_over_ranks(values, device):
+    """Element-wise maximum over ranks of per-rank timings: the slowest replica
+    sets the job's time (an all-reduce on timings only, never on solver data)."""
+    import torch
+    t = torch.tensor(values, dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return t.tolist()
+
+
+def job_throughput(units_per_rank, world, seconds):
+    """Whole-job rate: every rank solves its own replica of the workload."""
+    return world * units_per_rank / seconds
+
+
 # ---------------------------------------------------------------- clocks sampling
 
 class ClockSampler:
@@ -391,9 +405,7 @@ def run_cuda(args):
 
     # max over ranks
     if world > 1:
-        t = torch.tensor([step_ms, sweep_ms, e2e_s], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        step_ms, sweep_ms, e2e_s = t.tolist()
+        step_ms, sweep_ms, e2e_s = max_over_ranks([step_ms, sweep_ms, e2e_s], dev)
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()
@@ -409,7 +421,7 @@ def run_cuda(args):
            "sweep_launch": info, "launch_shape": "forced" if forced else "autotuned",
            "step": "one CUDA-graph replay of a Jacobi iteration (sweep, J^K_Q sums, SEE, residual)"}
     line = {
-        "metric": METRIC, "value": world * wl.updates / (step_ms * 1e-3), "unit": UNIT, "n_gpus": world,
+        "metric": METRIC, "value": job_throughput(wl.updates, world, step_ms * 1e-3), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": cfg,
@@ -421,7 +433,7 @@ def run_cuda(args):
                      "peak_basis": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (derived, not measured)"},
         "cpu_baseline": cpu,
         "clocks": clocks,
-        "e2e": {"value": world * wl.updates / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+        "e2e": {"value": job_throughput(wl.updates, world, e2e_s), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "residual": residual},
         "gpu_launches": 3 * args.steps,
         "fp64_plain": fp64,
