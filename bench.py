@@ -336,6 +336,7 @@ def run_cuda(args):
         barrier()
         sweep_ms = sum(e[0].elapsed_time(e[1]) for e in evs) / args.steps
     info = ctx.launch_info()
+    fill = ctx.fill_info()
 
     # end to end through the ABI with pinned host buffers: rho in, one iteration, rho and residual out
     rho_h = torch.from_numpy(wl.rho0.copy()).pin_memory()
@@ -418,7 +419,7 @@ def run_cuda(args):
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
     cfg = {"workload": wl.desc, **wl.config, "updates_per_step": wl.updates, "seed": "rank",
            "l2": "flushed between timed steps (256 MiB write)", "parallelism": f"replicas x{world}",
-           "sweep_launch": info, "launch_shape": "forced" if forced else "autotuned",
+           "sweep_launch": info, "sweep_fill": fill, "launch_shape": "forced" if forced else "autotuned",
            "step": "one CUDA-graph replay of a Jacobi iteration (sweep, J^K_Q sums, SEE, residual)"}
     line = {
         "metric": METRIC, "value": job_throughput(wl.updates, world, step_ms * 1e-3), "unit": UNIT, "n_gpus": world,
@@ -435,7 +436,7 @@ def run_cuda(args):
         "clocks": clocks,
         "e2e": {"value": job_throughput(wl.updates, world, e2e_s), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "residual": residual},
-        "gpu_launches": 3 * args.steps,
+        "gpu_launches": (4 if fill["cluster"] > 0 else 3) * args.steps,
         "fp64_plain": fp64,
         "adjoint": adjoint,
     }

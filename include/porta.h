@@ -205,10 +205,26 @@ int porta_probe_ray(porta_ctx *c, int m, double *out, double *lstar, int where);
 /* Autotuner of the sweep launch shape: times every fitting (cluster size,
    frequencies per pass) candidate on one wave of rays of the current problem
    (CUDA events on the context's stream), keeps the fastest for subsequent
-   calls and returns it in *cluster / *nu_group (either may be NULL).
-   Requires the atmosphere and rho. Overwrites the device-side partial
-   integrals (call porta_formal_solve afterwards). */
+   calls and returns it in *cluster / *nu_group (either may be NULL). It then
+   times a second, concurrent launch of a smaller cluster shape over the
+   cheapest fraction of the (box, ray) work list -- it runs on SMs that the
+   main shape's clusters cannot occupy -- and keeps it if it is faster
+   (porta_fill_info). With the filler, each launch takes its work items from
+   its own device counter; every item is computed by one fixed shape, so the
+   results do not depend on scheduling. Requires the atmosphere and rho.
+   Overwrites the device-side partial integrals (call porta_formal_solve
+   afterwards). */
 int porta_autotune(porta_ctx *c, int *cluster, int *nu_group);
+
+/* The concurrent filler launch kept by porta_autotune: CTAs per cluster,
+   frequencies per pass and the fraction of the work list it takes
+   (cluster size 0: none). */
+int porta_fill_info(const porta_ctx *c, int *cluster_size, int *nu_group, double *fraction);
+
+/* Sets (cluster_size >= 1) or removes (cluster_size 0) the concurrent filler
+   launch by hand: cluster size, frequencies per pass and the fraction of the
+   work list in (0, 1) it takes. PORTA_EINVAL if the shape does not fit. */
+int porta_set_fill(porta_ctx *c, int cluster_size, int nu_group, double fraction);
 
 /* Diagnostic: the coefficients of the BESSER-DELO step (Eqs. 8-12; Table 1
    series at small optical path) exactly as the sweep kernels of the given

@@ -75,6 +75,8 @@ _SIGS = {
     "porta_set_adjoint_launch": (_I, [_P, _I, _I]),
     "porta_adjoint_info": (_I, [_P, _P, _P, _P, _P]),
     "porta_adjoint_timing": (_I, [_P, _P, _P]),
+    "porta_fill_info": (_I, [_P, _P, _P, _P]),
+    "porta_set_fill": (_I, [_P, _I, _I, _D]),
 }
 
 _lib = None
@@ -263,6 +265,16 @@ def porta_adjoint_timing(h):
     return rc, dict(forward_ms=f.value, adjoint_ms=a.value)
 
 
+def porta_fill_info(h):
+    cl, nu, fr = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    rc = lib().porta_fill_info(h, ctypes.byref(cl), ctypes.byref(nu), ctypes.byref(fr))
+    return rc, dict(cluster=cl.value, nu_group=nu.value, fraction=fr.value)
+
+
+def porta_set_fill(h, cluster, nu_group, fraction):
+    return lib().porta_set_fill(h, cluster, nu_group, float(fraction))
+
+
 # ---- convenience wrapper ------------------------------------------------------------
 
 class Context:
@@ -431,6 +443,14 @@ class Context:
 
     def launch_info(self):
         rc, info = porta_launch_info(self.h)
+        self._check(rc)
+        return info
+
+    def set_fill(self, cluster=0, nu_group=0, fraction=0.0):
+        self._check(porta_set_fill(self.h, cluster, nu_group, fraction))
+
+    def fill_info(self):
+        rc, info = porta_fill_info(self.h)
         self._check(rc)
         return info
 

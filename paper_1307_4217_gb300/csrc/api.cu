@@ -281,7 +281,7 @@ std::vector<LaunchCfg> candidates(porta_ctx *c, int nitems)
             int F = (c->n_nu + G - 1) / G;
             if (F == last_f) continue;
             last_f = F;
-            LaunchCfg cfg;
+            LaunchCfg cfg{};
             if (choose_launch<Real, NS>(c, cfg, C, F, nitems) == PORTA_OK && cfg.F == F) {
                 out.push_back(cfg);
                 ++kept;
@@ -339,6 +339,64 @@ SweepArgs<Real> jkq_args(porta_ctx *c)
     return a;
 }
 
+cudaError_t ensure_fill(porta_ctx *c)
+{
+    if (c->fill) return cudaSuccess;
+    LaunchFill *f = new (std::nothrow) LaunchFill;
+    if (!f) return cudaErrorMemoryAllocation;
+    cudaError_t e = cudaStreamCreateWithFlags(&f->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&f->fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&f->join, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&f->d_ctr, 2 * sizeof(int));
+    c->fill = f;   // released by free_all also on failure
+    return e;
+}
+
+// J-mode sweep over the work items [items, items + nitems): one launch of the
+// main shape, or, with a filler configured, the main launch over the first
+// (costliest) items and a concurrent launch of the filler shape over the last
+// fraction, each taking its items dynamically from its own counter (every item
+// is computed by one fixed shape, so results do not depend on scheduling)
+template <typename Real>
+cudaError_t sweep_jkq(porta_ctx *c, SweepArgs<Real> a, LaunchCfg cfg, const int *items, int nitems, bool allow_fill)
+{
+    a.items = items;
+    a.nitems = nitems;
+    const int nB = (int)std::lround(c->fill_frac * nitems);
+    if (!allow_fill || c->fill_cfg.cluster <= 0 || nB < 1 || nB >= nitems)
+        return c->ns == 1 ? launch_sweep<Real, 1>(a, MODE_JKQ, cfg, c->stream) : launch_sweep<Real, 4>(a, MODE_JKQ, cfg, c->stream);
+    cudaError_t e = ensure_fill(c);
+    if (e != cudaSuccess) return e;
+    const int nA = nitems - nB;
+    SweepArgs<Real> b = a;
+    LaunchCfg fc = c->fill_cfg;
+    shape_args<Real>(c, b, fc);
+    b.items = items + nA;
+    b.nitems = nB;
+    b.next_item = c->fill->d_ctr + 1;
+    fc.clusters = std::min(fc.clusters, nB);
+    a.nitems = nA;
+    a.next_item = c->fill->d_ctr;
+    cfg.clusters = std::min(cfg.clusters, nA);
+    // the main launch's clusters are placed first; the filler takes what is left
+    int least = 0, greatest = 0;
+    e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    if (e != cudaSuccess) return e;
+    cfg.priority = greatest;
+    fc.priority = least;
+    e = cudaMemsetAsync(c->fill->d_ctr, 0, 2 * sizeof(int), c->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(c->fill->fork, c->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->fill->stream, c->fill->fork, 0);
+    if (e == cudaSuccess)
+        e = c->ns == 1 ? launch_sweep<Real, 1>(a, MODE_JKQ, cfg, c->stream) : launch_sweep<Real, 4>(a, MODE_JKQ, cfg, c->stream);
+    if (e == cudaSuccess)
+        e = c->ns == 1 ? launch_sweep<Real, 1>(b, MODE_JKQ, fc, c->fill->stream)
+                       : launch_sweep<Real, 4>(b, MODE_JKQ, fc, c->fill->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(c->fill->join, c->fill->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, c->fill->join, 0);
+    return e;
+}
+
 template <typename Real>
 int formal_solve_t(porta_ctx *c, int probe_ray, Real *probe, Real *probe_ls)
 {
@@ -346,13 +404,12 @@ int formal_solve_t(porta_ctx *c, int probe_ray, Real *probe, Real *probe_ls)
     a.probe_ray = probe_ray;
     a.probe = probe;
     a.probe_ls = probe_ls;
-    LaunchCfg cfg;
+    LaunchCfg cfg{};
     int rc = c->ns == 1 ? choose_launch<Real, 1>(c, cfg, c->opt_cluster, c->opt_nu_group, a.nitems)
                         : choose_launch<Real, 4>(c, cfg, c->opt_cluster, c->opt_nu_group, a.nitems);
     if (rc) return fail(c, rc, "no sweep launch shape fits this grid (shared memory / cluster limits)");
     shape_args<Real>(c, a, cfg);
-    cudaError_t e = c->ns == 1 ? launch_sweep<Real, 1>(a, MODE_JKQ, cfg, c->stream)
-                               : launch_sweep<Real, 4>(a, MODE_JKQ, cfg, c->stream);
+    cudaError_t e = sweep_jkq<Real>(c, a, cfg, a.items, a.nitems, probe_ray < 0);
     if (e != cudaSuccess) return fail(c, PORTA_ECUDA, std::string("sweep launch: ") + cudaGetErrorString(e));
     c->last = cfg;
     return PORTA_OK;
@@ -370,7 +427,9 @@ int autotune_t(porta_ctx *c)
     double best = 1e300;
     LaunchCfg pick = cand[0];
     int rc = PORTA_OK;
-    for (const LaunchCfg &cfg0 : cand) {
+    std::vector<double> est_of(cand.size(), 1e300);
+    for (size_t ci = 0; ci < cand.size(); ++ci) {
+        const LaunchCfg &cfg0 = cand[ci];
         LaunchCfg cfg = cfg0;
         SweepArgs<Real> a = jkq_args<Real>(c);
         shape_args<Real>(c, a, cfg);
@@ -398,19 +457,95 @@ int autotune_t(porta_ctx *c)
         double waves = c->nbox == 1 ? std::ceil((double)c->nray / cfg.clusters)
                                     : (double)c->nbox * c->nray / c->n_tune;
         double est = ms * waves;
+        est_of[ci] = est;
         if (est < best) {
             best = est;
             pick = cfg;
         }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    c->fill_cfg = LaunchCfg{};
+    c->fill_frac = 0.0;
     if (rc == PORTA_OK) {
         c->opt_cluster = pick.cluster;
         c->opt_nu_group = pick.F;
+        // Concurrent filler: smaller clusters over the cheapest fraction of the
+        // work list, on the SMs the main shape's clusters leave idle. Timed on the
+        // whole work list (one box) or the strided sample (batches) for every
+        // smaller cluster size up to 8 (its best F) x split fractions.
+        const int *titems = c->nbox == 1 ? c->d_items : c->d_tune_items;
+        const int tn = c->nbox == 1 ? nitems : c->n_tune;
+        auto time_split = [&](float &ms) {
+            SweepArgs<Real> a = jkq_args<Real>(c);
+            LaunchCfg cfg = pick;
+            shape_args<Real>(c, a, cfg);
+            ms = 1e30f;
+            for (int rep = 0; rep < 2; ++rep) {
+                cudaError_t e = cudaEventRecord(e0, c->stream);
+                if (e == cudaSuccess) e = sweep_jkq<Real>(c, a, cfg, titems, tn, true);
+                if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                float t = 0;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+                if (e != cudaSuccess) return e;
+                ms = std::min(ms, t);
+            }
+            return cudaSuccess;
+        };
+        std::vector<std::pair<double, LaunchCfg>> small;
+        for (int C = 1; C < std::min(pick.cluster, 9); ++C) {
+            double b = 1e300;
+            LaunchCfg k{};
+            for (size_t ci = 0; ci < cand.size(); ++ci)
+                if (cand[ci].cluster == C && est_of[ci] < b) {
+                    b = est_of[ci];
+                    k = cand[ci];
+                }
+            if (k.cluster > 0) small.push_back({b, k});
+        }
+
+        float base = 0;
+        cudaError_t e = tn >= 8 && !small.empty() ? ensure_fill(c) : cudaSuccess;
+        if (e == cudaSuccess && tn >= 8 && !small.empty()) e = time_split(base);
+        float best_split = base;
+        LaunchCfg best_fill{};
+        double best_frac = 0.0;
+        // split points: one box -> the main launch keeps a whole number of rounds
+        // of its resident clusters (rays cost the same); batches -> fractions
+        std::vector<double> fracs;
+        if (c->nbox == 1) {
+            const int rounds = (tn + pick.clusters - 1) / pick.clusters;
+            for (int r = rounds - 1; r >= std::max(1, rounds - 6); --r) {
+                const int nB = tn - r * pick.clusters;
+                if (nB > 0 && nB < tn) fracs.push_back((double)nB / tn);
+            }
+        } else {
+            fracs = {0.05, 0.1, 0.15, 0.2, 0.25, 0.3};
+        }
+        for (const auto &sk : small) {
+            if (e != cudaSuccess || tn < 8) break;
+            for (double frac : fracs) {
+                c->fill_cfg = sk.second;
+                c->fill_frac = frac;
+                float t = 0;
+                e = time_split(t);
+                if (e != cudaSuccess) break;
+                if (t < best_split) {
+                    best_split = t;
+                    best_fill = sk.second;
+                    best_frac = frac;
+                }
+            }
+        }
+        if (e != cudaSuccess) rc = fail(c, PORTA_ECUDA, std::string("autotune (filler): ") + cudaGetErrorString(e));
+        // keep a filler only if it beats the single launch by more than the timing noise
+        const bool keep = rc == PORTA_OK && best_fill.cluster > 0 && best_split < 0.98f * base;
+        c->fill_cfg = keep ? best_fill : LaunchCfg{};
+        c->fill_frac = keep ? best_frac : 0.0;
         c->have_fs = c->have_jkq = false;
         drop_graph(c);
     }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
     return rc;
 }
 
@@ -445,7 +580,7 @@ int emergent_shape(porta_ctx *c, SweepArgs<Real> &a, int ndir, LaunchCfg &cfg)
             const int F = (c->n_nu + G - 1) / G;
             if (F == last_f) continue;
             last_f = F;
-            LaunchCfg k;
+            LaunchCfg k{};
             if (choose_launch<Real, NS>(c, k, C, F, ndir * G) == PORTA_OK && k.F == F) cand.push_back(k);
         }
     }
@@ -501,7 +636,7 @@ int emergent_t(porta_ctx *c, int ndir, const double *mu, const double *chi, doub
         a.geom = dg;
         a.rays = dr;
         a.out = dout;
-        LaunchCfg cfg;
+        LaunchCfg cfg{};
         rc = c->ns == 1 ? emergent_shape<Real, 1>(c, a, ndir, cfg) : emergent_shape<Real, 4>(c, a, ndir, cfg);
         if (rc) break;
         e = c->ns == 1 ? launch_sweep<Real, 1>(a, MODE_EMERGENT, cfg, c->stream)
@@ -568,7 +703,7 @@ int choose_adjoint(porta_ctx *c, LaunchCfg &best, int force_c, int force_f, int 
             const double item = c->nz * (passes * F * 3.0 + 0.5 * F + 4.0);
             const double cost = std::ceil((double)items / ncl) * item;
             if (all) {
-                LaunchCfg k;
+                LaunchCfg k{};
                 k.cluster = C;
                 k.F = F;
                 k.threads = threads;
@@ -625,7 +760,7 @@ int emergent_vjp_t(porta_ctx *c, int ndir, const double *mu, const double *chi, 
         a.rays = dr;
         a.out = dout ? dout : scratch_out;
         a.store = (Real *)c->d_tape;
-        LaunchCfg cfg;
+        LaunchCfg cfg{};
         rc = c->ns == 1 ? emergent_shape<Real, 1>(c, a, ndir, cfg) : emergent_shape<Real, 4>(c, a, ndir, cfg);
         if (rc) break;
         e = cudaEventRecord(c->adj_ev[0], c->stream);
@@ -636,7 +771,7 @@ int emergent_vjp_t(porta_ctx *c, int ndir, const double *mu, const double *chi, 
         if (e != cudaSuccess) { rc = fail(c, PORTA_ECUDA, std::string("emergent_vjp forward: ") + cudaGetErrorString(e)); break; }
         // adjoint: launch shape forced, or timed once per direction count over
         // every fitting shape (each trial overwrites the same outputs)
-        LaunchCfg acfg;
+        LaunchCfg acfg{};
         std::vector<LaunchCfg> cand;
         const bool forced = c->adj_cluster > 0 || c->adj_nu_group > 0;
         const bool tune = !forced && c->adj_tuned_ndir != ndir;
@@ -712,6 +847,14 @@ int emergent_vjp_t(porta_ctx *c, int ndir, const double *mu, const double *chi, 
 void free_all(porta_ctx *c)
 {
     drop_graph(c);
+    if (c->fill) {
+        if (c->fill->stream) cudaStreamDestroy(c->fill->stream);
+        if (c->fill->fork) cudaEventDestroy(c->fill->fork);
+        if (c->fill->join) cudaEventDestroy(c->fill->join);
+        if (c->fill->d_ctr) cudaFree(c->fill->d_ctr);
+        delete c->fill;
+        c->fill = nullptr;
+    }
     for (cudaEvent_t &ev : c->adj_ev)
         if (ev) cudaEventDestroy(ev);
     void *ptrs[] = {c->d_atm, c->d_eps, c->d_bpl, c->d_b, c->d_rho, c->d_rhoR, c->d_invn, c->d_geom, c->d_rays,
@@ -918,7 +1061,7 @@ static int create_impl(int nbox, const porta_grid *grids, const porta_atom *at, 
             ok(cudaMemcpy(c->d_freq, fr.data(), fr.size() * sizeof(double), cudaMemcpyHostToDevice));
         }
         // a launch shape must exist for this grid
-        LaunchCfg cfg;
+        LaunchCfg cfg{};
         int r2 = prec == PORTA_FP32
                      ? (c->ns == 1 ? choose_launch<float, 1>(c, cfg, c->opt_cluster, c->opt_nu_group, c->nray)
                                    : choose_launch<float, 4>(c, cfg, c->opt_cluster, c->opt_nu_group, c->nray))
@@ -1376,7 +1519,7 @@ int porta_run_iterations(porta_ctx *c, int iterations, double *max_change)
             return rc;
         }
         if (e == cudaSuccess) e = e2;
-        if (e == cudaSuccess) e = cudaGraphInstantiate(&c->graph_exec, g, 0);
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&c->graph_exec, g, cudaGraphInstantiateFlagUseNodePriority);
         if (e != cudaSuccess) {
             if (g) cudaGraphDestroy(g);
             c->graph_exec = nullptr;
@@ -1395,6 +1538,42 @@ int porta_run_iterations(porta_ctx *c, int iterations, double *max_change)
         std::memcpy(&v, &bits, sizeof(v));
         *max_change = v;
     }
+    return PORTA_OK;
+}
+
+int porta_set_fill(porta_ctx *c, int cluster, int nu_group, double fraction)
+{
+    if (!c) return PORTA_EINVAL;
+    if (cluster == 0) {
+        c->fill_cfg = LaunchCfg{};
+        c->fill_frac = 0.0;
+        drop_graph(c);
+        return PORTA_OK;
+    }
+    if (cluster < 1 || cluster > 16 || nu_group < 1 || nu_group > c->n_nu || !(fraction > 0.0 && fraction < 1.0))
+        return fail(c, PORTA_EINVAL, "set_fill: cluster in 1..16, nu_group in 1..n_nu, fraction in (0, 1)");
+    LaunchCfg k{};
+    const int nitems = c->nbox * c->nray;
+    int rc = c->precision == PORTA_FP32
+                 ? (c->ns == 1 ? choose_launch<float, 1>(c, k, cluster, nu_group, nitems) : choose_launch<float, 4>(c, k, cluster, nu_group, nitems))
+                 : (c->ns == 1 ? choose_launch<double, 1>(c, k, cluster, nu_group, nitems) : choose_launch<double, 4>(c, k, cluster, nu_group, nitems));
+    if (rc || k.F != nu_group) return fail(c, PORTA_EINVAL, "set_fill: this launch shape does not fit");
+    // stream, events and counters exist before any graph capture uses them
+    cudaError_t e = ensure_fill(c);
+    if (e != cudaSuccess) return fail(c, PORTA_ECUDA, std::string("set_fill: ") + cudaGetErrorString(e));
+    c->fill_cfg = k;
+    c->fill_frac = fraction;
+    c->have_fs = c->have_jkq = false;
+    drop_graph(c);
+    return PORTA_OK;
+}
+
+int porta_fill_info(const porta_ctx *c, int *cluster_size, int *nu_group, double *fraction)
+{
+    if (!c) return PORTA_EINVAL;
+    if (cluster_size) *cluster_size = c->fill_cfg.cluster;
+    if (nu_group) *nu_group = c->fill_cfg.F;
+    if (fraction) *fraction = c->fill_frac;
     return PORTA_OK;
 }
 

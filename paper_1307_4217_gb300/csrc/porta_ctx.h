@@ -8,6 +8,13 @@
 
 #include "porta_internal.cuh"
 
+// stream, fork/join events and work-list counters of the concurrent launch
+struct LaunchFill {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+    int *d_ctr = nullptr;   // [2]: next item of the main and of the filler launch
+};
+
 struct porta_ctx {
     int nx = 0, ny = 0, nz = 0;
     double lx = 0, ly = 0;
@@ -60,6 +67,12 @@ struct porta_ctx {
     cudaStream_t graph_stream = nullptr;
     // last launch of the formal solution
     porta::LaunchCfg last{};
+    // optional second, concurrent sweep launch of smaller clusters over the
+    // cheapest fraction `fill_frac` of the work list: it runs on SMs that the
+    // main launch's clusters cannot occupy (fill_cfg.cluster == 0: none)
+    porta::LaunchCfg fill_cfg{};
+    double fill_frac = 0.0;
+    LaunchFill *fill = nullptr;
     // reverse mode of the emergent sweep: tape of the forward Stokes vectors,
     // per-item partial gradients, forced launch shape (0 = automatic), last launch
     void *d_tape = nullptr;

@@ -63,6 +63,7 @@ struct SweepArgs {
     int probe_ray;                 // -1 or the ray whose Stokes vectors are written to probe
     Real *probe;                   // [nu][nvox][ns]
     Real *probe_ls;                // [nu][nvox]
+    int *next_item;                // J mode: null (static striding) or the launch's work-list counter
     // reverse mode of the emergent sweep (single box)
     Real *store;                   // emergent: null, or the Stokes vectors of every plane [dir][nu][nvox][ns]
     const double *gout;            // adjoint: dL/dI on the top plane [dir][nu][ny][nx][ns]
@@ -75,6 +76,7 @@ struct LaunchCfg {
     int threads;
     int smem;        // dynamic shared memory bytes
     int clusters;    // clusters launched
+    int priority;    // launch priority (0: the stream's; else a value of cudaDeviceGetStreamPriorityRange)
 };
 
 template <typename Real, int NS>

@@ -411,6 +411,29 @@ __global__ void __launch_bounds__(512, 1) sweep_kernel(const SweepArgs<Real> a)
     Real *ibuf = reinterpret_cast<Real *>(ring + 3 * a.ring_plane);
     Real *lane_buf = ibuf + 2 * a.F * NS * a.ipts_max;
     cluster.sync();
+    if constexpr (MODE == MODE_JKQ) {
+        if (a.next_item) {
+            // dynamic work list: CTA 0 of the cluster takes the next item from the
+            // launch's counter and writes it into every CTA's shared memory before
+            // the cluster barrier (slot k & 1: a slot is rewritten only after every
+            // CTA has passed the barrier that followed its last read)
+            __shared__ int s_item[2];
+            for (int k = 0;; ++k) {
+                if (rank == 0 && threadIdx.x == 0) {
+                    const int it = atomicAdd(a.next_item, 1);
+                    for (int r = 0; r < C; ++r) *cluster.map_shared_rank(s_item + (k & 1), r) = it;
+                }
+                cluster.sync();
+                const int item = s_item[k & 1];
+                if (item >= a.nitems) break;
+                const int code = a.items ? a.items[item] : item;
+                const int box = code / a.nray, m = code - box * a.nray;
+                for (int g = 0; g < a.ngroups; ++g)
+                    sweep_item<Real, NS, MODE>(a, cluster, ring, ibuf, lane_buf, box, m, g, rank, C, 0);
+            }
+            return;
+        }
+    }
     for (int item = cid; item < a.nitems; item += ncl) {
         if constexpr (MODE == MODE_JKQ) {
             const int code = a.items ? a.items[item] : item;
@@ -469,13 +492,18 @@ cudaError_t launch_sweep(const SweepArgs<Real> &a, int mode, LaunchCfg &cfg, cud
     lc.blockDim = dim3(cfg.threads);
     lc.dynamicSmemBytes = cfg.smem;
     lc.stream = st;
-    cudaLaunchAttribute at[1];
+    cudaLaunchAttribute at[2];
     at[0].id = cudaLaunchAttributeClusterDimension;
     at[0].val.clusterDim.x = cfg.cluster;
     at[0].val.clusterDim.y = 1;
     at[0].val.clusterDim.z = 1;
     lc.attrs = at;
     lc.numAttrs = 1;
+    if (cfg.priority != 0) {
+        at[1].id = cudaLaunchAttributePriority;
+        at[1].val.priority = cfg.priority;
+        lc.numAttrs = 2;
+    }
     if (mode == MODE_JKQ)
         return cudaLaunchKernelEx(&lc, sweep_kernel<Real, NS, MODE_JKQ>, a);
     return cudaLaunchKernelEx(&lc, sweep_kernel<Real, NS, MODE_EMERGENT>, a);

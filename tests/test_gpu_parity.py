@@ -233,3 +233,43 @@ def test_graph_iterations_match_eager_iterations():
     mc_g = graph.run_iterations(2)
     assert mc_g == mc_e
     assert np.array_equal(graph.get_rho(), eager.get_rho())
+
+
+@pytest.mark.parametrize("prec", [P.PORTA_FP64, P.PORTA_FP32])
+@pytest.mark.parametrize("main,fill,frac", [((8, 7), (2, 3), 0.3), ((4, 21), (3, 5), 0.5), ((16, 7), (1, 2), 0.1)])
+def test_concurrent_filler_launch(prec, main, fill, frac):
+    """A second launch of a smaller shape over the cheapest fraction of the rays:
+    oracle parity, and the dynamic work lists give the same bits on every call."""
+    atm = polarized_case(9, 20, 10, seed=31)
+    rho = initial_rho(atm, 1, seed=32)
+    ctx = make_ctx(atm, 1, 2, 4, 21, prec, cluster=main[0], nu_group=main[1], rho=rho)
+    ctx.set_fill(fill[0], fill[1], frac)
+    assert ctx.fill_info() == {"cluster": fill[0], "nu_group": fill[1], "fraction": frac}
+    out = []
+    for _ in range(2):
+        ctx.formal_solve()
+        out.append(ctx.accumulate_jkq())
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    _, (jo, lo) = oracle_fs(atm, 1, 2, 4, 21, rho)
+    _check_j(out[0][0], out[0][1], jo, lo, TOL[prec])
+
+
+def test_graph_iterations_with_filler_match_eager():
+    torch = pytest.importorskip("torch")
+    atm = polarized_case(12, 10, 12, seed=35)
+    rho = initial_rho(atm, 1, seed=36)
+    ctxs = []
+    for _ in range(2):
+        c = make_ctx(atm, 1, 3, 8, 9, P.PORTA_FP32, cluster=5, nu_group=9, rho=rho)
+        c.set_fill(2, 3, 0.25)
+        ctxs.append(c)
+    eager, graph = ctxs
+    for _ in range(3):
+        eager.formal_solve()
+        eager.accumulate_jkq(want=False)
+        mc_e = eager.see_update()
+    graph.set_stream(torch.cuda.Stream())
+    graph.run_iterations(1)
+    mc_g = graph.run_iterations(2)
+    assert mc_g == mc_e
+    assert np.array_equal(graph.get_rho(), eager.get_rho())
