@@ -88,6 +88,8 @@ def _declare(L):
         "or_control_point_vjp": (None, [_D, _D, _D, _D, _D, _I, _I, _D, _P]),
         "or_step_vjp": (_I, [_I, _P, _P, _P, _P, _P, _D, _P, _D, _D, _I, _I, _P,
                              _P, _P, _P, _P, _P, _P, _P]),
+        "or_see_apply": (_I, [_P, _P, _P, _P]),
+        "or_see_update_src": (_I, [_P, _P, _P, _P, _P, _P]),
         "or_flops_reset": (None, [_I]),
         "or_flops_get": (ctypes.c_longlong, []),
         "or_nray": (_I, [_P]),
@@ -236,6 +238,24 @@ def see_update(prob, jkq, lstar, rho):
     rho = _f64(rho).copy().ravel()
     mc = np.zeros(1)
     assert lib().or_see_update(prob.ref, _ptr(jkq), _ptr(lstar), _ptr(rho), _ptr(mc)) == 0
+    return rho.reshape(prob.shape + (nl_of(prob.model),)), float(mc[0])
+
+
+def see_apply(prob, jkq, rho):
+    """A(S) of the statistical-equilibrium equations written as A(S) = f."""
+    jkq = _f64(jkq).ravel(); rho = _f64(rho).ravel()
+    out = np.zeros_like(rho)
+    assert lib().or_see_apply(prob.ref, _ptr(jkq), _ptr(rho), _ptr(out)) == 0
+    return out.reshape(prob.shape + (nl_of(prob.model),))
+
+
+def see_update_src(prob, jkq, lstar, rho, src=None):
+    """Jacobi update of A(S) = src (src None: the two-level problem, src = eps B delta_K0)."""
+    jkq = _f64(jkq).ravel(); lstar = _f64(lstar).ravel()
+    rho = _f64(rho).copy().ravel()
+    s = _f64(src).ravel() if src is not None else None
+    mc = np.zeros(1)
+    assert lib().or_see_update_src(prob.ref, _ptr(jkq), _ptr(lstar), _ptr(s), _ptr(rho), _ptr(mc)) == 0
     return rho.reshape(prob.shape + (nl_of(prob.model),)), float(mc[0])
 
 

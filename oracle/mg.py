@@ -1,0 +1,159 @@
+"""Non-linear multigrid (FAS) V-cycle of the oracle (test infrastructure only).
+
+Sec. 6 of Stepan & Trujillo Bueno (2013): with the statistical-equilibrium
+equations written as A_l(rho) = f_l on grid level l (A from the formal
+solution, f = eps B delta_K0 on the finest grid),
+  residual         r_l = f_l - A_l(rho_l)                                  (Eq. 14)
+  coarse equation  A_{l-1}(rho') = A_{l-1}(R rho_l) + R r_l                (Eq. 17)
+  correction       rho_l <- rho_l + P (rho' - R rho_l)                     (Eq. 18)
+with Jacobi smoothing before and after the coarse-grid correction (Sec. 6.3:
+2 pre- and 4 post-smoothing iterations). The coarse grid keeps every other
+node on each axis (coarse node (i, j, k) = fine node (2i, 2j, 2k), Sec. 6.1);
+the atmosphere on a coarse grid is the fine one at those nodes.
+
+Prolongation P (Sec. 6.2): tri-linear -- a fine node that coincides with a
+coarse node takes its value, others interpolate linearly along each axis in
+which they fall between coarse nodes (periodic in x and y; linear in the
+height z). With an even number of fine planes the top fine plane lies above
+the coarse grid and takes the linear extrapolation of the two top coarse
+planes. Restriction R: the transpose of P normalized so that a constant is
+restricted to itself (the adjoint of the tri-linear prolongation over the 3^3
+fine nodes around a coarse node; fewer at the bottom and top).
+
+The operators are written as 1D matrices per axis (built node by node from the
+definition above) applied along each axis; the V-cycle calls the oracle's
+formal solution and statistical-equilibrium routines in the order above.
+"""
+import numpy as np
+
+from . import Problem, formal_solve, nl_of, see_apply, see_update_src
+
+
+def coarse_nz(nz):
+    return (nz + 1) // 2 if nz % 2 else nz // 2
+
+
+def prolong_1d_periodic(nf):
+    """nf x nf/2 matrix: even fine node -> its coarse node; odd -> mean of the two neighbours."""
+    assert nf % 2 == 0
+    nc = nf // 2
+    P = np.zeros((nf, nc))
+    for i in range(nf):
+        if i % 2 == 0:
+            P[i, i // 2] = 1.0
+        else:
+            P[i, (i - 1) // 2] += 0.5
+            P[i, ((i + 1) // 2) % nc] += 0.5
+    return P
+
+
+def prolong_1d_z(zf):
+    """nz x nz_c matrix of linear interpolation in the height z between coarse planes."""
+    nf = len(zf)
+    nc = coarse_nz(nf)
+    zc = zf[0:2 * nc:2]
+    P = np.zeros((nf, nc))
+    for k in range(nf):
+        if k % 2 == 0:
+            P[k, k // 2] = 1.0
+            continue
+        k0 = (k - 1) // 2
+        if k0 + 1 >= nc:            # above the top coarse plane: extrapolate from the top two
+            k0 = nc - 2
+        k1 = k0 + 1
+        t = (zf[k] - zc[k0]) / (zc[k1] - zc[k0])
+        P[k, k0] = 1.0 - t
+        P[k, k1] = t
+    return P
+
+
+class Level:
+    """One grid level: the problem, its atmosphere and the prolongation from the next coarser level."""
+
+    def __init__(self, atm, model, quad):
+        self.atm = atm
+        self.model = model
+        self.quad = quad
+        self.prob = Problem(atm, model, *quad)
+        self.shape = self.prob.shape
+
+
+def coarsen(atm):
+    """Coarse-grid atmosphere: every other node on each axis (injection)."""
+    nz, ny, nx = atm["nz"], atm["ny"], atm["nx"]
+    assert nx % 2 == 0 and ny % 2 == 0
+    ncz = coarse_nz(nz)
+    c = dict(atm)
+    c.update(nx=nx // 2, ny=ny // 2, nz=ncz, z=np.asarray(atm["z"])[0:2 * ncz:2])
+    for k in ("chi", "eps", "bpl", "vel", "bx", "by", "bz"):
+        if atm.get(k) is not None:
+            c[k] = np.ascontiguousarray(np.asarray(atm[k])[0:2 * ncz:2, 0::2, 0::2])
+    return c
+
+
+def hierarchy(atm, model, quad, nlevels):
+    """Levels from the finest (index 0) to the coarsest."""
+    levels = [Level(atm, model, quad)]
+    for _ in range(nlevels - 1):
+        levels.append(Level(coarsen(levels[-1].atm), model, quad))
+    return levels
+
+
+def _mats(fine):
+    a = fine.atm
+    return (prolong_1d_z(np.asarray(a["z"])), prolong_1d_periodic(a["ny"]), prolong_1d_periodic(a["nx"]))
+
+
+def prolong(fine, coarse_field):
+    """P applied to a coarse field (nzc, nyc, nxc, nl) -> fine field."""
+    Pz, Py, Px = _mats(fine)
+    return np.einsum("kK,jJ,iI,KJIc->kjic", Pz, Py, Px, coarse_field)
+
+
+def restrict(fine, fine_field):
+    """R = normalized transpose of P: fine field -> coarse field."""
+    Pz, Py, Px = _mats(fine)
+    num = np.einsum("kK,jJ,iI,kjic->KJIc", Pz, Py, Px, fine_field)
+    den = np.einsum("K,J,I->KJI", Pz.sum(0), Py.sum(0), Px.sum(0))
+    return num / den[..., None]
+
+
+def apply_A(level, rho):
+    """A(rho) on a level: formal solution for J, then the SEE operator."""
+    jkq, _ = formal_solve(level.prob, rho)
+    return see_apply(level.prob, jkq, rho)
+
+
+def f_fine(level):
+    """Right-hand side of the two-level problem: eps B delta_K0."""
+    nl = nl_of(level.model)
+    f = np.zeros(level.shape + (nl,))
+    f[..., 0] = np.asarray(level.atm["eps"]) * np.asarray(level.atm["bpl"])
+    return f
+
+
+def jacobi(level, rho, src, n):
+    mc = None
+    for _ in range(n):
+        jkq, ls = formal_solve(level.prob, rho)
+        rho, mc = see_update_src(level.prob, jkq, ls, rho, src)
+    return rho, mc
+
+
+def vcycle(levels, rho, src=None, l=0, npre=2, npost=4, ncoarse=8):
+    """One V-cycle from level l down to the coarsest; returns the new rho on level l.
+    src None on the finest level means f = eps B delta_K0."""
+    lev = levels[l]
+    f = f_fine(lev) if src is None else src
+    if l == len(levels) - 1:
+        rho, _ = jacobi(lev, rho, f, ncoarse)
+        return rho
+    rho, _ = jacobi(lev, rho, f, npre)
+    r = f - apply_A(lev, rho)
+    coarse = levels[l + 1]
+    rho_c0 = restrict(lev, rho)
+    f_c = apply_A(coarse, rho_c0) + restrict(lev, r)
+    rho_c = vcycle(levels, rho_c0, f_c, l + 1, npre, npost, ncoarse)
+    rho = rho + prolong(lev, rho_c - rho_c0)
+    rho, _ = jacobi(lev, rho, f, npost)
+    return rho

@@ -18,26 +18,22 @@
  * the K = 2 components explicitly from the current J^2_Q (5x5 Hanle solve).
  */
 #include <math.h>
+#include <stddef.h>
 #include "or_common.h"
 #include <complex.h>
 #undef I
 #define IU _Complex_I
 
-/* solve sum_Q' (delta_QQ' + i gamma K_QQ') S_Q' = rhs_Q for K = 2; rhs6 and s6 in the
-   real layout (X00, X20, Re X21, Im X21, Re X22, Im X22); entry 0 is ignored/zeroed */
-int or_hanle_solve(double gamma, double bx, double by, double bz, const double *rhs6, double *s6)
+/* M = 1 + i gamma K for K = 2 (rows and columns Q = -2..2) for the field (bx, by, bz) */
+static void hanle_matrix(double gamma, double bx, double by, double bz, double complex M[5][5])
 {
     const int K = 2;
     double b = sqrt(bx * bx + by * by + bz * bz);
     double ct = b > 0 ? bz / b : 1.0;
     double st = sqrt(fmax(0.0, 1.0 - ct * ct));
     double chib = (bx == 0.0 && by == 0.0) ? 0.0 : atan2(by, bx);
-    double complex M[5][5], r[5], x[5];
-    double complex rq[3] = {rhs6[1], rhs6[2] + IU * rhs6[3], rhs6[4] + IU * rhs6[5]};
     for (int a = 0; a < 5; a++) {
         int Q = a - 2;
-        /* rhs_{-Q} = (-1)^Q conj(rhs_Q) */
-        r[a] = Q >= 0 ? rq[Q] : ((Q % 2) ? -1.0 : 1.0) * conj(rq[-Q]);
         for (int c = 0; c < 5; c++) {
             int Qp = c - 2;
             double complex k = 0.0;
@@ -47,6 +43,26 @@ int or_hanle_solve(double gamma, double bx, double by, double bz, const double *
             M[a][c] = (a == c ? 1.0 : 0.0) + IU * gamma * k;
         }
     }
+}
+
+/* real layout (X00, X20, Re X21, Im X21, Re X22, Im X22) -> complex X_Q, Q = -2..2,
+   using X_{-Q} = (-1)^Q conj(X_Q) */
+static void to_complex(const double *r6, double complex x[5])
+{
+    double complex xq[3] = {r6[1], r6[2] + IU * r6[3], r6[4] + IU * r6[5]};
+    for (int a = 0; a < 5; a++) {
+        int Q = a - 2;
+        x[a] = Q >= 0 ? xq[Q] : ((Q % 2) ? -1.0 : 1.0) * conj(xq[-Q]);
+    }
+}
+
+/* solve sum_Q' (delta_QQ' + i gamma K_QQ') S_Q' = rhs_Q for K = 2; rhs6 and s6 in the
+   real layout (X00, X20, Re X21, Im X21, Re X22, Im X22); entry 0 is ignored/zeroed */
+int or_hanle_solve(double gamma, double bx, double by, double bz, const double *rhs6, double *s6)
+{
+    double complex M[5][5], r[5], x[5];
+    hanle_matrix(gamma, bx, by, bz, M);
+    to_complex(rhs6, r);
     /* complex Gaussian elimination with partial pivoting */
     for (int c = 0; c < 5; c++) {
         int piv = c;
@@ -74,15 +90,64 @@ int or_hanle_solve(double gamma, double bx, double by, double bz, const double *
     return 0;
 }
 
-int or_see_update(const or_problem *p, const double *jkq, const double *lstar, double *rho, double *max_change)
+/*
+ * The statistical-equilibrium operator of the two-level atom written as
+ * A(S) = f (Eq. 2 as L rho = f): per voxel
+ *   A(S)^0_0 = S^0_0 - (1-eps) J^0_0,
+ *   A(S)^2_Q = S^2_Q + i (1-eps) Gamma_u sum_Q' K_QQ' S^2_Q' - (1-eps) J^2_Q,
+ * with J = J[S] from the formal solution and f = eps B delta_K0 delta_Q0.
+ * out = A(S) (nvox * nl, the layout of rho).
+ */
+int or_see_apply(const or_problem *p, const double *jkq, const double *rho, double *out)
 {
     long nv = (long)p->nx * p->ny * p->nz;
+    for (long v = 0; v < nv; v++) {
+        double e = p->eps[v];
+        if (p->model == OR_MODEL_UNPOL) {
+            out[v] = rho[v] - (1.0 - e) * jkq[v];
+            continue;
+        }
+        const double *s = rho + 6 * v, *J = jkq + 6 * v;
+        double *o = out + 6 * v;
+        double bx = p->bx[v], by = p->by[v], bz = p->bz[v];
+        double gamma = (1.0 - e) * sqrt(bx * bx + by * by + bz * bz) / p->bcrit;
+        double complex M[5][5], x[5];
+        hanle_matrix(gamma, bx, by, bz, M);
+        to_complex(s, x);
+        double complex y[5];
+        for (int a = 0; a < 5; a++) {
+            y[a] = 0.0;
+            for (int c = 0; c < 5; c++) y[a] += M[a][c] * x[c];
+        }
+        o[0] = s[0] - (1.0 - e) * J[0];
+        o[1] = creal(y[2]) - (1.0 - e) * J[1];
+        o[2] = creal(y[3]) - (1.0 - e) * J[2];
+        o[3] = cimag(y[3]) - (1.0 - e) * J[3];
+        o[4] = creal(y[4]) - (1.0 - e) * J[4];
+        o[5] = cimag(y[4]) - (1.0 - e) * J[5];
+    }
+    return 0;
+}
+
+/*
+ * Jacobi (ALI) update of A(S) = src for a general per-voxel right-hand side src
+ * (nvox * nl, the layout of rho): the update of or_see_update with eps B
+ * replaced by src^0_0 and src^2_Q added to (1-eps) J^2_Q. src = NULL is the
+ * two-level problem itself (src = eps B delta_K0 delta_Q0). The coarse-grid
+ * problems of the multigrid method have this form (Sec. 6.1).
+ */
+int or_see_update_src(const or_problem *p, const double *jkq, const double *lstar, const double *src, double *rho,
+                      double *max_change)
+{
+    long nv = (long)p->nx * p->ny * p->nz;
+    int nl = or_nl(p->model);
     double mc = 0.0;
     for (long v = 0; v < nv; v++) {
-        double e = p->eps[v], B = p->bpl[v];
+        double e = p->eps[v];
+        double f0 = src ? src[v * nl] : e * p->bpl[v];
         if (p->model == OR_MODEL_UNPOL) {
             double S = rho[v];
-            double dS = ((1.0 - e) * jkq[v] + e * B - S) / (1.0 - (1.0 - e) * lstar[v]);
+            double dS = ((1.0 - e) * jkq[v] + f0 - S) / (1.0 - (1.0 - e) * lstar[v]);
             double ch = fabs(dS) / fabs(S);
             if (ch > mc || ch != ch) mc = ch;
             rho[v] = S + dS;
@@ -90,10 +155,10 @@ int or_see_update(const or_problem *p, const double *jkq, const double *lstar, d
             double *s = rho + 6 * v;
             const double *J = jkq + 6 * v;
             double S00 = s[0];
-            double dS = ((1.0 - e) * J[0] + e * B - S00) / (1.0 - (1.0 - e) * lstar[v]);
+            double dS = ((1.0 - e) * J[0] + f0 - S00) / (1.0 - (1.0 - e) * lstar[v]);
             double S00n = S00 + dS;
             double rhs[6], s2[6];
-            for (int c = 0; c < 6; c++) rhs[c] = (1.0 - e) * J[c];
+            for (int c = 0; c < 6; c++) rhs[c] = (1.0 - e) * J[c] + (src && c > 0 ? src[v * nl + c] : 0.0);
             double gamma = (1.0 - e) * sqrt(p->bx[v] * p->bx[v] + p->by[v] * p->by[v] + p->bz[v] * p->bz[v]) / p->bcrit;
             if (or_hanle_solve(gamma, p->bx[v], p->by[v], p->bz[v], rhs, s2) != 0) return -3;
             double ch = fabs(dS) / fabs(S00);
@@ -108,4 +173,9 @@ int or_see_update(const or_problem *p, const double *jkq, const double *lstar, d
     }
     if (max_change) *max_change = mc;
     return 0;
+}
+
+int or_see_update(const or_problem *p, const double *jkq, const double *lstar, double *rho, double *max_change)
+{
+    return or_see_update_src(p, jkq, lstar, NULL, rho, max_change);
 }

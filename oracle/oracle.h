@@ -75,6 +75,11 @@ int or_step(int ns, const double *IM, const double *etaM, const double *epsM,
 int or_hanle_solve(double gamma, double bx, double by, double bz, const double *rhs6, double *s6);
 int or_see_update(const or_problem *p, const double *jkq, const double *lstar,
                   double *rho, double *max_change);
+/* A(S) of the SEE written as A(S) = f (f = eps B delta_K0), and the Jacobi update of
+   A(S) = src for a general per-voxel src (NULL: the two-level problem itself) */
+int or_see_apply(const or_problem *p, const double *jkq, const double *rho, double *out);
+int or_see_update_src(const or_problem *p, const double *jkq, const double *lstar, const double *src,
+                      double *rho, double *max_change);
 
 /* ---- 3D short-characteristics formal solution ---- */
 /* one ray m, one frequency j, full grid: I (nvox*ns) and Lambda* (nvox) */

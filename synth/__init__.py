@@ -55,9 +55,10 @@ def random_field(rng, shape, slope=-11.0 / 3.0):
     return g / sd if sd > 0 else g
 
 
-def plane_parallel_box(nx=16, ny=16, nz=32, modulation=0.2, eps=1e-2, bpl=1.0, lx=L_KM, ly=L_KM):
+def plane_parallel_box(nx=16, ny=16, nz=32, modulation=0.2, eps=1e-2, bpl=1.0, lx=L_KM, ly=L_KM,
+                       tau_top=TAU_TOP, tau_bot=TAU_BOT):
     """Unpolarized two-level test box: chi(x,y,z) = chi(z) (1 + a sin(2 pi x/Lx) cos(2 pi y/Ly))."""
-    z = log_tau_heights(nz)
+    z = log_tau_heights(nz, tau_top=tau_top, tau_bot=tau_bot)
     x = np.arange(nx) * lx / nx
     y = np.arange(ny) * ly / ny
     mod = 1.0 + modulation * np.sin(2 * np.pi * x / lx)[None, None, :] * np.cos(2 * np.pi * y / ly)[None, :, None]
@@ -71,7 +72,7 @@ def plane_parallel_box(nx=16, ny=16, nz=32, modulation=0.2, eps=1e-2, bpl=1.0, l
 
 def random_box(nx=64, ny=64, nz=64, seed=0, eps=1e-3, sigma_lnb=0.3, sigma_lnchi=0.2,
                b_median=10.0, sigma_lnbfield=1.0, sigma_v=1.0, lx=L_KM, ly=L_KM,
-               zeta=3.5e-4, gbar=1.0, bcrit=25.0):
+               zeta=3.5e-4, gbar=1.0, bcrit=25.0, tau_top=TAU_TOP, tau_bot=TAU_BOT):
     """Polarized two-level random atmosphere (all fields seeded from SeedSequence(seed))."""
     shape = (nz, ny, nx)
     ss = np.random.SeedSequence(seed).spawn(5)
@@ -79,7 +80,7 @@ def random_box(nx=64, ny=64, nz=64, seed=0, eps=1e-3, sigma_lnb=0.3, sigma_lnchi
     g1 = random_field(r[0], shape)
     g2 = random_field(r[1], shape)
     g3 = random_field(r[2], shape)
-    z = log_tau_heights(nz)
+    z = log_tau_heights(nz, tau_top=tau_top, tau_bot=tau_bot)
     chi = exponential_opacity(z)[:, None, None] * np.exp(sigma_lnchi * g2)
     bpl = np.exp(sigma_lnb * g1)
     vel = sigma_v * g3
