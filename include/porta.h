@@ -311,6 +311,35 @@ int porta_adjoint_timing(const porta_ctx *c, float *forward_ms, float *adjoint_m
 /* Launch statistics of the last adjoint sweep (as porta_launch_info). */
 int porta_adjoint_info(const porta_ctx *c, int *clusters, int *cluster_size, int *nu_group, int *smem_bytes);
 
+/* Non-linear multigrid (Sec. 6, full-approximation form). porta_mg_setup
+   builds nlevels - 1 coarser grids by keeping every other node on each axis
+   (coarse (i, j, k) = fine (2i, 2j, 2k); nz -> (nz + 1)/2 for odd nz, nz/2
+   for even nz), each a context of its own with the same atom, quadratures
+   and precision and the atmosphere sampled at its nodes. nx and ny must be
+   divisible by 2^(nlevels - 1) (PORTA_EINVAL otherwise); requires the
+   atmosphere (PORTA_ESTATE); call it again after porta_set_atmosphere. The
+   method needs the coarse grids to resolve the transfer problem (about one
+   plane per decade of optical depth or more, Sec. 6.3). */
+int porta_mg_setup(porta_ctx *c, int nlevels);
+
+/* Levels built by porta_mg_setup: *nlevels (0 before setup) and, if shapes is
+   not NULL, shapes[3 l + 0..2] = nx, ny, nz of level l, finest first. */
+int porta_mg_levels(const porta_ctx *c, int *nlevels, int *shapes);
+
+/* One V-cycle (Eqs. 14-18) from the finest level: npre Jacobi iterations;
+   residual r = f - A(rho), A the statistical-equilibrium operator (J^K_Q from
+   a formal solution) and f = eps B delta_K0; restriction of rho and r; coarse
+   right-hand side A_c(R rho) + R r; the same cycle on the coarser level
+   (ncoarse Jacobi iterations on the coarsest); correction rho += P (rho_c -
+   R rho); npost Jacobi iterations (Sec. 6.3 uses npre = 2, npost = 4).
+   Prolongation P: tri-linear, linear in height, linear extrapolation above
+   the top coarse plane (even nz); restriction R: the transpose of P normalized
+   to keep constants (adjoint of the tri-linear prolongation, Sec. 6.2).
+   max_change (host, may be NULL): the maximum relative change of rho over the
+   cycle, defined as for porta_see_update (synchronizes). All work is
+   enqueued on the context's stream. */
+int porta_mg_vcycle(porta_ctx *c, int npre, int npost, int ncoarse, double *max_change);
+
 #ifdef __cplusplus
 }
 #endif

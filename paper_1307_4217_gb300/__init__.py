@@ -16,5 +16,5 @@ from .binding import (  # noqa: F401
     porta_see_update, porta_emergent_stokes, porta_probe_ray, porta_launch_info, porta_autotune, porta_eval_coefficients,
     porta_formal_solve_noalloc, porta_run_iterations, PORTA_ESCRATCH, PORTA_NOALLOC_SCRATCH_BYTES,
     porta_emergent_vjp, porta_set_adjoint_launch, porta_adjoint_info, porta_adjoint_timing,
-    porta_fill_info, porta_set_fill,
+    porta_fill_info, porta_set_fill, porta_mg_setup, porta_mg_levels, porta_mg_vcycle,
 )

@@ -77,6 +77,9 @@ _SIGS = {
     "porta_adjoint_timing": (_I, [_P, _P, _P]),
     "porta_fill_info": (_I, [_P, _P, _P, _P]),
     "porta_set_fill": (_I, [_P, _I, _I, _D]),
+    "porta_mg_setup": (_I, [_P, _I]),
+    "porta_mg_levels": (_I, [_P, _P, _P]),
+    "porta_mg_vcycle": (_I, [_P, _I, _I, _I, _P]),
 }
 
 _lib = None
@@ -275,6 +278,21 @@ def porta_set_fill(h, cluster, nu_group, fraction):
     return lib().porta_set_fill(h, cluster, nu_group, float(fraction))
 
 
+def porta_mg_setup(h, nlevels):
+    return lib().porta_mg_setup(h, nlevels)
+
+
+def porta_mg_levels(h):
+    n = ctypes.c_int()
+    shapes = (ctypes.c_int * 24)()
+    rc = lib().porta_mg_levels(h, ctypes.byref(n), shapes)
+    return rc, [tuple(shapes[3 * l:3 * l + 3]) for l in range(n.value)]
+
+
+def porta_mg_vcycle(h, npre, npost, ncoarse, out=None):
+    return lib().porta_mg_vcycle(h, npre, npost, ncoarse, ctypes.byref(out) if out is not None else None)
+
+
 # ---- convenience wrapper ------------------------------------------------------------
 
 class Context:
@@ -445,6 +463,20 @@ class Context:
         rc, info = porta_launch_info(self.h)
         self._check(rc)
         return info
+
+    def mg_setup(self, nlevels):
+        self._check(porta_mg_setup(self.h, nlevels))
+
+    def mg_levels(self):
+        rc, shapes = porta_mg_levels(self.h)
+        self._check(rc)
+        return shapes
+
+    def mg_vcycle(self, npre=2, npost=4, ncoarse=8, residual=True):
+        """One multigrid V-cycle; returns the maximum relative change of rho (or None)."""
+        out = ctypes.c_double() if residual else None
+        self._check(porta_mg_vcycle(self.h, npre, npost, ncoarse, out))
+        return out.value if residual else None
 
     def set_fill(self, cluster=0, nu_group=0, fraction=0.0):
         self._check(porta_set_fill(self.h, cluster, nu_group, fraction))

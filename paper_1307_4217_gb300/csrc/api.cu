@@ -14,6 +14,7 @@
 #include "porta.h"
 #include "porta_ctx.h"
 #include "porta_internal.cuh"
+#include "mg_kernels.cuh"
 #include "see_kernels.cuh"
 
 using namespace porta;
@@ -844,9 +845,13 @@ int emergent_vjp_t(porta_ctx *c, int ndir, const double *mu, const double *chi, 
     return rc;
 }
 
+void mg_free(porta_ctx *c);
+
 void free_all(porta_ctx *c)
 {
     drop_graph(c);
+    mg_free(c);
+    if (c->d_cv64) cudaFree(c->d_cv64);
     if (c->fill) {
         if (c->fill->stream) cudaStreamDestroy(c->fill->stream);
         if (c->fill->fork) cudaEventDestroy(c->fill->fork);
@@ -888,6 +893,124 @@ int count_bad(porta_ctx *c, const double *d, long long n, double lo, double hi, 
     CK(cudaMemcpyAsync(out, c->d_resid, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     return PORTA_OK;
+}
+
+
+// ---------------------------------------------------------------- multigrid (Sec. 6)
+
+int coarse_nz(int nz) { return nz % 2 ? (nz + 1) / 2 : nz / 2; }
+
+void mg_free(porta_ctx *c)
+{
+    for (porta_ctx *L : c->mg) porta_destroy(L);
+    c->mg.clear();
+    double *bufs[] = {c->mg_res, c->mg_src, c->mg_rho0, c->mg_prev, c->mg_zr, c->mg_zp};
+    for (double *b : bufs)
+        if (b) cudaFree(b);
+    c->mg_res = c->mg_src = c->mg_rho0 = c->mg_prev = c->mg_zr = c->mg_zp = nullptr;
+}
+
+// z tables between a level with heights zf and the next coarser one (coarse
+// plane i = fine plane 2i): per fine plane (k0, w0, k1, w1) of the linear
+// interpolation in height (extrapolation from the top two coarse planes above
+// the coarse grid), and per coarse plane up to 4 (fine plane, weight) pairs of
+// the transposed interpolation
+void mg_ztables(const std::vector<double> &zf, std::vector<double> &zr, std::vector<double> &zp)
+{
+    const int nf = (int)zf.size(), nc = coarse_nz(nf);
+    zp.assign(4 * (size_t)nf, 0.0);
+    for (int k = 0; k < nf; ++k) {
+        if (k % 2 == 0) {
+            zp[4 * k] = zp[4 * k + 2] = k / 2;
+            zp[4 * k + 1] = 1.0;
+            continue;
+        }
+        int k0 = (k - 1) / 2;
+        if (k0 + 1 >= nc) k0 = nc - 2;
+        const int k1 = k0 + 1;
+        const double t = (zf[k] - zf[2 * k0]) / (zf[2 * k1] - zf[2 * k0]);
+        zp[4 * k] = k0;
+        zp[4 * k + 1] = 1.0 - t;
+        zp[4 * k + 2] = k1;
+        zp[4 * k + 3] = t;
+    }
+    zr.assign(8 * (size_t)nc, 0.0);
+    std::vector<int> used(nc, 0);
+    for (int k = 0; k < nf; ++k)
+        for (int e = 0; e < 2; ++e) {
+            const double w = zp[4 * k + 2 * e + 1];
+            if (w == 0.0) continue;
+            const int K = (int)zp[4 * k + 2 * e];
+            zr[8 * K + 2 * used[K]] = k;
+            zr[8 * K + 2 * used[K] + 1] = w;
+            ++used[K];
+        }
+}
+
+// formal solution and J^K_Q / Lambda-bar* of one level, kept on the device
+int mg_fs(porta_ctx *L)
+{
+    int rc = porta_formal_solve(L);
+    if (rc == PORTA_OK) rc = porta_accumulate_jkq(L, nullptr, nullptr, PORTA_DEVICE);
+    return rc;
+}
+
+// n Jacobi iterations of A(S) = src on one level (src null: eps B delta_K0)
+int mg_jacobi(porta_ctx *L, const double *src, int n)
+{
+    for (int it = 0; it < n; ++it) {
+        int rc = mg_fs(L);
+        if (rc) return rc;
+        cudaError_t e = L->precision == PORTA_FP32
+                            ? run_see<float>(L->nvox, L->nl, L->model, L->bcrit, L->d_eps, L->d_bpl, L->d_b, L->d_jkq,
+                                             L->d_lstar, L->d_rho, L->d_rhoR, L->d_resid, L->stream, src)
+                            : run_see<double>(L->nvox, L->nl, L->model, L->bcrit, L->d_eps, L->d_bpl, L->d_b, L->d_jkq,
+                                              L->d_lstar, L->d_rho, L->d_rhoR, L->d_resid, L->stream, src);
+        if (e != cudaSuccess) return fail(L, PORTA_ECUDA, std::string("mg jacobi: ") + cudaGetErrorString(e));
+        L->have_fs = L->have_jkq = false;
+    }
+    return PORTA_OK;
+}
+
+cudaError_t mg_rho_changed(porta_ctx *L)
+{
+    return L->precision == PORTA_FP32 ? run_rho_convert<float>(L->nvox, L->nl, L->d_rho, L->d_rhoR, L->stream)
+                                      : run_rho_convert<double>(L->nvox, L->nl, L->d_rho, L->d_rhoR, L->stream);
+}
+
+// One V-cycle (Eqs. 14-18) from level l of levels[0..n) down to the coarsest.
+int mg_vcycle(porta_ctx *const *levels, int n, int l, int npre, int npost, int ncoarse)
+{
+    porta_ctx *L = levels[l];
+    const double *src = l == 0 ? nullptr : L->mg_src;
+    if (l == n - 1) return mg_jacobi(L, src, ncoarse);
+    int rc = mg_jacobi(L, src, npre);
+    if (rc) return rc;
+    // residual r = f - A(rho)
+    if ((rc = mg_fs(L))) return rc;
+    cudaError_t e = run_see_apply(L->nvox, L->nl, L->model, L->bcrit, L->d_eps, L->d_bpl, L->d_b, L->d_jkq, L->d_rho,
+                                  -1.0, src, src ? 0 : 1, L->mg_res, L->stream);
+    porta_ctx *C = levels[l + 1];
+    // coarse unknowns R rho, coarse right-hand side A_c(R rho) + R r
+    if (e == cudaSuccess)
+        e = run_restrict(C->nx, C->ny, C->nz, L->nx, L->ny, L->nl, L->mg_zr, L->d_rho, C->mg_rho0, L->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(C->d_rho, C->mg_rho0, sizeof(double) * C->nvox * C->nl, cudaMemcpyDeviceToDevice, L->stream);
+    if (e == cudaSuccess) e = mg_rho_changed(C);
+    if (e == cudaSuccess)
+        e = run_restrict(C->nx, C->ny, C->nz, L->nx, L->ny, L->nl, L->mg_zr, L->mg_res, C->mg_src, L->stream);
+    if (e != cudaSuccess) return fail(L, PORTA_ECUDA, std::string("mg restrict: ") + cudaGetErrorString(e));
+    C->have_rho = true;
+    if ((rc = mg_fs(C))) return fail(L, rc, std::string("mg coarse level: ") + C->err);
+    e = run_see_apply(C->nvox, C->nl, C->model, C->bcrit, C->d_eps, C->d_bpl, C->d_b, C->d_jkq, C->d_rho, 1.0,
+                      C->mg_src, 0, C->mg_src, C->stream);
+    if (e != cudaSuccess) return fail(L, PORTA_ECUDA, std::string("mg coarse rhs: ") + cudaGetErrorString(e));
+    if ((rc = mg_vcycle(levels, n, l + 1, npre, npost, ncoarse))) return fail(L, rc, C->err);
+    // coarse-grid correction rho += P (rho_c - R rho)
+    e = run_prolong_add(L->nx, L->ny, L->nz, C->nx, C->ny, L->nl, L->mg_zp, C->d_rho, C->mg_rho0, L->d_rho, L->stream);
+    if (e == cudaSuccess) e = mg_rho_changed(L);
+    if (e != cudaSuccess) return fail(L, PORTA_ECUDA, std::string("mg prolong: ") + cudaGetErrorString(e));
+    return mg_jacobi(L, src, npost);
 }
 
 }  // namespace
@@ -1145,9 +1268,9 @@ int porta_set_atmosphere(porta_ctx *c, const porta_atmos *a, int where)
     if (pol && (!a->bx || !a->by || !a->bz)) return fail(c, PORTA_EINVAL, "atmosphere: magnetic field required");
     if (where != PORTA_HOST && where != PORTA_DEVICE) return fail(c, PORTA_EINVAL, "atmosphere: bad `where`");
     const long long n = c->nvox;
-    // stage FP64 copies on the device: eps, bpl, field (kept), chi and vel (temporary)
-    double *tmp = nullptr;
-    CK(dalloc(&tmp, 2 * n));
+    // stage FP64 copies on the device: eps, bpl, field, chi and vel (all kept)
+    if (!c->d_cv64) CK(dalloc(&c->d_cv64, 2 * n));
+    double *tmp = c->d_cv64;
     int rc = PORTA_OK;
     do {
         if ((rc = copy_in(c, tmp, a->chi, n, where))) break;
@@ -1208,7 +1331,6 @@ int porta_set_atmosphere(porta_ctx *c, const porta_atmos *a, int where)
         if (e != cudaSuccess) { rc = fail(c, PORTA_ECUDA, cudaGetErrorString(e)); break; }
     } while (0);
     cudaStreamSynchronize(c->stream);
-    cudaFree(tmp);
     if (rc == PORTA_OK) {
         c->have_atm = true;
         c->have_fs = c->have_jkq = false;
@@ -1584,6 +1706,152 @@ int porta_launch_info(const porta_ctx *c, int *clusters, int *cluster_size, int 
     if (cluster_size) *cluster_size = c->last.cluster;
     if (nu_group) *nu_group = c->last.F;
     if (smem_bytes) *smem_bytes = c->last.smem;
+    return PORTA_OK;
+}
+
+
+int porta_mg_setup(porta_ctx *c, int nlevels)
+{
+    if (!c) return PORTA_EINVAL;
+    if (c->nbox != 1) return fail(c, PORTA_EINVAL, "mg_setup: single-box contexts only");
+    if (nlevels < 2 || nlevels > 8) return fail(c, PORTA_EINVAL, "mg_setup: nlevels in 2..8");
+    if (!c->have_atm) return fail(c, PORTA_ESTATE, "mg_setup: atmosphere not set");
+    {
+        int nx = c->nx, ny = c->ny, nz = c->nz;
+        for (int l = 1; l < nlevels; ++l) {
+            if (nx % 2 || ny % 2)
+                return fail(c, PORTA_EINVAL, "mg_setup: nx and ny must be divisible by 2^(nlevels-1)");
+            nx /= 2;
+            ny /= 2;
+            nz = coarse_nz(nz);
+            if (nz < 2) return fail(c, PORTA_EINVAL, "mg_setup: too many levels for nz");
+        }
+    }
+    mg_free(c);
+    porta_ctx *F = c;
+    int rc = PORTA_OK;
+    for (int l = 1; l < nlevels && rc == PORTA_OK; ++l) {
+        const int nzc = coarse_nz(F->nz);
+        std::vector<double> zc(nzc);
+        for (int k = 0; k < nzc; ++k) zc[k] = F->z[2 * k];
+        porta_grid g{};
+        g.nx = F->nx / 2;
+        g.ny = F->ny / 2;
+        g.nz = nzc;
+        g.lx = c->lx;
+        g.ly = c->ly;
+        g.z = zc.data();
+        porta_atom a{};
+        a.model = c->model;
+        a.zeta = c->zeta;
+        a.gbar = c->gbar;
+        a.bcrit = c->bcrit;
+        porta_quad q{};
+        q.n_mu = c->n_mu;
+        q.n_chi = c->n_chi;
+        q.n_nu = c->n_nu;
+        q.x_max = c->x_max;
+        porta_opts o{};
+        o.precision = c->precision;
+        porta_ctx *L = nullptr;
+        if ((rc = porta_create(&g, &a, &q, &o, &L))) {
+            rc = fail(c, rc, "mg_setup: coarse level creation");
+            break;
+        }
+        c->mg.push_back(L);
+        porta_set_stream(L, c->stream);
+        // coarse atmosphere: the finer level's values at the coincident nodes
+        const long long nf = F->nvox, ncv = L->nvox;
+        double *tmp = nullptr;
+        cudaError_t e = dalloc(&tmp, 7 * (size_t)ncv);
+        const double *src[7] = {F->d_cv64, F->d_eps, F->d_bpl, F->d_cv64 + nf, F->d_b, F->d_b + nf, F->d_b + 2 * nf};
+        for (int f = 0; f < 7 && e == cudaSuccess; ++f)
+            e = run_inject(L->nx, L->ny, L->nz, F->nx, F->ny, src[f], tmp + f * ncv, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) {
+            cudaFree(tmp);
+            rc = fail(c, PORTA_ECUDA, std::string("mg_setup: ") + cudaGetErrorString(e));
+            break;
+        }
+        porta_atmos at{};
+        at.chi = tmp;
+        at.eps = tmp + ncv;
+        at.bpl = tmp + 2 * ncv;
+        at.vel = tmp + 3 * ncv;
+        at.bx = tmp + 4 * ncv;
+        at.by = tmp + 5 * ncv;
+        at.bz = tmp + 6 * ncv;
+        rc = porta_set_atmosphere(L, &at, PORTA_DEVICE);
+        cudaFree(tmp);
+        if (rc) {
+            rc = fail(c, rc, std::string("mg_setup: coarse atmosphere: ") + L->err);
+            break;
+        }
+        std::vector<double> zr, zp;
+        mg_ztables(F->z, zr, zp);
+        e = dalloc(&L->mg_src, (size_t)ncv * c->nl);
+        if (e == cudaSuccess) e = dalloc(&L->mg_rho0, (size_t)ncv * c->nl);
+        if (e == cudaSuccess) e = dalloc(&L->mg_res, (size_t)ncv * c->nl);
+        if (e == cudaSuccess) e = dalloc(&F->mg_zr, zr.size());
+        if (e == cudaSuccess) e = dalloc(&F->mg_zp, zp.size());
+        if (e == cudaSuccess) e = cudaMemcpy(F->mg_zr, zr.data(), zr.size() * sizeof(double), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(F->mg_zp, zp.data(), zp.size() * sizeof(double), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            rc = fail(c, PORTA_ENOMEM, "mg_setup: allocation");
+            break;
+        }
+        F = L;
+    }
+    if (rc == PORTA_OK) {
+        cudaError_t e = dalloc(&c->mg_res, (size_t)c->nvox * c->nl);
+        if (e == cudaSuccess) e = dalloc(&c->mg_prev, (size_t)c->nvox * c->nl);
+        if (e != cudaSuccess) rc = fail(c, PORTA_ENOMEM, "mg_setup: allocation");
+    }
+    if (rc) mg_free(c);
+    return rc;
+}
+
+int porta_mg_levels(const porta_ctx *c, int *nlevels, int *shapes)
+{
+    if (!c) return PORTA_EINVAL;
+    if (nlevels) *nlevels = c->mg.empty() ? 0 : 1 + (int)c->mg.size();
+    if (shapes && !c->mg.empty()) {
+        shapes[0] = c->nx;
+        shapes[1] = c->ny;
+        shapes[2] = c->nz;
+        for (size_t l = 0; l < c->mg.size(); ++l) {
+            shapes[3 * (l + 1)] = c->mg[l]->nx;
+            shapes[3 * (l + 1) + 1] = c->mg[l]->ny;
+            shapes[3 * (l + 1) + 2] = c->mg[l]->nz;
+        }
+    }
+    return PORTA_OK;
+}
+
+int porta_mg_vcycle(porta_ctx *c, int npre, int npost, int ncoarse, double *max_change)
+{
+    if (!c) return PORTA_EINVAL;
+    if (c->mg.empty()) return fail(c, PORTA_ESTATE, "mg_vcycle: call porta_mg_setup first");
+    if (!c->have_atm || !c->have_rho) return fail(c, PORTA_ESTATE, "mg_vcycle: atmosphere or rho not set");
+    if (npre < 0 || npost < 0 || ncoarse < 1) return fail(c, PORTA_EINVAL, "mg_vcycle: npre, npost >= 0, ncoarse >= 1");
+    std::vector<porta_ctx *> levels{c};
+    for (porta_ctx *L : c->mg) {
+        L->stream = c->stream;
+        levels.push_back(L);
+    }
+    CK(cudaMemcpyAsync(c->mg_prev, c->d_rho, sizeof(double) * c->nvox * c->nl, cudaMemcpyDeviceToDevice, c->stream));
+    int rc = mg_vcycle(levels.data(), (int)levels.size(), 0, npre, npost, ncoarse);
+    if (rc) return rc;
+    c->have_fs = c->have_jkq = false;
+    CK(cudaMemsetAsync(c->d_resid, 0, sizeof(unsigned long long), c->stream));
+    cudaError_t e = run_change(c->nvox, c->nl, c->mg_prev, c->d_rho, c->d_resid, c->stream);
+    if (e != cudaSuccess) return fail(c, PORTA_ECUDA, std::string("mg_vcycle: ") + cudaGetErrorString(e));
+    if (max_change) {
+        unsigned long long bits = 0;
+        CK(cudaMemcpyAsync(&bits, c->d_resid, sizeof(bits), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        std::memcpy(max_change, &bits, sizeof(double));
+    }
     return PORTA_OK;
 }
 

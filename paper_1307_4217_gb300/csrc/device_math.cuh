@@ -190,4 +190,15 @@ __device__ __forceinline__ void hanle_solve5(double gx, double gy, double gz, co
     }
 }
 
+// y = M x with M the real matrix of hanle_solve5 (same unknowns and equations)
+__device__ __forceinline__ void hanle_apply5(double gx, double gy, double gz, const double x[5], double y[5])
+{
+    const double s6 = 2.449489742783178098197284;  // sqrt(6)
+    y[0] = x[0] + s6 * gy * x[1] - s6 * gx * x[2];
+    y[1] = -0.5 * s6 * gy * x[0] + x[1] - gz * x[2] + gy * x[3] - gx * x[4];
+    y[2] = 0.5 * s6 * gx * x[0] + gz * x[1] + x[2] + gx * x[3] + gy * x[4];
+    y[3] = -gy * x[1] - gx * x[2] + x[3] - 2.0 * gz * x[4];
+    y[4] = gx * x[1] - gy * x[2] + 2.0 * gz * x[3] + x[4];
+}
+
 }  // namespace porta

@@ -1,0 +1,166 @@
+// Grid transfer of the non-linear multigrid method (Sec. 6): the coarse grid
+// keeps every other node on each axis (coarse (i, j, k) = fine (2i, 2j, 2k),
+// Sec. 6.1). Prolongation is tri-linear (Sec. 6.2): a fine node on a coarse
+// node takes its value, others interpolate along each axis where they fall
+// between coarse nodes (periodic in x and y, linear in the height z; above the
+// top coarse plane -- an even number of fine planes -- linear extrapolation
+// from the top two). Restriction is the transpose of the prolongation
+// normalized so that constants are kept: the adjoint of the tri-linear
+// prolongation over the 3 x 3 x (up to 4) fine nodes around a coarse node.
+// The z weights come as tables built on the host: per fine plane (k0, w0, k1,
+// w1) for the prolongation, per coarse plane up to 4 (fine plane, weight)
+// pairs for the restriction. Vectors of unknowns are [voxel][nl], FP64.
+#include "mg_kernels.cuh"
+
+namespace porta {
+
+namespace {
+
+inline int nblk(long long n, int t) { return (int)((n + t - 1) / t); }
+
+// coarse[v_c] = fine[v_f] at the coincident node, one per-voxel array
+__global__ void inject_kernel(int nxc, int nyc, long long nvc, int nxf, int nyf, const double *fine, double *coarse)
+{
+    long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (v >= nvc) return;
+    const int i = (int)(v % nxc);
+    const int j = (int)((v / nxc) % nyc);
+    const long long k = v / ((long long)nxc * nyc);
+    coarse[v] = fine[((2 * k) * nyf + 2 * j) * (long long)nxf + 2 * i];
+}
+
+__global__ void restrict_kernel(int nxc, int nyc, long long nvc, int nxf, int nyf, int nl, const double *zr,
+                                const double *fine, double *coarse)
+{
+    long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (v >= nvc) return;
+    const int I = (int)(v % nxc);
+    const int J = (int)((v / nxc) % nyc);
+    const int K = (int)(v / ((long long)nxc * nyc));
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    double den = 0.0;
+    for (int e = 0; e < 4; ++e) {
+        const double w = zr[8 * K + 2 * e + 1];
+        if (w == 0.0) continue;
+        const long long kf = (long long)zr[8 * K + 2 * e];
+        den += w;
+        for (int dy = -1; dy <= 1; ++dy) {
+            const double wy = dy == 0 ? 1.0 : 0.5;
+            const int jf = (2 * J + dy + nyf) % nyf;
+            for (int dx = -1; dx <= 1; ++dx) {
+                const double wx = dx == 0 ? 1.0 : 0.5;
+                const int xf = (2 * I + dx + nxf) % nxf;
+                const double *p = fine + ((kf * nyf + jf) * nxf + xf) * nl;
+                const double wt = w * wy * wx;
+                for (int c = 0; c < nl; ++c) acc[c] += wt * p[c];
+            }
+        }
+    }
+    // the horizontal weights sum to 2 per axis
+    const double inv = 1.0 / (4.0 * den);
+    for (int c = 0; c < nl; ++c) coarse[v * nl + c] = acc[c] * inv;
+}
+
+__global__ void prolong_add_kernel(int nxf, int nyf, long long nvf, int nxc, int nyc, int nl, const double *zp,
+                                   const double *cnew, const double *cold, double *fine)
+{
+    long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (v >= nvf) return;
+    const int i = (int)(v % nxf);
+    const int j = (int)((v / nxf) % nyf);
+    const int k = (int)(v / ((long long)nxf * nyf));
+    int xi[2], yj[2];
+    double wx[2], wy[2];
+    if (i % 2 == 0) {
+        xi[0] = xi[1] = i / 2;
+        wx[0] = 1.0;
+        wx[1] = 0.0;
+    } else {
+        xi[0] = (i - 1) / 2;
+        xi[1] = ((i + 1) / 2) % nxc;
+        wx[0] = wx[1] = 0.5;
+    }
+    if (j % 2 == 0) {
+        yj[0] = yj[1] = j / 2;
+        wy[0] = 1.0;
+        wy[1] = 0.0;
+    } else {
+        yj[0] = (j - 1) / 2;
+        yj[1] = ((j + 1) / 2) % nyc;
+        wy[0] = wy[1] = 0.5;
+    }
+    const long long kz[2] = {(long long)zp[4 * k], (long long)zp[4 * k + 2]};
+    const double wz[2] = {zp[4 * k + 1], zp[4 * k + 3]};
+    double d[6] = {0, 0, 0, 0, 0, 0};
+    for (int a = 0; a < 2; ++a) {
+        if (wz[a] == 0.0) continue;
+        for (int b = 0; b < 2; ++b) {
+            if (wy[b] == 0.0) continue;
+            for (int cx = 0; cx < 2; ++cx) {
+                if (wx[cx] == 0.0) continue;
+                const long long vc = (kz[a] * nyc + yj[b]) * nxc + xi[cx];
+                const double w = wz[a] * wy[b] * wx[cx];
+                for (int c = 0; c < nl; ++c) d[c] += w * (cnew[vc * nl + c] - cold[vc * nl + c]);
+            }
+        }
+    }
+    for (int c = 0; c < nl; ++c) fine[v * nl + c] += d[c];
+}
+
+// max over voxels of |dS00| / |S00_old| and |S2/S00 (new) - S2/S00 (old)|
+// (the residual of the Jacobi update), as the IEEE bits of a non-negative double
+__global__ void change_kernel(long long nvox, int nl, const double *old, const double *cur, unsigned long long *resid)
+{
+    long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    double ch = 0.0;
+    if (v < nvox) {
+        const double *o = old + v * nl, *n = cur + v * nl;
+        ch = fabs(n[0] - o[0]) / fabs(o[0]);
+        for (int c = 1; c < nl; ++c) ch = fmax(ch, fabs(n[c] / n[0] - o[c] / o[0]));
+    }
+    if (!(ch <= 1e300)) ch = 1e300;
+    for (int s = 16; s > 0; s >>= 1) ch = fmax(ch, __shfl_xor_sync(0xffffffffu, ch, s));
+    __shared__ double red[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) red[wid] = ch;
+    __syncthreads();
+    if (wid == 0) {
+        ch = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
+        for (int s = 16; s > 0; s >>= 1) ch = fmax(ch, __shfl_xor_sync(0xffffffffu, ch, s));
+        if (lane == 0) atomicMax(resid, (unsigned long long)__double_as_longlong(ch));
+    }
+}
+
+}  // namespace
+
+cudaError_t run_inject(int nxc, int nyc, int nzc, int nxf, int nyf, const double *fine, double *coarse, cudaStream_t st)
+{
+    const long long n = (long long)nxc * nyc * nzc;
+    inject_kernel<<<nblk(n, 256), 256, 0, st>>>(nxc, nyc, n, nxf, nyf, fine, coarse);
+    return cudaGetLastError();
+}
+
+cudaError_t run_restrict(int nxc, int nyc, int nzc, int nxf, int nyf, int nl, const double *zr, const double *fine,
+                         double *coarse, cudaStream_t st)
+{
+    const long long n = (long long)nxc * nyc * nzc;
+    restrict_kernel<<<nblk(n, 256), 256, 0, st>>>(nxc, nyc, n, nxf, nyf, nl, zr, fine, coarse);
+    return cudaGetLastError();
+}
+
+cudaError_t run_prolong_add(int nxf, int nyf, int nzf, int nxc, int nyc, int nl, const double *zp, const double *cnew,
+                            const double *cold, double *fine, cudaStream_t st)
+{
+    const long long n = (long long)nxf * nyf * nzf;
+    prolong_add_kernel<<<nblk(n, 256), 256, 0, st>>>(nxf, nyf, n, nxc, nyc, nl, zp, cnew, cold, fine);
+    return cudaGetLastError();
+}
+
+cudaError_t run_change(long long nvox, int nl, const double *old, const double *cur, unsigned long long *resid,
+                       cudaStream_t st)
+{
+    change_kernel<<<nblk(nvox, 256), 256, 0, st>>>(nvox, nl, old, cur, resid);
+    return cudaGetLastError();
+}
+
+}  // namespace porta

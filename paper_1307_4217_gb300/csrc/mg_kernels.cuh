@@ -1,0 +1,19 @@
+// Launchers of the multigrid grid-transfer kernels (mg.cu); internal to the library.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace porta {
+
+// coarse = fine at the coincident nodes, one per-voxel array
+cudaError_t run_inject(int nxc, int nyc, int nzc, int nxf, int nyf, const double *fine, double *coarse, cudaStream_t st);
+// restriction [v][nl] fine -> coarse; zr: per coarse plane 4 x (fine plane, weight)
+cudaError_t run_restrict(int nxc, int nyc, int nzc, int nxf, int nyf, int nl, const double *zr, const double *fine,
+                         double *coarse, cudaStream_t st);
+// fine += P (cnew - cold); zp: per fine plane (k0, w0, k1, w1)
+cudaError_t run_prolong_add(int nxf, int nyf, int nzf, int nxc, int nyc, int nl, const double *zp, const double *cnew,
+                            const double *cold, double *fine, cudaStream_t st);
+// max relative change between two vectors of unknowns (atomic max on the IEEE bits in *resid)
+cudaError_t run_change(long long nvox, int nl, const double *old, const double *cur, unsigned long long *resid,
+                       cudaStream_t st);
+
+}  // namespace porta

@@ -38,6 +38,7 @@ struct porta_ctx {
     // device memory
     size_t rsz = 4;                 // sizeof(Real) of the sweep
     void *d_atm = nullptr;          // Real SoA: chi, vel, bx, by, bz, bpl
+    double *d_cv64 = nullptr;       // FP64 chi and vel (2*nvox), kept for the multigrid's coarse atmospheres
     double *d_eps = nullptr;        // FP64 per-voxel eps, bpl, B (SEE)
     double *d_bpl = nullptr;
     double *d_b = nullptr;          // 3*nvox
@@ -73,6 +74,15 @@ struct porta_ctx {
     porta::LaunchCfg fill_cfg{};
     double fill_frac = 0.0;
     LaunchFill *fill = nullptr;
+    // non-linear multigrid (porta_mg_setup): coarse levels, finer first (each a
+    // context of its own), and work buffers [voxel][nl] FP64
+    std::vector<porta_ctx *> mg;
+    double *mg_res = nullptr;       // residual of this level
+    double *mg_src = nullptr;       // right-hand side of this level's problem (coarse levels)
+    double *mg_rho0 = nullptr;      // restriction of the finer level's unknowns (coarse levels)
+    double *mg_prev = nullptr;      // unknowns at the start of a V-cycle (finest level)
+    double *mg_zr = nullptr;        // to the next coarser level: per coarse plane 4 x (fine plane, weight)
+    double *mg_zp = nullptr;        // from the next coarser level: per fine plane (k0, w0, k1, w1)
     // reverse mode of the emergent sweep: tape of the forward Stokes vectors,
     // per-item partial gradients, forced launch shape (0 = automatic), last launch
     void *d_tape = nullptr;

@@ -102,15 +102,17 @@ __device__ __forceinline__ void atomic_max_nonneg(unsigned long long *addr, doub
 template <typename Real>
 __global__ void see_kernel(long long nvox, int nl, int model, double bcrit, const double *eps, const double *bpl,
                            const double *bvec, const double *jkq, const double *lstar, double *rho, Real *rhoR,
-                           unsigned long long *resid)
+                           unsigned long long *resid, const double *src)
 {
     long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     double change = 0.0;
     if (v < nvox) {
         const double e = eps[v], B = bpl[v];
+        // right-hand side of A(S) = f: eps B delta_K0, or a given source (coarse-grid problems)
+        const double f0 = src ? src[v * nl] : e * B;
         if (model == PORTA_MODEL_TWOLEVEL_UNPOL) {
             const double S = rho[v];
-            const double dS = ((1.0 - e) * jkq[v] + e * B - S) / (1.0 - (1.0 - e) * lstar[v]);
+            const double dS = ((1.0 - e) * jkq[v] + f0 - S) / (1.0 - (1.0 - e) * lstar[v]);
             const double Sn = S + dS;
             change = fabs(dS) / fabs(S);
             rho[v] = Sn;
@@ -119,13 +121,13 @@ __global__ void see_kernel(long long nvox, int nl, int model, double bcrit, cons
             double *s = rho + 6 * v;
             const double *J = jkq + 6 * v;
             const double S00 = s[0];
-            const double dS = ((1.0 - e) * J[0] + e * B - S00) / (1.0 - (1.0 - e) * lstar[v]);
+            const double dS = ((1.0 - e) * J[0] + f0 - S00) / (1.0 - (1.0 - e) * lstar[v]);
             const double S00n = S00 + dS;
             const double bx = bvec[v], by = bvec[nvox + v], bz = bvec[2 * nvox + v];
             const double gam = (1.0 - e) / bcrit;   // Gamma = (1-eps) |B| / bcrit; times B/|B| below
             double r[5], x[5];
 #pragma unroll
-            for (int c = 0; c < 5; ++c) r[c] = (1.0 - e) * J[1 + c];
+            for (int c = 0; c < 5; ++c) r[c] = (1.0 - e) * J[1 + c] + (src ? src[v * nl + 1 + c] : 0.0);
             hanle_solve5(gam * bx, gam * by, gam * bz, r, x);
             change = fabs(dS) / fabs(S00);
 #pragma unroll
@@ -215,10 +217,48 @@ cudaError_t run_jkq_finalize(long long nvox, int nray, const void *part, const d
 template <typename Real>
 cudaError_t run_see(long long nvox, int nl, int model, double bcrit, const double *eps, const double *bpl,
                     const double *bvec, const double *jkq, const double *lstar, double *rho, void *rhoR,
-                    unsigned long long *resid, cudaStream_t st)
+                    unsigned long long *resid, cudaStream_t st, const double *src)
 {
     see_kernel<Real><<<nblk(nvox, 256), 256, 0, st>>>(nvox, nl, model, bcrit, eps, bpl, bvec, jkq, lstar, rho,
-                                                      (Real *)rhoR, resid);
+                                                      (Real *)rhoR, resid, src);
+    return cudaGetLastError();
+}
+
+// out = alpha A(S) + add (+ eps B delta_K0 if with_eb), A the statistical-
+// equilibrium operator of A(S) = f: A(S)^0_0 = S^0_0 - (1-eps) J^0_0,
+// A(S)^2 = M S^2 - (1-eps) J^2 with M = 1 + i (1-eps) Gamma_u K (Eq. 2).
+// out may alias add (each element is read before it is written).
+__global__ void see_apply_kernel(long long nvox, int nl, int model, double bcrit, const double *eps, const double *bpl,
+                                 const double *bvec, const double *jkq, const double *rho, double alpha,
+                                 const double *add, int with_eb, double *out)
+{
+    long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (v >= nvox) return;
+    const double e = eps[v];
+    const double *s = rho + v * nl, *J = jkq + v * nl;
+    double a[6];
+    a[0] = s[0] - (1.0 - e) * J[0];
+    if (model != PORTA_MODEL_TWOLEVEL_UNPOL) {
+        const double gam = (1.0 - e) / bcrit;
+        double y[5];
+        hanle_apply5(gam * bvec[v], gam * bvec[nvox + v], gam * bvec[2 * nvox + v], s + 1, y);
+#pragma unroll
+        for (int c = 0; c < 5; ++c) a[1 + c] = y[c] - (1.0 - e) * J[1 + c];
+    }
+    for (int c = 0; c < nl; ++c) {
+        double o = alpha * a[c];
+        if (add) o += add[v * nl + c];
+        if (with_eb && c == 0) o += e * bpl[v];
+        out[v * nl + c] = o;
+    }
+}
+
+cudaError_t run_see_apply(long long nvox, int nl, int model, double bcrit, const double *eps, const double *bpl,
+                          const double *bvec, const double *jkq, const double *rho, double alpha, const double *add,
+                          int with_eb, double *out, cudaStream_t st)
+{
+    see_apply_kernel<<<nblk(nvox, 256), 256, 0, st>>>(nvox, nl, model, bcrit, eps, bpl, bvec, jkq, rho, alpha, add,
+                                                      with_eb, out);
     return cudaGetLastError();
 }
 
@@ -255,7 +295,7 @@ template cudaError_t run_coefficients<double>(int, const double *, double *, cud
                                                 cudaStream_t);                                                 \
     template cudaError_t run_see<R>(long long, int, int, double, const double *, const double *, const double *, \
                                     const double *, const double *, double *, void *, unsigned long long *,     \
-                                    cudaStream_t);                                                             \
+                                    cudaStream_t, const double *);                                             \
     template cudaError_t run_to_real<R>(long long, const double *, void *, cudaStream_t);
 INST(float)
 INST(double)

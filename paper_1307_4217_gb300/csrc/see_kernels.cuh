@@ -14,10 +14,15 @@ cudaError_t run_rho_convert(long long nvox, int nl, const double *rho, void *out
 template <typename Real, int NS>
 cudaError_t run_jkq_finalize(long long nvox, int nray, const void *part, const double *tw, double *jkq, double *lstar,
                              cudaStream_t st);
+// src: null (right-hand side eps B delta_K0) or a per-voxel right-hand side [v][nl]
 template <typename Real>
 cudaError_t run_see(long long nvox, int nl, int model, double bcrit, const double *eps, const double *bpl,
                     const double *bvec, const double *jkq, const double *lstar, double *rho, void *rhoR,
-                    unsigned long long *resid, cudaStream_t st);
+                    unsigned long long *resid, cudaStream_t st, const double *src = nullptr);
+// out = alpha A(rho) + add (+ eps B delta_K0 if with_eb); out may alias add
+cudaError_t run_see_apply(long long nvox, int nl, int model, double bcrit, const double *eps, const double *bpl,
+                          const double *bvec, const double *jkq, const double *rho, double alpha, const double *add,
+                          int with_eb, double *out, cudaStream_t st);
 cudaError_t run_count_bad(long long n, const double *x, double lo_excl, double hi_incl, unsigned long long *bad,
                           cudaStream_t st);
 template <typename Real>
