@@ -82,6 +82,7 @@ def args_parse():
     ap.add_argument("--cpu-sample-rays", type=int, default=4)
     ap.add_argument("--adjoint-reps", type=int, default=5,
                     help="timed calls of the emergent-Stokes adjoint (0 skips it)")
+    ap.add_argument("--mg-cycles", type=int, default=3, help="timed multigrid V-cycles (0 skips them)")
     ap.add_argument("--adjoint-cluster", type=int, default=0, help="force the adjoint cluster size (skips its tuning)")
     ap.add_argument("--adjoint-nu-group", type=int, default=0, help="force the adjoint frequencies per pass")
     ap.add_argument("--cluster", type=int, default=0, help="force the sweep cluster size (skips the autotuner)")
@@ -404,6 +405,35 @@ def run_cuda(args):
                    "timing": "CUDA events inside porta_emergent_vjp (forward emergent sweep with tape; "
                              "adjoint sweep + fixed-order reduction), median"}
 
+    # non-linear multigrid on the same box: 3 levels (64^3 -> 32^3 -> 16^3), V-cycles of
+    # 2 pre- and 4 post-smoothing Jacobi iterations and 8 on the coarsest grid, from
+    # rho0; Jacobi iterations of the same fine-grid cost (7 sweeps per cycle) beside it
+    mgres = None
+    if args.mg_cycles > 0 and wl.name == "pol64":
+        with torch.cuda.stream(stream):
+            ctx.mg_setup(3)
+            ctx.set_rho(wl.rho0)
+            ctx.mg_vcycle(2, 4, 8)                          # warm-up
+            ctx.set_rho(wl.rho0)
+            barrier()
+            cyc = []
+            for _ in range(args.mg_cycles):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                ch = ctx.mg_vcycle(2, 4, 8)
+                e1.record(stream)
+                e1.synchronize()
+                cyc.append((e0.elapsed_time(e1), ch))
+            ctx.set_rho(wl.rho0)
+            jac = []
+            for _ in range(args.mg_cycles):
+                jac.append(ctx.run_iterations(7))
+        mgres = {"levels": ctx.mg_levels(), "cycle": "2 pre + 4 post Jacobi, 8 on the coarsest, from S00 = B",
+                 "vcycle_ms": [round(t, 3) for t, _ in cyc], "vcycle_max_change": [c for _, c in cyc],
+                 "jacobi_ms_per_7_iterations": 7 * step_ms,
+                 "jacobi_max_change_after_7k_iterations": jac,
+                 "note": "max_change: of the whole V-cycle for MG, of the last iteration for Jacobi"}
+
     # max over ranks
     if world > 1:
         step_ms, sweep_ms, e2e_s = max_over_ranks([step_ms, sweep_ms, e2e_s], dev)
@@ -439,6 +469,7 @@ def run_cuda(args):
         "gpu_launches": (4 if fill["cluster"] > 0 else 3) * args.steps,
         "fp64_plain": fp64,
         "adjoint": adjoint,
+        "multigrid": mgres,
     }
     print(json.dumps(line))
     if world > 1:
