@@ -83,6 +83,7 @@ def args_parse():
     ap.add_argument("--adjoint-reps", type=int, default=5,
                     help="timed calls of the emergent-Stokes adjoint (0 skips it)")
     ap.add_argument("--mg-cycles", type=int, default=3, help="timed multigrid V-cycles (0 skips them)")
+    ap.add_argument("--fill", default="", help="force the concurrent filler launch: cluster,nu_group,fraction")
     ap.add_argument("--adjoint-cluster", type=int, default=0, help="force the adjoint cluster size (skips its tuning)")
     ap.add_argument("--adjoint-nu-group", type=int, default=0, help="force the adjoint frequencies per pass")
     ap.add_argument("--cluster", type=int, default=0, help="force the sweep cluster size (skips the autotuner)")
@@ -296,6 +297,9 @@ def run_cuda(args):
         if not forced:
             ctx.autotune()          # launch-shape autotuner (outside the timed region)
             ctx.set_rho(wl.rho0)
+        if args.fill:
+            cl, nu, fr = args.fill.split(",")
+            ctx.set_fill(int(cl), int(nu), float(fr))
         return ctx
 
     ctx = make(P.PORTA_FP32)
