@@ -90,6 +90,9 @@ def _declare(L):
                              _P, _P, _P, _P, _P, _P, _P]),
         "or_see_apply": (_I, [_P, _P, _P, _P]),
         "or_see_update_src": (_I, [_P, _P, _P, _P, _P, _P]),
+        "or_see_update_vjp": (_I, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
+        "or_jkq_vjp": (_I, [_P, _P, _P, _P, _P, _P, _P]),
+        "or_emergent_vjp_rho": (_I, [_P, _P, _I, _P, _P, _P, _P, _P, _P]),
         "or_flops_reset": (None, [_I]),
         "or_flops_get": (ctypes.c_longlong, []),
         "or_nray": (_I, [_P]),
@@ -311,6 +314,43 @@ def emergent_vjp(prob, rho, mu, chi, gout):
                                _ptr(g_chi), _ptr(g_e), _ptr(g_b))
     assert rc == 0, rc
     return g_chi.reshape(prob.shape), g_e.reshape(prob.shape), g_b.reshape((3,) + prob.shape)
+
+
+def see_update_vjp(prob, jkq, lstar, rho, g, src=None):
+    """Reverse mode of see_update_src: (dL/drho explicit, dL/dJ, dL/dLambda*, dL/dsrc^0_0, dL/dB)."""
+    nl, nj = nl_of(prob.model), nj_of(prob.model)
+    a = [_f64(x).ravel() for x in (jkq, lstar)]
+    sr = _f64(src).ravel() if src is not None else None
+    b = [_f64(x).ravel() for x in (rho, g)]
+    out = dict(rho=np.zeros(prob.nvox * nl), jkq=np.zeros(prob.nvox * nj), lstar=np.zeros(prob.nvox),
+               eb=np.zeros(prob.nvox), b=np.zeros(3 * prob.nvox))
+    rc = lib().or_see_update_vjp(prob.ref, _ptr(a[0]), _ptr(a[1]), _ptr(sr), _ptr(b[0]), _ptr(b[1]),
+                                 *[_ptr(out[k]) for k in ("rho", "jkq", "lstar", "eb", "b")])
+    assert rc == 0
+    sh = prob.shape
+    return (out["rho"].reshape(sh + (nl,)), out["jkq"].reshape(sh + (nj,)), out["lstar"].reshape(sh),
+            out["eb"].reshape(sh), out["b"].reshape((3,) + sh))
+
+
+def jkq_vjp(prob, rho, g_jkq, g_lstar):
+    """Gradients of sum(g_jkq J) + sum(g_lstar Lambda*) w.r.t. chi (fixed rho), rho, B."""
+    nl = nl_of(prob.model)
+    rho = _f64(rho).ravel(); gj = _f64(g_jkq).ravel(); gl = _f64(g_lstar).ravel()
+    g_chi = np.zeros(prob.nvox); g_rho = np.zeros(prob.nvox * nl); g_b = np.zeros(3 * prob.nvox)
+    rc = lib().or_jkq_vjp(prob.ref, _ptr(rho), _ptr(gj), _ptr(gl), _ptr(g_chi), _ptr(g_rho), _ptr(g_b))
+    assert rc == 0, rc
+    return g_chi.reshape(prob.shape), g_rho.reshape(prob.shape + (nl,)), g_b.reshape((3,) + prob.shape)
+
+
+def emergent_vjp_rho(prob, rho, mu, chi, gout):
+    """Adjoint of emergent in the unknowns: dL/dchi (fixed rho), dL/drho, dL/dB."""
+    nl = nl_of(prob.model)
+    rho = _f64(rho).ravel(); mu = _f64(mu); chi = _f64(chi); gout = _f64(gout).ravel()
+    g_chi = np.zeros(prob.nvox); g_rho = np.zeros(prob.nvox * nl); g_b = np.zeros(3 * prob.nvox)
+    rc = lib().or_emergent_vjp_rho(prob.ref, _ptr(rho), len(mu), _ptr(mu), _ptr(chi), _ptr(gout),
+                                   _ptr(g_chi), _ptr(g_rho), _ptr(g_b))
+    assert rc == 0, rc
+    return g_chi.reshape(prob.shape), g_rho.reshape(prob.shape + (nl,)), g_b.reshape((3,) + prob.shape)
 
 
 def initial_rho(prob, atm):

@@ -179,3 +179,109 @@ int or_see_update(const or_problem *p, const double *jkq, const double *lstar, d
 {
     return or_see_update_src(p, jkq, lstar, NULL, rho, max_change);
 }
+
+/* ------------------------------------------------------------------------
+ * Reverse mode of the Jacobi update (differentiation through iterations).
+ * ------------------------------------------------------------------------ */
+
+/* The K = 2 map S^2 -> M S^2 (M = 1 + i gamma K) as a real 5x5 matrix on the
+   layout (S20, Re S21, Im S21, Re S22, Im S22): column c is the image of the
+   c-th real unit vector. */
+static void hanle_real(double gamma, double bx, double by, double bz, double R[5][5])
+{
+    double complex M[5][5];
+    hanle_matrix(gamma, bx, by, bz, M);
+    for (int c = 0; c < 5; c++) {
+        double u[6] = {0, 0, 0, 0, 0, 0};
+        u[1 + c] = 1.0;
+        double complex x[5], y[5];
+        to_complex(u, x);
+        for (int a = 0; a < 5; a++) {
+            y[a] = 0.0;
+            for (int q = 0; q < 5; q++) y[a] += M[a][q] * x[q];
+        }
+        R[0][c] = creal(y[2]);
+        R[1][c] = creal(y[3]); R[2][c] = cimag(y[3]);
+        R[3][c] = creal(y[4]); R[4][c] = cimag(y[4]);
+    }
+}
+
+/* solve A x = b (5x5, partial pivoting); A and b are overwritten */
+static int solve5(double A[5][5], double *b, double *x)
+{
+    for (int c = 0; c < 5; c++) {
+        int piv = c;
+        for (int r = c + 1; r < 5; r++) if (fabs(A[r][c]) > fabs(A[piv][c])) piv = r;
+        if (A[piv][c] == 0.0) return -1;
+        if (piv != c) {
+            for (int q = 0; q < 5; q++) { double t = A[c][q]; A[c][q] = A[piv][q]; A[piv][q] = t; }
+            double t = b[c]; b[c] = b[piv]; b[piv] = t;
+        }
+        for (int r = c + 1; r < 5; r++) {
+            double f = A[r][c] / A[c][c];
+            for (int q = c; q < 5; q++) A[r][q] -= f * A[c][q];
+            b[r] -= f * b[c];
+        }
+    }
+    for (int r = 4; r >= 0; r--) {
+        double t = b[r];
+        for (int q = r + 1; q < 5; q++) t -= A[r][q] * x[q];
+        x[r] = t / A[r][r];
+    }
+    return 0;
+}
+
+/*
+ * Reverse mode of or_see_update_src for one iteration (src as there: NULL is
+ * eps B delta_K0; its K = 2 part must be 0). Inputs: the unknowns before the
+ * update rho, J and Lambda-bar* computed from them, and g = dL/d(rho after the
+ * update). Outputs (overwritten):
+ *   g_rho   dL/drho through the update's explicit dependence on rho (S^0_0),
+ *   g_jkq   dL/dJ^K_Q,  g_lstar  dL/dLambda-bar*,
+ *   g_eb    dL/d(eps B), or dL/dsrc^0_0 (the thermal emission term),
+ *   g_b     dL/dB (3 x nvox, added for the polarized model: the Hanle term).
+ * S00' = S00 + ((1-eps) J00 + eps B - S00) / D, D = 1 - (1-eps) Lambda*;
+ * S2' = M(B)^-1 (1-eps) J2 with M affine in B: M = 1 + (1-eps)/bcrit sum_c B_c N_c.
+ */
+int or_see_update_vjp(const or_problem *p, const double *jkq, const double *lstar, const double *src,
+                      const double *rho, const double *g, double *g_rho, double *g_jkq, double *g_lstar,
+                      double *g_eb, double *g_b)
+{
+    long nv = (long)p->nx * p->ny * p->nz;
+    int nl = or_nl(p->model), nj = or_nj(p->model);
+    for (long v = 0; v < nv; v++) {
+        double e = p->eps[v], B = p->bpl[v];
+        const double *s = rho + nl * v, *J = jkq + nj * v, *gv = g + nl * v;
+        double D = 1.0 - (1.0 - e) * lstar[v];
+        double num = (1.0 - e) * J[0] + (src ? src[nl * v] : e * B) - s[0];
+        for (int c = 0; c < nl; c++) g_rho[nl * v + c] = 0.0;
+        for (int c = 0; c < nj; c++) g_jkq[nj * v + c] = 0.0;
+        g_rho[nl * v] = gv[0] * (1.0 - 1.0 / D);
+        g_jkq[nj * v] = gv[0] * (1.0 - e) / D;
+        g_eb[v] = gv[0] / D;
+        g_lstar[v] = gv[0] * num * (1.0 - e) / (D * D);
+        if (p->model == OR_MODEL_UNPOL) continue;
+        double bx = p->bx[v], by = p->by[v], bz = p->bz[v];
+        double gamma = (1.0 - e) * sqrt(bx * bx + by * by + bz * bz) / p->bcrit;
+        double R[5][5], Rt[5][5], rhs[6], s2[6], z[5], b5[5];
+        hanle_real(gamma, bx, by, bz, R);
+        for (int c = 0; c < 6; c++) rhs[c] = (1.0 - e) * J[c];
+        if (or_hanle_solve(gamma, bx, by, bz, rhs, s2) != 0) return -3;
+        for (int a = 0; a < 5; a++) for (int c = 0; c < 5; c++) Rt[a][c] = R[c][a];
+        for (int a = 0; a < 5; a++) b5[a] = gv[1 + a];
+        if (solve5(Rt, b5, z) != 0) return -3;
+        for (int a = 0; a < 5; a++) g_jkq[nj * v + 1 + a] = (1.0 - e) * z[a];
+        /* dM/dB_c = (1-eps)/bcrit N_c, N_c = M(unit field along c, gamma 1) - 1; dS2' = -M^-1 dM S2' */
+        double unit[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+        for (int c = 0; c < 3; c++) {
+            double N[5][5];
+            hanle_real(1.0, unit[c][0], unit[c][1], unit[c][2], N);
+            double acc = 0.0;
+            for (int a = 0; a < 5; a++)
+                for (int q = 0; q < 5; q++) acc += z[a] * (N[a][q] - (a == q ? 1.0 : 0.0)) * s2[1 + q];
+            g_b[c * nv + v] += -(1.0 - e) / p->bcrit * acc;
+        }
+    }
+    return 0;
+}
+

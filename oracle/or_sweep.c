@@ -395,3 +395,209 @@ int or_emergent_vjp(const or_problem *p, const double *rho, int ndir, const doub
     free(xf); free(wf); free(I); free(lo); free(lam);
     return rc;
 }
+
+/* ------------------------------------------------------------------------
+ * Reverse mode in the unknowns rho (differentiation through iterations):
+ * node coefficients as functions of chi, rho and B (eps_i = chi phi S_i(rho),
+ * eps_V = S00 eta_V), and the J^K_Q / Lambda-bar* sums of a formal solution.
+ * ------------------------------------------------------------------------ */
+
+/* add dL/dchi (at fixed rho), dL/drho and dL/dB of node v from dL/d(eta 7) and dL/d(eps) */
+static void node_vjp_rho(const or_problem *p, const double *rho, long v, const or_ray *r, double x,
+                         const double *g_eta, const double *g_eps, double *g_chi, double *g_rho, double *g_b)
+{
+    long nv = (long)p->nx * p->ny * p->nz;
+    double xs = x - shift(p, v, r);
+    double phi = exp(-xs * xs);
+    double chi = p->chi[v], etaI = chi * phi;
+    if (p->model == OR_MODEL_UNPOL) {
+        g_chi[v] += phi * g_eta[0] + phi * rho[v] * g_eps[0];
+        g_rho[v] += etaI * g_eps[0];
+        return;
+    }
+    const double *s = rho + 6 * v;
+    double beta = 2.0 * p->gbar * p->zeta;
+    double bpar = p->bx[v] * r->ox + p->by[v] * r->oy + p->bz[v] * r->oz;
+    double etaV = beta * xs * bpar * etaI;
+    double gc = phi * g_eta[0] + beta * xs * bpar * phi * (g_eta[3] + s[0] * g_eps[3]);
+    for (int i = 0; i < 3; i++) {
+        const double *t = r->t + 6 * i;
+        gc += phi * angular_source(t, s) * g_eps[i];
+        double gS = etaI * g_eps[i];
+        g_rho[6 * v + 0] += gS * t[0];
+        g_rho[6 * v + 1] += gS * t[1];
+        for (int c = 2; c < 6; c++) g_rho[6 * v + c] += gS * 2.0 * t[c];
+    }
+    g_rho[6 * v + 0] += etaV * g_eps[3];
+    g_chi[v] += gc;
+    double gb = beta * xs * phi * chi * (g_eta[3] + s[0] * g_eps[3]);
+    g_b[v] += gb * r->ox;
+    g_b[nv + v] += gb * r->oy;
+    g_b[2 * nv + v] += gb * r->oz;
+}
+
+/* one (ray, frequency) reverse sweep: lam (nv*ns) holds dL/dI seeded by the caller or by
+   the injections (J weights wj per voxel and Lambda* weights wl per voxel, both may be NULL) */
+static int reverse_sweep(const or_problem *p, const double *rho, const or_ray *r, double x, const double *I,
+                         double *lam, const double *gj_dir, const double *wj, const double *wl,
+                         double *g_chi, double *g_rho, double *g_b)
+{
+    int ns = or_ns(p->model);
+    int nx = p->nx, ny = p->ny, nz = p->nz;
+    double dx = p->lx / nx, dy = p->ly / ny, amu = fabs(r->mu);
+    int up = r->mu > 0;
+    for (int ks = nz - 1; ks >= 1; ks--) {
+        int k = up ? ks : nz - 1 - ks;
+        int ku = up ? k - 1 : k + 1, kd = up ? k + 1 : k - 1, has_p = ks + 1 < nz;
+        double dsM = fabs(p->z[k] - p->z[ku]) / amu;
+        double dsP = has_p ? fabs(p->z[kd] - p->z[k]) / amu : 0.0;
+        for (int j = 0; j < ny; j++)
+            for (int i = 0; i < nx; i++) {
+                long v = vox(p, i, j, k);
+                /* dL/dI_O from J^K_Q = sum w T I (injection) */
+                if (wj)
+                    for (int q = 0; q < (ns == 1 ? 1 : 3); q++) lam[v * ns + q] += wj[v] * gj_dir[v * 3 + q];
+                int iM[4], jM[4], iP[4], jP[4];
+                double wM[4], wP[4];
+                double etaM[7] = {0}, epsM[4] = {0}, IM[4] = {0};
+                bilinear(p, i - dsM * r->ox / dx, j - dsM * r->oy / dy, iM, jM, wM);
+                for (int c = 0; c < 4; c++) {
+                    long u = vox(p, iM[c], jM[c], ku);
+                    double e7[7], e4[4];
+                    node_coeffs(p, rho, u, r, x, e7, e4);
+                    for (int q = 0; q < 7; q++) etaM[q] += wM[c] * e7[q];
+                    for (int q = 0; q < ns; q++) { epsM[q] += wM[c] * e4[q]; IM[q] += wM[c] * I[u * ns + q]; }
+                }
+                double etaO[7], epsO[4];
+                node_coeffs(p, rho, v, r, x, etaO, epsO);
+                double etaP = 0.0, epsP[4] = {0};
+                if (has_p) {
+                    bilinear(p, i + dsP * r->ox / dx, j + dsP * r->oy / dy, iP, jP, wP);
+                    for (int c = 0; c < 4; c++) {
+                        long u = vox(p, iP[c], jP[c], kd);
+                        double e7[7], e4[4];
+                        node_coeffs(p, rho, u, r, x, e7, e4);
+                        etaP += wP[c] * e7[0];
+                        for (int q = 0; q < ns; q++) epsP[q] += wP[c] * e4[q];
+                    }
+                }
+                double gIM[4], gEM[7], gSM[4], gEO[7], gSO[4], gEP, gSP[4];
+                if (or_step_vjp(ns, IM, etaM, epsM, etaO, epsO, etaP, epsP, dsM, dsP, has_p, p->method,
+                                lam + v * ns, gIM, gEM, gSM, gEO, gSO, &gEP, gSP) != 0)
+                    return -3;
+                if (wl && wl[v] != 0.0) {
+                    /* Lambda* = w_O + w_C c_M(0,1,0) of the step depends on tau_MO only (BESSER) */
+                    double tau = 0.5 * (etaM[0] + etaO[0]) * dsM, c[6], dc[6];
+                    or_coeffs(tau, c);
+                    or_coeffs_deriv(tau, c, dc);
+                    double gt = wl[v] * (dc[4] + (has_p ? 1.0 : 0.5) * dc[5]);
+                    gEM[0] += 0.5 * dsM * gt;
+                    gEO[0] += 0.5 * dsM * gt;
+                }
+                for (int c = 0; c < 4; c++) {
+                    long u = vox(p, iM[c], jM[c], ku);
+                    double ge7[7], ge4[4];
+                    for (int q = 0; q < ns; q++) lam[u * ns + q] += wM[c] * gIM[q];
+                    for (int q = 0; q < 7; q++) ge7[q] = wM[c] * gEM[q];
+                    for (int q = 0; q < ns; q++) ge4[q] = wM[c] * gSM[q];
+                    node_vjp_rho(p, rho, u, r, x, ge7, ge4, g_chi, g_rho, g_b);
+                }
+                node_vjp_rho(p, rho, v, r, x, gEO, gSO, g_chi, g_rho, g_b);
+                if (has_p)
+                    for (int c = 0; c < 4; c++) {
+                        long u = vox(p, iP[c], jP[c], kd);
+                        double ge7[7] = {wP[c] * gEP, 0, 0, 0, 0, 0, 0}, ge4[4];
+                        for (int q = 0; q < ns; q++) ge4[q] = wP[c] * gSP[q];
+                        node_vjp_rho(p, rho, u, r, x, ge7, ge4, g_chi, g_rho, g_b);
+                    }
+            }
+    }
+    return 0;
+}
+
+/*
+ * Gradients of L = sum g_jkq J^K_Q + sum g_lstar Lambda-bar* (J and Lambda-bar*
+ * of or_formal_solve at rho) with respect to chi (at fixed rho), rho and B;
+ * ADDED to g_chi (nvox), g_rho (nvox*nl) and g_b (3*nvox; ignored for the
+ * unpolarized model). BESSER only.
+ */
+int or_jkq_vjp(const or_problem *p, const double *rho, const double *g_jkq, const double *g_lstar,
+               double *g_chi, double *g_rho, double *g_b)
+{
+    if (check(p) || p->method != OR_BESSER) return -1;
+    int ns = or_ns(p->model), nj = or_nj(p->model), nr = or_nray(p), nn = p->n_nu;
+    long nv = (long)p->nx * p->ny * p->nz;
+    double *mu = malloc(sizeof(double) * nr), *ch = malloc(sizeof(double) * nr), *w = malloc(sizeof(double) * nr);
+    double *xf = malloc(sizeof(double) * nn), *wf = malloc(sizeof(double) * nn);
+    double *I = malloc(sizeof(double) * nv * ns), *lo = malloc(sizeof(double) * nv), *lam = malloc(sizeof(double) * nv * ns);
+    double *norm = malloc(sizeof(double) * nv), *wj = malloc(sizeof(double) * nv), *wl = malloc(sizeof(double) * nv);
+    double *gdir = malloc(sizeof(double) * nv * 3);
+    if (!mu || !ch || !w || !xf || !wf || !I || !lo || !lam || !norm || !wj || !wl || !gdir) return -2;
+    or_rays(p, mu, ch, w);
+    or_freqs(nn, p->x_max, xf, wf);
+    int rc = 0;
+    for (int m = 0; m < nr && rc == 0; m++) {
+        or_ray r;
+        make_ray(mu[m], ch[m], w[m], &r);
+        for (long v = 0; v < nv; v++) {
+            double s = shift(p, v, &r), sum = 0.0;
+            for (int j = 0; j < nn; j++) sum += wf[j] * exp(-(xf[j] - s) * (xf[j] - s)) / sqrt(M_PI);
+            norm[v] = sum;
+            /* dL/dI_p per unit weight: sum_c T^K_Q(p, Omega) g_J^K_Q */
+            for (int q = 0; q < 3; q++) {
+                double a = 0.0;
+                if (p->model == OR_MODEL_UNPOL) { if (q == 0) a = g_jkq[v]; }
+                else for (int c = 0; c < 6; c++) a += r.t[6 * q + c] * g_jkq[v * nj + c];
+                gdir[v * 3 + q] = a;
+            }
+        }
+        for (int j = 0; j < nn && rc == 0; j++) {
+            rc = sweep(p, rho, &r, xf[j], I, lo);
+            if (rc) break;
+            for (long v = 0; v < nv; v++) {
+                double xs = xf[j] - shift(p, v, &r);
+                double wt = r.w * wf[j] * exp(-xs * xs) / sqrt(M_PI) / norm[v];
+                wj[v] = wt;
+                wl[v] = wt * g_lstar[v];
+            }
+            memset(lam, 0, sizeof(double) * nv * ns);
+            rc = reverse_sweep(p, rho, &r, xf[j], I, lam, gdir, wj, wl, g_chi, g_rho, g_b);
+        }
+    }
+    free(mu); free(ch); free(w); free(xf); free(wf); free(I); free(lo); free(lam);
+    free(norm); free(wj); free(wl); free(gdir);
+    return rc;
+}
+
+/* adjoint of or_emergent in the unknowns: dL/dchi (fixed rho), dL/drho, dL/dB (overwritten) */
+int or_emergent_vjp_rho(const or_problem *p, const double *rho, int ndir, const double *mu, const double *chi,
+                        const double *gout, double *g_chi, double *g_rho, double *g_b)
+{
+    if (check(p)) return -1;
+    int ns = or_ns(p->model), nn = p->n_nu, nl = or_nl(p->model);
+    long nv = (long)p->nx * p->ny * p->nz, nxy = (long)p->nx * p->ny;
+    double *xf = malloc(sizeof(double) * nn), *wf = malloc(sizeof(double) * nn);
+    double *I = malloc(sizeof(double) * nv * ns), *lo = malloc(sizeof(double) * nv);
+    double *lam = malloc(sizeof(double) * nv * ns);
+    if (!xf || !wf || !I || !lo || !lam) return -2;
+    or_freqs(nn, p->x_max, xf, wf);
+    memset(g_chi, 0, sizeof(double) * nv);
+    memset(g_rho, 0, sizeof(double) * nv * nl);
+    if (g_b) memset(g_b, 0, sizeof(double) * 3 * nv);
+    int rc = 0;
+    for (int d = 0; d < ndir && rc == 0; d++) {
+        if (!(mu[d] > 0.0 && mu[d] <= 1.0)) { rc = -1; break; }
+        or_ray r;
+        make_ray(mu[d], chi[d], 0.0, &r);
+        for (int jf = 0; jf < nn && rc == 0; jf++) {
+            rc = sweep(p, rho, &r, xf[jf], I, lo);
+            if (rc) break;
+            memset(lam, 0, sizeof(double) * nv * ns);
+            memcpy(lam + (long)(p->nz - 1) * nxy * ns, gout + ((long)d * nn + jf) * nxy * ns, sizeof(double) * nxy * ns);
+            rc = reverse_sweep(p, rho, &r, xf[jf], I, lam, NULL, NULL, NULL, g_chi, g_rho, g_b);
+        }
+    }
+    free(xf); free(wf); free(I); free(lo); free(lam);
+    return rc;
+}
+

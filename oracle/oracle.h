@@ -80,6 +80,11 @@ int or_see_update(const or_problem *p, const double *jkq, const double *lstar,
 int or_see_apply(const or_problem *p, const double *jkq, const double *rho, double *out);
 int or_see_update_src(const or_problem *p, const double *jkq, const double *lstar, const double *src,
                       double *rho, double *max_change);
+/* reverse mode of or_see_update_src (src NULL: eps B): from g = dL/d(rho after) to dL/drho (explicit
+   part), dL/dJ^K_Q, dL/dLambda-bar*, dL/d(src^0_0) and (added to g_b, 3 x nvox) dL/dB of the Hanle term */
+int or_see_update_vjp(const or_problem *p, const double *jkq, const double *lstar, const double *src,
+                      const double *rho, const double *g, double *g_rho, double *g_jkq, double *g_lstar,
+                      double *g_eb, double *g_b);
 
 /* ---- 3D short-characteristics formal solution ---- */
 /* one ray m, one frequency j, full grid: I (nvox*ns) and Lambda* (nvox) */
@@ -98,6 +103,12 @@ int or_emergent(const or_problem *p, const double *rho, int ndir, const double *
    unpolarized model); gout has the layout of out */
 int or_emergent_vjp(const or_problem *p, const double *rho, int ndir, const double *mu,
                     const double *chi, const double *gout, double *g_chi, double *g_e, double *g_b);
+/* reverse mode in the unknowns: dL/dchi at fixed rho, dL/drho, dL/dB of the J^K_Q / Lambda-bar* of a
+   formal solution (added to the outputs) and of the emergent Stokes vector (overwritten) */
+int or_jkq_vjp(const or_problem *p, const double *rho, const double *g_jkq, const double *g_lstar,
+               double *g_chi, double *g_rho, double *g_b);
+int or_emergent_vjp_rho(const or_problem *p, const double *rho, int ndir, const double *mu, const double *chi,
+                        const double *gout, double *g_chi, double *g_rho, double *g_b);
 /* reverse mode of the step coefficients, control point and step (derivatives for the adjoint) */
 void or_coeffs_deriv(double tau, const double c[6], double dc[6]);
 void or_control_point_vjp(double yM, double yO, double yP, double hM, double hP, int has_p, int method,
