@@ -83,6 +83,8 @@ def args_parse():
     ap.add_argument("--adjoint-reps", type=int, default=5,
                     help="timed calls of the emergent-Stokes adjoint (0 skips it)")
     ap.add_argument("--mg-cycles", type=int, default=3, help="timed multigrid V-cycles (0 skips them)")
+    ap.add_argument("--iter-adjoint", default="20,5",
+                    help="gradients through Jacobi iterations: 'iterations,checkpoint spacing' (0 skips them)")
     ap.add_argument("--fill", default="", help="force the concurrent filler launch: cluster,nu_group,fraction")
     ap.add_argument("--adjoint-cluster", type=int, default=0, help="force the adjoint cluster size (skips its tuning)")
     ap.add_argument("--adjoint-nu-group", type=int, default=0, help="force the adjoint frequencies per pass")
@@ -409,6 +411,42 @@ def run_cuda(args):
                    "timing": "CUDA events inside porta_emergent_vjp (forward emergent sweep with tape; "
                              "adjoint sweep + fixed-order reduction), median"}
 
+    # gradients through Jacobi iterations (same box and emergent rays): forward
+    # iterations keeping rho checkpoints, then the checkpointed reverse pass
+    iter_adj = None
+    if args.iter_adjoint != "0" and wl.name == "pol64":
+        import synth
+        niter, ckpt = (int(x) for x in args.iter_adjoint.split(","))
+        mu, az = synth.emergent_directions()
+        nz, ny, nx = ctx.shape
+        gen = torch.Generator(device=dev).manual_seed(4321)
+        gout = torch.randn((len(mu), ctx.nnu, ny, nx, ctx.ns), dtype=torch.float64, device=dev, generator=gen)
+        gbuf = [torch.empty((nz, ny, nx), dtype=torch.float64, device=dev) for _ in range(2)]
+        gbuf.append(torch.empty((3, nz, ny, nx), dtype=torch.float64, device=dev))
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        with torch.cuda.stream(stream):
+            ctx.set_adjoint_launch(args.adjoint_cluster, args.adjoint_nu_group)
+            # warm-up: one iteration and its reverse (times the launch shapes once)
+            ctx.set_rho(wl.rho0)
+            ctx.iterate_ckpt(1, 1, residual=False)
+            ctx.iterate_vjp(mu, az, gout, g_chi=gbuf[0], g_f=gbuf[1], g_b=gbuf[2])
+            ctx.set_rho(wl.rho0)
+            barrier()
+            ev[0].record(stream)
+            ctx.iterate_ckpt(niter, ckpt, residual=False)
+            ev[1].record(stream)
+            ctx.iterate_vjp(mu, az, gout, g_chi=gbuf[0], g_f=gbuf[1], g_b=gbuf[2])
+            ev[2].record(stream)
+            barrier()
+        fwd_ms, rev_ms = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
+        iter_adj = {"workload": f"{nx}x{ny}x{nz} polarized, {ctx.nnu} frequencies, {ctx.nray} rays, "
+                                f"{niter} Jacobi iterations, checkpoints every {ckpt}; loss on the vertical + "
+                                "4 oblique emergent rays; gradients w.r.t. chi, f = eps B, B", "dtype": "f32 sweeps, f64 SEE",
+                    "forward_ms": fwd_ms, "reverse_ms": rev_ms, "ratio": rev_ms / fwd_ms,
+                    "launch": ctx.adjoint_info(), "phases": ctx.iterate_timing(),
+                    "timing": "CUDA events around porta_iterate_ckpt (eager iterations + checkpoint copies) "
+                              "and porta_iterate_vjp (recomputation, SEE and formal-solution adjoints)"}
+
     # non-linear multigrid on the same box: 3 levels (64^3 -> 32^3 -> 16^3), V-cycles of
     # 2 pre- and 4 post-smoothing Jacobi iterations and 8 on the coarsest grid, from
     # rho0; Jacobi iterations of the same fine-grid cost (7 sweeps per cycle) beside it
@@ -474,6 +512,7 @@ def run_cuda(args):
         "fp64_plain": fp64,
         "adjoint": adjoint,
         "multigrid": mgres,
+        "iter_adjoint": iter_adj,
     }
     print(json.dumps(line))
     if world > 1:

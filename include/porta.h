@@ -311,6 +311,55 @@ int porta_adjoint_timing(const porta_ctx *c, float *forward_ms, float *adjoint_m
 /* Launch statistics of the last adjoint sweep (as porta_launch_info). */
 int porta_adjoint_info(const porta_ctx *c, int *clusters, int *cluster_size, int *nu_group, int *smem_bytes);
 
+/* Gradients through Jacobi iterations (reverse mode of Eqs. 12-13 composed
+   with the formal solution of Sec. 3; the paper has no counterpart).
+   porta_iterate_ckpt runs niter Jacobi iterations from the current rho
+   (formal solution, J^K_Q and Lambda-bar*, update, as porta_formal_solve,
+   porta_accumulate_jkq and porta_see_update) and keeps, on the device,
+   rho before every ckpt-th iteration ((niter + ckpt - 1)/ckpt vectors of
+   nvox*nl doubles) and rho after the last; rho is left at the last iterate.
+   max_change (host, may be NULL): that of the last update. A new call drops
+   the previous checkpoints. niter, ckpt >= 1 (PORTA_EINVAL otherwise);
+   single-box contexts; PORTA_ESTATE without atmosphere and rho. */
+int porta_iterate_ckpt(porta_ctx *c, int niter, int ckpt, double *max_change);
+
+/* L = sum(grad_out * out), out the emergent Stokes profiles (layout of
+   porta_emergent_stokes) of the last iterate of porta_iterate_ckpt, as a
+   function of per-voxel
+     chi  (line-centre opacity; rho follows from the iterations),
+     f    (the thermal source term eps B of the update, Eq. 12),
+     B    (magnetic field vector: Zeeman term of the sweeps and Hanle term of
+           the update).
+   The iterates are rebuilt from the nearest checkpoint (ckpt - 1 forward
+   iterations at most per step back); each step back runs the adjoint of the
+   update, then the adjoint of the formal solution's J^K_Q and Lambda-bar*
+   (rays in batches whose forward Stokes vectors fit a device tape of at most
+   16 GB, the same gather-form adjoint sweep as porta_emergent_vjp,
+   per-cluster FP64 accumulators summed in a fixed order; the limit is
+   porta_set_tape_limit's). Gradients at kinks
+   of the BESSER control point take the branch the forward took.
+   grad_out: ndir*n_nu*ny*nx*NS doubles; out (may be NULL) the forward
+   profiles; g_chi, g_f: nvox doubles; g_b: 3*nvox doubles, [x|y|z][voxel]
+   (ignored, may be NULL, for the unpolarized model). Caller arrays are host
+   or device per `where`; mu, chi are host arrays. PORTA_ESTATE before
+   porta_iterate_ckpt. rho is left at the last iterate. Synchronous. */
+int porta_iterate_vjp(porta_ctx *c, int ndir, const double *mu, const double *chi, const double *grad_out,
+                      double *out, double *g_chi, double *g_f, double *g_b, int where);
+
+/* Device memory for the forward Stokes vectors that porta_iterate_vjp keeps
+   per ray batch: at most `bytes` (at least one ray's worth); 0 restores the
+   default of 16 GB. Fewer bytes, more batches; the result is the same. */
+int porta_set_tape_limit(porta_ctx *c, long long bytes);
+
+/* Device time (ms, CUDA events on the context's stream) of the phases of the
+   last porta_iterate_vjp, summed over its steps back: ms[0] rebuilding the
+   iterates (checkpoint copy, forward iterations, formal solution, J^K_Q
+   sums), ms[1] the update's adjoint, ms[2] the forward sweeps that write the
+   tape, ms[3] the J^K_Q / Lambda-bar* adjoint sweeps, ms[4] the sums of the
+   per-cluster accumulators. The first call for a batch size also times the
+   adjoint launch shapes, outside these figures. */
+int porta_iterate_timing(const porta_ctx *c, float *ms);
+
 /* Non-linear multigrid (Sec. 6, full-approximation form). porta_mg_setup
    builds nlevels - 1 coarser grids by keeping every other node on each axis
    (coarse (i, j, k) = fine (2i, 2j, 2k); nz -> (nz + 1)/2 for odd nz, nz/2

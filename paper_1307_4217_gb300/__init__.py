@@ -17,4 +17,6 @@ from .binding import (  # noqa: F401
     porta_formal_solve_noalloc, porta_run_iterations, PORTA_ESCRATCH, PORTA_NOALLOC_SCRATCH_BYTES,
     porta_emergent_vjp, porta_set_adjoint_launch, porta_adjoint_info, porta_adjoint_timing,
     porta_fill_info, porta_set_fill, porta_mg_setup, porta_mg_levels, porta_mg_vcycle,
+    porta_iterate_ckpt, porta_iterate_vjp, porta_set_tape_limit,
+    porta_iterate_timing,
 )

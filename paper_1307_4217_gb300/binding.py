@@ -80,6 +80,10 @@ _SIGS = {
     "porta_mg_setup": (_I, [_P, _I]),
     "porta_mg_levels": (_I, [_P, _P, _P]),
     "porta_mg_vcycle": (_I, [_P, _I, _I, _I, _P]),
+    "porta_iterate_ckpt": (_I, [_P, _I, _I, _P]),
+    "porta_iterate_vjp": (_I, [_P, _I, _P, _P, _P, _P, _P, _P, _P, _I]),
+    "porta_set_tape_limit": (_I, [_P, ctypes.c_longlong]),
+    "porta_iterate_timing": (_I, [_P, _P]),
 }
 
 _lib = None
@@ -293,6 +297,25 @@ def porta_mg_vcycle(h, npre, npost, ncoarse, out=None):
     return lib().porta_mg_vcycle(h, npre, npost, ncoarse, ctypes.byref(out) if out is not None else None)
 
 
+def porta_iterate_ckpt(h, niter, ckpt, out=None):
+    return lib().porta_iterate_ckpt(h, niter, ckpt, ctypes.byref(out) if out is not None else None)
+
+
+def porta_iterate_vjp(h, ndir, mu_ptr, chi_ptr, grad_ptr, out_ptr, gchi_ptr, gf_ptr, gb_ptr, where):
+    return lib().porta_iterate_vjp(h, ndir, mu_ptr, chi_ptr, grad_ptr, out_ptr, gchi_ptr, gf_ptr, gb_ptr, where)
+
+
+def porta_set_tape_limit(h, nbytes):
+    return lib().porta_set_tape_limit(h, int(nbytes))
+
+
+def porta_iterate_timing(h):
+    ms = (ctypes.c_float * 5)()
+    rc = lib().porta_iterate_timing(h, ms)
+    keys = ("recompute_ms", "see_adjoint_ms", "tape_forward_ms", "jkq_adjoint_ms", "reduce_ms")
+    return rc, dict(zip(keys, list(ms)))
+
+
 # ---- convenience wrapper ------------------------------------------------------------
 
 class Context:
@@ -428,6 +451,48 @@ class Context:
             ptrs.append(p)
         self._check(porta_emergent_vjp(self.h, len(mu), mu.ctypes.data, chi.ctypes.data, pg, *ptrs, where))
         return (g_chi, g_e, g_b) if out is None else (g_chi, g_e, g_b, out)
+
+    def iterate_ckpt(self, niter, ckpt, residual=True):
+        """niter Jacobi iterations from the current rho keeping a checkpoint of rho
+        every ckpt iterations (for iterate_vjp); returns the last update's change."""
+        out = ctypes.c_double() if residual else None
+        self._check(porta_iterate_ckpt(self.h, niter, ckpt, out))
+        return out.value if residual else None
+
+    def iterate_vjp(self, mu, chi, grad_out, out=None, g_chi=None, g_f=None, g_b=None):
+        """Gradients of sum(grad_out * emergent_stokes(mu, chi)) at the last iterate of
+        iterate_ckpt with respect to per-voxel chi, the thermal term f = eps B and B,
+        through the iterations: returns (g_chi, g_f, g_b[, out]). grad_out and the
+        optional output arrays are all numpy (host) or all CUDA tensors."""
+        mu = np.ascontiguousarray(mu, dtype=np.float64)
+        chi = np.ascontiguousarray(chi, dtype=np.float64)
+        pg, where, kg = _ptr_where(grad_out)
+        if g_chi is None:
+            if where == PORTA_DEVICE:
+                import torch
+                dev = grad_out.device
+                g_chi = torch.empty(self.shape, dtype=torch.float64, device=dev)
+                g_f = torch.empty(self.shape, dtype=torch.float64, device=dev)
+                g_b = torch.empty((3,) + self.shape, dtype=torch.float64, device=dev)
+            else:
+                g_chi, g_f, g_b = np.zeros(self.shape), np.zeros(self.shape), np.zeros((3,) + self.shape)
+        ptrs = []
+        for arr in (out, g_chi, g_f, g_b):
+            p, w, keep = _ptr_where(arr)
+            if arr is not None and w != where:
+                raise TypeError("grad_out and the outputs must all be host or all device")
+            ptrs.append(p)
+        self._check(porta_iterate_vjp(self.h, len(mu), mu.ctypes.data, chi.ctypes.data, pg, *ptrs, where))
+        return (g_chi, g_f, g_b) if out is None else (g_chi, g_f, g_b, out)
+
+    def iterate_timing(self):
+        rc, t = porta_iterate_timing(self.h)
+        self._check(rc)
+        return t
+
+    def set_tape_limit(self, nbytes=0):
+        """Device bytes for the per-batch forward tape of iterate_vjp (0: 16 GB)."""
+        self._check(porta_set_tape_limit(self.h, nbytes))
 
     def set_adjoint_launch(self, cluster=0, nu_group=0):
         self._check(porta_set_adjoint_launch(self.h, cluster, nu_group))

@@ -132,10 +132,40 @@ __device__ __forceinline__ void node_param_grad(const Node<Real, NS> &n, Real x,
     }
 }
 
+// the same in the unknowns: dL/dchi at fixed rho, dL/dB (3) and dL/drho (up to 6)
+// added to o[10] (eps_i = chi phi S_i(rho), eps_V = S00 eta_V, S_i = sum_c T_ic rho_c
+// with the real multipole layout's factor 2 for Q != 0)
 template <typename Real, int NS>
+__device__ __forceinline__ void node_param_grad_rho(const Node<Real, NS> &n, const RayDev<Real> &ray, Real bfac, Real x,
+                                                    const Real *t, double *o)
+{
+    const Real xs = x - n.s;
+    const Real ph = profile_shape(xs);
+    if constexpr (NS == 1) {
+        o[0] += (double)(ph * (t[0] + n.S * t[1]));
+        o[4] += (double)(n.chi * ph * t[1]);
+    } else {
+        const Real bxs = n.b * xs;
+        o[0] += (double)(ph * (t[0] + bxs * t[1] + n.SI * t[2] + n.SQ * t[3] + n.SU * t[4] + bxs * n.S00 * t[5]));
+        const Real gb = bfac * xs * ph * n.chi * (t[1] + n.S00 * t[5]);
+        o[1] += (double)(gb * ray.ox);
+        o[2] += (double)(gb * ray.oy);
+        o[3] += (double)(gb * ray.oz);
+        const Real cp = n.chi * ph;
+        const Real gS[3] = {cp * t[2], cp * t[3], cp * t[4]};
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            const Real f2 = c >= 2 ? Real(2) : Real(1);
+            o[4 + c] += (double)(f2 * (ray.t[c] * gS[0] + ray.t[6 + c] * gS[1] + ray.t[12 + c] * gS[2]));
+        }
+        o[4] += (double)(cp * bxs * t[5]);
+    }
+}
+
+template <typename Real, int NS, int FORM>
 __device__ __forceinline__ void adjoint_item(const SweepArgs<Real> &a, cg::cluster_group &cluster,
                                              typename V16<Real>::T *ring, Real *gI, Real *gM, Real *gP, Real *T,
-                                             Real *tt, int d, int g, int rank, int C, int item)
+                                             Real *tt, int d, int g, int rank, int C, int item, int cid)
 {
     constexpr int NM = adj_nm<NS>(), NP = adj_np<NS>();
     constexpr int NCH = node_words<NS>() * (int)sizeof(Real) / 16;
@@ -165,7 +195,10 @@ __device__ __forceinline__ void adjoint_item(const SweepArgs<Real> &a, cg::clust
     const int plane = NCH * chunk;
     const int npts = R * nx;
     const Real *tape = a.store + (long long)d * a.nnu * a.nvox * NS;
-    Real *gout_part = a.gpart + (long long)item * 3 * a.nvox;
+    Real *gout_part = FORM == 0 ? a.gpart + (long long)item * 3 * a.nvox : nullptr;
+    double *acc = FORM != 0 ? a.gacc + (long long)cid * 10 * a.nvox : nullptr;
+    const int mglob = a.ray0 + d;                       // ray index for the J weights (form 2)
+    const Real wray = FORM == 2 ? (Real)a.tw[19 * mglob] : Real(0);
     // buffer offsets: gI[par][f][s][p], gM[f][k][p], gP[f][k][p], T[par][f][k][p]
     auto xI = [&](int par, int f, int s, int p) { return ((par * F + f) * NS + s) * ipts + p; };
     auto xM = [&](int f, int k, int p) { return (f * NM + k) * ipts + p; };
@@ -182,7 +215,7 @@ __device__ __forceinline__ void adjoint_item(const SweepArgs<Real> &a, cg::clust
             int pj = (row0 + lr - 1 + gq.ay) % ny;
             pj += pj < 0 ? ny : 0;
             const long long v = B.vox0 + ((long long)gq.kz * ny + pj) * nx + pi;
-            ring_store<Real, NS>(ring, plane, chunk, q % 3, idx, make_node<Real, NS>(a, ray, v, d, false));
+            ring_store<Real, NS>(ring, plane, chunk, q % 3, idx, make_node<Real, NS>(a, ray, v, mglob, FORM == 2));
         }
     };
     // physical voxel of sheared node (c, local row l) of plane q
@@ -204,6 +237,7 @@ __device__ __forceinline__ void adjoint_item(const SweepArgs<Real> &a, cg::clust
             const Real *ph = last ? gP_next : gP;
             const int lh = last ? 0 : (l + 1) * nx;
             Real gchi = 0, ge = 0, gb = 0;
+            double o[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
             for (int f = 0; f < nf; ++f) {
                 Real t[NM];
 #pragma unroll
@@ -220,12 +254,21 @@ __device__ __forceinline__ void adjoint_item(const SweepArgs<Real> &a, cg::clust
 #pragma unroll
                     for (int s = 0; s < NS; ++s) t[NM - NS + s] += gp[1 + s];
                 }
-                node_param_grad<Real, NS>(n, a.xf[j0 + f], t, gchi, ge, gb);
+                if constexpr (FORM == 0)
+                    node_param_grad<Real, NS>(n, a.xf[j0 + f], t, gchi, ge, gb);
+                else
+                    node_param_grad_rho<Real, NS>(n, ray, a.bfac, a.xf[j0 + f], t, o);
             }
             const long long v = B.vox0 + voxel(gq, c, l);
-            gout_part[v] = gchi;
-            gout_part[a.nvox + v] = ge;
-            gout_part[2 * a.nvox + v] = gb;
+            if constexpr (FORM == 0) {
+                gout_part[v] = gchi;
+                gout_part[a.nvox + v] = ge;
+                gout_part[2 * a.nvox + v] = gb;
+            } else {
+                // this cluster's accumulators; a node is finalized by one thread per item
+#pragma unroll
+                for (int k = 0; k < 10; ++k) acc[k * a.nvox + v] += o[k];
+            }
         }
     };
 
@@ -290,6 +333,23 @@ __device__ __forceinline__ void adjoint_item(const SweepArgs<Real> &a, cg::clust
                 kP[0] = kP[1] = kP[2] = kP[3] = corner_p<Real, NS>(nO, Real(0));
             }
             const long long vO = voxel(gq, c, l);
+            // form 2: dL/dI_p per unit J weight at O, sum_KQ T^K_Q(p, Omega) dL/dJ^K_Q, and dL/dLambda*
+            Real gdir[3] = {0, 0, 0}, gLv = 0;
+            if constexpr (FORM == 2) {
+                const double *gj = a.gjkq + (B.vox0 + vO) * (NS == 1 ? 1 : 6);
+                if constexpr (NS == 1) {
+                    gdir[0] = (Real)gj[0];
+                } else {
+#pragma unroll
+                    for (int s = 0; s < 3; ++s) {
+                        Real acc_s = 0;
+#pragma unroll
+                        for (int c6 = 0; c6 < 6; ++c6) acc_s += ray.t[6 * s + c6] * (Real)gj[c6];
+                        gdir[s] = acc_s;
+                    }
+                }
+                gLv = (Real)a.glstar[B.vox0 + vO];
+            }
             // rows of the Stokes-adjoint gather from plane q+1: (c|c-1, l|l-1)
             const bool first = l == 0;
             const Real *glo = first ? gI_prev : gI;
@@ -300,9 +360,14 @@ __device__ __forceinline__ void adjoint_item(const SweepArgs<Real> &a, cg::clust
                 const Real x = a.xf[j];
                 Real lam[NS];
                 if (q == nz - 1) {
-                    const double *go = a.gout + (((long long)d * a.nnu + j) * nxy + (vO - (long long)gq.kz * nxy)) * NS;
+                    if constexpr (FORM == 2) {
 #pragma unroll
-                    for (int s = 0; s < NS; ++s) lam[s] = (Real)go[s];
+                        for (int s = 0; s < NS; ++s) lam[s] = Real(0);
+                    } else {
+                        const double *go = a.gout + (((long long)d * a.nnu + j) * nxy + (vO - (long long)gq.kz * nxy)) * NS;
+#pragma unroll
+                        for (int s = 0; s < NS; ++s) lam[s] = (Real)go[s];
+                    }
                 } else {
 #pragma unroll
                     for (int s = 0; s < NS; ++s)
@@ -396,6 +461,17 @@ __device__ __forceinline__ void adjoint_item(const SweepArgs<Real> &a, cg::clust
 #pragma unroll
                     for (int s = 0; s < NS; ++s) cM[s] = Real(0.5) * (SM[s] + SO[s]);
                 }
+                // form 2: the J^K_Q and Lambda-bar* sums weigh I_O and Lambda*_O by w_m w_j phi_O / N
+                Real lw = 0;
+                if constexpr (FORM == 2) {
+                    const Real wt = wray * a.wf[j] * phO * nO.invn;
+                    lam[0] += wt * gdir[0];
+                    if constexpr (NS == 4) {
+                        lam[1] += wt * gdir[1];
+                        lam[2] += wt * gdir[2];
+                    }
+                    lw = wt * gLv;
+                }
                 // ---- reverse step ----
                 Real gr[NS], g_pm = 0, g_po = 0, g_kvM = 0, g_kvO = 0, kvM = 0, kvO = 0;
                 if constexpr (NS == 1) {
@@ -447,6 +523,8 @@ __device__ __forceinline__ void adjoint_item(const SweepArgs<Real> &a, cg::clust
                 }
                 const CoefD<Real> cd = coefficient_derivs(tMO, co);
                 g_tM += g_e * cd.de + g_pm * cd.dpm + g_po * cd.dpo + g_wm * cd.dwm + g_wo * cd.dwo + g_wc * cd.dwc;
+                if constexpr (FORM == 2)   // Lambda* = w_O + w_C (w_C/2 on the last plane)
+                    g_tM += lw * (cd.dwo + (has_p ? Real(1) : Real(0.5)) * cd.dwc);
                 Real g_etaM = Real(0.5) * dsM * g_tM;
                 Real g_etaO = Real(0.5) * dsM * g_tM + Real(0.5) * dsP * g_tP;
                 Real g_etaP = Real(0.5) * dsP * g_tP;
@@ -519,7 +597,7 @@ __device__ __forceinline__ void adjoint_item(const SweepArgs<Real> &a, cg::clust
     __syncthreads();
 }
 
-template <typename Real, int NS>
+template <typename Real, int NS, int FORM>
 __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 2 : 1) adjoint_kernel(const SweepArgs<Real> a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -539,7 +617,7 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 2 : 1) adjoint_kernel
     cluster.sync();
     for (int item = cid; item < a.nitems; item += ncl) {
         const int d = item / a.ngroups, g = item - d * a.ngroups;
-        adjoint_item<Real, NS>(a, cluster, ring, gI, gM, gP, T, tt, d, g, rank, C, item);
+        adjoint_item<Real, NS, FORM>(a, cluster, ring, gI, gM, gP, T, tt, d, g, rank, C, item, cid);
         cluster.sync();
     }
 }
@@ -572,18 +650,26 @@ __global__ void adjoint_reduce_kernel(const Real *gpart, int nitems, int ngroups
 }
 
 template <typename Real, int NS>
-static cudaError_t prepare_adjoint(int cluster, int smem)
+static void *adjoint_ptr(int form)
 {
-    cudaError_t e = cudaFuncSetAttribute(adjoint_kernel<Real, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    return form == 0 ? (void *)adjoint_kernel<Real, NS, 0>
+                     : (form == 1 ? (void *)adjoint_kernel<Real, NS, 1> : (void *)adjoint_kernel<Real, NS, 2>);
+}
+
+template <typename Real, int NS>
+static cudaError_t prepare_adjoint(int cluster, int smem, int form)
+{
+    const void *k = adjoint_ptr<Real, NS>(form);
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    if (cluster > 8) e = cudaFuncSetAttribute(adjoint_kernel<Real, NS>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (cluster > 8) e = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     return e;
 }
 
 template <typename Real, int NS>
-cudaError_t adjoint_max_active_clusters(int cluster, int smem, int threads, int *out)
+cudaError_t adjoint_max_active_clusters(int cluster, int smem, int threads, int *out, int form)
 {
-    cudaError_t e = prepare_adjoint<Real, NS>(cluster, smem);
+    cudaError_t e = prepare_adjoint<Real, NS>(cluster, smem, form);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t lc = {};
     lc.gridDim = dim3(cluster);
@@ -596,13 +682,13 @@ cudaError_t adjoint_max_active_clusters(int cluster, int smem, int threads, int 
     at[0].val.clusterDim.z = 1;
     lc.attrs = at;
     lc.numAttrs = 1;
-    return cudaOccupancyMaxActiveClusters(out, adjoint_kernel<Real, NS>, &lc);
+    return cudaOccupancyMaxActiveClusters(out, adjoint_ptr<Real, NS>(form), &lc);
 }
 
 template <typename Real, int NS>
-cudaError_t launch_adjoint(const SweepArgs<Real> &a, const LaunchCfg &cfg, cudaStream_t st)
+cudaError_t launch_adjoint(const SweepArgs<Real> &a, const LaunchCfg &cfg, cudaStream_t st, int form)
 {
-    cudaError_t e = prepare_adjoint<Real, NS>(cfg.cluster, cfg.smem);
+    cudaError_t e = prepare_adjoint<Real, NS>(cfg.cluster, cfg.smem, form);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t lc = {};
     lc.gridDim = dim3(cfg.clusters * cfg.cluster);
@@ -616,7 +702,39 @@ cudaError_t launch_adjoint(const SweepArgs<Real> &a, const LaunchCfg &cfg, cudaS
     at[0].val.clusterDim.z = 1;
     lc.attrs = at;
     lc.numAttrs = 1;
-    return cudaLaunchKernelEx(&lc, adjoint_kernel<Real, NS>, a);
+    if (form == 0) return cudaLaunchKernelEx(&lc, adjoint_kernel<Real, NS, 0>, a);
+    if (form == 1) return cudaLaunchKernelEx(&lc, adjoint_kernel<Real, NS, 1>, a);
+    return cudaLaunchKernelEx(&lc, adjoint_kernel<Real, NS, 2>, a);
+}
+
+// per voxel: sum of the per-cluster accumulators in cluster order
+__global__ void adjoint_acc_reduce_kernel(const double *gacc, int nclusters, long long nvox, int nl, double *g_chi,
+                                          double *g_b, double *g_rho)
+{
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < nvox; v += (long long)gridDim.x * blockDim.x) {
+        double s[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+        for (int cl = 0; cl < nclusters; ++cl) {
+            const double *p = gacc + (long long)cl * 10 * nvox + v;
+#pragma unroll
+            for (int k = 0; k < 10; ++k) s[k] += p[k * nvox];
+        }
+        g_chi[v] += s[0];
+        if (g_b) {
+            g_b[v] += s[1];
+            g_b[nvox + v] += s[2];
+            g_b[2 * nvox + v] += s[3];
+        }
+        for (int c = 0; c < nl; ++c) g_rho[v * nl + c] = s[4 + c];
+    }
+}
+
+cudaError_t launch_adjoint_acc_reduce(const double *gacc, int nclusters, long long nvox, int nl, double *g_chi,
+                                      double *g_b, double *g_rho, cudaStream_t st)
+{
+    const int threads = 256;
+    const long long blocks = std::min<long long>((nvox + threads - 1) / threads, 152LL * 16);
+    adjoint_acc_reduce_kernel<<<(int)blocks, threads, 0, st>>>(gacc, nclusters, nvox, nl, g_chi, g_b, g_rho);
+    return cudaGetLastError();
 }
 
 template <typename Real>
@@ -631,8 +749,8 @@ cudaError_t launch_adjoint_reduce(const Real *gpart, int nitems, int ngroups, lo
 
 #define PORTA_ADJ_INST(R, N)                                                                        \
     template int adjoint_smem_bytes<R, N>(int, int, int, int);                                      \
-    template cudaError_t adjoint_max_active_clusters<R, N>(int, int, int, int *);                   \
-    template cudaError_t launch_adjoint<R, N>(const SweepArgs<R> &, const LaunchCfg &, cudaStream_t);
+    template cudaError_t adjoint_max_active_clusters<R, N>(int, int, int, int *, int);              \
+    template cudaError_t launch_adjoint<R, N>(const SweepArgs<R> &, const LaunchCfg &, cudaStream_t, int);
 PORTA_ADJ_INST(float, 1)
 PORTA_ADJ_INST(float, 4)
 PORTA_ADJ_INST(double, 1)

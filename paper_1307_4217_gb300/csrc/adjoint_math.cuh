@@ -98,4 +98,43 @@ __device__ __forceinline__ CpGrad<Real> control_point_grad(Real yM, Real yO, Rea
     return r;
 }
 
+// Solve M^T x = r with M the real matrix of hanle_solve5 (same scaling
+// argument: M^T is the identity minus the antisymmetric part after the sqrt(2)
+// rescaling, so elimination without pivoting is stable).
+__device__ __forceinline__ void hanle_solve5_t(double gx, double gy, double gz, const double r[5], double x[5])
+{
+    const double s6 = 2.449489742783178098197284;  // sqrt(6)
+    const double M[5][5] = {
+        {1.0, s6 * gy, -s6 * gx, 0.0, 0.0},
+        {-0.5 * s6 * gy, 1.0, -gz, gy, -gx},
+        {0.5 * s6 * gx, gz, 1.0, gx, gy},
+        {0.0, -gy, -gx, 1.0, -2.0 * gz},
+        {0.0, gx, -gy, 2.0 * gz, 1.0},
+    };
+    double A[5][6];
+#pragma unroll
+    for (int a = 0; a < 5; ++a) {
+#pragma unroll
+        for (int c = 0; c < 5; ++c) A[a][c] = M[c][a];
+        A[a][5] = r[a];
+    }
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+        const double inv = 1.0 / A[c][c];
+#pragma unroll
+        for (int q = c + 1; q < 5; ++q) {
+            const double f = A[q][c] * inv;
+#pragma unroll
+            for (int s = c; s < 6; ++s) A[q][s] -= f * A[c][s];
+        }
+    }
+#pragma unroll
+    for (int q = 4; q >= 0; --q) {
+        double s = A[q][5];
+#pragma unroll
+        for (int t = q + 1; t < 5; ++t) s -= A[q][t] * x[t];
+        x[q] = s / A[q][q];
+    }
+}
+
 }  // namespace porta

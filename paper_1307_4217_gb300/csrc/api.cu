@@ -562,12 +562,12 @@ int emergent_shape(porta_ctx *c, SweepArgs<Real> &a, int ndir, LaunchCfg &cfg)
         a.nitems = ndir * a.ngroups;
         k.clusters = std::min(k.clusters, a.nitems);
     };
-    if (c->user_shape || c->emg_tuned_ndir == ndir) {
+    if (c->user_shape || c->emg_tuned.count(ndir)) {
         if (c->user_shape) {
             int rc = choose_launch<Real, NS>(c, cfg, c->opt_cluster, c->opt_nu_group, ndir);
             if (rc) return fail(c, rc, "no sweep launch shape fits this grid");
         } else {
-            cfg = c->emg_tuned;
+            cfg = c->emg_tuned[ndir];
         }
         shape(cfg);
         return PORTA_OK;
@@ -608,8 +608,7 @@ int emergent_shape(porta_ctx *c, SweepArgs<Real> &a, int ndir, LaunchCfg &cfg)
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (e != cudaSuccess) return fail(c, PORTA_ECUDA, std::string("emergent shape timing: ") + cudaGetErrorString(e));
-    c->emg_tuned = cfg;
-    c->emg_tuned_ndir = ndir;
+    c->emg_tuned[ndir] = cfg;
     shape(cfg);
     return PORTA_OK;
 }
@@ -729,7 +728,7 @@ int choose_adjoint(porta_ctx *c, LaunchCfg &best, int force_c, int force_f, int 
 // all pointers are device memory; dout may be null
 template <typename Real>
 int emergent_vjp_t(porta_ctx *c, int ndir, const double *mu, const double *chi, const double *dgrad, double *dout,
-                   double *dg_chi, double *dg_e, double *dg_b)
+                   double *dg_chi, double *dg_e, double *dg_b, double *dg_rho = nullptr)
 {
     std::vector<PlaneGeom<Real>> geom((size_t)ndir * c->nz);
     std::vector<RayDev<Real>> rays(ndir);
@@ -825,11 +824,24 @@ int emergent_vjp_t(porta_ctx *c, int ndir, const double *mu, const double *chi, 
             e = cudaEventRecord(c->adj_ev[1], c->stream);
         }
         SweepArgs<Real> b = args_for(acfg);
-        if (e == cudaSuccess)
-            e = c->ns == 1 ? launch_adjoint<Real, 1>(b, acfg, c->stream) : launch_adjoint<Real, 4>(b, acfg, c->stream);
-        if (e == cudaSuccess)
-            e = launch_adjoint_reduce<Real>((const Real *)c->d_gpart, b.nitems, b.ngroups, c->nvox, dr,
-                                            2.0 * c->gbar * c->zeta, dg_chi, dg_e, c->ns == 1 ? nullptr : dg_b, c->stream);
+        if (!dg_rho) {
+            if (e == cudaSuccess)
+                e = c->ns == 1 ? launch_adjoint<Real, 1>(b, acfg, c->stream) : launch_adjoint<Real, 4>(b, acfg, c->stream);
+            if (e == cudaSuccess)
+                e = launch_adjoint_reduce<Real>((const Real *)c->d_gpart, b.nitems, b.ngroups, c->nvox, dr,
+                                                2.0 * c->gbar * c->zeta, dg_chi, dg_e, c->ns == 1 ? nullptr : dg_b, c->stream);
+        } else {
+            // gradients in the unknowns: per-cluster accumulators, then their sum
+            if (e == cudaSuccess)
+                e = ensure_buf((void **)&c->d_gacc, c->gacc_bytes, (size_t)acfg.clusters * 10 * c->nvox * sizeof(double));
+            if (e == cudaSuccess) e = cudaMemsetAsync(c->d_gacc, 0, (size_t)acfg.clusters * 10 * c->nvox * sizeof(double), c->stream);
+            b.gacc = c->d_gacc;
+            if (e == cudaSuccess)
+                e = c->ns == 1 ? launch_adjoint<Real, 1>(b, acfg, c->stream, 1) : launch_adjoint<Real, 4>(b, acfg, c->stream, 1);
+            if (e == cudaSuccess)
+                e = launch_adjoint_acc_reduce(c->d_gacc, acfg.clusters, c->nvox, c->nl, dg_chi, c->ns == 1 ? nullptr : dg_b,
+                                              dg_rho, c->stream);
+        }
         if (e == cudaSuccess) e = cudaEventRecord(c->adj_ev[2], c->stream);
         if (e != cudaSuccess) { rc = fail(c, PORTA_ECUDA, std::string("emergent_vjp adjoint: ") + cudaGetErrorString(e)); break; }
         c->last_adj = acfg;
@@ -846,11 +858,16 @@ int emergent_vjp_t(porta_ctx *c, int ndir, const double *mu, const double *chi, 
 }
 
 void mg_free(porta_ctx *c);
+void it_free(porta_ctx *c);
 
 void free_all(porta_ctx *c)
 {
     drop_graph(c);
     mg_free(c);
+    it_free(c);
+    if (c->d_gacc) cudaFree(c->d_gacc);
+    for (cudaEvent_t &ev : c->it_ev)
+        if (ev) cudaEventDestroy(ev);
     if (c->d_cv64) cudaFree(c->d_cv64);
     if (c->fill) {
         if (c->fill->stream) cudaStreamDestroy(c->fill->stream);
@@ -895,6 +912,235 @@ int count_bad(porta_ctx *c, const double *d, long long n, double lo, double hi, 
     return PORTA_OK;
 }
 
+
+// ---------------------------------------------------------------- differentiation through iterations
+
+// Gradients of sum g_J J^K_Q + sum g_L Lambda-bar* (the sums of a formal solution at
+// the current rho) with respect to chi at fixed rho (added), B (added) and rho
+// (overwritten). Rays in batches: the emergent-mode sweep over a batch's rays writes
+// the tape, the adjoint (form 2) accumulates per cluster; one sum at the end.
+template <typename Real>
+int jkq_vjp_t(porta_ctx *c, const double *dgj, const double *dgl, double *dg_chi, double *dg_b, double *dg_rho)
+{
+    const long long nxy = (long long)c->nx * c->ny;
+    const size_t per_ray = (size_t)c->n_nu * c->nvox * c->ns * sizeof(Real);
+    // batches of equal size (the last one may be smaller) within the tape limit
+    const int nbmax = (int)std::max<size_t>(1, std::min<size_t>(c->nray, c->tape_limit / per_ray));
+    const int nbatch = (c->nray + nbmax - 1) / nbmax;
+    const int nb = (c->nray + nbatch - 1) / nbatch;
+    cudaError_t e = ensure_buf(&c->d_tape, c->tape_bytes, (size_t)nb * per_ray);
+    double *scratch = nullptr;
+    if (e == cudaSuccess) e = dalloc(&scratch, (size_t)nb * c->n_nu * nxy * c->ns);
+    for (int k = 0; k < 4 && e == cudaSuccess; ++k)
+        if (!c->it_ev[k]) e = cudaEventCreate(&c->it_ev[k]);
+    if (e != cudaSuccess) {
+        if (scratch) cudaFree(scratch);
+        return fail(c, PORTA_ENOMEM, "iterate_vjp: tape allocation");
+    }
+    // adjoint launch shape: forced, else timed once per batch size on the first batch
+    LaunchCfg acfg{};
+    std::vector<LaunchCfg> cand;
+    const bool forced = c->adj_cluster > 0 || c->adj_nu_group > 0;
+    const bool tune = !forced && !c->adj2_tuned.count(nb);
+    int rc = c->ns == 1 ? choose_adjoint<Real, 1>(c, acfg, c->adj_cluster, c->adj_nu_group, nb, tune ? &cand : nullptr)
+                        : choose_adjoint<Real, 4>(c, acfg, c->adj_cluster, c->adj_nu_group, nb, tune ? &cand : nullptr);
+    if (rc) {
+        cudaFree(scratch);
+        return fail(c, rc, "iterate_vjp: no adjoint launch shape fits");
+    }
+    if (!forced && !tune) acfg = c->adj2_tuned[nb];
+    int maxcl = acfg.clusters;
+    for (const LaunchCfg &k : cand) maxcl = std::max(maxcl, k.clusters);
+    e = ensure_buf((void **)&c->d_gacc, c->gacc_bytes, (size_t)maxcl * 10 * c->nvox * sizeof(double));
+    if (e != cudaSuccess) {
+        cudaFree(scratch);
+        return fail(c, PORTA_ENOMEM, "iterate_vjp: accumulator allocation");
+    }
+    // forward: Stokes vectors of every node for rays r0 .. r0 + n - 1
+    auto forward = [&](int r0, int n) -> int {
+        SweepArgs<Real> a = base_args<Real>(c);
+        a.geom = (const PlaneGeom<Real> *)c->d_geom + (size_t)r0 * c->nz;
+        a.rays = (const RayDev<Real> *)c->d_rays + r0;
+        a.out = scratch;
+        a.store = (Real *)c->d_tape;
+        LaunchCfg cfg{};
+        int r = c->ns == 1 ? emergent_shape<Real, 1>(c, a, n, cfg) : emergent_shape<Real, 4>(c, a, n, cfg);
+        if (r) return r;
+        e = c->ns == 1 ? launch_sweep<Real, 1>(a, MODE_EMERGENT, cfg, c->stream)
+                       : launch_sweep<Real, 4>(a, MODE_EMERGENT, cfg, c->stream);
+        return e == cudaSuccess ? PORTA_OK : fail(c, PORTA_ECUDA, std::string("iterate_vjp: ") + cudaGetErrorString(e));
+    };
+    // reverse: the J^K_Q and Lambda-bar* terms of the same rays
+    auto reverse = [&](int r0, int n, LaunchCfg k) -> int {
+        SweepArgs<Real> b = base_args<Real>(c);
+        b.geom = (const PlaneGeom<Real> *)c->d_geom + (size_t)r0 * c->nz;
+        b.rays = (const RayDev<Real> *)c->d_rays + r0;
+        b.store = (Real *)c->d_tape;
+        b.invn = (const Real *)c->d_invn;
+        b.gjkq = dgj;
+        b.glstar = dgl;
+        b.tw = c->d_tw;
+        b.ray0 = r0;
+        b.gacc = c->d_gacc;
+        b.F = k.F;
+        b.ngroups = (c->n_nu + k.F - 1) / k.F;
+        if (c->ns == 1)
+            launch_caps<Real, 1>(c, k.cluster, b.ring_plane, b.ipts_max);
+        else
+            launch_caps<Real, 4>(c, k.cluster, b.ring_plane, b.ipts_max);
+        b.nitems = n * b.ngroups;
+        k.clusters = std::min(k.clusters, b.nitems);
+        e = c->ns == 1 ? launch_adjoint<Real, 1>(b, k, c->stream, 2) : launch_adjoint<Real, 4>(b, k, c->stream, 2);
+        return e == cudaSuccess ? PORTA_OK : fail(c, PORTA_ECUDA, std::string("iterate_vjp adjoint: ") + cudaGetErrorString(e));
+    };
+    cudaEvent_t *ev = c->it_ev;
+    if (tune) {
+        rc = forward(0, nb);
+        float best = 1e30f;
+        for (const LaunchCfg &k : cand) {
+            if (rc) break;
+            float ms = 0;
+            e = cudaEventRecord(ev[0], c->stream);
+            if (e == cudaSuccess) rc = reverse(0, nb, k);
+            if (rc) break;
+            e = cudaEventRecord(ev[1], c->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev[0], ev[1]);
+            if (e != cudaSuccess) {
+                rc = fail(c, PORTA_ECUDA, std::string("iterate_vjp tuning: ") + cudaGetErrorString(e));
+                break;
+            }
+            if (ms < best) {
+                best = ms;
+                acfg = k;
+            }
+        }
+        if (rc == PORTA_OK) c->adj2_tuned[nb] = acfg;
+    }
+    if (rc == PORTA_OK) {
+        e = cudaMemsetAsync(c->d_gacc, 0, (size_t)acfg.clusters * 10 * c->nvox * sizeof(double), c->stream);
+        if (e != cudaSuccess) rc = fail(c, PORTA_ECUDA, cudaGetErrorString(e));
+    }
+    for (int r0 = 0; r0 < c->nray && rc == PORTA_OK; r0 += nb) {
+        const int n = std::min(nb, c->nray - r0);
+        float t0 = 0, t1 = 0;
+        e = cudaEventRecord(ev[0], c->stream);
+        if (e == cudaSuccess) rc = forward(r0, n);
+        if (rc) break;
+        e = cudaEventRecord(ev[1], c->stream);
+        if (e == cudaSuccess) rc = reverse(r0, n, acfg);
+        if (rc) break;
+        e = cudaEventRecord(ev[2], c->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(ev[2]);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t0, ev[0], ev[1]);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t1, ev[1], ev[2]);
+        if (e != cudaSuccess) rc = fail(c, PORTA_ECUDA, std::string("iterate_vjp: ") + cudaGetErrorString(e));
+        c->it_ms[2] += t0;
+        c->it_ms[3] += t1;
+    }
+    if (rc == PORTA_OK) {
+        float t = 0;
+        e = cudaEventRecord(ev[0], c->stream);
+        if (e == cudaSuccess)
+            e = launch_adjoint_acc_reduce(c->d_gacc, acfg.clusters, c->nvox, c->nl, dg_chi, c->ns == 1 ? nullptr : dg_b,
+                                          dg_rho, c->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[1], c->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, ev[0], ev[1]);
+        if (e != cudaSuccess) rc = fail(c, PORTA_ECUDA, std::string("iterate_vjp: ") + cudaGetErrorString(e));
+        c->it_ms[4] += t;
+        c->last_adj = acfg;
+    }
+    cudaStreamSynchronize(c->stream);
+    cudaFree(scratch);
+    return rc;
+}
+
+cudaError_t mg_rho_changed(porta_ctx *L);
+
+void it_free(porta_ctx *c)
+{
+    for (double *b : c->it_saved) cudaFree(b);
+    c->it_saved.clear();
+    if (c->it_final) cudaFree(c->it_final);
+    c->it_final = nullptr;
+    c->it_niter = c->it_ckpt = 0;
+}
+
+// one eager Jacobi iteration (formal solution, J^K_Q sums, update)
+int it_step(porta_ctx *c)
+{
+    int rc = porta_formal_solve(c);
+    if (rc == PORTA_OK) rc = porta_accumulate_jkq(c, nullptr, nullptr, PORTA_DEVICE);
+    if (rc == PORTA_OK) rc = porta_see_update(c, nullptr);
+    return rc;
+}
+
+int it_load(porta_ctx *c, const double *src)
+{
+    cudaError_t e = cudaMemcpyAsync(c->d_rho, src, sizeof(double) * c->nvox * c->nl, cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess) e = mg_rho_changed(c);
+    if (e != cudaSuccess) return fail(c, PORTA_ECUDA, std::string("iterate: ") + cudaGetErrorString(e));
+    c->have_rho = true;
+    c->have_fs = c->have_jkq = false;
+    return PORTA_OK;
+}
+
+template <typename Real>
+int iterate_vjp_t(porta_ctx *c, int ndir, const double *mu, const double *chi, const double *dgrad, double *dout,
+                  double *dg_chi, double *dg_f, double *dg_b)
+{
+    const size_t nr = (size_t)c->nvox * c->nl;
+    double *blk = nullptr;
+    // gbar (dL/drho of the current iterate), explicit part, dL/dJ, dL/dLambda*
+    CK(dalloc(&blk, 3 * nr + c->nvox));
+    double *gbar = blk, *gexp = blk + nr, *gj = blk + 2 * nr, *gl = blk + 3 * nr;
+    int rc = PORTA_OK;
+    cudaError_t e = cudaMemsetAsync(dg_chi, 0, sizeof(double) * c->nvox, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(dg_f, 0, sizeof(double) * c->nvox, c->stream);
+    if (e == cudaSuccess && dg_b) e = cudaMemsetAsync(dg_b, 0, sizeof(double) * 3 * c->nvox, c->stream);
+    if (e != cudaSuccess) rc = fail(c, PORTA_ECUDA, cudaGetErrorString(e));
+    // the loss: emergent Stokes of the final unknowns
+    if (rc == PORTA_OK) rc = it_load(c, c->it_final);
+    if (rc == PORTA_OK) rc = emergent_vjp_t<Real>(c, ndir, mu, chi, dgrad, dout, dg_chi, nullptr, dg_b, gbar);
+    for (float &t : c->it_ms) t = 0.f;
+    for (int k = 0; k < 4 && rc == PORTA_OK; ++k)
+        if (!c->it_ev[k] && cudaEventCreate(&c->it_ev[k]) != cudaSuccess) rc = fail(c, PORTA_ECUDA, "iterate_vjp: events");
+    cudaEvent_t *ev = c->it_ev;
+    for (int k = c->it_niter - 1; k >= 0 && rc == PORTA_OK; --k) {
+        // the iterate rho_k: from the checkpoint at or below k
+        const int base = k / c->it_ckpt;
+        e = cudaEventRecord(ev[0], c->stream);
+        rc = it_load(c, c->it_saved[base]);
+        for (int s = base * c->it_ckpt; s < k && rc == PORTA_OK; ++s) rc = it_step(c);
+        if (rc == PORTA_OK) rc = porta_formal_solve(c);
+        if (rc == PORTA_OK) rc = porta_accumulate_jkq(c, nullptr, nullptr, PORTA_DEVICE);
+        if (rc) break;
+        e = cudaEventRecord(ev[1], c->stream);
+        // reverse mode of the update rho_{k+1} = U(rho_k, J, Lambda*, f, B)
+        if (e == cudaSuccess)
+            e = run_see_vjp(c->nvox, c->nl, c->model, c->bcrit, c->d_eps, c->d_bpl, c->d_b, c->d_jkq, c->d_lstar, nullptr,
+                            c->d_rho, gbar, gexp, gj, gl, dg_f, dg_b, c->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[2], c->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(ev[2]);
+        float t0 = 0, t1 = 0;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t0, ev[0], ev[1]);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t1, ev[1], ev[2]);
+        if (e != cudaSuccess) { rc = fail(c, PORTA_ECUDA, std::string("iterate_vjp: ") + cudaGetErrorString(e)); break; }
+        c->it_ms[0] += t0;
+        c->it_ms[1] += t1;
+        // ... and of J^K_Q, Lambda-bar* (gbar <- their gradient in rho_k), plus the explicit term
+        rc = jkq_vjp_t<Real>(c, gj, gl, dg_chi, dg_b, gbar);
+        if (rc) break;
+        e = run_axpy((long long)nr, 1.0, gexp, gbar, c->stream);
+        if (e != cudaSuccess) rc = fail(c, PORTA_ECUDA, std::string("iterate_vjp: ") + cudaGetErrorString(e));
+    }
+    // leave the context at the final unknowns
+    int rc2 = it_load(c, c->it_final);
+    cudaStreamSynchronize(c->stream);
+    cudaFree(blk);
+    return rc ? rc : rc2;
+}
 
 // ---------------------------------------------------------------- multigrid (Sec. 6)
 
@@ -1497,6 +1743,106 @@ int porta_emergent_vjp(porta_ctx *c, int ndir, const double *mu, const double *c
     return rc;
 }
 
+int porta_iterate_ckpt(porta_ctx *c, int niter, int ckpt, double *max_change)
+{
+    if (!c) return PORTA_EINVAL;
+    if (niter < 1 || ckpt < 1) return fail(c, PORTA_EINVAL, "iterate_ckpt: niter >= 1, ckpt >= 1");
+    if (c->nbox != 1) return fail(c, PORTA_EINVAL, "iterate_ckpt: single-box contexts only");
+    if (!c->have_atm || !c->have_rho) return fail(c, PORTA_ESTATE, "iterate_ckpt: atmosphere or rho not set");
+    it_free(c);
+    const size_t nr = (size_t)c->nvox * c->nl;
+    const int nsave = (niter + ckpt - 1) / ckpt;
+    for (int i = 0; i <= nsave; ++i) {
+        double *b = nullptr;
+        cudaError_t e = dalloc(&b, nr);
+        if (e != cudaSuccess) {
+            it_free(c);
+            return fail(c, PORTA_ENOMEM, "iterate_ckpt: checkpoint allocation");
+        }
+        if (i < nsave)
+            c->it_saved.push_back(b);
+        else
+            c->it_final = b;
+    }
+    int rc = PORTA_OK;
+    for (int k = 0; k < niter && rc == PORTA_OK; ++k) {
+        if (k % ckpt == 0) {
+            cudaError_t e = cudaMemcpyAsync(c->it_saved[k / ckpt], c->d_rho, sizeof(double) * nr, cudaMemcpyDeviceToDevice,
+                                            c->stream);
+            if (e != cudaSuccess) rc = fail(c, PORTA_ECUDA, std::string("iterate_ckpt: ") + cudaGetErrorString(e));
+        }
+        if (rc == PORTA_OK) rc = porta_formal_solve(c);
+        if (rc == PORTA_OK) rc = porta_accumulate_jkq(c, nullptr, nullptr, PORTA_DEVICE);
+        if (rc == PORTA_OK) rc = porta_see_update(c, k == niter - 1 ? max_change : nullptr);
+    }
+    if (rc == PORTA_OK) {
+        cudaError_t e = cudaMemcpyAsync(c->it_final, c->d_rho, sizeof(double) * nr, cudaMemcpyDeviceToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) rc = fail(c, PORTA_ECUDA, std::string("iterate_ckpt: ") + cudaGetErrorString(e));
+    }
+    if (rc) {
+        it_free(c);
+        return rc;
+    }
+    c->it_niter = niter;
+    c->it_ckpt = ckpt;
+    return PORTA_OK;
+}
+
+int porta_iterate_timing(const porta_ctx *c, float *ms)
+{
+    if (!c || !ms) return PORTA_EINVAL;
+    for (int k = 0; k < 5; ++k) ms[k] = c->it_ms[k];
+    return PORTA_OK;
+}
+
+int porta_set_tape_limit(porta_ctx *c, long long bytes)
+{
+    if (!c) return PORTA_EINVAL;
+    if (bytes < 0) return fail(c, PORTA_EINVAL, "set_tape_limit: bytes >= 0");
+    c->tape_limit = bytes ? (size_t)bytes : (size_t)16 << 30;
+    return PORTA_OK;
+}
+
+int porta_iterate_vjp(porta_ctx *c, int ndir, const double *mu, const double *chi, const double *grad_out, double *out,
+                      double *g_chi, double *g_f, double *g_b, int where)
+{
+    if (!c) return PORTA_EINVAL;
+    if (ndir < 1 || !mu || !chi || !grad_out || !g_chi || !g_f || (c->ns > 1 && !g_b) ||
+        (where != PORTA_HOST && where != PORTA_DEVICE))
+        return fail(c, PORTA_EINVAL, "iterate_vjp: bad argument");
+    for (int d = 0; d < ndir; ++d)
+        if (!(mu[d] > 0.0 && mu[d] <= 1.0) || !std::isfinite(chi[d]))
+            return fail(c, PORTA_EINVAL, "iterate_vjp: mu must lie in (0, 1], chi finite");
+    if (c->it_niter < 1) return fail(c, PORTA_ESTATE, "iterate_vjp: call porta_iterate_ckpt first");
+    if (c->ns == 1) g_b = nullptr;
+    const long long nout = (long long)ndir * c->n_nu * c->nx * c->ny * c->ns;
+    const long long nv = c->nvox;
+    auto run = [&](const double *dgrad, double *dout, double *dchi, double *df, double *db) {
+        return c->precision == PORTA_FP32 ? iterate_vjp_t<float>(c, ndir, mu, chi, dgrad, dout, dchi, df, db)
+                                          : iterate_vjp_t<double>(c, ndir, mu, chi, dgrad, dout, dchi, df, db);
+    };
+    if (where == PORTA_DEVICE) return run(grad_out, out, g_chi, g_f, g_b);
+    const long long nb = g_b ? 3 * nv : 0;
+    double *blk = nullptr;
+    CK(dalloc(&blk, (size_t)(nout + (out ? nout : 0) + 2 * nv + nb)));
+    double *dgrad = blk, *dout = out ? blk + nout : nullptr;
+    double *dchi = blk + nout + (out ? nout : 0), *df = dchi + nv, *db = nb ? df + nv : nullptr;
+    int rc = PORTA_OK;
+    cudaError_t e = cudaMemcpy(dgrad, grad_out, nout * sizeof(double), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) rc = fail(c, PORTA_ECUDA, cudaGetErrorString(e));
+    if (rc == PORTA_OK) rc = run(dgrad, dout, dchi, df, db);
+    if (rc == PORTA_OK) {
+        e = cudaMemcpy(g_chi, dchi, nv * sizeof(double), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(g_f, df, nv * sizeof(double), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess && db) e = cudaMemcpy(g_b, db, 3 * nv * sizeof(double), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess && out) e = cudaMemcpy(out, dout, nout * sizeof(double), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) rc = fail(c, PORTA_ECUDA, cudaGetErrorString(e));
+    }
+    cudaFree(blk);
+    return rc;
+}
+
 int porta_set_adjoint_launch(porta_ctx *c, int cluster, int nu_group)
 {
     if (!c) return PORTA_EINVAL;
@@ -1506,6 +1852,7 @@ int porta_set_adjoint_launch(porta_ctx *c, int cluster, int nu_group)
     c->adj_cluster = cluster;
     c->adj_nu_group = nu_group;
     c->adj_tuned_ndir = 0;
+    c->adj2_tuned.clear();
     return PORTA_OK;
 }
 

@@ -131,7 +131,19 @@ __global__ void change_kernel(long long nvox, int nl, const double *old, const d
     }
 }
 
+__global__ void axpy_kernel(long long n, double alpha, const double *x, double *y)
+{
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) y[i] += alpha * x[i];
+}
+
 }  // namespace
+
+cudaError_t run_axpy(long long n, double alpha, const double *x, double *y, cudaStream_t st)
+{
+    axpy_kernel<<<nblk(n, 256), 256, 0, st>>>(n, alpha, x, y);
+    return cudaGetLastError();
+}
 
 cudaError_t run_inject(int nxc, int nyc, int nzc, int nxf, int nyf, const double *fine, double *coarse, cudaStream_t st)
 {

@@ -15,5 +15,7 @@ cudaError_t run_prolong_add(int nxf, int nyf, int nzf, int nxc, int nyc, int nl,
 // max relative change between two vectors of unknowns (atomic max on the IEEE bits in *resid)
 cudaError_t run_change(long long nvox, int nl, const double *old, const double *cur, unsigned long long *resid,
                        cudaStream_t st);
+// y += alpha x
+cudaError_t run_axpy(long long n, double alpha, const double *x, double *y, cudaStream_t st);
 
 }  // namespace porta

@@ -3,6 +3,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <map>
 #include <string>
 #include <vector>
 
@@ -26,8 +27,7 @@ struct porta_ctx {
     int precision = PORTA_FP32;
     int opt_cluster = 0, opt_nu_group = 0;
     bool user_shape = false;            // launch shape given in porta_opts (not autotuned)
-    int emg_tuned_ndir = 0;             // emergent sweep: shape timed once per direction count
-    porta::LaunchCfg emg_tuned{};
+    std::map<int, porta::LaunchCfg> emg_tuned;   // emergent sweep: shape timed once per direction count
     long long nvox = 0;
     int nray = 0;
     std::vector<double> mu, chi, w, xf, wf, tkq;  // quadratures, T^K_Q per ray (18)
@@ -91,6 +91,19 @@ struct porta_ctx {
     size_t gpart_bytes = 0;
     int adj_cluster = 0, adj_nu_group = 0;
     porta::LaunchCfg last_adj{};
+    double *d_gacc = nullptr;       // per-cluster FP64 gradient accumulators (gradients in rho)
+    size_t gacc_bytes = 0;
+    // differentiation through Jacobi iterations (porta_iterate_ckpt): checkpoints of
+    // rho [nvox][nl] every it_ckpt iterations, the iteration count, rho at the end
+    std::vector<double *> it_saved;
+    double *it_final = nullptr;
+    int it_niter = 0, it_ckpt = 0;
+    size_t tape_limit = (size_t)16 << 30;  // device tape of the J^K_Q reverse (ray batches)
+    std::map<int, porta::LaunchCfg> adj2_tuned;  // J^K_Q adjoint: shape timed once per batch size
+    cudaEvent_t it_ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    // device time (ms) of the last porta_iterate_vjp: recomputation of the iterates,
+    // update adjoint, forward tape sweeps, J^K_Q adjoint sweeps, accumulator sums
+    float it_ms[5] = {0, 0, 0, 0, 0};
     float adj_fwd_ms = 0.f, adj_rev_ms = 0.f;   // device time of the last porta_emergent_vjp
     int adj_tuned_ndir = 0;                     // automatic shape: timed once per direction count
     porta::LaunchCfg adj_tuned{};

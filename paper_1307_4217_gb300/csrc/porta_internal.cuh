@@ -68,6 +68,12 @@ struct SweepArgs {
     Real *store;                   // emergent: null, or the Stokes vectors of every plane [dir][nu][nvox][ns]
     const double *gout;            // adjoint: dL/dI on the top plane [dir][nu][ny][nx][ns]
     Real *gpart;                   // adjoint: per (dir, frequency group) partial gradients [item][3][nvox]
+    // adjoint in the unknowns rho (through iterations): per-cluster FP64 accumulators of
+    // dL/dchi (fixed rho), dL/dB (3), dL/drho (6) [cluster][10][nvox]; for the J^K_Q sums
+    // of a formal solution also dL/dJ [v][nj], dL/dLambda* [v], ray weights and T ([ray][19])
+    double *gacc;
+    const double *gjkq, *glstar, *tw;
+    int ray0;                      // first ray of the batch (rays and geom point at it)
 };
 
 struct LaunchCfg {
@@ -94,14 +100,20 @@ cudaError_t max_active_clusters(int cluster, int smem, int threads, int *out);
 // ring plane `ring_plane` (16-byte chunks), `ipts` points per strip, tape
 // tiles of `tile_pts` points and F frequencies per pass; occupancy; launch;
 // the fixed-order sum over items
+// form: 0 emergent Stokes, gradients in (chi, e = chi S00, B) per item; 1 emergent Stokes,
+// gradients in (chi, B, rho) accumulated per cluster; 2 the J^K_Q / Lambda-bar* of a formal
+// solution (rays of a batch), gradients in (chi, B, rho) accumulated per cluster
 template <typename Real, int NS>
 int adjoint_smem_bytes(int ring_plane, int ipts, int tile_pts, int F);
 template <typename Real, int NS>
-cudaError_t adjoint_max_active_clusters(int cluster, int smem, int threads, int *out);
+cudaError_t adjoint_max_active_clusters(int cluster, int smem, int threads, int *out, int form = 0);
 template <typename Real, int NS>
-cudaError_t launch_adjoint(const SweepArgs<Real> &a, const LaunchCfg &cfg, cudaStream_t st);
+cudaError_t launch_adjoint(const SweepArgs<Real> &a, const LaunchCfg &cfg, cudaStream_t st, int form = 0);
 template <typename Real>
 cudaError_t launch_adjoint_reduce(const Real *gpart, int nitems, int ngroups, long long nvox, const RayDev<Real> *rays,
                                   double bfac, double *g_chi, double *g_e, double *g_b, cudaStream_t st);
+// sum of the per-cluster accumulators in cluster order: g_chi and g_b added, g_rho overwritten
+cudaError_t launch_adjoint_acc_reduce(const double *gacc, int nclusters, long long nvox, int nl, double *g_chi,
+                                      double *g_b, double *g_rho, cudaStream_t st);
 
 }  // namespace porta

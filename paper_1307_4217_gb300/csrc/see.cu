@@ -4,6 +4,7 @@
 // Jacobi (ALI) statistical-equilibrium update with its convergence residual
 // (Eq. 2, Sec. 5).
 #include "device_math.cuh"
+#include "adjoint_math.cuh"
 #include "see_kernels.cuh"
 
 namespace porta {
@@ -251,6 +252,66 @@ __global__ void see_apply_kernel(long long nvox, int nl, int model, double bcrit
         if (with_eb && c == 0) o += e * bpl[v];
         out[v * nl + c] = o;
     }
+}
+
+// Reverse mode of the Jacobi update (src as in see_kernel): from g = dL/d(rho
+// after the update) to dL/drho through the explicit S^0_0 term (overwritten),
+// dL/dJ^K_Q and dL/dLambda-bar* (overwritten), dL/d(thermal term) and, through
+// the Hanle matrix M = 1 + sum_c g_c E_c (affine in g = (1-eps) B / bcrit),
+// dL/dB (both added):
+//   S00' = S00 + ((1-eps) J00 + f - S00) / D,  D = 1 - (1-eps) Lambda*,
+//   S2'  = M^-1 ((1-eps) J2 + f2),  dL/dJ2 = (1-eps) M^-T g2,
+//   dL/dB_c = -(1-eps)/bcrit (M^-T g2) . E_c S2'.
+__global__ void see_vjp_kernel(long long nvox, int nl, int model, double bcrit, const double *eps, const double *bpl,
+                               const double *bvec, const double *jkq, const double *lstar, const double *src,
+                               const double *rho, const double *g, double *g_rho, double *g_jkq, double *g_lstar,
+                               double *g_f, double *g_b)
+{
+    long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (v >= nvox) return;
+    const double e = eps[v];
+    const double f0 = src ? src[v * nl] : e * bpl[v];
+    const double *s = rho + v * nl, *J = jkq + v * nl, *gv = g + v * nl;
+    const double D = 1.0 - (1.0 - e) * lstar[v];
+    const double num = (1.0 - e) * J[0] + f0 - s[0];
+    g_rho[v * nl] = gv[0] * (1.0 - 1.0 / D);
+    g_jkq[v * nl] = gv[0] * (1.0 - e) / D;
+    g_lstar[v] = gv[0] * num * (1.0 - e) / (D * D);
+    g_f[v] += gv[0] / D;
+    if (model == PORTA_MODEL_TWOLEVEL_UNPOL) return;
+    const double gam = (1.0 - e) / bcrit;
+    const double gx = gam * bvec[v], gy = gam * bvec[nvox + v], gz = gam * bvec[2 * nvox + v];
+    double r[5], s2[5], z[5];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) r[c] = (1.0 - e) * J[1 + c] + (src ? src[v * nl + 1 + c] : 0.0);
+    hanle_solve5(gx, gy, gz, r, s2);
+    hanle_solve5_t(gx, gy, gz, gv + 1, z);
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+        g_rho[v * nl + 1 + c] = 0.0;
+        g_jkq[v * nl + 1 + c] = (1.0 - e) * z[c];
+    }
+    // E_c S2' = (M(unit g along c) - 1) S2'
+    const double unit[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        double y[5];
+        hanle_apply5(unit[c][0], unit[c][1], unit[c][2], s2, y);
+        double acc = 0.0;
+#pragma unroll
+        for (int a = 0; a < 5; ++a) acc += z[a] * (y[a] - s2[a]);
+        g_b[c * nvox + v] += -gam * acc;
+    }
+}
+
+cudaError_t run_see_vjp(long long nvox, int nl, int model, double bcrit, const double *eps, const double *bpl,
+                        const double *bvec, const double *jkq, const double *lstar, const double *src,
+                        const double *rho, const double *g, double *g_rho, double *g_jkq, double *g_lstar,
+                        double *g_f, double *g_b, cudaStream_t st)
+{
+    see_vjp_kernel<<<nblk(nvox, 256), 256, 0, st>>>(nvox, nl, model, bcrit, eps, bpl, bvec, jkq, lstar, src, rho, g,
+                                                    g_rho, g_jkq, g_lstar, g_f, g_b);
+    return cudaGetLastError();
 }
 
 cudaError_t run_see_apply(long long nvox, int nl, int model, double bcrit, const double *eps, const double *bpl,

@@ -19,6 +19,12 @@ template <typename Real>
 cudaError_t run_see(long long nvox, int nl, int model, double bcrit, const double *eps, const double *bpl,
                     const double *bvec, const double *jkq, const double *lstar, double *rho, void *rhoR,
                     unsigned long long *resid, cudaStream_t st, const double *src = nullptr);
+// reverse mode of the Jacobi update: dL/drho (explicit, overwritten), dL/dJ and dL/dLambda*
+// (overwritten), dL/d(thermal term) and dL/dB (added)
+cudaError_t run_see_vjp(long long nvox, int nl, int model, double bcrit, const double *eps, const double *bpl,
+                        const double *bvec, const double *jkq, const double *lstar, const double *src,
+                        const double *rho, const double *g, double *g_rho, double *g_jkq, double *g_lstar,
+                        double *g_f, double *g_b, cudaStream_t st);
 // out = alpha A(rho) + add (+ eps B delta_K0 if with_eb); out may alias add
 cudaError_t run_see_apply(long long nvox, int nl, int model, double bcrit, const double *eps, const double *bpl,
                           const double *bvec, const double *jkq, const double *rho, double alpha, const double *add,
