@@ -14,6 +14,10 @@ synthetic atmospheres of comparable scale):
   log-normal Planck function, opacity and magnetic-field strength, isotropic
   field directions and a Gaussian random vertical velocity.
 * ``batched_boxes``       256 boxes of uneven size with the random-box physics.
+* ``multilevel_atom`` / ``multilevel_box``  five-level atom (J = 0, 1, 2, 1, 2) with
+  four lines, seeded Einstein A and collisional destruction probabilities, in a
+  random atmosphere with the random-box statistics (temperature instead of a
+  Planck function: the lines have different Planck functions).
 
 Voxel arrays are float64 with shape (nz, ny, nx); index k = 0 is the bottom.
 """
@@ -106,12 +110,46 @@ def batched_boxes(n=256, seed=0, sizes=(8, 16, 24, 32, 48), nz_range=(16, 64)):
     return boxes
 
 
+# five-level model atom: levels J (lower 0-2, upper 3-4), energies in eV and
+# the four lines (upper, lower)
+ML_J = (0, 1, 2, 1, 2)
+ML_E_EV = (0.0, 1.692, 1.700, 3.123, 3.151)
+ML_LINES = ((3, 0), (3, 1), (4, 1), (4, 2))
+
+
+def multilevel_atom(seed=0, a_range=(1e7, 1e8), eps_range=(1e-4, 1e-2), J=ML_J, E=ML_E_EV, lines=ML_LINES):
+    """Einstein A (s^-1) and collisional destruction probability eps = C/(A + C)
+    per line, both log-uniform in the given ranges (seeded)."""
+    rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence([seed, 7])))
+    n = len(lines)
+    A = np.exp(rng.uniform(np.log(a_range[0]), np.log(a_range[1]), n))
+    eps = np.exp(rng.uniform(np.log(eps_range[0]), np.log(eps_range[1]), n))
+    return dict(J=np.array(J, dtype=np.int64), E=np.array(E, dtype=np.float64),
+                lines=np.array(lines, dtype=np.int64), A=A, eps=eps)
+
+
+def multilevel_box(nx=128, ny=128, nz=96, seed=0, kT0=0.5, sigma_lnt=0.05, sigma_lnchi=0.2, b_median=30.0,
+                   sigma_lnbfield=1.0, sigma_v=1.0, lx=L_KM, ly=L_KM, tau_top=TAU_TOP, tau_bot=TAU_BOT):
+    """Random atmosphere for the multilevel atom: the random-box fields with kT
+    (eV) = kT0 exp(sigma_lnt g1) in place of the Planck function (sigma_lnt = 0.05
+    gives the strongest line's Planck function a log-spread near 0.3, as in the
+    random box), chi = the opacity scale (line-centre opacity of the reference
+    line with every atom in its lower level), vel and the field B."""
+    a = random_box(nx, ny, nz, seed=seed, sigma_lnchi=sigma_lnchi, b_median=b_median,
+                   sigma_lnbfield=sigma_lnbfield, sigma_v=sigma_v, lx=lx, ly=ly, tau_top=tau_top, tau_bot=tau_bot)
+    g1 = np.log(a.pop("bpl")) / 0.3
+    a["kT"] = kT0 * np.exp(sigma_lnt * g1)
+    a.pop("eps")
+    return a
+
+
 # problem sizes of the benchmarked configurations
 CONFIGS = {
     # name: (atmosphere factory kwargs, model, n_mu per hemisphere, n_chi, n_nu)
     "plain16x16x32": dict(model=0, n_mu=3, n_chi=8, n_nu=11),
     "pol64": dict(model=1, n_mu=5, n_chi=16, n_nu=21),
     "batched256": dict(model=1, n_mu=4, n_chi=10, n_nu=21),
+    "ml128": dict(model=2, n_mu=5, n_chi=16, n_nu=31),
 }
 
 
