@@ -389,6 +389,65 @@ int porta_mg_levels(const porta_ctx *c, int *nlevels, int *shapes);
    enqueued on the context's stream. */
 int porta_mg_vcycle(porta_ctx *c, int npre, int npost, int ncoarse, double *max_change);
 
+/* Multilevel atom without polarization: the non-LTE problem of the first kind
+   (Sec. 1; the populations of the levels are the unknowns of Eq. 2, the
+   polarized problem with rho^0_0 alone). Levels with total angular momentum
+   J (weights 2J + 1) and energies E in eV; lines (upper, lower) with Einstein
+   A (s^-1) and collisional destruction probability eps = C/(A + C) in (0, 1).
+   Intensities are in units of 2 h nu^3 / c^2 of line 0: the Planck function of
+   line k is r^3 / (exp(dE/kT) - 1) with r = dE_k / dE_0 and A/B_ul = r^3; the
+   line-centre opacity is chi s_k (n_l - n_u g_l/g_u) with chi the atmosphere's
+   opacity scale and s_k = (g_u/g_l) A / dE^2 relative to line 0; the source
+   function S = r^3 n_u / (n_l g_u/g_l - n_u) (complete redistribution);
+   collisions on the line transitions C_ul = eps A/(1 - eps), C_lu = (g_u/g_l)
+   exp(-dE/kT) C_ul. Each line is one unpolarized formal solution (Sec. 3) of
+   a batched launch (one box per line on the same grid); the update solves the
+   rate equations per voxel in FP64 with the radiative rates preconditioned by
+   Lambda-bar* (J_eff = Jbar - Lambda-bar* S_old; P_ul = A (1 - Lambda-bar*) +
+   B_ul J_eff + C_ul, P_lu = B_lu J_eff + C_lu), linear in the new populations,
+   with the row of level 0 replaced by sum n = 1. 2 <= nlevel <= 8,
+   1 <= nline <= 8, 2J integral. */
+typedef struct {
+    int nlevel, nline;
+    const double *J, *E;           /* nlevel */
+    const int *upper, *lower;      /* nline level indices, E[upper] > E[lower] */
+    const double *A, *eps;         /* nline */
+} porta_ml_atom;
+
+/* Create a multilevel context on grid g (PORTA_EINVAL for an invalid atom or
+   grid). The generic calls porta_formal_solve, porta_accumulate_jkq,
+   porta_see_update, porta_run_iterations, porta_autotune and
+   porta_launch_info apply to it (J^K_Q and Lambda-bar* per line, the update
+   of the populations); porta_set_rho, porta_mg_setup and porta_iterate_ckpt
+   are rejected. Voxel arrays of the line boxes are [line][voxel]. */
+int porta_ml_create(const porta_grid *g, const porta_ml_atom *a, const porta_quad *q, const porta_opts *o,
+                    porta_ctx **out);
+
+/* Per-voxel atmosphere (nvox doubles each, host or device per `where`):
+   chi = opacity scale (> 0), kT = temperature in eV (> 0), vel = vertical
+   velocity in Doppler widths (the same for every line). */
+int porta_ml_set_atmosphere(porta_ctx *c, const double *chi, const double *kT, const double *vel, int where);
+
+/* Populations [voxel][level] (> 0; the update normalizes them to sum 1).
+   Writes every line's opacity, source and Planck functions; PORTA_EINVAL if a
+   line's opacity is not positive (population inversion). Requires the
+   atmosphere. */
+int porta_ml_set_pops(porta_ctx *c, const double *pops, int where);
+int porta_ml_get_pops(porta_ctx *c, double *pops, int where);
+
+/* Formal solution of every line and the sums Jbar, Lambda-bar* per line
+   ([line][voxel] doubles; NULL keeps them on the device). */
+int porta_ml_formal_solve(porta_ctx *c, double *jbar, double *lstar, int where);
+
+/* Update of the populations from the last sums; max_change (host, may be
+   NULL) is the maximum relative change of a population (synchronizes and then
+   reports PORTA_EKERNEL for a singular system or a non-positive result). */
+int porta_ml_see_update(porta_ctx *c, double *max_change);
+
+/* `iterations` eager Jacobi iterations (formal solution of every line, sums,
+   update); max_change as for porta_ml_see_update, of the last one. */
+int porta_ml_iterate(porta_ctx *c, int iterations, double *max_change);
+
 #ifdef __cplusplus
 }
 #endif

@@ -18,5 +18,6 @@ from .binding import (  # noqa: F401
     porta_emergent_vjp, porta_set_adjoint_launch, porta_adjoint_info, porta_adjoint_timing,
     porta_fill_info, porta_set_fill, porta_mg_setup, porta_mg_levels, porta_mg_vcycle,
     porta_iterate_ckpt, porta_iterate_vjp, porta_set_tape_limit,
-    porta_iterate_timing,
+    porta_iterate_timing, MlContext, porta_ml_create, porta_ml_set_atmosphere, porta_ml_set_pops,
+    porta_ml_get_pops, porta_ml_formal_solve, porta_ml_see_update, porta_ml_iterate,
 )

@@ -49,6 +49,12 @@ class _Atmos(ctypes.Structure):
     _fields_ = [(k, ctypes.c_void_p) for k in ("chi", "eps", "bpl", "vel", "bx", "by", "bz")]
 
 
+class _MlAtom(ctypes.Structure):
+    _fields_ = [("nlevel", ctypes.c_int), ("nline", ctypes.c_int), ("J", ctypes.c_void_p), ("E", ctypes.c_void_p),
+                ("upper", ctypes.c_void_p), ("lower", ctypes.c_void_p), ("A", ctypes.c_void_p),
+                ("eps", ctypes.c_void_p)]
+
+
 _P, _I, _D, _LL = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_longlong
 _SIGS = {
     "porta_create": (_I, [_P, _P, _P, _P, _P]),
@@ -84,6 +90,13 @@ _SIGS = {
     "porta_iterate_vjp": (_I, [_P, _I, _P, _P, _P, _P, _P, _P, _P, _I]),
     "porta_set_tape_limit": (_I, [_P, ctypes.c_longlong]),
     "porta_iterate_timing": (_I, [_P, _P]),
+    "porta_ml_create": (_I, [_P, _P, _P, _P, _P]),
+    "porta_ml_set_atmosphere": (_I, [_P, _P, _P, _P, _I]),
+    "porta_ml_set_pops": (_I, [_P, _P, _I]),
+    "porta_ml_get_pops": (_I, [_P, _P, _I]),
+    "porta_ml_formal_solve": (_I, [_P, _P, _P, _I]),
+    "porta_ml_see_update": (_I, [_P, _P]),
+    "porta_ml_iterate": (_I, [_P, _I, _P]),
 }
 
 _lib = None
@@ -314,6 +327,37 @@ def porta_iterate_timing(h):
     rc = lib().porta_iterate_timing(h, ms)
     keys = ("recompute_ms", "see_adjoint_ms", "tape_forward_ms", "jkq_adjoint_ms", "reduce_ms")
     return rc, dict(zip(keys, list(ms)))
+
+
+def porta_ml_create(grid, atom, quad, opts):
+    h = ctypes.c_void_p()
+    rc = lib().porta_ml_create(ctypes.byref(grid), ctypes.byref(atom), ctypes.byref(quad),
+                               ctypes.byref(opts) if opts is not None else None, ctypes.byref(h))
+    return rc, h
+
+
+def porta_ml_set_atmosphere(h, chi_ptr, kt_ptr, vel_ptr, where):
+    return lib().porta_ml_set_atmosphere(h, chi_ptr, kt_ptr, vel_ptr, where)
+
+
+def porta_ml_set_pops(h, ptr, where):
+    return lib().porta_ml_set_pops(h, ptr, where)
+
+
+def porta_ml_get_pops(h, ptr, where):
+    return lib().porta_ml_get_pops(h, ptr, where)
+
+
+def porta_ml_formal_solve(h, jbar_ptr, lstar_ptr, where):
+    return lib().porta_ml_formal_solve(h, jbar_ptr, lstar_ptr, where)
+
+
+def porta_ml_see_update(h, out=None):
+    return lib().porta_ml_see_update(h, ctypes.byref(out) if out is not None else None)
+
+
+def porta_ml_iterate(h, iterations, out=None):
+    return lib().porta_ml_iterate(h, iterations, ctypes.byref(out) if out is not None else None)
 
 
 # ---- convenience wrapper ------------------------------------------------------------
@@ -592,3 +636,82 @@ class BatchContext(Context):
     def split(self, arr):
         """Per-box views of a concatenated voxel array."""
         return [arr[self.offsets[b]:self.offsets[b + 1]] for b in range(len(self.box_sizes))]
+
+
+class MlContext(Context):
+    """Multilevel atom without polarization (porta_ml_create): ``atom`` as
+    produced by ``synth.multilevel_atom`` (J, E, lines (upper, lower), A, eps),
+    ``atm`` with nx, ny, nz, lx, ly, z. Line arrays come back [line][voxel]."""
+
+    def __init__(self, atm, atom, n_mu, n_chi, n_nu, x_max=4.0, precision=PORTA_FP32, cluster=0, nu_group=0):
+        self._keep = []
+        z = np.ascontiguousarray(atm["z"], dtype=np.float64)
+        J = np.ascontiguousarray(atom["J"], dtype=np.float64)
+        E = np.ascontiguousarray(atom["E"], dtype=np.float64)
+        lines = np.asarray(atom["lines"])
+        up = np.ascontiguousarray(lines[:, 0], dtype=np.int32)
+        lo = np.ascontiguousarray(lines[:, 1], dtype=np.int32)
+        A = np.ascontiguousarray(atom["A"], dtype=np.float64)
+        eps = np.ascontiguousarray(atom["eps"], dtype=np.float64)
+        self._keep += [z, J, E, up, lo, A, eps]
+        g = _Grid(atm["nx"], atm["ny"], atm["nz"], float(atm["lx"]), float(atm["ly"]), z.ctypes.data)
+        a = _MlAtom(len(J), len(A), J.ctypes.data, E.ctypes.data, up.ctypes.data, lo.ctypes.data, A.ctypes.data,
+                    eps.ctypes.data)
+        q = _Quad(n_mu, n_chi, n_nu, float(x_max))
+        o = _Opts(precision, cluster, nu_group)
+        self.h = None
+        rc, h = porta_ml_create(g, a, q, o)
+        if rc != PORTA_OK:
+            raise PortaError(rc, "porta_ml_create failed")
+        self.h = h
+        rc, s = porta_sizes(h)
+        self.__dict__.update(s)
+        self.grid_shape = (atm["nz"], atm["ny"], atm["nx"])
+        self.nlevel, self.nline = len(J), len(A)
+        self.shape = (self.nline,) + self.grid_shape
+        self.model = None
+
+    def set_atmosphere(self, atm):
+        ptrs, where = [], None
+        for k in ("chi", "kT", "vel"):
+            v = atm[k] if hasattr(atm[k], "data_ptr") else np.asarray(atm[k], dtype=np.float64)
+            p, w, keep = _ptr_where(v)
+            self._keep.append(keep)
+            where = w if where is None else where
+            if w != where:
+                raise TypeError("atmosphere arrays must all be host or all device")
+            ptrs.append(p)
+        self._check(porta_ml_set_atmosphere(self.h, *ptrs, where))
+
+    def set_pops(self, pops):
+        if not hasattr(pops, "data_ptr"):
+            pops = np.ascontiguousarray(pops, dtype=np.float64)
+        p, w, keep = _ptr_where(pops)
+        self._check(porta_ml_set_pops(self.h, p, w))
+
+    def get_pops(self, out=None):
+        if out is None:
+            out = np.zeros(self.grid_shape + (self.nlevel,))
+        p, w, keep = _ptr_where(out)
+        self._check(porta_ml_get_pops(self.h, p, w))
+        return out
+
+    def ml_formal_solve(self, jbar=None, lstar=None, want=True):
+        """Formal solution of every line; returns (Jbar, Lambda-bar*) [line][voxel] or (None, None)."""
+        if want and jbar is None:
+            jbar, lstar = np.zeros(self.shape), np.zeros(self.shape)
+        pj, wj, kj = _ptr_where(jbar)
+        pl, wl, kl = _ptr_where(lstar)
+        where = wj if jbar is not None else (wl if lstar is not None else PORTA_DEVICE)
+        self._check(porta_ml_formal_solve(self.h, pj, pl, where))
+        return jbar, lstar
+
+    def ml_see_update(self, residual=True):
+        out = ctypes.c_double() if residual else None
+        self._check(porta_ml_see_update(self.h, out))
+        return out.value if residual else None
+
+    def ml_iterate(self, n, residual=True):
+        out = ctypes.c_double() if residual else None
+        self._check(porta_ml_iterate(self.h, n, out))
+        return out.value if residual else None

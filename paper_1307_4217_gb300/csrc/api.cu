@@ -15,6 +15,7 @@
 #include "porta_ctx.h"
 #include "porta_internal.cuh"
 #include "mg_kernels.cuh"
+#include "ml_kernels.cuh"
 #include "see_kernels.cuh"
 
 using namespace porta;
@@ -865,6 +866,14 @@ void free_all(porta_ctx *c)
     drop_graph(c);
     mg_free(c);
     it_free(c);
+    if (c->ml) {
+        cudaFree(c->ml->d_pops);
+        cudaFree(c->ml->d_chis);
+        cudaFree(c->ml->d_kT);
+        cudaFree(c->ml->d_bad);
+        delete c->ml;
+        c->ml = nullptr;
+    }
     if (c->d_gacc) cudaFree(c->d_gacc);
     for (cudaEvent_t &ev : c->it_ev)
         if (ev) cudaEventDestroy(ev);
@@ -1259,6 +1268,39 @@ int mg_vcycle(porta_ctx *const *levels, int n, int l, int npre, int npost, int n
     return mg_jacobi(L, src, npost);
 }
 
+// line data of every line from the populations (sweep arrays of the line boxes)
+cudaError_t ml_prepare(porta_ctx *c)
+{
+    MlState *m = c->ml;
+    const size_t R = c->rsz;
+    char *atm = (char *)c->d_atm;
+    const long long n = c->nvox;
+    if (c->precision == PORTA_FP32)
+        return run_ml_prepare<float>(m->mc, m->nvox1, m->d_pops, m->d_chis, m->d_kT, (float *)atm,
+                                     (float *)(atm + 5 * n * R), (float *)c->d_rhoR, c->d_rho, m->d_bad, c->stream);
+    return run_ml_prepare<double>(m->mc, m->nvox1, m->d_pops, m->d_chis, m->d_kT, (double *)atm,
+                                  (double *)(atm + 5 * n * R), (double *)c->d_rhoR, c->d_rho, m->d_bad, c->stream);
+}
+
+// the update step of a Jacobi iteration, enqueued on the context's stream
+// (capturable): residual reset, then the two-level SEE update, or for the
+// multilevel atom the rate equations and the next iteration's line data
+cudaError_t enqueue_update(porta_ctx *c)
+{
+    cudaError_t e = cudaMemsetAsync(c->d_resid, 0, sizeof(unsigned long long), c->stream);
+    if (e != cudaSuccess) return e;
+    if (!c->ml)
+        return c->precision == PORTA_FP32
+                   ? run_see<float>(c->nvox, c->nl, c->model, c->bcrit, c->d_eps, c->d_bpl, c->d_b, c->d_jkq,
+                                    c->d_lstar, c->d_rho, c->d_rhoR, c->d_resid, c->stream)
+                   : run_see<double>(c->nvox, c->nl, c->model, c->bcrit, c->d_eps, c->d_bpl, c->d_b, c->d_jkq,
+                                     c->d_lstar, c->d_rho, c->d_rhoR, c->d_resid, c->stream);
+    MlState *m = c->ml;
+    e = run_ml_see(m->mc, m->nvox1, m->d_kT, c->d_jkq, c->d_lstar, m->d_pops, c->d_resid, m->d_bad, c->stream);
+    if (e != cudaSuccess) return e;
+    return ml_prepare(c);
+}
+
 }  // namespace
 
 extern "C" {
@@ -1587,6 +1629,7 @@ int porta_set_atmosphere(porta_ctx *c, const porta_atmos *a, int where)
 int porta_set_rho(porta_ctx *c, const double *rho, int where)
 {
     if (!c) return PORTA_EINVAL;
+    if (c->ml) return fail(c, PORTA_EINVAL, "set_rho: not for a multilevel context (porta_ml_*)");
     if (!rho || (where != PORTA_HOST && where != PORTA_DEVICE)) return fail(c, PORTA_EINVAL, "set_rho: bad argument");
     const long long n = c->nvox * c->nl;
     if (where == PORTA_HOST) {
@@ -1660,12 +1703,7 @@ int porta_see_update(porta_ctx *c, double *max_change)
 {
     if (!c) return PORTA_EINVAL;
     if (!c->have_jkq) return fail(c, PORTA_ESTATE, "see_update: J^K_Q not accumulated");
-    CK(cudaMemsetAsync(c->d_resid, 0, sizeof(unsigned long long), c->stream));
-    cudaError_t e = c->precision == PORTA_FP32
-                        ? run_see<float>(c->nvox, c->nl, c->model, c->bcrit, c->d_eps, c->d_bpl, c->d_b, c->d_jkq,
-                                         c->d_lstar, c->d_rho, c->d_rhoR, c->d_resid, c->stream)
-                        : run_see<double>(c->nvox, c->nl, c->model, c->bcrit, c->d_eps, c->d_bpl, c->d_b, c->d_jkq,
-                                          c->d_lstar, c->d_rho, c->d_rhoR, c->d_resid, c->stream);
+    cudaError_t e = enqueue_update(c);
     if (e != cudaSuccess) return fail(c, PORTA_ECUDA, std::string("see_update: ") + cudaGetErrorString(e));
     c->have_fs = c->have_jkq = false;
     if (max_change) {
@@ -1746,6 +1784,7 @@ int porta_emergent_vjp(porta_ctx *c, int ndir, const double *mu, const double *c
 int porta_iterate_ckpt(porta_ctx *c, int niter, int ckpt, double *max_change)
 {
     if (!c) return PORTA_EINVAL;
+    if (c->ml) return fail(c, PORTA_EINVAL, "iterate_ckpt: not for a multilevel context (porta_ml_*)");
     if (niter < 1 || ckpt < 1) return fail(c, PORTA_EINVAL, "iterate_ckpt: niter >= 1, ckpt >= 1");
     if (c->nbox != 1) return fail(c, PORTA_EINVAL, "iterate_ckpt: single-box contexts only");
     if (!c->have_atm || !c->have_rho) return fail(c, PORTA_ESTATE, "iterate_ckpt: atmosphere or rho not set");
@@ -1973,13 +2012,7 @@ int porta_run_iterations(porta_ctx *c, int iterations, double *max_change)
             else
                 e = c->ns == 1 ? run_jkq_finalize<double, 1>(c->nvox, c->nray, c->d_part, c->d_tw, c->d_jkq, c->d_lstar, c->stream)
                                : run_jkq_finalize<double, 4>(c->nvox, c->nray, c->d_part, c->d_tw, c->d_jkq, c->d_lstar, c->stream);
-            if (e == cudaSuccess) e = cudaMemsetAsync(c->d_resid, 0, sizeof(unsigned long long), c->stream);
-            if (e == cudaSuccess)
-                e = c->precision == PORTA_FP32
-                        ? run_see<float>(c->nvox, c->nl, c->model, c->bcrit, c->d_eps, c->d_bpl, c->d_b, c->d_jkq,
-                                         c->d_lstar, c->d_rho, c->d_rhoR, c->d_resid, c->stream)
-                        : run_see<double>(c->nvox, c->nl, c->model, c->bcrit, c->d_eps, c->d_bpl, c->d_b, c->d_jkq,
-                                          c->d_lstar, c->d_rho, c->d_rhoR, c->d_resid, c->stream);
+            if (e == cudaSuccess) e = enqueue_update(c);
         }
         cudaGraph_t g = nullptr;
         cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
@@ -2060,6 +2093,7 @@ int porta_launch_info(const porta_ctx *c, int *clusters, int *cluster_size, int 
 int porta_mg_setup(porta_ctx *c, int nlevels)
 {
     if (!c) return PORTA_EINVAL;
+    if (c->ml) return fail(c, PORTA_EINVAL, "mg_setup: not for a multilevel context (porta_ml_*)");
     if (c->nbox != 1) return fail(c, PORTA_EINVAL, "mg_setup: single-box contexts only");
     if (nlevels < 2 || nlevels > 8) return fail(c, PORTA_EINVAL, "mg_setup: nlevels in 2..8");
     if (!c->have_atm) return fail(c, PORTA_ESTATE, "mg_setup: atmosphere not set");
@@ -2200,6 +2234,193 @@ int porta_mg_vcycle(porta_ctx *c, int npre, int npost, int ncoarse, double *max_
         std::memcpy(max_change, &bits, sizeof(double));
     }
     return PORTA_OK;
+}
+
+// ---------------------------------------------------------------- multilevel atom (Sec. 1)
+
+int porta_ml_create(const porta_grid *g, const porta_ml_atom *a, const porta_quad *q, const porta_opts *o,
+                    porta_ctx **out)
+{
+    if (!out) return PORTA_EINVAL;
+    *out = nullptr;
+    if (!g || !a || !q || !a->J || !a->E || !a->upper || !a->lower || !a->A || !a->eps) return PORTA_EINVAL;
+    if (a->nlevel < 2 || a->nlevel > kMlMaxLevel || a->nline < 1 || a->nline > kMlMaxLine) return PORTA_EINVAL;
+    MlConst mc{};
+    mc.nlev = a->nlevel;
+    mc.nline = a->nline;
+    for (int i = 0; i < a->nlevel; ++i) {
+        const double j2 = 2.0 * a->J[i];
+        if (!(a->J[i] >= 0.0) || j2 != std::floor(j2) || j2 > 64 || !std::isfinite(a->E[i])) return PORTA_EINVAL;
+        mc.g[i] = j2 + 1.0;
+    }
+    for (int k = 0; k < a->nline; ++k) {
+        const int u = a->upper[k], l = a->lower[k];
+        if (u < 0 || u >= a->nlevel || l < 0 || l >= a->nlevel || !(a->E[u] > a->E[l])) return PORTA_EINVAL;
+        if (!(a->A[k] > 0.0) || !std::isfinite(a->A[k]) || !(a->eps[k] > 0.0 && a->eps[k] < 1.0)) return PORTA_EINVAL;
+        mc.up[k] = u;
+        mc.lo[k] = l;
+        mc.A[k] = a->A[k];
+        mc.dE[k] = a->E[u] - a->E[l];
+        mc.Cul[k] = a->eps[k] / (1.0 - a->eps[k]) * a->A[k];
+    }
+    // intensities in units of 2 h nu^3 / c^2 of line 0; opacity strengths relative to line 0
+    for (int k = 0; k < a->nline; ++k) {
+        const double r = mc.dE[k] / mc.dE[0];
+        mc.r3[k] = r * r * r;
+        mc.Bul[k] = mc.A[k] / mc.r3[k];
+        mc.Blu[k] = mc.g[mc.up[k]] / mc.g[mc.lo[k]] * mc.Bul[k];
+        mc.s[k] = mc.g[mc.up[k]] / mc.g[mc.lo[k]] * mc.A[k] / (mc.dE[k] * mc.dE[k]);
+    }
+    for (int k = a->nline - 1; k >= 0; --k) mc.s[k] /= mc.s[0];
+    std::vector<porta_grid> grids(a->nline, *g);
+    porta_atom at{PORTA_MODEL_TWOLEVEL_UNPOL, 0.0, 1.0, 25.0};
+    porta_ctx *c = nullptr;
+    int rc = create_impl(a->nline, grids.data(), &at, q, o, &c);
+    if (rc) return rc;
+    MlState *m = new (std::nothrow) MlState();
+    if (!m) {
+        porta_destroy(c);
+        return PORTA_ENOMEM;
+    }
+    c->ml = m;
+    m->mc = mc;
+    m->nvox1 = (long long)g->nx * g->ny * g->nz;
+    cudaError_t e = dalloc(&m->d_pops, (size_t)m->nvox1 * mc.nlev);
+    if (e == cudaSuccess) e = dalloc(&m->d_chis, (size_t)m->nvox1);
+    if (e == cudaSuccess) e = dalloc(&m->d_kT, (size_t)m->nvox1);
+    if (e == cudaSuccess) e = cudaMalloc(&m->d_bad, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(m->d_bad, 0, sizeof(unsigned long long));
+    if (e != cudaSuccess) {
+        porta_destroy(c);
+        return PORTA_ENOMEM;
+    }
+    *out = c;
+    return PORTA_OK;
+}
+
+int porta_ml_set_atmosphere(porta_ctx *c, const double *chi, const double *kT, const double *vel, int where)
+{
+    if (!c) return PORTA_EINVAL;
+    MlState *m = c->ml;
+    if (!m) return fail(c, PORTA_EINVAL, "ml_set_atmosphere: not a multilevel context");
+    if (!chi || !kT || !vel || (where != PORTA_HOST && where != PORTA_DEVICE))
+        return fail(c, PORTA_EINVAL, "ml_set_atmosphere: bad argument");
+    const long long n1 = m->nvox1, n = c->nvox;
+    std::vector<double> hv(n1);
+    cudaMemcpyKind k = where == PORTA_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    CK(cudaMemcpyAsync(m->d_chis, chi, n1 * sizeof(double), k, c->stream));
+    CK(cudaMemcpyAsync(m->d_kT, kT, n1 * sizeof(double), k, c->stream));
+    unsigned long long bad = 0;
+    int rc = count_bad(c, m->d_chis, n1, 0.0, 1e300, &bad);
+    if (rc) return rc;
+    if (bad) return fail(c, PORTA_EINVAL, "ml_set_atmosphere: chi must be finite and > 0");
+    if ((rc = count_bad(c, m->d_kT, n1, 0.0, 1e300, &bad))) return rc;
+    if (bad) return fail(c, PORTA_EINVAL, "ml_set_atmosphere: kT must be finite and > 0");
+    if (where == PORTA_DEVICE)
+        CK(cudaMemcpy(hv.data(), vel, n1 * sizeof(double), cudaMemcpyDeviceToHost));
+    else
+        std::memcpy(hv.data(), vel, n1 * sizeof(double));
+    // the line boxes share the grid and the velocity; their opacity, Planck
+    // function and source function are written from the populations
+    std::vector<double> vrep(n), ones(n, 1.0), half(n, 0.5);
+    for (int b = 0; b < m->mc.nline; ++b) std::memcpy(vrep.data() + b * n1, hv.data(), n1 * sizeof(double));
+    porta_atmos at{ones.data(), half.data(), ones.data(), vrep.data(), nullptr, nullptr, nullptr};
+    rc = porta_set_atmosphere(c, &at, PORTA_HOST);
+    if (rc) return rc;
+    m->have_atm = true;
+    if (m->have_pops) {
+        cudaError_t e = ml_prepare(c);
+        if (e != cudaSuccess) return fail(c, PORTA_ECUDA, cudaGetErrorString(e));
+    }
+    return PORTA_OK;
+}
+
+int porta_ml_set_pops(porta_ctx *c, const double *pops, int where)
+{
+    if (!c) return PORTA_EINVAL;
+    MlState *m = c->ml;
+    if (!m) return fail(c, PORTA_EINVAL, "ml_set_pops: not a multilevel context");
+    if (!pops || (where != PORTA_HOST && where != PORTA_DEVICE)) return fail(c, PORTA_EINVAL, "ml_set_pops: bad argument");
+    if (!m->have_atm) return fail(c, PORTA_ESTATE, "ml_set_pops: atmosphere not set");
+    const long long n = m->nvox1 * m->mc.nlev;
+    int rc = copy_in(c, m->d_pops, pops, n, where);
+    if (rc) return rc;
+    unsigned long long bad = 0;
+    if ((rc = count_bad(c, m->d_pops, n, 0.0, 1e300, &bad))) return rc;
+    if (bad) return fail(c, PORTA_EINVAL, "ml_set_pops: populations must be finite and > 0");
+    CK(cudaMemsetAsync(m->d_bad, 0, sizeof(unsigned long long), c->stream));
+    CK(ml_prepare(c));
+    unsigned long long hb = 0;
+    CK(cudaMemcpyAsync(&hb, m->d_bad, sizeof(hb), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (hb) return fail(c, PORTA_EINVAL, "ml_set_pops: a line has a non-positive opacity (population inversion)");
+    m->have_pops = true;
+    c->have_rho = true;
+    c->have_fs = c->have_jkq = false;
+    return PORTA_OK;
+}
+
+int porta_ml_get_pops(porta_ctx *c, double *pops, int where)
+{
+    if (!c) return PORTA_EINVAL;
+    MlState *m = c->ml;
+    if (!m) return fail(c, PORTA_EINVAL, "ml_get_pops: not a multilevel context");
+    if (!pops || (where != PORTA_HOST && where != PORTA_DEVICE)) return fail(c, PORTA_EINVAL, "ml_get_pops: bad argument");
+    if (!m->have_pops) return fail(c, PORTA_ESTATE, "ml_get_pops: populations not set");
+    CK(cudaMemcpyAsync(pops, m->d_pops, m->nvox1 * m->mc.nlev * sizeof(double),
+                       where == PORTA_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+    if (where == PORTA_HOST) CK(cudaStreamSynchronize(c->stream));
+    return PORTA_OK;
+}
+
+// the error counter of the line data and of the rate equations (synchronizes)
+static int ml_check(porta_ctx *c, const char *what)
+{
+    unsigned long long hb = 0;
+    CK(cudaMemcpyAsync(&hb, c->ml->d_bad, sizeof(hb), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (hb) {
+        cudaMemsetAsync(c->ml->d_bad, 0, sizeof(hb), c->stream);
+        return fail(c, PORTA_EKERNEL, std::string(what) + ": singular rate equations, non-positive population or "
+                                                          "line opacity (population inversion)");
+    }
+    return PORTA_OK;
+}
+
+int porta_ml_formal_solve(porta_ctx *c, double *jbar, double *lstar, int where)
+{
+    if (!c) return PORTA_EINVAL;
+    MlState *m = c->ml;
+    if (!m) return fail(c, PORTA_EINVAL, "ml_formal_solve: not a multilevel context");
+    if (!m->have_atm || !m->have_pops) return fail(c, PORTA_ESTATE, "ml_formal_solve: atmosphere or populations not set");
+    int rc = porta_formal_solve(c);
+    if (rc == PORTA_OK) rc = porta_accumulate_jkq(c, jbar, lstar, where);
+    return rc;
+}
+
+int porta_ml_see_update(porta_ctx *c, double *max_change)
+{
+    if (!c) return PORTA_EINVAL;
+    if (!c->ml) return fail(c, PORTA_EINVAL, "ml_see_update: not a multilevel context");
+    int rc = porta_see_update(c, max_change);
+    if (rc == PORTA_OK && max_change) rc = ml_check(c, "ml_see_update");
+    return rc;
+}
+
+int porta_ml_iterate(porta_ctx *c, int iterations, double *max_change)
+{
+    if (!c) return PORTA_EINVAL;
+    MlState *m = c->ml;
+    if (!m) return fail(c, PORTA_EINVAL, "ml_iterate: not a multilevel context");
+    if (!m->have_atm || !m->have_pops) return fail(c, PORTA_ESTATE, "ml_iterate: atmosphere or populations not set");
+    if (iterations < 0) return fail(c, PORTA_EINVAL, "ml_iterate: negative count");
+    int rc = PORTA_OK;
+    for (int it = 0; it < iterations && rc == PORTA_OK; ++it) {
+        rc = porta_ml_formal_solve(c, nullptr, nullptr, PORTA_DEVICE);
+        if (rc == PORTA_OK) rc = porta_see_update(c, it == iterations - 1 ? max_change : nullptr);
+    }
+    if (rc == PORTA_OK) rc = ml_check(c, "ml_iterate");
+    return rc;
 }
 
 }  // extern "C"

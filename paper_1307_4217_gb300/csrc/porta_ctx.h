@@ -7,7 +7,19 @@
 #include <string>
 #include <vector>
 
+#include "ml_kernels.cuh"
 #include "porta_internal.cuh"
+
+// multilevel atom without polarization: one box of the batch per line
+struct MlState {
+    porta::MlConst mc{};
+    long long nvox1 = 0;               // voxels of the grid (one box)
+    double *d_pops = nullptr;          // [nvox1][nlev]
+    double *d_chis = nullptr;          // opacity scale, nvox1
+    double *d_kT = nullptr;            // kT (eV), nvox1
+    unsigned long long *d_bad = nullptr;
+    bool have_atm = false, have_pops = false;
+};
 
 // stream, fork/join events and work-list counters of the concurrent launch
 struct LaunchFill {
@@ -98,6 +110,7 @@ struct porta_ctx {
     std::vector<double *> it_saved;
     double *it_final = nullptr;
     int it_niter = 0, it_ckpt = 0;
+    MlState *ml = nullptr;                 // multilevel atom (porta_ml_create), else null
     size_t tape_limit = (size_t)16 << 30;  // device tape of the J^K_Q reverse (ray batches)
     std::map<int, porta::LaunchCfg> adj2_tuned;  // J^K_Q adjoint: shape timed once per batch size
     cudaEvent_t it_ev[4] = {nullptr, nullptr, nullptr, nullptr};
