@@ -85,6 +85,8 @@ def args_parse():
     ap.add_argument("--mg-cycles", type=int, default=3, help="timed multigrid V-cycles (0 skips them)")
     ap.add_argument("--iter-adjoint", default="20,5",
                     help="gradients through Jacobi iterations: 'iterations,checkpoint spacing' (0 skips them)")
+    ap.add_argument("--ml-steps", type=int, default=3,
+                    help="timed Jacobi iterations of the multilevel atom on the 128x128x96 grid (0 skips them)")
     ap.add_argument("--fill", default="", help="force the concurrent filler launch: cluster,nu_group,fraction")
     ap.add_argument("--adjoint-cluster", type=int, default=0, help="force the adjoint cluster size (skips its tuning)")
     ap.add_argument("--adjoint-nu-group", type=int, default=0, help="force the adjoint frequencies per pass")
@@ -385,7 +387,6 @@ def run_cuda(args):
     # device time of the forward sweep with its tape and of the adjoint sweep
     adjoint = None
     if args.adjoint_reps > 0 and wl.name == "pol64":
-        import synth
         mu, az = synth.emergent_directions()
         nz, ny, nx = ctx.shape
         gen = torch.Generator(device=dev).manual_seed(1234)
@@ -415,7 +416,6 @@ def run_cuda(args):
     # iterations keeping rho checkpoints, then the checkpointed reverse pass
     iter_adj = None
     if args.iter_adjoint != "0" and wl.name == "pol64":
-        import synth
         niter, ckpt = (int(x) for x in args.iter_adjoint.split(","))
         mu, az = synth.emergent_directions()
         nz, ny, nx = ctx.shape
@@ -476,6 +476,45 @@ def run_cuda(args):
                  "jacobi_max_change_after_7k_iterations": jac,
                  "note": "max_change: of the whole V-cycle for MG, of the last iteration for Jacobi"}
 
+    # multilevel atom without polarization: five levels, four lines, 31 frequencies per
+    # line, 160 rays on the 128 x 128 x 96 grid; one Jacobi iteration (formal solution
+    # of every line in one batched launch, sums, FP64 rate equations) per step
+    mlres = None
+    if args.ml_steps > 0 and wl.name == "pol64":
+        nxm, nym, nzm = 128, 128, 96
+        atm_ml = synth.multilevel_box(nxm, nym, nzm, seed=rank)
+        atom = synth.multilevel_atom(seed=rank)
+        g = 2.0 * atom["J"] + 1
+        pops0 = g * np.exp(-atom["E"] / atm_ml["kT"][..., None])
+        pops0 /= pops0.sum(-1, keepdims=True)                  # LTE start
+        mctx = P.MlContext(atm_ml, atom, N_MU, N_CHI, 31, precision=P.PORTA_FP32)
+        mctx.set_stream(stream)
+        mctx.set_atmosphere(atm_ml)
+        mctx.set_pops(pops0)
+        with torch.cuda.stream(stream):
+            mctx.autotune()
+            mctx.set_pops(pops0)
+            mctx.run_iterations(1, residual=False)              # warm-up (graph capture)
+            barrier()
+            evm = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(args.ml_steps)]
+            chg = []
+            for k in range(args.ml_steps):
+                flush.zero_()
+                evm[k][0].record(stream)
+                mctx.run_iterations(1, residual=False)
+                evm[k][1].record(stream)
+            barrier()
+            chg = mctx.ml_iterate(1)
+        ml_ms = sum(e[0].elapsed_time(e[1]) for e in evm) / args.ml_steps
+        nupd = len(atom["A"]) * 31 * NRAY * nxm * nym * nzm
+        mlres = {"workload": f"{nxm}x{nym}x{nzm}, five-level atom (J = 0,1,2,1,2), four lines x 31 frequencies, "
+                             f"{NRAY} rays, populations only (FP32 sweeps, FP64 rate equations)",
+                 "ms_per_iteration": ml_ms, "updates_per_iteration": nupd,
+                 "updates_per_s": nupd / (ml_ms * 1e-3), "steps": args.ml_steps,
+                 "max_change_after": chg, "launch": mctx.launch_info(),
+                 "timing": "CUDA events around one graph replay per step, L2 flushed between steps"}
+        mctx.close()
+
     # max over ranks
     if world > 1:
         step_ms, sweep_ms, e2e_s = max_over_ranks([step_ms, sweep_ms, e2e_s], dev)
@@ -513,6 +552,7 @@ def run_cuda(args):
         "adjoint": adjoint,
         "multigrid": mgres,
         "iter_adjoint": iter_adj,
+        "multilevel": mlres,
     }
     print(json.dumps(line))
     if world > 1:
