@@ -36,11 +36,21 @@ equation of level 0 is replaced by sum_i n_i = 1. For two levels this is the
 two-level update of this package with eps' = C'/(A + C'), C' = C_ul (1 -
 exp(-dE/kT)).
 
+The non-linear multigrid cycle of Sec. 6 (Eqs. 14-18) carries over with the
+populations as the unknowns: A(n) = f with A(n)_0 = sum_i n_i and A(n)_i =
+(M n)_i (the plain rates of the formal solution's Jbar) for i >= 1, f = (1, 0,
+..., 0) on the finest grid and f = A_c(R n) + R r on a coarser one, whose
+Jacobi update takes f as the right-hand side; the coarse atmospheres (opacity
+scale, temperature, velocity) are the fine values at the coincident nodes and
+the grid transfer operators are those of oracle/mg.py.
+
 Pins (tests/test_oracle_ml.py): strong collisions give Boltzmann
 populations; LTE populations have S = B; Planckian radiation is a fixed point
 of the update; rate-matrix columns sum to zero; the two-level case equals the
-pinned two-level update and iteration; the converged populations satisfy the
-rate equations without preconditioning.
+pinned two-level update; the emissivity depends on the upper population
+alone; the converged populations satisfy the rate equations without
+preconditioning; V-cycles reach that solution faster than Jacobi iterations
+of equal cost and leave it unchanged.
 """
 import numpy as np
 
@@ -125,11 +135,29 @@ def solve_populations(M):
     return np.linalg.solve(M, rhs[..., None])[..., 0]
 
 
-def see_update(atom, kT, pops, jbar, lstar):
-    """One Jacobi update of the populations; returns (new, max relative change)."""
+def see_update(atom, kT, pops, jbar, lstar, src=None):
+    """One Jacobi update of the populations; returns (new, max relative change).
+    src (per voxel, nlevel) replaces the right-hand side (1, 0, ..., 0) of the
+    rate equations with their conservation row (the coarse-grid equations of
+    the multigrid cycle)."""
     jeff = jbar - lstar * source_function(atom, pops)
-    new = solve_populations(rate_matrix(atom, kT, jeff, lstar))
+    M = rate_matrix(atom, kT, jeff, lstar)
+    if src is None:
+        new = solve_populations(M)
+    else:
+        M = M.copy()
+        M[..., 0, :] = 1.0
+        new = np.linalg.solve(M, np.asarray(src)[..., None])[..., 0]
     return new, float(np.max(np.abs(new - pops) / np.abs(pops)))
+
+
+def rate_operator(atom, kT, pops, jbar):
+    """A(n) of the rate equations written as A(n) = (1, 0, ..., 0): row 0 is
+    sum_i n_i, rows i >= 1 are (M n)_i with the plain radiative rates of Jbar."""
+    M = rate_matrix(atom, kT, jbar, np.zeros_like(jbar))
+    An = np.einsum("...ij,...j->...i", M, pops)
+    An[..., 0] = pops.sum(-1)
+    return An
 
 
 def line_problem(atm, atom, pops, k, quad):
@@ -162,3 +190,75 @@ def iterate(atm, atom, pops, quad, n):
         jbar, lstar = formal_solve_lines(atm, atom, pops, quad)
         pops, change = see_update(atom, atm["kT"], pops, jbar, lstar)
     return pops, change
+
+
+# ---------------------------------------------------------------- multigrid (Sec. 6)
+# The non-linear multigrid cycle of Sec. 6 with the populations as the
+# unknowns: A(n) = f with f = (1, 0, ..., 0) on the finest grid; the grid
+# transfer operators are those of oracle/mg.py.
+
+class MlLevel:
+    def __init__(self, atm):
+        self.atm = atm
+        self.shape = (atm["nz"], atm["ny"], atm["nx"])
+
+
+def coarsen(atm):
+    """Coarse atmosphere: the fine values at the coincident nodes (coarse node
+    (i, j, k) = fine node (2i, 2j, 2k))."""
+    from .mg import coarse_nz
+    nz, ny, nx = atm["nz"], atm["ny"], atm["nx"]
+    assert nx % 2 == 0 and ny % 2 == 0
+    ncz = coarse_nz(nz)
+    c = dict(atm)
+    c.update(nx=nx // 2, ny=ny // 2, nz=ncz, z=np.asarray(atm["z"])[0:2 * ncz:2])
+    for k in ("chi", "kT", "vel", "bx", "by", "bz"):
+        if atm.get(k) is not None:
+            c[k] = np.ascontiguousarray(np.asarray(atm[k])[0:2 * ncz:2, 0::2, 0::2])
+    return c
+
+
+def hierarchy(atm, nlevels):
+    levels = [MlLevel(atm)]
+    for _ in range(nlevels - 1):
+        levels.append(MlLevel(coarsen(levels[-1].atm)))
+    return levels
+
+
+def apply_A(atm, atom, pops, quad):
+    jbar, _ = formal_solve_lines(atm, atom, pops, quad)
+    return rate_operator(atom, atm["kT"], pops, jbar)
+
+
+def f_fine(shape, nlevel):
+    f = np.zeros(tuple(shape) + (nlevel,))
+    f[..., 0] = 1.0
+    return f
+
+
+def jacobi(atm, atom, pops, quad, src, n):
+    change = None
+    for _ in range(n):
+        jbar, lstar = formal_solve_lines(atm, atom, pops, quad)
+        pops, change = see_update(atom, atm["kT"], pops, jbar, lstar, src)
+    return pops, change
+
+
+def vcycle(levels, atom, quad, pops, src=None, l=0, npre=2, npost=4, ncoarse=8):
+    """One V-cycle from level l down to the coarsest (Eqs. 14-18); returns the
+    new populations of level l. src None on the finest level: f = (1, 0, ...)."""
+    from .mg import prolong, restrict
+    lev = levels[l]
+    f = f_fine(lev.shape, pops.shape[-1]) if src is None else src
+    if l == len(levels) - 1:
+        pops, _ = jacobi(lev.atm, atom, pops, quad, f, ncoarse)
+        return pops
+    pops, _ = jacobi(lev.atm, atom, pops, quad, f, npre)
+    r = f - apply_A(lev.atm, atom, pops, quad)
+    coarse = levels[l + 1]
+    n_c0 = restrict(lev, pops)
+    f_c = apply_A(coarse.atm, atom, n_c0, quad) + restrict(lev, r)
+    n_c = vcycle(levels, atom, quad, n_c0, f_c, l + 1, npre, npost, ncoarse)
+    pops = pops + prolong(lev, n_c - n_c0)
+    pops, _ = jacobi(lev.atm, atom, pops, quad, f, npost)
+    return pops
