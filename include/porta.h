@@ -368,7 +368,10 @@ int porta_iterate_timing(const porta_ctx *c, float *ms);
    divisible by 2^(nlevels - 1) (PORTA_EINVAL otherwise); requires the
    atmosphere (PORTA_ESTATE); call it again after porta_set_atmosphere. The
    method needs the coarse grids to resolve the transfer problem (about one
-   plane per decade of optical depth or more, Sec. 6.3). */
+   plane per decade of optical depth or more, Sec. 6.3). On a multilevel
+   context (porta_ml_create) the coarse levels are multilevel contexts of the
+   same atom with the opacity scale, temperature and velocity at the
+   coincident nodes. */
 int porta_mg_setup(porta_ctx *c, int nlevels);
 
 /* Levels built by porta_mg_setup: *nlevels (0 before setup) and, if shapes is
@@ -386,7 +389,12 @@ int porta_mg_levels(const porta_ctx *c, int *nlevels, int *shapes);
    to keep constants (adjoint of the tri-linear prolongation, Sec. 6.2).
    max_change (host, may be NULL): the maximum relative change of rho over the
    cycle, defined as for porta_see_update (synchronizes). All work is
-   enqueued on the context's stream. */
+   enqueued on the context's stream. Multilevel contexts: the unknowns are the
+   populations, A(n)_0 = sum_i n_i and A(n)_i the rate equations with the
+   plain radiative rates of the formal solution (i >= 1), f = (1, 0, ..., 0);
+   max_change is the largest relative change of a population, and the call
+   synchronizes and reports PORTA_EKERNEL for a singular system or a
+   non-positive population on any level. */
 int porta_mg_vcycle(porta_ctx *c, int npre, int npost, int ncoarse, double *max_change);
 
 /* Multilevel atom without polarization: the non-LTE problem of the first kind
@@ -418,8 +426,10 @@ typedef struct {
    grid). The generic calls porta_formal_solve, porta_accumulate_jkq,
    porta_see_update, porta_run_iterations, porta_autotune and
    porta_launch_info apply to it (J^K_Q and Lambda-bar* per line, the update
-   of the populations); porta_set_rho, porta_mg_setup and porta_iterate_ckpt
-   are rejected. Voxel arrays of the line boxes are [line][voxel]. */
+   of the populations); porta_set_rho and porta_iterate_ckpt
+   are rejected; porta_mg_setup / porta_mg_vcycle run the multigrid cycle with
+   the populations as unknowns. Voxel arrays of the line boxes are
+   [line][voxel]. */
 int porta_ml_create(const porta_grid *g, const porta_ml_atom *a, const porta_quad *q, const porta_opts *o,
                     porta_ctx **out);
 

@@ -1210,27 +1210,53 @@ int mg_fs(porta_ctx *L)
     return rc;
 }
 
-// n Jacobi iterations of A(S) = src on one level (src null: eps B delta_K0)
+cudaError_t ml_prepare(porta_ctx *c);
+
+// the unknowns of a level: rho [v][nl] of the two-level atom, or the
+// populations [v][nlevel] of the multilevel atom
+double *mg_unk(porta_ctx *L) { return L->ml ? L->ml->d_pops : L->d_rho; }
+long long mg_nunk(const porta_ctx *L) { return L->ml ? L->ml->nvox1 : L->nvox; }
+int mg_ncomp(const porta_ctx *L) { return L->ml ? L->ml->mc.nlev : L->nl; }
+
+cudaError_t mg_rho_changed(porta_ctx *L)
+{
+    if (L->ml) return ml_prepare(L);
+    return L->precision == PORTA_FP32 ? run_rho_convert<float>(L->nvox, L->nl, L->d_rho, L->d_rhoR, L->stream)
+                                      : run_rho_convert<double>(L->nvox, L->nl, L->d_rho, L->d_rhoR, L->stream);
+}
+
+// out = alpha A(unknowns) + add + with_f f_fine, with J^K_Q of the last formal solution
+cudaError_t mg_apply(porta_ctx *L, double alpha, const double *add, int with_f, double *out)
+{
+    if (L->ml)
+        return run_ml_apply(L->ml->mc, L->ml->nvox1, L->ml->d_kT, L->d_jkq, L->ml->d_pops, alpha, add, with_f, out,
+                            L->stream);
+    return run_see_apply(L->nvox, L->nl, L->model, L->bcrit, L->d_eps, L->d_bpl, L->d_b, L->d_jkq, L->d_rho, alpha,
+                         add, with_f, out, L->stream);
+}
+
+// n Jacobi iterations of A(x) = src on one level (src null: the fine right-hand side)
 int mg_jacobi(porta_ctx *L, const double *src, int n)
 {
     for (int it = 0; it < n; ++it) {
         int rc = mg_fs(L);
         if (rc) return rc;
-        cudaError_t e = L->precision == PORTA_FP32
-                            ? run_see<float>(L->nvox, L->nl, L->model, L->bcrit, L->d_eps, L->d_bpl, L->d_b, L->d_jkq,
-                                             L->d_lstar, L->d_rho, L->d_rhoR, L->d_resid, L->stream, src)
-                            : run_see<double>(L->nvox, L->nl, L->model, L->bcrit, L->d_eps, L->d_bpl, L->d_b, L->d_jkq,
-                                              L->d_lstar, L->d_rho, L->d_rhoR, L->d_resid, L->stream, src);
+        cudaError_t e;
+        if (L->ml) {
+            e = run_ml_see(L->ml->mc, L->ml->nvox1, L->ml->d_kT, L->d_jkq, L->d_lstar, L->ml->d_pops, L->d_resid,
+                           L->ml->d_bad, L->stream, src);
+            if (e == cudaSuccess) e = ml_prepare(L);
+        } else {
+            e = L->precision == PORTA_FP32
+                    ? run_see<float>(L->nvox, L->nl, L->model, L->bcrit, L->d_eps, L->d_bpl, L->d_b, L->d_jkq,
+                                     L->d_lstar, L->d_rho, L->d_rhoR, L->d_resid, L->stream, src)
+                    : run_see<double>(L->nvox, L->nl, L->model, L->bcrit, L->d_eps, L->d_bpl, L->d_b, L->d_jkq,
+                                      L->d_lstar, L->d_rho, L->d_rhoR, L->d_resid, L->stream, src);
+        }
         if (e != cudaSuccess) return fail(L, PORTA_ECUDA, std::string("mg jacobi: ") + cudaGetErrorString(e));
         L->have_fs = L->have_jkq = false;
     }
     return PORTA_OK;
-}
-
-cudaError_t mg_rho_changed(porta_ctx *L)
-{
-    return L->precision == PORTA_FP32 ? run_rho_convert<float>(L->nvox, L->nl, L->d_rho, L->d_rhoR, L->stream)
-                                      : run_rho_convert<double>(L->nvox, L->nl, L->d_rho, L->d_rhoR, L->stream);
 }
 
 // One V-cycle (Eqs. 14-18) from level l of levels[0..n) down to the coarsest.
@@ -1241,28 +1267,28 @@ int mg_vcycle(porta_ctx *const *levels, int n, int l, int npre, int npost, int n
     if (l == n - 1) return mg_jacobi(L, src, ncoarse);
     int rc = mg_jacobi(L, src, npre);
     if (rc) return rc;
-    // residual r = f - A(rho)
+    // residual r = f - A(x)
     if ((rc = mg_fs(L))) return rc;
-    cudaError_t e = run_see_apply(L->nvox, L->nl, L->model, L->bcrit, L->d_eps, L->d_bpl, L->d_b, L->d_jkq, L->d_rho,
-                                  -1.0, src, src ? 0 : 1, L->mg_res, L->stream);
+    cudaError_t e = mg_apply(L, -1.0, src, src ? 0 : 1, L->mg_res);
     porta_ctx *C = levels[l + 1];
-    // coarse unknowns R rho, coarse right-hand side A_c(R rho) + R r
+    const int nc = mg_ncomp(L);
+    // coarse unknowns R x, coarse right-hand side A_c(R x) + R r
     if (e == cudaSuccess)
-        e = run_restrict(C->nx, C->ny, C->nz, L->nx, L->ny, L->nl, L->mg_zr, L->d_rho, C->mg_rho0, L->stream);
+        e = run_restrict(C->nx, C->ny, C->nz, L->nx, L->ny, nc, L->mg_zr, mg_unk(L), C->mg_rho0, L->stream);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(C->d_rho, C->mg_rho0, sizeof(double) * C->nvox * C->nl, cudaMemcpyDeviceToDevice, L->stream);
+        e = cudaMemcpyAsync(mg_unk(C), C->mg_rho0, sizeof(double) * mg_nunk(C) * nc, cudaMemcpyDeviceToDevice, L->stream);
     if (e == cudaSuccess) e = mg_rho_changed(C);
     if (e == cudaSuccess)
-        e = run_restrict(C->nx, C->ny, C->nz, L->nx, L->ny, L->nl, L->mg_zr, L->mg_res, C->mg_src, L->stream);
+        e = run_restrict(C->nx, C->ny, C->nz, L->nx, L->ny, nc, L->mg_zr, L->mg_res, C->mg_src, L->stream);
     if (e != cudaSuccess) return fail(L, PORTA_ECUDA, std::string("mg restrict: ") + cudaGetErrorString(e));
     C->have_rho = true;
+    if (C->ml) C->ml->have_pops = true;
     if ((rc = mg_fs(C))) return fail(L, rc, std::string("mg coarse level: ") + C->err);
-    e = run_see_apply(C->nvox, C->nl, C->model, C->bcrit, C->d_eps, C->d_bpl, C->d_b, C->d_jkq, C->d_rho, 1.0,
-                      C->mg_src, 0, C->mg_src, C->stream);
+    e = mg_apply(C, 1.0, C->mg_src, 0, C->mg_src);
     if (e != cudaSuccess) return fail(L, PORTA_ECUDA, std::string("mg coarse rhs: ") + cudaGetErrorString(e));
     if ((rc = mg_vcycle(levels, n, l + 1, npre, npost, ncoarse))) return fail(L, rc, C->err);
-    // coarse-grid correction rho += P (rho_c - R rho)
-    e = run_prolong_add(L->nx, L->ny, L->nz, C->nx, C->ny, L->nl, L->mg_zp, C->d_rho, C->mg_rho0, L->d_rho, L->stream);
+    // coarse-grid correction x += P (x_c - R x)
+    e = run_prolong_add(L->nx, L->ny, L->nz, C->nx, C->ny, nc, L->mg_zp, mg_unk(C), C->mg_rho0, mg_unk(L), L->stream);
     if (e == cudaSuccess) e = mg_rho_changed(L);
     if (e != cudaSuccess) return fail(L, PORTA_ECUDA, std::string("mg prolong: ") + cudaGetErrorString(e));
     return mg_jacobi(L, src, npost);
@@ -2090,11 +2116,13 @@ int porta_launch_info(const porta_ctx *c, int *clusters, int *cluster_size, int 
 }
 
 
+static int ml_check(porta_ctx *c, const char *what);
+
 int porta_mg_setup(porta_ctx *c, int nlevels)
 {
     if (!c) return PORTA_EINVAL;
-    if (c->ml) return fail(c, PORTA_EINVAL, "mg_setup: not for a multilevel context (porta_ml_*)");
-    if (c->nbox != 1) return fail(c, PORTA_EINVAL, "mg_setup: single-box contexts only");
+    if (c->nbox != 1 && !c->ml) return fail(c, PORTA_EINVAL, "mg_setup: single-box contexts only");
+    if (c->ml && !c->ml->have_atm) return fail(c, PORTA_ESTATE, "mg_setup: atmosphere not set");
     if (nlevels < 2 || nlevels > 8) return fail(c, PORTA_EINVAL, "mg_setup: nlevels in 2..8");
     if (!c->have_atm) return fail(c, PORTA_ESTATE, "mg_setup: atmosphere not set");
     {
@@ -2135,6 +2163,55 @@ int porta_mg_setup(porta_ctx *c, int nlevels)
         porta_opts o{};
         o.precision = c->precision;
         porta_ctx *L = nullptr;
+        if (c->ml) {
+            // multilevel: a coarse multilevel context of the same atom; its opacity
+            // scale, temperature and velocity at the coincident nodes
+            const MlState *m = c->ml;
+            porta_ml_atom ma{m->mc.nlev, m->mc.nline, m->J.data(), m->E.data(), m->up.data(), m->lo.data(),
+                             m->A.data(), m->eps.data()};
+            if ((rc = porta_ml_create(&g, &ma, &q, &o, &L))) {
+                rc = fail(c, rc, "mg_setup: coarse level creation");
+                break;
+            }
+            c->mg.push_back(L);
+            porta_set_stream(L, c->stream);
+            const MlState *mf = F->ml;
+            const long long ncv = L->ml->nvox1;
+            double *tmp = nullptr;
+            cudaError_t e = dalloc(&tmp, 3 * (size_t)ncv);
+            // F->d_cv64 + F->nvox: FP64 velocity of the line boxes (box 0 first)
+            const double *srcs[3] = {mf->d_chis, mf->d_kT, F->d_cv64 + F->nvox};
+            for (int f = 0; f < 3 && e == cudaSuccess; ++f)
+                e = run_inject(L->nx, L->ny, L->nz, F->nx, F->ny, srcs[f], tmp + f * ncv, c->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+            if (e != cudaSuccess) {
+                cudaFree(tmp);
+                rc = fail(c, PORTA_ECUDA, std::string("mg_setup: ") + cudaGetErrorString(e));
+                break;
+            }
+            rc = porta_ml_set_atmosphere(L, tmp, tmp + ncv, tmp + 2 * ncv, PORTA_DEVICE);
+            cudaFree(tmp);
+            if (rc) {
+                rc = fail(c, rc, std::string("mg_setup: coarse atmosphere: ") + L->err);
+                break;
+            }
+            std::vector<double> zr, zp;
+            mg_ztables(F->z, zr, zp);
+            const int nl = mg_ncomp(c);
+            e = dalloc(&L->mg_src, (size_t)ncv * nl);
+            if (e == cudaSuccess) e = dalloc(&L->mg_rho0, (size_t)ncv * nl);
+            if (e == cudaSuccess) e = dalloc(&L->mg_res, (size_t)ncv * nl);
+            if (e == cudaSuccess) e = dalloc(&F->mg_zr, zr.size());
+            if (e == cudaSuccess) e = dalloc(&F->mg_zp, zp.size());
+            if (e == cudaSuccess) e = cudaMemcpy(F->mg_zr, zr.data(), zr.size() * sizeof(double), cudaMemcpyHostToDevice);
+            if (e == cudaSuccess) e = cudaMemcpy(F->mg_zp, zp.data(), zp.size() * sizeof(double), cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) {
+                rc = fail(c, PORTA_ENOMEM, "mg_setup: allocation");
+                break;
+            }
+            F = L;
+            continue;
+        }
         if ((rc = porta_create(&g, &a, &q, &o, &L))) {
             rc = fail(c, rc, "mg_setup: coarse level creation");
             break;
@@ -2184,8 +2261,8 @@ int porta_mg_setup(porta_ctx *c, int nlevels)
         F = L;
     }
     if (rc == PORTA_OK) {
-        cudaError_t e = dalloc(&c->mg_res, (size_t)c->nvox * c->nl);
-        if (e == cudaSuccess) e = dalloc(&c->mg_prev, (size_t)c->nvox * c->nl);
+        cudaError_t e = dalloc(&c->mg_res, (size_t)mg_nunk(c) * mg_ncomp(c));
+        if (e == cudaSuccess) e = dalloc(&c->mg_prev, (size_t)mg_nunk(c) * mg_ncomp(c));
         if (e != cudaSuccess) rc = fail(c, PORTA_ENOMEM, "mg_setup: allocation");
     }
     if (rc) mg_free(c);
@@ -2220,18 +2297,25 @@ int porta_mg_vcycle(porta_ctx *c, int npre, int npost, int ncoarse, double *max_
         L->stream = c->stream;
         levels.push_back(L);
     }
-    CK(cudaMemcpyAsync(c->mg_prev, c->d_rho, sizeof(double) * c->nvox * c->nl, cudaMemcpyDeviceToDevice, c->stream));
+    if (c->ml && !c->ml->have_pops) return fail(c, PORTA_ESTATE, "mg_vcycle: populations not set");
+    const long long nu = mg_nunk(c);
+    const int nc = mg_ncomp(c);
+    CK(cudaMemcpyAsync(c->mg_prev, mg_unk(c), sizeof(double) * nu * nc, cudaMemcpyDeviceToDevice, c->stream));
     int rc = mg_vcycle(levels.data(), (int)levels.size(), 0, npre, npost, ncoarse);
     if (rc) return rc;
     c->have_fs = c->have_jkq = false;
     CK(cudaMemsetAsync(c->d_resid, 0, sizeof(unsigned long long), c->stream));
-    cudaError_t e = run_change(c->nvox, c->nl, c->mg_prev, c->d_rho, c->d_resid, c->stream);
+    cudaError_t e = run_change(nu, nc, c->mg_prev, mg_unk(c), c->d_resid, c->stream, c->ml ? 1 : 0);
     if (e != cudaSuccess) return fail(c, PORTA_ECUDA, std::string("mg_vcycle: ") + cudaGetErrorString(e));
     if (max_change) {
         unsigned long long bits = 0;
         CK(cudaMemcpyAsync(&bits, c->d_resid, sizeof(bits), cudaMemcpyDeviceToHost, c->stream));
         CK(cudaStreamSynchronize(c->stream));
         std::memcpy(max_change, &bits, sizeof(double));
+    }
+    if (c->ml) {
+        for (porta_ctx *L : levels)
+            if ((rc = ml_check(L, "mg_vcycle"))) return L == c ? rc : fail(c, rc, L->err);
     }
     return PORTA_OK;
 }
@@ -2284,6 +2368,12 @@ int porta_ml_create(const porta_grid *g, const porta_ml_atom *a, const porta_qua
     }
     c->ml = m;
     m->mc = mc;
+    m->J.assign(a->J, a->J + a->nlevel);
+    m->E.assign(a->E, a->E + a->nlevel);
+    m->A.assign(a->A, a->A + a->nline);
+    m->eps.assign(a->eps, a->eps + a->nline);
+    m->up.assign(a->upper, a->upper + a->nline);
+    m->lo.assign(a->lower, a->lower + a->nline);
     m->nvox1 = (long long)g->nx * g->ny * g->nz;
     cudaError_t e = dalloc(&m->d_pops, (size_t)m->nvox1 * mc.nlev);
     if (e == cudaSuccess) e = dalloc(&m->d_chis, (size_t)m->nvox1);

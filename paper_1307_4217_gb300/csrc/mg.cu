@@ -9,7 +9,7 @@
 // prolongation over the 3 x 3 x (up to 4) fine nodes around a coarse node.
 // The z weights come as tables built on the host: per fine plane (k0, w0, k1,
 // w1) for the prolongation, per coarse plane up to 4 (fine plane, weight)
-// pairs for the restriction. Vectors of unknowns are [voxel][nl], FP64.
+// pairs for the restriction. Vectors of unknowns are [voxel][nl] (nl <= 8), FP64.
 #include "mg_kernels.cuh"
 
 namespace porta {
@@ -37,7 +37,7 @@ __global__ void restrict_kernel(int nxc, int nyc, long long nvc, int nxf, int ny
     const int I = (int)(v % nxc);
     const int J = (int)((v / nxc) % nyc);
     const int K = (int)(v / ((long long)nxc * nyc));
-    double acc[6] = {0, 0, 0, 0, 0, 0};
+    double acc[kMgMaxComp] = {};
     double den = 0.0;
     for (int e = 0; e < 4; ++e) {
         const double w = zr[8 * K + 2 * e + 1];
@@ -91,7 +91,7 @@ __global__ void prolong_add_kernel(int nxf, int nyf, long long nvf, int nxc, int
     }
     const long long kz[2] = {(long long)zp[4 * k], (long long)zp[4 * k + 2]};
     const double wz[2] = {zp[4 * k + 1], zp[4 * k + 3]};
-    double d[6] = {0, 0, 0, 0, 0, 0};
+    double d[kMgMaxComp] = {};
     for (int a = 0; a < 2; ++a) {
         if (wz[a] == 0.0) continue;
         for (int b = 0; b < 2; ++b) {
@@ -108,15 +108,18 @@ __global__ void prolong_add_kernel(int nxf, int nyf, long long nvf, int nxc, int
 }
 
 // max over voxels of |dS00| / |S00_old| and |S2/S00 (new) - S2/S00 (old)|
-// (the residual of the Jacobi update), as the IEEE bits of a non-negative double
-__global__ void change_kernel(long long nvox, int nl, const double *old, const double *cur, unsigned long long *resid)
+// (the residual of the Jacobi update), or with rel_all the relative change of
+// every component (populations), as the IEEE bits of a non-negative double
+__global__ void change_kernel(long long nvox, int nl, const double *old, const double *cur, int rel_all,
+                              unsigned long long *resid)
 {
     long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     double ch = 0.0;
     if (v < nvox) {
         const double *o = old + v * nl, *n = cur + v * nl;
         ch = fabs(n[0] - o[0]) / fabs(o[0]);
-        for (int c = 1; c < nl; ++c) ch = fmax(ch, fabs(n[c] / n[0] - o[c] / o[0]));
+        for (int c = 1; c < nl; ++c)
+            ch = fmax(ch, rel_all ? fabs(n[c] - o[c]) / fabs(o[c]) : fabs(n[c] / n[0] - o[c] / o[0]));
     }
     if (!(ch <= 1e300)) ch = 1e300;
     for (int s = 16; s > 0; s >>= 1) ch = fmax(ch, __shfl_xor_sync(0xffffffffu, ch, s));
@@ -169,9 +172,9 @@ cudaError_t run_prolong_add(int nxf, int nyf, int nzf, int nxc, int nyc, int nl,
 }
 
 cudaError_t run_change(long long nvox, int nl, const double *old, const double *cur, unsigned long long *resid,
-                       cudaStream_t st)
+                       cudaStream_t st, int rel_all)
 {
-    change_kernel<<<nblk(nvox, 256), 256, 0, st>>>(nvox, nl, old, cur, resid);
+    change_kernel<<<nblk(nvox, 256), 256, 0, st>>>(nvox, nl, old, cur, rel_all, resid);
     return cudaGetLastError();
 }
 

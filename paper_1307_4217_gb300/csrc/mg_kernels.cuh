@@ -4,6 +4,8 @@
 
 namespace porta {
 
+constexpr int kMgMaxComp = 8;   // unknowns per voxel handled by the transfer kernels
+
 // coarse = fine at the coincident nodes, one per-voxel array
 cudaError_t run_inject(int nxc, int nyc, int nzc, int nxf, int nyf, const double *fine, double *coarse, cudaStream_t st);
 // restriction [v][nl] fine -> coarse; zr: per coarse plane 4 x (fine plane, weight)
@@ -12,9 +14,10 @@ cudaError_t run_restrict(int nxc, int nyc, int nzc, int nxf, int nyf, int nl, co
 // fine += P (cnew - cold); zp: per fine plane (k0, w0, k1, w1)
 cudaError_t run_prolong_add(int nxf, int nyf, int nzf, int nxc, int nyc, int nl, const double *zp, const double *cnew,
                             const double *cold, double *fine, cudaStream_t st);
-// max relative change between two vectors of unknowns (atomic max on the IEEE bits in *resid)
+// max relative change between two vectors of unknowns (atomic max on the IEEE bits in *resid):
+// of S00 and of S2/S00, or with rel_all of every component
 cudaError_t run_change(long long nvox, int nl, const double *old, const double *cur, unsigned long long *resid,
-                       cudaStream_t st);
+                       cudaStream_t st, int rel_all = 0);
 // y += alpha x
 cudaError_t run_axpy(long long n, double alpha, const double *x, double *y, cudaStream_t st);
 

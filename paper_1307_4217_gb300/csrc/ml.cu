@@ -46,8 +46,49 @@ __global__ void ml_prepare_kernel(const MlConst mc, long long nvox1, const doubl
     if (nbad) atomicAdd(bad, (unsigned long long)nbad);
 }
 
+// rate coefficients of line k at voxel v: P_ul, P_lu with radiation jrad and
+// escape factor (1 - ls) on the spontaneous rate
+__device__ __forceinline__ void ml_rates(const MlConst &mc, int k, double t, double jrad, double ls, double &pul,
+                                         double &plu)
+{
+    const int u = mc.up[k], l = mc.lo[k];
+    const double clu = mc.g[u] / mc.g[l] * exp(-mc.dE[k] / t) * mc.Cul[k];
+    pul = mc.A[k] * (1.0 - ls) + mc.Bul[k] * jrad + mc.Cul[k];
+    plu = mc.Blu[k] * jrad + clu;
+}
+
+// out = alpha A(n) + add + with_f (1, 0, ..., 0): A(n)_0 = sum_i n_i, A(n)_i =
+// (M n)_i with the plain rates of Jbar (i >= 1)
+__global__ void ml_apply_kernel(const MlConst mc, long long nvox1, const double *kT, const double *jbar,
+                                const double *pops, double alpha, const double *add, int with_f, double *out)
+{
+    const long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (v >= nvox1) return;
+    const int L = mc.nlev;
+    double n[kMlMaxLevel], y[kMlMaxLevel];
+    for (int i = 0; i < L; ++i) {
+        n[i] = pops[v * L + i];
+        y[i] = 0.0;
+    }
+    const double t = kT[v];
+    for (int k = 0; k < mc.nline; ++k) {
+        const int u = mc.up[k], l = mc.lo[k];
+        double pul, plu;
+        ml_rates(mc, k, t, jbar[(long long)k * nvox1 + v], 0.0, pul, plu);
+        const double down = pul * n[u], up = plu * n[l];
+        y[l] += down - up;
+        y[u] += up - down;
+    }
+    double sum = 0.0;
+    for (int i = 0; i < L; ++i) sum += n[i];
+    y[0] = sum;
+    for (int i = 0; i < L; ++i)
+        out[v * L + i] = alpha * y[i] + (add ? add[v * L + i] : 0.0) + (with_f && i == 0 ? 1.0 : 0.0);
+}
+
 __global__ void ml_see_kernel(const MlConst mc, long long nvox1, const double *kT, const double *jbar,
-                              const double *lstar, double *pops, unsigned long long *resid, unsigned long long *bad)
+                              const double *lstar, const double *src, double *pops, unsigned long long *resid,
+                              unsigned long long *bad)
 {
     const long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     double ch = 0.0;
@@ -64,10 +105,8 @@ __global__ void ml_see_kernel(const MlConst mc, long long nvox1, const double *k
             const long long o = (long long)k * nvox1 + v;
             const double Sold = mc.r3[k] * n[u] / (n[l] * mc.g[u] / mc.g[l] - n[u]);
             const double ls = lstar[o];
-            const double jeff = jbar[o] - ls * Sold;
-            const double clu = mc.g[u] / mc.g[l] * exp(-mc.dE[k] / t) * mc.Cul[k];
-            const double pul = mc.A[k] * (1.0 - ls) + mc.Bul[k] * jeff + mc.Cul[k];
-            const double plu = mc.Blu[k] * jeff + clu;
+            double pul, plu;
+            ml_rates(mc, k, t, jbar[o] - ls * Sold, ls, pul, plu);
             M[l][u] += pul;
             M[u][u] -= pul;
             M[u][l] += plu;
@@ -75,7 +114,7 @@ __global__ void ml_see_kernel(const MlConst mc, long long nvox1, const double *k
         }
         // conservation row; Gaussian elimination with partial pivoting
         for (int j = 0; j < L; ++j) M[0][j] = 1.0;
-        for (int i = 0; i < L; ++i) x[i] = i == 0 ? 1.0 : 0.0;
+        for (int i = 0; i < L; ++i) x[i] = src ? src[v * L + i] : (i == 0 ? 1.0 : 0.0);
         bool ok = true;
         for (int c = 0; c < L; ++c) {
             int p = c;
@@ -145,9 +184,17 @@ template cudaError_t run_ml_prepare<double>(const MlConst &, long long, const do
                                             double *, double *, double *, double *, unsigned long long *, cudaStream_t);
 
 cudaError_t run_ml_see(const MlConst &mc, long long nvox1, const double *kT, const double *jbar, const double *lstar,
-                       double *pops, unsigned long long *resid, unsigned long long *bad, cudaStream_t st)
+                       double *pops, unsigned long long *resid, unsigned long long *bad, cudaStream_t st,
+                       const double *src)
 {
-    ml_see_kernel<<<nblk(nvox1, 128), 128, 0, st>>>(mc, nvox1, kT, jbar, lstar, pops, resid, bad);
+    ml_see_kernel<<<nblk(nvox1, 128), 128, 0, st>>>(mc, nvox1, kT, jbar, lstar, src, pops, resid, bad);
+    return cudaGetLastError();
+}
+
+cudaError_t run_ml_apply(const MlConst &mc, long long nvox1, const double *kT, const double *jbar, const double *pops,
+                         double alpha, const double *add, int with_f, double *out, cudaStream_t st)
+{
+    ml_apply_kernel<<<nblk(nvox1, 128), 128, 0, st>>>(mc, nvox1, kT, jbar, pops, alpha, add, with_f, out);
     return cudaGetLastError();
 }
 

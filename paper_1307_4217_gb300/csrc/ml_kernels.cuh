@@ -36,7 +36,15 @@ cudaError_t run_ml_prepare(const MlConst &mc, long long nvox1, const double *pop
 // [line][voxel] order), populations updated in place; the maximum relative
 // change goes to *resid as the IEEE bits of a non-negative double (atomic
 // max), non-finite or non-positive results count into *bad
+// src (per voxel, nlev; null: (1, 0, ..., 0)) is the right-hand side of the
+// rate equations with their conservation row (coarse-grid equations)
 cudaError_t run_ml_see(const MlConst &mc, long long nvox1, const double *kT, const double *jbar, const double *lstar,
-                       double *pops, unsigned long long *resid, unsigned long long *bad, cudaStream_t st);
+                       double *pops, unsigned long long *resid, unsigned long long *bad, cudaStream_t st,
+                       const double *src = nullptr);
+
+// out = alpha A(n) + add + with_f (1, 0, ..., 0) with A(n)_0 = sum_i n_i and
+// A(n)_i = (M n)_i for the plain radiative rates of Jbar (i >= 1); add may be null
+cudaError_t run_ml_apply(const MlConst &mc, long long nvox1, const double *kT, const double *jbar, const double *pops,
+                         double alpha, const double *add, int with_f, double *out, cudaStream_t st);
 
 }  // namespace porta

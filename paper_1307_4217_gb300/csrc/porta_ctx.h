@@ -19,6 +19,9 @@ struct MlState {
     double *d_kT = nullptr;            // kT (eV), nvox1
     unsigned long long *d_bad = nullptr;
     bool have_atm = false, have_pops = false;
+    // the atom as given (coarse multigrid levels are created from it)
+    std::vector<double> J, E, A, eps;
+    std::vector<int> up, lo;
 };
 
 // stream, fork/join events and work-list counters of the concurrent launch

@@ -135,3 +135,47 @@ def test_invalid_inputs_are_rejected():
     bad["eps"] = np.array([0.5, 1.0, 0.5, 0.5])
     with pytest.raises(P.PortaError):
         P.MlContext(atm, bad, *QUAD)
+
+
+@pytest.mark.parametrize("prec", [P.PORTA_FP64, P.PORTA_FP32])
+def test_multigrid_cycles_match_oracle(prec):
+    quad = (2, 4, 5)
+    atm = synth.multilevel_box(8, 8, 17, seed=2, tau_top=1e-2, tau_bot=1e2)
+    atom = synth.multilevel_atom(seed=3, eps_range=(1e-2, 3e-2))
+    p0 = ml.lte_populations(atom, atm["kT"])
+    levels = ml.hierarchy(atm, 3)
+    ctx = P.MlContext(atm, atom, *quad, precision=prec)
+    ctx.set_atmosphere(atm)
+    ctx.set_pops(p0)
+    ctx.mg_setup(3)
+    assert ctx.mg_levels() == [(8, 8, 17), (4, 4, 9), (2, 2, 5)]
+    want = p0
+    tol = 1e-9 if prec == P.PORTA_FP64 else 1e-4
+    for _ in range(2):
+        prev = want
+        want = ml.vcycle(levels, atom, quad, want)
+        ch = ctx.mg_vcycle(2, 4, 8)
+        got = ctx.get_pops()
+        assert np.max(np.abs(got / want - 1)) < tol
+        wch = np.max(np.abs(want - prev) / prev)
+        assert abs(ch - wch) < 10 * tol * wch
+
+
+def test_multigrid_reaches_the_jacobi_fixed_point():
+    quad = (2, 4, 5)
+    atm = synth.multilevel_box(8, 8, 17, seed=4, tau_top=1e-2, tau_bot=1e2)
+    atom = synth.multilevel_atom(seed=5, eps_range=(1e-2, 3e-2))
+    p0 = ml.lte_populations(atom, atm["kT"])
+    def make(pops):
+        c = P.MlContext(atm, atom, *quad, precision=P.PORTA_FP64)
+        c.set_atmosphere(atm)
+        c.set_pops(pops)
+        return c
+    a = make(p0)
+    a.mg_setup(3)
+    for _ in range(8):
+        ch = a.mg_vcycle(2, 4, 8)
+    assert ch < 1e-9
+    b = make(a.get_pops())
+    # a Jacobi iteration leaves the multigrid solution in place
+    assert b.ml_iterate(1) < 1e-9
