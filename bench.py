@@ -87,6 +87,7 @@ def args_parse():
                     help="gradients through Jacobi iterations: 'iterations,checkpoint spacing' (0 skips them)")
     ap.add_argument("--ml-steps", type=int, default=3,
                     help="timed Jacobi iterations of the multilevel atom on the 128x128x96 grid (0 skips them)")
+    ap.add_argument("--ml-mg-cycles", type=int, default=3, help="timed multigrid V-cycles of the multilevel atom")
     ap.add_argument("--fill", default="", help="force the concurrent filler launch: cluster,nu_group,fraction")
     ap.add_argument("--adjoint-cluster", type=int, default=0, help="force the adjoint cluster size (skips its tuning)")
     ap.add_argument("--adjoint-nu-group", type=int, default=0, help="force the adjoint frequencies per pass")
@@ -505,6 +506,19 @@ def run_cuda(args):
                 evm[k][1].record(stream)
             barrier()
             chg = mctx.ml_iterate(1)
+            # non-linear multigrid on 128x128x96 -> 64x64x48 -> 32x32x24 from LTE
+            mctx.mg_setup(3)
+            mctx.set_pops(pops0)
+            mg_cyc = []
+            for _ in range(args.ml_mg_cycles):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                ch = mctx.mg_vcycle(2, 4, 8)
+                e1.record(stream)
+                e1.synchronize()
+                mg_cyc.append((e0.elapsed_time(e1), ch))
+            mctx.set_pops(pops0)
+            jac_ch = [mctx.ml_iterate(7) for _ in range(args.ml_mg_cycles)]
         ml_ms = sum(e[0].elapsed_time(e[1]) for e in evm) / args.ml_steps
         nupd = len(atom["A"]) * 31 * NRAY * nxm * nym * nzm
         mlres = {"workload": f"{nxm}x{nym}x{nzm}, five-level atom (J = 0,1,2,1,2), four lines x 31 frequencies, "
@@ -512,6 +526,10 @@ def run_cuda(args):
                  "ms_per_iteration": ml_ms, "updates_per_iteration": nupd,
                  "updates_per_s": nupd / (ml_ms * 1e-3), "steps": args.ml_steps,
                  "max_change_after": chg, "launch": mctx.launch_info(),
+                 "multigrid": {"levels": mctx.mg_levels(), "cycle": "2 pre + 4 post Jacobi, 8 on the coarsest, from LTE",
+                               "vcycle_ms": [round(t, 1) for t, _ in mg_cyc],
+                               "vcycle_max_change": [c for _, c in mg_cyc],
+                               "jacobi_max_change_after_7k_iterations": jac_ch},
                  "timing": "CUDA events around one graph replay per step, L2 flushed between steps"}
         mctx.close()
 
