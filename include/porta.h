@@ -420,7 +420,32 @@ typedef struct {
     const double *J, *E;           /* nlevel */
     const int *upper, *lower;      /* nline level indices, E[upper] > E[lower] */
     const double *A, *eps;         /* nline */
+    int polarized;                 /* 0: populations only; 1: all rho^K_Q(J), K <= 2J */
+    double zeta;                   /* polarized: weak-field Zeeman splitting per gauss (Doppler widths) */
 } porta_ml_atom;
+
+/* The polarized multilevel atom (polarized = 1): the unknowns are the
+   multipolar components rho^K_Q(J) of every level (K = 0 .. 2J, Q = -K .. K,
+   no interference between levels; sum_J (2J+1)^2 real unknowns per voxel, 69
+   for J = 0, 1, 2, 1, 2), stored per voxel in the real order level, K, then
+   rho^K_0, Re rho^K_1, Im rho^K_1, ..., Re rho^K_K, Im rho^K_K
+   (rho^K_-Q = (-1)^Q conj rho^K_Q). Rate equations (the multilevel atom
+   without interference between levels; the paper takes them from LL04 Sect.
+   7.2): absorption TA, spontaneous emission TE and stimulated emission TS into
+   a level, relaxation RA + RE + RS out of it (Wigner 3j/6j/9j coefficients
+   times the line's J^Kr_Qr, Kr = 0, 2), the Hanle term i 2 pi nu_L g_J (b.J)
+   with Lande factor 1 for every level and nu_L = 1.3996e6 Hz/G, collisions on
+   the line transitions moving populations and relaxing every multipole of the
+   level they leave. Jacobi: Lambda-bar* preconditioning of the population
+   terms as for the unpolarized atom, the trace row sum_J sqrt(2J+1)
+   rho^0_0(J) = 1; one warp per voxel solves the FP64 system in shared
+   memory. Line transfer: each line is a polarized two-level formal solution
+   (Sec. 3) with the line opacity of the populations, the emissivity of the
+   upper level's K = 0, 2 multipoles (S^K_Q = S_line w^(K) conj(rho^K_Q /
+   rho^0_0), w^(K) = (-1)^(1+Jl+Ju) sqrt(3(2Ju+1)) {1 1 K; Ju Ju Jl}) and the
+   weak-field Zeeman term with 2 zeta B; dichroism from the lower levels'
+   atomic polarization and the orientation (K = 1) terms are not included, so
+   J^1_Q = 0. The multigrid cycle is not available for it. */
 
 /* Create a multilevel context on grid g (PORTA_EINVAL for an invalid atom or
    grid). The generic calls porta_formal_solve, porta_accumulate_jkq,
@@ -435,10 +460,23 @@ int porta_ml_create(const porta_grid *g, const porta_ml_atom *a, const porta_qua
 
 /* Per-voxel atmosphere (nvox doubles each, host or device per `where`):
    chi = opacity scale (> 0), kT = temperature in eV (> 0), vel = vertical
-   velocity in Doppler widths (the same for every line). */
-int porta_ml_set_atmosphere(porta_ctx *c, const double *chi, const double *kT, const double *vel, int where);
+   velocity in Doppler widths (the same for every line); bx, by, bz = magnetic
+   field in gauss (required for the polarized atom, ignored (may be NULL)
+   otherwise). */
+int porta_ml_set_atmosphere(porta_ctx *c, const double *chi, const double *kT, const double *vel, const double *bx,
+                            const double *by, const double *bz, int where);
 
-/* Populations [voxel][level] (> 0; the update normalizes them to sum 1).
+/* Number of real unknowns per voxel (nlevel for the unpolarized atom). */
+int porta_ml_unknowns(const porta_ctx *c, int *nunk);
+
+/* The full vector of unknowns [voxel][nunk] (populations, or the multipoles of
+   the polarized atom in the order given above). set requires the atmosphere
+   and rejects non-positive populations or a population inversion. */
+int porta_ml_set_unknowns(porta_ctx *c, const double *x, int where);
+int porta_ml_get_unknowns(porta_ctx *c, double *x, int where);
+
+/* Populations [voxel][level] (> 0; the update normalizes them to sum 1; for
+   the polarized atom: no atomic polarization, rho^0_0 = n / sqrt(2J+1)).
    Writes every line's opacity, source and Planck functions; PORTA_EINVAL if a
    line's opacity is not positive (population inversion). Requires the
    atmosphere. */

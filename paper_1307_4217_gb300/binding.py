@@ -52,7 +52,7 @@ class _Atmos(ctypes.Structure):
 class _MlAtom(ctypes.Structure):
     _fields_ = [("nlevel", ctypes.c_int), ("nline", ctypes.c_int), ("J", ctypes.c_void_p), ("E", ctypes.c_void_p),
                 ("upper", ctypes.c_void_p), ("lower", ctypes.c_void_p), ("A", ctypes.c_void_p),
-                ("eps", ctypes.c_void_p)]
+                ("eps", ctypes.c_void_p), ("polarized", ctypes.c_int), ("zeta", ctypes.c_double)]
 
 
 _P, _I, _D, _LL = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_longlong
@@ -91,7 +91,10 @@ _SIGS = {
     "porta_set_tape_limit": (_I, [_P, ctypes.c_longlong]),
     "porta_iterate_timing": (_I, [_P, _P]),
     "porta_ml_create": (_I, [_P, _P, _P, _P, _P]),
-    "porta_ml_set_atmosphere": (_I, [_P, _P, _P, _P, _I]),
+    "porta_ml_set_atmosphere": (_I, [_P, _P, _P, _P, _P, _P, _P, _I]),
+    "porta_ml_unknowns": (_I, [_P, _P]),
+    "porta_ml_set_unknowns": (_I, [_P, _P, _I]),
+    "porta_ml_get_unknowns": (_I, [_P, _P, _I]),
     "porta_ml_set_pops": (_I, [_P, _P, _I]),
     "porta_ml_get_pops": (_I, [_P, _P, _I]),
     "porta_ml_formal_solve": (_I, [_P, _P, _P, _I]),
@@ -336,8 +339,22 @@ def porta_ml_create(grid, atom, quad, opts):
     return rc, h
 
 
-def porta_ml_set_atmosphere(h, chi_ptr, kt_ptr, vel_ptr, where):
-    return lib().porta_ml_set_atmosphere(h, chi_ptr, kt_ptr, vel_ptr, where)
+def porta_ml_set_atmosphere(h, chi_ptr, kt_ptr, vel_ptr, bx_ptr, by_ptr, bz_ptr, where):
+    return lib().porta_ml_set_atmosphere(h, chi_ptr, kt_ptr, vel_ptr, bx_ptr, by_ptr, bz_ptr, where)
+
+
+def porta_ml_unknowns(h):
+    n = ctypes.c_int()
+    rc = lib().porta_ml_unknowns(h, ctypes.byref(n))
+    return rc, n.value
+
+
+def porta_ml_set_unknowns(h, ptr, where):
+    return lib().porta_ml_set_unknowns(h, ptr, where)
+
+
+def porta_ml_get_unknowns(h, ptr, where):
+    return lib().porta_ml_get_unknowns(h, ptr, where)
 
 
 def porta_ml_set_pops(h, ptr, where):
@@ -643,7 +660,8 @@ class MlContext(Context):
     produced by ``synth.multilevel_atom`` (J, E, lines (upper, lower), A, eps),
     ``atm`` with nx, ny, nz, lx, ly, z. Line arrays come back [line][voxel]."""
 
-    def __init__(self, atm, atom, n_mu, n_chi, n_nu, x_max=4.0, precision=PORTA_FP32, cluster=0, nu_group=0):
+    def __init__(self, atm, atom, n_mu, n_chi, n_nu, x_max=4.0, precision=PORTA_FP32, cluster=0, nu_group=0,
+                 polarized=False, zeta=None):
         self._keep = []
         z = np.ascontiguousarray(atm["z"], dtype=np.float64)
         J = np.ascontiguousarray(atom["J"], dtype=np.float64)
@@ -655,8 +673,10 @@ class MlContext(Context):
         eps = np.ascontiguousarray(atom["eps"], dtype=np.float64)
         self._keep += [z, J, E, up, lo, A, eps]
         g = _Grid(atm["nx"], atm["ny"], atm["nz"], float(atm["lx"]), float(atm["ly"]), z.ctypes.data)
+        if zeta is None:
+            zeta = float(atm.get("zeta", 0.0))
         a = _MlAtom(len(J), len(A), J.ctypes.data, E.ctypes.data, up.ctypes.data, lo.ctypes.data, A.ctypes.data,
-                    eps.ctypes.data)
+                    eps.ctypes.data, 1 if polarized else 0, float(zeta))
         q = _Quad(n_mu, n_chi, n_nu, float(x_max))
         o = _Opts(precision, cluster, nu_group)
         self.h = None
@@ -668,12 +688,18 @@ class MlContext(Context):
         self.__dict__.update(s)
         self.grid_shape = (atm["nz"], atm["ny"], atm["nx"])
         self.nlevel, self.nline = len(J), len(A)
+        self.polarized = bool(polarized)
         self.shape = (self.nline,) + self.grid_shape
         self.model = None
+        rc, self.nunk = porta_ml_unknowns(h)
+        self._check(rc)
 
     def set_atmosphere(self, atm):
         ptrs, where = [], None
-        for k in ("chi", "kT", "vel"):
+        for k in ("chi", "kT", "vel", "bx", "by", "bz"):
+            if atm.get(k) is None:
+                ptrs.append(None)
+                continue
             v = atm[k] if hasattr(atm[k], "data_ptr") else np.asarray(atm[k], dtype=np.float64)
             p, w, keep = _ptr_where(v)
             self._keep.append(keep)
@@ -682,6 +708,21 @@ class MlContext(Context):
                 raise TypeError("atmosphere arrays must all be host or all device")
             ptrs.append(p)
         self._check(porta_ml_set_atmosphere(self.h, *ptrs, where))
+
+    def set_unknowns(self, x):
+        """the vector of unknowns [voxel][nunk] (populations, or the real multipoles
+        level, K, rho^K_0, Re/Im rho^K_Q (Q = 1..K) of the polarized atom)"""
+        if not hasattr(x, "data_ptr"):
+            x = np.ascontiguousarray(x, dtype=np.float64)
+        p, w, keep = _ptr_where(x)
+        self._check(porta_ml_set_unknowns(self.h, p, w))
+
+    def get_unknowns(self, out=None):
+        if out is None:
+            out = np.zeros(self.grid_shape + (self.nunk,))
+        p, w, keep = _ptr_where(out)
+        self._check(porta_ml_get_unknowns(self.h, p, w))
+        return out
 
     def set_pops(self, pops):
         if not hasattr(pops, "data_ptr"):
@@ -699,7 +740,8 @@ class MlContext(Context):
     def ml_formal_solve(self, jbar=None, lstar=None, want=True):
         """Formal solution of every line; returns (Jbar, Lambda-bar*) [line][voxel] or (None, None)."""
         if want and jbar is None:
-            jbar, lstar = np.zeros(self.shape), np.zeros(self.shape)
+            jbar = np.zeros(self.shape + ((6,) if self.polarized else ()))
+            lstar = np.zeros(self.shape)
         pj, wj, kj = _ptr_where(jbar)
         pl, wl, kl = _ptr_where(lstar)
         where = wj if jbar is not None else (wl if lstar is not None else PORTA_DEVICE)

@@ -16,6 +16,7 @@
 #include "porta_internal.cuh"
 #include "mg_kernels.cuh"
 #include "ml_kernels.cuh"
+#include "mlpol_kernels.cuh"
 #include "see_kernels.cuh"
 
 using namespace porta;
@@ -867,6 +868,8 @@ void free_all(porta_ctx *c)
     mg_free(c);
     it_free(c);
     if (c->ml) {
+        cudaFree(c->ml->d_x);
+        cudaFree(c->ml->d_tab);
         cudaFree(c->ml->d_pops);
         cudaFree(c->ml->d_chis);
         cudaFree(c->ml->d_kT);
@@ -1301,6 +1304,13 @@ cudaError_t ml_prepare(porta_ctx *c)
     const size_t R = c->rsz;
     char *atm = (char *)c->d_atm;
     const long long n = c->nvox;
+    if (m->pol) {
+        if (c->precision == PORTA_FP32)
+            return run_mlpol_prepare<float>(m->mc, m->dev, m->nvox1, m->d_x, m->d_chis, m->d_kT, (float *)atm,
+                                            (float *)(atm + 5 * n * R), (float *)c->d_rhoR, c->d_rho, m->d_bad, c->stream);
+        return run_mlpol_prepare<double>(m->mc, m->dev, m->nvox1, m->d_x, m->d_chis, m->d_kT, (double *)atm,
+                                         (double *)(atm + 5 * n * R), (double *)c->d_rhoR, c->d_rho, m->d_bad, c->stream);
+    }
     if (c->precision == PORTA_FP32)
         return run_ml_prepare<float>(m->mc, m->nvox1, m->d_pops, m->d_chis, m->d_kT, (float *)atm,
                                      (float *)(atm + 5 * n * R), (float *)c->d_rhoR, c->d_rho, m->d_bad, c->stream);
@@ -1322,7 +1332,11 @@ cudaError_t enqueue_update(porta_ctx *c)
                    : run_see<double>(c->nvox, c->nl, c->model, c->bcrit, c->d_eps, c->d_bpl, c->d_b, c->d_jkq,
                                      c->d_lstar, c->d_rho, c->d_rhoR, c->d_resid, c->stream);
     MlState *m = c->ml;
-    e = run_ml_see(m->mc, m->nvox1, m->d_kT, c->d_jkq, c->d_lstar, m->d_pops, c->d_resid, m->d_bad, c->stream);
+    if (m->pol)
+        e = run_mlpol_see(m->mc, m->dev, m->nvox1, m->d_kT, c->d_jkq, c->d_lstar, c->d_b, m->d_x, c->d_resid, m->d_bad,
+                          c->stream);
+    else
+        e = run_ml_see(m->mc, m->nvox1, m->d_kT, c->d_jkq, c->d_lstar, m->d_pops, c->d_resid, m->d_bad, c->stream);
     if (e != cudaSuccess) return e;
     return ml_prepare(c);
 }
@@ -2123,6 +2137,7 @@ int porta_mg_setup(porta_ctx *c, int nlevels)
     if (!c) return PORTA_EINVAL;
     if (c->nbox != 1 && !c->ml) return fail(c, PORTA_EINVAL, "mg_setup: single-box contexts only");
     if (c->ml && !c->ml->have_atm) return fail(c, PORTA_ESTATE, "mg_setup: atmosphere not set");
+    if (c->ml && c->ml->pol) return fail(c, PORTA_EINVAL, "mg_setup: not available for the polarized multilevel atom");
     if (nlevels < 2 || nlevels > 8) return fail(c, PORTA_EINVAL, "mg_setup: nlevels in 2..8");
     if (!c->have_atm) return fail(c, PORTA_ESTATE, "mg_setup: atmosphere not set");
     {
@@ -2189,7 +2204,7 @@ int porta_mg_setup(porta_ctx *c, int nlevels)
                 rc = fail(c, PORTA_ECUDA, std::string("mg_setup: ") + cudaGetErrorString(e));
                 break;
             }
-            rc = porta_ml_set_atmosphere(L, tmp, tmp + ncv, tmp + 2 * ncv, PORTA_DEVICE);
+            rc = porta_ml_set_atmosphere(L, tmp, tmp + ncv, tmp + 2 * ncv, nullptr, nullptr, nullptr, PORTA_DEVICE);
             cudaFree(tmp);
             if (rc) {
                 rc = fail(c, rc, std::string("mg_setup: coarse atmosphere: ") + L->err);
@@ -2356,8 +2371,18 @@ int porta_ml_create(const porta_grid *g, const porta_ml_atom *a, const porta_qua
         mc.s[k] = mc.g[mc.up[k]] / mc.g[mc.lo[k]] * mc.A[k] / (mc.dE[k] * mc.dE[k]);
     }
     for (int k = a->nline - 1; k >= 0; --k) mc.s[k] /= mc.s[0];
+    if (a->polarized != 0 && a->polarized != 1) return PORTA_EINVAL;
+    if (a->polarized && !(a->zeta >= 0.0 && std::isfinite(a->zeta))) return PORTA_EINVAL;
+    MlPolTables tab;
+    if (a->polarized) {
+        std::vector<double> J(a->J, a->J + a->nlevel), E(a->E, a->E + a->nlevel), A(a->A, a->A + a->nline),
+            eps(a->eps, a->eps + a->nline);
+        std::vector<int> up(a->upper, a->upper + a->nline), lo(a->lower, a->lower + a->nline);
+        if (mlpol_tables(J, E, up, lo, A, eps, tab)) return PORTA_EINVAL;
+    }
     std::vector<porta_grid> grids(a->nline, *g);
-    porta_atom at{PORTA_MODEL_TWOLEVEL_UNPOL, 0.0, 1.0, 25.0};
+    porta_atom at{a->polarized ? PORTA_MODEL_TWOLEVEL_HANLE : PORTA_MODEL_TWOLEVEL_UNPOL,
+                  a->polarized ? a->zeta : 0.0, 1.0, 25.0};
     porta_ctx *c = nullptr;
     int rc = create_impl(a->nline, grids.data(), &at, q, o, &c);
     if (rc) return rc;
@@ -2380,6 +2405,44 @@ int porta_ml_create(const porta_grid *g, const porta_ml_atom *a, const porta_qua
     if (e == cudaSuccess) e = dalloc(&m->d_kT, (size_t)m->nvox1);
     if (e == cudaSuccess) e = cudaMalloc(&m->d_bad, sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemset(m->d_bad, 0, sizeof(unsigned long long));
+    m->nunk = mc.nlev;
+    if (e == cudaSuccess && a->polarized) {
+        // the tables in one device allocation: ints first, then doubles (8-byte aligned)
+        m->pol = true;
+        m->tab = tab;
+        m->nunk = tab.nunk;
+        const size_t ni = tab.pop_idx.size() + tab.up2.size() + tab.cell_rc.size() + tab.cell_start.size() +
+                          tab.ent_src.size();
+        const size_t nd = tab.w2.size() + tab.trace.size() + tab.ent_coef.size();
+        const size_t ibytes = (ni * sizeof(int) + 7) / 8 * 8;
+        std::vector<char> h(ibytes + nd * sizeof(double));
+        int *ip = (int *)h.data();
+        double *dp = (double *)(h.data() + ibytes);
+        size_t io[5], doff[3], k = 0, kd = 0;
+        const std::vector<int> *iv[5] = {&tab.pop_idx, &tab.up2, &tab.cell_rc, &tab.cell_start, &tab.ent_src};
+        for (int q2 = 0; q2 < 5; ++q2) {
+            io[q2] = k;
+            for (int x : *iv[q2]) ip[k++] = x;
+        }
+        const std::vector<double> *dv[3] = {&tab.w2, &tab.trace, &tab.ent_coef};
+        for (int q2 = 0; q2 < 3; ++q2) {
+            doff[q2] = kd;
+            for (double x : *dv[q2]) dp[kd++] = x;
+        }
+        e = cudaMalloc(&m->d_tab, h.size());
+        if (e == cudaSuccess) e = cudaMemcpy(m->d_tab, h.data(), h.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = dalloc(&m->d_x, (size_t)m->nvox1 * tab.nunk);
+        const int *di = (const int *)m->d_tab;
+        const double *dd = (const double *)((const char *)m->d_tab + ibytes);
+        MlPolDev &d = m->dev;
+        d.nunk = tab.nunk;
+        d.nsrc = tab.nsrc;
+        d.ncell = (int)tab.cell_start.size() - 1;
+        d.row0 = tab.row0;
+        d.src_j = tab.src_j; d.src_b = tab.src_b; d.src_clu = tab.src_clu; d.src_pop = tab.src_pop; d.src_spop = tab.src_spop;
+        d.pop_idx = di + io[0]; d.up2 = di + io[1]; d.cell_rc = di + io[2]; d.cell_start = di + io[3]; d.ent_src = di + io[4];
+        d.w2 = dd + doff[0]; d.trace = dd + doff[1]; d.ent_coef = dd + doff[2];
+    }
     if (e != cudaSuccess) {
         porta_destroy(c);
         return PORTA_ENOMEM;
@@ -2388,13 +2451,15 @@ int porta_ml_create(const porta_grid *g, const porta_ml_atom *a, const porta_qua
     return PORTA_OK;
 }
 
-int porta_ml_set_atmosphere(porta_ctx *c, const double *chi, const double *kT, const double *vel, int where)
+int porta_ml_set_atmosphere(porta_ctx *c, const double *chi, const double *kT, const double *vel, const double *bx,
+                            const double *by, const double *bz, int where)
 {
     if (!c) return PORTA_EINVAL;
     MlState *m = c->ml;
     if (!m) return fail(c, PORTA_EINVAL, "ml_set_atmosphere: not a multilevel context");
     if (!chi || !kT || !vel || (where != PORTA_HOST && where != PORTA_DEVICE))
         return fail(c, PORTA_EINVAL, "ml_set_atmosphere: bad argument");
+    if (m->pol && (!bx || !by || !bz)) return fail(c, PORTA_EINVAL, "ml_set_atmosphere: magnetic field required");
     const long long n1 = m->nvox1, n = c->nvox;
     std::vector<double> hv(n1);
     cudaMemcpyKind k = where == PORTA_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
@@ -2414,7 +2479,20 @@ int porta_ml_set_atmosphere(porta_ctx *c, const double *chi, const double *kT, c
     // function and source function are written from the populations
     std::vector<double> vrep(n), ones(n, 1.0), half(n, 0.5);
     for (int b = 0; b < m->mc.nline; ++b) std::memcpy(vrep.data() + b * n1, hv.data(), n1 * sizeof(double));
-    porta_atmos at{ones.data(), half.data(), ones.data(), vrep.data(), nullptr, nullptr, nullptr};
+    std::vector<double> brep[3];
+    if (m->pol) {
+        const double *src[3] = {bx, by, bz};
+        for (int d = 0; d < 3; ++d) {
+            brep[d].resize(n);
+            if (where == PORTA_DEVICE)
+                CK(cudaMemcpy(brep[d].data(), src[d], n1 * sizeof(double), cudaMemcpyDeviceToHost));
+            else
+                std::memcpy(brep[d].data(), src[d], n1 * sizeof(double));
+            for (int b = 1; b < m->mc.nline; ++b) std::memcpy(brep[d].data() + b * n1, brep[d].data(), n1 * sizeof(double));
+        }
+    }
+    porta_atmos at{ones.data(), half.data(), ones.data(), vrep.data(), m->pol ? brep[0].data() : nullptr,
+                   m->pol ? brep[1].data() : nullptr, m->pol ? brep[2].data() : nullptr};
     rc = porta_set_atmosphere(c, &at, PORTA_HOST);
     if (rc) return rc;
     m->have_atm = true;
@@ -2438,6 +2516,16 @@ int porta_ml_set_pops(porta_ctx *c, const double *pops, int where)
     unsigned long long bad = 0;
     if ((rc = count_bad(c, m->d_pops, n, 0.0, 1e300, &bad))) return rc;
     if (bad) return fail(c, PORTA_EINVAL, "ml_set_pops: populations must be finite and > 0");
+    if (m->pol) {
+        // no atomic polarization: rho^0_0 = n / sqrt(2J+1)
+        std::vector<double> hp(n), hx((size_t)m->nvox1 * m->nunk, 0.0);
+        CK(cudaStreamSynchronize(c->stream));
+        CK(cudaMemcpy(hp.data(), m->d_pops, n * sizeof(double), cudaMemcpyDeviceToHost));
+        for (long long v = 0; v < m->nvox1; ++v)
+            for (int i = 0; i < m->mc.nlev; ++i)
+                hx[v * m->nunk + m->tab.pop_idx[i]] = hp[v * m->mc.nlev + i] / std::sqrt(m->mc.g[i]);
+        CK(cudaMemcpy(m->d_x, hx.data(), hx.size() * sizeof(double), cudaMemcpyHostToDevice));
+    }
     CK(cudaMemsetAsync(m->d_bad, 0, sizeof(unsigned long long), c->stream));
     CK(ml_prepare(c));
     unsigned long long hb = 0;
@@ -2457,7 +2545,66 @@ int porta_ml_get_pops(porta_ctx *c, double *pops, int where)
     if (!m) return fail(c, PORTA_EINVAL, "ml_get_pops: not a multilevel context");
     if (!pops || (where != PORTA_HOST && where != PORTA_DEVICE)) return fail(c, PORTA_EINVAL, "ml_get_pops: bad argument");
     if (!m->have_pops) return fail(c, PORTA_ESTATE, "ml_get_pops: populations not set");
+    if (m->pol) {
+        std::vector<double> hx((size_t)m->nvox1 * m->nunk), hp((size_t)m->nvox1 * m->mc.nlev);
+        CK(cudaMemcpyAsync(hx.data(), m->d_x, hx.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        for (long long v = 0; v < m->nvox1; ++v)
+            for (int i = 0; i < m->mc.nlev; ++i)
+                hp[v * m->mc.nlev + i] = std::sqrt(m->mc.g[i]) * hx[v * m->nunk + m->tab.pop_idx[i]];
+        CK(cudaMemcpy(pops, hp.data(), hp.size() * sizeof(double),
+                      where == PORTA_DEVICE ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost));
+        return PORTA_OK;
+    }
     CK(cudaMemcpyAsync(pops, m->d_pops, m->nvox1 * m->mc.nlev * sizeof(double),
+                       where == PORTA_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+    if (where == PORTA_HOST) CK(cudaStreamSynchronize(c->stream));
+    return PORTA_OK;
+}
+
+int porta_ml_unknowns(const porta_ctx *c, int *nunk)
+{
+    if (!c || !nunk) return PORTA_EINVAL;
+    if (!c->ml) return PORTA_EINVAL;
+    *nunk = c->ml->nunk;
+    return PORTA_OK;
+}
+
+int porta_ml_set_unknowns(porta_ctx *c, const double *x, int where)
+{
+    if (!c) return PORTA_EINVAL;
+    MlState *m = c->ml;
+    if (!m) return fail(c, PORTA_EINVAL, "ml_set_unknowns: not a multilevel context");
+    if (!m->pol) return porta_ml_set_pops(c, x, where);
+    if (!x || (where != PORTA_HOST && where != PORTA_DEVICE)) return fail(c, PORTA_EINVAL, "ml_set_unknowns: bad argument");
+    if (!m->have_atm) return fail(c, PORTA_ESTATE, "ml_set_unknowns: atmosphere not set");
+    const long long n = m->nvox1 * m->nunk;
+    int rc = copy_in(c, m->d_x, x, n, where);
+    if (rc) return rc;
+    unsigned long long bad = 0;
+    if ((rc = count_bad(c, m->d_x, n, -1e300, 1e300, &bad))) return rc;
+    if (bad) return fail(c, PORTA_EINVAL, "ml_set_unknowns: non-finite value");
+    CK(cudaMemsetAsync(m->d_bad, 0, sizeof(unsigned long long), c->stream));
+    CK(ml_prepare(c));
+    unsigned long long hb = 0;
+    CK(cudaMemcpyAsync(&hb, m->d_bad, sizeof(hb), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (hb) return fail(c, PORTA_EINVAL, "ml_set_unknowns: non-positive population or line opacity");
+    m->have_pops = true;
+    c->have_rho = true;
+    c->have_fs = c->have_jkq = false;
+    return PORTA_OK;
+}
+
+int porta_ml_get_unknowns(porta_ctx *c, double *x, int where)
+{
+    if (!c) return PORTA_EINVAL;
+    MlState *m = c->ml;
+    if (!m) return fail(c, PORTA_EINVAL, "ml_get_unknowns: not a multilevel context");
+    if (!m->pol) return porta_ml_get_pops(c, x, where);
+    if (!x || (where != PORTA_HOST && where != PORTA_DEVICE)) return fail(c, PORTA_EINVAL, "ml_get_unknowns: bad argument");
+    if (!m->have_pops) return fail(c, PORTA_ESTATE, "ml_get_unknowns: unknowns not set");
+    CK(cudaMemcpyAsync(x, m->d_x, m->nvox1 * m->nunk * sizeof(double),
                        where == PORTA_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
     if (where == PORTA_HOST) CK(cudaStreamSynchronize(c->stream));
     return PORTA_OK;

@@ -1,0 +1,539 @@
+// Polarized multilevel atom: the multipolar components rho^K_Q(J) of every
+// level (K = 0 .. 2J, no interference between levels) as the unknowns of
+// Eq. 2, with the radiative rates of the multilevel atom (absorption,
+// spontaneous and stimulated emission, relaxation; Wigner 3j, 6j and 9j
+// symbols), the Hanle term and collisions on the line transitions.
+//
+// Host: the rate equations are linear in a short list of per-voxel sources
+// (1, the radiation tensors J^K_Q of each line, the field B, the collisional
+// excitation rates, and the Lambda-bar* terms of the preconditioned population
+// equations), so they are tabulated once per atom as a sparse list of
+// (row, column) cells, each a sum of (source, coefficient) terms, over the
+// real unknowns (Q = 0 real parts, Q > 0 real and imaginary parts; the
+// components Q < 0 follow from rho^K_-Q = (-1)^Q conj rho^K_Q).
+//
+// Device: mlpol_prepare_kernel writes each line's opacity, Planck function
+// and emission multipoles S^K_Q = S_line w^(K) conj(rho^K_Q / rho^0_0)(J_u)
+// (K = 0, 2) into the sweep arrays of the line's box (the polarized two-level
+// formal solver then solves every line); mlpol_see_kernel assembles the
+// 69 x 69 (in general nunk x nunk) real system of one voxel per warp in
+// shared memory, replaces the row of level 0's population by the trace
+// sum_J sqrt(2J+1) rho^0_0(J) = 1, and solves it in FP64 by Gaussian
+// elimination with partial pivoting.
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <map>
+#include <vector>
+
+#include "mlpol_kernels.cuh"
+
+namespace porta {
+
+// ---------------------------------------------------------------- Wigner symbols (Racah formulas)
+
+namespace {
+
+double fact(int n)
+{
+    double f = 1.0;
+    for (int k = 2; k <= n; ++k) f *= k;
+    return f;
+}
+
+// arguments doubled (2j, 2m), so half-integers are integers
+bool tri2(int a, int b, int c) { return a + b >= c && b + c >= a && c + a >= b && (a + b + c) % 2 == 0; }
+
+double delta2(int a, int b, int c)
+{
+    return fact((a + b - c) / 2) * fact((a - b + c) / 2) * fact((-a + b + c) / 2) / fact((a + b + c) / 2 + 1);
+}
+
+double w3j2(int j1, int j2, int j3, int m1, int m2, int m3)
+{
+    if (m1 + m2 + m3 != 0 || !tri2(j1, j2, j3)) return 0.0;
+    const int jm[3][2] = {{j1, m1}, {j2, m2}, {j3, m3}};
+    for (auto &p : jm)
+        if (std::abs(p[1]) > p[0] || (p[0] + p[1]) % 2) return 0.0;
+    double pre = delta2(j1, j2, j3);
+    for (auto &p : jm) pre *= fact((p[0] + p[1]) / 2) * fact((p[0] - p[1]) / 2);
+    const int kmin = std::max({0, (j2 - j3 - m1) / 2, (j1 - j3 + m2) / 2});
+    const int kmax = std::min({(j1 + j2 - j3) / 2, (j1 - m1) / 2, (j2 + m2) / 2});
+    double s = 0.0;
+    for (int k = kmin; k <= kmax; ++k) {
+        const double d = fact(k) * fact((j3 - j2 + m1) / 2 + k) * fact((j3 - j1 - m2) / 2 + k) *
+                         fact((j1 + j2 - j3) / 2 - k) * fact((j1 - m1) / 2 - k) * fact((j2 + m2) / 2 - k);
+        s += (k % 2 ? -1.0 : 1.0) / d;
+    }
+    const int e = (j1 - j2 - m3) / 2;
+    return ((e % 2 + 2) % 2 ? -1.0 : 1.0) * s * std::sqrt(pre);
+}
+
+double w6j2(int a, int b, int c, int d, int e, int f)
+{
+    if (!tri2(a, b, c) || !tri2(a, e, f) || !tri2(d, b, f) || !tri2(d, e, c)) return 0.0;
+    const double pre = delta2(a, b, c) * delta2(a, e, f) * delta2(d, b, f) * delta2(d, e, c);
+    const int t1 = (a + b + c) / 2, t2 = (a + e + f) / 2, t3 = (d + b + f) / 2, t4 = (d + e + c) / 2;
+    const int u1 = (a + b + d + e) / 2, u2 = (b + c + e + f) / 2, u3 = (c + a + f + d) / 2;
+    double s = 0.0;
+    for (int k = std::max({t1, t2, t3, t4}); k <= std::min({u1, u2, u3}); ++k)
+        s += (k % 2 ? -1.0 : 1.0) * fact(k + 1) /
+             (fact(k - t1) * fact(k - t2) * fact(k - t3) * fact(k - t4) * fact(u1 - k) * fact(u2 - k) * fact(u3 - k));
+    return s * std::sqrt(pre);
+}
+
+double w9j2(int a, int b, int c, int d, int e, int f, int g, int h, int i)
+{
+    const int lo = std::max({std::abs(a - i), std::abs(h - d), std::abs(b - f)});
+    const int hi = std::min({a + i, h + d, b + f});
+    double s = 0.0;
+    for (int x = lo; x <= hi; x += 2)
+        s += (x % 2 ? -1.0 : 1.0) * (x + 1) * w6j2(a, b, c, f, i, x) * w6j2(d, e, f, b, x, h) * w6j2(g, h, i, x, a, d);
+    return s;
+}
+
+int two(double j) { return (int)std::lround(2.0 * j); }
+double W3(double a, double b, double c, double d, double e, double f) { return w3j2(two(a), two(b), two(c), two(d), two(e), two(f)); }
+double W6(double a, double b, double c, double d, double e, double f) { return w6j2(two(a), two(b), two(c), two(d), two(e), two(f)); }
+double W9(double a, double b, double c, double d, double e, double f, double g, double h, double i)
+{
+    return w9j2(two(a), two(b), two(c), two(d), two(e), two(f), two(g), two(h), two(i));
+}
+double sgn(double e) { return (std::lround(e) % 2 + 2) % 2 ? -1.0 : 1.0; }
+
+using cplx = std::complex<double>;
+using CMat = std::vector<cplx>;     // n x n, row-major
+
+}  // namespace
+
+int mlpol_tables(const std::vector<double> &J, const std::vector<double> &E, const std::vector<int> &up,
+                 const std::vector<int> &lo, const std::vector<double> &A, const std::vector<double> &eps,
+                 MlPolTables &t)
+{
+    const int nlev = (int)J.size(), nline = (int)up.size();
+    // complex basis (level, K, Q), Q = -K..K; real basis (level, K, Q >= 0, part)
+    std::vector<int> cl, cK, cQ;
+    std::map<long long, int> cidx;
+    auto ckey = [](int i, int K, int Q) { return ((long long)i * 64 + K) * 64 + (Q + 32); };
+    for (int i = 0; i < nlev; ++i)
+        for (int K = 0; K <= two(J[i]); ++K)
+            for (int Q = -K; Q <= K; ++Q) {
+                cidx[ckey(i, K, Q)] = (int)cl.size();
+                cl.push_back(i); cK.push_back(K); cQ.push_back(Q);
+            }
+    const int n = (int)cl.size();
+    std::vector<int> rl, rK, rQ, rp;
+    for (int i = 0; i < nlev; ++i)
+        for (int K = 0; K <= two(J[i]); ++K) {
+            rl.push_back(i); rK.push_back(K); rQ.push_back(0); rp.push_back(0);
+            for (int Q = 1; Q <= K; ++Q)
+                for (int p = 0; p < 2; ++p) {
+                    rl.push_back(i); rK.push_back(K); rQ.push_back(Q); rp.push_back(p);
+                }
+        }
+    const int nr = (int)rl.size();
+    if (nr != n || n > kMlPolMaxUnk) return -1;
+    // x = C r
+    CMat Cm((size_t)n * nr, 0.0);
+    for (int k = 0; k < nr; ++k) {
+        const int i = rl[k], K = rK[k], Q = rQ[k];
+        if (Q == 0) {
+            Cm[(size_t)cidx[ckey(i, K, 0)] * nr + k] = 1.0;
+            continue;
+        }
+        const cplx z = rp[k] == 0 ? cplx(1.0, 0.0) : cplx(0.0, 1.0);
+        Cm[(size_t)cidx[ckey(i, K, Q)] * nr + k] += z;
+        Cm[(size_t)cidx[ckey(i, K, -Q)] * nr + k] += sgn(Q) * std::conj(z);
+    }
+    std::vector<double> g(nlev);
+    for (int i = 0; i < nlev; ++i) g[i] = 2.0 * J[i] + 1.0;
+    // source layout: 0 const, 1 + 6 li + c (J real layout J00, J20, Re J21, Im J21, Re J22, Im J22),
+    // then B (3), C_lu per line, -Lambda* S_old per line, -Lambda* per line
+    t.nline = nline;
+    t.src_j = 1;
+    t.src_b = 1 + 6 * nline;
+    t.src_clu = t.src_b + 3;
+    t.src_pop = t.src_clu + nline;
+    t.src_spop = t.src_pop + nline;
+    t.nsrc = t.src_spop + nline;
+    std::vector<CMat> G(t.nsrc, CMat((size_t)n * n, 0.0));
+    auto at = [n](CMat &M, int a, int b) -> cplx & { return M[(size_t)a * n + b]; };
+    // radiative matrices per (Kr, Qr), Kr = 0, 2 (the transfer gives no J^1_Q)
+    for (int li = 0; li < nline; ++li) {
+        const int u = up[li], l = lo[li];
+        const double Ju = J[u], Jl = J[l];
+        const double r = (E[u] - E[l]) / (E[up[0]] - E[lo[0]]);
+        const double Bul = A[li] / (r * r * r), Blu = g[u] / g[l] * Bul;
+        const double Cul = eps[li] / (1.0 - eps[li]) * A[li];
+        std::map<int, CMat> Mr;          // key Kr * 8 + (Qr + 2)
+        CMat Mpop((size_t)n * n, 0.0), Mspop((size_t)n * n, 0.0);
+        auto mr = [&](int Kr, int Qr) -> CMat & {
+            auto it = Mr.find(Kr * 8 + Qr + 2);
+            if (it == Mr.end()) it = Mr.emplace(Kr * 8 + Qr + 2, CMat((size_t)n * n, 0.0)).first;
+            return it->second;
+        };
+        for (int a = 0; a < n; ++a) {
+            const int lev = cl[a], K = cK[a], Q = cQ[a];
+            if (lev == u) {
+                for (int Kl = 0; Kl <= two(Jl); ++Kl)
+                    for (int Ql = -Kl; Ql <= Kl; ++Ql) {
+                        const int b = cidx[ckey(l, Kl, Ql)];
+                        for (int Kr = 0; Kr <= 2; Kr += 2)
+                            for (int Qr = -Kr; Qr <= Kr; ++Qr) {
+                                const double v = (2 * Jl + 1) * Blu * std::sqrt(3.0 * (2 * K + 1) * (2 * Kl + 1) * (2 * Kr + 1)) *
+                                                 sgn(Kl + Ql) * W9(Ju, Jl, 1, Ju, Jl, 1, K, Kl, Kr) * W3(K, Kl, Kr, -Q, Ql, -Qr);
+                                if (v == 0.0) continue;
+                                at(mr(Kr, Qr), a, b) += v;
+                                if (K == 0 && Kl == 0 && Kr == 0) at(Mpop, a, b) += v;
+                            }
+                    }
+                at(G[0], a, a) -= A[li];
+                if (K == 0) at(Mspop, a, a) -= A[li];
+                for (int Kp = 0; Kp <= two(Ju); ++Kp)
+                    for (int Qp = -Kp; Qp <= Kp; ++Qp) {
+                        const int b = cidx[ckey(u, Kp, Qp)];
+                        for (int Kr = 0; Kr <= 2; Kr += 2)
+                            for (int Qr = -Kr; Qr <= Kr; ++Qr) {
+                                if ((K + Kp + Kr) % 2) continue;
+                                const double v = (2 * Ju + 1) * Bul * std::sqrt(3.0 * (2 * K + 1) * (2 * Kp + 1) * (2 * Kr + 1)) *
+                                                 sgn(1 + Jl - Ju + Qp) * W6(K, Kp, Kr, Ju, Ju, Ju) * W6(1, 1, Kr, Ju, Ju, Jl) *
+                                                 W3(K, Kp, Kr, Q, -Qp, Qr);
+                                if (v == 0.0) continue;
+                                at(mr(Kr, Qr), a, b) -= v;
+                                if (K == 0 && Kp == 0 && Kr == 0) at(Mpop, a, b) -= v;
+                            }
+                    }
+                at(G[0], a, a) -= Cul;
+            }
+            if (lev == l) {
+                auto itb = cidx.find(ckey(u, K, Q));
+                if (itb != cidx.end()) {
+                    const double v = (2 * Ju + 1) * A[li] * sgn(1 + Ju + Jl + K) * W6(Ju, Ju, K, Jl, Jl, 1);
+                    at(G[0], a, itb->second) += v;
+                    if (K == 0) at(Mspop, a, itb->second) += v;
+                }
+                for (int Ku = 0; Ku <= two(Ju); ++Ku)
+                    for (int Qu = -Ku; Qu <= Ku; ++Qu) {
+                        const int b = cidx[ckey(u, Ku, Qu)];
+                        for (int Kr = 0; Kr <= 2; Kr += 2)
+                            for (int Qr = -Kr; Qr <= Kr; ++Qr) {
+                                const double v = (2 * Ju + 1) * Bul * std::sqrt(3.0 * (2 * K + 1) * (2 * Ku + 1) * (2 * Kr + 1)) *
+                                                 sgn(Kr + Ku + Qu) * W9(Ju, Jl, 1, Ju, Jl, 1, Ku, K, Kr) * W3(K, Ku, Kr, -Q, Qu, -Qr);
+                                if (v == 0.0) continue;
+                                at(mr(Kr, Qr), a, b) += v;
+                                if (K == 0 && Ku == 0 && Kr == 0) at(Mpop, a, b) += v;
+                            }
+                    }
+                for (int Kp = 0; Kp <= two(Jl); ++Kp)
+                    for (int Qp = -Kp; Qp <= Kp; ++Qp) {
+                        const int b = cidx[ckey(l, Kp, Qp)];
+                        for (int Kr = 0; Kr <= 2; Kr += 2)
+                            for (int Qr = -Kr; Qr <= Kr; ++Qr) {
+                                if ((K + Kp + Kr) % 2) continue;
+                                const double v = (2 * Jl + 1) * Blu * std::sqrt(3.0 * (2 * K + 1) * (2 * Kp + 1) * (2 * Kr + 1)) *
+                                                 sgn(1 + Ju - Jl + Kr + Qp) * W6(K, Kp, Kr, Jl, Jl, Jl) * W6(1, 1, Kr, Jl, Jl, Ju) *
+                                                 W3(K, Kp, Kr, Q, -Qp, Qr);
+                                if (v == 0.0) continue;
+                                at(mr(Kr, Qr), a, b) -= v;
+                                if (K == 0 && Kp == 0 && Kr == 0) at(Mpop, a, b) -= v;
+                            }
+                    }
+                // collisional excitation out of the lower level (unit C_lu; all multipoles relax)
+                at(G[t.src_clu + li], a, a) -= 1.0;
+            }
+        }
+        // collisional transfer of populations (n = sqrt(2J+1) rho^0_0)
+        const int a0u = cidx[ckey(u, 0, 0)], a0l = cidx[ckey(l, 0, 0)];
+        at(G[t.src_clu + li], a0u, a0l) += std::sqrt(g[l] / g[u]);
+        at(G[0], a0l, a0u) += Cul * std::sqrt(g[u] / g[l]);
+        // J sources of this line in the real layout
+        auto addJ = [&](int s, int Kr, int Qr, cplx f) {
+            auto it = Mr.find(Kr * 8 + Qr + 2);
+            if (it == Mr.end()) return;
+            for (size_t e = 0; e < it->second.size(); ++e) G[s][e] += f * it->second[e];
+        };
+        const int s0 = t.src_j + 6 * li;
+        addJ(s0 + 0, 0, 0, 1.0);
+        addJ(s0 + 1, 2, 0, 1.0);
+        addJ(s0 + 2, 2, 1, 1.0); addJ(s0 + 2, 2, -1, -1.0);
+        addJ(s0 + 3, 2, 1, cplx(0, 1)); addJ(s0 + 3, 2, -1, cplx(0, 1));
+        addJ(s0 + 4, 2, 2, 1.0); addJ(s0 + 4, 2, -2, 1.0);
+        addJ(s0 + 5, 2, 2, cplx(0, 1)); addJ(s0 + 5, 2, -2, cplx(0, -1));
+        G[t.src_pop + li] = Mpop;
+        G[t.src_spop + li] = Mspop;
+    }
+    // Hanle: i w_J H^K(b), Lande factor 1, b in gauss
+    const double wj = 2.0 * M_PI * kLarmorPerGauss;
+    for (int a = 0; a < n; ++a) {
+        const int lev = cl[a], K = cK[a], Q = cQ[a];
+        at(G[t.src_b + 2], a, a) += cplx(0, wj * Q);
+        if (Q - 1 >= -K) {
+            const int b = cidx[ckey(lev, K, Q - 1)];
+            const double f = 0.5 * std::sqrt((double)(K + Q) * (K - Q + 1));
+            at(G[t.src_b + 0], a, b) += cplx(0, wj * f);
+            at(G[t.src_b + 1], a, b) += cplx(wj * f, 0);      // i * (-i) = 1
+        }
+        if (Q + 1 <= K) {
+            const int b = cidx[ckey(lev, K, Q + 1)];
+            const double f = 0.5 * std::sqrt((double)(K - Q) * (K + Q + 1));
+            at(G[t.src_b + 0], a, b) += cplx(0, wj * f);
+            at(G[t.src_b + 1], a, b) += cplx(-wj * f, 0);     // i * i = -1
+        }
+    }
+    // real system rows: (complex row, part); trace row
+    t.nunk = nr;
+    t.trace.assign(nr, 0.0);
+    t.pop_idx.assign(nlev, -1);
+    t.row0 = -1;
+    for (int k = 0; k < nr; ++k)
+        if (rK[k] == 0) {
+            t.trace[k] = std::sqrt(g[rl[k]]);
+            t.pop_idx[rl[k]] = k;
+            if (rl[k] == 0) t.row0 = k;
+        }
+    // sparse cells of the real matrices R_s = select(G_s C)
+    std::map<long long, std::vector<std::pair<int, double>>> cells;
+    for (int s = 0; s < t.nsrc; ++s)
+        for (int row = 0; row < nr; ++row) {
+            if (row == t.row0) continue;
+            const int ci = cidx[ckey(rl[row], rK[row], rQ[row])];
+            for (int col = 0; col < nr; ++col) {
+                cplx y = 0.0;
+                for (int b = 0; b < n; ++b) {
+                    const cplx m = G[s][(size_t)ci * n + b];
+                    if (m != 0.0) y += m * Cm[(size_t)b * nr + col];
+                }
+                const double v = rp[row] == 0 ? y.real() : y.imag();
+                if (std::abs(v) > 0.0) cells[(long long)row * nr + col].emplace_back(s, v);
+            }
+        }
+    t.cell_rc.clear(); t.cell_start.assign(1, 0); t.ent_src.clear(); t.ent_coef.clear();
+    for (auto &c : cells) {
+        t.cell_rc.push_back((int)(c.first / nr));
+        t.cell_rc.push_back((int)(c.first % nr));
+        for (auto &e : c.second) {
+            t.ent_src.push_back(e.first);
+            t.ent_coef.push_back(e.second);
+        }
+        t.cell_start.push_back((int)t.ent_src.size());
+    }
+    // emission multipoles of each line: rho^0_0 and rho^2_Q (Q = 0, 1 re/im, 2 re/im) of the upper level
+    t.w2.assign(nline, 0.0);
+    t.up2.assign(6 * (size_t)nline, -1);
+    for (int li = 0; li < nline; ++li) {
+        const int u = up[li], l = lo[li];
+        auto ridx = [&](int i, int K, int Q, int p) {
+            for (int k = 0; k < nr; ++k)
+                if (rl[k] == i && rK[k] == K && rQ[k] == Q && rp[k] == p) return k;
+            return -1;
+        };
+        t.up2[6 * li] = ridx(u, 0, 0, 0);
+        if (two(J[u]) >= 2) {
+            t.w2[li] = sgn(1 + J[l] + J[u]) * std::sqrt(3.0 * (2 * J[u] + 1)) * W6(1, 1, 2, J[u], J[u], J[l]);
+            t.up2[6 * li + 1] = ridx(u, 2, 0, 0);
+            t.up2[6 * li + 2] = ridx(u, 2, 1, 0);
+            t.up2[6 * li + 3] = ridx(u, 2, 1, 1);
+            t.up2[6 * li + 4] = ridx(u, 2, 2, 0);
+            t.up2[6 * li + 5] = ridx(u, 2, 2, 1);
+        }
+    }
+    return 0;
+}
+
+// ---------------------------------------------------------------- kernels
+
+namespace {
+
+inline int nblk(long long n, int t) { return (int)((n + t - 1) / t); }
+
+template <typename Real>
+__global__ void mlpol_prepare_kernel(const MlConst mc, MlPolDev T, long long nvox1, const double *x, const double *chis,
+                                     const double *kT, Real *chi_out, Real *bpl_out, Real *S_out, double *S64_out,
+                                     unsigned long long *bad)
+{
+    const long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (v >= nvox1) return;
+    const double *xv = x + v * T.nunk;
+    double n[kMlMaxLevel];
+    for (int i = 0; i < mc.nlev; ++i) n[i] = sqrt(mc.g[i]) * xv[T.pop_idx[i]];
+    const long long nvox = nvox1 * mc.nline;
+    const double chi = chis[v], t = kT[v];
+    int nbad = 0;
+    for (int k = 0; k < mc.nline; ++k) {
+        const int u = mc.up[k], l = mc.lo[k];
+        const double op = chi * mc.s[k] * (n[l] - n[u] * mc.g[l] / mc.g[u]);
+        const double S = mc.r3[k] * n[u] / (n[l] * mc.g[u] / mc.g[l] - n[u]);
+        const long long o = (long long)k * nvox1 + v;
+        nbad += !(op > 0.0 && op < 1e300) || !(fabs(S) < 1e300);
+        chi_out[o] = (Real)op;
+        bpl_out[o] = (Real)(mc.r3[k] / expm1(mc.dE[k] / t));
+        // S^K_Q = S w2 conj(rho^2_Q / rho^0_0)(upper), two-level real layout
+        double s6[6] = {S, 0, 0, 0, 0, 0};
+        const int *ix = T.up2 + 6 * k;
+        if (ix[1] >= 0) {
+            const double f = S * T.w2[k] / xv[ix[0]];
+            s6[1] = f * xv[ix[1]];
+            s6[2] = f * xv[ix[2]];
+            s6[3] = -f * xv[ix[3]];
+            s6[4] = f * xv[ix[4]];
+            s6[5] = -f * xv[ix[5]];
+        }
+        for (int c = 0; c < 6; ++c) {
+            S64_out[o * 6 + c] = s6[c];
+            S_out[c * nvox + o] = (Real)s6[c];
+        }
+    }
+    if (nbad) atomicAdd(bad, (unsigned long long)nbad);
+}
+
+// one warp per voxel; shared memory per warp: A[nunk][nunk + 1], x_old, x_new, sources
+__global__ void mlpol_see_kernel(const MlConst mc, MlPolDev T, long long nvox1, const double *kT, const double *jkq,
+                                 const double *lstar, const double *bvec, double *x, unsigned long long *resid,
+                                 unsigned long long *bad)
+{
+    extern __shared__ double sm[];
+    const int N = T.nunk, N1 = N + 1;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int per = N * N1 + 2 * N + T.nsrc;
+    double *A = sm + (size_t)wib * per;
+    double *xo = A + N * N1;
+    double *xn = xo + N;
+    double *s = xn + N;
+    const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
+    double ch_max = 0.0;
+    for (long long v = (long long)blockIdx.x * (blockDim.x >> 5) + wib; v < nvox1; v += nwarps) {
+        for (int k = lane; k < N; k += 32) xo[k] = x[v * N + k];
+        __syncwarp();
+        // sources
+        if (lane == 0) {
+            s[0] = 1.0;
+            s[T.src_b] = bvec[v];
+            s[T.src_b + 1] = bvec[nvox1 * mc.nline + v];
+            s[T.src_b + 2] = bvec[2 * nvox1 * mc.nline + v];
+        }
+        for (int k = lane; k < mc.nline; k += 32) {
+            const int u = mc.up[k], l = mc.lo[k];
+            const double nu = sqrt(mc.g[u]) * xo[T.pop_idx[u]], nl = sqrt(mc.g[l]) * xo[T.pop_idx[l]];
+            const double Sold = mc.r3[k] * nu / (nl * mc.g[u] / mc.g[l] - nu);
+            const long long o = (long long)k * nvox1 + v;
+            const double ls = lstar[o];
+            for (int c = 0; c < 6; ++c) s[T.src_j + 6 * k + c] = jkq[o * 6 + c];
+            s[T.src_clu + k] = mc.g[u] / mc.g[l] * exp(-mc.dE[k] / kT[v]) * mc.Cul[k];
+            s[T.src_pop + k] = -ls * Sold;
+            s[T.src_spop + k] = -ls;
+        }
+        for (int e = lane; e < N * N1; e += 32) A[e] = 0.0;
+        __syncwarp();
+        for (int c = lane; c < T.ncell; c += 32) {
+            double val = 0.0;
+            for (int e = T.cell_start[c]; e < T.cell_start[c + 1]; ++e) val += T.ent_coef[e] * s[T.ent_src[e]];
+            A[T.cell_rc[2 * c] * N1 + T.cell_rc[2 * c + 1]] = val;
+        }
+        __syncwarp();
+        for (int j = lane; j < N; j += 32) A[T.row0 * N1 + j] = T.trace[j];
+        for (int r = lane; r < N; r += 32) A[r * N1 + N] = r == T.row0 ? 1.0 : 0.0;
+        __syncwarp();
+        // Gaussian elimination with partial pivoting on [A | b]
+        bool ok = true;
+        for (int k = 0; k < N; ++k) {
+            double bv = -1.0;
+            int br = k;
+            for (int r = k + lane; r < N; r += 32) {
+                const double a = fabs(A[r * N1 + k]);
+                if (a > bv) { bv = a; br = r; }
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+                const int orr = __shfl_xor_sync(0xffffffffu, br, o);
+                if (ov > bv || (ov == bv && orr < br)) { bv = ov; br = orr; }
+            }
+            if (!(bv > 0.0)) { ok = false; break; }
+            if (br != k)
+                for (int j = k + lane; j <= N; j += 32) {
+                    const double tmp = A[k * N1 + j];
+                    A[k * N1 + j] = A[br * N1 + j];
+                    A[br * N1 + j] = tmp;
+                }
+            __syncwarp();
+            const double inv = 1.0 / A[k * N1 + k];
+            for (int j = k + 1 + lane; j <= N; j += 32) {
+                const double akj = A[k * N1 + j] * inv;
+                for (int r = k + 1; r < N; ++r) A[r * N1 + j] -= A[r * N1 + k] * akj;
+            }
+            __syncwarp();
+        }
+        double ch = 0.0;
+        if (ok) {
+            for (int k = N - 1; k >= 0; --k) {
+                double acc = 0.0;
+                for (int j = k + 1 + lane; j < N; j += 32) acc += A[k * N1 + j] * xn[j];
+                for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+                if (lane == 0) xn[k] = (A[k * N1 + N] - acc) / A[k * N1 + k];
+                __syncwarp();
+            }
+            int nb = 0;
+            for (int i = lane; i < mc.nlev; i += 32) {
+                const double p0 = xo[T.pop_idx[i]], p1 = xn[T.pop_idx[i]];
+                nb += !(p1 > 0.0 && p1 < 1e300);
+                ch = fmax(ch, fabs(p1 - p0) / fabs(p0));
+            }
+            for (int k = lane; k < N; k += 32) nb += !(fabs(xn[k]) < 1e300);
+            for (int o = 16; o > 0; o >>= 1) nb += __shfl_xor_sync(0xffffffffu, nb, o);
+            if (nb) {
+                ok = false;
+            } else {
+                for (int k = lane; k < N; k += 32) x[v * N + k] = xn[k];
+            }
+        }
+        if (!ok) {
+            if (lane == 0) atomicAdd(bad, 1ull);
+            ch = 1e300;
+        }
+        for (int o = 16; o > 0; o >>= 1) ch = fmax(ch, __shfl_xor_sync(0xffffffffu, ch, o));
+        ch_max = fmax(ch_max, ch);
+        __syncwarp();
+    }
+    if (lane == 0 && ch_max > 0.0) atomicMax(resid, (unsigned long long)__double_as_longlong(fmin(ch_max, 1e300)));
+}
+
+}  // namespace
+
+template <typename Real>
+cudaError_t run_mlpol_prepare(const MlConst &mc, const MlPolDev &T, long long nvox1, const double *x, const double *chis,
+                              const double *kT, Real *chi_out, Real *bpl_out, Real *S_out, double *S64_out,
+                              unsigned long long *bad, cudaStream_t st)
+{
+    mlpol_prepare_kernel<Real><<<nblk(nvox1, 128), 128, 0, st>>>(mc, T, nvox1, x, chis, kT, chi_out, bpl_out, S_out,
+                                                                 S64_out, bad);
+    return cudaGetLastError();
+}
+template cudaError_t run_mlpol_prepare<float>(const MlConst &, const MlPolDev &, long long, const double *, const double *,
+                                              const double *, float *, float *, float *, double *,
+                                              unsigned long long *, cudaStream_t);
+template cudaError_t run_mlpol_prepare<double>(const MlConst &, const MlPolDev &, long long, const double *, const double *,
+                                               const double *, double *, double *, double *, double *,
+                                               unsigned long long *, cudaStream_t);
+
+size_t mlpol_see_smem(const MlPolDev &T, int warps)
+{
+    return sizeof(double) * (size_t)warps * ((size_t)T.nunk * (T.nunk + 1) + 2 * T.nunk + T.nsrc);
+}
+
+cudaError_t run_mlpol_see(const MlConst &mc, const MlPolDev &T, long long nvox1, const double *kT, const double *jkq,
+                          const double *lstar, const double *bvec, double *x, unsigned long long *resid,
+                          unsigned long long *bad, cudaStream_t st)
+{
+    const int warps = 2;
+    const size_t smem = mlpol_see_smem(T, warps);
+    cudaError_t e = cudaFuncSetAttribute(mlpol_see_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const long long blocks = std::min<long long>((nvox1 + warps - 1) / warps, 2LL * nsm);
+    mlpol_see_kernel<<<(int)std::max<long long>(1, blocks), 32 * warps, smem, st>>>(mc, T, nvox1, kT, jkq, lstar, bvec,
+                                                                                   x, resid, bad);
+    return cudaGetLastError();
+}
+
+}  // namespace porta

@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "ml_kernels.cuh"
+#include "mlpol_kernels.cuh"
 #include "porta_internal.cuh"
 
 // multilevel atom without polarization: one box of the batch per line
@@ -22,6 +23,13 @@ struct MlState {
     // the atom as given (coarse multigrid levels are created from it)
     std::vector<double> J, E, A, eps;
     std::vector<int> up, lo;
+    // polarized atom: multipoles x [nvox1][nunk] and the rate-equation tables
+    bool pol = false;
+    int nunk = 0;
+    double *d_x = nullptr;
+    void *d_tab = nullptr;
+    porta::MlPolTables tab;
+    porta::MlPolDev dev{};
 };
 
 // stream, fork/join events and work-list counters of the concurrent launch

@@ -1,0 +1,158 @@
+"""Polarized multilevel atom on the GPU (porta_ml_* with polarized = 1) against
+the oracle (oracle/mlpol.py): per-line radiation tensors, one update of the 69
+multipoles per voxel from the same sums, iterations, the converged solution and
+graph replay.
+
+Tolerances. FP64: 1e-10 relative on J^0_0, 1e-10 of J^0_0 on J^2_Q, and one
+update from the same sums to 1e-11 of the largest unknown (the two sides
+assemble the same rate equations from differently ordered sums and solve them
+by elimination with pivoting). FP32 sweeps: J^0_0 to 2e-5 relative and J^2_Q to
+2e-6 of J^0_0 (the two-level tolerances), populations after iterations and at
+convergence to 1e-4 relative, multipole ratios rho^K_Q / rho^0_0 to 1e-5
+absolute.
+"""
+import numpy as np
+import pytest
+
+import paper_1307_4217_gb300 as P
+import synth
+from oracle import ml, mlpol
+
+pytestmark = pytest.mark.gpu
+
+QUAD = (2, 4, 5)
+
+
+def _case(nx=6, ny=5, nz=8, seed=2, eps_range=(1e-3, 1e-1)):
+    atm = synth.multilevel_box(nx, ny, nz, seed=seed, tau_top=1e-3, tau_bot=1e2)
+    atom = synth.multilevel_atom(seed=seed + 1, eps_range=eps_range)
+    tab = mlpol.Tables(atom)
+    x = mlpol.lte_unknowns(tab, atm["kT"])
+    rng = np.random.default_rng(seed)
+    rb = mlpol.real_basis(atom)
+    for k, (i, K, Q, part) in enumerate(rb):
+        r00 = x[..., rb.index((i, 0, 0, 0))]
+        if K == 0:
+            x[..., k] *= np.exp(0.2 * rng.normal(size=r00.shape))
+        elif K % 2 == 0:
+            x[..., k] = 0.02 * r00 * rng.normal(size=r00.shape)
+    return atm, atom, tab, x
+
+
+def _ctx(atm, atom, prec, x):
+    c = P.MlContext(atm, atom, *QUAD, precision=prec, polarized=True)
+    c.set_atmosphere(atm)
+    c.set_unknowns(x)
+    return c
+
+
+def _j9(j6):
+    """GPU [line][grid][6] (J00, J20, Re/Im J21, Re/Im J22) -> oracle [grid][line][9]"""
+    j6 = np.moveaxis(np.asarray(j6), 0, -2)
+    out = np.zeros(j6.shape[:-1] + (9,))
+    out[..., 0] = j6[..., 0]
+    out[..., 4:9] = j6[..., 1:6]
+    return out
+
+
+def _bvec(atm):
+    return np.stack([atm["bx"], atm["by"], atm["bz"]], -1)
+
+
+def test_sizes_and_unknown_layout():
+    atm, atom, tab, x = _case()
+    ctx = _ctx(atm, atom, P.PORTA_FP64, x)
+    assert ctx.nunk == 69
+    assert np.array_equal(ctx.get_unknowns(), x)
+    pops = ctx.get_pops()
+    assert np.allclose(pops, tab.populations(x), rtol=1e-15)
+
+
+@pytest.mark.parametrize("prec", [P.PORTA_FP64, P.PORTA_FP32])
+def test_line_radiation_tensors_match_oracle(prec):
+    atm, atom, tab, x = _case()
+    ctx = _ctx(atm, atom, prec, x)
+    jb, ls = ctx.ml_formal_solve()
+    oj, ol = mlpol.formal_solve_lines(atm, atom, tab, x, QUAD)
+    gj = _j9(jb)
+    fp64 = prec == P.PORTA_FP64
+    j00 = oj[..., 0]
+    assert np.max(np.abs(gj[..., 0] - j00) / j00) < (1e-10 if fp64 else 2e-5)
+    assert np.max(np.abs(gj[..., 4:9] - oj[..., 4:9]) / j00[..., None]) < (1e-10 if fp64 else 2e-6)
+    assert np.max(np.abs(np.moveaxis(ls, 0, -1) - ol)) < (1e-10 if fp64 else 2e-5) * np.max(ol)
+
+
+def test_update_matches_oracle_update():
+    atm, atom, tab, x = _case(seed=4)
+    ctx = _ctx(atm, atom, P.PORTA_FP64, x)
+    jb, ls = ctx.ml_formal_solve()
+    change = ctx.ml_see_update()
+    got = ctx.get_unknowns()
+    want, wchange = mlpol.see_update(tab, atm["kT"], x, _j9(jb), np.moveaxis(ls, 0, -1), _bvec(atm))
+    assert np.max(np.abs(got - want)) < 1e-11 * np.max(np.abs(want))
+    assert abs(change - wchange) < 1e-9 * wchange
+
+
+@pytest.mark.parametrize("prec", [P.PORTA_FP64, P.PORTA_FP32])
+def test_iterations_match_oracle(prec):
+    atm, atom, tab, x = _case(seed=5)
+    ctx = _ctx(atm, atom, prec, x)
+    ctx.ml_iterate(3)
+    got = ctx.get_unknowns()
+    want, _ = mlpol.iterate(atm, atom, tab, x, QUAD, 3)
+    fp64 = prec == P.PORTA_FP64
+    pg, pw = tab.populations(got), tab.populations(want)
+    assert np.max(np.abs(pg / pw - 1)) < (1e-9 if fp64 else 1e-4)
+    rb = mlpol.real_basis(atom)
+    r00 = np.stack([want[..., rb.index((i, 0, 0, 0))] for (i, K, Q, p) in rb], -1)
+    assert np.max(np.abs((got - want) / r00)) < (1e-9 if fp64 else 1e-5)
+
+
+@pytest.mark.parametrize("prec", [P.PORTA_FP64, P.PORTA_FP32])
+def test_converged_solution_matches_oracle(prec):
+    atm, atom, tab, _ = _case(nx=4, ny=4, nz=8, seed=7, eps_range=(3e-2, 1e-1))
+    x0 = mlpol.lte_unknowns(tab, atm["kT"])
+    want = x0
+    for _ in range(200):
+        want, ch = mlpol.iterate(atm, atom, tab, want, QUAD, 1)
+        if ch < 1e-12:
+            break
+    ctx = _ctx(atm, atom, prec, x0)
+    for _ in range(30):
+        ch = ctx.ml_iterate(10)
+        if ch < (1e-12 if prec == P.PORTA_FP64 else 1e-7):
+            break
+    got = ctx.get_unknowns()
+    rb = mlpol.real_basis(atom)
+    r00 = np.stack([want[..., rb.index((i, 0, 0, 0))] for (i, K, Q, p) in rb], -1)
+    fp64 = prec == P.PORTA_FP64
+    assert np.max(np.abs(tab.populations(got) / tab.populations(want) - 1)) < (1e-9 if fp64 else 1e-4)
+    assert np.max(np.abs((got - want) / r00)) < (1e-9 if fp64 else 1e-5)
+    # atomic polarization is present (alignment of the upper levels)
+    assert np.max(np.abs(want[..., rb.index((3, 2, 0, 0))] / want[..., rb.index((3, 0, 0, 0))])) > 1e-4
+
+
+def test_graph_replay_equals_eager_iterations():
+    import torch
+    atm, atom, tab, x = _case(seed=6)
+    a = _ctx(atm, atom, P.PORTA_FP32, x)
+    b = _ctx(atm, atom, P.PORTA_FP32, x)
+    s = torch.cuda.Stream()
+    b.set_stream(s)
+    a.ml_iterate(3)
+    with torch.cuda.stream(s):
+        b.run_iterations(3)
+    s.synchronize()
+    assert np.array_equal(a.get_unknowns(), b.get_unknowns())
+
+
+def test_invalid_inputs_are_rejected():
+    atm, atom, tab, x = _case()
+    ctx = P.MlContext(atm, atom, *QUAD, precision=P.PORTA_FP32, polarized=True)
+    no_field = {k: v for k, v in atm.items() if k not in ("bx", "by", "bz")}
+    with pytest.raises(P.PortaError):
+        ctx.set_atmosphere(no_field)
+    ctx.set_atmosphere(atm)
+    ctx.set_unknowns(x)
+    with pytest.raises(P.PortaError):
+        ctx.mg_setup(2)
