@@ -36,6 +36,7 @@ UNIT = "updates/s"
 NX = NY = NZ = 64
 N_MU, N_CHI, N_NU = 5, 16, 21
 NRAY = 2 * N_MU * N_CHI
+ML_ZETA = 1e-5          # Zeeman splitting per gauss (Doppler widths) of the multilevel lines
 UPDATES = NX * NY * NZ * NRAY * N_NU
 WORKLOAD = ("polarized two-level atom (Jl=0->Ju=1, Hanle + weak-field Zeeman), random box 64x64x64, "
             "160 rays, 21 frequencies; one Jacobi iteration per step (FP32 sweeps, FP64 SEE)")
@@ -88,6 +89,8 @@ def args_parse():
     ap.add_argument("--ml-steps", type=int, default=3,
                     help="timed Jacobi iterations of the multilevel atom on the 128x128x96 grid (0 skips them)")
     ap.add_argument("--ml-mg-cycles", type=int, default=3, help="timed multigrid V-cycles of the multilevel atom")
+    ap.add_argument("--mlpol-steps", type=int, default=2,
+                    help="timed Jacobi iterations of the polarized multilevel atom on 128x128x96 (0 skips them)")
     ap.add_argument("--fill", default="", help="force the concurrent filler launch: cluster,nu_group,fraction")
     ap.add_argument("--adjoint-cluster", type=int, default=0, help="force the adjoint cluster size (skips its tuning)")
     ap.add_argument("--adjoint-nu-group", type=int, default=0, help="force the adjoint frequencies per pass")
@@ -533,6 +536,57 @@ def run_cuda(args):
                  "timing": "CUDA events around one graph replay per step, L2 flushed between steps"}
         mctx.close()
 
+    # polarized multilevel atom (all rho^K_Q of the five levels, 69 per voxel) on the
+    # same grid and quadratures: FP32 sweeps of the four lines (polarized formal
+    # solver), FP64 rate equations one warp per voxel
+    mlpol = None
+    if args.mlpol_steps > 0 and wl.name == "pol64":
+        nxm, nym, nzm = 128, 128, 96
+        atm_ml = synth.multilevel_box(nxm, nym, nzm, seed=rank)
+        atom = synth.multilevel_atom(seed=rank)
+        g = 2.0 * atom["J"] + 1
+        pops0 = g * np.exp(-atom["E"] / atm_ml["kT"][..., None])
+        pops0 /= pops0.sum(-1, keepdims=True)
+        # Zeeman splitting per gauss small enough for the first-order term at the
+        # field tails of this atmosphere (2 zeta |B|max (x_max + |v|max) < 1)
+        pctx = P.MlContext(atm_ml, atom, N_MU, N_CHI, 31, precision=P.PORTA_FP32, polarized=True, zeta=ML_ZETA)
+        pctx.set_stream(stream)
+        pctx.set_atmosphere(atm_ml)
+        pctx.set_pops(pops0)
+        with torch.cuda.stream(stream):
+            pctx.autotune()
+            pctx.set_pops(pops0)
+            pctx.run_iterations(1, residual=False)              # warm-up (graph capture)
+            barrier()
+            evp = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(args.mlpol_steps)]
+            for k in range(args.mlpol_steps):
+                flush.zero_()
+                evp[k][0].record(stream)
+                pctx.run_iterations(1, residual=False)
+                evp[k][1].record(stream)
+            barrier()
+            # the formal solutions and sums alone (eager), for the split
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            flush.zero_()
+            e0.record(stream)
+            pctx.ml_formal_solve(want=False)
+            e1.record(stream)
+            barrier()
+            pch = pctx.ml_iterate(1)
+        p_ms = sum(e[0].elapsed_time(e[1]) for e in evp) / args.mlpol_steps
+        fs_ms = e0.elapsed_time(e1)
+        nupd = len(atom["A"]) * 31 * NRAY * nxm * nym * nzm
+        mlpol = {"workload": f"{nxm}x{nym}x{nzm}, five-level atom (J = 0,1,2,1,2), all rho^K_Q (69 per voxel), "
+                             f"zeta = {ML_ZETA} per G, "
+                             f"four lines x 31 frequencies, {NRAY} rays (FP32 sweeps of the polarized formal solver, "
+                             "FP64 rate equations)",
+                 "ms_per_iteration": p_ms, "formal_solution_ms": fs_ms, "rate_equations_ms": p_ms - fs_ms,
+                 "updates_per_iteration": nupd, "updates_per_s": nupd / (p_ms * 1e-3),
+                 "steps": args.mlpol_steps, "max_change_after": pch, "launch": pctx.launch_info(),
+                 "timing": "CUDA events around one graph replay per step (L2 flushed); formal_solution_ms: one eager "
+                           "formal solution + sums; rate_equations_ms: the difference"}
+        pctx.close()
+
     # max over ranks
     if world > 1:
         step_ms, sweep_ms, e2e_s = max_over_ranks([step_ms, sweep_ms, e2e_s], dev)
@@ -571,6 +625,7 @@ def run_cuda(args):
         "multigrid": mgres,
         "iter_adjoint": iter_adj,
         "multilevel": mlres,
+        "multilevel_polarized": mlpol,
     }
     print(json.dumps(line))
     if world > 1:

@@ -462,7 +462,8 @@ int porta_ml_create(const porta_grid *g, const porta_ml_atom *a, const porta_qua
    chi = opacity scale (> 0), kT = temperature in eV (> 0), vel = vertical
    velocity in Doppler widths (the same for every line); bx, by, bz = magnetic
    field in gauss (required for the polarized atom, ignored (may be NULL)
-   otherwise). */
+   otherwise). The polarized atom's first-order Zeeman term must stay a
+   propagation matrix: PORTA_EINVAL unless 2 zeta max|B| (x_max + max|vel|) < 1. */
 int porta_ml_set_atmosphere(porta_ctx *c, const double *chi, const double *kT, const double *vel, const double *bx,
                             const double *by, const double *bz, int where);
 

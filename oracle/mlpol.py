@@ -36,13 +36,18 @@ populations only (K = 0) and relax every multipole of the level they leave;
 no elastic depolarization. Units as in oracle/ml.py (A in s^-1, intensities
 in units of 2 h nu^3 / c^2 of line 0, B_ul = A_ul / r^3, B_lu = (g_u/g_l) B_ul).
 
-Jacobi update: the rate equations with Lambda-bar* preconditioning of the
-population (K = 0, Kr = 0) terms exactly as the unpolarized multilevel update
-(J^0_0 -> J_eff = Jbar^0_0 - Lambda-bar* S_old and A -> A (1 - Lambda-bar*)
-in the spontaneous K = 0 -> 0 transfer and relaxation), every other term with
-the current Jbar; the row of rho^0_0 of level 0 replaced by the trace
-sum_J sqrt(2J+1) rho^0_0(J) = 1. Without polarization this is the update of
-oracle/ml.py; the fixed point is that of the rate equations.
+Jacobi update (a reading; the paper's Jacobian method is that of its
+multilevel 1D code): in two blocks. (1) The population equations (the K = 0
+rows, the row of level 0 replaced by the trace sum_J sqrt(2J+1) rho^0_0(J) =
+1) with Lambda-bar* preconditioning of the population (K = 0, Kr = 0) terms
+exactly as the unpolarized multilevel update (J^0_0 -> J_eff = Jbar^0_0 -
+Lambda-bar* S_old and A -> A (1 - Lambda-bar*) in the spontaneous K = 0 -> 0
+transfer and relaxation), the K > 0 multipoles at their previous values;
+(2) the K > 0 equations with the plain rates of Jbar and the new populations.
+Solving both blocks at once would pair the small J_eff of optically thick
+layers with the full anisotropy J^2_Q and can give negative populations.
+Without polarization this is the update of oracle/ml.py; the fixed point is
+that of the rate equations.
 
 Line transfer (a reading, the first cut of the polarized multilevel atom): the
 emissivity of a line carries the upper level's multipoles K = 0, 2 (the
@@ -367,9 +372,25 @@ def formal_solve_lines(atm, atom, tab, x, quad):
 
 
 def see_update(tab, kT, x, jbar, lstar, bvec):
-    """one Jacobi update; returns (new real unknowns, max relative change of the populations)"""
+    """one Jacobi update in two blocks; returns (new real unknowns, max relative
+    change of the populations). (1) the population equations (K = 0 rows,
+    preconditioned, the trace row for level 0) with the K > 0 multipoles at their
+    old values; (2) the K > 0 equations (plain rates) with the new populations."""
     S_old = ml.source_function(tab.atom, tab.populations(x))
-    new = tab.solve(tab.matrix(kT, jbar, bvec, lstar, S_old))
+    R = tab.real_system(tab.matrix(kT, jbar, bvec, lstar, S_old))
+    R[..., tab.row0, :] = tab.trace
+    b = np.zeros(R.shape[:-1])
+    b[..., tab.row0] = 1.0
+    rb = real_basis(tab.atom)
+    k0 = [k for k, (i, K, Q, part) in enumerate(rb) if K == 0]
+    kp = [k for k, (i, K, Q, part) in enumerate(rb) if K > 0]
+    r1 = b[..., k0] - np.einsum("...ij,...j->...i", R[..., k0, :][..., :, kp], x[..., kp])
+    y = np.linalg.solve(R[..., k0, :][..., :, k0], r1[..., None])[..., 0]
+    r2 = b[..., kp] - np.einsum("...ij,...j->...i", R[..., kp, :][..., :, k0], y)
+    z = np.linalg.solve(R[..., kp, :][..., :, kp], r2[..., None])[..., 0]
+    new = np.zeros_like(x)
+    new[..., k0] = y
+    new[..., kp] = z
     p0, p1 = tab.populations(x), tab.populations(new)
     return new, float(np.max(np.abs(p1 - p0) / np.abs(p0)))
 

@@ -2490,6 +2490,16 @@ int porta_ml_set_atmosphere(porta_ctx *c, const double *chi, const double *kT, c
                 std::memcpy(brep[d].data(), src[d], n1 * sizeof(double));
             for (int b = 1; b < m->mc.nline; ++b) std::memcpy(brep[d].data() + b * n1, brep[d].data(), n1 * sizeof(double));
         }
+        // the first-order (weak-field) Zeeman term eta_V = 2 zeta (B.Omega)(x - s) eta_I is a
+        // propagation matrix only while |eta_V| < eta_I over the frequency grid
+        double bmax = 0.0, vmax = 0.0;
+        for (long long v = 0; v < n1; ++v) {
+            bmax = std::max(bmax, std::sqrt(brep[0][v] * brep[0][v] + brep[1][v] * brep[1][v] + brep[2][v] * brep[2][v]));
+            vmax = std::max(vmax, std::fabs(hv[v]));
+        }
+        if (!(2.0 * c->zeta * bmax * (c->x_max + vmax) < 1.0))
+            return fail(c, PORTA_EINVAL, "ml_set_atmosphere: the weak-field Zeeman term 2 zeta |B| (x_max + |v|) reaches 1 "
+                                         "(|eta_V| > eta_I); lower zeta or the field");
     }
     porta_atmos at{ones.data(), half.data(), ones.data(), vrep.data(), m->pol ? brep[0].data() : nullptr,
                    m->pol ? brep[1].data() : nullptr, m->pol ? brep[2].data() : nullptr};

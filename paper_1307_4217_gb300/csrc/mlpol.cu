@@ -18,8 +18,10 @@
 // formal solver then solves every line); mlpol_see_kernel assembles the
 // 69 x 69 (in general nunk x nunk) real system of one voxel per warp in
 // shared memory, replaces the row of level 0's population by the trace
-// sum_J sqrt(2J+1) rho^0_0(J) = 1, and solves it in FP64 by Gaussian
-// elimination with partial pivoting.
+// sum_J sqrt(2J+1) rho^0_0(J) = 1, and solves it in FP64 in two blocks: the
+// population rows (preconditioned) with the K > 0 multipoles at their old
+// values, then the K > 0 rows (plain rates) with the new populations, by
+// Gaussian elimination with partial pivoting.
 #include <algorithm>
 #include <cmath>
 #include <complex>
@@ -433,8 +435,70 @@ __global__ void mlpol_see_kernel(const MlConst mc, MlPolDev T, long long nvox1, 
         for (int j = lane; j < N; j += 32) A[T.row0 * N1 + j] = T.trace[j];
         for (int r = lane; r < N; r += 32) A[r * N1 + N] = r == T.row0 ? 1.0 : 0.0;
         __syncwarp();
+        // block 1: the population rows (K = 0) with the K > 0 multipoles at their old values
+        const int L = mc.nlev;
+        auto is_k0 = [&](int c) {
+            for (int i = 0; i < L; ++i)
+                if (T.pop_idx[i] == c) return true;
+            return false;
+        };
+        for (int i = 0; i < L; ++i) {
+            const int r = T.pop_idx[i];
+            double acc = 0.0;
+            for (int c = lane; c < N; c += 32)
+                if (!is_k0(c)) acc += A[r * N1 + c] * xo[c];
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (lane == 0) A[r * N1 + N] -= acc;
+        }
+        __syncwarp();
+        int ok1 = 1;
+        if (lane == 0) {
+            double m[kMlMaxLevel][kMlMaxLevel + 1];
+            for (int i = 0; i < L; ++i) {
+                for (int j = 0; j < L; ++j) m[i][j] = A[T.pop_idx[i] * N1 + T.pop_idx[j]];
+                m[i][L] = A[T.pop_idx[i] * N1 + N];
+            }
+            for (int c = 0; c < L && ok1; ++c) {
+                int p = c;
+                for (int r = c + 1; r < L; ++r)
+                    if (fabs(m[r][c]) > fabs(m[p][c])) p = r;
+                if (!(fabs(m[p][c]) > 0.0)) { ok1 = 0; break; }
+                if (p != c)
+                    for (int j = 0; j <= L; ++j) {
+                        const double tmp = m[c][j]; m[c][j] = m[p][j]; m[p][j] = tmp;
+                    }
+                for (int r = c + 1; r < L; ++r) {
+                    const double f = m[r][c] / m[c][c];
+                    for (int j = c; j <= L; ++j) m[r][j] -= f * m[c][j];
+                }
+            }
+            if (ok1)
+                for (int i = L - 1; i >= 0; --i) {
+                    double acc = m[i][L];
+                    for (int j = i + 1; j < L; ++j) acc -= m[i][j] * xn[T.pop_idx[j]];
+                    xn[T.pop_idx[i]] = acc / m[i][i];
+                }
+        }
+        ok1 = __shfl_sync(0xffffffffu, ok1, 0);
+        __syncwarp();
+        // block 2: the K > 0 rows with the new populations; population rows become identities
+        for (int r = lane; r < N; r += 32) {
+            if (is_k0(r)) {
+                for (int c = 0; c < N; ++c) A[r * N1 + c] = c == r ? 1.0 : 0.0;
+                A[r * N1 + N] = ok1 ? xn[r] : 1.0;
+            } else {
+                double bsub = 0.0;
+                for (int i = 0; i < L; ++i) {
+                    const int c = T.pop_idx[i];
+                    bsub += A[r * N1 + c] * (ok1 ? xn[c] : 1.0);
+                    A[r * N1 + c] = 0.0;
+                }
+                A[r * N1 + N] -= bsub;
+            }
+        }
+        __syncwarp();
         // Gaussian elimination with partial pivoting on [A | b]
-        bool ok = true;
+        bool ok = ok1 != 0;
         for (int k = 0; k < N; ++k) {
             double bv = -1.0;
             int br = k;

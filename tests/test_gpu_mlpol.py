@@ -25,6 +25,8 @@ QUAD = (2, 4, 5)
 
 def _case(nx=6, ny=5, nz=8, seed=2, eps_range=(1e-3, 1e-1)):
     atm = synth.multilevel_box(nx, ny, nz, seed=seed, tau_top=1e-3, tau_bot=1e2)
+    # first-order Zeeman term within its validity at these fields (2 zeta |B| (x_max + |v|) < 1)
+    atm["zeta"] = 5e-5
     atom = synth.multilevel_atom(seed=seed + 1, eps_range=eps_range)
     tab = mlpol.Tables(atom)
     x = mlpol.lte_unknowns(tab, atm["kT"])
@@ -156,3 +158,7 @@ def test_invalid_inputs_are_rejected():
     ctx.set_unknowns(x)
     with pytest.raises(P.PortaError):
         ctx.mg_setup(2)
+    # a Zeeman splitting that makes |eta_V| > eta_I in the line wings is rejected
+    strong = P.MlContext(atm, atom, *QUAD, precision=P.PORTA_FP32, polarized=True, zeta=3.5e-4)
+    with pytest.raises(P.PortaError):
+        strong.set_atmosphere(atm)
