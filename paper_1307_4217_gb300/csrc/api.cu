@@ -2412,15 +2412,16 @@ int porta_ml_create(const porta_grid *g, const porta_ml_atom *a, const porta_qua
         m->tab = tab;
         m->nunk = tab.nunk;
         const size_t ni = tab.pop_idx.size() + tab.up2.size() + tab.cell_rc.size() + tab.cell_start.size() +
-                          tab.ent_src.size();
+                          tab.ent_src.size() + tab.act.size() + tab.inact.size() + tab.apop.size();
         const size_t nd = tab.w2.size() + tab.trace.size() + tab.ent_coef.size();
         const size_t ibytes = (ni * sizeof(int) + 7) / 8 * 8;
         std::vector<char> h(ibytes + nd * sizeof(double));
         int *ip = (int *)h.data();
         double *dp = (double *)(h.data() + ibytes);
-        size_t io[5], doff[3], k = 0, kd = 0;
-        const std::vector<int> *iv[5] = {&tab.pop_idx, &tab.up2, &tab.cell_rc, &tab.cell_start, &tab.ent_src};
-        for (int q2 = 0; q2 < 5; ++q2) {
+        size_t io[8], doff[3], k = 0, kd = 0;
+        const std::vector<int> *iv[8] = {&tab.pop_idx, &tab.up2, &tab.cell_rc, &tab.cell_start, &tab.ent_src,
+                                         &tab.act, &tab.inact, &tab.apop};
+        for (int q2 = 0; q2 < 8; ++q2) {
             io[q2] = k;
             for (int x : *iv[q2]) ip[k++] = x;
         }
@@ -2441,6 +2442,9 @@ int porta_ml_create(const porta_grid *g, const porta_ml_atom *a, const porta_qua
         d.row0 = tab.row0;
         d.src_j = tab.src_j; d.src_b = tab.src_b; d.src_clu = tab.src_clu; d.src_pop = tab.src_pop; d.src_spop = tab.src_spop;
         d.pop_idx = di + io[0]; d.up2 = di + io[1]; d.cell_rc = di + io[2]; d.cell_start = di + io[3]; d.ent_src = di + io[4];
+        d.act = di + io[5]; d.inact = di + io[6]; d.apop = di + io[7];
+        d.nact = tab.nact;
+        d.ninact = (int)tab.inact.size();
         d.w2 = dd + doff[0]; d.trace = dd + doff[1]; d.ent_coef = dd + doff[2];
     }
     if (e != cudaSuccess) {

@@ -16,8 +16,9 @@
 // and emission multipoles S^K_Q = S_line w^(K) conj(rho^K_Q / rho^0_0)(J_u)
 // (K = 0, 2) into the sweep arrays of the line's box (the polarized two-level
 // formal solver then solves every line); mlpol_see_kernel assembles the
-// 69 x 69 (in general nunk x nunk) real system of one voxel per warp in
-// shared memory, replaces the row of level 0's population by the trace
+// real system of one voxel per warp in shared memory over the even-K
+// multipoles (43 of the 69 for J = 0, 1, 2, 1, 2: without J^1_Q the odd-K
+// ones decouple with a zero solution), replaces the row of level 0's population by the trace
 // sum_J sqrt(2J+1) rho^0_0(J) = 1, and solves it in FP64 in two blocks: the
 // population rows (preconditioned) with the K > 0 multipoles at their old
 // values, then the K > 0 rows (plain rates) with the new populations, by
@@ -282,22 +283,39 @@ int mlpol_tables(const std::vector<double> &J, const std::vector<double> &E, con
             at(G[t.src_b + 1], a, b) += cplx(-wj * f, 0);     // i * i = -1
         }
     }
-    // real system rows: (complex row, part); trace row
+    // real system rows: (complex row, part); the even-K unknowns (compact numbering); trace row
     t.nunk = nr;
-    t.trace.assign(nr, 0.0);
+    std::vector<int> cmp(nr, -1);
+    t.act.clear();
+    t.inact.clear();
+    for (int k = 0; k < nr; ++k) {
+        if (rK[k] % 2 == 0) {
+            cmp[k] = (int)t.act.size();
+            t.act.push_back(k);
+        } else {
+            t.inact.push_back(k);
+        }
+    }
+    t.nact = (int)t.act.size();
+    t.trace.assign(t.nact, 0.0);
     t.pop_idx.assign(nlev, -1);
+    t.apop.assign(nlev, -1);
     t.row0 = -1;
     for (int k = 0; k < nr; ++k)
         if (rK[k] == 0) {
-            t.trace[k] = std::sqrt(g[rl[k]]);
+            t.trace[cmp[k]] = std::sqrt(g[rl[k]]);
             t.pop_idx[rl[k]] = k;
-            if (rl[k] == 0) t.row0 = k;
+            t.apop[rl[k]] = cmp[k];
+            if (rl[k] == 0) t.row0 = cmp[k];
         }
     // sparse cells of the real matrices R_s = select(G_s C)
     std::map<long long, std::vector<std::pair<int, double>>> cells;
+    const int na = t.nact;
+    double rate_scale = 0.0;
+    for (int li = 0; li < nline; ++li) rate_scale += A[li];
     for (int s = 0; s < t.nsrc; ++s)
         for (int row = 0; row < nr; ++row) {
-            if (row == t.row0) continue;
+            if (cmp[row] == t.row0) continue;
             const int ci = cidx[ckey(rl[row], rK[row], rQ[row])];
             for (int col = 0; col < nr; ++col) {
                 cplx y = 0.0;
@@ -306,13 +324,22 @@ int mlpol_tables(const std::vector<double> &J, const std::vector<double> &E, con
                     if (m != 0.0) y += m * Cm[(size_t)b * nr + col];
                 }
                 const double v = rp[row] == 0 ? y.real() : y.imag();
-                if (std::abs(v) > 0.0) cells[(long long)row * nr + col].emplace_back(s, v);
+                if (std::abs(v) == 0.0) continue;
+                // odd and even K couple only through J^1_Q, which is not carried (the 9j
+                // symbols with two equal rows vanish for odd K + K' + Kr): what is left is
+                // rounding of the Racah sums
+                if ((rK[row] + rK[col]) % 2) {
+                    if (std::abs(v) > 1e-12 * rate_scale) return -2;
+                    continue;
+                }
+                if (cmp[row] < 0) continue;          // odd-K block: homogeneous, solution zero
+                cells[(long long)cmp[row] * na + cmp[col]].emplace_back(s, v);
             }
         }
     t.cell_rc.clear(); t.cell_start.assign(1, 0); t.ent_src.clear(); t.ent_coef.clear();
     for (auto &c : cells) {
-        t.cell_rc.push_back((int)(c.first / nr));
-        t.cell_rc.push_back((int)(c.first % nr));
+        t.cell_rc.push_back((int)(c.first / na));
+        t.cell_rc.push_back((int)(c.first % na));
         for (auto &e : c.second) {
             t.ent_src.push_back(e.first);
             t.ent_coef.push_back(e.second);
@@ -394,7 +421,7 @@ __global__ void mlpol_see_kernel(const MlConst mc, MlPolDev T, long long nvox1, 
                                  unsigned long long *bad)
 {
     extern __shared__ double sm[];
-    const int N = T.nunk, N1 = N + 1;
+    const int N = T.nact, N1 = N + 1;          // even-K unknowns (compact numbering)
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int per = N * N1 + 2 * N + T.nsrc;
     double *A = sm + (size_t)wib * per;
@@ -404,7 +431,7 @@ __global__ void mlpol_see_kernel(const MlConst mc, MlPolDev T, long long nvox1, 
     const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
     double ch_max = 0.0;
     for (long long v = (long long)blockIdx.x * (blockDim.x >> 5) + wib; v < nvox1; v += nwarps) {
-        for (int k = lane; k < N; k += 32) xo[k] = x[v * N + k];
+        for (int k = lane; k < N; k += 32) xo[k] = x[v * T.nunk + T.act[k]];
         __syncwarp();
         // sources
         if (lane == 0) {
@@ -415,7 +442,7 @@ __global__ void mlpol_see_kernel(const MlConst mc, MlPolDev T, long long nvox1, 
         }
         for (int k = lane; k < mc.nline; k += 32) {
             const int u = mc.up[k], l = mc.lo[k];
-            const double nu = sqrt(mc.g[u]) * xo[T.pop_idx[u]], nl = sqrt(mc.g[l]) * xo[T.pop_idx[l]];
+            const double nu = sqrt(mc.g[u]) * xo[T.apop[u]], nl = sqrt(mc.g[l]) * xo[T.apop[l]];
             const double Sold = mc.r3[k] * nu / (nl * mc.g[u] / mc.g[l] - nu);
             const long long o = (long long)k * nvox1 + v;
             const double ls = lstar[o];
@@ -439,11 +466,11 @@ __global__ void mlpol_see_kernel(const MlConst mc, MlPolDev T, long long nvox1, 
         const int L = mc.nlev;
         auto is_k0 = [&](int c) {
             for (int i = 0; i < L; ++i)
-                if (T.pop_idx[i] == c) return true;
+                if (T.apop[i] == c) return true;
             return false;
         };
         for (int i = 0; i < L; ++i) {
-            const int r = T.pop_idx[i];
+            const int r = T.apop[i];
             double acc = 0.0;
             for (int c = lane; c < N; c += 32)
                 if (!is_k0(c)) acc += A[r * N1 + c] * xo[c];
@@ -455,8 +482,8 @@ __global__ void mlpol_see_kernel(const MlConst mc, MlPolDev T, long long nvox1, 
         if (lane == 0) {
             double m[kMlMaxLevel][kMlMaxLevel + 1];
             for (int i = 0; i < L; ++i) {
-                for (int j = 0; j < L; ++j) m[i][j] = A[T.pop_idx[i] * N1 + T.pop_idx[j]];
-                m[i][L] = A[T.pop_idx[i] * N1 + N];
+                for (int j = 0; j < L; ++j) m[i][j] = A[T.apop[i] * N1 + T.apop[j]];
+                m[i][L] = A[T.apop[i] * N1 + N];
             }
             for (int c = 0; c < L && ok1; ++c) {
                 int p = c;
@@ -475,8 +502,8 @@ __global__ void mlpol_see_kernel(const MlConst mc, MlPolDev T, long long nvox1, 
             if (ok1)
                 for (int i = L - 1; i >= 0; --i) {
                     double acc = m[i][L];
-                    for (int j = i + 1; j < L; ++j) acc -= m[i][j] * xn[T.pop_idx[j]];
-                    xn[T.pop_idx[i]] = acc / m[i][i];
+                    for (int j = i + 1; j < L; ++j) acc -= m[i][j] * xn[T.apop[j]];
+                    xn[T.apop[i]] = acc / m[i][i];
                 }
         }
         ok1 = __shfl_sync(0xffffffffu, ok1, 0);
@@ -489,7 +516,7 @@ __global__ void mlpol_see_kernel(const MlConst mc, MlPolDev T, long long nvox1, 
             } else {
                 double bsub = 0.0;
                 for (int i = 0; i < L; ++i) {
-                    const int c = T.pop_idx[i];
+                    const int c = T.apop[i];
                     bsub += A[r * N1 + c] * (ok1 ? xn[c] : 1.0);
                     A[r * N1 + c] = 0.0;
                 }
@@ -537,7 +564,7 @@ __global__ void mlpol_see_kernel(const MlConst mc, MlPolDev T, long long nvox1, 
             }
             int nb = 0;
             for (int i = lane; i < mc.nlev; i += 32) {
-                const double p0 = xo[T.pop_idx[i]], p1 = xn[T.pop_idx[i]];
+                const double p0 = xo[T.apop[i]], p1 = xn[T.apop[i]];
                 nb += !(p1 > 0.0 && p1 < 1e300);
                 ch = fmax(ch, fabs(p1 - p0) / fabs(p0));
             }
@@ -546,7 +573,8 @@ __global__ void mlpol_see_kernel(const MlConst mc, MlPolDev T, long long nvox1, 
             if (nb) {
                 ok = false;
             } else {
-                for (int k = lane; k < N; k += 32) x[v * N + k] = xn[k];
+                for (int k = lane; k < N; k += 32) x[v * T.nunk + T.act[k]] = xn[k];
+                for (int k = lane; k < T.ninact; k += 32) x[v * T.nunk + T.inact[k]] = 0.0;
             }
         }
         if (!ok) {
@@ -580,21 +608,23 @@ template cudaError_t run_mlpol_prepare<double>(const MlConst &, const MlPolDev &
 
 size_t mlpol_see_smem(const MlPolDev &T, int warps)
 {
-    return sizeof(double) * (size_t)warps * ((size_t)T.nunk * (T.nunk + 1) + 2 * T.nunk + T.nsrc);
+    return sizeof(double) * (size_t)warps * ((size_t)T.nact * (T.nact + 1) + 2 * T.nact + T.nsrc);
 }
 
 cudaError_t run_mlpol_see(const MlConst &mc, const MlPolDev &T, long long nvox1, const double *kT, const double *jkq,
                           const double *lstar, const double *bvec, double *x, unsigned long long *resid,
                           unsigned long long *bad, cudaStream_t st)
 {
-    const int warps = 2;
+    const int warps = 4;
     const size_t smem = mlpol_see_smem(T, warps);
     cudaError_t e = cudaFuncSetAttribute(mlpol_see_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const long long blocks = std::min<long long>((nvox1 + warps - 1) / warps, 2LL * nsm);
+    int per_sm = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mlpol_see_kernel, 32 * warps, smem);
+    const long long blocks = std::min<long long>((nvox1 + warps - 1) / warps, (long long)std::max(1, per_sm) * nsm);
     mlpol_see_kernel<<<(int)std::max<long long>(1, blocks), 32 * warps, smem, st>>>(mc, T, nvox1, kT, jkq, lstar, bvec,
                                                                                    x, resid, bad);
     return cudaGetLastError();

@@ -18,7 +18,12 @@ constexpr double kLarmorPerGauss = 1.3996e6;   // Larmor frequency per gauss (Hz
 // field (3), the collisional excitation rate per line, -Lambda* S_old and
 // -Lambda* per line
 struct MlPolTables {
-    int nline = 0, nunk = 0, nsrc = 0, row0 = -1;
+    // With J^1_Q = 0 the odd-K multipoles decouple from the even ones and their
+    // equations are homogeneous (zero solution): the system is assembled and
+    // solved over the nact even-K unknowns act[] only; cells, trace, row0 and apop
+    // are in that compact numbering, pop_idx and up2 in the full one.
+    int nline = 0, nunk = 0, nsrc = 0, row0 = -1, nact = 0;
+    std::vector<int> act, inact, apop;
     int src_j = 0, src_b = 0, src_clu = 0, src_pop = 0, src_spop = 0;
     std::vector<double> trace;       // trace row (sqrt(2J+1) on each rho^0_0)
     std::vector<int> pop_idx;        // per level: index of rho^0_0
@@ -30,9 +35,9 @@ struct MlPolTables {
 
 // device copy (pointers into one allocation)
 struct MlPolDev {
-    int nunk, nsrc, ncell, row0;
+    int nunk, nsrc, ncell, row0, nact, ninact;
     int src_j, src_b, src_clu, src_pop, src_spop;
-    const int *pop_idx, *up2, *cell_rc, *cell_start, *ent_src;
+    const int *pop_idx, *up2, *cell_rc, *cell_start, *ent_src, *act, *inact, *apop;
     const double *w2, *trace, *ent_coef;
 };
 
