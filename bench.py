@@ -89,6 +89,8 @@ def args_parse():
     ap.add_argument("--ml-steps", type=int, default=3,
                     help="timed Jacobi iterations of the multilevel atom on the 128x128x96 grid (0 skips them)")
     ap.add_argument("--ml-mg-cycles", type=int, default=3, help="timed multigrid V-cycles of the multilevel atom")
+    ap.add_argument("--ml-grid", default="128,128,96",
+                    help="grid of the multilevel workloads nx,ny,nz (a smaller one for profiling captures)")
     ap.add_argument("--mlpol-steps", type=int, default=2,
                     help="timed Jacobi iterations of the polarized multilevel atom on 128x128x96 (0 skips them)")
     ap.add_argument("--fill", default="", help="force the concurrent filler launch: cluster,nu_group,fraction")
@@ -485,7 +487,7 @@ def run_cuda(args):
     # of every line in one batched launch, sums, FP64 rate equations) per step
     mlres = None
     if args.ml_steps > 0 and wl.name == "pol64":
-        nxm, nym, nzm = 128, 128, 96
+        nxm, nym, nzm = (int(v) for v in args.ml_grid.split(","))
         atm_ml = synth.multilevel_box(nxm, nym, nzm, seed=rank)
         atom = synth.multilevel_atom(seed=rank)
         g = 2.0 * atom["J"] + 1
@@ -541,7 +543,7 @@ def run_cuda(args):
     # solver), FP64 rate equations one warp per voxel
     mlpol = None
     if args.mlpol_steps > 0 and wl.name == "pol64":
-        nxm, nym, nzm = 128, 128, 96
+        nxm, nym, nzm = (int(v) for v in args.ml_grid.split(","))
         atm_ml = synth.multilevel_box(nxm, nym, nzm, seed=rank)
         atom = synth.multilevel_atom(seed=rank)
         g = 2.0 * atom["J"] + 1
