@@ -89,6 +89,8 @@ def args_parse():
     ap.add_argument("--ml-steps", type=int, default=3,
                     help="timed Jacobi iterations of the multilevel atom on the 128x128x96 grid (0 skips them)")
     ap.add_argument("--ml-mg-cycles", type=int, default=3, help="timed multigrid V-cycles of the multilevel atom")
+    ap.add_argument("--mlpol-mg-cycles", type=int, default=1,
+                    help="timed multigrid V-cycles of the polarized multilevel atom")
     ap.add_argument("--ml-grid", default="128,128,96",
                     help="grid of the multilevel workloads nx,ny,nz (a smaller one for profiling captures)")
     ap.add_argument("--mlpol-steps", type=int, default=2,
@@ -575,6 +577,18 @@ def run_cuda(args):
             e1.record(stream)
             barrier()
             pch = pctx.ml_iterate(1)
+            # multigrid V-cycle of the polarized atom (3 levels) from LTE
+            pmg = []
+            if args.mlpol_mg_cycles > 0:
+                pctx.mg_setup(3)
+                pctx.set_pops(pops0)
+                for _ in range(args.mlpol_mg_cycles):
+                    e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e2.record(stream)
+                    chm = pctx.mg_vcycle(2, 4, 8)
+                    e3.record(stream)
+                    e3.synchronize()
+                    pmg.append((e2.elapsed_time(e3), chm))
         p_ms = sum(e[0].elapsed_time(e[1]) for e in evp) / args.mlpol_steps
         fs_ms = e0.elapsed_time(e1)
         nupd = len(atom["A"]) * 31 * NRAY * nxm * nym * nzm
@@ -585,6 +599,9 @@ def run_cuda(args):
                  "ms_per_iteration": p_ms, "formal_solution_ms": fs_ms, "rate_equations_ms": p_ms - fs_ms,
                  "updates_per_iteration": nupd, "updates_per_s": nupd / (p_ms * 1e-3),
                  "steps": args.mlpol_steps, "max_change_after": pch, "launch": pctx.launch_info(),
+                 "multigrid": {"levels": pctx.mg_levels(), "cycle": "2 pre + 4 post Jacobi, 8 on the coarsest, from LTE",
+                               "vcycle_ms": [round(t, 1) for t, _ in pmg],
+                               "vcycle_max_change": [c for _, c in pmg]} if pmg else None,
                  "timing": "CUDA events around one graph replay per step (L2 flushed); formal_solution_ms: one eager "
                            "formal solution + sums; rate_equations_ms: the difference"}
         pctx.close()

@@ -445,7 +445,9 @@ typedef struct {
    rho^0_0), w^(K) = (-1)^(1+Jl+Ju) sqrt(3(2Ju+1)) {1 1 K; Ju Ju Jl}) and the
    weak-field Zeeman term with 2 zeta B; dichroism from the lower levels'
    atomic polarization and the orientation (K = 1) terms are not included, so
-   J^1_Q = 0. The multigrid cycle is not available for it. */
+   J^1_Q = 0. porta_mg_setup / porta_mg_vcycle run the multigrid cycle with
+   the multipoles as unknowns (A(x) the plain rate equations with the trace
+   row; max_change over the populations). */
 
 /* Create a multilevel context on grid g (PORTA_EINVAL for an invalid atom or
    grid). The generic calls porta_formal_solve, porta_accumulate_jkq,

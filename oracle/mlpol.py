@@ -260,40 +260,56 @@ class Tables:
                 self.trace[k] = np.sqrt(self.g[i])
         self.row0 = rb.index((0, 0, 0, 0))
 
-    def collisions(self, kT):
-        """collisional matrix per voxel (kT.shape + (n, n)), complex"""
-        atom = self.atom
-        cul, clu = ml.collision_rates(atom, kT)
+    def _collision_units(self):
+        """the collisional matrix as C_ul terms (constant) plus unit C_lu terms per line"""
+        cul, _ = ml.collision_rates(self.atom, np.array(1.0))
         n = self.n
-        M = np.zeros(np.shape(kT) + (n, n), dtype=complex)
+        const = np.zeros((n, n), dtype=complex)
+        unit = np.zeros((len(self.lines), n, n), dtype=complex)
         for li, (u, l) in enumerate(self.lines):
             gu, gl = self.g[u], self.g[l]
             a0u, a0l = self.idx[(u, 0, 0)], self.idx[(l, 0, 0)]
-            # populations n = sqrt(2J+1) rho^0_0: dn_u = C_lu n_l - C_ul n_u
-            M[..., a0u, a0l] += clu[..., li] * np.sqrt(gl / gu)
-            M[..., a0l, a0u] += cul[li] * np.sqrt(gu / gl)
+            # populations n = sqrt(2J+1) rho^0_0: dn_u = C_lu n_l - C_ul n_u; every
+            # multipole of the level left relaxes
+            unit[li, a0u, a0l] += np.sqrt(gl / gu)
+            const[a0l, a0u] += cul[li] * np.sqrt(gu / gl)
             for a, (lev, K, Q) in enumerate(self.cb):
                 if lev == u:
-                    M[..., a, a] -= cul[li]
+                    const[a, a] -= cul[li]
                 elif lev == l:
-                    M[..., a, a] -= clu[..., li]
-        return M
+                    unit[li, a, a] -= 1.0
+        return const, unit
+
+    def collisions(self, kT):
+        """collisional matrix per voxel (kT.shape + (n, n)), complex"""
+        const, unit = self._collision_units()
+        _, clu = ml.collision_rates(self.atom, kT)
+        return const + np.einsum("...l,lij->...ij", clu + 0j, unit)
 
     def matrix(self, kT, jbar, bvec, lstar=None, S_old=None):
         """complex rate matrix per voxel; jbar [..., nline, 9] real layout, bvec [..., 3];
-        with lstar and S_old, the preconditioned population terms"""
-        jc = [jkq_complex(jbar[..., li, :]) for li in range(len(self.lines))]
-        M = self.collisions(kT) + self.Ms
-        for li in range(len(self.lines)):
-            for c, kq in enumerate(self.jk):
-                M = M + jc[li][kq][..., None, None] * self.Mr[li, c]
-            if lstar is not None:
-                # J^0_0 -> J_eff and A -> A (1 - Lambda*) in the population terms
-                d = (-lstar[..., li] * S_old[..., li])[..., None, None]
-                M = M + d * self.Mpop[li] - lstar[..., li][..., None, None] * self.Mspop[li]
-        for k in range(3):
-            M = M + np.asarray(bvec)[..., k][..., None, None] * self.Mh[k]
-        return M
+        with lstar and S_old, the preconditioned population terms. The sum of
+        source x matrix is one product over all sources."""
+        nl, n = len(self.lines), self.n
+        const, unit = self._collision_units()
+        _, clu = ml.collision_rates(self.atom, kT)
+        coefs, mats = [clu + 0j], [unit]
+        jc = [jkq_complex(jbar[..., li, :]) for li in range(nl)]
+        coefs.append(np.stack([jc[li][kq] for li in range(nl) for kq in self.jk], -1))
+        mats.append(self.Mr.reshape(nl * len(self.jk), n, n))
+        if lstar is not None:
+            # J^0_0 -> J_eff and A -> A (1 - Lambda*) in the population terms
+            coefs.append(-lstar * S_old + 0j)
+            mats.append(self.Mpop)
+            coefs.append(-lstar + 0j)
+            mats.append(self.Mspop)
+        coefs.append(np.asarray(bvec) + 0j)
+        mats.append(self.Mh)
+        cf = np.concatenate(coefs, -1)
+        mt = np.concatenate(mats, 0)
+        shape = cf.shape[:-1]
+        M = (cf.reshape(-1, cf.shape[-1]) @ mt.reshape(mt.shape[0], n * n)).reshape(shape + (n, n))
+        return M + const + self.Ms
 
     def real_system(self, Mc):
         """real matrix of the equations (rows: Q = 0 real parts; Q > 0 real and imaginary parts)"""
@@ -371,16 +387,21 @@ def formal_solve_lines(atm, atom, tab, x, quad):
     return jbar, lstar
 
 
-def see_update(tab, kT, x, jbar, lstar, bvec):
+def see_update(tab, kT, x, jbar, lstar, bvec, src=None):
     """one Jacobi update in two blocks; returns (new real unknowns, max relative
     change of the populations). (1) the population equations (K = 0 rows,
     preconditioned, the trace row for level 0) with the K > 0 multipoles at their
-    old values; (2) the K > 0 equations (plain rates) with the new populations."""
+    old values; (2) the K > 0 equations (plain rates) with the new populations.
+    src (per voxel, nunk) replaces the right-hand side e_row0 (coarse-grid
+    equations of the multigrid cycle)."""
     S_old = ml.source_function(tab.atom, tab.populations(x))
     R = tab.real_system(tab.matrix(kT, jbar, bvec, lstar, S_old))
     R[..., tab.row0, :] = tab.trace
-    b = np.zeros(R.shape[:-1])
-    b[..., tab.row0] = 1.0
+    if src is None:
+        b = np.zeros(R.shape[:-1])
+        b[..., tab.row0] = 1.0
+    else:
+        b = np.array(src, dtype=np.float64)
     rb = real_basis(tab.atom)
     k0 = [k for k, (i, K, Q, part) in enumerate(rb) if K == 0]
     kp = [k for k, (i, K, Q, part) in enumerate(rb) if K > 0]
@@ -412,3 +433,53 @@ def iterate(atm, atom, tab, x, quad, n):
         jbar, lstar = formal_solve_lines(atm, atom, tab, x, quad)
         x, change = see_update(tab, atm["kT"], x, jbar, lstar, bvec)
     return x, change
+
+
+# ---------------------------------------------------------------- multigrid (Sec. 6)
+# The cycle of oracle/ml.py with the real multipoles as the unknowns: A(x)_row0 =
+# sum_J sqrt(2J+1) rho^0_0(J), the other rows the plain rate equations of the
+# formal solution's Jbar; f = e_row0 on the finest grid.
+
+def rate_operator(tab, kT, x, jbar, bvec):
+    R = tab.real_system(tab.matrix(kT, jbar, bvec))
+    R[..., tab.row0, :] = tab.trace
+    return np.einsum("...ij,...j->...i", R, x)
+
+
+def apply_A(atm, atom, tab, x, quad):
+    jbar, _ = formal_solve_lines(atm, atom, tab, x, quad)
+    return rate_operator(tab, atm["kT"], x, jbar, np.stack([atm["bx"], atm["by"], atm["bz"]], -1))
+
+
+def f_fine(tab, shape):
+    f = np.zeros(tuple(shape) + (len(tab.rows),))
+    f[..., tab.row0] = 1.0
+    return f
+
+
+def jacobi(atm, atom, tab, x, quad, src, n):
+    bvec = np.stack([atm["bx"], atm["by"], atm["bz"]], -1)
+    change = None
+    for _ in range(n):
+        jbar, lstar = formal_solve_lines(atm, atom, tab, x, quad)
+        x, change = see_update(tab, atm["kT"], x, jbar, lstar, bvec, src)
+    return x, change
+
+
+def vcycle(levels, atom, tab, quad, x, src=None, l=0, npre=2, npost=4, ncoarse=8):
+    """One V-cycle from level l (levels from ml.hierarchy) down to the coarsest."""
+    from .mg import prolong, restrict
+    lev = levels[l]
+    f = f_fine(tab, lev.shape) if src is None else src
+    if l == len(levels) - 1:
+        x, _ = jacobi(lev.atm, atom, tab, x, quad, f, ncoarse)
+        return x
+    x, _ = jacobi(lev.atm, atom, tab, x, quad, f, npre)
+    r = f - apply_A(lev.atm, atom, tab, x, quad)
+    coarse = levels[l + 1]
+    x_c0 = restrict(lev, x)
+    f_c = apply_A(coarse.atm, atom, tab, x_c0, quad) + restrict(lev, r)
+    x_c = vcycle(levels, atom, tab, quad, x_c0, f_c, l + 1, npre, npost, ncoarse)
+    x = x + prolong(lev, x_c - x_c0)
+    x, _ = jacobi(lev.atm, atom, tab, x, quad, f, npost)
+    return x

@@ -1217,9 +1217,9 @@ cudaError_t ml_prepare(porta_ctx *c);
 
 // the unknowns of a level: rho [v][nl] of the two-level atom, or the
 // populations [v][nlevel] of the multilevel atom
-double *mg_unk(porta_ctx *L) { return L->ml ? L->ml->d_pops : L->d_rho; }
+double *mg_unk(porta_ctx *L) { return L->ml ? (L->ml->pol ? L->ml->d_x : L->ml->d_pops) : L->d_rho; }
 long long mg_nunk(const porta_ctx *L) { return L->ml ? L->ml->nvox1 : L->nvox; }
-int mg_ncomp(const porta_ctx *L) { return L->ml ? L->ml->mc.nlev : L->nl; }
+int mg_ncomp(const porta_ctx *L) { return L->ml ? L->ml->nunk : L->nl; }
 
 cudaError_t mg_rho_changed(porta_ctx *L)
 {
@@ -1231,6 +1231,9 @@ cudaError_t mg_rho_changed(porta_ctx *L)
 // out = alpha A(unknowns) + add + with_f f_fine, with J^K_Q of the last formal solution
 cudaError_t mg_apply(porta_ctx *L, double alpha, const double *add, int with_f, double *out)
 {
+    if (L->ml && L->ml->pol)
+        return run_mlpol_apply(L->ml->mc, L->ml->dev, L->ml->nvox1, L->ml->d_kT, L->d_jkq, L->d_b, L->ml->d_x, alpha, add,
+                               with_f, out, L->stream);
     if (L->ml)
         return run_ml_apply(L->ml->mc, L->ml->nvox1, L->ml->d_kT, L->d_jkq, L->ml->d_pops, alpha, add, with_f, out,
                             L->stream);
@@ -1246,8 +1249,10 @@ int mg_jacobi(porta_ctx *L, const double *src, int n)
         if (rc) return rc;
         cudaError_t e;
         if (L->ml) {
-            e = run_ml_see(L->ml->mc, L->ml->nvox1, L->ml->d_kT, L->d_jkq, L->d_lstar, L->ml->d_pops, L->d_resid,
-                           L->ml->d_bad, L->stream, src);
+            e = L->ml->pol ? run_mlpol_see(L->ml->mc, L->ml->dev, L->ml->nvox1, L->ml->d_kT, L->d_jkq, L->d_lstar, L->d_b,
+                                           L->ml->d_x, L->d_resid, L->ml->d_bad, L->stream, src)
+                           : run_ml_see(L->ml->mc, L->ml->nvox1, L->ml->d_kT, L->d_jkq, L->d_lstar, L->ml->d_pops, L->d_resid,
+                                        L->ml->d_bad, L->stream, src);
             if (e == cudaSuccess) e = ml_prepare(L);
         } else {
             e = L->precision == PORTA_FP32
@@ -2137,7 +2142,6 @@ int porta_mg_setup(porta_ctx *c, int nlevels)
     if (!c) return PORTA_EINVAL;
     if (c->nbox != 1 && !c->ml) return fail(c, PORTA_EINVAL, "mg_setup: single-box contexts only");
     if (c->ml && !c->ml->have_atm) return fail(c, PORTA_ESTATE, "mg_setup: atmosphere not set");
-    if (c->ml && c->ml->pol) return fail(c, PORTA_EINVAL, "mg_setup: not available for the polarized multilevel atom");
     if (nlevels < 2 || nlevels > 8) return fail(c, PORTA_EINVAL, "mg_setup: nlevels in 2..8");
     if (!c->have_atm) return fail(c, PORTA_ESTATE, "mg_setup: atmosphere not set");
     {
@@ -2183,7 +2187,7 @@ int porta_mg_setup(porta_ctx *c, int nlevels)
             // scale, temperature and velocity at the coincident nodes
             const MlState *m = c->ml;
             porta_ml_atom ma{m->mc.nlev, m->mc.nline, m->J.data(), m->E.data(), m->up.data(), m->lo.data(),
-                             m->A.data(), m->eps.data()};
+                             m->A.data(), m->eps.data(), m->pol ? 1 : 0, c->zeta};
             if ((rc = porta_ml_create(&g, &ma, &q, &o, &L))) {
                 rc = fail(c, rc, "mg_setup: coarse level creation");
                 break;
@@ -2193,10 +2197,11 @@ int porta_mg_setup(porta_ctx *c, int nlevels)
             const MlState *mf = F->ml;
             const long long ncv = L->ml->nvox1;
             double *tmp = nullptr;
-            cudaError_t e = dalloc(&tmp, 3 * (size_t)ncv);
-            // F->d_cv64 + F->nvox: FP64 velocity of the line boxes (box 0 first)
-            const double *srcs[3] = {mf->d_chis, mf->d_kT, F->d_cv64 + F->nvox};
-            for (int f = 0; f < 3 && e == cudaSuccess; ++f)
+            cudaError_t e = dalloc(&tmp, 6 * (size_t)ncv);
+            // F->d_cv64 + F->nvox: FP64 velocity of the line boxes (box 0 first); F->d_b the field
+            const double *srcs[6] = {mf->d_chis, mf->d_kT, F->d_cv64 + F->nvox, F->d_b, F->d_b + F->nvox,
+                                     F->d_b + 2 * F->nvox};
+            for (int f = 0; f < (m->pol ? 6 : 3) && e == cudaSuccess; ++f)
                 e = run_inject(L->nx, L->ny, L->nz, F->nx, F->ny, srcs[f], tmp + f * ncv, c->stream);
             if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
             if (e != cudaSuccess) {
@@ -2204,7 +2209,8 @@ int porta_mg_setup(porta_ctx *c, int nlevels)
                 rc = fail(c, PORTA_ECUDA, std::string("mg_setup: ") + cudaGetErrorString(e));
                 break;
             }
-            rc = porta_ml_set_atmosphere(L, tmp, tmp + ncv, tmp + 2 * ncv, nullptr, nullptr, nullptr, PORTA_DEVICE);
+            rc = porta_ml_set_atmosphere(L, tmp, tmp + ncv, tmp + 2 * ncv, m->pol ? tmp + 3 * ncv : nullptr,
+                                         m->pol ? tmp + 4 * ncv : nullptr, m->pol ? tmp + 5 * ncv : nullptr, PORTA_DEVICE);
             cudaFree(tmp);
             if (rc) {
                 rc = fail(c, rc, std::string("mg_setup: coarse atmosphere: ") + L->err);
@@ -2320,7 +2326,9 @@ int porta_mg_vcycle(porta_ctx *c, int npre, int npost, int ncoarse, double *max_
     if (rc) return rc;
     c->have_fs = c->have_jkq = false;
     CK(cudaMemsetAsync(c->d_resid, 0, sizeof(unsigned long long), c->stream));
-    cudaError_t e = run_change(nu, nc, c->mg_prev, mg_unk(c), c->d_resid, c->stream, c->ml ? 1 : 0);
+    cudaError_t e = c->ml && c->ml->pol
+                        ? run_mlpol_change(c->ml->mc, c->ml->dev, nu, c->mg_prev, mg_unk(c), c->d_resid, c->stream)
+                        : run_change(nu, nc, c->mg_prev, mg_unk(c), c->d_resid, c->stream, c->ml ? 1 : 0);
     if (e != cudaSuccess) return fail(c, PORTA_ECUDA, std::string("mg_vcycle: ") + cudaGetErrorString(e));
     if (max_change) {
         unsigned long long bits = 0;

@@ -9,7 +9,7 @@
 // prolongation over the 3 x 3 x (up to 4) fine nodes around a coarse node.
 // The z weights come as tables built on the host: per fine plane (k0, w0, k1,
 // w1) for the prolongation, per coarse plane up to 4 (fine plane, weight)
-// pairs for the restriction. Vectors of unknowns are [voxel][nl] (nl <= 8), FP64.
+// pairs for the restriction. Vectors of unknowns are [voxel][nl], FP64.
 #include "mg_kernels.cuh"
 
 namespace porta {
@@ -37,28 +37,32 @@ __global__ void restrict_kernel(int nxc, int nyc, long long nvc, int nxf, int ny
     const int I = (int)(v % nxc);
     const int J = (int)((v / nxc) % nyc);
     const int K = (int)(v / ((long long)nxc * nyc));
-    double acc[kMgMaxComp] = {};
     double den = 0.0;
-    for (int e = 0; e < 4; ++e) {
-        const double w = zr[8 * K + 2 * e + 1];
-        if (w == 0.0) continue;
-        const long long kf = (long long)zr[8 * K + 2 * e];
-        den += w;
-        for (int dy = -1; dy <= 1; ++dy) {
-            const double wy = dy == 0 ? 1.0 : 0.5;
-            const int jf = (2 * J + dy + nyf) % nyf;
-            for (int dx = -1; dx <= 1; ++dx) {
-                const double wx = dx == 0 ? 1.0 : 0.5;
-                const int xf = (2 * I + dx + nxf) % nxf;
-                const double *p = fine + ((kf * nyf + jf) * nxf + xf) * nl;
-                const double wt = w * wy * wx;
-                for (int c = 0; c < nl; ++c) acc[c] += wt * p[c];
-            }
-        }
-    }
+    for (int e = 0; e < 4; ++e) den += zr[8 * K + 2 * e + 1];
     // the horizontal weights sum to 2 per axis
     const double inv = 1.0 / (4.0 * den);
-    for (int c = 0; c < nl; ++c) coarse[v * nl + c] = acc[c] * inv;
+    // components in chunks of kMgMaxComp
+    for (int c0 = 0; c0 < nl; c0 += kMgMaxComp) {
+        const int nc = min(kMgMaxComp, nl - c0);
+        double acc[kMgMaxComp] = {};
+        for (int e = 0; e < 4; ++e) {
+            const double w = zr[8 * K + 2 * e + 1];
+            if (w == 0.0) continue;
+            const long long kf = (long long)zr[8 * K + 2 * e];
+            for (int dy = -1; dy <= 1; ++dy) {
+                const double wy = dy == 0 ? 1.0 : 0.5;
+                const int jf = (2 * J + dy + nyf) % nyf;
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const double wx = dx == 0 ? 1.0 : 0.5;
+                    const int xf = (2 * I + dx + nxf) % nxf;
+                    const double *p = fine + ((kf * nyf + jf) * nxf + xf) * nl + c0;
+                    const double wt = w * wy * wx;
+                    for (int c = 0; c < nc; ++c) acc[c] += wt * p[c];
+                }
+            }
+        }
+        for (int c = 0; c < nc; ++c) coarse[v * nl + c0 + c] = acc[c] * inv;
+    }
 }
 
 __global__ void prolong_add_kernel(int nxf, int nyf, long long nvf, int nxc, int nyc, int nl, const double *zp,
@@ -91,20 +95,23 @@ __global__ void prolong_add_kernel(int nxf, int nyf, long long nvf, int nxc, int
     }
     const long long kz[2] = {(long long)zp[4 * k], (long long)zp[4 * k + 2]};
     const double wz[2] = {zp[4 * k + 1], zp[4 * k + 3]};
-    double d[kMgMaxComp] = {};
-    for (int a = 0; a < 2; ++a) {
-        if (wz[a] == 0.0) continue;
-        for (int b = 0; b < 2; ++b) {
-            if (wy[b] == 0.0) continue;
-            for (int cx = 0; cx < 2; ++cx) {
-                if (wx[cx] == 0.0) continue;
-                const long long vc = (kz[a] * nyc + yj[b]) * nxc + xi[cx];
-                const double w = wz[a] * wy[b] * wx[cx];
-                for (int c = 0; c < nl; ++c) d[c] += w * (cnew[vc * nl + c] - cold[vc * nl + c]);
+    for (int c0 = 0; c0 < nl; c0 += kMgMaxComp) {
+        const int nc = min(kMgMaxComp, nl - c0);
+        double d[kMgMaxComp] = {};
+        for (int a = 0; a < 2; ++a) {
+            if (wz[a] == 0.0) continue;
+            for (int b = 0; b < 2; ++b) {
+                if (wy[b] == 0.0) continue;
+                for (int cx = 0; cx < 2; ++cx) {
+                    if (wx[cx] == 0.0) continue;
+                    const long long vc = (kz[a] * nyc + yj[b]) * nxc + xi[cx];
+                    const double w = wz[a] * wy[b] * wx[cx];
+                    for (int c = 0; c < nc; ++c) d[c] += w * (cnew[vc * nl + c0 + c] - cold[vc * nl + c0 + c]);
+                }
             }
         }
+        for (int c = 0; c < nc; ++c) fine[v * nl + c0 + c] += d[c];
     }
-    for (int c = 0; c < nl; ++c) fine[v * nl + c] += d[c];
 }
 
 // max over voxels of |dS00| / |S00_old| and |S2/S00 (new) - S2/S00 (old)|

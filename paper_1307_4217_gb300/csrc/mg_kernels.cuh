@@ -4,7 +4,7 @@
 
 namespace porta {
 
-constexpr int kMgMaxComp = 8;   // unknowns per voxel handled by the transfer kernels
+constexpr int kMgMaxComp = 8;   // unknowns per voxel the transfer kernels accumulate at a time
 
 // coarse = fine at the coincident nodes, one per-voxel array
 cudaError_t run_inject(int nxc, int nyc, int nzc, int nxf, int nyf, const double *fine, double *coarse, cudaStream_t st);

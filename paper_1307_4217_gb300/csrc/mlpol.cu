@@ -415,10 +415,85 @@ __global__ void mlpol_prepare_kernel(const MlConst mc, MlPolDev T, long long nvo
     if (nbad) atomicAdd(bad, (unsigned long long)nbad);
 }
 
-// one warp per voxel; shared memory per warp: A[nunk][nunk + 1], x_old, x_new, sources
+// the real system of voxel v over the even-K unknowns into A [N][N + 1] (row of
+// level 0's population = the trace), sources into s; xo holds the old unknowns;
+// lstar null: the plain rates (no preconditioning)
+__device__ void mlpol_assemble(const MlConst &mc, const MlPolDev &T, long long nvox1, long long v, const double *kT,
+                               const double *jkq, const double *lstar, const double *bvec, const double *xo,
+                               double *A, double *s, int lane)
+{
+    const int N = T.nact, N1 = N + 1;
+    if (lane == 0) {
+        s[0] = 1.0;
+        s[T.src_b] = bvec[v];
+        s[T.src_b + 1] = bvec[nvox1 * mc.nline + v];
+        s[T.src_b + 2] = bvec[2 * nvox1 * mc.nline + v];
+    }
+    for (int k = lane; k < mc.nline; k += 32) {
+        const int u = mc.up[k], l = mc.lo[k];
+        const long long o = (long long)k * nvox1 + v;
+        for (int c = 0; c < 6; ++c) s[T.src_j + 6 * k + c] = jkq[o * 6 + c];
+        s[T.src_clu + k] = mc.g[u] / mc.g[l] * exp(-mc.dE[k] / kT[v]) * mc.Cul[k];
+        if (lstar) {
+            const double nu = sqrt(mc.g[u]) * xo[T.apop[u]], nl = sqrt(mc.g[l]) * xo[T.apop[l]];
+            const double Sold = mc.r3[k] * nu / (nl * mc.g[u] / mc.g[l] - nu);
+            const double ls = lstar[o];
+            s[T.src_pop + k] = -ls * Sold;
+            s[T.src_spop + k] = -ls;
+        } else {
+            s[T.src_pop + k] = 0.0;
+            s[T.src_spop + k] = 0.0;
+        }
+    }
+    for (int e = lane; e < N * N1; e += 32) A[e] = 0.0;
+    __syncwarp();
+    for (int c = lane; c < T.ncell; c += 32) {
+        double val = 0.0;
+        for (int e = T.cell_start[c]; e < T.cell_start[c + 1]; ++e) val += T.ent_coef[e] * s[T.ent_src[e]];
+        A[T.cell_rc[2 * c] * N1 + T.cell_rc[2 * c + 1]] = val;
+    }
+    __syncwarp();
+    for (int j = lane; j < N; j += 32) A[T.row0 * N1 + j] = T.trace[j];
+    __syncwarp();
+}
+
+// out = alpha A(x) + add + with_f e_row0 (full layout): A(x) the plain rate operator
+// with the trace row; one warp per voxel, shared memory as mlpol_see_kernel
+__global__ void mlpol_apply_kernel(const MlConst mc, MlPolDev T, long long nvox1, const double *kT, const double *jkq,
+                                   const double *bvec, const double *x, double alpha, const double *add, int with_f,
+                                   double *out)
+{
+    extern __shared__ double sm[];
+    const int N = T.nact, N1 = N + 1;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int per = N * N1 + 2 * N + T.nsrc;
+    double *A = sm + (size_t)wib * per;
+    double *xo = A + N * N1;
+    double *s = xo + 2 * N;
+    const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
+    const int row0full = T.act[T.row0];
+    for (long long v = (long long)blockIdx.x * (blockDim.x >> 5) + wib; v < nvox1; v += nwarps) {
+        for (int k = lane; k < N; k += 32) xo[k] = x[v * T.nunk + T.act[k]];
+        __syncwarp();
+        mlpol_assemble(mc, T, nvox1, v, kT, jkq, nullptr, bvec, xo, A, s, lane);
+        for (int r = lane; r < N; r += 32) {
+            double y = 0.0;
+            for (int c = 0; c < N; ++c) y += A[r * N1 + c] * xo[c];
+            const long long o = v * T.nunk + T.act[r];
+            out[o] = alpha * y + (add ? add[o] : 0.0) + (with_f && T.act[r] == row0full ? 1.0 : 0.0);
+        }
+        for (int k = lane; k < T.ninact; k += 32) {
+            const long long o = v * T.nunk + T.inact[k];
+            out[o] = add ? add[o] : 0.0;
+        }
+        __syncwarp();
+    }
+}
+
+// one warp per voxel; shared memory per warp: A[nact][nact + 1], x_old, x_new, sources
 __global__ void mlpol_see_kernel(const MlConst mc, MlPolDev T, long long nvox1, const double *kT, const double *jkq,
-                                 const double *lstar, const double *bvec, double *x, unsigned long long *resid,
-                                 unsigned long long *bad)
+                                 const double *lstar, const double *bvec, const double *src, double *x,
+                                 unsigned long long *resid, unsigned long long *bad)
 {
     extern __shared__ double sm[];
     const int N = T.nact, N1 = N + 1;          // even-K unknowns (compact numbering)
@@ -433,34 +508,9 @@ __global__ void mlpol_see_kernel(const MlConst mc, MlPolDev T, long long nvox1, 
     for (long long v = (long long)blockIdx.x * (blockDim.x >> 5) + wib; v < nvox1; v += nwarps) {
         for (int k = lane; k < N; k += 32) xo[k] = x[v * T.nunk + T.act[k]];
         __syncwarp();
-        // sources
-        if (lane == 0) {
-            s[0] = 1.0;
-            s[T.src_b] = bvec[v];
-            s[T.src_b + 1] = bvec[nvox1 * mc.nline + v];
-            s[T.src_b + 2] = bvec[2 * nvox1 * mc.nline + v];
-        }
-        for (int k = lane; k < mc.nline; k += 32) {
-            const int u = mc.up[k], l = mc.lo[k];
-            const double nu = sqrt(mc.g[u]) * xo[T.apop[u]], nl = sqrt(mc.g[l]) * xo[T.apop[l]];
-            const double Sold = mc.r3[k] * nu / (nl * mc.g[u] / mc.g[l] - nu);
-            const long long o = (long long)k * nvox1 + v;
-            const double ls = lstar[o];
-            for (int c = 0; c < 6; ++c) s[T.src_j + 6 * k + c] = jkq[o * 6 + c];
-            s[T.src_clu + k] = mc.g[u] / mc.g[l] * exp(-mc.dE[k] / kT[v]) * mc.Cul[k];
-            s[T.src_pop + k] = -ls * Sold;
-            s[T.src_spop + k] = -ls;
-        }
-        for (int e = lane; e < N * N1; e += 32) A[e] = 0.0;
-        __syncwarp();
-        for (int c = lane; c < T.ncell; c += 32) {
-            double val = 0.0;
-            for (int e = T.cell_start[c]; e < T.cell_start[c + 1]; ++e) val += T.ent_coef[e] * s[T.ent_src[e]];
-            A[T.cell_rc[2 * c] * N1 + T.cell_rc[2 * c + 1]] = val;
-        }
-        __syncwarp();
-        for (int j = lane; j < N; j += 32) A[T.row0 * N1 + j] = T.trace[j];
-        for (int r = lane; r < N; r += 32) A[r * N1 + N] = r == T.row0 ? 1.0 : 0.0;
+        mlpol_assemble(mc, T, nvox1, v, kT, jkq, lstar, bvec, xo, A, s, lane);
+        // right-hand side: (1, 0, ...) on the trace row, or the coarse-grid source
+        for (int r = lane; r < N; r += 32) A[r * N1 + N] = src ? src[v * T.nunk + T.act[r]] : (r == T.row0 ? 1.0 : 0.0);
         __syncwarp();
         // block 1: the population rows (K = 0) with the K > 0 multipoles at their old values
         const int L = mc.nlev;
@@ -611,22 +661,75 @@ size_t mlpol_see_smem(const MlPolDev &T, int warps)
     return sizeof(double) * (size_t)warps * ((size_t)T.nact * (T.nact + 1) + 2 * T.nact + T.nsrc);
 }
 
-cudaError_t run_mlpol_see(const MlConst &mc, const MlPolDev &T, long long nvox1, const double *kT, const double *jkq,
-                          const double *lstar, const double *bvec, double *x, unsigned long long *resid,
-                          unsigned long long *bad, cudaStream_t st)
+// max relative change of the populations between two vectors of unknowns
+__global__ void mlpol_change_kernel(const MlConst mc, MlPolDev T, long long nvox1, const double *old, const double *cur,
+                                    unsigned long long *resid)
 {
-    const int warps = 4;
-    const size_t smem = mlpol_see_smem(T, warps);
-    cudaError_t e = cudaFuncSetAttribute(mlpol_see_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    double ch = 0.0;
+    if (v < nvox1)
+        for (int i = 0; i < mc.nlev; ++i) {
+            const long long o = v * T.nunk + T.pop_idx[i];
+            ch = fmax(ch, fabs(cur[o] - old[o]) / fabs(old[o]));
+        }
+    if (!(ch <= 1e300)) ch = 1e300;
+    for (int s = 16; s > 0; s >>= 1) ch = fmax(ch, __shfl_xor_sync(0xffffffffu, ch, s));
+    __shared__ double red[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) red[wid] = ch;
+    __syncthreads();
+    if (wid == 0) {
+        ch = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
+        for (int s = 16; s > 0; s >>= 1) ch = fmax(ch, __shfl_xor_sync(0xffffffffu, ch, s));
+        if (lane == 0) atomicMax(resid, (unsigned long long)__double_as_longlong(ch));
+    }
+}
+
+cudaError_t run_mlpol_change(const MlConst &mc, const MlPolDev &T, long long nvox1, const double *old, const double *cur,
+                             unsigned long long *resid, cudaStream_t st)
+{
+    mlpol_change_kernel<<<nblk(nvox1, 256), 256, 0, st>>>(mc, T, nvox1, old, cur, resid);
+    return cudaGetLastError();
+}
+
+// persistent launch shape of the warp-per-voxel kernels
+template <typename K>
+static cudaError_t warp_launch_shape(K kernel, const MlPolDev &T, long long nvox1, int warps, size_t &smem, int &blocks)
+{
+    smem = mlpol_see_smem(T, warps);
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    int dev = 0, nsm = 0;
+    int dev = 0, nsm = 0, per_sm = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    int per_sm = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mlpol_see_kernel, 32 * warps, smem);
-    const long long blocks = std::min<long long>((nvox1 + warps - 1) / warps, (long long)std::max(1, per_sm) * nsm);
-    mlpol_see_kernel<<<(int)std::max<long long>(1, blocks), 32 * warps, smem, st>>>(mc, T, nvox1, kT, jkq, lstar, bvec,
-                                                                                   x, resid, bad);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 32 * warps, smem);
+    blocks = (int)std::max<long long>(1, std::min<long long>((nvox1 + warps - 1) / warps, (long long)std::max(1, per_sm) * nsm));
+    return cudaSuccess;
+}
+
+cudaError_t run_mlpol_see(const MlConst &mc, const MlPolDev &T, long long nvox1, const double *kT, const double *jkq,
+                          const double *lstar, const double *bvec, double *x, unsigned long long *resid,
+                          unsigned long long *bad, cudaStream_t st, const double *src)
+{
+    const int warps = 4;
+    size_t smem = 0;
+    int blocks = 1;
+    cudaError_t e = warp_launch_shape(mlpol_see_kernel, T, nvox1, warps, smem, blocks);
+    if (e != cudaSuccess) return e;
+    mlpol_see_kernel<<<blocks, 32 * warps, smem, st>>>(mc, T, nvox1, kT, jkq, lstar, bvec, src, x, resid, bad);
+    return cudaGetLastError();
+}
+
+cudaError_t run_mlpol_apply(const MlConst &mc, const MlPolDev &T, long long nvox1, const double *kT, const double *jkq,
+                            const double *bvec, const double *x, double alpha, const double *add, int with_f,
+                            double *out, cudaStream_t st)
+{
+    const int warps = 4;
+    size_t smem = 0;
+    int blocks = 1;
+    cudaError_t e = warp_launch_shape(mlpol_apply_kernel, T, nvox1, warps, smem, blocks);
+    if (e != cudaSuccess) return e;
+    mlpol_apply_kernel<<<blocks, 32 * warps, smem, st>>>(mc, T, nvox1, kT, jkq, bvec, x, alpha, add, with_f, out);
     return cudaGetLastError();
 }
 

@@ -55,10 +55,21 @@ cudaError_t run_mlpol_prepare(const MlConst &mc, const MlPolDev &T, long long nv
 
 // the rate equations per voxel (jkq [line voxel][6], lstar [line voxel], bvec [3][line voxel]);
 // x updated in place, max relative population change into *resid
+// src (per voxel, nunk; null: e_row0) is the right-hand side (coarse-grid equations)
 cudaError_t run_mlpol_see(const MlConst &mc, const MlPolDev &T, long long nvox1, const double *kT, const double *jkq,
                           const double *lstar, const double *bvec, double *x, unsigned long long *resid,
-                          unsigned long long *bad, cudaStream_t st);
+                          unsigned long long *bad, cudaStream_t st, const double *src = nullptr);
+
+// out = alpha A(x) + add + with_f e_row0 with A the plain rate operator (trace row for
+// level 0's population); add may be null; full layout [v][nunk]
+cudaError_t run_mlpol_apply(const MlConst &mc, const MlPolDev &T, long long nvox1, const double *kT, const double *jkq,
+                            const double *bvec, const double *x, double alpha, const double *add, int with_f,
+                            double *out, cudaStream_t st);
 
 size_t mlpol_see_smem(const MlPolDev &T, int warps);
+
+// max relative change of the populations between two vectors of unknowns (atomic max on the bits in *resid)
+cudaError_t run_mlpol_change(const MlConst &mc, const MlPolDev &T, long long nvox1, const double *old, const double *cur,
+                             unsigned long long *resid, cudaStream_t st);
 
 }  // namespace porta

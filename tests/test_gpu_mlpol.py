@@ -157,8 +157,56 @@ def test_invalid_inputs_are_rejected():
     ctx.set_atmosphere(atm)
     ctx.set_unknowns(x)
     with pytest.raises(P.PortaError):
-        ctx.mg_setup(2)
+        ctx.mg_setup(4)                          # 6 x 5 horizontal planes cannot be halved twice
     # a Zeeman splitting that makes |eta_V| > eta_I in the line wings is rejected
     strong = P.MlContext(atm, atom, *QUAD, precision=P.PORTA_FP32, polarized=True, zeta=3.5e-4)
     with pytest.raises(P.PortaError):
         strong.set_atmosphere(atm)
+
+
+def _mg_case():
+    atm = synth.multilevel_box(8, 8, 17, seed=2, tau_top=1e-2, tau_bot=1e2)
+    atm["zeta"] = 5e-5
+    atom = synth.multilevel_atom(seed=3, eps_range=(1e-2, 3e-2))
+    return atm, atom, mlpol.Tables(atom)
+
+
+@pytest.mark.parametrize("prec", [P.PORTA_FP64, P.PORTA_FP32])
+def test_multigrid_cycle_matches_oracle(prec):
+    quad = (2, 4, 5)
+    atm, atom, tab = _mg_case()
+    x0 = mlpol.lte_unknowns(tab, atm["kT"])
+    ctx = P.MlContext(atm, atom, *quad, precision=prec, polarized=True)
+    ctx.set_atmosphere(atm)
+    ctx.set_unknowns(x0)
+    ctx.mg_setup(3)
+    assert ctx.mg_levels() == [(8, 8, 17), (4, 4, 9), (2, 2, 5)]
+    ch = ctx.mg_vcycle(2, 4, 8)
+    got = ctx.get_unknowns()
+    want = mlpol.vcycle(ml.hierarchy(atm, 3), atom, tab, quad, x0)
+    rb = mlpol.real_basis(atom)
+    r00 = np.stack([want[..., rb.index((i, 0, 0, 0))] for (i, K, Q, p) in rb], -1)
+    fp64 = prec == P.PORTA_FP64
+    assert np.max(np.abs((got - want) / r00)) < (1e-9 if fp64 else 1e-4)
+    pw, p0 = tab.populations(want), tab.populations(x0)
+    wch = np.max(np.abs(pw - p0) / p0)
+    assert abs(ch - wch) < (1e-8 if fp64 else 1e-3) * wch
+
+
+def test_multigrid_reaches_the_jacobi_fixed_point():
+    quad = (2, 4, 5)
+    atm, atom, tab = _mg_case()
+    x0 = mlpol.lte_unknowns(tab, atm["kT"])
+
+    def make(x):
+        c = P.MlContext(atm, atom, *quad, precision=P.PORTA_FP64, polarized=True)
+        c.set_atmosphere(atm)
+        c.set_unknowns(x)
+        return c
+    a = make(x0)
+    a.mg_setup(3)
+    for _ in range(9):
+        ch = a.mg_vcycle(2, 4, 8)
+    assert ch < 1e-9
+    b = make(a.get_unknowns())
+    assert b.ml_iterate(1) < 1e-9
