@@ -59,6 +59,7 @@ class _Problem(ctypes.Structure):
         ("n_mu", ctypes.c_int), ("n_chi", ctypes.c_int), ("n_nu", ctypes.c_int),
         ("x_max", ctypes.c_double),
         ("method", ctypes.c_int),
+        ("dich", ctypes.c_void_p),
     ]
 
 
@@ -151,6 +152,9 @@ class Problem:
         s.n_mu, s.n_chi, s.n_nu = n_mu, n_chi, n_nu
         s.x_max = float(x_max)
         s.method = method
+        d = atm.get("dich")
+        self._keep["dich"] = _f64(d).ravel() if d is not None else None
+        s.dich = _ptr(self._keep["dich"])
         self.s = s
         self.nray = 2 * n_mu * n_chi
         self.n_nu = n_nu

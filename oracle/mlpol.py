@@ -49,16 +49,16 @@ layers with the full anisotropy J^2_Q and can give negative populations.
 Without polarization this is the update of oracle/ml.py; the fixed point is
 that of the rate equations.
 
-Line transfer (a reading, the first cut of the polarized multilevel atom): the
-emissivity of a line carries the upper level's multipoles K = 0, 2 (the
-two-level formal solver of this package, eps_i = eta_I sum_KQ (-1)^Q T^K_Q
-S^K_-Q with S^K_Q = S_line w^(K) conj(rho^K_Q / rho^0_0)(J_u), w^(K) =
-(-1)^(1+Jl+Ju) sqrt(3(2Ju+1)) {1 1 K; Ju Ju Jl}); the opacity is that of the
-populations (eta_Q,U,V from the lower level's atomic polarization --
-dichroism -- and the orientation terms are not included), and the weak-field
-Zeeman term uses the field scaled by the line's effective Lande factor (1
-for every level here). The formal solution therefore gives J^Kr_Qr for
-Kr = 0, 2 only.
+Line transfer (a reading): the emissivity of a line carries the upper level's
+multipoles K = 0, 2 (the two-level formal solver of this package, eps_i =
+eta_I sum_KQ (-1)^Q T^K_Q S^K_-Q with S^K_Q = S_line w^(K) conj(rho^K_Q /
+rho^0_0)(J_u), w^(K) = (-1)^(1+Jl+Ju) sqrt(3(2Ju+1)) {1 1 K; Ju Ju Jl}); the
+absorption matrix carries the line's dichroism from the alignment (K = 2) of
+its lower level (absorption) and upper level (stimulated emission),
+line_dichroism; the orientation (K = 1) terms are not included, and the
+weak-field Zeeman term uses the field scaled by the line's effective Lande
+factor (1 for every level here). The formal solution therefore gives
+J^Kr_Qr for Kr = 0, 2 only.
 """
 import numpy as np
 
@@ -360,17 +360,54 @@ def line_source_multipoles(tab, x):
     return out
 
 
-def line_problem(atm, atom, tab, x, li, quad):
-    """the two-level polarized formal-solution problem of line li"""
+def line_dichroism(tab, x, li):
+    """dichroism multipoles of line li in the formal solver's layout (D20, Re D21,
+    Im D21, Re D22, Im D22): the alignment terms of the line's absorption (lower
+    level) minus stimulated emission (upper level) relative to their K = 0 terms,
+    eta_i = eta_I [delta_i0 + sum_Q (-1)^Q T^2_Q(i, Omega) D^2_-Q] with
+      D^2_Q = conj([B_lu sqrt(2Jl+1) w2(Jl, Ju) rho^2_Q(Jl) - B_ul sqrt(2Ju+1) w2(Ju, Jl) rho^2_Q(Ju)]
+                    / [B_lu sqrt(2Jl+1) rho^0_0(Jl) - B_ul sqrt(2Ju+1) rho^0_0(Ju)]),
+    w2(J, J') = (-1)^(1+J+J') sqrt(3(2J+1)) {1 1 2; J J J'} (LL04's absorption and
+    stimulated-emission coefficients, the (-1)^K of absorption being 1 for K = 2)."""
+    u, l = tab.lines[li]
+    Ju, Jl = tab.J[u], tab.J[l]
+    xc = tab.to_complex(x)
+
+    def w2(J, Jp):
+        if J < 1:
+            return 0.0
+        return (-1) ** int(round(1 + J + Jp)) * np.sqrt(3 * (2 * J + 1)) * w6j(1, 1, 2, J, J, Jp)
+    al = tab.Blu[li] * np.sqrt(2 * Jl + 1)
+    au = tab.Bul[li] * np.sqrt(2 * Ju + 1)
+    den = al * xc[..., tab.idx[(l, 0, 0)]].real - au * xc[..., tab.idx[(u, 0, 0)]].real
+    out = np.zeros(x.shape[:-1] + (5,))
+    for Q, (kr, ki) in ((0, (0, None)), (1, (1, 2)), (2, (3, 4))):
+        num = np.zeros(x.shape[:-1], dtype=complex)
+        if Jl >= 1:
+            num = num + al * w2(Jl, Ju) * xc[..., tab.idx[(l, 2, Q)]]
+        if Ju >= 1:
+            num = num - au * w2(Ju, Jl) * xc[..., tab.idx[(u, 2, Q)]]
+        d = np.conj(num / den)
+        out[..., kr] = np.real(d)
+        if ki is not None:
+            out[..., ki] = np.imag(d)
+    return out
+
+
+def line_problem(atm, atom, tab, x, li, quad, dichroism=True):
+    """the two-level polarized formal-solution problem of line li (with the line's
+    dichroism from the atomic polarization of its levels unless dichroism=False)"""
     pops = tab.populations(x)
     a = dict(atm)
     a["chi"] = ml.line_opacity(atom, atm["chi"], pops)[..., li]
     a["bpl"] = ml.planck(atom, atm["kT"])[..., li]
     a["eps"] = np.ones_like(a["chi"])
+    if dichroism:
+        a["dich"] = line_dichroism(tab, x, li)
     return Problem(a, 1, *quad)
 
 
-def formal_solve_lines(atm, atom, tab, x, quad):
+def formal_solve_lines(atm, atom, tab, x, quad, dichroism=True):
     """Jbar (real layout of jkq_complex, Kr = 0, 2 filled) and Lambda-bar* per line"""
     src = line_source_multipoles(tab, x)
     nline = len(tab.lines)
@@ -378,7 +415,7 @@ def formal_solve_lines(atm, atom, tab, x, quad):
     jbar = np.zeros(shape + (nline, 9))
     lstar = np.zeros(shape + (nline,))
     for li in range(nline):
-        p = line_problem(atm, atom, tab, x, li, quad)
+        p = line_problem(atm, atom, tab, x, li, quad, dichroism)
         j, ls = formal_solve(p, src[..., li, :])
         # two-level layout (J00, J20, ReJ21, ImJ21, ReJ22, ImJ22) -> Kr = 0, 1, 2 layout
         jbar[..., li, 0] = j[..., 0]

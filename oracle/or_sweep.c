@@ -64,7 +64,10 @@ static double angular_source(const double *t6, const double *s)
  * Unpolarized two-level atom: eps_I = eta_I S.
  * Polarized two-level atom (Jl = 0 -> Ju = 1, w^(2) = 1): eps_i = eta_I S_i(Omega), i = I, Q, U;
  * weak-field Zeeman: eta_V = -gbar zeta (B.Omega) d(eta_I)/dx = 2 gbar zeta (x - s)(B.Omega) eta_I,
- * eps_V = S^0_0 eta_V; eta_Q = eta_U = rho_Q = rho_U = rho_V = 0.
+ * eps_V = S^0_0 eta_V; rho_Q = rho_U = rho_V = 0. With dichroism multipoles D^2_Q (the
+ * atomic polarization of the lower level of a multilevel line, p->dich), eta_i = eta_I
+ * [delta_i0 + sum_Q (-1)^Q T^2_Q(i, Omega) D^2_-Q] for i = I, Q, U (eta_V and the
+ * emissivities stay relative to eta_I = chi phi); otherwise eta_Q = eta_U = 0.
  */
 static void node_coeffs(const or_problem *p, const double *rho, long v, const or_ray *r, double x,
                         double eta[7], double eps[4])
@@ -85,6 +88,11 @@ static void node_coeffs(const or_problem *p, const double *rho, long v, const or
     for (int i = 0; i < 3; i++) eps[i] = etaI * angular_source(r->t + 6 * i, s);
     eps[3] = s[0] * eta[3];
     OR_FLOPS(5 + 5 + 3 * 12 + 1);
+    if (p->dich) {
+        const double *d = p->dich + 5 * v;
+        const double d6[6] = {1.0, d[0], d[1], d[2], d[3], d[4]};
+        for (int i = 0; i < 3; i++) eta[i] = etaI * angular_source(r->t + 6 * i, d6);
+    }
 }
 
 /* bilinear interpolation weights on a periodic plane at cell coordinates (xc, yc) */

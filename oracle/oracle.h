@@ -43,6 +43,10 @@ typedef struct {
     int n_mu, n_chi, n_nu;    /* inclinations per hemisphere, azimuths, frequencies */
     double x_max;             /* frequency grid covers [-x_max, x_max] Doppler widths */
     int method;               /* OR_BESSER or OR_DELOPAR */
+    /* polarized model, optional (NULL: none): dichroism multipoles per voxel,
+       5 doubles (D20, Re D21, Im D21, Re D22, Im D22): eta_i = chi phi
+       [delta_i0 + sum_Q (-1)^Q T^2_Q(i, Omega) D^2_-Q], i = I, Q, U */
+    const double *dich;
 } or_problem;
 
 /* number of unknowns per voxel (rho), Stokes parameters, radiation-field components */

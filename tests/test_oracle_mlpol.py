@@ -279,3 +279,39 @@ def test_multigrid_cycles_reach_the_fixed_point_faster_than_jacobi():
     assert np.max(np.abs(plain - x)) < 1e-8 * np.max(np.abs(x))
     x2 = mlpol.vcycle(levels, atom, tab, quad, x)
     assert np.max(np.abs(x2 - x)) < 1e-9 * np.max(np.abs(x))
+
+
+def _eta_ratios(d5, mu, chi):
+    """eta_i / eta_0 (i = I, Q, U) for dichroism multipoles d5 along (mu, chi)"""
+    t = oracle.tkq(mu, chi)
+    d6 = np.array([1.0, *d5])
+    out = []
+    for i in range(3):
+        a = d6 if i == 0 else np.concatenate([[0.0], d6[1:]])
+        out.append(t[i, 0] * a[0] + t[i, 1] * a[1] + 2 * (t[i, 2] * a[2] + t[i, 3] * a[3]) +
+                   2 * (t[i, 4] * a[4] + t[i, 5] * a[5]))
+    return np.array(out)
+
+
+def test_dichroism_follows_the_selection_rules():
+    """Absorption from a J = 1 lower level with only m = 0 populated towards J = 0
+    (a pure pi transition): nothing is absorbed along z (eta_I = 0) and, along x,
+    only light polarized along z (eta_I = eta_Q, reference direction e_a = -z). The
+    same holds for stimulated emission from a J = 1 upper level with only M = 0
+    populated towards J = 0. An unpolarized lower level gives no dichroism."""
+    at = _atom2(1, 0)
+    tab = mlpol.Tables(at)
+    x = _sublevels(tab, 0, [0.0, 1.0, 0.0])
+    d = mlpol.line_dichroism(tab, x, 0)
+    assert abs(_eta_ratios(d, 1.0, 0.3)[0]) < 1e-12
+    e = _eta_ratios(d, 0.0, 0.0)
+    assert abs(e[0] - e[1]) < 1e-12 and e[0] > 0.5 and abs(e[2]) < 1e-12
+    assert np.max(np.abs(mlpol.line_dichroism(tab, _sublevels(tab, 0, [1.0, 1.0, 1.0]), 0))) < 1e-14
+    # stimulated emission (an inverted upper level alone: negative absorption, the same pattern)
+    at = _atom2(0, 1)
+    tab = mlpol.Tables(at)
+    x = _sublevels(tab, 1, [0.0, 1.0, 0.0])
+    d = mlpol.line_dichroism(tab, x, 0)
+    assert abs(_eta_ratios(d, 1.0, 0.3)[0]) < 1e-12
+    e = _eta_ratios(d, 0.0, 1.1)
+    assert abs(e[0] - e[1]) < 1e-12 and e[0] > 0.5
