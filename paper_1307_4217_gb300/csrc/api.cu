@@ -190,11 +190,15 @@ template <typename Real, int NS>
 void launch_caps(const porta_ctx *c, int C, int &ring_plane, int &ipts_max)
 {
     const int nch = (NS == 1 ? 4 : 8) * (int)sizeof(Real) / 16;
+    const bool dich = NS == 4 && c->d_dich != nullptr;
     ring_plane = 0;
     ipts_max = 0;
     for (const BoxDev &b : c->boxes) {
         const int rmax = (b.ny + C - 1) / C;
-        ring_plane = std::max(ring_plane, nch * (rmax + 2) * b.nx);
+        const int chunk = (rmax + 2) * b.nx;
+        // with dichroism the slots of a second ring ((eta_Q, eta_U) / eta_I per node) follow the node ring
+        const int dchunks = dich ? (chunk * 2 * (int)sizeof(Real) + 15) / 16 : 0;
+        ring_plane = std::max(ring_plane, nch * chunk + dchunks);
         ipts_max = std::max(ipts_max, rmax * b.nx);
     }
 }
@@ -240,7 +244,7 @@ int choose_launch(porta_ctx *c, LaunchCfg &best, int force_c, int force_f, int n
         const int threads = std::min(kThreads, std::max(64, (ipts_max * F + 31) / 32 * 32));
         const int smem = sweep_smem_bytes<Real, NS>(ring_plane, ipts_max, F, threads);
         int act = 0;
-        if (max_active_clusters<Real, NS>(C, smem, threads, &act) != cudaSuccess) {
+        if (max_active_clusters<Real, NS>(C, smem, threads, &act, c->d_dich != nullptr) != cudaSuccess) {
             cudaGetLastError();
             continue;
         }
@@ -311,6 +315,7 @@ SweepArgs<Real> base_args(porta_ctx *c)
     a.bz = atm + 4 * c->nvox;
     a.bpl = atm + 5 * c->nvox;
     a.rho = (const Real *)c->d_rhoR;
+    a.dich = (const Real *)c->d_dich;
     a.xf = (const Real *)c->d_freq;
     a.wf = (const Real *)c->d_freq + c->n_nu;
     a.probe_ray = -1;
@@ -867,6 +872,7 @@ void free_all(porta_ctx *c)
     drop_graph(c);
     mg_free(c);
     it_free(c);
+    if (c->d_dich) cudaFree(c->d_dich);
     if (c->ml) {
         cudaFree(c->ml->d_x);
         cudaFree(c->ml->d_tab);
@@ -1312,9 +1318,11 @@ cudaError_t ml_prepare(porta_ctx *c)
     if (m->pol) {
         if (c->precision == PORTA_FP32)
             return run_mlpol_prepare<float>(m->mc, m->dev, m->nvox1, m->d_x, m->d_chis, m->d_kT, (float *)atm,
-                                            (float *)(atm + 5 * n * R), (float *)c->d_rhoR, c->d_rho, m->d_bad, c->stream);
+                                            (float *)(atm + 5 * n * R), (float *)c->d_rhoR, c->d_rho,
+                                            (float *)c->d_dich, m->d_bad, c->stream);
         return run_mlpol_prepare<double>(m->mc, m->dev, m->nvox1, m->d_x, m->d_chis, m->d_kT, (double *)atm,
-                                         (double *)(atm + 5 * n * R), (double *)c->d_rhoR, c->d_rho, m->d_bad, c->stream);
+                                         (double *)(atm + 5 * n * R), (double *)c->d_rhoR, c->d_rho,
+                                         (double *)c->d_dich, m->d_bad, c->stream);
     }
     if (c->precision == PORTA_FP32)
         return run_ml_prepare<float>(m->mc, m->nvox1, m->d_pops, m->d_chis, m->d_kT, (float *)atm,
@@ -2420,27 +2428,29 @@ int porta_ml_create(const porta_grid *g, const porta_ml_atom *a, const porta_qua
         m->tab = tab;
         m->nunk = tab.nunk;
         const size_t ni = tab.pop_idx.size() + tab.up2.size() + tab.cell_rc.size() + tab.cell_start.size() +
-                          tab.ent_src.size() + tab.act.size() + tab.inact.size() + tab.apop.size();
-        const size_t nd = tab.w2.size() + tab.trace.size() + tab.ent_coef.size();
+                          tab.ent_src.size() + tab.act.size() + tab.inact.size() + tab.apop.size() + tab.lo2.size();
+        const size_t nd = tab.w2.size() + tab.trace.size() + tab.ent_coef.size() + tab.w2lo.size();
         const size_t ibytes = (ni * sizeof(int) + 7) / 8 * 8;
         std::vector<char> h(ibytes + nd * sizeof(double));
         int *ip = (int *)h.data();
         double *dp = (double *)(h.data() + ibytes);
-        size_t io[8], doff[3], k = 0, kd = 0;
-        const std::vector<int> *iv[8] = {&tab.pop_idx, &tab.up2, &tab.cell_rc, &tab.cell_start, &tab.ent_src,
-                                         &tab.act, &tab.inact, &tab.apop};
-        for (int q2 = 0; q2 < 8; ++q2) {
+        size_t io[9], doff[4], k = 0, kd = 0;
+        const std::vector<int> *iv[9] = {&tab.pop_idx, &tab.up2, &tab.cell_rc, &tab.cell_start, &tab.ent_src,
+                                         &tab.act, &tab.inact, &tab.apop, &tab.lo2};
+        for (int q2 = 0; q2 < 9; ++q2) {
             io[q2] = k;
             for (int x : *iv[q2]) ip[k++] = x;
         }
-        const std::vector<double> *dv[3] = {&tab.w2, &tab.trace, &tab.ent_coef};
-        for (int q2 = 0; q2 < 3; ++q2) {
+        const std::vector<double> *dv[4] = {&tab.w2, &tab.trace, &tab.ent_coef, &tab.w2lo};
+        for (int q2 = 0; q2 < 4; ++q2) {
             doff[q2] = kd;
             for (double x : *dv[q2]) dp[kd++] = x;
         }
         e = cudaMalloc(&m->d_tab, h.size());
         if (e == cudaSuccess) e = cudaMemcpy(m->d_tab, h.data(), h.size(), cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = dalloc(&m->d_x, (size_t)m->nvox1 * tab.nunk);
+        if (e == cudaSuccess) e = cudaMalloc(&c->d_dich, (size_t)5 * c->nvox * c->rsz);
+        if (e == cudaSuccess) e = cudaMemset(c->d_dich, 0, (size_t)5 * c->nvox * c->rsz);
         const int *di = (const int *)m->d_tab;
         const double *dd = (const double *)((const char *)m->d_tab + ibytes);
         MlPolDev &d = m->dev;
@@ -2450,7 +2460,8 @@ int porta_ml_create(const porta_grid *g, const porta_ml_atom *a, const porta_qua
         d.row0 = tab.row0;
         d.src_j = tab.src_j; d.src_b = tab.src_b; d.src_clu = tab.src_clu; d.src_pop = tab.src_pop; d.src_spop = tab.src_spop;
         d.pop_idx = di + io[0]; d.up2 = di + io[1]; d.cell_rc = di + io[2]; d.cell_start = di + io[3]; d.ent_src = di + io[4];
-        d.act = di + io[5]; d.inact = di + io[6]; d.apop = di + io[7];
+        d.act = di + io[5]; d.inact = di + io[6]; d.apop = di + io[7]; d.lo2 = di + io[8];
+        d.w2lo = dd + doff[3];
         d.nact = tab.nact;
         d.ninact = (int)tab.inact.size();
         d.w2 = dd + doff[0]; d.trace = dd + doff[1]; d.ent_coef = dd + doff[2];

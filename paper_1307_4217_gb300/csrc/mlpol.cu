@@ -346,9 +346,12 @@ int mlpol_tables(const std::vector<double> &J, const std::vector<double> &E, con
         }
         t.cell_start.push_back((int)t.ent_src.size());
     }
-    // emission multipoles of each line: rho^0_0 and rho^2_Q (Q = 0, 1 re/im, 2 re/im) of the upper level
+    // emission multipoles of each line: rho^0_0 and rho^2_Q (Q = 0, 1 re/im, 2 re/im) of the upper
+    // level; dichroism: the same of the lower level
     t.w2.assign(nline, 0.0);
     t.up2.assign(6 * (size_t)nline, -1);
+    t.w2lo.assign(nline, 0.0);
+    t.lo2.assign(6 * (size_t)nline, -1);
     for (int li = 0; li < nline; ++li) {
         const int u = up[li], l = lo[li];
         auto ridx = [&](int i, int K, int Q, int p) {
@@ -357,6 +360,15 @@ int mlpol_tables(const std::vector<double> &J, const std::vector<double> &E, con
             return -1;
         };
         t.up2[6 * li] = ridx(u, 0, 0, 0);
+        t.lo2[6 * li] = ridx(l, 0, 0, 0);
+        if (two(J[l]) >= 2) {
+            t.w2lo[li] = sgn(1 + J[l] + J[u]) * std::sqrt(3.0 * (2 * J[l] + 1)) * W6(1, 1, 2, J[l], J[l], J[u]);
+            t.lo2[6 * li + 1] = ridx(l, 2, 0, 0);
+            t.lo2[6 * li + 2] = ridx(l, 2, 1, 0);
+            t.lo2[6 * li + 3] = ridx(l, 2, 1, 1);
+            t.lo2[6 * li + 4] = ridx(l, 2, 2, 0);
+            t.lo2[6 * li + 5] = ridx(l, 2, 2, 1);
+        }
         if (two(J[u]) >= 2) {
             t.w2[li] = sgn(1 + J[l] + J[u]) * std::sqrt(3.0 * (2 * J[u] + 1)) * W6(1, 1, 2, J[u], J[u], J[l]);
             t.up2[6 * li + 1] = ridx(u, 2, 0, 0);
@@ -378,7 +390,7 @@ inline int nblk(long long n, int t) { return (int)((n + t - 1) / t); }
 template <typename Real>
 __global__ void mlpol_prepare_kernel(const MlConst mc, MlPolDev T, long long nvox1, const double *x, const double *chis,
                                      const double *kT, Real *chi_out, Real *bpl_out, Real *S_out, double *S64_out,
-                                     unsigned long long *bad)
+                                     Real *dich_out, unsigned long long *bad)
 {
     const long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (v >= nvox1) return;
@@ -410,6 +422,24 @@ __global__ void mlpol_prepare_kernel(const MlConst mc, MlPolDev T, long long nvo
         for (int c = 0; c < 6; ++c) {
             S64_out[o * 6 + c] = s6[c];
             S_out[c * nvox + o] = (Real)s6[c];
+        }
+        // dichroism: D^2_Q = conj([B_lu sqrt(2Jl+1) w2lo rho^2_Q(l) - B_ul sqrt(2Ju+1) w2 rho^2_Q(u)]
+        //                        / [B_lu sqrt(2Jl+1) rho^0_0(l) - B_ul sqrt(2Ju+1) rho^0_0(u)])
+        if (dich_out) {
+            const int *il = T.lo2 + 6 * k;
+            const double al = mc.Blu[k] * sqrt(mc.g[l]), au = mc.Bul[k] * sqrt(mc.g[u]);
+            const double den = al * xv[il[0]] - au * xv[ix[0]];
+            double d5[5] = {0, 0, 0, 0, 0};
+            for (int c = 0; c < 5; ++c) {
+                double num = 0.0;
+                if (il[1 + c] >= 0) num += al * T.w2lo[k] * xv[il[1 + c]];
+                if (ix[1 + c] >= 0) num -= au * T.w2[k] * xv[ix[1 + c]];
+                d5[c] = num / den;
+            }
+            // conjugation: the imaginary parts change sign
+            d5[2] = -d5[2];
+            d5[4] = -d5[4];
+            for (int c = 0; c < 5; ++c) dich_out[c * nvox + o] = (Real)d5[c];
         }
     }
     if (nbad) atomicAdd(bad, (unsigned long long)nbad);
@@ -643,17 +673,17 @@ __global__ void mlpol_see_kernel(const MlConst mc, MlPolDev T, long long nvox1, 
 template <typename Real>
 cudaError_t run_mlpol_prepare(const MlConst &mc, const MlPolDev &T, long long nvox1, const double *x, const double *chis,
                               const double *kT, Real *chi_out, Real *bpl_out, Real *S_out, double *S64_out,
-                              unsigned long long *bad, cudaStream_t st)
+                              Real *dich_out, unsigned long long *bad, cudaStream_t st)
 {
     mlpol_prepare_kernel<Real><<<nblk(nvox1, 128), 128, 0, st>>>(mc, T, nvox1, x, chis, kT, chi_out, bpl_out, S_out,
-                                                                 S64_out, bad);
+                                                                 S64_out, dich_out, bad);
     return cudaGetLastError();
 }
 template cudaError_t run_mlpol_prepare<float>(const MlConst &, const MlPolDev &, long long, const double *, const double *,
-                                              const double *, float *, float *, float *, double *,
+                                              const double *, float *, float *, float *, double *, float *,
                                               unsigned long long *, cudaStream_t);
 template cudaError_t run_mlpol_prepare<double>(const MlConst &, const MlPolDev &, long long, const double *, const double *,
-                                               const double *, double *, double *, double *, double *,
+                                               const double *, double *, double *, double *, double *, double *,
                                                unsigned long long *, cudaStream_t);
 
 size_t mlpol_see_smem(const MlPolDev &T, int warps)

@@ -29,6 +29,8 @@ struct MlPolTables {
     std::vector<int> pop_idx;        // per level: index of rho^0_0
     std::vector<int> up2;            // per line: rho^0_0, rho^2_0, Re/Im rho^2_1, Re/Im rho^2_2 of the upper level (-1: none)
     std::vector<double> w2;          // per line: w^(2)_{Ju Jl}
+    std::vector<int> lo2;            // per line: the same six indices for the lower level (-1: none)
+    std::vector<double> w2lo;        // per line: w^(2)_{Jl Ju}
     std::vector<int> cell_rc, cell_start, ent_src;
     std::vector<double> ent_coef;
 };
@@ -37,8 +39,8 @@ struct MlPolTables {
 struct MlPolDev {
     int nunk, nsrc, ncell, row0, nact, ninact;
     int src_j, src_b, src_clu, src_pop, src_spop;
-    const int *pop_idx, *up2, *cell_rc, *cell_start, *ent_src, *act, *inact, *apop;
-    const double *w2, *trace, *ent_coef;
+    const int *pop_idx, *up2, *cell_rc, *cell_start, *ent_src, *act, *inact, *apop, *lo2;
+    const double *w2, *trace, *ent_coef, *w2lo;
 };
 
 // build the tables of an atom (levels J, energies E in eV; lines up/lo with A, eps); 0 on success
@@ -48,10 +50,11 @@ int mlpol_tables(const std::vector<double> &J, const std::vector<double> &E, con
 
 // per line and voxel: opacity, Planck function and the emission multipoles
 // S^K_Q (two-level real layout, AoS FP64 and SoA Real) from the unknowns x [v][nunk]
+// and the dichroism multipoles D^2_Q of each line (Real SoA [5][line voxel])
 template <typename Real>
 cudaError_t run_mlpol_prepare(const MlConst &mc, const MlPolDev &T, long long nvox1, const double *x, const double *chis,
                               const double *kT, Real *chi_out, Real *bpl_out, Real *S_out, double *S64_out,
-                              unsigned long long *bad, cudaStream_t st);
+                              Real *dich_out, unsigned long long *bad, cudaStream_t st);
 
 // the rate equations per voxel (jkq [line voxel][6], lstar [line voxel], bvec [3][line voxel]);
 // x updated in place, max relative population change into *resid

@@ -122,6 +122,7 @@ struct porta_ctx {
     double *it_final = nullptr;
     int it_niter = 0, it_ckpt = 0;
     MlState *ml = nullptr;                 // multilevel atom (porta_ml_create), else null
+    void *d_dich = nullptr;                // Real [5][nvox] dichroism multipoles of polarized lines (null: none)
     size_t tape_limit = (size_t)16 << 30;  // device tape of the J^K_Q reverse (ray batches)
     std::map<int, porta::LaunchCfg> adj2_tuned;  // J^K_Q adjoint: shape timed once per batch size
     cudaEvent_t it_ev[4] = {nullptr, nullptr, nullptr, nullptr};

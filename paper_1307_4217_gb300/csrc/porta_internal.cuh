@@ -61,6 +61,7 @@ struct SweepArgs {
     void *part;                    // [ray][nvox] partial integrals (J mode)
     double *out;                   // emergent: [dir][nu][ny][nx][ns]
     int probe_ray;                 // -1 or the ray whose Stokes vectors are written to probe
+    const Real *dich;              // polarized lines with dichroism: [5][nvox] D^2_Q (null: none)
     Real *probe;                   // [nu][nvox][ns]
     Real *probe_ls;                // [nu][nvox]
     int *next_item;                // J mode: null (static striding) or the launch's work-list counter
@@ -94,7 +95,7 @@ template <typename Real, int NS>
 int sweep_smem_bytes(int ring_plane, int ipts_max, int F, int threads);
 
 template <typename Real, int NS>
-cudaError_t max_active_clusters(int cluster, int smem, int threads, int *out);
+cudaError_t max_active_clusters(int cluster, int smem, int threads, int *out, bool dich = false);
 
 // adjoint of the emergent sweep (adjoint.cu): shared memory of a launch with
 // ring plane `ring_plane` (16-byte chunks), `ipts` points per strip, tape

@@ -61,7 +61,7 @@ __device__ __forceinline__ void accumulate_partial(const SweepArgs<Real> &a, int
     }
 }
 
-template <typename Real, int NS, int MODE>
+template <typename Real, int NS, int MODE, bool DI>
 __device__ __forceinline__ void sweep_item(const SweepArgs<Real> &a, cg::cluster_group &cluster,
                                            typename V16<Real>::T *ring, Real *ibuf, Real *lane_buf, int box, int m,
                                            int g, int rank, int C, int dir_out)
@@ -90,6 +90,13 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<Real> &a, cg::cluster
     constexpr int NCH = node_words<NS>() * (int)sizeof(Real) / 16;
     const int chunk = (rmax + 2) * nx;              // ring chunk-plane stride (16-byte chunks)
     const int plane = NCH * chunk;                  // ring plane stride
+    // dichroism (polarized lines whose levels carry alignment): eta_Q / eta_I and
+    // eta_U / eta_I per node in a second 3-slot ring after the node ring (the
+    // launch reserves it); the node's opacity, source terms and Zeeman factor are
+    // rescaled by eta_I / (chi phi) = 1 + d_I(Omega)
+    constexpr bool dich = NS == 4 && DI;
+    Real *dring = reinterpret_cast<Real *>(ring + 3 * plane);
+    const int dstride = (chunk * 2 * (int)sizeof(Real) + 15) / 16 * 16 / (int)sizeof(Real);
     const int ipts = rmax * nx;                     // points per Stokes plane
     const int ichunk = ipts;                        // Stokes chunk-plane stride (16-byte chunks)
     const int iplane = NS * ipts;                   // Reals per (buf, f) Stokes plane
@@ -118,7 +125,29 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<Real> &a, cg::cluster
             pj -= pj >= ny ? ny : 0;
             pj -= pj >= ny ? ny : 0;
             const long long v = B.vox0 + (kbase + pj) * nx + pi;
-            ring_store<Real, NS>(ring, plane, chunk, q % 3, idx, make_node<Real, NS>(a, ray, v, m, jmode));
+            Node<Real, NS> n = make_node<Real, NS>(a, ray, v, m, jmode);
+            if constexpr (NS == 4) {
+                if constexpr (dich) {
+                    const long long nv = a.nvox;
+                    const Real d20 = a.dich[v], d21r = a.dich[nv + v], d21i = a.dich[2 * nv + v];
+                    const Real d22r = a.dich[3 * nv + v], d22i = a.dich[4 * nv + v];
+                    Real dd[3];
+#pragma unroll
+                    for (int i = 0; i < 3; ++i) {
+                        const Real *t = ray.t + 6 * i;
+                        dd[i] = t[1] * d20 + Real(2) * (t[2] * d21r + t[3] * d21i) + Real(2) * (t[4] * d22r + t[5] * d22i);
+                    }
+                    const Real f = Real(1) + dd[0], inv = Real(1) / f;
+                    n.chi *= f;
+                    n.SI *= inv;
+                    n.SQ *= inv;
+                    n.SU *= inv;
+                    n.b *= inv;
+                    dring[(q % 3) * dstride + 2 * idx] = dd[1] * inv;
+                    dring[(q % 3) * dstride + 2 * idx + 1] = dd[2] * inv;
+                }
+            }
+            ring_store<Real, NS>(ring, plane, chunk, q % 3, idx, n);
             c += dc;
             lr += dl;
             if (c >= nx) { c -= nx; ++lr; }
@@ -207,6 +236,20 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<Real> &a, cg::cluster
                 } else {
                     kP[0] = kP[1] = kP[2] = kP[3] = corner_p<Real, NS>(nO, Real(0));
                 }
+                // dichroism ratios of the upwind corners and of O
+                Real mdq[4] = {0, 0, 0, 0}, mdu[4] = {0, 0, 0, 0}, odq = 0, odu = 0;
+                if constexpr (dich) {
+                    const Real *dm = dring + sM * dstride;
+                    const int ix[4] = {(l + 1) * nx + c, (l + 1) * nx + c1, (l + 2) * nx + c, (l + 2) * nx + c1};
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        mdq[k] = dm[2 * ix[k]];
+                        mdu[k] = dm[2 * ix[k] + 1];
+                    }
+                    const Real *dO = dring + sO * dstride;
+                    odq = dO[2 * ((l + 1) * nx + c)];
+                    odu = dO[2 * ((l + 1) * nx + c) + 1];
+                }
                 const Real wI[4] = {mx0 * my0, mx1 * my0, mx0 * my1, mx1 * my1};
                 const bool last_row = (l + 1 == R);
                 const int ilo = l * nx;                               // row l in this CTA
@@ -230,7 +273,7 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<Real> &a, cg::cluster
                         for (int s = 0; s < NS; ++s) IM[s] = wI[0] * t0[s] + wI[1] * t1[s] + wI[2] * t2[s] + wI[3] * t3[s];
                     }
                     // a2-a3: node transfer coefficients and bilinear interpolation at M and P
-                    Real etaM = 0, etaVM = 0, epsM[NS];
+                    Real etaM = 0, etaVM = 0, etaQM = 0, etaUM = 0, epsM[NS];
 #pragma unroll
                     for (int s = 0; s < NS; ++s) epsM[s] = 0;
 #pragma unroll
@@ -238,6 +281,10 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<Real> &a, cg::cluster
                         const Real xs = x - kM[k].s;
                         const Real we = kM[k].wchi * profile_shape(xs);
                         etaM += we;
+                        if constexpr (dich) {
+                            etaQM += we * mdq[k];
+                            etaUM += we * mdu[k];
+                        }
                         if constexpr (NS == 1) {
                             epsM[0] += we * kM[k].S;
                         } else {
@@ -308,6 +355,24 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<Real> &a, cg::cluster
                     Real IO[NS];
                     if constexpr (NS == 1) {
                         IO[0] = co.e * IM[0] + co.wm * SM[0] + co.wo * SO[0] + co.wc * cM[0];
+                    } else if constexpr (dich) {
+                        // K' with eta_Q, eta_U (dichroism) and eta_V entries over eta_I:
+                        // (K'I)_0 = q I_1 + u I_2 + v I_3, (K'I)_k = k_k I_0
+                        const Real qM = etaQM * iM, uM = etaUM * iM, vM = etaVM * iM;
+                        const Real qO = odq, uO = odu, vO = nO.b * xsO;
+                        Real rhs[4];
+#pragma unroll
+                        for (int s = 0; s < 4; ++s) rhs[s] = co.e * IM[s] + co.wm * SM[s] + co.wo * SO[s] + co.wc * cM[s];
+                        rhs[0] -= co.pm * (qM * IM[1] + uM * IM[2] + vM * IM[3]);
+                        rhs[1] -= co.pm * qM * IM[0];
+                        rhs[2] -= co.pm * uM * IM[0];
+                        rhs[3] -= co.pm * vM * IM[0];
+                        // (1 + psi'_O K'_O)^-1 of the arrow-shaped matrix
+                        const Real aq = co.po * qO, au = co.po * uO, av = co.po * vO;
+                        IO[0] = (rhs[0] - aq * rhs[1] - au * rhs[2] - av * rhs[3]) * rcp(Real(1) - aq * aq - au * au - av * av);
+                        IO[1] = rhs[1] - aq * IO[0];
+                        IO[2] = rhs[2] - au * IO[0];
+                        IO[3] = rhs[3] - av * IO[0];
                     } else {
                         // K' has only the eta_V / eta_I entries (weak-field Zeeman)
                         const Real kvM = etaVM * iM;
@@ -397,7 +462,7 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<Real> &a, cg::cluster
     }
 }
 
-template <typename Real, int NS, int MODE>
+template <typename Real, int NS, int MODE, bool DI = false>
 __global__ void __launch_bounds__(512, 1) sweep_kernel(const SweepArgs<Real> a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -429,7 +494,7 @@ __global__ void __launch_bounds__(512, 1) sweep_kernel(const SweepArgs<Real> a)
                 const int code = a.items ? a.items[item] : item;
                 const int box = code / a.nray, m = code - box * a.nray;
                 for (int g = 0; g < a.ngroups; ++g)
-                    sweep_item<Real, NS, MODE>(a, cluster, ring, ibuf, lane_buf, box, m, g, rank, C, 0);
+                    sweep_item<Real, NS, MODE, DI>(a, cluster, ring, ibuf, lane_buf, box, m, g, rank, C, 0);
             }
             return;
         }
@@ -439,24 +504,26 @@ __global__ void __launch_bounds__(512, 1) sweep_kernel(const SweepArgs<Real> a)
             const int code = a.items ? a.items[item] : item;
             const int box = code / a.nray, m = code - box * a.nray;
             for (int g = 0; g < a.ngroups; ++g)
-                sweep_item<Real, NS, MODE>(a, cluster, ring, ibuf, lane_buf, box, m, g, rank, C, 0);
+                sweep_item<Real, NS, MODE, DI>(a, cluster, ring, ibuf, lane_buf, box, m, g, rank, C, 0);
         } else {
             const int d = item / a.ngroups, g = item - d * a.ngroups;
-            sweep_item<Real, NS, MODE>(a, cluster, ring, ibuf, lane_buf, 0, d, g, rank, C, d);
+            sweep_item<Real, NS, MODE, DI>(a, cluster, ring, ibuf, lane_buf, 0, d, g, rank, C, d);
         }
     }
 }
 
 template <typename Real, int NS>
-static void *kernel_ptr(int mode)
+static void *kernel_ptr(int mode, bool dich = false)
 {
+    // the dichroism variant (polarized lines of the multilevel atom) exists for the J^K_Q sweep
+    if (NS == 4 && dich && mode == MODE_JKQ) return (void *)sweep_kernel<Real, NS, MODE_JKQ, NS == 4>;
     return mode == MODE_JKQ ? (void *)sweep_kernel<Real, NS, MODE_JKQ> : (void *)sweep_kernel<Real, NS, MODE_EMERGENT>;
 }
 
 template <typename Real, int NS>
-static cudaError_t prepare(int mode, int cluster, int smem)
+static cudaError_t prepare(int mode, int cluster, int smem, bool dich = false)
 {
-    void *k = kernel_ptr<Real, NS>(mode);
+    void *k = kernel_ptr<Real, NS>(mode, dich);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     if (cluster > 8) e = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
@@ -464,9 +531,9 @@ static cudaError_t prepare(int mode, int cluster, int smem)
 }
 
 template <typename Real, int NS>
-cudaError_t max_active_clusters(int cluster, int smem, int threads, int *out)
+cudaError_t max_active_clusters(int cluster, int smem, int threads, int *out, bool dich)
 {
-    cudaError_t e = prepare<Real, NS>(MODE_JKQ, cluster, smem);
+    cudaError_t e = prepare<Real, NS>(MODE_JKQ, cluster, smem, dich);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t lc = {};
     lc.gridDim = dim3(cluster);
@@ -479,13 +546,14 @@ cudaError_t max_active_clusters(int cluster, int smem, int threads, int *out)
     at[0].val.clusterDim.z = 1;
     lc.attrs = at;
     lc.numAttrs = 1;
-    return cudaOccupancyMaxActiveClusters(out, (void (*)(SweepArgs<Real>))kernel_ptr<Real, NS>(MODE_JKQ), &lc);
+    return cudaOccupancyMaxActiveClusters(out, (void (*)(SweepArgs<Real>))kernel_ptr<Real, NS>(MODE_JKQ, dich), &lc);
 }
 
 template <typename Real, int NS>
 cudaError_t launch_sweep(const SweepArgs<Real> &a, int mode, LaunchCfg &cfg, cudaStream_t st)
 {
-    cudaError_t e = prepare<Real, NS>(mode, cfg.cluster, cfg.smem);
+    const bool dich = NS == 4 && a.dich != nullptr && mode == MODE_JKQ;
+    cudaError_t e = prepare<Real, NS>(mode, cfg.cluster, cfg.smem, dich);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t lc = {};
     lc.gridDim = dim3(cfg.clusters * cfg.cluster);
@@ -504,6 +572,7 @@ cudaError_t launch_sweep(const SweepArgs<Real> &a, int mode, LaunchCfg &cfg, cud
         at[1].val.priority = cfg.priority;
         lc.numAttrs = 2;
     }
+    if (dich) return cudaLaunchKernelEx(&lc, sweep_kernel<Real, NS, MODE_JKQ, NS == 4>, a);
     if (mode == MODE_JKQ)
         return cudaLaunchKernelEx(&lc, sweep_kernel<Real, NS, MODE_JKQ>, a);
     return cudaLaunchKernelEx(&lc, sweep_kernel<Real, NS, MODE_EMERGENT>, a);
@@ -511,7 +580,7 @@ cudaError_t launch_sweep(const SweepArgs<Real> &a, int mode, LaunchCfg &cfg, cud
 
 #define PORTA_INST(R, N)                                                                           \
     template int sweep_smem_bytes<R, N>(int, int, int, int);                                            \
-    template cudaError_t max_active_clusters<R, N>(int, int, int, int *);                          \
+    template cudaError_t max_active_clusters<R, N>(int, int, int, int *, bool);                    \
     template cudaError_t launch_sweep<R, N>(const SweepArgs<R> &, int, LaunchCfg &, cudaStream_t);
 PORTA_INST(float, 1)
 PORTA_INST(float, 4)
