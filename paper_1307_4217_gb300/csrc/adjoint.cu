@@ -134,31 +134,32 @@ __device__ __forceinline__ void node_param_grad(const Node<Real, NS> &n, Real x,
 
 // the same in the unknowns: dL/dchi at fixed rho, dL/dB (3) and dL/drho (up to 6)
 // added to o[10] (eps_i = chi phi S_i(rho), eps_V = S00 eta_V, S_i = sum_c T_ic rho_c
-// with the real multipole layout's factor 2 for Q != 0)
+// with the real multipole layout's factor 2 for Q != 0); o in the sweep's precision
+// over one frequency group (the per-cluster sums across items are FP64)
 template <typename Real, int NS>
 __device__ __forceinline__ void node_param_grad_rho(const Node<Real, NS> &n, const RayDev<Real> &ray, Real bfac, Real x,
-                                                    const Real *t, double *o)
+                                                    const Real *t, Real *o)
 {
     const Real xs = x - n.s;
     const Real ph = profile_shape(xs);
     if constexpr (NS == 1) {
-        o[0] += (double)(ph * (t[0] + n.S * t[1]));
-        o[4] += (double)(n.chi * ph * t[1]);
+        o[0] += ph * (t[0] + n.S * t[1]);
+        o[4] += n.chi * ph * t[1];
     } else {
         const Real bxs = n.b * xs;
-        o[0] += (double)(ph * (t[0] + bxs * t[1] + n.SI * t[2] + n.SQ * t[3] + n.SU * t[4] + bxs * n.S00 * t[5]));
+        o[0] += ph * (t[0] + bxs * t[1] + n.SI * t[2] + n.SQ * t[3] + n.SU * t[4] + bxs * n.S00 * t[5]);
         const Real gb = bfac * xs * ph * n.chi * (t[1] + n.S00 * t[5]);
-        o[1] += (double)(gb * ray.ox);
-        o[2] += (double)(gb * ray.oy);
-        o[3] += (double)(gb * ray.oz);
+        o[1] += gb * ray.ox;
+        o[2] += gb * ray.oy;
+        o[3] += gb * ray.oz;
         const Real cp = n.chi * ph;
         const Real gS[3] = {cp * t[2], cp * t[3], cp * t[4]};
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
             const Real f2 = c >= 2 ? Real(2) : Real(1);
-            o[4 + c] += (double)(f2 * (ray.t[c] * gS[0] + ray.t[6 + c] * gS[1] + ray.t[12 + c] * gS[2]));
+            o[4 + c] += f2 * (ray.t[c] * gS[0] + ray.t[6 + c] * gS[1] + ray.t[12 + c] * gS[2]);
         }
-        o[4] += (double)(cp * bxs * t[5]);
+        o[4] += cp * bxs * t[5];
     }
 }
 
@@ -237,7 +238,7 @@ __device__ __forceinline__ void adjoint_item(const SweepArgs<Real> &a, cg::clust
             const Real *ph = last ? gP_next : gP;
             const int lh = last ? 0 : (l + 1) * nx;
             Real gchi = 0, ge = 0, gb = 0;
-            double o[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+            Real o[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
             for (int f = 0; f < nf; ++f) {
                 Real t[NM];
 #pragma unroll
@@ -267,7 +268,7 @@ __device__ __forceinline__ void adjoint_item(const SweepArgs<Real> &a, cg::clust
             } else {
                 // this cluster's accumulators; a node is finalized by one thread per item
 #pragma unroll
-                for (int k = 0; k < 10; ++k) acc[k * a.nvox + v] += o[k];
+                for (int k = 0; k < 10; ++k) acc[k * a.nvox + v] += (double)o[k];
             }
         }
     };
