@@ -469,6 +469,16 @@ int porta_ml_create(const porta_grid *g, const porta_ml_atom *a, const porta_qua
 int porta_ml_set_atmosphere(porta_ctx *c, const double *chi, const double *kT, const double *vel, const double *bx,
                             const double *by, const double *bz, int where);
 
+/* Emergent Stokes profiles of line `line` (Sec. 1: the emergent profiles of
+   any line and line of sight once the unknowns are known) for ndir
+   outgoing directions (mu in (0, 1], azimuth chi; host arrays): the
+   emergent-mode formal solution of the line with its opacity, emissivity,
+   dichroism and Zeeman term from the current unknowns. out:
+   ndir*n_nu*ny*nx*NS doubles (NS = 4 for the polarized atom, 1 otherwise),
+   [dir][nu][y][x][stokes], host or device per `where`. Synchronous. */
+int porta_ml_emergent_stokes(porta_ctx *c, int line, int ndir, const double *mu, const double *chi, double *out,
+                             int where);
+
 /* Number of real unknowns per voxel (nlevel for the unpolarized atom). */
 int porta_ml_unknowns(const porta_ctx *c, int *nunk);
 

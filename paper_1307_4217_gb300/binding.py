@@ -93,6 +93,7 @@ _SIGS = {
     "porta_ml_create": (_I, [_P, _P, _P, _P, _P]),
     "porta_ml_set_atmosphere": (_I, [_P, _P, _P, _P, _P, _P, _P, _I]),
     "porta_ml_unknowns": (_I, [_P, _P]),
+    "porta_ml_emergent_stokes": (_I, [_P, _I, _I, _P, _P, _P, _I]),
     "porta_ml_set_unknowns": (_I, [_P, _P, _I]),
     "porta_ml_get_unknowns": (_I, [_P, _P, _I]),
     "porta_ml_set_pops": (_I, [_P, _P, _I]),
@@ -341,6 +342,10 @@ def porta_ml_create(grid, atom, quad, opts):
 
 def porta_ml_set_atmosphere(h, chi_ptr, kt_ptr, vel_ptr, bx_ptr, by_ptr, bz_ptr, where):
     return lib().porta_ml_set_atmosphere(h, chi_ptr, kt_ptr, vel_ptr, bx_ptr, by_ptr, bz_ptr, where)
+
+
+def porta_ml_emergent_stokes(h, line, ndir, mu_ptr, chi_ptr, out_ptr, where):
+    return lib().porta_ml_emergent_stokes(h, line, ndir, mu_ptr, chi_ptr, out_ptr, where)
 
 
 def porta_ml_unknowns(h):
@@ -708,6 +713,17 @@ class MlContext(Context):
                 raise TypeError("atmosphere arrays must all be host or all device")
             ptrs.append(p)
         self._check(porta_ml_set_atmosphere(self.h, *ptrs, where))
+
+    def emergent_stokes(self, line, mu, chi, out=None):
+        """emergent Stokes profiles of line `line` along (mu, chi): [dir][nu][y][x][stokes]"""
+        mu = np.ascontiguousarray(mu, dtype=np.float64)
+        chi = np.ascontiguousarray(chi, dtype=np.float64)
+        nz, ny, nx = self.grid_shape
+        if out is None:
+            out = np.zeros((len(mu), self.nnu, ny, nx, self.ns))
+        p, w, keep = _ptr_where(out)
+        self._check(porta_ml_emergent_stokes(self.h, line, len(mu), mu.ctypes.data, chi.ctypes.data, p, w))
+        return out
 
     def set_unknowns(self, x):
         """the vector of unknowns [voxel][nunk] (populations, or the real multipoles

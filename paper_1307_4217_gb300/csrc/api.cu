@@ -621,7 +621,7 @@ int emergent_shape(porta_ctx *c, SweepArgs<Real> &a, int ndir, LaunchCfg &cfg)
 }
 
 template <typename Real>
-int emergent_t(porta_ctx *c, int ndir, const double *mu, const double *chi, double *dout)
+int emergent_t(porta_ctx *c, int ndir, const double *mu, const double *chi, double *dout, int box = 0)
 {
     std::vector<PlaneGeom<Real>> geom((size_t)ndir * c->nz);
     std::vector<RayDev<Real>> rays(ndir);
@@ -631,15 +631,27 @@ int emergent_t(porta_ctx *c, int ndir, const double *mu, const double *chi, doub
     }
     PlaneGeom<Real> *dg = nullptr;
     RayDev<Real> *dr = nullptr;
+    BoxDev *dbox = nullptr;
     CK(dalloc(&dg, geom.size()));
     cudaError_t e2 = dalloc(&dr, rays.size());
-    if (e2 != cudaSuccess) { cudaFree(dg); return fail(c, PORTA_ENOMEM, "emergent: device allocation"); }
+    if (e2 == cudaSuccess) e2 = cudaMalloc(&dbox, sizeof(BoxDev));
+    if (e2 != cudaSuccess) {
+        cudaFree(dg);
+        if (dr) cudaFree(dr);
+        return fail(c, PORTA_ENOMEM, "emergent: device allocation");
+    }
     int rc = PORTA_OK;
     do {
+        // the box of this call (a line of a multilevel context shares the grid): its
+        // voxels, with the per-direction geometry of this call (geometry offset 0)
+        BoxDev hb = c->boxes[box];
+        hb.geom0 = 0;
         cudaError_t e = cudaMemcpyAsync(dg, geom.data(), geom.size() * sizeof(geom[0]), cudaMemcpyHostToDevice, c->stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(dr, rays.data(), rays.size() * sizeof(rays[0]), cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dbox, &hb, sizeof(hb), cudaMemcpyHostToDevice, c->stream);
         if (e != cudaSuccess) { rc = fail(c, PORTA_ECUDA, cudaGetErrorString(e)); break; }
         SweepArgs<Real> a = base_args<Real>(c);
+        a.boxes = dbox;
         a.geom = dg;
         a.rays = dr;
         a.out = dout;
@@ -655,6 +667,7 @@ int emergent_t(porta_ctx *c, int ndir, const double *mu, const double *chi, doub
     cudaStreamSynchronize(c->stream);
     cudaFree(dg);
     cudaFree(dr);
+    cudaFree(dbox);
     return rc;
 }
 
@@ -2593,6 +2606,34 @@ int porta_ml_get_pops(porta_ctx *c, double *pops, int where)
                        where == PORTA_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
     if (where == PORTA_HOST) CK(cudaStreamSynchronize(c->stream));
     return PORTA_OK;
+}
+
+int porta_ml_emergent_stokes(porta_ctx *c, int line, int ndir, const double *mu, const double *chi, double *out,
+                             int where)
+{
+    if (!c) return PORTA_EINVAL;
+    MlState *m = c->ml;
+    if (!m) return fail(c, PORTA_EINVAL, "ml_emergent_stokes: not a multilevel context");
+    if (line < 0 || line >= m->mc.nline || ndir < 1 || !mu || !chi || !out ||
+        (where != PORTA_HOST && where != PORTA_DEVICE))
+        return fail(c, PORTA_EINVAL, "ml_emergent_stokes: bad argument");
+    for (int d = 0; d < ndir; ++d)
+        if (!(mu[d] > 0.0 && mu[d] <= 1.0) || !std::isfinite(chi[d]))
+            return fail(c, PORTA_EINVAL, "ml_emergent_stokes: mu must lie in (0, 1], chi finite");
+    if (!m->have_atm || !m->have_pops) return fail(c, PORTA_ESTATE, "ml_emergent_stokes: atmosphere or populations not set");
+    const long long n = (long long)ndir * c->n_nu * c->nx * c->ny * c->ns;
+    double *dout = out;
+    if (where == PORTA_HOST) CK(dalloc(&dout, n));
+    int rc = c->precision == PORTA_FP32 ? emergent_t<float>(c, ndir, mu, chi, dout, line)
+                                        : emergent_t<double>(c, ndir, mu, chi, dout, line);
+    if (where == PORTA_HOST) {
+        if (rc == PORTA_OK) {
+            cudaError_t e = cudaMemcpy(out, dout, n * sizeof(double), cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) rc = fail(c, PORTA_ECUDA, cudaGetErrorString(e));
+        }
+        cudaFree(dout);
+    }
+    return rc;
 }
 
 int porta_ml_unknowns(const porta_ctx *c, int *nunk)

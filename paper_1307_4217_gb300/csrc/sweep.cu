@@ -515,8 +515,10 @@ __global__ void __launch_bounds__(512, 1) sweep_kernel(const SweepArgs<Real> a)
 template <typename Real, int NS>
 static void *kernel_ptr(int mode, bool dich = false)
 {
-    // the dichroism variant (polarized lines of the multilevel atom) exists for the J^K_Q sweep
-    if (NS == 4 && dich && mode == MODE_JKQ) return (void *)sweep_kernel<Real, NS, MODE_JKQ, NS == 4>;
+    // the dichroism variant (polarized lines of the multilevel atom)
+    if (NS == 4 && dich)
+        return mode == MODE_JKQ ? (void *)sweep_kernel<Real, NS, MODE_JKQ, NS == 4>
+                                : (void *)sweep_kernel<Real, NS, MODE_EMERGENT, NS == 4>;
     return mode == MODE_JKQ ? (void *)sweep_kernel<Real, NS, MODE_JKQ> : (void *)sweep_kernel<Real, NS, MODE_EMERGENT>;
 }
 
@@ -552,7 +554,7 @@ cudaError_t max_active_clusters(int cluster, int smem, int threads, int *out, bo
 template <typename Real, int NS>
 cudaError_t launch_sweep(const SweepArgs<Real> &a, int mode, LaunchCfg &cfg, cudaStream_t st)
 {
-    const bool dich = NS == 4 && a.dich != nullptr && mode == MODE_JKQ;
+    const bool dich = NS == 4 && a.dich != nullptr;
     cudaError_t e = prepare<Real, NS>(mode, cfg.cluster, cfg.smem, dich);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t lc = {};
@@ -572,7 +574,9 @@ cudaError_t launch_sweep(const SweepArgs<Real> &a, int mode, LaunchCfg &cfg, cud
         at[1].val.priority = cfg.priority;
         lc.numAttrs = 2;
     }
-    if (dich) return cudaLaunchKernelEx(&lc, sweep_kernel<Real, NS, MODE_JKQ, NS == 4>, a);
+    if (dich)
+        return mode == MODE_JKQ ? cudaLaunchKernelEx(&lc, sweep_kernel<Real, NS, MODE_JKQ, NS == 4>, a)
+                                : cudaLaunchKernelEx(&lc, sweep_kernel<Real, NS, MODE_EMERGENT, NS == 4>, a);
     if (mode == MODE_JKQ)
         return cudaLaunchKernelEx(&lc, sweep_kernel<Real, NS, MODE_JKQ>, a);
     return cudaLaunchKernelEx(&lc, sweep_kernel<Real, NS, MODE_EMERGENT>, a);

@@ -179,3 +179,16 @@ def test_multigrid_reaches_the_jacobi_fixed_point():
     b = make(a.get_pops())
     # a Jacobi iteration leaves the multigrid solution in place
     assert b.ml_iterate(1) < 1e-9
+
+
+@pytest.mark.parametrize("prec", [P.PORTA_FP64, P.PORTA_FP32])
+def test_emergent_line_profiles_match_oracle(prec):
+    import oracle
+    atm, atom, pops = _case(seed=10)
+    ctx = _ctx(atm, atom, prec, pops)
+    mu, az = synth.emergent_directions()
+    S = ml.source_function(atom, pops)
+    for k in range(4):
+        got = ctx.emergent_stokes(k, mu, az)
+        want = oracle.emergent(ml.line_problem(atm, atom, pops, k, QUAD), S[..., k:k + 1], mu, az)
+        assert np.max(np.abs(got - want) / want) < (1e-10 if prec == P.PORTA_FP64 else 2e-5), k

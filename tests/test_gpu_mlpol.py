@@ -210,3 +210,24 @@ def test_multigrid_reaches_the_jacobi_fixed_point():
     assert ch < 1e-9
     b = make(a.get_unknowns())
     assert b.ml_iterate(1) < 1e-9
+
+
+@pytest.mark.parametrize("prec", [P.PORTA_FP64, P.PORTA_FP32])
+def test_emergent_line_profiles_match_oracle(prec):
+    """Emergent Stokes profiles of every line (with the dichroism and emissivity
+    of the current multipoles) against the oracle's emergent formal solution."""
+    import oracle
+    atm, atom, tab, x = _case(seed=9)
+    ctx = _ctx(atm, atom, prec, x)
+    mu, az = synth.emergent_directions()
+    src = mlpol.line_source_multipoles(tab, x)
+    for li in range(4):
+        got = ctx.emergent_stokes(li, mu, az)
+        want = oracle.emergent(mlpol.line_problem(atm, atom, tab, x, li, QUAD), src[..., li, :], mu, az)
+        I = want[..., :1]
+        if prec == P.PORTA_FP64:
+            assert np.max(np.abs(got - want) / I) < 1e-10, li
+        else:
+            assert np.max(np.abs(got[..., 0] - want[..., 0]) / want[..., 0]) < 2e-5, li
+            assert np.max(np.abs(got[..., 1:] - want[..., 1:]) / I) < 2e-6, li
+        assert np.max(np.abs(want[..., 1:3]) / I) > 1e-5        # linear polarization present
