@@ -196,8 +196,8 @@ void launch_caps(const porta_ctx *c, int C, int &ring_plane, int &ipts_max)
     for (const BoxDev &b : c->boxes) {
         const int rmax = (b.ny + C - 1) / C;
         const int chunk = (rmax + 2) * b.nx;
-        // with dichroism the slots of a second ring ((eta_Q, eta_U) / eta_I per node) follow the node ring
-        const int dchunks = dich ? (chunk * 2 * (int)sizeof(Real) + 15) / 16 : 0;
+        // with dichroism the slots of a second ring (eta_U / eta_I per node) follow the node ring
+        const int dchunks = dich ? (chunk * (int)sizeof(Real) + 15) / 16 : 0;
         ring_plane = std::max(ring_plane, nch * chunk + dchunks);
         ipts_max = std::max(ipts_max, rmax * b.nx);
     }

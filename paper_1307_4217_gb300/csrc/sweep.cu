@@ -90,13 +90,14 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<Real> &a, cg::cluster
     constexpr int NCH = node_words<NS>() * (int)sizeof(Real) / 16;
     const int chunk = (rmax + 2) * nx;              // ring chunk-plane stride (16-byte chunks)
     const int plane = NCH * chunk;                  // ring plane stride
-    // dichroism (polarized lines whose levels carry alignment): eta_Q / eta_I and
-    // eta_U / eta_I per node in a second 3-slot ring after the node ring (the
-    // launch reserves it); the node's opacity, source terms and Zeeman factor are
-    // rescaled by eta_I / (chi phi) = 1 + d_I(Omega)
+    // dichroism (polarized lines whose levels carry alignment): the node's opacity,
+    // source terms and Zeeman factor are rescaled by eta_I / (chi phi) = 1 + d_I(Omega);
+    // eta_Q / eta_I takes the node's profile-normalization word (the normalization is
+    // then read from global memory at O) and eta_U / eta_I sits in a second 3-slot
+    // ring after the node ring (the launch reserves it)
     constexpr bool dich = NS == 4 && DI;
     Real *dring = reinterpret_cast<Real *>(ring + 3 * plane);
-    const int dstride = (chunk * 2 * (int)sizeof(Real) + 15) / 16 * 16 / (int)sizeof(Real);
+    const int dstride = (chunk * (int)sizeof(Real) + 15) / 16 * 16 / (int)sizeof(Real);
     const int ipts = rmax * nx;                     // points per Stokes plane
     const int ichunk = ipts;                        // Stokes chunk-plane stride (16-byte chunks)
     const int iplane = NS * ipts;                   // Reals per (buf, f) Stokes plane
@@ -143,8 +144,8 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<Real> &a, cg::cluster
                     n.SQ *= inv;
                     n.SU *= inv;
                     n.b *= inv;
-                    dring[(q % 3) * dstride + 2 * idx] = dd[1] * inv;
-                    dring[(q % 3) * dstride + 2 * idx + 1] = dd[2] * inv;
+                    n.invn = dd[1] * inv;
+                    dring[(q % 3) * dstride + idx] = dd[2] * inv;
                 }
             }
             ring_store<Real, NS>(ring, plane, chunk, q % 3, idx, n);
@@ -189,6 +190,9 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<Real> &a, cg::cluster
             const long long vloc = ((long long)gq.kz * ny + pj) * nx + pi;
             const long long v = B.vox0 + vloc;
             const Node<Real, NS> nO = ring_load<Real, NS>(ring, plane, chunk, sO, (l + 1) * nx + c);
+            // profile normalization at O (in the ring, except for the dichroism variant)
+            Real invnO = nO.invn;
+            if constexpr (dich) invnO = jmode ? a.invn[(long long)m * a.nvox + v] : Real(1);
 #pragma unroll
             for (int s = 0; s < NA; ++s) acc[s] = Real(0);
 
@@ -209,7 +213,7 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<Real> &a, cg::cluster
                         }
                     }
                     if constexpr (MODE == MODE_JKQ) {
-                        const Real wt = a.wf[j] * profile_shape(a.xf[j] - nO.s) * nO.invn;
+                        const Real wt = a.wf[j] * profile_shape(a.xf[j] - nO.s) * invnO;
                         acc[0] += wt * I0[0];
                         if (a.probe_ray == m) {
 #pragma unroll
@@ -243,12 +247,11 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<Real> &a, cg::cluster
                     const int ix[4] = {(l + 1) * nx + c, (l + 1) * nx + c1, (l + 2) * nx + c, (l + 2) * nx + c1};
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
-                        mdq[k] = dm[2 * ix[k]];
-                        mdu[k] = dm[2 * ix[k] + 1];
+                        mdq[k] = ring_load<Real, NS>(ring, plane, chunk, sM, ix[k]).invn;
+                        mdu[k] = dm[ix[k]];
                     }
-                    const Real *dO = dring + sO * dstride;
-                    odq = dO[2 * ((l + 1) * nx + c)];
-                    odu = dO[2 * ((l + 1) * nx + c) + 1];
+                    odq = nO.invn;
+                    odu = dring[sO * dstride + (l + 1) * nx + c];
                 }
                 const Real wI[4] = {mx0 * my0, mx1 * my0, mx0 * my1, mx1 * my1};
                 const bool last_row = (l + 1 == R);
@@ -394,7 +397,7 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<Real> &a, cg::cluster
                     // a8: Lambda* (Eq. 13; w_O + w_C/2 on the last plane) and accumulation
                     if constexpr (MODE == MODE_JKQ) {
                         const Real ls = co.wo + (has_p ? co.wc : Real(0.5) * co.wc);
-                        const Real wt = a.wf[j] * phO * nO.invn;
+                        const Real wt = a.wf[j] * phO * invnO;
                         if constexpr (NS == 1) {
                             acc[0] += wt * IO[0];
                             acc[1] += wt * ls;
