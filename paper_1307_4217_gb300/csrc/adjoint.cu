@@ -52,7 +52,8 @@ __host__ __device__ constexpr int adj_np() { return NS + 1; }
 
 // bytes before the tape tile (16-byte aligned), and the whole shared memory:
 // ring, gI, gM, gP, T (per point and frequency), then the staged tape rows
-// of the upwind plane (tile_pts = (rows + 1) x nx points per frequency)
+// of the upwind plane (tile_pts = (rows + 1) x nx points per frequency) and
+// the reduced frequencies and quadrature weights of the group (2 F)
 template <typename Real, int NS>
 __host__ __device__ constexpr int adjoint_tile_offset(int ring_plane, int ipts, int F)
 {
@@ -63,7 +64,7 @@ __host__ __device__ constexpr int adjoint_tile_offset(int ring_plane, int ipts, 
 template <typename Real, int NS>
 int adjoint_smem_bytes(int ring_plane, int ipts, int tile_pts, int F)
 {
-    return adjoint_tile_offset<Real, NS>(ring_plane, ipts, F) + F * tile_pts * NS * (int)sizeof(Real);
+    return adjoint_tile_offset<Real, NS>(ring_plane, ipts, F) + (F * tile_pts * NS + 2 * F) * (int)sizeof(Real);
 }
 
 // asynchronous global -> shared copy of one Stokes vector (cp.async, 4/8/16 bytes per instruction)
@@ -195,6 +196,8 @@ __device__ __forceinline__ void adjoint_item(const SweepArgs<Real> &a, cg::clust
     const int chunk = (rmax + 2) * nx;
     const int plane = NCH * chunk;
     const int npts = R * nx;
+    const int tile_pts = (rmax + 1) * nx;               // staged tape points per frequency
+    Real *xsh = tt + (long long)F * tile_pts * NS;      // x_j and w_j of the group
     const Real *tape = a.store + (long long)d * a.nnu * a.nvox * NS;
     Real *gout_part = FORM == 0 ? a.gpart + (long long)item * 3 * a.nvox : nullptr;
     double *acc = FORM != 0 ? a.gacc + (long long)cid * 10 * a.nvox : nullptr;
@@ -206,32 +209,43 @@ __device__ __forceinline__ void adjoint_item(const SweepArgs<Real> &a, cg::clust
     auto xP = [&](int f, int k, int p) { return (f * NP + k) * ipts + p; };
     auto xT = [&](int par, int f, int k, int p) { return ((par * F + f) * NM + k) * ipts + p; };
 
+    // thread -> (row, column) of its first point, and the stride of the point
+    // loops in rows and columns (no integer division inside the loops)
+    const int tl0 = tid / nx, tc0 = tid - tl0 * nx;
+    const int dl = nt / nx, dc = nt - dl * nx;
+    auto step = [&](int &l, int &c) {
+        c += dc;
+        l += dl;
+        if (c >= nx) { c -= nx; ++l; }
+    };
     auto fill = [&](int q) {
         const PlaneGeom<Real> gq = G[q];
         const int nn = (R + 2) * nx;
+        int lr = tl0, c = tc0;                               // lr = ring row (local row + 1)
         for (int idx = tid; idx < nn; idx += nt) {
-            const int lr = idx / nx, c = idx - lr * nx;
             int pi = c + gq.ax;
             pi -= pi >= nx ? nx : 0;
-            int pj = (row0 + lr - 1 + gq.ay) % ny;
+            int pj = row0 + lr - 1 + gq.ay;                  // in [-1, 2 ny)
             pj += pj < 0 ? ny : 0;
+            pj -= pj >= ny ? ny : 0;
             const long long v = B.vox0 + ((long long)gq.kz * ny + pj) * nx + pi;
             ring_store<Real, NS>(ring, plane, chunk, q % 3, idx, make_node<Real, NS>(a, ray, v, mglob, FORM == 2));
+            step(lr, c);
         }
     };
-    // physical voxel of sheared node (c, local row l) of plane q
+    // physical voxel of sheared node (c, local row l) of plane q, l in [0, R]
     auto voxel = [&](const PlaneGeom<Real> &gq, int c, int l) {
         int pi = c + gq.ax;
         pi -= pi >= nx ? nx : 0;
-        const int pj = (row0 + l + gq.ay) % ny;
+        int pj = row0 + l + gq.ay;                           // in [0, 2 ny)
+        pj -= pj >= ny ? ny : 0;
         return ((long long)gq.kz * ny + pj) * nx + pi;
     };
     // parameter gradients of the nodes of plane pq (ring slot `slot`) from the
     // adjoint totals T[par] plus, with_p, the P gathers of plane pq-1
-    auto finalize = [&](int pq, int slot, int par, bool with_p, const Real *wP) {
-        const PlaneGeom<Real> gq = G[pq];
-        for (int p = tid; p < npts; p += nt) {
-            const int l = p / nx, c = p - l * nx;
+    auto finalize_pt = [&](const PlaneGeom<Real> &gq, int slot, int par, bool with_p, const Real *wP, int p, int l,
+                           int c) {
+        {
             const int c1 = c + 1 == nx ? 0 : c + 1;
             const Node<Real, NS> n = ring_load<Real, NS>(ring, plane, chunk, slot, (l + 1) * nx + c);
             const bool last = l + 1 == R;
@@ -256,9 +270,9 @@ __device__ __forceinline__ void adjoint_item(const SweepArgs<Real> &a, cg::clust
                     for (int s = 0; s < NS; ++s) t[NM - NS + s] += gp[1 + s];
                 }
                 if constexpr (FORM == 0)
-                    node_param_grad<Real, NS>(n, a.xf[j0 + f], t, gchi, ge, gb);
+                    node_param_grad<Real, NS>(n, xsh[f], t, gchi, ge, gb);
                 else
-                    node_param_grad_rho<Real, NS>(n, ray, a.bfac, a.xf[j0 + f], t, o);
+                    node_param_grad_rho<Real, NS>(n, ray, a.bfac, xsh[f], t, o);
             }
             const long long v = B.vox0 + voxel(gq, c, l);
             if constexpr (FORM == 0) {
@@ -272,17 +286,27 @@ __device__ __forceinline__ void adjoint_item(const SweepArgs<Real> &a, cg::clust
             }
         }
     };
+    auto finalize = [&](int pq, int slot, int par, bool with_p, const Real *wP) {
+        const PlaneGeom<Real> gq = G[pq];
+        int l = tl0, c = tc0;
+        for (int p = tid; p < npts; p += nt) {
+            finalize_pt(gq, slot, par, with_p, wP, p, l, c);
+            step(l, c);
+        }
+    };
 
     // tape rows 0..R of the strip (sheared frame) of plane qq, all frequencies of the group
-    const int tile_pts = (rmax + 1) * nx;
     auto stage = [&](int qq) {
         const PlaneGeom<Real> gg = G[qq];
         const int per = (R + 1) * nx;
-        for (int idx = tid; idx < per * nf; idx += nt) {
-            const int f = idx / per, r = idx - f * per;
-            const int lr = r / nx, c = r - lr * nx;
-            const long long v = B.vox0 + voxel(gg, c, lr);
-            copy_stokes_async<Real, NS>(tt + ((long long)f * tile_pts + r) * NS, tape + ((long long)(j0 + f) * a.nvox + v) * NS);
+        const Real *src0 = tape + (long long)j0 * a.nvox * NS;
+        int lr = tl0, c = tc0;
+        for (int r = tid; r < per; r += nt) {
+            const Real *src = src0 + (B.vox0 + voxel(gg, c, lr)) * NS;
+            Real *dst = tt + (long long)r * NS;
+            for (int f = 0; f < nf; ++f)
+                copy_stokes_async<Real, NS>(dst + (long long)f * tile_pts * NS, src + (long long)f * a.nvox * NS);
+            step(lr, c);
         }
         cp_async_commit();
     };
@@ -291,6 +315,10 @@ __device__ __forceinline__ void adjoint_item(const SweepArgs<Real> &a, cg::clust
     fill(nz - 2);
     stage(nz - 2);
     cp_async_wait_all();
+    for (int f = tid; f < nf; f += nt) {
+        xsh[f] = a.xf[j0 + f];
+        xsh[F + f] = FORM == 2 ? (Real)a.wf[j0 + f] : Real(0);
+    }
     for (int p = tid; p < npts; p += nt)
         for (int f = 0; f < nf; ++f)
 #pragma unroll
@@ -314,8 +342,9 @@ __device__ __forceinline__ void adjoint_item(const SweepArgs<Real> &a, cg::clust
         const Real dsM = gq.ds, dsP = has_p ? gp.ds : Real(0);
 
         // ---- phase 1: local reverse step at every point of the strip ----
-        for (int p = tid; p < npts; p += nt) {
-            const int l = p / nx, c = p - l * nx;
+        int pl = tl0, pc = tc0;
+        for (int p = tid; p < npts; p += nt, step(pl, pc)) {
+            const int l = pl, c = pc;
             const int c1 = c + 1 == nx ? 0 : c + 1;
             const int cm = c == 0 ? nx - 1 : c - 1;
             const Node<Real, NS> nO = ring_load<Real, NS>(ring, plane, chunk, sO, (l + 1) * nx + c);
@@ -358,7 +387,7 @@ __device__ __forceinline__ void adjoint_item(const SweepArgs<Real> &a, cg::clust
 
             for (int f = 0; f < nf; ++f) {
                 const int j = j0 + f;
-                const Real x = a.xf[j];
+                const Real x = xsh[f];
                 Real lam[NS];
                 if (q == nz - 1) {
                     if constexpr (FORM == 2) {
@@ -465,7 +494,7 @@ __device__ __forceinline__ void adjoint_item(const SweepArgs<Real> &a, cg::clust
                 // form 2: the J^K_Q and Lambda-bar* sums weigh I_O and Lambda*_O by w_m w_j phi_O / N
                 Real lw = 0;
                 if constexpr (FORM == 2) {
-                    const Real wt = wray * a.wf[j] * phO * nO.invn;
+                    const Real wt = wray * xsh[F + f] * phO * nO.invn;
                     lam[0] += wt * gdir[0];
                     if constexpr (NS == 4) {
                         lam[1] += wt * gdir[1];
@@ -558,26 +587,41 @@ __device__ __forceinline__ void adjoint_item(const SweepArgs<Real> &a, cg::clust
                 for (int k = 0; k < NM; ++k) T[xT(par, f, k, p)] += gout_o[k];
             }
         }
+        // phase 1 -> phase 2: the strip's gI, gM, gP are published to the
+        // neighbours (release); the rows that need none of the neighbours'
+        // values are completed while the barrier is pending
         __syncthreads();
-        cluster.sync();
+        cluster_arrive_release();
 
         // ---- phase 2: complete node adjoints ----
-        // (a) plane q+1 is complete once the P gathers of plane q are added
-        if (has_p) finalize(q + 1, sP, opar, true, wP);
+        // (a) plane q+1 is complete once the P gathers of plane q are added;
+        //     its last row gathers row 0 of the next strip
         // (b) the M gathers of plane q start the totals of plane q-1 (same
-        //     buffer and element as (a), read there before written here)
-        for (int p = tid; p < npts; p += nt) {
-            const int l = p / nx, c = p - l * nx;
-            const int cm = c == 0 ? nx - 1 : c - 1;
-            const bool first = l == 0;
-            const Real *mlo = first ? gM_prev : gM;
-            const int llo = first ? prev_last * nx : (l - 1) * nx;
-            for (int f = 0; f < nf; ++f)
+        //     buffer and element as (a), read there before written here by the
+        //     same thread); row 0 gathers the last row of the previous strip,
+        //     and the last row waits for its own (a)
+        const PlaneGeom<Real> gq1 = has_p ? G[q + 1] : gq;
+        auto phase2 = [&](bool remote) {
+            int l = tl0, c = tc0;
+            for (int p = tid; p < npts; p += nt) {
+                const bool firstrow = l == 0, lastrow = l + 1 == R;
+                if (has_p && lastrow == remote) finalize_pt(gq1, sP, opar, true, wP, p, l, c);
+                if ((firstrow || lastrow) == remote) {
+                    const int cm = c == 0 ? nx - 1 : c - 1;
+                    const Real *mlo = firstrow ? gM_prev : gM;
+                    const int llo = firstrow ? prev_last * nx : (l - 1) * nx;
+                    for (int f = 0; f < nf; ++f)
 #pragma unroll
-                for (int k = 0; k < NM; ++k)
-                    T[xT(opar, f, k, p)] = wM[0] * gM[xM(f, k, l * nx + c)] + wM[1] * gM[xM(f, k, l * nx + cm)] +
-                                           wM[2] * mlo[xM(f, k, llo + c)] + wM[3] * mlo[xM(f, k, llo + cm)];
-        }
+                        for (int k = 0; k < NM; ++k)
+                            T[xT(opar, f, k, p)] = wM[0] * gM[xM(f, k, l * nx + c)] + wM[1] * gM[xM(f, k, l * nx + cm)] +
+                                                   wM[2] * mlo[xM(f, k, llo + c)] + wM[3] * mlo[xM(f, k, llo + cm)];
+                }
+                step(l, c);
+            }
+        };
+        phase2(false);
+        cluster_wait_acquire();
+        phase2(true);
         // (c) the boundary plane has no O or P terms: complete now
         if (q == 1) finalize(0, sM, opar, false, wP);
         // end of step: the DSMEM gathers of phase 2 have been consumed, so this
