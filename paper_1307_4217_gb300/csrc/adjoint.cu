@@ -54,11 +54,16 @@ __host__ __device__ constexpr int adj_np() { return NS + 1; }
 // ring, gI, gM, gP, T (per point and frequency), then the staged tape rows
 // of the upwind plane (tile_pts = (rows + 1) x nx points per frequency) and
 // the reduced frequencies and quadrature weights of the group (2 F)
+// points per adjoint plane: the strip's points rounded up to a multiple of 4,
+// so that every vector plane below starts on a 16-byte boundary
+__host__ __device__ constexpr int adj_ipa(int ipts) { return (ipts + 3) / 4 * 4; }
+
 template <typename Real, int NS>
 __host__ __device__ constexpr int adjoint_tile_offset(int ring_plane, int ipts, int F)
 {
-    return (3 * ring_plane * 16 + F * ipts * (2 * NS + adj_nm<NS>() + adj_np<NS>() + 2 * adj_nm<NS>()) * (int)sizeof(Real) +
-            15) / 16 * 16;
+    return (3 * ring_plane * 16 +
+            F * adj_ipa(ipts) * (2 * NS + adj_nm<NS>() + adj_np<NS>() + 2 * adj_nm<NS>()) * (int)sizeof(Real) + 15) /
+           16 * 16;
 }
 
 template <typename Real, int NS>
@@ -105,6 +110,56 @@ __device__ __forceinline__ void load_stokes(const Real *p, Real v[NS])
         v[0] = p[0];
     }
 }
+
+// W Reals per point in shared memory: planes of 16-byte chunks ([chunk][p],
+// consecutive points in consecutive 16-byte words) for the first
+// W / (16 / sizeof(Real)) chunks and one narrower plane for the Reals left
+// over; n = points per plane (a multiple of 4), so every plane is 16-byte aligned
+template <typename Real, int W>
+struct SVec {
+    static constexpr int PER = 16 / (int)sizeof(Real);
+    static constexpr int NC = W / PER, REM = W - NC * PER;
+    static_assert(REM <= 2, "at most two Reals in the narrow plane");
+    using V = typename V16<Real>::T;
+    __device__ static __forceinline__ void load(const Real *b, int n, int p, Real v[W])
+    {
+#pragma unroll
+        for (int h = 0; h < NC; ++h) {
+            const V x = reinterpret_cast<const V *>(b + h * PER * n)[p];
+            if constexpr (PER == 4) {
+                v[4 * h] = x.x; v[4 * h + 1] = x.y; v[4 * h + 2] = x.z; v[4 * h + 3] = x.w;
+            } else {
+                v[2 * h] = x.x; v[2 * h + 1] = x.y;
+            }
+        }
+        const Real *r = b + NC * PER * n;
+        if constexpr (REM == 2) {
+            const R2<Real> x = reinterpret_cast<const R2<Real> *>(r)[p];
+            v[NC * PER] = x.x; v[NC * PER + 1] = x.y;
+        } else if constexpr (REM == 1) {
+            v[NC * PER] = r[p];
+        }
+    }
+    __device__ static __forceinline__ void store(Real *b, int n, int p, const Real v[W])
+    {
+#pragma unroll
+        for (int h = 0; h < NC; ++h) {
+            V x;
+            if constexpr (PER == 4) {
+                x.x = v[4 * h]; x.y = v[4 * h + 1]; x.z = v[4 * h + 2]; x.w = v[4 * h + 3];
+            } else {
+                x.x = v[2 * h]; x.y = v[2 * h + 1];
+            }
+            reinterpret_cast<V *>(b + h * PER * n)[p] = x;
+        }
+        Real *r = b + NC * PER * n;
+        if constexpr (REM == 2) {
+            reinterpret_cast<R2<Real> *>(r)[p] = R2<Real>{v[NC * PER], v[NC * PER + 1]};
+        } else if constexpr (REM == 1) {
+            r[p] = v[NC * PER];
+        }
+    }
+};
 
 // CTA owning sheared row r when CTA k owns rows floor(k ny / C) .. floor((k+1) ny / C) - 1
 __device__ __forceinline__ int row_owner(int r, int ny, int C)
@@ -183,7 +238,7 @@ __device__ __forceinline__ void adjoint_item(const SweepArgs<Real> &a, cg::clust
     const int prev_row = (row0 + ny - 1) % ny;
     const int prev_owner = row_owner(prev_row, ny, C);
     const int prev_last = prev_row - row_start(prev_owner, ny, C);
-    const int ipts = a.ipts_max;
+    const int ipa = adj_ipa(a.ipts_max);                // points per adjoint plane
     const Real *gI_prev = cluster.map_shared_rank(gI, prev_owner);
     const Real *gM_prev = cluster.map_shared_rank(gM, prev_owner);
     const Real *gP_next = cluster.map_shared_rank(gP, next_owner);
@@ -203,11 +258,14 @@ __device__ __forceinline__ void adjoint_item(const SweepArgs<Real> &a, cg::clust
     double *acc = FORM != 0 ? a.gacc + (long long)cid * 10 * a.nvox : nullptr;
     const int mglob = a.ray0 + d;                       // ray index for the J weights (form 2)
     const Real wray = FORM == 2 ? (Real)a.tw[19 * mglob] : Real(0);
-    // buffer offsets: gI[par][f][s][p], gM[f][k][p], gP[f][k][p], T[par][f][k][p]
-    auto xI = [&](int par, int f, int s, int p) { return ((par * F + f) * NS + s) * ipts + p; };
-    auto xM = [&](int f, int k, int p) { return (f * NM + k) * ipts + p; };
-    auto xP = [&](int f, int k, int p) { return (f * NP + k) * ipts + p; };
-    auto xT = [&](int par, int f, int k, int p) { return ((par * F + f) * NM + k) * ipts + p; };
+    // offsets of the vector planes (SVec): gI[par][f], gM[f], gP[f], T[par][f]
+    auto oI = [&](int par, int f) { return (par * F + f) * NS * ipa; };
+    auto oM = [&](int f) { return f * NM * ipa; };
+    auto oP = [&](int f) { return f * NP * ipa; };
+    auto oT = [&](int par, int f) { return (par * F + f) * NM * ipa; };
+    using VI = SVec<Real, NS>;
+    using VM = SVec<Real, NM>;
+    using VP = SVec<Real, NP>;
 
     // thread -> (row, column) of its first point, and the stride of the point
     // loops in rows and columns (no integer division inside the loops)
@@ -255,16 +313,17 @@ __device__ __forceinline__ void adjoint_item(const SweepArgs<Real> &a, cg::clust
             Real o[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
             for (int f = 0; f < nf; ++f) {
                 Real t[NM];
-#pragma unroll
-                for (int k = 0; k < NM; ++k) t[k] = T[xT(par, f, k, p)];
+                VM::load(T + oT(par, f), ipa, p, t);
                 if (with_p) {
                     // node (c, l) of plane pq is corner (c-1|c, l-1|l) of the points
                     // (c+1|c, l+1|l) of plane pq-1
-                    Real gp[NP];
+                    Real gp[NP], u0[NP], u1[NP], u2[NP], u3[NP];
+                    VP::load(ph + oP(f), ipa, lh + c1, u0);
+                    VP::load(ph + oP(f), ipa, lh + c, u1);
+                    VP::load(gP + oP(f), ipa, l * nx + c1, u2);
+                    VP::load(gP + oP(f), ipa, l * nx + c, u3);
 #pragma unroll
-                    for (int k = 0; k < NP; ++k)
-                        gp[k] = wP[0] * ph[xP(f, k, lh + c1)] + wP[1] * ph[xP(f, k, lh + c)] +
-                                wP[2] * gP[xP(f, k, l * nx + c1)] + wP[3] * gP[xP(f, k, l * nx + c)];
+                    for (int k = 0; k < NP; ++k) gp[k] = wP[0] * u0[k] + wP[1] * u1[k] + wP[2] * u2[k] + wP[3] * u3[k];
                     t[0] += gp[0];
 #pragma unroll
                     for (int s = 0; s < NS; ++s) t[NM - NS + s] += gp[1 + s];
@@ -320,9 +379,12 @@ __device__ __forceinline__ void adjoint_item(const SweepArgs<Real> &a, cg::clust
         xsh[F + f] = FORM == 2 ? (Real)a.wf[j0 + f] : Real(0);
     }
     for (int p = tid; p < npts; p += nt)
-        for (int f = 0; f < nf; ++f)
+        for (int f = 0; f < nf; ++f) {
+            Real z[NM];
 #pragma unroll
-            for (int k = 0; k < NM; ++k) T[xT((nz - 1) & 1, f, k, p)] = Real(0);
+            for (int k = 0; k < NM; ++k) z[k] = Real(0);
+            VM::store(T + oT((nz - 1) & 1, f), ipa, p, z);
+        }
     __syncthreads();
     cluster.sync();
 
@@ -399,10 +461,13 @@ __device__ __forceinline__ void adjoint_item(const SweepArgs<Real> &a, cg::clust
                         for (int s = 0; s < NS; ++s) lam[s] = (Real)go[s];
                     }
                 } else {
+                    Real u0[NS], u1[NS], u2[NS], u3[NS];
+                    VI::load(gI + oI(opar, f), ipa, l * nx + c, u0);
+                    VI::load(gI + oI(opar, f), ipa, l * nx + cm, u1);
+                    VI::load(glo + oI(opar, f), ipa, llo + c, u2);
+                    VI::load(glo + oI(opar, f), ipa, llo + cm, u3);
 #pragma unroll
-                    for (int s = 0; s < NS; ++s)
-                        lam[s] = wN[0] * gI[xI(opar, f, s, l * nx + c)] + wN[1] * gI[xI(opar, f, s, l * nx + cm)] +
-                                 wN[2] * glo[xI(opar, f, s, llo + c)] + wN[3] * glo[xI(opar, f, s, llo + cm)];
+                    for (int s = 0; s < NS; ++s) lam[s] = wN[0] * u0[s] + wN[1] * u1[s] + wN[2] * u2[s] + wN[3] * u3[s];
                 }
                 // ---- forward recomputation (the forward sweep's arithmetic) ----
                 // upwind Stokes vector from the staged tape rows l, l+1 of plane q-1
@@ -577,14 +642,16 @@ __device__ __forceinline__ void adjoint_item(const SweepArgs<Real> &a, cg::clust
                 gout_m[0] = g_etaM;
                 gout_o[0] = g_etaO;
                 gout_p[0] = g_etaP;
+                VI::store(gI + oI(par, f), ipa, p, gIM);
+                VM::store(gM + oM(f), ipa, p, gout_m);
+                VP::store(gP + oP(f), ipa, p, gout_p);
+                {
+                    Real t[NM];
+                    VM::load(T + oT(par, f), ipa, p, t);
 #pragma unroll
-                for (int s = 0; s < NS; ++s) gI[xI(par, f, s, p)] = gIM[s];
-#pragma unroll
-                for (int k = 0; k < NM; ++k) gM[xM(f, k, p)] = gout_m[k];
-#pragma unroll
-                for (int k = 0; k < NP; ++k) gP[xP(f, k, p)] = gout_p[k];
-#pragma unroll
-                for (int k = 0; k < NM; ++k) T[xT(par, f, k, p)] += gout_o[k];
+                    for (int k = 0; k < NM; ++k) t[k] += gout_o[k];
+                    VM::store(T + oT(par, f), ipa, p, t);
+                }
             }
         }
         // phase 1 -> phase 2: the strip's gI, gM, gP are published to the
@@ -610,11 +677,16 @@ __device__ __forceinline__ void adjoint_item(const SweepArgs<Real> &a, cg::clust
                     const int cm = c == 0 ? nx - 1 : c - 1;
                     const Real *mlo = firstrow ? gM_prev : gM;
                     const int llo = firstrow ? prev_last * nx : (l - 1) * nx;
-                    for (int f = 0; f < nf; ++f)
+                    for (int f = 0; f < nf; ++f) {
+                        Real u0[NM], u1[NM], u2[NM], u3[NM], t[NM];
+                        VM::load(gM + oM(f), ipa, l * nx + c, u0);
+                        VM::load(gM + oM(f), ipa, l * nx + cm, u1);
+                        VM::load(mlo + oM(f), ipa, llo + c, u2);
+                        VM::load(mlo + oM(f), ipa, llo + cm, u3);
 #pragma unroll
-                        for (int k = 0; k < NM; ++k)
-                            T[xT(opar, f, k, p)] = wM[0] * gM[xM(f, k, l * nx + c)] + wM[1] * gM[xM(f, k, l * nx + cm)] +
-                                                   wM[2] * mlo[xM(f, k, llo + c)] + wM[3] * mlo[xM(f, k, llo + cm)];
+                        for (int k = 0; k < NM; ++k) t[k] = wM[0] * u0[k] + wM[1] * u1[k] + wM[2] * u2[k] + wM[3] * u3[k];
+                        VM::store(T + oT(opar, f), ipa, p, t);
+                    }
                 }
                 step(l, c);
             }
@@ -654,10 +726,11 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 2 : 1) adjoint_kernel
     const int ncl = gridDim.x / C;
     using V = typename V16<Real>::T;
     V *ring = reinterpret_cast<V *>(smem_raw);
+    const int ipa = adj_ipa(a.ipts_max);
     Real *gI = reinterpret_cast<Real *>(ring + 3 * a.ring_plane);
-    Real *gM = gI + 2 * a.F * NS * a.ipts_max;
-    Real *gP = gM + a.F * NM * a.ipts_max;
-    Real *T = gP + a.F * NP * a.ipts_max;
+    Real *gM = gI + 2 * a.F * NS * ipa;
+    Real *gP = gM + a.F * NM * ipa;
+    Real *T = gP + a.F * NP * ipa;
     Real *tt = reinterpret_cast<Real *>(smem_raw + adjoint_tile_offset<Real, NS>(a.ring_plane, a.ipts_max, a.F));
     cluster.sync();
     for (int item = cid; item < a.nitems; item += ncl) {
