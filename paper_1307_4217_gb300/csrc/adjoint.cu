@@ -410,20 +410,11 @@ __device__ __forceinline__ void adjoint_item(const SweepArgs<Real> &a, cg::clust
             const int c1 = c + 1 == nx ? 0 : c + 1;
             const int cm = c == 0 ? nx - 1 : c - 1;
             const Node<Real, NS> nO = ring_load<Real, NS>(ring, plane, chunk, sO, (l + 1) * nx + c);
-            CornerM<Real, NS> kM[4];
-            kM[0] = corner_m<Real, NS>(ring_load<Real, NS>(ring, plane, chunk, sM, (l + 1) * nx + c), wM[0]);
-            kM[1] = corner_m<Real, NS>(ring_load<Real, NS>(ring, plane, chunk, sM, (l + 1) * nx + c1), wM[1]);
-            kM[2] = corner_m<Real, NS>(ring_load<Real, NS>(ring, plane, chunk, sM, (l + 2) * nx + c), wM[2]);
-            kM[3] = corner_m<Real, NS>(ring_load<Real, NS>(ring, plane, chunk, sM, (l + 2) * nx + c1), wM[3]);
-            CornerP<Real, NS> kP[4];
-            if (has_p) {
-                kP[0] = corner_p<Real, NS>(ring_load<Real, NS>(ring, plane, chunk, sP, l * nx + cm), wP[0]);
-                kP[1] = corner_p<Real, NS>(ring_load<Real, NS>(ring, plane, chunk, sP, l * nx + c), wP[1]);
-                kP[2] = corner_p<Real, NS>(ring_load<Real, NS>(ring, plane, chunk, sP, (l + 1) * nx + cm), wP[2]);
-                kP[3] = corner_p<Real, NS>(ring_load<Real, NS>(ring, plane, chunk, sP, (l + 1) * nx + c), wP[3]);
-            } else {
-                kP[0] = kP[1] = kP[2] = kP[3] = corner_p<Real, NS>(nO, Real(0));
-            }
+            // ring positions of the upwind (plane q-1) and downwind (plane q+1)
+            // stencil corners; their node data are read again for every frequency
+            // (shared-memory loads instead of ~50 live registers across the loop)
+            const int iM[4] = {(l + 1) * nx + c, (l + 1) * nx + c1, (l + 2) * nx + c, (l + 2) * nx + c1};
+            const int iP[4] = {l * nx + cm, l * nx + c, (l + 1) * nx + cm, (l + 1) * nx + c};
             const long long vO = voxel(gq, c, l);
             // form 2: dL/dI_p per unit J weight at O, sum_KQ T^K_Q(p, Omega) dL/dJ^K_Q, and dL/dLambda*
             Real gdir[3] = {0, 0, 0}, gLv = 0;
@@ -487,18 +478,19 @@ __device__ __forceinline__ void adjoint_item(const SweepArgs<Real> &a, cg::clust
                 for (int s = 0; s < NS; ++s) epsM[s] = 0;
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
-                    const Real xs = x - kM[k].s;
-                    const Real we = kM[k].wchi * profile_shape(xs);
+                    const CornerM<Real, NS> km = corner_m<Real, NS>(ring_load<Real, NS>(ring, plane, chunk, sM, iM[k]), wM[k]);
+                    const Real xs = x - km.s;
+                    const Real we = km.wchi * profile_shape(xs);
                     etaM += we;
                     if constexpr (NS == 1) {
-                        epsM[0] += we * kM[k].S;
+                        epsM[0] += we * km.S;
                     } else {
-                        const Real wkv = we * (kM[k].b * xs);
+                        const Real wkv = we * (km.b * xs);
                         etaVM += wkv;
-                        epsM[0] += we * kM[k].SI;
-                        epsM[1] += we * kM[k].SQ;
-                        epsM[2] += we * kM[k].SU;
-                        epsM[3] += wkv * kM[k].S00;
+                        epsM[0] += we * km.SI;
+                        epsM[1] += we * km.SQ;
+                        epsM[2] += we * km.SU;
+                        epsM[3] += wkv * km.S00;
                     }
                 }
                 Real etaP = 0, epsP[NS];
@@ -507,16 +499,18 @@ __device__ __forceinline__ void adjoint_item(const SweepArgs<Real> &a, cg::clust
                 if (has_p) {
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
-                        const Real xs = x - kP[k].s;
-                        const Real we = kP[k].wchi * profile_shape(xs);
+                        const CornerP<Real, NS> kp =
+                            corner_p<Real, NS>(ring_load<Real, NS>(ring, plane, chunk, sP, iP[k]), wP[k]);
+                        const Real xs = x - kp.s;
+                        const Real we = kp.wchi * profile_shape(xs);
                         etaP += we;
                         if constexpr (NS == 1) {
-                            epsP[0] += we * kP[k].S;
+                            epsP[0] += we * kp.S;
                         } else {
-                            epsP[0] += we * kP[k].SI;
-                            epsP[1] += we * kP[k].SQ;
-                            epsP[2] += we * kP[k].SU;
-                            epsP[3] += we * (kP[k].bS * xs);
+                            epsP[0] += we * kp.SI;
+                            epsP[1] += we * kp.SQ;
+                            epsP[2] += we * kp.SU;
+                            epsP[3] += we * (kp.bS * xs);
                         }
                     }
                 }
