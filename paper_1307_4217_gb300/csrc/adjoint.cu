@@ -541,11 +541,16 @@ __device__ __forceinline__ void adjoint_item(const SweepArgs<Real> &a, cg::clust
                 // control points exactly as the forward sweep computes them; their
                 // partial derivatives are formed per Stokes parameter where used
                 BesserGrad<Real> bg{};
+                int branches = 0;                  // control-point branch per Stokes parameter, 2 bits each
                 Real cM[NS];
                 if (has_p) {
                     bg = besser_grad(tMO, tOP);
 #pragma unroll
-                    for (int s = 0; s < NS; ++s) cM[s] = control_point(SM[s], SO[s], SP[s], bg.g);
+                    for (int s = 0; s < NS; ++s) {
+                        int br;
+                        cM[s] = control_point_branch(SM[s], SO[s], SP[s], bg.g, br);
+                        branches |= br << (2 * s);
+                    }
                 } else {
 #pragma unroll
                     for (int s = 0; s < NS; ++s) cM[s] = Real(0.5) * (SM[s] + SO[s]);
@@ -598,8 +603,8 @@ __device__ __forceinline__ void adjoint_item(const SweepArgs<Real> &a, cg::clust
                     g_wc += gr[s] * cM[s];
                     gIM[s] = gr[s] * co.e;
                     const Real gc = gr[s] * co.wc;
-                    CpGrad<Real> cp{cM[s], Real(0.5), Real(0.5), Real(0), Real(0), Real(0)};
-                    if (has_p) cp = control_point_grad(SM[s], SO[s], SP[s], bg);
+                    CpGrad<Real> cp{Real(0.5), Real(0.5), Real(0), Real(0), Real(0)};
+                    if (has_p) cp = control_point_grad((branches >> (2 * s)) & 3, SM[s], SO[s], SP[s], bg);
                     gSM[s] = gr[s] * co.wm + gc * cp.dyM;
                     gSO[s] = gr[s] * co.wo + gc * cp.dyO;
                     gSP[s] = gc * cp.dyP;

@@ -34,13 +34,13 @@ __device__ __forceinline__ CoefD<Real> coefficient_derivs(Real t, const Coef<Rea
     return d;
 }
 
-// BESSER control point and its partial derivatives with respect to
+// Partial derivatives of the BESSER control point with respect to
 // (y_M, y_O, y_P, h_M, h_P) on the branch it takes (Sec. 3.2):
 //   step 2 (extremum at O): c = y_O;  step 6 (overshoot in MO): c = y_M;
 //   steps 7-9 with c_P clipped: c = y_O - (h_M/h_P)(y_P - y_O);
 //   otherwise (step 4): c = y_O - h_M^2 (y_P - y_O)/(2 h_P s) - h_P (y_O - y_M)/(2 s),
 //   s = h_M + h_P.
-// The branch tests are those of control_point on the same BesserGeom, so the
+// The branch comes from control_point_branch on the same BesserGeom, so the
 // adjoint takes the branch the forward sweep took. The h-derivatives of the
 // parabola are linear in (d_P, d_M) = (y_P - y_O, y_O - y_M) with per-update
 // factors, computed once for the four Stokes parameters.
@@ -71,31 +71,28 @@ __device__ __forceinline__ BesserGrad<Real> besser_grad(Real hM, Real hP)
     return b;
 }
 
+// partial derivatives of the control point on the branch that
+// control_point_branch reported, selected without divergence
 template <typename Real>
 struct CpGrad {
-    Real c, dyM, dyO, dyP, dhM, dhP;
+    Real dyM, dyO, dyP, dhM, dhP;
 };
 
 template <typename Real>
-__device__ __forceinline__ CpGrad<Real> control_point_grad(Real yM, Real yO, Real yP, const BesserGrad<Real> &b)
+__device__ __forceinline__ CpGrad<Real> control_point_grad(int branch, Real yM, Real yO, Real yP, const BesserGrad<Real> &b)
 {
-    const BesserGeom<Real> &g = b.g;
     const Real dm = yO - yM, dp = yP - yO;
-    const Real yp = g.a * dp + g.b * dm;
-    const Real w = g.hm2 * yp;
-    const Real u = g.hp2 * yp;
-    CpGrad<Real> r;
-    if (!(dm * dp > Real(0))) {                       // step 2
-        r = CpGrad<Real>{yO, Real(0), Real(1), Real(0), Real(0), Real(0)};
-    } else if ((dm - w) * w < Real(0)) {              // steps 5-6
-        r = CpGrad<Real>{yM, Real(1), Real(0), Real(0), Real(0), Real(0)};
-    } else if (u * (u - dp) > Real(0)) {              // step 7 clipped, steps 8-9
-        r = CpGrad<Real>{yO - g.r * dp, Real(0), Real(1) + g.r, -g.r, -dp * b.ihP, g.r * dp * b.ihP};
-    } else {                                          // step 4
-        r = CpGrad<Real>{yO - w, b.dyM, Real(1) - b.dyM - b.dyP, b.dyP, b.hMp * dp + b.hMm * dm,
-                         b.hPp * dp + b.hPm * dm};
-    }
-    return r;
+    const Real rdp = dp * b.ihP;
+    const Real hM = b.hMp * dp + b.hMm * dm, hP = b.hPp * dp + b.hPm * dm;
+    const Real r = b.g.r;
+    const bool e = branch == 0, o = branch == 1, k = branch == 2, q = branch == 3;
+    CpGrad<Real> d;
+    d.dyM = o ? Real(1) : (q ? b.dyM : Real(0));
+    d.dyO = e ? Real(1) : (k ? Real(1) + r : (q ? Real(1) - b.dyM - b.dyP : Real(0)));
+    d.dyP = k ? -r : (q ? b.dyP : Real(0));
+    d.dhM = k ? -rdp : (q ? hM : Real(0));
+    d.dhP = k ? r * rdp : (q ? hP : Real(0));
+    return d;
 }
 
 // Solve M^T x = r with M the real matrix of hanle_solve5 (same scaling

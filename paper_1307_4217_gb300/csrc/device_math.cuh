@@ -134,17 +134,30 @@ __device__ __forceinline__ BesserGeom<Real> besser_geom(Real hM, Real hP)
 // Branch-free form: every step is evaluated and the outcome selected, so lanes
 // of a warp that take different branches do not diverge. Interval tests use
 // the sign of products ((c - y1)(c - y2) > 0 <=> c outside [min, max]).
+// `branch` reports the outcome: 0 extremum at O (step 2), 1 c_M clipped to y_M
+// (steps 5-6), 2 c_P clipped to y_P (steps 7-9), 3 the parabola (step 4).
 template <typename Real>
-__device__ __forceinline__ Real control_point(Real yM, Real yO, Real yP, const BesserGeom<Real> &g)
+__device__ __forceinline__ Real control_point_branch(Real yM, Real yO, Real yP, const BesserGeom<Real> &g, int &branch)
 {
     const Real dm = yO - yM, dp = yP - yO;           // step 1 (h_M d_M, h_P d_P)
     const Real yp = g.a * dp + g.b * dm;             // step 3 (Eq. 6)
     const Real w = g.hm2 * yp;                       // step 4: c_M = y_O - w
     Real u = g.hp2 * yp;                             //         c_P = y_O + u
-    u = (u * (u - dp) > Real(0)) ? dp : u;           // step 7: c_P outside [y_O, y_P] -> y_P
+    const bool clip = u * (u - dp) > Real(0);        // step 7: c_P outside [y_O, y_P] -> y_P
+    u = clip ? dp : u;
     const Real cM9 = yO - g.r * u;                   // steps 8-9: y'_O = 2 (c_P - y_O)/h_P
-    const Real r = ((dm - w) * w < Real(0)) ? yM : cM9;  // steps 5-6: c_M outside [y_M, y_O] -> y_M
-    return (dm * dp <= Real(0)) ? yO : r;            // step 2: extremum at O
+    const bool over = (dm - w) * w < Real(0);        // steps 5-6: c_M outside [y_M, y_O] -> y_M
+    const Real r = over ? yM : cM9;
+    const bool ext = dm * dp <= Real(0);             // step 2: extremum at O
+    branch = ext ? 0 : (over ? 1 : (clip ? 2 : 3));
+    return ext ? yO : r;
+}
+
+template <typename Real>
+__device__ __forceinline__ Real control_point(Real yM, Real yO, Real yP, const BesserGeom<Real> &g)
+{
+    int branch;
+    return control_point_branch(yM, yO, yP, g, branch);
 }
 
 // ---------------------------------------------------------------------------
