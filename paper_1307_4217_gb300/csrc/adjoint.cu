@@ -276,18 +276,33 @@ __device__ __forceinline__ void adjoint_item(const SweepArgs<Real> &a, cg::clust
         l += dl;
         if (c >= nx) { c -= nx; ++l; }
     };
-    auto fill = [&](int q) {
-        const PlaneGeom<Real> gq = G[q];
+    auto fill = [&](int q, const PlaneGeom<Real> &gq) {
         const int nn = (R + 2) * nx;
-        int lr = tl0, c = tc0;                               // lr = ring row (local row + 1)
-        for (int idx = tid; idx < nn; idx += nt) {
+        const long long kb = (long long)gq.kz * ny;
+        // voxel of ring node (lr, c), lr = ring row (local row + 1)
+        auto ring_voxel = [&](int lr, int c) {
             int pi = c + gq.ax;
             pi -= pi >= nx ? nx : 0;
             int pj = row0 + lr - 1 + gq.ay;                  // in [-1, 2 ny)
             pj += pj < 0 ? ny : 0;
             pj -= pj >= ny ? ny : 0;
-            const long long v = B.vox0 + ((long long)gq.kz * ny + pj) * nx + pi;
-            ring_store<Real, NS>(ring, plane, chunk, q % 3, idx, make_node<Real, NS>(a, ray, v, mglob, FORM == 2));
+            return B.vox0 + (kb + pj) * nx + pi;
+        };
+        // two nodes per thread and round, so that their global loads are in
+        // flight together
+        int lr = tl0, c = tc0;
+        for (int idx = tid; idx < nn; idx += 2 * nt) {
+            int lr2 = lr, c2 = c;
+            step(lr2, c2);
+            const bool two = idx + nt < nn;
+            const long long v = ring_voxel(lr, c);
+            const long long v2 = two ? ring_voxel(lr2, c2) : v;
+            const Node<Real, NS> n1 = make_node<Real, NS>(a, ray, v, mglob, FORM == 2);
+            const Node<Real, NS> n2 = make_node<Real, NS>(a, ray, v2, mglob, FORM == 2);
+            ring_store<Real, NS>(ring, plane, chunk, q % 3, idx, n1);
+            if (two) ring_store<Real, NS>(ring, plane, chunk, q % 3, idx + nt, n2);
+            lr = lr2;
+            c = c2;
             step(lr, c);
         }
     };
@@ -355,8 +370,7 @@ __device__ __forceinline__ void adjoint_item(const SweepArgs<Real> &a, cg::clust
     };
 
     // tape rows 0..R of the strip (sheared frame) of plane qq, all frequencies of the group
-    auto stage = [&](int qq) {
-        const PlaneGeom<Real> gg = G[qq];
+    auto stage = [&](const PlaneGeom<Real> &gg) {
         const int per = (R + 1) * nx;
         const Real *src0 = tape + (long long)j0 * a.nvox * NS;
         int lr = tl0, c = tc0;
@@ -370,9 +384,12 @@ __device__ __forceinline__ void adjoint_item(const SweepArgs<Real> &a, cg::clust
         cp_async_commit();
     };
 
-    fill(nz - 1);
-    fill(nz - 2);
-    stage(nz - 2);
+    {
+        const PlaneGeom<Real> g1 = G[nz - 1], g2 = G[nz - 2];
+        fill(nz - 1, g1);
+        fill(nz - 2, g2);
+        stage(g2);
+    }
     cp_async_wait_all();
     for (int f = tid; f < nf; f += nt) {
         xsh[f] = a.xf[j0 + f];
@@ -389,7 +406,7 @@ __device__ __forceinline__ void adjoint_item(const SweepArgs<Real> &a, cg::clust
     cluster.sync();
 
     for (int q = nz - 1; q >= 1; --q) {
-        const PlaneGeom<Real> gq = G[q], gm = G[q - 1];
+        const PlaneGeom<Real> gq = G[q];
         const bool has_p = q + 1 < nz;
         const PlaneGeom<Real> gp = has_p ? G[q + 1] : gq;
         const int sM = (q + 2) % 3, sO = q % 3, sP = (q + 1) % 3;
@@ -666,12 +683,11 @@ __device__ __forceinline__ void adjoint_item(const SweepArgs<Real> &a, cg::clust
         //     buffer and element as (a), read there before written here by the
         //     same thread); row 0 gathers the last row of the previous strip,
         //     and the last row waits for its own (a)
-        const PlaneGeom<Real> gq1 = has_p ? G[q + 1] : gq;
         auto phase2 = [&](bool remote) {
             int l = tl0, c = tc0;
             for (int p = tid; p < npts; p += nt) {
                 const bool firstrow = l == 0, lastrow = l + 1 == R;
-                if (has_p && lastrow == remote) finalize_pt(gq1, sP, opar, true, wP, p, l, c);
+                if (has_p && lastrow == remote) finalize_pt(gp, sP, opar, true, wP, p, l, c);
                 if ((firstrow || lastrow) == remote) {
                     const int cm = c == 0 ? nx - 1 : c - 1;
                     const Real *mlo = firstrow ? gM_prev : gM;
@@ -701,8 +717,9 @@ __device__ __forceinline__ void adjoint_item(const SweepArgs<Real> &a, cg::clust
         __syncthreads();
         cluster_arrive_relaxed();
         if (q - 2 >= 0) {
-            stage(q - 2);        // tape rows for step q-1, in flight during the refill and the barrier
-            fill(q - 2);
+            const PlaneGeom<Real> g2 = G[q - 2];
+            stage(g2);           // tape rows for step q-1, in flight during the refill and the barrier
+            fill(q - 2, g2);
         }
         cp_async_wait_all();
         __syncthreads();
