@@ -330,9 +330,12 @@ int porta_iterate_ckpt(porta_ctx *c, int niter, int ckpt, double *max_change);
      f    (the thermal source term eps B of the update, Eq. 12),
      B    (magnetic field vector: Zeeman term of the sweeps and Hanle term of
            the update).
-   The iterates are rebuilt from the nearest checkpoint (ckpt - 1 forward
-   iterations at most per step back); each step back runs the adjoint of the
-   update, then the adjoint of the formal solution's J^K_Q and Lambda-bar*
+   The iterates are rebuilt from the checkpoints, each segment of ckpt
+   iterations once (its iterates, J^K_Q and Lambda-bar* kept on the device,
+   ckpt*nvox*(nl + nj + 1) doubles; where that exceeds the tape limit below
+   or the free device memory, each step back rebuilds its iterate from the
+   nearest checkpoint instead); each step back
+   runs the adjoint of the update, then the adjoint of the formal solution's J^K_Q and Lambda-bar*
    (rays in batches whose forward Stokes vectors fit a device tape of at most
    16 GB, the same gather-form adjoint sweep as porta_emergent_vjp,
    per-cluster FP64 accumulators summed in a fixed order; the limit is

@@ -1098,15 +1098,6 @@ void it_free(porta_ctx *c)
     c->it_niter = c->it_ckpt = 0;
 }
 
-// one eager Jacobi iteration (formal solution, J^K_Q sums, update)
-int it_step(porta_ctx *c)
-{
-    int rc = porta_formal_solve(c);
-    if (rc == PORTA_OK) rc = porta_accumulate_jkq(c, nullptr, nullptr, PORTA_DEVICE);
-    if (rc == PORTA_OK) rc = porta_see_update(c, nullptr);
-    return rc;
-}
-
 int it_load(porta_ctx *c, const double *src)
 {
     cudaError_t e = cudaMemcpyAsync(c->d_rho, src, sizeof(double) * c->nvox * c->nl, cudaMemcpyDeviceToDevice, c->stream);
@@ -1138,14 +1129,58 @@ int iterate_vjp_t(porta_ctx *c, int ndir, const double *mu, const double *chi, c
     for (int k = 0; k < 4 && rc == PORTA_OK; ++k)
         if (!c->it_ev[k] && cudaEventCreate(&c->it_ev[k]) != cudaSuccess) rc = fail(c, PORTA_ECUDA, "iterate_vjp: events");
     cudaEvent_t *ev = c->it_ev;
+    // The iterates of one checkpoint segment with their J^K_Q and Lambda-bar*:
+    // each segment is rebuilt once from its checkpoint (ckpt formal solutions in
+    // all, as many as the forward iterations) and its steps back read them from
+    // here. Where that store exceeds the tape limit or the free device memory,
+    // every step back rebuilds its iterate from the checkpoint instead
+    // (ckpt (ckpt + 1) / 2 formal solutions per segment).
+    const int nslot = std::min(c->it_ckpt, c->it_niter);
+    const size_t nj = (size_t)c->nvox * c->nj, per_slot = nr + nj + c->nvox;
+    double *seg = nullptr;
+    const size_t seg_bytes = sizeof(double) * per_slot * nslot;
+    if (rc == PORTA_OK && seg_bytes <= c->tape_limit && cudaMalloc(&seg, seg_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        seg = nullptr;
+    }
+    auto slot = [&](int i) { return seg + per_slot * i; };
+    auto save = [&](int i) {
+        cudaError_t r = cudaMemcpyAsync(slot(i), c->d_rho, sizeof(double) * nr, cudaMemcpyDeviceToDevice, c->stream);
+        if (r == cudaSuccess)
+            r = cudaMemcpyAsync(slot(i) + nr, c->d_jkq, sizeof(double) * nj, cudaMemcpyDeviceToDevice, c->stream);
+        if (r == cudaSuccess)
+            r = cudaMemcpyAsync(slot(i) + nr + nj, c->d_lstar, sizeof(double) * c->nvox, cudaMemcpyDeviceToDevice,
+                                c->stream);
+        return r == cudaSuccess ? PORTA_OK : fail(c, PORTA_ECUDA, std::string("iterate_vjp: ") + cudaGetErrorString(r));
+    };
+    auto restore = [&](int i) {
+        int r = it_load(c, slot(i));
+        cudaError_t x = cudaSuccess;
+        if (r == PORTA_OK)
+            x = cudaMemcpyAsync(c->d_jkq, slot(i) + nr, sizeof(double) * nj, cudaMemcpyDeviceToDevice, c->stream);
+        if (r == PORTA_OK && x == cudaSuccess)
+            x = cudaMemcpyAsync(c->d_lstar, slot(i) + nr + nj, sizeof(double) * c->nvox, cudaMemcpyDeviceToDevice,
+                                c->stream);
+        if (r == PORTA_OK && x != cudaSuccess) r = fail(c, PORTA_ECUDA, std::string("iterate_vjp: ") + cudaGetErrorString(x));
+        return r;
+    };
+    int seg_base = -1;
     for (int k = c->it_niter - 1; k >= 0 && rc == PORTA_OK; --k) {
-        // the iterate rho_k: from the checkpoint at or below k
-        const int base = k / c->it_ckpt;
+        // the iterate rho_k with J^K_Q and Lambda-bar* at rho_k
+        const int base = k / c->it_ckpt, b0 = base * c->it_ckpt;
         e = cudaEventRecord(ev[0], c->stream);
-        rc = it_load(c, c->it_saved[base]);
-        for (int s = base * c->it_ckpt; s < k && rc == PORTA_OK; ++s) rc = it_step(c);
-        if (rc == PORTA_OK) rc = porta_formal_solve(c);
-        if (rc == PORTA_OK) rc = porta_accumulate_jkq(c, nullptr, nullptr, PORTA_DEVICE);
+        if (seg && base == seg_base) {
+            rc = restore(k - b0);
+        } else {
+            rc = it_load(c, c->it_saved[base]);
+            for (int s = b0; s <= k && rc == PORTA_OK; ++s) {
+                rc = porta_formal_solve(c);
+                if (rc == PORTA_OK) rc = porta_accumulate_jkq(c, nullptr, nullptr, PORTA_DEVICE);
+                if (rc == PORTA_OK && seg) rc = save(s - b0);
+                if (rc == PORTA_OK && s < k) rc = porta_see_update(c, nullptr);
+            }
+            seg_base = seg ? base : -1;
+        }
         if (rc) break;
         e = cudaEventRecord(ev[1], c->stream);
         // reverse mode of the update rho_{k+1} = U(rho_k, J, Lambda*, f, B)
@@ -1170,6 +1205,7 @@ int iterate_vjp_t(porta_ctx *c, int ndir, const double *mu, const double *chi, c
     int rc2 = it_load(c, c->it_final);
     cudaStreamSynchronize(c->stream);
     cudaFree(blk);
+    if (seg) cudaFree(seg);
     return rc ? rc : rc2;
 }
 

@@ -122,6 +122,30 @@ def test_launch_shapes_and_ray_batches_give_the_same_gradients(cluster, nu_group
         _cmp(g, r, 1e-11, what)
 
 
+def test_segment_store_and_per_step_rebuild_give_the_same_gradients():
+    """Each checkpoint segment rebuilt once with its iterates kept on the device
+    (the default) against every step back rebuilding its iterate from the
+    checkpoint (a tape limit just below that store): the same iterates, so the
+    FP64 gradients agree to the rounding of the different ray batches."""
+    atm, model = _case(True, nx=8, ny=6, nz=7, seed=5)
+    mu, az = synth.emergent_directions()
+    gout = np.random.default_rng(29).normal(size=(len(mu), QUAD[2], atm["ny"], atm["nx"], 4))
+    niter, ckpt = 6, 4
+    ref_ctx = _ctx(atm, model, P.PORTA_FP64)
+    ref_ctx.iterate_ckpt(niter, ckpt)
+    ref = ref_ctx.iterate_vjp(mu, az, gout)
+    ctx = _ctx(atm, model, P.PORTA_FP64)
+    nvox = atm["nx"] * atm["ny"] * atm["nz"]
+    store = ckpt * nvox * (6 + 6 + 1) * 8            # rho, J^K_Q and Lambda-bar* per iterate
+    ctx.set_tape_limit(store - 8)
+    ctx.iterate_ckpt(niter, ckpt)
+    got = ctx.iterate_vjp(mu, az, gout)
+    for g, r, what in zip(got, ref, ("chi", "f", "B")):
+        _cmp(g, r, 1e-11, what)
+    # the rebuild of the per-step path runs more formal solutions
+    assert ctx.iterate_timing()["recompute_ms"] > ref_ctx.iterate_timing()["recompute_ms"]
+
+
 def test_device_buffers_match_host_buffers():
     torch = pytest.importorskip("torch")
     atm, model = _case(True, seed=7)
