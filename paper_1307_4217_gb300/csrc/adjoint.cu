@@ -354,9 +354,13 @@ __device__ __forceinline__ void adjoint_item(const SweepArgs<Real> &a, cg::clust
                 gout_part[a.nvox + v] = ge;
                 gout_part[2 * a.nvox + v] = gb;
             } else {
-                // this cluster's accumulators; a node is finalized by one thread per item
+                // this cluster's accumulators, as reductions performed in the L2 (no
+                // load on this thread's path). A node is finalized by one thread per
+                // item and the cluster's items are separated by cluster barriers
+                // (release / acquire), so the additions into each accumulator happen
+                // in item order: the sums are reproducible.
 #pragma unroll
-                for (int k = 0; k < 10; ++k) acc[k * a.nvox + v] += (double)o[k];
+                for (int k = 0; k < 10; ++k) atomicAdd(acc + k * a.nvox + v, (double)o[k]);
             }
         }
     };
