@@ -765,14 +765,22 @@ template <typename Real>
 __global__ void adjoint_reduce_kernel(const Real *gpart, int nitems, int ngroups, long long nvox,
                                       const RayDev<Real> *rays, double bfac, double *g_chi, double *g_e, double *g_b)
 {
+    const int ndir = nitems / ngroups;
     for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < nvox; v += (long long)gridDim.x * blockDim.x) {
         double sc = 0, se = 0, bx = 0, by = 0, bz = 0;
-        for (int it = 0; it < nitems; ++it) {
-            const Real *p = gpart + (long long)it * 3 * nvox;
-            const RayDev<Real> &r = rays[it / ngroups];
-            const double gb = (double)p[2 * nvox + v];
-            sc += (double)p[v];
-            se += (double)p[nvox + v];
+        // directions in order, the groups of a direction in order (loads of
+        // several items in flight; the sums keep this fixed order)
+        for (int d = 0; d < ndir; ++d) {
+            const Real *p0 = gpart + (long long)d * ngroups * 3 * nvox;
+            double gb = 0;
+#pragma unroll 4
+            for (int g = 0; g < ngroups; ++g) {
+                const Real *p = p0 + (long long)g * 3 * nvox;
+                sc += (double)p[v];
+                se += (double)p[nvox + v];
+                gb += (double)p[2 * nvox + v];
+            }
+            const RayDev<Real> &r = rays[d];
             bx += gb * (double)r.ox;
             by += gb * (double)r.oy;
             bz += gb * (double)r.oz;
