@@ -21,8 +21,8 @@
 //   ibuf[2][F][NS/chunk][rows][nx] Stokes vectors of planes q-1 and q for F
 //                             frequencies.
 // Each thread owns points of its strip and loops over the F frequencies of the
-// pass, keeping the weighted data of its 8 stencil corners in registers, and
-// accumulates the
+// pass, reading the data of its 8 stencil corners from the node ring for each
+// frequency, and accumulates the
 // frequency-integrated Stokes I, Q, U and Lambda* of its point in registers;
 // one store (or read-modify-write for later frequency passes) per point and
 // plane writes the per-ray partial integrals.
@@ -226,20 +226,13 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<Real> &a, cg::cluster
                 const int c1 = (c + 1 == nx) ? 0 : c + 1;
                 const int cm = (c == 0) ? nx - 1 : c - 1;
                 // upwind corners (c|c1, l|l+1) on plane q-1; downwind (cm|c, l-1|l) on plane q+1
-                CornerM<Real, NS> kM[4];
-                kM[0] = corner_m<Real, NS>(ring_load<Real, NS>(ring, plane, chunk, sM, (l + 1) * nx + c), mx0 * my0);
-                kM[1] = corner_m<Real, NS>(ring_load<Real, NS>(ring, plane, chunk, sM, (l + 1) * nx + c1), mx1 * my0);
-                kM[2] = corner_m<Real, NS>(ring_load<Real, NS>(ring, plane, chunk, sM, (l + 2) * nx + c), mx0 * my1);
-                kM[3] = corner_m<Real, NS>(ring_load<Real, NS>(ring, plane, chunk, sM, (l + 2) * nx + c1), mx1 * my1);
-                CornerP<Real, NS> kP[4];
-                if (has_p) {
-                    kP[0] = corner_p<Real, NS>(ring_load<Real, NS>(ring, plane, chunk, sP, l * nx + cm), px0 * py0);
-                    kP[1] = corner_p<Real, NS>(ring_load<Real, NS>(ring, plane, chunk, sP, l * nx + c), px1 * py0);
-                    kP[2] = corner_p<Real, NS>(ring_load<Real, NS>(ring, plane, chunk, sP, (l + 1) * nx + cm), px0 * py1);
-                    kP[3] = corner_p<Real, NS>(ring_load<Real, NS>(ring, plane, chunk, sP, (l + 1) * nx + c), px1 * py1);
-                } else {
-                    kP[0] = kP[1] = kP[2] = kP[3] = corner_p<Real, NS>(nO, Real(0));
-                }
+                // ring positions and bilinear weights of the corners; their node data
+                // are read again for every frequency (shared-memory loads instead of
+                // ~50 registers held across the frequency loop)
+                const int iM[4] = {(l + 1) * nx + c, (l + 1) * nx + c1, (l + 2) * nx + c, (l + 2) * nx + c1};
+                const int iP[4] = {l * nx + cm, l * nx + c, (l + 1) * nx + cm, (l + 1) * nx + c};
+                const Real wM[4] = {mx0 * my0, mx1 * my0, mx0 * my1, mx1 * my1};
+                const Real wP[4] = {px0 * py0, px1 * py0, px0 * py1, px1 * py1};
                 // dichroism ratios of the upwind corners and of O
                 Real mdq[4] = {0, 0, 0, 0}, mdu[4] = {0, 0, 0, 0}, odq = 0, odu = 0;
                 if constexpr (dich) {
@@ -281,22 +274,23 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<Real> &a, cg::cluster
                     for (int s = 0; s < NS; ++s) epsM[s] = 0;
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
-                        const Real xs = x - kM[k].s;
-                        const Real we = kM[k].wchi * profile_shape(xs);
+                        const CornerM<Real, NS> km = corner_m<Real, NS>(ring_load<Real, NS>(ring, plane, chunk, sM, iM[k]), wM[k]);
+                        const Real xs = x - km.s;
+                        const Real we = km.wchi * profile_shape(xs);
                         etaM += we;
                         if constexpr (dich) {
                             etaQM += we * mdq[k];
                             etaUM += we * mdu[k];
                         }
                         if constexpr (NS == 1) {
-                            epsM[0] += we * kM[k].S;
+                            epsM[0] += we * km.S;
                         } else {
-                            const Real wkv = we * (kM[k].b * xs);
+                            const Real wkv = we * (km.b * xs);
                             etaVM += wkv;
-                            epsM[0] += we * kM[k].SI;
-                            epsM[1] += we * kM[k].SQ;
-                            epsM[2] += we * kM[k].SU;
-                            epsM[3] += wkv * kM[k].S00;
+                            epsM[0] += we * km.SI;
+                            epsM[1] += we * km.SQ;
+                            epsM[2] += we * km.SU;
+                            epsM[3] += wkv * km.S00;
                         }
                     }
                     Real etaP = 0, epsP[NS];
@@ -305,16 +299,18 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<Real> &a, cg::cluster
                     if (has_p) {
 #pragma unroll
                         for (int k = 0; k < 4; ++k) {
-                            const Real xs = x - kP[k].s;
-                            const Real we = kP[k].wchi * profile_shape(xs);
+                            const CornerP<Real, NS> kp =
+                                corner_p<Real, NS>(ring_load<Real, NS>(ring, plane, chunk, sP, iP[k]), wP[k]);
+                            const Real xs = x - kp.s;
+                            const Real we = kp.wchi * profile_shape(xs);
                             etaP += we;
                             if constexpr (NS == 1) {
-                                epsP[0] += we * kP[k].S;
+                                epsP[0] += we * kp.S;
                             } else {
-                                epsP[0] += we * kP[k].SI;
-                                epsP[1] += we * kP[k].SQ;
-                                epsP[2] += we * kP[k].SU;
-                                epsP[3] += we * (kP[k].bS * xs);
+                                epsP[0] += we * kp.SI;
+                                epsP[1] += we * kp.SQ;
+                                epsP[2] += we * kp.SU;
+                                epsP[3] += we * (kp.bS * xs);
                             }
                         }
                     }
