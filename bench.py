@@ -44,10 +44,9 @@ WORKLOAD = ("polarized two-level atom (Jl=0->Ju=1, Hanle + weak-field Zeeman), r
 # formal solution, counted stage by stage with each node's transfer coefficients
 # once per ray and frequency: node coefficients, bilinear interpolation at M and
 # P, source functions and optical paths 140, exponential-integral coefficients 25,
-# BESSER control points for the
-# 4 Stokes parameters 72, right-hand side of Eq. 7 34, the I-V coupling solve 9,
-# Lambda* and the frequency accumulation 11, the J^K_Q finalize per (ray, voxel)
-# spread over 21 frequencies 2
+# BESSER control points for the 4 Stokes parameters 72, right-hand side of Eq. 7
+# 34, the I-V coupling solve 9, Lambda* and the frequency accumulation 11, the
+# J^K_Q finalize per (ray, voxel) spread over 21 frequencies 2
 F_ALG = 293
 # FP32 issue peak of the GB300: 152 SMs x 128 FP32 lanes x 2 flops (FMA) x 2070 MHz
 SMS, LANES, SM_MAX_MHZ = 152, 128, 2070.0
