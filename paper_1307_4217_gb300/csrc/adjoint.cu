@@ -434,8 +434,8 @@ __device__ __forceinline__ void adjoint_item(const SweepArgs<Real> &a, cg::clust
             // ring positions of the upwind (plane q-1) and downwind (plane q+1)
             // stencil corners; their node data are read again for every frequency
             // (shared-memory loads instead of ~50 live registers across the loop)
-            const int iM[4] = {(l + 1) * nx + c, (l + 1) * nx + c1, (l + 2) * nx + c, (l + 2) * nx + c1};
-            const int iP[4] = {l * nx + cm, l * nx + c, (l + 1) * nx + cm, (l + 1) * nx + c};
+            const int rM[4] = {(l + 1) * nx + c, (l + 1) * nx + c1, (l + 2) * nx + c, (l + 2) * nx + c1};
+            const int rP[4] = {l * nx + cm, l * nx + c, (l + 1) * nx + cm, (l + 1) * nx + c};
             const long long vO = voxel(gq, c, l);
             // form 2: dL/dI_p per unit J weight at O, sum_KQ T^K_Q(p, Omega) dL/dJ^K_Q, and dL/dLambda*
             Real gdir[3] = {0, 0, 0}, gLv = 0;
@@ -499,7 +499,7 @@ __device__ __forceinline__ void adjoint_item(const SweepArgs<Real> &a, cg::clust
                 for (int s = 0; s < NS; ++s) epsM[s] = 0;
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
-                    const CornerM<Real, NS> km = corner_m<Real, NS>(ring_load<Real, NS>(ring, plane, chunk, sM, iM[k]), wM[k]);
+                    const CornerM<Real, NS> km = corner_m<Real, NS>(ring_load<Real, NS>(ring, plane, chunk, sM, rM[k]), wM[k]);
                     const Real xs = x - km.s;
                     const Real we = km.wchi * profile_shape(xs);
                     etaM += we;
@@ -521,7 +521,7 @@ __device__ __forceinline__ void adjoint_item(const SweepArgs<Real> &a, cg::clust
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
                         const CornerP<Real, NS> kp =
-                            corner_p<Real, NS>(ring_load<Real, NS>(ring, plane, chunk, sP, iP[k]), wP[k]);
+                            corner_p<Real, NS>(ring_load<Real, NS>(ring, plane, chunk, sP, rP[k]), wP[k]);
                         const Real xs = x - kp.s;
                         const Real we = kp.wchi * profile_shape(xs);
                         etaP += we;

@@ -229,8 +229,8 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<Real> &a, cg::cluster
                 // ring positions and bilinear weights of the corners; their node data
                 // are read again for every frequency (shared-memory loads instead of
                 // ~50 registers held across the frequency loop)
-                const int iM[4] = {(l + 1) * nx + c, (l + 1) * nx + c1, (l + 2) * nx + c, (l + 2) * nx + c1};
-                const int iP[4] = {l * nx + cm, l * nx + c, (l + 1) * nx + cm, (l + 1) * nx + c};
+                const int rM[4] = {(l + 1) * nx + c, (l + 1) * nx + c1, (l + 2) * nx + c, (l + 2) * nx + c1};
+                const int rP[4] = {l * nx + cm, l * nx + c, (l + 1) * nx + cm, (l + 1) * nx + c};
                 const Real wM[4] = {mx0 * my0, mx1 * my0, mx0 * my1, mx1 * my1};
                 const Real wP[4] = {px0 * py0, px1 * py0, px0 * py1, px1 * py1};
                 // dichroism ratios of the upwind corners and of O
@@ -274,7 +274,7 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<Real> &a, cg::cluster
                     for (int s = 0; s < NS; ++s) epsM[s] = 0;
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
-                        const CornerM<Real, NS> km = corner_m<Real, NS>(ring_load<Real, NS>(ring, plane, chunk, sM, iM[k]), wM[k]);
+                        const CornerM<Real, NS> km = corner_m<Real, NS>(ring_load<Real, NS>(ring, plane, chunk, sM, rM[k]), wM[k]);
                         const Real xs = x - km.s;
                         const Real we = km.wchi * profile_shape(xs);
                         etaM += we;
@@ -300,7 +300,7 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<Real> &a, cg::cluster
 #pragma unroll
                         for (int k = 0; k < 4; ++k) {
                             const CornerP<Real, NS> kp =
-                                corner_p<Real, NS>(ring_load<Real, NS>(ring, plane, chunk, sP, iP[k]), wP[k]);
+                                corner_p<Real, NS>(ring_load<Real, NS>(ring, plane, chunk, sP, rP[k]), wP[k]);
                             const Real xs = x - kp.s;
                             const Real we = kp.wchi * profile_shape(xs);
                             etaP += we;
