@@ -97,7 +97,8 @@ typedef struct {
 
 /* Atomic model. zeta: Zeeman splitting per gauss in Doppler widths; gbar:
    effective Lande factor; bcrit: Hanle critical field in gauss, so that the
-   upper-level Hanle parameter is Gamma_u = |B| / bcrit. */
+   upper-level Hanle parameter is Gamma_u = |B| / bcrit (the atom precesses
+   counterclockwise about B, as for a positive Lande factor). */
 typedef struct {
     int model;
     double zeta, gbar, bcrit;
@@ -436,8 +437,9 @@ typedef struct {
    without interference between levels; the paper takes them from LL04 Sect.
    7.2): absorption TA, spontaneous emission TE and stimulated emission TS into
    a level, relaxation RA + RE + RS out of it (Wigner 3j/6j/9j coefficients
-   times the line's J^Kr_Qr, Kr = 0, 2), the Hanle term i 2 pi nu_L g_J (b.J)
-   with Lande factor 1 for every level and nu_L = 1.3996e6 Hz/G, collisions on
+   times the line's J^Kr_Qr, Kr = 0, 2), the Hanle term -i 2 pi nu_L g_J (b.J)
+   of d rho / dt (counterclockwise precession about the field) with Lande
+   factor 1 for every level and nu_L = 1.3996e6 Hz/G, collisions on
    the line transitions moving populations and relaxing every multipole of the
    level they leave. Jacobi: Lambda-bar* preconditioning of the population
    terms as for the unpolarized atom, the trace row sum_J sqrt(2J+1)

@@ -8,7 +8,7 @@ The rate equations, in the multipole representation (rho^K_{-Q} = (-1)^Q
 conj(rho^K_Q)), with J^{Kr}_{Qr} of each line (Kr = 0, 1, 2; the radiation
 field tensors of Eq. 1) and 3j, 6j and 9j symbols (oracle/wigner.py):
 
-  d rho^K_Q(J)/dt =  i w_J sum_Q' H^K_{QQ'}(b) rho^K_Q'(J)                   (Hanle)
+  d rho^K_Q(J)/dt = -i w_J sum_Q' H^K_{QQ'}(b) rho^K_Q'(J)                   (Hanle)
       + sum_{l, KlQl} TA(J K Q; l Kl Ql) rho^Kl_Ql(l)                        (absorption from lower levels)
       + sum_{u, KuQu} [TE + TS](J K Q; u Ku Qu) rho^Ku_Qu(u)                 (emission from upper levels)
       - sum_{K'Q'} [RA + RE + RS](J K Q; K' Q') rho^K'_Q'(J)                 (relaxation)
@@ -29,8 +29,11 @@ field tensors of Eq. 1) and 3j, 6j and 9j symbols (oracle/wigner.py):
 H^K is the matrix of the field direction b . J on rank-K multipoles (H_QQ =
 Q b_z, H_{Q,Q-1} = (1/2)(b_x - i b_y) sqrt((K+Q)(K-Q+1)), H_{Q,Q+1} = (1/2)(b_x +
 i b_y) sqrt((K-Q)(K+Q+1))) and w_J = 2 pi nu_L g_J the Larmor frequency of
-the level (nu_L = 1.3996e6 Hz per gauss); its sense is the one of the
-two-level model of this package, to which the J = 0 -> 1 atom reduces.
+the level (nu_L = 1.3996e6 Hz per gauss): for b along z, rho^K_Q turns as
+e^{-i Q w_J t}, the counterclockwise precession of the atom about the field for
+g_J > 0 (rho^K_Q transform as e^{-i Q alpha} under a rotation by alpha about z).
+The two-level model of this package, to which the J = 0 -> 1 atom reduces,
+has the same sense.
 Collisions (a reading): inelastic collisions on the line transitions move
 populations only (K = 0) and relax every multipole of the level they leave;
 no elastic depolarization. Units as in oracle/ml.py (A in s^-1, intensities
@@ -233,10 +236,10 @@ class Tables:
                                     self.Mr[li, c, a, b] -= v
                                     if K == 0 and Kp == 0 and Kr == 0:
                                         self.Mpop[li, a, b] -= v
-        # Hanle: i w_J H^K(b) per field component (b_x, b_y, b_z in gauss)
+        # Hanle: -i w_J H^K(b) per field component (b_x, b_y, b_z in gauss)
         self.Mh = np.zeros((3, n, n), dtype=complex)
         for a, (lev, K, Q) in enumerate(cb):
-            wj = 2 * np.pi * NU_L_PER_G * 1.0          # Lande factor 1 for every level
+            wj = -2 * np.pi * NU_L_PER_G * 1.0         # -w_J, Lande factor 1 for every level
             for Qp in (Q - 1, Q, Q + 1):
                 if abs(Qp) > K:
                     continue

@@ -7,9 +7,12 @@
  * unpolarized, so the line absorption is unpolarized).
  *
  * Two-level atom, CRD, no stimulated emission:
- *   S^K_Q + i (1-eps) Gamma_u sum_Q' K^K_QQ'(B) S^K_Q' = (1-eps) w^(K) J^K_Q + eps B delta_K0 delta_Q0
+ *   S^K_Q - i (1-eps) Gamma_u sum_Q' K^K_QQ'(B) S^K_Q' = (1-eps) w^(K) J^K_Q + eps B delta_K0 delta_Q0
  * with Gamma_u = |B| / bcrit and K^K_QQ' the matrix of the angular momentum
- * component along the field direction (theta_B, chi_B):
+ * component along the field direction (theta_B, chi_B). The S^K_Q follow the
+ * convention of J^K_Q (they are the complex conjugates of the atomic rho^K_Q):
+ * the atom precesses counterclockwise about B (Lande factor > 0), which in this
+ * convention is the factor -i (HANLE_SENSE below) of the magnetic term.
  *   K_QQ = Q cos(theta_B),
  *   K_Q,Q-1 = 1/2 sin(theta_B) e^{+i chi_B} sqrt((K+Q)(K-Q+1)),
  *   K_Q,Q+1 = 1/2 sin(theta_B) e^{-i chi_B} sqrt((K-Q)(K+Q+1)).
@@ -23,6 +26,9 @@
 #include <complex.h>
 #undef I
 #define IU _Complex_I
+
+/* sign of the magnetic term of the equation above (see the header) */
+#define HANLE_SENSE (-1.0)
 
 /* M = 1 + i gamma K for K = 2 (rows and columns Q = -2..2) for the field (bx, by, bz) */
 static void hanle_matrix(double gamma, double bx, double by, double bz, double complex M[5][5])
@@ -94,7 +100,7 @@ int or_hanle_solve(double gamma, double bx, double by, double bz, const double *
  * The statistical-equilibrium operator of the two-level atom written as
  * A(S) = f (Eq. 2 as L rho = f): per voxel
  *   A(S)^0_0 = S^0_0 - (1-eps) J^0_0,
- *   A(S)^2_Q = S^2_Q + i (1-eps) Gamma_u sum_Q' K_QQ' S^2_Q' - (1-eps) J^2_Q,
+ *   A(S)^2_Q = S^2_Q - i (1-eps) Gamma_u sum_Q' K_QQ' S^2_Q' - (1-eps) J^2_Q,
  * with J = J[S] from the formal solution and f = eps B delta_K0 delta_Q0.
  * out = A(S) (nvox * nl, the layout of rho).
  */
@@ -110,7 +116,7 @@ int or_see_apply(const or_problem *p, const double *jkq, const double *rho, doub
         const double *s = rho + 6 * v, *J = jkq + 6 * v;
         double *o = out + 6 * v;
         double bx = p->bx[v], by = p->by[v], bz = p->bz[v];
-        double gamma = (1.0 - e) * sqrt(bx * bx + by * by + bz * bz) / p->bcrit;
+        double gamma = HANLE_SENSE * (1.0 - e) * sqrt(bx * bx + by * by + bz * bz) / p->bcrit;
         double complex M[5][5], x[5];
         hanle_matrix(gamma, bx, by, bz, M);
         to_complex(s, x);
@@ -159,7 +165,8 @@ int or_see_update_src(const or_problem *p, const double *jkq, const double *lsta
             double S00n = S00 + dS;
             double rhs[6], s2[6];
             for (int c = 0; c < 6; c++) rhs[c] = (1.0 - e) * J[c] + (src && c > 0 ? src[v * nl + c] : 0.0);
-            double gamma = (1.0 - e) * sqrt(p->bx[v] * p->bx[v] + p->by[v] * p->by[v] + p->bz[v] * p->bz[v]) / p->bcrit;
+            double gamma = HANLE_SENSE * (1.0 - e) *
+                           sqrt(p->bx[v] * p->bx[v] + p->by[v] * p->by[v] + p->bz[v] * p->bz[v]) / p->bcrit;
             if (or_hanle_solve(gamma, p->bx[v], p->by[v], p->bz[v], rhs, s2) != 0) return -3;
             double ch = fabs(dS) / fabs(S00);
             if (ch > mc || ch != ch) mc = ch;
@@ -241,7 +248,7 @@ static int solve5(double A[5][5], double *b, double *x)
  *   g_eb    dL/d(eps B), or dL/dsrc^0_0 (the thermal emission term),
  *   g_b     dL/dB (3 x nvox, added for the polarized model: the Hanle term).
  * S00' = S00 + ((1-eps) J00 + eps B - S00) / D, D = 1 - (1-eps) Lambda*;
- * S2' = M(B)^-1 (1-eps) J2 with M affine in B: M = 1 + (1-eps)/bcrit sum_c B_c N_c.
+ * S2' = M(B)^-1 (1-eps) J2 with M affine in B: M = 1 + HANLE_SENSE (1-eps)/bcrit sum_c B_c N_c.
  */
 int or_see_update_vjp(const or_problem *p, const double *jkq, const double *lstar, const double *src,
                       const double *rho, const double *g, double *g_rho, double *g_jkq, double *g_lstar,
@@ -262,7 +269,7 @@ int or_see_update_vjp(const or_problem *p, const double *jkq, const double *lsta
         g_lstar[v] = gv[0] * num * (1.0 - e) / (D * D);
         if (p->model == OR_MODEL_UNPOL) continue;
         double bx = p->bx[v], by = p->by[v], bz = p->bz[v];
-        double gamma = (1.0 - e) * sqrt(bx * bx + by * by + bz * bz) / p->bcrit;
+        double gamma = HANLE_SENSE * (1.0 - e) * sqrt(bx * bx + by * by + bz * bz) / p->bcrit;
         double R[5][5], Rt[5][5], rhs[6], s2[6], z[5], b5[5];
         hanle_real(gamma, bx, by, bz, R);
         for (int c = 0; c < 6; c++) rhs[c] = (1.0 - e) * J[c];
@@ -271,7 +278,8 @@ int or_see_update_vjp(const or_problem *p, const double *jkq, const double *lsta
         for (int a = 0; a < 5; a++) b5[a] = gv[1 + a];
         if (solve5(Rt, b5, z) != 0) return -3;
         for (int a = 0; a < 5; a++) g_jkq[nj * v + 1 + a] = (1.0 - e) * z[a];
-        /* dM/dB_c = (1-eps)/bcrit N_c, N_c = M(unit field along c, gamma 1) - 1; dS2' = -M^-1 dM S2' */
+        /* dM/dB_c = HANLE_SENSE (1-eps)/bcrit N_c, N_c = M(unit field along c, gamma 1) - 1;
+           dS2' = -M^-1 dM S2' */
         double unit[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
         for (int c = 0; c < 3; c++) {
             double N[5][5];
@@ -279,7 +287,7 @@ int or_see_update_vjp(const or_problem *p, const double *jkq, const double *lsta
             double acc = 0.0;
             for (int a = 0; a < 5; a++)
                 for (int q = 0; q < 5; q++) acc += z[a] * (N[a][q] - (a == q ? 1.0 : 0.0)) * s2[1 + q];
-            g_b[c * nv + v] += -(1.0 - e) / p->bcrit * acc;
+            g_b[c * nv + v] += -HANLE_SENSE * (1.0 - e) / p->bcrit * acc;
         }
     }
     return 0;

@@ -265,8 +265,9 @@ int mlpol_tables(const std::vector<double> &J, const std::vector<double> &E, con
         G[t.src_pop + li] = Mpop;
         G[t.src_spop + li] = Mspop;
     }
-    // Hanle: i w_J H^K(b), Lande factor 1, b in gauss
-    const double wj = 2.0 * M_PI * kLarmorPerGauss;
+    // Hanle: -i w_J H^K(b) in d rho / dt (rho^K_Q turns as e^{-i Q w_J t} for b along z:
+    // counterclockwise precession about the field), Lande factor 1, b in gauss
+    const double wj = -2.0 * M_PI * kLarmorPerGauss;
     for (int a = 0; a < n; ++a) {
         const int lev = cl[a], K = cK[a], Q = cQ[a];
         at(G[t.src_b + 2], a, a) += cplx(0, wj * Q);

@@ -9,6 +9,12 @@
 
 namespace porta {
 
+// Sign of the Hanle (magnetic) term of the update: the unknowns S^K_Q follow the
+// convention of J^K_Q (the complex conjugates of the atomic rho^K_Q), in which the
+// counterclockwise Larmor precession of the atom about B (Lande factor > 0) reads
+//   S^K_Q - i (1-eps) Gamma_u sum_Q' K_QQ'(B) S^K_Q' = (1-eps) J^K_Q + eps B delta_K0
+constexpr double kHanleSense = -1.0;
+
 // invn[m][v] = 1 / sum_j w_j exp(-(x_j - vel_v mu_m)^2): the profile is
 // renormalized on the frequency quadrature for each voxel and direction.
 template <typename Real>
@@ -125,7 +131,7 @@ __global__ void see_kernel(long long nvox, int nl, int model, double bcrit, cons
             const double dS = ((1.0 - e) * J[0] + f0 - S00) / (1.0 - (1.0 - e) * lstar[v]);
             const double S00n = S00 + dS;
             const double bx = bvec[v], by = bvec[nvox + v], bz = bvec[2 * nvox + v];
-            const double gam = (1.0 - e) / bcrit;   // Gamma = (1-eps) |B| / bcrit; times B/|B| below
+            const double gam = kHanleSense * (1.0 - e) / bcrit;   // Gamma = (1-eps) |B| / bcrit; times B/|B| below
             double r[5], x[5];
 #pragma unroll
             for (int c = 0; c < 5; ++c) r[c] = (1.0 - e) * J[1 + c] + (src ? src[v * nl + 1 + c] : 0.0);
@@ -240,7 +246,7 @@ __global__ void see_apply_kernel(long long nvox, int nl, int model, double bcrit
     double a[6];
     a[0] = s[0] - (1.0 - e) * J[0];
     if (model != PORTA_MODEL_TWOLEVEL_UNPOL) {
-        const double gam = (1.0 - e) / bcrit;
+        const double gam = kHanleSense * (1.0 - e) / bcrit;
         double y[5];
         hanle_apply5(gam * bvec[v], gam * bvec[nvox + v], gam * bvec[2 * nvox + v], s + 1, y);
 #pragma unroll
@@ -257,11 +263,11 @@ __global__ void see_apply_kernel(long long nvox, int nl, int model, double bcrit
 // Reverse mode of the Jacobi update (src as in see_kernel): from g = dL/d(rho
 // after the update) to dL/drho through the explicit S^0_0 term (overwritten),
 // dL/dJ^K_Q and dL/dLambda-bar* (overwritten), dL/d(thermal term) and, through
-// the Hanle matrix M = 1 + sum_c g_c E_c (affine in g = (1-eps) B / bcrit),
+// the Hanle matrix M = 1 + sum_c g_c E_c (affine in g = kHanleSense (1-eps) B / bcrit),
 // dL/dB (both added):
 //   S00' = S00 + ((1-eps) J00 + f - S00) / D,  D = 1 - (1-eps) Lambda*,
 //   S2'  = M^-1 ((1-eps) J2 + f2),  dL/dJ2 = (1-eps) M^-T g2,
-//   dL/dB_c = -(1-eps)/bcrit (M^-T g2) . E_c S2'.
+//   dL/dB_c = -kHanleSense (1-eps)/bcrit (M^-T g2) . E_c S2'.
 __global__ void see_vjp_kernel(long long nvox, int nl, int model, double bcrit, const double *eps, const double *bpl,
                                const double *bvec, const double *jkq, const double *lstar, const double *src,
                                const double *rho, const double *g, double *g_rho, double *g_jkq, double *g_lstar,
@@ -279,7 +285,7 @@ __global__ void see_vjp_kernel(long long nvox, int nl, int model, double bcrit, 
     g_lstar[v] = gv[0] * num * (1.0 - e) / (D * D);
     g_f[v] += gv[0] / D;
     if (model == PORTA_MODEL_TWOLEVEL_UNPOL) return;
-    const double gam = (1.0 - e) / bcrit;
+    const double gam = kHanleSense * (1.0 - e) / bcrit;
     const double gx = gam * bvec[v], gy = gam * bvec[nvox + v], gz = gam * bvec[2 * nvox + v];
     double r[5], s2[5], z[5];
 #pragma unroll

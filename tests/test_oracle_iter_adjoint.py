@@ -167,7 +167,10 @@ def test_gradient_through_iterations_matches_central_differences(pol):
     def check(name, make, x0, g, h=1e-4):
         """Richardson-extrapolated central differences of the quadratic loss, formed
         exactly from the outputs (sum (o+ - o-)(o+ + o- - 2 t)); components whose
-        steps h and h/2 disagree (a control-point branch changes) are skipped"""
+        steps h and h/2 disagree by more than 1e-5 relative are skipped: for a smooth
+        loss they agree to O(h^2) ~ 1e-8, so a larger gap means a BESSER control
+        point changes branch inside the interval (the kink of Sec. 3.2), where
+        neither difference is a derivative"""
         scale = np.max(np.abs(g))
         fails = checked = 0
         for i in range(x0.size):
@@ -178,7 +181,7 @@ def test_gradient_through_iterations_matches_central_differences(pol):
                 op, om = make(xp), make(xm)
                 return np.sum((op - om) * (op + om - 2 * target)) / (2 * d)
             c1, c2 = cd(h), cd(h / 2)
-            if abs(c1 - c2) > 1e-4 * abs(c2) + 1e-8 * scale:
+            if abs(c1 - c2) > 1e-5 * abs(c2) + 1e-8 * scale:
                 continue
             checked += 1
             if abs((4 * c2 - c1) / 3 - g.flat[i]) > 1e-6 * scale + 1e-5 * abs(c2):

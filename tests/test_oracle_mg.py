@@ -83,7 +83,7 @@ def test_see_apply_and_source_term_update(pol):
     if pol:
         B = np.stack([atm["bx"], atm["by"], atm["bz"]], -1)
         for idx in [(0, 0, 0), (3, 2, 1), (6, 3, 3)]:
-            gam = (1 - e[idx]) * np.linalg.norm(B[idx]) / atm["bcrit"]
+            gam = -(1 - e[idx]) * np.linalg.norm(B[idx]) / atm["bcrit"]      # the -i of the magnetic term
             x = oracle.hanle_solve(gam, B[idx], A[idx] + (1 - e[idx]) * jkq[idx])
             assert np.allclose(x[1:], rho[idx][1:], rtol=1e-12, atol=1e-15)
     # Jacobi with a general source converges to a solution of A(S) = src
