@@ -294,3 +294,25 @@ def test_emergent_matches_1d_for_homogeneous_layers():
             ref = oracle.solve_1d(tau, S_z, atm["bpl"][0, 0, 0])
             assert np.allclose(out[d, j, ..., 0], ref[-1], rtol=1e-13)
             assert np.allclose(out[d, j, ..., 1:], 0.0, atol=1e-15)
+
+
+def test_jacobi_convergence_rate_is_that_of_delopar():
+    """Fig. 4: the Jacobi iteration converges at the same rate with BESSER as with
+    DELOPAR: the asymptotic reduction factor of the maximum change per iteration,
+    which the approximate operator Lambda* of each step (Eq. 13 for BESSER) sets,
+    agrees within 2 %."""
+    atm = synth.plane_parallel_box(2, 2, 40, modulation=0.0, eps=1e-3)
+    rates = {}
+    for meth in (oracle.BESSER, oracle.DELOPAR):
+        p = oracle.Problem(atm, 0, 3, 4, 5, method=meth)
+        rho = np.zeros((40, 2, 2, 1))
+        rho[..., 0] = atm["bpl"]
+        ch = []
+        for _ in range(40):
+            J, L = oracle.formal_solve(p, rho)
+            rho, c = oracle.see_update(p, J, L, rho)
+            ch.append(c)
+        ch = np.array(ch)
+        rates[meth] = np.mean(ch[-10:] / ch[-11:-1])
+    assert 0.5 < rates[oracle.BESSER] < 0.95
+    assert rates[oracle.BESSER] == pytest.approx(rates[oracle.DELOPAR], rel=0.02)
