@@ -11,7 +11,7 @@
  *                            transfer coefficients and I_M interpolated bilinearly
  *                            on the neighbouring horizontal planes. The
  *                            frequency-integrated Stokes parameters and Lambda*
- *                            (Eq. 13) are reduced on the fly per ray.
+ *                            (Eq. 14) are reduced on the fly per ray.
  *   porta_accumulate_jkq  -- Eq. 1: J^K_Q = sum_p sum_m w_m T^K_Q(p, Omega_m)
  *                            sum_nu wt_nu I_p, and the angle- and profile-averaged
  *                            Lambda-bar*, summed in FP64 in a fixed order.
@@ -75,6 +75,9 @@ extern "C" {
 
 /* size of the fixed device scratch array used by porta_formal_solve_noalloc */
 #define PORTA_NOALLOC_SCRATCH_BYTES (32u << 20)
+/* largest number of height levels porta_formal_solve_noalloc accepts (the heights
+   are passed to the device by value, inside a kernel argument block) */
+#define PORTA_NOALLOC_MAX_NZ 1024
 
 #define PORTA_MODEL_TWOLEVEL_UNPOL 0
 #define PORTA_MODEL_TWOLEVEL_HANLE 1
@@ -227,7 +230,7 @@ int porta_fill_info(const porta_ctx *c, int *cluster_size, int *nu_group, double
    work list in (0, 1) it takes. PORTA_EINVAL if the shape does not fit. */
 int porta_set_fill(porta_ctx *c, int cluster_size, int nu_group, double fraction);
 
-/* Diagnostic: the coefficients of the BESSER-DELO step (Eqs. 8-12; Table 1
+/* Diagnostic: the coefficients of the BESSER-DELO step (Eqs. 9-13; Table 1
    series at small optical path) exactly as the sweep kernels of the given
    precision evaluate them, for n upwind optical paths t (host array, t > 0):
    out[6*i + 0..5] = e^-t, psi'_M, psi'_O, omega_M, omega_O, omega_C (host).
@@ -250,12 +253,16 @@ int porta_eval_coefficients(int precision, int n, const double *t, double *out);
    holds until the process exits; the call allocates nothing, host or device.
    The polarized model needs about nvox * (48 + 20 * nray) bytes, e.g. 10^4
    voxels with 160 rays; larger problems are rejected with PORTA_ESCRATCH
-   before anything is enqueued. n_mu is limited to 32.
-   The first call on a device looks up the array's device address there
-   (cudaGetSymbolAddress with that device current); make that first call
-   before any stream capture. All calls share the array and it keeps the last
-   call's contents (each call writes every part it reads); calls that overlap
-   on the GPU race on it. */
+   before anything is enqueued, as are grids of more than PORTA_NOALLOC_MAX_NZ
+   levels. n_mu is limited to 32. The heights g->z are read on the host during
+   the call (they reach the device inside a kernel's argument block).
+   Every call looks up the array's device address on the current device
+   (cudaGetSymbolAddress with that device current; the lookup allocates
+   nothing, and a device reset between calls is therefore harmless); the first
+   call on a device also loads the library's device code there, so make that
+   first call before any stream capture. All calls share the array and it keeps
+   the last call's contents (each call writes every part it reads); calls that
+   overlap on the GPU race on it. */
 int porta_formal_solve_noalloc(const porta_grid *g, const porta_atom *a, const porta_quad *q,
                                const porta_atmos *atm, const double *rho, double *jkq, double *lstar,
                                void *stream);
@@ -312,7 +319,7 @@ int porta_adjoint_timing(const porta_ctx *c, float *forward_ms, float *adjoint_m
 /* Launch statistics of the last adjoint sweep (as porta_launch_info). */
 int porta_adjoint_info(const porta_ctx *c, int *clusters, int *cluster_size, int *nu_group, int *smem_bytes);
 
-/* Gradients through Jacobi iterations (reverse mode of Eqs. 12-13 composed
+/* Gradients through Jacobi iterations (reverse mode of Eq. 2 composed
    with the formal solution of Sec. 3; the paper has no counterpart).
    porta_iterate_ckpt runs niter Jacobi iterations from the current rho
    (formal solution, J^K_Q and Lambda-bar*, update, as porta_formal_solve,
@@ -328,7 +335,7 @@ int porta_iterate_ckpt(porta_ctx *c, int niter, int ckpt, double *max_change);
    porta_emergent_stokes) of the last iterate of porta_iterate_ckpt, as a
    function of per-voxel
      chi  (line-centre opacity; rho follows from the iterations),
-     f    (the thermal source term eps B of the update, Eq. 12),
+     f    (the thermal source term eps B of the update, Eq. 2),
      B    (magnetic field vector: Zeeman term of the sweeps and Hanle term of
            the update).
    The iterates are rebuilt from the checkpoints, each segment of ckpt
@@ -364,7 +371,7 @@ int porta_set_tape_limit(porta_ctx *c, long long bytes);
    adjoint launch shapes, outside these figures. */
 int porta_iterate_timing(const porta_ctx *c, float *ms);
 
-/* Non-linear multigrid (Sec. 6, full-approximation form). porta_mg_setup
+/* Non-linear multigrid (Sec. 5, full-approximation form). porta_mg_setup
    builds nlevels - 1 coarser grids by keeping every other node on each axis
    (coarse (i, j, k) = fine (2i, 2j, 2k); nz -> (nz + 1)/2 for odd nz, nz/2
    for even nz), each a context of its own with the same atom, quadratures
@@ -372,7 +379,7 @@ int porta_iterate_timing(const porta_ctx *c, float *ms);
    divisible by 2^(nlevels - 1) (PORTA_EINVAL otherwise); requires the
    atmosphere (PORTA_ESTATE); call it again after porta_set_atmosphere. The
    method needs the coarse grids to resolve the transfer problem (about one
-   plane per decade of optical depth or more, Sec. 6.3). On a multilevel
+   plane per decade of optical depth or more, Sec. 5.3). On a multilevel
    context (porta_ml_create) the coarse levels are multilevel contexts of the
    same atom with the opacity scale, temperature and velocity at the
    coincident nodes. */
@@ -382,15 +389,15 @@ int porta_mg_setup(porta_ctx *c, int nlevels);
    not NULL, shapes[3 l + 0..2] = nx, ny, nz of level l, finest first. */
 int porta_mg_levels(const porta_ctx *c, int *nlevels, int *shapes);
 
-/* One V-cycle (Eqs. 14-18) from the finest level: npre Jacobi iterations;
+/* One V-cycle (Eqs. 30-34) from the finest level: npre Jacobi iterations;
    residual r = f - A(rho), A the statistical-equilibrium operator (J^K_Q from
    a formal solution) and f = eps B delta_K0; restriction of rho and r; coarse
    right-hand side A_c(R rho) + R r; the same cycle on the coarser level
    (ncoarse Jacobi iterations on the coarsest); correction rho += P (rho_c -
-   R rho); npost Jacobi iterations (Sec. 6.3 uses npre = 2, npost = 4).
+   R rho); npost Jacobi iterations (Sec. 5.3 uses npre = 2, npost = 4).
    Prolongation P: tri-linear, linear in height, linear extrapolation above
    the top coarse plane (even nz); restriction R: the transpose of P normalized
-   to keep constants (adjoint of the tri-linear prolongation, Sec. 6.2).
+   to keep constants (adjoint of the tri-linear prolongation, Sec. 5.2).
    max_change (host, may be NULL): the maximum relative change of rho over the
    cycle, defined as for porta_see_update (synchronizes). All work is
    enqueued on the context's stream. Multilevel contexts: the unknowns are the

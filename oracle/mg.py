@@ -1,17 +1,17 @@
 """Non-linear multigrid (FAS) V-cycle of the oracle (test infrastructure only).
 
-Sec. 6 of Stepan & Trujillo Bueno (2013): with the statistical-equilibrium
+Sec. 5 of Stepan & Trujillo Bueno (2013): with the statistical-equilibrium
 equations written as A_l(rho) = f_l on grid level l (A from the formal
 solution, f = eps B delta_K0 on the finest grid),
-  residual         r_l = f_l - A_l(rho_l)                                  (Eq. 14)
-  coarse equation  A_{l-1}(rho') = A_{l-1}(R rho_l) + R r_l                (Eq. 17)
-  correction       rho_l <- rho_l + P (rho' - R rho_l)                     (Eq. 18)
-with Jacobi smoothing before and after the coarse-grid correction (Sec. 6.3:
+  residual         r_l = f_l - A_l(rho_l)                                  (Eq. 30)
+  coarse equation  A_{l-1}(rho') = A_{l-1}(R rho_l) + R r_l                (Eq. 33)
+  correction       rho_l <- rho_l + P (rho' - R rho_l)                     (Eq. 34)
+with Jacobi smoothing before and after the coarse-grid correction (Sec. 5.3:
 2 pre- and 4 post-smoothing iterations). The coarse grid keeps every other
-node on each axis (coarse node (i, j, k) = fine node (2i, 2j, 2k), Sec. 6.1);
+node on each axis (coarse node (i, j, k) = fine node (2i, 2j, 2k), Sec. 5.1);
 the atmosphere on a coarse grid is the fine one at those nodes.
 
-Prolongation P (Sec. 6.2): tri-linear -- a fine node that coincides with a
+Prolongation P (Sec. 5.2): tri-linear -- a fine node that coincides with a
 coarse node takes its value, others interpolate linearly along each axis in
 which they fall between coarse nodes (periodic in x and y; linear in the
 height z). With an even number of fine planes the top fine plane lies above

@@ -36,7 +36,7 @@ equation of level 0 is replaced by sum_i n_i = 1. For two levels this is the
 two-level update of this package with eps' = C'/(A + C'), C' = C_ul (1 -
 exp(-dE/kT)).
 
-The non-linear multigrid cycle of Sec. 6 (Eqs. 14-18) carries over with the
+The non-linear multigrid cycle of Sec. 5 (Eqs. 30-34) carries over with the
 populations as the unknowns: A(n) = f with A(n)_0 = sum_i n_i and A(n)_i =
 (M n)_i (the plain rates of the formal solution's Jbar) for i >= 1, f = (1, 0,
 ..., 0) on the finest grid and f = A_c(R n) + R r on a coarser one, whose
@@ -192,8 +192,8 @@ def iterate(atm, atom, pops, quad, n):
     return pops, change
 
 
-# ---------------------------------------------------------------- multigrid (Sec. 6)
-# The non-linear multigrid cycle of Sec. 6 with the populations as the
+# ---------------------------------------------------------------- multigrid (Sec. 5)
+# The non-linear multigrid cycle of Sec. 5 with the populations as the
 # unknowns: A(n) = f with f = (1, 0, ..., 0) on the finest grid; the grid
 # transfer operators are those of oracle/mg.py.
 
@@ -245,7 +245,7 @@ def jacobi(atm, atom, pops, quad, src, n):
 
 
 def vcycle(levels, atom, quad, pops, src=None, l=0, npre=2, npost=4, ncoarse=8):
-    """One V-cycle from level l down to the coarsest (Eqs. 14-18); returns the
+    """One V-cycle from level l down to the coarsest (Eqs. 30-34); returns the
     new populations of level l. src None on the finest level: f = (1, 0, ...)."""
     from .mg import prolong, restrict
     lev = levels[l]

@@ -475,7 +475,7 @@ def iterate(atm, atom, tab, x, quad, n):
     return x, change
 
 
-# ---------------------------------------------------------------- multigrid (Sec. 6)
+# ---------------------------------------------------------------- multigrid (Sec. 5)
 # The cycle of oracle/ml.py with the real multipoles as the unknowns: A(x)_row0 =
 # sum_J sqrt(2J+1) rho^0_0(J), the other rows the plain rate equations of the
 # formal solution's Jbar; f = e_row0 on the finest grid.

@@ -1,6 +1,6 @@
 /*
  * BESSER formal solver of the oracle (test infrastructure only).
- * Sec. 3.2 (control points, steps 1-9), Sec. 3.3 (Eqs. 7-13, Table 1).
+ * Sec. 3.2 (control points, steps 1-9), Sec. 3.3 (Eqs. 7-14, Table 1).
  */
 #include <math.h>
 #include "or_common.h"
@@ -49,9 +49,9 @@ void or_coeffs(double t, double c[6])
         c[2] = (e + t - 1.0) / t;                  /* psi'_O */
     }
     double t2 = t * t;
-    c[3] = t < 0.14 ? series_omega_m(t) : (2.0 - e * (t2 + 2.0 * t + 2.0)) / t2;   /* Eq. 10 */
-    c[4] = t < 0.18 ? series_omega_o(t) : 1.0 - 2.0 * (e + t - 1.0) / t2;          /* Eq. 11 */
-    c[5] = t < 0.18 ? series_omega_c(t) : 2.0 * (t - 2.0 + e * (t + 2.0)) / t2;    /* Eq. 12 */
+    c[3] = t < 0.14 ? series_omega_m(t) : (2.0 - e * (t2 + 2.0 * t + 2.0)) / t2;   /* Eq. 11 */
+    c[4] = t < 0.18 ? series_omega_o(t) : 1.0 - 2.0 * (e + t - 1.0) / t2;          /* Eq. 12 */
+    c[5] = t < 0.18 ? series_omega_c(t) : 2.0 * (t - 2.0 + e * (t + 2.0)) / t2;    /* Eq. 13 */
     OR_FLOPS(30);
 }
 
@@ -146,12 +146,12 @@ static int gauss_solve(int n, double A[4][4], double *b, double *x)
 }
 
 /*
- * One BESSER step at point O (Eqs. 7-13):
+ * One BESSER step at point O (Eqs. 7-14):
  *   kappa^-1 I_O = [e^-tau 1 - psi'_M K'_M] I_M + w_M S_M + w_O S_O + w_C c_M,
  *   kappa^-1 = 1 + psi'_O K'_O,
  * with S = eps/eta_I, tau_MO = (eta_M + eta_O)/2 * ds_M and
  * tau_OP = (eta_O + eta_P)/2 * ds_P (trapezoid along the segments).
- * Lambda* = w_O + w_C c_M(0,1,0): the paper's w_O + w_C (Eq. 13) where a
+ * Lambda* = w_O + w_C c_M(0,1,0): the paper's w_O + w_C (Eq. 14) where a
  * downwind point exists, w_O + w_C/2 on the last plane of a sweep.
  */
 int or_step(int ns, const double *IM, const double *etaM, const double *epsM,
@@ -211,7 +211,7 @@ int or_step(int ns, const double *IM, const double *etaM, const double *epsM,
  * ------------------------------------------------------------------------ */
 
 /* d/dt of (e^-t, psi'_M, psi'_O, w_M, w_O, w_C), differentiating the closed
-   forms of Eqs. 8-12 and writing the result through the coefficients
+   forms of Eqs. 9-13 and writing the result through the coefficients
    themselves:
      de = -e,               dpsi'_M = e - psi'_M/t,   dpsi'_O = psi'_M/t,
      dw_M = e - 2 w_M/t,    dw_O = w_C/t,             dw_C = 2 (psi'_M - w_C)/t.

@@ -2,9 +2,9 @@
  * Quadratures of the oracle (test infrastructure only).
  *
  * Angles: Gauss-Legendre inclinations per hemisphere and equally weighted
- * (trapezoid on a periodic interval) azimuths, as in App. A ("five inclination
- * angles per octant (Gaussian) and four azimuthal angles per octant
- * (trapezoidal)"). Azimuths sit at the interval midpoints chi_a = (a+1/2) 2pi/Nchi.
+ * (trapezoid on a periodic interval) azimuths, the product rule of App. A
+ * (Gauss inclinations x trapezoid azimuths per octant). Azimuths sit at the
+ * interval midpoints chi_a = (a+1/2) 2pi/Nchi.
  * Frequencies: uniform grid on [-x_max, x_max] with trapezoid weights.
  */
 #include <math.h>

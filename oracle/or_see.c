@@ -140,7 +140,7 @@ int or_see_apply(const or_problem *p, const double *jkq, const double *rho, doub
  * (nvox * nl, the layout of rho): the update of or_see_update with eps B
  * replaced by src^0_0 and src^2_Q added to (1-eps) J^2_Q. src = NULL is the
  * two-level problem itself (src = eps B delta_K0 delta_Q0). The coarse-grid
- * problems of the multigrid method have this form (Sec. 6.1).
+ * problems of the multigrid method have this form (Sec. 5.1).
  */
 int or_see_update_src(const or_problem *p, const double *jkq, const double *lstar, const double *src, double *rho,
                       double *max_change)

@@ -1,5 +1,5 @@
 // Derivatives of the formal-solver step for the adjoint sweep (adjoint.cu):
-// t-derivatives of the Bezier/DELO coefficients (Eqs. 8-12) and the partial
+// t-derivatives of the Bezier/DELO coefficients (Eqs. 9-13) and the partial
 // derivatives of the BESSER control point (Sec. 3.2) on the branch it takes.
 #pragma once
 #include "device_math.cuh"
@@ -8,7 +8,7 @@ namespace porta {
 
 // ---------------------------------------------------------------------------
 // Derivatives for the adjoint sweep.
-// d/dt of the step coefficients (Eqs. 8-12), from differentiating the closed
+// d/dt of the step coefficients (Eqs. 9-13), from differentiating the closed
 // forms and writing the result through the coefficients themselves:
 //   de = -e,              dpsi'_M = e - psi'_M/t,   dpsi'_O = psi'_M/t,
 //   dw_M = e - 2 w_M/t,   dw_O = w_C/t,             dw_C = 2 (psi'_M - w_C)/t.

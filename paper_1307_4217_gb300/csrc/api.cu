@@ -1209,7 +1209,7 @@ int iterate_vjp_t(porta_ctx *c, int ndir, const double *mu, const double *chi, c
     return rc ? rc : rc2;
 }
 
-// ---------------------------------------------------------------- multigrid (Sec. 6)
+// ---------------------------------------------------------------- multigrid (Sec. 5)
 
 int coarse_nz(int nz) { return nz % 2 ? (nz + 1) / 2 : nz / 2; }
 
@@ -1322,7 +1322,7 @@ int mg_jacobi(porta_ctx *L, const double *src, int n)
     return PORTA_OK;
 }
 
-// One V-cycle (Eqs. 14-18) from level l of levels[0..n) down to the coarsest.
+// One V-cycle (Eqs. 30-34) from level l of levels[0..n) down to the coarsest.
 int mg_vcycle(porta_ctx *const *levels, int n, int l, int npre, int npost, int ncoarse)
 {
     porta_ctx *L = levels[l];

@@ -11,7 +11,7 @@ namespace porta {
 //   e = exp(-t),
 //   psi'_M = (1 - e (1 + t)) / t,          psi'_O = (e + t - 1) / t,
 //   w_M = (2 - e (t^2 + 2t + 2)) / t^2,    w_O = 1 - 2 (e + t - 1) / t^2,
-//   w_C = 2 (t - 2 + e (t + 2)) / t^2      (Eqs. 8-12).
+//   w_C = 2 (t - 2 + e (t + 2)) / t^2      (Eqs. 9-13).
 // Below a crossover the closed forms lose digits to cancellation and the
 // Taylor series at t = 0 is used instead (Table 1 for double precision).
 // Series coefficients of t^k, k >= 1, from expanding the closed forms:

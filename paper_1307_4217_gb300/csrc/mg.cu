@@ -1,6 +1,6 @@
-// Grid transfer of the non-linear multigrid method (Sec. 6): the coarse grid
+// Grid transfer of the non-linear multigrid method (Sec. 5): the coarse grid
 // keeps every other node on each axis (coarse (i, j, k) = fine (2i, 2j, 2k),
-// Sec. 6.1). Prolongation is tri-linear (Sec. 6.2): a fine node on a coarse
+// Sec. 5.1). Prolongation is tri-linear (Sec. 5.2): a fine node on a coarse
 // node takes its value, others interpolate along each axis where they fall
 // between coarse nodes (periodic in x and y, linear in the height z; above the
 // top coarse plane -- an even number of fine planes -- linear extrapolation

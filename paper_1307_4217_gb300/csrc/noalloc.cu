@@ -19,7 +19,6 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
-#include <mutex>
 
 #include "porta.h"
 #include "porta_internal.cuh"
@@ -30,8 +29,8 @@ using namespace porta;
 namespace {
 
 constexpr size_t kScratchBytes = (size_t)PORTA_NOALLOC_SCRATCH_BYTES;
-constexpr int kMaxDevices = 64;
 constexpr int kMaxMu = 32;
+constexpr int kMaxNz = PORTA_NOALLOC_MAX_NZ;   // heights travel in the kernel's argument block
 
 }  // namespace
 
@@ -39,26 +38,18 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[PORTA_NOALLOC_S
 
 namespace {
 
-std::mutex g_mutex;
-void *g_scratch_ptr[kMaxDevices] = {};
-
-// Device address of the scratch array on the current device (looked up once
-// per device with that device current; the host-side symbol itself is not a
-// device address).
+// Device address of the scratch array on the current device. The host-side
+// symbol itself is not a device address. The address is looked up on every
+// call with the caller's device current: the lookup allocates nothing, and a
+// cached address would go stale if the caller reset the device (a new context
+// loads the module again, possibly elsewhere). The first call on a device also
+// loads the library's device code there.
 cudaError_t scratch_address(void **out)
 {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_mutex);
-    if (!g_scratch_ptr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_ptr[dev] = p;
-    }
-    *out = g_scratch_ptr[dev];
+    *out = p;
     return cudaSuccess;
 }
 
@@ -102,7 +93,7 @@ struct TableArgs {
     int n_mu, n_chi, n_nu, nx, ny, nz;
     double lx, ly, x_max;
     GaussNodes gl;
-    const double *z;
+    double z[kMaxNz];
     BoxDev *box;
     RayDev<float> *rays;
     PlaneGeom<float> *geom;
@@ -190,7 +181,7 @@ __global__ void noalloc_tables_kernel(TableArgs a)
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-    size_t atm, rho, invn, part, geom, rays, xf, xd, mu, tw, z, box, total;
+    size_t atm, rho, invn, part, geom, rays, xf, xd, mu, tw, box, total;
 };
 
 Layout layout(long long nvox, int nray, int nz, int nnu, int nl, int ns)
@@ -207,7 +198,6 @@ Layout layout(long long nvox, int nray, int nz, int nnu, int nl, int ns)
     L.xd = o;   o = align256(o + 2 * (size_t)nnu * sizeof(double));
     L.mu = o;   o = align256(o + (size_t)nray * sizeof(double));
     L.tw = o;   o = align256(o + (size_t)nray * 19 * sizeof(double));
-    L.z = o;    o = align256(o + (size_t)nz * sizeof(double));
     L.box = o;  o = align256(o + sizeof(BoxDev));
     L.total = o;
     return L;
@@ -263,13 +253,13 @@ int run(const porta_grid *g, const porta_atom *at, const porta_quad *q, const po
     }
     if (best.cluster == 0) return PORTA_EINVAL;
 
-    cudaError_t e = cudaMemcpyAsync(B + L.z, g->z, g->nz * sizeof(double), cudaMemcpyHostToDevice, st);
+    cudaError_t e = cudaSuccess;
     TableArgs ta{};
     ta.n_mu = q->n_mu; ta.n_chi = q->n_chi; ta.n_nu = q->n_nu;
     ta.nx = g->nx; ta.ny = g->ny; ta.nz = g->nz;
     ta.lx = g->lx; ta.ly = g->ly; ta.x_max = q->x_max;
     gauss_nodes(q->n_mu, ta.gl);
-    ta.z = (const double *)(B + L.z);
+    for (int k = 0; k < g->nz; ++k) ta.z[k] = g->z[k];
     ta.box = (BoxDev *)(B + L.box);
     ta.rays = (RayDev<float> *)(B + L.rays);
     ta.geom = (PlaneGeom<float> *)(B + L.geom);
@@ -330,6 +320,7 @@ extern "C" int porta_formal_solve_noalloc(const porta_grid *g, const porta_atom 
 {
     if (!g || !at || !q || !atm || !g->z || !rho || !jkq || !lstar) return PORTA_EINVAL;
     if (g->nx < 1 || g->ny < 1 || g->nz < 2 || !(g->lx > 0) || !(g->ly > 0)) return PORTA_EINVAL;
+    if (g->nz > kMaxNz) return PORTA_ESCRATCH;
     if (q->n_mu < 1 || q->n_mu > kMaxMu || q->n_chi < 1 || q->n_nu < 1 || !(q->x_max > 0)) return PORTA_EINVAL;
     for (int k = 1; k < g->nz; ++k)
         if (!(g->z[k] > g->z[k - 1])) return PORTA_EINVAL;

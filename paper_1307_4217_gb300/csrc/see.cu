@@ -181,7 +181,7 @@ __global__ void to_real_kernel(long long n, const double *x, Real *y)
     if (i < n) y[i] = (Real)x[i];
 }
 
-// diagnostic: the sweep's coefficient function (Eqs. 8-12 / Table 1) on the GPU
+// diagnostic: the sweep's coefficient function (Eqs. 9-13 / Table 1) on the GPU
 template <typename Real>
 __global__ void coefficients_kernel(int n, const double *t, double *out)
 {

@@ -390,7 +390,7 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<Real> &a, cg::cluster
                         IO[2] = rhs[2];
                     }
                     StokesIO<Real, NS>::store(iw + f * iplane, ichunk, l * nx + c, IO);
-                    // a8: Lambda* (Eq. 13; w_O + w_C/2 on the last plane) and accumulation
+                    // a8: Lambda* (Eq. 14; w_O + w_C/2 on the last plane) and accumulation
                     if constexpr (MODE == MODE_JKQ) {
                         const Real ls = co.wo + (has_p ? co.wc : Real(0.5) * co.wc);
                         const Real wt = a.wf[j] * phO * invnO;

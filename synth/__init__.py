@@ -5,8 +5,8 @@ It holds none of the method's arithmetic (no quadratures, no transfer, no
 statistical equilibrium) and is shared by the tests, the oracle runs and the
 benchmark so that both sides see identical inputs.
 
-Workloads (the paper's FAL-C / Ca II and Ly-alpha models are replaced by
-synthetic atmospheres of comparable scale):
+Workloads (the paper's FAL-C / Ca II and Ly-alpha models are not available;
+synthetic atmospheres of comparable scale stand in for them):
 
 * ``plane_parallel_box``  16x16x32 unpolarized two-level atom (eps = 1e-2, B = 1),
   exponential opacity with an optional horizontal modulation.

@@ -1,4 +1,4 @@
-"""The exponential-integral coefficients of the BESSER-DELO step (Eqs. 8-12)
+"""The exponential-integral coefficients of the BESSER-DELO step (Eqs. 9-13)
 as the sweep kernels evaluate them on the GPU, against 40-digit evaluations of
 the closed forms.
 

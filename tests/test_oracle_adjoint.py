@@ -3,7 +3,7 @@
 The adjoint is checked against central finite differences of the oracle's own
 forward solution (itself pinned by the tests of test_oracle_sweep.py), piece
 by piece (step coefficients against mpmath derivatives of the closed forms of
-Eqs. 8-12, BESSER control point, 4x4 step) and as a whole on tiny grids.
+Eqs. 9-13, BESSER control point, 4x4 step) and as a whole on tiny grids.
 """
 import numpy as np
 import pytest

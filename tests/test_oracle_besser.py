@@ -37,7 +37,7 @@ def test_omega_are_bezier_integrals(tau):
 
 def test_coefficient_identities_and_lambda_range():
     mpmath.mp.dps = 40
-    """w_M + w_O + w_C = psi'_M + psi'_O = 1 - e^-tau, and Lambda* = w_O + w_C in [0, 1) (Eq. 13)."""
+    """w_M + w_O + w_C = psi'_M + psi'_O = 1 - e^-tau, and Lambda* = w_O + w_C in [0, 1) (Eq. 14)."""
     for tau in np.geomspace(1e-8, 1e4, 400):
         c = oracle.coeffs(tau)
         one_m_e = -math.expm1(-tau)
@@ -45,13 +45,13 @@ def test_coefficient_identities_and_lambda_range():
         assert c[1] + c[2] == pytest.approx(one_m_e, rel=1e-12)
         lam = c[4] + c[5]
         assert 0.0 <= lam < 1.0
-        # Eq. 13 closed form, evaluated with 40 significant digits
+        # Eq. 14 closed form, evaluated with 40 significant digits
         t = mpmath.mpf(tau)
         assert lam == pytest.approx(float(1 + 2 * (mpmath.exp(-t) * (1 + t) - 1) / t**2), rel=1e-11)
 
 
 def test_table1_is_taylor_series_of_closed_forms():
-    """The printed Table 1 polynomials are the Taylor series of Eqs. 10-12 to t^8,
+    """The printed Table 1 polynomials are the Taylor series of Eqs. 11-13 to t^8,
     and the oracle's coefficients agree with them below the printed thresholds."""
     sp = pytest.importorskip("sympy")
     t = sp.symbols("t")
@@ -88,7 +88,7 @@ def _Ia(z):
 
 
 def test_sigmoid_analytic_solution_and_printed_boundary():
-    """Eq. 15 solves dI/dz = S - I with S from Eq. 14; its value at z = -12 is the printed 2.77176e-7."""
+    """Eq. 17 solves dI/dz = S - I with S from Eq. 15; its value at z = -12 is the printed 2.77176e-7."""
     val, tol = [float(v) for v in open(os.path.join(GOLDEN, "sigmoid_boundary.txt")).read().split("\n")[-2].split()]
     assert _Ia(-12.0) == pytest.approx(val, rel=tol)
     mpmath.mp.dps = 50

@@ -1,6 +1,6 @@
-"""Pins of the oracle's multigrid pieces: transfer operators (Sec. 6.2), the
+"""Pins of the oracle's multigrid pieces: transfer operators (Sec. 5.2), the
 statistical-equilibrium operator A and its Jacobi update with a source term,
-and the FAS V-cycle (Sec. 6.1), against definitions, brute force and the
+and the FAS V-cycle (Sec. 5.1), against definitions, brute force and the
 Jacobi fixed point."""
 import numpy as np
 import pytest
@@ -101,7 +101,7 @@ def _residual(level, rho):
 @pytest.mark.parametrize("pol,nz", [(False, 33), (True, 32)])
 def test_vcycles_solve_the_fine_grid_equations(pol, nz):
     # 8 planes per decade of optical depth on the finest grid, 2 on the coarsest
-    # (the method needs the coarse grids to resolve the transfer problem, Sec. 6.3)
+    # (the method needs the coarse grids to resolve the transfer problem, Sec. 5.3)
     atm = _atm(8, 8, nz, pol, seed=5)
     atm["eps"] = np.full_like(atm["eps"], 1e-2)
     model = 1 if pol else 0

@@ -299,7 +299,7 @@ def test_emergent_matches_1d_for_homogeneous_layers():
 def test_jacobi_convergence_rate_is_that_of_delopar():
     """Fig. 4: the Jacobi iteration converges at the same rate with BESSER as with
     DELOPAR: the asymptotic reduction factor of the maximum change per iteration,
-    which the approximate operator Lambda* of each step (Eq. 13 for BESSER) sets,
+    which the approximate operator Lambda* of each step (Eq. 14 for BESSER) sets,
     agrees within 2 %."""
     atm = synth.plane_parallel_box(2, 2, 40, modulation=0.0, eps=1e-3)
     rates = {}
