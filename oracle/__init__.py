@@ -97,6 +97,8 @@ def _declare(L):
         "or_flops_reset": (None, [_I]),
         "or_flops_get": (ctypes.c_longlong, []),
         "or_nray": (_I, [_P]),
+        "or_branch_sig_reset": (None, [_I]),
+        "or_branch_sig_get": (ctypes.c_ulonglong, []),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -388,3 +390,19 @@ def flops_per_update(prob, rho, m=0, j=None):
     n = L.or_flops_get()
     L.or_flops_reset(0)
     return n / prob.nvox
+
+
+def branch_signature(fn, *args, **kw):
+    """Run fn(*args, **kw) with the control-point branch recorder on; returns
+    (fn's result, signature). The signature hashes the sequence of BESSER branches
+    (Sec. 3.2, steps 2, 6, 7, the parabola, and the linear last step) of every
+    control point the oracle evaluated, in order: equal signatures mean the same
+    branch was taken at every control point."""
+    L = lib()
+    L.or_branch_sig_reset(1)
+    try:
+        out = fn(*args, **kw)
+        sig = int(L.or_branch_sig_get())
+    finally:
+        L.or_branch_sig_reset(0)
+    return out, sig

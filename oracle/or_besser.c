@@ -66,7 +66,7 @@ static double dmax(double a, double b) { return a > b ? a : b; }
  */
 double or_control_point(double yM, double yO, double yP, double hM, double hP, int has_p, int method)
 {
-    if (!has_p) { OR_FLOPS(2); return 0.5 * (yM + yO); }
+    if (!has_p) { OR_FLOPS(2); OR_BRANCH(4); return 0.5 * (yM + yO); }
     double dM = (yO - yM) / hM;                          /* step 1 */
     double dP = (yP - yO) / hP;
     OR_FLOPS(4);
@@ -76,15 +76,18 @@ double or_control_point(double yM, double yO, double yP, double hM, double hP, i
         return yO - 0.5 * hM * yp;
     }
     OR_FLOPS(1);
-    if (dM * dP <= 0.0) return yO;                       /* step 2 */
+    if (dM * dP <= 0.0) { OR_BRANCH(0); return yO; }     /* step 2 */
     double yp = (hM * dP + hP * dM) / (hM + hP);         /* step 3, Eq. 6 */
     double cM = yO - 0.5 * hM * yp;                      /* step 4 */
     double cP = yO + 0.5 * hP * yp;
     OR_FLOPS(11);
-    if (cM < dmin(yM, yO) || cM > dmax(yM, yO))          /* step 5 */
+    if (cM < dmin(yM, yO) || cM > dmax(yM, yO)) {        /* step 5 */
+        OR_BRANCH(1);
         return yM;                                       /* step 6 */
-    if (cP < dmin(yO, yP) || cP > dmax(yO, yP))          /* step 7 */
-        cP = yP;
+    }
+    int clip = cP < dmin(yO, yP) || cP > dmax(yO, yP);   /* step 7 */
+    if (clip) cP = yP;
+    OR_BRANCH(clip ? 2 : 3);
     yp = (cP - yO) / (0.5 * hP);                         /* step 8 */
     OR_FLOPS(6);
     return yO - 0.5 * hM * yp;                           /* step 9 */

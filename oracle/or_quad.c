@@ -15,6 +15,10 @@ int or_count_on = 0;
 long long or_count = 0;
 void or_flops_reset(int enable) { or_count_on = enable; or_count = 0; }
 long long or_flops_get(void) { return or_count; }
+int or_sig_on = 0;
+unsigned long long or_sig = 14695981039346656037ULL;
+void or_branch_sig_reset(int enable) { or_sig_on = enable; or_sig = 14695981039346656037ULL; }
+unsigned long long or_branch_sig_get(void) { return or_sig; }
 
 int or_nl(int model) { return model == OR_MODEL_UNPOL ? 1 : 6; }
 int or_ns(int model) { return model == OR_MODEL_UNPOL ? 1 : 4; }

@@ -126,6 +126,9 @@ int or_step_vjp(int ns, const double *IM, const double *etaM, const double *epsM
 /* flop counter for one update (counted once per voxel.ray.frequency) */
 void or_flops_reset(int enable);
 long long or_flops_get(void);
+/* branch signature of the control points evaluated while recording (test support) */
+void or_branch_sig_reset(int enable);
+unsigned long long or_branch_sig_get(void);
 
 #ifdef __cplusplus
 }

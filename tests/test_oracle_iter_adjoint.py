@@ -164,29 +164,42 @@ def test_gradient_through_iterations_matches_central_differences(pol):
         _, o = diff.forward(a, model, quad, f, 3, mu, az)
         return o
 
-    def check(name, make, x0, g, h=1e-4):
+    def check(name, make, x0, g, h=1e-5, signed=False):
         """Richardson-extrapolated central differences of the quadratic loss, formed
-        exactly from the outputs (sum (o+ - o-)(o+ + o- - 2 t)); components whose
-        steps h and h/2 disagree by more than 1e-5 relative are skipped: for a smooth
-        loss they agree to O(h^2) ~ 1e-8, so a larger gap means a BESSER control
-        point changes branch inside the interval (the kink of Sec. 3.2), where
-        neither difference is a derivative"""
+        exactly from the outputs (sum (o+ - o-)(o+ + o- - 2 t)). A sample is rejected
+        only where a BESSER control point changes branch inside the interval (the
+        piecewise-smooth control point of Sec. 3.2, where a difference is not a
+        derivative): the oracle's branch signature at x0 +- h and x0 +- h/2 must equal
+        the one at x0. The rejected components are reported; at least 80 % are kept."""
+        _, sig0 = oracle.branch_signature(make, x0)
         scale = np.max(np.abs(g))
-        fails = checked = 0
+        # steps relative to each component; for a signed parameter (the field)
+        # at least relative to its RMS, since a step relative to a near-zero
+        # component is lost in the outputs' rounding
+        xs = np.sqrt(np.mean(x0 ** 2)) if signed else 0.0
+        fails, rejected, worst = [], [], 0.0
         for i in range(x0.size):
+            sigs = []
+
             def cd(step):
-                d = step * abs(x0.flat[i])
+                d = step * max(abs(x0.flat[i]), xs)
                 xp, xm = x0.copy(), x0.copy()
                 xp.flat[i] += d; xm.flat[i] -= d
-                op, om = make(xp), make(xm)
+                op, sp = oracle.branch_signature(make, xp)
+                om, sm = oracle.branch_signature(make, xm)
+                sigs.extend([sp, sm])
                 return np.sum((op - om) * (op + om - 2 * target)) / (2 * d)
             c1, c2 = cd(h), cd(h / 2)
-            if abs(c1 - c2) > 1e-5 * abs(c2) + 1e-8 * scale:
+            if any(s != sig0 for s in sigs):
+                rejected.append(i)
                 continue
-            checked += 1
-            if abs((4 * c2 - c1) / 3 - g.flat[i]) > 1e-6 * scale + 1e-5 * abs(c2):
-                fails += 1
-        assert fails == 0 and checked >= 0.8 * x0.size, (name, fails, checked, x0.size)
+            err = abs((4 * c2 - c1) / 3 - g.flat[i]) / (scale + abs(c2))
+            worst = max(worst, err)
+            if err > 1e-6:
+                fails.append((i, err))
+        kept = x0.size - len(rejected)
+        print(f"{name}: kept {kept}/{x0.size}, rejected (branch change) {rejected}, worst {worst:.2e}")
+        assert not fails and kept >= 0.8 * x0.size, (name, fails, rejected, x0.size)
 
     def with_chi(x):
         a = dict(atm); a["chi"] = x
@@ -197,7 +210,7 @@ def test_gradient_through_iterations_matches_central_differences(pol):
         def with_b(x):
             a = dict(atm); a["bx"], a["by"], a["bz"] = x[0], x[1], x[2]
             return loss(a, f0)
-        check("B", with_b, np.stack([atm["bx"], atm["by"], atm["bz"]]), g_b)
+        check("B", with_b, np.stack([atm["bx"], atm["by"], atm["bz"]]), g_b, signed=True)
     # checkpoint spacing does not change the result
     L2, c2, f2, b2, _ = diff.loss_and_grad(atm, model, quad, f0, 3, 1, mu, az, target)
     assert L2 == L and np.array_equal(c2, g_chi) and np.array_equal(f2, g_f) and np.array_equal(b2, g_b)
