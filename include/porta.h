@@ -70,6 +70,7 @@ extern "C" {
 #define PORTA_ENOMEM   -2   /* device or host allocation failed */
 #define PORTA_ECUDA    -3   /* CUDA runtime error */
 #define PORTA_ESTATE   -4   /* call order: a required input has not been set */
+#define PORTA_ENOTCONV -5   /* an iteration did not reach its tolerance within its iteration cap */
 #define PORTA_EKERNEL  -7   /* a kernel reported a failure (error word set) */
 #define PORTA_ESCRATCH -8   /* problem too large for the fixed scratch of porta_formal_solve_noalloc */
 
@@ -131,6 +132,17 @@ typedef struct {
 typedef struct {
     const double *chi, *eps, *bpl, *vel, *bx, *by, *bz;
 } porta_atmos;
+
+/* Process-wide cap on the device memory the library allocates (bytes; 0, the
+   default, means no cap). Every context allocation (creation, adjoint tapes,
+   multigrid levels, scratch of a call) counts against the live total; one that
+   would exceed the cap fails with PORTA_ENOMEM before reaching the CUDA
+   runtime, and the call that needed it returns PORTA_ENOMEM (porta_create
+   returns no context). For callers that share the GPU with other work and must
+   bound this library's footprint. porta_device_bytes returns the live total.
+   The paper has no counterpart. */
+int porta_set_device_limit(long long bytes);
+long long porta_device_bytes(void);
 
 /* Create a context: validates sizes, builds the quadratures and the per-ray
    plane geometry, allocates device buffers. Returns PORTA_EINVAL for
@@ -275,6 +287,19 @@ int porta_formal_solve_noalloc(const porta_grid *g, const porta_atom *a, const p
    the atmosphere and rho. max_change (host, may be NULL) receives the
    residual of the last iteration (synchronizes the stream). */
 int porta_run_iterations(porta_ctx *c, int iterations, double *max_change);
+
+/* Jacobi (ALI) iterations to a tolerance (Eq. 2 with the Jacobi update of
+   Sec. 5; the stop criterion is the maximum relative change R_c of Sec. 5.3):
+   replays the captured iteration of porta_run_iterations until the maximum
+   change of an iteration is below tol, reading the change after every
+   check_every-th iteration (1: after each, so that the count is exact).
+   iterations_out and max_change_out (host, may be NULL) receive the number of
+   iterations done and the last change read. Returns PORTA_ENOTCONV when
+   max_iter iterations leave the change at or above tol (rho is left at the last
+   iterate), PORTA_EINVAL for tol <= 0, max_iter < 1 or check_every < 1, and the
+   errors of porta_run_iterations. */
+int porta_iterate_to(porta_ctx *c, double tol, int max_iter, int check_every, int *iterations_out,
+                     double *max_change_out);
 
 /* Launch statistics of the last formal solution: clusters launched, CTAs per
    cluster, frequencies per pass, dynamic shared memory per CTA (bytes). */

@@ -12,6 +12,7 @@ import numpy as np
 from . import build as _build
 
 PORTA_OK, PORTA_EINVAL, PORTA_ENOMEM, PORTA_ECUDA, PORTA_ESTATE, PORTA_EKERNEL = 0, -1, -2, -3, -4, -7
+PORTA_ENOTCONV = -5
 PORTA_ESCRATCH = -8
 PORTA_NOALLOC_SCRATCH_BYTES = 32 << 20
 PORTA_MODEL_TWOLEVEL_UNPOL, PORTA_MODEL_TWOLEVEL_HANLE = 0, 1
@@ -19,6 +20,7 @@ PORTA_FP64, PORTA_FP32 = 0, 1
 PORTA_HOST, PORTA_DEVICE = 0, 1
 
 _STATUS = {0: "PORTA_OK", -1: "PORTA_EINVAL", -2: "PORTA_ENOMEM", -3: "PORTA_ECUDA", -4: "PORTA_ESTATE",
+           -5: "PORTA_ENOTCONV",
            -7: "PORTA_EKERNEL", -8: "PORTA_ESCRATCH"}
 
 
@@ -75,6 +77,9 @@ _SIGS = {
     "porta_launch_info": (_I, [_P, _P, _P, _P, _P]),
     "porta_autotune": (_I, [_P, _P, _P]),
     "porta_run_iterations": (_I, [_P, _I, _P]),
+    "porta_iterate_to": (_I, [_P, ctypes.c_double, _I, _I, _P, _P]),
+    "porta_set_device_limit": (_I, [ctypes.c_longlong]),
+    "porta_device_bytes": (ctypes.c_longlong, []),
     "porta_eval_coefficients": (_I, [_I, _I, _P, _P]),
     "porta_formal_solve_noalloc": (_I, [_P, _P, _P, _P, _P, _P, _P, _P]),
     "porta_emergent_vjp": (_I, [_P, _I, _P, _P, _P, _P, _P, _P, _P, _I]),
@@ -261,6 +266,22 @@ def porta_formal_solve_noalloc(atm, model, n_mu, n_chi, n_nu, x_max, datm, rho_p
 
 def porta_run_iterations(h, iterations, out=None):
     return lib().porta_run_iterations(h, iterations, ctypes.byref(out) if out is not None else None)
+
+
+def porta_set_device_limit(nbytes):
+    """Process-wide cap on the library's device allocations (0: none)."""
+    return lib().porta_set_device_limit(int(nbytes))
+
+
+def porta_device_bytes():
+    return lib().porta_device_bytes()
+
+
+def porta_iterate_to(h, tol, max_iter, check_every=1):
+    """Returns (status, iterations done, last maximum change)."""
+    n, ch = ctypes.c_int(), ctypes.c_double()
+    rc = lib().porta_iterate_to(h, float(tol), int(max_iter), int(check_every), ctypes.byref(n), ctypes.byref(ch))
+    return rc, n.value, ch.value
 
 
 def porta_launch_info(h):
@@ -584,6 +605,16 @@ class Context:
         out = ctypes.c_double() if residual else None
         self._check(porta_run_iterations(self.h, n, out))
         return out.value if residual else None
+
+    def iterate_to(self, tol, max_iter, check_every=1):
+        """Jacobi iterations (graph replay) until the maximum change is below tol.
+        Returns (iterations, last change, converged); PORTA_ENOTCONV is reported as
+        converged = False, every other error raises."""
+        rc, n, ch = porta_iterate_to(self.h, tol, max_iter, check_every)
+        if rc == PORTA_ENOTCONV:
+            return n, ch, False
+        self._check(rc)
+        return n, ch, True
 
     def autotune(self):
         rc, r = porta_autotune(self.h)

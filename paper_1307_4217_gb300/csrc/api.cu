@@ -7,8 +7,10 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "porta.h"
@@ -38,12 +40,55 @@ int fail(porta_ctx *c, int code, const std::string &msg)
             return fail(c, PORTA_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));   \
     } while (0)
 
+// Device allocations of the library go through pmalloc / pfree, which keep the
+// live byte count and honour the process-wide cap of porta_set_device_limit: an
+// allocation that would exceed the cap fails with cudaErrorMemoryAllocation
+// (reported as PORTA_ENOMEM) without calling the CUDA runtime.
+std::mutex g_alloc_mutex;
+std::unordered_map<void *, size_t> g_alloc_sizes;
+size_t g_alloc_live = 0, g_alloc_limit = 0;
+
+cudaError_t pmalloc_bytes(void **p, size_t bytes)
+{
+    *p = nullptr;
+    std::lock_guard<std::mutex> lock(g_alloc_mutex);
+    if (g_alloc_limit > 0 && g_alloc_live + bytes > g_alloc_limit) return cudaErrorMemoryAllocation;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) return e;
+    g_alloc_sizes[*p] = bytes;
+    g_alloc_live += bytes;
+    return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t pmalloc(T **p, size_t bytes)
+{
+    void *q = nullptr;
+    cudaError_t e = pmalloc_bytes(&q, bytes);
+    *p = (T *)q;
+    return e;
+}
+
+cudaError_t pfree(void *p)
+{
+    if (!p) return cudaSuccess;
+    {
+        std::lock_guard<std::mutex> lock(g_alloc_mutex);
+        auto it = g_alloc_sizes.find(p);
+        if (it != g_alloc_sizes.end()) {
+            g_alloc_live -= it->second;
+            g_alloc_sizes.erase(it);
+        }
+    }
+    return cudaFree(p);
+}
+
 template <typename T>
 cudaError_t dalloc(T **p, size_t n)
 {
     *p = nullptr;
     if (n == 0) return cudaSuccess;
-    return cudaMalloc((void **)p, n * sizeof(T));
+    return pmalloc(p, n * sizeof(T));
 }
 
 // Gauss-Legendre nodes/weights on (0, 1): Newton's method on the Legendre
@@ -355,7 +400,7 @@ cudaError_t ensure_fill(porta_ctx *c)
     cudaError_t e = cudaStreamCreateWithFlags(&f->stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&f->fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&f->join, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaMalloc((void **)&f->d_ctr, 2 * sizeof(int));
+    if (e == cudaSuccess) e = pmalloc((void **)&f->d_ctr, 2 * sizeof(int));
     c->fill = f;   // released by free_all also on failure
     return e;
 }
@@ -634,10 +679,10 @@ int emergent_t(porta_ctx *c, int ndir, const double *mu, const double *chi, doub
     BoxDev *dbox = nullptr;
     CK(dalloc(&dg, geom.size()));
     cudaError_t e2 = dalloc(&dr, rays.size());
-    if (e2 == cudaSuccess) e2 = cudaMalloc(&dbox, sizeof(BoxDev));
+    if (e2 == cudaSuccess) e2 = pmalloc(&dbox, sizeof(BoxDev));
     if (e2 != cudaSuccess) {
-        cudaFree(dg);
-        if (dr) cudaFree(dr);
+        pfree(dg);
+        if (dr) pfree(dr);
         return fail(c, PORTA_ENOMEM, "emergent: device allocation");
     }
     int rc = PORTA_OK;
@@ -665,9 +710,9 @@ int emergent_t(porta_ctx *c, int ndir, const double *mu, const double *chi, doub
         if (e != cudaSuccess) rc = fail(c, PORTA_ECUDA, std::string("emergent: ") + cudaGetErrorString(e));
     } while (0);
     cudaStreamSynchronize(c->stream);
-    cudaFree(dg);
-    cudaFree(dr);
-    cudaFree(dbox);
+    pfree(dg);
+    pfree(dr);
+    pfree(dbox);
     return rc;
 }
 
@@ -675,10 +720,10 @@ int emergent_t(porta_ctx *c, int ndir, const double *mu, const double *chi, doub
 cudaError_t ensure_buf(void **p, size_t &cap, size_t need)
 {
     if (need <= cap && *p) return cudaSuccess;
-    if (*p) cudaFree(*p);
+    if (*p) pfree(*p);
     *p = nullptr;
     cap = 0;
-    cudaError_t e = cudaMalloc(p, need);
+    cudaError_t e = pmalloc(p, need);
     if (e == cudaSuccess) cap = need;
     return e;
 }
@@ -871,9 +916,9 @@ int emergent_vjp_t(porta_ctx *c, int ndir, const double *mu, const double *chi, 
         if (e != cudaSuccess) rc = fail(c, PORTA_ECUDA, std::string("emergent_vjp: ") + cudaGetErrorString(e));
     } while (0);
     cudaStreamSynchronize(c->stream);
-    cudaFree(dg);
-    cudaFree(dr);
-    if (scratch_out) cudaFree(scratch_out);
+    pfree(dg);
+    pfree(dr);
+    if (scratch_out) pfree(scratch_out);
     return rc;
 }
 
@@ -885,26 +930,26 @@ void free_all(porta_ctx *c)
     drop_graph(c);
     mg_free(c);
     it_free(c);
-    if (c->d_dich) cudaFree(c->d_dich);
+    if (c->d_dich) pfree(c->d_dich);
     if (c->ml) {
-        cudaFree(c->ml->d_x);
-        cudaFree(c->ml->d_tab);
-        cudaFree(c->ml->d_pops);
-        cudaFree(c->ml->d_chis);
-        cudaFree(c->ml->d_kT);
-        cudaFree(c->ml->d_bad);
+        pfree(c->ml->d_x);
+        pfree(c->ml->d_tab);
+        pfree(c->ml->d_pops);
+        pfree(c->ml->d_chis);
+        pfree(c->ml->d_kT);
+        pfree(c->ml->d_bad);
         delete c->ml;
         c->ml = nullptr;
     }
-    if (c->d_gacc) cudaFree(c->d_gacc);
+    if (c->d_gacc) pfree(c->d_gacc);
     for (cudaEvent_t &ev : c->it_ev)
         if (ev) cudaEventDestroy(ev);
-    if (c->d_cv64) cudaFree(c->d_cv64);
+    if (c->d_cv64) pfree(c->d_cv64);
     if (c->fill) {
         if (c->fill->stream) cudaStreamDestroy(c->fill->stream);
         if (c->fill->fork) cudaEventDestroy(c->fill->fork);
         if (c->fill->join) cudaEventDestroy(c->fill->join);
-        if (c->fill->d_ctr) cudaFree(c->fill->d_ctr);
+        if (c->fill->d_ctr) pfree(c->fill->d_ctr);
         delete c->fill;
         c->fill = nullptr;
     }
@@ -914,7 +959,7 @@ void free_all(porta_ctx *c)
                     c->d_freq, c->d_part, c->d_tw, c->d_jkq, c->d_lstar, c->d_resid, c->d_err, c->d_boxes,
                     c->d_items, c->d_tune_items, c->d_tape, c->d_gpart};
     for (void *p : ptrs)
-        if (p) cudaFree(p);
+        if (p) pfree(p);
 }
 
 bool finite_host(const double *x, long long n)
@@ -965,7 +1010,7 @@ int jkq_vjp_t(porta_ctx *c, const double *dgj, const double *dgl, double *dg_chi
     for (int k = 0; k < 4 && e == cudaSuccess; ++k)
         if (!c->it_ev[k]) e = cudaEventCreate(&c->it_ev[k]);
     if (e != cudaSuccess) {
-        if (scratch) cudaFree(scratch);
+        if (scratch) pfree(scratch);
         return fail(c, PORTA_ENOMEM, "iterate_vjp: tape allocation");
     }
     // adjoint launch shape: forced, else timed once per batch size on the first batch
@@ -976,7 +1021,7 @@ int jkq_vjp_t(porta_ctx *c, const double *dgj, const double *dgl, double *dg_chi
     int rc = c->ns == 1 ? choose_adjoint<Real, 1>(c, acfg, c->adj_cluster, c->adj_nu_group, nb, tune ? &cand : nullptr)
                         : choose_adjoint<Real, 4>(c, acfg, c->adj_cluster, c->adj_nu_group, nb, tune ? &cand : nullptr);
     if (rc) {
-        cudaFree(scratch);
+        pfree(scratch);
         return fail(c, rc, "iterate_vjp: no adjoint launch shape fits");
     }
     if (!forced && !tune) acfg = c->adj2_tuned[nb];
@@ -984,7 +1029,7 @@ int jkq_vjp_t(porta_ctx *c, const double *dgj, const double *dgl, double *dg_chi
     for (const LaunchCfg &k : cand) maxcl = std::max(maxcl, k.clusters);
     e = ensure_buf((void **)&c->d_gacc, c->gacc_bytes, (size_t)maxcl * 10 * c->nvox * sizeof(double));
     if (e != cudaSuccess) {
-        cudaFree(scratch);
+        pfree(scratch);
         return fail(c, PORTA_ENOMEM, "iterate_vjp: accumulator allocation");
     }
     // forward: Stokes vectors of every node for rays r0 .. r0 + n - 1
@@ -1083,7 +1128,7 @@ int jkq_vjp_t(porta_ctx *c, const double *dgj, const double *dgl, double *dg_chi
         c->last_adj = acfg;
     }
     cudaStreamSynchronize(c->stream);
-    cudaFree(scratch);
+    pfree(scratch);
     return rc;
 }
 
@@ -1091,9 +1136,9 @@ cudaError_t mg_rho_changed(porta_ctx *L);
 
 void it_free(porta_ctx *c)
 {
-    for (double *b : c->it_saved) cudaFree(b);
+    for (double *b : c->it_saved) pfree(b);
     c->it_saved.clear();
-    if (c->it_final) cudaFree(c->it_final);
+    if (c->it_final) pfree(c->it_final);
     c->it_final = nullptr;
     c->it_niter = c->it_ckpt = 0;
 }
@@ -1139,7 +1184,7 @@ int iterate_vjp_t(porta_ctx *c, int ndir, const double *mu, const double *chi, c
     const size_t nj = (size_t)c->nvox * c->nj, per_slot = nr + nj + c->nvox;
     double *seg = nullptr;
     const size_t seg_bytes = sizeof(double) * per_slot * nslot;
-    if (rc == PORTA_OK && seg_bytes <= c->tape_limit && cudaMalloc(&seg, seg_bytes) != cudaSuccess) {
+    if (rc == PORTA_OK && seg_bytes <= c->tape_limit && pmalloc(&seg, seg_bytes) != cudaSuccess) {
         cudaGetLastError();
         seg = nullptr;
     }
@@ -1204,8 +1249,8 @@ int iterate_vjp_t(porta_ctx *c, int ndir, const double *mu, const double *chi, c
     // leave the context at the final unknowns
     int rc2 = it_load(c, c->it_final);
     cudaStreamSynchronize(c->stream);
-    cudaFree(blk);
-    if (seg) cudaFree(seg);
+    pfree(blk);
+    if (seg) pfree(seg);
     return rc ? rc : rc2;
 }
 
@@ -1219,7 +1264,7 @@ void mg_free(porta_ctx *c)
     c->mg.clear();
     double *bufs[] = {c->mg_res, c->mg_src, c->mg_rho0, c->mg_prev, c->mg_zr, c->mg_zp};
     for (double *b : bufs)
-        if (b) cudaFree(b);
+        if (b) pfree(b);
     c->mg_res = c->mg_src = c->mg_rho0 = c->mg_prev = c->mg_zr = c->mg_zp = nullptr;
 }
 
@@ -1499,21 +1544,21 @@ static int create_impl(int nbox, const porta_grid *grids, const porta_atom *at, 
         }
     };
     const size_t R = c->rsz;
-    ok(cudaMalloc(&c->d_atm, 6 * nvox * R));
+    ok(pmalloc(&c->d_atm, 6 * nvox * R));
     ok(dalloc(&c->d_eps, nvox));
     ok(dalloc(&c->d_bpl, nvox));
     ok(dalloc(&c->d_b, 3 * nvox));
     ok(dalloc(&c->d_rho, nvox * c->nl));
-    ok(cudaMalloc(&c->d_rhoR, nvox * c->nl * R));
-    ok(cudaMalloc(&c->d_invn, (size_t)c->nray * nvox * R));
-    ok(cudaMalloc(&c->d_geom, (size_t)c->nray * nplane * (prec == PORTA_FP32 ? sizeof(PlaneGeom<float>) : sizeof(PlaneGeom<double>))));
-    ok(cudaMalloc(&c->d_boxes, (size_t)nbox * sizeof(BoxDev)));
+    ok(pmalloc(&c->d_rhoR, nvox * c->nl * R));
+    ok(pmalloc(&c->d_invn, (size_t)c->nray * nvox * R));
+    ok(pmalloc(&c->d_geom, (size_t)c->nray * nplane * (prec == PORTA_FP32 ? sizeof(PlaneGeom<float>) : sizeof(PlaneGeom<double>))));
+    ok(pmalloc(&c->d_boxes, (size_t)nbox * sizeof(BoxDev)));
     ok(dalloc(&c->d_items, (size_t)nbox * c->nray));
     c->n_tune = (int)std::min<long long>((long long)nbox * c->nray, 256);
     ok(dalloc(&c->d_tune_items, (size_t)c->n_tune));
-    ok(cudaMalloc(&c->d_rays, (size_t)c->nray * (prec == PORTA_FP32 ? sizeof(RayDev<float>) : sizeof(RayDev<double>))));
-    ok(cudaMalloc(&c->d_freq, 2 * (size_t)c->n_nu * R));
-    ok(cudaMalloc(&c->d_part, (size_t)c->nray * nvox * (c->ns == 1 ? 2 : 4) * R));
+    ok(pmalloc(&c->d_rays, (size_t)c->nray * (prec == PORTA_FP32 ? sizeof(RayDev<float>) : sizeof(RayDev<double>))));
+    ok(pmalloc(&c->d_freq, 2 * (size_t)c->n_nu * R));
+    ok(pmalloc(&c->d_part, (size_t)c->nray * nvox * (c->ns == 1 ? 2 : 4) * R));
     ok(dalloc(&c->d_tw, (size_t)c->nray * 19));
     ok(dalloc(&c->d_jkq, nvox * c->nj));
     ok(dalloc(&c->d_lstar, nvox));
@@ -1716,7 +1761,7 @@ int porta_set_atmosphere(porta_ctx *c, const porta_atmos *a, int where)
                     ? run_profile_norm<float>(n, c->nray, c->n_nu, dq, dq + c->nray, dq + c->nray + c->n_nu, tmp + n, c->d_invn, c->stream)
                     : run_profile_norm<double>(n, c->nray, c->n_nu, dq, dq + c->nray, dq + c->nray + c->n_nu, tmp + n, c->d_invn, c->stream);
         cudaError_t e2 = cudaStreamSynchronize(c->stream);
-        cudaFree(dq);
+        pfree(dq);
         if (e == cudaSuccess) e = e2;
         if (e != cudaSuccess) { rc = fail(c, PORTA_ECUDA, cudaGetErrorString(e)); break; }
     } while (0);
@@ -1838,7 +1883,7 @@ int porta_emergent_stokes(porta_ctx *c, int ndir, const double *mu, const double
             cudaError_t e = cudaMemcpy(out, dout, n * sizeof(double), cudaMemcpyDeviceToHost);
             if (e != cudaSuccess) rc = fail(c, PORTA_ECUDA, cudaGetErrorString(e));
         }
-        cudaFree(dout);
+        pfree(dout);
     }
     return rc;
 }
@@ -1879,7 +1924,7 @@ int porta_emergent_vjp(porta_ctx *c, int ndir, const double *mu, const double *c
         if (e == cudaSuccess && out) e = cudaMemcpy(out, dout, nout * sizeof(double), cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) rc = fail(c, PORTA_ECUDA, cudaGetErrorString(e));
     }
-    cudaFree(blk);
+    pfree(blk);
     return rc;
 }
 
@@ -1980,7 +2025,7 @@ int porta_iterate_vjp(porta_ctx *c, int ndir, const double *mu, const double *ch
         if (e == cudaSuccess && out) e = cudaMemcpy(out, dout, nout * sizeof(double), cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) rc = fail(c, PORTA_ECUDA, cudaGetErrorString(e));
     }
-    cudaFree(blk);
+    pfree(blk);
     return rc;
 }
 
@@ -2024,9 +2069,9 @@ int porta_probe_ray(porta_ctx *c, int m, double *out, double *lstar, int where)
     if (!c->have_atm || !c->have_rho) return fail(c, PORTA_ESTATE, "probe_ray: atmosphere or rho not set");
     const long long n = (long long)c->n_nu * c->nvox;
     void *pr = nullptr, *pl = nullptr;
-    CK(cudaMalloc(&pr, n * c->ns * c->rsz));
-    cudaError_t e = cudaMalloc(&pl, n * c->rsz);
-    if (e != cudaSuccess) { cudaFree(pr); return fail(c, PORTA_ENOMEM, "probe_ray: allocation"); }
+    CK(pmalloc(&pr, n * c->ns * c->rsz));
+    cudaError_t e = pmalloc(&pl, n * c->rsz);
+    if (e != cudaSuccess) { pfree(pr); return fail(c, PORTA_ENOMEM, "probe_ray: allocation"); }
     int rc = c->precision == PORTA_FP32 ? formal_solve_t<float>(c, m, (float *)pr, (float *)pl)
                                         : formal_solve_t<double>(c, m, (double *)pr, (double *)pl);
     double *d1 = nullptr, *d2 = nullptr;
@@ -2056,10 +2101,10 @@ int porta_probe_ray(porta_ctx *c, int m, double *out, double *lstar, int where)
         if (e != cudaSuccess) rc = fail(c, PORTA_ECUDA, std::string("probe_ray: ") + cudaGetErrorString(e));
     }
     cudaStreamSynchronize(c->stream);
-    cudaFree(pr);
-    cudaFree(pl);
-    if (d1) cudaFree(d1);
-    if (d2) cudaFree(d2);
+    pfree(pr);
+    pfree(pl);
+    if (d1) pfree(d1);
+    if (d2) pfree(d2);
     if (rc == PORTA_OK) {
         c->have_fs = true;
         c->have_jkq = false;
@@ -2073,12 +2118,12 @@ int porta_eval_coefficients(int precision, int n, const double *t, double *out)
     for (int i = 0; i < n; ++i)
         if (!(t[i] > 0) || !std::isfinite(t[i])) return PORTA_EINVAL;
     double *d = nullptr;
-    if (cudaMalloc(&d, sizeof(double) * 7 * (size_t)n) != cudaSuccess) return PORTA_ENOMEM;
+    if (pmalloc(&d, sizeof(double) * 7 * (size_t)n) != cudaSuccess) return PORTA_ENOMEM;
     cudaError_t e = cudaMemcpy(d, t, sizeof(double) * n, cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = precision == PORTA_FP32 ? run_coefficients<float>(n, d, d + n, nullptr) : run_coefficients<double>(n, d, d + n, nullptr);
     if (e == cudaSuccess) e = cudaMemcpy(out, d + n, sizeof(double) * 6 * (size_t)n, cudaMemcpyDeviceToHost);
-    cudaFree(d);
+    pfree(d);
     return e == cudaSuccess ? PORTA_OK : PORTA_ECUDA;
 }
 
@@ -2143,6 +2188,41 @@ int porta_run_iterations(porta_ctx *c, int iterations, double *max_change)
         *max_change = v;
     }
     return PORTA_OK;
+}
+
+int porta_set_device_limit(long long bytes)
+{
+    if (bytes < 0) return PORTA_EINVAL;
+    std::lock_guard<std::mutex> lock(g_alloc_mutex);
+    g_alloc_limit = (size_t)bytes;
+    return PORTA_OK;
+}
+
+long long porta_device_bytes(void)
+{
+    std::lock_guard<std::mutex> lock(g_alloc_mutex);
+    return (long long)g_alloc_live;
+}
+
+int porta_iterate_to(porta_ctx *c, double tol, int max_iter, int check_every, int *iterations_out,
+                     double *max_change_out)
+{
+    if (!c) return PORTA_EINVAL;
+    if (!(tol > 0) || max_iter < 1 || check_every < 1)
+        return fail(c, PORTA_EINVAL, "iterate_to: tol > 0, max_iter >= 1 and check_every >= 1 required");
+    int done = 0;
+    double change = 0.0;
+    while (done < max_iter) {
+        const int n = std::min(check_every, max_iter - done);
+        int rc = porta_run_iterations(c, n, &change);
+        if (rc != PORTA_OK) return rc;
+        done += n;
+        if (iterations_out) *iterations_out = done;
+        if (max_change_out) *max_change_out = change;
+        if (change < tol) return PORTA_OK;
+    }
+    return fail(c, PORTA_ENOTCONV, "iterate_to: maximum change " + std::to_string(change) + " >= tolerance after " +
+                                       std::to_string(done) + " iterations");
 }
 
 int porta_set_fill(porta_ctx *c, int cluster, int nu_group, double fraction)
@@ -2262,13 +2342,13 @@ int porta_mg_setup(porta_ctx *c, int nlevels)
                 e = run_inject(L->nx, L->ny, L->nz, F->nx, F->ny, srcs[f], tmp + f * ncv, c->stream);
             if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
             if (e != cudaSuccess) {
-                cudaFree(tmp);
+                pfree(tmp);
                 rc = fail(c, PORTA_ECUDA, std::string("mg_setup: ") + cudaGetErrorString(e));
                 break;
             }
             rc = porta_ml_set_atmosphere(L, tmp, tmp + ncv, tmp + 2 * ncv, m->pol ? tmp + 3 * ncv : nullptr,
                                          m->pol ? tmp + 4 * ncv : nullptr, m->pol ? tmp + 5 * ncv : nullptr, PORTA_DEVICE);
-            cudaFree(tmp);
+            pfree(tmp);
             if (rc) {
                 rc = fail(c, rc, std::string("mg_setup: coarse atmosphere: ") + L->err);
                 break;
@@ -2305,7 +2385,7 @@ int porta_mg_setup(porta_ctx *c, int nlevels)
             e = run_inject(L->nx, L->ny, L->nz, F->nx, F->ny, src[f], tmp + f * ncv, c->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
         if (e != cudaSuccess) {
-            cudaFree(tmp);
+            pfree(tmp);
             rc = fail(c, PORTA_ECUDA, std::string("mg_setup: ") + cudaGetErrorString(e));
             break;
         }
@@ -2318,7 +2398,7 @@ int porta_mg_setup(porta_ctx *c, int nlevels)
         at.by = tmp + 5 * ncv;
         at.bz = tmp + 6 * ncv;
         rc = porta_set_atmosphere(L, &at, PORTA_DEVICE);
-        cudaFree(tmp);
+        pfree(tmp);
         if (rc) {
             rc = fail(c, rc, std::string("mg_setup: coarse atmosphere: ") + L->err);
             break;
@@ -2468,7 +2548,7 @@ int porta_ml_create(const porta_grid *g, const porta_ml_atom *a, const porta_qua
     cudaError_t e = dalloc(&m->d_pops, (size_t)m->nvox1 * mc.nlev);
     if (e == cudaSuccess) e = dalloc(&m->d_chis, (size_t)m->nvox1);
     if (e == cudaSuccess) e = dalloc(&m->d_kT, (size_t)m->nvox1);
-    if (e == cudaSuccess) e = cudaMalloc(&m->d_bad, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = pmalloc(&m->d_bad, sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemset(m->d_bad, 0, sizeof(unsigned long long));
     m->nunk = mc.nlev;
     if (e == cudaSuccess && a->polarized) {
@@ -2495,10 +2575,10 @@ int porta_ml_create(const porta_grid *g, const porta_ml_atom *a, const porta_qua
             doff[q2] = kd;
             for (double x : *dv[q2]) dp[kd++] = x;
         }
-        e = cudaMalloc(&m->d_tab, h.size());
+        e = pmalloc(&m->d_tab, h.size());
         if (e == cudaSuccess) e = cudaMemcpy(m->d_tab, h.data(), h.size(), cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = dalloc(&m->d_x, (size_t)m->nvox1 * tab.nunk);
-        if (e == cudaSuccess) e = cudaMalloc(&c->d_dich, (size_t)5 * c->nvox * c->rsz);
+        if (e == cudaSuccess) e = pmalloc(&c->d_dich, (size_t)5 * c->nvox * c->rsz);
         if (e == cudaSuccess) e = cudaMemset(c->d_dich, 0, (size_t)5 * c->nvox * c->rsz);
         const int *di = (const int *)m->d_tab;
         const double *dd = (const double *)((const char *)m->d_tab + ibytes);
@@ -2667,7 +2747,7 @@ int porta_ml_emergent_stokes(porta_ctx *c, int line, int ndir, const double *mu,
             cudaError_t e = cudaMemcpy(out, dout, n * sizeof(double), cudaMemcpyDeviceToHost);
             if (e != cudaSuccess) rc = fail(c, PORTA_ECUDA, cudaGetErrorString(e));
         }
-        cudaFree(dout);
+        pfree(dout);
     }
     return rc;
 }

@@ -71,3 +71,23 @@ def test_product_path_has_no_oracle_import():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt and "oracle.h" not in txt, f
+
+
+def test_capped_allocator_reports_enomem_without_gpu():
+    """A device-memory cap below a context's needs makes porta_create fail with
+    PORTA_ENOMEM before the CUDA runtime is asked for memory (so this runs on a
+    host without a GPU); lifting the cap restores the default."""
+    import paper_1307_4217_gb300 as P
+    from paper_1307_4217_gb300.binding import _Grid, _Atom, _Quad, _Opts
+    z = np.linspace(0, 1, 4)
+    before = P.porta_device_bytes()
+    assert P.porta_set_device_limit(1024) == P.PORTA_OK
+    try:
+        rc, h = P.porta_create(_Grid(4, 4, 4, 1.0, 1.0, z.ctypes.data), _Atom(0, 0.0, 1.0, 25.0),
+                               _Quad(2, 4, 3, 4.0), _Opts(P.PORTA_FP32, 0, 0))
+        assert rc == P.PORTA_ENOMEM
+        assert not h.value
+        assert P.porta_device_bytes() == before
+    finally:
+        assert P.porta_set_device_limit(0) == P.PORTA_OK
+    assert P.porta_set_device_limit(-1) == P.PORTA_EINVAL
