@@ -48,13 +48,14 @@ WORKLOAD = ("polarized two-level atom (Jl=0->Ju=1, Hanle + weak-field Zeeman), r
 # 34, the I-V coupling solve 9, Lambda* and the frequency accumulation 11, the
 # J^K_Q finalize per (ray, voxel) spread over 21 frequencies 2
 F_ALG = 293
-# FP32 issue peak of the GB300: 152 SMs x 128 FP32 lanes x 2 flops (FMA) x 2070 MHz
+# FP32 issue peak of the GB300 from its unit counts (152 SMs x 128 FP32 lanes x 2
+# flops per FMA x 2070 MHz); the roofline uses the measured peak (porta_fma_peak)
 SMS, LANES, SM_MAX_MHZ = 152, 128, 2070.0
-PEAK_FP32_TFLOPS = SMS * LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+PEAK_FP32_TFLOPS_NOMINAL = SMS * LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
 L2_FLUSH_BYTES = 256 << 20
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "sweep_pol64_traffic.json")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_1307_4217_gb300", "csrc", f)
-                  for f in ("sweep.cu", "sweep_common.cuh", "device_math.cuh", "porta_internal.cuh")]
+                  for f in ("sweep_j.cu", "sweep_common.cuh", "device_math.cuh", "porta_internal.cuh")]
 
 
 def kernel_hash():
@@ -106,6 +107,10 @@ def args_parse():
     ap.add_argument("--nu-group", type=int, default=0, help="force frequencies per pass (skips the autotuner)")
     ap.add_argument("--workload", choices=["pol64", "batched256"], default="pol64",
                     help="pol64: the 64^3 polarized box (default); batched256: 256 uneven boxes in one launch")
+    ap.add_argument("--batch-steps", type=int, default=3,
+                    help="timed Jacobi iterations of the 256-box batch beside the default workload (0 skips them)")
+    ap.add_argument("--c0", type=int, default=1, help="time the unpolarized 16x16x32 box to convergence (0 skips it)")
+    ap.add_argument("--peak-seconds", type=float, default=1.0, help="device time per FMA-peak measurement")
     return ap.parse_args()
 
 
@@ -120,11 +125,6 @@ def max_over_ranks(values, device):
     t = torch.tensor(values, dtype=torch.float64, device=device)
     torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
     return t.tolist()
-
-
-def job_throughput(units_per_rank, world, seconds):
-    """Whole-job rate: every rank solves its own replica of the workload."""
-    return world * units_per_rank / seconds
 
 
 # ---------------------------------------------------------------- clocks sampling
@@ -180,6 +180,32 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- CPU baseline (oracle)
+
+def _oracle_ray(args):
+    import oracle
+    atm, m = args
+    p = oracle.Problem(atm, oracle.MODEL_HANLE, N_MU, N_CHI, N_NU)
+    oracle.formal_solve(p, oracle.initial_rho(p, atm), rays_range=(m, m + 1))
+    return m
+
+
+def oracle_sample_all_cores(seed=0):
+    """Time the FP64 oracle, as it stands, on all host cores: one full ray (all 21
+    frequencies, the whole 64^3 box) per core, rays spread over the hemispheres,
+    in a process pool (spawned: the GPU context of this process is not shared)."""
+    import multiprocessing as mp
+    ncores = os.cpu_count() or 1
+    atm = synth.random_box(NX, NY, NZ, seed=seed)
+    rays = np.linspace(0, NRAY - 1, ncores).astype(int)
+    with mp.get_context("spawn").Pool(ncores) as pool:
+        pool.map(_oracle_ray, [(atm, int(rays[0]))] * min(ncores, 2))   # start-up (imports, library load)
+        t0 = time.perf_counter()
+        pool.map(_oracle_ray, [(atm, int(m)) for m in rays], chunksize=1)
+        dt = time.perf_counter() - t0
+    n = ncores * NX * NY * NZ * N_NU
+    return n / dt, dt, ncores, (f"{ncores} rays x 21 frequencies over the full 64^3 box, one ray per core "
+                                f"({n} updates, {dt:.1f} s)")
+
 
 def oracle_sample(nrays, seed=0):
     """Time the FP64 oracle on `nrays` full rays (all 21 frequencies, the whole 64^3 box)."""
@@ -301,9 +327,21 @@ def run_cuda(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     B.build()
+    from paper_1307_4217_gb300 import shard
 
-    # Each rank solves its own problem (independent replicas: weak scaling, no data-path collective).
-    wl = Workload(args.workload, rank)
+    # measured FMA peaks of this GPU (the roofline's denominator): FP32 FFMA and
+    # packed FFMA2 chains (the better of the two is the FP32 peak), FP64 DFMA
+    peaks = {}
+    for kind, name in ((0, "fp32_ffma"), (1, "fp32_ffma2"), (2, "fp64_dfma")):
+        rc, tf, ms = P.porta_fma_peak(kind, args.peak_seconds if kind < 2 else 0.5 * args.peak_seconds)
+        peaks[name] = tf if rc == P.PORTA_OK else None
+    peak_fp32 = max(v for k, v in peaks.items() if k.startswith("fp32") and v) if any(peaks.values()) else None
+
+    # N > 1: the ranks split the frequencies of every formal solution of the same box
+    # (bands, one all-reduce of the partial sums per iteration: strong scaling); N = 1:
+    # one context, one captured Jacobi iteration per step
+    wl = Workload(args.workload, 0 if world > 1 else rank)
+    bands = world > 1
     stream = torch.cuda.Stream(device=dev)
     forced = args.cluster > 0 or args.nu_group > 0
 
@@ -320,6 +358,19 @@ def run_cuda(args):
 
     ctx = make(P.PORTA_FP32)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    if bands:
+        band_it = shard.BandIteration(ctx, rank, world, device=dev)
+        ctx.autotune()                      # the band's own launch shape
+        ctx.set_rho(wl.rho0)
+
+        def step(residual=False):
+            return band_it.step(residual=residual)
+    else:
+        band_it = None
+
+        def step(residual=False):
+            return ctx.run_iterations(1, residual=residual)
+    swept = wl.updates if not bands else wl.updates * (band_it.band[1] - band_it.band[0]) // N_NU
 
     def barrier():
         torch.cuda.synchronize(dev)
@@ -329,12 +380,16 @@ def run_cuda(args):
     with torch.cuda.stream(stream):
         # warm-up: eager calls, then the captured graph of one Jacobi iteration
         for _ in range(args.warmup):
-            ctx.formal_solve()
-            ctx.accumulate_jkq(want=False)
-            ctx.see_update(residual=False)
-        ctx.run_iterations(1, residual=False)
+            if bands:
+                step()
+            else:
+                ctx.formal_solve()
+                ctx.accumulate_jkq(want=False)
+                ctx.see_update(residual=False)
+        step()
         barrier()
-        # timed steps: one graph replay (formal solution, J^K_Q sums, SEE, residual) each
+        # timed steps: one graph replay (formal solution, J^K_Q sums, SEE, residual) each;
+        # with bands: the band's formal solution, one all-reduce of the partial sums, the update
         ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(args.steps)]
         sampler = ClockSampler(local)
         sampler.start()
@@ -342,7 +397,7 @@ def run_cuda(args):
         for k in range(args.steps):
             flush.zero_()                       # L2 flush between timed steps (outside the events)
             ev[k][0].record(stream)
-            ctx.run_iterations(1, residual=False)
+            step()
             ev[k][1].record(stream)
         barrier()
         clocks = sampler.stop()
@@ -364,13 +419,13 @@ def run_cuda(args):
     rho_out = torch.empty_like(rho_h).pin_memory()
     with torch.cuda.stream(stream):
         ctx.set_rho(rho_h)
-        ctx.run_iterations(1)
+        step(residual=True)
         ctx.get_rho(rho_out)
         barrier()
         t0 = time.perf_counter()
         for _ in range(args.steps):
             ctx.set_rho(rho_h)
-            residual = ctx.run_iterations(1)
+            residual = step(residual=True)
             ctx.get_rho(rho_out)
         barrier()
         e2e_s = (time.perf_counter() - t0) / args.steps
@@ -379,7 +434,8 @@ def run_cuda(args):
 
     # FP64 plain form of the same step (single box only: the FP64 batch takes ~15 s per step)
     fp64 = None
-    if args.fp64_steps > 0 and wl.name == "pol64":
+    accuracy = None
+    if args.fp64_steps > 0 and wl.name == "pol64" and world == 1:
         ctx64 = make(P.PORTA_FP64)
         with torch.cuda.stream(stream):
             ctx64.run_iterations(1, residual=False)
@@ -389,16 +445,38 @@ def run_cuda(args):
             ctx64.run_iterations(args.fp64_steps, residual=False)
             e1.record(stream)
             barrier()
+            # accuracy of the FP32 form against the FP64 form (which the parity tests hold to
+            # 1e-10 of the FP64 oracle) on the benchmarked box: one formal solution and one
+            # update from the same unknowns, in the benchmarked launch shape
+            out = {}
+            for name, cc in (("f32", ctx), ("f64", ctx64)):
+                cc.set_rho(wl.rho0)
+                cc.formal_solve()
+                jj, ll = cc.accumulate_jkq()
+                cc.see_update(residual=False)
+                out[name] = (jj, ll, cc.get_rho())
+            barrier()
         ms64 = e0.elapsed_time(e1) / args.fp64_steps
         fp64 = {"value": world * wl.updates / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64, "dtype": "f64",
                 "launch": ctx64.launch_info()}
+        (j32, l32, r32), (j64, l64, r64) = out["f32"], out["f64"]
+        s = np.abs(j64[..., :1])
+        accuracy = {
+            "against": "the FP64 form on the same box (parity-tested to 1e-10 of the FP64 oracle)",
+            "J00_rel": float(np.max(np.abs(j32[..., 0] - j64[..., 0]) / s[..., 0])),
+            "J2Q_abs_over_J00": float(np.max(np.abs(j32[..., 1:] - j64[..., 1:]) / s)),
+            "lambda_rel": float(np.max(np.abs(l32 - l64) / np.abs(l64))),
+            "S00_rel_after_update": float(np.max(np.abs(r32[..., 0] - r64[..., 0]) / np.abs(r64[..., 0]))),
+            "sigma2Q_abs_after_update": float(np.max(np.abs(r32[..., 1:] / r32[..., :1] - r64[..., 1:] / r64[..., :1]))),
+            "tolerance": "1e-5 relative on J00 and Lambda*, 1e-5 J00 on J2Q",
+        }
         ctx64.close()
 
     # reverse mode of the emergent Stokes profiles (differentiation workload: the
     # same 64^3 box, vertical + 4 oblique emergent rays, all frequencies), FP32:
     # device time of the forward sweep with its tape and of the adjoint sweep
     adjoint = None
-    if args.adjoint_reps > 0 and wl.name == "pol64":
+    if args.adjoint_reps > 0 and wl.name == "pol64" and world == 1:
         mu, az = synth.emergent_directions()
         nz, ny, nx = ctx.shape
         gen = torch.Generator(device=dev).manual_seed(1234)
@@ -413,21 +491,35 @@ def run_cuda(args):
             for _ in range(args.adjoint_reps):
                 ctx.emergent_vjp(mu, az, gout, g_chi=gbuf[0], g_e=gbuf[1], g_b=gbuf[2])
                 ts.append(ctx.adjoint_timing())
+            # the forward emergent formal solution alone (no tape), same directions
+            eout = torch.empty((len(mu), ctx.nnu, ny, nx, ctx.ns), dtype=torch.float64, device=dev)
+            ctx.emergent_stokes(mu, az, out=eout)                                     # shape tuning
+            tf = []
+            for _ in range(args.adjoint_reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                ctx.emergent_stokes(mu, az, out=eout)
+                e1.record(stream)
+                e1.synchronize()
+                tf.append(e0.elapsed_time(e1))
         f_ms = float(np.median([t["forward_ms"] for t in ts]))
         a_ms = float(np.median([t["adjoint_ms"] for t in ts]))
+        f0_ms = float(np.median(tf))
         nupd = len(mu) * ctx.nnu * nx * ny * nz
         adjoint = {"workload": f"{nx}x{ny}x{nz} polarized, {ctx.nnu} frequencies, vertical + 4 oblique (mu=0.5) "
                                "emergent rays; gradients w.r.t. chi, e, B", "dtype": "f32",
                    "forward_ms": f_ms, "adjoint_ms": a_ms, "ratio": a_ms / f_ms,
+                   "forward_notape_ms": f0_ms, "ratio_vs_forward_notape": a_ms / f0_ms,
                    "adjoint_updates_per_s": nupd / (a_ms * 1e-3), "reps": args.adjoint_reps,
                    "launch": ctx.adjoint_info(),
                    "timing": "CUDA events inside porta_emergent_vjp (forward emergent sweep with tape; "
-                             "adjoint sweep + fixed-order reduction), median"}
+                             "adjoint sweep + fixed-order reduction), median; forward_notape_ms: CUDA events "
+                             "around porta_emergent_stokes of the same directions (no tape), median"}
 
     # gradients through Jacobi iterations (same box and emergent rays): forward
     # iterations keeping rho checkpoints, then the checkpointed reverse pass
     iter_adj = None
-    if args.iter_adjoint != "0" and wl.name == "pol64":
+    if args.iter_adjoint != "0" and wl.name == "pol64" and world == 1:
         niter, ckpt = (int(x) for x in args.iter_adjoint.split(","))
         mu, az = synth.emergent_directions()
         nz, ny, nx = ctx.shape
@@ -463,7 +555,7 @@ def run_cuda(args):
     # 2 pre- and 4 post-smoothing Jacobi iterations and 8 on the coarsest grid, from
     # rho0; Jacobi iterations of the same fine-grid cost (7 sweeps per cycle) beside it
     mgres = None
-    if args.mg_cycles > 0 and wl.name == "pol64":
+    if args.mg_cycles > 0 and wl.name == "pol64" and world == 1:
         with torch.cuda.stream(stream):
             ctx.mg_setup(3)
             ctx.set_rho(wl.rho0)
@@ -471,28 +563,33 @@ def run_cuda(args):
             ctx.set_rho(wl.rho0)
             barrier()
             cyc = []
+            res0 = ctx.residual()
             for _ in range(args.mg_cycles):
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
                 ch = ctx.mg_vcycle(2, 4, 8)
                 e1.record(stream)
                 e1.synchronize()
-                cyc.append((e0.elapsed_time(e1), ch))
+                cyc.append((e0.elapsed_time(e1), ch, ctx.residual()))
             ctx.set_rho(wl.rho0)
-            jac = []
+            jac, jres = [], []
             for _ in range(args.mg_cycles):
                 jac.append(ctx.run_iterations(7))
+                jres.append(ctx.residual())
         mgres = {"levels": ctx.mg_levels(), "cycle": "2 pre + 4 post Jacobi, 8 on the coarsest, from S00 = B",
-                 "vcycle_ms": [round(t, 3) for t, _ in cyc], "vcycle_max_change": [c for _, c in cyc],
+                 "vcycle_ms": [round(t, 3) for t, _, _ in cyc], "vcycle_max_change": [c for _, c, _ in cyc],
+                 "residual_start": res0, "vcycle_residual": [r for _, _, r in cyc],
                  "jacobi_ms_per_7_iterations": 7 * step_ms,
-                 "jacobi_max_change_after_7k_iterations": jac,
-                 "note": "max_change: of the whole V-cycle for MG, of the last iteration for Jacobi"}
+                 "jacobi_max_change_after_7k_iterations": jac, "jacobi_residual_after_7k_iterations": jres,
+                 "note": ("max_change: of the whole V-cycle for MG, of the last iteration for Jacobi; residual: "
+                          "porta_residual, max over voxels of |f - A(x)| relative to the voxel's largest unknown; "
+                          "7 Jacobi iterations cost the fine-grid formal solutions of one V-cycle (2 + 4 + 1)")}
 
     # multilevel atom without polarization: five levels, four lines, 31 frequencies per
     # line, 160 rays on the 128 x 128 x 96 grid; one Jacobi iteration (formal solution
     # of every line in one batched launch, sums, FP64 rate equations) per step
     mlres = None
-    if args.ml_steps > 0 and wl.name == "pol64":
+    if args.ml_steps > 0 and wl.name == "pol64" and world == 1:
         nxm, nym, nzm = (int(v) for v in args.ml_grid.split(","))
         atm_ml = synth.multilevel_box(nxm, nym, nzm, seed=rank)
         atom = synth.multilevel_atom(seed=rank)
@@ -548,7 +645,7 @@ def run_cuda(args):
     # same grid and quadratures: FP32 sweeps of the four lines (polarized formal
     # solver), FP64 rate equations one warp per voxel
     mlpol = None
-    if args.mlpol_steps > 0 and wl.name == "pol64":
+    if args.mlpol_steps > 0 and wl.name == "pol64" and world == 1:
         nxm, nym, nzm = (int(v) for v in args.ml_grid.split(","))
         atm_ml = synth.multilevel_box(nxm, nym, nzm, seed=rank)
         atom = synth.multilevel_atom(seed=rank)
@@ -610,6 +707,72 @@ def run_cuda(args):
                            "formal solution + sums; rate_equations_ms: the difference"}
         pctx.close()
 
+    # the unpolarized box of 16x16x32 voxels (48 rays, 11 frequencies): Jacobi (ALI)
+    # iterations to convergence, FP64 (max relative change < 1e-8) and FP32 (< 1e-6, or its
+    # noise floor), graph replays; with no horizontal modulation, the sqrt(eps) law
+    c0 = None
+    if args.c0 and wl.name == "pol64" and world == 1:
+        atm0 = synth.plane_parallel_box(16, 16, 32)
+        c0 = {"workload": "unpolarized two-level atom, 16x16x32, eps = 1e-2, B = 1, chi modulated by 1 + 0.2 sin cos, "
+                          "48 rays (3 x 8 per hemisphere), 11 frequencies; Jacobi iterations from S = B",
+              "updates_per_iteration": 16 * 16 * 32 * 48 * 11}
+        for prec, name, tol in ((P.PORTA_FP64, "f64", 1e-8), (P.PORTA_FP32, "f32", 1e-6)):
+            cc = P.Context(atm0, P.PORTA_MODEL_TWOLEVEL_UNPOL, 3, 8, 11, precision=prec)
+            cc.set_stream(stream)
+            cc.set_atmosphere(atm0)
+            r0 = np.ones((32, 16, 16, 1))
+            cc.set_rho(r0)
+            with torch.cuda.stream(stream):
+                cc.run_iterations(1, residual=False)             # graph capture (warm-up)
+                cc.set_rho(r0)
+                barrier()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                n, ch, conv = cc.iterate_to(tol, 2000 if prec == P.PORTA_FP64 else 400, check_every=10)
+                e1.record(stream)
+                barrier()
+            ms = e0.elapsed_time(e1) / n
+            c0[name] = {"iterations": n, "last_change": ch, "converged": conv, "tolerance": tol,
+                        "ms_per_iteration": ms, "updates_per_s": c0["updates_per_iteration"] / (ms * 1e-3),
+                        "timing": "CUDA events around porta_iterate_to (graph replays, change read every 10)"}
+            cc.close()
+        flat = synth.plane_parallel_box(16, 16, 32, modulation=0.0)
+        cc = P.Context(flat, P.PORTA_MODEL_TWOLEVEL_UNPOL, 3, 8, 11, precision=P.PORTA_FP64)
+        cc.set_stream(stream)
+        cc.set_atmosphere(flat)
+        cc.set_rho(np.ones((32, 16, 16, 1)))
+        with torch.cuda.stream(stream):
+            cc.iterate_to(1e-8, 2000)
+        s = cc.get_rho()[..., 0]
+        cc.close()
+        c0["sqrt_eps_law"] = {"S_top_over_sqrt_eps_B": float(s[-1, 0, 0] / np.sqrt(1e-2)),
+                              "column_spread": float(np.max(np.abs(s - s[:, :1, :1])))}
+
+    # the 256 boxes of uneven size in one persistent launch per sweep (graph replays)
+    batch = None
+    if args.batch_steps > 0 and wl.name == "pol64" and world == 1:
+        bw = Workload("batched256", rank)
+        bc = bw.context(P.PORTA_FP32, args.cluster, args.nu_group)
+        bc.set_stream(stream)
+        with torch.cuda.stream(stream):
+            if not forced:
+                bc.autotune()
+                bc.set_rho(bw.rho0)
+            bc.run_iterations(1, residual=False)
+            barrier()
+            evb = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(args.batch_steps)]
+            for k in range(args.batch_steps):
+                flush.zero_()
+                evb[k][0].record(stream)
+                bc.run_iterations(1, residual=False)
+                evb[k][1].record(stream)
+            barrier()
+        bms = sum(e[0].elapsed_time(e[1]) for e in evb) / args.batch_steps
+        batch = {"workload": bw.desc, "updates_per_iteration": bw.updates, "ms_per_iteration": bms,
+                 "updates_per_s": bw.updates / (bms * 1e-3), "launch": bc.launch_info(), "fill": bc.fill_info(),
+                 "timing": "CUDA events around one graph replay of a Jacobi iteration, L2 flushed between steps"}
+        bc.close()
+
     # max over ranks
     if world > 1:
         step_ms, sweep_ms, e2e_s = max_over_ranks([step_ms, sweep_ms, e2e_s], dev)
@@ -618,32 +781,49 @@ def run_cuda(args):
             torch.distributed.destroy_process_group()
         return
 
-    achieved = F_ALG * wl.updates / (sweep_ms * 1e-3) / 1e12
+    # the sweep's rate over the updates this rank swept (its band, for N > 1)
+    achieved = F_ALG * swept / (sweep_ms * 1e-3) / 1e12
+    peak = peak_fp32 if peak_fp32 else PEAK_FP32_TFLOPS_NOMINAL
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        v, dt, sample = wl.oracle_sample(args.cpu_sample_rays)
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
-    cfg = {"workload": wl.desc, **wl.config, "updates_per_step": wl.updates, "seed": "rank",
-           "l2": "flushed between timed steps (256 MiB write)", "parallelism": f"replicas x{world}",
+        v1, dt1, sample1 = wl.oracle_sample(args.cpu_sample_rays)
+        if wl.name == "pol64":
+            v, dt, ncores, sample = oracle_sample_all_cores()
+        else:
+            v, ncores, sample = v1, 1, sample1
+        cpu = {"value": v, "unit": UNIT, "cores": ncores, "kind": "oracle", "sample": sample,
+               "single_core": {"value": v1, "cores": 1, "sample": sample1}}
+    cfg = {"workload": wl.desc, **wl.config, "updates_per_step": wl.updates, "seed": 0 if world > 1 else "rank",
+           "l2": "flushed between timed steps (256 MiB write)",
+           "parallelism": (f"frequency bands x{world} (one all-reduce of the int64 partial sums per iteration)"
+                           if bands else "one GPU"),
            "sweep_launch": info, "sweep_fill": fill, "launch_shape": "forced" if forced else "autotuned",
-           "step": "one CUDA-graph replay of a Jacobi iteration (sweep, J^K_Q sums, SEE, residual)"}
+           "step": ("the rank's band: formal solution, all-reduce of the partial sums, SEE and residual" if bands else
+                    "one CUDA-graph replay of a Jacobi iteration (sweep, J^K_Q sums, SEE, residual)")}
+    # kernels per step: sums' set-up, main sweep (+ concurrent filler), sums' finalize, SEE
+    per_step = 4 + (1 if fill["cluster"] > 0 else 0)
     line = {
-        "metric": METRIC, "value": job_throughput(wl.updates, world, step_ms * 1e-3), "unit": UNIT, "n_gpus": world,
+        "metric": METRIC, "value": wl.updates / (step_ms * 1e-3), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "scaling": "strong" if bands else "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": cfg,
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": PEAK_FP32_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / PEAK_FP32_TFLOPS,
-                     "traffic": measured_traffic() if wl.name == "pol64" else None,
-                     "kernel": "sweep_kernel<float,4,JKQ>", "flops_per_update": F_ALG,
-                     "kernel_ms": sweep_ms,
-                     "peak_basis": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (derived, not measured)"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak,
+                     "traffic": measured_traffic() if wl.name == "pol64" and not bands else None,
+                     "kernel": "jsweep_kernel<float,4>", "flops_per_update": F_ALG,
+                     "kernel_ms": sweep_ms, "updates_per_launch": swept,
+                     "peak_basis": ("measured: porta_fma_peak, best FP32 FMA chain (FFMA or packed FFMA2) over ~1 s "
+                                    "of this GPU" if peak_fp32 else "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (nominal)"),
+                     "peaks_measured_tflops": peaks, "peak_nominal_tflops": PEAK_FP32_TFLOPS_NOMINAL},
         "cpu_baseline": cpu,
         "clocks": clocks,
-        "e2e": {"value": job_throughput(wl.updates, world, e2e_s), "unit": UNIT, "h2d_bytes_per_step": h2d,
+        "e2e": {"value": wl.updates / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "residual": residual},
-        "gpu_launches": (4 if fill["cluster"] > 0 else 3) * args.steps,
+        "gpu_launches": per_step * args.steps,
+        "accuracy": accuracy,
         "fp64_plain": fp64,
+        "unpolarized_c0": c0,
+        "batched256": batch,
         "adjoint": adjoint,
         "multigrid": mgres,
         "iter_adjoint": iter_adj,

@@ -133,6 +133,43 @@ typedef struct {
     const double *chi, *eps, *bpl, *vel, *bx, *by, *bz;
 } porta_atmos;
 
+/* Measured arithmetic peak (TFLOP/s) of the current GPU for the roofline of
+   the formal solver: kind 0 = FP32 fused multiply-add (FFMA), 1 = packed FP32
+   FMA on float2 pairs (FFMA2), 2 = FP64 FMA (DFMA). Kernels of independent FMA
+   chains (8 per thread, 64 warps per SM) are launched back to back for about
+   `seconds` seconds of device time (CUDA events); *tflops receives the best
+   launch (2 flops per FMA), *total_ms (may be NULL) the device time spent.
+   Allocates a few MB of device memory for the results and frees it.
+   The paper has no counterpart. */
+int porta_fma_peak(int kind, double seconds, double *tflops, double *total_ms);
+
+/* Frequency bands: the (ray, frequency) pairs of a formal solution are
+   independent and J^K_Q / Lambda-bar* are sums over them (Eq. 1; the band
+   parallelization of Sec. 4.3), so a formal solution can be split into bands
+   swept on different GPUs and the bands' partial sums added.
+   porta_set_freq_range limits the formal solutions of this context to the
+   frequencies [j0, j1) (0 <= j0 < j1 <= n_nu; (0, 0) or (0, n_nu) restores the
+   whole grid); the profile normalization stays that of the whole grid, so the
+   bands' sums add up to J^K_Q and Lambda-bar*. Single-box two-level contexts
+   (and batches); PORTA_EINVAL for multilevel contexts and bad bounds.
+   porta_partial_size gives the partial sums' element count, (NJ + 1) * nvox,
+   and element size (8 bytes). After porta_formal_solve, porta_get_partial
+   copies them to `out` (host or device, `where`): in the FP32 form the exact
+   fixed-point sums as int64, [NJ + 1][nvox] (J^K_Q components, then
+   Lambda-bar*; the voxels' scales are identical on every context with the same
+   unknowns and atmosphere), in the FP64 form doubles, J^K_Q [nvox][NJ] then
+   Lambda-bar* [nvox]. Element-wise sums of such buffers over the bands (int64
+   in FP32: exact, so independent of the order of the reduction) are again
+   partial sums; porta_set_partial loads one into a context that has run a
+   formal solution and makes it the J^K_Q / Lambda-bar* that porta_see_update
+   uses (PORTA_ESTATE without a formal solution). The paper's distributed
+   scheme (domain decomposition, Sec. 4.1-4.2) is not used: every rank holds the
+   whole box. */
+int porta_set_freq_range(porta_ctx *c, int j0, int j1);
+int porta_partial_size(const porta_ctx *c, long long *elements, int *elem_bytes);
+int porta_get_partial(porta_ctx *c, void *out, int where);
+int porta_set_partial(porta_ctx *c, const void *in, int where);
+
 /* Process-wide cap on the device memory the library allocates (bytes; 0, the
    default, means no cap). Every context allocation (creation, adjoint tapes,
    multigrid levels, scratch of a call) counts against the live total; one that
@@ -413,6 +450,17 @@ int porta_mg_setup(porta_ctx *c, int nlevels);
 /* Levels built by porta_mg_setup: *nlevels (0 before setup) and, if shapes is
    not NULL, shapes[3 l + 0..2] = nx, ny, nz of level l, finest first. */
 int porta_mg_levels(const porta_ctx *c, int *nlevels, int *shapes);
+
+/* Residual of the statistical-equilibrium equations written as A(x) = f
+   (Eq. 30 of the multigrid section, Sec. 5.1) at the current unknowns: a
+   formal solution (J^K_Q, Lambda-bar*), then r = f - A(x); *rnorm (host)
+   receives max over voxels of max_c |r_c| / max_c |x_c| (the residual relative
+   to each voxel's largest unknown). It measures the distance from the discrete
+   solution independently of the iteration's step (unlike the maximum change).
+   Allocates a temporary of the unknowns' size; leaves no formal solution
+   behind (PORTA_ESTATE for porta_accumulate_jkq afterwards). PORTA_ESTATE
+   without atmosphere and unknowns, or with a frequency band set. */
+int porta_residual(porta_ctx *c, double *rnorm);
 
 /* One V-cycle (Eqs. 30-34) from the finest level: npre Jacobi iterations;
    residual r = f - A(rho), A the statistical-equilibrium operator (J^K_Q from

@@ -79,6 +79,12 @@ _SIGS = {
     "porta_run_iterations": (_I, [_P, _I, _P]),
     "porta_iterate_to": (_I, [_P, ctypes.c_double, _I, _I, _P, _P]),
     "porta_set_device_limit": (_I, [ctypes.c_longlong]),
+    "porta_fma_peak": (_I, [_I, ctypes.c_double, _P, _P]),
+    "porta_set_freq_range": (_I, [_P, _I, _I]),
+    "porta_residual": (_I, [_P, _P]),
+    "porta_partial_size": (_I, [_P, _P, _P]),
+    "porta_get_partial": (_I, [_P, _P, _I]),
+    "porta_set_partial": (_I, [_P, _P, _I]),
     "porta_device_bytes": (ctypes.c_longlong, []),
     "porta_eval_coefficients": (_I, [_I, _I, _P, _P]),
     "porta_formal_solve_noalloc": (_I, [_P, _P, _P, _P, _P, _P, _P, _P]),
@@ -133,6 +139,22 @@ class PortaError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"{_STATUS.get(code, code)}: {msg}")
         self.code = code
+
+
+def _raw_ptr(a, n, dtype):
+    """(pointer, where) of a contiguous buffer of n elements of dtype: a numpy
+    array (host) or a CUDA tensor (device)."""
+    if isinstance(a, np.ndarray):
+        if a.dtype != dtype or not a.flags.c_contiguous or a.size != n:
+            raise TypeError(f"host buffer must be a contiguous {np.dtype(dtype).name} array of {n} elements")
+        return a.ctypes.data, PORTA_HOST
+    if getattr(a, "is_cuda", False):
+        import torch
+        want = torch.int64 if dtype == np.int64 else torch.float64
+        if a.dtype != want or not a.is_contiguous() or a.numel() != n:
+            raise TypeError(f"device buffer must be a contiguous {want} CUDA tensor of {n} elements")
+        return a.data_ptr(), PORTA_DEVICE
+    raise TypeError("buffer must be a numpy array or a CUDA tensor")
 
 
 def _ptr_where(a):
@@ -266,6 +288,37 @@ def porta_formal_solve_noalloc(atm, model, n_mu, n_chi, n_nu, x_max, datm, rho_p
 
 def porta_run_iterations(h, iterations, out=None):
     return lib().porta_run_iterations(h, iterations, ctypes.byref(out) if out is not None else None)
+
+
+def porta_fma_peak(kind, seconds=1.0):
+    """Measured FMA peak: kind 0 FP32, 1 packed FP32 (float2), 2 FP64. Returns (status, TFLOP/s, ms)."""
+    tf, ms = ctypes.c_double(), ctypes.c_double()
+    rc = lib().porta_fma_peak(int(kind), float(seconds), ctypes.byref(tf), ctypes.byref(ms))
+    return rc, tf.value, ms.value
+
+
+def porta_residual(h):
+    r = ctypes.c_double()
+    rc = lib().porta_residual(h, ctypes.byref(r))
+    return rc, r.value
+
+
+def porta_set_freq_range(h, j0, j1):
+    return lib().porta_set_freq_range(h, int(j0), int(j1))
+
+
+def porta_partial_size(h):
+    n, b = ctypes.c_longlong(), ctypes.c_int()
+    rc = lib().porta_partial_size(h, ctypes.byref(n), ctypes.byref(b))
+    return rc, n.value, b.value
+
+
+def porta_get_partial(h, out, where):
+    return lib().porta_get_partial(h, out, where)
+
+
+def porta_set_partial(h, buf, where):
+    return lib().porta_set_partial(h, buf, where)
 
 
 def porta_set_device_limit(nbytes):
@@ -429,6 +482,7 @@ class Context:
         self.__dict__.update(s)
         self.shape = (atm["nz"], atm["ny"], atm["nx"])
         self.model = model
+        self.precision = precision
 
     def close(self):
         if self.h is not None:
@@ -495,6 +549,41 @@ class Context:
         where = wj if jkq is not None else wl
         self._check(porta_accumulate_jkq(self.h, pj, pl, where))
         return jkq, lstar
+
+    def residual(self):
+        """max relative residual of A(x) = f at the current unknowns (porta_residual)."""
+        rc, r = porta_residual(self.h)
+        self._check(rc)
+        return r
+
+    # ---- frequency bands (multi-GPU splitting of a formal solution)
+    def set_freq_range(self, j0, j1):
+        """Sweep only the frequencies [j0, j1) in later formal solutions ((0, 0): all)."""
+        self._check(porta_set_freq_range(self.h, j0, j1))
+
+    def partial_dtype(self):
+        """numpy dtype of the partial sums: int64 fixed point (FP32 form) or float64."""
+        return np.int64 if self.precision == PORTA_FP32 else np.float64
+
+    def get_partial(self, out=None):
+        """The last formal solution's partial sums of J^K_Q and Lambda-bar* into `out`
+        (a numpy array or a contiguous CUDA tensor of partial_dtype(), partial_size()
+        elements); a new numpy array if out is None."""
+        rc, n, _ = porta_partial_size(self.h)
+        self._check(rc)
+        if out is None:
+            out = np.zeros(n, dtype=self.partial_dtype())
+        ptr, where = _raw_ptr(out, n, self.partial_dtype())
+        self._check(porta_get_partial(self.h, ptr, where))
+        return out
+
+    def set_partial(self, buf):
+        """Make summed partial sums (same layout as get_partial) this context's J^K_Q and
+        Lambda-bar* for the next see_update."""
+        rc, n, _ = porta_partial_size(self.h)
+        self._check(rc)
+        ptr, where = _raw_ptr(buf, n, self.partial_dtype())
+        self._check(porta_set_partial(self.h, ptr, where))
 
     def see_update(self, residual=True):
         if not residual:
@@ -676,6 +765,7 @@ class BatchContext(Context):
         self.offsets = np.concatenate([[0], np.cumsum(self.box_sizes)])
         self.shape = (int(self.offsets[-1]),)
         self.model = model
+        self.precision = precision
 
     @staticmethod
     def concat(atms, key):

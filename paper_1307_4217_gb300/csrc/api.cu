@@ -209,9 +209,10 @@ void plane_geometry(int nx, int ny, int nz, double lx, double ly, const double *
 }
 
 template <typename Real>
-RayDev<Real> ray_dev(double mu, double chi)
+RayDev<Real> ray_dev(double mu, double chi, double w = 0.0)
 {
     RayDev<Real> r{};
+    r.w = (Real)w;
     double st = std::sqrt(std::max(0.0, 1.0 - mu * mu));
     r.mu = (Real)mu;
     r.ox = (Real)(st * std::cos(chi));
@@ -232,7 +233,7 @@ const int kSmemLimit = 220 * 1024;
 // Shared-memory capacities of a launch with cluster size C over all boxes:
 // ring plane (16-byte chunks) and Stokes-plane points, each the maximum over boxes.
 template <typename Real, int NS>
-void launch_caps(const porta_ctx *c, int C, int &ring_plane, int &ipts_max)
+void launch_caps(const porta_ctx *c, int C, int &ring_plane, int &ipts_max, bool jk = false)
 {
     const int nch = (NS == 1 ? 4 : 8) * (int)sizeof(Real) / 16;
     const bool dich = NS == 4 && c->d_dich != nullptr;
@@ -241,12 +242,33 @@ void launch_caps(const porta_ctx *c, int C, int &ring_plane, int &ipts_max)
     for (const BoxDev &b : c->boxes) {
         const int rmax = (b.ny + C - 1) / C;
         const int chunk = (rmax + 2) * b.nx;
+        if (jk) {
+            // the J^K_Q sweep (sweep_j.cu): ring capacity in nodes
+            ring_plane = std::max(ring_plane, chunk);
+            ipts_max = std::max(ipts_max, rmax * b.nx);
+            continue;
+        }
         // with dichroism the slots of a second ring (eta_U / eta_I per node) follow the node ring
         const int dchunks = dich ? (chunk * (int)sizeof(Real) + 15) / 16 : 0;
         ring_plane = std::max(ring_plane, nch * chunk + dchunks);
         ipts_max = std::max(ipts_max, rmax * b.nx);
     }
 }
+
+// The J^K_Q formal solution runs the kernel of sweep_j.cu (per-frequency
+// node coefficients in shared memory) unless the lines carry dichroism, which
+// only the general sweep (sweep.cu) implements, or a plane is too wide for its
+// shared memory (then the general sweep, which needs less per frequency, runs).
+bool use_jk(const porta_ctx *c) { return c->d_dich == nullptr && c->jk_fits; }
+
+// The J^K_Q sweep sums an FP32 formal solution into fixed-point accumulators;
+// an FP64 one keeps per-ray partial integrals summed in ray order in FP64 (a
+// fixed-point scale cannot hold 1e-10 relative precision for quantities that
+// span many decades within one voxel, as Lambda-bar* does with optical depth).
+bool jfixed(const porta_ctx *c) { return use_jk(c) && c->precision == PORTA_FP32; }
+
+// frequencies of the J^K_Q formal solution (its band, porta_set_freq_range)
+int jnu(const porta_ctx *c) { return c->fr1 > c->fr0 ? c->fr1 - c->fr0 : c->n_nu; }
 
 int max_ny(const porta_ctx *c)
 {
@@ -262,8 +284,10 @@ int max_ny(const porta_ctx *c)
 // point updates, the ring fill (halo rows included), the partial-integral
 // writes and a barrier.
 template <typename Real, int NS>
-int choose_launch(porta_ctx *c, LaunchCfg &best, int force_c, int force_f, int nitems)
+int choose_launch(porta_ctx *c, LaunchCfg &best, int force_c, int force_f, int nitems, bool jk = false, int nnu = 0)
 {
+    const int NU = nnu > 0 ? nnu : c->n_nu;     // frequencies swept
+    if (force_f > NU) force_f = NU;
     const int NA = NS == 1 ? 2 : 4;
     double best_cost = 1e300;
     best = LaunchCfg{};
@@ -273,23 +297,35 @@ int choose_launch(porta_ctx *c, LaunchCfg &best, int force_c, int force_f, int n
         if (force_c <= 0 && C > 1 && (C & (C - 1)) != 0 && C != 6 && C != 12) continue;   // heuristic set
         if (C > ny_max) continue;
         int ring_plane, ipts_max;
-        launch_caps<Real, NS>(c, C, ring_plane, ipts_max);
-        const long long ring = 3LL * ring_plane * 16;
-        const long long per_nu = 2LL * ipts_max * NS * (long long)sizeof(Real);
-        const long long scratch = (long long)kThreads * NA * (long long)sizeof(Real);
-        if (ring + per_nu + scratch > kSmemLimit) continue;
-        int fmax = (int)std::min<long long>(c->n_nu, (kSmemLimit - ring - scratch) / per_nu);
+        launch_caps<Real, NS>(c, C, ring_plane, ipts_max, jk);
+        int fmax = 0;
+        if (jk) {
+            // J^K_Q kernel: besides the Stokes planes, each frequency of a pass keeps
+            // the nodes' coefficients of three planes (jsweep_smem_bytes)
+            for (int f = NU; f >= 1 && fmax == 0; --f)
+                if (jsweep_smem_bytes<Real, NS>(ring_plane, ipts_max, f, kThreads) <= kSmemLimit) fmax = f;
+            if (fmax == 0) continue;
+        } else {
+            const long long ring = 3LL * ring_plane * 16;
+            const long long per_nu = 2LL * ipts_max * NS * (long long)sizeof(Real);
+            const long long scratch = (long long)kThreads * NA * (long long)sizeof(Real);
+            if (ring + per_nu + scratch > kSmemLimit) continue;
+            fmax = (int)std::min<long long>(NU, (kSmemLimit - ring - scratch) / per_nu);
+        }
         if (force_f > 0) {
             if (force_f > fmax) continue;
             fmax = force_f;
         }
-        const int G = (c->n_nu + fmax - 1) / fmax;
-        const int F = (c->n_nu + G - 1) / G;
+        const int G = (NU + fmax - 1) / fmax;
+        const int F = (NU + G - 1) / G;
         // threads: the strip's points times the frequency lanes they can use, whole warps, 64..512
         const int threads = std::min(kThreads, std::max(64, (ipts_max * F + 31) / 32 * 32));
-        const int smem = sweep_smem_bytes<Real, NS>(ring_plane, ipts_max, F, threads);
+        const int smem = jk ? jsweep_smem_bytes<Real, NS>(ring_plane, ipts_max, F, threads)
+                            : sweep_smem_bytes<Real, NS>(ring_plane, ipts_max, F, threads);
+        if (smem > kSmemLimit + 16) continue;
         int act = 0;
-        if (max_active_clusters<Real, NS>(C, smem, threads, &act, c->d_dich != nullptr) != cudaSuccess) {
+        if ((jk ? jsweep_max_active_clusters<Real, NS>(C, smem, threads, &act)
+                : max_active_clusters<Real, NS>(C, smem, threads, &act, c->d_dich != nullptr)) != cudaSuccess) {
             cudaGetLastError();
             continue;
         }
@@ -329,12 +365,12 @@ std::vector<LaunchCfg> candidates(porta_ctx *c, int nitems)
     for (int C = 1; C <= 16; ++C) {
         if (C > ny_max) continue;
         int last_f = -1, kept = 0;
-        for (int G = 1; G <= c->n_nu && kept < 3; ++G) {
-            int F = (c->n_nu + G - 1) / G;
+        for (int G = 1; G <= jnu(c) && kept < 3; ++G) {
+            int F = (jnu(c) + G - 1) / G;
             if (F == last_f) continue;
             last_f = F;
             LaunchCfg cfg{};
-            if (choose_launch<Real, NS>(c, cfg, C, F, nitems) == PORTA_OK && cfg.F == F) {
+            if (choose_launch<Real, NS>(c, cfg, C, F, nitems, use_jk(c), jnu(c)) == PORTA_OK && cfg.F == F) {
                 out.push_back(cfg);
                 ++kept;
             }
@@ -369,27 +405,99 @@ SweepArgs<Real> base_args(porta_ctx *c)
 
 // fill the launch-dependent fields of the arguments
 template <typename Real>
-void shape_args(porta_ctx *c, SweepArgs<Real> &a, const LaunchCfg &cfg)
+void shape_args(porta_ctx *c, SweepArgs<Real> &a, const LaunchCfg &cfg, bool jk = false)
 {
     a.F = cfg.F;
-    a.ngroups = (c->n_nu + cfg.F - 1) / cfg.F;
+    a.ngroups = (a.nnu + cfg.F - 1) / cfg.F;
     if (c->ns == 1)
-        launch_caps<Real, 1>(c, cfg.cluster, a.ring_plane, a.ipts_max);
+        launch_caps<Real, 1>(c, cfg.cluster, a.ring_plane, a.ipts_max, jk);
     else
-        launch_caps<Real, 4>(c, cfg.cluster, a.ring_plane, a.ipts_max);
+        launch_caps<Real, 4>(c, cfg.cluster, a.ring_plane, a.ipts_max, jk);
+    a.cstride = jsweep_stride(a.ring_plane * (c->ns == 1 ? 1 : 2), (int)sizeof(Real));
+    a.istride = jsweep_stride(a.ipts_max * c->ns, (int)sizeof(Real));
+}
+
+// one J-mode sweep launch with the kernel use_jk selects
+template <typename Real>
+cudaError_t launch_j(porta_ctx *c, const SweepArgs<Real> &a, LaunchCfg &cfg, cudaStream_t st)
+{
+    if (use_jk(c))
+        return c->ns == 1 ? launch_jsweep<Real, 1>(a, cfg, st) : launch_jsweep<Real, 4>(a, cfg, st);
+    return c->ns == 1 ? launch_sweep<Real, 1>(a, MODE_JKQ, cfg, st) : launch_sweep<Real, 4>(a, MODE_JKQ, cfg, st);
 }
 
 template <typename Real>
 SweepArgs<Real> jkq_args(porta_ctx *c)
 {
     SweepArgs<Real> a = base_args<Real>(c);
+    if (c->fr1 > c->fr0) {
+        // a frequency band: its nodes and weights (the profile normalization stays
+        // the one of the whole frequency grid, so the bands' sums add up to J^K_Q)
+        a.xf += c->fr0;
+        a.wf += c->fr0;
+        a.nnu = c->fr1 - c->fr0;
+    }
     a.geom = (const PlaneGeom<Real> *)c->d_geom;
     a.rays = (const RayDev<Real> *)c->d_rays;
     a.invn = (const Real *)c->d_invn;
-    a.part = c->d_part;
+    a.part = jfixed(c) ? nullptr : c->d_part;
+    a.jacc = jfixed(c) ? c->d_jacc : nullptr;
+    a.jexp = c->d_jexp;
+    a.jerr = c->d_err;
+    a.tw = c->d_tw;
     a.items = c->d_items;
     a.nitems = c->nbox * c->nray;
     return a;
+}
+
+// Device buffers of the J^K_Q formal solution, allocated on first use (before
+// any graph capture): the fixed-point sums of the J^K_Q sweep, or the per-ray
+// partial integrals of the general sweep.
+cudaError_t ensure_sweep_buffers(porta_ctx *c)
+{
+    if (jfixed(c)) {
+        cudaError_t e = cudaSuccess;
+        if (!c->d_jacc) e = pmalloc(&c->d_jacc, (size_t)(c->nj + 1) * c->nvox * sizeof(unsigned long long));
+        if (e == cudaSuccess && !c->d_jexp) e = pmalloc(&c->d_jexp, (size_t)c->nvox * sizeof(int));
+        return e;
+    }
+    if (c->d_part) return cudaSuccess;
+    return pmalloc(&c->d_part, (size_t)c->nray * c->nvox * (c->ns == 1 ? 2 : 4) * c->rsz);
+}
+
+// zero the fixed-point sums and set the voxels' scales before a J^K_Q sweep
+template <typename Real>
+cudaError_t jacc_prepare(porta_ctx *c, const SweepArgs<Real> &a)
+{
+    if (!jfixed(c)) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
+    if (e != cudaSuccess) return e;
+    return c->ns == 1 ? launch_jacc_prepare<Real, 1>(a, c->stream) : launch_jacc_prepare<Real, 4>(a, c->stream);
+}
+
+// J^K_Q and Lambda-bar* (FP64) from the sums of the last formal solution
+cudaError_t finalize_jkq(porta_ctx *c)
+{
+    if (jfixed(c))
+        return c->ns == 1 ? launch_jacc_finalize<1>(c->nvox, c->d_jacc, c->d_jexp, c->d_jkq, c->d_lstar, c->stream)
+                          : launch_jacc_finalize<4>(c->nvox, c->d_jacc, c->d_jexp, c->d_jkq, c->d_lstar, c->stream);
+    if (c->precision == PORTA_FP32)
+        return c->ns == 1 ? run_jkq_finalize<float, 1>(c->nvox, c->nray, c->d_part, c->d_tw, c->d_jkq, c->d_lstar, c->stream)
+                          : run_jkq_finalize<float, 4>(c->nvox, c->nray, c->d_part, c->d_tw, c->d_jkq, c->d_lstar, c->stream);
+    return c->ns == 1 ? run_jkq_finalize<double, 1>(c->nvox, c->nray, c->d_part, c->d_tw, c->d_jkq, c->d_lstar, c->stream)
+                      : run_jkq_finalize<double, 4>(c->nvox, c->nray, c->d_part, c->d_tw, c->d_jkq, c->d_lstar, c->stream);
+}
+
+// the fixed-point sums' overflow flag (reads device memory: synchronizes the stream)
+int check_jacc(porta_ctx *c)
+{
+    if (!jfixed(c)) return PORTA_OK;
+    int flag = 0;
+    CK(cudaMemcpyAsync(&flag, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (flag) return fail(c, PORTA_EKERNEL, "formal solution: a J^K_Q term exceeded the fixed-point range (2^16 times "
+                                            "max(|S^0_0|, |B|) of its voxel), or was not finite");
+    return PORTA_OK;
 }
 
 cudaError_t ensure_fill(porta_ctx *c)
@@ -416,14 +524,13 @@ cudaError_t sweep_jkq(porta_ctx *c, SweepArgs<Real> a, LaunchCfg cfg, const int 
     a.items = items;
     a.nitems = nitems;
     const int nB = (int)std::lround(c->fill_frac * nitems);
-    if (!allow_fill || c->fill_cfg.cluster <= 0 || nB < 1 || nB >= nitems)
-        return c->ns == 1 ? launch_sweep<Real, 1>(a, MODE_JKQ, cfg, c->stream) : launch_sweep<Real, 4>(a, MODE_JKQ, cfg, c->stream);
+    if (!allow_fill || c->fill_cfg.cluster <= 0 || nB < 1 || nB >= nitems) return launch_j<Real>(c, a, cfg, c->stream);
     cudaError_t e = ensure_fill(c);
     if (e != cudaSuccess) return e;
     const int nA = nitems - nB;
     SweepArgs<Real> b = a;
     LaunchCfg fc = c->fill_cfg;
-    shape_args<Real>(c, b, fc);
+    shape_args<Real>(c, b, fc, use_jk(c));
     b.items = items + nA;
     b.nitems = nB;
     b.next_item = c->fill->d_ctr + 1;
@@ -440,11 +547,8 @@ cudaError_t sweep_jkq(porta_ctx *c, SweepArgs<Real> a, LaunchCfg cfg, const int 
     e = cudaMemsetAsync(c->fill->d_ctr, 0, 2 * sizeof(int), c->stream);
     if (e == cudaSuccess) e = cudaEventRecord(c->fill->fork, c->stream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(c->fill->stream, c->fill->fork, 0);
-    if (e == cudaSuccess)
-        e = c->ns == 1 ? launch_sweep<Real, 1>(a, MODE_JKQ, cfg, c->stream) : launch_sweep<Real, 4>(a, MODE_JKQ, cfg, c->stream);
-    if (e == cudaSuccess)
-        e = c->ns == 1 ? launch_sweep<Real, 1>(b, MODE_JKQ, fc, c->fill->stream)
-                       : launch_sweep<Real, 4>(b, MODE_JKQ, fc, c->fill->stream);
+    if (e == cudaSuccess) e = launch_j<Real>(c, a, cfg, c->stream);
+    if (e == cudaSuccess) e = launch_j<Real>(c, b, fc, c->fill->stream);
     if (e == cudaSuccess) e = cudaEventRecord(c->fill->join, c->fill->stream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, c->fill->join, 0);
     return e;
@@ -458,11 +562,17 @@ int formal_solve_t(porta_ctx *c, int probe_ray, Real *probe, Real *probe_ls)
     a.probe = probe;
     a.probe_ls = probe_ls;
     LaunchCfg cfg{};
-    int rc = c->ns == 1 ? choose_launch<Real, 1>(c, cfg, c->opt_cluster, c->opt_nu_group, a.nitems)
-                        : choose_launch<Real, 4>(c, cfg, c->opt_cluster, c->opt_nu_group, a.nitems);
+    int rc = c->ns == 1 ? choose_launch<Real, 1>(c, cfg, c->opt_cluster, c->opt_nu_group, a.nitems, use_jk(c), jnu(c))
+                        : choose_launch<Real, 4>(c, cfg, c->opt_cluster, c->opt_nu_group, a.nitems, use_jk(c), jnu(c));
     if (rc) return fail(c, rc, "no sweep launch shape fits this grid (shared memory / cluster limits)");
-    shape_args<Real>(c, a, cfg);
-    cudaError_t e = sweep_jkq<Real>(c, a, cfg, a.items, a.nitems, probe_ray < 0);
+    shape_args<Real>(c, a, cfg, use_jk(c));
+    cudaError_t e = ensure_sweep_buffers(c);
+    if (e != cudaSuccess) return fail(c, PORTA_ENOMEM, std::string("formal solution buffers: ") + cudaGetErrorString(e));
+    a.part = jfixed(c) ? nullptr : c->d_part;
+    a.jacc = jfixed(c) ? c->d_jacc : nullptr;
+    a.jexp = c->d_jexp;
+    e = jacc_prepare<Real>(c, a);
+    if (e == cudaSuccess) e = sweep_jkq<Real>(c, a, cfg, a.items, a.nitems, probe_ray < 0);
     if (e != cudaSuccess) return fail(c, PORTA_ECUDA, std::string("sweep launch: ") + cudaGetErrorString(e));
     c->last = cfg;
     return PORTA_OK;
@@ -474,6 +584,13 @@ int autotune_t(porta_ctx *c)
     const int nitems = c->nbox * c->nray;
     std::vector<LaunchCfg> cand = c->ns == 1 ? candidates<Real, 1>(c, nitems) : candidates<Real, 4>(c, nitems);
     if (cand.empty()) return fail(c, PORTA_EINVAL, "autotune: no launch shape fits");
+    {
+        // the timing launches write the formal solution's buffers (their sums are
+        // discarded: every formal solution starts from zero)
+        cudaError_t eb = ensure_sweep_buffers(c);
+        if (eb == cudaSuccess) eb = jacc_prepare<Real>(c, jkq_args<Real>(c));
+        if (eb != cudaSuccess) return fail(c, PORTA_ECUDA, std::string("autotune: ") + cudaGetErrorString(eb));
+    }
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
@@ -485,7 +602,7 @@ int autotune_t(porta_ctx *c)
         const LaunchCfg &cfg0 = cand[ci];
         LaunchCfg cfg = cfg0;
         SweepArgs<Real> a = jkq_args<Real>(c);
-        shape_args<Real>(c, a, cfg);
+        shape_args<Real>(c, a, cfg, use_jk(c));
         // one box: time one wave (every resident cluster sweeps one ray);
         // batches: time a strided sample of the (box, ray) items
         if (c->nbox == 1) {
@@ -497,8 +614,7 @@ int autotune_t(porta_ctx *c)
         float ms = 1e30f;
         for (int rep = 0; rep < 2 && rc == PORTA_OK; ++rep) {
             cudaError_t e = cudaEventRecord(e0, c->stream);
-            if (e == cudaSuccess)
-                e = c->ns == 1 ? launch_sweep<Real, 1>(a, MODE_JKQ, cfg, c->stream) : launch_sweep<Real, 4>(a, MODE_JKQ, cfg, c->stream);
+            if (e == cudaSuccess) e = launch_j<Real>(c, a, cfg, c->stream);
             if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
             if (e == cudaSuccess) e = cudaEventSynchronize(e1);
             float t = 0;
@@ -530,7 +646,7 @@ int autotune_t(porta_ctx *c)
         auto time_split = [&](float &ms) {
             SweepArgs<Real> a = jkq_args<Real>(c);
             LaunchCfg cfg = pick;
-            shape_args<Real>(c, a, cfg);
+            shape_args<Real>(c, a, cfg, use_jk(c));
             ms = 1e30f;
             for (int rep = 0; rep < 2; ++rep) {
                 cudaError_t e = cudaEventRecord(e0, c->stream);
@@ -957,7 +1073,7 @@ void free_all(porta_ctx *c)
         if (ev) cudaEventDestroy(ev);
     void *ptrs[] = {c->d_atm, c->d_eps, c->d_bpl, c->d_b, c->d_rho, c->d_rhoR, c->d_invn, c->d_geom, c->d_rays,
                     c->d_freq, c->d_part, c->d_tw, c->d_jkq, c->d_lstar, c->d_resid, c->d_err, c->d_boxes,
-                    c->d_items, c->d_tune_items, c->d_tape, c->d_gpart};
+                    c->d_items, c->d_tune_items, c->d_tape, c->d_gpart, c->d_jacc, c->d_jexp};
     for (void *p : ptrs)
         if (p) pfree(p);
 }
@@ -1558,7 +1674,6 @@ static int create_impl(int nbox, const porta_grid *grids, const porta_atom *at, 
     ok(dalloc(&c->d_tune_items, (size_t)c->n_tune));
     ok(pmalloc(&c->d_rays, (size_t)c->nray * (prec == PORTA_FP32 ? sizeof(RayDev<float>) : sizeof(RayDev<double>))));
     ok(pmalloc(&c->d_freq, 2 * (size_t)c->n_nu * R));
-    ok(pmalloc(&c->d_part, (size_t)c->nray * nvox * (c->ns == 1 ? 2 : 4) * R));
     ok(dalloc(&c->d_tw, (size_t)c->nray * 19));
     ok(dalloc(&c->d_jkq, nvox * c->nj));
     ok(dalloc(&c->d_lstar, nvox));
@@ -1598,7 +1713,7 @@ static int create_impl(int nbox, const porta_grid *grids, const porta_atom *at, 
                     plane_geometry<float>(c->boxes[b].nx, c->boxes[b].ny, c->boxes[b].nz, c->blx[b], c->bly[b],
                                           c->bz[b].data(), c->mu[m], c->chi[m],
                                           geom.data() + c->boxes[b].geom0 + (size_t)m * c->boxes[b].nz);
-            for (int m = 0; m < c->nray; ++m) rays[m] = ray_dev<float>(c->mu[m], c->chi[m]);
+            for (int m = 0; m < c->nray; ++m) rays[m] = ray_dev<float>(c->mu[m], c->chi[m], c->w[m]);
             for (int j = 0; j < c->n_nu; ++j) { fr[j] = (float)c->xf[j]; fr[c->n_nu + j] = (float)c->wf[j]; }
             ok(cudaMemcpy(c->d_geom, geom.data(), geom.size() * sizeof(geom[0]), cudaMemcpyHostToDevice));
             ok(cudaMemcpy(c->d_rays, rays.data(), rays.size() * sizeof(rays[0]), cudaMemcpyHostToDevice));
@@ -1612,7 +1727,7 @@ static int create_impl(int nbox, const porta_grid *grids, const porta_atom *at, 
                     plane_geometry<double>(c->boxes[b].nx, c->boxes[b].ny, c->boxes[b].nz, c->blx[b], c->bly[b],
                                            c->bz[b].data(), c->mu[m], c->chi[m],
                                            geom.data() + c->boxes[b].geom0 + (size_t)m * c->boxes[b].nz);
-            for (int m = 0; m < c->nray; ++m) rays[m] = ray_dev<double>(c->mu[m], c->chi[m]);
+            for (int m = 0; m < c->nray; ++m) rays[m] = ray_dev<double>(c->mu[m], c->chi[m], c->w[m]);
             for (int j = 0; j < c->n_nu; ++j) { fr[j] = c->xf[j]; fr[c->n_nu + j] = c->wf[j]; }
             ok(cudaMemcpy(c->d_geom, geom.data(), geom.size() * sizeof(geom[0]), cudaMemcpyHostToDevice));
             ok(cudaMemcpy(c->d_rays, rays.data(), rays.size() * sizeof(rays[0]), cudaMemcpyHostToDevice));
@@ -1620,11 +1735,15 @@ static int create_impl(int nbox, const porta_grid *grids, const porta_atom *at, 
         }
         // a launch shape must exist for this grid
         LaunchCfg cfg{};
-        int r2 = prec == PORTA_FP32
-                     ? (c->ns == 1 ? choose_launch<float, 1>(c, cfg, c->opt_cluster, c->opt_nu_group, c->nray)
-                                   : choose_launch<float, 4>(c, cfg, c->opt_cluster, c->opt_nu_group, c->nray))
-                     : (c->ns == 1 ? choose_launch<double, 1>(c, cfg, c->opt_cluster, c->opt_nu_group, c->nray)
-                                   : choose_launch<double, 4>(c, cfg, c->opt_cluster, c->opt_nu_group, c->nray));
+        int r2 = PORTA_OK;
+        for (int jk = 1; jk >= 0; --jk) {
+            r2 = prec == PORTA_FP32
+                     ? (c->ns == 1 ? choose_launch<float, 1>(c, cfg, c->opt_cluster, c->opt_nu_group, c->nray, jk)
+                                   : choose_launch<float, 4>(c, cfg, c->opt_cluster, c->opt_nu_group, c->nray, jk))
+                     : (c->ns == 1 ? choose_launch<double, 1>(c, cfg, c->opt_cluster, c->opt_nu_group, c->nray, jk)
+                                   : choose_launch<double, 4>(c, cfg, c->opt_cluster, c->opt_nu_group, c->nray, jk));
+            if (jk) c->jk_fits = r2 == PORTA_OK;
+        }
         if (rc == PORTA_OK && r2 != PORTA_OK) {
             rc = PORTA_EINVAL;
             c->err = "no sweep launch shape fits this grid (nx too large for shared memory)";
@@ -1820,6 +1939,7 @@ int porta_formal_solve(porta_ctx *c)
                                         : formal_solve_t<double>(c, -1, nullptr, nullptr);
     if (rc == PORTA_OK) {
         c->have_fs = true;
+        c->jkq_loaded = false;
         c->have_jkq = false;
     }
     return rc;
@@ -1830,18 +1950,16 @@ int porta_accumulate_jkq(porta_ctx *c, double *jkq, double *lstar, int where)
     if (!c) return PORTA_EINVAL;
     if (!c->have_fs) return fail(c, PORTA_ESTATE, "accumulate_jkq: no formal solution");
     if (where != PORTA_HOST && where != PORTA_DEVICE) return fail(c, PORTA_EINVAL, "accumulate_jkq: bad `where`");
-    cudaError_t e;
-    if (c->precision == PORTA_FP32)
-        e = c->ns == 1 ? run_jkq_finalize<float, 1>(c->nvox, c->nray, c->d_part, c->d_tw, c->d_jkq, c->d_lstar, c->stream)
-                       : run_jkq_finalize<float, 4>(c->nvox, c->nray, c->d_part, c->d_tw, c->d_jkq, c->d_lstar, c->stream);
-    else
-        e = c->ns == 1 ? run_jkq_finalize<double, 1>(c->nvox, c->nray, c->d_part, c->d_tw, c->d_jkq, c->d_lstar, c->stream)
-                       : run_jkq_finalize<double, 4>(c->nvox, c->nray, c->d_part, c->d_tw, c->d_jkq, c->d_lstar, c->stream);
+    // (J^K_Q loaded by porta_set_partial is already final)
+    cudaError_t e = c->jkq_loaded ? cudaSuccess : finalize_jkq(c);
     if (e != cudaSuccess) return fail(c, PORTA_ECUDA, std::string("accumulate_jkq: ") + cudaGetErrorString(e));
     cudaMemcpyKind k = where == PORTA_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     if (jkq) CK(cudaMemcpyAsync(jkq, c->d_jkq, c->nvox * c->nj * sizeof(double), k, c->stream));
     if (lstar) CK(cudaMemcpyAsync(lstar, c->d_lstar, c->nvox * sizeof(double), k, c->stream));
-    if (where == PORTA_HOST && (jkq || lstar)) CK(cudaStreamSynchronize(c->stream));
+    if (where == PORTA_HOST && (jkq || lstar)) {
+        int rc = check_jacc(c);
+        if (rc != PORTA_OK) return rc;
+    }
     c->have_jkq = true;
     return PORTA_OK;
 }
@@ -2066,6 +2184,7 @@ int porta_probe_ray(porta_ctx *c, int m, double *out, double *lstar, int where)
     if (m < 0 || m >= c->nray || !out || (where != PORTA_HOST && where != PORTA_DEVICE))
         return fail(c, PORTA_EINVAL, "probe_ray: bad argument");
     if (c->nbox != 1) return fail(c, PORTA_EINVAL, "probe_ray: single-box contexts only");
+    if (c->fr1 > c->fr0) return fail(c, PORTA_ESTATE, "probe_ray: needs the whole frequency grid (porta_set_freq_range)");
     if (!c->have_atm || !c->have_rho) return fail(c, PORTA_ESTATE, "probe_ray: atmosphere or rho not set");
     const long long n = (long long)c->n_nu * c->nvox;
     void *pr = nullptr, *pl = nullptr;
@@ -2107,6 +2226,7 @@ int porta_probe_ray(porta_ctx *c, int m, double *out, double *lstar, int where)
     if (d2) pfree(d2);
     if (rc == PORTA_OK) {
         c->have_fs = true;
+        c->jkq_loaded = false;
         c->have_jkq = false;
     }
     return rc;
@@ -2147,18 +2267,15 @@ int porta_run_iterations(porta_ctx *c, int iterations, double *max_change)
     if (!c->stream) return fail(c, PORTA_ESTATE, "run_iterations: needs a non-default stream (porta_set_stream)");
     if (c->graph_exec && c->graph_stream != c->stream) drop_graph(c);
     if (!c->graph_exec) {
+        cudaError_t eb = ensure_sweep_buffers(c);   // no allocation inside the capture
+        if (eb != cudaSuccess) return fail(c, PORTA_ENOMEM, std::string("run_iterations: ") + cudaGetErrorString(eb));
         // capture one iteration: formal solution, J^K_Q sums, SEE update and residual
         CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
         int rc = c->precision == PORTA_FP32 ? formal_solve_t<float>(c, -1, nullptr, nullptr)
                                             : formal_solve_t<double>(c, -1, nullptr, nullptr);
         cudaError_t e = cudaSuccess;
         if (rc == PORTA_OK) {
-            if (c->precision == PORTA_FP32)
-                e = c->ns == 1 ? run_jkq_finalize<float, 1>(c->nvox, c->nray, c->d_part, c->d_tw, c->d_jkq, c->d_lstar, c->stream)
-                               : run_jkq_finalize<float, 4>(c->nvox, c->nray, c->d_part, c->d_tw, c->d_jkq, c->d_lstar, c->stream);
-            else
-                e = c->ns == 1 ? run_jkq_finalize<double, 1>(c->nvox, c->nray, c->d_part, c->d_tw, c->d_jkq, c->d_lstar, c->stream)
-                               : run_jkq_finalize<double, 4>(c->nvox, c->nray, c->d_part, c->d_tw, c->d_jkq, c->d_lstar, c->stream);
+            e = finalize_jkq(c);
             if (e == cudaSuccess) e = enqueue_update(c);
         }
         cudaGraph_t g = nullptr;
@@ -2186,6 +2303,8 @@ int porta_run_iterations(porta_ctx *c, int iterations, double *max_change)
         double v;
         std::memcpy(&v, &bits, sizeof(v));
         *max_change = v;
+        int rc = check_jacc(c);
+        if (rc != PORTA_OK) return rc;
     }
     return PORTA_OK;
 }
@@ -2225,6 +2344,70 @@ int porta_iterate_to(porta_ctx *c, double tol, int max_iter, int check_every, in
                                        std::to_string(done) + " iterations");
 }
 
+int porta_set_freq_range(porta_ctx *c, int j0, int j1)
+{
+    if (!c) return PORTA_EINVAL;
+    if (c->ml) return fail(c, PORTA_EINVAL, "set_freq_range: two-level contexts only");
+    if (j0 == 0 && (j1 == 0 || j1 == c->n_nu)) {
+        c->fr0 = c->fr1 = 0;
+    } else {
+        if (j0 < 0 || j1 <= j0 || j1 > c->n_nu) return fail(c, PORTA_EINVAL, "set_freq_range: need 0 <= j0 < j1 <= n_nu");
+        c->fr0 = j0;
+        c->fr1 = j1;
+    }
+    c->have_fs = c->have_jkq = false;
+    drop_graph(c);
+    return PORTA_OK;
+}
+
+int porta_partial_size(const porta_ctx *c, long long *elements, int *elem_bytes)
+{
+    if (!c) return PORTA_EINVAL;
+    if (elements) *elements = (long long)(c->nj + 1) * c->nvox;
+    if (elem_bytes) *elem_bytes = 8;
+    return PORTA_OK;
+}
+
+int porta_get_partial(porta_ctx *c, void *out, int where)
+{
+    if (!c || !out) return PORTA_EINVAL;
+    if (!c->have_fs) return fail(c, PORTA_ESTATE, "get_partial: no formal solution");
+    if (where != PORTA_HOST && where != PORTA_DEVICE) return fail(c, PORTA_EINVAL, "get_partial: bad `where`");
+    const cudaMemcpyKind k = where == PORTA_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (jfixed(c)) {
+        CK(cudaMemcpyAsync(out, c->d_jacc, (size_t)(c->nj + 1) * c->nvox * sizeof(unsigned long long), k, c->stream));
+    } else {
+        cudaError_t e = finalize_jkq(c);
+        if (e != cudaSuccess) return fail(c, PORTA_ECUDA, std::string("get_partial: ") + cudaGetErrorString(e));
+        double *o = (double *)out;
+        CK(cudaMemcpyAsync(o, c->d_jkq, (size_t)c->nj * c->nvox * sizeof(double), k, c->stream));
+        CK(cudaMemcpyAsync(o + (size_t)c->nj * c->nvox, c->d_lstar, (size_t)c->nvox * sizeof(double), k, c->stream));
+    }
+    if (where == PORTA_HOST) CK(cudaStreamSynchronize(c->stream));
+    return PORTA_OK;
+}
+
+int porta_set_partial(porta_ctx *c, const void *in, int where)
+{
+    if (!c || !in) return PORTA_EINVAL;
+    if (!c->have_fs) return fail(c, PORTA_ESTATE, "set_partial: no formal solution on this context");
+    if (where != PORTA_HOST && where != PORTA_DEVICE) return fail(c, PORTA_EINVAL, "set_partial: bad `where`");
+    const cudaMemcpyKind k = where == PORTA_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (jfixed(c)) {
+        CK(cudaMemcpyAsync(c->d_jacc, in, (size_t)(c->nj + 1) * c->nvox * sizeof(unsigned long long), k, c->stream));
+        cudaError_t e = finalize_jkq(c);
+        if (e != cudaSuccess) return fail(c, PORTA_ECUDA, std::string("set_partial: ") + cudaGetErrorString(e));
+    } else {
+        const double *i = (const double *)in;
+        CK(cudaMemcpyAsync(c->d_jkq, i, (size_t)c->nj * c->nvox * sizeof(double), k, c->stream));
+        CK(cudaMemcpyAsync(c->d_lstar, i + (size_t)c->nj * c->nvox, (size_t)c->nvox * sizeof(double), k, c->stream));
+    }
+    if (where == PORTA_HOST) CK(cudaStreamSynchronize(c->stream));
+    c->have_jkq = true;
+    c->jkq_loaded = true;
+    return PORTA_OK;
+}
+
 int porta_set_fill(porta_ctx *c, int cluster, int nu_group, double fraction)
 {
     if (!c) return PORTA_EINVAL;
@@ -2238,9 +2421,11 @@ int porta_set_fill(porta_ctx *c, int cluster, int nu_group, double fraction)
         return fail(c, PORTA_EINVAL, "set_fill: cluster in 1..16, nu_group in 1..n_nu, fraction in (0, 1)");
     LaunchCfg k{};
     const int nitems = c->nbox * c->nray;
+    const bool jk = use_jk(c);
+    const int nu = jnu(c);
     int rc = c->precision == PORTA_FP32
-                 ? (c->ns == 1 ? choose_launch<float, 1>(c, k, cluster, nu_group, nitems) : choose_launch<float, 4>(c, k, cluster, nu_group, nitems))
-                 : (c->ns == 1 ? choose_launch<double, 1>(c, k, cluster, nu_group, nitems) : choose_launch<double, 4>(c, k, cluster, nu_group, nitems));
+                 ? (c->ns == 1 ? choose_launch<float, 1>(c, k, cluster, nu_group, nitems, jk, nu) : choose_launch<float, 4>(c, k, cluster, nu_group, nitems, jk, nu))
+                 : (c->ns == 1 ? choose_launch<double, 1>(c, k, cluster, nu_group, nitems, jk, nu) : choose_launch<double, 4>(c, k, cluster, nu_group, nitems, jk, nu));
     if (rc || k.F != nu_group) return fail(c, PORTA_EINVAL, "set_fill: this launch shape does not fit");
     // stream, events and counters exist before any graph capture uses them
     cudaError_t e = ensure_fill(c);
@@ -2442,6 +2627,33 @@ int porta_mg_levels(const porta_ctx *c, int *nlevels, int *shapes)
         }
     }
     return PORTA_OK;
+}
+
+int porta_residual(porta_ctx *c, double *rnorm)
+{
+    if (!c || !rnorm) return PORTA_EINVAL;
+    if (!c->have_atm || !c->have_rho) return fail(c, PORTA_ESTATE, "residual: atmosphere or unknowns not set");
+    if (c->ml && !c->ml->have_pops) return fail(c, PORTA_ESTATE, "residual: populations not set");
+    if (c->fr1 > c->fr0) return fail(c, PORTA_ESTATE, "residual: needs the whole frequency grid");
+    const long long nu = mg_nunk(c);
+    const int nc = mg_ncomp(c);
+    double *r = nullptr;
+    cudaError_t e = pmalloc(&r, sizeof(double) * nu * nc);
+    if (e != cudaSuccess) return fail(c, PORTA_ENOMEM, "residual: allocation");
+    int rc = mg_fs(c);
+    if (rc == PORTA_OK) {
+        e = mg_apply(c, -1.0, nullptr, 1, r);                    // r = f - A(x)
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->d_resid, 0, sizeof(unsigned long long), c->stream);
+        if (e == cudaSuccess) e = run_rel_residual(nu, nc, r, mg_unk(c), c->d_resid, c->stream);
+        unsigned long long bits = 0;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&bits, c->d_resid, sizeof(bits), cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e == cudaSuccess) std::memcpy(rnorm, &bits, sizeof(double));
+        else rc = fail(c, PORTA_ECUDA, std::string("residual: ") + cudaGetErrorString(e));
+    }
+    pfree(r);
+    c->have_fs = c->have_jkq = false;
+    return rc;
 }
 
 int porta_mg_vcycle(porta_ctx *c, int npre, int npost, int ncoarse, double *max_change)

@@ -141,6 +141,34 @@ __global__ void change_kernel(long long nvox, int nl, const double *old, const d
     }
 }
 
+// max over voxels of max_c |r[v][c]| / max_c |x[v][c]|: a residual relative to each
+// voxel's largest unknown, as the IEEE bits of a non-negative double
+__global__ void rel_residual_kernel(long long nvox, int nl, const double *r, const double *x,
+                                    unsigned long long *out)
+{
+    long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    double q = 0.0;
+    if (v < nvox) {
+        double rm = 0.0, xm = 0.0;
+        for (int c = 0; c < nl; ++c) {
+            rm = fmax(rm, fabs(r[v * nl + c]));
+            xm = fmax(xm, fabs(x[v * nl + c]));
+        }
+        q = rm / xm;
+    }
+    if (!(q <= 1e300)) q = 1e300;
+    for (int s = 16; s > 0; s >>= 1) q = fmax(q, __shfl_xor_sync(0xffffffffu, q, s));
+    __shared__ double red[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) red[wid] = q;
+    __syncthreads();
+    if (wid == 0) {
+        q = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
+        for (int s = 16; s > 0; s >>= 1) q = fmax(q, __shfl_xor_sync(0xffffffffu, q, s));
+        if (lane == 0) atomicMax(out, (unsigned long long)__double_as_longlong(q));
+    }
+}
+
 __global__ void axpy_kernel(long long n, double alpha, const double *x, double *y)
 {
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -175,6 +203,13 @@ cudaError_t run_prolong_add(int nxf, int nyf, int nzf, int nxc, int nyc, int nl,
 {
     const long long n = (long long)nxf * nyf * nzf;
     prolong_add_kernel<<<nblk(n, 256), 256, 0, st>>>(nxf, nyf, n, nxc, nyc, nl, zp, cnew, cold, fine);
+    return cudaGetLastError();
+}
+
+cudaError_t run_rel_residual(long long nvox, int nl, const double *r, const double *x, unsigned long long *out,
+                             cudaStream_t st)
+{
+    rel_residual_kernel<<<nblk(nvox, 256), 256, 0, st>>>(nvox, nl, r, x, out);
     return cudaGetLastError();
 }
 

@@ -18,6 +18,9 @@ cudaError_t run_prolong_add(int nxf, int nyf, int nzf, int nxc, int nyc, int nl,
 // of S00 and of S2/S00, or with rel_all of every component
 cudaError_t run_change(long long nvox, int nl, const double *old, const double *cur, unsigned long long *resid,
                        cudaStream_t st, int rel_all = 0);
+// max over voxels of max_c |r| / max_c |x| (atomic max on the IEEE bits in *out)
+cudaError_t run_rel_residual(long long nvox, int nl, const double *r, const double *x, unsigned long long *out,
+                             cudaStream_t st);
 // y += alpha x
 cudaError_t run_axpy(long long n, double alpha, const double *x, double *y, cudaStream_t st);
 

@@ -48,6 +48,9 @@ struct porta_ctx {
     int n_mu = 0, n_chi = 0, n_nu = 0;
     double x_max = 4;
     int precision = PORTA_FP32;
+    bool jk_fits = true;                // a launch shape of the J^K_Q sweep kernel (sweep_j.cu) fits the grid
+    int fr0 = 0, fr1 = 0;               // frequency band [fr0, fr1) of the J^K_Q formal solution (fr1 = 0: all)
+    bool jkq_loaded = false;            // J^K_Q / Lambda-bar* set by porta_set_partial (not from this context's sweep)
     int opt_cluster = 0, opt_nu_group = 0;
     bool user_shape = false;            // launch shape given in porta_opts (not autotuned)
     std::map<int, porta::LaunchCfg> emg_tuned;   // emergent sweep: shape timed once per direction count
@@ -71,7 +74,9 @@ struct porta_ctx {
     void *d_geom = nullptr;         // nray*nz PlaneGeom
     void *d_rays = nullptr;         // nray RayDev
     void *d_freq = nullptr;         // xf, wf (Real)
-    void *d_part = nullptr;         // nray*nvox*(ns==1 ? 2 : 4) Real
+    void *d_part = nullptr;         // nray*nvox*(ns==1 ? 2 : 4) Real (general sweep only; allocated on first use)
+    unsigned long long *d_jacc = nullptr;   // J^K_Q sweep: fixed-point sums [nj + 1][nvox] (allocated on first use)
+    int *d_jexp = nullptr;                  // J^K_Q sweep: per-voxel fixed-point exponent
     double *d_tw = nullptr;         // nray*19 FP64: w_m, T (18)
     double *d_jkq = nullptr, *d_lstar = nullptr;
     unsigned long long *d_resid = nullptr;

@@ -27,7 +27,8 @@ template <typename Real>
 struct RayDev {
     Real mu, ox, oy, oz;
     Real t[18];
-    Real pad[2];
+    Real w;          // quadrature weight w_m of the ray (0 for a line of sight)
+    Real pad;
 };
 
 enum SweepMode { MODE_JKQ = 0, MODE_EMERGENT = 1 };
@@ -50,6 +51,7 @@ struct SweepArgs {
     int ngroups, F;      // frequency groups and frequencies per group
     int ring_plane;      // shared-memory ring plane capacity (16-byte chunks), max over boxes
     int ipts_max;        // Stokes-plane capacity (points), max over boxes
+    int cstride, istride;  // J^K_Q sweep: Reals per (slot, frequency) coefficient plane and per (buffer, frequency) Stokes plane
     Real bfac;           // 2 * gbar * zeta (weak-field Zeeman, eta_V / (eta_I x B.Omega))
     const PlaneGeom<Real> *geom;   // per box: [ray][nz]
     const RayDev<Real> *rays;      // [ray]
@@ -75,6 +77,12 @@ struct SweepArgs {
     double *gacc;
     const double *gjkq, *glstar, *tw;
     int ray0;                      // first ray of the batch (rays and geom point at it)
+    // J^K_Q formal solution (sweep_j.cu): fixed-point accumulators of the weighted
+    // ray sums [NJ + 1][nvox] (J^K_Q components, then Lambda-bar*), the power-of-two
+    // exponent of each voxel's fixed-point scale, and the overflow flag
+    unsigned long long *jacc;
+    const int *jexp;
+    int *jerr;
 };
 
 struct LaunchCfg {
@@ -96,6 +104,30 @@ int sweep_smem_bytes(int ring_plane, int ipts_max, int F, int threads);
 
 template <typename Real, int NS>
 cudaError_t max_active_clusters(int cluster, int smem, int threads, int *out, bool dich = false);
+
+// the J^K_Q formal solution (sweep_j.cu): per-frequency node coefficients in
+// shared memory; ring capacity `nodes` per slot, Stokes planes of `ipts` points.
+// Plane strides are padded to 16 (mod 32) 4-byte words, so that the two
+// frequency lanes of a point (adjacent threads) read distinct banks.
+__host__ __device__ inline int jsweep_stride(int reals, int real_bytes)
+{
+    int words = reals * real_bytes / 4;
+    words += ((16 - words % 32) + 32) % 32;
+    return words * 4 / real_bytes;
+}
+template <typename Real, int NS>
+int jsweep_smem_bytes(int nodes, int ipts, int F, int threads);
+template <typename Real, int NS>
+cudaError_t jsweep_max_active_clusters(int cluster, int smem, int threads, int *out);
+template <typename Real, int NS>
+cudaError_t launch_jsweep(const SweepArgs<Real> &a, LaunchCfg &cfg, cudaStream_t st);
+// before a J^K_Q formal solution: zero the fixed-point accumulators and set each
+// voxel's scale exponent; after it: J^K_Q and Lambda-bar* in FP64 from them
+template <typename Real, int NS>
+cudaError_t launch_jacc_prepare(const SweepArgs<Real> &a, cudaStream_t st);
+template <int NS>
+cudaError_t launch_jacc_finalize(long long nvox, const unsigned long long *jacc, const int *jexp, double *jkq,
+                                 double *lstar, cudaStream_t st);
 
 // adjoint of the emergent sweep (adjoint.cu): shared memory of a launch with
 // ring plane `ring_plane` (16-byte chunks), `ipts` points per strip, tape
