@@ -618,15 +618,19 @@ def run_cuda(args):
             mctx.mg_setup(3)
             mctx.set_pops(pops0)
             mg_cyc = []
+            ml_res0 = mctx.residual()
             for _ in range(args.ml_mg_cycles):
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
                 ch = mctx.mg_vcycle(2, 4, 8)
                 e1.record(stream)
                 e1.synchronize()
-                mg_cyc.append((e0.elapsed_time(e1), ch))
+                mg_cyc.append((e0.elapsed_time(e1), ch, mctx.residual()))
             mctx.set_pops(pops0)
-            jac_ch = [mctx.ml_iterate(7) for _ in range(args.ml_mg_cycles)]
+            jac_ch, jac_res = [], []
+            for _ in range(args.ml_mg_cycles):
+                jac_ch.append(mctx.ml_iterate(7))
+                jac_res.append(mctx.residual())
         ml_ms = sum(e[0].elapsed_time(e[1]) for e in evm) / args.ml_steps
         nupd = len(atom["A"]) * 31 * NRAY * nxm * nym * nzm
         mlres = {"workload": f"{nxm}x{nym}x{nzm}, five-level atom (J = 0,1,2,1,2), four lines x 31 frequencies, "
@@ -635,9 +639,11 @@ def run_cuda(args):
                  "updates_per_s": nupd / (ml_ms * 1e-3), "steps": args.ml_steps,
                  "max_change_after": chg, "launch": mctx.launch_info(),
                  "multigrid": {"levels": mctx.mg_levels(), "cycle": "2 pre + 4 post Jacobi, 8 on the coarsest, from LTE",
-                               "vcycle_ms": [round(t, 1) for t, _ in mg_cyc],
-                               "vcycle_max_change": [c for _, c in mg_cyc],
-                               "jacobi_max_change_after_7k_iterations": jac_ch},
+                               "vcycle_ms": [round(t, 1) for t, _, _ in mg_cyc],
+                               "vcycle_max_change": [c for _, c, _ in mg_cyc],
+                               "residual_start": ml_res0, "vcycle_residual": [r for _, _, r in mg_cyc],
+                               "jacobi_max_change_after_7k_iterations": jac_ch,
+                               "jacobi_residual_after_7k_iterations": jac_res},
                  "timing": "CUDA events around one graph replay per step, L2 flushed between steps"}
         mctx.close()
 
@@ -689,7 +695,7 @@ def run_cuda(args):
                     chm = pctx.mg_vcycle(2, 4, 8)
                     e3.record(stream)
                     e3.synchronize()
-                    pmg.append((e2.elapsed_time(e3), chm))
+                    pmg.append((e2.elapsed_time(e3), chm, pctx.residual()))
         p_ms = sum(e[0].elapsed_time(e[1]) for e in evp) / args.mlpol_steps
         fs_ms = e0.elapsed_time(e1)
         nupd = len(atom["A"]) * 31 * NRAY * nxm * nym * nzm
@@ -701,8 +707,9 @@ def run_cuda(args):
                  "updates_per_iteration": nupd, "updates_per_s": nupd / (p_ms * 1e-3),
                  "steps": args.mlpol_steps, "max_change_after": pch, "launch": pctx.launch_info(),
                  "multigrid": {"levels": pctx.mg_levels(), "cycle": "2 pre + 4 post Jacobi, 8 on the coarsest, from LTE",
-                               "vcycle_ms": [round(t, 1) for t, _ in pmg],
-                               "vcycle_max_change": [c for _, c in pmg]} if pmg else None,
+                               "vcycle_ms": [round(t, 1) for t, _, _ in pmg],
+                               "vcycle_max_change": [c for _, c, _ in pmg],
+                               "vcycle_residual": [r for _, _, r in pmg]} if pmg else None,
                  "timing": "CUDA events around one graph replay per step (L2 flushed); formal_solution_ms: one eager "
                            "formal solution + sums; rate_equations_ms: the difference"}
         pctx.close()

@@ -143,6 +143,18 @@ typedef struct {
    The paper has no counterpart. */
 int porta_fma_peak(int kind, double seconds, double *tflops, double *total_ms);
 
+/* Diagnostic: the BESSER-DELO step of Eq. 7 with a general propagation
+   matrix (all seven elements eta_I, eta_Q, eta_U, eta_V, rho_Q, rho_U, rho_V
+   at M and O; kappa^-1 = 1 + psi'_O K'_O of Eq. 8 solved in full) evaluated on
+   the GPU in the given precision, for n cases. in (host): [n][34] =
+   I_M (4), eta_M (7), eps_M (4), eta_O (7), eps_O (4), eta_P,I (1), eps_P (4),
+   ds_M, ds_P, has_p (nonzero: a downwind point exists); out (host): [n][5] =
+   I_O (4), Lambda*. tau_MO = (eta_I,M + eta_I,O) ds_M / 2 and likewise for OP
+   (trapezoid), S = eps / eta_I. The two-level sweeps run the specializations of
+   this step for their propagation matrices (I-V coupling, or the arrow form of
+   dichroism). PORTA_EINVAL for non-finite inputs or non-positive eta_I, ds. */
+int porta_eval_step(int precision, int n, const double *in, double *out);
+
 /* Frequency bands: the (ray, frequency) pairs of a formal solution are
    independent and J^K_Q / Lambda-bar* are sums over them (Eq. 1; the band
    parallelization of Sec. 4.3), so a formal solution can be split into bands

@@ -82,6 +82,7 @@ _SIGS = {
     "porta_fma_peak": (_I, [_I, ctypes.c_double, _P, _P]),
     "porta_set_freq_range": (_I, [_P, _I, _I]),
     "porta_residual": (_I, [_P, _P]),
+    "porta_eval_step": (_I, [_I, _I, _P, _P]),
     "porta_partial_size": (_I, [_P, _P, _P]),
     "porta_get_partial": (_I, [_P, _P, _I]),
     "porta_set_partial": (_I, [_P, _P, _I]),
@@ -295,6 +296,14 @@ def porta_fma_peak(kind, seconds=1.0):
     tf, ms = ctypes.c_double(), ctypes.c_double()
     rc = lib().porta_fma_peak(int(kind), float(seconds), ctypes.byref(tf), ctypes.byref(ms))
     return rc, tf.value, ms.value
+
+
+def porta_eval_step(precision, cases):
+    """The GPU's general BESSER-DELO step on rows of 34 inputs; returns (status, [n][5] outputs)."""
+    cases = np.ascontiguousarray(cases, dtype=np.float64).reshape(-1, 34)
+    out = np.zeros((cases.shape[0], 5))
+    rc = lib().porta_eval_step(int(precision), cases.shape[0], cases.ctypes.data, out.ctypes.data)
+    return rc, out
 
 
 def porta_residual(h):

@@ -2247,6 +2247,25 @@ int porta_eval_coefficients(int precision, int n, const double *t, double *out)
     return e == cudaSuccess ? PORTA_OK : PORTA_ECUDA;
 }
 
+int porta_eval_step(int precision, int n, const double *in, double *out)
+{
+    if (n < 1 || !in || !out || (precision != PORTA_FP32 && precision != PORTA_FP64)) return PORTA_EINVAL;
+    for (int i = 0; i < n; ++i) {
+        const double *p = in + (size_t)i * 34;
+        for (int k = 0; k < 34; ++k)
+            if (!std::isfinite(p[k])) return PORTA_EINVAL;
+        if (!(p[4] > 0) || !(p[15] > 0) || !(p[31] > 0) || (p[33] != 0.0 && (!(p[26] > 0) || !(p[32] > 0))))
+            return PORTA_EINVAL;
+    }
+    double *d = nullptr;
+    if (pmalloc(&d, sizeof(double) * 39 * (size_t)n) != cudaSuccess) return PORTA_ENOMEM;
+    cudaError_t e = cudaMemcpy(d, in, sizeof(double) * 34 * (size_t)n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = run_step_eval(precision, n, d, d + 34 * (size_t)n, nullptr);
+    if (e == cudaSuccess) e = cudaMemcpy(out, d + 34 * (size_t)n, sizeof(double) * 5 * (size_t)n, cudaMemcpyDeviceToHost);
+    pfree(d);
+    return e == cudaSuccess ? PORTA_OK : PORTA_ECUDA;
+}
+
 int porta_autotune(porta_ctx *c, int *cluster, int *nu_group)
 {
     if (!c) return PORTA_EINVAL;

@@ -51,19 +51,24 @@ __device__ __forceinline__ Real horner(Real t)
     return t * horner_tail<Real, COEF, 1, DEG>(t);
 }
 
+// The linear-interpolation coefficients follow from the quadratic ones: a
+// linear source on MO is the Bezier curve whose control point is the midpoint
+// c_M = (y_M + y_O)/2, so psi'_M = w_M + w_C/2 and psi'_O = w_O + w_C/2 (all
+// terms positive: no cancellation). Only the three w series are evaluated.
+
 // Double precision: degree 8 (the order of Table 1), crossovers of Table 1
-// (w_M 0.14, w_O and w_C 0.18) and 0.1 for psi'.
+// (w_M 0.14, w_O and w_C 0.18).
 __device__ __forceinline__ Coef<double> coefficients(double t)
 {
     Coef<double> c;
     double e = exp(-t);
     c.e = e;
     double it = 1.0 / t, it2 = it * it;
-    c.pm = t < 0.1 ? horner<double, 8, c_pm>(t) : (1.0 - e * (1.0 + t)) * it;
-    c.po = t < 0.1 ? horner<double, 8, c_po>(t) : (e + t - 1.0) * it;
     c.wm = t < 0.14 ? horner<double, 8, c_wm>(t) : (2.0 - e * (t * t + 2.0 * t + 2.0)) * it2;
     c.wo = t < 0.18 ? horner<double, 8, c_wo>(t) : 1.0 - 2.0 * (e + t - 1.0) * it2;
     c.wc = t < 0.18 ? horner<double, 8, c_wc>(t) : 2.0 * (t - 2.0 + e * (t + 2.0)) * it2;
+    c.pm = c.wm + 0.5 * c.wc;
+    c.po = c.wo + 0.5 * c.wc;
     return c;
 }
 
@@ -76,26 +81,21 @@ __device__ __forceinline__ Coef<float> coefficients(float t)
     Coef<float> c;
     c.e = expf(-t);
     if (t < 0.25f) {
-        c.pm = horner<float, 7, c_pm>(t);
-        c.po = horner<float, 7, c_po>(t);
         c.wm = horner<float, 7, c_wm>(t);
         c.wo = horner<float, 7, c_wo>(t);
         c.wc = horner<float, 7, c_wc>(t);
     } else if (t < 1.5f) {
-        c.pm = horner<float, 12, c_pm>(t);
-        c.po = horner<float, 12, c_po>(t);
         c.wm = horner<float, 12, c_wm>(t);
         c.wo = horner<float, 12, c_wo>(t);
         c.wc = horner<float, 12, c_wc>(t);
     } else {
         const float e = c.e, it = 1.0f / t, it2 = it * it;
-        const float d1 = e + t - 1.0f;
-        c.pm = (1.0f - e * (1.0f + t)) * it;
-        c.po = d1 * it;
         c.wm = (2.0f - e * (t * t + 2.0f * t + 2.0f)) * it2;
-        c.wo = 1.0f - 2.0f * d1 * it2;
+        c.wo = 1.0f - 2.0f * (e + t - 1.0f) * it2;
         c.wc = 2.0f * (t - 2.0f + e * (t + 2.0f)) * it2;
     }
+    c.pm = c.wm + 0.5f * c.wc;
+    c.po = c.wo + 0.5f * c.wc;
     return c;
 }
 
@@ -158,6 +158,93 @@ __device__ __forceinline__ Real control_point(Real yM, Real yO, Real yP, const B
 {
     int branch;
     return control_point_branch(yM, yO, yP, g, branch);
+}
+
+// ---------------------------------------------------------------------------
+// The BESSER-DELO step (Eq. 7) with a general propagation matrix: the seven
+// elements (eta_I, eta_Q, eta_U, eta_V, rho_Q, rho_U, rho_V) at M and at O,
+// K' = K/eta_I - 1 with the off-diagonal pattern of the Unno-Rachkovsky
+// matrix, kappa^-1 = 1 + psi'_O K'_O (Eq. 8) solved by Gaussian elimination
+// with partial pivoting. The two-level sweeps use its specializations (an I-V
+// block, or the arrow of dichroism); this form is the general one.
+// ---------------------------------------------------------------------------
+template <typename Real>
+__device__ __forceinline__ void kprime4(const Real *eta, Real K[4][4])
+{
+    const Real a = Real(1) / eta[0];
+    const Real q = eta[1] * a, u = eta[2] * a, v = eta[3] * a, rq = eta[4] * a, ru = eta[5] * a, rv = eta[6] * a;
+    K[0][0] = 0;  K[0][1] = q;   K[0][2] = u;   K[0][3] = v;
+    K[1][0] = q;  K[1][1] = 0;   K[1][2] = rv;  K[1][3] = -ru;
+    K[2][0] = u;  K[2][1] = -rv; K[2][2] = 0;   K[2][3] = rq;
+    K[3][0] = v;  K[3][1] = ru;  K[3][2] = -rq; K[3][3] = 0;
+}
+
+template <typename Real>
+__device__ __forceinline__ void delo_step_general(const Real IM[4], const Real etaM[7], const Real epsM[4],
+                                                  const Real etaO[7], const Real epsO[4], Real etaP_I,
+                                                  const Real epsP[4], Real dsM, Real dsP, bool has_p, Real IO[4],
+                                                  Real &lstar)
+{
+    Real SM[4], SO[4], SP[4];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+        SM[s] = epsM[s] / etaM[0];
+        SO[s] = epsO[s] / etaO[0];
+        SP[s] = has_p ? epsP[s] / etaP_I : Real(0);
+    }
+    const Real tMO = Real(0.5) * (etaM[0] + etaO[0]) * dsM;
+    const Real tOP = has_p ? Real(0.5) * (etaO[0] + etaP_I) * dsP : Real(1);
+    const Coef<Real> co = coefficients(tMO);
+    Real cM[4];
+    if (has_p) {
+        const BesserGeom<Real> bg = besser_geom(tMO, tOP);
+#pragma unroll
+        for (int s = 0; s < 4; ++s) cM[s] = control_point(SM[s], SO[s], SP[s], bg);
+    } else {
+#pragma unroll
+        for (int s = 0; s < 4; ++s) cM[s] = Real(0.5) * (SM[s] + SO[s]);
+    }
+    Real kM[4][4], kO[4][4], A[4][5];
+    kprime4(etaM, kM);
+    kprime4(etaO, kO);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        Real acc = co.e * IM[r];
+#pragma unroll
+        for (int s = 0; s < 4; ++s) acc -= co.pm * kM[r][s] * IM[s];
+        A[r][4] = acc + co.wm * SM[r] + co.wo * SO[r] + co.wc * cM[r];
+#pragma unroll
+        for (int s = 0; s < 4; ++s) A[r][s] = (r == s ? Real(1) : Real(0)) + co.po * kO[r][s];
+    }
+    // elimination with partial pivoting (the diagonal is 1 + 0, off-diagonals psi'_O K'_O)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        int piv = c;
+#pragma unroll
+        for (int r = c + 1; r < 4; ++r)
+            if (fabs(A[r][c]) > fabs(A[piv][c])) piv = r;
+#pragma unroll
+        for (int s = 0; s < 5; ++s) {
+            const Real x = A[c][s];
+            A[c][s] = A[piv][s];
+            A[piv][s] = x;
+        }
+        const Real inv = Real(1) / A[c][c];
+#pragma unroll
+        for (int r = c + 1; r < 4; ++r) {
+            const Real f = A[r][c] * inv;
+#pragma unroll
+            for (int s = c; s < 5; ++s) A[r][s] -= f * A[c][s];
+        }
+    }
+#pragma unroll
+    for (int r = 3; r >= 0; --r) {
+        Real s = A[r][4];
+#pragma unroll
+        for (int q = r + 1; q < 4; ++q) s -= A[r][q] * IO[q];
+        IO[r] = s / A[r][r];
+    }
+    lstar = co.wo + (has_p ? co.wc : Real(0.5) * co.wc);
 }
 
 // ---------------------------------------------------------------------------

@@ -181,6 +181,32 @@ __global__ void to_real_kernel(long long n, const double *x, Real *y)
     if (i < n) y[i] = (Real)x[i];
 }
 
+// diagnostic: the general BESSER-DELO step (delo_step_general) on a batch of
+// inputs [n][34]: IM 4, eta_M 7, eps_M 4, eta_O 7, eps_O 4, eta_P,I 1, eps_P 4,
+// ds_M, ds_P, has_p; outputs [n][5]: I_O 4, Lambda*
+template <typename Real>
+__global__ void step_eval_kernel(int n, const double *in, double *out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double *p = in + (long long)i * 34;
+    Real IM[4], eM[7], sM[4], eO[7], sO[4], sP[4];
+    for (int k = 0; k < 4; ++k) { IM[k] = (Real)p[k]; sM[k] = (Real)p[11 + k]; sO[k] = (Real)p[22 + k]; sP[k] = (Real)p[27 + k]; }
+    for (int k = 0; k < 7; ++k) { eM[k] = (Real)p[4 + k]; eO[k] = (Real)p[15 + k]; }
+    Real IO[4], ls;
+    delo_step_general<Real>(IM, eM, sM, eO, sO, (Real)p[26], sP, (Real)p[31], (Real)p[32], p[33] != 0.0, IO, ls);
+    for (int k = 0; k < 4; ++k) out[(long long)i * 5 + k] = (double)IO[k];
+    out[(long long)i * 5 + 4] = (double)ls;
+}
+
+cudaError_t run_step_eval(int precision, int n, const double *in, double *out, cudaStream_t st)
+{
+    const int bs = 128;
+    if (precision == PORTA_FP32) step_eval_kernel<float><<<(n + bs - 1) / bs, bs, 0, st>>>(n, in, out);
+    else step_eval_kernel<double><<<(n + bs - 1) / bs, bs, 0, st>>>(n, in, out);
+    return cudaGetLastError();
+}
+
 // diagnostic: the sweep's coefficient function (Eqs. 9-13 / Table 1) on the GPU
 template <typename Real>
 __global__ void coefficients_kernel(int n, const double *t, double *out)

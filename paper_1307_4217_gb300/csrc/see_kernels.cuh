@@ -33,6 +33,7 @@ cudaError_t run_count_bad(long long n, const double *x, double lo_excl, double h
                           cudaStream_t st);
 template <typename Real>
 cudaError_t run_coefficients(int n, const double *t, double *out, cudaStream_t st);
+cudaError_t run_step_eval(int precision, int n, const double *in, double *out, cudaStream_t st);
 template <typename Real>
 cudaError_t run_to_real(long long n, const double *x, void *y, cudaStream_t st);
 

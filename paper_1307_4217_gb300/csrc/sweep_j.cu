@@ -349,6 +349,13 @@ __device__ __forceinline__ void jsweep_item(const SweepArgs<Real> &a, cg::cluste
         const Real dsM = Real(0.5) * gq.ds, dsP = has_p ? Real(0.5) * gp.ds : Real(0);
         const Real wM[4] = {mx0 * my0, mx1 * my0, mx0 * my1, mx1 * my1};
         const Real wP[4] = {px0 * py0, px1 * py0, px0 * py1, px1 * py1};
+        // the weights as pairs (both lanes equal), for the pair arithmetic
+        P2 wM2[4], wP2[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            wM2[k] = pmk(wM[k], wM[k]);
+            wP2[k] = pmk(wP[k], wP[k]);
+        }
         const Real *cMb = coef + sM * F * cplane, *cPb = coef + sP * F * cplane;
         const V *rMb = ringv + sM * W::s_chunks * nodes, *rOb = ringv + sO * W::s_chunks * nodes;
         const V *rPb = ringv + sP * W::s_chunks * nodes;
@@ -409,17 +416,20 @@ __device__ __forceinline__ void jsweep_item(const SweepArgs<Real> &a, cg::cluste
                     const int cm = (c == 0) ? nx - 1 : c - 1;
                     const int rM[4] = {(l + 1) * nx + c, (l + 1) * nx + c1, (l + 2) * nx + c, (l + 2) * nx + c1};
                     const int rP[4] = {l * nx + cm, l * nx + c, (l + 1) * nx + cm, (l + 1) * nx + c};
-                    // upwind corners' source vectors, held across the frequency loop (the
-                    // downwind corners' are read again for each frequency: holding both
-                    // spills at the register cap)
+                    // upwind corners' source vectors times their bilinear weights, held
+                    // across the frequency loop (the downwind corners' sources are read
+                    // again for each frequency: holding both spills at the register cap)
                     Real SMk[4][W::s_words];
+                    P2 A01[4], A23[4];
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
                         if constexpr (NS == 1) {
-                            SMk[k][0] = ring[sM * nodes + rM[k]];
+                            SMk[k][0] = wM[k] * ring[sM * nodes + rM[k]];
                         } else {
 #pragma unroll
                             for (int h = 0; h < W::s_chunks; ++h) chunk_get<Real>(rMb + h * nodes + rM[k], SMk[k] + h * W::per);
+                            A01[k] = pmul(wM2[k], pmk(SMk[k][0], SMk[k][1]));
+                            A23[k] = pmul(wM2[k], pmk(SMk[k][2], SMk[k][3]));
                         }
                     }
                     const bool last_row = (l + 1 == R);
@@ -444,9 +454,9 @@ __device__ __forceinline__ void jsweep_item(const SweepArgs<Real> &a, cg::cluste
                             Real etaM = 0, epsM = 0, etaP = 0, epsP = 0;
 #pragma unroll
                             for (int k = 0; k < 4; ++k) {
-                                const Real we = wM[k] * cM[rM[k]];
-                                etaM += we;
-                                epsM += we * SMk[k][0];
+                                const Real ek = cM[rM[k]];
+                                etaM += wM[k] * ek;
+                                epsM += SMk[k][0] * ek;           // (w S)_k eta_k
                             }
                             if (has_p) {
 #pragma unroll
@@ -487,25 +497,24 @@ __device__ __forceinline__ void jsweep_item(const SweepArgs<Real> &a, cg::cluste
                                 StokesIO<Real, 4>::load(pl, ipts, ilo + c1, t[1]);
                                 StokesIO<Real, 4>::load(ph, ipts, ihi + c, t[2]);
                                 StokesIO<Real, 4>::load(ph, ipts, ihi + c1, t[3]);
-                                IM01 = pmul(pmk(wM[0], wM[0]), pmk(t[0][0], t[0][1]));
-                                IM23 = pmul(pmk(wM[0], wM[0]), pmk(t[0][2], t[0][3]));
+                                IM01 = pmul(wM2[0], pmk(t[0][0], t[0][1]));
+                                IM23 = pmul(wM2[0], pmk(t[0][2], t[0][3]));
 #pragma unroll
                                 for (int k = 1; k < 4; ++k) {
-                                    IM01 = pfma(pmk(wM[k], wM[k]), pmk(t[k][0], t[k][1]), IM01);
-                                    IM23 = pfma(pmk(wM[k], wM[k]), pmk(t[k][2], t[k][3]), IM23);
+                                    IM01 = pfma(wM2[k], pmk(t[k][0], t[k][1]), IM01);
+                                    IM23 = pfma(wM2[k], pmk(t[k][2], t[k][3]), IM23);
                                 }
                             }
                             // a2-a3: transfer coefficients at M and P from the corners' (eta_I, eta_V):
-                            // (eta, eta_V) += w (eta_k, eta_V,k); (eps_I, eps_Q) += w eta_k (S_I, S_Q)_k;
-                            // (eps_U, eps_V) += (w eta_k, w eta_V,k) (S_U, S^0_0)_k
+                            // (eta, eta_V) += w (eta_k, eta_V,k); (eps_I, eps_Q) += eta_k w (S_I, S_Q)_k;
+                            // (eps_U, eps_V) += (eta_k, eta_V,k) w (S_U, S^0_0)_k
                             P2 eM = pmk(Real(0), Real(0)), eM01 = eM, eM23 = eM;
 #pragma unroll
                             for (int k = 0; k < 4; ++k) {
-                                const R2<Real> e2 = reinterpret_cast<const R2<Real> *>(cM)[rM[k]];
-                                const P2 wk = pmul(pmk(wM[k], wM[k]), pmk(e2.x, e2.y));
-                                eM = padd(eM, wk);
-                                eM01 = pfma(pmk(wk.x, wk.x), pmk(SMk[k][0], SMk[k][1]), eM01);
-                                eM23 = pfma(wk, pmk(SMk[k][2], SMk[k][3]), eM23);
+                                const P2 e2 = reinterpret_cast<const P2 *>(cM)[rM[k]];
+                                eM = pfma(wM2[k], e2, eM);
+                                eM01 = pfma(A01[k], pmk(e2.x, e2.x), eM01);
+                                eM23 = pfma(A23[k], e2, eM23);
                             }
                             P2 eP = pmk(Real(0), Real(0)), eP01 = eP, eP23 = eP;
                             if (has_p) {
@@ -514,8 +523,8 @@ __device__ __forceinline__ void jsweep_item(const SweepArgs<Real> &a, cg::cluste
                                     Real sp[4];
 #pragma unroll
                                     for (int h = 0; h < W::s_chunks; ++h) chunk_get<Real>(rPb + h * nodes + rP[k], sp + h * W::per);
-                                    const R2<Real> e2 = reinterpret_cast<const R2<Real> *>(cP)[rP[k]];
-                                    const P2 wk = pmul(pmk(wP[k], wP[k]), pmk(e2.x, e2.y));
+                                    const P2 e2 = reinterpret_cast<const P2 *>(cP)[rP[k]];
+                                    const P2 wk = pmul(wP2[k], e2);
                                     eP = padd(eP, wk);
                                     eP01 = pfma(pmk(wk.x, wk.x), pmk(sp[0], sp[1]), eP01);
                                     eP23 = pfma(wk, pmk(sp[2], sp[3]), eP23);
