@@ -1,6 +1,7 @@
 // C ABI of the formal-solver library (include/porta.h): argument checks,
-// quadratures and per-ray plane geometry (host, FP64), device buffers, and the
-// launch sequence formal_solve -> accumulate_jkq -> see_update.
+// quadratures and per-ray plane geometry (host, FP64), device buffers, the
+// launch sequence formal_solve -> accumulate_jkq -> see_update, the captured
+// Jacobi iteration and the frequency bands of a formal solution.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -13,9 +14,7 @@
 #include <unordered_map>
 #include <vector>
 
-#include "porta.h"
-#include "porta_ctx.h"
-#include "porta_internal.cuh"
+#include "api_internal.h"
 #include "mg_kernels.cuh"
 #include "ml_kernels.cuh"
 #include "mlpol_kernels.cuh"
@@ -23,7 +22,7 @@
 
 using namespace porta;
 
-namespace {
+namespace porta_api {
 
 const char *kNullCtx = "null context";
 
@@ -33,12 +32,6 @@ int fail(porta_ctx *c, int code, const std::string &msg)
     return code;
 }
 
-#define CK(call)                                                                               \
-    do {                                                                                       \
-        cudaError_t e_ = (call);                                                               \
-        if (e_ != cudaSuccess)                                                                 \
-            return fail(c, PORTA_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));   \
-    } while (0)
 
 // Device allocations of the library go through pmalloc / pfree, which keep the
 // live byte count and honour the process-wide cap of porta_set_device_limit: an
@@ -60,14 +53,6 @@ cudaError_t pmalloc_bytes(void **p, size_t bytes)
     return cudaSuccess;
 }
 
-template <typename T>
-cudaError_t pmalloc(T **p, size_t bytes)
-{
-    void *q = nullptr;
-    cudaError_t e = pmalloc_bytes(&q, bytes);
-    *p = (T *)q;
-    return e;
-}
 
 cudaError_t pfree(void *p)
 {
@@ -83,47 +68,35 @@ cudaError_t pfree(void *p)
     return cudaFree(p);
 }
 
-template <typename T>
-cudaError_t dalloc(T **p, size_t n)
-{
-    *p = nullptr;
-    if (n == 0) return cudaSuccess;
-    return pmalloc(p, n * sizeof(T));
-}
-
 // Gauss-Legendre nodes/weights on (0, 1): Newton's method on the Legendre
-// polynomial P_n evaluated by its three-term recurrence.
-void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w)
+// polynomial P_n evaluated by its three-term recurrence; x and w receive n values
+// in increasing order of x
+void gauss_legendre(int n, double *x, double *w)
 {
-    x.assign(n, 0.0);
-    w.assign(n, 0.0);
+    auto legendre = [n](double t, double &p, double &pm1) {
+        pm1 = 1.0;
+        p = t;
+        for (int k = 1; k < n; ++k) {
+            double pn = ((2 * k + 1) * t * p - k * pm1) / (k + 1);
+            pm1 = p;
+            p = pn;
+        }
+        if (n == 1) {
+            p = t;
+            pm1 = 1.0;
+        }
+    };
     for (int i = 0; i < n; ++i) {
         double t = std::cos(M_PI * (4.0 * i + 3.0) / (4.0 * n + 2.0));
-        double dp = 1.0;
+        double p, pm1;
         for (int it = 0; it < 100; ++it) {
-            double pm1 = 1.0, p = t;
-            for (int k = 1; k < n; ++k) {
-                double pn = ((2 * k + 1) * t * p - k * pm1) / (k + 1);
-                pm1 = p;
-                p = pn;
-            }
-            if (n == 1) { p = t; pm1 = 1.0; }
-            dp = n * (pm1 - t * p) / (1.0 - t * t);
-            double dt = p / dp;
+            legendre(t, p, pm1);
+            double dt = p / (n * (pm1 - t * p) / (1.0 - t * t));
             t -= dt;
-            if (std::fabs(dt) < 1e-16) {
-                // one more derivative evaluation at the final node
-                pm1 = 1.0; p = t;
-                for (int k = 1; k < n; ++k) {
-                    double pn = ((2 * k + 1) * t * p - k * pm1) / (k + 1);
-                    pm1 = p;
-                    p = pn;
-                }
-                if (n == 1) { p = t; pm1 = 1.0; }
-                dp = n * (pm1 - t * p) / (1.0 - t * t);
-                break;
-            }
+            if (std::fabs(dt) < 1e-16) break;
         }
+        legendre(t, p, pm1);   // P'_n at the final node
+        const double dp = n * (pm1 - t * p) / (1.0 - t * t);
         x[n - 1 - i] = 0.5 * (t + 1.0);
         w[n - 1 - i] = 1.0 / ((1.0 - t * t) * dp * dp);   // (2/((1-t^2) P'^2)) / 2
     }
@@ -170,90 +143,8 @@ void drop_graph(porta_ctx *c)
     c->graph_stream = nullptr;
 }
 
-long long wrapll(long long a, long long n)
-{
-    long long r = a % n;
-    return r < 0 ? r + n : r;
-}
-
-// plane geometry of one direction in sweep order (see PlaneGeom) for a grid
-// nx x ny x nz with periods lx, ly and heights z
-template <typename Real>
-void plane_geometry(int nx, int ny, int nz, double lx, double ly, const double *z, double mu, double chi,
-                    PlaneGeom<Real> *g)
-{
-    const bool up = mu > 0;
-    const double st = std::sqrt(std::max(0.0, 1.0 - mu * mu));
-    const double ox = st * std::cos(chi), oy = st * std::sin(chi);
-    const double hx = lx / nx, hy = ly / ny, amu = std::fabs(mu);
-    long long ax = 0, ay = 0;
-    for (int q = 0; q < nz; ++q) {
-        int kz = up ? q : nz - 1 - q;
-        PlaneGeom<Real> p{};
-        p.kz = kz;
-        if (q > 0) {
-            int ku = up ? kz - 1 : kz + 1;
-            double ds = std::fabs(z[kz] - z[ku]) / amu;
-            double dx = ds * ox / hx, dy = ds * oy / hy;
-            double cx = std::ceil(dx), cy = std::ceil(dy);
-            ax = wrapll(ax + (long long)cx, nx);
-            ay = wrapll(ay + (long long)cy, ny);
-            p.tx = (Real)(cx - dx);
-            p.ty = (Real)(cy - dy);
-            p.ds = (Real)ds;
-        }
-        p.ax = (int)ax;
-        p.ay = (int)ay;
-        g[q] = p;
-    }
-}
-
-template <typename Real>
-RayDev<Real> ray_dev(double mu, double chi, double w = 0.0)
-{
-    RayDev<Real> r{};
-    r.w = (Real)w;
-    double st = std::sqrt(std::max(0.0, 1.0 - mu * mu));
-    r.mu = (Real)mu;
-    r.ox = (Real)(st * std::cos(chi));
-    r.oy = (Real)(st * std::sin(chi));
-    r.oz = (Real)mu;
-    double t[18];
-    tkq_tensors(mu, chi, t);
-    for (int i = 0; i < 18; ++i) r.t[i] = (Real)t[i];
-    return r;
-}
-
 int ns_of(int model) { return model == PORTA_MODEL_TWOLEVEL_UNPOL ? 1 : 4; }
 int nl_of(int model) { return model == PORTA_MODEL_TWOLEVEL_UNPOL ? 1 : 6; }
-
-const int kThreads = 512;   // maximum threads per CTA of the sweep kernel
-const int kSmemLimit = 220 * 1024;
-
-// Shared-memory capacities of a launch with cluster size C over all boxes:
-// ring plane (16-byte chunks) and Stokes-plane points, each the maximum over boxes.
-template <typename Real, int NS>
-void launch_caps(const porta_ctx *c, int C, int &ring_plane, int &ipts_max, bool jk = false)
-{
-    const int nch = (NS == 1 ? 4 : 8) * (int)sizeof(Real) / 16;
-    const bool dich = NS == 4 && c->d_dich != nullptr;
-    ring_plane = 0;
-    ipts_max = 0;
-    for (const BoxDev &b : c->boxes) {
-        const int rmax = (b.ny + C - 1) / C;
-        const int chunk = (rmax + 2) * b.nx;
-        if (jk) {
-            // the J^K_Q sweep (sweep_j.cu): ring capacity in nodes
-            ring_plane = std::max(ring_plane, chunk);
-            ipts_max = std::max(ipts_max, rmax * b.nx);
-            continue;
-        }
-        // with dichroism the slots of a second ring (eta_U / eta_I per node) follow the node ring
-        const int dchunks = dich ? (chunk * (int)sizeof(Real) + 15) / 16 : 0;
-        ring_plane = std::max(ring_plane, nch * chunk + dchunks);
-        ipts_max = std::max(ipts_max, rmax * b.nx);
-    }
-}
 
 // The J^K_Q formal solution runs the kernel of sweep_j.cu (per-frequency
 // node coefficients in shared memory) unless the lines carry dichroism, which
@@ -275,83 +166,6 @@ int max_ny(const porta_ctx *c)
     int m = 0;
     for (const BoxDev &b : c->boxes) m = std::max(m, b.ny);
     return m;
-}
-
-// Launch shape of the sweep: cluster size C (CTAs sharing one ray's plane)
-// and frequencies per pass F. Estimated time of a candidate (in units of one
-// point update): the (box, ray) work items spread over the resident clusters,
-// each item costing, per plane and frequency pass, the thread slots of its
-// point updates, the ring fill (halo rows included), the partial-integral
-// writes and a barrier.
-template <typename Real, int NS>
-int choose_launch(porta_ctx *c, LaunchCfg &best, int force_c, int force_f, int nitems, bool jk = false, int nnu = 0)
-{
-    const int NU = nnu > 0 ? nnu : c->n_nu;     // frequencies swept
-    if (force_f > NU) force_f = NU;
-    const int NA = NS == 1 ? 2 : 4;
-    double best_cost = 1e300;
-    best = LaunchCfg{};
-    const int ny_max = max_ny(c);
-    for (int C = 1; C <= 16; ++C) {
-        if (force_c > 0 && C != force_c) continue;
-        if (force_c <= 0 && C > 1 && (C & (C - 1)) != 0 && C != 6 && C != 12) continue;   // heuristic set
-        if (C > ny_max) continue;
-        int ring_plane, ipts_max;
-        launch_caps<Real, NS>(c, C, ring_plane, ipts_max, jk);
-        int fmax = 0;
-        if (jk) {
-            // J^K_Q kernel: besides the Stokes planes, each frequency of a pass keeps
-            // the nodes' coefficients of three planes (jsweep_smem_bytes)
-            for (int f = NU; f >= 1 && fmax == 0; --f)
-                if (jsweep_smem_bytes<Real, NS>(ring_plane, ipts_max, f, kThreads) <= kSmemLimit) fmax = f;
-            if (fmax == 0) continue;
-        } else {
-            const long long ring = 3LL * ring_plane * 16;
-            const long long per_nu = 2LL * ipts_max * NS * (long long)sizeof(Real);
-            const long long scratch = (long long)kThreads * NA * (long long)sizeof(Real);
-            if (ring + per_nu + scratch > kSmemLimit) continue;
-            fmax = (int)std::min<long long>(NU, (kSmemLimit - ring - scratch) / per_nu);
-        }
-        if (force_f > 0) {
-            if (force_f > fmax) continue;
-            fmax = force_f;
-        }
-        const int G = (NU + fmax - 1) / fmax;
-        const int F = (NU + G - 1) / G;
-        // threads: the strip's points times the frequency lanes they can use, whole warps, 64..512
-        const int threads = std::min(kThreads, std::max(64, (ipts_max * F + 31) / 32 * 32));
-        const int smem = jk ? jsweep_smem_bytes<Real, NS>(ring_plane, ipts_max, F, threads)
-                            : sweep_smem_bytes<Real, NS>(ring_plane, ipts_max, F, threads);
-        if (smem > kSmemLimit + 16) continue;
-        int act = 0;
-        if ((jk ? jsweep_max_active_clusters<Real, NS>(C, smem, threads, &act)
-                : max_active_clusters<Real, NS>(C, smem, threads, &act, c->d_dich != nullptr)) != cudaSuccess) {
-            cudaGetLastError();
-            continue;
-        }
-        if (act < 1) continue;
-        const int ncl = std::min(act, nitems);
-        double total = 0.0, item_max = 0.0;
-        for (const BoxDev &b : c->boxes) {
-            const int rmax = (b.ny + C - 1) / C;
-            const double pts = (double)rmax * b.nx;
-            const double slots = std::ceil(pts * F / threads) * kThreads;   // per-SM issue slots per pass
-            const double item = b.nz * G * (slots + 0.15 * (rmax + 2) * b.nx + 0.05 * pts + 300.0);
-            total += item * c->nray;
-            item_max = std::max(item_max, item);
-        }
-        const double cost = c->nbox == 1 ? std::ceil((double)nitems / ncl) * item_max
-                                         : std::max(total / ncl, item_max) * 1.05;
-        if (cost < best_cost) {
-            best_cost = cost;
-            best.cluster = C;
-            best.F = F;
-            best.threads = threads;
-            best.smem = smem;
-            best.clusters = ncl;
-        }
-    }
-    return best.cluster > 0 ? PORTA_OK : PORTA_EINVAL;
 }
 
 // all launch shapes that fit, with their resident-cluster counts
@@ -377,44 +191,6 @@ std::vector<LaunchCfg> candidates(porta_ctx *c, int nitems)
         }
     }
     return out;
-}
-
-template <typename Real>
-SweepArgs<Real> base_args(porta_ctx *c)
-{
-    SweepArgs<Real> a{};
-    a.nnu = c->n_nu;
-    a.nray = c->nray;
-    a.nvox = c->nvox;
-    a.boxes = (const BoxDev *)c->d_boxes;
-    a.bfac = (Real)(2.0 * c->gbar * c->zeta);
-    const Real *atm = (const Real *)c->d_atm;
-    a.chi = atm;
-    a.vel = atm + c->nvox;
-    a.bx = atm + 2 * c->nvox;
-    a.by = atm + 3 * c->nvox;
-    a.bz = atm + 4 * c->nvox;
-    a.bpl = atm + 5 * c->nvox;
-    a.rho = (const Real *)c->d_rhoR;
-    a.dich = (const Real *)c->d_dich;
-    a.xf = (const Real *)c->d_freq;
-    a.wf = (const Real *)c->d_freq + c->n_nu;
-    a.probe_ray = -1;
-    return a;
-}
-
-// fill the launch-dependent fields of the arguments
-template <typename Real>
-void shape_args(porta_ctx *c, SweepArgs<Real> &a, const LaunchCfg &cfg, bool jk = false)
-{
-    a.F = cfg.F;
-    a.ngroups = (a.nnu + cfg.F - 1) / cfg.F;
-    if (c->ns == 1)
-        launch_caps<Real, 1>(c, cfg.cluster, a.ring_plane, a.ipts_max, jk);
-    else
-        launch_caps<Real, 4>(c, cfg.cluster, a.ring_plane, a.ipts_max, jk);
-    a.cstride = jsweep_stride(a.ring_plane * (c->ns == 1 ? 1 : 2), (int)sizeof(Real));
-    a.istride = jsweep_stride(a.ipts_max * c->ns, (int)sizeof(Real));
 }
 
 // one J-mode sweep launch with the kernel use_jk selects
@@ -718,329 +494,6 @@ int autotune_t(porta_ctx *c)
     return rc;
 }
 
-// Launch shape of the emergent sweep for ndir directions: the one given in
-// porta_opts, else timed once per direction count over the fitting shapes
-// (cluster sizes x frequencies per pass; each trial rewrites the same outputs).
-// Leaves the arguments shaped for the chosen launch.
-template <typename Real, int NS>
-int emergent_shape(porta_ctx *c, SweepArgs<Real> &a, int ndir, LaunchCfg &cfg)
-{
-    auto shape = [&](LaunchCfg &k) {
-        shape_args<Real>(c, a, k);
-        a.nitems = ndir * a.ngroups;
-        k.clusters = std::min(k.clusters, a.nitems);
-    };
-    if (c->user_shape || c->emg_tuned.count(ndir)) {
-        if (c->user_shape) {
-            int rc = choose_launch<Real, NS>(c, cfg, c->opt_cluster, c->opt_nu_group, ndir);
-            if (rc) return fail(c, rc, "no sweep launch shape fits this grid");
-        } else {
-            cfg = c->emg_tuned[ndir];
-        }
-        shape(cfg);
-        return PORTA_OK;
-    }
-    std::vector<LaunchCfg> cand;
-    const int sizes[] = {1, 2, 3, 4, 6, 8, 12, 16};
-    for (int C : sizes) {
-        if (C > c->ny) continue;
-        int last_f = -1;
-        for (int G = 1; G <= c->n_nu; ++G) {
-            const int F = (c->n_nu + G - 1) / G;
-            if (F == last_f) continue;
-            last_f = F;
-            LaunchCfg k{};
-            if (choose_launch<Real, NS>(c, k, C, F, ndir * G) == PORTA_OK && k.F == F) cand.push_back(k);
-        }
-    }
-    if (cand.empty()) return fail(c, PORTA_EINVAL, "no sweep launch shape fits this grid");
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    CK(cudaEventCreate(&e0));
-    CK(cudaEventCreate(&e1));
-    float best = 1e30f;
-    cudaError_t e = cudaSuccess;
-    for (LaunchCfg k : cand) {
-        shape(k);
-        float ms = 0;
-        e = cudaEventRecord(e0, c->stream);
-        if (e == cudaSuccess) e = launch_sweep<Real, NS>(a, MODE_EMERGENT, k, c->stream);
-        if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
-        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-        if (e != cudaSuccess) break;
-        if (ms < best) {
-            best = ms;
-            cfg = k;
-        }
-    }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    if (e != cudaSuccess) return fail(c, PORTA_ECUDA, std::string("emergent shape timing: ") + cudaGetErrorString(e));
-    c->emg_tuned[ndir] = cfg;
-    shape(cfg);
-    return PORTA_OK;
-}
-
-template <typename Real>
-int emergent_t(porta_ctx *c, int ndir, const double *mu, const double *chi, double *dout, int box = 0)
-{
-    std::vector<PlaneGeom<Real>> geom((size_t)ndir * c->nz);
-    std::vector<RayDev<Real>> rays(ndir);
-    for (int d = 0; d < ndir; ++d) {
-        plane_geometry<Real>(c->nx, c->ny, c->nz, c->lx, c->ly, c->z.data(), mu[d], chi[d], geom.data() + (size_t)d * c->nz);
-        rays[d] = ray_dev<Real>(mu[d], chi[d]);
-    }
-    PlaneGeom<Real> *dg = nullptr;
-    RayDev<Real> *dr = nullptr;
-    BoxDev *dbox = nullptr;
-    CK(dalloc(&dg, geom.size()));
-    cudaError_t e2 = dalloc(&dr, rays.size());
-    if (e2 == cudaSuccess) e2 = pmalloc(&dbox, sizeof(BoxDev));
-    if (e2 != cudaSuccess) {
-        pfree(dg);
-        if (dr) pfree(dr);
-        return fail(c, PORTA_ENOMEM, "emergent: device allocation");
-    }
-    int rc = PORTA_OK;
-    do {
-        // the box of this call (a line of a multilevel context shares the grid): its
-        // voxels, with the per-direction geometry of this call (geometry offset 0)
-        BoxDev hb = c->boxes[box];
-        hb.geom0 = 0;
-        cudaError_t e = cudaMemcpyAsync(dg, geom.data(), geom.size() * sizeof(geom[0]), cudaMemcpyHostToDevice, c->stream);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(dr, rays.data(), rays.size() * sizeof(rays[0]), cudaMemcpyHostToDevice, c->stream);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(dbox, &hb, sizeof(hb), cudaMemcpyHostToDevice, c->stream);
-        if (e != cudaSuccess) { rc = fail(c, PORTA_ECUDA, cudaGetErrorString(e)); break; }
-        SweepArgs<Real> a = base_args<Real>(c);
-        a.boxes = dbox;
-        a.geom = dg;
-        a.rays = dr;
-        a.out = dout;
-        LaunchCfg cfg{};
-        rc = c->ns == 1 ? emergent_shape<Real, 1>(c, a, ndir, cfg) : emergent_shape<Real, 4>(c, a, ndir, cfg);
-        if (rc) break;
-        e = c->ns == 1 ? launch_sweep<Real, 1>(a, MODE_EMERGENT, cfg, c->stream)
-                       : launch_sweep<Real, 4>(a, MODE_EMERGENT, cfg, c->stream);
-        if (e != cudaSuccess) { rc = fail(c, PORTA_ECUDA, std::string("emergent launch: ") + cudaGetErrorString(e)); break; }
-        e = cudaStreamSynchronize(c->stream);
-        if (e != cudaSuccess) rc = fail(c, PORTA_ECUDA, std::string("emergent: ") + cudaGetErrorString(e));
-    } while (0);
-    cudaStreamSynchronize(c->stream);
-    pfree(dg);
-    pfree(dr);
-    pfree(dbox);
-    return rc;
-}
-
-// grow-only device buffer held by the context
-cudaError_t ensure_buf(void **p, size_t &cap, size_t need)
-{
-    if (need <= cap && *p) return cudaSuccess;
-    if (*p) pfree(*p);
-    *p = nullptr;
-    cap = 0;
-    cudaError_t e = pmalloc(p, need);
-    if (e == cudaSuccess) cap = need;
-    return e;
-}
-
-const int kAdjThreads = 256;   // maximum threads per CTA of the adjoint kernel
-
-// Launch shape of the adjoint sweep: cluster size C and frequencies per pass
-// F. Estimated time: the (direction, frequency group) items spread over the
-// resident clusters, each costing per plane its point passes (F frequencies
-// per pass) plus the two cluster barriers, the ring fill and the node
-// finalization.
-template <typename Real, int NS>
-int choose_adjoint(porta_ctx *c, LaunchCfg &best, int force_c, int force_f, int ndir,
-                   std::vector<LaunchCfg> *all = nullptr)
-{
-    best = LaunchCfg{};
-    double best_cost = 1e300;
-    for (int C = 1; C <= 16; ++C) {
-        if (force_c > 0 && C != force_c) continue;
-        if (force_c <= 0 && C > 1 && (C & (C - 1)) != 0 && C != 6 && C != 12) continue;
-        if (C > c->ny) continue;
-        int ring_plane, ipts;
-        launch_caps<Real, NS>(c, C, ring_plane, ipts);
-        const int threads = std::min(kAdjThreads, std::max(64, (ipts + 31) / 32 * 32));
-        int last_f = -1;
-        for (int G = 1; G <= c->n_nu; ++G) {
-            const int F = force_f > 0 ? force_f : (c->n_nu + G - 1) / G;
-            if (F == last_f) continue;
-            last_f = F;
-            const int smem = adjoint_smem_bytes<Real, NS>(ring_plane, ipts, ipts + c->nx, F);
-            if (smem > kSmemLimit) continue;
-            int act = 0;
-            if (adjoint_max_active_clusters<Real, NS>(C, smem, threads, &act) != cudaSuccess) {
-                cudaGetLastError();
-                continue;
-            }
-            if (act < 1) continue;
-            const int Gr = (c->n_nu + F - 1) / F;
-            const int items = ndir * Gr;
-            const int ncl = std::min(act, items);
-            const double passes = std::ceil((double)ipts / threads);
-            const double item = c->nz * (passes * F * 3.0 + 0.5 * F + 4.0);
-            const double cost = std::ceil((double)items / ncl) * item;
-            if (all) {
-                LaunchCfg k{};
-                k.cluster = C;
-                k.F = F;
-                k.threads = threads;
-                k.smem = smem;
-                k.clusters = ncl;
-                all->push_back(k);
-            }
-            if (cost < best_cost) {
-                best_cost = cost;
-                best.cluster = C;
-                best.F = F;
-                best.threads = threads;
-                best.smem = smem;
-                best.clusters = ncl;
-            }
-        }
-    }
-    return best.cluster > 0 ? PORTA_OK : PORTA_EINVAL;
-}
-
-// forward emergent sweep with the tape, adjoint sweep, fixed-order reduction;
-// all pointers are device memory; dout may be null
-template <typename Real>
-int emergent_vjp_t(porta_ctx *c, int ndir, const double *mu, const double *chi, const double *dgrad, double *dout,
-                   double *dg_chi, double *dg_e, double *dg_b, double *dg_rho = nullptr)
-{
-    std::vector<PlaneGeom<Real>> geom((size_t)ndir * c->nz);
-    std::vector<RayDev<Real>> rays(ndir);
-    for (int d = 0; d < ndir; ++d) {
-        plane_geometry<Real>(c->nx, c->ny, c->nz, c->lx, c->ly, c->z.data(), mu[d], chi[d], geom.data() + (size_t)d * c->nz);
-        rays[d] = ray_dev<Real>(mu[d], chi[d]);
-    }
-    const long long nxy = (long long)c->nx * c->ny;
-    PlaneGeom<Real> *dg = nullptr;
-    RayDev<Real> *dr = nullptr;
-    double *scratch_out = nullptr;
-    CK(dalloc(&dg, geom.size()));
-    cudaError_t e2 = dalloc(&dr, rays.size());
-    if (e2 == cudaSuccess && !dout) e2 = dalloc(&scratch_out, (size_t)ndir * c->n_nu * nxy * c->ns);
-    int rc = PORTA_OK;
-    do {
-        if (e2 != cudaSuccess) { rc = fail(c, PORTA_ENOMEM, "emergent_vjp: device allocation"); break; }
-        cudaError_t e = cudaMemcpyAsync(dg, geom.data(), geom.size() * sizeof(geom[0]), cudaMemcpyHostToDevice, c->stream);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(dr, rays.data(), rays.size() * sizeof(rays[0]), cudaMemcpyHostToDevice, c->stream);
-        if (e == cudaSuccess)
-            e = ensure_buf(&c->d_tape, c->tape_bytes, (size_t)ndir * c->n_nu * c->nvox * c->ns * sizeof(Real));
-        if (e != cudaSuccess) { rc = fail(c, PORTA_ENOMEM, std::string("emergent_vjp: ") + cudaGetErrorString(e)); break; }
-        // forward: emergent Stokes and the Stokes vectors of every plane
-        for (int k = 0; k < 3 && e == cudaSuccess; ++k)
-            if (!c->adj_ev[k]) e = cudaEventCreate(&c->adj_ev[k]);
-        if (e != cudaSuccess) { rc = fail(c, PORTA_ECUDA, std::string("emergent_vjp: ") + cudaGetErrorString(e)); break; }
-        SweepArgs<Real> a = base_args<Real>(c);
-        a.geom = dg;
-        a.rays = dr;
-        a.out = dout ? dout : scratch_out;
-        a.store = (Real *)c->d_tape;
-        LaunchCfg cfg{};
-        rc = c->ns == 1 ? emergent_shape<Real, 1>(c, a, ndir, cfg) : emergent_shape<Real, 4>(c, a, ndir, cfg);
-        if (rc) break;
-        e = cudaEventRecord(c->adj_ev[0], c->stream);
-        if (e == cudaSuccess)
-            e = c->ns == 1 ? launch_sweep<Real, 1>(a, MODE_EMERGENT, cfg, c->stream)
-                           : launch_sweep<Real, 4>(a, MODE_EMERGENT, cfg, c->stream);
-        if (e == cudaSuccess) e = cudaEventRecord(c->adj_ev[1], c->stream);
-        if (e != cudaSuccess) { rc = fail(c, PORTA_ECUDA, std::string("emergent_vjp forward: ") + cudaGetErrorString(e)); break; }
-        // adjoint: launch shape forced, or timed once per direction count over
-        // every fitting shape (each trial overwrites the same outputs)
-        LaunchCfg acfg{};
-        std::vector<LaunchCfg> cand;
-        const bool forced = c->adj_cluster > 0 || c->adj_nu_group > 0;
-        const bool tune = !forced && c->adj_tuned_ndir != ndir;
-        rc = c->ns == 1 ? choose_adjoint<Real, 1>(c, acfg, c->adj_cluster, c->adj_nu_group, ndir, tune ? &cand : nullptr)
-                        : choose_adjoint<Real, 4>(c, acfg, c->adj_cluster, c->adj_nu_group, ndir, tune ? &cand : nullptr);
-        if (rc) { rc = fail(c, rc, "no adjoint launch shape fits this grid"); break; }
-        if (!forced && !tune) acfg = c->adj_tuned;
-        e = ensure_buf(&c->d_gpart, c->gpart_bytes, (size_t)ndir * c->n_nu * 3 * c->nvox * sizeof(Real));
-        if (e != cudaSuccess) { rc = fail(c, PORTA_ENOMEM, "emergent_vjp: partial-gradient allocation"); break; }
-        auto args_for = [&](LaunchCfg &k) {
-            SweepArgs<Real> b = base_args<Real>(c);
-            b.geom = dg;
-            b.rays = dr;
-            b.store = (Real *)c->d_tape;
-            b.gout = dgrad;
-            b.gpart = (Real *)c->d_gpart;
-            b.F = k.F;
-            b.ngroups = (c->n_nu + k.F - 1) / k.F;
-            if (c->ns == 1)
-                launch_caps<Real, 1>(c, k.cluster, b.ring_plane, b.ipts_max);
-            else
-                launch_caps<Real, 4>(c, k.cluster, b.ring_plane, b.ipts_max);
-            b.nitems = ndir * b.ngroups;
-            k.clusters = std::min(k.clusters, b.nitems);
-            return b;
-        };
-        if (tune) {
-            // the forward's time is read before the trials reuse the events
-            e = cudaEventSynchronize(c->adj_ev[1]);
-            if (e == cudaSuccess) e = cudaEventElapsedTime(&c->adj_fwd_ms, c->adj_ev[0], c->adj_ev[1]);
-            float best_ms = 1e30f;
-            for (LaunchCfg k : cand) {
-                SweepArgs<Real> b = args_for(k);
-                float ms = 0;
-                e = cudaEventRecord(c->adj_ev[1], c->stream);
-                if (e == cudaSuccess)
-                    e = c->ns == 1 ? launch_adjoint<Real, 1>(b, k, c->stream) : launch_adjoint<Real, 4>(b, k, c->stream);
-                if (e == cudaSuccess) e = cudaEventRecord(c->adj_ev[2], c->stream);
-                if (e == cudaSuccess) e = cudaEventSynchronize(c->adj_ev[2]);
-                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, c->adj_ev[1], c->adj_ev[2]);
-                if (e != cudaSuccess) break;
-                if (ms < best_ms) {
-                    best_ms = ms;
-                    acfg = k;
-                }
-            }
-            if (e != cudaSuccess) { rc = fail(c, PORTA_ECUDA, std::string("emergent_vjp tuning: ") + cudaGetErrorString(e)); break; }
-            c->adj_tuned = acfg;
-            c->adj_tuned_ndir = ndir;
-            e = cudaEventRecord(c->adj_ev[1], c->stream);
-        }
-        SweepArgs<Real> b = args_for(acfg);
-        if (!dg_rho) {
-            if (e == cudaSuccess)
-                e = c->ns == 1 ? launch_adjoint<Real, 1>(b, acfg, c->stream) : launch_adjoint<Real, 4>(b, acfg, c->stream);
-            if (e == cudaSuccess)
-                e = launch_adjoint_reduce<Real>((const Real *)c->d_gpart, b.nitems, b.ngroups, c->nvox, dr,
-                                                2.0 * c->gbar * c->zeta, dg_chi, dg_e, c->ns == 1 ? nullptr : dg_b, c->stream);
-        } else {
-            // gradients in the unknowns: per-cluster accumulators, then their sum
-            if (e == cudaSuccess)
-                e = ensure_buf((void **)&c->d_gacc, c->gacc_bytes, (size_t)acfg.clusters * 10 * c->nvox * sizeof(double));
-            if (e == cudaSuccess) e = cudaMemsetAsync(c->d_gacc, 0, (size_t)acfg.clusters * 10 * c->nvox * sizeof(double), c->stream);
-            b.gacc = c->d_gacc;
-            if (e == cudaSuccess)
-                e = c->ns == 1 ? launch_adjoint<Real, 1>(b, acfg, c->stream, 1) : launch_adjoint<Real, 4>(b, acfg, c->stream, 1);
-            if (e == cudaSuccess)
-                e = launch_adjoint_acc_reduce(c->d_gacc, acfg.clusters, c->nvox, c->nl, dg_chi, c->ns == 1 ? nullptr : dg_b,
-                                              dg_rho, c->stream);
-        }
-        if (e == cudaSuccess) e = cudaEventRecord(c->adj_ev[2], c->stream);
-        if (e != cudaSuccess) { rc = fail(c, PORTA_ECUDA, std::string("emergent_vjp adjoint: ") + cudaGetErrorString(e)); break; }
-        c->last_adj = acfg;
-        e = cudaStreamSynchronize(c->stream);
-        if (e == cudaSuccess && !tune) e = cudaEventElapsedTime(&c->adj_fwd_ms, c->adj_ev[0], c->adj_ev[1]);
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&c->adj_rev_ms, c->adj_ev[1], c->adj_ev[2]);
-        if (e != cudaSuccess) rc = fail(c, PORTA_ECUDA, std::string("emergent_vjp: ") + cudaGetErrorString(e));
-    } while (0);
-    cudaStreamSynchronize(c->stream);
-    pfree(dg);
-    pfree(dr);
-    if (scratch_out) pfree(scratch_out);
-    return rc;
-}
-
-void mg_free(porta_ctx *c);
-void it_free(porta_ctx *c);
-
 void free_all(porta_ctx *c)
 {
     drop_graph(c);
@@ -1104,443 +557,6 @@ int count_bad(porta_ctx *c, const double *d, long long n, double lo, double hi, 
     return PORTA_OK;
 }
 
-
-// ---------------------------------------------------------------- differentiation through iterations
-
-// Gradients of sum g_J J^K_Q + sum g_L Lambda-bar* (the sums of a formal solution at
-// the current rho) with respect to chi at fixed rho (added), B (added) and rho
-// (overwritten). Rays in batches: the emergent-mode sweep over a batch's rays writes
-// the tape, the adjoint (form 2) accumulates per cluster; one sum at the end.
-template <typename Real>
-int jkq_vjp_t(porta_ctx *c, const double *dgj, const double *dgl, double *dg_chi, double *dg_b, double *dg_rho)
-{
-    const long long nxy = (long long)c->nx * c->ny;
-    const size_t per_ray = (size_t)c->n_nu * c->nvox * c->ns * sizeof(Real);
-    // batches of equal size (the last one may be smaller) within the tape limit
-    const int nbmax = (int)std::max<size_t>(1, std::min<size_t>(c->nray, c->tape_limit / per_ray));
-    const int nbatch = (c->nray + nbmax - 1) / nbmax;
-    const int nb = (c->nray + nbatch - 1) / nbatch;
-    cudaError_t e = ensure_buf(&c->d_tape, c->tape_bytes, (size_t)nb * per_ray);
-    double *scratch = nullptr;
-    if (e == cudaSuccess) e = dalloc(&scratch, (size_t)nb * c->n_nu * nxy * c->ns);
-    for (int k = 0; k < 4 && e == cudaSuccess; ++k)
-        if (!c->it_ev[k]) e = cudaEventCreate(&c->it_ev[k]);
-    if (e != cudaSuccess) {
-        if (scratch) pfree(scratch);
-        return fail(c, PORTA_ENOMEM, "iterate_vjp: tape allocation");
-    }
-    // adjoint launch shape: forced, else timed once per batch size on the first batch
-    LaunchCfg acfg{};
-    std::vector<LaunchCfg> cand;
-    const bool forced = c->adj_cluster > 0 || c->adj_nu_group > 0;
-    const bool tune = !forced && !c->adj2_tuned.count(nb);
-    int rc = c->ns == 1 ? choose_adjoint<Real, 1>(c, acfg, c->adj_cluster, c->adj_nu_group, nb, tune ? &cand : nullptr)
-                        : choose_adjoint<Real, 4>(c, acfg, c->adj_cluster, c->adj_nu_group, nb, tune ? &cand : nullptr);
-    if (rc) {
-        pfree(scratch);
-        return fail(c, rc, "iterate_vjp: no adjoint launch shape fits");
-    }
-    if (!forced && !tune) acfg = c->adj2_tuned[nb];
-    int maxcl = acfg.clusters;
-    for (const LaunchCfg &k : cand) maxcl = std::max(maxcl, k.clusters);
-    e = ensure_buf((void **)&c->d_gacc, c->gacc_bytes, (size_t)maxcl * 10 * c->nvox * sizeof(double));
-    if (e != cudaSuccess) {
-        pfree(scratch);
-        return fail(c, PORTA_ENOMEM, "iterate_vjp: accumulator allocation");
-    }
-    // forward: Stokes vectors of every node for rays r0 .. r0 + n - 1
-    auto forward = [&](int r0, int n) -> int {
-        SweepArgs<Real> a = base_args<Real>(c);
-        a.geom = (const PlaneGeom<Real> *)c->d_geom + (size_t)r0 * c->nz;
-        a.rays = (const RayDev<Real> *)c->d_rays + r0;
-        a.out = scratch;
-        a.store = (Real *)c->d_tape;
-        LaunchCfg cfg{};
-        int r = c->ns == 1 ? emergent_shape<Real, 1>(c, a, n, cfg) : emergent_shape<Real, 4>(c, a, n, cfg);
-        if (r) return r;
-        e = c->ns == 1 ? launch_sweep<Real, 1>(a, MODE_EMERGENT, cfg, c->stream)
-                       : launch_sweep<Real, 4>(a, MODE_EMERGENT, cfg, c->stream);
-        return e == cudaSuccess ? PORTA_OK : fail(c, PORTA_ECUDA, std::string("iterate_vjp: ") + cudaGetErrorString(e));
-    };
-    // reverse: the J^K_Q and Lambda-bar* terms of the same rays
-    auto reverse = [&](int r0, int n, LaunchCfg k) -> int {
-        SweepArgs<Real> b = base_args<Real>(c);
-        b.geom = (const PlaneGeom<Real> *)c->d_geom + (size_t)r0 * c->nz;
-        b.rays = (const RayDev<Real> *)c->d_rays + r0;
-        b.store = (Real *)c->d_tape;
-        b.invn = (const Real *)c->d_invn;
-        b.gjkq = dgj;
-        b.glstar = dgl;
-        b.tw = c->d_tw;
-        b.ray0 = r0;
-        b.gacc = c->d_gacc;
-        b.F = k.F;
-        b.ngroups = (c->n_nu + k.F - 1) / k.F;
-        if (c->ns == 1)
-            launch_caps<Real, 1>(c, k.cluster, b.ring_plane, b.ipts_max);
-        else
-            launch_caps<Real, 4>(c, k.cluster, b.ring_plane, b.ipts_max);
-        b.nitems = n * b.ngroups;
-        k.clusters = std::min(k.clusters, b.nitems);
-        e = c->ns == 1 ? launch_adjoint<Real, 1>(b, k, c->stream, 2) : launch_adjoint<Real, 4>(b, k, c->stream, 2);
-        return e == cudaSuccess ? PORTA_OK : fail(c, PORTA_ECUDA, std::string("iterate_vjp adjoint: ") + cudaGetErrorString(e));
-    };
-    cudaEvent_t *ev = c->it_ev;
-    if (tune) {
-        rc = forward(0, nb);
-        float best = 1e30f;
-        for (const LaunchCfg &k : cand) {
-            if (rc) break;
-            float ms = 0;
-            e = cudaEventRecord(ev[0], c->stream);
-            if (e == cudaSuccess) rc = reverse(0, nb, k);
-            if (rc) break;
-            e = cudaEventRecord(ev[1], c->stream);
-            if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
-            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev[0], ev[1]);
-            if (e != cudaSuccess) {
-                rc = fail(c, PORTA_ECUDA, std::string("iterate_vjp tuning: ") + cudaGetErrorString(e));
-                break;
-            }
-            if (ms < best) {
-                best = ms;
-                acfg = k;
-            }
-        }
-        if (rc == PORTA_OK) c->adj2_tuned[nb] = acfg;
-    }
-    if (rc == PORTA_OK) {
-        e = cudaMemsetAsync(c->d_gacc, 0, (size_t)acfg.clusters * 10 * c->nvox * sizeof(double), c->stream);
-        if (e != cudaSuccess) rc = fail(c, PORTA_ECUDA, cudaGetErrorString(e));
-    }
-    for (int r0 = 0; r0 < c->nray && rc == PORTA_OK; r0 += nb) {
-        const int n = std::min(nb, c->nray - r0);
-        float t0 = 0, t1 = 0;
-        e = cudaEventRecord(ev[0], c->stream);
-        if (e == cudaSuccess) rc = forward(r0, n);
-        if (rc) break;
-        e = cudaEventRecord(ev[1], c->stream);
-        if (e == cudaSuccess) rc = reverse(r0, n, acfg);
-        if (rc) break;
-        e = cudaEventRecord(ev[2], c->stream);
-        if (e == cudaSuccess) e = cudaEventSynchronize(ev[2]);
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&t0, ev[0], ev[1]);
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&t1, ev[1], ev[2]);
-        if (e != cudaSuccess) rc = fail(c, PORTA_ECUDA, std::string("iterate_vjp: ") + cudaGetErrorString(e));
-        c->it_ms[2] += t0;
-        c->it_ms[3] += t1;
-    }
-    if (rc == PORTA_OK) {
-        float t = 0;
-        e = cudaEventRecord(ev[0], c->stream);
-        if (e == cudaSuccess)
-            e = launch_adjoint_acc_reduce(c->d_gacc, acfg.clusters, c->nvox, c->nl, dg_chi, c->ns == 1 ? nullptr : dg_b,
-                                          dg_rho, c->stream);
-        if (e == cudaSuccess) e = cudaEventRecord(ev[1], c->stream);
-        if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, ev[0], ev[1]);
-        if (e != cudaSuccess) rc = fail(c, PORTA_ECUDA, std::string("iterate_vjp: ") + cudaGetErrorString(e));
-        c->it_ms[4] += t;
-        c->last_adj = acfg;
-    }
-    cudaStreamSynchronize(c->stream);
-    pfree(scratch);
-    return rc;
-}
-
-cudaError_t mg_rho_changed(porta_ctx *L);
-
-void it_free(porta_ctx *c)
-{
-    for (double *b : c->it_saved) pfree(b);
-    c->it_saved.clear();
-    if (c->it_final) pfree(c->it_final);
-    c->it_final = nullptr;
-    c->it_niter = c->it_ckpt = 0;
-}
-
-int it_load(porta_ctx *c, const double *src)
-{
-    cudaError_t e = cudaMemcpyAsync(c->d_rho, src, sizeof(double) * c->nvox * c->nl, cudaMemcpyDeviceToDevice, c->stream);
-    if (e == cudaSuccess) e = mg_rho_changed(c);
-    if (e != cudaSuccess) return fail(c, PORTA_ECUDA, std::string("iterate: ") + cudaGetErrorString(e));
-    c->have_rho = true;
-    c->have_fs = c->have_jkq = false;
-    return PORTA_OK;
-}
-
-template <typename Real>
-int iterate_vjp_t(porta_ctx *c, int ndir, const double *mu, const double *chi, const double *dgrad, double *dout,
-                  double *dg_chi, double *dg_f, double *dg_b)
-{
-    const size_t nr = (size_t)c->nvox * c->nl;
-    double *blk = nullptr;
-    // gbar (dL/drho of the current iterate), explicit part, dL/dJ, dL/dLambda*
-    CK(dalloc(&blk, 3 * nr + c->nvox));
-    double *gbar = blk, *gexp = blk + nr, *gj = blk + 2 * nr, *gl = blk + 3 * nr;
-    int rc = PORTA_OK;
-    cudaError_t e = cudaMemsetAsync(dg_chi, 0, sizeof(double) * c->nvox, c->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(dg_f, 0, sizeof(double) * c->nvox, c->stream);
-    if (e == cudaSuccess && dg_b) e = cudaMemsetAsync(dg_b, 0, sizeof(double) * 3 * c->nvox, c->stream);
-    if (e != cudaSuccess) rc = fail(c, PORTA_ECUDA, cudaGetErrorString(e));
-    // the loss: emergent Stokes of the final unknowns
-    if (rc == PORTA_OK) rc = it_load(c, c->it_final);
-    if (rc == PORTA_OK) rc = emergent_vjp_t<Real>(c, ndir, mu, chi, dgrad, dout, dg_chi, nullptr, dg_b, gbar);
-    for (float &t : c->it_ms) t = 0.f;
-    for (int k = 0; k < 4 && rc == PORTA_OK; ++k)
-        if (!c->it_ev[k] && cudaEventCreate(&c->it_ev[k]) != cudaSuccess) rc = fail(c, PORTA_ECUDA, "iterate_vjp: events");
-    cudaEvent_t *ev = c->it_ev;
-    // The iterates of one checkpoint segment with their J^K_Q and Lambda-bar*:
-    // each segment is rebuilt once from its checkpoint (ckpt formal solutions in
-    // all, as many as the forward iterations) and its steps back read them from
-    // here. Where that store exceeds the tape limit or the free device memory,
-    // every step back rebuilds its iterate from the checkpoint instead
-    // (ckpt (ckpt + 1) / 2 formal solutions per segment).
-    const int nslot = std::min(c->it_ckpt, c->it_niter);
-    const size_t nj = (size_t)c->nvox * c->nj, per_slot = nr + nj + c->nvox;
-    double *seg = nullptr;
-    const size_t seg_bytes = sizeof(double) * per_slot * nslot;
-    if (rc == PORTA_OK && seg_bytes <= c->tape_limit && pmalloc(&seg, seg_bytes) != cudaSuccess) {
-        cudaGetLastError();
-        seg = nullptr;
-    }
-    auto slot = [&](int i) { return seg + per_slot * i; };
-    auto save = [&](int i) {
-        cudaError_t r = cudaMemcpyAsync(slot(i), c->d_rho, sizeof(double) * nr, cudaMemcpyDeviceToDevice, c->stream);
-        if (r == cudaSuccess)
-            r = cudaMemcpyAsync(slot(i) + nr, c->d_jkq, sizeof(double) * nj, cudaMemcpyDeviceToDevice, c->stream);
-        if (r == cudaSuccess)
-            r = cudaMemcpyAsync(slot(i) + nr + nj, c->d_lstar, sizeof(double) * c->nvox, cudaMemcpyDeviceToDevice,
-                                c->stream);
-        return r == cudaSuccess ? PORTA_OK : fail(c, PORTA_ECUDA, std::string("iterate_vjp: ") + cudaGetErrorString(r));
-    };
-    auto restore = [&](int i) {
-        int r = it_load(c, slot(i));
-        cudaError_t x = cudaSuccess;
-        if (r == PORTA_OK)
-            x = cudaMemcpyAsync(c->d_jkq, slot(i) + nr, sizeof(double) * nj, cudaMemcpyDeviceToDevice, c->stream);
-        if (r == PORTA_OK && x == cudaSuccess)
-            x = cudaMemcpyAsync(c->d_lstar, slot(i) + nr + nj, sizeof(double) * c->nvox, cudaMemcpyDeviceToDevice,
-                                c->stream);
-        if (r == PORTA_OK && x != cudaSuccess) r = fail(c, PORTA_ECUDA, std::string("iterate_vjp: ") + cudaGetErrorString(x));
-        return r;
-    };
-    int seg_base = -1;
-    for (int k = c->it_niter - 1; k >= 0 && rc == PORTA_OK; --k) {
-        // the iterate rho_k with J^K_Q and Lambda-bar* at rho_k
-        const int base = k / c->it_ckpt, b0 = base * c->it_ckpt;
-        e = cudaEventRecord(ev[0], c->stream);
-        if (seg && base == seg_base) {
-            rc = restore(k - b0);
-        } else {
-            rc = it_load(c, c->it_saved[base]);
-            for (int s = b0; s <= k && rc == PORTA_OK; ++s) {
-                rc = porta_formal_solve(c);
-                if (rc == PORTA_OK) rc = porta_accumulate_jkq(c, nullptr, nullptr, PORTA_DEVICE);
-                if (rc == PORTA_OK && seg) rc = save(s - b0);
-                if (rc == PORTA_OK && s < k) rc = porta_see_update(c, nullptr);
-            }
-            seg_base = seg ? base : -1;
-        }
-        if (rc) break;
-        e = cudaEventRecord(ev[1], c->stream);
-        // reverse mode of the update rho_{k+1} = U(rho_k, J, Lambda*, f, B)
-        if (e == cudaSuccess)
-            e = run_see_vjp(c->nvox, c->nl, c->model, c->bcrit, c->d_eps, c->d_bpl, c->d_b, c->d_jkq, c->d_lstar, nullptr,
-                            c->d_rho, gbar, gexp, gj, gl, dg_f, dg_b, c->stream);
-        if (e == cudaSuccess) e = cudaEventRecord(ev[2], c->stream);
-        if (e == cudaSuccess) e = cudaEventSynchronize(ev[2]);
-        float t0 = 0, t1 = 0;
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&t0, ev[0], ev[1]);
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&t1, ev[1], ev[2]);
-        if (e != cudaSuccess) { rc = fail(c, PORTA_ECUDA, std::string("iterate_vjp: ") + cudaGetErrorString(e)); break; }
-        c->it_ms[0] += t0;
-        c->it_ms[1] += t1;
-        // ... and of J^K_Q, Lambda-bar* (gbar <- their gradient in rho_k), plus the explicit term
-        rc = jkq_vjp_t<Real>(c, gj, gl, dg_chi, dg_b, gbar);
-        if (rc) break;
-        e = run_axpy((long long)nr, 1.0, gexp, gbar, c->stream);
-        if (e != cudaSuccess) rc = fail(c, PORTA_ECUDA, std::string("iterate_vjp: ") + cudaGetErrorString(e));
-    }
-    // leave the context at the final unknowns
-    int rc2 = it_load(c, c->it_final);
-    cudaStreamSynchronize(c->stream);
-    pfree(blk);
-    if (seg) pfree(seg);
-    return rc ? rc : rc2;
-}
-
-// ---------------------------------------------------------------- multigrid (Sec. 5)
-
-int coarse_nz(int nz) { return nz % 2 ? (nz + 1) / 2 : nz / 2; }
-
-void mg_free(porta_ctx *c)
-{
-    for (porta_ctx *L : c->mg) porta_destroy(L);
-    c->mg.clear();
-    double *bufs[] = {c->mg_res, c->mg_src, c->mg_rho0, c->mg_prev, c->mg_zr, c->mg_zp};
-    for (double *b : bufs)
-        if (b) pfree(b);
-    c->mg_res = c->mg_src = c->mg_rho0 = c->mg_prev = c->mg_zr = c->mg_zp = nullptr;
-}
-
-// z tables between a level with heights zf and the next coarser one (coarse
-// plane i = fine plane 2i): per fine plane (k0, w0, k1, w1) of the linear
-// interpolation in height (extrapolation from the top two coarse planes above
-// the coarse grid), and per coarse plane up to 4 (fine plane, weight) pairs of
-// the transposed interpolation
-void mg_ztables(const std::vector<double> &zf, std::vector<double> &zr, std::vector<double> &zp)
-{
-    const int nf = (int)zf.size(), nc = coarse_nz(nf);
-    zp.assign(4 * (size_t)nf, 0.0);
-    for (int k = 0; k < nf; ++k) {
-        if (k % 2 == 0) {
-            zp[4 * k] = zp[4 * k + 2] = k / 2;
-            zp[4 * k + 1] = 1.0;
-            continue;
-        }
-        int k0 = (k - 1) / 2;
-        if (k0 + 1 >= nc) k0 = nc - 2;
-        const int k1 = k0 + 1;
-        const double t = (zf[k] - zf[2 * k0]) / (zf[2 * k1] - zf[2 * k0]);
-        zp[4 * k] = k0;
-        zp[4 * k + 1] = 1.0 - t;
-        zp[4 * k + 2] = k1;
-        zp[4 * k + 3] = t;
-    }
-    zr.assign(8 * (size_t)nc, 0.0);
-    std::vector<int> used(nc, 0);
-    for (int k = 0; k < nf; ++k)
-        for (int e = 0; e < 2; ++e) {
-            const double w = zp[4 * k + 2 * e + 1];
-            if (w == 0.0) continue;
-            const int K = (int)zp[4 * k + 2 * e];
-            zr[8 * K + 2 * used[K]] = k;
-            zr[8 * K + 2 * used[K] + 1] = w;
-            ++used[K];
-        }
-}
-
-// formal solution and J^K_Q / Lambda-bar* of one level, kept on the device
-int mg_fs(porta_ctx *L)
-{
-    int rc = porta_formal_solve(L);
-    if (rc == PORTA_OK) rc = porta_accumulate_jkq(L, nullptr, nullptr, PORTA_DEVICE);
-    return rc;
-}
-
-cudaError_t ml_prepare(porta_ctx *c);
-
-// the unknowns of a level: rho [v][nl] of the two-level atom, or the
-// populations [v][nlevel] of the multilevel atom
-double *mg_unk(porta_ctx *L) { return L->ml ? (L->ml->pol ? L->ml->d_x : L->ml->d_pops) : L->d_rho; }
-long long mg_nunk(const porta_ctx *L) { return L->ml ? L->ml->nvox1 : L->nvox; }
-int mg_ncomp(const porta_ctx *L) { return L->ml ? L->ml->nunk : L->nl; }
-
-cudaError_t mg_rho_changed(porta_ctx *L)
-{
-    if (L->ml) return ml_prepare(L);
-    return L->precision == PORTA_FP32 ? run_rho_convert<float>(L->nvox, L->nl, L->d_rho, L->d_rhoR, L->stream)
-                                      : run_rho_convert<double>(L->nvox, L->nl, L->d_rho, L->d_rhoR, L->stream);
-}
-
-// out = alpha A(unknowns) + add + with_f f_fine, with J^K_Q of the last formal solution
-cudaError_t mg_apply(porta_ctx *L, double alpha, const double *add, int with_f, double *out)
-{
-    if (L->ml && L->ml->pol)
-        return run_mlpol_apply(L->ml->mc, L->ml->dev, L->ml->nvox1, L->ml->d_kT, L->d_jkq, L->d_b, L->ml->d_x, alpha, add,
-                               with_f, out, L->stream);
-    if (L->ml)
-        return run_ml_apply(L->ml->mc, L->ml->nvox1, L->ml->d_kT, L->d_jkq, L->ml->d_pops, alpha, add, with_f, out,
-                            L->stream);
-    return run_see_apply(L->nvox, L->nl, L->model, L->bcrit, L->d_eps, L->d_bpl, L->d_b, L->d_jkq, L->d_rho, alpha,
-                         add, with_f, out, L->stream);
-}
-
-// n Jacobi iterations of A(x) = src on one level (src null: the fine right-hand side)
-int mg_jacobi(porta_ctx *L, const double *src, int n)
-{
-    for (int it = 0; it < n; ++it) {
-        int rc = mg_fs(L);
-        if (rc) return rc;
-        cudaError_t e;
-        if (L->ml) {
-            e = L->ml->pol ? run_mlpol_see(L->ml->mc, L->ml->dev, L->ml->nvox1, L->ml->d_kT, L->d_jkq, L->d_lstar, L->d_b,
-                                           L->ml->d_x, L->d_resid, L->ml->d_bad, L->stream, src)
-                           : run_ml_see(L->ml->mc, L->ml->nvox1, L->ml->d_kT, L->d_jkq, L->d_lstar, L->ml->d_pops, L->d_resid,
-                                        L->ml->d_bad, L->stream, src);
-            if (e == cudaSuccess) e = ml_prepare(L);
-        } else {
-            e = L->precision == PORTA_FP32
-                    ? run_see<float>(L->nvox, L->nl, L->model, L->bcrit, L->d_eps, L->d_bpl, L->d_b, L->d_jkq,
-                                     L->d_lstar, L->d_rho, L->d_rhoR, L->d_resid, L->stream, src)
-                    : run_see<double>(L->nvox, L->nl, L->model, L->bcrit, L->d_eps, L->d_bpl, L->d_b, L->d_jkq,
-                                      L->d_lstar, L->d_rho, L->d_rhoR, L->d_resid, L->stream, src);
-        }
-        if (e != cudaSuccess) return fail(L, PORTA_ECUDA, std::string("mg jacobi: ") + cudaGetErrorString(e));
-        L->have_fs = L->have_jkq = false;
-    }
-    return PORTA_OK;
-}
-
-// One V-cycle (Eqs. 30-34) from level l of levels[0..n) down to the coarsest.
-int mg_vcycle(porta_ctx *const *levels, int n, int l, int npre, int npost, int ncoarse)
-{
-    porta_ctx *L = levels[l];
-    const double *src = l == 0 ? nullptr : L->mg_src;
-    if (l == n - 1) return mg_jacobi(L, src, ncoarse);
-    int rc = mg_jacobi(L, src, npre);
-    if (rc) return rc;
-    // residual r = f - A(x)
-    if ((rc = mg_fs(L))) return rc;
-    cudaError_t e = mg_apply(L, -1.0, src, src ? 0 : 1, L->mg_res);
-    porta_ctx *C = levels[l + 1];
-    const int nc = mg_ncomp(L);
-    // coarse unknowns R x, coarse right-hand side A_c(R x) + R r
-    if (e == cudaSuccess)
-        e = run_restrict(C->nx, C->ny, C->nz, L->nx, L->ny, nc, L->mg_zr, mg_unk(L), C->mg_rho0, L->stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(mg_unk(C), C->mg_rho0, sizeof(double) * mg_nunk(C) * nc, cudaMemcpyDeviceToDevice, L->stream);
-    if (e == cudaSuccess) e = mg_rho_changed(C);
-    if (e == cudaSuccess)
-        e = run_restrict(C->nx, C->ny, C->nz, L->nx, L->ny, nc, L->mg_zr, L->mg_res, C->mg_src, L->stream);
-    if (e != cudaSuccess) return fail(L, PORTA_ECUDA, std::string("mg restrict: ") + cudaGetErrorString(e));
-    C->have_rho = true;
-    if (C->ml) C->ml->have_pops = true;
-    if ((rc = mg_fs(C))) return fail(L, rc, std::string("mg coarse level: ") + C->err);
-    e = mg_apply(C, 1.0, C->mg_src, 0, C->mg_src);
-    if (e != cudaSuccess) return fail(L, PORTA_ECUDA, std::string("mg coarse rhs: ") + cudaGetErrorString(e));
-    if ((rc = mg_vcycle(levels, n, l + 1, npre, npost, ncoarse))) return fail(L, rc, C->err);
-    // coarse-grid correction x += P (x_c - R x)
-    e = run_prolong_add(L->nx, L->ny, L->nz, C->nx, C->ny, nc, L->mg_zp, mg_unk(C), C->mg_rho0, mg_unk(L), L->stream);
-    if (e == cudaSuccess) e = mg_rho_changed(L);
-    if (e != cudaSuccess) return fail(L, PORTA_ECUDA, std::string("mg prolong: ") + cudaGetErrorString(e));
-    return mg_jacobi(L, src, npost);
-}
-
-// line data of every line from the populations (sweep arrays of the line boxes)
-cudaError_t ml_prepare(porta_ctx *c)
-{
-    MlState *m = c->ml;
-    const size_t R = c->rsz;
-    char *atm = (char *)c->d_atm;
-    const long long n = c->nvox;
-    if (m->pol) {
-        if (c->precision == PORTA_FP32)
-            return run_mlpol_prepare<float>(m->mc, m->dev, m->nvox1, m->d_x, m->d_chis, m->d_kT, (float *)atm,
-                                            (float *)(atm + 5 * n * R), (float *)c->d_rhoR, c->d_rho,
-                                            (float *)c->d_dich, m->d_bad, c->stream);
-        return run_mlpol_prepare<double>(m->mc, m->dev, m->nvox1, m->d_x, m->d_chis, m->d_kT, (double *)atm,
-                                         (double *)(atm + 5 * n * R), (double *)c->d_rhoR, c->d_rho,
-                                         (double *)c->d_dich, m->d_bad, c->stream);
-    }
-    if (c->precision == PORTA_FP32)
-        return run_ml_prepare<float>(m->mc, m->nvox1, m->d_pops, m->d_chis, m->d_kT, (float *)atm,
-                                     (float *)(atm + 5 * n * R), (float *)c->d_rhoR, c->d_rho, m->d_bad, c->stream);
-    return run_ml_prepare<double>(m->mc, m->nvox1, m->d_pops, m->d_chis, m->d_kT, (double *)atm,
-                                  (double *)(atm + 5 * n * R), (double *)c->d_rhoR, c->d_rho, m->d_bad, c->stream);
-}
-
 // the update step of a Jacobi iteration, enqueued on the context's stream
 // (capturable): residual reset, then the two-level SEE update, or for the
 // multilevel atom the rate equations and the next iteration's line data
@@ -1564,12 +580,9 @@ cudaError_t enqueue_update(porta_ctx *c)
     return ml_prepare(c);
 }
 
-}  // namespace
 
-extern "C" {
-
-static int create_impl(int nbox, const porta_grid *grids, const porta_atom *at, const porta_quad *q,
-                       const porta_opts *o, porta_ctx **out)
+int create_impl(int nbox, const porta_grid *grids, const porta_atom *at, const porta_quad *q,
+                const porta_opts *o, porta_ctx **out)
 {
     if (!out) return PORTA_EINVAL;
     *out = nullptr;
@@ -1628,8 +641,8 @@ static int create_impl(int nbox, const porta_grid *grids, const porta_atom *at, 
     c->rsz = prec == PORTA_FP32 ? sizeof(float) : sizeof(double);
 
     // angular quadrature: Gauss inclinations per hemisphere x equally weighted azimuths at midpoints
-    std::vector<double> xg, wg;
-    gauss_legendre(q->n_mu, xg, wg);
+    std::vector<double> xg(q->n_mu), wg(q->n_mu);
+    gauss_legendre(q->n_mu, xg.data(), wg.data());
     c->mu.resize(c->nray); c->chi.resize(c->nray); c->w.resize(c->nray);
     for (int h = 0; h < 2; ++h)
         for (int i = 0; i < q->n_mu; ++i)
@@ -1757,6 +770,12 @@ static int create_impl(int nbox, const porta_grid *grids, const porta_atom *at, 
     *out = c;
     return PORTA_OK;
 }
+
+}  // namespace porta_api
+
+using namespace porta_api;
+
+extern "C" {
 
 int porta_create(const porta_grid *g, const porta_atom *at, const porta_quad *q, const porta_opts *o, porta_ctx **out)
 {
@@ -1979,202 +998,6 @@ int porta_see_update(porta_ctx *c, double *max_change)
         std::memcpy(&v, &bits, sizeof(v));
         *max_change = v;
     }
-    return PORTA_OK;
-}
-
-int porta_emergent_stokes(porta_ctx *c, int ndir, const double *mu, const double *chi, double *out, int where)
-{
-    if (!c) return PORTA_EINVAL;
-    if (ndir < 1 || !mu || !chi || !out || (where != PORTA_HOST && where != PORTA_DEVICE))
-        return fail(c, PORTA_EINVAL, "emergent_stokes: bad argument");
-    for (int d = 0; d < ndir; ++d)
-        if (!(mu[d] > 0.0 && mu[d] <= 1.0) || !std::isfinite(chi[d]))
-            return fail(c, PORTA_EINVAL, "emergent_stokes: mu must lie in (0, 1], chi finite");
-    if (c->nbox != 1) return fail(c, PORTA_EINVAL, "emergent_stokes: single-box contexts only");
-    if (!c->have_atm || !c->have_rho) return fail(c, PORTA_ESTATE, "emergent_stokes: atmosphere or rho not set");
-    const long long n = (long long)ndir * c->n_nu * c->nx * c->ny * c->ns;
-    double *dout = out;
-    if (where == PORTA_HOST) CK(dalloc(&dout, n));
-    int rc = c->precision == PORTA_FP32 ? emergent_t<float>(c, ndir, mu, chi, dout) : emergent_t<double>(c, ndir, mu, chi, dout);
-    if (where == PORTA_HOST) {
-        if (rc == PORTA_OK) {
-            cudaError_t e = cudaMemcpy(out, dout, n * sizeof(double), cudaMemcpyDeviceToHost);
-            if (e != cudaSuccess) rc = fail(c, PORTA_ECUDA, cudaGetErrorString(e));
-        }
-        pfree(dout);
-    }
-    return rc;
-}
-
-int porta_emergent_vjp(porta_ctx *c, int ndir, const double *mu, const double *chi, const double *grad_out,
-                       double *out, double *g_chi, double *g_e, double *g_b, int where)
-{
-    if (!c) return PORTA_EINVAL;
-    if (ndir < 1 || !mu || !chi || !grad_out || !g_chi || !g_e || (c->ns > 1 && !g_b) ||
-        (where != PORTA_HOST && where != PORTA_DEVICE))
-        return fail(c, PORTA_EINVAL, "emergent_vjp: bad argument");
-    for (int d = 0; d < ndir; ++d)
-        if (!(mu[d] > 0.0 && mu[d] <= 1.0) || !std::isfinite(chi[d]))
-            return fail(c, PORTA_EINVAL, "emergent_vjp: mu must lie in (0, 1], chi finite");
-    if (c->nbox != 1) return fail(c, PORTA_EINVAL, "emergent_vjp: single-box contexts only");
-    if (!c->have_atm || !c->have_rho) return fail(c, PORTA_ESTATE, "emergent_vjp: atmosphere or rho not set");
-    const long long nout = (long long)ndir * c->n_nu * c->nx * c->ny * c->ns;
-    const long long nv = c->nvox;
-    if (where == PORTA_DEVICE)
-        return c->precision == PORTA_FP32 ? emergent_vjp_t<float>(c, ndir, mu, chi, grad_out, out, g_chi, g_e, g_b)
-                                          : emergent_vjp_t<double>(c, ndir, mu, chi, grad_out, out, g_chi, g_e, g_b);
-    // host buffers: one device block for grad_out, out, g_chi, g_e, g_b
-    const long long nb = c->ns > 1 ? 3 * nv : 0;
-    double *blk = nullptr;
-    CK(dalloc(&blk, (size_t)(nout + (out ? nout : 0) + 2 * nv + nb)));
-    double *dgrad = blk, *dout = out ? blk + nout : nullptr;
-    double *dchi = blk + nout + (out ? nout : 0), *de = dchi + nv, *db = nb ? de + nv : nullptr;
-    int rc = PORTA_OK;
-    cudaError_t e = cudaMemcpy(dgrad, grad_out, nout * sizeof(double), cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) rc = fail(c, PORTA_ECUDA, cudaGetErrorString(e));
-    if (rc == PORTA_OK)
-        rc = c->precision == PORTA_FP32 ? emergent_vjp_t<float>(c, ndir, mu, chi, dgrad, dout, dchi, de, db)
-                                        : emergent_vjp_t<double>(c, ndir, mu, chi, dgrad, dout, dchi, de, db);
-    if (rc == PORTA_OK) {
-        e = cudaMemcpy(g_chi, dchi, nv * sizeof(double), cudaMemcpyDeviceToHost);
-        if (e == cudaSuccess) e = cudaMemcpy(g_e, de, nv * sizeof(double), cudaMemcpyDeviceToHost);
-        if (e == cudaSuccess && db) e = cudaMemcpy(g_b, db, 3 * nv * sizeof(double), cudaMemcpyDeviceToHost);
-        if (e == cudaSuccess && out) e = cudaMemcpy(out, dout, nout * sizeof(double), cudaMemcpyDeviceToHost);
-        if (e != cudaSuccess) rc = fail(c, PORTA_ECUDA, cudaGetErrorString(e));
-    }
-    pfree(blk);
-    return rc;
-}
-
-int porta_iterate_ckpt(porta_ctx *c, int niter, int ckpt, double *max_change)
-{
-    if (!c) return PORTA_EINVAL;
-    if (c->ml) return fail(c, PORTA_EINVAL, "iterate_ckpt: not for a multilevel context (porta_ml_*)");
-    if (niter < 1 || ckpt < 1) return fail(c, PORTA_EINVAL, "iterate_ckpt: niter >= 1, ckpt >= 1");
-    if (c->nbox != 1) return fail(c, PORTA_EINVAL, "iterate_ckpt: single-box contexts only");
-    if (!c->have_atm || !c->have_rho) return fail(c, PORTA_ESTATE, "iterate_ckpt: atmosphere or rho not set");
-    it_free(c);
-    const size_t nr = (size_t)c->nvox * c->nl;
-    const int nsave = (niter + ckpt - 1) / ckpt;
-    for (int i = 0; i <= nsave; ++i) {
-        double *b = nullptr;
-        cudaError_t e = dalloc(&b, nr);
-        if (e != cudaSuccess) {
-            it_free(c);
-            return fail(c, PORTA_ENOMEM, "iterate_ckpt: checkpoint allocation");
-        }
-        if (i < nsave)
-            c->it_saved.push_back(b);
-        else
-            c->it_final = b;
-    }
-    int rc = PORTA_OK;
-    for (int k = 0; k < niter && rc == PORTA_OK; ++k) {
-        if (k % ckpt == 0) {
-            cudaError_t e = cudaMemcpyAsync(c->it_saved[k / ckpt], c->d_rho, sizeof(double) * nr, cudaMemcpyDeviceToDevice,
-                                            c->stream);
-            if (e != cudaSuccess) rc = fail(c, PORTA_ECUDA, std::string("iterate_ckpt: ") + cudaGetErrorString(e));
-        }
-        if (rc == PORTA_OK) rc = porta_formal_solve(c);
-        if (rc == PORTA_OK) rc = porta_accumulate_jkq(c, nullptr, nullptr, PORTA_DEVICE);
-        if (rc == PORTA_OK) rc = porta_see_update(c, k == niter - 1 ? max_change : nullptr);
-    }
-    if (rc == PORTA_OK) {
-        cudaError_t e = cudaMemcpyAsync(c->it_final, c->d_rho, sizeof(double) * nr, cudaMemcpyDeviceToDevice, c->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-        if (e != cudaSuccess) rc = fail(c, PORTA_ECUDA, std::string("iterate_ckpt: ") + cudaGetErrorString(e));
-    }
-    if (rc) {
-        it_free(c);
-        return rc;
-    }
-    c->it_niter = niter;
-    c->it_ckpt = ckpt;
-    return PORTA_OK;
-}
-
-int porta_iterate_timing(const porta_ctx *c, float *ms)
-{
-    if (!c || !ms) return PORTA_EINVAL;
-    for (int k = 0; k < 5; ++k) ms[k] = c->it_ms[k];
-    return PORTA_OK;
-}
-
-int porta_set_tape_limit(porta_ctx *c, long long bytes)
-{
-    if (!c) return PORTA_EINVAL;
-    if (bytes < 0) return fail(c, PORTA_EINVAL, "set_tape_limit: bytes >= 0");
-    c->tape_limit = bytes ? (size_t)bytes : (size_t)16 << 30;
-    return PORTA_OK;
-}
-
-int porta_iterate_vjp(porta_ctx *c, int ndir, const double *mu, const double *chi, const double *grad_out, double *out,
-                      double *g_chi, double *g_f, double *g_b, int where)
-{
-    if (!c) return PORTA_EINVAL;
-    if (ndir < 1 || !mu || !chi || !grad_out || !g_chi || !g_f || (c->ns > 1 && !g_b) ||
-        (where != PORTA_HOST && where != PORTA_DEVICE))
-        return fail(c, PORTA_EINVAL, "iterate_vjp: bad argument");
-    for (int d = 0; d < ndir; ++d)
-        if (!(mu[d] > 0.0 && mu[d] <= 1.0) || !std::isfinite(chi[d]))
-            return fail(c, PORTA_EINVAL, "iterate_vjp: mu must lie in (0, 1], chi finite");
-    if (c->it_niter < 1) return fail(c, PORTA_ESTATE, "iterate_vjp: call porta_iterate_ckpt first");
-    if (c->ns == 1) g_b = nullptr;
-    const long long nout = (long long)ndir * c->n_nu * c->nx * c->ny * c->ns;
-    const long long nv = c->nvox;
-    auto run = [&](const double *dgrad, double *dout, double *dchi, double *df, double *db) {
-        return c->precision == PORTA_FP32 ? iterate_vjp_t<float>(c, ndir, mu, chi, dgrad, dout, dchi, df, db)
-                                          : iterate_vjp_t<double>(c, ndir, mu, chi, dgrad, dout, dchi, df, db);
-    };
-    if (where == PORTA_DEVICE) return run(grad_out, out, g_chi, g_f, g_b);
-    const long long nb = g_b ? 3 * nv : 0;
-    double *blk = nullptr;
-    CK(dalloc(&blk, (size_t)(nout + (out ? nout : 0) + 2 * nv + nb)));
-    double *dgrad = blk, *dout = out ? blk + nout : nullptr;
-    double *dchi = blk + nout + (out ? nout : 0), *df = dchi + nv, *db = nb ? df + nv : nullptr;
-    int rc = PORTA_OK;
-    cudaError_t e = cudaMemcpy(dgrad, grad_out, nout * sizeof(double), cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) rc = fail(c, PORTA_ECUDA, cudaGetErrorString(e));
-    if (rc == PORTA_OK) rc = run(dgrad, dout, dchi, df, db);
-    if (rc == PORTA_OK) {
-        e = cudaMemcpy(g_chi, dchi, nv * sizeof(double), cudaMemcpyDeviceToHost);
-        if (e == cudaSuccess) e = cudaMemcpy(g_f, df, nv * sizeof(double), cudaMemcpyDeviceToHost);
-        if (e == cudaSuccess && db) e = cudaMemcpy(g_b, db, 3 * nv * sizeof(double), cudaMemcpyDeviceToHost);
-        if (e == cudaSuccess && out) e = cudaMemcpy(out, dout, nout * sizeof(double), cudaMemcpyDeviceToHost);
-        if (e != cudaSuccess) rc = fail(c, PORTA_ECUDA, cudaGetErrorString(e));
-    }
-    pfree(blk);
-    return rc;
-}
-
-int porta_set_adjoint_launch(porta_ctx *c, int cluster, int nu_group)
-{
-    if (!c) return PORTA_EINVAL;
-    if (cluster < 0 || cluster > 16 || nu_group < 0 || nu_group > c->n_nu)
-        return fail(c, PORTA_EINVAL, "set_adjoint_launch: cluster in 0..16, nu_group in 0..n_nu");
-    if (cluster > c->ny) return fail(c, PORTA_EINVAL, "set_adjoint_launch: cluster larger than ny");
-    c->adj_cluster = cluster;
-    c->adj_nu_group = nu_group;
-    c->adj_tuned_ndir = 0;
-    c->adj2_tuned.clear();
-    return PORTA_OK;
-}
-
-int porta_adjoint_timing(const porta_ctx *c, float *forward_ms, float *adjoint_ms)
-{
-    if (!c) return PORTA_EINVAL;
-    if (forward_ms) *forward_ms = c->adj_fwd_ms;
-    if (adjoint_ms) *adjoint_ms = c->adj_rev_ms;
-    return PORTA_OK;
-}
-
-int porta_adjoint_info(const porta_ctx *c, int *clusters, int *cluster_size, int *nu_group, int *smem_bytes)
-{
-    if (!c) return PORTA_EINVAL;
-    if (clusters) *clusters = c->last_adj.clusters;
-    if (cluster_size) *cluster_size = c->last_adj.cluster;
-    if (nu_group) *nu_group = c->last_adj.F;
-    if (smem_bytes) *smem_bytes = c->last_adj.smem;
     return PORTA_OK;
 }
 
@@ -2474,611 +1297,4 @@ int porta_launch_info(const porta_ctx *c, int *clusters, int *cluster_size, int 
     if (smem_bytes) *smem_bytes = c->last.smem;
     return PORTA_OK;
 }
-
-
-static int ml_check(porta_ctx *c, const char *what);
-
-int porta_mg_setup(porta_ctx *c, int nlevels)
-{
-    if (!c) return PORTA_EINVAL;
-    if (c->nbox != 1 && !c->ml) return fail(c, PORTA_EINVAL, "mg_setup: single-box contexts only");
-    if (c->ml && !c->ml->have_atm) return fail(c, PORTA_ESTATE, "mg_setup: atmosphere not set");
-    if (nlevels < 2 || nlevels > 8) return fail(c, PORTA_EINVAL, "mg_setup: nlevels in 2..8");
-    if (!c->have_atm) return fail(c, PORTA_ESTATE, "mg_setup: atmosphere not set");
-    {
-        int nx = c->nx, ny = c->ny, nz = c->nz;
-        for (int l = 1; l < nlevels; ++l) {
-            if (nx % 2 || ny % 2)
-                return fail(c, PORTA_EINVAL, "mg_setup: nx and ny must be divisible by 2^(nlevels-1)");
-            nx /= 2;
-            ny /= 2;
-            nz = coarse_nz(nz);
-            if (nz < 2) return fail(c, PORTA_EINVAL, "mg_setup: too many levels for nz");
-        }
-    }
-    mg_free(c);
-    porta_ctx *F = c;
-    int rc = PORTA_OK;
-    for (int l = 1; l < nlevels && rc == PORTA_OK; ++l) {
-        const int nzc = coarse_nz(F->nz);
-        std::vector<double> zc(nzc);
-        for (int k = 0; k < nzc; ++k) zc[k] = F->z[2 * k];
-        porta_grid g{};
-        g.nx = F->nx / 2;
-        g.ny = F->ny / 2;
-        g.nz = nzc;
-        g.lx = c->lx;
-        g.ly = c->ly;
-        g.z = zc.data();
-        porta_atom a{};
-        a.model = c->model;
-        a.zeta = c->zeta;
-        a.gbar = c->gbar;
-        a.bcrit = c->bcrit;
-        porta_quad q{};
-        q.n_mu = c->n_mu;
-        q.n_chi = c->n_chi;
-        q.n_nu = c->n_nu;
-        q.x_max = c->x_max;
-        porta_opts o{};
-        o.precision = c->precision;
-        porta_ctx *L = nullptr;
-        if (c->ml) {
-            // multilevel: a coarse multilevel context of the same atom; its opacity
-            // scale, temperature and velocity at the coincident nodes
-            const MlState *m = c->ml;
-            porta_ml_atom ma{m->mc.nlev, m->mc.nline, m->J.data(), m->E.data(), m->up.data(), m->lo.data(),
-                             m->A.data(), m->eps.data(), m->pol ? 1 : 0, c->zeta};
-            if ((rc = porta_ml_create(&g, &ma, &q, &o, &L))) {
-                rc = fail(c, rc, "mg_setup: coarse level creation");
-                break;
-            }
-            c->mg.push_back(L);
-            porta_set_stream(L, c->stream);
-            const MlState *mf = F->ml;
-            const long long ncv = L->ml->nvox1;
-            double *tmp = nullptr;
-            cudaError_t e = dalloc(&tmp, 6 * (size_t)ncv);
-            // F->d_cv64 + F->nvox: FP64 velocity of the line boxes (box 0 first); F->d_b the field
-            const double *srcs[6] = {mf->d_chis, mf->d_kT, F->d_cv64 + F->nvox, F->d_b, F->d_b + F->nvox,
-                                     F->d_b + 2 * F->nvox};
-            for (int f = 0; f < (m->pol ? 6 : 3) && e == cudaSuccess; ++f)
-                e = run_inject(L->nx, L->ny, L->nz, F->nx, F->ny, srcs[f], tmp + f * ncv, c->stream);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-            if (e != cudaSuccess) {
-                pfree(tmp);
-                rc = fail(c, PORTA_ECUDA, std::string("mg_setup: ") + cudaGetErrorString(e));
-                break;
-            }
-            rc = porta_ml_set_atmosphere(L, tmp, tmp + ncv, tmp + 2 * ncv, m->pol ? tmp + 3 * ncv : nullptr,
-                                         m->pol ? tmp + 4 * ncv : nullptr, m->pol ? tmp + 5 * ncv : nullptr, PORTA_DEVICE);
-            pfree(tmp);
-            if (rc) {
-                rc = fail(c, rc, std::string("mg_setup: coarse atmosphere: ") + L->err);
-                break;
-            }
-            std::vector<double> zr, zp;
-            mg_ztables(F->z, zr, zp);
-            const int nl = mg_ncomp(c);
-            e = dalloc(&L->mg_src, (size_t)ncv * nl);
-            if (e == cudaSuccess) e = dalloc(&L->mg_rho0, (size_t)ncv * nl);
-            if (e == cudaSuccess) e = dalloc(&L->mg_res, (size_t)ncv * nl);
-            if (e == cudaSuccess) e = dalloc(&F->mg_zr, zr.size());
-            if (e == cudaSuccess) e = dalloc(&F->mg_zp, zp.size());
-            if (e == cudaSuccess) e = cudaMemcpy(F->mg_zr, zr.data(), zr.size() * sizeof(double), cudaMemcpyHostToDevice);
-            if (e == cudaSuccess) e = cudaMemcpy(F->mg_zp, zp.data(), zp.size() * sizeof(double), cudaMemcpyHostToDevice);
-            if (e != cudaSuccess) {
-                rc = fail(c, PORTA_ENOMEM, "mg_setup: allocation");
-                break;
-            }
-            F = L;
-            continue;
-        }
-        if ((rc = porta_create(&g, &a, &q, &o, &L))) {
-            rc = fail(c, rc, "mg_setup: coarse level creation");
-            break;
-        }
-        c->mg.push_back(L);
-        porta_set_stream(L, c->stream);
-        // coarse atmosphere: the finer level's values at the coincident nodes
-        const long long nf = F->nvox, ncv = L->nvox;
-        double *tmp = nullptr;
-        cudaError_t e = dalloc(&tmp, 7 * (size_t)ncv);
-        const double *src[7] = {F->d_cv64, F->d_eps, F->d_bpl, F->d_cv64 + nf, F->d_b, F->d_b + nf, F->d_b + 2 * nf};
-        for (int f = 0; f < 7 && e == cudaSuccess; ++f)
-            e = run_inject(L->nx, L->ny, L->nz, F->nx, F->ny, src[f], tmp + f * ncv, c->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-        if (e != cudaSuccess) {
-            pfree(tmp);
-            rc = fail(c, PORTA_ECUDA, std::string("mg_setup: ") + cudaGetErrorString(e));
-            break;
-        }
-        porta_atmos at{};
-        at.chi = tmp;
-        at.eps = tmp + ncv;
-        at.bpl = tmp + 2 * ncv;
-        at.vel = tmp + 3 * ncv;
-        at.bx = tmp + 4 * ncv;
-        at.by = tmp + 5 * ncv;
-        at.bz = tmp + 6 * ncv;
-        rc = porta_set_atmosphere(L, &at, PORTA_DEVICE);
-        pfree(tmp);
-        if (rc) {
-            rc = fail(c, rc, std::string("mg_setup: coarse atmosphere: ") + L->err);
-            break;
-        }
-        std::vector<double> zr, zp;
-        mg_ztables(F->z, zr, zp);
-        e = dalloc(&L->mg_src, (size_t)ncv * c->nl);
-        if (e == cudaSuccess) e = dalloc(&L->mg_rho0, (size_t)ncv * c->nl);
-        if (e == cudaSuccess) e = dalloc(&L->mg_res, (size_t)ncv * c->nl);
-        if (e == cudaSuccess) e = dalloc(&F->mg_zr, zr.size());
-        if (e == cudaSuccess) e = dalloc(&F->mg_zp, zp.size());
-        if (e == cudaSuccess) e = cudaMemcpy(F->mg_zr, zr.data(), zr.size() * sizeof(double), cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = cudaMemcpy(F->mg_zp, zp.data(), zp.size() * sizeof(double), cudaMemcpyHostToDevice);
-        if (e != cudaSuccess) {
-            rc = fail(c, PORTA_ENOMEM, "mg_setup: allocation");
-            break;
-        }
-        F = L;
-    }
-    if (rc == PORTA_OK) {
-        cudaError_t e = dalloc(&c->mg_res, (size_t)mg_nunk(c) * mg_ncomp(c));
-        if (e == cudaSuccess) e = dalloc(&c->mg_prev, (size_t)mg_nunk(c) * mg_ncomp(c));
-        if (e != cudaSuccess) rc = fail(c, PORTA_ENOMEM, "mg_setup: allocation");
-    }
-    if (rc) mg_free(c);
-    return rc;
-}
-
-int porta_mg_levels(const porta_ctx *c, int *nlevels, int *shapes)
-{
-    if (!c) return PORTA_EINVAL;
-    if (nlevels) *nlevels = c->mg.empty() ? 0 : 1 + (int)c->mg.size();
-    if (shapes && !c->mg.empty()) {
-        shapes[0] = c->nx;
-        shapes[1] = c->ny;
-        shapes[2] = c->nz;
-        for (size_t l = 0; l < c->mg.size(); ++l) {
-            shapes[3 * (l + 1)] = c->mg[l]->nx;
-            shapes[3 * (l + 1) + 1] = c->mg[l]->ny;
-            shapes[3 * (l + 1) + 2] = c->mg[l]->nz;
-        }
-    }
-    return PORTA_OK;
-}
-
-int porta_residual(porta_ctx *c, double *rnorm)
-{
-    if (!c || !rnorm) return PORTA_EINVAL;
-    if (!c->have_atm || !c->have_rho) return fail(c, PORTA_ESTATE, "residual: atmosphere or unknowns not set");
-    if (c->ml && !c->ml->have_pops) return fail(c, PORTA_ESTATE, "residual: populations not set");
-    if (c->fr1 > c->fr0) return fail(c, PORTA_ESTATE, "residual: needs the whole frequency grid");
-    const long long nu = mg_nunk(c);
-    const int nc = mg_ncomp(c);
-    double *r = nullptr;
-    cudaError_t e = pmalloc(&r, sizeof(double) * nu * nc);
-    if (e != cudaSuccess) return fail(c, PORTA_ENOMEM, "residual: allocation");
-    int rc = mg_fs(c);
-    if (rc == PORTA_OK) {
-        e = mg_apply(c, -1.0, nullptr, 1, r);                    // r = f - A(x)
-        if (e == cudaSuccess) e = cudaMemsetAsync(c->d_resid, 0, sizeof(unsigned long long), c->stream);
-        if (e == cudaSuccess) e = run_rel_residual(nu, nc, r, mg_unk(c), c->d_resid, c->stream);
-        unsigned long long bits = 0;
-        if (e == cudaSuccess) e = cudaMemcpyAsync(&bits, c->d_resid, sizeof(bits), cudaMemcpyDeviceToHost, c->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-        if (e == cudaSuccess) std::memcpy(rnorm, &bits, sizeof(double));
-        else rc = fail(c, PORTA_ECUDA, std::string("residual: ") + cudaGetErrorString(e));
-    }
-    pfree(r);
-    c->have_fs = c->have_jkq = false;
-    return rc;
-}
-
-int porta_mg_vcycle(porta_ctx *c, int npre, int npost, int ncoarse, double *max_change)
-{
-    if (!c) return PORTA_EINVAL;
-    if (c->mg.empty()) return fail(c, PORTA_ESTATE, "mg_vcycle: call porta_mg_setup first");
-    if (!c->have_atm || !c->have_rho) return fail(c, PORTA_ESTATE, "mg_vcycle: atmosphere or rho not set");
-    if (npre < 0 || npost < 0 || ncoarse < 1) return fail(c, PORTA_EINVAL, "mg_vcycle: npre, npost >= 0, ncoarse >= 1");
-    std::vector<porta_ctx *> levels{c};
-    for (porta_ctx *L : c->mg) {
-        L->stream = c->stream;
-        levels.push_back(L);
-    }
-    if (c->ml && !c->ml->have_pops) return fail(c, PORTA_ESTATE, "mg_vcycle: populations not set");
-    const long long nu = mg_nunk(c);
-    const int nc = mg_ncomp(c);
-    CK(cudaMemcpyAsync(c->mg_prev, mg_unk(c), sizeof(double) * nu * nc, cudaMemcpyDeviceToDevice, c->stream));
-    int rc = mg_vcycle(levels.data(), (int)levels.size(), 0, npre, npost, ncoarse);
-    if (rc) return rc;
-    c->have_fs = c->have_jkq = false;
-    CK(cudaMemsetAsync(c->d_resid, 0, sizeof(unsigned long long), c->stream));
-    cudaError_t e = c->ml && c->ml->pol
-                        ? run_mlpol_change(c->ml->mc, c->ml->dev, nu, c->mg_prev, mg_unk(c), c->d_resid, c->stream)
-                        : run_change(nu, nc, c->mg_prev, mg_unk(c), c->d_resid, c->stream, c->ml ? 1 : 0);
-    if (e != cudaSuccess) return fail(c, PORTA_ECUDA, std::string("mg_vcycle: ") + cudaGetErrorString(e));
-    if (max_change) {
-        unsigned long long bits = 0;
-        CK(cudaMemcpyAsync(&bits, c->d_resid, sizeof(bits), cudaMemcpyDeviceToHost, c->stream));
-        CK(cudaStreamSynchronize(c->stream));
-        std::memcpy(max_change, &bits, sizeof(double));
-    }
-    if (c->ml) {
-        for (porta_ctx *L : levels)
-            if ((rc = ml_check(L, "mg_vcycle"))) return L == c ? rc : fail(c, rc, L->err);
-    }
-    return PORTA_OK;
-}
-
-// ---------------------------------------------------------------- multilevel atom (Sec. 1)
-
-int porta_ml_create(const porta_grid *g, const porta_ml_atom *a, const porta_quad *q, const porta_opts *o,
-                    porta_ctx **out)
-{
-    if (!out) return PORTA_EINVAL;
-    *out = nullptr;
-    if (!g || !a || !q || !a->J || !a->E || !a->upper || !a->lower || !a->A || !a->eps) return PORTA_EINVAL;
-    if (a->nlevel < 2 || a->nlevel > kMlMaxLevel || a->nline < 1 || a->nline > kMlMaxLine) return PORTA_EINVAL;
-    MlConst mc{};
-    mc.nlev = a->nlevel;
-    mc.nline = a->nline;
-    for (int i = 0; i < a->nlevel; ++i) {
-        const double j2 = 2.0 * a->J[i];
-        if (!(a->J[i] >= 0.0) || j2 != std::floor(j2) || j2 > 64 || !std::isfinite(a->E[i])) return PORTA_EINVAL;
-        mc.g[i] = j2 + 1.0;
-    }
-    for (int k = 0; k < a->nline; ++k) {
-        const int u = a->upper[k], l = a->lower[k];
-        if (u < 0 || u >= a->nlevel || l < 0 || l >= a->nlevel || !(a->E[u] > a->E[l])) return PORTA_EINVAL;
-        if (!(a->A[k] > 0.0) || !std::isfinite(a->A[k]) || !(a->eps[k] > 0.0 && a->eps[k] < 1.0)) return PORTA_EINVAL;
-        mc.up[k] = u;
-        mc.lo[k] = l;
-        mc.A[k] = a->A[k];
-        mc.dE[k] = a->E[u] - a->E[l];
-        mc.Cul[k] = a->eps[k] / (1.0 - a->eps[k]) * a->A[k];
-    }
-    // intensities in units of 2 h nu^3 / c^2 of line 0; opacity strengths relative to line 0
-    for (int k = 0; k < a->nline; ++k) {
-        const double r = mc.dE[k] / mc.dE[0];
-        mc.r3[k] = r * r * r;
-        mc.Bul[k] = mc.A[k] / mc.r3[k];
-        mc.Blu[k] = mc.g[mc.up[k]] / mc.g[mc.lo[k]] * mc.Bul[k];
-        mc.s[k] = mc.g[mc.up[k]] / mc.g[mc.lo[k]] * mc.A[k] / (mc.dE[k] * mc.dE[k]);
-    }
-    for (int k = a->nline - 1; k >= 0; --k) mc.s[k] /= mc.s[0];
-    if (a->polarized != 0 && a->polarized != 1) return PORTA_EINVAL;
-    if (a->polarized && !(a->zeta >= 0.0 && std::isfinite(a->zeta))) return PORTA_EINVAL;
-    MlPolTables tab;
-    if (a->polarized) {
-        std::vector<double> J(a->J, a->J + a->nlevel), E(a->E, a->E + a->nlevel), A(a->A, a->A + a->nline),
-            eps(a->eps, a->eps + a->nline);
-        std::vector<int> up(a->upper, a->upper + a->nline), lo(a->lower, a->lower + a->nline);
-        if (mlpol_tables(J, E, up, lo, A, eps, tab)) return PORTA_EINVAL;
-    }
-    std::vector<porta_grid> grids(a->nline, *g);
-    porta_atom at{a->polarized ? PORTA_MODEL_TWOLEVEL_HANLE : PORTA_MODEL_TWOLEVEL_UNPOL,
-                  a->polarized ? a->zeta : 0.0, 1.0, 25.0};
-    porta_ctx *c = nullptr;
-    int rc = create_impl(a->nline, grids.data(), &at, q, o, &c);
-    if (rc) return rc;
-    MlState *m = new (std::nothrow) MlState();
-    if (!m) {
-        porta_destroy(c);
-        return PORTA_ENOMEM;
-    }
-    c->ml = m;
-    m->mc = mc;
-    m->J.assign(a->J, a->J + a->nlevel);
-    m->E.assign(a->E, a->E + a->nlevel);
-    m->A.assign(a->A, a->A + a->nline);
-    m->eps.assign(a->eps, a->eps + a->nline);
-    m->up.assign(a->upper, a->upper + a->nline);
-    m->lo.assign(a->lower, a->lower + a->nline);
-    m->nvox1 = (long long)g->nx * g->ny * g->nz;
-    cudaError_t e = dalloc(&m->d_pops, (size_t)m->nvox1 * mc.nlev);
-    if (e == cudaSuccess) e = dalloc(&m->d_chis, (size_t)m->nvox1);
-    if (e == cudaSuccess) e = dalloc(&m->d_kT, (size_t)m->nvox1);
-    if (e == cudaSuccess) e = pmalloc(&m->d_bad, sizeof(unsigned long long));
-    if (e == cudaSuccess) e = cudaMemset(m->d_bad, 0, sizeof(unsigned long long));
-    m->nunk = mc.nlev;
-    if (e == cudaSuccess && a->polarized) {
-        // the tables in one device allocation: ints first, then doubles (8-byte aligned)
-        m->pol = true;
-        m->tab = tab;
-        m->nunk = tab.nunk;
-        const size_t ni = tab.pop_idx.size() + tab.up2.size() + tab.cell_rc.size() + tab.cell_start.size() +
-                          tab.ent_src.size() + tab.act.size() + tab.inact.size() + tab.apop.size() + tab.lo2.size();
-        const size_t nd = tab.w2.size() + tab.trace.size() + tab.ent_coef.size() + tab.w2lo.size();
-        const size_t ibytes = (ni * sizeof(int) + 7) / 8 * 8;
-        std::vector<char> h(ibytes + nd * sizeof(double));
-        int *ip = (int *)h.data();
-        double *dp = (double *)(h.data() + ibytes);
-        size_t io[9], doff[4], k = 0, kd = 0;
-        const std::vector<int> *iv[9] = {&tab.pop_idx, &tab.up2, &tab.cell_rc, &tab.cell_start, &tab.ent_src,
-                                         &tab.act, &tab.inact, &tab.apop, &tab.lo2};
-        for (int q2 = 0; q2 < 9; ++q2) {
-            io[q2] = k;
-            for (int x : *iv[q2]) ip[k++] = x;
-        }
-        const std::vector<double> *dv[4] = {&tab.w2, &tab.trace, &tab.ent_coef, &tab.w2lo};
-        for (int q2 = 0; q2 < 4; ++q2) {
-            doff[q2] = kd;
-            for (double x : *dv[q2]) dp[kd++] = x;
-        }
-        e = pmalloc(&m->d_tab, h.size());
-        if (e == cudaSuccess) e = cudaMemcpy(m->d_tab, h.data(), h.size(), cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = dalloc(&m->d_x, (size_t)m->nvox1 * tab.nunk);
-        if (e == cudaSuccess) e = pmalloc(&c->d_dich, (size_t)5 * c->nvox * c->rsz);
-        if (e == cudaSuccess) e = cudaMemset(c->d_dich, 0, (size_t)5 * c->nvox * c->rsz);
-        const int *di = (const int *)m->d_tab;
-        const double *dd = (const double *)((const char *)m->d_tab + ibytes);
-        MlPolDev &d = m->dev;
-        d.nunk = tab.nunk;
-        d.nsrc = tab.nsrc;
-        d.ncell = (int)tab.cell_start.size() - 1;
-        d.row0 = tab.row0;
-        d.src_j = tab.src_j; d.src_b = tab.src_b; d.src_clu = tab.src_clu; d.src_pop = tab.src_pop; d.src_spop = tab.src_spop;
-        d.pop_idx = di + io[0]; d.up2 = di + io[1]; d.cell_rc = di + io[2]; d.cell_start = di + io[3]; d.ent_src = di + io[4];
-        d.act = di + io[5]; d.inact = di + io[6]; d.apop = di + io[7]; d.lo2 = di + io[8];
-        d.w2lo = dd + doff[3];
-        d.nact = tab.nact;
-        d.ninact = (int)tab.inact.size();
-        d.w2 = dd + doff[0]; d.trace = dd + doff[1]; d.ent_coef = dd + doff[2];
-    }
-    if (e != cudaSuccess) {
-        porta_destroy(c);
-        return PORTA_ENOMEM;
-    }
-    *out = c;
-    return PORTA_OK;
-}
-
-int porta_ml_set_atmosphere(porta_ctx *c, const double *chi, const double *kT, const double *vel, const double *bx,
-                            const double *by, const double *bz, int where)
-{
-    if (!c) return PORTA_EINVAL;
-    MlState *m = c->ml;
-    if (!m) return fail(c, PORTA_EINVAL, "ml_set_atmosphere: not a multilevel context");
-    if (!chi || !kT || !vel || (where != PORTA_HOST && where != PORTA_DEVICE))
-        return fail(c, PORTA_EINVAL, "ml_set_atmosphere: bad argument");
-    if (m->pol && (!bx || !by || !bz)) return fail(c, PORTA_EINVAL, "ml_set_atmosphere: magnetic field required");
-    const long long n1 = m->nvox1, n = c->nvox;
-    std::vector<double> hv(n1);
-    cudaMemcpyKind k = where == PORTA_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    CK(cudaMemcpyAsync(m->d_chis, chi, n1 * sizeof(double), k, c->stream));
-    CK(cudaMemcpyAsync(m->d_kT, kT, n1 * sizeof(double), k, c->stream));
-    unsigned long long bad = 0;
-    int rc = count_bad(c, m->d_chis, n1, 0.0, 1e300, &bad);
-    if (rc) return rc;
-    if (bad) return fail(c, PORTA_EINVAL, "ml_set_atmosphere: chi must be finite and > 0");
-    if ((rc = count_bad(c, m->d_kT, n1, 0.0, 1e300, &bad))) return rc;
-    if (bad) return fail(c, PORTA_EINVAL, "ml_set_atmosphere: kT must be finite and > 0");
-    if (where == PORTA_DEVICE)
-        CK(cudaMemcpy(hv.data(), vel, n1 * sizeof(double), cudaMemcpyDeviceToHost));
-    else
-        std::memcpy(hv.data(), vel, n1 * sizeof(double));
-    // the line boxes share the grid and the velocity; their opacity, Planck
-    // function and source function are written from the populations
-    std::vector<double> vrep(n), ones(n, 1.0), half(n, 0.5);
-    for (int b = 0; b < m->mc.nline; ++b) std::memcpy(vrep.data() + b * n1, hv.data(), n1 * sizeof(double));
-    std::vector<double> brep[3];
-    if (m->pol) {
-        const double *src[3] = {bx, by, bz};
-        for (int d = 0; d < 3; ++d) {
-            brep[d].resize(n);
-            if (where == PORTA_DEVICE)
-                CK(cudaMemcpy(brep[d].data(), src[d], n1 * sizeof(double), cudaMemcpyDeviceToHost));
-            else
-                std::memcpy(brep[d].data(), src[d], n1 * sizeof(double));
-            for (int b = 1; b < m->mc.nline; ++b) std::memcpy(brep[d].data() + b * n1, brep[d].data(), n1 * sizeof(double));
-        }
-        // the first-order (weak-field) Zeeman term eta_V = 2 zeta (B.Omega)(x - s) eta_I is a
-        // propagation matrix only while |eta_V| < eta_I over the frequency grid
-        double bmax = 0.0, vmax = 0.0;
-        for (long long v = 0; v < n1; ++v) {
-            bmax = std::max(bmax, std::sqrt(brep[0][v] * brep[0][v] + brep[1][v] * brep[1][v] + brep[2][v] * brep[2][v]));
-            vmax = std::max(vmax, std::fabs(hv[v]));
-        }
-        if (!(2.0 * c->zeta * bmax * (c->x_max + vmax) < 1.0))
-            return fail(c, PORTA_EINVAL, "ml_set_atmosphere: the weak-field Zeeman term 2 zeta |B| (x_max + |v|) reaches 1 "
-                                         "(|eta_V| > eta_I); lower zeta or the field");
-    }
-    porta_atmos at{ones.data(), half.data(), ones.data(), vrep.data(), m->pol ? brep[0].data() : nullptr,
-                   m->pol ? brep[1].data() : nullptr, m->pol ? brep[2].data() : nullptr};
-    rc = porta_set_atmosphere(c, &at, PORTA_HOST);
-    if (rc) return rc;
-    m->have_atm = true;
-    if (m->have_pops) {
-        cudaError_t e = ml_prepare(c);
-        if (e != cudaSuccess) return fail(c, PORTA_ECUDA, cudaGetErrorString(e));
-    }
-    return PORTA_OK;
-}
-
-int porta_ml_set_pops(porta_ctx *c, const double *pops, int where)
-{
-    if (!c) return PORTA_EINVAL;
-    MlState *m = c->ml;
-    if (!m) return fail(c, PORTA_EINVAL, "ml_set_pops: not a multilevel context");
-    if (!pops || (where != PORTA_HOST && where != PORTA_DEVICE)) return fail(c, PORTA_EINVAL, "ml_set_pops: bad argument");
-    if (!m->have_atm) return fail(c, PORTA_ESTATE, "ml_set_pops: atmosphere not set");
-    const long long n = m->nvox1 * m->mc.nlev;
-    int rc = copy_in(c, m->d_pops, pops, n, where);
-    if (rc) return rc;
-    unsigned long long bad = 0;
-    if ((rc = count_bad(c, m->d_pops, n, 0.0, 1e300, &bad))) return rc;
-    if (bad) return fail(c, PORTA_EINVAL, "ml_set_pops: populations must be finite and > 0");
-    if (m->pol) {
-        // no atomic polarization: rho^0_0 = n / sqrt(2J+1)
-        std::vector<double> hp(n), hx((size_t)m->nvox1 * m->nunk, 0.0);
-        CK(cudaStreamSynchronize(c->stream));
-        CK(cudaMemcpy(hp.data(), m->d_pops, n * sizeof(double), cudaMemcpyDeviceToHost));
-        for (long long v = 0; v < m->nvox1; ++v)
-            for (int i = 0; i < m->mc.nlev; ++i)
-                hx[v * m->nunk + m->tab.pop_idx[i]] = hp[v * m->mc.nlev + i] / std::sqrt(m->mc.g[i]);
-        CK(cudaMemcpy(m->d_x, hx.data(), hx.size() * sizeof(double), cudaMemcpyHostToDevice));
-    }
-    CK(cudaMemsetAsync(m->d_bad, 0, sizeof(unsigned long long), c->stream));
-    CK(ml_prepare(c));
-    unsigned long long hb = 0;
-    CK(cudaMemcpyAsync(&hb, m->d_bad, sizeof(hb), cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
-    if (hb) return fail(c, PORTA_EINVAL, "ml_set_pops: a line has a non-positive opacity (population inversion)");
-    m->have_pops = true;
-    c->have_rho = true;
-    c->have_fs = c->have_jkq = false;
-    return PORTA_OK;
-}
-
-int porta_ml_get_pops(porta_ctx *c, double *pops, int where)
-{
-    if (!c) return PORTA_EINVAL;
-    MlState *m = c->ml;
-    if (!m) return fail(c, PORTA_EINVAL, "ml_get_pops: not a multilevel context");
-    if (!pops || (where != PORTA_HOST && where != PORTA_DEVICE)) return fail(c, PORTA_EINVAL, "ml_get_pops: bad argument");
-    if (!m->have_pops) return fail(c, PORTA_ESTATE, "ml_get_pops: populations not set");
-    if (m->pol) {
-        std::vector<double> hx((size_t)m->nvox1 * m->nunk), hp((size_t)m->nvox1 * m->mc.nlev);
-        CK(cudaMemcpyAsync(hx.data(), m->d_x, hx.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-        CK(cudaStreamSynchronize(c->stream));
-        for (long long v = 0; v < m->nvox1; ++v)
-            for (int i = 0; i < m->mc.nlev; ++i)
-                hp[v * m->mc.nlev + i] = std::sqrt(m->mc.g[i]) * hx[v * m->nunk + m->tab.pop_idx[i]];
-        CK(cudaMemcpy(pops, hp.data(), hp.size() * sizeof(double),
-                      where == PORTA_DEVICE ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost));
-        return PORTA_OK;
-    }
-    CK(cudaMemcpyAsync(pops, m->d_pops, m->nvox1 * m->mc.nlev * sizeof(double),
-                       where == PORTA_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
-    if (where == PORTA_HOST) CK(cudaStreamSynchronize(c->stream));
-    return PORTA_OK;
-}
-
-int porta_ml_emergent_stokes(porta_ctx *c, int line, int ndir, const double *mu, const double *chi, double *out,
-                             int where)
-{
-    if (!c) return PORTA_EINVAL;
-    MlState *m = c->ml;
-    if (!m) return fail(c, PORTA_EINVAL, "ml_emergent_stokes: not a multilevel context");
-    if (line < 0 || line >= m->mc.nline || ndir < 1 || !mu || !chi || !out ||
-        (where != PORTA_HOST && where != PORTA_DEVICE))
-        return fail(c, PORTA_EINVAL, "ml_emergent_stokes: bad argument");
-    for (int d = 0; d < ndir; ++d)
-        if (!(mu[d] > 0.0 && mu[d] <= 1.0) || !std::isfinite(chi[d]))
-            return fail(c, PORTA_EINVAL, "ml_emergent_stokes: mu must lie in (0, 1], chi finite");
-    if (!m->have_atm || !m->have_pops) return fail(c, PORTA_ESTATE, "ml_emergent_stokes: atmosphere or populations not set");
-    const long long n = (long long)ndir * c->n_nu * c->nx * c->ny * c->ns;
-    double *dout = out;
-    if (where == PORTA_HOST) CK(dalloc(&dout, n));
-    int rc = c->precision == PORTA_FP32 ? emergent_t<float>(c, ndir, mu, chi, dout, line)
-                                        : emergent_t<double>(c, ndir, mu, chi, dout, line);
-    if (where == PORTA_HOST) {
-        if (rc == PORTA_OK) {
-            cudaError_t e = cudaMemcpy(out, dout, n * sizeof(double), cudaMemcpyDeviceToHost);
-            if (e != cudaSuccess) rc = fail(c, PORTA_ECUDA, cudaGetErrorString(e));
-        }
-        pfree(dout);
-    }
-    return rc;
-}
-
-int porta_ml_unknowns(const porta_ctx *c, int *nunk)
-{
-    if (!c || !nunk) return PORTA_EINVAL;
-    if (!c->ml) return PORTA_EINVAL;
-    *nunk = c->ml->nunk;
-    return PORTA_OK;
-}
-
-int porta_ml_set_unknowns(porta_ctx *c, const double *x, int where)
-{
-    if (!c) return PORTA_EINVAL;
-    MlState *m = c->ml;
-    if (!m) return fail(c, PORTA_EINVAL, "ml_set_unknowns: not a multilevel context");
-    if (!m->pol) return porta_ml_set_pops(c, x, where);
-    if (!x || (where != PORTA_HOST && where != PORTA_DEVICE)) return fail(c, PORTA_EINVAL, "ml_set_unknowns: bad argument");
-    if (!m->have_atm) return fail(c, PORTA_ESTATE, "ml_set_unknowns: atmosphere not set");
-    const long long n = m->nvox1 * m->nunk;
-    int rc = copy_in(c, m->d_x, x, n, where);
-    if (rc) return rc;
-    unsigned long long bad = 0;
-    if ((rc = count_bad(c, m->d_x, n, -1e300, 1e300, &bad))) return rc;
-    if (bad) return fail(c, PORTA_EINVAL, "ml_set_unknowns: non-finite value");
-    CK(cudaMemsetAsync(m->d_bad, 0, sizeof(unsigned long long), c->stream));
-    CK(ml_prepare(c));
-    unsigned long long hb = 0;
-    CK(cudaMemcpyAsync(&hb, m->d_bad, sizeof(hb), cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
-    if (hb) return fail(c, PORTA_EINVAL, "ml_set_unknowns: non-positive population or line opacity");
-    m->have_pops = true;
-    c->have_rho = true;
-    c->have_fs = c->have_jkq = false;
-    return PORTA_OK;
-}
-
-int porta_ml_get_unknowns(porta_ctx *c, double *x, int where)
-{
-    if (!c) return PORTA_EINVAL;
-    MlState *m = c->ml;
-    if (!m) return fail(c, PORTA_EINVAL, "ml_get_unknowns: not a multilevel context");
-    if (!m->pol) return porta_ml_get_pops(c, x, where);
-    if (!x || (where != PORTA_HOST && where != PORTA_DEVICE)) return fail(c, PORTA_EINVAL, "ml_get_unknowns: bad argument");
-    if (!m->have_pops) return fail(c, PORTA_ESTATE, "ml_get_unknowns: unknowns not set");
-    CK(cudaMemcpyAsync(x, m->d_x, m->nvox1 * m->nunk * sizeof(double),
-                       where == PORTA_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
-    if (where == PORTA_HOST) CK(cudaStreamSynchronize(c->stream));
-    return PORTA_OK;
-}
-
-// the error counter of the line data and of the rate equations (synchronizes)
-static int ml_check(porta_ctx *c, const char *what)
-{
-    unsigned long long hb = 0;
-    CK(cudaMemcpyAsync(&hb, c->ml->d_bad, sizeof(hb), cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
-    if (hb) {
-        cudaMemsetAsync(c->ml->d_bad, 0, sizeof(hb), c->stream);
-        return fail(c, PORTA_EKERNEL, std::string(what) + ": singular rate equations, non-positive population or "
-                                                          "line opacity (population inversion)");
-    }
-    return PORTA_OK;
-}
-
-int porta_ml_formal_solve(porta_ctx *c, double *jbar, double *lstar, int where)
-{
-    if (!c) return PORTA_EINVAL;
-    MlState *m = c->ml;
-    if (!m) return fail(c, PORTA_EINVAL, "ml_formal_solve: not a multilevel context");
-    if (!m->have_atm || !m->have_pops) return fail(c, PORTA_ESTATE, "ml_formal_solve: atmosphere or populations not set");
-    int rc = porta_formal_solve(c);
-    if (rc == PORTA_OK) rc = porta_accumulate_jkq(c, jbar, lstar, where);
-    return rc;
-}
-
-int porta_ml_see_update(porta_ctx *c, double *max_change)
-{
-    if (!c) return PORTA_EINVAL;
-    if (!c->ml) return fail(c, PORTA_EINVAL, "ml_see_update: not a multilevel context");
-    int rc = porta_see_update(c, max_change);
-    if (rc == PORTA_OK && max_change) rc = ml_check(c, "ml_see_update");
-    return rc;
-}
-
-int porta_ml_iterate(porta_ctx *c, int iterations, double *max_change)
-{
-    if (!c) return PORTA_EINVAL;
-    MlState *m = c->ml;
-    if (!m) return fail(c, PORTA_EINVAL, "ml_iterate: not a multilevel context");
-    if (!m->have_atm || !m->have_pops) return fail(c, PORTA_ESTATE, "ml_iterate: atmosphere or populations not set");
-    if (iterations < 0) return fail(c, PORTA_EINVAL, "ml_iterate: negative count");
-    int rc = PORTA_OK;
-    for (int it = 0; it < iterations && rc == PORTA_OK; ++it) {
-        rc = porta_ml_formal_solve(c, nullptr, nullptr, PORTA_DEVICE);
-        if (rc == PORTA_OK) rc = porta_see_update(c, it == iterations - 1 ? max_change : nullptr);
-    }
-    if (rc == PORTA_OK) rc = ml_check(c, "ml_iterate");
-    return rc;
-}
-
 }  // extern "C"

@@ -20,6 +20,7 @@
 
 #include <cmath>
 
+#include "api_internal.h"
 #include "porta.h"
 #include "porta_internal.cuh"
 #include "see_kernels.cuh"
@@ -57,37 +58,8 @@ struct GaussNodes {
     double x[kMaxMu], w[kMaxMu];
 };
 
-// Gauss-Legendre nodes and weights on (0, 1) (Newton iteration on P_n), into a
-// fixed-size argument block
-void gauss_nodes(int n, GaussNodes &g)
-{
-    for (int i = 0; i < n; ++i) {
-        double t = std::cos(M_PI * (4.0 * i + 3.0) / (4.0 * n + 2.0)), dp = 1.0;
-        for (int it = 0; it < 100; ++it) {
-            double pm1 = 1.0, p = t;
-            for (int k = 1; k < n; ++k) {
-                double pn = ((2 * k + 1) * t * p - k * pm1) / (k + 1);
-                pm1 = p;
-                p = pn;
-            }
-            if (n == 1) { p = t; pm1 = 1.0; }
-            dp = n * (pm1 - t * p) / (1.0 - t * t);
-            double dt = p / dp;
-            t -= dt;
-            if (std::fabs(dt) < 1e-16) break;
-        }
-        double pm1 = 1.0, p = t;
-        for (int k = 1; k < n; ++k) {
-            double pn = ((2 * k + 1) * t * p - k * pm1) / (k + 1);
-            pm1 = p;
-            p = pn;
-        }
-        if (n == 1) { p = t; pm1 = 1.0; }
-        dp = n * (pm1 - t * p) / (1.0 - t * t);
-        g.x[n - 1 - i] = 0.5 * (t + 1.0);
-        g.w[n - 1 - i] = 1.0 / ((1.0 - t * t) * dp * dp);
-    }
-}
+// Gauss-Legendre nodes and weights on (0, 1) into a fixed-size argument block
+void gauss_nodes(int n, GaussNodes &g) { porta_api::gauss_legendre(n, g.x, g.w); }
 
 struct TableArgs {
     int n_mu, n_chi, n_nu, nx, ny, nz;
