@@ -76,24 +76,30 @@ __device__ __forceinline__ Coef<double> coefficients(double t)
 // within 6e-7 relative of its exact value for all t > 0 when evaluated in
 // FP32: degree-7 series for t < 0.25, degree-12 series for t < 1.5, closed
 // forms above (where their cancellation costs at most a factor ~5).
+// w_M, w_O, w_C of one optical path t given e = exp(-t)
+__device__ __forceinline__ void wcoef(float t, float e, float &wm, float &wo, float &wc)
+{
+    if (t < 0.25f) {
+        wm = horner<float, 7, c_wm>(t);
+        wo = horner<float, 7, c_wo>(t);
+        wc = horner<float, 7, c_wc>(t);
+    } else if (t < 1.5f) {
+        wm = horner<float, 12, c_wm>(t);
+        wo = horner<float, 12, c_wo>(t);
+        wc = horner<float, 12, c_wc>(t);
+    } else {
+        const float it = 1.0f / t, it2 = it * it;
+        wm = (2.0f - e * (t * t + 2.0f * t + 2.0f)) * it2;
+        wo = 1.0f - 2.0f * (e + t - 1.0f) * it2;
+        wc = 2.0f * (t - 2.0f + e * (t + 2.0f)) * it2;
+    }
+}
+
 __device__ __forceinline__ Coef<float> coefficients(float t)
 {
     Coef<float> c;
     c.e = expf(-t);
-    if (t < 0.25f) {
-        c.wm = horner<float, 7, c_wm>(t);
-        c.wo = horner<float, 7, c_wo>(t);
-        c.wc = horner<float, 7, c_wc>(t);
-    } else if (t < 1.5f) {
-        c.wm = horner<float, 12, c_wm>(t);
-        c.wo = horner<float, 12, c_wo>(t);
-        c.wc = horner<float, 12, c_wc>(t);
-    } else {
-        const float e = c.e, it = 1.0f / t, it2 = it * it;
-        c.wm = (2.0f - e * (t * t + 2.0f * t + 2.0f)) * it2;
-        c.wo = 1.0f - 2.0f * (e + t - 1.0f) * it2;
-        c.wc = 2.0f * (t - 2.0f + e * (t + 2.0f)) * it2;
-    }
+    wcoef(t, c.e, c.wm, c.wo, c.wc);
     c.pm = c.wm + 0.5f * c.wc;
     c.po = c.wo + 0.5f * c.wc;
     return c;

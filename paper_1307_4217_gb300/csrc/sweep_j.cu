@@ -360,7 +360,9 @@ __device__ __forceinline__ void jsweep_item(const SweepArgs<Real> &a, cg::cluste
         const V *rMb = ringv + sM * W::s_chunks * nodes, *rOb = ringv + sO * W::s_chunks * nodes;
         const V *rPb = ringv + sP * W::s_chunks * nodes;
 
-        Real acc[NA];
+        Real acc[NA], accp[NA];
+        bool pend = false, row0_written = false;
+        int vpend = 0;
         int l = pfirst / nx, c = pfirst - (pfirst / nx) * nx;
         // every warp takes the same number of point rounds (the lane shuffles below)
         for (int pb = 0; pb < npts; pb += pstep) {
@@ -371,6 +373,7 @@ __device__ __forceinline__ void jsweep_item(const SweepArgs<Real> &a, cg::cluste
                 if (c >= nx) { c -= nx; ++l; }
             }
             const bool active = p < npts;
+            row0_written |= active && l == 0;
 #pragma unroll
             for (int s = 0; s < NA; ++s) acc[s] = Real(0);
             int v = 0;
@@ -495,8 +498,15 @@ __device__ __forceinline__ void jsweep_item(const SweepArgs<Real> &a, cg::cluste
                                 Real t[4][4];
                                 StokesIO<Real, 4>::load(pl, ipts, ilo + c, t[0]);
                                 StokesIO<Real, 4>::load(pl, ipts, ilo + c1, t[1]);
-                                StokesIO<Real, 4>::load(ph, ipts, ihi + c, t[2]);
-                                StokesIO<Real, 4>::load(ph, ipts, ihi + c1, t[3]);
+                                // the row after the strip's last is the next CTA's row 0 (DSMEM, a
+                                // generic load); the others are local (shared-memory loads)
+                                if (last_row) {
+                                    StokesIO<Real, 4>::load(ph, ipts, c, t[2]);
+                                    StokesIO<Real, 4>::load(ph, ipts, c1, t[3]);
+                                } else {
+                                    StokesIO<Real, 4>::load(pl, ipts, ilo + nx + c, t[2]);
+                                    StokesIO<Real, 4>::load(pl, ipts, ilo + nx + c1, t[3]);
+                                }
                                 IM01 = pmul(wM2[0], pmk(t[0][0], t[0][1]));
                                 IM23 = pmul(wM2[0], pmk(t[0][2], t[0][3]));
 #pragma unroll
@@ -593,13 +603,29 @@ __device__ __forceinline__ void jsweep_item(const SweepArgs<Real> &a, cg::cluste
                 for (int s = 0; s < NA; ++s) acc[s] += __shfl_xor_sync(0xffffffffu, acc[s], o);
             }
             if (active && lane == 0) {
-                if (a.jacc) add_terms(v, acc);
-                else store_partial<Real, NS>(a, m, v, g, acc);
+                if (pb + pstep < npts) {
+                    if (a.jacc) add_terms(v, acc);
+                    else store_partial<Real, NS>(a, m, v, g, acc);
+                } else {
+                    pend = true;
+                    vpend = v;
+#pragma unroll
+                    for (int s = 0; s < NA; ++s) accp[s] = acc[s];
+                }
             }
         }
-        // plane q done here: arrive (release), stage plane q+2, wait (acquire)
+        // plane q done here: arrive (release), stage plane q+2, wait (acquire). The
+        // last point round's sums go to global memory after the arrive, so that its
+        // release does not wait for them (nothing in the sweep reads them).
         __syncthreads();
-        cluster_arrive_release();
+        // release by the warps that wrote row 0 (the only Stokes vectors another CTA
+        // reads, through DSMEM); the others' plane data are read in this CTA only
+        if (__any_sync(0xffffffffu, row0_written)) cluster_arrive_release();
+        else cluster_arrive_relaxed();
+        if (pend) {
+            if (a.jacc) add_terms(vpend, accp);
+            else store_partial<Real, NS>(a, m, vpend, g, accp);
+        }
         if (q + 2 < nz) fill(q + 2);
         __syncthreads();
         cluster_wait_acquire();

@@ -126,7 +126,11 @@ def test_polarized_box_converged_fp32_and_fp64_match_the_converged_oracle():
     s0 = ro[..., 0]
     sig = ro[..., 1:] / s0[..., None]
     n64 = 0
-    for prec, tol_it, tol in ((P.PORTA_FP64, 1e-8, 1e-8), (P.PORTA_FP32, 1e-6, 1e-4)):
+    # FP32: the Jacobi step divides a change of J by 1 - (1 - eps) Lambda-bar* >= eps, so
+    # the FP32 rounding of J (a few 1e-7 relative: unit roundoff 6e-8 over the chain of
+    # a formal solution) leaves the converged S^0_0 within ~3e-7 / eps of the exact one
+    eps_min = float(np.min(atm["eps"]))
+    for prec, tol_it, tol in ((P.PORTA_FP64, 1e-8, 1e-8), (P.PORTA_FP32, 1e-6, 3e-7 / eps_min)):
         ctx = make_ctx(atm, 1, *quad, prec)
         ctx.set_stream(torch.cuda.Stream())
         n, ch, conv = ctx.iterate_to(tol_it, 3000 if prec == P.PORTA_FP64 else 2 * n64)
