@@ -22,6 +22,9 @@ MODEL_UNPOL = 0
 MODEL_HANLE = 1
 BESSER = 0
 DELOPAR = 1
+LINEAR = 2
+BEZIER_FB = 3
+CBEZIER = 4
 
 
 def build(force=False):
@@ -208,6 +211,39 @@ def solve_1d(tau, S, I0, method=BESSER):
     return out
 
 
+# ---- the one-ray sigmoid benchmark of Sec. 3.4 (Eqs. 15-18) ----
+def sigmoid(a, d, z):
+    """Eq. 16: sigma(a, d, z) = 1 / (1 + exp(-a (z - d)))."""
+    return 1.0 / (1.0 + np.exp(-a * (np.asarray(z, dtype=np.float64) - d)))
+
+
+def sigmoid_source(z):
+    """Eq. 15: S(z) = sigma(2, -5, z) sigma(-2, 5, z) (constant opacity, z = tau)."""
+    return sigmoid(2.0, -5.0, z) * sigmoid(-2.0, 5.0, z)
+
+
+def sigmoid_exact(z):
+    """Eq. 17: the analytic intensity towards +z for I(-inf) = 0."""
+    z = np.asarray(z, dtype=np.float64)
+    return np.exp(15.0 - z) / (np.exp(20.0) - 1.0) * (np.exp(10.0) * np.arctan(np.exp(z - 5.0))
+                                                      - np.arctan(np.exp(z + 5.0)))
+
+
+def sigmoid_grid(dtau, shift=0.0):
+    """Nodes z_k = -12 + shift + k dtau within [-12, 12] (shift in [0, dtau))."""
+    n = int(np.floor((24.0 - shift) / dtau + 1e-9)) + 1
+    return -12.0 + shift + dtau * np.arange(n)
+
+
+def sigmoid_error(dtau, method=BESSER, shift=0.0):
+    """E(dtau) (Eq. 18): max over the nodes of |I - I_a| / I_a, starting from the
+    exact intensity at the first node (the paper's boundary value at z = -12)."""
+    z = sigmoid_grid(dtau, shift)
+    ia = sigmoid_exact(z)
+    I = solve_1d(z - z[0], sigmoid_source(z), ia[0], method)
+    return float(np.max(np.abs((I - ia) / ia)))
+
+
 def step(ns, IM, etaM, epsM, etaO, epsO, etaP_I, epsP, dsM, dsP, has_p=True, method=BESSER):
     a = [_f64(x) for x in (IM, etaM, epsM, etaO, epsO, epsP)]
     IO = np.zeros(ns); ls = np.zeros(1)
@@ -287,7 +323,10 @@ def coeffs_deriv(tau):
 
 
 def control_point_vjp(yM, yO, yP, hM, hP, has_p=True, method=BESSER, gc=1.0):
-    """Gradient of the control point with respect to (yM, yO, yP, hM, hP), times gc."""
+    """Gradient of the control point with respect to (yM, yO, yP, hM, hP), times gc
+    (BESSER and DELOPAR)."""
+    if method not in (BESSER, DELOPAR):
+        raise ValueError("reverse mode is defined for BESSER and DELOPAR")
     g = np.zeros(5)
     lib().or_control_point_vjp(yM, yO, yP, hM, hP, int(has_p), method, float(gc), _ptr(g))
     return g

@@ -62,11 +62,15 @@ static double dmax(double a, double b) { return a > b ? a : b; }
  * Upwind control point c_M of the quadratic Bezier spline on MO (Sec. 3.2,
  * steps 1-9). h_M = tau_MO, h_P = tau_OP. Without a downwind point the
  * interpolation on MO is linear, c_M = (y_M + y_O)/2. DELOPAR is the
- * parabola through M, O, P (step 4 without the overshoot checks).
+ * parabola through M, O, P (step 4 without the overshoot checks). The linear
+ * method is the Bezier curve with c_M at the midpoint (a straight line).
+ * BEZIER_FB takes the derivative at O from the weighted harmonic mean of the
+ * two one-sided slopes (Fritsch & Butland 1984; 0 where they differ in sign),
+ * and CBEZIER adds the upwind overshoot test of steps 5-6.
  */
 double or_control_point(double yM, double yO, double yP, double hM, double hP, int has_p, int method)
 {
-    if (!has_p) { OR_FLOPS(2); OR_BRANCH(4); return 0.5 * (yM + yO); }
+    if (!has_p || method == OR_LINEAR) { OR_FLOPS(2); OR_BRANCH(4); return 0.5 * (yM + yO); }
     double dM = (yO - yM) / hM;                          /* step 1 */
     double dP = (yP - yO) / hP;
     OR_FLOPS(4);
@@ -74,6 +78,16 @@ double or_control_point(double yM, double yO, double yP, double hM, double hP, i
         double yp = (hM * dP + hP * dM) / (hM + hP);
         OR_FLOPS(9);
         return yO - 0.5 * hM * yp;
+    }
+    if (method == OR_BEZIER_FB || method == OR_CBEZIER) {
+        if (dM * dP <= 0.0) return yO;
+        /* 1/y'_O = alpha/d_M + (1 - alpha)/d_P, alpha = (1 + h_P/(h_M + h_P))/3 */
+        double alpha = (1.0 + hP / (hM + hP)) / 3.0;
+        double yp = dM * dP / (alpha * dP + (1.0 - alpha) * dM);
+        double cM = yO - 0.5 * hM * yp;
+        OR_FLOPS(12);
+        if (method == OR_CBEZIER && (cM < dmin(yM, yO) || cM > dmax(yM, yO))) return yM;
+        return cM;
     }
     OR_FLOPS(1);
     if (dM * dP <= 0.0) { OR_BRANCH(0); return yO; }     /* step 2 */
@@ -105,6 +119,11 @@ int or_solve_1d(int n, const double *tau, const double *S, double I0, int method
         double hP = has_p ? tau[i + 1] - tau[i] : 0.0;
         double c[6];
         or_coeffs(hM, c);
+        if (method == OR_LINEAR) {
+            /* S linear on MO: I_O = e I_M + psi'_M S_M + psi'_O S_O (Sec. 3.3) */
+            I[i] = c[0] * I[i - 1] + c[1] * S[i - 1] + c[2] * S[i];
+            continue;
+        }
         double cM = or_control_point(S[i - 1], S[i], has_p ? S[i + 1] : 0.0, hM, hP, has_p, method);
         I[i] = c[0] * I[i - 1] + c[3] * S[i - 1] + c[4] * S[i] + c[5] * cM;
     }

@@ -24,7 +24,12 @@ extern "C" {
 enum { OR_MODEL_UNPOL = 0,   /* two-level atom, Stokes I only (non-LTE problem of the 1st kind) */
        OR_MODEL_HANLE = 1 }; /* two-level atom Jl=0 -> Ju=1, rho^K_Q K=0,2, Hanle + weak-field Zeeman */
 
-enum { OR_BESSER = 0, OR_DELOPAR = 1 };
+/* formal solvers of the upwind interval MO (Sec. 3.2; the family compared on the
+   sigmoid benchmark of Sec. 3.4): BESSER; DELOPAR (the parabola through M, O, P:
+   the standard parabolic short characteristics for Stokes I); linear SC; quadratic
+   Bezier with the Fritsch-Butland derivative at O, without (BEZIER_FB) and with
+   (CBEZIER) the c_M overshoot correction */
+enum { OR_BESSER = 0, OR_DELOPAR = 1, OR_LINEAR = 2, OR_BEZIER_FB = 3, OR_CBEZIER = 4 };
 
 typedef struct {
     int nx, ny, nz;
@@ -42,7 +47,7 @@ typedef struct {
     double bcrit;             /* Hanle critical field (G): Gamma_u = |B|/bcrit */
     int n_mu, n_chi, n_nu;    /* inclinations per hemisphere, azimuths, frequencies */
     double x_max;             /* frequency grid covers [-x_max, x_max] Doppler widths */
-    int method;               /* OR_BESSER or OR_DELOPAR */
+    int method;               /* OR_BESSER, OR_DELOPAR, OR_LINEAR, OR_BEZIER_FB or OR_CBEZIER */
     /* polarized model, optional (NULL: none): dichroism multipoles per voxel,
        5 doubles (D20, Re D21, Im D21, Re D22, Im D22): eta_i = chi phi
        [delta_i0 + sum_Q (-1)^Q T^2_Q(i, Omega) D^2_-Q], i = I, Q, U */
