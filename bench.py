@@ -110,6 +110,8 @@ def args_parse():
     ap.add_argument("--batch-steps", type=int, default=3,
                     help="timed Jacobi iterations of the 256-box batch beside the default workload (0 skips them)")
     ap.add_argument("--c0", type=int, default=1, help="time the unpolarized 16x16x32 box to convergence (0 skips it)")
+    ap.add_argument("--solver-family", type=int, default=1,
+                    help="E(dtau) of the Sec. 3.4 solver family on the sigmoid benchmark (0 skips it)")
     ap.add_argument("--peak-seconds", type=float, default=1.0, help="device time per FMA-peak measurement")
     return ap.parse_args()
 
@@ -755,6 +757,28 @@ def run_cuda(args):
         c0["sqrt_eps_law"] = {"S_top_over_sqrt_eps_B": float(s[-1, 0, 0] / np.sqrt(1e-2)),
                               "column_spread": float(np.max(np.abs(s - s[:, :1, :1])))}
 
+    # the family of formal solvers of Sec. 3.4 on the one-ray sigmoid benchmark (Fig. 5):
+    # E(dtau) per method on the GPU (FP64), 200 log-spaced spacings x 4 grid shifts per call
+    family = None
+    if args.solver_family and wl.name == "pol64" and world == 1:
+        names = {P.PORTA_SC_BESSER: "BESSER", P.PORTA_SC_PARABOLIC: "parabolic", P.PORTA_SC_LINEAR: "linear",
+                 P.PORTA_SC_BEZIER_FB: "Bezier_FB", P.PORTA_SC_CBEZIER: "CBezier"}
+        show = [2.0, 1.0, 0.5, 0.1, 0.01, 0.005]
+        family = {"workload": "one ray, constant opacity, S = sigma(2,-5,z) sigma(-2,5,z) on z in [-12, 12], "
+                              "exact I at the first node; E = max relative true error (Eq. 18)",
+                  "dtau": show, "E": {}}
+        dts = np.repeat(np.logspace(np.log10(0.002), np.log10(2.0), 200), 4)
+        shifts = dts * np.tile([0.0, 0.25, 0.5, 0.75], 200)
+        for m, nm in names.items():
+            rc, e_show = P.porta_sigmoid_error(P.PORTA_FP64, m, show)
+            t0 = time.perf_counter()
+            rc2, e_all = P.porta_sigmoid_error(P.PORTA_FP64, m, dts, shifts)
+            dt_call = time.perf_counter() - t0
+            family["E"][nm] = [float(x) for x in e_show]
+            family.setdefault("call_ms", {})[nm] = dt_call * 1e3
+        family["cases_per_call"] = int(dts.size)
+        family["timing"] = "wall clock around porta_sigmoid_error (host copies and one launch, one thread per case)"
+
     # the 256 boxes of uneven size in one persistent launch per sweep (graph replays)
     batch = None
     if args.batch_steps > 0 and wl.name == "pol64" and world == 1:
@@ -830,6 +854,7 @@ def run_cuda(args):
         "accuracy": accuracy,
         "fp64_plain": fp64,
         "unpolarized_c0": c0,
+        "solver_family": family,
         "batched256": batch,
         "adjoint": adjoint,
         "multigrid": mgres,

@@ -155,6 +155,25 @@ int porta_fma_peak(int kind, double seconds, double *tflops, double *total_ms);
    dichroism). PORTA_EINVAL for non-finite inputs or non-positive eta_I, ds. */
 int porta_eval_step(int precision, int n, const double *in, double *out);
 
+/* The family of formal solvers compared on the one-ray sigmoid benchmark of
+   Sec. 3.4 (Eqs. 15-18, Fig. 5): constant opacity, z = tau, S(z) = sigma(2, -5, z)
+   sigma(-2, 5, z), uniform nodes z_i = -12 + shift + i dtau in [-12, 12], the
+   exact intensity (Eq. 17) at the first node. Methods of the upwind interval:
+   BESSER (Sec. 3.2); PARABOLIC (the parabola through M, O, P: y'_O of Eq. 6 without
+   the overshoot tests); LINEAR (psi'_M, psi'_O of Eqs. 9-10); BEZIER_FB (quadratic
+   Bezier, y'_O the Fritsch-Butland weighted harmonic mean of the one-sided slopes,
+   0 where they differ in sign); CBEZIER (BEZIER_FB with c_M outside [y_M, y_O]
+   moved to y_M). */
+enum { PORTA_SC_BESSER = 0, PORTA_SC_PARABOLIC = 1, PORTA_SC_LINEAR = 2, PORTA_SC_BEZIER_FB = 3, PORTA_SC_CBEZIER = 4 };
+
+/* E(dtau) of Eq. 18 (maximum over the nodes of |I - I_a| / I_a, I_a of Eq. 17 in
+   FP64) for ncase cases, each (method[k], dtau[k], shift[k]) one ray solved on the
+   GPU in the given precision; host arrays in and out (E: ncase). Synchronous.
+   PORTA_EINVAL for an unknown method, dtau outside [1e-4, 24] or shift outside
+   [0, dtau); PORTA_ENOMEM if the device buffers cannot be allocated. */
+int porta_sigmoid_error(int precision, int ncase, const int *method, const double *dtau, const double *shift,
+                        double *E);
+
 /* Frequency bands: the (ray, frequency) pairs of a formal solution are
    independent and J^K_Q / Lambda-bar* are sums over them (Eq. 1; the band
    parallelization of Sec. 4.3), so a formal solution can be split into bands

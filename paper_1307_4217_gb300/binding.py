@@ -18,6 +18,7 @@ PORTA_NOALLOC_SCRATCH_BYTES = 32 << 20
 PORTA_MODEL_TWOLEVEL_UNPOL, PORTA_MODEL_TWOLEVEL_HANLE = 0, 1
 PORTA_FP64, PORTA_FP32 = 0, 1
 PORTA_HOST, PORTA_DEVICE = 0, 1
+PORTA_SC_BESSER, PORTA_SC_PARABOLIC, PORTA_SC_LINEAR, PORTA_SC_BEZIER_FB, PORTA_SC_CBEZIER = 0, 1, 2, 3, 4
 
 _STATUS = {0: "PORTA_OK", -1: "PORTA_EINVAL", -2: "PORTA_ENOMEM", -3: "PORTA_ECUDA", -4: "PORTA_ESTATE",
            -5: "PORTA_ENOTCONV",
@@ -83,6 +84,7 @@ _SIGS = {
     "porta_set_freq_range": (_I, [_P, _I, _I]),
     "porta_residual": (_I, [_P, _P]),
     "porta_eval_step": (_I, [_I, _I, _P, _P]),
+    "porta_sigmoid_error": (_I, [_I, _I, _P, _P, _P, _P]),
     "porta_partial_size": (_I, [_P, _P, _P]),
     "porta_get_partial": (_I, [_P, _P, _I]),
     "porta_set_partial": (_I, [_P, _P, _I]),
@@ -304,6 +306,19 @@ def porta_eval_step(precision, cases):
     out = np.zeros((cases.shape[0], 5))
     rc = lib().porta_eval_step(int(precision), cases.shape[0], cases.ctypes.data, out.ctypes.data)
     return rc, out
+
+
+def porta_sigmoid_error(precision, method, dtau, shift=None):
+    """E(dtau) of the sigmoid benchmark (Sec. 3.4) for each case (method, dtau, shift),
+    solved on the GPU; returns (status, E)."""
+    dtau = np.ascontiguousarray(dtau, dtype=np.float64).ravel()
+    method = np.ascontiguousarray(np.broadcast_to(method, dtau.shape), dtype=np.int32)
+    shift = np.zeros_like(dtau) if shift is None else np.ascontiguousarray(np.broadcast_to(shift, dtau.shape),
+                                                                            dtype=np.float64)
+    E = np.zeros_like(dtau)
+    rc = lib().porta_sigmoid_error(int(precision), dtau.size, method.ctypes.data, dtau.ctypes.data,
+                                   shift.ctypes.data, E.ctypes.data)
+    return rc, E
 
 
 def porta_residual(h):
