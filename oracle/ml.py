@@ -244,7 +244,7 @@ def jacobi(atm, atom, pops, quad, src, n):
     return pops, change
 
 
-def vcycle(levels, atom, quad, pops, src=None, l=0, npre=2, npost=4, ncoarse=8):
+def vcycle(levels, atom, quad, pops, src=None, l=0, npre=2, npost=4, ncoarse=8, order=1):
     """One V-cycle from level l down to the coarsest (Eqs. 30-34); returns the
     new populations of level l. src None on the finest level: f = (1, 0, ...)."""
     from .mg import prolong, restrict
@@ -258,7 +258,7 @@ def vcycle(levels, atom, quad, pops, src=None, l=0, npre=2, npost=4, ncoarse=8):
     coarse = levels[l + 1]
     n_c0 = restrict(lev, pops)
     f_c = apply_A(coarse.atm, atom, n_c0, quad) + restrict(lev, r)
-    n_c = vcycle(levels, atom, quad, n_c0, f_c, l + 1, npre, npost, ncoarse)
-    pops = pops + prolong(lev, n_c - n_c0)
+    n_c = vcycle(levels, atom, quad, n_c0, f_c, l + 1, npre, npost, ncoarse, order)
+    pops = pops + prolong(lev, n_c - n_c0, order)
     pops, _ = jacobi(lev.atm, atom, pops, quad, f, npost)
     return pops

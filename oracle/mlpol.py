@@ -506,7 +506,7 @@ def jacobi(atm, atom, tab, x, quad, src, n):
     return x, change
 
 
-def vcycle(levels, atom, tab, quad, x, src=None, l=0, npre=2, npost=4, ncoarse=8):
+def vcycle(levels, atom, tab, quad, x, src=None, l=0, npre=2, npost=4, ncoarse=8, order=1):
     """One V-cycle from level l (levels from ml.hierarchy) down to the coarsest."""
     from .mg import prolong, restrict
     lev = levels[l]
@@ -519,7 +519,7 @@ def vcycle(levels, atom, tab, quad, x, src=None, l=0, npre=2, npost=4, ncoarse=8
     coarse = levels[l + 1]
     x_c0 = restrict(lev, x)
     f_c = apply_A(coarse.atm, atom, tab, x_c0, quad) + restrict(lev, r)
-    x_c = vcycle(levels, atom, tab, quad, x_c0, f_c, l + 1, npre, npost, ncoarse)
-    x = x + prolong(lev, x_c - x_c0)
+    x_c = vcycle(levels, atom, tab, quad, x_c0, f_c, l + 1, npre, npost, ncoarse, order)
+    x = x + prolong(lev, x_c - x_c0, order)
     x, _ = jacobi(lev.atm, atom, tab, x, quad, f, npost)
     return x

@@ -125,3 +125,63 @@ def test_vcycles_solve_the_fine_grid_equations(pol, nz):
     for _ in range(10):
         rho = mg.vcycle(levels, rho)
     assert _residual(fine, rho) < 1e-8      # K=0 shrinks ~5x per cycle, K=2 ~2.5x
+
+
+@pytest.mark.parametrize("nz", [17, 16])
+def test_cubic_prolongation_reproduces_cubics_in_height(nz):
+    """Tri-cubic-centered prolongation (Sec. 5.2): a field cubic in z (constant
+    horizontally) is reproduced at every fine plane, the extrapolated top one included."""
+    atm = _atm(8, 8, nz, False)
+    lev = mg.Level(atm, 0, (1, 2, 2))
+    nc = mg.coarse_nz(nz)
+    z = np.asarray(atm["z"])
+    u = (z - z.mean()) / (z.max() - z.min())
+    poly = lambda s: 0.3 - 1.2 * s + 0.7 * s ** 2 + 2.1 * s ** 3
+    c = np.broadcast_to(poly(u[0:2 * nc:2])[:, None, None, None], (nc, 4, 4, 1))
+    ref = np.broadcast_to(poly(u)[:, None, None, None], (nz, 8, 8, 1))
+    assert np.allclose(mg.prolong(lev, c, 3), ref, rtol=0, atol=1e-12)
+    # the tri-linear operator does not (the field is not linear)
+    assert np.max(np.abs(mg.prolong(lev, c, 1) - ref)) > 1e-3
+
+
+def test_cubic_prolongation_horizontal_stencil():
+    nf = 16
+    P = mg.prolong_1d_periodic_cubic(nf)
+    assert np.allclose(P.sum(1), 1.0)                          # constants are kept
+    assert np.array_equal(P[0::2], np.eye(nf // 2))           # injection at coarse nodes
+    xc = np.arange(nf // 2, dtype=np.float64)
+    xf = np.arange(nf) / 2.0
+    cub = lambda x: 1.0 + 0.5 * x - 0.25 * x ** 2 + 0.05 * x ** 3
+    got = P @ cub(xc)
+    # exact where the four coarse nodes do not wrap around the period
+    inner = [i for i in range(1, nf, 2) if 1 <= (i - 1) // 2 <= nf // 2 - 3]
+    assert np.allclose(got[inner], cub(xf[inner]), rtol=0, atol=1e-12)
+    # fourth order on a smooth periodic field: the error falls 16x per refinement
+    err = []
+    for n in (16, 32, 64):
+        xc = np.arange(n // 2) * 2 * np.pi / (n // 2)
+        xf = np.arange(n) * 2 * np.pi / n
+        err.append(np.max(np.abs(mg.prolong_1d_periodic_cubic(n) @ np.sin(xc) - np.sin(xf))))
+    assert err[0] / err[1] == pytest.approx(16.0, rel=0.1)
+    assert err[1] / err[2] == pytest.approx(16.0, rel=0.05)
+
+
+def test_nested_multigrid_and_cubic_vcycles():
+    """The nested method (Sec. 5.1) starts each level from the prolonged coarser
+    solution: one cycle per level leaves a smaller fine residual than one V-cycle from
+    S = B, and the cycles with either prolongation converge to A(rho) = f."""
+    atm = _atm(16, 16, 33, False, seed=5)
+    atm["eps"] = np.full_like(atm["eps"], 1e-2)
+    quad = (2, 4, 3)
+    levels = mg.hierarchy(atm, 0, quad, 3)
+    fine, coarsest = levels[0], levels[-1]
+    rho0 = oracle.initial_rho(fine.prob, atm)
+    r_v1 = _residual(fine, mg.vcycle(levels, rho0.copy(), order=3))
+    rho = mg.nested(levels, oracle.initial_rho(coarsest.prob, coarsest.atm), ncycles=1, order=3)
+    r_n1 = _residual(fine, rho)
+    assert r_n1 < r_v1, (r_n1, r_v1)
+    for order in (3, 1):
+        r = rho.copy()
+        for _ in range(12):
+            r = mg.vcycle(levels, r, order=order)
+        assert _residual(fine, r) < 1e-8, order
