@@ -573,12 +573,34 @@ def run_cuda(args):
                 e1.record(stream)
                 e1.synchronize()
                 cyc.append((e0.elapsed_time(e1), ch, ctx.residual()))
+            # the tri-cubic-centered prolongation, and the nested method (Sec. 5.1: the
+            # coarsest grid's problem first, each finer level from the prolonged solution)
+            ctx.mg_set_prolongation(3)
+            ctx.set_rho(wl.rho0)
+            cub = []
+            for _ in range(args.mg_cycles):
+                ctx.mg_vcycle(2, 4, 8)
+                cub.append(ctx.residual())
+            ctx.set_rho(wl.rho0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.mg_nested(1, 2, 4, 8)
+            e1.record(stream)
+            e1.synchronize()
+            nested = {"ms": e0.elapsed_time(e1), "residual": [ctx.residual()]}
+            for _ in range(args.mg_cycles - 1):
+                ctx.mg_vcycle(2, 4, 8)
+                nested["residual"].append(ctx.residual())
+            ctx.mg_set_prolongation(1)
             ctx.set_rho(wl.rho0)
             jac, jres = [], []
             for _ in range(args.mg_cycles):
                 jac.append(ctx.run_iterations(7))
                 jres.append(ctx.residual())
         mgres = {"levels": ctx.mg_levels(), "cycle": "2 pre + 4 post Jacobi, 8 on the coarsest, from S00 = B",
+                 "vcycle_cubic_residual": cub,
+                 "nested": dict(nested, note="one nested pass (8 Jacobi on 16^3, then 1 V-cycle on 32^3 and on 64^3, "
+                                             "tri-cubic prolongation), then tri-cubic V-cycles; residual after each"),
                  "vcycle_ms": [round(t, 3) for t, _, _ in cyc], "vcycle_max_change": [c for _, c, _ in cyc],
                  "residual_start": res0, "vcycle_residual": [r for _, _, r in cyc],
                  "jacobi_ms_per_7_iterations": 7 * step_ms,

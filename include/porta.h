@@ -499,9 +499,10 @@ int porta_residual(porta_ctx *c, double *rnorm);
    right-hand side A_c(R rho) + R r; the same cycle on the coarser level
    (ncoarse Jacobi iterations on the coarsest); correction rho += P (rho_c -
    R rho); npost Jacobi iterations (Sec. 5.3 uses npre = 2, npost = 4).
-   Prolongation P: tri-linear, linear in height, linear extrapolation above
-   the top coarse plane (even nz); restriction R: the transpose of P normalized
-   to keep constants (adjoint of the tri-linear prolongation, Sec. 5.2).
+   Prolongation P (porta_mg_set_prolongation): tri-linear, linear in height,
+   linear extrapolation above the top coarse plane (even nz); or
+   tri-cubic-centered; restriction R: the transpose of the tri-linear P
+   normalized to keep constants (adjoint of the tri-linear prolongation, Sec. 5.2).
    max_change (host, may be NULL): the maximum relative change of rho over the
    cycle, defined as for porta_see_update (synchronizes). All work is
    enqueued on the context's stream. Multilevel contexts: the unknowns are the
@@ -511,6 +512,32 @@ int porta_residual(porta_ctx *c, double *rnorm);
    synchronizes and reports PORTA_EKERNEL for a singular system or a
    non-positive population on any level. */
 int porta_mg_vcycle(porta_ctx *c, int npre, int npost, int ncoarse, double *max_change);
+
+/* The prolongation of the multigrid cycles (Sec. 5.2, the two operators the
+   paper names): order 1 tri-linear (the default after porta_mg_setup), order 3
+   tri-cubic-centered -- a fine node between coarse nodes of an axis takes the
+   cubic through the four nearest coarse nodes of that axis (periodic in x and
+   y with weights -1/16, 9/16, 9/16, -1/16; in height the Lagrange cubic through
+   the four coarse planes around it, the four innermost next to the bottom and
+   top, the top four above the coarse grid), a tensor product over the axes,
+   injection at coincident nodes. The cubic needs at least 4 coarse nodes per
+   axis on every level (PORTA_EINVAL otherwise, and for another order);
+   PORTA_ESTATE before porta_mg_setup. */
+int porta_mg_set_prolongation(porta_ctx *c, int order);
+
+/* Nested multigrid (Sec. 5.1, the nested method): the unknowns of every
+   coarser grid are first set to the finest grid's at the coincident nodes;
+   then ncoarse Jacobi iterations solve the coarsest grid's own problem
+   (A_c(x) = f_c, the same equations sampled on that grid); then, for each
+   finer level up to the finest, its unknowns are set to the prolongation of
+   the coarser solution and ncycles V-cycles (as porta_mg_vcycle, with that
+   level as the finest) follow. The finest grid's starting unknowns thus
+   matter only through their injection (S^0_0 = B, S^2_Q = 0, or LTE
+   populations, reproduce those of the coarsest grid). max_change (host, may
+   be NULL): as porta_mg_vcycle, over the finest level's last V-cycle.
+   PORTA_ESTATE before porta_mg_setup or without atmosphere and unknowns;
+   PORTA_EINVAL for ncycles < 1, ncoarse < 1 or negative npre, npost. */
+int porta_mg_nested(porta_ctx *c, int ncycles, int npre, int npost, int ncoarse, double *max_change);
 
 /* Multilevel atom without polarization: the non-LTE problem of the first kind
    (Sec. 1; the populations of the levels are the unknowns of Eq. 2, the

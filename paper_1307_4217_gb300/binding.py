@@ -100,6 +100,8 @@ _SIGS = {
     "porta_mg_setup": (_I, [_P, _I]),
     "porta_mg_levels": (_I, [_P, _P, _P]),
     "porta_mg_vcycle": (_I, [_P, _I, _I, _I, _P]),
+    "porta_mg_set_prolongation": (_I, [_P, _I]),
+    "porta_mg_nested": (_I, [_P, _I, _I, _I, _I, _P]),
     "porta_iterate_ckpt": (_I, [_P, _I, _I, _P]),
     "porta_iterate_vjp": (_I, [_P, _I, _P, _P, _P, _P, _P, _P, _P, _I]),
     "porta_set_tape_limit": (_I, [_P, ctypes.c_longlong]),
@@ -410,6 +412,14 @@ def porta_mg_levels(h):
 
 def porta_mg_vcycle(h, npre, npost, ncoarse, out=None):
     return lib().porta_mg_vcycle(h, npre, npost, ncoarse, ctypes.byref(out) if out is not None else None)
+
+
+def porta_mg_set_prolongation(h, order):
+    return lib().porta_mg_set_prolongation(h, int(order))
+
+
+def porta_mg_nested(h, ncycles, npre, npost, ncoarse, out=None):
+    return lib().porta_mg_nested(h, ncycles, npre, npost, ncoarse, ctypes.byref(out) if out is not None else None)
 
 
 def porta_iterate_ckpt(h, niter, ckpt, out=None):
@@ -751,6 +761,17 @@ class Context:
         """One multigrid V-cycle; returns the maximum relative change of rho (or None)."""
         out = ctypes.c_double() if residual else None
         self._check(porta_mg_vcycle(self.h, npre, npost, ncoarse, out))
+        return out.value if residual else None
+
+    def mg_set_prolongation(self, order):
+        """Prolongation of the multigrid cycles: 1 tri-linear, 3 tri-cubic-centered."""
+        self._check(porta_mg_set_prolongation(self.h, order))
+
+    def mg_nested(self, ncycles=1, npre=2, npost=4, ncoarse=8, residual=True):
+        """Nested multigrid from the coarsest grid up; returns the maximum relative change
+        over the finest level's last V-cycle (or None)."""
+        out = ctypes.c_double() if residual else None
+        self._check(porta_mg_nested(self.h, ncycles, npre, npost, ncoarse, out))
         return out.value if residual else None
 
     def set_fill(self, cluster=0, nu_group=0, fraction=0.0):

@@ -31,10 +31,11 @@ void mg_free(porta_ctx *c)
 {
     for (porta_ctx *L : c->mg) porta_destroy(L);
     c->mg.clear();
-    double *bufs[] = {c->mg_res, c->mg_src, c->mg_rho0, c->mg_prev, c->mg_zr, c->mg_zp};
+    double *bufs[] = {c->mg_res, c->mg_src, c->mg_rho0, c->mg_prev, c->mg_zr, c->mg_zp, c->mg_zp3};
     for (double *b : bufs)
         if (b) pfree(b);
-    c->mg_res = c->mg_src = c->mg_rho0 = c->mg_prev = c->mg_zr = c->mg_zp = nullptr;
+    c->mg_res = c->mg_src = c->mg_rho0 = c->mg_prev = c->mg_zr = c->mg_zp = c->mg_zp3 = nullptr;
+    c->mg_order = 1;
 }
 
 // z tables between a level with heights zf and the next coarser one (coarse
@@ -72,6 +73,44 @@ void mg_ztables(const std::vector<double> &zf, std::vector<double> &zr, std::vec
             zr[8 * K + 2 * used[K] + 1] = w;
             ++used[K];
         }
+}
+
+// the cubic prolongation in height between a level with heights zf and the next
+// coarser one: per fine plane 4 (coarse plane, weight) pairs -- the coarse plane
+// itself (weight 1) for a coincident plane, else the Lagrange cubic through the
+// four coarse planes around it (the four innermost next to the bottom and top, the
+// top four for a fine plane above the coarse grid). Needs at least 4 coarse planes.
+void mg_ztable_cubic(const std::vector<double> &zf, std::vector<double> &zp3)
+{
+    const int nf = (int)zf.size(), nc = coarse_nz(nf);
+    zp3.assign(8 * (size_t)nf, 0.0);
+    for (int k = 0; k < nf; ++k) {
+        if (k % 2 == 0) {
+            for (int a = 0; a < 4; ++a) zp3[8 * k + 2 * a] = k / 2;
+            zp3[8 * k + 1] = 1.0;
+            continue;
+        }
+        const int s = std::min(std::max((k - 1) / 2 - 1, 0), nc - 4);
+        for (int a = 0; a < 4; ++a) {
+            double w = 1.0;
+            for (int b = 0; b < 4; ++b)
+                if (b != a) w *= (zf[k] - zf[2 * (s + b)]) / (zf[2 * (s + a)] - zf[2 * (s + b)]);
+            zp3[8 * k + 2 * a] = s + a;
+            zp3[8 * k + 2 * a + 1] = w;
+        }
+    }
+}
+
+// the cubic table of the prolongation from coarse level L to F (null where L has
+// fewer than 4 nodes on an axis: the cubic is then not available)
+cudaError_t mg_cubic_table(porta_ctx *F, const porta_ctx *L)
+{
+    if (L->nx < 4 || L->ny < 4 || L->nz < 4) return cudaSuccess;
+    std::vector<double> zp3;
+    mg_ztable_cubic(F->z, zp3);
+    cudaError_t e = dalloc(&F->mg_zp3, zp3.size());
+    if (e == cudaSuccess) e = cudaMemcpy(F->mg_zp3, zp3.data(), zp3.size() * sizeof(double), cudaMemcpyHostToDevice);
+    return e;
 }
 
 // formal solution and J^K_Q / Lambda-bar* of one level, kept on the device
@@ -134,11 +173,13 @@ int mg_jacobi(porta_ctx *L, const double *src, int n)
     return PORTA_OK;
 }
 
-// One V-cycle (Eqs. 30-34) from level l of levels[0..n) down to the coarsest.
-int mg_vcycle(porta_ctx *const *levels, int n, int l, int npre, int npost, int ncoarse)
+// One V-cycle (Eqs. 30-34) from level l of levels[0..n) down to the coarsest;
+// level `top` solves its own problem (right-hand side f), the coarser ones the
+// FAS equations; order: the prolongation (1 tri-linear, 3 tri-cubic-centered).
+int mg_vcycle(porta_ctx *const *levels, int n, int l, int top, int order, int npre, int npost, int ncoarse)
 {
     porta_ctx *L = levels[l];
-    const double *src = l == 0 ? nullptr : L->mg_src;
+    const double *src = l == top ? nullptr : L->mg_src;
     if (l == n - 1) return mg_jacobi(L, src, ncoarse);
     int rc = mg_jacobi(L, src, npre);
     if (rc) return rc;
@@ -161,9 +202,10 @@ int mg_vcycle(porta_ctx *const *levels, int n, int l, int npre, int npost, int n
     if ((rc = mg_fs(C))) return fail(L, rc, std::string("mg coarse level: ") + C->err);
     e = mg_apply(C, 1.0, C->mg_src, 0, C->mg_src);
     if (e != cudaSuccess) return fail(L, PORTA_ECUDA, std::string("mg coarse rhs: ") + cudaGetErrorString(e));
-    if ((rc = mg_vcycle(levels, n, l + 1, npre, npost, ncoarse))) return fail(L, rc, C->err);
+    if ((rc = mg_vcycle(levels, n, l + 1, top, order, npre, npost, ncoarse))) return fail(L, rc, C->err);
     // coarse-grid correction x += P (x_c - R x)
-    e = run_prolong_add(L->nx, L->ny, L->nz, C->nx, C->ny, nc, L->mg_zp, mg_unk(C), C->mg_rho0, mg_unk(L), L->stream);
+    e = run_prolong(L->nx, L->ny, L->nz, C->nx, C->ny, nc, order, order == 3 ? L->mg_zp3 : L->mg_zp, mg_unk(C),
+                    C->mg_rho0, mg_unk(L), 0, L->stream);
     if (e == cudaSuccess) e = mg_rho_changed(L);
     if (e != cudaSuccess) return fail(L, PORTA_ECUDA, std::string("mg prolong: ") + cudaGetErrorString(e));
     return mg_jacobi(L, src, npost);
@@ -265,6 +307,7 @@ int porta_mg_setup(porta_ctx *c, int nlevels)
             if (e == cudaSuccess) e = dalloc(&F->mg_zp, zp.size());
             if (e == cudaSuccess) e = cudaMemcpy(F->mg_zr, zr.data(), zr.size() * sizeof(double), cudaMemcpyHostToDevice);
             if (e == cudaSuccess) e = cudaMemcpy(F->mg_zp, zp.data(), zp.size() * sizeof(double), cudaMemcpyHostToDevice);
+            if (e == cudaSuccess) e = mg_cubic_table(F, L);
             if (e != cudaSuccess) {
                 rc = fail(c, PORTA_ENOMEM, "mg_setup: allocation");
                 break;
@@ -314,6 +357,7 @@ int porta_mg_setup(porta_ctx *c, int nlevels)
         if (e == cudaSuccess) e = dalloc(&F->mg_zp, zp.size());
         if (e == cudaSuccess) e = cudaMemcpy(F->mg_zr, zr.data(), zr.size() * sizeof(double), cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(F->mg_zp, zp.data(), zp.size() * sizeof(double), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = mg_cubic_table(F, L);
         if (e != cudaSuccess) {
             rc = fail(c, PORTA_ENOMEM, "mg_setup: allocation");
             break;
@@ -388,7 +432,7 @@ int porta_mg_vcycle(porta_ctx *c, int npre, int npost, int ncoarse, double *max_
     const long long nu = mg_nunk(c);
     const int nc = mg_ncomp(c);
     CK(cudaMemcpyAsync(c->mg_prev, mg_unk(c), sizeof(double) * nu * nc, cudaMemcpyDeviceToDevice, c->stream));
-    int rc = mg_vcycle(levels.data(), (int)levels.size(), 0, npre, npost, ncoarse);
+    int rc = mg_vcycle(levels.data(), (int)levels.size(), 0, 0, c->mg_order, npre, npost, ncoarse);
     if (rc) return rc;
     c->have_fs = c->have_jkq = false;
     CK(cudaMemsetAsync(c->d_resid, 0, sizeof(unsigned long long), c->stream));
@@ -405,6 +449,87 @@ int porta_mg_vcycle(porta_ctx *c, int npre, int npost, int ncoarse, double *max_
     if (c->ml) {
         for (porta_ctx *L : levels)
             if ((rc = ml_check(L, "mg_vcycle"))) return L == c ? rc : fail(c, rc, L->err);
+    }
+    return PORTA_OK;
+}
+
+int porta_mg_set_prolongation(porta_ctx *c, int order)
+{
+    if (!c) return PORTA_EINVAL;
+    if (c->mg.empty()) return fail(c, PORTA_ESTATE, "mg_set_prolongation: call porta_mg_setup first");
+    if (order != 1 && order != 3) return fail(c, PORTA_EINVAL, "mg_set_prolongation: order 1 or 3");
+    if (order == 3) {
+        porta_ctx *F = c;
+        for (porta_ctx *L : c->mg) {
+            if (!F->mg_zp3)
+                return fail(c, PORTA_EINVAL, "mg_set_prolongation: the cubic needs 4 coarse nodes per axis on every level");
+            F = L;
+        }
+    }
+    c->mg_order = order;
+    return PORTA_OK;
+}
+
+int porta_mg_nested(porta_ctx *c, int ncycles, int npre, int npost, int ncoarse, double *max_change)
+{
+    if (!c) return PORTA_EINVAL;
+    if (c->mg.empty()) return fail(c, PORTA_ESTATE, "mg_nested: call porta_mg_setup first");
+    if (!c->have_atm || !c->have_rho) return fail(c, PORTA_ESTATE, "mg_nested: atmosphere or rho not set");
+    if (c->ml && !c->ml->have_pops) return fail(c, PORTA_ESTATE, "mg_nested: populations not set");
+    if (ncycles < 1 || npre < 0 || npost < 0 || ncoarse < 1)
+        return fail(c, PORTA_EINVAL, "mg_nested: ncycles >= 1, npre, npost >= 0, ncoarse >= 1");
+    std::vector<porta_ctx *> levels{c};
+    for (porta_ctx *L : c->mg) {
+        L->stream = c->stream;
+        levels.push_back(L);
+    }
+    const int n = (int)levels.size(), nc = mg_ncomp(c), order = c->mg_order;
+    // the starting unknowns of the coarsest grid: the finest grid's at the coincident nodes
+    cudaError_t e = cudaSuccess;
+    for (int l = 1; l < n && e == cudaSuccess; ++l) {
+        porta_ctx *F = levels[l - 1], *L = levels[l];
+        e = run_inject_vec(L->nx, L->ny, L->nz, F->nx, F->ny, nc, mg_unk(F), mg_unk(L), c->stream);
+    }
+    if (e != cudaSuccess) return fail(c, PORTA_ECUDA, std::string("mg_nested: ") + cudaGetErrorString(e));
+    porta_ctx *K = levels[n - 1];
+    if ((e = mg_rho_changed(K)) != cudaSuccess) return fail(c, PORTA_ECUDA, std::string("mg_nested: ") + cudaGetErrorString(e));
+    K->have_rho = true;
+    if (K->ml) K->ml->have_pops = true;
+    // the coarsest grid's own problem, then each finer level from the prolonged solution
+    int rc = mg_jacobi(K, nullptr, ncoarse);
+    if (rc) return fail(c, rc, std::string("mg_nested: coarsest level: ") + K->err);
+    const long long nu = mg_nunk(c);
+    for (int l = n - 2; l >= 0 && rc == PORTA_OK; --l) {
+        porta_ctx *L = levels[l], *C = levels[l + 1];
+        e = run_prolong(L->nx, L->ny, L->nz, C->nx, C->ny, nc, order, order == 3 ? L->mg_zp3 : L->mg_zp, mg_unk(C),
+                        nullptr, mg_unk(L), 1, c->stream);
+        if (e == cudaSuccess) e = mg_rho_changed(L);
+        if (e != cudaSuccess) return fail(c, PORTA_ECUDA, std::string("mg_nested: ") + cudaGetErrorString(e));
+        L->have_rho = true;
+        if (L->ml) L->ml->have_pops = true;
+        for (int k = 0; k < ncycles && rc == PORTA_OK; ++k) {
+            if (l == 0 && k == ncycles - 1)
+                CK(cudaMemcpyAsync(c->mg_prev, mg_unk(c), sizeof(double) * nu * nc, cudaMemcpyDeviceToDevice, c->stream));
+            rc = mg_vcycle(levels.data(), n, l, l, order, npre, npost, ncoarse);
+        }
+        if (rc && L != c) rc = fail(c, rc, L->err);
+    }
+    if (rc) return rc;
+    c->have_fs = c->have_jkq = false;
+    // the change over the finest level's last V-cycle
+    CK(cudaMemsetAsync(c->d_resid, 0, sizeof(unsigned long long), c->stream));
+    e = c->ml && c->ml->pol ? run_mlpol_change(c->ml->mc, c->ml->dev, nu, c->mg_prev, mg_unk(c), c->d_resid, c->stream)
+                            : run_change(nu, nc, c->mg_prev, mg_unk(c), c->d_resid, c->stream, c->ml ? 1 : 0);
+    if (e != cudaSuccess) return fail(c, PORTA_ECUDA, std::string("mg_nested: ") + cudaGetErrorString(e));
+    if (max_change) {
+        unsigned long long bits = 0;
+        CK(cudaMemcpyAsync(&bits, c->d_resid, sizeof(bits), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        std::memcpy(max_change, &bits, sizeof(double));
+    }
+    if (c->ml) {
+        for (porta_ctx *L : levels)
+            if ((rc = ml_check(L, "mg_nested"))) return L == c ? rc : fail(c, rc, L->err);
     }
     return PORTA_OK;
 }

@@ -1,15 +1,18 @@
 // Grid transfer of the non-linear multigrid method (Sec. 5): the coarse grid
 // keeps every other node on each axis (coarse (i, j, k) = fine (2i, 2j, 2k),
-// Sec. 5.1). Prolongation is tri-linear (Sec. 5.2): a fine node on a coarse
-// node takes its value, others interpolate along each axis where they fall
-// between coarse nodes (periodic in x and y, linear in the height z; above the
-// top coarse plane -- an even number of fine planes -- linear extrapolation
-// from the top two). Restriction is the transpose of the prolongation
-// normalized so that constants are kept: the adjoint of the tri-linear
-// prolongation over the 3 x 3 x (up to 4) fine nodes around a coarse node.
-// The z weights come as tables built on the host: per fine plane (k0, w0, k1,
-// w1) for the prolongation, per coarse plane up to 4 (fine plane, weight)
-// pairs for the restriction. Vectors of unknowns are [voxel][nl], FP64.
+// Sec. 5.1). Prolongation (Sec. 5.2), tri-linear or tri-cubic-centered: a fine
+// node on a coarse node takes its value, others interpolate along each axis
+// where they fall between coarse nodes -- linearly between the two neighbours,
+// or with the cubic through the four nearest coarse nodes (periodic in x and y
+// with unit spacing: -1/16, 9/16, 9/16, -1/16; in the height z with the
+// weights of a table; above the top coarse plane -- an even number of fine
+// planes -- extrapolation from the top two or four). Restriction is the
+// transpose of the tri-linear prolongation normalized so that constants are
+// kept: its adjoint over the 3 x 3 x (up to 4) fine nodes around a coarse node.
+// The z weights come as tables built on the host: per fine plane 2 (linear) or
+// 4 (cubic) (coarse plane, weight) pairs for the prolongation, per coarse plane
+// up to 4 (fine plane, weight) pairs for the restriction. Vectors of unknowns
+// are [voxel][nl], FP64.
 #include "mg_kernels.cuh"
 
 namespace porta {
@@ -65,53 +68,86 @@ __global__ void restrict_kernel(int nxc, int nyc, long long nvc, int nxf, int ny
     }
 }
 
-__global__ void prolong_add_kernel(int nxf, int nyf, long long nvf, int nxc, int nyc, int nl, const double *zp,
-                                   const double *cnew, const double *cold, double *fine)
+// one axis of the horizontal prolongation: the NP coarse nodes of fine node i and their weights
+template <int NP>
+__device__ __forceinline__ void prolong_axis(int i, int nc, int idx[NP], double w[NP])
+{
+    for (int a = 0; a < NP; ++a) {
+        idx[a] = i / 2;
+        w[a] = 0.0;
+    }
+    if (i % 2 == 0) {
+        w[0] = 1.0;
+    } else if (NP == 2) {
+        idx[0] = (i - 1) / 2;
+        idx[1] = ((i + 1) / 2) % nc;
+        w[0] = w[1] = 0.5;
+    } else {
+        // the cubic through coarse nodes left-1 .. left+2 at the midpoint of [left, left+1]
+        const double cw[4] = {-1.0 / 16.0, 9.0 / 16.0, 9.0 / 16.0, -1.0 / 16.0};
+        const int left = (i - 1) / 2;
+        for (int a = 0; a < NP && a < 4; ++a) {
+            idx[a] = ((left - 1 + a) % nc + nc) % nc;
+            w[a] = cw[a];
+        }
+    }
+}
+
+// fine (+)= P (cnew - cold); cold may be null (zero); NP = 2 tri-linear, 4 tri-cubic;
+// zp: per fine plane NP (coarse plane, weight) pairs
+template <int NP>
+__global__ void prolong_kernel(int nxf, int nyf, long long nvf, int nxc, int nyc, int nl, const double *zp,
+                               const double *cnew, const double *cold, double *fine, int assign)
 {
     long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (v >= nvf) return;
     const int i = (int)(v % nxf);
     const int j = (int)((v / nxf) % nyf);
     const int k = (int)(v / ((long long)nxf * nyf));
-    int xi[2], yj[2];
-    double wx[2], wy[2];
-    if (i % 2 == 0) {
-        xi[0] = xi[1] = i / 2;
-        wx[0] = 1.0;
-        wx[1] = 0.0;
-    } else {
-        xi[0] = (i - 1) / 2;
-        xi[1] = ((i + 1) / 2) % nxc;
-        wx[0] = wx[1] = 0.5;
+    int xi[NP], yj[NP];
+    double wx[NP], wy[NP];
+    prolong_axis<NP>(i, nxc, xi, wx);
+    prolong_axis<NP>(j, nyc, yj, wy);
+    long long kz[NP];
+    double wz[NP];
+    for (int a = 0; a < NP; ++a) {
+        kz[a] = (long long)zp[2 * NP * k + 2 * a];
+        wz[a] = zp[2 * NP * k + 2 * a + 1];
     }
-    if (j % 2 == 0) {
-        yj[0] = yj[1] = j / 2;
-        wy[0] = 1.0;
-        wy[1] = 0.0;
-    } else {
-        yj[0] = (j - 1) / 2;
-        yj[1] = ((j + 1) / 2) % nyc;
-        wy[0] = wy[1] = 0.5;
-    }
-    const long long kz[2] = {(long long)zp[4 * k], (long long)zp[4 * k + 2]};
-    const double wz[2] = {zp[4 * k + 1], zp[4 * k + 3]};
     for (int c0 = 0; c0 < nl; c0 += kMgMaxComp) {
         const int nc = min(kMgMaxComp, nl - c0);
         double d[kMgMaxComp] = {};
-        for (int a = 0; a < 2; ++a) {
+        for (int a = 0; a < NP; ++a) {
             if (wz[a] == 0.0) continue;
-            for (int b = 0; b < 2; ++b) {
+            for (int b = 0; b < NP; ++b) {
                 if (wy[b] == 0.0) continue;
-                for (int cx = 0; cx < 2; ++cx) {
+                for (int cx = 0; cx < NP; ++cx) {
                     if (wx[cx] == 0.0) continue;
                     const long long vc = (kz[a] * nyc + yj[b]) * nxc + xi[cx];
                     const double w = wz[a] * wy[b] * wx[cx];
-                    for (int c = 0; c < nc; ++c) d[c] += w * (cnew[vc * nl + c0 + c] - cold[vc * nl + c0 + c]);
+                    for (int c = 0; c < nc; ++c)
+                        d[c] += w * (cnew[vc * nl + c0 + c] - (cold ? cold[vc * nl + c0 + c] : 0.0));
                 }
             }
         }
-        for (int c = 0; c < nc; ++c) fine[v * nl + c0 + c] += d[c];
+        for (int c = 0; c < nc; ++c) {
+            double *o = fine + v * nl + c0 + c;
+            *o = assign ? d[c] : *o + d[c];
+        }
     }
+}
+
+// coarse[v_c][c] = fine[v_f][c] at the coincident node, nl components per voxel
+__global__ void inject_vec_kernel(int nxc, int nyc, long long nvc, int nxf, int nyf, int nl, const double *fine,
+                                  double *coarse)
+{
+    long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (v >= nvc) return;
+    const int i = (int)(v % nxc);
+    const int j = (int)((v / nxc) % nyc);
+    const long long k = v / ((long long)nxc * nyc);
+    const double *src = fine + (((2 * k) * nyf + 2 * j) * (long long)nxf + 2 * i) * nl;
+    for (int c = 0; c < nl; ++c) coarse[v * nl + c] = src[c];
 }
 
 // max over voxels of |dS00| / |S00_old| and |S2/S00 (new) - S2/S00 (old)|
@@ -198,11 +234,22 @@ cudaError_t run_restrict(int nxc, int nyc, int nzc, int nxf, int nyf, int nl, co
     return cudaGetLastError();
 }
 
-cudaError_t run_prolong_add(int nxf, int nyf, int nzf, int nxc, int nyc, int nl, const double *zp, const double *cnew,
-                            const double *cold, double *fine, cudaStream_t st)
+cudaError_t run_prolong(int nxf, int nyf, int nzf, int nxc, int nyc, int nl, int order, const double *zp,
+                        const double *cnew, const double *cold, double *fine, int assign, cudaStream_t st)
 {
     const long long n = (long long)nxf * nyf * nzf;
-    prolong_add_kernel<<<nblk(n, 256), 256, 0, st>>>(nxf, nyf, n, nxc, nyc, nl, zp, cnew, cold, fine);
+    if (order == 3)
+        prolong_kernel<4><<<nblk(n, 256), 256, 0, st>>>(nxf, nyf, n, nxc, nyc, nl, zp, cnew, cold, fine, assign);
+    else
+        prolong_kernel<2><<<nblk(n, 256), 256, 0, st>>>(nxf, nyf, n, nxc, nyc, nl, zp, cnew, cold, fine, assign);
+    return cudaGetLastError();
+}
+
+cudaError_t run_inject_vec(int nxc, int nyc, int nzc, int nxf, int nyf, int nl, const double *fine, double *coarse,
+                           cudaStream_t st)
+{
+    const long long n = (long long)nxc * nyc * nzc;
+    inject_vec_kernel<<<nblk(n, 256), 256, 0, st>>>(nxc, nyc, n, nxf, nyf, nl, fine, coarse);
     return cudaGetLastError();
 }
 

@@ -111,6 +111,8 @@ struct porta_ctx {
     double *mg_prev = nullptr;      // unknowns at the start of a V-cycle (finest level)
     double *mg_zr = nullptr;        // to the next coarser level: per coarse plane 4 x (fine plane, weight)
     double *mg_zp = nullptr;        // from the next coarser level: per fine plane (k0, w0, k1, w1)
+    double *mg_zp3 = nullptr;       // the same for the cubic: per fine plane 4 x (coarse plane, weight)
+    int mg_order = 1;               // prolongation: 1 tri-linear, 3 tri-cubic-centered (finest level)
     // reverse mode of the emergent sweep: tape of the forward Stokes vectors,
     // per-item partial gradients, forced launch shape (0 = automatic), last launch
     void *d_tape = nullptr;

@@ -99,3 +99,53 @@ def test_mg_setup_and_vcycle_errors():
     ctx.mg_setup(2)
     assert ctx.mg_levels() == [(6, 8, 9), (3, 4, 5)]
     ctx.mg_vcycle(1, 1, 2)
+
+
+@pytest.mark.parametrize("prec", [P.PORTA_FP64, P.PORTA_FP32])
+@pytest.mark.parametrize("pol,nz", [(False, 17), (True, 16)])
+def test_cubic_vcycle_and_nested_cycle_match_oracle(prec, pol, nz):
+    """Tri-cubic-centered prolongation (Sec. 5.2) and the nested method (Sec. 5.1)
+    against oracle/mg.py; same tolerances as the tri-linear cycle."""
+    atm = _atm(16, 16, nz, pol)
+    model = 1 if pol else 0
+    rho0 = initial_rho(atm, model)
+    levels = mg.hierarchy(atm, model, QUAD, 3)
+    tol = (1e-9, 1e-10) if prec == P.PORTA_FP64 else (1e-4, 1e-5)
+    ctx = make_ctx(atm, model, *QUAD, prec, rho=rho0)
+    ctx.mg_setup(3)
+    ctx.mg_set_prolongation(3)
+    ro = rho0.copy()
+    for _ in range(2):
+        ctx.mg_vcycle(2, 4, 8)
+        ro = mg.vcycle(levels, ro, npre=2, npost=4, ncoarse=8, order=3)
+        _cmp_rho(ctx.get_rho(), ro, *tol)
+    ctx.close()
+    # nested: from the injection of S^0_0 = B, S^2_Q = 0 on the coarsest grid
+    ctx = make_ctx(atm, model, *QUAD, prec, rho=rho0)
+    ctx.mg_setup(3)
+    ctx.mg_set_prolongation(3)
+    ctx.mg_nested(1, 2, 4, 8)
+    rc0 = initial_rho(levels[-1].atm, model)
+    rn = mg.nested(levels, rc0, ncycles=1, npre=2, npost=4, ncoarse=8, order=3)
+    _cmp_rho(ctx.get_rho(), rn, *tol)
+    ctx.close()
+
+
+def test_mg_prolongation_option_errors():
+    atm = _atm(8, 8, 17, False)
+    ctx = make_ctx(atm, 0, *QUAD, P.PORTA_FP64, rho=initial_rho(atm, 0))
+    with pytest.raises(P.PortaError) as e:
+        ctx.mg_set_prolongation(3)
+    assert e.value.code == P.PORTA_ESTATE
+    ctx.mg_setup(3)                          # 8 -> 4 -> 2: too few coarse nodes for the cubic
+    with pytest.raises(P.PortaError) as e:
+        ctx.mg_set_prolongation(3)
+    assert e.value.code == P.PORTA_EINVAL
+    with pytest.raises(P.PortaError) as e:
+        ctx.mg_set_prolongation(2)
+    assert e.value.code == P.PORTA_EINVAL
+    with pytest.raises(P.PortaError) as e:
+        ctx.mg_nested(0)
+    assert e.value.code == P.PORTA_EINVAL
+    ctx.mg_set_prolongation(1)
+    ctx.mg_nested(1, 1, 1, 2)
