@@ -63,6 +63,7 @@ class _Problem(ctypes.Structure):
         ("x_max", ctypes.c_double),
         ("method", ctypes.c_int),
         ("dich", ctypes.c_void_p),
+        ("interp", ctypes.c_int),
     ]
 
 
@@ -79,6 +80,7 @@ def _declare(L):
         "or_tkq": (None, [_D, _D, _P]),
         "or_coeffs": (None, [_D, _P]),
         "or_control_point": (_D, [_D, _D, _D, _D, _D, _I, _I]),
+        "or_interp_weights": (_I, [_P, _D, _D, _I, _P, _P, _P]),
         "or_solve_1d": (_I, [_I, _P, _P, _D, _I, _P]),
         "or_step": (_I, [_I, _P, _P, _P, _P, _P, _D, _P, _D, _D, _I, _I, _P, _P]),
         "or_hanle_solve": (_I, [_D, _D, _D, _D, _P, _P]),
@@ -137,7 +139,7 @@ class Problem:
     plus the atomic constants zeta, gbar, bcrit.
     """
 
-    def __init__(self, atm, model, n_mu, n_chi, n_nu, x_max=4.0, method=BESSER):
+    def __init__(self, atm, model, n_mu, n_chi, n_nu, x_max=4.0, method=BESSER, interp=1):
         self.model = model
         self.shape = (atm["nz"], atm["ny"], atm["nx"])
         self.nvox = int(np.prod(self.shape))
@@ -160,6 +162,8 @@ class Problem:
         d = atm.get("dich")
         self._keep["dich"] = _f64(d).ravel() if d is not None else None
         s.dich = _ptr(self._keep["dich"])
+        s.interp = int(interp)          # 1 bilinear, 2 biquadratic (Sec. 3.1)
+        self.interp = int(interp)
         self.s = s
         self.nray = 2 * n_mu * n_chi
         self.n_nu = n_nu
@@ -198,6 +202,16 @@ def coeffs(tau):
     c = np.zeros(6)
     lib().or_coeffs(float(tau), _ptr(c))
     return c
+
+
+def interp_weights(prob, xc, yc, order):
+    """nodes (i, j) and weights of the sweep's periodic interpolation stencil at cell
+    coordinates (xc, yc): order 1 bilinear, 2 biquadratic"""
+    ii = (ctypes.c_int * 9)()
+    jj = (ctypes.c_int * 9)()
+    w = (ctypes.c_double * 9)()
+    n = lib().or_interp_weights(prob.ref, float(xc), float(yc), int(order), ii, jj, w)
+    return [(ii[k], jj[k], w[k]) for k in range(n)]
 
 
 def control_point(yM, yO, yP, hM, hP, has_p=True, method=BESSER):

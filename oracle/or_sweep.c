@@ -5,8 +5,9 @@
  * the upwind point M and downwind point P of the short characteristic through
  * grid point O lie on the neighbouring horizontal planes, where the
  * transfer coefficients (emission and absorption) and the upwind Stokes
- * vector are interpolated bilinearly from the 4 surrounding nodes. The grid
- * is periodic in x and y. Bottom boundary (rays with mu > 0): I = (B, 0, 0, 0);
+ * vector are interpolated bilinearly from the 4 surrounding nodes, or
+ * biquadratically from 9 (per axis the quadratic through the nearest node and
+ * its two neighbours). The grid is periodic in x and y. Bottom boundary (rays with mu > 0): I = (B, 0, 0, 0);
  * top boundary (mu < 0): I = 0; Lambda* = 0 on the boundary plane.
  * Sec. 4.2: directions in the outer loop, frequencies in the inner loop; the
  * line profile is renormalized per direction on the frequency quadrature.
@@ -109,6 +110,35 @@ static void bilinear(const or_problem *p, double xc, double yc, int ii[4], int j
     ii[3] = ib; jj[3] = jb; w[3] = fx * fy;
 }
 
+/* biquadratic interpolation weights on a periodic plane at cell coordinates (xc, yc):
+   per axis the Lagrange quadratic through the nearest node n and n - 1, n + 1,
+   evaluated at the offset f = xc - n in [-1/2, 1/2) */
+static void biquadratic(const or_problem *p, double xc, double yc, int ii[9], int jj[9], double w[9])
+{
+    double nxn = floor(xc + 0.5), nyn = floor(yc + 0.5);
+    double fx = xc - nxn, fy = yc - nyn;
+    double wx[3] = {0.5 * fx * (fx - 1.0), (1.0 - fx) * (1.0 + fx), 0.5 * fx * (fx + 1.0)};
+    double wy[3] = {0.5 * fy * (fy - 1.0), (1.0 - fy) * (1.0 + fy), 0.5 * fy * (fy + 1.0)};
+    long i0 = (long)nxn, j0 = (long)nyn;
+    for (int b = 0; b < 3; b++)
+        for (int a = 0; a < 3; a++) {
+            int c = 3 * b + a;
+            ii[c] = (int)((((i0 + a - 1) % p->nx) + p->nx) % p->nx);
+            jj[c] = (int)((((j0 + b - 1) % p->ny) + p->ny) % p->ny);
+            w[c] = wx[a] * wy[b];
+        }
+}
+
+int or_interp_weights(const or_problem *p, double xc, double yc, int order, int *ii, int *jj, double *w)
+{
+    if (order == 2) {
+        biquadratic(p, xc, yc, ii, jj, w);
+        return 9;
+    }
+    bilinear(p, xc, yc, ii, jj, w);
+    return 4;
+}
+
 /* one (ray, frequency) sweep; I (nvox*ns) and lstar (nvox) are outputs */
 static int sweep(const or_problem *p, const double *rho, const or_ray *r, double x, double *I, double *lstar)
 {
@@ -134,14 +164,15 @@ static int sweep(const or_problem *p, const double *rho, const or_ray *r, double
         double amu = fabs(r->mu);
         double dsM = fabs(p->z[k] - p->z[ku]) / amu;
         double dsP = has_p ? fabs(p->z[kd] - p->z[k]) / amu : 0.0;
+        const int order = p->interp == 2 ? 2 : 1;
         for (int j = 0; j < ny; j++)
             for (int i = 0; i < nx; i++) {
                 long v = vox(p, i, j, k);
-                int ii[4], jj[4];
-                double w[4];
+                int ii[9], jj[9];
+                double w[9];
                 double etaM[7] = {0}, epsM[4] = {0}, IM[4] = {0};
-                bilinear(p, i - dsM * r->ox / dx, j - dsM * r->oy / dy, ii, jj, w);
-                for (int c = 0; c < 4; c++) {
+                int nc = or_interp_weights(p, i - dsM * r->ox / dx, j - dsM * r->oy / dy, order, ii, jj, w);
+                for (int c = 0; c < nc; c++) {
                     long u = vox(p, ii[c], jj[c], ku);
                     double e7[7], e4[4];
                     corner_coeffs(p, rho, u, r, x, e7, e4);
@@ -153,8 +184,8 @@ static int sweep(const or_problem *p, const double *rho, const or_ray *r, double
                 node_coeffs(p, rho, v, r, x, etaO, epsO);
                 double etaP = 0.0, epsP[4] = {0};
                 if (has_p) {
-                    bilinear(p, i + dsP * r->ox / dx, j + dsP * r->oy / dy, ii, jj, w);
-                    for (int c = 0; c < 4; c++) {
+                    nc = or_interp_weights(p, i + dsP * r->ox / dx, j + dsP * r->oy / dy, order, ii, jj, w);
+                    for (int c = 0; c < nc; c++) {
                         long u = vox(p, ii[c], jj[c], kd);
                         double e7[7], e4[4];
                         corner_coeffs(p, rho, u, r, x, e7, e4);
@@ -178,6 +209,7 @@ static int check(const or_problem *p)
     if (!p || p->nx < 1 || p->ny < 1 || p->nz < 2 || p->n_mu < 1 || p->n_chi < 1 || p->n_nu < 1) return -1;
     if (p->model != OR_MODEL_UNPOL && p->model != OR_MODEL_HANLE) return -1;
     if (p->model == OR_MODEL_HANLE && (!p->bx || !p->by || !p->bz)) return -1;
+    if (p->interp < 0 || p->interp > 2) return -1;
     return 0;
 }
 
@@ -317,6 +349,7 @@ static void node_vjp(const or_problem *p, const double *rho, long v, const or_ra
 int or_emergent_vjp(const or_problem *p, const double *rho, int ndir, const double *mu, const double *chi,
                     const double *gout, double *g_chi, double *g_e, double *g_b)
 {
+    if (p && p->interp == 2) return -1;   /* reverse mode: bilinear stencils only */
     if (check(p)) return -1;
     if (p->model != OR_MODEL_UNPOL && !g_b) return -1;
     int ns = or_ns(p->model), nn = p->n_nu;
@@ -532,6 +565,7 @@ static int reverse_sweep(const or_problem *p, const double *rho, const or_ray *r
 int or_jkq_vjp(const or_problem *p, const double *rho, const double *g_jkq, const double *g_lstar,
                double *g_chi, double *g_rho, double *g_b)
 {
+    if (p && p->interp == 2) return -1;   /* reverse mode: bilinear stencils only */
     if (check(p) || p->method != OR_BESSER) return -1;
     int ns = or_ns(p->model), nj = or_nj(p->model), nr = or_nray(p), nn = p->n_nu;
     long nv = (long)p->nx * p->ny * p->nz;
@@ -581,6 +615,7 @@ int or_jkq_vjp(const or_problem *p, const double *rho, const double *g_jkq, cons
 int or_emergent_vjp_rho(const or_problem *p, const double *rho, int ndir, const double *mu, const double *chi,
                         const double *gout, double *g_chi, double *g_rho, double *g_b)
 {
+    if (p && p->interp == 2) return -1;   /* reverse mode: bilinear stencils only */
     if (check(p)) return -1;
     int ns = or_ns(p->model), nn = p->n_nu, nl = or_nl(p->model);
     long nv = (long)p->nx * p->ny * p->nz, nxy = (long)p->nx * p->ny;

@@ -52,7 +52,15 @@ typedef struct {
        5 doubles (D20, Re D21, Im D21, Re D22, Im D22): eta_i = chi phi
        [delta_i0 + sum_Q (-1)^Q T^2_Q(i, Omega) D^2_-Q], i = I, Q, U */
     const double *dich;
+    /* interpolation at M and P (Sec. 3.1): 0 or 1 bilinear (4 nodes), 2 biquadratic
+       (9 nodes: per axis the quadratic through the nearest node and its two neighbours) */
+    int interp;
 } or_problem;
+
+/* the periodic interpolation stencil of the sweep at cell coordinates (xc, yc) of a
+   plane (node (i, j) at (i, j)): order 1 bilinear (4 nodes), 2 biquadratic (9 nodes);
+   ii, jj, w receive the nodes and weights, the return value is their number */
+int or_interp_weights(const or_problem *p, double xc, double yc, int order, int *ii, int *jj, double *w);
 
 /* number of unknowns per voxel (rho), Stokes parameters, radiation-field components */
 int or_nl(int model);
