@@ -64,6 +64,8 @@ class _Problem(ctypes.Structure):
         ("method", ctypes.c_int),
         ("dich", ctypes.c_void_p),
         ("interp", ctypes.c_int),
+        ("kexpl", ctypes.c_void_p),
+        ("sexpl", ctypes.c_void_p),
     ]
 
 
@@ -163,6 +165,12 @@ class Problem:
         self._keep["dich"] = _f64(d).ravel() if d is not None else None
         s.dich = _ptr(self._keep["dich"])
         s.interp = int(interp)          # 1 bilinear, 2 biquadratic (Sec. 3.1)
+        # explicit medium: atm["kexpl"] (6, nz, ny, nx) = (eta_Q, eta_U, eta_V, rho_Q, rho_U,
+        # rho_V) / eta_I and atm["sexpl"] (4, nz, ny, nx) = S, per voxel (polarized model)
+        for k in ("kexpl", "sexpl"):
+            v = atm.get(k)
+            self._keep[k] = _f64(v).ravel() if v is not None else None
+            setattr(s, k, _ptr(self._keep[k]))
         self.interp = int(interp)
         self.s = s
         self.nray = 2 * n_mu * n_chi

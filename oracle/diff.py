@@ -3,7 +3,7 @@ infrastructure only).
 
 The unknowns start from S^0_0 = B (Planck), S^2_Q = 0 and take `niter`
 Jacobi (ALI) iterations of the statistical-equilibrium equations (Sec. 2,
-Eq. 2; the iteration of Sec. 6 without the coarse-grid correction), each a
+Eq. 2; the smoothing iteration of Sec. 5.1 without the coarse-grid correction), each a
 formal solution (J^K_Q, Lambda-bar*) and an update; the loss is a function of
 the emergent Stokes vector of the final unknowns. Parameters per voxel: the
 line-centre opacity chi, the thermal emission term f = eps B of the

@@ -83,6 +83,14 @@ static void node_coeffs(const or_problem *p, const double *rho, long v, const or
         OR_FLOPS(1);
         return;
     }
+    if (p->kexpl) {
+        /* explicit medium: K'/eta_I and S given per voxel (a general propagation matrix) */
+        long nv = (long)p->nx * p->ny * p->nz;
+        for (int q = 1; q < 7; q++) eta[q] = etaI * p->kexpl[(q - 1) * nv + v];
+        for (int i = 0; i < 4; i++) eps[i] = etaI * p->sexpl[i * nv + v];
+        OR_FLOPS(10);
+        return;
+    }
     const double *s = rho + 6 * v;
     double bpar = p->bx[v] * r->ox + p->by[v] * r->oy + p->bz[v] * r->oz;
     eta[3] = 2.0 * p->gbar * p->zeta * xs * bpar * etaI;
@@ -349,7 +357,7 @@ static void node_vjp(const or_problem *p, const double *rho, long v, const or_ra
 int or_emergent_vjp(const or_problem *p, const double *rho, int ndir, const double *mu, const double *chi,
                     const double *gout, double *g_chi, double *g_e, double *g_b)
 {
-    if (p && p->interp == 2) return -1;   /* reverse mode: bilinear stencils only */
+    if (p && (p->interp == 2 || p->kexpl)) return -1;   /* reverse mode: bilinear, two-level media only */
     if (check(p)) return -1;
     if (p->model != OR_MODEL_UNPOL && !g_b) return -1;
     int ns = or_ns(p->model), nn = p->n_nu;
@@ -565,7 +573,7 @@ static int reverse_sweep(const or_problem *p, const double *rho, const or_ray *r
 int or_jkq_vjp(const or_problem *p, const double *rho, const double *g_jkq, const double *g_lstar,
                double *g_chi, double *g_rho, double *g_b)
 {
-    if (p && p->interp == 2) return -1;   /* reverse mode: bilinear stencils only */
+    if (p && (p->interp == 2 || p->kexpl)) return -1;   /* reverse mode: bilinear, two-level media only */
     if (check(p) || p->method != OR_BESSER) return -1;
     int ns = or_ns(p->model), nj = or_nj(p->model), nr = or_nray(p), nn = p->n_nu;
     long nv = (long)p->nx * p->ny * p->nz;
@@ -615,7 +623,7 @@ int or_jkq_vjp(const or_problem *p, const double *rho, const double *g_jkq, cons
 int or_emergent_vjp_rho(const or_problem *p, const double *rho, int ndir, const double *mu, const double *chi,
                         const double *gout, double *g_chi, double *g_rho, double *g_b)
 {
-    if (p && p->interp == 2) return -1;   /* reverse mode: bilinear stencils only */
+    if (p && (p->interp == 2 || p->kexpl)) return -1;   /* reverse mode: bilinear, two-level media only */
     if (check(p)) return -1;
     int ns = or_ns(p->model), nn = p->n_nu, nl = or_nl(p->model);
     long nv = (long)p->nx * p->ny * p->nz, nxy = (long)p->nx * p->ny;

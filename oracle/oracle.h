@@ -55,6 +55,11 @@ typedef struct {
     /* interpolation at M and P (Sec. 3.1): 0 or 1 bilinear (4 nodes), 2 biquadratic
        (9 nodes: per axis the quadratic through the nearest node and its two neighbours) */
     int interp;
+    /* explicit medium (polarized model, optional; NULL: none): per voxel the
+       propagation matrix over eta_I, (eta_Q, eta_U, eta_V, rho_Q, rho_U, rho_V)/eta_I
+       (kexpl, 6 x nvox), and the source vector (S_I, S_Q, S_U, S_V) (sexpl, 4 x nvox),
+       both independent of direction and frequency; eta_I = chi phi(x - s) */
+    const double *kexpl, *sexpl;
 } or_problem;
 
 /* the periodic interpolation stencil of the sweep at cell coordinates (xc, yc) of a
