@@ -155,6 +155,36 @@ int porta_fma_peak(int kind, double seconds, double *tflops, double *total_ms);
    dichroism). PORTA_EINVAL for non-finite inputs or non-positive eta_I, ds. */
 int porta_eval_step(int precision, int n, const double *in, double *out);
 
+/* An explicit medium for the emergent Stokes profiles (porta_emergent_stokes):
+   the propagation matrix of Eqs. 7-8 with all seven elements, given per voxel as
+   kexpl[k][v] = (eta_Q, eta_U, eta_V, rho_Q, rho_U, rho_V)[k] / eta_I (k = 0..5)
+   and the source vector sexpl[i][v] = S_i (i = I, Q, U, V), both independent of
+   direction and frequency; eta_I = chi phi(x - v mu) from the atmosphere. The
+   emergent sweep then interpolates eta_I (1, K'/eta_I) and eta_I S bilinearly at M
+   and P and takes the BESSER-DELO step with kappa^-1 = 1 + psi'_O K'_O solved in full
+   (the general step of porta_eval_step). Arrays of nvox doubles each, host or
+   device (where); the library keeps a copy. NULL for either clears the medium
+   (the two-level physics of the unknowns again). Polarized two-level single-box
+   contexts with bilinear interpolation only (PORTA_EINVAL otherwise); while an
+   explicit medium is set, the J^K_Q formal solution and the reverse-mode calls
+   return PORTA_EINVAL. */
+int porta_set_explicit_medium(porta_ctx *c, const double *kexpl, const double *sexpl, int where);
+
+/* Interpolation of the transfer coefficients and of the upwind Stokes vector at
+   the points M and P (Sec. 3.1, where both are offered): order 1 bilinear from
+   the 4 surrounding nodes (the default), order 2 biquadratic from the 9 nodes
+   around the nearest one (per horizontal axis the quadratic through the
+   nearest node and its two neighbours; periodic). The biquadratic stencils run
+   in the general sweep, whose strips then need at least two rows per CTA
+   (cluster sizes up to ny/2); they can overshoot where the atmosphere changes
+   abruptly (no clamping, as in the oracle). Changing the order returns the
+   launch shape to porta_opts' choice (an autotuned shape is dropped) and
+   drops any captured iteration graph. PORTA_EINVAL for another order, for order 2 on a
+   multilevel context (its lines carry dichroism, which the biquadratic sweep
+   has not) or with ny < 2. The reverse-mode calls (porta_emergent_vjp,
+   porta_iterate_vjp) accept bilinear interpolation only. */
+int porta_set_interpolation(porta_ctx *c, int order);
+
 /* The family of formal solvers compared on the one-ray sigmoid benchmark of
    Sec. 3.4 (Eqs. 15-18, Fig. 5): constant opacity, z = tau, S(z) = sigma(2, -5, z)
    sigma(-2, 5, z), uniform nodes z_i = -12 + shift + i dtau in [-12, 12], the

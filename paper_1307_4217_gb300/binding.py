@@ -85,6 +85,8 @@ _SIGS = {
     "porta_residual": (_I, [_P, _P]),
     "porta_eval_step": (_I, [_I, _I, _P, _P]),
     "porta_sigmoid_error": (_I, [_I, _I, _P, _P, _P, _P]),
+    "porta_set_interpolation": (_I, [_P, _I]),
+    "porta_set_explicit_medium": (_I, [_P, _P, _P, _I]),
     "porta_partial_size": (_I, [_P, _P, _P]),
     "porta_get_partial": (_I, [_P, _P, _I]),
     "porta_set_partial": (_I, [_P, _P, _I]),
@@ -321,6 +323,14 @@ def porta_sigmoid_error(precision, method, dtau, shift=None):
     rc = lib().porta_sigmoid_error(int(precision), dtau.size, method.ctypes.data, dtau.ctypes.data,
                                    shift.ctypes.data, E.ctypes.data)
     return rc, E
+
+
+def porta_set_interpolation(h, order):
+    return lib().porta_set_interpolation(h, int(order))
+
+
+def porta_set_explicit_medium(h, kexpl_ptr, sexpl_ptr, where):
+    return lib().porta_set_explicit_medium(h, kexpl_ptr, sexpl_ptr, where)
 
 
 def porta_residual(h):
@@ -762,6 +772,21 @@ class Context:
         out = ctypes.c_double() if residual else None
         self._check(porta_mg_vcycle(self.h, npre, npost, ncoarse, out))
         return out.value if residual else None
+
+    def set_explicit_medium(self, kexpl=None, sexpl=None):
+        """Explicit medium for the emergent profiles: kexpl (6, nz, ny, nx) =
+        (eta_Q, eta_U, eta_V, rho_Q, rho_U, rho_V) / eta_I and sexpl (4, nz, ny, nx) = S
+        (host arrays); None clears it."""
+        if kexpl is None or sexpl is None:
+            self._check(porta_set_explicit_medium(self.h, None, None, PORTA_HOST))
+            return
+        k = np.ascontiguousarray(kexpl, dtype=np.float64)
+        s = np.ascontiguousarray(sexpl, dtype=np.float64)
+        self._check(porta_set_explicit_medium(self.h, k.ctypes.data, s.ctypes.data, PORTA_HOST))
+
+    def set_interpolation(self, order):
+        """Interpolation at M and P: 1 bilinear, 2 biquadratic (Sec. 3.1)."""
+        self._check(porta_set_interpolation(self.h, order))
 
     def mg_set_prolongation(self, order):
         """Prolongation of the multigrid cycles: 1 tri-linear, 3 tri-cubic-centered."""

@@ -150,7 +150,8 @@ int nl_of(int model) { return model == PORTA_MODEL_TWOLEVEL_UNPOL ? 1 : 6; }
 // node coefficients in shared memory) unless the lines carry dichroism, which
 // only the general sweep (sweep.cu) implements, or a plane is too wide for its
 // shared memory (then the general sweep, which needs less per frequency, runs).
-bool use_jk(const porta_ctx *c) { return c->d_dich == nullptr && c->jk_fits; }
+// (and the biquadratic stencils, which only the general sweep has)
+bool use_jk(const porta_ctx *c) { return c->d_dich == nullptr && c->jk_fits && c->interp != 2; }
 
 // The J^K_Q sweep sums an FP32 formal solution into fixed-point accumulators;
 // an FP64 one keeps per-ray partial integrals summed in ray order in FP64 (a
@@ -160,6 +161,13 @@ bool jfixed(const porta_ctx *c) { return use_jk(c) && c->precision == PORTA_FP32
 
 // frequencies of the J^K_Q formal solution (its band, porta_set_freq_range)
 int jnu(const porta_ctx *c) { return c->fr1 > c->fr0 ? c->fr1 - c->fr0 : c->n_nu; }
+
+int min_ny(const porta_ctx *c)
+{
+    int m = 1 << 30;
+    for (const BoxDev &b : c->boxes) m = std::min(m, b.ny);
+    return m;
+}
 
 int max_ny(const porta_ctx *c)
 {
@@ -333,6 +341,7 @@ cudaError_t sweep_jkq(porta_ctx *c, SweepArgs<Real> a, LaunchCfg cfg, const int 
 template <typename Real>
 int formal_solve_t(porta_ctx *c, int probe_ray, Real *probe, Real *probe_ls)
 {
+    if (c->d_kexpl) return fail(c, PORTA_EINVAL, "formal solution: an explicit medium has emergent profiles only");
     SweepArgs<Real> a = jkq_args<Real>(c);
     a.probe_ray = probe_ray;
     a.probe = probe;
@@ -526,7 +535,7 @@ void free_all(porta_ctx *c)
         if (ev) cudaEventDestroy(ev);
     void *ptrs[] = {c->d_atm, c->d_eps, c->d_bpl, c->d_b, c->d_rho, c->d_rhoR, c->d_invn, c->d_geom, c->d_rays,
                     c->d_freq, c->d_part, c->d_tw, c->d_jkq, c->d_lstar, c->d_resid, c->d_err, c->d_boxes,
-                    c->d_items, c->d_tune_items, c->d_tape, c->d_gpart, c->d_jacc, c->d_jexp};
+                    c->d_items, c->d_tune_items, c->d_tape, c->d_gpart, c->d_jacc, c->d_jexp, c->d_kexpl, c->d_sexpl};
     for (void *p : ptrs)
         if (p) pfree(p);
 }
@@ -617,8 +626,8 @@ int create_impl(int nbox, const porta_grid *grids, const porta_atom *at, const p
     c->n_mu = q->n_mu; c->n_chi = q->n_chi; c->n_nu = q->n_nu; c->x_max = q->x_max;
     c->precision = prec;
     c->user_shape = o && (o->cluster > 0 || o->nu_group > 0);
-    c->opt_cluster = o ? o->cluster : 0;
-    c->opt_nu_group = o ? o->nu_group : 0;
+    c->opt_cluster = c->user_cluster = o ? o->cluster : 0;
+    c->opt_nu_group = c->user_nu_group = o ? o->nu_group : 0;
     c->nvox = nvox;
     c->nray = 2 * q->n_mu * q->n_chi;
     c->nbox = nbox;
@@ -1297,4 +1306,50 @@ int porta_launch_info(const porta_ctx *c, int *clusters, int *cluster_size, int 
     if (smem_bytes) *smem_bytes = c->last.smem;
     return PORTA_OK;
 }
+int porta_set_explicit_medium(porta_ctx *c, const double *kexpl, const double *sexpl, int where)
+{
+    if (!c) return PORTA_EINVAL;
+    if (!kexpl || !sexpl) {
+        if (c->d_kexpl) pfree(c->d_kexpl);
+        if (c->d_sexpl) pfree(c->d_sexpl);
+        c->d_kexpl = c->d_sexpl = nullptr;
+        c->emg_tuned.clear();
+        return PORTA_OK;
+    }
+    if (c->ns != 4 || c->ml || c->d_dich || c->nbox != 1)
+        return fail(c, PORTA_EINVAL, "set_explicit_medium: polarized two-level single-box contexts only");
+    if (c->interp == 2) return fail(c, PORTA_EINVAL, "set_explicit_medium: bilinear interpolation only");
+    if (where != PORTA_HOST && where != PORTA_DEVICE) return fail(c, PORTA_EINVAL, "set_explicit_medium: where");
+    if (where == PORTA_HOST && (!finite_host(kexpl, 6 * c->nvox) || !finite_host(sexpl, 4 * c->nvox)))
+        return fail(c, PORTA_EINVAL, "set_explicit_medium: non-finite values");
+    if (!c->d_kexpl) CK(dalloc(&c->d_kexpl, 6 * (size_t)c->nvox));
+    if (!c->d_sexpl) CK(dalloc(&c->d_sexpl, 4 * (size_t)c->nvox));
+    int rc = copy_in(c, c->d_kexpl, kexpl, 6 * c->nvox, where);
+    if (rc == PORTA_OK) rc = copy_in(c, c->d_sexpl, sexpl, 4 * c->nvox, where);
+    if (rc == PORTA_OK) CK(cudaStreamSynchronize(c->stream));
+    c->emg_tuned.clear();
+    return rc;
+}
+
+int porta_set_interpolation(porta_ctx *c, int order)
+{
+    if (!c) return PORTA_EINVAL;
+    if (order != 1 && order != 2) return fail(c, PORTA_EINVAL, "set_interpolation: order 1 (bilinear) or 2 (biquadratic)");
+    if (order == 2 && (c->ml || c->d_dich))
+        return fail(c, PORTA_EINVAL, "set_interpolation: the biquadratic stencils have no dichroism (multilevel lines)");
+    if (order == 2 && min_ny(c) < 2) return fail(c, PORTA_EINVAL, "set_interpolation: biquadratic needs ny >= 2");
+    if (order == 2 && c->d_kexpl) return fail(c, PORTA_EINVAL, "set_interpolation: explicit media are bilinear");
+    if (order == c->interp) return PORTA_OK;
+    c->interp = order;
+    // an autotuned shape of the other stencil need not fit: back to porta_opts' choice
+    c->opt_cluster = c->user_cluster;
+    c->opt_nu_group = c->user_nu_group;
+    c->fill_cfg = LaunchCfg{};
+    c->fill_frac = 0.0;
+    c->emg_tuned.clear();
+    c->have_fs = c->have_jkq = false;
+    drop_graph(c);
+    return PORTA_OK;
+}
+
 }  // extern "C"

@@ -644,6 +644,8 @@ int porta_emergent_stokes(porta_ctx *c, int ndir, const double *mu, const double
 int porta_emergent_vjp(porta_ctx *c, int ndir, const double *mu, const double *chi, const double *grad_out,
                        double *out, double *g_chi, double *g_e, double *g_b, int where)
 {
+    if (c && (c->interp == 2 || c->d_kexpl))
+        return fail(c, PORTA_EINVAL, "reverse mode: bilinear interpolation and the two-level media only");
     if (!c) return PORTA_EINVAL;
     if (ndir < 1 || !mu || !chi || !grad_out || !g_chi || !g_e || (c->ns > 1 && !g_b) ||
         (where != PORTA_HOST && where != PORTA_DEVICE))
@@ -746,6 +748,8 @@ int porta_set_tape_limit(porta_ctx *c, long long bytes)
 int porta_iterate_vjp(porta_ctx *c, int ndir, const double *mu, const double *chi, const double *grad_out, double *out,
                       double *g_chi, double *g_f, double *g_b, int where)
 {
+    if (c && (c->interp == 2 || c->d_kexpl))
+        return fail(c, PORTA_EINVAL, "reverse mode: bilinear interpolation and the two-level media only");
     if (!c) return PORTA_EINVAL;
     if (ndir < 1 || !mu || !chi || !grad_out || !g_chi || !g_f || (c->ns > 1 && !g_b) ||
         (where != PORTA_HOST && where != PORTA_DEVICE))

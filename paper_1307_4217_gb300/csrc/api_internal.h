@@ -144,9 +144,13 @@ void launch_caps(const porta_ctx *c, int C, int &ring_plane, int &ipts_max, bool
             ipts_max = std::max(ipts_max, rmax * b.nx);
             continue;
         }
-        // with dichroism the slots of a second ring (eta_U / eta_I per node) follow the node ring
-        const int dchunks = dich ? (chunk * (int)sizeof(Real) + 15) / 16 : 0;
-        ring_plane = std::max(ring_plane, nch * chunk + dchunks);
+        // with dichroism the slots of a second ring (eta_U / eta_I per node) follow the node ring;
+        // the biquadratic stencils need two halo rows on each side instead of one
+        const int gchunk = c->interp == 2 && !c->d_kexpl ? (rmax + 4) * b.nx : chunk;
+        // an explicit medium keeps K'/eta_I (6 words per node) in the second ring
+        const int dchunks = dich ? (chunk * (int)sizeof(Real) + 15) / 16
+                                 : (c->d_kexpl ? (6 * ((chunk * (int)sizeof(Real) + 15) / 16 * 16) + 15) / 16 : 0);
+        ring_plane = std::max(ring_plane, nch * gchunk + dchunks);
         ipts_max = std::max(ipts_max, rmax * b.nx);
     }
 }
@@ -166,8 +170,9 @@ bool jfixed(const porta_ctx *c);
 // frequencies of the J^K_Q formal solution (its band, porta_set_freq_range)
 int jnu(const porta_ctx *c);
 
-// largest plane height ny over the context's boxes
+// largest / smallest plane height ny over the context's boxes
 int max_ny(const porta_ctx *c);
+int min_ny(const porta_ctx *c);
 
 // Launch shape of the sweep: cluster size C (CTAs sharing one ray's plane)
 // and frequencies per pass F. Estimated time of a candidate (in units of one
@@ -188,6 +193,8 @@ int choose_launch(porta_ctx *c, LaunchCfg &best, int force_c, int force_f, int n
         if (force_c > 0 && C != force_c) continue;
         if (force_c <= 0 && C > 1 && (C & (C - 1)) != 0 && C != 6 && C != 12) continue;   // heuristic set
         if (C > ny_max) continue;
+        // biquadratic stencils reach two rows into the next strip: every CTA needs two rows
+        if (c->interp == 2 && !c->d_kexpl && !jk && min_ny(c) / C < 2) continue;
         int ring_plane, ipts_max;
         launch_caps<Real, NS>(c, C, ring_plane, ipts_max, jk);
         int fmax = 0;
@@ -217,7 +224,9 @@ int choose_launch(porta_ctx *c, LaunchCfg &best, int force_c, int force_f, int n
         if (smem > kSmemLimit + 16) continue;
         int act = 0;
         if ((jk ? jsweep_max_active_clusters<Real, NS>(C, smem, threads, &act)
-                : max_active_clusters<Real, NS>(C, smem, threads, &act, c->d_dich != nullptr)) != cudaSuccess) {
+                : max_active_clusters<Real, NS>(C, smem, threads, &act, c->d_dich != nullptr,
+                                                c->interp == 2 && !c->d_kexpl, c->d_kexpl != nullptr)) !=
+            cudaSuccess) {
             cudaGetLastError();
             continue;
         }
@@ -268,6 +277,9 @@ SweepArgs<Real> base_args(porta_ctx *c)
     a.xf = (const Real *)c->d_freq;
     a.wf = (const Real *)c->d_freq + c->n_nu;
     a.probe_ray = -1;
+    a.interp = c->interp;
+    a.kexpl = c->d_kexpl;
+    a.sexpl = c->d_sexpl;
     return a;
 }
 

@@ -52,6 +52,7 @@ struct porta_ctx {
     int fr0 = 0, fr1 = 0;               // frequency band [fr0, fr1) of the J^K_Q formal solution (fr1 = 0: all)
     bool jkq_loaded = false;            // J^K_Q / Lambda-bar* set by porta_set_partial (not from this context's sweep)
     int opt_cluster = 0, opt_nu_group = 0;
+    int user_cluster = 0, user_nu_group = 0;     // as given in porta_opts (0: automatic)
     bool user_shape = false;            // launch shape given in porta_opts (not autotuned)
     std::map<int, porta::LaunchCfg> emg_tuned;   // emergent sweep: shape timed once per direction count
     long long nvox = 0;
@@ -113,6 +114,9 @@ struct porta_ctx {
     double *mg_zp = nullptr;        // from the next coarser level: per fine plane (k0, w0, k1, w1)
     double *mg_zp3 = nullptr;       // the same for the cubic: per fine plane 4 x (coarse plane, weight)
     int mg_order = 1;               // prolongation: 1 tri-linear, 3 tri-cubic-centered (finest level)
+    int interp = 1;                 // interpolation at M and P: 1 bilinear, 2 biquadratic (general sweep)
+    double *d_kexpl = nullptr;      // explicit medium: K'/eta_I [6][nvox] and S [4][nvox] (emergent sweep)
+    double *d_sexpl = nullptr;
     // reverse mode of the emergent sweep: tape of the forward Stokes vectors,
     // per-item partial gradients, forced launch shape (0 = automatic), last launch
     void *d_tape = nullptr;

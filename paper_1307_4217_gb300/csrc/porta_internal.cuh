@@ -52,6 +52,9 @@ struct SweepArgs {
     int ring_plane;      // shared-memory ring plane capacity (16-byte chunks), max over boxes
     int ipts_max;        // Stokes-plane capacity (points), max over boxes
     int cstride, istride;  // J^K_Q sweep: Reals per (slot, frequency) coefficient plane and per (buffer, frequency) Stokes plane
+    int interp;            // general sweep: 2 biquadratic interpolation at M and P, else bilinear
+    // explicit medium (emergent general sweep, NS = 4): K'/eta_I [6][nvox] and S [4][nvox], FP64
+    const double *kexpl, *sexpl;
     Real bfac;           // 2 * gbar * zeta (weak-field Zeeman, eta_V / (eta_I x B.Omega))
     const PlaneGeom<Real> *geom;   // per box: [ray][nz]
     const RayDev<Real> *rays;      // [ray]
@@ -103,7 +106,8 @@ template <typename Real, int NS>
 int sweep_smem_bytes(int ring_plane, int ipts_max, int F, int threads);
 
 template <typename Real, int NS>
-cudaError_t max_active_clusters(int cluster, int smem, int threads, int *out, bool dich = false);
+cudaError_t max_active_clusters(int cluster, int smem, int threads, int *out, bool dich = false, bool bq = false,
+                                bool gk = false);
 
 // the J^K_Q formal solution (sweep_j.cu): per-frequency node coefficients in
 // shared memory; ring capacity `nodes` per slot, Stokes planes of `ipts` points.

@@ -61,7 +61,20 @@ __device__ __forceinline__ void accumulate_partial(const SweepArgs<Real> &a, int
     }
 }
 
-template <typename Real, int NS, int MODE, bool DI>
+// Lagrange weights at offset f of the quadratic through nodes -1, 0, 1
+template <typename Real>
+__device__ __forceinline__ void quad3(Real f, Real w[3])
+{
+    w[0] = Real(0.5) * f * (f - Real(1));
+    w[1] = (Real(1) - f) * (Real(1) + f);
+    w[2] = Real(0.5) * f * (f + Real(1));
+}
+
+// BQ: biquadratic (9-point) interpolation at M and P instead of bilinear (Sec. 3.1);
+// the ring then keeps two halo rows on each side of the strip
+// GK: an explicit medium (a general propagation matrix, per voxel K'/eta_I and S
+// independent of direction and frequency; emergent mode, NS = 4, bilinear)
+template <typename Real, int NS, int MODE, bool DI, bool BQ, bool GK>
 __device__ __forceinline__ void sweep_item(const SweepArgs<Real> &a, cg::cluster_group &cluster,
                                            typename V16<Real>::T *ring, Real *ibuf, Real *lane_buf, int box, int m,
                                            int g, int rank, int C, int dir_out)
@@ -79,6 +92,15 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<Real> &a, cg::cluster
     const int next_row = (row0 + R) % ny;
     const int next_owner = (int)(((long long)(next_row + 1) * C + ny - 1) / ny) - 1;
     const Real *ibuf_next = cluster.map_shared_rank(ibuf, next_owner);
+    // the sheared row before this strip (biquadratic stencils reach it): the last row
+    // of the CTA that owns it
+    const int prev_row = (row0 + ny - 1) % ny;
+    const int prev_owner = (int)(((long long)(prev_row + 1) * C + ny - 1) / ny) - 1;
+    const int prev_local = prev_row - (int)(((long long)prev_owner * ny) / C);
+    const Real *ibuf_prev = cluster.map_shared_rank(ibuf, prev_owner);
+    static_assert(!(BQ && DI), "the biquadratic variant has no dichroism");
+    static_assert(!GK || (NS == 4 && !DI && !BQ && MODE == MODE_EMERGENT), "explicit media: emergent, bilinear");
+    constexpr int H = BQ ? 2 : 1;                   // halo rows of the ring on each side
     const int j0 = g * F;
     const int nf = min(F, a.nnu - j0);
     const PlaneGeom<Real> *G = a.geom + B.geom0 + (long long)m * nz;
@@ -88,7 +110,7 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<Real> &a, cg::cluster
     const bool jmode = (MODE == MODE_JKQ);
     const int tid = threadIdx.x, nt = blockDim.x;
     constexpr int NCH = node_words<NS>() * (int)sizeof(Real) / 16;
-    const int chunk = (rmax + 2) * nx;              // ring chunk-plane stride (16-byte chunks)
+    const int chunk = (rmax + 2 * H) * nx;          // ring chunk-plane stride (16-byte chunks)
     const int plane = NCH * chunk;                  // ring plane stride
     // dichroism (polarized lines whose levels carry alignment): the node's opacity,
     // source terms and Zeeman factor are rescaled by eta_I / (chi phi) = 1 + d_I(Omega);
@@ -115,18 +137,34 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<Real> &a, cg::cluster
 
     auto fill = [&](int q) {
         const PlaneGeom<Real> gq = G[q];
-        const int nn = (R + 2) * nx;
+        const int nn = (R + 2 * H) * nx;
         const long long kbase = (long long)gq.kz * ny;
         int lr = tid / nx, c = tid - (tid / nx) * nx;      // lr = ring row (local row + 1)
         for (int idx = tid; idx < nn; idx += nt) {
             int pi = c + gq.ax;
             pi -= pi >= nx ? nx : 0;
-            int pj = row0 + lr - 1 + gq.ay;                  // in [-1, 2 ny]
-            pj += pj < 0 ? ny : 0;
-            pj -= pj >= ny ? ny : 0;
-            pj -= pj >= ny ? ny : 0;
+            int pj = row0 + lr - H + gq.ay;                  // in [-H, 2 ny + H)
+            if constexpr (BQ) {
+                pj = ((pj % ny) + ny) % ny;
+            } else {
+                pj += pj < 0 ? ny : 0;
+                pj -= pj >= ny ? ny : 0;
+                pj -= pj >= ny ? ny : 0;
+            }
             const long long v = B.vox0 + (kbase + pj) * nx + pi;
             Node<Real, NS> n = make_node<Real, NS>(a, ray, v, m, jmode);
+            if constexpr (GK) {
+                // the node's S (S_V in the S^0_0 word) and its K'/eta_I in the second ring
+                const long long nv = a.nvox;
+                n.SI = (Real)a.sexpl[v];
+                n.SQ = (Real)a.sexpl[nv + v];
+                n.SU = (Real)a.sexpl[2 * nv + v];
+                n.S00 = (Real)a.sexpl[3 * nv + v];
+                n.b = Real(0);
+                Real *gk = dring + (q % 3) * 6 * dstride + idx;
+#pragma unroll
+                for (int k = 0; k < 6; ++k) gk[k * dstride] = (Real)a.kexpl[k * nv + v];
+            }
             if constexpr (NS == 4) {
                 if constexpr (dich) {
                     const long long nv = a.nvox;
@@ -189,7 +227,7 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<Real> &a, cg::cluster
             pj -= pj >= ny ? ny : 0;
             const long long vloc = ((long long)gq.kz * ny + pj) * nx + pi;
             const long long v = B.vox0 + vloc;
-            const Node<Real, NS> nO = ring_load<Real, NS>(ring, plane, chunk, sO, (l + 1) * nx + c);
+            const Node<Real, NS> nO = ring_load<Real, NS>(ring, plane, chunk, sO, (l + H) * nx + c);
             // profile normalization at O (in the ring, except for the dichroism variant)
             Real invnO = nO.invn;
             if constexpr (dich) invnO = jmode ? a.invn[(long long)m * a.nvox + v] : Real(1);
@@ -251,15 +289,61 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<Real> &a, cg::cluster
                 const int ilo = l * nx;                               // row l in this CTA
                 const Real *ihi_base = last_row ? irn : ir;          // row l+1 (next CTA's row 0)
                 const int ihi = last_row ? 0 : (l + 1) * nx;
+                // biquadratic stencils: per axis the quadratic through the nearest node and
+                // its two neighbours; M at (c + t_x, l + t_y) on plane q-1, P at
+                // (c - t'_x, l - t'_y) on plane q+1 (sheared frame). Upwind Stokes rows
+                // before the strip are the previous CTA's, after it the next CTA's.
+                int bqM[9], bqP[9], bqI[3], bqC[3];
+                Real bwM[9], bwP[9];
+                const Real *bqB[3];
+                if constexpr (BQ) {
+                    const int oxm = gq.tx >= Real(0.5) ? 1 : 0, oym = gq.ty >= Real(0.5) ? 1 : 0;
+                    const int oxp = gp.tx > Real(0.5) ? -1 : 0, oyp = gp.ty > Real(0.5) ? -1 : 0;
+                    Real qxm[3], qym[3], qxp[3], qyp[3];
+                    quad3<Real>(gq.tx - Real(oxm), qxm);
+                    quad3<Real>(gq.ty - Real(oym), qym);
+                    quad3<Real>(-gp.tx - Real(oxp), qxp);
+                    quad3<Real>(-gp.ty - Real(oyp), qyp);
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        const int cmx = ((c + oxm - 1 + a) % nx + nx) % nx, cpx = ((c + oxp - 1 + a) % nx + nx) % nx;
+                        bqC[a] = cmx;
+#pragma unroll
+                        for (int b = 0; b < 3; ++b) {
+                            bqM[3 * b + a] = (l + oym - 1 + b + H) * nx + cmx;
+                            bwM[3 * b + a] = qxm[a] * qym[b];
+                            bqP[3 * b + a] = (l + oyp - 1 + b + H) * nx + cpx;
+                            bwP[3 * b + a] = qxp[a] * qyp[b];
+                        }
+                    }
+#pragma unroll
+                    for (int b = 0; b < 3; ++b) {
+                        const int r = l + oym - 1 + b;                     // in [-1, R + 1]
+                        bqB[b] = r < 0 ? ibuf_prev + ro : (r >= R ? irn : ir);
+                        bqI[b] = (r < 0 ? prev_local : (r >= R ? r - R : r)) * nx;
+                    }
+                }
 
                 for (int f = lane; f < nf; f += L) {
                     const int j = j0 + f;
                     const Real x = a.xf[j];
                     const Real *pl = ir + f * iplane;
                     const Real *ph = ihi_base + f * iplane;
-                    // a3: upwind Stokes vector (bilinear)
+                    // a3: upwind Stokes vector (bilinear or biquadratic)
                     Real IM[NS];
-                    {
+                    if constexpr (BQ) {
+#pragma unroll
+                        for (int s = 0; s < NS; ++s) IM[s] = Real(0);
+#pragma unroll
+                        for (int b = 0; b < 3; ++b)
+#pragma unroll
+                            for (int a2 = 0; a2 < 3; ++a2) {
+                                Real t[NS];
+                                StokesIO<Real, NS>::load(bqB[b] + f * iplane, ichunk, bqI[b] + bqC[a2], t);
+#pragma unroll
+                                for (int s = 0; s < NS; ++s) IM[s] += bwM[3 * b + a2] * t[s];
+                            }
+                    } else {
                         Real t0[NS], t1[NS], t2[NS], t3[NS];
                         StokesIO<Real, NS>::load(pl, ichunk, ilo + c, t0);
                         StokesIO<Real, NS>::load(pl, ichunk, ilo + c1, t1);
@@ -268,126 +352,176 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<Real> &a, cg::cluster
 #pragma unroll
                         for (int s = 0; s < NS; ++s) IM[s] = wI[0] * t0[s] + wI[1] * t1[s] + wI[2] * t2[s] + wI[3] * t3[s];
                     }
-                    // a2-a3: node transfer coefficients and bilinear interpolation at M and P
-                    Real etaM = 0, etaVM = 0, etaQM = 0, etaUM = 0, epsM[NS];
+                    Real IO[NS];
+                    Coef<Real> co{};                          // (used by the J^K_Q sums below)
+                    Real phO = Real(0);
+                    if constexpr (GK) {
+                        // explicit medium: eta = eta_I (1, K'/eta_I) and eps = eta_I S at the nodes, interpolated
+                        // at M and P; the BESSER-DELO step with the full kappa^-1 = 1 + psi'_O K'_O (Eqs. 7-8)
+                        Real etaM7[7], epsM4[4], etaO7[7], epsO4[4], epsP4[4], etaPI = 0;
 #pragma unroll
-                    for (int s = 0; s < NS; ++s) epsM[s] = 0;
+                        for (int q = 0; q < 7; ++q) etaM7[q] = Real(0);
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        const CornerM<Real, NS> km = corner_m<Real, NS>(ring_load<Real, NS>(ring, plane, chunk, sM, rM[k]), wM[k]);
-                        const Real xs = x - km.s;
-                        const Real we = km.wchi * profile_shape(xs);
-                        etaM += we;
-                        if constexpr (dich) {
-                            etaQM += we * mdq[k];
-                            etaUM += we * mdu[k];
-                        }
-                        if constexpr (NS == 1) {
-                            epsM[0] += we * km.S;
-                        } else {
-                            const Real wkv = we * (km.b * xs);
-                            etaVM += wkv;
-                            epsM[0] += we * km.SI;
-                            epsM[1] += we * km.SQ;
-                            epsM[2] += we * km.SU;
-                            epsM[3] += wkv * km.S00;
-                        }
-                    }
-                    Real etaP = 0, epsP[NS];
-#pragma unroll
-                    for (int s = 0; s < NS; ++s) epsP[s] = 0;
-                    if (has_p) {
+                        for (int s = 0; s < 4; ++s) epsM4[s] = epsP4[s] = Real(0);
 #pragma unroll
                         for (int k = 0; k < 4; ++k) {
-                            const CornerP<Real, NS> kp =
-                                corner_p<Real, NS>(ring_load<Real, NS>(ring, plane, chunk, sP, rP[k]), wP[k]);
-                            const Real xs = x - kp.s;
-                            const Real we = kp.wchi * profile_shape(xs);
-                            etaP += we;
-                            if constexpr (NS == 1) {
-                                epsP[0] += we * kp.S;
-                            } else {
-                                epsP[0] += we * kp.SI;
-                                epsP[1] += we * kp.SQ;
-                                epsP[2] += we * kp.SU;
-                                epsP[3] += we * (kp.bS * xs);
+                            const CornerM<Real, NS> km = corner_m<Real, NS>(ring_load<Real, NS>(ring, plane, chunk, sM, rM[k]), wM[k]);
+                            const Real we = km.wchi * profile_shape(x - km.s);
+                            const Real *gk = dring + sM * 6 * dstride + rM[k];
+                            etaM7[0] += we;
+#pragma unroll
+                            for (int q = 1; q < 7; ++q) etaM7[q] += we * gk[(q - 1) * dstride];
+                            epsM4[0] += we * km.SI;
+                            epsM4[1] += we * km.SQ;
+                            epsM4[2] += we * km.SU;
+                            epsM4[3] += we * km.S00;
+                        }
+                        if (has_p) {
+#pragma unroll
+                            for (int k = 0; k < 4; ++k) {
+                                const CornerM<Real, NS> kp = corner_m<Real, NS>(ring_load<Real, NS>(ring, plane, chunk, sP, rP[k]), wP[k]);
+                                const Real we = kp.wchi * profile_shape(x - kp.s);
+                                etaPI += we;
+                                epsP4[0] += we * kp.SI;
+                                epsP4[1] += we * kp.SQ;
+                                epsP4[2] += we * kp.SU;
+                                epsP4[3] += we * kp.S00;
                             }
                         }
-                    }
-                    const Real xsO = x - nO.s;
-                    const Real phO = profile_shape(xsO);
-                    const Real etaO = nO.chi * phO;
-                    Real SO[NS], SM[NS], SP[NS];
-                    const Real iM = rcp(etaM);
-                    if constexpr (NS == 1) {
-                        SO[0] = nO.S;
+                        const Real etaOI = nO.chi * profile_shape(x - nO.s);
+                        const Real *gkO = dring + sO * 6 * dstride + (l + H) * nx + c;
+                        etaO7[0] = etaOI;
+#pragma unroll
+                        for (int q = 1; q < 7; ++q) etaO7[q] = etaOI * gkO[(q - 1) * dstride];
+                        epsO4[0] = etaOI * nO.SI;
+                        epsO4[1] = etaOI * nO.SQ;
+                        epsO4[2] = etaOI * nO.SU;
+                        epsO4[3] = etaOI * nO.S00;
+                        Real lsg;
+                        delo_step_general<Real>(IM, etaM7, epsM4, etaO7, epsO4, etaPI, epsP4, dsM, dsP, has_p, IO, lsg);
                     } else {
-                        SO[0] = nO.SI; SO[1] = nO.SQ; SO[2] = nO.SU; SO[3] = nO.b * xsO * nO.S00;
-                    }
-#pragma unroll
-                    for (int s = 0; s < NS; ++s) SM[s] = epsM[s] * iM;
-                    // a4: optical paths (trapezoid along MO and OP)
-                    const Real tMO = Real(0.5) * (etaM + etaO) * dsM;
-                    Real tOP = Real(1);
-                    if (has_p) {
-                        const Real iP = rcp(etaP);
-#pragma unroll
-                        for (int s = 0; s < NS; ++s) SP[s] = epsP[s] * iP;
-                        tOP = Real(0.5) * (etaO + etaP) * dsP;
-                    } else {
-#pragma unroll
-                        for (int s = 0; s < NS; ++s) SP[s] = Real(0);
-                    }
-                    // a6: exponential-integral coefficients
-                    const Coef<Real> co = coefficients(tMO);
-                    // a5: BESSER control points per Stokes parameter
-                    Real cM[NS];
-                    if (has_p) {
-                        const BesserGeom<Real> bg = besser_geom(tMO, tOP);
-#pragma unroll
-                        for (int s = 0; s < NS; ++s) cM[s] = control_point(SM[s], SO[s], SP[s], bg);
-                    } else {
-#pragma unroll
-                        for (int s = 0; s < NS; ++s) cM[s] = Real(0.5) * (SM[s] + SO[s]);
-                    }
-                    // a7: BESSER-DELO step (Eq. 7)
-                    Real IO[NS];
-                    if constexpr (NS == 1) {
-                        IO[0] = co.e * IM[0] + co.wm * SM[0] + co.wo * SO[0] + co.wc * cM[0];
-                    } else if constexpr (dich) {
-                        // K' with eta_Q, eta_U (dichroism) and eta_V entries over eta_I:
-                        // (K'I)_0 = q I_1 + u I_2 + v I_3, (K'I)_k = k_k I_0
-                        const Real qM = etaQM * iM, uM = etaUM * iM, vM = etaVM * iM;
-                        const Real qO = odq, uO = odu, vO = nO.b * xsO;
-                        Real rhs[4];
-#pragma unroll
-                        for (int s = 0; s < 4; ++s) rhs[s] = co.e * IM[s] + co.wm * SM[s] + co.wo * SO[s] + co.wc * cM[s];
-                        rhs[0] -= co.pm * (qM * IM[1] + uM * IM[2] + vM * IM[3]);
-                        rhs[1] -= co.pm * qM * IM[0];
-                        rhs[2] -= co.pm * uM * IM[0];
-                        rhs[3] -= co.pm * vM * IM[0];
-                        // (1 + psi'_O K'_O)^-1 of the arrow-shaped matrix
-                        const Real aq = co.po * qO, au = co.po * uO, av = co.po * vO;
-                        IO[0] = (rhs[0] - aq * rhs[1] - au * rhs[2] - av * rhs[3]) * rcp(Real(1) - aq * aq - au * au - av * av);
-                        IO[1] = rhs[1] - aq * IO[0];
-                        IO[2] = rhs[2] - au * IO[0];
-                        IO[3] = rhs[3] - av * IO[0];
-                    } else {
-                        // K' has only the eta_V / eta_I entries (weak-field Zeeman)
-                        const Real kvM = etaVM * iM;
-                        const Real kvO = nO.b * xsO;
-                        Real rhs[4];
-#pragma unroll
-                        for (int s = 0; s < 4; ++s) rhs[s] = co.e * IM[s] + co.wm * SM[s] + co.wo * SO[s] + co.wc * cM[s];
-                        rhs[0] -= co.pm * kvM * IM[3];
-                        rhs[3] -= co.pm * kvM * IM[0];
-                        // kappa^-1 = 1 + psi'_O K'_O couples I and V only
-                        const Real av = co.po * kvO;
-                        const Real idet = rcp(Real(1) - av * av);
-                        IO[0] = (rhs[0] - av * rhs[3]) * idet;
-                        IO[3] = (rhs[3] - av * rhs[0]) * idet;
-                        IO[1] = rhs[1];
-                        IO[2] = rhs[2];
+                        // a2-a3: node transfer coefficients and bilinear interpolation at M and P
+                        Real etaM = 0, etaVM = 0, etaQM = 0, etaUM = 0, epsM[NS];
+    #pragma unroll
+                        for (int s = 0; s < NS; ++s) epsM[s] = 0;
+                        constexpr int NK = BQ ? 9 : 4;           // interpolation corners
+    #pragma unroll
+                        for (int k = 0; k < NK; ++k) {
+                            const CornerM<Real, NS> km = corner_m<Real, NS>(
+                                ring_load<Real, NS>(ring, plane, chunk, sM, BQ ? bqM[k] : rM[k]), BQ ? bwM[k] : wM[k]);
+                            const Real xs = x - km.s;
+                            const Real we = km.wchi * profile_shape(xs);
+                            etaM += we;
+                            if constexpr (dich) {
+                                etaQM += we * mdq[k];
+                                etaUM += we * mdu[k];
+                            }
+                            if constexpr (NS == 1) {
+                                epsM[0] += we * km.S;
+                            } else {
+                                const Real wkv = we * (km.b * xs);
+                                etaVM += wkv;
+                                epsM[0] += we * km.SI;
+                                epsM[1] += we * km.SQ;
+                                epsM[2] += we * km.SU;
+                                epsM[3] += wkv * km.S00;
+                            }
+                        }
+                        Real etaP = 0, epsP[NS];
+    #pragma unroll
+                        for (int s = 0; s < NS; ++s) epsP[s] = 0;
+                        if (has_p) {
+    #pragma unroll
+                            for (int k = 0; k < NK; ++k) {
+                                const CornerP<Real, NS> kp = corner_p<Real, NS>(
+                                    ring_load<Real, NS>(ring, plane, chunk, sP, BQ ? bqP[k] : rP[k]), BQ ? bwP[k] : wP[k]);
+                                const Real xs = x - kp.s;
+                                const Real we = kp.wchi * profile_shape(xs);
+                                etaP += we;
+                                if constexpr (NS == 1) {
+                                    epsP[0] += we * kp.S;
+                                } else {
+                                    epsP[0] += we * kp.SI;
+                                    epsP[1] += we * kp.SQ;
+                                    epsP[2] += we * kp.SU;
+                                    epsP[3] += we * (kp.bS * xs);
+                                }
+                            }
+                        }
+                        const Real xsO = x - nO.s;
+                        phO = profile_shape(xsO);
+                        const Real etaO = nO.chi * phO;
+                        Real SO[NS], SM[NS], SP[NS];
+                        const Real iM = rcp(etaM);
+                        if constexpr (NS == 1) {
+                            SO[0] = nO.S;
+                        } else {
+                            SO[0] = nO.SI; SO[1] = nO.SQ; SO[2] = nO.SU; SO[3] = nO.b * xsO * nO.S00;
+                        }
+    #pragma unroll
+                        for (int s = 0; s < NS; ++s) SM[s] = epsM[s] * iM;
+                        // a4: optical paths (trapezoid along MO and OP)
+                        const Real tMO = Real(0.5) * (etaM + etaO) * dsM;
+                        Real tOP = Real(1);
+                        if (has_p) {
+                            const Real iP = rcp(etaP);
+    #pragma unroll
+                            for (int s = 0; s < NS; ++s) SP[s] = epsP[s] * iP;
+                            tOP = Real(0.5) * (etaO + etaP) * dsP;
+                        } else {
+    #pragma unroll
+                            for (int s = 0; s < NS; ++s) SP[s] = Real(0);
+                        }
+                        // a6: exponential-integral coefficients
+                        co = coefficients(tMO);
+                        // a5: BESSER control points per Stokes parameter
+                        Real cM[NS];
+                        if (has_p) {
+                            const BesserGeom<Real> bg = besser_geom(tMO, tOP);
+    #pragma unroll
+                            for (int s = 0; s < NS; ++s) cM[s] = control_point(SM[s], SO[s], SP[s], bg);
+                        } else {
+    #pragma unroll
+                            for (int s = 0; s < NS; ++s) cM[s] = Real(0.5) * (SM[s] + SO[s]);
+                        }
+                        // a7: BESSER-DELO step (Eq. 7)
+                        if constexpr (NS == 1) {
+                            IO[0] = co.e * IM[0] + co.wm * SM[0] + co.wo * SO[0] + co.wc * cM[0];
+                        } else if constexpr (dich) {
+                            // K' with eta_Q, eta_U (dichroism) and eta_V entries over eta_I:
+                            // (K'I)_0 = q I_1 + u I_2 + v I_3, (K'I)_k = k_k I_0
+                            const Real qM = etaQM * iM, uM = etaUM * iM, vM = etaVM * iM;
+                            const Real qO = odq, uO = odu, vO = nO.b * xsO;
+                            Real rhs[4];
+    #pragma unroll
+                            for (int s = 0; s < 4; ++s) rhs[s] = co.e * IM[s] + co.wm * SM[s] + co.wo * SO[s] + co.wc * cM[s];
+                            rhs[0] -= co.pm * (qM * IM[1] + uM * IM[2] + vM * IM[3]);
+                            rhs[1] -= co.pm * qM * IM[0];
+                            rhs[2] -= co.pm * uM * IM[0];
+                            rhs[3] -= co.pm * vM * IM[0];
+                            // (1 + psi'_O K'_O)^-1 of the arrow-shaped matrix
+                            const Real aq = co.po * qO, au = co.po * uO, av = co.po * vO;
+                            IO[0] = (rhs[0] - aq * rhs[1] - au * rhs[2] - av * rhs[3]) * rcp(Real(1) - aq * aq - au * au - av * av);
+                            IO[1] = rhs[1] - aq * IO[0];
+                            IO[2] = rhs[2] - au * IO[0];
+                            IO[3] = rhs[3] - av * IO[0];
+                        } else {
+                            // K' has only the eta_V / eta_I entries (weak-field Zeeman)
+                            const Real kvM = etaVM * iM;
+                            const Real kvO = nO.b * xsO;
+                            Real rhs[4];
+    #pragma unroll
+                            for (int s = 0; s < 4; ++s) rhs[s] = co.e * IM[s] + co.wm * SM[s] + co.wo * SO[s] + co.wc * cM[s];
+                            rhs[0] -= co.pm * kvM * IM[3];
+                            rhs[3] -= co.pm * kvM * IM[0];
+                            // kappa^-1 = 1 + psi'_O K'_O couples I and V only
+                            const Real av = co.po * kvO;
+                            const Real idet = rcp(Real(1) - av * av);
+                            IO[0] = (rhs[0] - av * rhs[3]) * idet;
+                            IO[3] = (rhs[3] - av * rhs[0]) * idet;
+                            IO[1] = rhs[1];
+                            IO[2] = rhs[2];
+                        }
                     }
                     StokesIO<Real, NS>::store(iw + f * iplane, ichunk, l * nx + c, IO);
                     // a8: Lambda* (Eq. 14; w_O + w_C/2 on the last plane) and accumulation
@@ -461,7 +595,7 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<Real> &a, cg::cluster
     }
 }
 
-template <typename Real, int NS, int MODE, bool DI = false>
+template <typename Real, int NS, int MODE, bool DI = false, bool BQ = false, bool GK = false>
 __global__ void __launch_bounds__(512, 1) sweep_kernel(const SweepArgs<Real> a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -493,7 +627,7 @@ __global__ void __launch_bounds__(512, 1) sweep_kernel(const SweepArgs<Real> a)
                 const int code = a.items ? a.items[item] : item;
                 const int box = code / a.nray, m = code - box * a.nray;
                 for (int g = 0; g < a.ngroups; ++g)
-                    sweep_item<Real, NS, MODE, DI>(a, cluster, ring, ibuf, lane_buf, box, m, g, rank, C, 0);
+                    sweep_item<Real, NS, MODE, DI, BQ, GK>(a, cluster, ring, ibuf, lane_buf, box, m, g, rank, C, 0);
             }
             return;
         }
@@ -503,28 +637,35 @@ __global__ void __launch_bounds__(512, 1) sweep_kernel(const SweepArgs<Real> a)
             const int code = a.items ? a.items[item] : item;
             const int box = code / a.nray, m = code - box * a.nray;
             for (int g = 0; g < a.ngroups; ++g)
-                sweep_item<Real, NS, MODE, DI>(a, cluster, ring, ibuf, lane_buf, box, m, g, rank, C, 0);
+                sweep_item<Real, NS, MODE, DI, BQ, GK>(a, cluster, ring, ibuf, lane_buf, box, m, g, rank, C, 0);
         } else {
             const int d = item / a.ngroups, g = item - d * a.ngroups;
-            sweep_item<Real, NS, MODE, DI>(a, cluster, ring, ibuf, lane_buf, 0, d, g, rank, C, d);
+            sweep_item<Real, NS, MODE, DI, BQ, GK>(a, cluster, ring, ibuf, lane_buf, 0, d, g, rank, C, d);
         }
     }
 }
 
 template <typename Real, int NS>
-static void *kernel_ptr(int mode, bool dich = false)
+static void *kernel_ptr(int mode, bool dich = false, bool bq = false, bool gk = false)
 {
+    // the explicit medium (general propagation matrix), emergent mode
+    if constexpr (NS == 4)
+        if (gk) return (void *)sweep_kernel<Real, NS, MODE_EMERGENT, false, false, true>;
     // the dichroism variant (polarized lines of the multilevel atom)
     if (NS == 4 && dich)
         return mode == MODE_JKQ ? (void *)sweep_kernel<Real, NS, MODE_JKQ, NS == 4>
                                 : (void *)sweep_kernel<Real, NS, MODE_EMERGENT, NS == 4>;
+    // biquadratic interpolation
+    if (bq)
+        return mode == MODE_JKQ ? (void *)sweep_kernel<Real, NS, MODE_JKQ, false, true>
+                                : (void *)sweep_kernel<Real, NS, MODE_EMERGENT, false, true>;
     return mode == MODE_JKQ ? (void *)sweep_kernel<Real, NS, MODE_JKQ> : (void *)sweep_kernel<Real, NS, MODE_EMERGENT>;
 }
 
 template <typename Real, int NS>
-static cudaError_t prepare(int mode, int cluster, int smem, bool dich = false)
+static cudaError_t prepare(int mode, int cluster, int smem, bool dich = false, bool bq = false, bool gk = false)
 {
-    void *k = kernel_ptr<Real, NS>(mode, dich);
+    void *k = kernel_ptr<Real, NS>(mode, dich, bq, gk);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     if (cluster > 8) e = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
@@ -532,9 +673,9 @@ static cudaError_t prepare(int mode, int cluster, int smem, bool dich = false)
 }
 
 template <typename Real, int NS>
-cudaError_t max_active_clusters(int cluster, int smem, int threads, int *out, bool dich)
+cudaError_t max_active_clusters(int cluster, int smem, int threads, int *out, bool dich, bool bq, bool gk)
 {
-    cudaError_t e = prepare<Real, NS>(MODE_JKQ, cluster, smem, dich);
+    cudaError_t e = prepare<Real, NS>(gk ? MODE_EMERGENT : MODE_JKQ, cluster, smem, dich, bq, gk);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t lc = {};
     lc.gridDim = dim3(cluster);
@@ -547,14 +688,18 @@ cudaError_t max_active_clusters(int cluster, int smem, int threads, int *out, bo
     at[0].val.clusterDim.z = 1;
     lc.attrs = at;
     lc.numAttrs = 1;
-    return cudaOccupancyMaxActiveClusters(out, (void (*)(SweepArgs<Real>))kernel_ptr<Real, NS>(MODE_JKQ, dich), &lc);
+    return cudaOccupancyMaxActiveClusters(
+        out, (void (*)(SweepArgs<Real>))kernel_ptr<Real, NS>(gk ? MODE_EMERGENT : MODE_JKQ, dich, bq, gk), &lc);
 }
 
 template <typename Real, int NS>
 cudaError_t launch_sweep(const SweepArgs<Real> &a, int mode, LaunchCfg &cfg, cudaStream_t st)
 {
     const bool dich = NS == 4 && a.dich != nullptr;
-    cudaError_t e = prepare<Real, NS>(mode, cfg.cluster, cfg.smem, dich);
+    const bool gk = NS == 4 && a.kexpl != nullptr;
+    const bool bq = !dich && !gk && a.interp == 2;
+    if (gk && mode != MODE_EMERGENT) return cudaErrorInvalidValue;
+    cudaError_t e = prepare<Real, NS>(mode, cfg.cluster, cfg.smem, dich, bq, gk);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t lc = {};
     lc.gridDim = dim3(cfg.clusters * cfg.cluster);
@@ -573,9 +718,14 @@ cudaError_t launch_sweep(const SweepArgs<Real> &a, int mode, LaunchCfg &cfg, cud
         at[1].val.priority = cfg.priority;
         lc.numAttrs = 2;
     }
+    if constexpr (NS == 4)
+        if (gk) return cudaLaunchKernelEx(&lc, sweep_kernel<Real, NS, MODE_EMERGENT, false, false, true>, a);
     if (dich)
         return mode == MODE_JKQ ? cudaLaunchKernelEx(&lc, sweep_kernel<Real, NS, MODE_JKQ, NS == 4>, a)
                                 : cudaLaunchKernelEx(&lc, sweep_kernel<Real, NS, MODE_EMERGENT, NS == 4>, a);
+    if (bq)
+        return mode == MODE_JKQ ? cudaLaunchKernelEx(&lc, sweep_kernel<Real, NS, MODE_JKQ, false, true>, a)
+                                : cudaLaunchKernelEx(&lc, sweep_kernel<Real, NS, MODE_EMERGENT, false, true>, a);
     if (mode == MODE_JKQ)
         return cudaLaunchKernelEx(&lc, sweep_kernel<Real, NS, MODE_JKQ>, a);
     return cudaLaunchKernelEx(&lc, sweep_kernel<Real, NS, MODE_EMERGENT>, a);
@@ -583,7 +733,7 @@ cudaError_t launch_sweep(const SweepArgs<Real> &a, int mode, LaunchCfg &cfg, cud
 
 #define PORTA_INST(R, N)                                                                           \
     template int sweep_smem_bytes<R, N>(int, int, int, int);                                            \
-    template cudaError_t max_active_clusters<R, N>(int, int, int, int *, bool);                    \
+    template cudaError_t max_active_clusters<R, N>(int, int, int, int *, bool, bool, bool);        \
     template cudaError_t launch_sweep<R, N>(const SweepArgs<R> &, int, LaunchCfg &, cudaStream_t);
 PORTA_INST(float, 1)
 PORTA_INST(float, 4)
