@@ -66,6 +66,9 @@ class _Problem(ctypes.Structure):
         ("interp", ctypes.c_int),
         ("kexpl", ctypes.c_void_p),
         ("sexpl", ctypes.c_void_p),
+        ("orient", ctypes.c_void_p),
+        ("dich1", ctypes.c_void_p),
+        ("j1", ctypes.c_void_p),
     ]
 
 
@@ -171,6 +174,13 @@ class Problem:
             v = atm.get(k)
             self._keep[k] = _f64(v).ravel() if v is not None else None
             setattr(s, k, _ptr(self._keep[k]))
+        # orientation terms of a polarized line: atm["orient"] (nz, ny, nx, 3) = S^1_Q and
+        # atm["dich1"] (nz, ny, nx, 3) = D^1_Q in the layout (X10, Re X11, Im X11)
+        for k in ("orient", "dich1"):
+            v = atm.get(k)
+            self._keep[k] = _f64(v).ravel() if v is not None else None
+            setattr(s, k, _ptr(self._keep[k]))
+        s.j1 = None
         self.interp = int(interp)
         self.s = s
         self.nray = 2 * n_mu * n_chi
@@ -281,15 +291,21 @@ def hanle_solve(gamma, b, rhs6):
     return out
 
 
-def formal_solve(prob, rho, rays_range=None, freq_range=None):
+def formal_solve(prob, rho, rays_range=None, freq_range=None, with_j1=False):
+    """J^K_Q (K = 0, 2) and Lambda-bar*; with_j1 also J^1_Q (layout J10, Re J11, Im J11,
+    from Stokes V; polarized model)."""
     rho = _f64(rho).ravel()
     assert rho.size == prob.nvox * nl_of(prob.model)
     jkq = np.zeros(prob.nvox * nj_of(prob.model)); ls = np.zeros(prob.nvox)
     m0, m1 = rays_range if rays_range else (0, prob.nray)
     j0, j1 = freq_range if freq_range else (0, prob.n_nu)
+    jo = np.zeros(prob.nvox * 3) if with_j1 else None
+    prob.s.j1 = _ptr(jo) if with_j1 else None
     rc = lib().or_formal_solve_part(prob.ref, _ptr(rho), m0, m1, j0, j1, _ptr(jkq), _ptr(ls))
+    prob.s.j1 = None
     assert rc == 0, rc
-    return jkq.reshape(prob.shape + (nj_of(prob.model),)), ls.reshape(prob.shape)
+    out = (jkq.reshape(prob.shape + (nj_of(prob.model),)), ls.reshape(prob.shape))
+    return out + (jo.reshape(prob.shape + (3,)),) if with_j1 else out
 
 
 def sweep_ray(prob, rho, m, j):

@@ -53,15 +53,16 @@ Without polarization this is the update of oracle/ml.py; the fixed point is
 that of the rate equations.
 
 Line transfer (a reading): the emissivity of a line carries the upper level's
-multipoles K = 0, 2 (the two-level formal solver of this package, eps_i =
+multipoles K = 0, 1, 2 (the two-level formal solver of this package, eps_i =
 eta_I sum_KQ (-1)^Q T^K_Q S^K_-Q with S^K_Q = S_line w^(K) conj(rho^K_Q /
-rho^0_0)(J_u), w^(K) = (-1)^(1+Jl+Ju) sqrt(3(2Ju+1)) {1 1 K; Ju Ju Jl}); the
-absorption matrix carries the line's dichroism from the alignment (K = 2) of
-its lower level (absorption) and upper level (stimulated emission),
-line_dichroism; the orientation (K = 1) terms are not included, and the
-weak-field Zeeman term uses the field scaled by the line's effective Lande
-factor (1 for every level here). The formal solution therefore gives
-J^Kr_Qr for Kr = 0, 2 only.
+rho^0_0)(J_u), w^(K) = (-1)^(1+Jl+Ju) sqrt(3(2Ju+1)) {1 1 K; Ju Ju Jl}; the
+orientation K = 1 enters Stokes V only, through T^1_Q(V, Omega) = sqrt(3/2)
+Omega_Q); the absorption matrix carries the line's dichroism from the
+alignment (K = 2) and orientation (K = 1) of its lower level (absorption, with
+the factor (-1)^K of absorption against emission) and upper level (stimulated
+emission), line_dichroism; the weak-field Zeeman term uses the field scaled by
+the line's effective Lande factor (1 for every level here). The formal solution
+gives J^Kr_Qr for Kr = 0, 1, 2 (J^1_Q from Stokes V).
 """
 import numpy as np
 
@@ -363,6 +364,57 @@ def line_source_multipoles(tab, x):
     return out
 
 
+def _w(K, J, Jp):
+    """w^(K)_{J J'} = (-1)^(1+J+J') sqrt(3(2J+1)) {1 1 K; J J J'} (0 where 2J < K)"""
+    if 2 * J < K:
+        return 0.0
+    return (-1) ** int(round(1 + J + Jp)) * np.sqrt(3 * (2 * J + 1)) * w6j(1, 1, K, J, J, Jp)
+
+
+def line_orientation_multipoles(tab, x):
+    """per line, the orientation emission multipoles S^1_Q = S_line w^(1) conj(rho^1_Q /
+    rho^0_0)(J_u) in the layout (S10, Re S11, Im S11)"""
+    atom = tab.atom
+    S = ml.source_function(atom, tab.populations(x))
+    xc = tab.to_complex(x)
+    out = np.zeros(x.shape[:-1] + (len(tab.lines), 3))
+    for li, (u, l) in enumerate(tab.lines):
+        Ju, Jl = tab.J[u], tab.J[l]
+        if 2 * Ju < 1:
+            continue
+        r00 = xc[..., tab.idx[(u, 0, 0)]].real
+        s = {Q: np.conj(xc[..., tab.idx[(u, 1, Q)]]) / r00 * _w(1, Ju, Jl) * S[..., li] for Q in (0, 1)}
+        out[..., li, 0] = s[0].real
+        out[..., li, 1], out[..., li, 2] = s[1].real, s[1].imag
+    return out
+
+
+def line_dichroism_orientation(tab, x, li):
+    """the orientation dichroism multipoles of line li, D^1_Q in the layout (D10, Re D11,
+    Im D11): eta_V gains eta_I sum_Q (-1)^Q T^1_Q(V, Omega) D^1_-Q with
+      D^1_Q = conj([-B_lu sqrt(2Jl+1) w1(Jl, Ju) rho^1_Q(Jl) - B_ul sqrt(2Ju+1) w1(Ju, Jl) rho^1_Q(Ju)]
+                    / [B_lu sqrt(2Jl+1) rho^0_0(Jl) - B_ul sqrt(2Ju+1) rho^0_0(Ju)])
+    (line_dichroism with K = 1: the absorption term carries (-1)^K = -1)."""
+    u, l = tab.lines[li]
+    Ju, Jl = tab.J[u], tab.J[l]
+    xc = tab.to_complex(x)
+    al = tab.Blu[li] * np.sqrt(2 * Jl + 1)
+    au = tab.Bul[li] * np.sqrt(2 * Ju + 1)
+    den = al * xc[..., tab.idx[(l, 0, 0)]].real - au * xc[..., tab.idx[(u, 0, 0)]].real
+    out = np.zeros(x.shape[:-1] + (3,))
+    for Q, (kr, ki) in ((0, (0, None)), (1, (1, 2))):
+        num = np.zeros(x.shape[:-1], dtype=complex)
+        if 2 * Jl >= 1:
+            num = num - al * _w(1, Jl, Ju) * xc[..., tab.idx[(l, 1, Q)]]
+        if 2 * Ju >= 1:
+            num = num - au * _w(1, Ju, Jl) * xc[..., tab.idx[(u, 1, Q)]]
+        d = np.conj(num / den)
+        out[..., kr] = np.real(d)
+        if ki is not None:
+            out[..., ki] = np.imag(d)
+    return out
+
+
 def line_dichroism(tab, x, li):
     """dichroism multipoles of line li in the formal solver's layout (D20, Re D21,
     Im D21, Re D22, Im D22): the alignment terms of the line's absorption (lower
@@ -407,11 +459,13 @@ def line_problem(atm, atom, tab, x, li, quad, dichroism=True):
     a["eps"] = np.ones_like(a["chi"])
     if dichroism:
         a["dich"] = line_dichroism(tab, x, li)
+        a["dich1"] = line_dichroism_orientation(tab, x, li)
+    a["orient"] = line_orientation_multipoles(tab, x)[..., li, :]
     return Problem(a, 1, *quad)
 
 
 def formal_solve_lines(atm, atom, tab, x, quad, dichroism=True):
-    """Jbar (real layout of jkq_complex, Kr = 0, 2 filled) and Lambda-bar* per line"""
+    """Jbar (real layout of jkq_complex, Kr = 0, 1, 2) and Lambda-bar* per line"""
     src = line_source_multipoles(tab, x)
     nline = len(tab.lines)
     shape = x.shape[:-1]
@@ -419,9 +473,10 @@ def formal_solve_lines(atm, atom, tab, x, quad, dichroism=True):
     lstar = np.zeros(shape + (nline,))
     for li in range(nline):
         p = line_problem(atm, atom, tab, x, li, quad, dichroism)
-        j, ls = formal_solve(p, src[..., li, :])
-        # two-level layout (J00, J20, ReJ21, ImJ21, ReJ22, ImJ22) -> Kr = 0, 1, 2 layout
+        j, ls, j1 = formal_solve(p, src[..., li, :], with_j1=True)
+        # two-level layout (J00, J20, ReJ21, ImJ21, ReJ22, ImJ22) and J^1 -> Kr = 0, 1, 2 layout
         jbar[..., li, 0] = j[..., 0]
+        jbar[..., li, 1:4] = j1
         jbar[..., li, 4:9] = j[..., 1:6]
         lstar[..., li] = ls
     return jbar, lstar

@@ -22,6 +22,7 @@ typedef struct {
     double mu, chi, w;
     double ox, oy, oz;     /* unit direction */
     double t[18];          /* T^K_Q(i, Omega) */
+    double t1[3];          /* T^1_Q(V, Omega): (T10, Re T11, Im T11) */
 } or_ray;
 
 static void make_ray(double mu, double chi, double w, or_ray *r)
@@ -30,6 +31,11 @@ static void make_ray(double mu, double chi, double w, or_ray *r)
     r->mu = mu; r->chi = chi; r->w = w;
     r->ox = st * cos(chi); r->oy = st * sin(chi); r->oz = mu;
     or_tkq(mu, chi, r->t);
+    /* T^1_Q(V, Omega) = sqrt(3/2) Omega_Q, the spherical components of the direction:
+       Omega_0 = Omega_z, Omega_{+1} = -(Omega_x + i Omega_y)/sqrt(2) */
+    r->t1[0] = sqrt(1.5) * r->oz;
+    r->t1[1] = -sqrt(0.75) * r->ox;
+    r->t1[2] = -sqrt(0.75) * r->oy;
 }
 
 /* node coefficients at an interpolation corner: each node's coefficients are
@@ -57,6 +63,12 @@ static double shift(const or_problem *p, long v, const or_ray *r) { return p->ve
 static double angular_source(const double *t6, const double *s)
 {
     return t6[0] * s[0] + t6[1] * s[1] + 2.0 * (t6[2] * s[2] + t6[3] * s[3]) + 2.0 * (t6[4] * s[4] + t6[5] * s[5]);
+}
+
+/* sum_Q (-1)^Q T^1_Q S^1_{-Q} = T10 S10 + 2 Re(T11 conj S11) (rank-1 tensors, S^1_-Q = -conj S^1_Q) */
+static double angular1(const double *t1, const double *s)
+{
+    return t1[0] * s[0] + 2.0 * (t1[1] * s[1] + t1[2] * s[2]);
 }
 
 /*
@@ -97,6 +109,8 @@ static void node_coeffs(const or_problem *p, const double *rho, long v, const or
     for (int i = 0; i < 3; i++) eps[i] = etaI * angular_source(r->t + 6 * i, s);
     eps[3] = s[0] * eta[3];
     OR_FLOPS(5 + 5 + 3 * 12 + 1);
+    if (p->orient) eps[3] += etaI * angular1(r->t1, p->orient + 3 * v);
+    if (p->dich1) eta[3] += etaI * angular1(r->t1, p->dich1 + 3 * v);
     if (p->dich) {
         const double *d = p->dich + 5 * v;
         const double d6[6] = {1.0, d[0], d[1], d[2], d[3], d[4]};
@@ -253,6 +267,7 @@ int or_formal_solve_part(const or_problem *p, const double *rho, int m0, int m1,
     or_freqs(nn, p->x_max, xf, wf);
     memset(jkq, 0, sizeof(double) * nv * nj);
     memset(lstar, 0, sizeof(double) * nv);
+    if (p->j1) memset(p->j1, 0, sizeof(double) * nv * 3);
     int rc = 0;
     for (int m = m0; m < m1 && rc == 0; m++) {                 /* directions: outer loop */
         or_ray r;
@@ -276,6 +291,8 @@ int or_formal_solve_part(const or_problem *p, const double *rho, int m0, int m1,
                     for (int c = 0; c < 6; c++)
                         jkq[v * 6 + c] += wt * (r.t[c] * Iv[0] + r.t[6 + c] * Iv[1] + r.t[12 + c] * Iv[2]);
                     OR_FLOPS(6 * 7);
+                    if (p->j1)
+                        for (int c = 0; c < 3; c++) p->j1[v * 3 + c] += wt * r.t1[c] * Iv[3];
                 }
                 lstar[v] += wt * lo[v];
                 OR_FLOPS(2 + 7);   /* Lambda* accumulation; weight (profile and normalization) */

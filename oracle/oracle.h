@@ -60,6 +60,13 @@ typedef struct {
        (kexpl, 6 x nvox), and the source vector (S_I, S_Q, S_U, S_V) (sexpl, 4 x nvox),
        both independent of direction and frequency; eta_I = chi phi(x - s) */
     const double *kexpl, *sexpl;
+    /* orientation (K = 1) terms of a polarized line (optional; NULL: none), 3 doubles per
+       voxel in the layout (X10, Re X11, Im X11): the emission multipoles S^1_Q
+       (orient: eps_V += eta_I sum_Q (-1)^Q T^1_Q(V, Omega) S^1_-Q) and the dichroism
+       multipoles D^1_Q (dich1: eta_V += eta_I sum_Q (-1)^Q T^1_Q(V, Omega) D^1_-Q);
+       j1 (output, or_formal_solve_part): J^1_Q = sum_m w_m T^1_Q(V, Omega_m) Vbar, zeroed first */
+    const double *orient, *dich1;
+    double *j1;
 } or_problem;
 
 /* the periodic interpolation stencil of the sweep at cell coordinates (xc, yc) of a
