@@ -213,8 +213,9 @@ int porta_sigmoid_error(int precision, int ncase, const int *method, const doubl
    whole grid); the profile normalization stays that of the whole grid, so the
    bands' sums add up to J^K_Q and Lambda-bar*. Single-box two-level contexts
    (and batches); PORTA_EINVAL for multilevel contexts and bad bounds.
-   porta_partial_size gives the partial sums' element count, (NJ + 1) * nvox,
-   and element size (8 bytes). After porta_formal_solve, porta_get_partial
+   porta_partial_size gives the partial sums' element count, (NJ + 1) * nvox
+   (and 3 * nvox more, J^1_Q [nvox][3] after Lambda-bar*, on a polarized
+   multilevel context), and element size (8 bytes). After porta_formal_solve, porta_get_partial
    copies them to `out` (host or device, `where`): in the FP32 form the exact
    fixed-point sums as int64, [NJ + 1][nvox] (J^K_Q components, then
    Lambda-bar*; the voxels' scales are identical on every context with the same
@@ -605,7 +606,7 @@ typedef struct {
    without interference between levels; the paper takes them from LL04 Sect.
    7.2): absorption TA, spontaneous emission TE and stimulated emission TS into
    a level, relaxation RA + RE + RS out of it (Wigner 3j/6j/9j coefficients
-   times the line's J^Kr_Qr, Kr = 0, 2), the Hanle term -i 2 pi nu_L g_J (b.J)
+   times the line's J^Kr_Qr, Kr = 0, 1, 2), the Hanle term -i 2 pi nu_L g_J (b.J)
    of d rho / dt (counterclockwise precession about the field) with Lande
    factor 1 for every level and nu_L = 1.3996e6 Hz/G, collisions on
    the line transitions moving populations and relaxing every multipole of the
@@ -614,13 +615,17 @@ typedef struct {
    rho^0_0(J) = 1; one warp per voxel solves the FP64 system in shared
    memory. Line transfer: each line is a polarized two-level formal solution
    (Sec. 3) with the line opacity of the populations, the emissivity of the
-   upper level's K = 0, 2 multipoles (S^K_Q = S_line w^(K) conj(rho^K_Q /
-   rho^0_0), w^(K) = (-1)^(1+Jl+Ju) sqrt(3(2Ju+1)) {1 1 K; Ju Ju Jl}) and the
-   weak-field Zeeman term with 2 zeta B; dichroism from the lower levels'
-   atomic polarization and the orientation (K = 1) terms are not included, so
-   J^1_Q = 0. porta_mg_setup / porta_mg_vcycle run the multigrid cycle with
-   the multipoles as unknowns (A(x) the plain rate equations with the trace
-   row; max_change over the populations). */
+   upper level's K = 0, 1, 2 multipoles (S^K_Q = S_line w^(K) conj(rho^K_Q /
+   rho^0_0), w^(K) = (-1)^(1+Jl+Ju) sqrt(3(2Ju+1)) {1 1 K; Ju Ju Jl}; K = 0, 2
+   in eps_I, eps_Q, eps_U, the orientation K = 1 in eps_V through
+   T^1_Q(V, Omega) = sqrt(3/2) Omega_Q), the weak-field Zeeman term with
+   2 zeta B, and the dichroism of the line's absorption (lower level) and
+   stimulated emission (upper level) from their alignment (K = 2; eta_Q,
+   eta_U and a rescaled eta_I) and orientation (K = 1; eta_V, the absorption
+   term with the sign (-1)^K); J^1_Q = sum_m w_m T^1_Q(V, Omega_m) Vbar_m
+   comes from Stokes V. porta_mg_setup / porta_mg_vcycle run the multigrid
+   cycle with the multipoles as unknowns (A(x) the plain rate equations with
+   the trace row; max_change over the populations). */
 
 /* Create a multilevel context on grid g (PORTA_EINVAL for an invalid atom or
    grid). The generic calls porta_formal_solve, porta_accumulate_jkq,
@@ -670,7 +675,9 @@ int porta_ml_set_pops(porta_ctx *c, const double *pops, int where);
 int porta_ml_get_pops(porta_ctx *c, double *pops, int where);
 
 /* Formal solution of every line and the sums Jbar, Lambda-bar* per line
-   ([line][voxel] doubles; NULL keeps them on the device). */
+   ([line][voxel] doubles; NULL keeps them on the device). Polarized atom:
+   jbar is [line][voxel][9] in the order J00, J10, Re J11, Im J11, J20,
+   Re J21, Im J21, Re J22, Im J22 (J^K_-Q = (-1)^Q conj J^K_Q). */
 int porta_ml_formal_solve(porta_ctx *c, double *jbar, double *lstar, int where);
 
 /* Update of the populations from the last sums; max_change (host, may be

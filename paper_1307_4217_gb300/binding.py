@@ -945,9 +945,11 @@ class MlContext(Context):
         return out
 
     def ml_formal_solve(self, jbar=None, lstar=None, want=True):
-        """Formal solution of every line; returns (Jbar, Lambda-bar*) [line][voxel] or (None, None)."""
+        """Formal solution of every line; returns (Jbar, Lambda-bar*) [line][voxel] or (None, None).
+        Polarized atom: Jbar [line][voxel][9] = (J00, J10, Re J11, Im J11, J20, Re J21, Im J21,
+        Re J22, Im J22)."""
         if want and jbar is None:
-            jbar = np.zeros(self.shape + ((6,) if self.polarized else ()))
+            jbar = np.zeros(self.shape + ((9,) if self.polarized else ()))
             lstar = np.zeros(self.shape)
         pj, wj, kj = _ptr_where(jbar)
         pl, wl, kl = _ptr_where(lstar)

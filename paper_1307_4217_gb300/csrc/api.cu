@@ -225,6 +225,7 @@ SweepArgs<Real> jkq_args(porta_ctx *c)
     a.rays = (const RayDev<Real> *)c->d_rays;
     a.invn = (const Real *)c->d_invn;
     a.part = jfixed(c) ? nullptr : c->d_part;
+    a.partv = (Real *)c->d_partv;
     a.jacc = jfixed(c) ? c->d_jacc : nullptr;
     a.jexp = c->d_jexp;
     a.jerr = c->d_err;
@@ -245,8 +246,11 @@ cudaError_t ensure_sweep_buffers(porta_ctx *c)
         if (e == cudaSuccess && !c->d_jexp) e = pmalloc(&c->d_jexp, (size_t)c->nvox * sizeof(int));
         return e;
     }
-    if (c->d_part) return cudaSuccess;
-    return pmalloc(&c->d_part, (size_t)c->nray * c->nvox * (c->ns == 1 ? 2 : 4) * c->rsz);
+    cudaError_t e = cudaSuccess;
+    if (!c->d_part) e = pmalloc(&c->d_part, (size_t)c->nray * c->nvox * (c->ns == 1 ? 2 : 4) * c->rsz);
+    // polarized lines of a multilevel atom: the per-ray integrals of Stokes V (J^1_Q)
+    if (e == cudaSuccess && c->d_dich && !c->d_partv) e = pmalloc(&c->d_partv, (size_t)c->nray * c->nvox * c->rsz);
+    return e;
 }
 
 // zero the fixed-point sums and set the voxels' scales before a J^K_Q sweep
@@ -259,9 +263,16 @@ cudaError_t jacc_prepare(porta_ctx *c, const SweepArgs<Real> &a)
     return c->ns == 1 ? launch_jacc_prepare<Real, 1>(a, c->stream) : launch_jacc_prepare<Real, 4>(a, c->stream);
 }
 
-// J^K_Q and Lambda-bar* (FP64) from the sums of the last formal solution
+// J^K_Q and Lambda-bar* (FP64) from the sums of the last formal solution; for the
+// polarized lines of a multilevel atom also J^1_Q (d_j1)
 cudaError_t finalize_jkq(porta_ctx *c)
 {
+    if (c->d_j1) {
+        cudaError_t e = c->precision == PORTA_FP32
+                            ? run_j1_finalize<float>(c->nvox, c->nray, c->d_partv, c->d_tw1, c->d_j1, c->stream)
+                            : run_j1_finalize<double>(c->nvox, c->nray, c->d_partv, c->d_tw1, c->d_j1, c->stream);
+        if (e != cudaSuccess) return e;
+    }
     if (jfixed(c))
         return c->ns == 1 ? launch_jacc_finalize<1>(c->nvox, c->d_jacc, c->d_jexp, c->d_jkq, c->d_lstar, c->stream)
                           : launch_jacc_finalize<4>(c->nvox, c->d_jacc, c->d_jexp, c->d_jkq, c->d_lstar, c->stream);
@@ -354,6 +365,7 @@ int formal_solve_t(porta_ctx *c, int probe_ray, Real *probe, Real *probe_ls)
     cudaError_t e = ensure_sweep_buffers(c);
     if (e != cudaSuccess) return fail(c, PORTA_ENOMEM, std::string("formal solution buffers: ") + cudaGetErrorString(e));
     a.part = jfixed(c) ? nullptr : c->d_part;
+    a.partv = (Real *)c->d_partv;
     a.jacc = jfixed(c) ? c->d_jacc : nullptr;
     a.jexp = c->d_jexp;
     e = jacc_prepare<Real>(c, a);
@@ -535,7 +547,8 @@ void free_all(porta_ctx *c)
         if (ev) cudaEventDestroy(ev);
     void *ptrs[] = {c->d_atm, c->d_eps, c->d_bpl, c->d_b, c->d_rho, c->d_rhoR, c->d_invn, c->d_geom, c->d_rays,
                     c->d_freq, c->d_part, c->d_tw, c->d_jkq, c->d_lstar, c->d_resid, c->d_err, c->d_boxes,
-                    c->d_items, c->d_tune_items, c->d_tape, c->d_gpart, c->d_jacc, c->d_jexp, c->d_kexpl, c->d_sexpl};
+                    c->d_items, c->d_tune_items, c->d_tape, c->d_gpart, c->d_jacc, c->d_jexp, c->d_kexpl, c->d_sexpl,
+                    c->d_partv, c->d_j1, c->d_tw1};
     for (void *p : ptrs)
         if (p) pfree(p);
 }
@@ -581,8 +594,8 @@ cudaError_t enqueue_update(porta_ctx *c)
                                      c->d_lstar, c->d_rho, c->d_rhoR, c->d_resid, c->stream);
     MlState *m = c->ml;
     if (m->pol)
-        e = run_mlpol_see(m->mc, m->dev, m->nvox1, m->d_kT, c->d_jkq, c->d_lstar, c->d_b, m->d_x, c->d_resid, m->d_bad,
-                          c->stream);
+        e = run_mlpol_see(m->mc, m->dev, m->nvox1, m->d_kT, c->d_jkq, c->d_j1, c->d_lstar, c->d_b, m->d_x, c->d_resid,
+                          m->d_bad, c->stream);
     else
         e = run_ml_see(m->mc, m->nvox1, m->d_kT, c->d_jkq, c->d_lstar, m->d_pops, c->d_resid, m->d_bad, c->stream);
     if (e != cudaSuccess) return e;
@@ -1214,7 +1227,8 @@ int porta_set_freq_range(porta_ctx *c, int j0, int j1)
 int porta_partial_size(const porta_ctx *c, long long *elements, int *elem_bytes)
 {
     if (!c) return PORTA_EINVAL;
-    if (elements) *elements = (long long)(c->nj + 1) * c->nvox;
+    // (polarized lines of a multilevel atom: J^1_Q, 3 per voxel, follow)
+    if (elements) *elements = (long long)(c->nj + 1 + (c->d_j1 ? 3 : 0)) * c->nvox;
     if (elem_bytes) *elem_bytes = 8;
     return PORTA_OK;
 }
@@ -1233,6 +1247,8 @@ int porta_get_partial(porta_ctx *c, void *out, int where)
         double *o = (double *)out;
         CK(cudaMemcpyAsync(o, c->d_jkq, (size_t)c->nj * c->nvox * sizeof(double), k, c->stream));
         CK(cudaMemcpyAsync(o + (size_t)c->nj * c->nvox, c->d_lstar, (size_t)c->nvox * sizeof(double), k, c->stream));
+        if (c->d_j1)
+            CK(cudaMemcpyAsync(o + (size_t)(c->nj + 1) * c->nvox, c->d_j1, (size_t)3 * c->nvox * sizeof(double), k, c->stream));
     }
     if (where == PORTA_HOST) CK(cudaStreamSynchronize(c->stream));
     return PORTA_OK;
@@ -1252,6 +1268,8 @@ int porta_set_partial(porta_ctx *c, const void *in, int where)
         const double *i = (const double *)in;
         CK(cudaMemcpyAsync(c->d_jkq, i, (size_t)c->nj * c->nvox * sizeof(double), k, c->stream));
         CK(cudaMemcpyAsync(c->d_lstar, i + (size_t)c->nj * c->nvox, (size_t)c->nvox * sizeof(double), k, c->stream));
+        if (c->d_j1)
+            CK(cudaMemcpyAsync(c->d_j1, i + (size_t)(c->nj + 1) * c->nvox, (size_t)3 * c->nvox * sizeof(double), k, c->stream));
     }
     if (where == PORTA_HOST) CK(cudaStreamSynchronize(c->stream));
     c->have_jkq = true;

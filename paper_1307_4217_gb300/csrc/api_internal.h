@@ -144,12 +144,12 @@ void launch_caps(const porta_ctx *c, int C, int &ring_plane, int &ipts_max, bool
             ipts_max = std::max(ipts_max, rmax * b.nx);
             continue;
         }
-        // with dichroism the slots of a second ring (eta_U / eta_I per node) follow the node ring;
-        // the biquadratic stencils need two halo rows on each side instead of one
+        // with dichroism the slots of a second ring follow the node ring (eta_U / eta_I and the
+        // two orientation terms, 3 words per node); an explicit medium keeps K'/eta_I there
+        // (6 words per node); the biquadratic stencils need two halo rows on each side instead of one
         const int gchunk = c->interp == 2 && !c->d_kexpl ? (rmax + 4) * b.nx : chunk;
-        // an explicit medium keeps K'/eta_I (6 words per node) in the second ring
-        const int dchunks = dich ? (chunk * (int)sizeof(Real) + 15) / 16
-                                 : (c->d_kexpl ? (6 * ((chunk * (int)sizeof(Real) + 15) / 16 * 16) + 15) / 16 : 0);
+        const int dwords = dich ? 3 : (c->d_kexpl ? 6 : 0);
+        const int dchunks = (dwords * ((chunk * (int)sizeof(Real) + 15) / 16 * 16) + 15) / 16;
         ring_plane = std::max(ring_plane, nch * gchunk + dchunks);
         ipts_max = std::max(ipts_max, rmax * b.nx);
     }
@@ -185,7 +185,8 @@ int choose_launch(porta_ctx *c, LaunchCfg &best, int force_c, int force_f, int n
 {
     const int NU = nnu > 0 ? nnu : c->n_nu;     // frequencies swept
     if (force_f > NU) force_f = NU;
-    const int NA = NS == 1 ? 2 : 4;
+    // accumulated quantities per point (Stokes V too for the polarized lines of a multilevel atom)
+    const int NA = NS == 1 ? 2 : (c->d_dich ? 5 : 4);
     double best_cost = 1e300;
     best = LaunchCfg{};
     const int ny_max = max_ny(c);
@@ -220,7 +221,7 @@ int choose_launch(porta_ctx *c, LaunchCfg &best, int force_c, int force_f, int n
         // threads: the strip's points times the frequency lanes they can use, whole warps, 64..512
         const int threads = std::min(kThreads, std::max(64, (ipts_max * F + 31) / 32 * 32));
         const int smem = jk ? jsweep_smem_bytes<Real, NS>(ring_plane, ipts_max, F, threads)
-                            : sweep_smem_bytes<Real, NS>(ring_plane, ipts_max, F, threads);
+                            : sweep_smem_bytes<Real, NS>(ring_plane, ipts_max, F, threads, NA);
         if (smem > kSmemLimit + 16) continue;
         int act = 0;
         if ((jk ? jsweep_max_active_clusters<Real, NS>(C, smem, threads, &act)

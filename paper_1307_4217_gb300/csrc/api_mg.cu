@@ -138,8 +138,8 @@ cudaError_t mg_rho_changed(porta_ctx *L)
 cudaError_t mg_apply(porta_ctx *L, double alpha, const double *add, int with_f, double *out)
 {
     if (L->ml && L->ml->pol)
-        return run_mlpol_apply(L->ml->mc, L->ml->dev, L->ml->nvox1, L->ml->d_kT, L->d_jkq, L->d_b, L->ml->d_x, alpha, add,
-                               with_f, out, L->stream);
+        return run_mlpol_apply(L->ml->mc, L->ml->dev, L->ml->nvox1, L->ml->d_kT, L->d_jkq, L->d_j1, L->d_b, L->ml->d_x,
+                               alpha, add, with_f, out, L->stream);
     if (L->ml)
         return run_ml_apply(L->ml->mc, L->ml->nvox1, L->ml->d_kT, L->d_jkq, L->ml->d_pops, alpha, add, with_f, out,
                             L->stream);
@@ -155,7 +155,7 @@ int mg_jacobi(porta_ctx *L, const double *src, int n)
         if (rc) return rc;
         cudaError_t e;
         if (L->ml) {
-            e = L->ml->pol ? run_mlpol_see(L->ml->mc, L->ml->dev, L->ml->nvox1, L->ml->d_kT, L->d_jkq, L->d_lstar, L->d_b,
+            e = L->ml->pol ? run_mlpol_see(L->ml->mc, L->ml->dev, L->ml->nvox1, L->ml->d_kT, L->d_jkq, L->d_j1, L->d_lstar, L->d_b,
                                            L->ml->d_x, L->d_resid, L->ml->d_bad, L->stream, src)
                            : run_ml_see(L->ml->mc, L->ml->nvox1, L->ml->d_kT, L->d_jkq, L->d_lstar, L->ml->d_pops, L->d_resid,
                                         L->ml->d_bad, L->stream, src);

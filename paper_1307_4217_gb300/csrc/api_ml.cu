@@ -142,21 +142,20 @@ int porta_ml_create(const porta_grid *g, const porta_ml_atom *a, const porta_qua
         m->pol = true;
         m->tab = tab;
         m->nunk = tab.nunk;
-        const size_t ni = tab.pop_idx.size() + tab.up2.size() + tab.cell_rc.size() + tab.cell_start.size() +
-                          tab.ent_src.size() + tab.act.size() + tab.inact.size() + tab.apop.size() + tab.lo2.size();
-        const size_t nd = tab.w2.size() + tab.trace.size() + tab.ent_coef.size() + tab.w2lo.size();
+        const std::vector<int> *iv[6] = {&tab.pop_idx, &tab.upk, &tab.lok, &tab.cell_rc, &tab.cell_start, &tab.ent_src};
+        const std::vector<double> *dv[4] = {&tab.wu, &tab.wl, &tab.trace, &tab.ent_coef};
+        size_t ni = 0, nd = 0;
+        for (auto *p : iv) ni += p->size();
+        for (auto *p : dv) nd += p->size();
         const size_t ibytes = (ni * sizeof(int) + 7) / 8 * 8;
         std::vector<char> h(ibytes + nd * sizeof(double));
         int *ip = (int *)h.data();
         double *dp = (double *)(h.data() + ibytes);
-        size_t io[9], doff[4], k = 0, kd = 0;
-        const std::vector<int> *iv[9] = {&tab.pop_idx, &tab.up2, &tab.cell_rc, &tab.cell_start, &tab.ent_src,
-                                         &tab.act, &tab.inact, &tab.apop, &tab.lo2};
-        for (int q2 = 0; q2 < 9; ++q2) {
+        size_t io[6], doff[4], k = 0, kd = 0;
+        for (int q2 = 0; q2 < 6; ++q2) {
             io[q2] = k;
             for (int x : *iv[q2]) ip[k++] = x;
         }
-        const std::vector<double> *dv[4] = {&tab.w2, &tab.trace, &tab.ent_coef, &tab.w2lo};
         for (int q2 = 0; q2 < 4; ++q2) {
             doff[q2] = kd;
             for (double x : *dv[q2]) dp[kd++] = x;
@@ -164,8 +163,23 @@ int porta_ml_create(const porta_grid *g, const porta_ml_atom *a, const porta_qua
         e = pmalloc(&m->d_tab, h.size());
         if (e == cudaSuccess) e = cudaMemcpy(m->d_tab, h.data(), h.size(), cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = dalloc(&m->d_x, (size_t)m->nvox1 * tab.nunk);
-        if (e == cudaSuccess) e = pmalloc(&c->d_dich, (size_t)5 * c->nvox * c->rsz);
-        if (e == cudaSuccess) e = cudaMemset(c->d_dich, 0, (size_t)5 * c->nvox * c->rsz);
+        // line polarization terms of the sweep ([11][line voxel]), J^1_Q and w_m T^1_Q(V, Omega_m)
+        // = w_m sqrt(3/2) Omega_Q per ray (T10 = sqrt(3/2) Omega_z, T11 = -sqrt(3/4) (Omega_x + i Omega_y))
+        if (e == cudaSuccess) e = pmalloc(&c->d_dich, (size_t)11 * c->nvox * c->rsz);
+        if (e == cudaSuccess) e = cudaMemset(c->d_dich, 0, (size_t)11 * c->nvox * c->rsz);
+        if (e == cudaSuccess) e = dalloc(&c->d_j1, (size_t)3 * c->nvox);
+        if (e == cudaSuccess) e = cudaMemset(c->d_j1, 0, (size_t)3 * c->nvox * sizeof(double));
+        if (e == cudaSuccess) e = dalloc(&c->d_tw1, (size_t)3 * c->nray);
+        if (e == cudaSuccess) {
+            std::vector<double> tw1((size_t)3 * c->nray);
+            for (int r = 0; r < c->nray; ++r) {
+                const double st = std::sqrt(1.0 - c->mu[r] * c->mu[r]);
+                tw1[3 * r] = c->w[r] * std::sqrt(1.5) * c->mu[r];
+                tw1[3 * r + 1] = -c->w[r] * std::sqrt(0.75) * st * std::cos(c->chi[r]);
+                tw1[3 * r + 2] = -c->w[r] * std::sqrt(0.75) * st * std::sin(c->chi[r]);
+            }
+            e = cudaMemcpy(c->d_tw1, tw1.data(), tw1.size() * sizeof(double), cudaMemcpyHostToDevice);
+        }
         const int *di = (const int *)m->d_tab;
         const double *dd = (const double *)((const char *)m->d_tab + ibytes);
         MlPolDev &d = m->dev;
@@ -174,12 +188,9 @@ int porta_ml_create(const porta_grid *g, const porta_ml_atom *a, const porta_qua
         d.ncell = (int)tab.cell_start.size() - 1;
         d.row0 = tab.row0;
         d.src_j = tab.src_j; d.src_b = tab.src_b; d.src_clu = tab.src_clu; d.src_pop = tab.src_pop; d.src_spop = tab.src_spop;
-        d.pop_idx = di + io[0]; d.up2 = di + io[1]; d.cell_rc = di + io[2]; d.cell_start = di + io[3]; d.ent_src = di + io[4];
-        d.act = di + io[5]; d.inact = di + io[6]; d.apop = di + io[7]; d.lo2 = di + io[8];
-        d.w2lo = dd + doff[3];
-        d.nact = tab.nact;
-        d.ninact = (int)tab.inact.size();
-        d.w2 = dd + doff[0]; d.trace = dd + doff[1]; d.ent_coef = dd + doff[2];
+        d.pop_idx = di + io[0]; d.upk = di + io[1]; d.lok = di + io[2];
+        d.cell_rc = di + io[3]; d.cell_start = di + io[4]; d.ent_src = di + io[5];
+        d.wu = dd + doff[0]; d.wl = dd + doff[1]; d.trace = dd + doff[2]; d.ent_coef = dd + doff[3];
     }
     if (e != cudaSuccess) {
         porta_destroy(c);
@@ -393,8 +404,21 @@ int porta_ml_formal_solve(porta_ctx *c, double *jbar, double *lstar, int where)
     if (!m) return fail(c, PORTA_EINVAL, "ml_formal_solve: not a multilevel context");
     if (!m->have_atm || !m->have_pops) return fail(c, PORTA_ESTATE, "ml_formal_solve: atmosphere or populations not set");
     int rc = porta_formal_solve(c);
-    if (rc == PORTA_OK) rc = porta_accumulate_jkq(c, jbar, lstar, where);
-    return rc;
+    if (rc != PORTA_OK) return rc;
+    if (!m->pol) return porta_accumulate_jkq(c, jbar, lstar, where);
+    // polarized lines: jbar [line voxel][9] in the Kr = 0, 1, 2 layout
+    rc = porta_accumulate_jkq(c, nullptr, lstar, where);
+    if (rc != PORTA_OK || !jbar) return rc;
+    double *d9 = jbar;
+    if (where == PORTA_HOST) CK(dalloc(&d9, (size_t)9 * c->nvox));
+    cudaError_t e = run_mlpol_jbar9(c->nvox, c->d_jkq, c->d_j1, d9, c->stream);
+    if (e == cudaSuccess && where == PORTA_HOST) {
+        e = cudaMemcpyAsync(jbar, d9, (size_t)9 * c->nvox * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    }
+    if (where == PORTA_HOST) pfree(d9);
+    if (e != cudaSuccess) return fail(c, PORTA_ECUDA, std::string("ml_formal_solve: ") + cudaGetErrorString(e));
+    return PORTA_OK;
 }
 
 int porta_ml_see_update(porta_ctx *c, double *max_change)

@@ -14,11 +14,12 @@
 //
 // Device: mlpol_prepare_kernel writes each line's opacity, Planck function
 // and emission multipoles S^K_Q = S_line w^(K) conj(rho^K_Q / rho^0_0)(J_u)
-// (K = 0, 2) into the sweep arrays of the line's box (the polarized two-level
-// formal solver then solves every line); mlpol_see_kernel assembles the
-// real system of one voxel per warp in shared memory over the even-K
-// multipoles (43 of the 69 for J = 0, 1, 2, 1, 2: without J^1_Q the odd-K
-// ones decouple with a zero solution), replaces the row of level 0's population by the trace
+// (K = 0, 1, 2) and its dichroism multipoles D^K_Q (K = 1, 2) into the sweep
+// arrays of the line's box (the polarized two-level formal solver, with the
+// orientation terms in eps_V and eta_V, then solves every line; J^1_Q comes
+// from Stokes V); mlpol_see_kernel assembles the real system of one voxel per
+// warp in shared memory over all multipoles (69 for J = 0, 1, 2, 1, 2),
+// replaces the row of level 0's population by the trace
 // sum_J sqrt(2J+1) rho^0_0(J) = 1, and solves it in FP64 in two blocks: the
 // population rows (preconditioned) with the K > 0 multipoles at their old
 // values, then the K > 0 rows (plain rates) with the new populations, by
@@ -150,18 +151,18 @@ int mlpol_tables(const std::vector<double> &J, const std::vector<double> &E, con
     }
     std::vector<double> g(nlev);
     for (int i = 0; i < nlev; ++i) g[i] = 2.0 * J[i] + 1.0;
-    // source layout: 0 const, 1 + 6 li + c (J real layout J00, J20, Re J21, Im J21, Re J22, Im J22),
-    // then B (3), C_lu per line, -Lambda* S_old per line, -Lambda* per line
+    // source layout: 0 const, 1 + 9 li + c (J real layout J00, J10, Re J11, Im J11, J20, Re J21,
+    // Im J21, Re J22, Im J22), then B (3), C_lu per line, -Lambda* S_old per line, -Lambda* per line
     t.nline = nline;
     t.src_j = 1;
-    t.src_b = 1 + 6 * nline;
+    t.src_b = 1 + 9 * nline;
     t.src_clu = t.src_b + 3;
     t.src_pop = t.src_clu + nline;
     t.src_spop = t.src_pop + nline;
     t.nsrc = t.src_spop + nline;
     std::vector<CMat> G(t.nsrc, CMat((size_t)n * n, 0.0));
     auto at = [n](CMat &M, int a, int b) -> cplx & { return M[(size_t)a * n + b]; };
-    // radiative matrices per (Kr, Qr), Kr = 0, 2 (the transfer gives no J^1_Q)
+    // radiative matrices per (Kr, Qr), Kr = 0, 1, 2
     for (int li = 0; li < nline; ++li) {
         const int u = up[li], l = lo[li];
         const double Ju = J[u], Jl = J[l];
@@ -181,7 +182,7 @@ int mlpol_tables(const std::vector<double> &J, const std::vector<double> &E, con
                 for (int Kl = 0; Kl <= two(Jl); ++Kl)
                     for (int Ql = -Kl; Ql <= Kl; ++Ql) {
                         const int b = cidx[ckey(l, Kl, Ql)];
-                        for (int Kr = 0; Kr <= 2; Kr += 2)
+                        for (int Kr = 0; Kr <= 2; ++Kr)
                             for (int Qr = -Kr; Qr <= Kr; ++Qr) {
                                 const double v = (2 * Jl + 1) * Blu * std::sqrt(3.0 * (2 * K + 1) * (2 * Kl + 1) * (2 * Kr + 1)) *
                                                  sgn(Kl + Ql) * W9(Ju, Jl, 1, Ju, Jl, 1, K, Kl, Kr) * W3(K, Kl, Kr, -Q, Ql, -Qr);
@@ -195,7 +196,7 @@ int mlpol_tables(const std::vector<double> &J, const std::vector<double> &E, con
                 for (int Kp = 0; Kp <= two(Ju); ++Kp)
                     for (int Qp = -Kp; Qp <= Kp; ++Qp) {
                         const int b = cidx[ckey(u, Kp, Qp)];
-                        for (int Kr = 0; Kr <= 2; Kr += 2)
+                        for (int Kr = 0; Kr <= 2; ++Kr)
                             for (int Qr = -Kr; Qr <= Kr; ++Qr) {
                                 if ((K + Kp + Kr) % 2) continue;
                                 const double v = (2 * Ju + 1) * Bul * std::sqrt(3.0 * (2 * K + 1) * (2 * Kp + 1) * (2 * Kr + 1)) *
@@ -218,7 +219,7 @@ int mlpol_tables(const std::vector<double> &J, const std::vector<double> &E, con
                 for (int Ku = 0; Ku <= two(Ju); ++Ku)
                     for (int Qu = -Ku; Qu <= Ku; ++Qu) {
                         const int b = cidx[ckey(u, Ku, Qu)];
-                        for (int Kr = 0; Kr <= 2; Kr += 2)
+                        for (int Kr = 0; Kr <= 2; ++Kr)
                             for (int Qr = -Kr; Qr <= Kr; ++Qr) {
                                 const double v = (2 * Ju + 1) * Bul * std::sqrt(3.0 * (2 * K + 1) * (2 * Ku + 1) * (2 * Kr + 1)) *
                                                  sgn(Kr + Ku + Qu) * W9(Ju, Jl, 1, Ju, Jl, 1, Ku, K, Kr) * W3(K, Ku, Kr, -Q, Qu, -Qr);
@@ -230,7 +231,7 @@ int mlpol_tables(const std::vector<double> &J, const std::vector<double> &E, con
                 for (int Kp = 0; Kp <= two(Jl); ++Kp)
                     for (int Qp = -Kp; Qp <= Kp; ++Qp) {
                         const int b = cidx[ckey(l, Kp, Qp)];
-                        for (int Kr = 0; Kr <= 2; Kr += 2)
+                        for (int Kr = 0; Kr <= 2; ++Kr)
                             for (int Qr = -Kr; Qr <= Kr; ++Qr) {
                                 if ((K + Kp + Kr) % 2) continue;
                                 const double v = (2 * Jl + 1) * Blu * std::sqrt(3.0 * (2 * K + 1) * (2 * Kp + 1) * (2 * Kr + 1)) *
@@ -255,13 +256,17 @@ int mlpol_tables(const std::vector<double> &J, const std::vector<double> &E, con
             if (it == Mr.end()) return;
             for (size_t e = 0; e < it->second.size(); ++e) G[s][e] += f * it->second[e];
         };
-        const int s0 = t.src_j + 6 * li;
+        // (J^K_-Q = (-1)^Q conj J^K_Q: J^K_{+-1} = +-Re + i Im, J^2_{+-2} = Re +- i Im)
+        const int s0 = t.src_j + 9 * li;
         addJ(s0 + 0, 0, 0, 1.0);
-        addJ(s0 + 1, 2, 0, 1.0);
-        addJ(s0 + 2, 2, 1, 1.0); addJ(s0 + 2, 2, -1, -1.0);
-        addJ(s0 + 3, 2, 1, cplx(0, 1)); addJ(s0 + 3, 2, -1, cplx(0, 1));
-        addJ(s0 + 4, 2, 2, 1.0); addJ(s0 + 4, 2, -2, 1.0);
-        addJ(s0 + 5, 2, 2, cplx(0, 1)); addJ(s0 + 5, 2, -2, cplx(0, -1));
+        addJ(s0 + 1, 1, 0, 1.0);
+        addJ(s0 + 2, 1, 1, 1.0); addJ(s0 + 2, 1, -1, -1.0);
+        addJ(s0 + 3, 1, 1, cplx(0, 1)); addJ(s0 + 3, 1, -1, cplx(0, 1));
+        addJ(s0 + 4, 2, 0, 1.0);
+        addJ(s0 + 5, 2, 1, 1.0); addJ(s0 + 5, 2, -1, -1.0);
+        addJ(s0 + 6, 2, 1, cplx(0, 1)); addJ(s0 + 6, 2, -1, cplx(0, 1));
+        addJ(s0 + 7, 2, 2, 1.0); addJ(s0 + 7, 2, -2, 1.0);
+        addJ(s0 + 8, 2, 2, cplx(0, 1)); addJ(s0 + 8, 2, -2, cplx(0, -1));
         G[t.src_pop + li] = Mpop;
         G[t.src_spop + li] = Mspop;
     }
@@ -284,39 +289,22 @@ int mlpol_tables(const std::vector<double> &J, const std::vector<double> &E, con
             at(G[t.src_b + 1], a, b) += cplx(-wj * f, 0);     // i * i = -1
         }
     }
-    // real system rows: (complex row, part); the even-K unknowns (compact numbering); trace row
+    // real system rows: (complex row, part); trace row
     t.nunk = nr;
-    std::vector<int> cmp(nr, -1);
-    t.act.clear();
-    t.inact.clear();
-    for (int k = 0; k < nr; ++k) {
-        if (rK[k] % 2 == 0) {
-            cmp[k] = (int)t.act.size();
-            t.act.push_back(k);
-        } else {
-            t.inact.push_back(k);
-        }
-    }
-    t.nact = (int)t.act.size();
-    t.trace.assign(t.nact, 0.0);
+    t.trace.assign(nr, 0.0);
     t.pop_idx.assign(nlev, -1);
-    t.apop.assign(nlev, -1);
     t.row0 = -1;
     for (int k = 0; k < nr; ++k)
         if (rK[k] == 0) {
-            t.trace[cmp[k]] = std::sqrt(g[rl[k]]);
+            t.trace[k] = std::sqrt(g[rl[k]]);
             t.pop_idx[rl[k]] = k;
-            t.apop[rl[k]] = cmp[k];
-            if (rl[k] == 0) t.row0 = cmp[k];
+            if (rl[k] == 0) t.row0 = k;
         }
     // sparse cells of the real matrices R_s = select(G_s C)
     std::map<long long, std::vector<std::pair<int, double>>> cells;
-    const int na = t.nact;
-    double rate_scale = 0.0;
-    for (int li = 0; li < nline; ++li) rate_scale += A[li];
     for (int s = 0; s < t.nsrc; ++s)
         for (int row = 0; row < nr; ++row) {
-            if (cmp[row] == t.row0) continue;
+            if (row == t.row0) continue;
             const int ci = cidx[ckey(rl[row], rK[row], rQ[row])];
             for (int col = 0; col < nr; ++col) {
                 cplx y = 0.0;
@@ -326,57 +314,46 @@ int mlpol_tables(const std::vector<double> &J, const std::vector<double> &E, con
                 }
                 const double v = rp[row] == 0 ? y.real() : y.imag();
                 if (std::abs(v) == 0.0) continue;
-                // odd and even K couple only through J^1_Q, which is not carried (the 9j
-                // symbols with two equal rows vanish for odd K + K' + Kr): what is left is
-                // rounding of the Racah sums
-                if ((rK[row] + rK[col]) % 2) {
-                    if (std::abs(v) > 1e-12 * rate_scale) return -2;
-                    continue;
-                }
-                if (cmp[row] < 0) continue;          // odd-K block: homogeneous, solution zero
-                cells[(long long)cmp[row] * na + cmp[col]].emplace_back(s, v);
+                cells[(long long)row * nr + col].emplace_back(s, v);
             }
         }
     t.cell_rc.clear(); t.cell_start.assign(1, 0); t.ent_src.clear(); t.ent_coef.clear();
     for (auto &c : cells) {
-        t.cell_rc.push_back((int)(c.first / na));
-        t.cell_rc.push_back((int)(c.first % na));
+        t.cell_rc.push_back((int)(c.first / nr));
+        t.cell_rc.push_back((int)(c.first % nr));
         for (auto &e : c.second) {
             t.ent_src.push_back(e.first);
             t.ent_coef.push_back(e.second);
         }
         t.cell_start.push_back((int)t.ent_src.size());
     }
-    // emission multipoles of each line: rho^0_0 and rho^2_Q (Q = 0, 1 re/im, 2 re/im) of the upper
-    // level; dichroism: the same of the lower level
-    t.w2.assign(nline, 0.0);
-    t.up2.assign(6 * (size_t)nline, -1);
-    t.w2lo.assign(nline, 0.0);
-    t.lo2.assign(6 * (size_t)nline, -1);
+    // per line the multipoles rho^0_0, rho^1_Q, rho^2_Q of the upper level (emission; stimulated
+    // emission in the dichroism) and of the lower level (absorption), with
+    // w^(K)_{J J'} = (-1)^(1+J+J') sqrt(3(2J+1)) {1 1 K; J J J'}
+    t.upk.assign(9 * (size_t)nline, -1);
+    t.lok.assign(9 * (size_t)nline, -1);
+    t.wu.assign(2 * (size_t)nline, 0.0);
+    t.wl.assign(2 * (size_t)nline, 0.0);
+    auto ridx = [&](int i, int K, int Q, int p) {
+        for (int k = 0; k < nr; ++k)
+            if (rl[k] == i && rK[k] == K && rQ[k] == Q && rp[k] == p) return k;
+        return -1;
+    };
+    auto fill9 = [&](int i, int *ix) {
+        const int KQp[9][3] = {{0, 0, 0}, {1, 0, 0}, {1, 1, 0}, {1, 1, 1}, {2, 0, 0},
+                               {2, 1, 0}, {2, 1, 1}, {2, 2, 0}, {2, 2, 1}};
+        for (int c = 0; c < 9; ++c)
+            if (KQp[c][0] <= two(J[i])) ix[c] = ridx(i, KQp[c][0], KQp[c][1], KQp[c][2]);
+    };
     for (int li = 0; li < nline; ++li) {
         const int u = up[li], l = lo[li];
-        auto ridx = [&](int i, int K, int Q, int p) {
-            for (int k = 0; k < nr; ++k)
-                if (rl[k] == i && rK[k] == K && rQ[k] == Q && rp[k] == p) return k;
-            return -1;
-        };
-        t.up2[6 * li] = ridx(u, 0, 0, 0);
-        t.lo2[6 * li] = ridx(l, 0, 0, 0);
-        if (two(J[l]) >= 2) {
-            t.w2lo[li] = sgn(1 + J[l] + J[u]) * std::sqrt(3.0 * (2 * J[l] + 1)) * W6(1, 1, 2, J[l], J[l], J[u]);
-            t.lo2[6 * li + 1] = ridx(l, 2, 0, 0);
-            t.lo2[6 * li + 2] = ridx(l, 2, 1, 0);
-            t.lo2[6 * li + 3] = ridx(l, 2, 1, 1);
-            t.lo2[6 * li + 4] = ridx(l, 2, 2, 0);
-            t.lo2[6 * li + 5] = ridx(l, 2, 2, 1);
-        }
-        if (two(J[u]) >= 2) {
-            t.w2[li] = sgn(1 + J[l] + J[u]) * std::sqrt(3.0 * (2 * J[u] + 1)) * W6(1, 1, 2, J[u], J[u], J[l]);
-            t.up2[6 * li + 1] = ridx(u, 2, 0, 0);
-            t.up2[6 * li + 2] = ridx(u, 2, 1, 0);
-            t.up2[6 * li + 3] = ridx(u, 2, 1, 1);
-            t.up2[6 * li + 4] = ridx(u, 2, 2, 0);
-            t.up2[6 * li + 5] = ridx(u, 2, 2, 1);
+        fill9(u, &t.upk[9 * (size_t)li]);
+        fill9(l, &t.lok[9 * (size_t)li]);
+        for (int K = 1; K <= 2; ++K) {
+            if (two(J[u]) >= K)
+                t.wu[2 * li + K - 1] = sgn(1 + J[l] + J[u]) * std::sqrt(3.0 * (2 * J[u] + 1)) * W6(1, 1, K, J[u], J[u], J[l]);
+            if (two(J[l]) >= K)
+                t.wl[2 * li + K - 1] = sgn(1 + J[l] + J[u]) * std::sqrt(3.0 * (2 * J[l] + 1)) * W6(1, 1, K, J[l], J[l], J[u]);
         }
     }
     return 0;
@@ -391,7 +368,7 @@ inline int nblk(long long n, int t) { return (int)((n + t - 1) / t); }
 template <typename Real>
 __global__ void mlpol_prepare_kernel(const MlConst mc, MlPolDev T, long long nvox1, const double *x, const double *chis,
                                      const double *kT, Real *chi_out, Real *bpl_out, Real *S_out, double *S64_out,
-                                     Real *dich_out, unsigned long long *bad)
+                                     Real *pol_out, unsigned long long *bad)
 {
     const long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (v >= nvox1) return;
@@ -409,51 +386,62 @@ __global__ void mlpol_prepare_kernel(const MlConst mc, MlPolDev T, long long nvo
         nbad += !(op > 0.0 && op < 1e300) || !(fabs(S) < 1e300);
         chi_out[o] = (Real)op;
         bpl_out[o] = (Real)(mc.r3[k] / expm1(mc.dE[k] / t));
-        // S^K_Q = S w2 conj(rho^2_Q / rho^0_0)(upper), two-level real layout
-        double s6[6] = {S, 0, 0, 0, 0, 0};
-        const int *ix = T.up2 + 6 * k;
-        if (ix[1] >= 0) {
-            const double f = S * T.w2[k] / xv[ix[0]];
-            s6[1] = f * xv[ix[1]];
-            s6[2] = f * xv[ix[2]];
-            s6[3] = -f * xv[ix[3]];
-            s6[4] = f * xv[ix[4]];
-            s6[5] = -f * xv[ix[5]];
+        // S^K_Q = S w^(K) conj(rho^K_Q / rho^0_0)(upper): K = 0, 2 in the two-level real layout
+        // (S00, S20, Re/Im S21, Re/Im S22), K = 1 as (S10, Re S11, Im S11); conjugation
+        // negates the imaginary parts
+        const int *iu = T.upk + 9 * k, *il = T.lok + 9 * k;
+        const double *wu = T.wu + 2 * k, *wl = T.wl + 2 * k;
+        double s6[6] = {S, 0, 0, 0, 0, 0}, s3[3] = {0, 0, 0};
+        if (iu[4] >= 0) {
+            const double f = S * wu[1] / xv[iu[0]];
+            s6[1] = f * xv[iu[4]];
+            s6[2] = f * xv[iu[5]];
+            s6[3] = -f * xv[iu[6]];
+            s6[4] = f * xv[iu[7]];
+            s6[5] = -f * xv[iu[8]];
+        }
+        if (iu[1] >= 0) {
+            const double f = S * wu[0] / xv[iu[0]];
+            s3[0] = f * xv[iu[1]];
+            s3[1] = f * xv[iu[2]];
+            s3[2] = -f * xv[iu[3]];
         }
         for (int c = 0; c < 6; ++c) {
             S64_out[o * 6 + c] = s6[c];
             S_out[c * nvox + o] = (Real)s6[c];
         }
-        // dichroism: D^2_Q = conj([B_lu sqrt(2Jl+1) w2lo rho^2_Q(l) - B_ul sqrt(2Ju+1) w2 rho^2_Q(u)]
-        //                        / [B_lu sqrt(2Jl+1) rho^0_0(l) - B_ul sqrt(2Ju+1) rho^0_0(u)])
-        if (dich_out) {
-            const int *il = T.lo2 + 6 * k;
-            const double al = mc.Blu[k] * sqrt(mc.g[l]), au = mc.Bul[k] * sqrt(mc.g[u]);
-            const double den = al * xv[il[0]] - au * xv[ix[0]];
-            double d5[5] = {0, 0, 0, 0, 0};
-            for (int c = 0; c < 5; ++c) {
-                double num = 0.0;
-                if (il[1 + c] >= 0) num += al * T.w2lo[k] * xv[il[1 + c]];
-                if (ix[1 + c] >= 0) num -= au * T.w2[k] * xv[ix[1 + c]];
-                d5[c] = num / den;
-            }
-            // conjugation: the imaginary parts change sign
-            d5[2] = -d5[2];
-            d5[4] = -d5[4];
-            for (int c = 0; c < 5; ++c) dich_out[c * nvox + o] = (Real)d5[c];
+        // dichroism: D^K_Q = conj([(-1)^K B_lu sqrt(2Jl+1) w^(K)(l) rho^K_Q(l) - B_ul sqrt(2Ju+1) w^(K)(u) rho^K_Q(u)]
+        //                        / [B_lu sqrt(2Jl+1) rho^0_0(l) - B_ul sqrt(2Ju+1) rho^0_0(u)]),
+        // K = 2 (D20, Re/Im D21, Re/Im D22) then K = 1 (D10, Re/Im D11)
+        const double al = mc.Blu[k] * sqrt(mc.g[l]), au = mc.Bul[k] * sqrt(mc.g[u]);
+        const double den = al * xv[il[0]] - au * xv[iu[0]];
+        double d8[8];
+        for (int c = 0; c < 8; ++c) {
+            const int j = c < 5 ? 4 + c : c - 4;           // component in the Kr = 0, 1, 2 layout
+            const int K = c < 5 ? 2 : 1;
+            const double sa = K == 2 ? 1.0 : -1.0;
+            double num = 0.0;
+            if (il[j] >= 0) num += sa * al * wl[K - 1] * xv[il[j]];
+            if (iu[j] >= 0) num -= au * wu[K - 1] * xv[iu[j]];
+            d8[c] = num / den;
         }
+        d8[2] = -d8[2];
+        d8[4] = -d8[4];
+        d8[7] = -d8[7];
+        for (int c = 0; c < 8; ++c) pol_out[c * nvox + o] = (Real)d8[c];
+        for (int c = 0; c < 3; ++c) pol_out[(8 + c) * nvox + o] = (Real)s3[c];
     }
     if (nbad) atomicAdd(bad, (unsigned long long)nbad);
 }
 
-// the real system of voxel v over the even-K unknowns into A [N][N + 1] (row of
-// level 0's population = the trace), sources into s; xo holds the old unknowns;
-// lstar null: the plain rates (no preconditioning)
+// the real system of voxel v into A [N][N + 1] (row of level 0's population =
+// the trace), sources into s; xo holds the old unknowns; lstar null: the plain
+// rates (no preconditioning)
 __device__ void mlpol_assemble(const MlConst &mc, const MlPolDev &T, long long nvox1, long long v, const double *kT,
-                               const double *jkq, const double *lstar, const double *bvec, const double *xo,
-                               double *A, double *s, int lane)
+                               const double *jkq, const double *j1, const double *lstar, const double *bvec,
+                               const double *xo, double *A, double *s, int lane)
 {
-    const int N = T.nact, N1 = N + 1;
+    const int N = T.nunk, N1 = N + 1;
     if (lane == 0) {
         s[0] = 1.0;
         s[T.src_b] = bvec[v];
@@ -463,10 +451,13 @@ __device__ void mlpol_assemble(const MlConst &mc, const MlPolDev &T, long long n
     for (int k = lane; k < mc.nline; k += 32) {
         const int u = mc.up[k], l = mc.lo[k];
         const long long o = (long long)k * nvox1 + v;
-        for (int c = 0; c < 6; ++c) s[T.src_j + 6 * k + c] = jkq[o * 6 + c];
+        double *sj = s + T.src_j + 9 * k;
+        sj[0] = jkq[o * 6];
+        for (int c = 0; c < 3; ++c) sj[1 + c] = j1[o * 3 + c];
+        for (int c = 1; c < 6; ++c) sj[3 + c] = jkq[o * 6 + c];
         s[T.src_clu + k] = mc.g[u] / mc.g[l] * exp(-mc.dE[k] / kT[v]) * mc.Cul[k];
         if (lstar) {
-            const double nu = sqrt(mc.g[u]) * xo[T.apop[u]], nl = sqrt(mc.g[l]) * xo[T.apop[l]];
+            const double nu = sqrt(mc.g[u]) * xo[T.pop_idx[u]], nl = sqrt(mc.g[l]) * xo[T.pop_idx[l]];
             const double Sold = mc.r3[k] * nu / (nl * mc.g[u] / mc.g[l] - nu);
             const double ls = lstar[o];
             s[T.src_pop + k] = -ls * Sold;
@@ -491,43 +482,38 @@ __device__ void mlpol_assemble(const MlConst &mc, const MlPolDev &T, long long n
 // out = alpha A(x) + add + with_f e_row0 (full layout): A(x) the plain rate operator
 // with the trace row; one warp per voxel, shared memory as mlpol_see_kernel
 __global__ void mlpol_apply_kernel(const MlConst mc, MlPolDev T, long long nvox1, const double *kT, const double *jkq,
-                                   const double *bvec, const double *x, double alpha, const double *add, int with_f,
-                                   double *out)
+                                   const double *j1, const double *bvec, const double *x, double alpha, const double *add,
+                                   int with_f, double *out)
 {
     extern __shared__ double sm[];
-    const int N = T.nact, N1 = N + 1;
+    const int N = T.nunk, N1 = N + 1;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int per = N * N1 + 2 * N + T.nsrc;
     double *A = sm + (size_t)wib * per;
     double *xo = A + N * N1;
     double *s = xo + 2 * N;
     const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
-    const int row0full = T.act[T.row0];
     for (long long v = (long long)blockIdx.x * (blockDim.x >> 5) + wib; v < nvox1; v += nwarps) {
-        for (int k = lane; k < N; k += 32) xo[k] = x[v * T.nunk + T.act[k]];
+        for (int k = lane; k < N; k += 32) xo[k] = x[v * N + k];
         __syncwarp();
-        mlpol_assemble(mc, T, nvox1, v, kT, jkq, nullptr, bvec, xo, A, s, lane);
+        mlpol_assemble(mc, T, nvox1, v, kT, jkq, j1, nullptr, bvec, xo, A, s, lane);
         for (int r = lane; r < N; r += 32) {
             double y = 0.0;
             for (int c = 0; c < N; ++c) y += A[r * N1 + c] * xo[c];
-            const long long o = v * T.nunk + T.act[r];
-            out[o] = alpha * y + (add ? add[o] : 0.0) + (with_f && T.act[r] == row0full ? 1.0 : 0.0);
-        }
-        for (int k = lane; k < T.ninact; k += 32) {
-            const long long o = v * T.nunk + T.inact[k];
-            out[o] = add ? add[o] : 0.0;
+            const long long o = v * N + r;
+            out[o] = alpha * y + (add ? add[o] : 0.0) + (with_f && r == T.row0 ? 1.0 : 0.0);
         }
         __syncwarp();
     }
 }
 
-// one warp per voxel; shared memory per warp: A[nact][nact + 1], x_old, x_new, sources
+// one warp per voxel; shared memory per warp: A[nunk][nunk + 1], x_old, x_new, sources
 __global__ void mlpol_see_kernel(const MlConst mc, MlPolDev T, long long nvox1, const double *kT, const double *jkq,
-                                 const double *lstar, const double *bvec, const double *src, double *x,
+                                 const double *j1, const double *lstar, const double *bvec, const double *src, double *x,
                                  unsigned long long *resid, unsigned long long *bad)
 {
     extern __shared__ double sm[];
-    const int N = T.nact, N1 = N + 1;          // even-K unknowns (compact numbering)
+    const int N = T.nunk, N1 = N + 1;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int per = N * N1 + 2 * N + T.nsrc;
     double *A = sm + (size_t)wib * per;
@@ -537,21 +523,21 @@ __global__ void mlpol_see_kernel(const MlConst mc, MlPolDev T, long long nvox1, 
     const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
     double ch_max = 0.0;
     for (long long v = (long long)blockIdx.x * (blockDim.x >> 5) + wib; v < nvox1; v += nwarps) {
-        for (int k = lane; k < N; k += 32) xo[k] = x[v * T.nunk + T.act[k]];
+        for (int k = lane; k < N; k += 32) xo[k] = x[v * N + k];
         __syncwarp();
-        mlpol_assemble(mc, T, nvox1, v, kT, jkq, lstar, bvec, xo, A, s, lane);
+        mlpol_assemble(mc, T, nvox1, v, kT, jkq, j1, lstar, bvec, xo, A, s, lane);
         // right-hand side: (1, 0, ...) on the trace row, or the coarse-grid source
-        for (int r = lane; r < N; r += 32) A[r * N1 + N] = src ? src[v * T.nunk + T.act[r]] : (r == T.row0 ? 1.0 : 0.0);
+        for (int r = lane; r < N; r += 32) A[r * N1 + N] = src ? src[v * N + r] : (r == T.row0 ? 1.0 : 0.0);
         __syncwarp();
         // block 1: the population rows (K = 0) with the K > 0 multipoles at their old values
         const int L = mc.nlev;
         auto is_k0 = [&](int c) {
             for (int i = 0; i < L; ++i)
-                if (T.apop[i] == c) return true;
+                if (T.pop_idx[i] == c) return true;
             return false;
         };
         for (int i = 0; i < L; ++i) {
-            const int r = T.apop[i];
+            const int r = T.pop_idx[i];
             double acc = 0.0;
             for (int c = lane; c < N; c += 32)
                 if (!is_k0(c)) acc += A[r * N1 + c] * xo[c];
@@ -563,8 +549,8 @@ __global__ void mlpol_see_kernel(const MlConst mc, MlPolDev T, long long nvox1, 
         if (lane == 0) {
             double m[kMlMaxLevel][kMlMaxLevel + 1];
             for (int i = 0; i < L; ++i) {
-                for (int j = 0; j < L; ++j) m[i][j] = A[T.apop[i] * N1 + T.apop[j]];
-                m[i][L] = A[T.apop[i] * N1 + N];
+                for (int j = 0; j < L; ++j) m[i][j] = A[T.pop_idx[i] * N1 + T.pop_idx[j]];
+                m[i][L] = A[T.pop_idx[i] * N1 + N];
             }
             for (int c = 0; c < L && ok1; ++c) {
                 int p = c;
@@ -583,8 +569,8 @@ __global__ void mlpol_see_kernel(const MlConst mc, MlPolDev T, long long nvox1, 
             if (ok1)
                 for (int i = L - 1; i >= 0; --i) {
                     double acc = m[i][L];
-                    for (int j = i + 1; j < L; ++j) acc -= m[i][j] * xn[T.apop[j]];
-                    xn[T.apop[i]] = acc / m[i][i];
+                    for (int j = i + 1; j < L; ++j) acc -= m[i][j] * xn[T.pop_idx[j]];
+                    xn[T.pop_idx[i]] = acc / m[i][i];
                 }
         }
         ok1 = __shfl_sync(0xffffffffu, ok1, 0);
@@ -597,7 +583,7 @@ __global__ void mlpol_see_kernel(const MlConst mc, MlPolDev T, long long nvox1, 
             } else {
                 double bsub = 0.0;
                 for (int i = 0; i < L; ++i) {
-                    const int c = T.apop[i];
+                    const int c = T.pop_idx[i];
                     bsub += A[r * N1 + c] * (ok1 ? xn[c] : 1.0);
                     A[r * N1 + c] = 0.0;
                 }
@@ -645,7 +631,7 @@ __global__ void mlpol_see_kernel(const MlConst mc, MlPolDev T, long long nvox1, 
             }
             int nb = 0;
             for (int i = lane; i < mc.nlev; i += 32) {
-                const double p0 = xo[T.apop[i]], p1 = xn[T.apop[i]];
+                const double p0 = xo[T.pop_idx[i]], p1 = xn[T.pop_idx[i]];
                 nb += !(p1 > 0.0 && p1 < 1e300);
                 ch = fmax(ch, fabs(p1 - p0) / fabs(p0));
             }
@@ -654,8 +640,7 @@ __global__ void mlpol_see_kernel(const MlConst mc, MlPolDev T, long long nvox1, 
             if (nb) {
                 ok = false;
             } else {
-                for (int k = lane; k < N; k += 32) x[v * T.nunk + T.act[k]] = xn[k];
-                for (int k = lane; k < T.ninact; k += 32) x[v * T.nunk + T.inact[k]] = 0.0;
+                for (int k = lane; k < N; k += 32) x[v * N + k] = xn[k];
             }
         }
         if (!ok) {
@@ -674,10 +659,10 @@ __global__ void mlpol_see_kernel(const MlConst mc, MlPolDev T, long long nvox1, 
 template <typename Real>
 cudaError_t run_mlpol_prepare(const MlConst &mc, const MlPolDev &T, long long nvox1, const double *x, const double *chis,
                               const double *kT, Real *chi_out, Real *bpl_out, Real *S_out, double *S64_out,
-                              Real *dich_out, unsigned long long *bad, cudaStream_t st)
+                              Real *pol_out, unsigned long long *bad, cudaStream_t st)
 {
     mlpol_prepare_kernel<Real><<<nblk(nvox1, 128), 128, 0, st>>>(mc, T, nvox1, x, chis, kT, chi_out, bpl_out, S_out,
-                                                                 S64_out, dich_out, bad);
+                                                                 S64_out, pol_out, bad);
     return cudaGetLastError();
 }
 template cudaError_t run_mlpol_prepare<float>(const MlConst &, const MlPolDev &, long long, const double *, const double *,
@@ -689,7 +674,27 @@ template cudaError_t run_mlpol_prepare<double>(const MlConst &, const MlPolDev &
 
 size_t mlpol_see_smem(const MlPolDev &T, int warps)
 {
-    return sizeof(double) * (size_t)warps * ((size_t)T.nact * (T.nact + 1) + 2 * T.nact + T.nsrc);
+    return sizeof(double) * (size_t)warps * ((size_t)T.nunk * (T.nunk + 1) + 2 * T.nunk + T.nsrc);
+}
+
+namespace {
+
+__global__ void mlpol_jbar9_kernel(long long n, const double *jkq, const double *j1, double *jbar)
+{
+    const long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (o >= n) return;
+    double *b = jbar + o * 9;
+    b[0] = jkq[o * 6];
+    for (int c = 0; c < 3; ++c) b[1 + c] = j1[o * 3 + c];
+    for (int c = 1; c < 6; ++c) b[3 + c] = jkq[o * 6 + c];
+}
+
+}  // namespace
+
+cudaError_t run_mlpol_jbar9(long long n, const double *jkq, const double *j1, double *jbar, cudaStream_t st)
+{
+    mlpol_jbar9_kernel<<<nblk(n, 256), 256, 0, st>>>(n, jkq, j1, jbar);
+    return cudaGetLastError();
 }
 
 // max relative change of the populations between two vectors of unknowns
@@ -723,44 +728,47 @@ cudaError_t run_mlpol_change(const MlConst &mc, const MlPolDev &T, long long nvo
     return cudaGetLastError();
 }
 
-// persistent launch shape of the warp-per-voxel kernels
+// persistent launch shape of the warp-per-voxel kernels: up to 4 warps (voxels) per
+// block, as many as the block's shared memory holds
 template <typename K>
-static cudaError_t warp_launch_shape(K kernel, const MlPolDev &T, long long nvox1, int warps, size_t &smem, int &blocks)
+static cudaError_t warp_launch_shape(K kernel, const MlPolDev &T, long long nvox1, int &warps, size_t &smem, int &blocks)
 {
-    smem = mlpol_see_smem(T, warps);
-    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    int dev = 0, nsm = 0, per_sm = 1;
+    int dev = 0, nsm = 0, per_sm = 1, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    warps = 4;
+    while (warps > 1 && mlpol_see_smem(T, warps) > (size_t)optin) --warps;
+    smem = mlpol_see_smem(T, warps);
+    if (smem > (size_t)optin) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 32 * warps, smem);
     blocks = (int)std::max<long long>(1, std::min<long long>((nvox1 + warps - 1) / warps, (long long)std::max(1, per_sm) * nsm));
     return cudaSuccess;
 }
 
 cudaError_t run_mlpol_see(const MlConst &mc, const MlPolDev &T, long long nvox1, const double *kT, const double *jkq,
-                          const double *lstar, const double *bvec, double *x, unsigned long long *resid,
+                          const double *j1, const double *lstar, const double *bvec, double *x, unsigned long long *resid,
                           unsigned long long *bad, cudaStream_t st, const double *src)
 {
-    const int warps = 4;
+    int warps = 4, blocks = 1;
     size_t smem = 0;
-    int blocks = 1;
     cudaError_t e = warp_launch_shape(mlpol_see_kernel, T, nvox1, warps, smem, blocks);
     if (e != cudaSuccess) return e;
-    mlpol_see_kernel<<<blocks, 32 * warps, smem, st>>>(mc, T, nvox1, kT, jkq, lstar, bvec, src, x, resid, bad);
+    mlpol_see_kernel<<<blocks, 32 * warps, smem, st>>>(mc, T, nvox1, kT, jkq, j1, lstar, bvec, src, x, resid, bad);
     return cudaGetLastError();
 }
 
 cudaError_t run_mlpol_apply(const MlConst &mc, const MlPolDev &T, long long nvox1, const double *kT, const double *jkq,
-                            const double *bvec, const double *x, double alpha, const double *add, int with_f,
-                            double *out, cudaStream_t st)
+                            const double *j1, const double *bvec, const double *x, double alpha, const double *add,
+                            int with_f, double *out, cudaStream_t st)
 {
-    const int warps = 4;
+    int warps = 4, blocks = 1;
     size_t smem = 0;
-    int blocks = 1;
     cudaError_t e = warp_launch_shape(mlpol_apply_kernel, T, nvox1, warps, smem, blocks);
     if (e != cudaSuccess) return e;
-    mlpol_apply_kernel<<<blocks, 32 * warps, smem, st>>>(mc, T, nvox1, kT, jkq, bvec, x, alpha, add, with_f, out);
+    mlpol_apply_kernel<<<blocks, 32 * warps, smem, st>>>(mc, T, nvox1, kT, jkq, j1, bvec, x, alpha, add, with_f, out);
     return cudaGetLastError();
 }
 

@@ -207,7 +207,7 @@ int run(const porta_grid *g, const porta_atom *at, const porta_quad *q, const po
         const int fmax = (int)std::min<long long>(q->n_nu, (limit - ring - scratch) / per_nu);
         const int G = (q->n_nu + fmax - 1) / fmax, F = (q->n_nu + G - 1) / G;
         const int threads = std::min(512, std::max(64, (ipts * F + 31) / 32 * 32));
-        const int smem = sweep_smem_bytes<float, NS>(ring_plane, ipts, F, threads);
+        const int smem = sweep_smem_bytes<float, NS>(ring_plane, ipts, F, threads, NS == 1 ? 2 : 4);
         int act = 0;
         if (max_active_clusters<float, NS>(C, smem, threads, &act) != cudaSuccess) {
             cudaGetLastError();

@@ -133,7 +133,13 @@ struct porta_ctx {
     double *it_final = nullptr;
     int it_niter = 0, it_ckpt = 0;
     MlState *ml = nullptr;                 // multilevel atom (porta_ml_create), else null
-    void *d_dich = nullptr;                // Real [5][nvox] dichroism multipoles of polarized lines (null: none)
+    // polarized lines of a multilevel atom (null: none): Real [11][nvox] the dichroism multipoles
+    // D^2_Q (5), D^1_Q (3) and the orientation emission multipoles S^1_Q (3); the per-ray
+    // frequency integrals of Stokes V (Real [ray][nvox], allocated on first use), J^1_Q
+    // (FP64 [nvox][3]: J10, Re J11, Im J11) and the ray weights times T^1_Q(V, Omega) ([ray][3])
+    void *d_dich = nullptr;
+    void *d_partv = nullptr;
+    double *d_j1 = nullptr, *d_tw1 = nullptr;
     size_t tape_limit = (size_t)16 << 30;  // device tape of the J^K_Q reverse (ray batches)
     std::map<int, porta::LaunchCfg> adj2_tuned;  // J^K_Q adjoint: shape timed once per batch size
     cudaEvent_t it_ev[4] = {nullptr, nullptr, nullptr, nullptr};

@@ -66,7 +66,12 @@ struct SweepArgs {
     void *part;                    // [ray][nvox] partial integrals (J mode)
     double *out;                   // emergent: [dir][nu][ny][nx][ns]
     int probe_ray;                 // -1 or the ray whose Stokes vectors are written to probe
-    const Real *dich;              // polarized lines with dichroism: [5][nvox] D^2_Q (null: none)
+    // polarized lines of the multilevel atom (null: none): [11][nvox] the dichroism
+    // multipoles D^2_Q (D20, Re/Im D21, Re/Im D22), D^1_Q (D10, Re/Im D11) and the
+    // orientation emission multipoles S^1_Q (S10, Re/Im S11); J mode: partv [ray][nvox]
+    // the per-ray frequency integrals of Stokes V (for J^1_Q)
+    const Real *dich;
+    Real *partv;
     Real *probe;                   // [nu][nvox][ns]
     Real *probe_ls;                // [nu][nvox]
     int *next_item;                // J mode: null (static striding) or the launch's work-list counter
@@ -101,9 +106,10 @@ template <typename Real, int NS>
 cudaError_t launch_sweep(const SweepArgs<Real> &a, int mode, LaunchCfg &cfg, cudaStream_t st);
 
 // shared memory of the sweep: ring (3 planes of `ring_plane` chunks),
-// Stokes planes (2 x F x ipts_max points), lane-reduction scratch
+// Stokes planes (2 x F x ipts_max points), lane-reduction scratch (na
+// accumulated quantities per thread)
 template <typename Real, int NS>
-int sweep_smem_bytes(int ring_plane, int ipts_max, int F, int threads);
+int sweep_smem_bytes(int ring_plane, int ipts_max, int F, int threads, int na);
 
 template <typename Real, int NS>
 cudaError_t max_active_clusters(int cluster, int smem, int threads, int *out, bool dich = false, bool bq = false,

@@ -97,6 +97,23 @@ __global__ void jkq_finalize_kernel(long long nvox, int nray, const void *part, 
     }
 }
 
+// J^1_Q of polarized lines from the per-ray frequency integrals of Stokes V:
+// J^1_Q = sum_m w_m T^1_Q(V, Omega_m) Vbar_m, tw1 [ray][3] = w_m T^1_Q (J10, Re J11, Im J11)
+template <typename Real>
+__global__ void j1_finalize_kernel(long long nvox, int nray, const Real *partv, const double *tw1, double *j1)
+{
+    const long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (v >= nvox) return;
+    KahanSum<Real> J[3];
+    for (int m = 0; m < nray; ++m) {
+        const Real pv = partv[(long long)m * nvox + v];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) J[c].add((Real)tw1[3 * m + c] * pv);
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) j1[v * 3 + c] = (double)J[c].s;
+}
+
 // atomic max of non-negative doubles through their IEEE bit patterns (the
 // ordering of the bit patterns is that of the values for non-negative doubles)
 __device__ __forceinline__ void atomic_max_nonneg(unsigned long long *addr, double v)
@@ -248,6 +265,13 @@ cudaError_t run_jkq_finalize(long long nvox, int nray, const void *part, const d
 }
 
 template <typename Real>
+cudaError_t run_j1_finalize(long long nvox, int nray, const void *partv, const double *tw1, double *j1, cudaStream_t st)
+{
+    j1_finalize_kernel<Real><<<nblk(nvox, 256), 256, 0, st>>>(nvox, nray, (const Real *)partv, tw1, j1);
+    return cudaGetLastError();
+}
+
+template <typename Real>
 cudaError_t run_see(long long nvox, int nl, int model, double bcrit, const double *eps, const double *bpl,
                     const double *bvec, const double *jkq, const double *lstar, double *rho, void *rhoR,
                     unsigned long long *resid, cudaStream_t st, const double *src)
@@ -386,6 +410,7 @@ template cudaError_t run_coefficients<double>(int, const double *, double *, cud
                                                 cudaStream_t);                                                 \
     template cudaError_t run_jkq_finalize<R, 4>(long long, int, const void *, const double *, double *, double *, \
                                                 cudaStream_t);                                                 \
+    template cudaError_t run_j1_finalize<R>(long long, int, const void *, const double *, double *, cudaStream_t); \
     template cudaError_t run_see<R>(long long, int, int, double, const double *, const double *, const double *, \
                                     const double *, const double *, double *, void *, unsigned long long *,     \
                                     cudaStream_t, const double *);                                             \

@@ -14,6 +14,10 @@ cudaError_t run_rho_convert(long long nvox, int nl, const double *rho, void *out
 template <typename Real, int NS>
 cudaError_t run_jkq_finalize(long long nvox, int nray, const void *part, const double *tw, double *jkq, double *lstar,
                              cudaStream_t st);
+// J^1_Q [v][3] (J10, Re J11, Im J11) = sum_m tw1[m][c] partv[m][v]: tw1 = w_m T^1_Q(V, Omega_m),
+// partv (Real [ray][nvox]) the per-ray frequency integrals of Stokes V
+template <typename Real>
+cudaError_t run_j1_finalize(long long nvox, int nray, const void *partv, const double *tw1, double *j1, cudaStream_t st);
 // src: null (right-hand side eps B delta_K0) or a per-voxel right-hand side [v][nl]
 template <typename Real>
 cudaError_t run_see(long long nvox, int nl, int model, double bcrit, const double *eps, const double *bpl,

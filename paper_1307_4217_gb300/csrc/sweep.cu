@@ -37,17 +37,21 @@ namespace cg = cooperative_groups;
 namespace porta {
 
 template <typename Real, int NS>
-int sweep_smem_bytes(int ring_plane, int ipts_max, int F, int threads)
+int sweep_smem_bytes(int ring_plane, int ipts_max, int F, int threads, int na)
 {
-    return 3 * ring_plane * 16 + (2 * F * ipts_max * NS + threads * (NS == 1 ? 2 : 4)) * (int)sizeof(Real);
+    return 3 * ring_plane * 16 + (2 * F * ipts_max * NS + threads * na) * (int)sizeof(Real);
 }
 
 
 // per-ray partial integrals of a point: store on the first frequency pass,
-// read-modify-write on later passes
-template <typename Real, int NS>
+// read-modify-write on later passes; PV: also the integral of Stokes V (acc[4])
+template <typename Real, int NS, bool PV = false>
 __device__ __forceinline__ void accumulate_partial(const SweepArgs<Real> &a, int m, long long v, int g, const Real *acc)
 {
+    if constexpr (PV) {
+        Real *pv = a.partv + (long long)m * a.nvox + v;
+        *pv = g > 0 ? *pv + acc[4] : acc[4];
+    }
     if constexpr (NS == 1) {
         R2<Real> *pp = reinterpret_cast<R2<Real> *>(a.part) + (long long)m * a.nvox + v;
         R2<Real> o = {acc[0], acc[1]};
@@ -80,7 +84,9 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<Real> &a, cg::cluster
                                            int g, int rank, int C, int dir_out)
 {
     using V = typename V16<Real>::T;
-    constexpr int NA = NS == 1 ? 2 : 4;                  // accumulated quantities per point
+    // accumulated quantities per point: (I, Lambda*), (I, Q, U, Lambda*), and for polarized
+    // lines of the multilevel atom also V (for J^1_Q)
+    constexpr int NA = NS == 1 ? 2 : (DI ? 5 : 4);
     const BoxDev B = a.boxes[box];
     const int nx = B.nx, ny = B.ny, nz = B.nz, F = a.F;
     const int rmax = (ny + C - 1) / C;
@@ -112,11 +118,13 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<Real> &a, cg::cluster
     constexpr int NCH = node_words<NS>() * (int)sizeof(Real) / 16;
     const int chunk = (rmax + 2 * H) * nx;          // ring chunk-plane stride (16-byte chunks)
     const int plane = NCH * chunk;                  // ring plane stride
-    // dichroism (polarized lines whose levels carry alignment): the node's opacity,
-    // source terms and Zeeman factor are rescaled by eta_I / (chi phi) = 1 + d_I(Omega);
-    // eta_Q / eta_I takes the node's profile-normalization word (the normalization is
-    // then read from global memory at O) and eta_U / eta_I sits in a second 3-slot
-    // ring after the node ring (the launch reserves it)
+    // dichroism and orientation (polarized lines of the multilevel atom): the node's
+    // opacity, source terms and Zeeman factor are rescaled by eta_I / (chi phi) =
+    // 1 + d_I(Omega); eta_Q / eta_I takes the node's profile-normalization word (the
+    // normalization is then read from global memory at O); a second 3-slot ring after
+    // the node ring (the launch reserves it) holds per node eta_U / eta_I, the
+    // orientation emission term of S_V and the orientation term of eta_V / eta_I
+    // (both independent of frequency): words 0, 1, 2 at stride dstride
     constexpr bool dich = NS == 4 && DI;
     Real *dring = reinterpret_cast<Real *>(ring + 3 * plane);
     const int dstride = (chunk * (int)sizeof(Real) + 15) / 16 * 16 / (int)sizeof(Real);
@@ -176,6 +184,13 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<Real> &a, cg::cluster
                         const Real *t = ray.t + 6 * i;
                         dd[i] = t[1] * d20 + Real(2) * (t[2] * d21r + t[3] * d21i) + Real(2) * (t[4] * d22r + t[5] * d22i);
                     }
+                    // orientation: sum_Q (-1)^Q T^1_Q(V, Omega) X^1_-Q = T10 X10 + 2 (ReT11 ReX11 + ImT11 ImX11)
+                    // with T^1_Q(V, Omega) = sqrt(3/2) Omega_Q: T10 = sqrt(3/2) Omega_z,
+                    // T11 = -sqrt(3/4) (Omega_x + i Omega_y)
+                    const Real t10 = Real(1.2247448713915890491) * ray.oz;
+                    const Real t11r = Real(-0.86602540378443864676) * ray.ox, t11i = Real(-0.86602540378443864676) * ray.oy;
+                    const Real dv = t10 * a.dich[5 * nv + v] + Real(2) * (t11r * a.dich[6 * nv + v] + t11i * a.dich[7 * nv + v]);
+                    const Real sv = t10 * a.dich[8 * nv + v] + Real(2) * (t11r * a.dich[9 * nv + v] + t11i * a.dich[10 * nv + v]);
                     const Real f = Real(1) + dd[0], inv = Real(1) / f;
                     n.chi *= f;
                     n.SI *= inv;
@@ -183,7 +198,10 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<Real> &a, cg::cluster
                     n.SU *= inv;
                     n.b *= inv;
                     n.invn = dd[1] * inv;
-                    dring[(q % 3) * dstride + idx] = dd[2] * inv;
+                    Real *dr = dring + (q % 3) * 3 * dstride + idx;
+                    dr[0] = dd[2] * inv;
+                    dr[dstride] = sv * inv;
+                    dr[2 * dstride] = dv * inv;
                 }
             }
             ring_store<Real, NS>(ring, plane, chunk, q % 3, idx, n);
@@ -271,18 +289,30 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<Real> &a, cg::cluster
                 const int rP[4] = {l * nx + cm, l * nx + c, (l + 1) * nx + cm, (l + 1) * nx + c};
                 const Real wM[4] = {mx0 * my0, mx1 * my0, mx0 * my1, mx1 * my1};
                 const Real wP[4] = {px0 * py0, px1 * py0, px0 * py1, px1 * py1};
-                // dichroism ratios of the upwind corners and of O
-                Real mdq[4] = {0, 0, 0, 0}, mdu[4] = {0, 0, 0, 0}, odq = 0, odu = 0;
+                // dichroism ratios and orientation terms of the upwind corners, of O and
+                // (emission only) of the downwind corners
+                Real mdq[4] = {0, 0, 0, 0}, mdu[4] = {0, 0, 0, 0}, msv[4] = {0, 0, 0, 0}, mdv[4] = {0, 0, 0, 0};
+                Real psv[4] = {0, 0, 0, 0}, odq = 0, odu = 0, osv = 0, odv = 0;
                 if constexpr (dich) {
-                    const Real *dm = dring + sM * dstride;
+                    const Real *dm = dring + sM * 3 * dstride;
                     const int ix[4] = {(l + 1) * nx + c, (l + 1) * nx + c1, (l + 2) * nx + c, (l + 2) * nx + c1};
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
                         mdq[k] = ring_load<Real, NS>(ring, plane, chunk, sM, ix[k]).invn;
                         mdu[k] = dm[ix[k]];
+                        msv[k] = dm[dstride + ix[k]];
+                        mdv[k] = dm[2 * dstride + ix[k]];
                     }
                     odq = nO.invn;
-                    odu = dring[sO * dstride + (l + 1) * nx + c];
+                    const Real *dO = dring + sO * 3 * dstride + (l + 1) * nx + c;
+                    odu = dO[0];
+                    osv = dO[dstride];
+                    odv = dO[2 * dstride];
+                    if (has_p) {
+                        const Real *dp = dring + sP * 3 * dstride + dstride;
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) psv[k] = dp[rP[k]];
+                    }
                 }
                 const Real wI[4] = {mx0 * my0, mx1 * my0, mx0 * my1, mx1 * my1};
                 const bool last_row = (l + 1 == R);
@@ -415,6 +445,8 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<Real> &a, cg::cluster
                             if constexpr (dich) {
                                 etaQM += we * mdq[k];
                                 etaUM += we * mdu[k];
+                                etaVM += we * mdv[k];
+                                epsM[3] += we * msv[k];
                             }
                             if constexpr (NS == 1) {
                                 epsM[0] += we * km.S;
@@ -445,6 +477,7 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<Real> &a, cg::cluster
                                     epsP[1] += we * kp.SQ;
                                     epsP[2] += we * kp.SU;
                                     epsP[3] += we * (kp.bS * xs);
+                                    if constexpr (dich) epsP[3] += we * psv[k];
                                 }
                             }
                         }
@@ -457,6 +490,7 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<Real> &a, cg::cluster
                             SO[0] = nO.S;
                         } else {
                             SO[0] = nO.SI; SO[1] = nO.SQ; SO[2] = nO.SU; SO[3] = nO.b * xsO * nO.S00;
+                            if constexpr (dich) SO[3] += osv;
                         }
     #pragma unroll
                         for (int s = 0; s < NS; ++s) SM[s] = epsM[s] * iM;
@@ -491,7 +525,7 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<Real> &a, cg::cluster
                             // K' with eta_Q, eta_U (dichroism) and eta_V entries over eta_I:
                             // (K'I)_0 = q I_1 + u I_2 + v I_3, (K'I)_k = k_k I_0
                             const Real qM = etaQM * iM, uM = etaUM * iM, vM = etaVM * iM;
-                            const Real qO = odq, uO = odu, vO = nO.b * xsO;
+                            const Real qO = odq, uO = odu, vO = nO.b * xsO + odv;
                             Real rhs[4];
     #pragma unroll
                             for (int s = 0; s < 4; ++s) rhs[s] = co.e * IM[s] + co.wm * SM[s] + co.wo * SO[s] + co.wc * cM[s];
@@ -536,6 +570,7 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<Real> &a, cg::cluster
                             acc[1] += wt * IO[1];
                             acc[2] += wt * IO[2];
                             acc[3] += wt * ls;
+                            if constexpr (NA == 5) acc[4] += wt * IO[3];
                         }
                         if (a.probe_ray == m) {
 #pragma unroll
@@ -558,7 +593,7 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<Real> &a, cg::cluster
             }
             if constexpr (MODE == MODE_JKQ) {
                 if (L == 1) {
-                    accumulate_partial<Real, NS>(a, m, v, g, acc);
+                    accumulate_partial<Real, NS, NA == 5>(a, m, v, g, acc);
                 } else {
 #pragma unroll
                     for (int s = 0; s < NA; ++s) lane_buf[(s * L + lane) * npts + p] = acc[s];
@@ -578,7 +613,7 @@ __device__ __forceinline__ void sweep_item(const SweepArgs<Real> &a, cg::cluster
                         tot[s] = Real(0);
                         for (int k = 0; k < L; ++k) tot[s] += lane_buf[(s * L + k) * npts + p_lane];
                     }
-                    accumulate_partial<Real, NS>(a, m, v_lane, g, tot);
+                    accumulate_partial<Real, NS, NA == 5>(a, m, v_lane, g, tot);
                 }
             }
         }
@@ -732,7 +767,7 @@ cudaError_t launch_sweep(const SweepArgs<Real> &a, int mode, LaunchCfg &cfg, cud
 }
 
 #define PORTA_INST(R, N)                                                                           \
-    template int sweep_smem_bytes<R, N>(int, int, int, int);                                            \
+    template int sweep_smem_bytes<R, N>(int, int, int, int, int);                                            \
     template cudaError_t max_active_clusters<R, N>(int, int, int, int *, bool, bool, bool);        \
     template cudaError_t launch_sweep<R, N>(const SweepArgs<R> &, int, LaunchCfg &, cudaStream_t);
 PORTA_INST(float, 1)

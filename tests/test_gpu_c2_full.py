@@ -5,8 +5,9 @@ every voxel, and the oracle's update of sampled voxels from the same inputs.
 
 * the trace sum_J sqrt(2J+1) rho^0_0(J) = 1 and positive populations;
 * the update of 64 random voxels, recomputed by the oracle from the GPU's
-  radiation tensors, Lambda-bar* and old multipoles, to 1e-11 of the largest
-  unknown (the update runs in FP64 on both sides).
+  radiation tensors (J^K_Q, K = 0, 1, 2), Lambda-bar* and old multipoles, to
+  1e-11 of the largest unknown (the update runs in FP64 on both sides);
+* orientation (K = 1) present in J^1_Q and in the updated multipoles.
 """
 import numpy as np
 import pytest
@@ -45,10 +46,7 @@ def test_full_size_update_matches_oracle_on_sampled_voxels():
     rng = np.random.default_rng(0)
     idx = rng.choice(nx * ny * nz, 64, replace=False)
     flat = lambda a: a.reshape((nz * ny * nx,) + a.shape[3:])
-    j9 = np.zeros((nz, ny, nx, 4, 9))
-    jj = np.moveaxis(jb, 0, -2)
-    j9[..., 0] = jj[..., 0]
-    j9[..., 4:9] = jj[..., 1:6]
+    j9 = np.moveaxis(jb, 0, -2)
     bv = np.stack([atm["bx"], atm["by"], atm["bz"]], -1)
     want, _ = mlpol.see_update(tab, flat(atm["kT"])[idx], flat(x0)[idx], flat(j9)[idx],
                                flat(np.moveaxis(ls, 0, -1))[idx], flat(bv)[idx])
@@ -56,3 +54,6 @@ def test_full_size_update_matches_oracle_on_sampled_voxels():
     assert np.max(np.abs(got - want)) < 1e-11 * np.max(np.abs(want))
     rb = mlpol.real_basis(atom)
     assert np.max(np.abs(x1[..., rb.index((3, 2, 0, 0))])) > 0
+    # orientation from the circular polarization of the Zeeman effect (J^1_Q from Stokes V)
+    assert np.max(np.abs(jb[..., 1:4])) > 0
+    assert np.max(np.abs(x1[..., rb.index((3, 1, 0, 0))])) > 0

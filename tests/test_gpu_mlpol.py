@@ -1,12 +1,14 @@
 """Polarized multilevel atom on the GPU (porta_ml_* with polarized = 1) against
-the oracle (oracle/mlpol.py): per-line radiation tensors, one update of the 69
-multipoles per voxel from the same sums, iterations, the converged solution and
-graph replay.
+the oracle (oracle/mlpol.py): per-line radiation tensors J^K_Q (K = 0, 1, 2),
+one update of the 69 multipoles per voxel from the same sums, iterations, the
+converged solution and graph replay. The starting multipoles carry alignment
+and orientation (K = 1, 2), so the dichroism (eta_Q, eta_U, eta_V) and the
+orientation emission (eps_V) of every line are exercised.
 
-Tolerances. FP64: 1e-10 relative on J^0_0, 1e-10 of J^0_0 on J^2_Q, and one
+Tolerances. FP64: 1e-10 relative on J^0_0, 1e-10 of J^0_0 on J^1_Q and J^2_Q, and one
 update from the same sums to 1e-11 of the largest unknown (the two sides
 assemble the same rate equations from differently ordered sums and solve them
-by elimination with pivoting). FP32 sweeps: J^0_0 to 2e-5 relative and J^2_Q to
+by elimination with pivoting). FP32 sweeps: J^0_0 to 2e-5 relative and J^1_Q, J^2_Q to
 2e-6 of J^0_0 (the two-level tolerances), populations after iterations and at
 convergence to 1e-4 relative, multipole ratios rho^K_Q / rho^0_0 to 1e-5
 absolute.
@@ -36,7 +38,7 @@ def _case(nx=6, ny=5, nz=8, seed=2, eps_range=(1e-3, 1e-1)):
         r00 = x[..., rb.index((i, 0, 0, 0))]
         if K == 0:
             x[..., k] *= np.exp(0.2 * rng.normal(size=r00.shape))
-        elif K % 2 == 0:
+        else:
             x[..., k] = 0.02 * r00 * rng.normal(size=r00.shape)
     return atm, atom, tab, x
 
@@ -48,13 +50,9 @@ def _ctx(atm, atom, prec, x):
     return c
 
 
-def _j9(j6):
-    """GPU [line][grid][6] (J00, J20, Re/Im J21, Re/Im J22) -> oracle [grid][line][9]"""
-    j6 = np.moveaxis(np.asarray(j6), 0, -2)
-    out = np.zeros(j6.shape[:-1] + (9,))
-    out[..., 0] = j6[..., 0]
-    out[..., 4:9] = j6[..., 1:6]
-    return out
+def _j9(jb):
+    """GPU [line][grid][9] -> oracle [grid][line][9] (J00, J10, Re/Im J11, J20, Re/Im J21, Re/Im J22)"""
+    return np.moveaxis(np.asarray(jb), 0, -2)
 
 
 def _bvec(atm):
@@ -80,7 +78,9 @@ def test_line_radiation_tensors_match_oracle(prec):
     fp64 = prec == P.PORTA_FP64
     j00 = oj[..., 0]
     assert np.max(np.abs(gj[..., 0] - j00) / j00) < (1e-10 if fp64 else 2e-5)
-    assert np.max(np.abs(gj[..., 4:9] - oj[..., 4:9]) / j00[..., None]) < (1e-10 if fp64 else 2e-6)
+    assert np.max(np.abs(gj[..., 1:9] - oj[..., 1:9]) / j00[..., None]) < (1e-10 if fp64 else 2e-6)
+    # orientation and Zeeman circular polarization give J^1_Q
+    assert np.max(np.abs(oj[..., 1:4]) / j00[..., None]) > 1e-3
     assert np.max(np.abs(np.moveaxis(ls, 0, -1) - ol)) < (1e-10 if fp64 else 2e-5) * np.max(ol)
 
 
