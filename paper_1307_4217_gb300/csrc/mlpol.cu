@@ -18,7 +18,7 @@
 // arrays of the line's box (the polarized two-level formal solver, with the
 // orientation terms in eps_V and eta_V, then solves every line; J^1_Q comes
 // from Stokes V); mlpol_see_kernel assembles the real system of one voxel per
-// warp in shared memory over all multipoles (69 for J = 0, 1, 2, 1, 2),
+// CTA in shared memory over all multipoles (69 for J = 0, 1, 2, 1, 2),
 // replaces the row of level 0's population by the trace
 // sum_J sqrt(2J+1) rho^0_0(J) = 1, and solves it in FP64 in two blocks: the
 // population rows (preconditioned) with the K > 0 multipoles at their old
@@ -434,21 +434,72 @@ __global__ void mlpol_prepare_kernel(const MlConst mc, MlPolDev T, long long nvo
     if (nbad) atomicAdd(bad, (unsigned long long)nbad);
 }
 
+// One CTA of kVoxThreads threads per voxel (a persistent loop over voxels): the
+// voxel's system lives in shared memory (40 KB for 69 unknowns), so an SM holds
+// about five voxels; the warps of a CTA share its assembly, reductions and
+// elimination, which keeps ~20 warps per SM in flight for the latency-bound
+// shared-memory and table loads.
+constexpr int kVoxThreads = 128;
+constexpr int kVoxWarps = kVoxThreads / 32;
+
+// sum over the CTA, the same value (and the same order of additions) in every thread
+__device__ __forceinline__ double cta_sum(double v, double *red)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();                                  // red is free (its last readers passed here)
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+    for (int w = 0; w < kVoxWarps; ++w) t += red[w];
+    return t;
+}
+
+__device__ __forceinline__ double cta_max(double v, double *red)
+{
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = red[0];
+    for (int w = 1; w < kVoxWarps; ++w) t = fmax(t, red[w]);
+    return t;
+}
+
+// largest |value| with the smallest row among equal values (partial pivoting)
+__device__ __forceinline__ void cta_argmax(double &bv, int &br, double *red, int *redi)
+{
+    for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int orr = __shfl_xor_sync(0xffffffffu, br, o);
+        if (ov > bv || (ov == bv && orr < br)) { bv = ov; br = orr; }
+    }
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) {
+        red[threadIdx.x >> 5] = bv;
+        redi[threadIdx.x >> 5] = br;
+    }
+    __syncthreads();
+    bv = red[0];
+    br = redi[0];
+    for (int w = 1; w < kVoxWarps; ++w)
+        if (red[w] > bv || (red[w] == bv && redi[w] < br)) { bv = red[w]; br = redi[w]; }
+}
+
 // the real system of voxel v into A [N][N + 1] (row of level 0's population =
 // the trace), sources into s; xo holds the old unknowns; lstar null: the plain
-// rates (no preconditioning)
+// rates (no preconditioning). Called by all threads of the voxel's CTA.
 __device__ void mlpol_assemble(const MlConst &mc, const MlPolDev &T, long long nvox1, long long v, const double *kT,
                                const double *jkq, const double *j1, const double *lstar, const double *bvec,
-                               const double *xo, double *A, double *s, int lane)
+                               const double *xo, double *A, double *s)
 {
-    const int N = T.nunk, N1 = N + 1;
-    if (lane == 0) {
+    const int N = T.nunk, N1 = N + 1, tid = threadIdx.x;
+    if (tid == 0) {
         s[0] = 1.0;
         s[T.src_b] = bvec[v];
         s[T.src_b + 1] = bvec[nvox1 * mc.nline + v];
         s[T.src_b + 2] = bvec[2 * nvox1 * mc.nline + v];
     }
-    for (int k = lane; k < mc.nline; k += 32) {
+    for (int k = tid; k < mc.nline; k += kVoxThreads) {
         const int u = mc.up[k], l = mc.lo[k];
         const long long o = (long long)k * nvox1 + v;
         double *sj = s + T.src_j + 9 * k;
@@ -467,68 +518,68 @@ __device__ void mlpol_assemble(const MlConst &mc, const MlPolDev &T, long long n
             s[T.src_spop + k] = 0.0;
         }
     }
-    for (int e = lane; e < N * N1; e += 32) A[e] = 0.0;
-    __syncwarp();
-    for (int c = lane; c < T.ncell; c += 32) {
+    for (int e = tid; e < N * N1; e += kVoxThreads) A[e] = 0.0;
+    __syncthreads();
+    for (int c = tid; c < T.ncell; c += kVoxThreads) {
         double val = 0.0;
         for (int e = T.cell_start[c]; e < T.cell_start[c + 1]; ++e) val += T.ent_coef[e] * s[T.ent_src[e]];
         A[T.cell_rc[2 * c] * N1 + T.cell_rc[2 * c + 1]] = val;
     }
-    __syncwarp();
-    for (int j = lane; j < N; j += 32) A[T.row0 * N1 + j] = T.trace[j];
-    __syncwarp();
+    __syncthreads();
+    for (int j = tid; j < N; j += kVoxThreads) A[T.row0 * N1 + j] = T.trace[j];
+    __syncthreads();
 }
 
 // out = alpha A(x) + add + with_f e_row0 (full layout): A(x) the plain rate operator
-// with the trace row; one warp per voxel, shared memory as mlpol_see_kernel
-__global__ void mlpol_apply_kernel(const MlConst mc, MlPolDev T, long long nvox1, const double *kT, const double *jkq,
-                                   const double *j1, const double *bvec, const double *x, double alpha, const double *add,
-                                   int with_f, double *out)
+// with the trace row; one CTA per voxel, shared memory as mlpol_see_kernel
+__global__ void __launch_bounds__(kVoxThreads) mlpol_apply_kernel(const MlConst mc, MlPolDev T, long long nvox1,
+                                                                  const double *kT, const double *jkq, const double *j1,
+                                                                  const double *bvec, const double *x, double alpha,
+                                                                  const double *add, int with_f, double *out)
 {
     extern __shared__ double sm[];
-    const int N = T.nunk, N1 = N + 1;
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int per = N * N1 + 2 * N + T.nsrc;
-    double *A = sm + (size_t)wib * per;
+    const int N = T.nunk, N1 = N + 1, tid = threadIdx.x;
+    double *A = sm;
     double *xo = A + N * N1;
     double *s = xo + 2 * N;
-    const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
-    for (long long v = (long long)blockIdx.x * (blockDim.x >> 5) + wib; v < nvox1; v += nwarps) {
-        for (int k = lane; k < N; k += 32) xo[k] = x[v * N + k];
-        __syncwarp();
-        mlpol_assemble(mc, T, nvox1, v, kT, jkq, j1, nullptr, bvec, xo, A, s, lane);
-        for (int r = lane; r < N; r += 32) {
+    for (long long v = blockIdx.x; v < nvox1; v += gridDim.x) {
+        for (int k = tid; k < N; k += kVoxThreads) xo[k] = x[v * N + k];
+        __syncthreads();
+        mlpol_assemble(mc, T, nvox1, v, kT, jkq, j1, nullptr, bvec, xo, A, s);
+        for (int r = tid; r < N; r += kVoxThreads) {
             double y = 0.0;
             for (int c = 0; c < N; ++c) y += A[r * N1 + c] * xo[c];
             const long long o = v * N + r;
             out[o] = alpha * y + (add ? add[o] : 0.0) + (with_f && r == T.row0 ? 1.0 : 0.0);
         }
-        __syncwarp();
+        __syncthreads();
     }
 }
 
-// one warp per voxel; shared memory per warp: A[nunk][nunk + 1], x_old, x_new, sources
-__global__ void mlpol_see_kernel(const MlConst mc, MlPolDev T, long long nvox1, const double *kT, const double *jkq,
-                                 const double *j1, const double *lstar, const double *bvec, const double *src, double *x,
-                                 unsigned long long *resid, unsigned long long *bad)
+// one CTA per voxel; shared memory: A[nunk][nunk + 1], x_old, x_new, sources
+__global__ void __launch_bounds__(kVoxThreads) mlpol_see_kernel(const MlConst mc, MlPolDev T, long long nvox1,
+                                                                const double *kT, const double *jkq, const double *j1,
+                                                                const double *lstar, const double *bvec,
+                                                                const double *src, double *x, unsigned long long *resid,
+                                                                unsigned long long *bad)
 {
     extern __shared__ double sm[];
+    __shared__ double red[kVoxWarps];
+    __shared__ int redi[kVoxWarps];
     const int N = T.nunk, N1 = N + 1;
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int per = N * N1 + 2 * N + T.nsrc;
-    double *A = sm + (size_t)wib * per;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    double *A = sm;
     double *xo = A + N * N1;
     double *xn = xo + N;
     double *s = xn + N;
-    const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
     double ch_max = 0.0;
-    for (long long v = (long long)blockIdx.x * (blockDim.x >> 5) + wib; v < nvox1; v += nwarps) {
-        for (int k = lane; k < N; k += 32) xo[k] = x[v * N + k];
-        __syncwarp();
-        mlpol_assemble(mc, T, nvox1, v, kT, jkq, j1, lstar, bvec, xo, A, s, lane);
+    for (long long v = blockIdx.x; v < nvox1; v += gridDim.x) {
+        for (int k = tid; k < N; k += kVoxThreads) xo[k] = x[v * N + k];
+        __syncthreads();
+        mlpol_assemble(mc, T, nvox1, v, kT, jkq, j1, lstar, bvec, xo, A, s);
         // right-hand side: (1, 0, ...) on the trace row, or the coarse-grid source
-        for (int r = lane; r < N; r += 32) A[r * N1 + N] = src ? src[v * N + r] : (r == T.row0 ? 1.0 : 0.0);
-        __syncwarp();
+        for (int r = tid; r < N; r += kVoxThreads) A[r * N1 + N] = src ? src[v * N + r] : (r == T.row0 ? 1.0 : 0.0);
+        __syncthreads();
         // block 1: the population rows (K = 0) with the K > 0 multipoles at their old values
         const int L = mc.nlev;
         auto is_k0 = [&](int c) {
@@ -539,14 +590,14 @@ __global__ void mlpol_see_kernel(const MlConst mc, MlPolDev T, long long nvox1, 
         for (int i = 0; i < L; ++i) {
             const int r = T.pop_idx[i];
             double acc = 0.0;
-            for (int c = lane; c < N; c += 32)
+            for (int c = tid; c < N; c += kVoxThreads)
                 if (!is_k0(c)) acc += A[r * N1 + c] * xo[c];
-            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-            if (lane == 0) A[r * N1 + N] -= acc;
+            acc = cta_sum(acc, red);
+            if (tid == 0) A[r * N1 + N] -= acc;
         }
-        __syncwarp();
-        int ok1 = 1;
-        if (lane == 0) {
+        __syncthreads();
+        if (tid == 0) {
+            int ok1 = 1;
             double m[kMlMaxLevel][kMlMaxLevel + 1];
             for (int i = 0; i < L; ++i) {
                 for (int j = 0; j < L; ++j) m[i][j] = A[T.pop_idx[i] * N1 + T.pop_idx[j]];
@@ -572,11 +623,12 @@ __global__ void mlpol_see_kernel(const MlConst mc, MlPolDev T, long long nvox1, 
                     for (int j = i + 1; j < L; ++j) acc -= m[i][j] * xn[T.pop_idx[j]];
                     xn[T.pop_idx[i]] = acc / m[i][i];
                 }
+            redi[0] = ok1;
         }
-        ok1 = __shfl_sync(0xffffffffu, ok1, 0);
-        __syncwarp();
+        __syncthreads();
+        const int ok1 = redi[0];
         // block 2: the K > 0 rows with the new populations; population rows become identities
-        for (int r = lane; r < N; r += 32) {
+        for (int r = tid; r < N; r += kVoxThreads) {
             if (is_k0(r)) {
                 for (int c = 0; c < N; ++c) A[r * N1 + c] = c == r ? 1.0 : 0.0;
                 A[r * N1 + N] = ok1 ? xn[r] : 1.0;
@@ -590,68 +642,69 @@ __global__ void mlpol_see_kernel(const MlConst mc, MlPolDev T, long long nvox1, 
                 A[r * N1 + N] -= bsub;
             }
         }
-        __syncwarp();
-        // Gaussian elimination with partial pivoting on [A | b]
+        __syncthreads();
+        // Gaussian elimination with partial pivoting on [A | b]: for pivot k the lanes
+        // take the columns, the warps the rows of the trailing block
         bool ok = ok1 != 0;
         for (int k = 0; k < N; ++k) {
             double bv = -1.0;
             int br = k;
-            for (int r = k + lane; r < N; r += 32) {
+            for (int r = k + tid; r < N; r += kVoxThreads) {
                 const double a = fabs(A[r * N1 + k]);
                 if (a > bv) { bv = a; br = r; }
             }
-            for (int o = 16; o > 0; o >>= 1) {
-                const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
-                const int orr = __shfl_xor_sync(0xffffffffu, br, o);
-                if (ov > bv || (ov == bv && orr < br)) { bv = ov; br = orr; }
-            }
+            cta_argmax(bv, br, red, redi);
             if (!(bv > 0.0)) { ok = false; break; }
             if (br != k)
-                for (int j = k + lane; j <= N; j += 32) {
+                for (int j = k + tid; j <= N; j += kVoxThreads) {
                     const double tmp = A[k * N1 + j];
                     A[k * N1 + j] = A[br * N1 + j];
                     A[br * N1 + j] = tmp;
                 }
-            __syncwarp();
+            __syncthreads();
             const double inv = 1.0 / A[k * N1 + k];
             for (int j = k + 1 + lane; j <= N; j += 32) {
                 const double akj = A[k * N1 + j] * inv;
-                for (int r = k + 1; r < N; ++r) A[r * N1 + j] -= A[r * N1 + k] * akj;
+#pragma unroll 4
+                for (int r = k + 1 + wid; r < N; r += kVoxWarps) A[r * N1 + j] -= A[r * N1 + k] * akj;
             }
-            __syncwarp();
+            __syncthreads();
         }
         double ch = 0.0;
         if (ok) {
-            for (int k = N - 1; k >= 0; --k) {
-                double acc = 0.0;
-                for (int j = k + 1 + lane; j < N; j += 32) acc += A[k * N1 + j] * xn[j];
-                for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-                if (lane == 0) xn[k] = (A[k * N1 + N] - acc) / A[k * N1 + k];
-                __syncwarp();
-            }
-            int nb = 0;
-            for (int i = lane; i < mc.nlev; i += 32) {
+            // back substitution (warp 0)
+            if (wid == 0)
+                for (int k = N - 1; k >= 0; --k) {
+                    double acc = 0.0;
+                    for (int j = k + 1 + lane; j < N; j += 32) acc += A[k * N1 + j] * xn[j];
+                    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+                    if (lane == 0) xn[k] = (A[k * N1 + N] - acc) / A[k * N1 + k];
+                    __syncwarp();
+                }
+            __syncthreads();
+            double nb = 0.0;
+            for (int i = tid; i < mc.nlev; i += kVoxThreads) {
                 const double p0 = xo[T.pop_idx[i]], p1 = xn[T.pop_idx[i]];
                 nb += !(p1 > 0.0 && p1 < 1e300);
                 ch = fmax(ch, fabs(p1 - p0) / fabs(p0));
             }
-            for (int k = lane; k < N; k += 32) nb += !(fabs(xn[k]) < 1e300);
-            for (int o = 16; o > 0; o >>= 1) nb += __shfl_xor_sync(0xffffffffu, nb, o);
-            if (nb) {
+            for (int k = tid; k < N; k += kVoxThreads) nb += !(fabs(xn[k]) < 1e300);
+            nb = cta_sum(nb, red);
+            if (nb > 0.0) {
                 ok = false;
             } else {
-                for (int k = lane; k < N; k += 32) x[v * N + k] = xn[k];
+                for (int k = tid; k < N; k += kVoxThreads) x[v * N + k] = xn[k];
             }
         }
         if (!ok) {
-            if (lane == 0) atomicAdd(bad, 1ull);
+            if (tid == 0) atomicAdd(bad, 1ull);
             ch = 1e300;
         }
-        for (int o = 16; o > 0; o >>= 1) ch = fmax(ch, __shfl_xor_sync(0xffffffffu, ch, o));
+        ch = cta_max(ch, red);
         ch_max = fmax(ch_max, ch);
-        __syncwarp();
+        __syncthreads();
     }
-    if (lane == 0 && ch_max > 0.0) atomicMax(resid, (unsigned long long)__double_as_longlong(fmin(ch_max, 1e300)));
+    if (tid == 0 && ch_max > 0.0) atomicMax(resid, (unsigned long long)__double_as_longlong(fmin(ch_max, 1e300)));
 }
 
 }  // namespace
@@ -672,9 +725,9 @@ template cudaError_t run_mlpol_prepare<double>(const MlConst &, const MlPolDev &
                                                const double *, double *, double *, double *, double *, double *,
                                                unsigned long long *, cudaStream_t);
 
-size_t mlpol_see_smem(const MlPolDev &T, int warps)
+size_t mlpol_see_smem(const MlPolDev &T, int voxels)
 {
-    return sizeof(double) * (size_t)warps * ((size_t)T.nunk * (T.nunk + 1) + 2 * T.nunk + T.nsrc);
+    return sizeof(double) * (size_t)voxels * ((size_t)T.nunk * (T.nunk + 1) + 2 * T.nunk + T.nsrc);
 }
 
 namespace {
@@ -728,23 +781,20 @@ cudaError_t run_mlpol_change(const MlConst &mc, const MlPolDev &T, long long nvo
     return cudaGetLastError();
 }
 
-// persistent launch shape of the warp-per-voxel kernels: up to 4 warps (voxels) per
-// block, as many as the block's shared memory holds
+// persistent launch shape of the CTA-per-voxel kernels: as many CTAs as fit on the GPU
 template <typename K>
-static cudaError_t warp_launch_shape(K kernel, const MlPolDev &T, long long nvox1, int &warps, size_t &smem, int &blocks)
+static cudaError_t voxel_launch_shape(K kernel, const MlPolDev &T, long long nvox1, size_t &smem, int &blocks)
 {
     int dev = 0, nsm = 0, per_sm = 1, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    warps = 4;
-    while (warps > 1 && mlpol_see_smem(T, warps) > (size_t)optin) --warps;
-    smem = mlpol_see_smem(T, warps);
+    smem = mlpol_see_smem(T, 1);
     if (smem > (size_t)optin) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 32 * warps, smem);
-    blocks = (int)std::max<long long>(1, std::min<long long>((nvox1 + warps - 1) / warps, (long long)std::max(1, per_sm) * nsm));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kVoxThreads, smem);
+    blocks = (int)std::max<long long>(1, std::min<long long>(nvox1, (long long)std::max(1, per_sm) * nsm));
     return cudaSuccess;
 }
 
@@ -752,11 +802,11 @@ cudaError_t run_mlpol_see(const MlConst &mc, const MlPolDev &T, long long nvox1,
                           const double *j1, const double *lstar, const double *bvec, double *x, unsigned long long *resid,
                           unsigned long long *bad, cudaStream_t st, const double *src)
 {
-    int warps = 4, blocks = 1;
     size_t smem = 0;
-    cudaError_t e = warp_launch_shape(mlpol_see_kernel, T, nvox1, warps, smem, blocks);
+    int blocks = 1;
+    cudaError_t e = voxel_launch_shape(mlpol_see_kernel, T, nvox1, smem, blocks);
     if (e != cudaSuccess) return e;
-    mlpol_see_kernel<<<blocks, 32 * warps, smem, st>>>(mc, T, nvox1, kT, jkq, j1, lstar, bvec, src, x, resid, bad);
+    mlpol_see_kernel<<<blocks, kVoxThreads, smem, st>>>(mc, T, nvox1, kT, jkq, j1, lstar, bvec, src, x, resid, bad);
     return cudaGetLastError();
 }
 
@@ -764,11 +814,11 @@ cudaError_t run_mlpol_apply(const MlConst &mc, const MlPolDev &T, long long nvox
                             const double *j1, const double *bvec, const double *x, double alpha, const double *add,
                             int with_f, double *out, cudaStream_t st)
 {
-    int warps = 4, blocks = 1;
     size_t smem = 0;
-    cudaError_t e = warp_launch_shape(mlpol_apply_kernel, T, nvox1, warps, smem, blocks);
+    int blocks = 1;
+    cudaError_t e = voxel_launch_shape(mlpol_apply_kernel, T, nvox1, smem, blocks);
     if (e != cudaSuccess) return e;
-    mlpol_apply_kernel<<<blocks, 32 * warps, smem, st>>>(mc, T, nvox1, kT, jkq, j1, bvec, x, alpha, add, with_f, out);
+    mlpol_apply_kernel<<<blocks, kVoxThreads, smem, st>>>(mc, T, nvox1, kT, jkq, j1, bvec, x, alpha, add, with_f, out);
     return cudaGetLastError();
 }
 

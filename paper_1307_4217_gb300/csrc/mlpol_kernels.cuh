@@ -68,7 +68,8 @@ cudaError_t run_mlpol_apply(const MlConst &mc, const MlPolDev &T, long long nvox
                             const double *j1, const double *bvec, const double *x, double alpha, const double *add, int with_f,
                             double *out, cudaStream_t st);
 
-size_t mlpol_see_smem(const MlPolDev &T, int warps);
+// dynamic shared memory of the rate-equation kernels for `voxels` voxels per CTA
+size_t mlpol_see_smem(const MlPolDev &T, int voxels);
 
 // jbar [line voxel][9] (J00, J10, Re/Im J11, J20, Re/Im J21, Re/Im J22) from jkq and j1
 cudaError_t run_mlpol_jbar9(long long n, const double *jkq, const double *j1, double *jbar, cudaStream_t st);

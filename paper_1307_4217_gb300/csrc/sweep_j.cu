@@ -291,43 +291,46 @@ __device__ __forceinline__ void jsweep_item(const SweepArgs<Real> &a, cg::cluste
             if (c >= nx) { c -= nx; ++lr; }
         }
         __syncthreads();
-        // (node, frequency) pairs, node-fastest so that a warp writes consecutive words
-        const int tot = nn * nf;
-        int f = tid / nn, idx = tid - (tid / nn) * nn;
-        const int df = nt / nn, di = nt - df * nn;
-        for (int k = tid; k < tot; k += nt) {
-            const Real xs = sfreq[f] - stage[nodes + idx];
-            const Real eta = stage[idx] * profile_shape(xs);
-            Real *cp = coef + (s * F + f) * cplane + idx * CW;
-            if constexpr (NS == 1) {
-                cp[0] = eta;
-            } else {
-                R2<Real> e2 = {eta, stage[2 * nodes + idx] * xs * eta};
-                *reinterpret_cast<R2<Real> *>(cp) = e2;
+        // per node its coefficients at every frequency of the pass (a warp writes
+        // consecutive nodes); when the slot has fewer nodes than threads, the
+        // frequencies are split between nt / nn thread groups
+        const int ngrp = max(1, min(nf, nt / nn));
+        const int grp = tid / nn;
+        for (int idx = tid - grp * nn; grp < ngrp && idx < nn; idx += nt) {
+            const Real chi_n = stage[idx], s_n = stage[nodes + idx];
+            Real b_n = 0;
+            if constexpr (NS == 4) b_n = stage[2 * nodes + idx];
+            Real *cp = coef + (s * F + grp) * cplane + idx * CW;
+            for (int f = grp; f < nf; f += ngrp, cp += ngrp * cplane) {
+                const Real xs = sfreq[f] - s_n;
+                const Real eta = chi_n * profile_shape(xs);
+                if constexpr (NS == 1) {
+                    cp[0] = eta;
+                } else {
+                    R2<Real> e2 = {eta, b_n * xs * eta};
+                    *reinterpret_cast<R2<Real> *>(cp) = e2;
+                }
             }
-            idx += di;
-            f += df;
-            if (idx >= nn) { idx -= nn; ++f; }
         }
     };
 
     // the fixed-point terms of a point's frequency-integrated Stokes parameters and
     // Lambda* for this pass: J^K_Q += w_m sum_p T^K_Q(p, m) I_p, Lambda-bar* += w_m L
     // (the ray's weight and tensors in the sweep's precision; FP32 terms convert
-    // to fixed point without rounding)
+    // to fixed point without rounding). The L frequency lanes of a point hold the
+    // same totals and share the terms: lane k adds the components c = k mod L.
     auto add_terms = [&](int v, const Real *tot) {
         const Real scale = pow2(Real(0), a.jexp[v]);
         const Real w = sray[22];
         unsigned long long *acc = a.jacc + v;
         if constexpr (NS == 1) {
-            jadd(acc, w * tot[0] * scale, a.jerr);
-            jadd(acc + nvox, w * tot[1] * scale, a.jerr);
+            if (lane == 0) jadd(acc, w * tot[0] * scale, a.jerr);
+            if (lane == (L > 1 ? 1 : 0)) jadd(acc + nvox, w * tot[1] * scale, a.jerr);
         } else {
             const Real pI = w * tot[0] * scale, pQ = w * tot[1] * scale, pU = w * tot[2] * scale;
-#pragma unroll
-            for (int k = 0; k < 6; ++k)
+            for (int k = lane; k < 6; k += L)
                 jadd(acc + (size_t)k * nvox, sray[4 + k] * pI + sray[10 + k] * pQ + sray[16 + k] * pU, a.jerr);
-            jadd(acc + (size_t)6 * nvox, w * tot[3] * scale, a.jerr);
+            if (lane == 6 % L) jadd(acc + (size_t)6 * nvox, w * tot[3] * scale, a.jerr);
         }
     };
 
@@ -597,12 +600,13 @@ __device__ __forceinline__ void jsweep_item(const SweepArgs<Real> &a, cg::cluste
                     }
                 }
             }   // active
-            // fixed-order sum over the frequency lanes of each point (adjacent threads)
+            // fixed-order sum over the frequency lanes of each point (adjacent threads;
+            // every lane ends with the same totals, the additions being commutative)
             for (int o = 1; o < L; o <<= 1) {
 #pragma unroll
                 for (int s = 0; s < NA; ++s) acc[s] += __shfl_xor_sync(0xffffffffu, acc[s], o);
             }
-            if (active && lane == 0) {
+            if (active && (a.jacc || lane == 0)) {
                 if (pb + pstep < npts) {
                     if (a.jacc) add_terms(v, acc);
                     else store_partial<Real, NS>(a, m, v, g, acc);
