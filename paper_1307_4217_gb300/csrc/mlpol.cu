@@ -556,7 +556,115 @@ __global__ void __launch_bounds__(kVoxThreads) mlpol_apply_kernel(const MlConst 
     }
 }
 
-// one CTA per voxel; shared memory: A[nunk][nunk + 1], x_old, x_new, sources
+// Solve of the K > 0 block B x = b (B = A restricted to the M = N - L unknowns
+// kidx[], b their right-hand sides; A itself is left unchanged) by LU factors in
+// FP32 and iterative refinement with FP64 residuals: x = 0, r = b, then
+// d = (LU)^-1 P r, x += d, r = b - B x until the correction is below 1e-13 of x
+// (or has stopped shrinking below 1e-12 of it, the floor of FP64 residuals).
+// The factorization costs a third of the FP64 elimination's M^3 operations in
+// FP32 (64 times the FP64 rate on this GPU); each refinement step costs M^2 in
+// FP64. Returns false (the same in every thread) when a pivot vanishes or the
+// refinement does not converge: the caller then eliminates in FP64. On success
+// xn[kidx[i]] = x_i.
+__device__ bool mlpol_refine_solve(const double *A, int N, int M, const int *kidx, float *LU, float *y, int *piv,
+                                   double *xr, double *rr, double *xn, double *red, int *redi)
+{
+    const int N1 = N + 1, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    for (int e = tid; e < M * M; e += kVoxThreads) {
+        const int i = e / M, j = e - (e / M) * M;
+        LU[e] = (float)A[kidx[i] * N1 + kidx[j]];
+    }
+    for (int i = tid; i < M; i += kVoxThreads) {
+        rr[i] = A[kidx[i] * N1 + N];
+        xr[i] = 0.0;
+    }
+    __syncthreads();
+    // LU with partial pivoting (rows swapped in place, multipliers below the diagonal)
+    for (int k = 0; k < M; ++k) {
+        double bv = -1.0;
+        int br = k;
+        for (int r = k + tid; r < M; r += kVoxThreads) {
+            const double a = fabsf(LU[r * M + k]);
+            if (a > bv) { bv = a; br = r; }
+        }
+        cta_argmax(bv, br, red, redi);
+        if (!(bv > 0.0)) return false;
+        if (tid == 0) piv[k] = br;
+        if (br != k)
+            for (int j = tid; j < M; j += kVoxThreads) {
+                const float tmp = LU[k * M + j];
+                LU[k * M + j] = LU[br * M + j];
+                LU[br * M + j] = tmp;
+            }
+        __syncthreads();
+        const float inv = 1.0f / LU[k * M + k];
+        for (int j = k + 1 + lane; j < M; j += 32) {
+            const float ukj = LU[k * M + j];
+#pragma unroll 4
+            for (int r = k + 1 + wid; r < M; r += kVoxWarps) LU[r * M + j] -= (LU[r * M + k] * inv) * ukj;
+        }
+        __syncthreads();
+        for (int r = k + 1 + tid; r < M; r += kVoxThreads) LU[r * M + k] *= inv;
+        __syncthreads();
+    }
+    double dprev = 1e300;
+    for (int it = 0; it < 8; ++it) {
+        // d = U^-1 L^-1 P r in FP32 (warp 0)
+        if (wid == 0) {
+            for (int i = lane; i < M; i += 32) y[i] = (float)rr[i];
+            __syncwarp();
+            if (lane == 0)
+                for (int k = 0; k < M; ++k) {
+                    const int p = piv[k];
+                    if (p != k) {
+                        const float t = y[k]; y[k] = y[p]; y[p] = t;
+                    }
+                }
+            __syncwarp();
+            for (int k = 0; k + 1 < M; ++k) {
+                const float yk = y[k];
+                for (int i = k + 1 + lane; i < M; i += 32) y[i] -= LU[i * M + k] * yk;
+                __syncwarp();
+            }
+            for (int k = M - 1; k >= 0; --k) {
+                const float yk = y[k] / LU[k * M + k];
+                for (int i = lane; i < k; i += 32) y[i] -= LU[i * M + k] * yk;
+                __syncwarp();
+                if (lane == 0) y[k] = yk;
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+        double dm = 0.0, xm = 0.0;
+        for (int i = tid; i < M; i += kVoxThreads) {
+            xr[i] += (double)y[i];
+            dm = fmax(dm, fabs((double)y[i]));
+            xm = fmax(xm, fabs(xr[i]));
+        }
+        dm = cta_max(dm, red);
+        xm = cta_max(xm, red);
+        if (!(dm < 1e300 && xm < 1e300)) return false;
+        if (dm <= 1e-13 * xm || (dm <= 1e-12 * xm && dm > 0.5 * dprev)) {
+            for (int i = tid; i < M; i += kVoxThreads) xn[kidx[i]] = xr[i];
+            __syncthreads();
+            return true;
+        }
+        dprev = dm;
+        // r = b - B x (FP64)
+        for (int i = tid; i < M; i += kVoxThreads) {
+            const double *Ar = A + kidx[i] * N1;
+            double acc = Ar[N];
+            for (int j = 0; j < M; ++j) acc -= Ar[kidx[j]] * xr[j];
+            rr[i] = acc;
+        }
+        __syncthreads();
+    }
+    return false;
+}
+
+// one CTA per voxel; shared memory: A[nunk][nunk + 1], x_old, x_new, sources, and
+// for the refinement solve FP64 x and r, the FP32 LU factors and work vector,
+// pivots and the indices of the K > 0 unknowns
 __global__ void __launch_bounds__(kVoxThreads) mlpol_see_kernel(const MlConst mc, MlPolDev T, long long nvox1,
                                                                 const double *kT, const double *jkq, const double *j1,
                                                                 const double *lstar, const double *bvec,
@@ -572,6 +680,22 @@ __global__ void __launch_bounds__(kVoxThreads) mlpol_see_kernel(const MlConst mc
     double *xo = A + N * N1;
     double *xn = xo + N;
     double *s = xn + N;
+    double *xr = s + T.nsrc;
+    double *rr = xr + N;
+    float *LU = reinterpret_cast<float *>(rr + N);
+    float *y = LU + N * N;
+    int *kidx = reinterpret_cast<int *>(y + N);
+    int *piv = kidx + N;
+    // the K > 0 unknowns (all but the populations)
+    const int M = N - mc.nlev;
+    if (tid == 0) {
+        int m = 0;
+        for (int k = 0; k < N; ++k) {
+            bool pop = false;
+            for (int i = 0; i < mc.nlev; ++i) pop |= T.pop_idx[i] == k;
+            if (!pop) kidx[m++] = k;
+        }
+    }
     double ch_max = 0.0;
     for (long long v = blockIdx.x; v < nvox1; v += gridDim.x) {
         for (int k = tid; k < N; k += kVoxThreads) xo[k] = x[v * N + k];
@@ -643,10 +767,12 @@ __global__ void __launch_bounds__(kVoxThreads) mlpol_see_kernel(const MlConst mc
             }
         }
         __syncthreads();
-        // Gaussian elimination with partial pivoting on [A | b]: for pivot k the lanes
+        // the K > 0 block by FP32 factors and FP64 refinement; if that fails, Gaussian
+        // elimination in FP64 with partial pivoting on [A | b]: for pivot k the lanes
         // take the columns, the warps the rows of the trailing block
         bool ok = ok1 != 0;
-        for (int k = 0; k < N; ++k) {
+        const bool refined = ok && M > 0 && mlpol_refine_solve(A, N, M, kidx, LU, y, piv, xr, rr, xn, red, redi);
+        for (int k = 0; k < N && !refined; ++k) {
             double bv = -1.0;
             int br = k;
             for (int r = k + tid; r < N; r += kVoxThreads) {
@@ -673,7 +799,7 @@ __global__ void __launch_bounds__(kVoxThreads) mlpol_see_kernel(const MlConst mc
         double ch = 0.0;
         if (ok) {
             // back substitution (warp 0)
-            if (wid == 0)
+            if (wid == 0 && !refined)
                 for (int k = N - 1; k >= 0; --k) {
                     double acc = 0.0;
                     for (int j = k + 1 + lane; j < N; j += 32) acc += A[k * N1 + j] * xn[j];
@@ -727,7 +853,9 @@ template cudaError_t run_mlpol_prepare<double>(const MlConst &, const MlPolDev &
 
 size_t mlpol_see_smem(const MlPolDev &T, int voxels)
 {
-    return sizeof(double) * (size_t)voxels * ((size_t)T.nunk * (T.nunk + 1) + 2 * T.nunk + T.nsrc);
+    const size_t N = T.nunk;
+    return (size_t)voxels * (sizeof(double) * (N * (N + 1) + 4 * N + T.nsrc) + sizeof(float) * (N * N + N) +
+                             sizeof(int) * 2 * N);
 }
 
 namespace {
