@@ -117,6 +117,21 @@ __device__ __forceinline__ float rcp(float x)
     return r;
 }
 
+// Profile shape exp(-(x - s)^2). In FP32 it is evaluated as a power of two by
+// the hardware approximation ex2.approx.ftz (max 2 ulp; the rounding of the FP32
+// argument x - s already bounds its accuracy to ~1e-7 (x-s)^2 relative), and the
+// exponent is capped at 60 so that eta_I and its reciprocal stay normal numbers
+// far in the wings (the flush-to-zero form then never sees a subnormal result);
+// the capped terms are below 1e-26 relative to line centre, where the optical
+// paths vanish.
+__device__ __forceinline__ float profile_shape(float xs)
+{
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(fminf(xs * xs, 60.0f) * -1.4426950408889634f));
+    return r;
+}
+__device__ __forceinline__ double profile_shape(double xs) { return exp(-xs * xs); }
+
 // ---------------------------------------------------------------------------
 // BESSER upwind control point c_M of the quadratic Bezier spline on MO
 // (Sec. 3.2, steps 1-9); ihM = 1/h_M, ihP = 1/h_P, ihMP = 1/(h_M + h_P).

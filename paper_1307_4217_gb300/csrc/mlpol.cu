@@ -485,6 +485,27 @@ __device__ __forceinline__ void cta_argmax(double &bv, int &br, double *red, int
         if (red[w] > bv || (red[w] == bv && redi[w] < br)) { bv = red[w]; br = redi[w]; }
 }
 
+// the same over FP32 values (FP32 compares: the FP64 pipe of this GPU is a small
+// fraction of its FP32 rate, and compares occupy it like arithmetic)
+__device__ __forceinline__ void cta_argmax(float &bv, int &br, float *red, int *redi)
+{
+    for (int o = 16; o > 0; o >>= 1) {
+        const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int orr = __shfl_xor_sync(0xffffffffu, br, o);
+        if (ov > bv || (ov == bv && orr < br)) { bv = ov; br = orr; }
+    }
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) {
+        red[threadIdx.x >> 5] = bv;
+        redi[threadIdx.x >> 5] = br;
+    }
+    __syncthreads();
+    bv = red[0];
+    br = redi[0];
+    for (int w = 1; w < kVoxWarps; ++w)
+        if (red[w] > bv || (red[w] == bv && redi[w] < br)) { bv = red[w]; br = redi[w]; }
+}
+
 // the real system of voxel v into A [N][N + 1] (row of level 0's population =
 // the trace), sources into s; xo holds the old unknowns; lstar null: the plain
 // rates (no preconditioning). Called by all threads of the voxel's CTA.
@@ -567,7 +588,7 @@ __global__ void __launch_bounds__(kVoxThreads) mlpol_apply_kernel(const MlConst 
 // refinement does not converge: the caller then eliminates in FP64. On success
 // xn[kidx[i]] = x_i.
 __device__ bool mlpol_refine_solve(const double *A, int N, int M, const int *kidx, float *LU, float *y, int *piv,
-                                   double *xr, double *rr, double *xn, double *red, int *redi)
+                                   double *xr, double *rr, double *xn, double *red, float *redf, int *redi)
 {
     const int N1 = N + 1, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     for (int e = tid; e < M * M; e += kVoxThreads) {
@@ -581,14 +602,14 @@ __device__ bool mlpol_refine_solve(const double *A, int N, int M, const int *kid
     __syncthreads();
     // LU with partial pivoting (rows swapped in place, multipliers below the diagonal)
     for (int k = 0; k < M; ++k) {
-        double bv = -1.0;
+        float bv = -1.0f;
         int br = k;
         for (int r = k + tid; r < M; r += kVoxThreads) {
-            const double a = fabsf(LU[r * M + k]);
+            const float a = fabsf(LU[r * M + k]);
             if (a > bv) { bv = a; br = r; }
         }
-        cta_argmax(bv, br, red, redi);
-        if (!(bv > 0.0)) return false;
+        cta_argmax(bv, br, redf, redi);
+        if (!(bv > 0.0f)) return false;
         if (tid == 0) piv[k] = br;
         if (br != k)
             for (int j = tid; j < M; j += kVoxThreads) {
@@ -673,6 +694,7 @@ __global__ void __launch_bounds__(kVoxThreads) mlpol_see_kernel(const MlConst mc
 {
     extern __shared__ double sm[];
     __shared__ double red[kVoxWarps];
+    __shared__ float redf[kVoxWarps];
     __shared__ int redi[kVoxWarps];
     const int N = T.nunk, N1 = N + 1;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -771,7 +793,7 @@ __global__ void __launch_bounds__(kVoxThreads) mlpol_see_kernel(const MlConst mc
         // elimination in FP64 with partial pivoting on [A | b]: for pivot k the lanes
         // take the columns, the warps the rows of the trailing block
         bool ok = ok1 != 0;
-        const bool refined = ok && M > 0 && mlpol_refine_solve(A, N, M, kidx, LU, y, piv, xr, rr, xn, red, redi);
+        const bool refined = ok && M > 0 && mlpol_refine_solve(A, N, M, kidx, LU, y, piv, xr, rr, xn, red, redf, redi);
         for (int k = 0; k < N && !refined; ++k) {
             double bv = -1.0;
             int br = k;

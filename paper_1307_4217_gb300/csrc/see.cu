@@ -25,12 +25,27 @@ __global__ void profile_norm_kernel(long long nvox, int nray, int nnu, const dou
     if (idx >= nvox * nray) return;
     int m = (int)(idx / nvox);
     long long v = idx - (long long)m * nvox;
-    double s = vel[v] * mu[m], sum = 0.0;
-    for (int j = 0; j < nnu; ++j) {
-        double xs = xf[j] - s;
-        sum += wf[j] * exp(-xs * xs);
+    if constexpr (sizeof(Real) == 4) {
+        // FP32 sweeps: the sum of the profile they evaluate (FP32 shift and profile),
+        // compensated, so that their integration weights w_j phi_j / N sum to 1 in
+        // their own arithmetic (and without the low-rate FP64 exponential)
+        const float s = (float)vel[v] * (float)mu[m];
+        float sum = 0.0f, comp = 0.0f;
+        for (int j = 0; j < nnu; ++j) {
+            const float y = (float)wf[j] * profile_shape((float)xf[j] - s) - comp;
+            const float t = sum + y;
+            comp = (t - sum) - y;
+            sum = t;
+        }
+        invn[idx] = (Real)(1.0f / sum);
+    } else {
+        double s = vel[v] * mu[m], sum = 0.0;
+        for (int j = 0; j < nnu; ++j) {
+            double xs = xf[j] - s;
+            sum += wf[j] * exp(-xs * xs);
+        }
+        invn[idx] = (Real)(1.0 / sum);
     }
-    invn[idx] = (Real)(1.0 / sum);
 }
 
 // rho (FP64, [v][nl]) -> sweep copy (Real, [c][v])
@@ -67,14 +82,20 @@ template <typename Real, int NS>
 __global__ void jkq_finalize_kernel(long long nvox, int nray, const void *part, const double *tw,
                                     double *jkq, double *lstar)
 {
+    // the ray weights and tensors in the sums' precision, converted once per block
+    extern __shared__ __align__(16) unsigned char fin_smem[];
+    Real *stw = reinterpret_cast<Real *>(fin_smem);
+    for (int i = threadIdx.x; i < nray * 19; i += blockDim.x) stw[i] = (Real)tw[i];
+    __syncthreads();
     long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (v >= nvox) return;
     const Real *p = reinterpret_cast<const Real *>(part);
     if constexpr (NS == 1) {
         KahanSum<Real> J, L;
+#pragma unroll 4
         for (int m = 0; m < nray; ++m) {
             const Real *q = p + 2 * ((long long)m * nvox + v);
-            const Real w = (Real)tw[m * 19];
+            const Real w = stw[m * 19];
             J.add(w * q[0]);
             L.add(w * q[1]);
         }
@@ -82,13 +103,14 @@ __global__ void jkq_finalize_kernel(long long nvox, int nray, const void *part, 
         lstar[v] = (double)L.s;
     } else {
         KahanSum<Real> J[6], L;
+#pragma unroll 2
         for (int m = 0; m < nray; ++m) {
             const Real *q = p + 4 * ((long long)m * nvox + v);
-            const double *t = tw + m * 19;
-            const Real w = (Real)t[0];
+            const Real *t = stw + m * 19;
+            const Real w = t[0];
             const Real pI = w * q[0], pQ = w * q[1], pU = w * q[2];
 #pragma unroll
-            for (int c = 0; c < 6; ++c) J[c].add((Real)t[1 + c] * pI + (Real)t[7 + c] * pQ + (Real)t[13 + c] * pU);
+            for (int c = 0; c < 6; ++c) J[c].add(t[1 + c] * pI + t[7 + c] * pQ + t[13 + c] * pU);
             L.add(w * q[3]);
         }
 #pragma unroll
@@ -102,13 +124,18 @@ __global__ void jkq_finalize_kernel(long long nvox, int nray, const void *part, 
 template <typename Real>
 __global__ void j1_finalize_kernel(long long nvox, int nray, const Real *partv, const double *tw1, double *j1)
 {
+    extern __shared__ __align__(16) unsigned char fin_smem[];
+    Real *stw = reinterpret_cast<Real *>(fin_smem);
+    for (int i = threadIdx.x; i < nray * 3; i += blockDim.x) stw[i] = (Real)tw1[i];
+    __syncthreads();
     const long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (v >= nvox) return;
     KahanSum<Real> J[3];
+#pragma unroll 4
     for (int m = 0; m < nray; ++m) {
         const Real pv = partv[(long long)m * nvox + v];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) J[c].add((Real)tw1[3 * m + c] * pv);
+        for (int c = 0; c < 3; ++c) J[c].add(stw[3 * m + c] * pv);
     }
 #pragma unroll
     for (int c = 0; c < 3; ++c) j1[v * 3 + c] = (double)J[c].s;
@@ -260,14 +287,20 @@ template <typename Real, int NS>
 cudaError_t run_jkq_finalize(long long nvox, int nray, const void *part, const double *tw, double *jkq, double *lstar,
                              cudaStream_t st)
 {
-    jkq_finalize_kernel<Real, NS><<<nblk(nvox, 256), 256, 0, st>>>(nvox, nray, part, tw, jkq, lstar);
+    const size_t smem = (size_t)nray * 19 * sizeof(Real);
+    cudaError_t e = cudaFuncSetAttribute(jkq_finalize_kernel<Real, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    jkq_finalize_kernel<Real, NS><<<nblk(nvox, 256), 256, smem, st>>>(nvox, nray, part, tw, jkq, lstar);
     return cudaGetLastError();
 }
 
 template <typename Real>
 cudaError_t run_j1_finalize(long long nvox, int nray, const void *partv, const double *tw1, double *j1, cudaStream_t st)
 {
-    j1_finalize_kernel<Real><<<nblk(nvox, 256), 256, 0, st>>>(nvox, nray, (const Real *)partv, tw1, j1);
+    const size_t smem = (size_t)nray * 3 * sizeof(Real);
+    cudaError_t e = cudaFuncSetAttribute(j1_finalize_kernel<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    j1_finalize_kernel<Real><<<nblk(nvox, 256), 256, smem, st>>>(nvox, nray, (const Real *)partv, tw1, j1);
     return cudaGetLastError();
 }
 
