@@ -255,7 +255,7 @@ __device__ __forceinline__ void adjoint_item(const SweepArgs<Real> &a, cg::clust
     Real *xsh = tt + (long long)F * tile_pts * NS;      // x_j and w_j of the group
     const Real *tape = a.store + (long long)d * a.nnu * a.nvox * NS;
     Real *gout_part = FORM == 0 ? a.gpart + (long long)item * 3 * a.nvox : nullptr;
-    double *acc = FORM != 0 ? a.gacc + (long long)cid * 10 * a.nvox : nullptr;
+    Real *acc = FORM != 0 ? reinterpret_cast<Real *>(a.gacc) + (long long)cid * 10 * a.nvox : nullptr;
     const int mglob = a.ray0 + d;                       // ray index for the J weights (form 2)
     const Real wray = FORM == 2 ? (Real)a.tw[19 * mglob] : Real(0);
     // offsets of the vector planes (SVec): gI[par][f], gM[f], gP[f], T[par][f]
@@ -355,12 +355,13 @@ __device__ __forceinline__ void adjoint_item(const SweepArgs<Real> &a, cg::clust
                 gout_part[2 * a.nvox + v] = gb;
             } else {
                 // this cluster's accumulators, as reductions performed in the L2 (no
-                // load on this thread's path). A node is finalized by one thread per
-                // item and the cluster's items are separated by cluster barriers
-                // (release / acquire), so the additions into each accumulator happen
-                // in item order: the sums are reproducible.
+                // load on this thread's path), in the sweep's precision (an FP32 sweep
+                // adds FP32 terms: no conversions on the GPU's low-rate FP64 pipe). A
+                // node is finalized by one thread per item and the cluster's items are
+                // separated by cluster barriers (release / acquire), so the additions
+                // into each accumulator happen in item order: the sums are reproducible.
 #pragma unroll
-                for (int k = 0; k < 10; ++k) atomicAdd(acc + k * a.nvox + v, (double)o[k]);
+                for (int k = 0; k < 10; ++k) atomicAdd(acc + k * a.nvox + v, o[k]);
             }
         }
     };
@@ -766,6 +767,41 @@ __global__ void adjoint_reduce_kernel(const Real *gpart, int nitems, int ngroups
                                       const RayDev<Real> *rays, double bfac, double *g_chi, double *g_e, double *g_b)
 {
     const int ndir = nitems / ngroups;
+    if constexpr (sizeof(Real) == 4) {
+        // FP32 partials: compensated FP32 sums in the same order (no FP64 arithmetic,
+        // which this GPU runs at a small fraction of the FP32 rate)
+        auto kadd = [](float &s, float &c, float x) {
+            const float y = x - c, t = s + y;
+            c = (t - s) - y;
+            s = t;
+        };
+        for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < nvox; v += (long long)gridDim.x * blockDim.x) {
+            float sc = 0, cc = 0, se = 0, ce = 0, bx = 0, cx = 0, by = 0, cy = 0, bz = 0, cz = 0;
+            for (int d = 0; d < ndir; ++d) {
+                const Real *p0 = gpart + (long long)d * ngroups * 3 * nvox;
+                float gb = 0, cb = 0;
+#pragma unroll 4
+                for (int g = 0; g < ngroups; ++g) {
+                    const Real *p = p0 + (long long)g * 3 * nvox;
+                    kadd(sc, cc, p[v]);
+                    kadd(se, ce, p[nvox + v]);
+                    kadd(gb, cb, p[2 * nvox + v]);
+                }
+                const RayDev<Real> &r = rays[d];
+                kadd(bx, cx, gb * r.ox);
+                kadd(by, cy, gb * r.oy);
+                kadd(bz, cz, gb * r.oz);
+            }
+            g_chi[v] = sc;
+            g_e[v] = se;
+            if (g_b) {
+                g_b[v] = bfac * bx;
+                g_b[nvox + v] = bfac * by;
+                g_b[2 * nvox + v] = bfac * bz;
+            }
+        }
+        return;
+    }
     for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < nvox; v += (long long)gridDim.x * blockDim.x) {
         double sc = 0, se = 0, bx = 0, by = 0, bz = 0;
         // directions in order, the groups of a direction in order (loads of
@@ -853,16 +889,17 @@ cudaError_t launch_adjoint(const SweepArgs<Real> &a, const LaunchCfg &cfg, cudaS
     return cudaLaunchKernelEx(&lc, adjoint_kernel<Real, NS, 2>, a);
 }
 
-// per voxel: sum of the per-cluster accumulators in cluster order
-__global__ void adjoint_acc_reduce_kernel(const double *gacc, int nclusters, long long nvox, int nl, double *g_chi,
+// per voxel: sum of the per-cluster accumulators in cluster order (FP64)
+template <typename Real>
+__global__ void adjoint_acc_reduce_kernel(const Real *gacc, int nclusters, long long nvox, int nl, double *g_chi,
                                           double *g_b, double *g_rho)
 {
     for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < nvox; v += (long long)gridDim.x * blockDim.x) {
         double s[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
         for (int cl = 0; cl < nclusters; ++cl) {
-            const double *p = gacc + (long long)cl * 10 * nvox + v;
+            const Real *p = gacc + (long long)cl * 10 * nvox + v;
 #pragma unroll
-            for (int k = 0; k < 10; ++k) s[k] += p[k * nvox];
+            for (int k = 0; k < 10; ++k) s[k] += (double)p[k * nvox];
         }
         g_chi[v] += s[0];
         if (g_b) {
@@ -874,14 +911,19 @@ __global__ void adjoint_acc_reduce_kernel(const double *gacc, int nclusters, lon
     }
 }
 
-cudaError_t launch_adjoint_acc_reduce(const double *gacc, int nclusters, long long nvox, int nl, double *g_chi,
+template <typename Real>
+cudaError_t launch_adjoint_acc_reduce(const Real *gacc, int nclusters, long long nvox, int nl, double *g_chi,
                                       double *g_b, double *g_rho, cudaStream_t st)
 {
     const int threads = 256;
     const long long blocks = std::min<long long>((nvox + threads - 1) / threads, 152LL * 16);
-    adjoint_acc_reduce_kernel<<<(int)blocks, threads, 0, st>>>(gacc, nclusters, nvox, nl, g_chi, g_b, g_rho);
+    adjoint_acc_reduce_kernel<Real><<<(int)blocks, threads, 0, st>>>(gacc, nclusters, nvox, nl, g_chi, g_b, g_rho);
     return cudaGetLastError();
 }
+template cudaError_t launch_adjoint_acc_reduce<float>(const float *, int, long long, int, double *, double *, double *,
+                                                      cudaStream_t);
+template cudaError_t launch_adjoint_acc_reduce<double>(const double *, int, long long, int, double *, double *, double *,
+                                                       cudaStream_t);
 
 template <typename Real>
 cudaError_t launch_adjoint_reduce(const Real *gpart, int nitems, int ngroups, long long nvox, const RayDev<Real> *rays,

@@ -321,13 +321,13 @@ int emergent_vjp_t(porta_ctx *c, int ndir, const double *mu, const double *chi, 
         } else {
             // gradients in the unknowns: per-cluster accumulators, then their sum
             if (e == cudaSuccess)
-                e = ensure_buf((void **)&c->d_gacc, c->gacc_bytes, (size_t)acfg.clusters * 10 * c->nvox * sizeof(double));
-            if (e == cudaSuccess) e = cudaMemsetAsync(c->d_gacc, 0, (size_t)acfg.clusters * 10 * c->nvox * sizeof(double), c->stream);
+                e = ensure_buf((void **)&c->d_gacc, c->gacc_bytes, (size_t)acfg.clusters * 10 * c->nvox * sizeof(Real));
+            if (e == cudaSuccess) e = cudaMemsetAsync(c->d_gacc, 0, (size_t)acfg.clusters * 10 * c->nvox * sizeof(Real), c->stream);
             b.gacc = c->d_gacc;
             if (e == cudaSuccess)
                 e = c->ns == 1 ? launch_adjoint<Real, 1>(b, acfg, c->stream, 1) : launch_adjoint<Real, 4>(b, acfg, c->stream, 1);
             if (e == cudaSuccess)
-                e = launch_adjoint_acc_reduce(c->d_gacc, acfg.clusters, c->nvox, c->nl, dg_chi, c->ns == 1 ? nullptr : dg_b,
+                e = launch_adjoint_acc_reduce<Real>((const Real *)c->d_gacc, acfg.clusters, c->nvox, c->nl, dg_chi, c->ns == 1 ? nullptr : dg_b,
                                               dg_rho, c->stream);
         }
         if (e == cudaSuccess) e = cudaEventRecord(c->adj_ev[2], c->stream);
@@ -386,7 +386,7 @@ int jkq_vjp_t(porta_ctx *c, const double *dgj, const double *dgl, double *dg_chi
     if (!forced && !tune) acfg = c->adj2_tuned[nb];
     int maxcl = acfg.clusters;
     for (const LaunchCfg &k : cand) maxcl = std::max(maxcl, k.clusters);
-    e = ensure_buf((void **)&c->d_gacc, c->gacc_bytes, (size_t)maxcl * 10 * c->nvox * sizeof(double));
+    e = ensure_buf((void **)&c->d_gacc, c->gacc_bytes, (size_t)maxcl * 10 * c->nvox * sizeof(Real));
     if (e != cudaSuccess) {
         pfree(scratch);
         return fail(c, PORTA_ENOMEM, "iterate_vjp: accumulator allocation");
@@ -453,7 +453,7 @@ int jkq_vjp_t(porta_ctx *c, const double *dgj, const double *dgl, double *dg_chi
         if (rc == PORTA_OK) c->adj2_tuned[nb] = acfg;
     }
     if (rc == PORTA_OK) {
-        e = cudaMemsetAsync(c->d_gacc, 0, (size_t)acfg.clusters * 10 * c->nvox * sizeof(double), c->stream);
+        e = cudaMemsetAsync(c->d_gacc, 0, (size_t)acfg.clusters * 10 * c->nvox * sizeof(Real), c->stream);
         if (e != cudaSuccess) rc = fail(c, PORTA_ECUDA, cudaGetErrorString(e));
     }
     for (int r0 = 0; r0 < c->nray && rc == PORTA_OK; r0 += nb) {
@@ -477,7 +477,7 @@ int jkq_vjp_t(porta_ctx *c, const double *dgj, const double *dgl, double *dg_chi
         float t = 0;
         e = cudaEventRecord(ev[0], c->stream);
         if (e == cudaSuccess)
-            e = launch_adjoint_acc_reduce(c->d_gacc, acfg.clusters, c->nvox, c->nl, dg_chi, c->ns == 1 ? nullptr : dg_b,
+            e = launch_adjoint_acc_reduce<Real>((const Real *)c->d_gacc, acfg.clusters, c->nvox, c->nl, dg_chi, c->ns == 1 ? nullptr : dg_b,
                                           dg_rho, c->stream);
         if (e == cudaSuccess) e = cudaEventRecord(ev[1], c->stream);
         if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);

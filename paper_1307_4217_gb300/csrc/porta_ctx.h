@@ -125,7 +125,7 @@ struct porta_ctx {
     size_t gpart_bytes = 0;
     int adj_cluster = 0, adj_nu_group = 0;
     porta::LaunchCfg last_adj{};
-    double *d_gacc = nullptr;       // per-cluster FP64 gradient accumulators (gradients in rho)
+    void *d_gacc = nullptr;         // per-cluster gradient accumulators, Real (gradients in rho)
     size_t gacc_bytes = 0;
     // differentiation through Jacobi iterations (porta_iterate_ckpt): checkpoints of
     // rho [nvox][nl] every it_ckpt iterations, the iteration count, rho at the end

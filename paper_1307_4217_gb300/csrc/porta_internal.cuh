@@ -79,10 +79,10 @@ struct SweepArgs {
     Real *store;                   // emergent: null, or the Stokes vectors of every plane [dir][nu][nvox][ns]
     const double *gout;            // adjoint: dL/dI on the top plane [dir][nu][ny][nx][ns]
     Real *gpart;                   // adjoint: per (dir, frequency group) partial gradients [item][3][nvox]
-    // adjoint in the unknowns rho (through iterations): per-cluster FP64 accumulators of
+    // adjoint in the unknowns rho (through iterations): per-cluster accumulators (Real) of
     // dL/dchi (fixed rho), dL/dB (3), dL/drho (6) [cluster][10][nvox]; for the J^K_Q sums
     // of a formal solution also dL/dJ [v][nj], dL/dLambda* [v], ray weights and T ([ray][19])
-    double *gacc;
+    void *gacc;
     const double *gjkq, *glstar, *tw;
     int ray0;                      // first ray of the batch (rays and geom point at it)
     // J^K_Q formal solution (sweep_j.cu): fixed-point accumulators of the weighted
@@ -156,7 +156,8 @@ template <typename Real>
 cudaError_t launch_adjoint_reduce(const Real *gpart, int nitems, int ngroups, long long nvox, const RayDev<Real> *rays,
                                   double bfac, double *g_chi, double *g_e, double *g_b, cudaStream_t st);
 // sum of the per-cluster accumulators in cluster order: g_chi and g_b added, g_rho overwritten
-cudaError_t launch_adjoint_acc_reduce(const double *gacc, int nclusters, long long nvox, int nl, double *g_chi,
+template <typename Real>
+cudaError_t launch_adjoint_acc_reduce(const Real *gacc, int nclusters, long long nvox, int nl, double *g_chi,
                                       double *g_b, double *g_rho, cudaStream_t st);
 
 }  // namespace porta
