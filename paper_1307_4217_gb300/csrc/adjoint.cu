@@ -441,19 +441,19 @@ __device__ __forceinline__ void adjoint_item(const SweepArgs<Real> &a, cg::clust
             // form 2: dL/dI_p per unit J weight at O, sum_KQ T^K_Q(p, Omega) dL/dJ^K_Q, and dL/dLambda*
             Real gdir[3] = {0, 0, 0}, gLv = 0;
             if constexpr (FORM == 2) {
-                const double *gj = a.gjkq + (B.vox0 + vO) * (NS == 1 ? 1 : 6);
+                const Real *gj = a.gjkq + (B.vox0 + vO) * (NS == 1 ? 1 : 6);
                 if constexpr (NS == 1) {
-                    gdir[0] = (Real)gj[0];
+                    gdir[0] = gj[0];
                 } else {
 #pragma unroll
                     for (int s = 0; s < 3; ++s) {
                         Real acc_s = 0;
 #pragma unroll
-                        for (int c6 = 0; c6 < 6; ++c6) acc_s += ray.t[6 * s + c6] * (Real)gj[c6];
+                        for (int c6 = 0; c6 < 6; ++c6) acc_s += ray.t[6 * s + c6] * gj[c6];
                         gdir[s] = acc_s;
                     }
                 }
-                gLv = (Real)a.glstar[B.vox0 + vO];
+                gLv = a.glstar[B.vox0 + vO];
             }
             // rows of the Stokes-adjoint gather from plane q+1: (c|c-1, l|l-1)
             const bool first = l == 0;

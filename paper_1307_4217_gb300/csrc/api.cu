@@ -548,7 +548,7 @@ void free_all(porta_ctx *c)
     void *ptrs[] = {c->d_atm, c->d_eps, c->d_bpl, c->d_b, c->d_rho, c->d_rhoR, c->d_invn, c->d_geom, c->d_rays,
                     c->d_freq, c->d_part, c->d_tw, c->d_jkq, c->d_lstar, c->d_resid, c->d_err, c->d_boxes,
                     c->d_items, c->d_tune_items, c->d_tape, c->d_gpart, c->d_jacc, c->d_jexp, c->d_kexpl, c->d_sexpl,
-                    c->d_partv, c->d_j1, c->d_tw1};
+                    c->d_partv, c->d_j1, c->d_tw1, c->d_gjR, c->d_vjp_out};
     for (void *p : ptrs)
         if (p) pfree(p);
 }

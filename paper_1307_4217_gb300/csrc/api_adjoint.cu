@@ -364,14 +364,18 @@ int jkq_vjp_t(porta_ctx *c, const double *dgj, const double *dgl, double *dg_chi
     const int nbatch = (c->nray + nbmax - 1) / nbmax;
     const int nb = (c->nray + nbatch - 1) / nbatch;
     cudaError_t e = ensure_buf(&c->d_tape, c->tape_bytes, (size_t)nb * per_ray);
-    double *scratch = nullptr;
-    if (e == cudaSuccess) e = dalloc(&scratch, (size_t)nb * c->n_nu * nxy * c->ns);
+    if (e == cudaSuccess)
+        e = ensure_buf((void **)&c->d_vjp_out, c->vjp_out_bytes, (size_t)nb * c->n_nu * nxy * c->ns * sizeof(double));
+    // dL/dJ^K_Q and dL/dLambda* in the sweep's precision (read per point and item)
+    if (e == cudaSuccess) e = ensure_buf(&c->d_gjR, c->gjR_bytes, (size_t)c->nvox * (c->nj + 1) * sizeof(Real));
     for (int k = 0; k < 4 && e == cudaSuccess; ++k)
         if (!c->it_ev[k]) e = cudaEventCreate(&c->it_ev[k]);
-    if (e != cudaSuccess) {
-        if (scratch) pfree(scratch);
-        return fail(c, PORTA_ENOMEM, "iterate_vjp: tape allocation");
-    }
+    if (e != cudaSuccess) return fail(c, PORTA_ENOMEM, "iterate_vjp: tape allocation");
+    double *scratch = c->d_vjp_out;
+    Real *gjR = (Real *)c->d_gjR;
+    e = run_to_real<Real>((long long)c->nvox * c->nj, dgj, gjR, c->stream);
+    if (e == cudaSuccess) e = run_to_real<Real>((long long)c->nvox, dgl, gjR + (size_t)c->nvox * c->nj, c->stream);
+    if (e != cudaSuccess) return fail(c, PORTA_ECUDA, std::string("iterate_vjp: ") + cudaGetErrorString(e));
     // adjoint launch shape: forced, else timed once per batch size on the first batch
     LaunchCfg acfg{};
     std::vector<LaunchCfg> cand;
@@ -379,18 +383,12 @@ int jkq_vjp_t(porta_ctx *c, const double *dgj, const double *dgl, double *dg_chi
     const bool tune = !forced && !c->adj2_tuned.count(nb);
     int rc = c->ns == 1 ? choose_adjoint<Real, 1>(c, acfg, c->adj_cluster, c->adj_nu_group, nb, tune ? &cand : nullptr)
                         : choose_adjoint<Real, 4>(c, acfg, c->adj_cluster, c->adj_nu_group, nb, tune ? &cand : nullptr);
-    if (rc) {
-        pfree(scratch);
-        return fail(c, rc, "iterate_vjp: no adjoint launch shape fits");
-    }
+    if (rc) return fail(c, rc, "iterate_vjp: no adjoint launch shape fits");
     if (!forced && !tune) acfg = c->adj2_tuned[nb];
     int maxcl = acfg.clusters;
     for (const LaunchCfg &k : cand) maxcl = std::max(maxcl, k.clusters);
     e = ensure_buf((void **)&c->d_gacc, c->gacc_bytes, (size_t)maxcl * 10 * c->nvox * sizeof(Real));
-    if (e != cudaSuccess) {
-        pfree(scratch);
-        return fail(c, PORTA_ENOMEM, "iterate_vjp: accumulator allocation");
-    }
+    if (e != cudaSuccess) return fail(c, PORTA_ENOMEM, "iterate_vjp: accumulator allocation");
     // forward: Stokes vectors of every node for rays r0 .. r0 + n - 1
     auto forward = [&](int r0, int n) -> int {
         SweepArgs<Real> a = base_args<Real>(c);
@@ -412,8 +410,8 @@ int jkq_vjp_t(porta_ctx *c, const double *dgj, const double *dgl, double *dg_chi
         b.rays = (const RayDev<Real> *)c->d_rays + r0;
         b.store = (Real *)c->d_tape;
         b.invn = (const Real *)c->d_invn;
-        b.gjkq = dgj;
-        b.glstar = dgl;
+        b.gjkq = gjR;
+        b.glstar = gjR + (size_t)c->nvox * c->nj;
         b.tw = c->d_tw;
         b.ray0 = r0;
         b.gacc = c->d_gacc;
@@ -487,7 +485,6 @@ int jkq_vjp_t(porta_ctx *c, const double *dgj, const double *dgl, double *dg_chi
         c->last_adj = acfg;
     }
     cudaStreamSynchronize(c->stream);
-    pfree(scratch);
     return rc;
 }
 

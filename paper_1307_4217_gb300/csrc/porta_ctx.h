@@ -126,6 +126,10 @@ struct porta_ctx {
     int adj_cluster = 0, adj_nu_group = 0;
     porta::LaunchCfg last_adj{};
     void *d_gacc = nullptr;         // per-cluster gradient accumulators, Real (gradients in rho)
+    void *d_gjR = nullptr;          // dL/dJ^K_Q and dL/dLambda* in the sweep's precision ([nvox][nj], [nvox])
+    size_t gjR_bytes = 0;
+    double *d_vjp_out = nullptr;    // emergent output of the taped forward sweeps (not read)
+    size_t vjp_out_bytes = 0;
     size_t gacc_bytes = 0;
     // differentiation through Jacobi iterations (porta_iterate_ckpt): checkpoints of
     // rho [nvox][nl] every it_ckpt iterations, the iteration count, rho at the end

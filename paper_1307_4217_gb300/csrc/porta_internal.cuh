@@ -83,7 +83,8 @@ struct SweepArgs {
     // dL/dchi (fixed rho), dL/dB (3), dL/drho (6) [cluster][10][nvox]; for the J^K_Q sums
     // of a formal solution also dL/dJ [v][nj], dL/dLambda* [v], ray weights and T ([ray][19])
     void *gacc;
-    const double *gjkq, *glstar, *tw;
+    const Real *gjkq, *glstar;     // (in the sweep's precision)
+    const double *tw;
     int ray0;                      // first ray of the batch (rays and geom point at it)
     // J^K_Q formal solution (sweep_j.cu): fixed-point accumulators of the weighted
     // ray sums [NJ + 1][nvox] (J^K_Q components, then Lambda-bar*), the power-of-two
