@@ -657,6 +657,17 @@ int porta_ml_set_atmosphere(porta_ctx *c, const double *chi, const double *kT, c
 int porta_ml_emergent_stokes(porta_ctx *c, int line, int ndir, const double *mu, const double *chi, double *out,
                              int where);
 
+/* Solve of the rate equations' K > 0 block (polarized atom, after the population
+   block): mode 0 (default) factors it in FP32 with partial pivoting and refines
+   the solution with FP64 residuals until the correction is below 1e-13 of it,
+   falling back to mode 1 for a voxel whose refinement stalls or whose pivot
+   vanishes; mode 1 eliminates the whole system in FP64 with partial pivoting.
+   Both give the FP64 solution to its rounding (mode 0 does ~1/8 of the FP64
+   arithmetic, which this GPU runs at a small fraction of its FP32 rate).
+   PORTA_EINVAL for another mode or a context that is not a polarized
+   multilevel one. Drops any captured iteration graph. */
+int porta_ml_set_solve(porta_ctx *c, int mode);
+
 /* Number of real unknowns per voxel (nlevel for the unpolarized atom). */
 int porta_ml_unknowns(const porta_ctx *c, int *nunk);
 

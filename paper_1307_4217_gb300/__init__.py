@@ -25,5 +25,5 @@ from .binding import (  # noqa: F401
     porta_iterate_ckpt, porta_iterate_vjp, porta_set_tape_limit,
     porta_iterate_timing, MlContext, porta_ml_create, porta_ml_set_atmosphere, porta_ml_set_pops,
     porta_ml_get_pops, porta_ml_formal_solve, porta_ml_see_update, porta_ml_iterate,
-    porta_ml_unknowns, porta_ml_set_unknowns, porta_ml_get_unknowns, porta_ml_emergent_stokes,
+    porta_ml_unknowns, porta_ml_set_solve, porta_ml_set_unknowns, porta_ml_get_unknowns, porta_ml_emergent_stokes,
 )

@@ -111,6 +111,7 @@ _SIGS = {
     "porta_ml_create": (_I, [_P, _P, _P, _P, _P]),
     "porta_ml_set_atmosphere": (_I, [_P, _P, _P, _P, _P, _P, _P, _I]),
     "porta_ml_unknowns": (_I, [_P, _P]),
+    "porta_ml_set_solve": (_I, [_P, _I]),
     "porta_ml_emergent_stokes": (_I, [_P, _I, _I, _P, _P, _P, _I]),
     "porta_ml_set_unknowns": (_I, [_P, _P, _I]),
     "porta_ml_get_unknowns": (_I, [_P, _P, _I]),
@@ -464,6 +465,10 @@ def porta_ml_set_atmosphere(h, chi_ptr, kt_ptr, vel_ptr, bx_ptr, by_ptr, bz_ptr,
 
 def porta_ml_emergent_stokes(h, line, ndir, mu_ptr, chi_ptr, out_ptr, where):
     return lib().porta_ml_emergent_stokes(h, line, ndir, mu_ptr, chi_ptr, out_ptr, where)
+
+
+def porta_ml_set_solve(h, mode):
+    return lib().porta_ml_set_solve(h, mode)
 
 
 def porta_ml_unknowns(h):
@@ -915,6 +920,11 @@ class MlContext(Context):
         p, w, keep = _ptr_where(out)
         self._check(porta_ml_emergent_stokes(self.h, line, len(mu), mu.ctypes.data, chi.ctypes.data, p, w))
         return out
+
+    def set_solve(self, mode):
+        """rate equations of the polarized atom: 0 FP32 factors with FP64 refinement
+        (default), 1 FP64 elimination"""
+        self._check(porta_ml_set_solve(self.h, mode))
 
     def set_unknowns(self, x):
         """the vector of unknowns [voxel][nunk] (populations, or the real multipoles

@@ -184,6 +184,7 @@ int porta_ml_create(const porta_grid *g, const porta_ml_atom *a, const porta_qua
         const double *dd = (const double *)((const char *)m->d_tab + ibytes);
         MlPolDev &d = m->dev;
         d.nunk = tab.nunk;
+        d.solve = 0;
         d.nsrc = tab.nsrc;
         d.ncell = (int)tab.cell_start.size() - 1;
         d.row0 = tab.row0;
@@ -347,6 +348,16 @@ int porta_ml_emergent_stokes(porta_ctx *c, int line, int ndir, const double *mu,
         pfree(dout);
     }
     return rc;
+}
+
+int porta_ml_set_solve(porta_ctx *c, int mode)
+{
+    if (!c) return PORTA_EINVAL;
+    if (!c->ml || !c->ml->pol) return fail(c, PORTA_EINVAL, "ml_set_solve: not a polarized multilevel context");
+    if (mode != 0 && mode != 1) return fail(c, PORTA_EINVAL, "ml_set_solve: mode 0 or 1");
+    c->ml->dev.solve = mode;
+    drop_graph(c);
+    return PORTA_OK;
 }
 
 int porta_ml_unknowns(const porta_ctx *c, int *nunk)

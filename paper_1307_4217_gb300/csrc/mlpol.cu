@@ -600,15 +600,21 @@ __device__ bool mlpol_refine_solve(const double *A, int N, int M, const int *kid
         xr[i] = 0.0;
     }
     __syncthreads();
-    // LU with partial pivoting (rows swapped in place, multipliers below the diagonal)
+    // LU with partial pivoting (rows swapped in place, multipliers below the diagonal).
+    // Step k: swap the pivot row in, then each warp updates its rows r = k+1+w (mod 4)
+    // with the lanes over the columns, stores the row's multiplier, and lane 0 (which
+    // holds column k+1) keeps the largest |value| of that column among the warp's rows:
+    // the next pivot comes from the four warps' candidates after one barrier (two
+    // barriers per step; the pivot is the largest |value|, the smallest row on ties).
+    constexpr int kCols = (kMlPolMaxUnk + 31) / 32;     // column slots per lane
+    float bv = -1.0f;
+    int br = 0;
+    for (int r = tid; r < M; r += kVoxThreads) {
+        const float a = fabsf(LU[r * M]);
+        if (a > bv) { bv = a; br = r; }
+    }
+    cta_argmax(bv, br, redf, redi);
     for (int k = 0; k < M; ++k) {
-        float bv = -1.0f;
-        int br = k;
-        for (int r = k + tid; r < M; r += kVoxThreads) {
-            const float a = fabsf(LU[r * M + k]);
-            if (a > bv) { bv = a; br = r; }
-        }
-        cta_argmax(bv, br, redf, redi);
         if (!(bv > 0.0f)) return false;
         if (tid == 0) piv[k] = br;
         if (br != k)
@@ -619,14 +625,38 @@ __device__ bool mlpol_refine_solve(const double *A, int N, int M, const int *kid
             }
         __syncthreads();
         const float inv = 1.0f / LU[k * M + k];
-        for (int j = k + 1 + lane; j < M; j += 32) {
-            const float ukj = LU[k * M + j];
-#pragma unroll 4
-            for (int r = k + 1 + wid; r < M; r += kVoxWarps) LU[r * M + j] -= (LU[r * M + k] * inv) * ukj;
+        float u[kCols];
+#pragma unroll
+        for (int m = 0; m < kCols; ++m) {
+            const int j = k + 1 + lane + 32 * m;
+            u[m] = j < M ? LU[k * M + j] : 0.0f;
+        }
+        float cv = -1.0f;
+        int cr = M;
+        for (int r = k + 1 + wid; r < M; r += kVoxWarps) {
+            const float l = LU[r * M + k] * inv;
+#pragma unroll
+            for (int m = 0; m < kCols; ++m) {
+                const int j = k + 1 + lane + 32 * m;
+                if (j < M) LU[r * M + j] -= l * u[m];
+            }
+            if (lane == 0) {                // (r > k, so column k + 1 exists)
+                const float a = fabsf(LU[r * M + k + 1]);
+                if (a > cv) { cv = a; cr = r; }
+            }
+        }
+        __syncwarp();
+        for (int r = k + 1 + wid + kVoxWarps * lane; r < M; r += 32 * kVoxWarps) LU[r * M + k] *= inv;
+        if (lane == 0) {
+            redf[wid] = cv;
+            redi[wid] = cr;
         }
         __syncthreads();
-        for (int r = k + 1 + tid; r < M; r += kVoxThreads) LU[r * M + k] *= inv;
-        __syncthreads();
+        bv = redf[0];
+        br = redi[0];
+        for (int w = 1; w < kVoxWarps; ++w)
+            if (redf[w] > bv || (redf[w] == bv && redi[w] < br)) { bv = redf[w]; br = redi[w]; }
+        // (the next step writes red only after its swap barrier)
     }
     double dprev = 1e300;
     for (int it = 0; it < 8; ++it) {
@@ -793,7 +823,8 @@ __global__ void __launch_bounds__(kVoxThreads) mlpol_see_kernel(const MlConst mc
         // elimination in FP64 with partial pivoting on [A | b]: for pivot k the lanes
         // take the columns, the warps the rows of the trailing block
         bool ok = ok1 != 0;
-        const bool refined = ok && M > 0 && mlpol_refine_solve(A, N, M, kidx, LU, y, piv, xr, rr, xn, red, redf, redi);
+        const bool refined =
+            ok && M > 0 && T.solve == 0 && mlpol_refine_solve(A, N, M, kidx, LU, y, piv, xr, rr, xn, red, redf, redi);
         for (int k = 0; k < N && !refined; ++k) {
             double bv = -1.0;
             int br = k;

@@ -35,6 +35,7 @@ struct MlPolTables {
 // device copy (pointers into one allocation)
 struct MlPolDev {
     int nunk, nsrc, ncell, row0;
+    int solve;                       // K > 0 block: 0 FP32 factors + FP64 refinement, 1 FP64 elimination
     int src_j, src_b, src_clu, src_pop, src_spop;
     const int *pop_idx, *upk, *lok, *cell_rc, *cell_start, *ent_src;
     const double *wu, *wl, *trace, *ent_coef;

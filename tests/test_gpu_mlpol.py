@@ -134,6 +134,25 @@ def test_converged_solution_matches_oracle(prec):
     assert np.max(np.abs(want[..., rb.index((3, 2, 0, 0))] / want[..., rb.index((3, 0, 0, 0))])) > 1e-4
 
 
+@pytest.mark.parametrize("prec", [P.PORTA_FP64, P.PORTA_FP32])
+def test_refined_solve_equals_fp64_elimination(prec):
+    """The default solve of the K > 0 block (FP32 factors, FP64 refinement) against the
+    FP64 elimination of the whole system, over iterations from oriented multipoles."""
+    atm, atom, tab, x = _case(seed=11)
+    a = _ctx(atm, atom, prec, x)
+    b = _ctx(atm, atom, prec, x)
+    b.set_solve(1)
+    # FP32 sweeps: one iteration (afterwards the two unknowns, equal to ~1e-13, may round to
+    # FP32 sources one ulp apart)
+    n = 2 if prec == P.PORTA_FP64 else 1
+    a.ml_iterate(n)
+    b.ml_iterate(n)
+    ga, gb = a.get_unknowns(), b.get_unknowns()
+    assert np.max(np.abs(ga - gb)) < 1e-11 * np.max(np.abs(gb))
+    with pytest.raises(P.PortaError):
+        a.set_solve(2)
+
+
 def test_graph_replay_equals_eager_iterations():
     import torch
     atm, atom, tab, x = _case(seed=6)
