@@ -74,15 +74,16 @@ __device__ __forceinline__ Coef<double> coefficients(double t)
 
 // Single precision: three regimes, chosen so that every coefficient stays
 // within 6e-7 relative of its exact value for all t > 0 when evaluated in
-// FP32: degree-7 series for t < 0.25, degree-12 series for t < 1.5, closed
-// forms above (where their cancellation costs at most a factor ~5).
+// FP32: degree-6 series for t < 0.25 (truncation below 2e-7 there), degree-12
+// series for t < 1.5, closed forms above (where their cancellation costs at
+// most a factor ~5).
 // w_M, w_O, w_C of one optical path t given e = exp(-t)
 __device__ __forceinline__ void wcoef(float t, float e, float &wm, float &wo, float &wc)
 {
     if (t < 0.25f) {
-        wm = horner<float, 7, c_wm>(t);
-        wo = horner<float, 7, c_wo>(t);
-        wc = horner<float, 7, c_wc>(t);
+        wm = horner<float, 6, c_wm>(t);
+        wo = horner<float, 6, c_wo>(t);
+        wc = horner<float, 6, c_wc>(t);
     } else if (t < 1.5f) {
         wm = horner<float, 12, c_wm>(t);
         wo = horner<float, 12, c_wo>(t);

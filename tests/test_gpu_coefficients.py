@@ -5,7 +5,7 @@ the closed forms.
 FP64 bound 5e-12: just above the Table 1 crossover (t = 0.14) the closed form of
 omega_M subtracts two numbers near 2 to leave ~t^3/3 = 9e-4, amplifying a few
 ulps (2.2e-16 each) of rounding by ~2200. FP32 bound 1e-6: the three-regime
-evaluation (series of degree 7 / 12, closed forms above t = 1.5) keeps the
+evaluation (series of degree 6 / 12, closed forms above t = 1.5) keeps the
 truncation and cancellation errors below 6e-7."""
 import mpmath
 import numpy as np
