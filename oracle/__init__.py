@@ -69,6 +69,7 @@ class _Problem(ctypes.Structure):
         ("orient", ctypes.c_void_p),
         ("dich1", ctypes.c_void_p),
         ("j1", ctypes.c_void_p),
+        ("sc_faces", ctypes.c_int),
     ]
 
 
@@ -144,7 +145,7 @@ class Problem:
     plus the atomic constants zeta, gbar, bcrit.
     """
 
-    def __init__(self, atm, model, n_mu, n_chi, n_nu, x_max=4.0, method=BESSER, interp=1):
+    def __init__(self, atm, model, n_mu, n_chi, n_nu, x_max=4.0, method=BESSER, interp=1, sc_faces=0):
         self.model = model
         self.shape = (atm["nz"], atm["ny"], atm["nx"])
         self.nvox = int(np.prod(self.shape))
@@ -168,6 +169,9 @@ class Problem:
         self._keep["dich"] = _f64(d).ravel() if d is not None else None
         s.dich = _ptr(self._keep["dich"])
         s.interp = int(interp)          # 1 bilinear, 2 biquadratic (Sec. 3.1)
+        # 0: M and P on the next horizontal planes; 1: on the first cell face the short
+        # characteristic crosses, vertical faces included (Sec. 3.1; forward sweeps only)
+        s.sc_faces = int(sc_faces)
         # explicit medium: atm["kexpl"] (6, nz, ny, nx) = (eta_Q, eta_U, eta_V, rho_Q, rho_U,
         # rho_V) / eta_I and atm["sexpl"] (4, nz, ny, nx) = S, per voxel (polarized model)
         for k in ("kexpl", "sexpl"):

@@ -161,6 +161,119 @@ int or_interp_weights(const or_problem *p, double xc, double yc, int order, int 
     return 4;
 }
 
+/* the bilinear stencil of a point on the first cell face that the short characteristic
+   through node (i, j) crosses between planes k (fraction 0) and k2 (fraction 1), the
+   horizontal offset over that layer being (fx, fy) cells with |fx| or |fy| above 1 (a
+   vertical face): s = 1/max(|fx|, |fy|) of the layer, the face x = x_(i + sgn fx) when
+   |fx| >= |fy| (offset fy s along y, between rows j and j + sgn fy), else y = y_(j + sgn fy);
+   nodes (ii, jj, kk) with weights w; returns the fraction s */
+static double face_stencil(const or_problem *p, int i, int j, int k, int k2, double fx, double fy,
+                           int ii[4], int jj[4], int kk[4], double w[4])
+{
+    const int nx = p->nx, ny = p->ny;
+    const double ax = fabs(fx), ay = fabs(fy);
+    const double s = 1.0 / (ax >= ay ? ax : ay);
+    const int sx = fx > 0 ? 1 : (fx < 0 ? -1 : 0), sy = fy > 0 ? 1 : (fy < 0 ? -1 : 0);
+    int i0, j0, i1, j1;                 /* the two nodes along the face's horizontal direction */
+    double g;                           /* weight of the second one */
+    if (ax >= ay) {
+        i0 = i1 = i + sx;
+        j0 = j;
+        j1 = j + (sy != 0 ? sy : 1);
+        g = ay * s;
+    } else {
+        j0 = j1 = j + sy;
+        i0 = i;
+        i1 = i + (sx != 0 ? sx : 1);
+        g = ax * s;
+    }
+    i0 = ((i0 % nx) + nx) % nx; i1 = ((i1 % nx) + nx) % nx;
+    j0 = ((j0 % ny) + ny) % ny; j1 = ((j1 % ny) + ny) % ny;
+    ii[0] = i0; jj[0] = j0; kk[0] = k;  w[0] = (1.0 - g) * (1.0 - s);
+    ii[1] = i1; jj[1] = j1; kk[1] = k;  w[1] = g * (1.0 - s);
+    ii[2] = i0; jj[2] = j0; kk[2] = k2; w[2] = (1.0 - g) * s;
+    ii[3] = i1; jj[3] = j1; kk[3] = k2; w[3] = g * s;
+    return s;
+}
+
+/* plane k of a sweep whose upwind or downwind characteristic meets a vertical face
+   (sc_faces = 1): every point from the face stencils (or the plane stencil where the
+   offset stays within one cell), the points of the plane in the upwind order, the pass
+   repeated until no intensity changes by more than 1e-15 of the plane's largest
+   (the upwind face's upper nodes are points of this plane; the periodic wrap closes
+   their chain on itself) */
+static int sweep_plane_faces(const or_problem *p, const double *rho, const or_ray *r, double x, double *I,
+                             double *lstar, int k, int ku, int kd, int has_p, double dsM, double dsP)
+{
+    const int ns = or_ns(p->model), nx = p->nx, ny = p->ny;
+    const double dx = p->lx / nx, dy = p->ly / ny;
+    /* horizontal offsets (cells) from O to the upwind plane (backwards) and the downwind plane */
+    const double fxM = -dsM * r->ox / dx, fyM = -dsM * r->oy / dy;
+    const double fxP = dsP * r->ox / dx, fyP = dsP * r->oy / dy;
+    const int vertM = fabs(fxM) > 1.0 || fabs(fyM) > 1.0;
+    const int vertP = has_p && (fabs(fxP) > 1.0 || fabs(fyP) > 1.0);
+    /* upwind order: a point depends on its neighbours towards the upwind offset */
+    const int di = fxM < 0 ? 1 : -1, dj = fyM < 0 ? 1 : -1;
+    for (int pass = 0; pass < 100000; pass++) {
+        double change = 0.0, big = 0.0;
+        for (int jn = 0; jn < ny; jn++)
+            for (int in = 0; in < nx; in++) {
+                const int i = di > 0 ? in : nx - 1 - in, j = dj > 0 ? jn : ny - 1 - jn;
+                const long v = vox(p, i, j, k);
+                int ii[9], jj[9], kk[9];
+                double w[9];
+                double etaM[7] = {0}, epsM[4] = {0}, IM[4] = {0};
+                double sM = 1.0;
+                int nc;
+                if (vertM) {
+                    sM = face_stencil(p, i, j, k, ku, fxM, fyM, ii, jj, kk, w);
+                    nc = 4;
+                } else {
+                    nc = or_interp_weights(p, i + fxM, j + fyM, 1, ii, jj, w);
+                    for (int c = 0; c < nc; c++) kk[c] = ku;
+                }
+                for (int c = 0; c < nc; c++) {
+                    const long u = vox(p, ii[c], jj[c], kk[c]);
+                    double e7[7], e4[4];
+                    corner_coeffs(p, rho, u, r, x, e7, e4);
+                    for (int q = 0; q < 7; q++) etaM[q] += w[c] * e7[q];
+                    for (int s = 0; s < ns; s++) { epsM[s] += w[c] * e4[s]; IM[s] += w[c] * I[u * ns + s]; }
+                }
+                double etaO[7], epsO[4];
+                node_coeffs(p, rho, v, r, x, etaO, epsO);
+                double etaP = 0.0, epsP[4] = {0}, sP = 1.0;
+                if (has_p) {
+                    if (vertP) {
+                        sP = face_stencil(p, i, j, k, kd, fxP, fyP, ii, jj, kk, w);
+                        nc = 4;
+                    } else {
+                        nc = or_interp_weights(p, i + fxP, j + fyP, 1, ii, jj, w);
+                        for (int c = 0; c < nc; c++) kk[c] = kd;
+                    }
+                    for (int c = 0; c < nc; c++) {
+                        const long u = vox(p, ii[c], jj[c], kk[c]);
+                        double e7[7], e4[4];
+                        corner_coeffs(p, rho, u, r, x, e7, e4);
+                        etaP += w[c] * e7[0];
+                        for (int s = 0; s < ns; s++) epsP[s] += w[c] * e4[s];
+                    }
+                }
+                double Io[4], lo;
+                if (or_step(ns, IM, etaM, epsM, etaO, epsO, etaP, epsP, sM * dsM, sP * dsP, has_p, p->method, Io,
+                            &lo) != 0)
+                    return -3;
+                for (int s = 0; s < ns; s++) {
+                    change = fmax(change, fabs(Io[s] - I[v * ns + s]));
+                    big = fmax(big, fabs(Io[s]));
+                    I[v * ns + s] = Io[s];
+                }
+                lstar[v] = lo;
+            }
+        if (!vertM || change <= 1e-15 * big) return 0;
+    }
+    return -4;
+}
+
 /* one (ray, frequency) sweep; I (nvox*ns) and lstar (nvox) are outputs */
 static int sweep(const or_problem *p, const double *rho, const or_ray *r, double x, double *I, double *lstar)
 {
@@ -187,6 +300,14 @@ static int sweep(const or_problem *p, const double *rho, const or_ray *r, double
         double dsM = fabs(p->z[k] - p->z[ku]) / amu;
         double dsP = has_p ? fabs(p->z[kd] - p->z[k]) / amu : 0.0;
         const int order = p->interp == 2 ? 2 : 1;
+        if (p->sc_faces && (fabs(dsM * r->ox / dx) > 1.0 || fabs(dsM * r->oy / dy) > 1.0 ||
+                            (has_p && (fabs(dsP * r->ox / dx) > 1.0 || fabs(dsP * r->oy / dy) > 1.0)))) {
+            for (long v = vox(p, 0, 0, k); v < vox(p, 0, 0, k) + (long)nx * ny; v++)
+                for (int s = 0; s < ns; s++) I[v * ns + s] = 0.0;
+            int rc = sweep_plane_faces(p, rho, r, x, I, lstar, k, ku, kd, has_p, dsM, dsP);
+            if (rc) return rc;
+            continue;
+        }
         for (int j = 0; j < ny; j++)
             for (int i = 0; i < nx; i++) {
                 long v = vox(p, i, j, k);
@@ -232,6 +353,8 @@ static int check(const or_problem *p)
     if (p->model != OR_MODEL_UNPOL && p->model != OR_MODEL_HANLE) return -1;
     if (p->model == OR_MODEL_HANLE && (!p->bx || !p->by || !p->bz)) return -1;
     if (p->interp < 0 || p->interp > 2) return -1;
+    if (p->sc_faces != 0 && p->sc_faces != 1) return -1;
+    if (p->sc_faces && p->interp == 2) return -1;         /* vertical faces: bilinear stencils */
     return 0;
 }
 

@@ -67,6 +67,15 @@ typedef struct {
        j1 (output, or_formal_solve_part): J^1_Q = sum_m w_m T^1_Q(V, Omega_m) Vbar, zeroed first */
     const double *orient, *dich1;
     double *j1;
+    /* where the short characteristic of a point meets the grid (Sec. 3.1): 0 on the
+       horizontal plane of the next upwind / downwind layer (the sheared-frame sweep,
+       offsets of any length); 1 on the first cell face it crosses, a vertical face
+       (x or y = const) when the horizontal offset over the layer exceeds one cell:
+       bilinear in the face's horizontal coordinate and in height between the two
+       planes, the upwind face's upper nodes lying on the point's own plane, whose
+       intensities the plane then determines jointly (periodic in x and y: solved by
+       sweeps in the upwind order repeated to convergence). Forward sweeps only. */
+    int sc_faces;
 } or_problem;
 
 /* the periodic interpolation stencil of the sweep at cell coordinates (xc, yc) of a
