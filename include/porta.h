@@ -185,6 +185,25 @@ int porta_set_explicit_medium(porta_ctx *c, const double *kexpl, const double *s
    porta_iterate_vjp) accept bilinear interpolation only. */
 int porta_set_interpolation(porta_ctx *c, int order);
 
+/* Where the short characteristics of the J^K_Q formal solution end (Sec. 3.1:
+   M and P may lie on a vertical plane of the grid). on = 0 (the default): on the
+   horizontal plane of the next layer, at offsets of any length (the sheared-frame
+   sweeps). on = 1: on the first cell face crossed -- where a ray's horizontal offset
+   over a layer, (f_x, f_y) cells, exceeds one cell, on the vertical face x = x_(i +
+   sgn f_x) (|f_x| >= |f_y|) or y = y_(j + sgn f_y) at the fraction 1/max(|f_x|, |f_y|)
+   of the layer, the face point's quantities bilinear in the face's horizontal
+   coordinate and in height. The upwind face's upper nodes are points of the same
+   plane; with the periodic boundaries (Sec. 4.2) each such plane is solved jointly,
+   by passes over all its points repeated until no intensity changes by more than
+   1e-15 (FP64) or 2e-7 (FP32) of the plane's largest; the face points' Lambda* is
+   their own term (Eq. 14). One CTA per ray, frequencies and planes in order, the
+   per-ray partial sums of the general sweep. Single-box two-level contexts with
+   bilinear stencils (PORTA_EINVAL otherwise); porta_emergent_stokes and the
+   reverse-mode calls reject it, and porta_probe_ray too. A plane still changing after
+   1e5 passes is reported as PORTA_ENOTCONV by the synchronizing calls that read the
+   sums (porta_accumulate_jkq to host). Drops any captured iteration graph. */
+int porta_set_sc_faces(porta_ctx *c, int on);
+
 /* The family of formal solvers compared on the one-ray sigmoid benchmark of
    Sec. 3.4 (Eqs. 15-18, Fig. 5): constant opacity, z = tau, S(z) = sigma(2, -5, z)
    sigma(-2, 5, z), uniform nodes z_i = -12 + shift + i dtau in [-12, 12], the

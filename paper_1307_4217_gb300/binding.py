@@ -112,6 +112,7 @@ _SIGS = {
     "porta_ml_set_atmosphere": (_I, [_P, _P, _P, _P, _P, _P, _P, _I]),
     "porta_ml_unknowns": (_I, [_P, _P]),
     "porta_ml_set_solve": (_I, [_P, _I]),
+    "porta_set_sc_faces": (_I, [_P, _I]),
     "porta_ml_emergent_stokes": (_I, [_P, _I, _I, _P, _P, _P, _I]),
     "porta_ml_set_unknowns": (_I, [_P, _P, _I]),
     "porta_ml_get_unknowns": (_I, [_P, _P, _I]),
@@ -467,6 +468,10 @@ def porta_ml_emergent_stokes(h, line, ndir, mu_ptr, chi_ptr, out_ptr, where):
     return lib().porta_ml_emergent_stokes(h, line, ndir, mu_ptr, chi_ptr, out_ptr, where)
 
 
+def porta_set_sc_faces(h, on):
+    return lib().porta_set_sc_faces(h, on)
+
+
 def porta_ml_set_solve(h, mode):
     return lib().porta_ml_set_solve(h, mode)
 
@@ -792,6 +797,11 @@ class Context:
     def set_interpolation(self, order):
         """Interpolation at M and P: 1 bilinear, 2 biquadratic (Sec. 3.1)."""
         self._check(porta_set_interpolation(self.h, order))
+
+    def set_sc_faces(self, on):
+        """1: short characteristics end on the first cell face they cross (vertical
+        faces included, Sec. 3.1); 0: on the next horizontal plane."""
+        self._check(porta_set_sc_faces(self.h, int(on)))
 
     def mg_set_prolongation(self, order):
         """Prolongation of the multigrid cycles: 1 tri-linear, 3 tri-cubic-centered."""

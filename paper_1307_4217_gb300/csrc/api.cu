@@ -151,7 +151,7 @@ int nl_of(int model) { return model == PORTA_MODEL_TWOLEVEL_UNPOL ? 1 : 6; }
 // only the general sweep (sweep.cu) implements, or a plane is too wide for its
 // shared memory (then the general sweep, which needs less per frequency, runs).
 // (and the biquadratic stencils, which only the general sweep has)
-bool use_jk(const porta_ctx *c) { return c->d_dich == nullptr && c->jk_fits && c->interp != 2; }
+bool use_jk(const porta_ctx *c) { return c->d_dich == nullptr && c->jk_fits && c->interp != 2 && !c->sc_faces; }
 
 // The J^K_Q sweep sums an FP32 formal solution into fixed-point accumulators;
 // an FP64 one keeps per-ray partial integrals summed in ray order in FP64 (a
@@ -286,10 +286,11 @@ cudaError_t finalize_jkq(porta_ctx *c)
 // the fixed-point sums' overflow flag (reads device memory: synchronizes the stream)
 int check_jacc(porta_ctx *c)
 {
-    if (!jfixed(c)) return PORTA_OK;
+    if (!jfixed(c) && !c->sc_faces) return PORTA_OK;
     int flag = 0;
     CK(cudaMemcpyAsync(&flag, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    if (flag & 2) return fail(c, PORTA_ENOTCONV, "formal solution: a plane of face points did not converge");
     if (flag) return fail(c, PORTA_EKERNEL, "formal solution: a J^K_Q term exceeded the fixed-point range (2^16 times "
                                             "max(|S^0_0|, |B|) of its voxel), or was not finite");
     return PORTA_OK;
@@ -349,10 +350,39 @@ cudaError_t sweep_jkq(porta_ctx *c, SweepArgs<Real> a, LaunchCfg cfg, const int 
     return e;
 }
 
+// the formal solution with short characteristics on the first cell face crossed
+template <typename Real>
+int faces_solve_t(porta_ctx *c)
+{
+    cudaError_t e = ensure_sweep_buffers(c);
+    const size_t need = (size_t)c->nray * (3 * c->ns + 1) * c->nx * c->ny * sizeof(Real);
+    if (e == cudaSuccess && c->faces_bytes < need) {
+        if (c->d_faces) pfree(c->d_faces);
+        c->d_faces = nullptr;
+        c->faces_bytes = 0;
+        e = pmalloc(&c->d_faces, need);
+        if (e == cudaSuccess) c->faces_bytes = need;
+    }
+    if (e != cudaSuccess) return fail(c, PORTA_ENOMEM, std::string("formal solution buffers: ") + cudaGetErrorString(e));
+    SweepArgs<Real> a = jkq_args<Real>(c);
+    a.part = c->d_part;
+    e = cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
+    const double dx = c->lx / c->nx, dy = c->ly / c->ny;
+    if (e == cudaSuccess)
+        e = c->ns == 1 ? launch_faces<Real, 1>(a, (Real *)c->d_faces, dx, dy, 100000, c->d_err, c->stream)
+                       : launch_faces<Real, 4>(a, (Real *)c->d_faces, dx, dy, 100000, c->d_err, c->stream);
+    if (e != cudaSuccess) return fail(c, PORTA_ECUDA, std::string("face sweep: ") + cudaGetErrorString(e));
+    return PORTA_OK;
+}
+
 template <typename Real>
 int formal_solve_t(porta_ctx *c, int probe_ray, Real *probe, Real *probe_ls)
 {
     if (c->d_kexpl) return fail(c, PORTA_EINVAL, "formal solution: an explicit medium has emergent profiles only");
+    if (c->sc_faces) {
+        if (probe_ray >= 0) return fail(c, PORTA_EINVAL, "probe ray: not with face intersections");
+        return faces_solve_t<Real>(c);
+    }
     SweepArgs<Real> a = jkq_args<Real>(c);
     a.probe_ray = probe_ray;
     a.probe = probe;
@@ -548,7 +578,7 @@ void free_all(porta_ctx *c)
     void *ptrs[] = {c->d_atm, c->d_eps, c->d_bpl, c->d_b, c->d_rho, c->d_rhoR, c->d_invn, c->d_geom, c->d_rays,
                     c->d_freq, c->d_part, c->d_tw, c->d_jkq, c->d_lstar, c->d_resid, c->d_err, c->d_boxes,
                     c->d_items, c->d_tune_items, c->d_tape, c->d_gpart, c->d_jacc, c->d_jexp, c->d_kexpl, c->d_sexpl,
-                    c->d_partv, c->d_j1, c->d_tw1, c->d_gjR, c->d_vjp_out};
+                    c->d_partv, c->d_j1, c->d_tw1, c->d_gjR, c->d_vjp_out, c->d_faces};
     for (void *p : ptrs)
         if (p) pfree(p);
 }
@@ -1349,6 +1379,19 @@ int porta_set_explicit_medium(porta_ctx *c, const double *kexpl, const double *s
     return rc;
 }
 
+int porta_set_sc_faces(porta_ctx *c, int on)
+{
+    if (!c) return PORTA_EINVAL;
+    if (on != 0 && on != 1) return fail(c, PORTA_EINVAL, "set_sc_faces: 0 or 1");
+    if (on && (c->nbox != 1 || c->ml || c->d_dich || c->d_kexpl || c->interp == 2))
+        return fail(c, PORTA_EINVAL, "set_sc_faces: single-box two-level contexts with bilinear stencils only");
+    if (on == c->sc_faces) return PORTA_OK;
+    c->sc_faces = on;
+    c->have_fs = c->have_jkq = false;
+    drop_graph(c);
+    return PORTA_OK;
+}
+
 int porta_set_interpolation(porta_ctx *c, int order)
 {
     if (!c) return PORTA_EINVAL;
@@ -1357,6 +1400,7 @@ int porta_set_interpolation(porta_ctx *c, int order)
         return fail(c, PORTA_EINVAL, "set_interpolation: the biquadratic stencils have no dichroism (multilevel lines)");
     if (order == 2 && min_ny(c) < 2) return fail(c, PORTA_EINVAL, "set_interpolation: biquadratic needs ny >= 2");
     if (order == 2 && c->d_kexpl) return fail(c, PORTA_EINVAL, "set_interpolation: explicit media are bilinear");
+    if (order == 2 && c->sc_faces) return fail(c, PORTA_EINVAL, "set_interpolation: face intersections are bilinear");
     if (order == c->interp) return PORTA_OK;
     c->interp = order;
     // an autotuned shape of the other stencil need not fit: back to porta_opts' choice

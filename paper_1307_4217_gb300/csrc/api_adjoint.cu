@@ -623,6 +623,7 @@ int porta_emergent_stokes(porta_ctx *c, int ndir, const double *mu, const double
         if (!(mu[d] > 0.0 && mu[d] <= 1.0) || !std::isfinite(chi[d]))
             return fail(c, PORTA_EINVAL, "emergent_stokes: mu must lie in (0, 1], chi finite");
     if (c->nbox != 1) return fail(c, PORTA_EINVAL, "emergent_stokes: single-box contexts only");
+    if (c->sc_faces) return fail(c, PORTA_EINVAL, "emergent_stokes: face intersections are built for the J^K_Q formal solution only");
     if (!c->have_atm || !c->have_rho) return fail(c, PORTA_ESTATE, "emergent_stokes: atmosphere or rho not set");
     const long long n = (long long)ndir * c->n_nu * c->nx * c->ny * c->ns;
     double *dout = out;
@@ -641,8 +642,8 @@ int porta_emergent_stokes(porta_ctx *c, int ndir, const double *mu, const double
 int porta_emergent_vjp(porta_ctx *c, int ndir, const double *mu, const double *chi, const double *grad_out,
                        double *out, double *g_chi, double *g_e, double *g_b, int where)
 {
-    if (c && (c->interp == 2 || c->d_kexpl))
-        return fail(c, PORTA_EINVAL, "reverse mode: bilinear interpolation and the two-level media only");
+    if (c && (c->interp == 2 || c->d_kexpl || c->sc_faces))
+        return fail(c, PORTA_EINVAL, "reverse mode: bilinear interpolation on the horizontal planes, two-level media only");
     if (!c) return PORTA_EINVAL;
     if (ndir < 1 || !mu || !chi || !grad_out || !g_chi || !g_e || (c->ns > 1 && !g_b) ||
         (where != PORTA_HOST && where != PORTA_DEVICE))
@@ -745,8 +746,8 @@ int porta_set_tape_limit(porta_ctx *c, long long bytes)
 int porta_iterate_vjp(porta_ctx *c, int ndir, const double *mu, const double *chi, const double *grad_out, double *out,
                       double *g_chi, double *g_f, double *g_b, int where)
 {
-    if (c && (c->interp == 2 || c->d_kexpl))
-        return fail(c, PORTA_EINVAL, "reverse mode: bilinear interpolation and the two-level media only");
+    if (c && (c->interp == 2 || c->d_kexpl || c->sc_faces))
+        return fail(c, PORTA_EINVAL, "reverse mode: bilinear interpolation on the horizontal planes, two-level media only");
     if (!c) return PORTA_EINVAL;
     if (ndir < 1 || !mu || !chi || !grad_out || !g_chi || !g_f || (c->ns > 1 && !g_b) ||
         (where != PORTA_HOST && where != PORTA_DEVICE))

@@ -115,6 +115,9 @@ struct porta_ctx {
     double *mg_zp3 = nullptr;       // the same for the cubic: per fine plane 4 x (coarse plane, weight)
     int mg_order = 1;               // prolongation: 1 tri-linear, 3 tri-cubic-centered (finest level)
     int interp = 1;                 // interpolation at M and P: 1 bilinear, 2 biquadratic (general sweep)
+    int sc_faces = 0;               // 1: M and P on the first cell face crossed (faces.cu, J^K_Q formal solution)
+    void *d_faces = nullptr;        // its per-ray plane buffers (allocated on first use)
+    size_t faces_bytes = 0;
     double *d_kexpl = nullptr;      // explicit medium: K'/eta_I [6][nvox] and S [4][nvox] (emergent sweep)
     double *d_sexpl = nullptr;
     // reverse mode of the emergent sweep: tape of the forward Stokes vectors,

@@ -1,0 +1,80 @@
+"""Short characteristics ending on the first cell face they cross (Sec. 3.1,
+porta_set_sc_faces(1), faces.cu) against the oracle's face sweep (oracle
+`sc_faces=1`): J^K_Q and Lambda-bar* of a formal solution of a random box whose
+grazing rays meet vertical faces (each such plane solved jointly, the periodic
+chains closed), the Jacobi update from them, determinism, and the rejected
+combinations. Tolerances as the bilinear parity tests: FP64 1e-10, FP32 1e-5
+(the FP32 plane solve stops at 2e-7 of the plane's largest change)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_1307_4217_gb300 as P
+import synth
+from gpu_util import initial_rho, make_ctx
+
+pytestmark = pytest.mark.gpu
+
+
+def _max_offset(atm, p):
+    mu, chi, _ = oracle.rays(p)
+    dz = np.min(np.abs(np.diff(atm["z"])))
+    dx, dy = atm["lx"] / atm["nx"], atm["ly"] / atm["ny"]
+    t = np.sqrt(1 - mu ** 2) / np.abs(mu)
+    return np.max(dz * t * np.maximum(np.abs(np.cos(chi)) / dx, np.abs(np.sin(chi)) / dy))
+
+
+def _check(jg, lg, jo, lo, tol):
+    s = np.abs(jo[..., :1])
+    assert np.max(np.abs(jg - jo) / s) < tol
+    assert np.max(np.abs(lg - lo) / np.abs(lo)) < tol
+
+
+@pytest.mark.parametrize("prec,tol", [(P.PORTA_FP64, 1e-10), (P.PORTA_FP32, 1e-5)])
+@pytest.mark.parametrize("model", [0, 1])
+def test_face_formal_solution_matches_oracle(prec, tol, model):
+    atm = synth.random_box(9, 7, 10, seed=21, sigma_lnchi=0.1, sigma_v=0.3)
+    rho = initial_rho(atm, model, seed=22)
+    quad = (2, 4, 5)
+    p = oracle.Problem(atm, model, *quad, sc_faces=1)
+    assert _max_offset(atm, p) > 2.0              # grazing rays cross vertical faces
+    ctx = make_ctx(atm, model, *quad, prec, rho=rho)
+    ctx.set_sc_faces(1)
+    ctx.formal_solve()
+    jg, lg = ctx.accumulate_jkq()
+    jo, lo = oracle.formal_solve(p, rho)
+    _check(jg, lg, jo, lo, tol)
+    # the placement matters: the plane sweep gives another field
+    jb, _ = oracle.formal_solve(oracle.Problem(atm, model, *quad), rho)
+    assert np.max(np.abs(jb - jo) / np.abs(jo[..., :1])) > 100 * tol
+    # the update from these sums is the oracle's
+    ch = ctx.see_update()
+    _, cho = oracle.see_update(p, jo, lo, rho)
+    assert abs(ch - cho) < 10 * tol * cho
+    ctx.close()
+
+
+def test_face_formal_solution_is_deterministic_and_options_are_checked():
+    atm = synth.random_box(8, 6, 8, seed=5)
+    rho = initial_rho(atm, 1, seed=6)
+    ctx = make_ctx(atm, 1, 2, 4, 3, P.PORTA_FP32, rho=rho)
+    ctx.set_sc_faces(1)
+    ctx.formal_solve()
+    j1, l1 = ctx.accumulate_jkq()
+    ctx.formal_solve()
+    j2, l2 = ctx.accumulate_jkq()
+    assert np.array_equal(j1, j2) and np.array_equal(l1, l2)
+    with pytest.raises(P.PortaError):
+        ctx.set_sc_faces(2)
+    with pytest.raises(P.PortaError):
+        ctx.set_interpolation(2)
+    mu, az = synth.emergent_directions()
+    with pytest.raises(P.PortaError):
+        ctx.emergent_stokes(mu, az)
+    ctx.set_sc_faces(0)                          # back to the plane sweep
+    ctx.formal_solve()
+    j3, _ = ctx.accumulate_jkq()
+    assert not np.array_equal(j1, j3)
+    ctx.close()
