@@ -110,6 +110,8 @@ def args_parse():
     ap.add_argument("--batch-steps", type=int, default=3,
                     help="timed Jacobi iterations of the 256-box batch beside the default workload (0 skips them)")
     ap.add_argument("--c0", type=int, default=1, help="time the unpolarized 16x16x32 box to convergence (0 skips it)")
+    ap.add_argument("--faces", type=int, default=1,
+                    help="time the formal solution with short characteristics on the first cell face (0 skips it)")
     ap.add_argument("--solver-family", type=int, default=1,
                     help="E(dtau) of the Sec. 3.4 solver family on the sigmoid benchmark (0 skips it)")
     ap.add_argument("--peak-seconds", type=float, default=1.0, help="device time per FMA-peak measurement")
@@ -801,6 +803,30 @@ def run_cuda(args):
         family["cases_per_call"] = int(dts.size)
         family["timing"] = "wall clock around porta_sigmoid_error (host copies and one launch, one thread per case)"
 
+    # the same formal solution with M and P on the first cell face crossed (vertical faces for
+    # grazing rays: each such plane solved by ordered line sweeps repeated to convergence)
+    faces = None
+    if args.faces and wl.name == "pol64" and world == 1:
+        with torch.cuda.stream(stream):
+            ctx.set_sc_faces(1)
+            ctx.formal_solve()
+            jf, lf = ctx.accumulate_jkq()
+            evf = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            flush.zero_()
+            evf[0].record(stream)
+            ctx.formal_solve()
+            evf[1].record(stream)
+            barrier()
+            f_ms = evf[0].elapsed_time(evf[1])
+            ctx.set_sc_faces(0)
+            ctx.formal_solve()
+            jp, lp = ctx.accumulate_jkq()
+        faces = {"workload": wl.desc.split(";")[0] + "; one J^K_Q formal solution, FP32",
+                 "ms": f_ms, "updates_per_s": wl.updates / (f_ms * 1e-3),
+                 "ratio_to_plane_sweep": f_ms / sweep_ms,
+                 "J00_rel_diff_to_plane_placement": float(np.max(np.abs(jf[..., 0] - jp[..., 0]) / np.abs(jp[..., 0]))),
+                 "timing": "CUDA events around one porta_formal_solve with porta_set_sc_faces(1) (L2 flushed)"}
+
     # the 256 boxes of uneven size in one persistent launch per sweep (graph replays)
     batch = None
     if args.batch_steps > 0 and wl.name == "pol64" and world == 1:
@@ -877,6 +903,7 @@ def run_cuda(args):
         "fp64_plain": fp64,
         "unpolarized_c0": c0,
         "solver_family": family,
+        "sc_faces": faces,
         "batched256": batch,
         "adjoint": adjoint,
         "multigrid": mgres,

@@ -14,7 +14,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libporta_gb300.so")
 SOURCES = ["sweep.cu", "see.cu", "api.cu", "api_adjoint.cu", "api_mg.cu", "api_ml.cu", "noalloc.cu", "adjoint.cu", "mg.cu", "ml.cu", "mlpol.cu", "peak.cu", "sweep_j.cu", "solvers.cu", "faces.cu"]
-HEADERS = ["device_math.cuh", "porta_internal.cuh", "see_kernels.cuh", "sweep_common.cuh", "adjoint_math.cuh", "porta_ctx.h", "api_internal.h", "mg_kernels.cuh", "ml_kernels.cuh", "mlpol_kernels.cuh"]
+HEADERS = ["device_math.cuh", "porta_internal.cuh", "see_kernels.cuh", "sweep_common.cuh", "adjoint_math.cuh", "porta_ctx.h", "api_internal.h", "mg_kernels.cuh", "ml_kernels.cuh", "mlpol_kernels.cuh", "faces_kernels.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 

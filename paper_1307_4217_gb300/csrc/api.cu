@@ -17,6 +17,7 @@
 #include "api_internal.h"
 #include "mg_kernels.cuh"
 #include "ml_kernels.cuh"
+#include "faces_kernels.cuh"
 #include "mlpol_kernels.cuh"
 #include "see_kernels.cuh"
 
@@ -355,7 +356,9 @@ template <typename Real>
 int faces_solve_t(porta_ctx *c)
 {
     cudaError_t e = ensure_sweep_buffers(c);
-    const size_t need = (size_t)c->nray * (3 * c->ns + 1) * c->nx * c->ny * sizeof(Real);
+    const long long nxy = (long long)c->nx * c->ny;
+    const size_t need = c->ns == 1 ? faces_scratch_bytes<Real, 1>(c->nray, jnu(c), nxy, c->nvox)
+                                   : faces_scratch_bytes<Real, 4>(c->nray, jnu(c), nxy, c->nvox);
     if (e == cudaSuccess && c->faces_bytes < need) {
         if (c->d_faces) pfree(c->d_faces);
         c->d_faces = nullptr;
@@ -369,8 +372,8 @@ int faces_solve_t(porta_ctx *c)
     e = cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
     const double dx = c->lx / c->nx, dy = c->ly / c->ny;
     if (e == cudaSuccess)
-        e = c->ns == 1 ? launch_faces<Real, 1>(a, (Real *)c->d_faces, dx, dy, 100000, c->d_err, c->stream)
-                       : launch_faces<Real, 4>(a, (Real *)c->d_faces, dx, dy, 100000, c->d_err, c->stream);
+        e = c->ns == 1 ? launch_faces<Real, 1>(a, (Real *)c->d_faces, nxy, dx, dy, 100000, c->d_err, c->stream)
+                       : launch_faces<Real, 4>(a, (Real *)c->d_faces, nxy, dx, dy, 100000, c->d_err, c->stream);
     if (e != cudaSuccess) return fail(c, PORTA_ECUDA, std::string("face sweep: ") + cudaGetErrorString(e));
     return PORTA_OK;
 }

@@ -10,23 +10,26 @@
 // between the two planes. The upwind face's upper nodes belong to the point's
 // own plane, so the plane's intensities depend on each other; with periodic
 // horizontal boundaries their chains close on themselves (Sec. 4.2). Each such
-// plane is solved here by Jacobi passes over all its points (every pass from
-// the previous pass's values of the plane and the finished upwind plane)
-// repeated until no intensity changes by more than a tolerance of the plane's
-// largest: the fixed point of the plane's SC relations. Where the offset stays
-// within a cell, M (or P) lies on the neighbouring plane and one pass is exact.
+// plane is swept line by line in the upwind order (the points of a line depend
+// only on the line before it), in place, and the pass repeated until no
+// intensity changes by more than a tolerance of the plane's largest: the fixed
+// point of the plane's SC relations (a pass carries the chain once around the
+// periodic domain, so the wrap converges geometrically, by ~(1 - s)^n per pass
+// over n lines). Where the offset stays within a cell, M (or P) lies on the
+// neighbouring plane and one parallel pass is exact.
 //
 // One CTA per ray (a grid-stride loop over rays), the frequencies in order, the
-// planes in sweep order; the ray's three plane buffers (the upwind plane and
-// two iterates of the current one) and its Lambda* plane live in global scratch
-// memory; the per-ray partial sums are those of the general sweep (stored on
-// the first frequency, added on the later ones, then summed over rays in ray
-// order by the J^K_Q finalize). A plane that does not converge within maxpass
-// passes sets bit 2 of the error flag and keeps its last pass.
+// planes in sweep order; the ray's Stokes planes (upwind and current), its
+// Lambda* plane and the per-frequency transfer coefficients of the planes ku, k
+// and kd (computed once per plane and frequency) live in global scratch memory
+// (L2-resident at these sizes); the per-ray partial sums are those of the general
+// sweep (stored on the first frequency, added on the later ones, then summed
+// over rays in ray order by the J^K_Q finalize). A plane that does not converge
+// within maxpass passes sets bit 2 of the error flag and keeps its last pass.
 #include <algorithm>
 
 #include "device_math.cuh"
-#include "porta_internal.cuh"
+#include "faces_kernels.cuh"
 #include "sweep_common.cuh"
 
 namespace porta {
@@ -111,76 +114,95 @@ __device__ __forceinline__ void node_coef(const Node<Real, NS> &n, Real x, Real 
     }
 }
 
+// the transfer coefficients of every node of plane k at frequency x: eta_I, eta_V,
+// eps (NS) at cw[(c * nxy) + p], c = 0 .. NS + 1
 template <typename Real, int NS>
-__global__ void __launch_bounds__(256) faces_kernel(const SweepArgs<Real> a, Real *scratch, double dx, double dy,
-                                                   int maxpass, Real tol, int *err)
+__device__ __forceinline__ void plane_coefs(const SweepArgs<Real> &a, const RayDev<Real> &ray, int m, long long base,
+                                            long long nxy, Real x, Real *cw)
 {
-    __shared__ Real red[8];
+    for (long long p = threadIdx.x; p < nxy; p += blockDim.x) {
+        const Node<Real, NS> n = make_node<Real, NS>(a, ray, base + p, m, false);
+        Real eI, eV, e4[NS];
+        node_coef<Real, NS>(n, x, eI, eV, e4);
+        cw[p] = eI;
+        cw[nxy + p] = eV;
+#pragma unroll
+        for (int s = 0; s < NS; ++s) cw[(2 + s) * nxy + p] = e4[s];
+    }
+}
+
+// One CTA per ray. Per frequency and plane: the coefficients of the planes k (the
+// points and the upper nodes of their faces), ku (upwind) and kd (downwind) in the
+// ray's scratch, then the plane's points. Where M lies on the upwind plane (offset
+// within a cell) one parallel pass is exact; where it lies on vertical faces the
+// plane is swept line by line in the upwind order (columns for x faces, rows for y
+// faces: a line's points depend only on the line before), in place, and the pass is
+// repeated until no intensity changes by more than tol of the plane's largest (the
+// first line of a pass reads the last line of the previous one: the periodic chain).
+template <typename Real, int NS>
+__global__ void __launch_bounds__(128) faces_kernel(const SweepArgs<Real> a, Real *scratch, Real *gpart, int ngroups,
+                                                   double dx, double dy, int maxpass, Real tol, int *err)
+{
+    constexpr int NC = NS + 2;                    // coefficient words per node
+    __shared__ Real red[4];
     const BoxDev B = a.boxes[0];
     const int nx = B.nx, ny = B.ny, nz = B.nz;
     const long long nxy = (long long)nx * ny;
-    for (int m = blockIdx.x; m < a.nray; m += gridDim.x) {
+    const int fper = (a.nnu + ngroups - 1) / ngroups;
+    // work items: (ray, frequency group), each CTA with its own scratch slot
+    for (int item = blockIdx.x; item < a.nray * ngroups; item += gridDim.x) {
+        const int m = item / ngroups, grp = item - m * ngroups;
         const RayDev<Real> ray = a.rays[m];
         const PlaneGeom<Real> *G = a.geom + B.geom0 + (long long)m * nz;
         const bool upward = ray.mu > Real(0);
-        Real *buf[3] = {scratch + ((long long)m * (3 * NS + 1)) * nxy, nullptr, nullptr};
-        buf[1] = buf[0] + NS * nxy;
-        buf[2] = buf[1] + NS * nxy;
-        Real *lsb = buf[2] + NS * nxy;
-        for (int j = 0; j < a.nnu; ++j) {
+        // scratch of the CTA: I of the upwind plane and of the current one, Lambda*,
+        // the coefficients of planes ku, k, kd
+        Real *Iu = scratch + (long long)blockIdx.x * (2 * NS + 1 + 3 * NC) * nxy;
+        Real *Ik = Iu + NS * nxy;
+        Real *lsb = Ik + NS * nxy;
+        Real *cu = lsb + nxy, *ck = cu + NC * nxy, *cd = ck + NC * nxy;
+        // this item's partial sums over its frequencies: [ray][group][nvox]
+        Real *part = gpart + ((long long)m * ngroups + grp) * a.nvox * (NS == 1 ? 2 : 4);
+        const int jb = grp * fper, je = min(a.nnu, jb + fper);
+        for (int j = jb; j < je; ++j) {
             const Real x = a.xf[j], wf = a.wf[j];
-            int up = 0;                                   // buffer of the finished upwind plane
             for (int q = 0; q < nz; ++q) {
                 const int k = G[q].kz;
+                const long long base = B.vox0 + (long long)k * nxy;
                 if (q == 0) {
                     for (long long p = threadIdx.x; p < nxy; p += blockDim.x) {
-                        const long long v = B.vox0 + (long long)k * nxy + p;
+                        const long long v = base + p;
                         Real I0[NS];
 #pragma unroll
                         for (int s = 0; s < NS; ++s) I0[s] = Real(0);
                         if (upward) I0[0] = a.bpl[v];
 #pragma unroll
-                        for (int s = 0; s < NS; ++s) buf[0][s * nxy + p] = I0[s];
-                        const Node<Real, NS> nO = make_node<Real, NS>(a, ray, v, m, true);
-                        const Real wt = wf * profile_shape(x - nO.s) * nO.invn;
-                        Real acc[NS == 1 ? 2 : 4] = {};
-                        acc[0] = wt * I0[0];
-                        if constexpr (NS == 1) {
-                            R2<Real> *pp = reinterpret_cast<R2<Real> *>(a.part) + (long long)m * a.nvox + v;
-                            R2<Real> o = {acc[0], acc[1]};
-                            if (j > 0) { const R2<Real> old = *pp; o.x += old.x; o.y += old.y; }
-                            *pp = o;
-                        } else {
-                            R4<Real> *pp = reinterpret_cast<R4<Real> *>(a.part) + (long long)m * a.nvox + v;
-                            R4<Real> o = {acc[0], acc[1], acc[2], acc[3]};
-                            if (j > 0) { const R4<Real> old = *pp; o.x += old.x; o.y += old.y; o.z += old.z; o.w += old.w; }
-                            *pp = o;
-                        }
+                        for (int s = 0; s < NS; ++s) Ik[s * nxy + p] = I0[s];
+                        lsb[p] = Real(0);
                     }
+                } else {
+                    const int ku = G[q - 1].kz;
+                    const bool has_p = q + 1 < nz;
+                    const int kd = has_p ? G[q + 1].kz : k;
+                    const double dsM = (double)G[q].ds, dsP = has_p ? (double)G[q + 1].ds : 0.0;
+                    const double fxM = -dsM * (double)ray.ox / dx, fyM = -dsM * (double)ray.oy / dy;
+                    const double fxP = dsP * (double)ray.ox / dx, fyP = dsP * (double)ray.oy / dy;
+                    const bool vertM = fabs(fxM) > 1.0 || fabs(fyM) > 1.0;
+                    const bool vertP = has_p && (fabs(fxP) > 1.0 || fabs(fyP) > 1.0);
+                    // the finished plane becomes the upwind one; coefficients of ku, k, kd
+                    for (long long e = threadIdx.x; e < NS * nxy; e += blockDim.x) {
+                        Iu[e] = Ik[e];
+                        Ik[e] = Real(0);
+                    }
+                    plane_coefs<Real, NS>(a, ray, m, B.vox0 + (long long)ku * nxy, nxy, x, cu);
+                    plane_coefs<Real, NS>(a, ray, m, base, nxy, x, ck);
+                    if (has_p) plane_coefs<Real, NS>(a, ray, m, B.vox0 + (long long)kd * nxy, nxy, x, cd);
                     __syncthreads();
-                    continue;
-                }
-                const int ku = G[q - 1].kz;
-                const bool has_p = q + 1 < nz;
-                const int kd = has_p ? G[q + 1].kz : k;
-                const double dsM = (double)G[q].ds, dsP = has_p ? (double)G[q + 1].ds : 0.0;
-                const double fxM = -dsM * (double)ray.ox / dx, fyM = -dsM * (double)ray.oy / dy;
-                const double fxP = dsP * (double)ray.ox / dx, fyP = dsP * (double)ray.oy / dy;
-                const bool vertM = fabs(fxM) > 1.0 || fabs(fyM) > 1.0;
-                const bool vertP = has_p && (fabs(fxP) > 1.0 || fabs(fyP) > 1.0);
-                int cur = (up + 1) % 3, nxt = (up + 2) % 3;
-                // start the plane's iterate from zero
-                for (long long p = threadIdx.x; p < NS * nxy; p += blockDim.x) buf[cur][p] = Real(0);
-                __syncthreads();
-                int pass = 0;
-                for (;; ++pass) {
-                    Real change = 0, big = 0;
-                    for (long long p = threadIdx.x; p < nxy; p += blockDim.x) {
-                        const int jy = (int)(p / nx), ix = (int)(p - (long long)jy * nx);
-                        const long long vO = B.vox0 + (long long)k * nxy + p;
+                    // one point's update (in place into Ik); returns the change of its Stokes vector
+                    auto update = [&](int ix, int jy, Real &chg, Real &mag) {
+                        const long long p = (long long)jy * nx + ix;
                         int ii[4], jj[4];
                         double w[4];
-                        // upwind point M
                         Real etaM = 0, etaVM = 0, epsM[NS], IM[NS];
 #pragma unroll
                         for (int s = 0; s < NS; ++s) epsM[s] = IM[s] = Real(0);
@@ -189,27 +211,23 @@ __global__ void __launch_bounds__(256) faces_kernel(const SweepArgs<Real> a, Rea
                         else plane_stencil(nx, ny, ix, jy, fxM, fyM, ii, jj, w);
 #pragma unroll
                         for (int c = 0; c < 4; ++c) {
-                            const int kk = vertM && c < 2 ? k : ku;
-                            const Real *Ib = vertM && c < 2 ? buf[cur] : buf[up];
+                            const bool own = vertM && c < 2;
+                            const Real *cc = own ? ck : cu;
+                            const Real *Ib = own ? Ik : Iu;
                             const long long pc = (long long)jj[c] * nx + ii[c];
-                            const long long u = B.vox0 + (long long)kk * nxy + pc;
-                            const Node<Real, NS> n = make_node<Real, NS>(a, ray, u, m, false);
-                            Real eI, eV, e4[NS];
-                            node_coef<Real, NS>(n, x, eI, eV, e4);
                             const Real wc = (Real)w[c];
-                            etaM += wc * eI;
-                            etaVM += wc * eV;
+                            etaM += wc * cc[pc];
+                            etaVM += wc * cc[nxy + pc];
 #pragma unroll
                             for (int s = 0; s < NS; ++s) {
-                                epsM[s] += wc * e4[s];
+                                epsM[s] += wc * cc[(2 + s) * nxy + pc];
                                 IM[s] += wc * Ib[s * nxy + pc];
                             }
                         }
-                        // the point O
-                        const Node<Real, NS> nO = make_node<Real, NS>(a, ray, vO, m, true);
-                        Real etaO, etaVO, epsO[NS];
-                        node_coef<Real, NS>(nO, x, etaO, etaVO, epsO);
-                        // downwind point P
+                        const Real etaO = ck[p], etaVO = ck[nxy + p];
+                        Real epsO[NS];
+#pragma unroll
+                        for (int s = 0; s < NS; ++s) epsO[s] = ck[(2 + s) * nxy + p];
                         Real etaP = 0, epsP[NS];
 #pragma unroll
                         for (int s = 0; s < NS; ++s) epsP[s] = Real(0);
@@ -219,15 +237,12 @@ __global__ void __launch_bounds__(256) faces_kernel(const SweepArgs<Real> a, Rea
                             else plane_stencil(nx, ny, ix, jy, fxP, fyP, ii, jj, w);
 #pragma unroll
                             for (int c = 0; c < 4; ++c) {
-                                const int kk = vertP && c < 2 ? k : kd;
-                                const long long u = B.vox0 + (long long)kk * nxy + (long long)jj[c] * nx + ii[c];
-                                const Node<Real, NS> n = make_node<Real, NS>(a, ray, u, m, false);
-                                Real eI, eV, e4[NS];
-                                node_coef<Real, NS>(n, x, eI, eV, e4);
+                                const Real *cc = vertP && c < 2 ? ck : cd;
+                                const long long pc = (long long)jj[c] * nx + ii[c];
                                 const Real wc = (Real)w[c];
-                                etaP += wc * eI;
+                                etaP += wc * cc[pc];
 #pragma unroll
-                                for (int s = 0; s < NS; ++s) epsP[s] += wc * e4[s];
+                                for (int s = 0; s < NS; ++s) epsP[s] += wc * cc[(2 + s) * nxy + pc];
                             }
                         }
                         const Real dM = (Real)(sM * dsM), dP = (Real)(sP * dsP);
@@ -251,66 +266,133 @@ __global__ void __launch_bounds__(256) faces_kernel(const SweepArgs<Real> a, Rea
                         }
 #pragma unroll
                         for (int s = 0; s < NS; ++s) {
-                            const Real old = buf[cur][s * nxy + p];
-                            change = fmax(change, fabs(IO[s] - old));
-                            big = fmax(big, fabs(IO[s]));
-                            buf[nxt][s * nxy + p] = IO[s];
+                            chg = fmax(chg, fabs(IO[s] - Ik[s * nxy + p]));
+                            mag = fmax(mag, fabs(IO[s]));
+                            Ik[s * nxy + p] = IO[s];
                         }
                         lsb[p] = ls;
-                    }
-                    change = block_max(change, red);
-                    big = block_max(big, red);
-                    {
-                        const int t = cur; cur = nxt; nxt = t;
-                    }
-                    __syncthreads();
-                    if (!vertM || !(change > tol * big)) break;
-                    if (pass + 1 >= maxpass) {
-                        if (threadIdx.x == 0) atomicOr(err, 2);
-                        break;
+                    };
+                    if (!vertM) {
+                        Real chg = 0, mag = 0;
+                        for (long long p = threadIdx.x; p < nxy; p += blockDim.x) {
+                            const int jy = (int)(p / nx), ix = (int)(p - (long long)jy * nx);
+                            update(ix, jy, chg, mag);
+                        }
+                    } else {
+                        // lines in the upwind order: a point depends on the line at +sgn(f)
+                        const bool xface = fabs(fxM) >= fabs(fyM);
+                        const int n_lines = xface ? nx : ny, n_pts = xface ? ny : nx;
+                        const int step = xface ? (fxM > 0 ? -1 : 1) : (fyM > 0 ? -1 : 1);
+                        for (int pass = 0;; ++pass) {
+                            Real chg = 0, mag = 0;
+                            for (int t = 0; t < n_lines; ++t) {
+                                const int line = (((step * t) % n_lines) + n_lines) % n_lines;
+                                for (int i = threadIdx.x; i < n_pts; i += blockDim.x) {
+                                    if (xface) update(line, i, chg, mag);
+                                    else update(i, line, chg, mag);
+                                }
+                                __syncthreads();
+                            }
+                            chg = block_max(chg, red);
+                            mag = block_max(mag, red);
+                            if (!(chg > tol * mag)) break;
+                            if (pass + 1 >= maxpass) {
+                                if (threadIdx.x == 0) atomicOr(err, 2);
+                                break;
+                            }
+                        }
                     }
                 }
+                __syncthreads();
                 // the plane's sums: w_j phi_O / N (I, Q, U, Lambda*) added to the ray's partials
                 for (long long p = threadIdx.x; p < nxy; p += blockDim.x) {
-                    const long long vO = B.vox0 + (long long)k * nxy + p;
+                    const long long vO = base + p;
                     const Node<Real, NS> nO = make_node<Real, NS>(a, ray, vO, m, true);
                     const Real wt = wf * profile_shape(x - nO.s) * nO.invn;
                     if constexpr (NS == 1) {
-                        R2<Real> *pp = reinterpret_cast<R2<Real> *>(a.part) + (long long)m * a.nvox + vO;
-                        R2<Real> o = {wt * buf[cur][p], wt * lsb[p]};
-                        if (j > 0) { const R2<Real> old = *pp; o.x += old.x; o.y += old.y; }
+                        R2<Real> *pp = reinterpret_cast<R2<Real> *>(part) + vO;
+                        R2<Real> o = {wt * Ik[p], wt * lsb[p]};
+                        if (j > jb) { const R2<Real> old = *pp; o.x += old.x; o.y += old.y; }
                         *pp = o;
                     } else {
-                        R4<Real> *pp = reinterpret_cast<R4<Real> *>(a.part) + (long long)m * a.nvox + vO;
-                        R4<Real> o = {wt * buf[cur][p], wt * buf[cur][nxy + p], wt * buf[cur][2 * nxy + p], wt * lsb[p]};
-                        if (j > 0) { const R4<Real> old = *pp; o.x += old.x; o.y += old.y; o.z += old.z; o.w += old.w; }
+                        R4<Real> *pp = reinterpret_cast<R4<Real> *>(part) + vO;
+                        R4<Real> o = {wt * Ik[p], wt * Ik[nxy + p], wt * Ik[2 * nxy + p], wt * lsb[p]};
+                        if (j > jb) { const R4<Real> old = *pp; o.x += old.x; o.y += old.y; o.z += old.z; o.w += old.w; }
                         *pp = o;
                     }
                 }
                 __syncthreads();
-                up = cur;
             }
         }
     }
 }
 
+// per ray and voxel: the frequency groups' partial sums added in group order
+template <typename Real, int NA>
+__global__ void faces_group_sum_kernel(const Real *gpart, int ngroups, long long nvox, int nray, Real *part)
+{
+    const long long n = (long long)nray * nvox;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const long long m = e / nvox, v = e - m * nvox;
+        Real s[NA] = {};
+        for (int g = 0; g < ngroups; ++g) {
+            const Real *p = gpart + ((m * ngroups + g) * nvox + v) * NA;
+#pragma unroll
+            for (int c = 0; c < NA; ++c) s[c] += p[c];
+        }
+#pragma unroll
+        for (int c = 0; c < NA; ++c) part[e * NA + c] = s[c];
+    }
+}
+
 }  // namespace
 
+// frequency groups per ray: enough (ray, group) items for ~8 CTAs per SM
+int faces_groups(int nray, int nnu)
+{
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    return std::max(1, std::min(nnu, (8 * std::max(1, nsm) + nray - 1) / std::max(1, nray)));
+}
+
 template <typename Real, int NS>
-cudaError_t launch_faces(const SweepArgs<Real> &a, Real *scratch, double dx, double dy, int maxpass, int *err,
-                         cudaStream_t st)
+size_t faces_scratch_bytes(int nray, int nnu, long long nxy, long long nvox)
+{
+    const int ng = faces_groups(nray, nnu);
+    const long long items = (long long)nray * ng;
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const long long ctas = std::min<long long>(items, 8LL * std::max(1, nsm));
+    return sizeof(Real) * ((size_t)ctas * (2 * NS + 1 + 3 * (NS + 2)) * nxy + (size_t)items * nvox * (NS == 1 ? 2 : 4));
+}
+
+template <typename Real, int NS>
+cudaError_t launch_faces(const SweepArgs<Real> &a, Real *scratch, long long nxy, double dx, double dy, int maxpass,
+                         int *err, cudaStream_t st)
 {
     const Real tol = sizeof(Real) == 8 ? Real(1e-15) : Real(2e-7);
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const int blocks = std::max(1, std::min(a.nray, 4 * nsm));
-    faces_kernel<Real, NS><<<blocks, 256, 0, st>>>(a, scratch, dx, dy, maxpass, tol, err);
+    const int ng = faces_groups(a.nray, a.nnu);
+    const long long items = (long long)a.nray * ng;
+    const int ctas = (int)std::min<long long>(items, 8LL * std::max(1, nsm));
+    Real *gpart = scratch + (size_t)ctas * (2 * NS + 1 + 3 * (NS + 2)) * nxy;
+    faces_kernel<Real, NS><<<ctas, 128, 0, st>>>(a, scratch, gpart, ng, dx, dy, maxpass, tol, err);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const long long n = (long long)a.nray * a.nvox;
+    const int blocks = (int)std::min<long long>((n + 255) / 256, 16LL * std::max(1, nsm));
+    faces_group_sum_kernel<Real, NS == 1 ? 2 : 4><<<blocks, 256, 0, st>>>(gpart, ng, a.nvox, a.nray, (Real *)a.part);
     return cudaGetLastError();
 }
 
 #define PORTA_FACES_INST(R, N)                                                                              \
-    template cudaError_t launch_faces<R, N>(const SweepArgs<R> &, R *, double, double, int, int *, cudaStream_t);
+    template cudaError_t launch_faces<R, N>(const SweepArgs<R> &, R *, long long, double, double, int, int *,   \
+                                            cudaStream_t);                                                     \
+    template size_t faces_scratch_bytes<R, N>(int, int, long long, long long);
 PORTA_FACES_INST(float, 1)
 PORTA_FACES_INST(float, 4)
 PORTA_FACES_INST(double, 1)

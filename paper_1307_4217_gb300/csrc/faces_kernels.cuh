@@ -1,0 +1,20 @@
+// Short characteristics ending on the first cell face they cross (faces.cu);
+// internal to the library.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "porta_internal.cuh"
+
+namespace porta {
+
+// The J^K_Q formal solution of one box (nxy points per plane) with the face
+// placement: per-ray partials into a.part; scratch holds the per-CTA work planes
+// and the per-(ray, frequency group) partial sums (faces_scratch_bytes); a plane
+// still changing after maxpass passes sets bit 2 of *err
+template <typename Real, int NS>
+cudaError_t launch_faces(const SweepArgs<Real> &a, Real *scratch, long long nxy, double dx, double dy, int maxpass,
+                         int *err, cudaStream_t st);
+template <typename Real, int NS>
+size_t faces_scratch_bytes(int nray, int nnu, long long nxy, long long nvox);
+
+}  // namespace porta

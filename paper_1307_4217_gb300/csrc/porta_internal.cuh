@@ -106,14 +106,6 @@ struct LaunchCfg {
 template <typename Real, int NS>
 cudaError_t launch_sweep(const SweepArgs<Real> &a, int mode, LaunchCfg &cfg, cudaStream_t st);
 
-// the J^K_Q formal solution of one box with short characteristics ending on the first
-// cell face they cross (faces.cu): per-ray partials in a.part; scratch holds per ray
-// three Stokes planes and a Lambda* plane (nray * (3 NS + 1) * nx * ny Reals); a plane
-// still changing after maxpass passes sets bit 2 of *err
-template <typename Real, int NS>
-cudaError_t launch_faces(const SweepArgs<Real> &a, Real *scratch, double dx, double dy, int maxpass, int *err,
-                         cudaStream_t st);
-
 // shared memory of the sweep: ring (3 planes of `ring_plane` chunks),
 // Stokes planes (2 x F x ipts_max points), lane-reduction scratch (na
 // accumulated quantities per thread)
