@@ -251,6 +251,23 @@ cudaError_t ensure_sweep_buffers(porta_ctx *c)
     if (!c->d_part) e = pmalloc(&c->d_part, (size_t)c->nray * c->nvox * (c->ns == 1 ? 2 : 4) * c->rsz);
     // polarized lines of a multilevel atom: the per-ray integrals of Stokes V (J^1_Q)
     if (e == cudaSuccess && c->d_dich && !c->d_partv) e = pmalloc(&c->d_partv, (size_t)c->nray * c->nvox * c->rsz);
+    // short characteristics on cell faces: the work planes and per-group partials
+    if (e == cudaSuccess && c->sc_faces) {
+        const long long nxy = (long long)c->nx * c->ny;
+        const size_t need =
+            c->precision == PORTA_FP32
+                ? (c->ns == 1 ? faces_scratch_bytes<float, 1>(c->nray, jnu(c), nxy, c->nvox)
+                              : faces_scratch_bytes<float, 4>(c->nray, jnu(c), nxy, c->nvox))
+                : (c->ns == 1 ? faces_scratch_bytes<double, 1>(c->nray, jnu(c), nxy, c->nvox)
+                              : faces_scratch_bytes<double, 4>(c->nray, jnu(c), nxy, c->nvox));
+        if (c->faces_bytes < need) {
+            if (c->d_faces) pfree(c->d_faces);
+            c->d_faces = nullptr;
+            c->faces_bytes = 0;
+            e = pmalloc(&c->d_faces, need);
+            if (e == cudaSuccess) c->faces_bytes = need;
+        }
+    }
     return e;
 }
 
@@ -355,17 +372,8 @@ cudaError_t sweep_jkq(porta_ctx *c, SweepArgs<Real> a, LaunchCfg cfg, const int 
 template <typename Real>
 int faces_solve_t(porta_ctx *c)
 {
-    cudaError_t e = ensure_sweep_buffers(c);
+    cudaError_t e = ensure_sweep_buffers(c);   // (with the face work planes)
     const long long nxy = (long long)c->nx * c->ny;
-    const size_t need = c->ns == 1 ? faces_scratch_bytes<Real, 1>(c->nray, jnu(c), nxy, c->nvox)
-                                   : faces_scratch_bytes<Real, 4>(c->nray, jnu(c), nxy, c->nvox);
-    if (e == cudaSuccess && c->faces_bytes < need) {
-        if (c->d_faces) pfree(c->d_faces);
-        c->d_faces = nullptr;
-        c->faces_bytes = 0;
-        e = pmalloc(&c->d_faces, need);
-        if (e == cudaSuccess) c->faces_bytes = need;
-    }
     if (e != cudaSuccess) return fail(c, PORTA_ENOMEM, std::string("formal solution buffers: ") + cudaGetErrorString(e));
     SweepArgs<Real> a = jkq_args<Real>(c);
     a.part = c->d_part;

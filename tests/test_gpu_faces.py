@@ -78,3 +78,27 @@ def test_face_formal_solution_is_deterministic_and_options_are_checked():
     j3, _ = ctx.accumulate_jkq()
     assert not np.array_equal(j1, j3)
     ctx.close()
+
+
+def test_face_iterations_graph_replay_equals_eager():
+    """Jacobi iterations with the face sweep captured as a CUDA graph (its work planes
+    allocated before the capture) give the eager iterations' unknowns bitwise."""
+    import torch
+    atm = synth.random_box(8, 6, 8, seed=7)
+    rho = initial_rho(atm, 1, seed=8)
+    a = make_ctx(atm, 1, 2, 4, 3, P.PORTA_FP32, rho=rho)
+    b = make_ctx(atm, 1, 2, 4, 3, P.PORTA_FP32, rho=rho)
+    a.set_sc_faces(1)
+    b.set_sc_faces(1)
+    for _ in range(2):
+        a.formal_solve()
+        a.accumulate_jkq()
+        a.see_update()
+    s = torch.cuda.Stream()
+    b.set_stream(s)
+    with torch.cuda.stream(s):
+        b.run_iterations(2)
+    s.synchronize()
+    assert np.array_equal(a.get_rho(), b.get_rho())
+    a.close()
+    b.close()
