@@ -197,9 +197,9 @@ int porta_set_interpolation(porta_ctx *c, int order);
    by passes over all its points repeated until no intensity changes by more than
    1e-15 (FP64) or 2e-7 (FP32) of the plane's largest; the face points' Lambda* is
    their own term (Eq. 14). One CTA per ray, frequencies and planes in order, the
-   per-ray partial sums of the general sweep. Single-box two-level contexts with
-   bilinear stencils (PORTA_EINVAL otherwise); porta_emergent_stokes and the
-   reverse-mode calls reject it, and porta_probe_ray too. A plane still changing after
+   per-ray partial sums of the general sweep; porta_emergent_stokes then sweeps its
+   lines of sight the same way. Single-box two-level contexts with bilinear stencils
+   (PORTA_EINVAL otherwise); the reverse-mode calls and porta_probe_ray reject it. A plane still changing after
    1e5 passes is reported as PORTA_ENOTCONV by the synchronizing calls that read the
    sums (porta_accumulate_jkq to host). Drops any captured iteration graph. */
 int porta_set_sc_faces(porta_ctx *c, int on);

@@ -17,6 +17,7 @@
 #include "api_internal.h"
 #include "mg_kernels.cuh"
 #include "ml_kernels.cuh"
+#include "faces_kernels.cuh"
 #include "mlpol_kernels.cuh"
 #include "see_kernels.cuh"
 
@@ -123,6 +124,25 @@ int emergent_t(porta_ctx *c, int ndir, const double *mu, const double *chi, doub
         a.geom = dg;
         a.rays = dr;
         a.out = dout;
+        if (c->sc_faces) {
+            // short characteristics on cell faces (faces.cu), its own work buffer
+            a.nray = ndir;
+            const long long nxy = (long long)c->nx * c->ny;
+            Real *ws = nullptr;
+            e = pmalloc((void **)&ws, c->ns == 1 ? faces_scratch_bytes<Real, 1>(ndir, c->n_nu, nxy, c->nvox)
+                                                 : faces_scratch_bytes<Real, 4>(ndir, c->n_nu, nxy, c->nvox));
+            if (e == cudaSuccess) e = cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
+            if (e == cudaSuccess)
+                e = c->ns == 1 ? launch_faces<Real, 1>(a, ws, nxy, c->lx / c->nx, c->ly / c->ny, 100000, c->d_err, c->stream, true)
+                               : launch_faces<Real, 4>(a, ws, nxy, c->lx / c->nx, c->ly / c->ny, 100000, c->d_err, c->stream, true);
+            int flag = 0;
+            if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+            if (ws) pfree(ws);
+            if (e != cudaSuccess) rc = fail(c, PORTA_ECUDA, std::string("emergent (faces): ") + cudaGetErrorString(e));
+            else if (flag & 2) rc = fail(c, PORTA_ENOTCONV, "emergent (faces): a plane of face points did not converge");
+            break;
+        }
         LaunchCfg cfg{};
         rc = c->ns == 1 ? emergent_shape<Real, 1>(c, a, ndir, cfg) : emergent_shape<Real, 4>(c, a, ndir, cfg);
         if (rc) break;
@@ -623,7 +643,6 @@ int porta_emergent_stokes(porta_ctx *c, int ndir, const double *mu, const double
         if (!(mu[d] > 0.0 && mu[d] <= 1.0) || !std::isfinite(chi[d]))
             return fail(c, PORTA_EINVAL, "emergent_stokes: mu must lie in (0, 1], chi finite");
     if (c->nbox != 1) return fail(c, PORTA_EINVAL, "emergent_stokes: single-box contexts only");
-    if (c->sc_faces) return fail(c, PORTA_EINVAL, "emergent_stokes: face intersections are built for the J^K_Q formal solution only");
     if (!c->have_atm || !c->have_rho) return fail(c, PORTA_ESTATE, "emergent_stokes: atmosphere or rho not set");
     const long long n = (long long)ndir * c->n_nu * c->nx * c->ny * c->ns;
     double *dout = out;

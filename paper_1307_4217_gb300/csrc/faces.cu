@@ -141,7 +141,7 @@ __device__ __forceinline__ void plane_coefs(const SweepArgs<Real> &a, const RayD
 // first line of a pass reads the last line of the previous one: the periodic chain).
 template <typename Real, int NS>
 __global__ void __launch_bounds__(128) faces_kernel(const SweepArgs<Real> a, Real *scratch, Real *gpart, int ngroups,
-                                                   double dx, double dy, int maxpass, Real tol, int *err)
+                                                   double dx, double dy, int maxpass, Real tol, int *err, int emergent)
 {
     constexpr int NC = NS + 2;                    // coefficient words per node
     __shared__ Real red[4];
@@ -304,6 +304,16 @@ __global__ void __launch_bounds__(128) faces_kernel(const SweepArgs<Real> a, Rea
                     }
                 }
                 __syncthreads();
+                if (emergent) {
+                    // lines of sight: the Stokes vectors of the top plane, [dir][nu][y][x][ns]
+                    if (q == nz - 1)
+                        for (long long p = threadIdx.x; p < nxy; p += blockDim.x)
+#pragma unroll
+                            for (int s = 0; s < NS; ++s)
+                                a.out[(((long long)m * a.nnu + j) * nxy + p) * NS + s] = (double)Ik[s * nxy + p];
+                    __syncthreads();
+                    continue;
+                }
                 // the plane's sums: w_j phi_O / N (I, Q, U, Lambda*) added to the ray's partials
                 for (long long p = threadIdx.x; p < nxy; p += blockDim.x) {
                     const long long vO = base + p;
@@ -370,7 +380,7 @@ size_t faces_scratch_bytes(int nray, int nnu, long long nxy, long long nvox)
 
 template <typename Real, int NS>
 cudaError_t launch_faces(const SweepArgs<Real> &a, Real *scratch, long long nxy, double dx, double dy, int maxpass,
-                         int *err, cudaStream_t st)
+                         int *err, cudaStream_t st, bool emergent)
 {
     const Real tol = sizeof(Real) == 8 ? Real(1e-15) : Real(2e-7);
     int dev = 0, nsm = 0;
@@ -380,9 +390,9 @@ cudaError_t launch_faces(const SweepArgs<Real> &a, Real *scratch, long long nxy,
     const long long items = (long long)a.nray * ng;
     const int ctas = (int)std::min<long long>(items, 8LL * std::max(1, nsm));
     Real *gpart = scratch + (size_t)ctas * (2 * NS + 1 + 3 * (NS + 2)) * nxy;
-    faces_kernel<Real, NS><<<ctas, 128, 0, st>>>(a, scratch, gpart, ng, dx, dy, maxpass, tol, err);
+    faces_kernel<Real, NS><<<ctas, 128, 0, st>>>(a, scratch, gpart, ng, dx, dy, maxpass, tol, err, emergent ? 1 : 0);
     cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    if (e != cudaSuccess || emergent) return e;
     const long long n = (long long)a.nray * a.nvox;
     const int blocks = (int)std::min<long long>((n + 255) / 256, 16LL * std::max(1, nsm));
     faces_group_sum_kernel<Real, NS == 1 ? 2 : 4><<<blocks, 256, 0, st>>>(gpart, ng, a.nvox, a.nray, (Real *)a.part);
@@ -391,7 +401,7 @@ cudaError_t launch_faces(const SweepArgs<Real> &a, Real *scratch, long long nxy,
 
 #define PORTA_FACES_INST(R, N)                                                                              \
     template cudaError_t launch_faces<R, N>(const SweepArgs<R> &, R *, long long, double, double, int, int *,   \
-                                            cudaStream_t);                                                     \
+                                            cudaStream_t, bool);                                               \
     template size_t faces_scratch_bytes<R, N>(int, int, long long, long long);
 PORTA_FACES_INST(float, 1)
 PORTA_FACES_INST(float, 4)

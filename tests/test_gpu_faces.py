@@ -2,7 +2,8 @@
 porta_set_sc_faces(1), faces.cu) against the oracle's face sweep (oracle
 `sc_faces=1`): J^K_Q and Lambda-bar* of a formal solution of a random box whose
 grazing rays meet vertical faces (each such plane solved jointly, the periodic
-chains closed), the Jacobi update from them, determinism, and the rejected
+chains closed), the Jacobi update from them, emergent Stokes profiles of
+grazing lines of sight, graph replay, determinism, and the rejected
 combinations. Tolerances as the bilinear parity tests: FP64 1e-10, FP32 1e-5
 (the FP32 plane solve stops at 2e-7 of the plane's largest change)."""
 import math
@@ -72,7 +73,7 @@ def test_face_formal_solution_is_deterministic_and_options_are_checked():
         ctx.set_interpolation(2)
     mu, az = synth.emergent_directions()
     with pytest.raises(P.PortaError):
-        ctx.emergent_stokes(mu, az)
+        ctx.emergent_vjp(mu, az, np.ones((len(mu), 3, 6, 8, 4)))
     ctx.set_sc_faces(0)                          # back to the plane sweep
     ctx.formal_solve()
     j3, _ = ctx.accumulate_jkq()
@@ -102,3 +103,22 @@ def test_face_iterations_graph_replay_equals_eager():
     assert np.array_equal(a.get_rho(), b.get_rho())
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("prec,tol", [(P.PORTA_FP64, 1e-10), (P.PORTA_FP32, 1e-5)])
+def test_face_emergent_profiles_match_oracle(prec, tol):
+    atm = synth.random_box(9, 7, 10, seed=23, sigma_lnchi=0.1, sigma_v=0.3)
+    rho = initial_rho(atm, 1, seed=24)
+    ctx = make_ctx(atm, 1, 2, 4, 5, prec, rho=rho)
+    ctx.set_sc_faces(1)
+    mu = np.array([1.0, 0.5, 0.2, 0.08])          # the last two meet vertical faces
+    chi = np.array([0.0, 0.7, 2.2, 4.0])
+    eg = ctx.emergent_stokes(mu, chi)
+    p = oracle.Problem(atm, 1, 2, 4, 5, sc_faces=1)
+    eo = oracle.emergent(p, rho, mu, chi)
+    assert np.max(np.abs(eg - eo) / np.abs(eo[..., :1])) < tol
+    # grazing lines of sight differ from the plane placement, the vertical one does not
+    ep = oracle.emergent(oracle.Problem(atm, 1, 2, 4, 5), rho, mu, chi)
+    assert np.max(np.abs(ep[0] - eo[0]) / np.abs(eo[0, ..., :1])) < 1e-12
+    assert np.max(np.abs(ep[3] - eo[3]) / np.abs(eo[3, ..., :1])) > 100 * tol
+    ctx.close()
