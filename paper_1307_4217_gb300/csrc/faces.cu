@@ -18,13 +18,15 @@
 // over n lines). Where the offset stays within a cell, M (or P) lies on the
 // neighbouring plane and one parallel pass is exact.
 //
-// One CTA per ray (a grid-stride loop over rays), the frequencies in order, the
-// planes in sweep order; the ray's Stokes planes (upwind and current), its
+// One CTA of four warps per (ray, frequency group) item (a grid-stride loop over
+// the items, about eight CTAs per SM), the group's frequencies in order, the
+// planes in sweep order; the CTA's Stokes planes (upwind and current), its
 // Lambda* plane and the per-frequency transfer coefficients of the planes ku, k
 // and kd (computed once per plane and frequency) live in global scratch memory
-// (L2-resident at these sizes); the per-ray partial sums are those of the general
-// sweep (stored on the first frequency, added on the later ones, then summed
-// over rays in ray order by the J^K_Q finalize). A plane that does not converge
+// (L2-resident at these sizes); each item's partial sums (stored on its first
+// frequency, added on the later ones) are added over the groups in group order
+// into the general sweep's per-ray partials, which the J^K_Q finalize sums over
+// rays in ray order. A plane that does not converge
 // within maxpass passes sets bit 2 of the error flag and keeps its last pass.
 #include <algorithm>
 
@@ -131,7 +133,7 @@ __device__ __forceinline__ void plane_coefs(const SweepArgs<Real> &a, const RayD
     }
 }
 
-// One CTA per ray. Per frequency and plane: the coefficients of the planes k (the
+// One CTA per (ray, frequency group). Per frequency and plane: the coefficients of the planes k (the
 // points and the upper nodes of their faces), ku (upwind) and kd (downwind) in the
 // ray's scratch, then the plane's points. Where M lies on the upwind plane (offset
 // within a cell) one parallel pass is exact; where it lies on vertical faces the
