@@ -194,10 +194,11 @@ int porta_set_interpolation(porta_ctx *c, int order);
    of the layer, the face point's quantities bilinear in the face's horizontal
    coordinate and in height. The upwind face's upper nodes are points of the same
    plane; with the periodic boundaries (Sec. 4.2) each such plane is solved jointly,
-   by passes over all its points repeated until no intensity changes by more than
-   1e-15 (FP64) or 2e-7 (FP32) of the plane's largest; the face points' Lambda* is
-   their own term (Eq. 14). One CTA per ray, frequencies and planes in order, the
-   per-ray partial sums of the general sweep; porta_emergent_stokes then sweeps its
+   by passes over its lines in the upwind order repeated until no intensity changes
+   by more than 1e-15 (FP64) or 2e-7 (FP32) of the plane's largest; the face points'
+   Lambda* is their own term (Eq. 14). One CTA per (ray, frequency group), the planes
+   in order; the groups' partial sums are added in group order into the per-ray
+   partial sums of the general sweep; porta_emergent_stokes then sweeps its
    lines of sight the same way. Single-box two-level contexts with bilinear stencils
    (PORTA_EINVAL otherwise); the reverse-mode calls and porta_probe_ray reject it. A plane still changing after
    1e5 passes is reported as PORTA_ENOTCONV by the synchronizing calls that read the
