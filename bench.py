@@ -148,10 +148,20 @@ class ClockSampler:
         os.close(fd)
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
+
+    def wait_first(self, timeout=5.0):
+        """Block until the sampler has written its first row (nvidia-smi takes a few
+        hundred ms to start), so that the timed region that follows is sampled."""
+        t_end = time.time() + timeout
+        while self.proc is not None and time.time() < t_end and self.proc.poll() is None:
+            with open(self.path) as f:
+                if "\n" in f.read():
+                    return
+            time.sleep(0.02)
 
     def stop(self):
         if self.proc is None:
@@ -397,6 +407,7 @@ def run_cuda(args):
         ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(args.steps)]
         sampler = ClockSampler(local)
         sampler.start()
+        sampler.wait_first()
         barrier()
         for k in range(args.steps):
             flush.zero_()                       # L2 flush between timed steps (outside the events)

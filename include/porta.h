@@ -195,7 +195,9 @@ int porta_set_interpolation(porta_ctx *c, int order);
    coordinate and in height. The upwind face's upper nodes are points of the same
    plane; with the periodic boundaries (Sec. 4.2) each such plane is solved jointly,
    by passes over its lines in the upwind order repeated until no intensity changes
-   by more than 1e-15 (FP64) or 2e-7 (FP32) of the plane's largest; the face points'
+   by more than 1e-15 (FP64) or 2e-7 (FP32) of the plane's largest, or until the
+   change, within 8 times that and no longer halving per pass, has reached the
+   rounding floor (where (1 - s)^n <= 1/4 over the plane's n lines); the face points'
    Lambda* is their own term (Eq. 14). One CTA per (ray, frequency group), the planes
    in order; the groups' partial sums are added in group order into the per-ray
    partial sums of the general sweep; porta_emergent_stokes then sweeps its

@@ -18,16 +18,21 @@
 // over n lines). Where the offset stays within a cell, M (or P) lies on the
 // neighbouring plane and one parallel pass is exact.
 //
-// One CTA of four warps per (ray, frequency group) item (a grid-stride loop over
-// the items, about eight CTAs per SM), the group's frequencies in order, the
+// One CTA of two warps per (ray, frequency group) item (a grid-stride loop over
+// the items, about eight CTAs per SM: the line passes are bound by the latency of
+// their dependent loads, so many small CTAs), the group's frequencies in order, the
 // planes in sweep order; the CTA's Stokes planes (upwind and current), its
 // Lambda* plane and the per-frequency transfer coefficients of the planes ku, k
-// and kd (computed once per plane and frequency) live in global scratch memory
-// (L2-resident at these sizes); each item's partial sums (stored on its first
+// and kd (each computed once per plane and frequency) live in global scratch
+// memory, laid out per ray so that the points of a line are adjacent (columns
+// first for the rays whose face planes are swept in columns); each item's partial sums (stored on its first
 // frequency, added on the later ones) are added over the groups in group order
 // into the general sweep's per-ray partials, which the J^K_Q finalize sums over
-// rays in ray order. A plane that does not converge
-// within maxpass passes sets bit 2 of the error flag and keeps its last pass.
+// rays in ray order. A face plane's passes stop when no intensity changes by more
+// than tol of the plane's largest, or, where a pass shrinks the change at least
+// fourfold, once the change stops halving within 8 tol (the rounding floor); a
+// plane that does neither within maxpass passes sets bit 2 of the error flag and
+// keeps its last pass.
 #include <algorithm>
 
 #include "device_math.cuh"
@@ -38,51 +43,114 @@ namespace porta {
 
 namespace {
 
-// bilinear stencil (4 nodes, periodic) of the point at offset (fx, fy) cells from
-// node (i, j) on a neighbouring plane
-__device__ __forceinline__ void plane_stencil(int nx, int ny, int i, int j, double fx, double fy, int *ii, int *jj,
-                                              double *w)
+// The interpolation stencil of M (or P), the same for every point of a plane (the
+// offset (f_x, f_y) of a layer is uniform): per corner its node offset from the
+// point, taken modulo the grid (>= 0), and its weight; on a vertical face corners
+// 0, 1 lie on the point's own plane (weight 1 - s) and 2, 3 on the neighbouring one
+// (weight s), else all four lie on the neighbouring plane (bilinear). ds = s times
+// the layer's path length (s = 1 off the faces).
+template <typename Real>
+struct Sten {
+    int ox[4], oy[4];
+    Real w[4];
+    Real ds;
+    double s;
+    bool vert;
+    bool xface;        // a vertical face x = const (|f_x| >= |f_y|), else y = const
+    int step;          // order of the plane's lines in a pass: -1 where f > 0 (upwind first)
+};
+
+__device__ __forceinline__ int pmod(int i, int n) { return ((i % n) + n) % n; }
+
+template <typename Real>
+__device__ __forceinline__ Sten<Real> make_sten(int nx, int ny, double fx, double fy, double ds)
 {
-    const double xc = i + fx, yc = j + fy;
-    const double x0 = floor(xc), y0 = floor(yc);
-    const double gx = xc - x0, gy = yc - y0;
-    const long long i0 = (long long)x0, j0 = (long long)y0;
-    const int ia = (int)(((i0 % nx) + nx) % nx), ja = (int)(((j0 % ny) + ny) % ny);
-    const int ib = ia + 1 == nx ? 0 : ia + 1, jb = ja + 1 == ny ? 0 : ja + 1;
-    ii[0] = ia; jj[0] = ja; w[0] = (1 - gx) * (1 - gy);
-    ii[1] = ib; jj[1] = ja; w[1] = gx * (1 - gy);
-    ii[2] = ia; jj[2] = jb; w[2] = (1 - gx) * gy;
-    ii[3] = ib; jj[3] = jb; w[3] = gx * gy;
+    Sten<Real> st;
+    int di[4], dj[4];
+    double w[4], s = 1.0;
+    st.vert = fabs(fx) > 1.0 || fabs(fy) > 1.0;
+    st.xface = fabs(fx) >= fabs(fy);
+    st.step = (st.xface ? fx : fy) > 0 ? -1 : 1;
+    if (st.vert) {
+        // the first face crossed: x = x_(i + sgn f_x) where |f_x| >= |f_y|, at s = 1 / max(|f_x|, |f_y|)
+        const double ax = fabs(fx), ay = fabs(fy);
+        s = 1.0 / (ax >= ay ? ax : ay);
+        const int sx = fx > 0 ? 1 : (fx < 0 ? -1 : 0), sy = fy > 0 ? 1 : (fy < 0 ? -1 : 0);
+        double g;
+        if (ax >= ay) {
+            di[0] = di[1] = sx;
+            dj[0] = 0;
+            dj[1] = sy != 0 ? sy : 1;
+            g = ay * s;
+        } else {
+            dj[0] = dj[1] = sy;
+            di[0] = 0;
+            di[1] = sx != 0 ? sx : 1;
+            g = ax * s;
+        }
+        di[2] = di[0]; dj[2] = dj[0];
+        di[3] = di[1]; dj[3] = dj[1];
+        w[0] = (1 - g) * (1 - s); w[1] = g * (1 - s);
+        w[2] = (1 - g) * s;       w[3] = g * s;
+    } else {
+        const double x0 = floor(fx), y0 = floor(fy), gx = fx - x0, gy = fy - y0;
+        const int i0 = (int)x0, j0 = (int)y0;
+        di[0] = i0; dj[0] = j0; di[1] = i0 + 1; dj[1] = j0;
+        di[2] = i0; dj[2] = j0 + 1; di[3] = i0 + 1; dj[3] = j0 + 1;
+        w[0] = (1 - gx) * (1 - gy); w[1] = gx * (1 - gy);
+        w[2] = (1 - gx) * gy;       w[3] = gx * gy;
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        st.ox[c] = pmod(di[c], nx);
+        st.oy[c] = pmod(dj[c], ny);
+        st.w[c] = (Real)w[c];
+    }
+    st.ds = (Real)(s * ds);
+    st.s = s;
+    return st;
 }
 
-// face stencil: nodes 0, 1 on the point's own plane (weight 1 - s), 2, 3 on the
-// neighbouring plane (weight s); returns s
-__device__ __forceinline__ double face_stencil(int nx, int ny, int i, int j, double fx, double fy, int *ii, int *jj,
-                                               double *w)
+// The BESSER-DELO step (Eq. 7) where the propagation matrix holds eta_I and eta_V
+// only (the two-level atoms' weak-field Zeeman term): kappa^-1 = 1 + psi'_O K'_O
+// (Eq. 8) couples I and V alone and is inverted in closed form; Q and U are the
+// scalar step. Lambda* as in Eq. 14 (w_O + w_C/2 on the last plane).
+template <typename Real>
+__device__ __forceinline__ void delo_step_iv(const Real IM[4], Real etaM, Real etaVM, const Real epsM[4], Real etaO,
+                                             Real etaVO, const Real epsO[4], Real etaP, const Real epsP[4], Real dM,
+                                             Real dP, bool has_p, Real IO[4], Real &ls)
 {
-    const double ax = fabs(fx), ay = fabs(fy);
-    const double s = 1.0 / (ax >= ay ? ax : ay);
-    const int sx = fx > 0 ? 1 : (fx < 0 ? -1 : 0), sy = fy > 0 ? 1 : (fy < 0 ? -1 : 0);
-    int i0, j0, i1, j1;
-    double g;
-    if (ax >= ay) {
-        i0 = i1 = i + sx;
-        j0 = j;
-        j1 = j + (sy != 0 ? sy : 1);
-        g = ay * s;
-    } else {
-        j0 = j1 = j + sy;
-        i0 = i;
-        i1 = i + (sx != 0 ? sx : 1);
-        g = ax * s;
+    const Real iM = Real(1) / etaM, iO = Real(1) / etaO, iP = has_p ? Real(1) / etaP : Real(0);
+    Real SM[4], SO[4], SP[4];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+        SM[s] = epsM[s] * iM;
+        SO[s] = epsO[s] * iO;
+        SP[s] = epsP[s] * iP;
     }
-    i0 = ((i0 % nx) + nx) % nx; i1 = ((i1 % nx) + nx) % nx;
-    j0 = ((j0 % ny) + ny) % ny; j1 = ((j1 % ny) + ny) % ny;
-    ii[0] = i0; jj[0] = j0; w[0] = (1 - g) * (1 - s);
-    ii[1] = i1; jj[1] = j1; w[1] = g * (1 - s);
-    ii[2] = i0; jj[2] = j0; w[2] = (1 - g) * s;
-    ii[3] = i1; jj[3] = j1; w[3] = g * s;
-    return s;
+    const Real tMO = Real(0.5) * (etaM + etaO) * dM;
+    const Coef<Real> co = coefficients(tMO);
+    Real cM[4];
+    if (has_p) {
+        const BesserGeom<Real> bg = besser_geom(tMO, Real(0.5) * (etaO + etaP) * dP);
+#pragma unroll
+        for (int s = 0; s < 4; ++s) cM[s] = control_point(SM[s], SO[s], SP[s], bg);
+    } else {
+#pragma unroll
+        for (int s = 0; s < 4; ++s) cM[s] = Real(0.5) * (SM[s] + SO[s]);
+    }
+    Real r[4];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) r[s] = co.e * IM[s] + co.wm * SM[s] + co.wo * SO[s] + co.wc * cM[s];
+    const Real pk = co.pm * (etaVM * iM);
+    r[0] -= pk * IM[3];
+    r[3] -= pk * IM[0];
+    const Real av = co.po * (etaVO * iO), idet = Real(1) / (Real(1) - av * av);
+    IO[0] = (r[0] - av * r[3]) * idet;
+    IO[3] = (r[3] - av * r[0]) * idet;
+    IO[1] = r[1];
+    IO[2] = r[2];
+    ls = co.wo + (has_p ? co.wc : Real(0.5) * co.wc);
 }
 
 template <typename Real>
@@ -116,37 +184,49 @@ __device__ __forceinline__ void node_coef(const Node<Real, NS> &n, Real x, Real 
     }
 }
 
+// A ray's planes in scratch memory: row-major (p = j nx + i), or column-major
+// (p = i ny + j) for the rays whose face planes are swept in columns (x faces),
+// so that the points of a line lie together in both cases.
+struct Layout {
+    int nx, ny;
+    bool col;
+    __device__ __forceinline__ int at(int i, int j) const { return col ? i * ny + j : j * nx + i; }
+};
+
 // the transfer coefficients of every node of plane k at frequency x: eta_I, eta_V,
-// eps (NS) at cw[(c * nxy) + p], c = 0 .. NS + 1
+// eps (NS) at cw[(c * nxy) + L.at(i, j)], c = 0 .. NS + 1 (the nodes read in the
+// atmosphere's order)
 template <typename Real, int NS>
 __device__ __forceinline__ void plane_coefs(const SweepArgs<Real> &a, const RayDev<Real> &ray, int m, long long base,
-                                            long long nxy, Real x, Real *cw)
+                                            const Layout &L, Real x, Real *cw)
 {
-    for (long long p = threadIdx.x; p < nxy; p += blockDim.x) {
+    const int nxy = L.nx * L.ny;
+    for (int p = threadIdx.x; p < nxy; p += blockDim.x) {
         const Node<Real, NS> n = make_node<Real, NS>(a, ray, base + p, m, false);
         Real eI, eV, e4[NS];
         node_coef<Real, NS>(n, x, eI, eV, e4);
-        cw[p] = eI;
-        cw[nxy + p] = eV;
+        const int jy = p / L.nx, lp = L.at(p - jy * L.nx, jy);
+        cw[lp] = eI;
+        cw[nxy + lp] = eV;
 #pragma unroll
-        for (int s = 0; s < NS; ++s) cw[(2 + s) * nxy + p] = e4[s];
+        for (int s = 0; s < NS; ++s) cw[(2 + s) * nxy + lp] = e4[s];
     }
 }
 
-// One CTA per (ray, frequency group). Per frequency and plane: the coefficients of the planes k (the
-// points and the upper nodes of their faces), ku (upwind) and kd (downwind) in the
-// ray's scratch, then the plane's points. Where M lies on the upwind plane (offset
+// One CTA per (ray, frequency group). Per frequency and plane: the coefficients of
+// the downwind plane kd (those of the planes ku and k carried over from the two
+// planes before), then the plane's points. Where M lies on the upwind plane (offset
 // within a cell) one parallel pass is exact; where it lies on vertical faces the
 // plane is swept line by line in the upwind order (columns for x faces, rows for y
 // faces: a line's points depend only on the line before), in place, and the pass is
 // repeated until no intensity changes by more than tol of the plane's largest (the
 // first line of a pass reads the last line of the previous one: the periodic chain).
 template <typename Real, int NS>
-__global__ void __launch_bounds__(128) faces_kernel(const SweepArgs<Real> a, Real *scratch, Real *gpart, int ngroups,
+__global__ void __launch_bounds__(64) faces_kernel(const SweepArgs<Real> a, Real *scratch, Real *gpart, int ngroups,
                                                    double dx, double dy, int maxpass, Real tol, int *err, int emergent)
 {
     constexpr int NC = NS + 2;                    // coefficient words per node
-    __shared__ Real red[4];
+    __shared__ Real red[2];
     const BoxDev B = a.boxes[0];
     const int nx = B.nx, ny = B.ny, nz = B.nz;
     const long long nxy = (long long)nx * ny;
@@ -157,8 +237,9 @@ __global__ void __launch_bounds__(128) faces_kernel(const SweepArgs<Real> a, Rea
         const RayDev<Real> ray = a.rays[m];
         const PlaneGeom<Real> *G = a.geom + B.geom0 + (long long)m * nz;
         const bool upward = ray.mu > Real(0);
-        // scratch of the CTA: I of the upwind plane and of the current one, Lambda*,
-        // the coefficients of planes ku, k, kd
+        const Layout L = {nx, ny, fabs((double)ray.ox / dx) >= fabs((double)ray.oy / dy)};
+        // scratch of the CTA: two Stokes planes (upwind and current, swapped per
+        // plane), Lambda*, three coefficient planes (ku, k, kd, rotated per plane)
         Real *Iu = scratch + (long long)blockIdx.x * (2 * NS + 1 + 3 * NC) * nxy;
         Real *Ik = Iu + NS * nxy;
         Real *lsb = Ik + NS * nxy;
@@ -172,52 +253,63 @@ __global__ void __launch_bounds__(128) faces_kernel(const SweepArgs<Real> a, Rea
                 const int k = G[q].kz;
                 const long long base = B.vox0 + (long long)k * nxy;
                 if (q == 0) {
-                    for (long long p = threadIdx.x; p < nxy; p += blockDim.x) {
+                    for (int p = threadIdx.x; p < nxy; p += blockDim.x) {
                         const long long v = base + p;
+                        const int jy = p / nx, lp = L.at(p - jy * nx, jy);
                         Real I0[NS];
 #pragma unroll
                         for (int s = 0; s < NS; ++s) I0[s] = Real(0);
                         if (upward) I0[0] = a.bpl[v];
 #pragma unroll
-                        for (int s = 0; s < NS; ++s) Ik[s * nxy + p] = I0[s];
-                        lsb[p] = Real(0);
+                        for (int s = 0; s < NS; ++s) Ik[s * nxy + lp] = I0[s];
+                        lsb[lp] = Real(0);
                     }
                 } else {
                     const int ku = G[q - 1].kz;
                     const bool has_p = q + 1 < nz;
                     const int kd = has_p ? G[q + 1].kz : k;
                     const double dsM = (double)G[q].ds, dsP = has_p ? (double)G[q + 1].ds : 0.0;
-                    const double fxM = -dsM * (double)ray.ox / dx, fyM = -dsM * (double)ray.oy / dy;
-                    const double fxP = dsP * (double)ray.ox / dx, fyP = dsP * (double)ray.oy / dy;
-                    const bool vertM = fabs(fxM) > 1.0 || fabs(fyM) > 1.0;
-                    const bool vertP = has_p && (fabs(fxP) > 1.0 || fabs(fyP) > 1.0);
-                    // the finished plane becomes the upwind one; coefficients of ku, k, kd
-                    for (long long e = threadIdx.x; e < NS * nxy; e += blockDim.x) {
-                        Iu[e] = Ik[e];
-                        Ik[e] = Real(0);
+                    const Sten<Real> sm = make_sten<Real>(nx, ny, -dsM * (double)ray.ox / dx, -dsM * (double)ray.oy / dy, dsM);
+                    const Sten<Real> sp = make_sten<Real>(nx, ny, dsP * (double)ray.ox / dx, dsP * (double)ray.oy / dy, dsP);
+                    const bool vertP = has_p && sp.vert;
+                    // the finished plane becomes the upwind one; the coefficients of
+                    // ku and k are those of the previous step's k and kd
+                    {
+                        Real *t = Iu;
+                        Iu = Ik;
+                        Ik = t;
                     }
-                    plane_coefs<Real, NS>(a, ray, m, B.vox0 + (long long)ku * nxy, nxy, x, cu);
-                    plane_coefs<Real, NS>(a, ray, m, base, nxy, x, ck);
-                    if (has_p) plane_coefs<Real, NS>(a, ray, m, B.vox0 + (long long)kd * nxy, nxy, x, cd);
+                    if (q >= 2) {
+                        Real *t = cu;
+                        cu = ck;
+                        ck = cd;
+                        cd = t;
+                    }
+                    // a face plane's passes start from zero intensities
+                    if (sm.vert)
+                        for (long long e = threadIdx.x; e < NS * nxy; e += blockDim.x) Ik[e] = Real(0);
+                    if (q == 1) {
+                        plane_coefs<Real, NS>(a, ray, m, B.vox0 + (long long)ku * nxy, L, x, cu);
+                        plane_coefs<Real, NS>(a, ray, m, base, L, x, ck);
+                    }
+                    if (has_p) plane_coefs<Real, NS>(a, ray, m, B.vox0 + (long long)kd * nxy, L, x, cd);
                     __syncthreads();
                     // one point's update (in place into Ik); returns the change of its Stokes vector
                     auto update = [&](int ix, int jy, Real &chg, Real &mag) {
-                        const long long p = (long long)jy * nx + ix;
-                        int ii[4], jj[4];
-                        double w[4];
+                        const int p = L.at(ix, jy);
                         Real etaM = 0, etaVM = 0, epsM[NS], IM[NS];
 #pragma unroll
                         for (int s = 0; s < NS; ++s) epsM[s] = IM[s] = Real(0);
-                        double sM = 1.0;
-                        if (vertM) sM = face_stencil(nx, ny, ix, jy, fxM, fyM, ii, jj, w);
-                        else plane_stencil(nx, ny, ix, jy, fxM, fyM, ii, jj, w);
 #pragma unroll
                         for (int c = 0; c < 4; ++c) {
-                            const bool own = vertM && c < 2;
+                            int ia = ix + sm.ox[c], ja = jy + sm.oy[c];
+                            ia -= ia >= nx ? nx : 0;
+                            ja -= ja >= ny ? ny : 0;
+                            const bool own = sm.vert && c < 2;
                             const Real *cc = own ? ck : cu;
                             const Real *Ib = own ? Ik : Iu;
-                            const long long pc = (long long)jj[c] * nx + ii[c];
-                            const Real wc = (Real)w[c];
+                            const int pc = L.at(ia, ja);
+                            const Real wc = sm.w[c];
                             etaM += wc * cc[pc];
                             etaVM += wc * cc[nxy + pc];
 #pragma unroll
@@ -233,21 +325,21 @@ __global__ void __launch_bounds__(128) faces_kernel(const SweepArgs<Real> a, Rea
                         Real etaP = 0, epsP[NS];
 #pragma unroll
                         for (int s = 0; s < NS; ++s) epsP[s] = Real(0);
-                        double sP = 1.0;
                         if (has_p) {
-                            if (vertP) sP = face_stencil(nx, ny, ix, jy, fxP, fyP, ii, jj, w);
-                            else plane_stencil(nx, ny, ix, jy, fxP, fyP, ii, jj, w);
 #pragma unroll
                             for (int c = 0; c < 4; ++c) {
+                                int ia = ix + sp.ox[c], ja = jy + sp.oy[c];
+                                ia -= ia >= nx ? nx : 0;
+                                ja -= ja >= ny ? ny : 0;
                                 const Real *cc = vertP && c < 2 ? ck : cd;
-                                const long long pc = (long long)jj[c] * nx + ii[c];
-                                const Real wc = (Real)w[c];
+                                const int pc = L.at(ia, ja);
+                                const Real wc = sp.w[c];
                                 etaP += wc * cc[pc];
 #pragma unroll
                                 for (int s = 0; s < NS; ++s) epsP[s] += wc * cc[(2 + s) * nxy + pc];
                             }
                         }
-                        const Real dM = (Real)(sM * dsM), dP = (Real)(sP * dsP);
+                        const Real dM = sm.ds, dP = sp.ds;
                         Real IO[NS], ls;
                         if constexpr (NS == 1) {
                             const Real SM = epsM[0] / etaM, SO = epsO[0] / etaO;
@@ -263,8 +355,7 @@ __global__ void __launch_bounds__(128) faces_kernel(const SweepArgs<Real> a, Rea
                             IO[0] = co.e * IM[0] + co.wm * SM + co.wo * SO + co.wc * cM;
                             ls = co.wo + (has_p ? co.wc : Real(0.5) * co.wc);
                         } else {
-                            const Real etaM7[7] = {etaM, 0, 0, etaVM, 0, 0, 0}, etaO7[7] = {etaO, 0, 0, etaVO, 0, 0, 0};
-                            delo_step_general<Real>(IM, etaM7, epsM, etaO7, epsO, etaP, epsP, dM, dP, has_p, IO, ls);
+                            delo_step_iv<Real>(IM, etaM, etaVM, epsM, etaO, etaVO, epsO, etaP, epsP, dM, dP, has_p, IO, ls);
                         }
 #pragma unroll
                         for (int s = 0; s < NS; ++s) {
@@ -274,17 +365,26 @@ __global__ void __launch_bounds__(128) faces_kernel(const SweepArgs<Real> a, Rea
                         }
                         lsb[p] = ls;
                     };
-                    if (!vertM) {
+                    if (!sm.vert) {
                         Real chg = 0, mag = 0;
-                        for (long long p = threadIdx.x; p < nxy; p += blockDim.x) {
-                            const int jy = (int)(p / nx), ix = (int)(p - (long long)jy * nx);
-                            update(ix, jy, chg, mag);
+                        // the points in the layout's order
+                        const int n_in = L.col ? ny : nx;
+                        for (int p = threadIdx.x; p < nxy; p += blockDim.x) {
+                            const int o = p / n_in, r = p - o * n_in;
+                            if (L.col) update(o, r, chg, mag);
+                            else update(r, o, chg, mag);
                         }
                     } else {
                         // lines in the upwind order: a point depends on the line at +sgn(f)
-                        const bool xface = fabs(fxM) >= fabs(fyM);
+                        const bool xface = sm.xface;
                         const int n_lines = xface ? nx : ny, n_pts = xface ? ny : nx;
-                        const int step = xface ? (fxM > 0 ? -1 : 1) : (fyM > 0 ? -1 : 1);
+                        const int step = sm.step;
+                        // (1 - s)^n bounds the factor by which a pass shrinks the change of
+                        // the plane (the chain's own-plane weight 1 - s over n lines, times
+                        // transmissions e^-tau <= 1); where it is below 1/4, a change that no
+                        // longer halves from one pass to the next is rounding noise
+                        const bool fast = pow(1.0 - sm.s, (double)n_lines) <= 0.25;
+                        Real prev = 0;
                         for (int pass = 0;; ++pass) {
                             Real chg = 0, mag = 0;
                             for (int t = 0; t < n_lines; ++t) {
@@ -298,6 +398,8 @@ __global__ void __launch_bounds__(128) faces_kernel(const SweepArgs<Real> a, Rea
                             chg = block_max(chg, red);
                             mag = block_max(mag, red);
                             if (!(chg > tol * mag)) break;
+                            if (fast && pass >= 1 && chg >= Real(0.5) * prev && chg <= Real(8) * tol * mag) break;
+                            prev = chg;
                             if (pass + 1 >= maxpass) {
                                 if (threadIdx.x == 0) atomicOr(err, 2);
                                 break;
@@ -309,26 +411,28 @@ __global__ void __launch_bounds__(128) faces_kernel(const SweepArgs<Real> a, Rea
                 if (emergent) {
                     // lines of sight: the Stokes vectors of the top plane, [dir][nu][y][x][ns]
                     if (q == nz - 1)
-                        for (long long p = threadIdx.x; p < nxy; p += blockDim.x)
+                        for (int p = threadIdx.x; p < nxy; p += blockDim.x) {
+                            const int jy = p / nx, lp = L.at(p - jy * nx, jy);
 #pragma unroll
                             for (int s = 0; s < NS; ++s)
-                                a.out[(((long long)m * a.nnu + j) * nxy + p) * NS + s] = (double)Ik[s * nxy + p];
+                                a.out[(((long long)m * a.nnu + j) * nxy + p) * NS + s] = (double)Ik[s * nxy + lp];
+                        }
                     __syncthreads();
                     continue;
                 }
                 // the plane's sums: w_j phi_O / N (I, Q, U, Lambda*) added to the ray's partials
-                for (long long p = threadIdx.x; p < nxy; p += blockDim.x) {
+                for (int p = threadIdx.x; p < nxy; p += blockDim.x) {
                     const long long vO = base + p;
-                    const Node<Real, NS> nO = make_node<Real, NS>(a, ray, vO, m, true);
-                    const Real wt = wf * profile_shape(x - nO.s) * nO.invn;
+                    const int jy = p / nx, lp = L.at(p - jy * nx, jy);
+                    const Real wt = wf * profile_shape(x - a.vel[vO] * ray.mu) * a.invn[(long long)m * a.nvox + vO];
                     if constexpr (NS == 1) {
                         R2<Real> *pp = reinterpret_cast<R2<Real> *>(part) + vO;
-                        R2<Real> o = {wt * Ik[p], wt * lsb[p]};
+                        R2<Real> o = {wt * Ik[lp], wt * lsb[lp]};
                         if (j > jb) { const R2<Real> old = *pp; o.x += old.x; o.y += old.y; }
                         *pp = o;
                     } else {
                         R4<Real> *pp = reinterpret_cast<R4<Real> *>(part) + vO;
-                        R4<Real> o = {wt * Ik[p], wt * Ik[nxy + p], wt * Ik[2 * nxy + p], wt * lsb[p]};
+                        R4<Real> o = {wt * Ik[lp], wt * Ik[nxy + lp], wt * Ik[2 * nxy + lp], wt * lsb[lp]};
                         if (j > jb) { const R4<Real> old = *pp; o.x += old.x; o.y += old.y; o.z += old.z; o.w += old.w; }
                         *pp = o;
                     }
@@ -392,7 +496,7 @@ cudaError_t launch_faces(const SweepArgs<Real> &a, Real *scratch, long long nxy,
     const long long items = (long long)a.nray * ng;
     const int ctas = (int)std::min<long long>(items, 8LL * std::max(1, nsm));
     Real *gpart = scratch + (size_t)ctas * (2 * NS + 1 + 3 * (NS + 2)) * nxy;
-    faces_kernel<Real, NS><<<ctas, 128, 0, st>>>(a, scratch, gpart, ng, dx, dy, maxpass, tol, err, emergent ? 1 : 0);
+    faces_kernel<Real, NS><<<ctas, 64, 0, st>>>(a, scratch, gpart, ng, dx, dy, maxpass, tol, err, emergent ? 1 : 0);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || emergent) return e;
     const long long n = (long long)a.nray * a.nvox;
