@@ -198,11 +198,14 @@ int porta_set_interpolation(porta_ctx *c, int order);
    by more than 1e-15 (FP64) or 2e-7 (FP32) of the plane's largest, or until the
    change, within 8 times that and no longer halving per pass, has reached the
    rounding floor (where (1 - s)^n <= 1/4 over the plane's n lines); the face points'
-   Lambda* is their own term (Eq. 14). One CTA per (ray, frequency group), the planes
-   in order; the groups' partial sums are added in group order into the per-ray
-   partial sums of the general sweep; porta_emergent_stokes then sweeps its
-   lines of sight the same way. Single-box two-level contexts with bilinear stencils
-   (PORTA_EINVAL otherwise); the reverse-mode calls and porta_probe_ray reject it. A plane still changing after
+   Lambda* is their own term (Eq. 14). One CTA per (box, ray, frequency group), the
+   planes in order, each box with its own cell size; the groups' partial sums are
+   added in group order into the per-ray partial sums of the general sweep;
+   porta_emergent_stokes then sweeps its lines of sight the same way. Two-level
+   contexts (one box or several), and the unpolarized line boxes of a multilevel
+   context (porta_ml_formal_solve and the iterations); bilinear stencils only, not
+   with an explicit medium nor the polarized multilevel lines (PORTA_EINVAL); the
+   reverse-mode calls and porta_probe_ray reject it. A plane still changing after
    1e5 passes is reported as PORTA_ENOTCONV by the synchronizing calls that read the
    sums (porta_accumulate_jkq to host). Drops any captured iteration graph. */
 int porta_set_sc_faces(porta_ctx *c, int on);

@@ -160,23 +160,24 @@ def rate_operator(atom, kT, pops, jbar):
     return An
 
 
-def line_problem(atm, atom, pops, k, quad):
-    """The two-level formal-solution problem of line k (opacity, Planck function)."""
+def line_problem(atm, atom, pops, k, quad, sc_faces=0):
+    """The two-level formal-solution problem of line k (opacity, Planck function);
+    sc_faces: M and P on the first cell face crossed (Sec. 3.1), as for the two-level atom."""
     a = dict(atm)
     a["chi"] = line_opacity(atom, atm["chi"], pops)[..., k]
     a["bpl"] = planck(atom, atm["kT"])[..., k]
     a["eps"] = np.ones_like(a["chi"])
-    return Problem(a, 0, *quad)
+    return Problem(a, 0, *quad, sc_faces=sc_faces)
 
 
-def formal_solve_lines(atm, atom, pops, quad):
+def formal_solve_lines(atm, atom, pops, quad, sc_faces=0):
     """Jbar and Lambda-bar* of every line, shape (nz, ny, nx, nline)."""
     S = source_function(atom, pops)
     nline = len(atom["lines"])
     jbar = np.zeros(pops.shape[:-1] + (nline,))
     lstar = np.zeros_like(jbar)
     for k in range(nline):
-        p = line_problem(atm, atom, pops, k, quad)
+        p = line_problem(atm, atom, pops, k, quad, sc_faces)
         j, ls = formal_solve(p, S[..., k:k + 1])
         jbar[..., k] = j[..., 0]
         lstar[..., k] = ls

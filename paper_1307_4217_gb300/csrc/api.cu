@@ -236,6 +236,24 @@ SweepArgs<Real> jkq_args(porta_ctx *c)
     return a;
 }
 
+// the largest plane of the boxes, and (dx, dy) per box, for the face sweep
+long long faces_nxy_max(const porta_ctx *c)
+{
+    long long n = 0;
+    for (const BoxDev &b : c->boxes) n = std::max(n, (long long)b.nx * b.ny);
+    return n;
+}
+
+std::vector<double> faces_cell_sizes(const porta_ctx *c)
+{
+    std::vector<double> d(2 * c->boxes.size());
+    for (size_t b = 0; b < c->boxes.size(); ++b) {
+        d[2 * b] = c->blx[b] / c->boxes[b].nx;
+        d[2 * b + 1] = c->bly[b] / c->boxes[b].ny;
+    }
+    return d;
+}
+
 // Device buffers of the J^K_Q formal solution, allocated on first use (before
 // any graph capture): the fixed-point sums of the J^K_Q sweep, or the per-ray
 // partial integrals of the general sweep.
@@ -253,13 +271,18 @@ cudaError_t ensure_sweep_buffers(porta_ctx *c)
     if (e == cudaSuccess && c->d_dich && !c->d_partv) e = pmalloc(&c->d_partv, (size_t)c->nray * c->nvox * c->rsz);
     // short characteristics on cell faces: the work planes and per-group partials
     if (e == cudaSuccess && c->sc_faces) {
-        const long long nxy = (long long)c->nx * c->ny;
+        const long long nxy = faces_nxy_max(c);
         const size_t need =
             c->precision == PORTA_FP32
-                ? (c->ns == 1 ? faces_scratch_bytes<float, 1>(c->nray, jnu(c), nxy, c->nvox)
-                              : faces_scratch_bytes<float, 4>(c->nray, jnu(c), nxy, c->nvox))
-                : (c->ns == 1 ? faces_scratch_bytes<double, 1>(c->nray, jnu(c), nxy, c->nvox)
-                              : faces_scratch_bytes<double, 4>(c->nray, jnu(c), nxy, c->nvox));
+                ? (c->ns == 1 ? faces_scratch_bytes<float, 1>(c->nbox, c->nray, jnu(c), nxy, c->nvox)
+                              : faces_scratch_bytes<float, 4>(c->nbox, c->nray, jnu(c), nxy, c->nvox))
+                : (c->ns == 1 ? faces_scratch_bytes<double, 1>(c->nbox, c->nray, jnu(c), nxy, c->nvox)
+                              : faces_scratch_bytes<double, 4>(c->nbox, c->nray, jnu(c), nxy, c->nvox));
+        if (!c->d_fdxy) {
+            const std::vector<double> dxy = faces_cell_sizes(c);
+            e = pmalloc(&c->d_fdxy, dxy.size() * sizeof(double));
+            if (e == cudaSuccess) e = cudaMemcpy(c->d_fdxy, dxy.data(), dxy.size() * sizeof(double), cudaMemcpyHostToDevice);
+        }
         if (c->faces_bytes < need) {
             if (c->d_faces) pfree(c->d_faces);
             c->d_faces = nullptr;
@@ -373,15 +396,15 @@ template <typename Real>
 int faces_solve_t(porta_ctx *c)
 {
     cudaError_t e = ensure_sweep_buffers(c);   // (with the face work planes)
-    const long long nxy = (long long)c->nx * c->ny;
+    const long long nxy = faces_nxy_max(c);
     if (e != cudaSuccess) return fail(c, PORTA_ENOMEM, std::string("formal solution buffers: ") + cudaGetErrorString(e));
     SweepArgs<Real> a = jkq_args<Real>(c);
     a.part = c->d_part;
     e = cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
-    const double dx = c->lx / c->nx, dy = c->ly / c->ny;
+    const double *dxy = (const double *)c->d_fdxy;
     if (e == cudaSuccess)
-        e = c->ns == 1 ? launch_faces<Real, 1>(a, (Real *)c->d_faces, nxy, dx, dy, 100000, c->d_err, c->stream)
-                       : launch_faces<Real, 4>(a, (Real *)c->d_faces, nxy, dx, dy, 100000, c->d_err, c->stream);
+        e = c->ns == 1 ? launch_faces<Real, 1>(a, (Real *)c->d_faces, c->nbox, nxy, dxy, 100000, c->d_err, c->stream)
+                       : launch_faces<Real, 4>(a, (Real *)c->d_faces, c->nbox, nxy, dxy, 100000, c->d_err, c->stream);
     if (e != cudaSuccess) return fail(c, PORTA_ECUDA, std::string("face sweep: ") + cudaGetErrorString(e));
     return PORTA_OK;
 }
@@ -589,7 +612,7 @@ void free_all(porta_ctx *c)
     void *ptrs[] = {c->d_atm, c->d_eps, c->d_bpl, c->d_b, c->d_rho, c->d_rhoR, c->d_invn, c->d_geom, c->d_rays,
                     c->d_freq, c->d_part, c->d_tw, c->d_jkq, c->d_lstar, c->d_resid, c->d_err, c->d_boxes,
                     c->d_items, c->d_tune_items, c->d_tape, c->d_gpart, c->d_jacc, c->d_jexp, c->d_kexpl, c->d_sexpl,
-                    c->d_partv, c->d_j1, c->d_tw1, c->d_gjR, c->d_vjp_out, c->d_faces};
+                    c->d_partv, c->d_j1, c->d_tw1, c->d_gjR, c->d_vjp_out, c->d_faces, c->d_fdxy};
     for (void *p : ptrs)
         if (p) pfree(p);
 }
@@ -1394,8 +1417,9 @@ int porta_set_sc_faces(porta_ctx *c, int on)
 {
     if (!c) return PORTA_EINVAL;
     if (on != 0 && on != 1) return fail(c, PORTA_EINVAL, "set_sc_faces: 0 or 1");
-    if (on && (c->nbox != 1 || c->ml || c->d_dich || c->d_kexpl || c->interp == 2))
-        return fail(c, PORTA_EINVAL, "set_sc_faces: single-box two-level contexts with bilinear stencils only");
+    if (on && (c->d_dich || c->d_kexpl || c->interp == 2))
+        return fail(c, PORTA_EINVAL,
+                    "set_sc_faces: bilinear stencils only, and not with explicit media or polarized multilevel lines");
     if (on == c->sc_faces) return PORTA_OK;
     c->sc_faces = on;
     c->have_fs = c->have_jkq = false;

@@ -127,18 +127,24 @@ int emergent_t(porta_ctx *c, int ndir, const double *mu, const double *chi, doub
         if (c->sc_faces) {
             // short characteristics on cell faces (faces.cu), its own work buffer
             a.nray = ndir;
-            const long long nxy = (long long)c->nx * c->ny;
+            const BoxDev &hb0 = c->boxes[box];
+            const long long nxy = (long long)hb0.nx * hb0.ny;
+            const double dxy[2] = {c->blx[box] / hb0.nx, c->bly[box] / hb0.ny};
             Real *ws = nullptr;
-            e = pmalloc((void **)&ws, c->ns == 1 ? faces_scratch_bytes<Real, 1>(ndir, c->n_nu, nxy, c->nvox)
-                                                 : faces_scratch_bytes<Real, 4>(ndir, c->n_nu, nxy, c->nvox));
+            double *ddxy = nullptr;
+            e = pmalloc((void **)&ws, c->ns == 1 ? faces_scratch_bytes<Real, 1>(1, ndir, c->n_nu, nxy, c->nvox)
+                                                 : faces_scratch_bytes<Real, 4>(1, ndir, c->n_nu, nxy, c->nvox));
+            if (e == cudaSuccess) e = pmalloc((void **)&ddxy, sizeof(dxy));
+            if (e == cudaSuccess) e = cudaMemcpyAsync(ddxy, dxy, sizeof(dxy), cudaMemcpyHostToDevice, c->stream);
             if (e == cudaSuccess) e = cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
             if (e == cudaSuccess)
-                e = c->ns == 1 ? launch_faces<Real, 1>(a, ws, nxy, c->lx / c->nx, c->ly / c->ny, 100000, c->d_err, c->stream, true)
-                               : launch_faces<Real, 4>(a, ws, nxy, c->lx / c->nx, c->ly / c->ny, 100000, c->d_err, c->stream, true);
+                e = c->ns == 1 ? launch_faces<Real, 1>(a, ws, 1, nxy, ddxy, 100000, c->d_err, c->stream, true)
+                               : launch_faces<Real, 4>(a, ws, 1, nxy, ddxy, 100000, c->d_err, c->stream, true);
             int flag = 0;
             if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
             if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
             if (ws) pfree(ws);
+            if (ddxy) pfree(ddxy);
             if (e != cudaSuccess) rc = fail(c, PORTA_ECUDA, std::string("emergent (faces): ") + cudaGetErrorString(e));
             else if (flag & 2) rc = fail(c, PORTA_ENOTCONV, "emergent (faces): a plane of face points did not converge");
             break;

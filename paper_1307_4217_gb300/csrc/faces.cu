@@ -1,6 +1,7 @@
 // Short characteristics that end on the first cell face they cross (Sec. 3.1:
 // the upwind and downwind points M and P may lie on a vertical plane of the
-// grid), for the J^K_Q formal solution of one box.
+// grid), for the J^K_Q formal solution of a set of boxes (one box, the line boxes
+// of a multilevel atom, or independent boxes).
 //
 // Where the horizontal offset of a ray over a layer, (f_x, f_y) cells, exceeds
 // one cell, the characteristic through a node leaves its cell through the
@@ -18,7 +19,7 @@
 // over n lines). Where the offset stays within a cell, M (or P) lies on the
 // neighbouring plane and one parallel pass is exact.
 //
-// One CTA of two warps per (ray, frequency group) item (a grid-stride loop over
+// One CTA of two warps per (box, ray, frequency group) item (a grid-stride loop over
 // the items, about eight CTAs per SM: the line passes are bound by the latency of
 // their dependent loads, so many small CTAs), the group's frequencies in order, the
 // planes in sweep order; the CTA's Stokes planes (upwind and current), its
@@ -213,7 +214,7 @@ __device__ __forceinline__ void plane_coefs(const SweepArgs<Real> &a, const RayD
     }
 }
 
-// One CTA per (ray, frequency group). Per frequency and plane: the coefficients of
+// One CTA per (box, ray, frequency group). Per frequency and plane: the coefficients of
 // the downwind plane kd (those of the planes ku and k carried over from the two
 // planes before), then the plane's points. Where M lies on the upwind plane (offset
 // within a cell) one parallel pass is exact; where it lies on vertical faces the
@@ -222,29 +223,33 @@ __device__ __forceinline__ void plane_coefs(const SweepArgs<Real> &a, const RayD
 // repeated until no intensity changes by more than tol of the plane's largest (the
 // first line of a pass reads the last line of the previous one: the periodic chain).
 template <typename Real, int NS>
-__global__ void __launch_bounds__(64) faces_kernel(const SweepArgs<Real> a, Real *scratch, Real *gpart, int ngroups,
-                                                   double dx, double dy, int maxpass, Real tol, int *err, int emergent)
+__global__ void __launch_bounds__(64) faces_kernel(const SweepArgs<Real> a, Real *scratch, long long cta_words,
+                                                  Real *gpart, int nbox, int ngroups, const double *dxy, int maxpass,
+                                                  Real tol, int *err, int emergent)
 {
     constexpr int NC = NS + 2;                    // coefficient words per node
     __shared__ Real red[2];
-    const BoxDev B = a.boxes[0];
-    const int nx = B.nx, ny = B.ny, nz = B.nz;
-    const long long nxy = (long long)nx * ny;
     const int fper = (a.nnu + ngroups - 1) / ngroups;
-    // work items: (ray, frequency group), each CTA with its own scratch slot
-    for (int item = blockIdx.x; item < a.nray * ngroups; item += gridDim.x) {
-        const int m = item / ngroups, grp = item - m * ngroups;
+    const int per_box = a.nray * ngroups;
+    // work items: (box, ray, frequency group), each CTA with its own scratch slot
+    for (int item = blockIdx.x; item < nbox * per_box; item += gridDim.x) {
+        const int box = item / per_box, r = item - box * per_box;
+        const int m = r / ngroups, grp = r - m * ngroups;
+        const BoxDev B = a.boxes[box];
+        const int nx = B.nx, ny = B.ny, nz = B.nz;
+        const long long nxy = (long long)nx * ny;
+        const double dx = dxy[2 * box], dy = dxy[2 * box + 1];
         const RayDev<Real> ray = a.rays[m];
         const PlaneGeom<Real> *G = a.geom + B.geom0 + (long long)m * nz;
         const bool upward = ray.mu > Real(0);
         const Layout L = {nx, ny, fabs((double)ray.ox / dx) >= fabs((double)ray.oy / dy)};
         // scratch of the CTA: two Stokes planes (upwind and current, swapped per
         // plane), Lambda*, three coefficient planes (ku, k, kd, rotated per plane)
-        Real *Iu = scratch + (long long)blockIdx.x * (2 * NS + 1 + 3 * NC) * nxy;
+        Real *Iu = scratch + (long long)blockIdx.x * cta_words;
         Real *Ik = Iu + NS * nxy;
         Real *lsb = Ik + NS * nxy;
         Real *cu = lsb + nxy, *ck = cu + NC * nxy, *cd = ck + NC * nxy;
-        // this item's partial sums over its frequencies: [ray][group][nvox]
+        // this item's partial sums over its frequencies: [ray][group][nvox] (the box's voxels)
         Real *part = gpart + ((long long)m * ngroups + grp) * a.nvox * (NS == 1 ? 2 : 4);
         const int jb = grp * fper, je = min(a.nnu, jb + fper);
         for (int j = jb; j < je; ++j) {
@@ -463,42 +468,50 @@ __global__ void faces_group_sum_kernel(const Real *gpart, int ngroups, long long
 
 }  // namespace
 
-// frequency groups per ray: enough (ray, group) items for ~8 CTAs per SM
-int faces_groups(int nray, int nnu)
+// frequency groups: enough (box, ray, group) items for ~8 CTAs per SM
+static int faces_groups(int nbox, int nray, int nnu)
 {
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    return std::max(1, std::min(nnu, (8 * std::max(1, nsm) + nray - 1) / std::max(1, nray)));
+    const long long base = std::max(1LL, (long long)nbox * nray);
+    return (int)std::max(1LL, std::min<long long>(nnu, (8LL * std::max(1, nsm) + base - 1) / base));
 }
 
-template <typename Real, int NS>
-size_t faces_scratch_bytes(int nray, int nnu, long long nxy, long long nvox)
+static int faces_ctas(long long items)
 {
-    const int ng = faces_groups(nray, nnu);
-    const long long items = (long long)nray * ng;
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const long long ctas = std::min<long long>(items, 8LL * std::max(1, nsm));
-    return sizeof(Real) * ((size_t)ctas * (2 * NS + 1 + 3 * (NS + 2)) * nxy + (size_t)items * nvox * (NS == 1 ? 2 : 4));
+    return (int)std::max(1LL, std::min<long long>(items, 8LL * std::max(1, nsm)));
 }
 
 template <typename Real, int NS>
-cudaError_t launch_faces(const SweepArgs<Real> &a, Real *scratch, long long nxy, double dx, double dy, int maxpass,
-                         int *err, cudaStream_t st, bool emergent)
+size_t faces_scratch_bytes(int nbox, int nray, int nnu, long long nxy_max, long long nvox)
+{
+    const int ng = faces_groups(nbox, nray, nnu);
+    const int ctas = faces_ctas((long long)nbox * nray * ng);
+    // with one group the items write the per-ray partials directly
+    const size_t gpart = ng > 1 ? (size_t)nray * ng * nvox * (NS == 1 ? 2 : 4) : 0;
+    return sizeof(Real) * ((size_t)ctas * (2 * NS + 1 + 3 * (NS + 2)) * nxy_max + gpart);
+}
+
+template <typename Real, int NS>
+cudaError_t launch_faces(const SweepArgs<Real> &a, Real *scratch, int nbox, long long nxy_max, const double *dxy,
+                         int maxpass, int *err, cudaStream_t st, bool emergent)
 {
     const Real tol = sizeof(Real) == 8 ? Real(1e-15) : Real(2e-7);
+    const int ng = faces_groups(nbox, a.nray, a.nnu);
+    const int ctas = faces_ctas((long long)nbox * a.nray * ng);
+    const long long cta_words = (long long)(2 * NS + 1 + 3 * (NS + 2)) * nxy_max;
+    Real *gpart = ng > 1 ? scratch + (size_t)ctas * cta_words : (Real *)a.part;
+    faces_kernel<Real, NS><<<ctas, 64, 0, st>>>(a, scratch, cta_words, gpart, nbox, ng, dxy, maxpass, tol, err,
+                                                emergent ? 1 : 0);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || emergent || ng == 1) return e;
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const int ng = faces_groups(a.nray, a.nnu);
-    const long long items = (long long)a.nray * ng;
-    const int ctas = (int)std::min<long long>(items, 8LL * std::max(1, nsm));
-    Real *gpart = scratch + (size_t)ctas * (2 * NS + 1 + 3 * (NS + 2)) * nxy;
-    faces_kernel<Real, NS><<<ctas, 64, 0, st>>>(a, scratch, gpart, ng, dx, dy, maxpass, tol, err, emergent ? 1 : 0);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess || emergent) return e;
     const long long n = (long long)a.nray * a.nvox;
     const int blocks = (int)std::min<long long>((n + 255) / 256, 16LL * std::max(1, nsm));
     faces_group_sum_kernel<Real, NS == 1 ? 2 : 4><<<blocks, 256, 0, st>>>(gpart, ng, a.nvox, a.nray, (Real *)a.part);
@@ -506,9 +519,9 @@ cudaError_t launch_faces(const SweepArgs<Real> &a, Real *scratch, long long nxy,
 }
 
 #define PORTA_FACES_INST(R, N)                                                                              \
-    template cudaError_t launch_faces<R, N>(const SweepArgs<R> &, R *, long long, double, double, int, int *,   \
-                                            cudaStream_t, bool);                                               \
-    template size_t faces_scratch_bytes<R, N>(int, int, long long, long long);
+    template cudaError_t launch_faces<R, N>(const SweepArgs<R> &, R *, int, long long, const double *, int, int *, \
+                                            cudaStream_t, bool);                                                 \
+    template size_t faces_scratch_bytes<R, N>(int, int, int, long long, long long);
 PORTA_FACES_INST(float, 1)
 PORTA_FACES_INST(float, 4)
 PORTA_FACES_INST(double, 1)

@@ -7,16 +7,17 @@
 
 namespace porta {
 
-// The J^K_Q formal solution of one box (nxy points per plane) with the face
+// The J^K_Q formal solution of nbox boxes (at most nxy_max points per plane;
+// dxy[2 b], dxy[2 b + 1]: the cell sizes of box b, on the device) with the face
 // placement: per-ray partials into a.part; scratch holds the per-CTA work planes
-// and the per-(ray, frequency group) partial sums (faces_scratch_bytes); a plane
-// still changing after maxpass passes sets bit 2 of *err. emergent: a.rays are
-// lines of sight (mu > 0) and the top plane's Stokes vectors go to a.out
-// ([dir][nu][y][x][ns], FP64) instead of the sums
+// and, with more than one frequency group, the per-(ray, group) partial sums
+// (faces_scratch_bytes); a plane still changing after maxpass passes sets bit 2
+// of *err. emergent: one box, a.rays are lines of sight (mu > 0) and the top
+// plane's Stokes vectors go to a.out ([dir][nu][y][x][ns], FP64) instead of the sums
 template <typename Real, int NS>
-cudaError_t launch_faces(const SweepArgs<Real> &a, Real *scratch, long long nxy, double dx, double dy, int maxpass,
-                         int *err, cudaStream_t st, bool emergent = false);
+cudaError_t launch_faces(const SweepArgs<Real> &a, Real *scratch, int nbox, long long nxy_max, const double *dxy,
+                         int maxpass, int *err, cudaStream_t st, bool emergent = false);
 template <typename Real, int NS>
-size_t faces_scratch_bytes(int nray, int nnu, long long nxy, long long nvox);
+size_t faces_scratch_bytes(int nbox, int nray, int nnu, long long nxy_max, long long nvox);
 
 }  // namespace porta

@@ -117,6 +117,7 @@ struct porta_ctx {
     int interp = 1;                 // interpolation at M and P: 1 bilinear, 2 biquadratic (general sweep)
     int sc_faces = 0;               // 1: M and P on the first cell face crossed (faces.cu, J^K_Q formal solution)
     void *d_faces = nullptr;        // its per-ray plane buffers (allocated on first use)
+    void *d_fdxy = nullptr;         // its cell sizes, (dx, dy) per box
     size_t faces_bytes = 0;
     double *d_kexpl = nullptr;      // explicit medium: K'/eta_I [6][nvox] and S [4][nvox] (emergent sweep)
     double *d_sexpl = nullptr;

@@ -122,3 +122,52 @@ def test_face_emergent_profiles_match_oracle(prec, tol):
     assert np.max(np.abs(ep[0] - eo[0]) / np.abs(eo[0, ..., :1])) < 1e-12
     assert np.max(np.abs(ep[3] - eo[3]) / np.abs(eo[3, ..., :1])) > 100 * tol
     ctx.close()
+
+
+@pytest.mark.parametrize("prec,tol", [(P.PORTA_FP64, 1e-10), (P.PORTA_FP32, 2e-5)])
+def test_multilevel_lines_with_face_intersections_match_oracle(prec, tol):
+    """The line boxes of the multilevel atom through the face sweep (one launch over
+    (line, ray, frequency group) items) against the oracle's per-line face sweeps;
+    tolerances of the multilevel parity tests."""
+    from oracle import ml
+    atm = synth.multilevel_box(8, 6, 12, seed=2, tau_top=1e-3, tau_bot=1e2)
+    atom = synth.multilevel_atom(seed=3, eps_range=(1e-3, 1e-1))
+    pops = ml.lte_populations(atom, atm["kT"])
+    quad = (2, 4, 7)
+    assert _max_offset(atm, ml.line_problem(atm, atom, pops, 0, quad, sc_faces=1)) > 2.0
+    c = P.MlContext(atm, atom, *quad, precision=prec)
+    c.set_atmosphere(atm)
+    c.set_pops(pops)
+    c.set_sc_faces(1)
+    jb, ls = c.ml_formal_solve()
+    jb, ls = np.moveaxis(np.asarray(jb), 0, -1), np.moveaxis(np.asarray(ls), 0, -1)
+    oj, ol = ml.formal_solve_lines(atm, atom, pops, quad, sc_faces=1)
+    assert np.max(np.abs(jb - oj) / oj) < tol
+    assert np.max(np.abs(ls - ol)) < tol * np.max(ol)
+    pj, _ = ml.formal_solve_lines(atm, atom, pops, quad)
+    assert np.max(np.abs(pj - oj) / oj) > 100 * tol
+    c.close()
+
+
+@pytest.mark.parametrize("prec,tol", [(P.PORTA_FP64, 1e-10), (P.PORTA_FP32, 1e-5)])
+def test_batched_boxes_with_face_intersections_match_oracle(prec, tol):
+    """Independent boxes of uneven size (their own cell sizes) in one face-sweep
+    launch, box by box against the oracle's face sweep."""
+    dims = [(9, 7, 10), (5, 12, 9), (12, 5, 6), (3, 3, 12)]
+    atms = [synth.random_box(nx, ny, nz, seed=[60, b], sigma_lnchi=0.1, sigma_v=0.3)
+            for b, (nx, ny, nz) in enumerate(dims)]
+    rhos = [initial_rho(a, 1, seed=70 + b).reshape(-1, 6) for b, a in enumerate(atms)]
+    ctx = P.BatchContext(atms, 1, 2, 4, 5, precision=prec)
+    ctx.set_atmosphere(atms)
+    ctx.set_rho(np.concatenate(rhos))
+    ctx.set_sc_faces(1)
+    ctx.formal_solve()
+    jg, lg = ctx.accumulate_jkq()
+    grazing = 0
+    for b, (atm, jb, lb) in enumerate(zip(atms, ctx.split(jg), ctx.split(lg))):
+        p = oracle.Problem(atm, 1, 2, 4, 5, sc_faces=1)
+        grazing += _max_offset(atm, p) > 2.0
+        jo, lo = oracle.formal_solve(p, rhos[b].reshape(p.shape + (6,)))
+        _check(jb, lb, jo.reshape(-1, 6), lo.ravel(), tol)
+    assert grazing >= 2
+    ctx.close()

@@ -19,6 +19,7 @@ import numpy as np
 import pytest
 
 import oracle
+import synth
 
 
 def _uniform_atm(nx, ny, nz, chi=1.0, dz=1.0, dx=1.0, bpl=1.0):
@@ -138,3 +139,23 @@ def test_faces_and_planes_converge_to_the_same_field():
         diffs.append(d)
     assert diffs[0] > 0
     assert diffs[2] < 0.5 * diffs[1] < 0.25 * diffs[0], diffs
+
+
+def test_multilevel_lines_take_the_face_option():
+    """The lines of the multilevel atom are two-level problems each (Sec. 2), so the
+    face placement applies per line: with short offsets every line's sums equal the
+    plane sweep's exactly; with grazing offsets they differ."""
+    from oracle import ml
+    atom = synth.multilevel_atom(seed=4, eps_range=(1e-3, 1e-1))
+    quad = (2, 4, 3)
+    wide = synth.multilevel_box(4, 3, 8, seed=5, tau_top=1e-2, tau_bot=1e1)
+    wide["lx"], wide["ly"] = 1e5, 1e5              # cells far wider than any offset
+    pops = ml.lte_populations(atom, wide["kT"])
+    ja, la = ml.formal_solve_lines(wide, atom, pops, quad)
+    jb, lb = ml.formal_solve_lines(wide, atom, pops, quad, sc_faces=1)
+    assert np.array_equal(ja, jb) and np.array_equal(la, lb)
+    narrow = synth.multilevel_box(4, 3, 8, seed=5, tau_top=1e-2, tau_bot=1e1)
+    narrow["lx"], narrow["ly"] = 40.0, 30.0        # 10 km cells under ~100 km layers
+    ja, _ = ml.formal_solve_lines(narrow, atom, pops, quad)
+    jb, _ = ml.formal_solve_lines(narrow, atom, pops, quad, sc_faces=1)
+    assert np.max(np.abs(jb / ja - 1)) > 1e-3
