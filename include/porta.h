@@ -202,10 +202,11 @@ int porta_set_interpolation(porta_ctx *c, int order);
    planes in order, each box with its own cell size; the groups' partial sums are
    added in group order into the per-ray partial sums of the general sweep;
    porta_emergent_stokes then sweeps its lines of sight the same way. Two-level
-   contexts (one box or several), and the unpolarized line boxes of a multilevel
-   context (porta_ml_formal_solve and the iterations); bilinear stencils only, not
-   with an explicit medium nor the polarized multilevel lines (PORTA_EINVAL); the
-   reverse-mode calls and porta_probe_ray reject it. A plane still changing after
+   contexts (one box or several) and the line boxes of multilevel contexts, the
+   polarized ones with their dichroism and orientation terms and the Stokes-V
+   integrals (porta_ml_formal_solve and the iterations); bilinear stencils only,
+   not with an explicit medium (PORTA_EINVAL); the reverse-mode calls and
+   porta_probe_ray reject it. A plane still changing after
    1e5 passes is reported as PORTA_ENOTCONV by the synchronizing calls that read the
    sums (porta_accumulate_jkq to host). Drops any captured iteration graph. */
 int porta_set_sc_faces(porta_ctx *c, int on);

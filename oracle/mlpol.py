@@ -449,9 +449,10 @@ def line_dichroism(tab, x, li):
     return out
 
 
-def line_problem(atm, atom, tab, x, li, quad, dichroism=True):
+def line_problem(atm, atom, tab, x, li, quad, dichroism=True, sc_faces=0):
     """the two-level polarized formal-solution problem of line li (with the line's
-    dichroism from the atomic polarization of its levels unless dichroism=False)"""
+    dichroism from the atomic polarization of its levels unless dichroism=False);
+    sc_faces: M and P on the first cell face crossed (Sec. 3.1)"""
     pops = tab.populations(x)
     a = dict(atm)
     a["chi"] = ml.line_opacity(atom, atm["chi"], pops)[..., li]
@@ -461,10 +462,10 @@ def line_problem(atm, atom, tab, x, li, quad, dichroism=True):
         a["dich"] = line_dichroism(tab, x, li)
         a["dich1"] = line_dichroism_orientation(tab, x, li)
     a["orient"] = line_orientation_multipoles(tab, x)[..., li, :]
-    return Problem(a, 1, *quad)
+    return Problem(a, 1, *quad, sc_faces=sc_faces)
 
 
-def formal_solve_lines(atm, atom, tab, x, quad, dichroism=True):
+def formal_solve_lines(atm, atom, tab, x, quad, dichroism=True, sc_faces=0):
     """Jbar (real layout of jkq_complex, Kr = 0, 1, 2) and Lambda-bar* per line"""
     src = line_source_multipoles(tab, x)
     nline = len(tab.lines)
@@ -472,7 +473,7 @@ def formal_solve_lines(atm, atom, tab, x, quad, dichroism=True):
     jbar = np.zeros(shape + (nline, 9))
     lstar = np.zeros(shape + (nline,))
     for li in range(nline):
-        p = line_problem(atm, atom, tab, x, li, quad, dichroism)
+        p = line_problem(atm, atom, tab, x, li, quad, dichroism, sc_faces)
         j, ls, j1 = formal_solve(p, src[..., li, :], with_j1=True)
         # two-level layout (J00, J20, ReJ21, ImJ21, ReJ22, ImJ22) and J^1 -> Kr = 0, 1, 2 layout
         jbar[..., li, 0] = j[..., 0]

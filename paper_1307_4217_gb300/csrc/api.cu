@@ -274,10 +274,10 @@ cudaError_t ensure_sweep_buffers(porta_ctx *c)
         const long long nxy = faces_nxy_max(c);
         const size_t need =
             c->precision == PORTA_FP32
-                ? (c->ns == 1 ? faces_scratch_bytes<float, 1>(c->nbox, c->nray, jnu(c), nxy, c->nvox)
-                              : faces_scratch_bytes<float, 4>(c->nbox, c->nray, jnu(c), nxy, c->nvox))
-                : (c->ns == 1 ? faces_scratch_bytes<double, 1>(c->nbox, c->nray, jnu(c), nxy, c->nvox)
-                              : faces_scratch_bytes<double, 4>(c->nbox, c->nray, jnu(c), nxy, c->nvox));
+                ? (c->ns == 1 ? faces_scratch_bytes<float, 1>(c->nbox, c->nray, jnu(c), nxy, c->nvox, c->d_dich != nullptr)
+                              : faces_scratch_bytes<float, 4>(c->nbox, c->nray, jnu(c), nxy, c->nvox, c->d_dich != nullptr))
+                : (c->ns == 1 ? faces_scratch_bytes<double, 1>(c->nbox, c->nray, jnu(c), nxy, c->nvox, c->d_dich != nullptr)
+                              : faces_scratch_bytes<double, 4>(c->nbox, c->nray, jnu(c), nxy, c->nvox, c->d_dich != nullptr));
         if (!c->d_fdxy) {
             const std::vector<double> dxy = faces_cell_sizes(c);
             e = pmalloc(&c->d_fdxy, dxy.size() * sizeof(double));
@@ -1417,9 +1417,8 @@ int porta_set_sc_faces(porta_ctx *c, int on)
 {
     if (!c) return PORTA_EINVAL;
     if (on != 0 && on != 1) return fail(c, PORTA_EINVAL, "set_sc_faces: 0 or 1");
-    if (on && (c->d_dich || c->d_kexpl || c->interp == 2))
-        return fail(c, PORTA_EINVAL,
-                    "set_sc_faces: bilinear stencils only, and not with explicit media or polarized multilevel lines");
+    if (on && (c->d_kexpl || c->interp == 2))
+        return fail(c, PORTA_EINVAL, "set_sc_faces: bilinear stencils only, and not with an explicit medium");
     if (on == c->sc_faces) return PORTA_OK;
     c->sc_faces = on;
     c->have_fs = c->have_jkq = false;

@@ -166,23 +166,49 @@ __device__ __forceinline__ Real block_max(Real v, Real *red)
     return t;
 }
 
-// transfer coefficients of node v at frequency x: eta_I, eta_V (weak-field Zeeman) and
-// eps (I, Q, U, V) as the general sweep forms them (Sec. 2)
-template <typename Real, int NS>
-__device__ __forceinline__ void node_coef(const Node<Real, NS> &n, Real x, Real &etaI, Real &etaV, Real *eps)
+// Coefficient words per node: eta_I, eta_V (weak-field Zeeman), eps (NS); with the
+// dichroism of a polarized multilevel line (DI): eta_I, eta_Q, eta_U, eta_V, eps (4).
+template <int NS, bool DI>
+struct CW {
+    static constexpr int n = DI ? 8 : NS + 2;
+    static constexpr int ev = DI ? 3 : 1;        // eta_V
+    static constexpr int eps = DI ? 4 : 2;       // first emission word
+};
+
+// The line's dichroism and orientation terms at node v for the ray (a polarized
+// multilevel line, Sec. 2): eta_i / (chi phi) = 1 + d_i(Omega) from the lower-level
+// multipoles D^2_Q (i = I, Q, U) and D^1_Q (V); the node's opacity is rescaled by
+// 1 + d_I, its source terms and Zeeman factor by 1 / (1 + d_I); returns the ratios
+// eta_Q / eta_I, eta_U / eta_I, the orientation term of eta_V / eta_I and the
+// orientation emission of S_V (the emission multipoles S^1_Q projected on V).
+template <typename Real>
+__device__ __forceinline__ void dich_terms(const SweepArgs<Real> &a, const RayDev<Real> &ray, long long v,
+                                           Node<Real, 4> &n, Real &dq, Real &du, Real &dv, Real &sv)
 {
-    const Real xs = x - n.s;
-    etaI = n.chi * profile_shape(xs);
-    if constexpr (NS == 1) {
-        etaV = Real(0);
-        eps[0] = etaI * n.S;
-    } else {
-        etaV = etaI * n.b * xs;
-        eps[0] = etaI * n.SI;
-        eps[1] = etaI * n.SQ;
-        eps[2] = etaI * n.SU;
-        eps[3] = etaV * n.S00;
+    const long long nv = a.nvox;
+    const Real d20 = a.dich[v], d21r = a.dich[nv + v], d21i = a.dich[2 * nv + v];
+    const Real d22r = a.dich[3 * nv + v], d22i = a.dich[4 * nv + v];
+    Real dd[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const Real *t = ray.t + 6 * i;
+        dd[i] = t[1] * d20 + Real(2) * (t[2] * d21r + t[3] * d21i) + Real(2) * (t[4] * d22r + t[5] * d22i);
     }
+    // T^1_Q(V, Omega) = sqrt(3/2) Omega_Q: T10 = sqrt(3/2) Omega_z, T11 = -sqrt(3/4) (Omega_x + i Omega_y)
+    const Real t10 = Real(1.2247448713915890491) * ray.oz;
+    const Real t11r = Real(-0.86602540378443864676) * ray.ox, t11i = Real(-0.86602540378443864676) * ray.oy;
+    const Real dvr = t10 * a.dich[5 * nv + v] + Real(2) * (t11r * a.dich[6 * nv + v] + t11i * a.dich[7 * nv + v]);
+    const Real svr = t10 * a.dich[8 * nv + v] + Real(2) * (t11r * a.dich[9 * nv + v] + t11i * a.dich[10 * nv + v]);
+    const Real f = Real(1) + dd[0], inv = Real(1) / f;
+    n.chi *= f;
+    n.SI *= inv;
+    n.SQ *= inv;
+    n.SU *= inv;
+    n.b *= inv;
+    dq = dd[1] * inv;
+    du = dd[2] * inv;
+    dv = dvr * inv;
+    sv = svr * inv;
 }
 
 // A ray's planes in scratch memory: row-major (p = j nx + i), or column-major
@@ -194,24 +220,83 @@ struct Layout {
     __device__ __forceinline__ int at(int i, int j) const { return col ? i * ny + j : j * nx + i; }
 };
 
-// the transfer coefficients of every node of plane k at frequency x: eta_I, eta_V,
-// eps (NS) at cw[(c * nxy) + L.at(i, j)], c = 0 .. NS + 1 (the nodes read in the
-// atmosphere's order)
-template <typename Real, int NS>
+// the transfer coefficients of every node of plane k at frequency x, word c of
+// node (i, j) at cw[(c * nxy) + L.at(i, j)] (the nodes read in the atmosphere's order)
+template <typename Real, int NS, bool DI>
 __device__ __forceinline__ void plane_coefs(const SweepArgs<Real> &a, const RayDev<Real> &ray, int m, long long base,
                                             const Layout &L, Real x, Real *cw)
 {
+    using C = CW<NS, DI>;
     const int nxy = L.nx * L.ny;
     for (int p = threadIdx.x; p < nxy; p += blockDim.x) {
-        const Node<Real, NS> n = make_node<Real, NS>(a, ray, base + p, m, false);
-        Real eI, eV, e4[NS];
-        node_coef<Real, NS>(n, x, eI, eV, e4);
+        Node<Real, NS> n = make_node<Real, NS>(a, ray, base + p, m, false);
+        Real w[C::n];
+        const Real xs = x - n.s;
+        if constexpr (NS == 1) {
+            w[0] = n.chi * profile_shape(xs);
+            w[1] = Real(0);
+            w[2] = w[0] * n.S;
+        } else {
+            Real dq = 0, du = 0, dv = 0, sv = 0;
+            if constexpr (DI) dich_terms<Real>(a, ray, base + p, n, dq, du, dv, sv);
+            const Real eI = n.chi * profile_shape(xs), bx = n.b * xs;
+            w[0] = eI;
+            if constexpr (DI) {
+                w[1] = eI * dq;
+                w[2] = eI * du;
+            }
+            w[C::ev] = eI * (bx + dv);
+            w[C::eps] = eI * n.SI;
+            w[C::eps + 1] = eI * n.SQ;
+            w[C::eps + 2] = eI * n.SU;
+            w[C::eps + 3] = eI * (bx * n.S00 + sv);
+        }
         const int jy = p / L.nx, lp = L.at(p - jy * L.nx, jy);
-        cw[lp] = eI;
-        cw[nxy + lp] = eV;
 #pragma unroll
-        for (int s = 0; s < NS; ++s) cw[(2 + s) * nxy + lp] = e4[s];
+        for (int c = 0; c < C::n; ++c) cw[c * nxy + lp] = w[c];
     }
+}
+
+// The BESSER-DELO step (Eq. 7) of a polarized multilevel line: K' holds eta_Q,
+// eta_U (dichroism) and eta_V over eta_I, so kappa^-1 = 1 + psi'_O K'_O (Eq. 8) is an
+// arrow matrix (first row and column, unit diagonal), inverted in closed form.
+template <typename Real>
+__device__ __forceinline__ void delo_step_arrow(const Real IM[4], const Real eM[8], const Real eO[8], Real etaP,
+                                                const Real epsP[4], Real dM, Real dP, bool has_p, Real IO[4], Real &ls)
+{
+    const Real iM = Real(1) / eM[0], iO = Real(1) / eO[0], iP = has_p ? Real(1) / etaP : Real(0);
+    Real SM[4], SO[4], SP[4];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+        SM[s] = eM[4 + s] * iM;
+        SO[s] = eO[4 + s] * iO;
+        SP[s] = epsP[s] * iP;
+    }
+    const Real tMO = Real(0.5) * (eM[0] + eO[0]) * dM;
+    const Coef<Real> co = coefficients(tMO);
+    Real cM[4];
+    if (has_p) {
+        const BesserGeom<Real> bg = besser_geom(tMO, Real(0.5) * (eO[0] + etaP) * dP);
+#pragma unroll
+        for (int s = 0; s < 4; ++s) cM[s] = control_point(SM[s], SO[s], SP[s], bg);
+    } else {
+#pragma unroll
+        for (int s = 0; s < 4; ++s) cM[s] = Real(0.5) * (SM[s] + SO[s]);
+    }
+    const Real qM = eM[1] * iM, uM = eM[2] * iM, vM = eM[3] * iM;
+    Real r[4];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) r[s] = co.e * IM[s] + co.wm * SM[s] + co.wo * SO[s] + co.wc * cM[s];
+    r[0] -= co.pm * (qM * IM[1] + uM * IM[2] + vM * IM[3]);
+    r[1] -= co.pm * qM * IM[0];
+    r[2] -= co.pm * uM * IM[0];
+    r[3] -= co.pm * vM * IM[0];
+    const Real aq = co.po * (eO[1] * iO), au = co.po * (eO[2] * iO), av = co.po * (eO[3] * iO);
+    IO[0] = (r[0] - aq * r[1] - au * r[2] - av * r[3]) / (Real(1) - aq * aq - au * au - av * av);
+    IO[1] = r[1] - aq * IO[0];
+    IO[2] = r[2] - au * IO[0];
+    IO[3] = r[3] - av * IO[0];
+    ls = co.wo + (has_p ? co.wc : Real(0.5) * co.wc);
 }
 
 // One CTA per (box, ray, frequency group). Per frequency and plane: the coefficients of
@@ -222,12 +307,14 @@ __device__ __forceinline__ void plane_coefs(const SweepArgs<Real> &a, const RayD
 // faces: a line's points depend only on the line before), in place, and the pass is
 // repeated until no intensity changes by more than tol of the plane's largest (the
 // first line of a pass reads the last line of the previous one: the periodic chain).
-template <typename Real, int NS>
-__global__ void __launch_bounds__(64) faces_kernel(const SweepArgs<Real> a, Real *scratch, long long cta_words,
-                                                  Real *gpart, int nbox, int ngroups, const double *dxy, int maxpass,
-                                                  Real tol, int *err, int emergent)
+// (FP32: eight CTAs of 64 threads per SM, i.e. at most 128 registers a thread)
+template <typename Real, int NS, bool DI>
+__global__ void __launch_bounds__(64, sizeof(Real) == 4 ? 8 : 3) faces_kernel(const SweepArgs<Real> a, Real *scratch, long long cta_words,
+                                                  Real *gpart, Real *gpartv, int nbox, int ngroups, const double *dxy,
+                                                  int maxpass, Real tol, int *err, int emergent)
 {
-    constexpr int NC = NS + 2;                    // coefficient words per node
+    using C = CW<NS, DI>;
+    constexpr int NC = C::n;                      // coefficient words per node
     __shared__ Real red[2];
     const int fper = (a.nnu + ngroups - 1) / ngroups;
     const int per_box = a.nray * ngroups;
@@ -249,8 +336,10 @@ __global__ void __launch_bounds__(64) faces_kernel(const SweepArgs<Real> a, Real
         Real *Ik = Iu + NS * nxy;
         Real *lsb = Ik + NS * nxy;
         Real *cu = lsb + nxy, *ck = cu + NC * nxy, *cd = ck + NC * nxy;
-        // this item's partial sums over its frequencies: [ray][group][nvox] (the box's voxels)
+        // this item's partial sums over its frequencies: [ray][group][nvox] (the box's
+        // voxels); with dichroism also the integral of Stokes V (J^1_Q)
         Real *part = gpart + ((long long)m * ngroups + grp) * a.nvox * (NS == 1 ? 2 : 4);
+        Real *partv = DI ? gpartv + ((long long)m * ngroups + grp) * a.nvox : nullptr;
         const int jb = grp * fper, je = min(a.nnu, jb + fper);
         for (int j = jb; j < je; ++j) {
             const Real x = a.xf[j], wf = a.wf[j];
@@ -294,17 +383,20 @@ __global__ void __launch_bounds__(64) faces_kernel(const SweepArgs<Real> a, Real
                     if (sm.vert)
                         for (long long e = threadIdx.x; e < NS * nxy; e += blockDim.x) Ik[e] = Real(0);
                     if (q == 1) {
-                        plane_coefs<Real, NS>(a, ray, m, B.vox0 + (long long)ku * nxy, L, x, cu);
-                        plane_coefs<Real, NS>(a, ray, m, base, L, x, ck);
+                        plane_coefs<Real, NS, DI>(a, ray, m, B.vox0 + (long long)ku * nxy, L, x, cu);
+                        plane_coefs<Real, NS, DI>(a, ray, m, base, L, x, ck);
                     }
-                    if (has_p) plane_coefs<Real, NS>(a, ray, m, B.vox0 + (long long)kd * nxy, L, x, cd);
+                    if (has_p) plane_coefs<Real, NS, DI>(a, ray, m, B.vox0 + (long long)kd * nxy, L, x, cd);
                     __syncthreads();
                     // one point's update (in place into Ik); returns the change of its Stokes vector
                     auto update = [&](int ix, int jy, Real &chg, Real &mag) {
                         const int p = L.at(ix, jy);
-                        Real etaM = 0, etaVM = 0, epsM[NS], IM[NS];
+                        // M: every coefficient word and the Stokes vector, interpolated
+                        Real eM[NC], IM[NS];
 #pragma unroll
-                        for (int s = 0; s < NS; ++s) epsM[s] = IM[s] = Real(0);
+                        for (int w = 0; w < NC; ++w) eM[w] = Real(0);
+#pragma unroll
+                        for (int s = 0; s < NS; ++s) IM[s] = Real(0);
 #pragma unroll
                         for (int c = 0; c < 4; ++c) {
                             int ia = ix + sm.ox[c], ja = jy + sm.oy[c];
@@ -315,18 +407,15 @@ __global__ void __launch_bounds__(64) faces_kernel(const SweepArgs<Real> a, Real
                             const Real *Ib = own ? Ik : Iu;
                             const int pc = L.at(ia, ja);
                             const Real wc = sm.w[c];
-                            etaM += wc * cc[pc];
-                            etaVM += wc * cc[nxy + pc];
 #pragma unroll
-                            for (int s = 0; s < NS; ++s) {
-                                epsM[s] += wc * cc[(2 + s) * nxy + pc];
-                                IM[s] += wc * Ib[s * nxy + pc];
-                            }
+                            for (int w = 0; w < NC; ++w) eM[w] += wc * cc[w * nxy + pc];
+#pragma unroll
+                            for (int s = 0; s < NS; ++s) IM[s] += wc * Ib[s * nxy + pc];
                         }
-                        const Real etaO = ck[p], etaVO = ck[nxy + p];
-                        Real epsO[NS];
+                        Real eO[NC];
 #pragma unroll
-                        for (int s = 0; s < NS; ++s) epsO[s] = ck[(2 + s) * nxy + p];
+                        for (int w = 0; w < NC; ++w) eO[w] = ck[w * nxy + p];
+                        // P: eta_I and the emission
                         Real etaP = 0, epsP[NS];
 #pragma unroll
                         for (int s = 0; s < NS; ++s) epsP[s] = Real(0);
@@ -341,26 +430,28 @@ __global__ void __launch_bounds__(64) faces_kernel(const SweepArgs<Real> a, Real
                                 const Real wc = sp.w[c];
                                 etaP += wc * cc[pc];
 #pragma unroll
-                                for (int s = 0; s < NS; ++s) epsP[s] += wc * cc[(2 + s) * nxy + pc];
+                                for (int s = 0; s < NS; ++s) epsP[s] += wc * cc[(C::eps + s) * nxy + pc];
                             }
                         }
                         const Real dM = sm.ds, dP = sp.ds;
                         Real IO[NS], ls;
                         if constexpr (NS == 1) {
-                            const Real SM = epsM[0] / etaM, SO = epsO[0] / etaO;
-                            const Real tMO = Real(0.5) * (etaM + etaO) * dM;
+                            const Real SM = eM[2] / eM[0], SO = eO[2] / eO[0];
+                            const Real tMO = Real(0.5) * (eM[0] + eO[0]) * dM;
                             const Coef<Real> co = coefficients(tMO);
                             Real cM;
                             if (has_p) {
-                                const Real SP = epsP[0] / etaP, tOP = Real(0.5) * (etaO + etaP) * dP;
+                                const Real SP = epsP[0] / etaP, tOP = Real(0.5) * (eO[0] + etaP) * dP;
                                 cM = control_point(SM, SO, SP, besser_geom(tMO, tOP));
                             } else {
                                 cM = Real(0.5) * (SM + SO);
                             }
                             IO[0] = co.e * IM[0] + co.wm * SM + co.wo * SO + co.wc * cM;
                             ls = co.wo + (has_p ? co.wc : Real(0.5) * co.wc);
+                        } else if constexpr (DI) {
+                            delo_step_arrow<Real>(IM, eM, eO, etaP, epsP, dM, dP, has_p, IO, ls);
                         } else {
-                            delo_step_iv<Real>(IM, etaM, etaVM, epsM, etaO, etaVO, epsO, etaP, epsP, dM, dP, has_p, IO, ls);
+                            delo_step_iv<Real>(IM, eM[0], eM[1], eM + 2, eO[0], eO[1], eO + 2, etaP, epsP, dM, dP, has_p, IO, ls);
                         }
 #pragma unroll
                         for (int s = 0; s < NS; ++s) {
@@ -440,6 +531,7 @@ __global__ void __launch_bounds__(64) faces_kernel(const SweepArgs<Real> a, Real
                         R4<Real> o = {wt * Ik[lp], wt * Ik[nxy + lp], wt * Ik[2 * nxy + lp], wt * lsb[lp]};
                         if (j > jb) { const R4<Real> old = *pp; o.x += old.x; o.y += old.y; o.z += old.z; o.w += old.w; }
                         *pp = o;
+                        if constexpr (DI) partv[vO] = (j > jb ? partv[vO] : Real(0)) + wt * Ik[3 * nxy + lp];
                     }
                 }
                 __syncthreads();
@@ -475,7 +567,7 @@ static int faces_groups(int nbox, int nray, int nnu)
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const long long base = std::max(1LL, (long long)nbox * nray);
-    return (int)std::max(1LL, std::min<long long>(nnu, (8LL * std::max(1, nsm) + base - 1) / base));
+    return (int)std::max(1LL, std::min<long long>(nnu, 8LL * std::max(1, nsm) / base));
 }
 
 static int faces_ctas(long long items)
@@ -487,26 +579,31 @@ static int faces_ctas(long long items)
 }
 
 template <typename Real, int NS>
-size_t faces_scratch_bytes(int nbox, int nray, int nnu, long long nxy_max, long long nvox)
+size_t faces_scratch_bytes(int nbox, int nray, int nnu, long long nxy_max, long long nvox, bool dich)
 {
     const int ng = faces_groups(nbox, nray, nnu);
     const int ctas = faces_ctas((long long)nbox * nray * ng);
+    const bool di = NS == 4 && dich;
+    const int nc = di ? 8 : NS + 2;
     // with one group the items write the per-ray partials directly
-    const size_t gpart = ng > 1 ? (size_t)nray * ng * nvox * (NS == 1 ? 2 : 4) : 0;
-    return sizeof(Real) * ((size_t)ctas * (2 * NS + 1 + 3 * (NS + 2)) * nxy_max + gpart);
+    const size_t na = (NS == 1 ? 2 : 4) + (di ? 1 : 0);
+    const size_t gpart = ng > 1 ? (size_t)nray * ng * nvox * na : 0;
+    return sizeof(Real) * ((size_t)ctas * (2 * NS + 1 + 3 * nc) * nxy_max + gpart);
 }
 
-template <typename Real, int NS>
-cudaError_t launch_faces(const SweepArgs<Real> &a, Real *scratch, int nbox, long long nxy_max, const double *dxy,
-                         int maxpass, int *err, cudaStream_t st, bool emergent)
+template <typename Real, int NS, bool DI>
+static cudaError_t launch_faces_k(const SweepArgs<Real> &a, Real *scratch, int nbox, long long nxy_max,
+                                  const double *dxy, int maxpass, int *err, cudaStream_t st, bool emergent)
 {
     const Real tol = sizeof(Real) == 8 ? Real(1e-15) : Real(2e-7);
     const int ng = faces_groups(nbox, a.nray, a.nnu);
     const int ctas = faces_ctas((long long)nbox * a.nray * ng);
-    const long long cta_words = (long long)(2 * NS + 1 + 3 * (NS + 2)) * nxy_max;
+    const long long cta_words = (long long)(2 * NS + 1 + 3 * CW<NS, DI>::n) * nxy_max;
+    constexpr int NA = NS == 1 ? 2 : 4;
     Real *gpart = ng > 1 ? scratch + (size_t)ctas * cta_words : (Real *)a.part;
-    faces_kernel<Real, NS><<<ctas, 64, 0, st>>>(a, scratch, cta_words, gpart, nbox, ng, dxy, maxpass, tol, err,
-                                                emergent ? 1 : 0);
+    Real *gpartv = ng > 1 ? gpart + (size_t)a.nray * ng * a.nvox * NA : a.partv;
+    faces_kernel<Real, NS, DI><<<ctas, 64, 0, st>>>(a, scratch, cta_words, gpart, gpartv, nbox, ng, dxy, maxpass, tol,
+                                                    err, emergent ? 1 : 0);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || emergent || ng == 1) return e;
     int dev = 0, nsm = 0;
@@ -514,14 +611,29 @@ cudaError_t launch_faces(const SweepArgs<Real> &a, Real *scratch, int nbox, long
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const long long n = (long long)a.nray * a.nvox;
     const int blocks = (int)std::min<long long>((n + 255) / 256, 16LL * std::max(1, nsm));
-    faces_group_sum_kernel<Real, NS == 1 ? 2 : 4><<<blocks, 256, 0, st>>>(gpart, ng, a.nvox, a.nray, (Real *)a.part);
-    return cudaGetLastError();
+    faces_group_sum_kernel<Real, NA><<<blocks, 256, 0, st>>>(gpart, ng, a.nvox, a.nray, (Real *)a.part);
+    e = cudaGetLastError();
+    if (e == cudaSuccess && DI) {
+        faces_group_sum_kernel<Real, 1><<<blocks, 256, 0, st>>>(gpartv, ng, a.nvox, a.nray, a.partv);
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
+template <typename Real, int NS>
+cudaError_t launch_faces(const SweepArgs<Real> &a, Real *scratch, int nbox, long long nxy_max, const double *dxy,
+                         int maxpass, int *err, cudaStream_t st, bool emergent)
+{
+    if constexpr (NS == 4) {
+        if (a.dich) return launch_faces_k<Real, 4, true>(a, scratch, nbox, nxy_max, dxy, maxpass, err, st, emergent);
+    }
+    return launch_faces_k<Real, NS, false>(a, scratch, nbox, nxy_max, dxy, maxpass, err, st, emergent);
 }
 
 #define PORTA_FACES_INST(R, N)                                                                              \
     template cudaError_t launch_faces<R, N>(const SweepArgs<R> &, R *, int, long long, const double *, int, int *, \
                                             cudaStream_t, bool);                                                 \
-    template size_t faces_scratch_bytes<R, N>(int, int, int, long long, long long);
+    template size_t faces_scratch_bytes<R, N>(int, int, int, long long, long long, bool);
 PORTA_FACES_INST(float, 1)
 PORTA_FACES_INST(float, 4)
 PORTA_FACES_INST(double, 1)

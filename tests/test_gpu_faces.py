@@ -171,3 +171,42 @@ def test_batched_boxes_with_face_intersections_match_oracle(prec, tol):
         _check(jb, lb, jo.reshape(-1, 6), lo.ravel(), tol)
     assert grazing >= 2
     ctx.close()
+
+
+@pytest.mark.parametrize("prec", [P.PORTA_FP64, P.PORTA_FP32])
+def test_polarized_multilevel_lines_with_face_intersections_match_oracle(prec):
+    """The polarized multilevel lines (dichroism D^2_Q, orientation D^1_Q and S^1_Q,
+    J^1_Q from Stokes V) through the face sweep against the oracle's per-line face
+    sweeps; tolerances of the polarized multilevel parity tests."""
+    from oracle import mlpol
+    atm = synth.multilevel_box(6, 5, 8, seed=2, tau_top=1e-3, tau_bot=1e2)
+    atm["zeta"] = 5e-5
+    atom = synth.multilevel_atom(seed=3, eps_range=(1e-3, 1e-1))
+    tab = mlpol.Tables(atom)
+    x = mlpol.lte_unknowns(tab, atm["kT"])
+    rng = np.random.default_rng(2)
+    rb = mlpol.real_basis(atom)
+    for k, (i, K, Q, part) in enumerate(rb):
+        r00 = x[..., rb.index((i, 0, 0, 0))]
+        if K == 0:
+            x[..., k] *= np.exp(0.2 * rng.normal(size=r00.shape))
+        else:
+            x[..., k] = 0.02 * r00 * rng.normal(size=r00.shape)
+    quad = (2, 4, 5)
+    assert _max_offset(atm, mlpol.line_problem(atm, atom, tab, x, 0, quad, sc_faces=1)) > 2.0
+    c = P.MlContext(atm, atom, *quad, precision=prec, polarized=True)
+    c.set_atmosphere(atm)
+    c.set_unknowns(x)
+    c.set_sc_faces(1)
+    jb, ls = c.ml_formal_solve()
+    oj, ol = mlpol.formal_solve_lines(atm, atom, tab, x, quad, sc_faces=1)
+    gj = np.moveaxis(np.asarray(jb), 0, -2)
+    fp64 = prec == P.PORTA_FP64
+    j00 = oj[..., 0]
+    assert np.max(np.abs(gj[..., 0] - j00) / j00) < (1e-10 if fp64 else 2e-5)
+    assert np.max(np.abs(gj[..., 1:9] - oj[..., 1:9]) / j00[..., None]) < (1e-10 if fp64 else 2e-6)
+    assert np.max(np.abs(oj[..., 1:4]) / j00[..., None]) > 1e-3
+    assert np.max(np.abs(np.moveaxis(ls, 0, -1) - ol)) < (1e-10 if fp64 else 2e-5) * np.max(ol)
+    pj, _ = mlpol.formal_solve_lines(atm, atom, tab, x, quad)
+    assert np.max(np.abs(pj[..., 0] - j00) / j00) > 1e-6
+    c.close()
