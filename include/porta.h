@@ -211,6 +211,18 @@ int porta_set_interpolation(porta_ctx *c, int order);
    sums (porta_accumulate_jkq to host). Drops any captured iteration graph. */
 int porta_set_sc_faces(porta_ctx *c, int on);
 
+/* The J^K_Q formal solution (and the emergent profiles) by the global-memory sweep
+   of porta_set_sc_faces in the plane placement (Sec. 3.1: M and P on the
+   neighbouring horizontal planes at any offset, bilinear and periodic; the same
+   discretization as the shared-memory sweeps), its work planes in device memory
+   instead of a shared-memory ring: on = 1 asks for it; a context whose planes are
+   too wide for every shared-memory launch shape (e.g. the FP64 polarized atom on
+   128-wide planes) takes it by itself on its first formal solution, and on = 0
+   lets it check again. Bilinear stencils only, not with an explicit medium
+   (PORTA_EINVAL); the reverse-mode calls and porta_probe_ray reject it; the face
+   option (porta_set_sc_faces) takes precedence. Drops any captured iteration graph. */
+int porta_set_global_sweep(porta_ctx *c, int on);
+
 /* The family of formal solvers compared on the one-ray sigmoid benchmark of
    Sec. 3.4 (Eqs. 15-18, Fig. 5): constant opacity, z = tau, S(z) = sigma(2, -5, z)
    sigma(-2, 5, z), uniform nodes z_i = -12 + shift + i dtau in [-12, 12], the

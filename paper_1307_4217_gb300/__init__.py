@@ -16,7 +16,7 @@ from .binding import (  # noqa: F401
     porta_see_update, porta_emergent_stokes, porta_probe_ray, porta_launch_info, porta_autotune, porta_eval_coefficients,
     porta_formal_solve_noalloc, porta_run_iterations, porta_iterate_to, PORTA_ENOTCONV, porta_set_device_limit, porta_device_bytes, porta_fma_peak,
     porta_set_freq_range, porta_partial_size, porta_get_partial, porta_set_partial, porta_residual, porta_eval_step, porta_sigmoid_error, porta_mg_set_prolongation, porta_mg_nested,
-    porta_set_interpolation, porta_set_sc_faces, porta_set_explicit_medium,
+    porta_set_interpolation, porta_set_sc_faces, porta_set_global_sweep, porta_set_explicit_medium,
     PORTA_ESCRATCH,
     PORTA_NOALLOC_SCRATCH_BYTES, PORTA_SC_BESSER, PORTA_SC_PARABOLIC, PORTA_SC_LINEAR, PORTA_SC_BEZIER_FB,
     PORTA_SC_CBEZIER,

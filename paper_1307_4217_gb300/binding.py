@@ -113,6 +113,7 @@ _SIGS = {
     "porta_ml_unknowns": (_I, [_P, _P]),
     "porta_ml_set_solve": (_I, [_P, _I]),
     "porta_set_sc_faces": (_I, [_P, _I]),
+    "porta_set_global_sweep": (_I, [_P, _I]),
     "porta_ml_emergent_stokes": (_I, [_P, _I, _I, _P, _P, _P, _I]),
     "porta_ml_set_unknowns": (_I, [_P, _P, _I]),
     "porta_ml_get_unknowns": (_I, [_P, _P, _I]),
@@ -472,6 +473,10 @@ def porta_set_sc_faces(h, on):
     return lib().porta_set_sc_faces(h, on)
 
 
+def porta_set_global_sweep(h, on):
+    return lib().porta_set_global_sweep(h, on)
+
+
 def porta_ml_set_solve(h, mode):
     return lib().porta_ml_set_solve(h, mode)
 
@@ -802,6 +807,12 @@ class Context:
         """1: short characteristics end on the first cell face they cross (vertical
         faces included, Sec. 3.1); 0: on the next horizontal plane."""
         self._check(porta_set_sc_faces(self.h, int(on)))
+
+    def set_global_sweep(self, on):
+        """1: the J^K_Q formal solution by the global-memory sweep in the plane
+        placement (taken by itself where no shared-memory sweep fits); 0: the
+        shared-memory sweeps where they fit."""
+        self._check(porta_set_global_sweep(self.h, int(on)))
 
     def mg_set_prolongation(self, order):
         """Prolongation of the multigrid cycles: 1 tri-linear, 3 tri-cubic-centered."""

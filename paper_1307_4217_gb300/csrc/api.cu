@@ -152,7 +152,10 @@ int nl_of(int model) { return model == PORTA_MODEL_TWOLEVEL_UNPOL ? 1 : 6; }
 // only the general sweep (sweep.cu) implements, or a plane is too wide for its
 // shared memory (then the general sweep, which needs less per frequency, runs).
 // (and the biquadratic stencils, which only the general sweep has)
-bool use_jk(const porta_ctx *c) { return c->d_dich == nullptr && c->jk_fits && c->interp != 2 && !c->sc_faces; }
+bool use_jk(const porta_ctx *c)
+{
+    return c->d_dich == nullptr && c->jk_fits && c->interp != 2 && !c->sc_faces && !c->gsweep;
+}
 
 // The J^K_Q sweep sums an FP32 formal solution into fixed-point accumulators;
 // an FP64 one keeps per-ray partial integrals summed in ray order in FP64 (a
@@ -257,8 +260,33 @@ std::vector<double> faces_cell_sizes(const porta_ctx *c)
 // Device buffers of the J^K_Q formal solution, allocated on first use (before
 // any graph capture): the fixed-point sums of the J^K_Q sweep, or the per-ray
 // partial integrals of the general sweep.
+// whether a shared-memory sweep has some launch shape for this context's planes
+static bool smem_sweep_fits(porta_ctx *c)
+{
+    LaunchCfg cfg{};
+    const int n = c->nbox * c->nray;
+    int rc;
+    if (c->precision == PORTA_FP32)
+        rc = c->ns == 1 ? choose_launch<float, 1>(c, cfg, 0, 0, n, use_jk(c), jnu(c))
+                        : choose_launch<float, 4>(c, cfg, 0, 0, n, use_jk(c), jnu(c));
+    else
+        rc = c->ns == 1 ? choose_launch<double, 1>(c, cfg, 0, 0, n, use_jk(c), jnu(c))
+                        : choose_launch<double, 4>(c, cfg, 0, 0, n, use_jk(c), jnu(c));
+    return rc == 0;
+}
+
+// planes too wide for the shared-memory ring: the global-memory sweep (decided on
+// the first formal solution's buffers, before any graph capture)
+void check_global_sweep(porta_ctx *c)
+{
+    if (c->gsweep_checked) return;
+    c->gsweep_checked = true;
+    if (!c->sc_faces && !c->gsweep && c->d_kexpl == nullptr && c->interp != 2 && !smem_sweep_fits(c)) c->gsweep = 2;
+}
+
 cudaError_t ensure_sweep_buffers(porta_ctx *c)
 {
+    check_global_sweep(c);
     if (jfixed(c)) {
         cudaError_t e = cudaSuccess;
         if (!c->d_jacc) e = pmalloc(&c->d_jacc, (size_t)(c->nj + 1) * c->nvox * sizeof(unsigned long long));
@@ -270,7 +298,7 @@ cudaError_t ensure_sweep_buffers(porta_ctx *c)
     // polarized lines of a multilevel atom: the per-ray integrals of Stokes V (J^1_Q)
     if (e == cudaSuccess && c->d_dich && !c->d_partv) e = pmalloc(&c->d_partv, (size_t)c->nray * c->nvox * c->rsz);
     // short characteristics on cell faces: the work planes and per-group partials
-    if (e == cudaSuccess && c->sc_faces) {
+    if (e == cudaSuccess && (c->sc_faces || c->gsweep)) {
         const long long nxy = faces_nxy_max(c);
         const size_t need =
             c->precision == PORTA_FP32
@@ -327,7 +355,7 @@ cudaError_t finalize_jkq(porta_ctx *c)
 // the fixed-point sums' overflow flag (reads device memory: synchronizes the stream)
 int check_jacc(porta_ctx *c)
 {
-    if (!jfixed(c) && !c->sc_faces) return PORTA_OK;
+    if (!jfixed(c) && !c->sc_faces && !c->gsweep) return PORTA_OK;
     int flag = 0;
     CK(cudaMemcpyAsync(&flag, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
@@ -391,9 +419,10 @@ cudaError_t sweep_jkq(porta_ctx *c, SweepArgs<Real> a, LaunchCfg cfg, const int 
     return e;
 }
 
-// the formal solution with short characteristics on the first cell face crossed
+// the formal solution with short characteristics on the first cell face crossed,
+// or (planes) the plane placement by the same global-memory sweep
 template <typename Real>
-int faces_solve_t(porta_ctx *c)
+int faces_solve_t(porta_ctx *c, bool planes)
 {
     cudaError_t e = ensure_sweep_buffers(c);   // (with the face work planes)
     const long long nxy = faces_nxy_max(c);
@@ -403,8 +432,10 @@ int faces_solve_t(porta_ctx *c)
     e = cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
     const double *dxy = (const double *)c->d_fdxy;
     if (e == cudaSuccess)
-        e = c->ns == 1 ? launch_faces<Real, 1>(a, (Real *)c->d_faces, c->nbox, nxy, dxy, 100000, c->d_err, c->stream)
-                       : launch_faces<Real, 4>(a, (Real *)c->d_faces, c->nbox, nxy, dxy, 100000, c->d_err, c->stream);
+        e = c->ns == 1 ? launch_faces<Real, 1>(a, (Real *)c->d_faces, c->nbox, nxy, dxy, 100000, c->d_err, c->stream,
+                                               false, planes)
+                       : launch_faces<Real, 4>(a, (Real *)c->d_faces, c->nbox, nxy, dxy, 100000, c->d_err, c->stream,
+                                               false, planes);
     if (e != cudaSuccess) return fail(c, PORTA_ECUDA, std::string("face sweep: ") + cudaGetErrorString(e));
     return PORTA_OK;
 }
@@ -413,9 +444,9 @@ template <typename Real>
 int formal_solve_t(porta_ctx *c, int probe_ray, Real *probe, Real *probe_ls)
 {
     if (c->d_kexpl) return fail(c, PORTA_EINVAL, "formal solution: an explicit medium has emergent profiles only");
-    if (c->sc_faces) {
-        if (probe_ray >= 0) return fail(c, PORTA_EINVAL, "probe ray: not with face intersections");
-        return faces_solve_t<Real>(c);
+    if (c->sc_faces || c->gsweep) {
+        if (probe_ray >= 0) return fail(c, PORTA_EINVAL, "probe ray: not with the global-memory sweep");
+        return faces_solve_t<Real>(c, !c->sc_faces);
     }
     SweepArgs<Real> a = jkq_args<Real>(c);
     a.probe_ray = probe_ray;
@@ -424,7 +455,15 @@ int formal_solve_t(porta_ctx *c, int probe_ray, Real *probe, Real *probe_ls)
     LaunchCfg cfg{};
     int rc = c->ns == 1 ? choose_launch<Real, 1>(c, cfg, c->opt_cluster, c->opt_nu_group, a.nitems, use_jk(c), jnu(c))
                         : choose_launch<Real, 4>(c, cfg, c->opt_cluster, c->opt_nu_group, a.nitems, use_jk(c), jnu(c));
-    if (rc) return fail(c, rc, "no sweep launch shape fits this grid (shared memory / cluster limits)");
+    if (rc) {
+        // planes too wide for the shared-memory ring: the global-memory sweep (a
+        // forced shape that does not fit is an error)
+        if (probe_ray >= 0 || smem_sweep_fits(c))
+            return fail(c, rc, "no sweep launch shape fits this grid (shared memory / cluster limits)");
+        c->gsweep = 2;
+        c->gsweep_checked = true;
+        return faces_solve_t<Real>(c, true);
+    }
     shape_args<Real>(c, a, cfg, use_jk(c));
     cudaError_t e = ensure_sweep_buffers(c);
     if (e != cudaSuccess) return fail(c, PORTA_ENOMEM, std::string("formal solution buffers: ") + cudaGetErrorString(e));
@@ -844,8 +883,14 @@ int create_impl(int nbox, const porta_grid *grids, const porta_atom *at, const p
             if (jk) c->jk_fits = r2 == PORTA_OK;
         }
         if (rc == PORTA_OK && r2 != PORTA_OK) {
-            rc = PORTA_EINVAL;
-            c->err = "no sweep launch shape fits this grid (nx too large for shared memory)";
+            if (c->opt_cluster > 0 || c->opt_nu_group > 0) {
+                rc = PORTA_EINVAL;
+                c->err = "the forced sweep launch shape does not fit this grid (shared memory / cluster limits)";
+            } else {
+                // planes too wide for every shared-memory ring: the global-memory sweep
+                c->gsweep = 2;
+                c->gsweep_checked = true;
+            }
         }
     }
     if (rc != PORTA_OK) {
@@ -1413,6 +1458,19 @@ int porta_set_explicit_medium(porta_ctx *c, const double *kexpl, const double *s
     return rc;
 }
 
+int porta_set_global_sweep(porta_ctx *c, int on)
+{
+    if (!c) return PORTA_EINVAL;
+    if (on != 0 && on != 1) return fail(c, PORTA_EINVAL, "set_global_sweep: 0 or 1");
+    if (on && (c->d_kexpl || c->interp == 2))
+        return fail(c, PORTA_EINVAL, "set_global_sweep: bilinear stencils only, and not with an explicit medium");
+    c->gsweep = on;
+    c->gsweep_checked = on != 0;           // off: the shared-memory shapes are checked again
+    c->have_fs = c->have_jkq = false;
+    drop_graph(c);
+    return PORTA_OK;
+}
+
 int porta_set_sc_faces(porta_ctx *c, int on)
 {
     if (!c) return PORTA_EINVAL;
@@ -1434,7 +1492,8 @@ int porta_set_interpolation(porta_ctx *c, int order)
         return fail(c, PORTA_EINVAL, "set_interpolation: the biquadratic stencils have no dichroism (multilevel lines)");
     if (order == 2 && min_ny(c) < 2) return fail(c, PORTA_EINVAL, "set_interpolation: biquadratic needs ny >= 2");
     if (order == 2 && c->d_kexpl) return fail(c, PORTA_EINVAL, "set_interpolation: explicit media are bilinear");
-    if (order == 2 && c->sc_faces) return fail(c, PORTA_EINVAL, "set_interpolation: face intersections are bilinear");
+    if (order == 2 && (c->sc_faces || c->gsweep))
+        return fail(c, PORTA_EINVAL, "set_interpolation: the global-memory sweep (face intersections) is bilinear");
     if (order == c->interp) return PORTA_OK;
     c->interp = order;
     // an autotuned shape of the other stencil need not fit: back to porta_opts' choice

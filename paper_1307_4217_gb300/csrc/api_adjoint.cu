@@ -124,8 +124,10 @@ int emergent_t(porta_ctx *c, int ndir, const double *mu, const double *chi, doub
         a.geom = dg;
         a.rays = dr;
         a.out = dout;
-        if (c->sc_faces) {
-            // short characteristics on cell faces (faces.cu), its own work buffer
+        check_global_sweep(c);
+        if (c->sc_faces || c->gsweep) {
+            // short characteristics on cell faces, or the plane placement of the
+            // global-memory sweep (faces.cu), its own work buffer
             a.nray = ndir;
             const BoxDev &hb0 = c->boxes[box];
             const long long nxy = (long long)hb0.nx * hb0.ny;
@@ -138,8 +140,8 @@ int emergent_t(porta_ctx *c, int ndir, const double *mu, const double *chi, doub
             if (e == cudaSuccess) e = cudaMemcpyAsync(ddxy, dxy, sizeof(dxy), cudaMemcpyHostToDevice, c->stream);
             if (e == cudaSuccess) e = cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
             if (e == cudaSuccess)
-                e = c->ns == 1 ? launch_faces<Real, 1>(a, ws, 1, nxy, ddxy, 100000, c->d_err, c->stream, true)
-                               : launch_faces<Real, 4>(a, ws, 1, nxy, ddxy, 100000, c->d_err, c->stream, true);
+                e = c->ns == 1 ? launch_faces<Real, 1>(a, ws, 1, nxy, ddxy, 100000, c->d_err, c->stream, true, !c->sc_faces)
+                               : launch_faces<Real, 4>(a, ws, 1, nxy, ddxy, 100000, c->d_err, c->stream, true, !c->sc_faces);
             int flag = 0;
             if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
             if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -667,7 +669,7 @@ int porta_emergent_stokes(porta_ctx *c, int ndir, const double *mu, const double
 int porta_emergent_vjp(porta_ctx *c, int ndir, const double *mu, const double *chi, const double *grad_out,
                        double *out, double *g_chi, double *g_e, double *g_b, int where)
 {
-    if (c && (c->interp == 2 || c->d_kexpl || c->sc_faces))
+    if (c && (c->interp == 2 || c->d_kexpl || c->sc_faces || c->gsweep))
         return fail(c, PORTA_EINVAL, "reverse mode: bilinear interpolation on the horizontal planes, two-level media only");
     if (!c) return PORTA_EINVAL;
     if (ndir < 1 || !mu || !chi || !grad_out || !g_chi || !g_e || (c->ns > 1 && !g_b) ||
@@ -771,7 +773,7 @@ int porta_set_tape_limit(porta_ctx *c, long long bytes)
 int porta_iterate_vjp(porta_ctx *c, int ndir, const double *mu, const double *chi, const double *grad_out, double *out,
                       double *g_chi, double *g_f, double *g_b, int where)
 {
-    if (c && (c->interp == 2 || c->d_kexpl || c->sc_faces))
+    if (c && (c->interp == 2 || c->d_kexpl || c->sc_faces || c->gsweep))
         return fail(c, PORTA_EINVAL, "reverse mode: bilinear interpolation on the horizontal planes, two-level media only");
     if (!c) return PORTA_EINVAL;
     if (ndir < 1 || !mu || !chi || !grad_out || !g_chi || !g_f || (c->ns > 1 && !g_b) ||

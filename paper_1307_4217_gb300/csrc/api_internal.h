@@ -68,6 +68,8 @@ void gauss_legendre(int n, double *x, double *w);
 
 // drops the context's captured Jacobi-iteration graph
 void drop_graph(porta_ctx *c);
+// set c->gsweep = 2 (the global-memory sweep) once, where no shared-memory sweep fits
+void check_global_sweep(porta_ctx *c);
 
 inline long long wrapll(long long a, long long n)
 {

@@ -64,12 +64,13 @@ struct Sten {
 __device__ __forceinline__ int pmod(int i, int n) { return ((i % n) + n) % n; }
 
 template <typename Real>
-__device__ __forceinline__ Sten<Real> make_sten(int nx, int ny, double fx, double fy, double ds)
+__device__ __forceinline__ Sten<Real> make_sten(int nx, int ny, double fx, double fy, double ds, bool planes)
 {
     Sten<Real> st;
     int di[4], dj[4];
     double w[4], s = 1.0;
-    st.vert = fabs(fx) > 1.0 || fabs(fy) > 1.0;
+    // planes: M and P on the neighbouring horizontal planes at any offset (bilinear, periodic)
+    st.vert = !planes && (fabs(fx) > 1.0 || fabs(fy) > 1.0);
     st.xface = fabs(fx) >= fabs(fy);
     st.step = (st.xface ? fx : fy) > 0 ? -1 : 1;
     if (st.vert) {
@@ -311,7 +312,7 @@ __device__ __forceinline__ void delo_step_arrow(const Real IM[4], const Real eM[
 template <typename Real, int NS, bool DI>
 __global__ void __launch_bounds__(64, sizeof(Real) == 4 ? 8 : 3) faces_kernel(const SweepArgs<Real> a, Real *scratch, long long cta_words,
                                                   Real *gpart, Real *gpartv, int nbox, int ngroups, const double *dxy,
-                                                  int maxpass, Real tol, int *err, int emergent)
+                                                  int maxpass, Real tol, int *err, int emergent, int planes)
 {
     using C = CW<NS, DI>;
     constexpr int NC = C::n;                      // coefficient words per node
@@ -363,8 +364,10 @@ __global__ void __launch_bounds__(64, sizeof(Real) == 4 ? 8 : 3) faces_kernel(co
                     const bool has_p = q + 1 < nz;
                     const int kd = has_p ? G[q + 1].kz : k;
                     const double dsM = (double)G[q].ds, dsP = has_p ? (double)G[q + 1].ds : 0.0;
-                    const Sten<Real> sm = make_sten<Real>(nx, ny, -dsM * (double)ray.ox / dx, -dsM * (double)ray.oy / dy, dsM);
-                    const Sten<Real> sp = make_sten<Real>(nx, ny, dsP * (double)ray.ox / dx, dsP * (double)ray.oy / dy, dsP);
+                    const Sten<Real> sm =
+                        make_sten<Real>(nx, ny, -dsM * (double)ray.ox / dx, -dsM * (double)ray.oy / dy, dsM, planes != 0);
+                    const Sten<Real> sp =
+                        make_sten<Real>(nx, ny, dsP * (double)ray.ox / dx, dsP * (double)ray.oy / dy, dsP, planes != 0);
                     const bool vertP = has_p && sp.vert;
                     // the finished plane becomes the upwind one; the coefficients of
                     // ku and k are those of the previous step's k and kd
@@ -593,7 +596,7 @@ size_t faces_scratch_bytes(int nbox, int nray, int nnu, long long nxy_max, long 
 
 template <typename Real, int NS, bool DI>
 static cudaError_t launch_faces_k(const SweepArgs<Real> &a, Real *scratch, int nbox, long long nxy_max,
-                                  const double *dxy, int maxpass, int *err, cudaStream_t st, bool emergent)
+                                  const double *dxy, int maxpass, int *err, cudaStream_t st, bool emergent, bool planes)
 {
     const Real tol = sizeof(Real) == 8 ? Real(1e-15) : Real(2e-7);
     const int ng = faces_groups(nbox, a.nray, a.nnu);
@@ -603,7 +606,7 @@ static cudaError_t launch_faces_k(const SweepArgs<Real> &a, Real *scratch, int n
     Real *gpart = ng > 1 ? scratch + (size_t)ctas * cta_words : (Real *)a.part;
     Real *gpartv = ng > 1 ? gpart + (size_t)a.nray * ng * a.nvox * NA : a.partv;
     faces_kernel<Real, NS, DI><<<ctas, 64, 0, st>>>(a, scratch, cta_words, gpart, gpartv, nbox, ng, dxy, maxpass, tol,
-                                                    err, emergent ? 1 : 0);
+                                                    err, emergent ? 1 : 0, planes ? 1 : 0);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || emergent || ng == 1) return e;
     int dev = 0, nsm = 0;
@@ -622,17 +625,18 @@ static cudaError_t launch_faces_k(const SweepArgs<Real> &a, Real *scratch, int n
 
 template <typename Real, int NS>
 cudaError_t launch_faces(const SweepArgs<Real> &a, Real *scratch, int nbox, long long nxy_max, const double *dxy,
-                         int maxpass, int *err, cudaStream_t st, bool emergent)
+                         int maxpass, int *err, cudaStream_t st, bool emergent, bool planes)
 {
     if constexpr (NS == 4) {
-        if (a.dich) return launch_faces_k<Real, 4, true>(a, scratch, nbox, nxy_max, dxy, maxpass, err, st, emergent);
+        if (a.dich)
+            return launch_faces_k<Real, 4, true>(a, scratch, nbox, nxy_max, dxy, maxpass, err, st, emergent, planes);
     }
-    return launch_faces_k<Real, NS, false>(a, scratch, nbox, nxy_max, dxy, maxpass, err, st, emergent);
+    return launch_faces_k<Real, NS, false>(a, scratch, nbox, nxy_max, dxy, maxpass, err, st, emergent, planes);
 }
 
 #define PORTA_FACES_INST(R, N)                                                                              \
     template cudaError_t launch_faces<R, N>(const SweepArgs<R> &, R *, int, long long, const double *, int, int *, \
-                                            cudaStream_t, bool);                                                 \
+                                            cudaStream_t, bool, bool);                                           \
     template size_t faces_scratch_bytes<R, N>(int, int, int, long long, long long, bool);
 PORTA_FACES_INST(float, 1)
 PORTA_FACES_INST(float, 4)

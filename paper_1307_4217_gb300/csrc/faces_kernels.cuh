@@ -14,10 +14,13 @@ namespace porta {
 // (faces_scratch_bytes; dich: the dichroism variant, used when a.dich is set, with
 // the Stokes-V integrals into a.partv); a plane still changing after maxpass passes sets bit 2
 // of *err. emergent: one box, a.rays are lines of sight (mu > 0) and the top
-// plane's Stokes vectors go to a.out ([dir][nu][y][x][ns], FP64) instead of the sums
+// plane's Stokes vectors go to a.out ([dir][nu][y][x][ns], FP64) instead of the sums.
+// planes: M and P on the neighbouring horizontal planes at any offset (the plane
+// placement of the shared-memory sweeps, here with the work planes in global memory:
+// the sweep for planes too wide for the shared-memory ring)
 template <typename Real, int NS>
 cudaError_t launch_faces(const SweepArgs<Real> &a, Real *scratch, int nbox, long long nxy_max, const double *dxy,
-                         int maxpass, int *err, cudaStream_t st, bool emergent = false);
+                         int maxpass, int *err, cudaStream_t st, bool emergent = false, bool planes = false);
 template <typename Real, int NS>
 size_t faces_scratch_bytes(int nbox, int nray, int nnu, long long nxy_max, long long nvox, bool dich = false);
 

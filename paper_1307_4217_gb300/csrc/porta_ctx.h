@@ -116,6 +116,9 @@ struct porta_ctx {
     int mg_order = 1;               // prolongation: 1 tri-linear, 3 tri-cubic-centered (finest level)
     int interp = 1;                 // interpolation at M and P: 1 bilinear, 2 biquadratic (general sweep)
     int sc_faces = 0;               // 1: M and P on the first cell face crossed (faces.cu, J^K_Q formal solution)
+    int gsweep = 0;                 // J^K_Q formal solution by the global-memory sweep of faces.cu in the plane
+                                    // placement: 1 asked for, 2 where no shared-memory launch shape fits
+    bool gsweep_checked = false;    // whether the shared-memory shapes have been checked
     void *d_faces = nullptr;        // its per-ray plane buffers (allocated on first use)
     void *d_fdxy = nullptr;         // its cell sizes, (dx, dy) per box
     size_t faces_bytes = 0;
