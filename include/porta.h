@@ -155,7 +155,8 @@ int porta_fma_peak(int kind, double seconds, double *tflops, double *total_ms);
    dichroism). PORTA_EINVAL for non-finite inputs or non-positive eta_I, ds. */
 int porta_eval_step(int precision, int n, const double *in, double *out);
 
-/* An explicit medium for the emergent Stokes profiles (porta_emergent_stokes):
+/* An explicit medium for the emergent Stokes profiles (porta_emergent_stokes) and
+   the J^K_Q formal solution:
    the propagation matrix of Eqs. 7-8 with all seven elements, given per voxel as
    kexpl[k][v] = (eta_Q, eta_U, eta_V, rho_Q, rho_U, rho_V)[k] / eta_I (k = 0..5)
    and the source vector sexpl[i][v] = S_i (i = I, Q, U, V), both independent of
@@ -165,8 +166,10 @@ int porta_eval_step(int precision, int n, const double *in, double *out);
    (the general step of porta_eval_step). Arrays of nvox doubles each, host or
    device (where); the library keeps a copy. NULL for either clears the medium
    (the two-level physics of the unknowns again). Polarized two-level single-box
-   contexts with bilinear interpolation only (PORTA_EINVAL otherwise); while an
-   explicit medium is set, the J^K_Q formal solution and the reverse-mode calls
+   contexts with bilinear interpolation only (PORTA_EINVAL otherwise). While an
+   explicit medium is set, porta_formal_solve sweeps it with the global-memory sweep
+   of porta_set_global_sweep (the same seven-element step) and porta_accumulate_jkq
+   returns its J^K_Q and Lambda-bar*; the reverse-mode calls and porta_probe_ray
    return PORTA_EINVAL. */
 int porta_set_explicit_medium(porta_ctx *c, const double *kexpl, const double *sexpl, int where);
 

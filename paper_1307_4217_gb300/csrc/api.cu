@@ -154,7 +154,7 @@ int nl_of(int model) { return model == PORTA_MODEL_TWOLEVEL_UNPOL ? 1 : 6; }
 // (and the biquadratic stencils, which only the general sweep has)
 bool use_jk(const porta_ctx *c)
 {
-    return c->d_dich == nullptr && c->jk_fits && c->interp != 2 && !c->sc_faces && !c->gsweep;
+    return c->d_dich == nullptr && c->d_kexpl == nullptr && c->jk_fits && c->interp != 2 && !c->sc_faces && !c->gsweep;
 }
 
 // The J^K_Q sweep sums an FP32 formal solution into fixed-point accumulators;
@@ -298,14 +298,14 @@ cudaError_t ensure_sweep_buffers(porta_ctx *c)
     // polarized lines of a multilevel atom: the per-ray integrals of Stokes V (J^1_Q)
     if (e == cudaSuccess && c->d_dich && !c->d_partv) e = pmalloc(&c->d_partv, (size_t)c->nray * c->nvox * c->rsz);
     // short characteristics on cell faces: the work planes and per-group partials
-    if (e == cudaSuccess && (c->sc_faces || c->gsweep)) {
+    if (e == cudaSuccess && (c->sc_faces || c->gsweep || c->d_kexpl)) {
         const long long nxy = faces_nxy_max(c);
         const size_t need =
             c->precision == PORTA_FP32
-                ? (c->ns == 1 ? faces_scratch_bytes<float, 1>(c->nbox, c->nray, jnu(c), nxy, c->nvox, c->d_dich != nullptr)
-                              : faces_scratch_bytes<float, 4>(c->nbox, c->nray, jnu(c), nxy, c->nvox, c->d_dich != nullptr))
-                : (c->ns == 1 ? faces_scratch_bytes<double, 1>(c->nbox, c->nray, jnu(c), nxy, c->nvox, c->d_dich != nullptr)
-                              : faces_scratch_bytes<double, 4>(c->nbox, c->nray, jnu(c), nxy, c->nvox, c->d_dich != nullptr));
+                ? (c->ns == 1 ? faces_scratch_bytes<float, 1>(c->nbox, c->nray, jnu(c), nxy, c->nvox, c->d_dich ? 1 : (c->d_kexpl ? 2 : 0))
+                              : faces_scratch_bytes<float, 4>(c->nbox, c->nray, jnu(c), nxy, c->nvox, c->d_dich ? 1 : (c->d_kexpl ? 2 : 0)))
+                : (c->ns == 1 ? faces_scratch_bytes<double, 1>(c->nbox, c->nray, jnu(c), nxy, c->nvox, c->d_dich ? 1 : (c->d_kexpl ? 2 : 0))
+                              : faces_scratch_bytes<double, 4>(c->nbox, c->nray, jnu(c), nxy, c->nvox, c->d_dich ? 1 : (c->d_kexpl ? 2 : 0)));
         if (!c->d_fdxy) {
             const std::vector<double> dxy = faces_cell_sizes(c);
             e = pmalloc(&c->d_fdxy, dxy.size() * sizeof(double));
@@ -355,7 +355,7 @@ cudaError_t finalize_jkq(porta_ctx *c)
 // the fixed-point sums' overflow flag (reads device memory: synchronizes the stream)
 int check_jacc(porta_ctx *c)
 {
-    if (!jfixed(c) && !c->sc_faces && !c->gsweep) return PORTA_OK;
+    if (!jfixed(c) && !c->sc_faces && !c->gsweep && !c->d_kexpl) return PORTA_OK;
     int flag = 0;
     CK(cudaMemcpyAsync(&flag, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
@@ -443,7 +443,11 @@ int faces_solve_t(porta_ctx *c, bool planes)
 template <typename Real>
 int formal_solve_t(porta_ctx *c, int probe_ray, Real *probe, Real *probe_ls)
 {
-    if (c->d_kexpl) return fail(c, PORTA_EINVAL, "formal solution: an explicit medium has emergent profiles only");
+    if (c->d_kexpl) {
+        // an explicit medium: the seven-element step of the global-memory sweep
+        if (probe_ray >= 0) return fail(c, PORTA_EINVAL, "probe ray: not with an explicit medium");
+        return faces_solve_t<Real>(c, true);
+    }
     if (c->sc_faces || c->gsweep) {
         if (probe_ray >= 0) return fail(c, PORTA_EINVAL, "probe ray: not with the global-memory sweep");
         return faces_solve_t<Real>(c, !c->sc_faces);

@@ -134,8 +134,8 @@ int emergent_t(porta_ctx *c, int ndir, const double *mu, const double *chi, doub
             const double dxy[2] = {c->blx[box] / hb0.nx, c->bly[box] / hb0.ny};
             Real *ws = nullptr;
             double *ddxy = nullptr;
-            e = pmalloc((void **)&ws, c->ns == 1 ? faces_scratch_bytes<Real, 1>(1, ndir, c->n_nu, nxy, c->nvox, c->d_dich != nullptr)
-                                                 : faces_scratch_bytes<Real, 4>(1, ndir, c->n_nu, nxy, c->nvox, c->d_dich != nullptr));
+            e = pmalloc((void **)&ws, c->ns == 1 ? faces_scratch_bytes<Real, 1>(1, ndir, c->n_nu, nxy, c->nvox, c->d_dich ? 1 : (c->d_kexpl ? 2 : 0))
+                                                 : faces_scratch_bytes<Real, 4>(1, ndir, c->n_nu, nxy, c->nvox, c->d_dich ? 1 : (c->d_kexpl ? 2 : 0)));
             if (e == cudaSuccess) e = pmalloc((void **)&ddxy, sizeof(dxy));
             if (e == cudaSuccess) e = cudaMemcpyAsync(ddxy, dxy, sizeof(dxy), cudaMemcpyHostToDevice, c->stream);
             if (e == cudaSuccess) e = cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);

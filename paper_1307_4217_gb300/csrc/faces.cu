@@ -167,13 +167,19 @@ __device__ __forceinline__ Real block_max(Real v, Real *red)
     return t;
 }
 
-// Coefficient words per node: eta_I, eta_V (weak-field Zeeman), eps (NS); with the
-// dichroism of a polarized multilevel line (DI): eta_I, eta_Q, eta_U, eta_V, eps (4).
-template <int NS, bool DI>
+// Media of the sweep: the two-level atoms (I-V coupling by the weak-field Zeeman
+// term), a polarized multilevel line (dichroism), or an explicit medium (a general
+// propagation matrix given per voxel).
+enum FaceMedium { FM_PLAIN = 0, FM_DICH = 1, FM_GEN = 2 };
+
+// Coefficient words per node: eta_I, eta_V, eps (NS); with dichroism: eta_I, eta_Q,
+// eta_U, eta_V, eps (4); explicit medium: eta_I, eta_Q, eta_U, eta_V, rho_Q, rho_U,
+// rho_V, eps (4).
+template <int NS, int FM>
 struct CW {
-    static constexpr int n = DI ? 8 : NS + 2;
-    static constexpr int ev = DI ? 3 : 1;        // eta_V
-    static constexpr int eps = DI ? 4 : 2;       // first emission word
+    static constexpr int n = FM == FM_GEN ? 11 : (FM == FM_DICH ? 8 : NS + 2);
+    static constexpr int ev = FM == FM_PLAIN ? 1 : 3;                       // eta_V
+    static constexpr int eps = FM == FM_GEN ? 7 : (FM == FM_DICH ? 4 : 2);  // first emission word
 };
 
 // The line's dichroism and orientation terms at node v for the ray (a polarized
@@ -223,11 +229,12 @@ struct Layout {
 
 // the transfer coefficients of every node of plane k at frequency x, word c of
 // node (i, j) at cw[(c * nxy) + L.at(i, j)] (the nodes read in the atmosphere's order)
-template <typename Real, int NS, bool DI>
+template <typename Real, int NS, int FM>
 __device__ __forceinline__ void plane_coefs(const SweepArgs<Real> &a, const RayDev<Real> &ray, int m, long long base,
                                             const Layout &L, Real x, Real *cw)
 {
-    using C = CW<NS, DI>;
+    using C = CW<NS, FM>;
+    constexpr bool DI = FM == FM_DICH;
     const int nxy = L.nx * L.ny;
     for (int p = threadIdx.x; p < nxy; p += blockDim.x) {
         Node<Real, NS> n = make_node<Real, NS>(a, ray, base + p, m, false);
@@ -237,6 +244,15 @@ __device__ __forceinline__ void plane_coefs(const SweepArgs<Real> &a, const RayD
             w[0] = n.chi * profile_shape(xs);
             w[1] = Real(0);
             w[2] = w[0] * n.S;
+        } else if constexpr (FM == FM_GEN) {
+            // explicit medium: K'/eta_I (eta_Q, eta_U, eta_V, rho_Q, rho_U, rho_V) and S per voxel
+            const long long v = base + p, nv = a.nvox;
+            const Real eI = n.chi * profile_shape(xs);
+            w[0] = eI;
+#pragma unroll
+            for (int k = 0; k < 6; ++k) w[1 + k] = eI * (Real)a.kexpl[k * nv + v];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) w[7 + i] = eI * (Real)a.sexpl[i * nv + v];
         } else {
             Real dq = 0, du = 0, dv = 0, sv = 0;
             if constexpr (DI) dich_terms<Real>(a, ray, base + p, n, dq, du, dv, sv);
@@ -309,12 +325,13 @@ __device__ __forceinline__ void delo_step_arrow(const Real IM[4], const Real eM[
 // repeated until no intensity changes by more than tol of the plane's largest (the
 // first line of a pass reads the last line of the previous one: the periodic chain).
 // (FP32: eight CTAs of 64 threads per SM, i.e. at most 128 registers a thread)
-template <typename Real, int NS, bool DI>
+template <typename Real, int NS, int FM>
 __global__ void __launch_bounds__(64, sizeof(Real) == 4 ? 8 : 3) faces_kernel(const SweepArgs<Real> a, Real *scratch, long long cta_words,
                                                   Real *gpart, Real *gpartv, int nbox, int ngroups, const double *dxy,
                                                   int maxpass, Real tol, int *err, int emergent, int planes)
 {
-    using C = CW<NS, DI>;
+    using C = CW<NS, FM>;
+    constexpr bool DI = FM == FM_DICH;
     constexpr int NC = C::n;                      // coefficient words per node
     __shared__ Real red[2];
     const int fper = (a.nnu + ngroups - 1) / ngroups;
@@ -386,10 +403,10 @@ __global__ void __launch_bounds__(64, sizeof(Real) == 4 ? 8 : 3) faces_kernel(co
                     if (sm.vert)
                         for (long long e = threadIdx.x; e < NS * nxy; e += blockDim.x) Ik[e] = Real(0);
                     if (q == 1) {
-                        plane_coefs<Real, NS, DI>(a, ray, m, B.vox0 + (long long)ku * nxy, L, x, cu);
-                        plane_coefs<Real, NS, DI>(a, ray, m, base, L, x, ck);
+                        plane_coefs<Real, NS, FM>(a, ray, m, B.vox0 + (long long)ku * nxy, L, x, cu);
+                        plane_coefs<Real, NS, FM>(a, ray, m, base, L, x, ck);
                     }
-                    if (has_p) plane_coefs<Real, NS, DI>(a, ray, m, B.vox0 + (long long)kd * nxy, L, x, cd);
+                    if (has_p) plane_coefs<Real, NS, FM>(a, ray, m, B.vox0 + (long long)kd * nxy, L, x, cd);
                     __syncthreads();
                     // one point's update (in place into Ik); returns the change of its Stokes vector
                     auto update = [&](int ix, int jy, Real &chg, Real &mag) {
@@ -453,6 +470,9 @@ __global__ void __launch_bounds__(64, sizeof(Real) == 4 ? 8 : 3) faces_kernel(co
                             ls = co.wo + (has_p ? co.wc : Real(0.5) * co.wc);
                         } else if constexpr (DI) {
                             delo_step_arrow<Real>(IM, eM, eO, etaP, epsP, dM, dP, has_p, IO, ls);
+                        } else if constexpr (FM == FM_GEN) {
+                            // the seven elements of K' (Eqs. 7-8), pivoted elimination
+                            delo_step_general<Real>(IM, eM, eM + 7, eO, eO + 7, etaP, epsP, dM, dP, has_p, IO, ls);
                         } else {
                             delo_step_iv<Real>(IM, eM[0], eM[1], eM + 2, eO[0], eO[1], eO + 2, etaP, epsP, dM, dP, has_p, IO, ls);
                         }
@@ -582,30 +602,31 @@ static int faces_ctas(long long items)
 }
 
 template <typename Real, int NS>
-size_t faces_scratch_bytes(int nbox, int nray, int nnu, long long nxy_max, long long nvox, bool dich)
+size_t faces_scratch_bytes(int nbox, int nray, int nnu, long long nxy_max, long long nvox, int medium)
 {
     const int ng = faces_groups(nbox, nray, nnu);
     const int ctas = faces_ctas((long long)nbox * nray * ng);
-    const bool di = NS == 4 && dich;
-    const int nc = di ? 8 : NS + 2;
+    const bool di = NS == 4 && medium == FM_DICH;
+    const int nc = NS == 4 && medium == FM_GEN ? 11 : (di ? 8 : NS + 2);
     // with one group the items write the per-ray partials directly
     const size_t na = (NS == 1 ? 2 : 4) + (di ? 1 : 0);
     const size_t gpart = ng > 1 ? (size_t)nray * ng * nvox * na : 0;
     return sizeof(Real) * ((size_t)ctas * (2 * NS + 1 + 3 * nc) * nxy_max + gpart);
 }
 
-template <typename Real, int NS, bool DI>
+template <typename Real, int NS, int FM>
 static cudaError_t launch_faces_k(const SweepArgs<Real> &a, Real *scratch, int nbox, long long nxy_max,
                                   const double *dxy, int maxpass, int *err, cudaStream_t st, bool emergent, bool planes)
 {
     const Real tol = sizeof(Real) == 8 ? Real(1e-15) : Real(2e-7);
     const int ng = faces_groups(nbox, a.nray, a.nnu);
     const int ctas = faces_ctas((long long)nbox * a.nray * ng);
-    const long long cta_words = (long long)(2 * NS + 1 + 3 * CW<NS, DI>::n) * nxy_max;
+    constexpr bool DI = FM == FM_DICH;
+    const long long cta_words = (long long)(2 * NS + 1 + 3 * CW<NS, FM>::n) * nxy_max;
     constexpr int NA = NS == 1 ? 2 : 4;
     Real *gpart = ng > 1 ? scratch + (size_t)ctas * cta_words : (Real *)a.part;
     Real *gpartv = ng > 1 ? gpart + (size_t)a.nray * ng * a.nvox * NA : a.partv;
-    faces_kernel<Real, NS, DI><<<ctas, 64, 0, st>>>(a, scratch, cta_words, gpart, gpartv, nbox, ng, dxy, maxpass, tol,
+    faces_kernel<Real, NS, FM><<<ctas, 64, 0, st>>>(a, scratch, cta_words, gpart, gpartv, nbox, ng, dxy, maxpass, tol,
                                                     err, emergent ? 1 : 0, planes ? 1 : 0);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || emergent || ng == 1) return e;
@@ -629,15 +650,17 @@ cudaError_t launch_faces(const SweepArgs<Real> &a, Real *scratch, int nbox, long
 {
     if constexpr (NS == 4) {
         if (a.dich)
-            return launch_faces_k<Real, 4, true>(a, scratch, nbox, nxy_max, dxy, maxpass, err, st, emergent, planes);
+            return launch_faces_k<Real, 4, FM_DICH>(a, scratch, nbox, nxy_max, dxy, maxpass, err, st, emergent, planes);
+        if (a.kexpl)
+            return launch_faces_k<Real, 4, FM_GEN>(a, scratch, nbox, nxy_max, dxy, maxpass, err, st, emergent, planes);
     }
-    return launch_faces_k<Real, NS, false>(a, scratch, nbox, nxy_max, dxy, maxpass, err, st, emergent, planes);
+    return launch_faces_k<Real, NS, FM_PLAIN>(a, scratch, nbox, nxy_max, dxy, maxpass, err, st, emergent, planes);
 }
 
 #define PORTA_FACES_INST(R, N)                                                                              \
     template cudaError_t launch_faces<R, N>(const SweepArgs<R> &, R *, int, long long, const double *, int, int *, \
                                             cudaStream_t, bool, bool);                                           \
-    template size_t faces_scratch_bytes<R, N>(int, int, int, long long, long long, bool);
+    template size_t faces_scratch_bytes<R, N>(int, int, int, long long, long long, int);
 PORTA_FACES_INST(float, 1)
 PORTA_FACES_INST(float, 4)
 PORTA_FACES_INST(double, 1)
