@@ -112,6 +112,8 @@ def args_parse():
     ap.add_argument("--c0", type=int, default=1, help="time the unpolarized 16x16x32 box to convergence (0 skips it)")
     ap.add_argument("--faces", type=int, default=1,
                     help="time the formal solution with short characteristics on the first cell face (0 skips it)")
+    ap.add_argument("--faces-grid", type=int, default=64,
+                    help="box of that section, n^3 (64: the benchmark box; a smaller one for profiling captures)")
     ap.add_argument("--solver-family", type=int, default=1,
                     help="E(dtau) of the Sec. 3.4 solver family on the sigmoid benchmark (0 skips it)")
     ap.add_argument("--peak-seconds", type=float, default=1.0, help="device time per FMA-peak measurement")
@@ -818,25 +820,47 @@ def run_cuda(args):
     # grazing rays: each such plane solved by ordered line sweeps repeated to convergence)
     faces = None
     if args.faces and wl.name == "pol64" and world == 1:
+        fctx, f_updates, f_desc = ctx, wl.updates, wl.desc.split(";")[0]
+        if args.faces_grid != 64:
+            # a smaller box of the same statistics (profiling captures), S^0_0 = B
+            n = args.faces_grid
+            fatm = synth.random_box(n, n, n, seed=0)
+            fctx = P.Context(fatm, P.PORTA_MODEL_TWOLEVEL_HANLE, *wl.quad, precision=P.PORTA_FP32)
+            fctx.set_atmosphere(fatm)
+            frho = np.zeros((n, n, n, 6))
+            frho[..., 0] = fatm["bpl"]
+            fctx.set_rho(frho)
+            fctx.set_stream(stream)
+            f_updates = n ** 3 * (2 * wl.quad[0] * wl.quad[1]) * wl.quad[2]
+            f_desc = f"polarized two-level atom, random box {n}x{n}x{n}, {(2 * wl.quad[0] * wl.quad[1])} rays, {wl.quad[2]} frequencies"
         with torch.cuda.stream(stream):
-            ctx.set_sc_faces(1)
-            ctx.formal_solve()
-            jf, lf = ctx.accumulate_jkq()
+            fctx.set_sc_faces(0)
+            ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            fctx.formal_solve()
+            flush.zero_()
+            ev0[0].record(stream)
+            fctx.formal_solve()
+            ev0[1].record(stream)
+            jp, lp = fctx.accumulate_jkq()
+            p_ms = ev0[0].elapsed_time(ev0[1])
+            fctx.set_sc_faces(1)
+            fctx.formal_solve()
+            jf, lf = fctx.accumulate_jkq()
             evf = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
             flush.zero_()
             evf[0].record(stream)
-            ctx.formal_solve()
+            fctx.formal_solve()
             evf[1].record(stream)
             barrier()
             f_ms = evf[0].elapsed_time(evf[1])
-            ctx.set_sc_faces(0)
-            ctx.formal_solve()
-            jp, lp = ctx.accumulate_jkq()
-        faces = {"workload": wl.desc.split(";")[0] + "; one J^K_Q formal solution, FP32",
-                 "ms": f_ms, "updates_per_s": wl.updates / (f_ms * 1e-3),
-                 "ratio_to_plane_sweep": f_ms / sweep_ms,
+            fctx.set_sc_faces(0)
+        if fctx is not ctx:
+            fctx.close()
+        faces = {"workload": f_desc + "; one J^K_Q formal solution, FP32",
+                 "ms": f_ms, "updates_per_s": f_updates / (f_ms * 1e-3),
+                 "ratio_to_plane_sweep": f_ms / p_ms,
                  "J00_rel_diff_to_plane_placement": float(np.max(np.abs(jf[..., 0] - jp[..., 0]) / np.abs(jp[..., 0]))),
-                 "timing": "CUDA events around one porta_formal_solve with porta_set_sc_faces(1) (L2 flushed)"}
+                 "timing": "CUDA events around one porta_formal_solve with porta_set_sc_faces(1), and one with 0 for the ratio (L2 flushed)"}
 
     # the 256 boxes of uneven size in one persistent launch per sweep (graph replays)
     batch = None
